@@ -1,0 +1,39 @@
+"""Compile the CPU oracle into oracle/_build/liboracle.so.
+
+Test infrastructure only: the oracle is the checker for the CUDA library, never part of it.
+Plain g++ with floating-point contraction off, so that float arithmetic is performed one
+IEEE operation at a time on x86-64 and AArch64 alike.
+"""
+import os
+import subprocess
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+OUT_DIR = os.path.join(HERE, "_build")
+LIB = os.path.join(OUT_DIR, "liboracle.so")
+SOURCES = ["ora_capi.cpp"]
+HEADERS = ["ora_common.hpp", "ora_dsmc.hpp", "ora_lbm.hpp", "ora_mapping.hpp"]
+
+
+def _stale():
+    if not os.path.exists(LIB):
+        return True
+    t = os.path.getmtime(LIB)
+    return any(os.path.getmtime(os.path.join(HERE, f)) > t for f in SOURCES + HEADERS)
+
+
+def build(force=False, verbose=False):
+    if not force and not _stale():
+        return LIB
+    os.makedirs(OUT_DIR, exist_ok=True)
+    cmd = ["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-ffp-contract=off",
+           "-fno-fast-math", "-Wall", "-o", LIB + ".tmp"]
+    cmd += [os.path.join(HERE, s) for s in SOURCES]
+    if verbose:
+        print(" ".join(cmd))
+    subprocess.run(cmd, check=True)
+    os.replace(LIB + ".tmp", LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force=True, verbose=True))

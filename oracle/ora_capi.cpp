@@ -1,0 +1,260 @@
+// Oracle: C entry points for the Python test harness (ctypes).
+//
+// TEST INFRASTRUCTURE ONLY (see ora_common.hpp). Holds one DSMC + LBM state in host memory,
+// in float or double, and exposes the steps of the method one call at a time.
+#include "ora_mapping.hpp"
+
+using namespace ora;
+
+namespace {
+
+struct Handle {
+    int rb = 8;
+    Dsmc<float> df;
+    Lbm<float> lf;
+    Dsmc<double> dd;
+    Lbm<double> ld;
+};
+
+enum ArrayId {
+    A_X = 0, A_Y = 1, A_VX = 2, A_VY = 3, A_VZ = 4, A_CELL_START = 5, A_CRMAX = 6,
+    A_REM = 7, A_NBAR_SUM = 8, A_ACC = 9, A_F = 10,
+};
+
+template <class T>
+int64_t copy_out(const std::vector<T>& v, void* out) {
+    if (out) std::memcpy(out, v.data(), v.size() * sizeof(T));
+    return (int64_t)v.size();
+}
+template <class T>
+int set_in(std::vector<T>& v, const void* in, int64_t n, bool resize) {
+    if (resize) v.resize((size_t)n);
+    if ((int64_t)v.size() != n) return -1;
+    std::memcpy(v.data(), in, (size_t)n * sizeof(T));
+    return 0;
+}
+
+template <class Real>
+int64_t get_impl(Dsmc<Real>& D, Lbm<Real>& B, int which, void* out) {
+    switch (which) {
+        case A_X: return copy_out(D.x, out);
+        case A_Y: return copy_out(D.y, out);
+        case A_VX: return copy_out(D.vx, out);
+        case A_VY: return copy_out(D.vy, out);
+        case A_VZ: return copy_out(D.vz, out);
+        case A_CELL_START: return copy_out(D.cell_start, out);
+        case A_CRMAX: return copy_out(D.crmax, out);
+        case A_REM: return copy_out(D.rem, out);
+        case A_NBAR_SUM: return copy_out(D.nbar_sum, out);
+        case A_ACC: return copy_out(D.acc, out);
+        case A_F: return copy_out(B.f, out);
+    }
+    return -1;
+}
+
+template <class Real>
+int set_impl(Dsmc<Real>& D, Lbm<Real>& B, int which, const void* in, int64_t n) {
+    switch (which) {
+        case A_X: return set_in(D.x, in, n, true);
+        case A_Y: return set_in(D.y, in, n, true);
+        case A_VX: return set_in(D.vx, in, n, true);
+        case A_VY: return set_in(D.vy, in, n, true);
+        case A_VZ: return set_in(D.vz, in, n, true);
+        case A_CELL_START: return set_in(D.cell_start, in, n, false);
+        case A_CRMAX: return set_in(D.crmax, in, n, false);
+        case A_REM: return set_in(D.rem, in, n, false);
+        case A_NBAR_SUM: return set_in(D.nbar_sum, in, n, false);
+        case A_ACC: return set_in(D.acc, in, n, false);
+        case A_F: return set_in(B.f, in, n, false);
+    }
+    return -1;
+}
+
+bool valid(const Params* p) {
+    return p && p->ncx >= 6 && p->ncy >= 1 && (p->lb_ratio == 1 || p->lb_ratio == 2) &&
+           p->ppc >= 1 && (p->lattice == 39 || p->lattice == 19) &&
+           (p->real_bytes == 4 || p->real_bytes == 8) && p->sample_every >= 1 && p->kn > 0.0 &&
+           p->capacity_factor >= 1.0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ora_derive(const Params* p, Derived* out) {
+    if (!valid(p)) return 1;
+    *out = derive(*p);
+    return 0;
+}
+
+void ora_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out, int64_t n) {
+    for (int64_t i = 0; i < n; ++i) {
+        U4 r = philox4x32_10(U4{ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]},
+                             (uint32_t)seed, (uint32_t)(seed >> 32));
+        for (int k = 0; k < 4; ++k) out[4 * i + k] = r[k];
+    }
+}
+
+int ora_lattice(int q, int32_t* e, double* w, double* r) {
+    if (q != 39 && q != 19) return 1;
+    Lattice L = make_lattice(q);
+    for (int a = 0; a < q; ++a) {
+        for (int i = 0; i < 3; ++i) e[3 * a + i] = L.e[a][i];
+        w[a] = L.w[a];
+    }
+    *r = L.r;
+    return 0;
+}
+
+void* ora_create(const Params* p) {
+    if (!valid(p)) return nullptr;
+    Handle* h = new Handle();
+    h->rb = p->real_bytes;
+    if (h->rb == 4) {
+        h->df.init(*p);
+        h->lf.init(*p);
+    } else {
+        h->dd.init(*p);
+        h->ld.init(*p);
+    }
+    return h;
+}
+
+void ora_destroy(void* hv) { delete (Handle*)hv; }
+
+int ora_dsmc_step(void* hv, int n) {
+    Handle* h = (Handle*)hv;
+    for (int i = 0; i < n; ++i) (h->rb == 4) ? h->df.step_once() : h->dd.step_once();
+    return 0;
+}
+
+// One phase of a DSMC step: 0 move + sort, 1 collide, 2 sample + advance the step counter.
+int ora_dsmc_phase(void* hv, int phase) {
+    Handle* h = (Handle*)hv;
+    if (phase < 0 || phase > 2) return 1;
+    if (h->rb == 4) {
+        if (phase == 0) h->df.phase_move_sort();
+        if (phase == 1) h->df.phase_collide();
+        if (phase == 2) h->df.phase_sample_advance();
+    } else {
+        if (phase == 0) h->dd.phase_move_sort();
+        if (phase == 1) h->dd.phase_collide();
+        if (phase == 2) h->dd.phase_sample_advance();
+    }
+    return 0;
+}
+
+int ora_lbm_step(void* hv, int n) {
+    Handle* h = (Handle*)hv;
+    for (int i = 0; i < n; ++i) (h->rb == 4) ? h->lf.step_once() : h->ld.step_once();
+    return 0;
+}
+
+int ora_map_dsmc_to_lbm(void* hv, const int32_t* nodes, int n) {
+    Handle* h = (Handle*)hv;
+    if (h->rb == 4) map_dsmc_to_lbm(h->df, h->lf, nodes, n);
+    else map_dsmc_to_lbm(h->dd, h->ld, nodes, n);
+    return 0;
+}
+
+int ora_map_lbm_to_dsmc(void* hv, const int32_t* cells, int n) {
+    Handle* h = (Handle*)hv;
+    if (h->rb == 4) map_lbm_to_dsmc(h->df, h->lf, cells, n);
+    else map_lbm_to_dsmc(h->dd, h->ld, cells, n);
+    return 0;
+}
+
+int64_t ora_get(void* hv, int which, void* out) {
+    Handle* h = (Handle*)hv;
+    return (h->rb == 4) ? get_impl(h->df, h->lf, which, out) : get_impl(h->dd, h->ld, which, out);
+}
+
+int ora_set(void* hv, int which, const void* in, int64_t n) {
+    Handle* h = (Handle*)hv;
+    return (h->rb == 4) ? set_impl(h->df, h->lf, which, in, n) : set_impl(h->dd, h->ld, which, in, n);
+}
+
+// scalars: [0] step, [1] nsamples, [2] status, [3] ntot
+void ora_scalars(void* hv, uint64_t* out) {
+    Handle* h = (Handle*)hv;
+    if (h->rb == 4) {
+        out[0] = h->df.step; out[1] = h->df.nsamples; out[2] = h->df.status; out[3] = h->df.ntot();
+    } else {
+        out[0] = h->dd.step; out[1] = h->dd.nsamples; out[2] = h->dd.status; out[3] = h->dd.ntot();
+    }
+}
+
+void ora_set_scalars(void* hv, uint64_t step, uint64_t nsamples) {
+    Handle* h = (Handle*)hv;
+    if (h->rb == 4) { h->df.step = step; h->df.nsamples = nsamples; }
+    else { h->dd.step = step; h->dd.nsamples = nsamples; }
+}
+
+void ora_counters(void* hv, uint64_t* out) {
+    Handle* h = (Handle*)hv;
+    const uint64_t* c = (h->rb == 4) ? h->df.counters : h->dd.counters;
+    for (int i = 0; i < C_NUM; ++i) out[i] = c[i];
+}
+
+// One node's collision from streamed populations fs (double), for pins.
+int ora_lbm_collide(const Params* p, const double* fs, double* out) {
+    if (!valid(p)) return 1;
+    Lbm<double> B;
+    B.p = *p;
+    B.d = derive(*p);
+    B.L = make_lattice(p->lattice);
+    B.collide(fs, out);
+    return 0;
+}
+
+// DSMC2LB populations of one node from 20 cumulative sums over S samples.
+int ora_dsmc2lb_node(int q, const double* m, uint64_t S, int ppc, double* out) {
+    if (q != 39 && q != 19) return 1;
+    Lattice L = make_lattice(q);
+    Coeffs a;
+    if (!dsmc_coefficients(m, S, ppc, a)) return 2;
+    for (int k = 0; k < q; ++k) out[k] = L.w[k] * hermite_series(a, L.xi[k].data(), q == 39 ? 3 : 2);
+    return 0;
+}
+
+// Grad coefficients of a population vector: out = [rho, u(3), a2(9), a3(27), M, C].
+int ora_grad_coeffs(int q, const double* f, double* out) {
+    if (q != 39 && q != 19) return 1;
+    Lattice L = make_lattice(q);
+    GradCell g = grad_from_populations(L, f, q == 39 ? 3 : 2);
+    out[0] = g.rho;
+    for (int i = 0; i < 3; ++i) out[1 + i] = g.u[i];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            out[4 + 3 * i + j] = g.ahat.a2[i][j];
+            for (int k = 0; k < 3; ++k) out[13 + 9 * i + 3 * j + k] = g.ahat.a3[i][j][k];
+        }
+    out[40] = g.M;
+    out[41] = g.C;
+    return 0;
+}
+
+// Table 1 sampler applied nsamp times to one population vector (double velocities).
+// info = [attempts, envelope violations, cap hits].
+int ora_grad_sample(int q, const double* f, uint64_t seed, uint32_t cell, uint32_t t,
+                    int64_t nsamp, double* v_out, uint64_t* info) {
+    if (q != 39 && q != 19) return 1;
+    if (nsamp > 0xFFFFFF) return 2;
+    Lattice L = make_lattice(q);
+    const int order = q == 39 ? 3 : 2;
+    GradCell g = grad_from_populations(L, f, order);
+    uint64_t env = 0, att = 0, cap = 0;
+    for (int64_t k = 0; k < nsamp; ++k) {
+        double v[3];
+        int a = grad_sample_one<double>(g, order, seed, cell, t, (uint32_t)k, v, &env);
+        if (a > kMaxL2DAttempts) cap += 1;
+        att += (uint64_t)std::min(a, kMaxL2DAttempts);
+        for (int i = 0; i < 3; ++i) v_out[3 * k + i] = v[i];
+    }
+    info[0] = att;
+    info[1] = env;
+    info[2] = cap;
+    return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,256 @@
+// Oracle: common definitions (parameters, derived constants, Philox, lattices).
+//
+// TEST INFRASTRUCTURE ONLY. This directory is a plain, slow, CPU-only restatement of the
+// DSMC-LBM mapping method of Di Staso, Clercx, Succi and Toschi (arXiv 1512.08042). It exists
+// to check the CUDA library against the paper. Only the test suite, the smoke check and the
+// CPU-baseline leg of the benchmark may load it; the product path never does. It shares no
+// code, header, table or constant generator with the CUDA library.
+//
+// Units (the reading of the paper's Appendix A used throughout):
+//   length   : DSMC cell size (cubic cells, App. A "length scale" L0 = dx_DSMC)
+//   velocity : thermal speed c_th = sqrt(kT/m); the Hermite weight function then has unit
+//              variance (Sec. 2.2, Eq. globalMax with T = 1)
+//   time     : one DSMC step equals one LB step, T0 = (c_s/a) dx_LB with a = c_th
+//              (App. A "time scale", isothermal reading of a)
+//   density  : LB density 1 corresponds to `ppc` particles per DSMC cell
+//              (App. A "mass scale", mass conserved at the coupling sites)
+#pragma once
+#include <array>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+namespace ora {
+
+// ---------------------------------------------------------------------------------------
+// Parameters. Field order is a binary interface with oracle.py (ctypes).
+struct Params {
+    uint32_t abi_version;
+    int32_t ncx;           // DSMC cells across the channel, walls at x = 0 and x = ncx
+    int32_t ncy;           // DSMC cells streamwise, periodic
+    int32_t lb_ratio;      // LB nodes per DSMC cell per axis
+    int32_t ppc;           // particles per cell at initialisation
+    int32_t lattice;       // 39 (D3Q39, Hermite order 3) or 19 (D3Q19, order 2)
+    int32_t real_bytes;    // 4 (float state) or 8 (double state)
+    int32_t sample_every;  // moment sampling cadence in DSMC steps
+    uint64_t seed;
+    double kn;             // Knudsen number based on channel height
+    double ma;             // Mach number of the no-slip centreline velocity, u_max / c_s
+    double crmax_init;     // initial (sigma_T c_r)_max / sigma_T, in c_th units
+    double capacity_factor;
+    double T_K;            // temperature [K], SI reporting only
+    double mass_kg;        // molecular mass [kg], SI reporting only
+};
+
+// Derived constants. Field order is a binary interface with oracle.py.
+struct Derived {
+    double r_lat;     // lattice scale: xi_a = r_lat * e_a in Hermite units (c/c_s)
+    double cs_lat;    // lattice sound speed in lattice units, 1 / r_lat
+    double H_lat;     // LB nodes across the channel
+    double tau;       // BGK relaxation time, Eq. tau
+    double dt;        // DSMC (= LB) time step in cell / c_th units
+    double lambda;    // hard-sphere mean free path in DSMC cells, lambda = Kn * H
+    double coll_dt;   // F_N sigma_T dt / V_c in the NTC count, Eq. collisionnumber
+    double g_step;    // body-force velocity increment per step (Hermite units)
+    double c_th_ms;   // sqrt(k T / m) in m/s
+    int64_t ncells, nx, ny, nnodes, capacity;
+    int32_t q, order;
+};
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kBoltzmann = 1.380649e-23;
+
+// Eq. tau for the lattice relaxation time; Eq. MFP read in DSMC cell units; the NTC factor
+// of Eq. collisionnumber with F_N sigma_T / V_c = 1 / (sqrt(2) lambda ppc) because the
+// number density is ppc F_N / V_c. The force is fixed by the no-slip parabola
+// u_max = g H^2 / (8 nu) at u_max = Ma c_s (Sec. 3.1), nu = (tau - 1/2) c_s^2.
+inline Derived derive(const Params& p) {
+    Derived d{};
+    d.r_lat = (p.lattice == 39) ? std::sqrt(1.5) : std::sqrt(3.0);
+    d.cs_lat = 1.0 / d.r_lat;
+    d.H_lat = (double)p.ncx * (double)p.lb_ratio;
+    d.tau = std::sqrt(kPi / 8.0) * d.r_lat * p.kn * d.H_lat + 0.5;
+    d.dt = d.cs_lat / (double)p.lb_ratio;
+    d.lambda = p.kn * (double)p.ncx;
+    d.coll_dt = d.dt / (std::sqrt(2.0) * d.lambda * (double)p.ppc);
+    d.g_step = 8.0 * (d.tau - 0.5) * p.ma * d.cs_lat * d.cs_lat / (d.H_lat * d.H_lat);
+    d.c_th_ms = std::sqrt(kBoltzmann * p.T_K / p.mass_kg);
+    d.ncells = (int64_t)p.ncx * p.ncy;
+    d.nx = (int64_t)p.ncx * p.lb_ratio;
+    d.ny = (int64_t)p.ncy * p.lb_ratio;
+    d.nnodes = d.nx * d.ny;
+    d.capacity = (int64_t)std::ceil(p.capacity_factor * (double)d.ncells * (double)p.ppc);
+    d.q = p.lattice;
+    d.order = (p.lattice == 39) ? 3 : 2;
+    return d;
+}
+
+// ---------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3",
+// SC'11): ten rounds of two 32x32->64 multiplies; the key is bumped by the Weyl constants
+// between rounds.
+using U4 = std::array<uint32_t, 4>;
+
+inline U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
+    const uint64_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = M0 * (uint64_t)c[0];
+        uint64_t p1 = M1 * (uint64_t)c[2];
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        c = U4{hi1 ^ c[1] ^ k0, lo1, hi0 ^ c[3] ^ k1, lo0};
+    }
+    return c;
+}
+
+// Purpose tags of the counter layout (entity, step, tag << 24 | sub-index, block).
+enum Tag : uint32_t {
+    TAG_INIT_POS = 1,
+    TAG_INIT_VEL = 2,
+    TAG_WALL = 3,
+    TAG_NTC_PAIR = 4,
+    TAG_NTC_SCAT = 5,
+    TAG_L2D_VEL = 6,
+    TAG_L2D_POS = 7,
+    TAG_L2D_ROUND = 8,
+};
+
+inline U4 draw(uint64_t seed, uint32_t entity, uint32_t step, uint32_t tag, uint32_t sub,
+               uint32_t block) {
+    return philox4x32_10(U4{entity, step, (tag << 24) | (sub & 0xFFFFFFu), block},
+                         (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+// Uniform on [0,1) with 24 bits, exact in float.
+inline float u01f(uint32_t r) { return (float)(r >> 8) * 0x1p-24f; }
+// Uniform on (0,1), for logarithms.
+inline double u01open(uint32_t r) { return ((double)r + 0.5) * 0x1p-32; }
+// Uniform on [0,1) with 32 bits.
+inline double u01d(uint32_t r) { return (double)r * 0x1p-32; }
+// Integer uniform on [0, n) by the 64-bit multiply-shift map.
+inline uint32_t uindex(uint32_t r, uint32_t n) { return (uint32_t)(((uint64_t)r * n) >> 32); }
+
+// Box-Muller transform (Box and Muller 1958), the sampler Table 1 step 4 names.
+inline void box_muller(uint32_t r1, uint32_t r2, double& n1, double& n2) {
+    double rad = std::sqrt(-2.0 * std::log(u01open(r1)));
+    double th = 6.283185307179586 * u01open(r2);
+    n1 = rad * std::cos(th);
+    n2 = rad * std::sin(th);
+}
+
+// ---------------------------------------------------------------------------------------
+// Lattices. The paper names D3Q19 and the 39-speed sixth-order-isotropic Gauss-Hermite set
+// (Sec. 1, Sec. 3.1) without listing them; these are the Shan-Yuan-Chen (2006) sets, pinned
+// by the quadrature-degree tests. Row order is the population layout of the library.
+struct Lattice {
+    int q;
+    double r;
+    std::vector<std::array<int, 3>> e;
+    std::vector<double> w;
+    std::vector<std::array<double, 3>> xi;  // r * e, Hermite units
+};
+
+inline Lattice make_lattice(int q) {
+    Lattice L;
+    L.q = q;
+    auto add = [&](int x, int y, int z, double w) {
+        L.e.push_back({x, y, z});
+        L.w.push_back(w);
+    };
+    if (q == 39) {
+        L.r = std::sqrt(1.5);
+        add(0, 0, 0, 1.0 / 12.0);
+        const int s1[6][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
+        for (auto& v : s1) add(v[0], v[1], v[2], 1.0 / 12.0);
+        const int s3[8][3] = {{1, 1, 1},  {-1, 1, 1},  {1, -1, 1},  {-1, -1, 1},
+                              {1, 1, -1}, {-1, 1, -1}, {1, -1, -1}, {-1, -1, -1}};
+        for (auto& v : s3) add(v[0], v[1], v[2], 1.0 / 27.0);
+        for (auto& v : s1) add(2 * v[0], 2 * v[1], 2 * v[2], 2.0 / 135.0);
+        const int s8[12][3] = {{2, 2, 0},  {-2, 2, 0},  {2, -2, 0},  {-2, -2, 0},
+                               {2, 0, 2},  {-2, 0, 2},  {2, 0, -2},  {-2, 0, -2},
+                               {0, 2, 2},  {0, -2, 2},  {0, 2, -2},  {0, -2, -2}};
+        for (auto& v : s8) add(v[0], v[1], v[2], 1.0 / 432.0);
+        for (auto& v : s1) add(3 * v[0], 3 * v[1], 3 * v[2], 1.0 / 1620.0);
+    } else {
+        L.r = std::sqrt(3.0);
+        add(0, 0, 0, 1.0 / 3.0);
+        const int s1[6][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
+        for (auto& v : s1) add(v[0], v[1], v[2], 1.0 / 18.0);
+        const int s2[12][3] = {{1, 1, 0},  {-1, 1, 0},  {1, -1, 0},  {-1, -1, 0},
+                               {1, 0, 1},  {-1, 0, 1},  {1, 0, -1},  {-1, 0, -1},
+                               {0, 1, 1},  {0, -1, 1},  {0, 1, -1},  {0, -1, -1}};
+        for (auto& v : s2) add(v[0], v[1], v[2], 1.0 / 36.0);
+    }
+    for (auto& e : L.e) L.xi.push_back({L.r * e[0], L.r * e[1], L.r * e[2]});
+    return L;
+}
+
+// ---------------------------------------------------------------------------------------
+// Hermite polynomials (Grad 1949; Shan, Yuan, Chen 2006), Sec. 2 Eq. series:
+// H0 = 1, H1_i = xi_i, H2_ij = xi_i xi_j - d_ij, H3_ijk = xi_i xi_j xi_k - xi_i d_jk
+// - xi_j d_ik - xi_k d_ij.
+inline double kd(int i, int j) { return i == j ? 1.0 : 0.0; }
+inline double H2(const double* x, int i, int j) { return x[i] * x[j] - kd(i, j); }
+inline double H3(const double* x, int i, int j, int k) {
+    return x[i] * x[j] * x[k] - x[i] * kd(j, k) - x[j] * kd(i, k) - x[k] * kd(i, j);
+}
+
+// Full tensors, no symmetry packing.
+struct Coeffs {
+    double a0;
+    double a1[3];
+    double a2[3][3];
+    double a3[3][3][3];
+};
+
+// Truncated series of Eq. seriestrunc divided by the weight: sum_{n<=N} a^(n) H^(n)(xi) / n!
+inline double hermite_series(const Coeffs& a, const double* x, int order) {
+    double s = a.a0;
+    for (int i = 0; i < 3; ++i) s += a.a1[i] * x[i];
+    double s2 = 0.0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) s2 += a.a2[i][j] * H2(x, i, j);
+    s += 0.5 * s2;
+    if (order >= 3) {
+        double s3 = 0.0;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                for (int k = 0; k < 3; ++k) s3 += a.a3[i][j][k] * H3(x, i, j, k);
+        s += s3 / 6.0;
+    }
+    return s;
+}
+
+// Eq. coefficients_LBM: a^(n) = sum_a f_a H^(n)(xi_a).
+inline Coeffs project(const Lattice& L, const double* f) {
+    Coeffs a{};
+    for (int q = 0; q < L.q; ++q) {
+        const double* x = L.xi[q].data();
+        a.a0 += f[q];
+        for (int i = 0; i < 3; ++i) {
+            a.a1[i] += f[q] * x[i];
+            for (int j = 0; j < 3; ++j) {
+                a.a2[i][j] += f[q] * H2(x, i, j);
+                for (int k = 0; k < 3; ++k) a.a3[i][j][k] += f[q] * H3(x, i, j, k);
+            }
+        }
+    }
+    return a;
+}
+
+// Status bits of the sticky status word (same meanings as the library's).
+enum StatusBit : uint32_t {
+    ST_CAPACITY = 1u << 0,
+    ST_BOUNCE_CAP = 1u << 1,
+    ST_SCATTER_CAP = 1u << 2,
+    ST_SAMPLING_CAP = 1u << 3,
+    ST_CELL_OVERFLOW = 1u << 4,
+    ST_BAD_INPUT = 1u << 5,
+};
+
+}  // namespace ora

@@ -1,0 +1,292 @@
+// Oracle: DSMC particle step (move with diffuse isothermal walls, cell sort, NTC hard-sphere
+// collisions, per-cell Hermite-moment sampling).
+//
+// TEST INFRASTRUCTURE ONLY (see ora_common.hpp). Plain loops in the order Bird's DSMC step
+// takes them (move -> index -> collide -> sample), which the paper adopts in Sec. 5
+// (Eq. collisionnumber and the NTC scheme it names). With Real = float the arithmetic is the
+// float arithmetic the GPU state uses, step for step, so that cell keys, the sort
+// permutation and the selected collision pairs can be compared bit for bit; transcendental
+// draws (Box-Muller, wall re-emission) are evaluated in double and rounded.
+#pragma once
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
+#include "ora_common.hpp"
+
+namespace ora {
+
+constexpr int kMaxBounces = 8;        // wall interactions per particle per step
+constexpr int kMaxScatterBlocks = 16; // Marsaglia attempts = 2 per block
+constexpr uint32_t kDeadKey = 0xFFFFFFFFu;
+constexpr int kNumMoments = 20;
+
+enum Counter {
+    C_WALL_HITS = 0,
+    C_CANDIDATES = 1,
+    C_COLLISIONS = 2,
+    C_CREATED = 3,
+    C_DELETED = 4,
+    C_L2D_ATTEMPTS = 5,
+    C_ENVELOPE = 6,
+    C_BOUNCE_CAP = 7,
+    C_NUM = 16,
+};
+
+template <class Real>
+struct Dsmc {
+    Params p;
+    Derived d;
+    // Particle state, ordered by cell after every step (Sec. 5, "per cell" NTC).
+    std::vector<Real> x, y, vx, vy, vz;
+    std::vector<uint32_t> cell_start;  // ncells + 1
+    // Per-cell collision state of the NTC scheme.
+    std::vector<Real> crmax;           // (sigma_T c_r)_max / sigma_T
+    std::vector<double> rem;           // fractional candidate carried to the next step
+    std::vector<double> nbar_sum;      // sum of N over steps, for N-bar = <N>
+    // Cumulative sums for the DSMC2LB mapping (Sec. 2.1 "cumulative averages"):
+    // [N, S vx, vy, vz, S vv (xx xy xz yy yz zz), S vvv (xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz)]
+    std::vector<double> acc;
+    uint64_t step = 0, nsamples = 0;
+    uint32_t status = 0;
+    uint64_t counters[C_NUM] = {};
+
+    void init(const Params& pp) {
+        p = pp;
+        d = derive(p);
+        const int64_t n = d.ncells * p.ppc;
+        x.assign(n, 0); y.assign(n, 0); vx.assign(n, 0); vy.assign(n, 0); vz.assign(n, 0);
+        cell_start.assign(d.ncells + 1, 0);
+        // Sec. 3.1: a fixed number of particles placed in each cell, Maxwellian at T
+        // (Eq. globalMax with unit variance), drawn by Box-Muller.
+        for (int64_t c = 0; c < d.ncells; ++c) {
+            const int ix = (int)(c % p.ncx), iy = (int)(c / p.ncx);
+            cell_start[c] = (uint32_t)(c * p.ppc);
+            for (int k = 0; k < p.ppc; ++k) {
+                const int64_t s = c * p.ppc + k;
+                U4 rp = draw(p.seed, (uint32_t)c, 0, TAG_INIT_POS, (uint32_t)k, 0);
+                x[s] = (Real)ix + (Real)u01f(rp[0]);
+                y[s] = (Real)iy + (Real)u01f(rp[1]);
+                U4 rv = draw(p.seed, (uint32_t)c, 0, TAG_INIT_VEL, (uint32_t)k, 0);
+                double n0, n1, n2, n3;
+                box_muller(rv[0], rv[1], n0, n1);
+                box_muller(rv[2], rv[3], n2, n3);
+                vx[s] = (Real)n0;
+                vy[s] = (Real)n1;
+                vz[s] = (Real)n2;
+            }
+        }
+        cell_start[d.ncells] = (uint32_t)n;
+        crmax.assign(d.ncells, (Real)p.crmax_init);
+        rem.assign(d.ncells, 0.0);
+        nbar_sum.assign(d.ncells, 0.0);
+        acc.assign(d.ncells * kNumMoments, 0.0);
+        step = 0;
+        nsamples = 0;
+        status = 0;
+        std::memset(counters, 0, sizeof(counters));
+    }
+
+    size_t ntot() const { return x.size(); }
+
+    // Diffuse isothermal re-emission from a wall at rest (Sec. 3.1, "fully diffuse
+    // reflection"): normal speed from the flux-weighted Maxwellian sqrt(-2 ln U), tangential
+    // components Gaussian. `sign` points into the gas.
+    void reemit(uint32_t slot, uint32_t s, int bounce, Real sign, Real& ux, Real& uy, Real& uz) {
+        U4 r = draw(p.seed, slot, s, TAG_WALL, (uint32_t)bounce, 0);
+        const double vn = std::sqrt(-2.0 * std::log(u01open(r[0])));
+        double t1, t2;
+        box_muller(r[1], r[2], t1, t2);
+        ux = sign * (Real)vn;
+        uy = (Real)t1;
+        uz = (Real)t2;
+    }
+
+    uint32_t cell_key(Real xx, Real yy) const {
+        int ix = (int)std::floor(xx);
+        int iy = (int)std::floor(yy);
+        if (ix < 0) ix = 0;
+        if (ix > p.ncx - 1) ix = p.ncx - 1;
+        if (iy < 0) iy = 0;
+        if (iy > p.ncy - 1) iy = p.ncy - 1;
+        return (uint32_t)(iy * p.ncx + ix);
+    }
+
+    // Move one particle through one time step: body-force kick, free flight, wall hits,
+    // periodic wrap in the streamwise direction. Returns the new cell key.
+    uint32_t move_one(uint32_t i, uint32_t s) {
+        if (!(x[i] >= (Real)0)) return kDeadKey;  // deleted by a coupling step
+        const Real H = (Real)p.ncx;
+        const Real L = (Real)p.ncy;
+        Real px = x[i], py = y[i];
+        Real ux = vx[i], uy = vy[i] + (Real)d.g_step, uz = vz[i];
+        Real t = (Real)d.dt;
+        for (int b = 0;; ++b) {
+            const Real xn = px + ux * t;
+            const bool left = xn < (Real)0;
+            const bool right = xn > H;
+            if (!left && !right) {
+                px = xn;
+                py = py + uy * t;
+                break;
+            }
+            if (b == kMaxBounces) {
+                status |= ST_BOUNCE_CAP;
+                counters[C_BOUNCE_CAP] += 1;
+                px = left ? (Real)0 : H;
+                py = py + uy * t;
+                break;
+            }
+            counters[C_WALL_HITS] += 1;
+            Real th = left ? px / (-ux) : (H - px) / ux;
+            py = py + uy * th;
+            px = left ? (Real)0 : H;
+            t = t - th;
+            if (t < (Real)0) t = (Real)0;
+            reemit(i, s, b, left ? (Real)1 : (Real)-1, ux, uy, uz);
+        }
+        if (py < (Real)0 || py >= L) {
+            py = py - L * std::floor(py / L);
+            if (py < (Real)0) py = py + L;
+            if (py >= L) py = py - L;
+        }
+        x[i] = px;
+        y[i] = py;
+        vx[i] = ux;
+        vy[i] = uy;
+        vz[i] = uz;
+        return cell_key(px, py);
+    }
+
+    // Stable counting order by cell key: ties keep the previous slot order. Deleted
+    // particles are dropped.
+    void sort_by_cell(const std::vector<uint32_t>& key) {
+        std::vector<uint32_t> idx;
+        idx.reserve(key.size());
+        for (uint32_t i = 0; i < key.size(); ++i)
+            if (key[i] != kDeadKey) idx.push_back(i);
+        std::stable_sort(idx.begin(), idx.end(),
+                         [&](uint32_t a, uint32_t b) { return key[a] < key[b]; });
+        auto permute = [&](std::vector<Real>& v) {
+            std::vector<Real> o(idx.size());
+            for (size_t k = 0; k < idx.size(); ++k) o[k] = v[idx[k]];
+            v.swap(o);
+        };
+        permute(x); permute(y); permute(vx); permute(vy); permute(vz);
+        std::fill(cell_start.begin(), cell_start.end(), 0u);
+        for (uint32_t i : idx) cell_start[key[i] + 1] += 1;
+        for (int64_t c = 0; c < d.ncells; ++c) cell_start[c + 1] += cell_start[c];
+    }
+
+    // Isotropic unit vector by Marsaglia (1972): (u1, u2) uniform in the unit disc,
+    // n = (2 u1 sqrt(1-s), 2 u2 sqrt(1-s), 1 - 2 s).
+    bool unit_vector(uint32_t c, uint32_t s, uint32_t k, Real* n) {
+        for (int blk = 0; blk < kMaxScatterBlocks; ++blk) {
+            U4 r = draw(p.seed, c, s, TAG_NTC_SCAT, k, (uint32_t)blk);
+            for (int h = 0; h < 2; ++h) {
+                const Real u1 = (Real)2 * (Real)u01f(r[2 * h]) - (Real)1;
+                const Real u2 = (Real)2 * (Real)u01f(r[2 * h + 1]) - (Real)1;
+                const Real ss = u1 * u1 + u2 * u2;
+                if (ss < (Real)1) {
+                    const Real a = (Real)2 * std::sqrt((Real)1 - ss);
+                    n[0] = u1 * a;
+                    n[1] = u2 * a;
+                    n[2] = (Real)1 - (Real)2 * ss;
+                    return true;
+                }
+            }
+        }
+        return false;
+    }
+
+    // NTC hard-sphere collisions in one cell (Sec. 5, Eq. collisionnumber):
+    // N_cand = 1/2 N Nbar F_N (sigma_T c_r)_max dt / V_c plus the carried remainder; each
+    // candidate pair (i, j != i) collides with probability c_r / c_r,max; post-collision
+    // velocities are v_cm +- c_r n / 2 with n isotropic (hard spheres).
+    void collide_cell(uint32_t c, uint32_t s) {
+        const uint32_t base = cell_start[c];
+        const uint32_t n = cell_start[c + 1] - base;
+        nbar_sum[c] += (double)n;
+        const double nbar = nbar_sum[c] / (double)(s + 1);
+        if (n < 2) return;
+        const double ncand = 0.5 * (double)n * nbar * (double)crmax[c] * d.coll_dt + rem[c];
+        const double nsel_d = std::floor(ncand);
+        rem[c] = ncand - nsel_d;
+        uint64_t nsel = (uint64_t)nsel_d;
+        if (nsel > 0xFFFFFFu) {
+            status |= ST_CELL_OVERFLOW;
+            nsel = 0xFFFFFFu;
+        }
+        counters[C_CANDIDATES] += nsel;
+        for (uint32_t k = 0; k < nsel; ++k) {
+            U4 r = draw(p.seed, c, s, TAG_NTC_PAIR, k, 0);
+            const uint32_t i = uindex(r[0], n);
+            uint32_t j = uindex(r[1], n - 1);
+            if (j >= i) j += 1;
+            const Real R = (Real)u01f(r[2]);
+            const uint32_t a = base + i, b = base + j;
+            const Real dx = vx[a] - vx[b], dy = vy[a] - vy[b], dz = vz[a] - vz[b];
+            const Real cr = std::sqrt(dx * dx + dy * dy + dz * dz);
+            if (cr > crmax[c]) crmax[c] = cr;
+            if (cr > R * crmax[c]) {
+                Real nv[3];
+                if (!unit_vector(c, s, k, nv)) {
+                    status |= ST_SCATTER_CAP;
+                    continue;
+                }
+                const Real cx = (vx[a] + vx[b]) * (Real)0.5;
+                const Real cy = (vy[a] + vy[b]) * (Real)0.5;
+                const Real cz = (vz[a] + vz[b]) * (Real)0.5;
+                const Real h = cr * (Real)0.5;
+                vx[a] = cx + h * nv[0]; vy[a] = cy + h * nv[1]; vz[a] = cz + h * nv[2];
+                vx[b] = cx - h * nv[0]; vy[b] = cy - h * nv[1]; vz[b] = cz - h * nv[2];
+                counters[C_COLLISIONS] += 1;
+            }
+        }
+    }
+
+    // Per-cell sums of 1, v, vv, vvv (Sec. 2.1 and Fig. 1: cumulative averages of the
+    // hydrodynamic moments rho, u, P, Q).
+    void sample_cell(uint32_t c) {
+        double m[kNumMoments] = {};
+        for (uint32_t i = cell_start[c]; i < cell_start[c + 1]; ++i) {
+            const double v[3] = {(double)vx[i], (double)vy[i], (double)vz[i]};
+            m[0] += 1.0;
+            for (int a = 0; a < 3; ++a) m[1 + a] += v[a];
+            int o = 4;
+            for (int a = 0; a < 3; ++a)
+                for (int b = a; b < 3; ++b) m[o++] += v[a] * v[b];
+            for (int a = 0; a < 3; ++a)
+                for (int b = a; b < 3; ++b)
+                    for (int e = b; e < 3; ++e) m[o++] += v[a] * v[b] * v[e];
+        }
+        for (int k = 0; k < kNumMoments; ++k) acc[(size_t)c * kNumMoments + k] += m[k];
+    }
+
+    // The three phases of one step; step_once runs them in order.
+    void phase_move_sort() {
+        const uint32_t s = (uint32_t)step;
+        std::vector<uint32_t> key(ntot());
+        for (uint32_t i = 0; i < key.size(); ++i) key[i] = move_one(i, s);
+        sort_by_cell(key);
+    }
+    void phase_collide() {
+        const uint32_t s = (uint32_t)step;
+        for (int64_t c = 0; c < d.ncells; ++c) collide_cell((uint32_t)c, s);
+    }
+    void phase_sample_advance() {
+        const uint32_t s = (uint32_t)step;
+        if (s % (uint32_t)p.sample_every == 0) {
+            for (int64_t c = 0; c < d.ncells; ++c) sample_cell((uint32_t)c);
+            nsamples += 1;
+        }
+        step += 1;
+    }
+    void step_once() {
+        phase_move_sort();
+        phase_collide();
+        phase_sample_advance();
+    }
+};
+
+}  // namespace ora

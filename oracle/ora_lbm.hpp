@@ -1,0 +1,135 @@
+// Oracle: regularised lattice-Boltzmann stream-collide with diffuse kinetic walls and a
+// body force, on D3Q39 (Hermite order 3) or D3Q19 (order 2).
+//
+// TEST INFRASTRUCTURE ONLY (see ora_common.hpp). Every node is updated with double
+// arithmetic by full-tensor loops over the Hermite expansion of Sec. 2 (Eq. series,
+// Eq. coefficients_LBM), so each step can be read against its definition:
+//   pull streaming along e_a; populations entering through a wall are re-emitted by the
+//   wall Maxwellian at rest with the wall density that balances the mass leaving through
+//   that wall on the same streamwise row (the "kinetic boundary conditions" of Sec. 2);
+//   rho = sum f, rho u = sum f xi + rho g / 2;
+//   f_eq = w rho sum_{n<=N} u^n : H^n / n!;
+//   f_neq projected onto H1, H2 (and H3) by the quadrature (the "regularization" of
+//   Sec. 2);
+//   F = w sum_{n=1..N} n (g (x) a_eq^(n-1)) : H^n / n! (Hermite expansion of -g . grad_xi f);
+//   f' = f_eq + (1 - 1/tau) f_neq_reg + (1 - 1/(2 tau)) F.
+// Relaxation time from Eq. tau. The quasi-2D slab has one periodic layer in z.
+#pragma once
+#include "ora_common.hpp"
+
+namespace ora {
+
+template <class Real>
+struct Lbm {
+    Params p;
+    Derived d;
+    Lattice L;
+    std::vector<Real> f;  // f[a * nnodes + y * nx + x]
+
+    void init(const Params& pp) {
+        p = pp;
+        d = derive(p);
+        L = make_lattice(p.lattice);
+        f.assign((size_t)L.q * d.nnodes, 0);
+        for (int a = 0; a < L.q; ++a)
+            for (int64_t n = 0; n < d.nnodes; ++n) f[(size_t)a * d.nnodes + n] = (Real)L.w[a];
+    }
+
+    double fa(int a, int64_t x, int64_t y) const {
+        return (double)f[(size_t)a * d.nnodes + y * d.nx + x];
+    }
+    int64_t wrap_y(int64_t y) const { return ((y % d.ny) + d.ny) % d.ny; }
+
+    // Collision of one node given its streamed populations fs[q]; writes out[q].
+    void collide(const double* fs, double* out) const {
+        const int N = d.order;
+        double rho = 0.0, j[3] = {0, 0, 0};
+        for (int a = 0; a < L.q; ++a) {
+            rho += fs[a];
+            for (int i = 0; i < 3; ++i) j[i] += fs[a] * L.xi[a][i];
+        }
+        const double g[3] = {0.0, d.g_step, 0.0};
+        double u[3];
+        for (int i = 0; i < 3; ++i) u[i] = (j[i] + 0.5 * rho * g[i]) / rho;
+
+        Coeffs aeq{};
+        aeq.a0 = rho;
+        for (int i = 0; i < 3; ++i) {
+            aeq.a1[i] = rho * u[i];
+            for (int k = 0; k < 3; ++k) {
+                aeq.a2[i][k] = rho * u[i] * u[k];
+                for (int l = 0; l < 3; ++l) aeq.a3[i][k][l] = rho * u[i] * u[k] * u[l];
+            }
+        }
+        std::vector<double> feq(L.q), fneq(L.q);
+        for (int a = 0; a < L.q; ++a) {
+            feq[a] = L.w[a] * hermite_series(aeq, L.xi[a].data(), N);
+            fneq[a] = fs[a] - feq[a];
+        }
+        // Projection of f_neq onto H1..HN. The H1 part is -rho g / 2 (the half-step force
+        // shift of u); keeping it makes the momentum gained per step exactly rho g.
+        Coeffs aneq = project(L, fneq.data());
+        aneq.a0 = 0.0;
+        if (N < 3) std::memset(aneq.a3, 0, sizeof(aneq.a3));
+
+        Coeffs bf{};
+        for (int i = 0; i < 3; ++i) {
+            bf.a1[i] = g[i] * aeq.a0;
+            for (int k = 0; k < 3; ++k) {
+                bf.a2[i][k] = 2.0 * g[i] * aeq.a1[k];
+                for (int l = 0; l < 3; ++l) bf.a3[i][k][l] = 3.0 * g[i] * aeq.a2[k][l];
+            }
+        }
+        const double om = 1.0 - 1.0 / d.tau;
+        const double of = 1.0 - 1.0 / (2.0 * d.tau);
+        for (int a = 0; a < L.q; ++a) {
+            const double* x = L.xi[a].data();
+            const double freg = L.w[a] * hermite_series(aneq, x, N);
+            const double F = L.w[a] * hermite_series(bf, x, N);
+            out[a] = feq[a] + om * freg + of * F;
+        }
+    }
+
+    void step_once() {
+        const int64_t nx = d.nx, ny = d.ny;
+        std::vector<Real> nf(f.size());
+        // Mass flux normalisation of the wall Maxwellian: sum over incoming a of e_x w_a.
+        double flux_norm = 0.0;
+        for (int a = 0; a < L.q; ++a)
+            if (L.e[a][0] > 0) flux_norm += L.e[a][0] * L.w[a];
+        std::vector<double> rhoL(ny), rhoR(ny);
+        for (int64_t y = 0; y < ny; ++y) {
+            double ml = 0.0, mr = 0.0;
+            for (int a = 0; a < L.q; ++a) {
+                const int ex = L.e[a][0];
+                const int64_t sy = wrap_y(y - L.e[a][1]);
+                if (ex < 0)
+                    for (int64_t i = 0; i < -ex; ++i) ml += fa(a, i, sy);
+                if (ex > 0)
+                    for (int64_t i = nx - ex; i < nx; ++i) mr += fa(a, i, sy);
+            }
+            rhoL[y] = ml / flux_norm;
+            rhoR[y] = mr / flux_norm;
+        }
+        std::vector<double> fs(L.q), out(L.q);
+        for (int64_t y = 0; y < ny; ++y)
+            for (int64_t x = 0; x < nx; ++x) {
+                for (int a = 0; a < L.q; ++a) {
+                    const int64_t sx = x - L.e[a][0];
+                    const int64_t sy = wrap_y(y - L.e[a][1]);
+                    if (sx < 0)
+                        fs[a] = L.w[a] * rhoL[y];
+                    else if (sx >= nx)
+                        fs[a] = L.w[a] * rhoR[y];
+                    else
+                        fs[a] = fa(a, sx, sy);
+                }
+                collide(fs.data(), out.data());
+                for (int a = 0; a < L.q; ++a)
+                    nf[(size_t)a * d.nnodes + y * nx + x] = (Real)out[a];
+            }
+        f.swap(nf);
+    }
+};
+
+}  // namespace ora

@@ -1,0 +1,250 @@
+"""ctypes wrapper around the CPU oracle (test infrastructure only).
+
+The oracle is a plain, slow restatement of the DSMC-LBM mapping method (arXiv 1512.08042)
+used to check the CUDA library. Only the tests, the smoke check and the CPU-baseline leg of
+the benchmark may import this module; the library itself never does.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_LIB = None
+
+A_X, A_Y, A_VX, A_VY, A_VZ, A_CELL_START, A_CRMAX, A_REM, A_NBAR_SUM, A_ACC, A_F = range(11)
+COUNTER_NAMES = ["wall_hits", "candidates", "collisions", "created", "deleted",
+                 "l2d_attempts", "envelope", "bounce_cap"]
+ST_CAPACITY, ST_BOUNCE_CAP, ST_SCATTER_CAP, ST_SAMPLING_CAP, ST_CELL_OVERFLOW, ST_BAD_INPUT = (
+    1, 2, 4, 8, 16, 32)
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("abi_version", ctypes.c_uint32),
+        ("ncx", ctypes.c_int32),
+        ("ncy", ctypes.c_int32),
+        ("lb_ratio", ctypes.c_int32),
+        ("ppc", ctypes.c_int32),
+        ("lattice", ctypes.c_int32),
+        ("real_bytes", ctypes.c_int32),
+        ("sample_every", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+        ("kn", ctypes.c_double),
+        ("ma", ctypes.c_double),
+        ("crmax_init", ctypes.c_double),
+        ("capacity_factor", ctypes.c_double),
+        ("T_K", ctypes.c_double),
+        ("mass_kg", ctypes.c_double),
+    ]
+
+
+class Derived(ctypes.Structure):
+    _fields_ = [
+        ("r_lat", ctypes.c_double),
+        ("cs_lat", ctypes.c_double),
+        ("H_lat", ctypes.c_double),
+        ("tau", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("lam", ctypes.c_double),
+        ("coll_dt", ctypes.c_double),
+        ("g_step", ctypes.c_double),
+        ("c_th_ms", ctypes.c_double),
+        ("ncells", ctypes.c_int64),
+        ("nx", ctypes.c_int64),
+        ("ny", ctypes.c_int64),
+        ("nnodes", ctypes.c_int64),
+        ("capacity", ctypes.c_int64),
+        ("q", ctypes.c_int32),
+        ("order", ctypes.c_int32),
+    ]
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        vp, i32, i64, u32, u64, dbl = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
+                                       ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double)
+        L.ora_derive.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(Derived)]
+        L.ora_philox.argtypes = [vp, u64, vp, i64]
+        L.ora_lattice.argtypes = [ctypes.c_int, vp, vp, ctypes.POINTER(dbl)]
+        L.ora_create.argtypes = [ctypes.POINTER(Params)]
+        L.ora_create.restype = vp
+        L.ora_destroy.argtypes = [vp]
+        L.ora_dsmc_step.argtypes = [vp, ctypes.c_int]
+        L.ora_lbm_step.argtypes = [vp, ctypes.c_int]
+        L.ora_dsmc_phase.argtypes = [vp, ctypes.c_int]
+        L.ora_map_dsmc_to_lbm.argtypes = [vp, vp, ctypes.c_int]
+        L.ora_map_lbm_to_dsmc.argtypes = [vp, vp, ctypes.c_int]
+        L.ora_get.argtypes = [vp, ctypes.c_int, vp]
+        L.ora_get.restype = i64
+        L.ora_set.argtypes = [vp, ctypes.c_int, vp, i64]
+        L.ora_scalars.argtypes = [vp, vp]
+        L.ora_set_scalars.argtypes = [vp, u64, u64]
+        L.ora_counters.argtypes = [vp, vp]
+        L.ora_lbm_collide.argtypes = [ctypes.POINTER(Params), vp, vp]
+        L.ora_dsmc2lb_node.argtypes = [ctypes.c_int, vp, u64, ctypes.c_int, vp]
+        L.ora_grad_coeffs.argtypes = [ctypes.c_int, vp, vp]
+        L.ora_grad_sample.argtypes = [ctypes.c_int, vp, u64, u32, u32, i64, vp, vp]
+        _LIB = L
+    return _LIB
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def make_params(cfg):
+    p = Params()
+    p.abi_version = 1
+    for name, _ in Params._fields_:
+        if name != "abi_version" and name in cfg:
+            setattr(p, name, cfg[name])
+    return p
+
+
+def derive(cfg):
+    d = Derived()
+    rc = lib().ora_derive(ctypes.byref(make_params(cfg)), ctypes.byref(d))
+    if rc != 0:
+        raise ValueError("invalid parameters")
+    return {name: getattr(d, name) for name, _ in Derived._fields_}
+
+
+def philox(ctr, seed):
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    out = np.empty_like(ctr)
+    lib().ora_philox(_ptr(ctr), ctypes.c_uint64(seed), _ptr(out), ctr.shape[0])
+    return out
+
+
+def lattice(q):
+    e = np.zeros((q, 3), np.int32)
+    w = np.zeros(q, np.float64)
+    r = ctypes.c_double()
+    if lib().ora_lattice(q, _ptr(e), _ptr(w), ctypes.byref(r)) != 0:
+        raise ValueError(q)
+    return e, w, r.value
+
+
+def lbm_collide(cfg, fs):
+    fs = np.ascontiguousarray(fs, np.float64)
+    out = np.empty_like(fs)
+    if lib().ora_lbm_collide(ctypes.byref(make_params(cfg)), _ptr(fs), _ptr(out)) != 0:
+        raise ValueError("invalid parameters")
+    return out
+
+
+def dsmc2lb_node(q, m20, S, ppc):
+    m = np.ascontiguousarray(m20, np.float64)
+    out = np.empty(q, np.float64)
+    rc = lib().ora_dsmc2lb_node(q, _ptr(m), S, ppc, _ptr(out))
+    if rc != 0:
+        raise ValueError(rc)
+    return out
+
+
+def grad_coeffs(q, f):
+    f = np.ascontiguousarray(f, np.float64)
+    out = np.empty(42, np.float64)
+    lib().ora_grad_coeffs(q, _ptr(f), _ptr(out))
+    return {"rho": out[0], "u": out[1:4].copy(), "a2": out[4:13].reshape(3, 3).copy(),
+            "a3": out[13:40].reshape(3, 3, 3).copy(), "M": out[40], "C": out[41]}
+
+
+def grad_sample(q, f, seed, cell, t, n):
+    f = np.ascontiguousarray(f, np.float64)
+    v = np.empty((n, 3), np.float64)
+    info = np.zeros(3, np.uint64)
+    rc = lib().ora_grad_sample(q, _ptr(f), seed, cell, t, n, _ptr(v), _ptr(info))
+    if rc != 0:
+        raise ValueError(rc)
+    return v, {"attempts": int(info[0]), "envelope": int(info[1]), "cap": int(info[2])}
+
+
+class Oracle:
+    """One DSMC + LBM state on the host (float or double, per cfg['real_bytes'])."""
+
+    def __init__(self, cfg):
+        self.cfg = dict(cfg)
+        self.params = make_params(cfg)
+        self.d = derive(cfg)
+        self.h = lib().ora_create(ctypes.byref(self.params))
+        if not self.h:
+            raise ValueError("invalid parameters")
+        self.real = np.float32 if cfg["real_bytes"] == 4 else np.float64
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().ora_destroy(self.h)
+            self.h = None
+
+    def dsmc_step(self, n=1):
+        lib().ora_dsmc_step(self.h, n)
+
+    def dsmc_phase(self, phase):
+        """0: move + sort, 1: collide, 2: sample + advance the step counter."""
+        lib().ora_dsmc_phase(self.h, phase)
+
+    def lbm_step(self, n=1):
+        lib().ora_lbm_step(self.h, n)
+
+    def map_dsmc_to_lbm(self, nodes):
+        nodes = np.ascontiguousarray(nodes, np.int32)
+        lib().ora_map_dsmc_to_lbm(self.h, _ptr(nodes), len(nodes))
+
+    def map_lbm_to_dsmc(self, cells):
+        cells = np.ascontiguousarray(cells, np.int32)
+        lib().ora_map_lbm_to_dsmc(self.h, _ptr(cells), len(cells))
+
+    _DT = {A_CELL_START: np.uint32, A_REM: np.float64, A_NBAR_SUM: np.float64,
+           A_ACC: np.float64}
+
+    def _dtype(self, which):
+        return self._DT.get(which, self.real)
+
+    def get(self, which):
+        n = lib().ora_get(self.h, which, None)
+        out = np.empty(n, self._dtype(which))
+        lib().ora_get(self.h, which, _ptr(out))
+        return out
+
+    def set(self, which, arr):
+        arr = np.ascontiguousarray(arr, self._dtype(which))
+        if lib().ora_set(self.h, which, _ptr(arr), arr.size) != 0:
+            raise ValueError("size mismatch for array %d" % which)
+
+    def particles(self):
+        return {k: self.get(a) for k, a in
+                (("x", A_X), ("y", A_Y), ("vx", A_VX), ("vy", A_VY), ("vz", A_VZ))}
+
+    def set_particles(self, x, y, vx, vy, vz, cell_start):
+        for a, v in ((A_X, x), (A_Y, y), (A_VX, vx), (A_VY, vy), (A_VZ, vz)):
+            self.set(a, v)
+        self.set(A_CELL_START, cell_start)
+
+    def f(self):
+        return self.get(A_F).reshape(self.d["q"], self.d["ny"], self.d["nx"])
+
+    def set_f(self, f):
+        self.set(A_F, np.asarray(f).reshape(-1))
+
+    def acc(self):
+        return self.get(A_ACC).reshape(-1, 20)
+
+    def scalars(self):
+        out = np.zeros(4, np.uint64)
+        lib().ora_scalars(self.h, _ptr(out))
+        return {"step": int(out[0]), "nsamples": int(out[1]), "status": int(out[2]),
+                "ntot": int(out[3])}
+
+    def set_scalars(self, step, nsamples):
+        lib().ora_set_scalars(self.h, step, nsamples)
+
+    def counters(self):
+        out = np.zeros(16, np.uint64)
+        lib().ora_counters(self.h, _ptr(out))
+        return {n: int(out[i]) for i, n in enumerate(COUNTER_NAMES)}

@@ -1,0 +1,102 @@
+"""Synthetic workloads and seeded input generators.
+
+The paper measures force-driven plane Poiseuille channels of an Argon-like hard-sphere gas
+(Sec. 3.1: T = 273 K, m = 6.63e-26 kg, Ma = 0.1 on the centreline velocity; 100 particles
+per cell initially) and publishes no dataset, so every input here is synthetic: a parameter
+set plus a seed. This module holds no arithmetic of the method; it only builds parameter
+dictionaries, coupling index lists and seeded random arrays that the CUDA library and the
+CPU oracle both take as inputs.
+"""
+import numpy as np
+
+ARGON = dict(T_K=273.0, mass_kg=6.63e-26)
+
+_BASE = dict(lb_ratio=1, lattice=39, real_bytes=4, sample_every=1, kn=0.1, ma=0.1,
+             crmax_init=6.0, capacity_factor=1.5, **ARGON)
+
+
+def config(**kw):
+    cfg = dict(_BASE)
+    cfg.update(kw)
+    return cfg
+
+
+# Named workloads. Across-channel cells (walls) = ncx, streamwise periodic cells = ncy.
+WORKLOADS = {
+    # Plain hybrid, 64 cells across x 1 periodic cell, 100 particles/cell, Kn 0.1, FP64,
+    # 64-node D3Q39 lattice, mapping at 2 coupling nodes (i = 1 and i = H - 2).
+    "poiseuille_64x1_ppc100_fp64": config(ncx=64, ncy=1, ppc=100, real_bytes=8, kn=0.1, seed=1),
+    # 2D channel: 64 x 256 DSMC cells, 50 particles/cell (819,200), Kn 0.05, FP32 state,
+    # 128 x 512 D3Q39 lattice (two LB nodes per cell per axis), 8-node coupling strip.
+    "poiseuille_64x256_ppc50_fp32": config(ncx=64, ncy=256, ppc=50, lb_ratio=2, kn=0.05,
+                                            capacity_factor=1.25, seed=2),
+    # Large channel: 512 x 4096 DSMC cells, 50 particles/cell (104,857,600), FP32 state,
+    # 1024 x 8192 D3Q39 lattice.
+    "poiseuille_512x4096_ppc50_fp32": config(ncx=512, ncy=4096, ppc=50, lb_ratio=2, kn=0.05,
+                                              capacity_factor=1.25, seed=5),
+}
+
+
+def coupling_sites(cfg, strip_cells=None):
+    """Coupling nodes and cells.
+
+    With ncy == 1 (the channel of Sec. 3.2/3.3) the sites are the first fluid node/cell next
+    to each wall (i = 1 and i = H - 2). Otherwise a strip `strip_cells` DSMC cells wide
+    (default 4, i.e. 8 LB nodes at two nodes per cell) across the whole channel height, in
+    the middle of the streamwise period, as the one-cell buffer layer of Sec. 4 widened.
+    Returns (nodes, cells) as int32 arrays; node = y * nx + x, cell = iy * ncx + ix.
+    """
+    ncx, ncy, r = cfg["ncx"], cfg["ncy"], cfg["lb_ratio"]
+    nx = ncx * r
+    if ncy == 1:
+        cells = np.array([1, ncx - 2], np.int32)
+        nodes = []
+        for c in cells:
+            for dy in range(r):
+                for dx in range(r):
+                    nodes.append(dy * nx + c * r + dx)
+        return np.array(nodes, np.int32), cells
+    w = strip_cells if strip_cells is not None else 4
+    y0 = ncy // 2 - w // 2
+    cells = np.array([iy * ncx + ix for iy in range(y0, y0 + w) for ix in range(ncx)], np.int32)
+    nodes = np.array([y * nx + x for y in range(y0 * r, (y0 + w) * r) for x in range(nx)],
+                     np.int32)
+    return nodes, cells
+
+
+def gen_populations(weights, nnodes, seed, eps=0.05, rho_eps=0.02):
+    """Populations f[a, node] = w_a * rho_node * (1 + eps * U(-1, 1)), rho_node = 1 + rho_eps * U(-1,1)."""
+    rng = np.random.default_rng(seed)
+    w = np.asarray(weights, np.float64)[:, None]
+    rho = 1.0 + rho_eps * rng.uniform(-1, 1, size=(1, nnodes))
+    return w * rho * (1.0 + eps * rng.uniform(-1, 1, size=(len(weights), nnodes)))
+
+
+def gen_particles(ncx, ncy, mean_ppc, seed, empty_fraction=0.0, vel_scale=1.0, drift=(0, 0, 0)):
+    """A cell-ordered particle set: per-cell counts ~ Poisson(mean_ppc) (a fraction of cells
+    forced empty), positions uniform inside their cell, Gaussian velocities.
+
+    Returns dict of float64 arrays x, y, vx, vy, vz and uint32 cell_start (ncells + 1).
+    """
+    rng = np.random.default_rng(seed)
+    ncells = ncx * ncy
+    counts = rng.poisson(mean_ppc, size=ncells)
+    if empty_fraction > 0:
+        counts[rng.random(ncells) < empty_fraction] = 0
+    cell = np.repeat(np.arange(ncells), counts)
+    n = cell.size
+    ix, iy = cell % ncx, cell // ncx
+    out = {
+        "x": ix + rng.random(n),
+        "y": iy + rng.random(n),
+        "vx": drift[0] + vel_scale * rng.standard_normal(n),
+        "vy": drift[1] + vel_scale * rng.standard_normal(n),
+        "vz": drift[2] + vel_scale * rng.standard_normal(n),
+    }
+    # keep positions strictly inside their cell after any rounding to float
+    out["x"] = np.minimum(out["x"], ix + 0.999)
+    out["y"] = np.minimum(out["y"], iy + 0.999)
+    cs = np.zeros(ncells + 1, np.uint32)
+    cs[1:] = np.cumsum(counts)
+    out["cell_start"] = cs
+    return out

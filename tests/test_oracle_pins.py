@@ -1,0 +1,559 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: published known-answer
+vectors, closed forms, exact quadrature identities, conservation laws, textbook special cases
+and statistical laws with confidence intervals. No GPU is used.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1512_08042_gb300 import workloads as W
+from conftest import read_golden_numbers
+
+
+def small_cfg(**kw):
+    base = dict(ncx=16, ncy=4, ppc=40, real_bytes=8, seed=7, kn=0.1)
+    base.update(kw)
+    return W.config(**base)
+
+
+# ---------------------------------------------------------------------------------------
+# Philox4x32-10 (Salmon et al., SC'11)
+
+def test_philox_known_answers(golden_dir):
+    rows = []
+    with open(os.path.join(golden_dir, "philox4x32_10_kat.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                rows.append([int(t, 16) for t in line.split()])
+    assert len(rows) == 3
+    for r in rows:
+        ctr, key, want = r[0:4], r[4:6], r[6:10]
+        got = O.philox(ctr, key[0] | (key[1] << 32))[0]
+        assert [int(v) for v in got] == want
+
+
+def test_philox_uniformity_chi2():
+    n = 1 << 18
+    ctr = np.zeros((n // 4, 4), np.uint32)
+    ctr[:, 0] = np.arange(n // 4)
+    words = O.philox(ctr, 12345).reshape(-1)
+    u = (words >> 8).astype(np.float64) * 2.0 ** -24
+    hist, _ = np.histogram(u, bins=64, range=(0, 1))
+    e = n / 64
+    chi2 = ((hist - e) ** 2 / e).sum()
+    # 63 dof: mean 63, sd 11.2; 99.99% upper tail ~ 110
+    assert chi2 < 110
+
+
+# ---------------------------------------------------------------------------------------
+# Gauss-Hermite lattices (Sec. 1, Sec. 3.1: D3Q39 has sixth-order isotropy; the quadrature
+# must be exact to degree >= 2N, Sec. 2.1)
+
+def gaussian_moment(alpha):
+    m = 1.0
+    for a in alpha:
+        if a % 2:
+            return 0.0
+        m *= math.prod(range(a - 1, 0, -2)) if a > 0 else 1.0
+    return m
+
+
+def quadrature_max_exact_degree(q):
+    e, w, r = O.lattice(q)
+    xi = e * r
+    deg = 0
+    for n in range(0, 10):
+        ok = True
+        for alpha in itertools.product(range(n + 1), repeat=3):
+            if sum(alpha) != n:
+                continue
+            val = (w * np.prod(xi ** np.array(alpha), axis=1)).sum()
+            if abs(val - gaussian_moment(alpha)) > 1e-12 * max(1.0, gaussian_moment(alpha)):
+                ok = False
+                break
+        if not ok:
+            return deg
+        deg = n
+    return deg
+
+
+def test_d3q39_quadrature_degree_7():
+    e, w, r = O.lattice(39)
+    assert len(w) == 39 and abs(w.sum() - 1) < 1e-15
+    assert abs(r - math.sqrt(1.5)) < 1e-15
+    assert len({tuple(v) for v in e}) == 39
+    assert quadrature_max_exact_degree(39) == 7
+
+
+def test_d3q19_quadrature_degree_5():
+    e, w, r = O.lattice(19)
+    assert len(w) == 19 and abs(w.sum() - 1) < 1e-15
+    assert quadrature_max_exact_degree(19) == 5
+
+
+# ---------------------------------------------------------------------------------------
+# Derived constants: Eq. tau, Eq. MFP, Appendix A, Table 3
+
+def test_tau_relation_eq_tau(golden_dir):
+    g = read_golden_numbers(os.path.join(golden_dir, "paper_numbers.txt"))
+    for q, key in ((39, "c_over_cs_d3q39"), (19, "c_over_cs_d3q19")):
+        for kn, H in ((0.1, 64), (0.05, 32), (0.25, 20)):
+            d = O.derive(W.config(ncx=H, ncy=1, ppc=10, lattice=q, kn=kn, seed=1))
+            assert d["r_lat"] == pytest.approx(g[key], rel=1e-15)
+            assert d["tau"] == pytest.approx(math.sqrt(math.pi / 8) * g[key] * kn * H + 0.5,
+                                             rel=1e-14)
+    d = O.derive(W.WORKLOADS["poiseuille_64x1_ppc100_fp64"])
+    assert d["tau"] == pytest.approx(5.412, abs=1e-3)
+    d = O.derive(W.WORKLOADS["poiseuille_64x256_ppc50_fp32"])
+    assert d["tau"] == pytest.approx(5.412, abs=1e-3)
+
+
+def test_thermal_speed_matches_table3(golden_dir):
+    g = read_golden_numbers(os.path.join(golden_dir, "paper_numbers.txt"))
+    cfg = W.config(ncx=16, ncy=1, ppc=10, seed=1, T_K=g["gas_temperature_K"],
+                   mass_kg=g["gas_mass_kg"])
+    c_th = O.derive(cfg)["c_th_ms"]
+    # Table 3's standard deviations of v_y agree with sqrt(kT/m) to 0.5%, not sqrt(2kT/m).
+    for k in ("table3_sigma_vy_dsmc_kn015", "table3_sigma_vy_lb2dsmc_kn015",
+              "table3_sigma_vy_dsmc_kn025", "table3_sigma_vy_lb2dsmc_kn025"):
+        assert abs(g[k] / c_th - 1) < 0.005
+        assert abs(g[k] / (math.sqrt(2) * c_th) - 1) > 0.25
+
+
+def test_force_from_no_slip_parabola():
+    # u_max = g H^2 / (8 nu) with u_max = Ma c_s (Sec. 3.1), in lattice units, times r.
+    cfg = W.config(ncx=20, ncy=1, ppc=10, seed=1, kn=0.07, ma=0.1, lb_ratio=2)
+    d = O.derive(cfg)
+    nu = (d["tau"] - 0.5) / 1.5
+    g_lat = 8 * nu * 0.1 * math.sqrt(2 / 3) / (40.0 ** 2)
+    assert d["g_step"] == pytest.approx(g_lat * math.sqrt(1.5), rel=1e-13)
+    assert d["dt"] == pytest.approx(math.sqrt(2 / 3) / 2, rel=1e-15)
+    assert d["lam"] == pytest.approx(0.07 * 20, rel=1e-15)
+
+
+# ---------------------------------------------------------------------------------------
+# DSMC: initialisation, NTC collisions, walls, sort
+
+def test_init_maxwellian_and_uniform_positions():
+    cfg = small_cfg(ncx=32, ncy=8, ppc=200)
+    o = O.Oracle(cfg)
+    p = o.particles()
+    n = p["x"].size
+    assert n == 32 * 8 * 200
+    v = np.stack([p["vx"], p["vy"], p["vz"]])
+    se = 1 / math.sqrt(n)
+    assert np.all(np.abs(v.mean(1)) < 5 * se)
+    assert np.all(np.abs(v.var(1) - 1) < 5 * math.sqrt(2) * se)
+    # fourth moment of a unit Gaussian is 3
+    assert np.all(np.abs((v ** 4).mean(1) - 3) < 5 * math.sqrt(96) * se)
+    cs = o.get(O.A_CELL_START)
+    cell = np.repeat(np.arange(32 * 8), np.diff(cs))
+    assert np.all(np.floor(p["x"]) == cell % 32)
+    assert np.all(np.floor(p["y"]) == cell // 32)
+    frac = p["x"] - np.floor(p["x"])
+    hist, _ = np.histogram(frac, bins=16, range=(0, 1))
+    assert ((hist - n / 16) ** 2 / (n / 16)).sum() < 45  # 15 dof
+
+
+def test_ntc_candidate_count_eq_collisionnumber():
+    cfg = small_cfg(ma=0.0)
+    o = O.Oracle(cfg)
+    d = o.d
+    o.dsmc_phase(0)
+    N = np.diff(o.get(O.A_CELL_START)).astype(np.float64)
+    before = o.counters()["candidates"]
+    o.dsmc_phase(1)
+    got = o.counters()["candidates"] - before
+    # first step: N-bar = N, (sigma c_r)_max at its initial value, no remainder
+    ncand = 0.5 * N * N * cfg["crmax_init"] * d["coll_dt"]
+    want = int(np.floor(ncand[N >= 2]).sum())
+    assert got == want
+
+
+def _cell_sums(o):
+    p = o.particles()
+    cs = o.get(O.A_CELL_START)
+    cell = np.repeat(np.arange(len(cs) - 1), np.diff(cs))
+    v = np.stack([p["vx"], p["vy"], p["vz"]], 1)
+    mom = np.zeros((len(cs) - 1, 3))
+    en = np.zeros(len(cs) - 1)
+    np.add.at(mom, cell, v)
+    np.add.at(en, cell, (v ** 2).sum(1))
+    return mom, en
+
+
+def test_collisions_conserve_momentum_and_energy_per_cell():
+    o = O.Oracle(small_cfg(ppc=60))
+    o.dsmc_phase(0)
+    m0, e0 = _cell_sums(o)
+    c0 = o.counters()["collisions"]
+    o.dsmc_phase(1)
+    assert o.counters()["collisions"] - c0 > 50
+    m1, e1 = _cell_sums(o)
+    assert np.abs(m1 - m0).max() < 1e-12
+    assert np.abs(e1 - e0).max() < 1e-11
+    # and the velocities did change
+    p = o.particles()
+    assert not np.allclose(e0, 0)
+
+
+def test_hard_sphere_collision_rate_equals_mean_speed_over_mfp():
+    # Equilibrium box: collisions per step = 1/2 N_tot (<c>/lambda) dt with <c> = sqrt(8/pi)
+    # (Eq. MFP: lambda = <c>/nu for hard spheres).
+    cfg = small_cfg(ncx=24, ncy=8, ppc=50, ma=0.0, kn=0.08, crmax_init=5.0)
+    o = O.Oracle(cfg)
+    d = o.d
+    o.dsmc_step(20)  # let (sigma c_r)_max settle
+    c0 = o.counters()["collisions"]
+    steps = 200
+    o.dsmc_step(steps)
+    got = (o.counters()["collisions"] - c0) / steps
+    ntot = 24 * 8 * 50
+    want = 0.5 * ntot * math.sqrt(8 / math.pi) / d["lam"] * d["dt"]
+    # counts per step are ~Poisson with mean `want`; 200 steps, allow 4 sigma + 1% bias
+    assert abs(got - want) < 4 * math.sqrt(want / steps) + 0.01 * want
+
+
+def test_wall_flux_and_equilibrium_is_kept():
+    cfg = small_cfg(ncx=20, ncy=6, ppc=80, ma=0.0, kn=0.2)
+    o = O.Oracle(cfg)
+    d = o.d
+    steps = 100
+    o.dsmc_step(steps)
+    hits = o.counters()["wall_hits"] / steps
+    # one-sided Maxwellian flux n <c>/4 through each wall of area ncy (cell units)
+    want = 2 * 80 * math.sqrt(8 / math.pi) / 4 * 6 * d["dt"]
+    assert abs(hits / want - 1) < 0.05
+    p = o.particles()
+    v = np.stack([p["vx"], p["vy"], p["vz"]])
+    n = v.shape[1]
+    assert np.all(np.abs(v.var(1) - 1) < 0.05)
+    assert np.all(np.abs(v.mean(1)) < 5 / math.sqrt(n) * 3)
+    assert o.scalars()["ntot"] == 20 * 6 * 80
+
+
+def test_sort_is_stable_by_cell_brute_force():
+    # zero velocities and no force: a step is sort + sampling only
+    cfg = small_cfg(ncx=7, ncy=3, ppc=5, ma=0.0, real_bytes=4)
+    o = O.Oracle(cfg)
+    rng = np.random.default_rng(3)
+    n = 60
+    x = rng.uniform(0, 7, n).astype(np.float32)
+    y = rng.uniform(0, 3, n).astype(np.float32)
+    z = np.zeros(n, np.float32)
+    o.set_particles(x, y, z, z, z, np.zeros(22, np.uint32))
+    o.dsmc_step(1)
+    key = (np.floor(y).astype(int) * 7 + np.floor(x).astype(int))
+    order = sorted(range(n), key=lambda i: key[i])  # Python's sort is stable
+    p = o.particles()
+    assert np.array_equal(p["x"], x[order]) and np.array_equal(p["y"], y[order])
+    cs = o.get(O.A_CELL_START)
+    assert np.array_equal(np.diff(cs), np.bincount(key, minlength=21))
+
+
+def test_sampling_sums_match_direct_moments():
+    o = O.Oracle(small_cfg(ncx=8, ncy=2, ppc=30))
+    o.dsmc_step(1)
+    acc = o.acc()
+    p = o.particles()
+    cs = o.get(O.A_CELL_START)
+    c = 5
+    sl = slice(cs[c], cs[c + 1])
+    v = np.stack([p["vx"][sl], p["vy"][sl], p["vz"][sl]], 1)
+    assert acc[c, 0] == v.shape[0]
+    assert np.allclose(acc[c, 1:4], v.sum(0), rtol=1e-13, atol=1e-13)
+    assert acc[c, 4 + 1] == pytest.approx((v[:, 0] * v[:, 1]).sum(), rel=1e-12)  # xy
+    assert acc[c, 10 + 4] == pytest.approx((v[:, 0] * v[:, 1] * v[:, 2]).sum(), rel=1e-12)  # xyz
+    assert acc[c, 19] == pytest.approx((v[:, 2] ** 3).sum(), rel=1e-12)  # zzz
+
+
+def test_cell_velocity_scatter_matches_sigma_u():
+    # Sec. 5: sigma_u = sqrt(kT / (m <N>)) / sqrt(S) for S independent samples; samples
+    # every 50 steps are independent (corr(u_x, u_y) = -0.008).
+    cfg = small_cfg(ncx=16, ncy=4, ppc=40, ma=0.0, kn=0.1, sample_every=50)
+    o = O.Oracle(cfg)
+    o.dsmc_step(50 * 30)
+    acc = o.acc()
+    S = o.scalars()["nsamples"]
+    assert S == 30
+    u = acc[:, 2] / acc[:, 0]
+    sigma_u = 1 / math.sqrt(40 * S)
+    ratio = u.std() / sigma_u
+    # 64 cells: the sample sd of a Gaussian has relative sd ~ 1/sqrt(2*63) = 0.09
+    assert 0.7 < ratio < 1.3
+
+
+# ---------------------------------------------------------------------------------------
+# LBM: conservation, force moments, Poiseuille
+
+def _lb_moments(q, f):
+    e, w, r = O.lattice(q)
+    xi = e * r
+    rho = f.sum()
+    j = (f[:, None] * xi).sum(0)
+    Pi = np.einsum("a,ai,aj->ij", f, xi, xi)
+    Q = np.einsum("a,ai,aj,ak->ijk", f, xi, xi, xi)
+    return rho, j, Pi, Q, xi, w
+
+
+@pytest.mark.parametrize("q", [39, 19])
+def test_lbm_collision_moments(q):
+    # Mass kept; momentum gains rho g per step; second moment relaxes as BGK with the Guo
+    # force term: Pi' = Pi_eq + (1 - 1/tau)(Pi - Pi_eq) + (1 - 1/2tau) rho (g u + u g).
+    cfg = W.config(ncx=16, ncy=1, ppc=10, lattice=q, real_bytes=8, kn=0.2, ma=0.3, seed=1)
+    d = O.derive(cfg)
+    e, w, r = O.lattice(q)
+    rng = np.random.default_rng(1)
+    fs = w * (1 + 0.1 * rng.uniform(-1, 1, q))
+    out = O.lbm_collide(cfg, fs)
+    rho, j, Pi, Q, xi, _ = _lb_moments(q, fs)
+    rho2, j2, Pi2, Q2, _, _ = _lb_moments(q, out)
+    g = np.array([0, d["g_step"], 0])
+    tau = d["tau"]
+    assert rho2 == pytest.approx(rho, rel=1e-14)
+    assert np.allclose(j2 - j, rho * g, atol=1e-14)
+    u = (j + 0.5 * rho * g) / rho
+    Pieq = rho * (np.outer(u, u) + np.eye(3))
+    want = Pieq + (1 - 1 / tau) * (Pi - Pieq) + (1 - 0.5 / tau) * rho * (
+        np.outer(g, u) + np.outer(u, g))
+    assert np.allclose(Pi2, want, atol=1e-13)
+    if q == 39:
+        # third Hermite coefficient: rho uuu + (1 - 1/tau) a3neq + (1 - 1/2tau) rho sym(g u u)
+        def h3(F):
+            I = np.eye(3)
+            m3 = np.einsum("a,ai,aj,ak->ijk", F, xi, xi, xi)
+            m1 = (F[:, None] * xi).sum(0)
+            return (m3 - np.einsum("i,jk->ijk", m1, I) - np.einsum("j,ik->ijk", m1, I)
+                    - np.einsum("k,ij->ijk", m1, I))
+        uuu = np.einsum("i,j,k->ijk", u, u, u)
+        a3neq = h3(fs) - rho * uuu
+        gsym = (np.einsum("i,j,k->ijk", g, u, u) + np.einsum("i,j,k->ijk", u, g, u)
+                + np.einsum("i,j,k->ijk", u, u, g))
+        want3 = rho * uuu + (1 - 1 / tau) * a3neq + (1 - 0.5 / tau) * rho * gsym
+        assert np.allclose(h3(out), want3, atol=1e-13)
+
+
+def test_lbm_mass_conserved_with_walls_and_force():
+    cfg = W.config(ncx=12, ncy=5, ppc=10, lb_ratio=2, real_bytes=8, kn=0.1, ma=0.1, seed=1)
+    o = O.Oracle(cfg)
+    e, w, r = O.lattice(39)
+    f0 = W.gen_populations(w, o.d["nnodes"], seed=4)
+    o.set_f(f0)
+    m0 = f0.sum()
+    o.lbm_step(50)
+    assert o.f().sum() == pytest.approx(m0, rel=1e-13)
+
+
+@pytest.mark.parametrize("q,H,steps,skip,tol", [(19, 16, 6000, 0, 1e-4), (39, 32, 10000, 8, 2e-3)])
+def test_lbm_poiseuille_small_kn(q, H, steps, skip, tol):
+    # Steady plane Poiseuille: u'' = -g / nu with nu = (tau - 1/2) c_s^2 away from the
+    # walls' kinetic layer (the Navier-Stokes limit the paper's LB recovers at small Kn).
+    cfg = W.config(ncx=H, ncy=1, ppc=10, lattice=q, real_bytes=8, kn=0.01, ma=0.1, seed=1)
+    o = O.Oracle(cfg)
+    d = o.d
+    o.lbm_step(steps)
+    f = o.f()[:, 0, :]
+    e, w, r = O.lattice(q)
+    rho = f.sum(0)
+    u = ((f * (e[:, 1, None] * r)).sum(0) + 0.5 * rho * d["g_step"]) / rho
+    nu = (d["tau"] - 0.5) * d["cs_lat"] ** 2
+    curv = (u[2:] - 2 * u[1:-1] + u[:-2]) / (-d["g_step"] / nu)
+    inner = curv[skip:len(curv) - skip] if skip else curv
+    assert np.all(np.abs(inner - 1) < tol)
+    assert np.allclose(rho, 1.0, atol=1e-3)
+    # the profile is symmetric and peaks mid-channel
+    assert np.allclose(u, u[::-1], rtol=1e-9, atol=1e-12)
+    assert np.argmax(u) in (H // 2 - 1, H // 2)
+
+
+# ---------------------------------------------------------------------------------------
+# DSMC2LB (Sec. 2.1)
+
+def _sums_from_coeffs(rho, u, P, Q, S, ppc):
+    """Cumulative sums of a cell whose per-particle raw moments are u, P (<v v>), Q (<v v v>)."""
+    NS = rho * ppc * S
+    m = np.zeros(20)
+    m[0] = NS
+    m[1:4] = NS * u
+    o = 4
+    for a in range(3):
+        for b in range(a, 3):
+            m[o] = NS * P[a, b]
+            o += 1
+    for a in range(3):
+        for b in range(a, 3):
+            for c in range(b, 3):
+                m[o] = NS * Q[a, b, c]
+                o += 1
+    return m
+
+
+def _herm_coeffs_of_f(q, f):
+    e, w, r = O.lattice(q)
+    xi = e * r
+    I = np.eye(3)
+    a0 = f.sum()
+    a1 = (f[:, None] * xi).sum(0)
+    a2 = np.einsum("a,ai,aj->ij", f, xi, xi) - a0 * I
+    m3 = np.einsum("a,ai,aj,ak->ijk", f, xi, xi, xi)
+    a3 = m3 - np.einsum("i,jk->ijk", a1, I) - np.einsum("j,ik->ijk", a1, I) - np.einsum(
+        "k,ij->ijk", a1, I)
+    return a0, a1, a2, a3
+
+
+def test_dsmc2lb_round_trip_recovers_moments():
+    rng = np.random.default_rng(11)
+    rho, u = 1.07, np.array([0.03, 0.11, -0.02])
+    A = rng.normal(0, 0.05, (3, 3))
+    P = np.eye(3) + np.outer(u, u) + (A + A.T) / 2
+    B = rng.normal(0, 0.05, (3, 3, 3))
+    Qs = sum(np.transpose(B, p) for p in itertools.permutations(range(3))) / 6
+    Q = Qs + np.einsum("i,jk->ijk", u, P) * 0  # arbitrary symmetric third moment
+    S, ppc = 37, 50
+    f = O.dsmc2lb_node(39, _sums_from_coeffs(rho, u, P, Q, S, ppc), S, ppc)
+    a0, a1, a2, a3 = _herm_coeffs_of_f(39, f)
+    I = np.eye(3)
+    assert a0 == pytest.approx(rho, rel=1e-13)
+    assert np.allclose(a1, rho * u, atol=1e-13)
+    assert np.allclose(a2, rho * (P - I), atol=1e-13)
+    want3 = rho * (Q - np.einsum("i,jk->ijk", u, I) - np.einsum("j,ik->ijk", u, I)
+                   - np.einsum("k,ij->ijk", u, I))
+    assert np.allclose(a3, want3, atol=1e-13)
+
+
+def test_dsmc2lb_of_a_maxwellian_is_the_third_order_equilibrium():
+    rho, u = 0.93, np.array([-0.04, 0.12, 0.05])
+    I = np.eye(3)
+    P = I + np.outer(u, u)
+    Q = (np.einsum("i,j,k->ijk", u, u, u) + np.einsum("i,jk->ijk", u, I)
+         + np.einsum("j,ik->ijk", u, I) + np.einsum("k,ij->ijk", u, I))
+    f = O.dsmc2lb_node(39, _sums_from_coeffs(rho, u, P, Q, 10, 100), 10, 100)
+    e, w, r = O.lattice(39)
+    xu = (e * r) @ u
+    u2 = u @ u
+    feq = w * rho * (1 + xu + 0.5 * (xu ** 2 - u2) + xu * (xu ** 2 - 3 * u2) / 6)
+    assert np.allclose(f, feq, rtol=1e-13, atol=1e-16)
+
+
+def test_dsmc2lb_d3q19_reduces_to_eq_feq_dsmc():
+    # Sec. 4, Eq. feq_dsmc, written in lattice units with c_s^2 = 1/3.
+    rho, uH = 1.02, np.array([0.01, 0.09, -0.03])
+    I = np.eye(3)
+    P = I + np.outer(uH, uH)
+    Q = np.zeros((3, 3, 3))
+    f = O.dsmc2lb_node(19, _sums_from_coeffs(rho, uH, P, Q, 5, 20), 5, 20)
+    e, w, r = O.lattice(19)
+    u_lat = uH / r
+    cs2 = 1.0 / 3.0
+    eu = e @ u_lat
+    feq = w * rho * (1 + eu / cs2 + eu ** 2 / (2 * cs2 ** 2) - (u_lat @ u_lat) / (2 * cs2))
+    assert np.allclose(f, feq, rtol=1e-13, atol=1e-16)
+
+
+# ---------------------------------------------------------------------------------------
+# LB2DSMC (Sec. 2.2, Table 1)
+
+def _eq_populations(q, rho, u):
+    e, w, r = O.lattice(q)
+    xu = (e * r) @ u
+    u2 = u @ u
+    return w * rho * (1 + xu + 0.5 * (xu ** 2 - u2) + xu * (xu ** 2 - 3 * u2) / 6)
+
+
+def test_lb2dsmc_at_equilibrium_is_textbook_box_muller():
+    u = np.array([0.02, 0.08, -0.01])
+    f = _eq_populations(39, 1.0, u)
+    g = O.grad_coeffs(39, f)
+    assert g["M"] < 1e-14 and g["C"] == pytest.approx(1.0, abs=1e-12)
+    assert np.allclose(g["u"], u, atol=1e-15)
+    n = 2000
+    v, info = O.grad_sample(39, f, seed=99, cell=3, t=17, n=n)
+    assert info["cap"] == 0 and info["attempts"] == n  # every first trial accepted
+    # textbook Box-Muller on the same Philox words (counter: cell, step, tag 6 << 24 | k, 0)
+    k = np.arange(n, dtype=np.uint32)
+    ctr = np.stack([np.full(n, 3, np.uint32), np.full(n, 17, np.uint32),
+                    (np.uint32(6) << np.uint32(24)) | k, np.zeros(n, np.uint32)], 1)
+    r = O.philox(ctr, 99).astype(np.float64)
+    uo = (r + 0.5) * 2.0 ** -32
+    rad1 = np.sqrt(-2 * np.log(uo[:, 0]))
+    rad2 = np.sqrt(-2 * np.log(uo[:, 2]))
+    xi = np.stack([rad1 * np.cos(2 * np.pi * uo[:, 1]), rad1 * np.sin(2 * np.pi * uo[:, 1]),
+                   rad2 * np.cos(2 * np.pi * uo[:, 3])], 1)
+    assert np.allclose(v - u, xi, atol=1e-12)
+
+
+def test_lb2dsmc_sampled_moments_match_grad_coefficients():
+    # Non-equilibrium populations from a DSMC2LB projection with stress and heat flux
+    rho, u = 1.0, np.array([0.0, 0.1, 0.0])
+    I = np.eye(3)
+    P = I + np.outer(u, u) + np.array([[0.06, -0.04, 0], [-0.04, -0.03, 0], [0, 0, -0.03]])
+    Q = (np.einsum("i,j,k->ijk", u, u, u) + np.einsum("i,jk->ijk", u, I)
+         + np.einsum("j,ik->ijk", u, I) + np.einsum("k,ij->ijk", u, I))
+    Q = Q.copy()
+    for perm in set(itertools.permutations((0, 1, 1))):
+        Q[perm] += 0.05
+    for perm in set(itertools.permutations((0, 0, 0))):
+        Q[perm] += 0.04
+    f = O.dsmc2lb_node(39, _sums_from_coeffs(rho, u, P, Q, 1, 100), 1, 100)
+    g = O.grad_coeffs(39, f)
+    assert 0.03 < g["M"] < 0.1
+    n = 2_000_000
+    v, info = O.grad_sample(39, f, seed=5, cell=1, t=0, n=n)
+    assert info["cap"] == 0
+    c = v - g["u"]
+    se = 1 / math.sqrt(n)
+    m2 = np.einsum("ni,nj->ij", c, c) / n
+    # E[c c] = delta + a2; the sd of a product of unit Gaussians is <= sqrt(3)
+    assert np.all(np.abs(m2 - (I + g["a2"])) < 5 * math.sqrt(3) * se)
+    m3 = np.einsum("ni,nj,nk->ijk", c, c, c) / n
+    assert np.all(np.abs(m3 - g["a3"]) < 5 * math.sqrt(15) * se)
+    assert np.all(np.abs(c.mean(0)) < 5 * se)
+    # acceptance efficiency is 1/C (Table 1 comments), up to the envelope violations
+    eff = n / info["attempts"]
+    assert abs(eff * g["C"] - 1) < 0.01
+    assert info["envelope"] < 1e-3 * info["attempts"]
+
+
+def test_lb2dsmc_particle_count_conserves_mass():
+    cfg = small_cfg(ncx=10, ncy=3, ppc=40, real_bytes=8)
+    o = O.Oracle(cfg)
+    e, w, r = O.lattice(39)
+    rho_cells = {4: 1.1737, 15: 0.6021, 22: 1.0}
+    f = o.f().copy()
+    for c, rho in rho_cells.items():
+        ix, iy = c % 10, c // 10
+        f[:, iy, ix] = w * rho
+    o.set_f(f)
+    n0 = o.scalars()["ntot"]
+    cells = np.array(sorted(rho_cells), np.int32)
+    o.map_lbm_to_dsmc(cells)
+    s = o.scalars()
+    created = o.counters()["created"]
+    assert s["ntot"] == n0 + created
+    assert o.counters()["deleted"] == 3 * 40
+    lo = sum(math.floor(rho * 40) for rho in rho_cells.values())
+    assert lo <= created <= lo + 3
+    p = o.particles()
+    new_x, new_y = p["x"][n0:], p["y"][n0:]
+    assert set(np.unique(np.floor(new_y) * 10 + np.floor(new_x)).astype(int)) == set(rho_cells)
+    assert np.sum(p["x"][:n0] < 0) == 3 * 40  # the old particles are marked deleted
+    o.dsmc_step(1)
+    assert o.scalars()["ntot"] == n0 - 3 * 40 + created
+
+
+def test_lb2dsmc_sigma_matches_table3_in_si_units(golden_dir):
+    g = read_golden_numbers(os.path.join(golden_dir, "paper_numbers.txt"))
+    c_th = O.derive(small_cfg())["c_th_ms"]
+    u = np.array([0.0, 10.5 / c_th, 0.0])
+    f = _eq_populations(39, 1.0, u)
+    v, info = O.grad_sample(39, f, seed=3, cell=0, t=0, n=200_000)
+    sigma = v[:, 1].std() * c_th
+    # Table 3: sigma_vy of LB2DSMC particles 239.3 m/s (Kn 0.15), within sampling error
+    assert abs(sigma / g["table3_sigma_vy_lb2dsmc_kn015"] - 1) < 0.01
+    assert abs(v[:, 1].mean() * c_th - 10.5) < 5 * 240 / math.sqrt(200_000)
