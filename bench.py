@@ -1,0 +1,321 @@
+"""Benchmark of the hybrid DSMC-LBM hot path on GB300.
+
+One step = one hybrid step over the whole channel: DSMC step (move, sort, NTC collisions,
+sampling), DSMC2LB on the coupling strip, LB stream-collide, LB2DSMC on the coupling strip.
+Default workload: 64 x 256 DSMC cells at 50 particles/cell (819,200 particles), Kn 0.05,
+FP32 state with FP64 moment sums, 128 x 512 D3Q39 lattice, 8-node-wide coupling strip.
+Inputs are synthetic (seeded Maxwellian start). The L2 cache is flushed before every timed
+step (a 512 MB write), and every step is timed with CUDA events on the library's stream.
+
+Prints one JSON line. `--impl reference` times the CPU oracle instead (the reference arm:
+there is no reference implementation of the paper's method to run, only its restatement).
+Under torchrun each rank runs an independent replica on its own GPU (replicas only: the
+paper's method has no exchange between ranks at this workload).
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1512_08042_gb300 import workloads as W  # noqa: E402
+
+METRIC = "DSMC particle-updates/s, LBM MLUPS, hybrid steps/s on 1 GB300 at stated tol"
+DEFAULT_WORKLOAD = "poiseuille_64x256_ppc50_fp32"
+FLUSH_BYTES = 512 << 20
+LAUNCHES_PER_STEP = 9  # move, tile sums, scan, rank, collide, dsmc2lb, lbm, lb2dsmc x2
+
+
+def kernel_algorithmic_bytes(name, cfg, d, n_particles, n_nodes_map, n_cells_map):
+    """Bytes a kernel must move per launch (reads + writes of its inputs and outputs)."""
+    rb = cfg["real_bytes"]
+    ncells = d["ncells"]
+    if name == "collide":
+        # perm (4) + gather 5 Real + write 5 Real per particle; per cell: cell_start (4),
+        # crmax r/w, rem r/w (16), nbar_sum r/w (16), 20 FP64 sums r/w (320)
+        return n_particles * (4 + 10 * rb) + ncells * (4 + 2 * rb + 16 + 16 + 320)
+    if name == "move":
+        # 5 Real read + written in place, key and arrival written, per-cell count atomics
+        return n_particles * (10 * rb + 8) + ncells * 4
+    if name == "rank":
+        return n_particles * 16
+    if name == "lbm":
+        return d["nnodes"] * 2 * d["q"] * rb
+    if name in ("tile_sums", "scan"):
+        return ncells * (4 if name == "tile_sums" else 12)
+    if name == "dsmc2lb":
+        return n_nodes_map * (160 + d["q"] * rb)
+    return 0
+
+
+def sample_clocks(stop, out):
+    cmd = ["nvidia-smi", "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+           "--format=csv,noheader,nounits", "-i", os.environ.get("BENCH_GPU_INDEX", "0")]
+    while not stop.is_set():
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=5)
+            if r.returncode == 0 and r.stdout.strip():
+                out.append(r.stdout.strip().splitlines()[0])
+        except Exception:
+            return
+        stop.wait(0.2)
+
+
+def summarize_clocks(lines):
+    if not lines:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+    sm, smax, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for ln in lines:
+        parts = [p.strip() for p in ln.split(",")]
+        try:
+            sm.append(float(parts[0]))
+            smax = float(parts[1])
+        except ValueError:
+            continue
+        for nm, v in zip(names, parts[3:7]):
+            if v.lower() == "active":
+                reasons.add(nm)
+    sm.sort()
+    return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax,
+            "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_record(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None if the
+    kernel source changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(p))[kernel]
+    except Exception:
+        return None
+    src = os.path.join(ROOT, "paper_1512_08042_gb300", "csrc", rec["source"])
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return rec["bytes_per_launch"] if h == rec["source_sha"] else None
+
+
+def run_oracle(cfg, steps, budget_s):
+    """Time the CPU oracle on hybrid steps of `cfg`; returns (steps/s, steps run)."""
+    from oracle import oracle as O
+    nodes, cells = W.coupling_sites(cfg)
+    o = O.Oracle(cfg)
+    done, t0 = 0, time.perf_counter()
+    while done < steps:
+        o.dsmc_step(1)
+        o.map_dsmc_to_lbm(nodes)
+        o.lbm_step(1)
+        o.map_lbm_to_dsmc(cells)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    return done / (time.perf_counter() - t0), done
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(W.WORKLOADS))
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--profile-kernel", default=None)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    cfg = W.WORKLOADS[args.workload]
+    nodes_np, cells_np = W.coupling_sites(cfg)
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        from oracle import build as OB
+        OB.build()
+        per_step_budget = max(5.0, args.cpu_budget)
+        rate, done = run_oracle(cfg, args.warmup + args.steps, per_step_budget * 4)
+        d = __import__("oracle.oracle", fromlist=["x"]).derive(cfg)
+        n = d["ncells"] * cfg["ppc"]
+        line = {
+            "impl": "reference", "metric": METRIC, "value": rate, "unit": "hybrid steps/s",
+            "n_gpus": args.gpus, "steps": done, "warmup": 0,
+            "ms_per_step": 1e3 / rate, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "particles": n, "lb_nodes": d["nnodes"]},
+            "cpu_baseline": {"value": rate, "unit": "hybrid steps/s", "cores": 1,
+                             "kind": "oracle",
+                             "sample": "%d hybrid steps of the full workload (time-bounded)" % done},
+            "e2e": {"value": rate, "unit": "hybrid steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    import __graft_entry__ as G
+    G.build() if rank == 0 else None
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        dist = tdist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        dist.barrier()
+        if rank != 0:
+            G.build()
+    from paper_1512_08042_gb300 import binding as B
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    h = B.Hybrid(cfg, device=dev)
+    d = h.d
+    n_particles = d["ncells"] * cfg["ppc"]
+    nodes = torch.from_numpy(nodes_np).to(dev)
+    cells = torch.from_numpy(cells_np).to(dev)
+    use_graph = not args.no_graph
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = h.stream
+
+    def step():
+        h.hybrid_step(nodes, cells, nsteps=1, use_graph=use_graph)
+
+    # warm-up, and pick the dominant kernel by timing each one over a few steps
+    for _ in range(args.warmup):
+        step()
+    h.sync()
+    kernel_ms = {}
+    for name, kid in B.KERNELS.items():
+        h.profile(kid)
+        h.profile_harvest()
+        ms0, n0 = h.profile_read()
+        for _ in range(3):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            step()
+            h.profile_harvest()
+        ms1, n1 = h.profile_read()
+        kernel_ms[name] = (ms1 - ms0) / max(1, n1 - n0)
+    dominant = args.profile_kernel or max(kernel_ms, key=kernel_ms.get)
+    h.profile(B.KERNELS[dominant])
+    h.profile_harvest()
+    kms0, kn0 = h.profile_read()
+
+    # timed region
+    clock_lines, stop = [], threading.Event()
+    th = threading.Thread(target=sample_clocks, args=(stop, clock_lines), daemon=True)
+    th.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        starts[k].record(stream)
+        step()
+        ends[k].record(stream)
+        h.profile_harvest()
+    torch.cuda.synchronize(dev)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    stop.set()
+    th.join(timeout=5)
+    kms1, kn1 = h.profile_read()
+    dom_ms = (kms1 - kms0) / max(1, kn1 - kn0)
+    rc, bits = h.sync_status()
+
+    # end to end through the public API: host lists in, strip moments out, every step
+    pin_nodes = torch.from_numpy(nodes_np).pin_memory()
+    pin_cells = torch.from_numpy(cells_np).pin_memory()
+    out_acc = torch.empty(len(cells_np), 20, dtype=torch.float64).pin_memory()
+    out_status = torch.empty(16, dtype=torch.int32).pin_memory()
+    cells_long = cells.long()
+    e2e_steps = max(10, args.steps // 2)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        with torch.cuda.stream(stream):
+            nodes.copy_(pin_nodes, non_blocking=True)
+            cells.copy_(pin_cells, non_blocking=True)
+        step()
+        with torch.cuda.stream(stream):
+            out_acc.copy_(h.acc().index_select(0, cells_long), non_blocking=True)
+            out_status.copy_(h.ctrl(), non_blocking=True)
+        stream.synchronize()
+    e2e_s = time.perf_counter() - t0
+    h2d = pin_nodes.numel() * 4 + pin_cells.numel() * 4
+    d2h = out_acc.numel() * 8 + out_status.numel() * 4
+
+    value = world * args.steps / (total_ms / 1e3)
+    peak, peak_kind = measured_peak_hbm()
+    alg = kernel_algorithmic_bytes(dominant, cfg, d, n_particles, len(nodes_np), len(cells_np))
+    achieved = alg / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else None
+    line = {
+        "metric": METRIC, "value": value, "unit": "hybrid steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if cfg["real_bytes"] == 4 else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "particles": n_particles, "lb_nodes": d["nnodes"],
+                   "lattice": "D3Q%d" % d["q"], "coupling_nodes": len(nodes_np),
+                   "coupling_cells": len(cells_np), "graph": use_graph,
+                   "l2": "flushed before every timed step (512 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "dsmc_particle_updates_per_s": value * n_particles,
+        "lbm_mlups": value * d["nnodes"] / 1e6,
+        "roofline": {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": achieved / peak if achieved else None,
+                     "algorithmic_bytes_per_launch": alg, "ms_per_launch": dom_ms,
+                     "traffic": traffic_record(dominant)},
+        "kernel_ms": kernel_ms,
+        "clocks": summarize_clocks(clock_lines),
+        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+        "status": {"code": rc, "bits": bits},
+        "e2e": {"value": world * e2e_steps / e2e_s, "unit": "hybrid steps/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+    }
+    if rank == 0 and world == 1:
+        from oracle import build as OB
+        OB.build()
+        rate, done = run_oracle(cfg, 10 ** 9, args.cpu_budget)
+        line["cpu_baseline"] = {"value": rate, "unit": "hybrid steps/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": "%d hybrid steps of the full workload, FP%d oracle, "
+                                          "single thread, %.0f s budget"
+                                          % (done, 8 * cfg["real_bytes"], args.cpu_budget)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,227 @@
+/*
+ * dsmclbm.h - C ABI of the GB300 (sm_103a) hot path of the hybrid DSMC-LBM method of
+ * Di Staso, Clercx, Succi and Toschi, "DSMC-LBM mapping scheme for rarefied and
+ * non-rarefied gas flows" (arXiv 1512.08042).
+ *
+ * The library advances a force-driven plane channel (Sec. 3.1) with two solvers and maps
+ * between them (Sec. 2):
+ *   dsmc_step        DSMC of a hard-sphere gas: move with diffuse isothermal walls, stable
+ *                    counting sort by cell, no-time-counter collisions (Sec. 5,
+ *                    Eq. collisionnumber), per-cell Hermite-moment sampling.
+ *   lbm_step         regularised BGK lattice Boltzmann on D3Q39 (Hermite order 3) or D3Q19
+ *                    (order 2) with kinetic walls and a body force (Sec. 2 "ingredients",
+ *                    Sec. 3.1, Eq. tau).
+ *   map_dsmc_to_lbm  DSMC2LB projection (Sec. 2.1, Eq. discretefunctions).
+ *   map_lbm_to_dsmc  LB2DSMC reconstruction by acceptance-rejection (Sec. 2.2, Table 1).
+ *   sample_moments   the cumulative DSMC moment sums the projection reads (Sec. 2.1, Fig. 1).
+ *
+ * Units: lengths in DSMC cells, velocities in c_th = sqrt(kT/m) (Hermite units, unit-variance
+ * weight function of Eq. globalMax), one DSMC step = one LB step = T0 of Appendix A with the
+ * isothermal sound speed. LB density 1 corresponds to `ppc` particles per DSMC cell.
+ *
+ * Memory: the caller owns all device memory. It allocates one arena of
+ * hyb_layout.total_bytes (256-byte aligned) on the device and passes it to dsmc_init; the
+ * library keeps a borrowed pointer for the context's lifetime and never frees it. Byte
+ * offsets of every array inside the arena are given by hyb_layout_compute, so the caller can
+ * read and write state directly (e.g. through torch tensors).
+ *
+ * Streams: every call that launches work enqueues it on the stream given to dsmc_init and
+ * returns without synchronising, except the functions marked "synchronises". Argument errors
+ * return HYB_EINVAL and launch nothing. Errors found on the device (capacity overflow, a
+ * capped device loop, a bad coupling index) are recorded in a sticky status word that
+ * hyb_sync_status reads. No C++ exception and no exit() crosses this interface.
+ */
+#ifndef DSMCLBM_H
+#define DSMCLBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HYB_ABI_VERSION 1u
+
+typedef enum {
+    HYB_OK = 0,
+    HYB_EINVAL = 1,     /* invalid argument; nothing was launched */
+    HYB_ENOMEM = 2,     /* arena too small */
+    HYB_ECUDA = 3,      /* a CUDA runtime call failed; see hyb_last_error */
+    HYB_ECAPACITY = 4,  /* particle capacity or per-cell bound exceeded on the device */
+    HYB_ETIMEOUT = 5,   /* a capped device loop (wall bounces, scattering draws) hit its cap */
+    HYB_ESAMPLING = 6,  /* LB2DSMC acceptance-rejection hit its attempt cap */
+    HYB_ESTATE = 7      /* call out of order (e.g. graph capture already in progress) */
+} hyb_status;
+
+/* Bits of the sticky device status word. */
+#define HYB_ST_CAPACITY (1u << 0)      /* appended particles would exceed capacity */
+#define HYB_ST_BOUNCE_CAP (1u << 1)    /* a particle hit the walls more than 8 times in a step */
+#define HYB_ST_SCATTER_CAP (1u << 2)   /* 32 Marsaglia draws rejected in a row */
+#define HYB_ST_SAMPLING_CAP (1u << 3)  /* 1000 LB2DSMC trials rejected in a row */
+#define HYB_ST_CELL_OVERFLOW (1u << 4) /* more than 2^24 NTC candidates in one cell */
+#define HYB_ST_BAD_INPUT (1u << 5)     /* coupling index out of range, or no DSMC samples */
+
+/* Counters (hyb_read_counters): index meaning. */
+#define HYB_C_WALL_HITS 0
+#define HYB_C_CANDIDATES 1
+#define HYB_C_COLLISIONS 2
+#define HYB_C_CREATED 3
+#define HYB_C_DELETED 4
+#define HYB_C_L2D_ATTEMPTS 5
+#define HYB_C_ENVELOPE 6   /* trials with G > C, which the envelope C g0 does not cover */
+#define HYB_C_BOUNCE_CAP 7
+#define HYB_NCOUNTERS 16
+
+/* Problem parameters (plain data; the library copies it). */
+typedef struct {
+    uint32_t abi_version;   /* HYB_ABI_VERSION */
+    int32_t ncx;            /* DSMC cells across the channel; walls at x = 0 and x = ncx (>= 6) */
+    int32_t ncy;            /* DSMC cells streamwise, periodic (>= 1) */
+    int32_t lb_ratio;       /* LB nodes per DSMC cell per axis: 1 or 2 */
+    int32_t ppc;            /* particles per cell at initialisation (>= 1) */
+    int32_t lattice;        /* 39: D3Q39, Hermite order 3; 19: D3Q19, order 2 */
+    int32_t real_bytes;     /* 4: float particle and population state; 8: double */
+    int32_t sample_every;   /* moments sampled every `sample_every` DSMC steps (>= 1) */
+    uint64_t seed;          /* Philox key */
+    double kn;              /* Knudsen number on the channel height (> 0) */
+    double ma;              /* Mach number of the no-slip centreline velocity, u_max / c_s */
+    double crmax_init;      /* initial (sigma_T c_r)_max / sigma_T in c_th units (> 0) */
+    double capacity_factor; /* particle capacity = ceil(capacity_factor * ncx * ncy * ppc) */
+    double T_K;             /* temperature [K], for SI conversion only */
+    double mass_kg;         /* molecular mass [kg], for SI conversion only */
+} hyb_params;
+
+/* Constants derived from hyb_params (hyb_derive). */
+typedef struct {
+    double r_lat;    /* c / c_s of the lattice: sqrt(3/2) (D3Q39) or sqrt(3) (D3Q19) */
+    double cs_lat;   /* lattice sound speed in lattice units, 1 / r_lat */
+    double H_lat;    /* LB nodes across the channel */
+    double tau;      /* relaxation time, Eq. tau: sqrt(pi/8) (c/c_s) Kn H + 1/2 */
+    double dt;       /* step in cell / c_th units: cs_lat / lb_ratio */
+    double lambda;   /* mean free path in DSMC cells: Kn * ncx */
+    double coll_dt;  /* F_N sigma_T dt / V_c of Eq. collisionnumber: dt / (sqrt(2) lambda ppc) */
+    double g_step;   /* body-force velocity increment per step, 8 (tau-1/2) Ma cs^2 / H^2 */
+    double c_th_ms;  /* sqrt(k T / m) [m/s] */
+    int64_t ncells, nx, ny, nnodes, capacity;
+    int32_t q, order;
+} hyb_derived;
+
+/* Byte offsets of the arrays inside the caller's arena (hyb_layout_compute). Arrays marked
+ * [2] are ping-pong pairs; hyb_current says which half holds the current state. Real is
+ * float or double per real_bytes.
+ *   x, y          Real[capacity]   positions in cell units (x across, y streamwise);
+ *                                  x < 0 marks a deleted particle
+ *   vx, vy, vz    Real[capacity]   velocities in c_th units
+ *   key           u32[capacity]    cell of each slot after the move (0xFFFFFFFF deleted)
+ *   arrival       u32[capacity]    arrival index of each slot in its new cell
+ *   perm          u32[capacity]    old slot of each new position
+ *   count         u32[ncells]      particles per cell (zero between steps)
+ *   cell_start    u32[ncells + 1]  first slot of each cell in the current buffer
+ *   tile_sum      u32[ntiles]      per-tile sums of `count` (scan scratch)
+ *   crmax         Real[ncells]     (sigma_T c_r)_max / sigma_T per cell
+ *   rem           f64[ncells]      NTC fractional candidate carried between steps
+ *   nbar_sum      f64[ncells]      running sum of N per cell, for N-bar
+ *   acc           f64[ncells][20]  cumulative sums N, S v (3), S vv (6: xx xy xz yy yz zz),
+ *                                  S vvv (10: xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz)
+ *   f             Real[q][ny][nx]  populations, x fastest; f[2]
+ *   ctrl          u32[16]          [0] status bits, [1] particle slots in use, [2] DSMC
+ *                                  steps taken, [3] moment samples taken, [4]..[7] scratch
+ *   counters      u64[16]          event counters, HYB_C_*
+ *   map_scratch                    LB2DSMC per-cell records */
+typedef struct {
+    uint64_t total_bytes;
+    int64_t capacity, ncells, nnodes, ntiles;
+    int32_t q, real_bytes;
+    uint64_t x[2], y[2], vx[2], vy[2], vz[2];
+    uint64_t key, arrival, perm, count, cell_start, tile_sum;
+    uint64_t crmax, rem, nbar_sum, acc;
+    uint64_t f[2];
+    uint64_t ctrl, counters, map_scratch;
+} hyb_layout;
+
+typedef struct hyb_ctx hyb_ctx; /* opaque, owned by the library */
+
+/* Host-only helpers (no GPU needed). Return HYB_EINVAL for invalid parameters. */
+hyb_status hyb_derive(const hyb_params* p, hyb_derived* out);
+hyb_status hyb_layout_compute(const hyb_params* p, hyb_layout* out);
+/* The library's lattice: e[q][3] integer speeds, w[q] weights, r = c/c_s. Row order is the
+ * population layout. `q` is 39 or 19; e and w must hold q rows. */
+hyb_status hyb_lattice(int32_t q, int32_t* e, double* w, double* r);
+const char* hyb_status_string(hyb_status s);
+
+/* Create a context on the current CUDA device and initialise the state in `arena`:
+ * ppc particles per cell, uniform inside the cell, Maxwellian at T (Sec. 3.1 "100
+ * computational molecules are initially placed in each cell"), and the LB populations at
+ * rest with density 1. `arena` is device memory of at least hyb_layout.total_bytes,
+ * 256-byte aligned, owned by the caller. `stream` is a cudaStream_t (NULL: legacy default
+ * stream; graph replay needs a non-default stream). On success *out owns the context. */
+hyb_status dsmc_init(const hyb_params* p, void* arena, uint64_t arena_bytes, void* stream,
+                     hyb_ctx** out);
+
+/* `nsteps` DSMC steps (Sec. 5; the NTC order move -> index -> collide -> sample).
+ * Draws are keyed by (seed; slot or cell, step, purpose, index). */
+hyb_status dsmc_step(hyb_ctx* ctx, int32_t nsteps);
+
+/* `nsteps` LB stream-collide steps (Sec. 2, Sec. 3.1). */
+hyb_status lbm_step(hyb_ctx* ctx, int32_t nsteps);
+
+/* Copy the cumulative moment sums acc[ncells][20] into `out` (device memory, may be NULL)
+ * and, if `reset`, zero the sums and the sample count. The sums are ordered as in acc. */
+hyb_status sample_moments(hyb_ctx* ctx, double* out, int32_t reset);
+
+/* DSMC2LB (Sec. 2.1): for each LB node in dev_nodes[n] (device int32, node = y * nx + x,
+ * distinct), overwrite its populations with the projection of the cumulative moments of the
+ * DSMC cell that contains it: f_a = w_a sum_{n<=N} a^(n) : H^(n)(xi_a) / n! (Eq.
+ * discretefunctions), a^(n) the raw Hermite coefficients of the sampled moments (FP64). */
+hyb_status map_dsmc_to_lbm(hyb_ctx* ctx, const int32_t* dev_nodes, int32_t n);
+
+/* LB2DSMC (Sec. 2.2, Table 1): for each DSMC cell in dev_cells[n] (device int32,
+ * cell = iy * ncx + ix, distinct), delete its particles and append floor(rho ppc + U) new
+ * ones, with rho the mean LB density of the cell's lb_ratio^2 nodes; velocities drawn from
+ * the Grad distribution of the cell's populations by acceptance-rejection with envelope
+ * C = 1 + 30 M; positions uniform in the cell. Call at most once between two dsmc_step
+ * calls (deletion uses the cell layout of the last step). */
+hyb_status map_lbm_to_dsmc(hyb_ctx* ctx, const int32_t* dev_cells, int32_t n);
+
+/* One or more hybrid steps: dsmc_step(1), map_dsmc_to_lbm, lbm_step(1), map_lbm_to_dsmc.
+ * n_nodes or n_cells may be 0 to skip a mapping. With use_graph != 0 each step is replayed
+ * from a CUDA graph captured on first use (one per ping-pong parity; recaptured if the
+ * arguments change); the stream must not be the legacy default stream. */
+hyb_status hyb_hybrid_step(hyb_ctx* ctx, const int32_t* dev_nodes, int32_t n_nodes,
+                           const int32_t* dev_cells, int32_t n_cells, int32_t nsteps,
+                           int32_t use_graph);
+
+/* Which ping-pong halves hold the current particle and population state (0 or 1). */
+hyb_status hyb_current(const hyb_ctx* ctx, int32_t* particle_half, int32_t* lb_half);
+
+/* Synchronises. Returns the sticky device status mapped to a hyb_status (HYB_OK if clear),
+ * and the raw bits in *bits if not NULL. */
+hyb_status hyb_sync_status(hyb_ctx* ctx, uint32_t* bits);
+
+/* Synchronises. Copies the HYB_NCOUNTERS event counters into out (host memory). */
+hyb_status hyb_read_counters(hyb_ctx* ctx, uint64_t* out);
+
+/* Kernel timing on the context's stream: after hyb_profile(ctx, k) every launch of kernel k
+ * (0 move, 1 tile sums, 2 scan, 3 rank, 4 collide, 5 lbm, 6 dsmc2lb, 7 lb2dsmc prepare,
+ * 8 lb2dsmc sample; -1 off) is bracketed by CUDA events. hyb_profile_harvest synchronises
+ * and adds the elapsed times of the launches since the last harvest; call it after every
+ * hybrid step when graphs are used. hyb_profile_read returns the totals. */
+hyb_status hyb_profile(hyb_ctx* ctx, int32_t kernel);
+hyb_status hyb_profile_harvest(hyb_ctx* ctx);
+hyb_status hyb_profile_read(const hyb_ctx* ctx, double* total_ms, int64_t* launches);
+
+/* Philox4x32-10 (Salmon et al., SC'11) on the device: out[4i..4i+3] = Philox(ctr[4i..4i+3],
+ * key = (seed, seed >> 32)), for checking the generator against an independent one.
+ * ctr and out are device pointers of n * 4 u32. */
+hyb_status hyb_debug_philox(const uint32_t* dev_ctr, uint64_t seed, uint32_t* dev_out, int64_t n,
+                            void* stream);
+
+const char* hyb_last_error(const hyb_ctx* ctx);
+/* Synchronises the stream, releases graphs and events; does not touch the arena. */
+void hyb_destroy(hyb_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DSMCLBM_H */

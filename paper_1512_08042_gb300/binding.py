@@ -1,0 +1,318 @@
+"""Thin ctypes binding of libdsmclbm.so (C ABI in include/dsmclbm.h).
+
+Only argument marshalling lives here: PyTorch allocates the device arena and provides the
+stream; every step of the method runs in the library's CUDA kernels. There is no CPU
+fallback: if the library is missing or cannot be loaded, `lib()` raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libdsmclbm.so")
+ABI_VERSION = 1
+
+HYB_OK, HYB_EINVAL, HYB_ENOMEM, HYB_ECUDA, HYB_ECAPACITY, HYB_ETIMEOUT, HYB_ESAMPLING, HYB_ESTATE = range(8)
+ST_CAPACITY, ST_BOUNCE_CAP, ST_SCATTER_CAP, ST_SAMPLING_CAP, ST_CELL_OVERFLOW, ST_BAD_INPUT = (
+    1, 2, 4, 8, 16, 32)
+COUNTER_NAMES = ["wall_hits", "candidates", "collisions", "created", "deleted",
+                 "l2d_attempts", "envelope", "bounce_cap"]
+KERNELS = {"move": 0, "tile_sums": 1, "scan": 2, "rank": 3, "collide": 4, "lbm": 5,
+           "dsmc2lb": 6, "lb2dsmc_prep": 7, "lb2dsmc_sample": 8}
+CTRL_STATUS, CTRL_NTOT, CTRL_STEP, CTRL_NSAMPLES = 0, 1, 2, 3
+
+_u32, _i32, _i64, _u64, _dbl, _vp = (ctypes.c_uint32, ctypes.c_int32, ctypes.c_int64,
+                                     ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p)
+
+
+class HybParams(ctypes.Structure):
+    _fields_ = [("abi_version", _u32), ("ncx", _i32), ("ncy", _i32), ("lb_ratio", _i32),
+                ("ppc", _i32), ("lattice", _i32), ("real_bytes", _i32), ("sample_every", _i32),
+                ("seed", _u64), ("kn", _dbl), ("ma", _dbl), ("crmax_init", _dbl),
+                ("capacity_factor", _dbl), ("T_K", _dbl), ("mass_kg", _dbl)]
+
+
+class HybDerived(ctypes.Structure):
+    _fields_ = [("r_lat", _dbl), ("cs_lat", _dbl), ("H_lat", _dbl), ("tau", _dbl), ("dt", _dbl),
+                ("lam", _dbl), ("coll_dt", _dbl), ("g_step", _dbl), ("c_th_ms", _dbl),
+                ("ncells", _i64), ("nx", _i64), ("ny", _i64), ("nnodes", _i64),
+                ("capacity", _i64), ("q", _i32), ("order", _i32)]
+
+
+class HybLayout(ctypes.Structure):
+    _fields_ = [("total_bytes", _u64), ("capacity", _i64), ("ncells", _i64), ("nnodes", _i64),
+                ("ntiles", _i64), ("q", _i32), ("real_bytes", _i32),
+                ("x", _u64 * 2), ("y", _u64 * 2), ("vx", _u64 * 2), ("vy", _u64 * 2),
+                ("vz", _u64 * 2), ("key", _u64), ("arrival", _u64), ("perm", _u64),
+                ("count", _u64), ("cell_start", _u64), ("tile_sum", _u64), ("crmax", _u64),
+                ("rem", _u64), ("nbar_sum", _u64), ("acc", _u64), ("f", _u64 * 2),
+                ("ctrl", _u64), ("counters", _u64), ("map_scratch", _u64)]
+
+
+EXPORTS = ["hyb_derive", "hyb_layout_compute", "hyb_lattice", "hyb_status_string", "dsmc_init",
+           "dsmc_step", "lbm_step", "sample_moments", "map_dsmc_to_lbm", "map_lbm_to_dsmc",
+           "hyb_hybrid_step", "hyb_current", "hyb_sync_status", "hyb_read_counters",
+           "hyb_profile", "hyb_profile_harvest", "hyb_profile_read", "hyb_debug_philox",
+           "hyb_last_error", "hyb_destroy"]
+
+_LIB = None
+
+
+class HybError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__("%s (status %d)%s" % (_status_str(status), status,
+                                               (": " + msg) if msg else ""))
+
+
+def _status_str(s):
+    try:
+        return lib().hyb_status_string(s).decode()
+    except Exception:
+        return "status"
+
+
+def lib():
+    """Load libdsmclbm.so; raise if it has not been built."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libdsmclbm.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    L.hyb_derive.argtypes = [P(HybParams), P(HybDerived)]
+    L.hyb_layout_compute.argtypes = [P(HybParams), P(HybLayout)]
+    L.hyb_lattice.argtypes = [_i32, _vp, _vp, P(_dbl)]
+    L.hyb_status_string.argtypes = [ctypes.c_int]
+    L.hyb_status_string.restype = ctypes.c_char_p
+    L.dsmc_init.argtypes = [P(HybParams), _vp, _u64, _vp, P(_vp)]
+    L.dsmc_step.argtypes = [_vp, _i32]
+    L.lbm_step.argtypes = [_vp, _i32]
+    L.sample_moments.argtypes = [_vp, _vp, _i32]
+    L.map_dsmc_to_lbm.argtypes = [_vp, _vp, _i32]
+    L.map_lbm_to_dsmc.argtypes = [_vp, _vp, _i32]
+    L.hyb_hybrid_step.argtypes = [_vp, _vp, _i32, _vp, _i32, _i32, _i32]
+    L.hyb_current.argtypes = [_vp, P(_i32), P(_i32)]
+    L.hyb_sync_status.argtypes = [_vp, P(_u32)]
+    L.hyb_read_counters.argtypes = [_vp, _vp]
+    L.hyb_profile.argtypes = [_vp, _i32]
+    L.hyb_profile_harvest.argtypes = [_vp]
+    L.hyb_profile_read.argtypes = [_vp, P(_dbl), P(_i64)]
+    L.hyb_debug_philox.argtypes = [_vp, _u64, _vp, _i64, _vp]
+    L.hyb_last_error.argtypes = [_vp]
+    L.hyb_last_error.restype = ctypes.c_char_p
+    L.hyb_destroy.argtypes = [_vp]
+    L.hyb_destroy.restype = None
+    _LIB = L
+    return L
+
+
+def make_params(cfg):
+    p = HybParams()
+    p.abi_version = ABI_VERSION
+    for name, _ in HybParams._fields_:
+        if name != "abi_version" and name in cfg:
+            setattr(p, name, cfg[name])
+    return p
+
+
+def _check(rc, ctx=None):
+    if rc != HYB_OK:
+        msg = lib().hyb_last_error(ctx).decode() if ctx else ""
+        raise HybError(rc, msg)
+
+
+def derive(cfg):
+    d = HybDerived()
+    _check(lib().hyb_derive(ctypes.byref(make_params(cfg)), ctypes.byref(d)))
+    return {n: getattr(d, n) for n, _ in HybDerived._fields_}
+
+
+def layout(cfg):
+    L = HybLayout()
+    _check(lib().hyb_layout_compute(ctypes.byref(make_params(cfg)), ctypes.byref(L)))
+    return L
+
+
+def lattice(q):
+    e = np.zeros((q, 3), np.int32)
+    w = np.zeros(q, np.float64)
+    r = ctypes.c_double()
+    _check(lib().hyb_lattice(q, e.ctypes.data_as(_vp), w.ctypes.data_as(_vp), ctypes.byref(r)))
+    return e, w, r.value
+
+
+def debug_philox(ctr_dev, seed, out_dev, stream_ptr=0):
+    """Philox4x32-10 of device u32 counters [n, 4] into out_dev [n, 4] (torch tensors)."""
+    n = ctr_dev.numel() // 4
+    _check(lib().hyb_debug_philox(ctr_dev.data_ptr(), seed, out_dev.data_ptr(), n, stream_ptr))
+
+
+class Hybrid:
+    """One channel: DSMC particles, LB populations and the mappings, on one GPU.
+
+    The state lives in a torch uint8 arena on `device`; the library launches on `stream`
+    (a dedicated torch.cuda.Stream by default). Methods enqueue work and return; use
+    `sync()` (or a synchronising call) before reading views from another stream.
+    """
+
+    def __init__(self, cfg, device="cuda:0", stream=None):
+        import torch
+        self.torch = torch
+        self.cfg = dict(cfg)
+        self.device = torch.device(device)
+        self.params = make_params(cfg)
+        self.d = derive(cfg)
+        self.L = layout(cfg)
+        self.real = torch.float32 if cfg["real_bytes"] == 4 else torch.float64
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+            self.arena = torch.empty(int(self.L.total_bytes), dtype=torch.uint8, device=self.device)
+        torch.cuda.synchronize(self.device)
+        ctx = _vp()
+        with torch.cuda.device(self.device):
+            rc = lib().dsmc_init(ctypes.byref(self.params), self.arena.data_ptr(),
+                                 int(self.L.total_bytes), self.stream.cuda_stream, ctypes.byref(ctx))
+        _check(rc)
+        self.ctx = ctx
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib().hyb_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- steps -------------------------------------------------------------------------
+    def dsmc_step(self, n=1):
+        _check(lib().dsmc_step(self.ctx, n), self.ctx)
+
+    def lbm_step(self, n=1):
+        _check(lib().lbm_step(self.ctx, n), self.ctx)
+
+    def map_dsmc_to_lbm(self, nodes):
+        _check(lib().map_dsmc_to_lbm(self.ctx, nodes.data_ptr(), nodes.numel()), self.ctx)
+
+    def map_lbm_to_dsmc(self, cells):
+        _check(lib().map_lbm_to_dsmc(self.ctx, cells.data_ptr(), cells.numel()), self.ctx)
+
+    def hybrid_step(self, nodes=None, cells=None, nsteps=1, use_graph=True):
+        np_ = nodes.data_ptr() if nodes is not None else None
+        cp_ = cells.data_ptr() if cells is not None else None
+        nn = nodes.numel() if nodes is not None else 0
+        nc = cells.numel() if cells is not None else 0
+        _check(lib().hyb_hybrid_step(self.ctx, np_, nn, cp_, nc, nsteps, 1 if use_graph else 0),
+               self.ctx)
+
+    def sample_moments(self, out=None, reset=False):
+        ptr = out.data_ptr() if out is not None else None
+        _check(lib().sample_moments(self.ctx, ptr, 1 if reset else 0), self.ctx)
+
+    # -- status ------------------------------------------------------------------------
+    def sync(self):
+        self.stream.synchronize()
+
+    def sync_status(self):
+        bits = _u32()
+        rc = lib().hyb_sync_status(self.ctx, ctypes.byref(bits))
+        return rc, bits.value
+
+    def counters(self):
+        out = np.zeros(16, np.uint64)
+        _check(lib().hyb_read_counters(self.ctx, out.ctypes.data_as(_vp)), self.ctx)
+        return {n: int(out[i]) for i, n in enumerate(COUNTER_NAMES)}
+
+    def current(self):
+        p, f = _i32(), _i32()
+        _check(lib().hyb_current(self.ctx, ctypes.byref(p), ctypes.byref(f)))
+        return p.value, f.value
+
+    def profile(self, kernel):
+        _check(lib().hyb_profile(self.ctx, KERNELS[kernel] if isinstance(kernel, str) else kernel))
+
+    def profile_harvest(self):
+        _check(lib().hyb_profile_harvest(self.ctx), self.ctx)
+
+    def profile_read(self):
+        ms, n = _dbl(), _i64()
+        _check(lib().hyb_profile_read(self.ctx, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    # -- views into the arena ----------------------------------------------------------
+    def _view(self, off, count, dtype):
+        torch = self.torch
+        esize = torch.empty((), dtype=dtype).element_size()
+        return self.arena[int(off):int(off) + int(count) * esize].view(dtype)
+
+    def ctrl(self):
+        return self._view(self.L.ctrl, 16, self.torch.int32)
+
+    def n_tot(self):
+        self.sync()
+        return int(self.ctrl()[CTRL_NTOT].item())
+
+    def particle_arrays(self, half=None):
+        h = self.current()[0] if half is None else half
+        cap = self.L.capacity
+        return {k: self._view(getattr(self.L, k)[h], cap, self.real)
+                for k in ("x", "y", "vx", "vy", "vz")}
+
+    def particles(self):
+        """Current particle arrays sliced to the slots in use (views)."""
+        n = self.n_tot()
+        return {k: v[:n] for k, v in self.particle_arrays().items()}
+
+    def cell_start(self):
+        return self._view(self.L.cell_start, self.L.ncells + 1, self.torch.int32)
+
+    def acc(self):
+        return self._view(self.L.acc, self.L.ncells * 20, self.torch.float64).view(-1, 20)
+
+    def crmax(self):
+        return self._view(self.L.crmax, self.L.ncells, self.real)
+
+    def f(self, half=None):
+        h = self.current()[1] if half is None else half
+        q, ny, nx = self.d["q"], self.d["ny"], self.d["nx"]
+        return self._view(self.L.f[h], q * nx * ny, self.real).view(q, ny, nx)
+
+    # -- state transfer (checkpoint / restore, synthetic states) ------------------------
+    def load_particles(self, x, y, vx, vy, vz, cell_start):
+        """Write a cell-ordered particle set into the current half (host or device arrays)."""
+        torch = self.torch
+        n = len(x)
+        if n > self.L.capacity:
+            raise ValueError("more particles than capacity")
+        arr = self.particle_arrays()
+        for k, v in (("x", x), ("y", y), ("vx", vx), ("vy", vy), ("vz", vz)):
+            arr[k][:n].copy_(torch.as_tensor(np.asarray(v), dtype=self.real))
+        self.cell_start().copy_(torch.as_tensor(np.asarray(cell_start, np.int64).astype(np.int32)))
+        self.ctrl()[CTRL_NTOT] = n
+        torch.cuda.synchronize(self.device)
+
+    def set_counters(self, step=None, nsamples=None):
+        if step is not None:
+            self.ctrl()[CTRL_STEP] = int(step)
+        if nsamples is not None:
+            self.ctrl()[CTRL_NSAMPLES] = int(nsamples)
+        self.torch.cuda.synchronize(self.device)
+
+    def save_state(self):
+        """Host copy of the whole arena plus the ping-pong parities (bit-exact resume)."""
+        self.sync()
+        return {"arena": self.arena.cpu(), "current": self.current(), "cfg": dict(self.cfg)}
+
+    def load_state(self, state):
+        if state["cfg"] != self.cfg:
+            raise ValueError("state was saved for different parameters")
+        if tuple(state["current"]) != self.current():
+            raise ValueError("restore into a context with the same ping-pong parity")
+        self.sync()
+        self.arena.copy_(state["arena"].to(self.device))
+        self.torch.cuda.synchronize(self.device)

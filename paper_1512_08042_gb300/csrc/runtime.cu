@@ -1,0 +1,526 @@
+// Host runtime of the DSMC-LBM library: parameter validation, derived constants, arena
+// layout, context lifetime, launch sequencing, CUDA-graph replay of a hybrid step, kernel
+// timing and error reporting. Every entry point of include/dsmclbm.h is defined here.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "hyb_internal.cuh"
+
+using namespace hyb;
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+const double kBoltzmann = 1.380649e-23;
+
+bool params_valid(const hyb_params* p) {
+    if (!p || p->abi_version != HYB_ABI_VERSION) return false;
+    if (p->ncx < 6 || p->ncy < 1 || (p->lb_ratio != 1 && p->lb_ratio != 2) || p->ppc < 1) return false;
+    if (p->lattice != 39 && p->lattice != 19) return false;
+    if (p->real_bytes != 4 && p->real_bytes != 8) return false;
+    if (p->sample_every < 1) return false;
+    if (!(p->kn > 0.0) || !(p->crmax_init > 0.0) || !(p->capacity_factor >= 1.0)) return false;
+    if (!(p->ma >= 0.0) || !(p->T_K > 0.0) || !(p->mass_kg > 0.0)) return false;
+    const double cap = std::ceil(p->capacity_factor * (double)p->ncx * (double)p->ncy * (double)p->ppc);
+    if (cap >= 4294967295.0) return false;          // slot indices are u32
+    if ((double)p->ncx * p->ncy >= 4294967295.0) return false;
+    return true;
+}
+
+// Same definitions as the derived-constant list in dsmclbm.h: Eq. tau, Eq. MFP in cell
+// units, the NTC factor of Eq. collisionnumber, and the no-slip parabola of Sec. 3.1.
+void derive(const hyb_params& p, hyb_derived& d) {
+    std::memset(&d, 0, sizeof(d));
+    d.r_lat = (p.lattice == 39) ? std::sqrt(1.5) : std::sqrt(3.0);
+    d.cs_lat = 1.0 / d.r_lat;
+    d.H_lat = (double)p.ncx * (double)p.lb_ratio;
+    d.tau = std::sqrt(kPi / 8.0) * d.r_lat * p.kn * d.H_lat + 0.5;
+    d.dt = d.cs_lat / (double)p.lb_ratio;
+    d.lambda = p.kn * (double)p.ncx;
+    d.coll_dt = d.dt / (std::sqrt(2.0) * d.lambda * (double)p.ppc);
+    d.g_step = 8.0 * (d.tau - 0.5) * p.ma * d.cs_lat * d.cs_lat / (d.H_lat * d.H_lat);
+    d.c_th_ms = std::sqrt(kBoltzmann * p.T_K / p.mass_kg);
+    d.ncells = (int64_t)p.ncx * p.ncy;
+    d.nx = (int64_t)p.ncx * p.lb_ratio;
+    d.ny = (int64_t)p.ncy * p.lb_ratio;
+    d.nnodes = d.nx * d.ny;
+    d.capacity = (int64_t)std::ceil(p.capacity_factor * (double)d.ncells * (double)p.ppc);
+    d.q = p.lattice;
+    d.order = (p.lattice == 39) ? 3 : 2;
+}
+
+void layout(const hyb_params& p, const hyb_derived& d, hyb_layout& L) {
+    std::memset(&L, 0, sizeof(L));
+    const uint64_t rb = (uint64_t)p.real_bytes;
+    const uint64_t cap = (uint64_t)d.capacity, nc = (uint64_t)d.ncells, nn = (uint64_t)d.nnodes;
+    const uint64_t q = (uint64_t)d.q;
+    const uint64_t ntiles = (nc + kScanTile - 1) / kScanTile;
+    uint64_t off = 0;
+    auto take = [&](uint64_t bytes) {
+        const uint64_t o = off;
+        off = (off + bytes + 255) & ~255ull;
+        return o;
+    };
+    for (int h = 0; h < 2; ++h) {
+        L.x[h] = take(cap * rb);
+        L.y[h] = take(cap * rb);
+        L.vx[h] = take(cap * rb);
+        L.vy[h] = take(cap * rb);
+        L.vz[h] = take(cap * rb);
+    }
+    L.key = take(cap * 4);
+    L.arrival = take(cap * 4);
+    L.perm = take(cap * 4);
+    L.count = take(nc * 4);
+    L.cell_start = take((nc + 1) * 4);
+    L.tile_sum = take(ntiles * 4);
+    L.crmax = take(nc * rb);
+    L.rem = take(nc * 8);
+    L.nbar_sum = take(nc * 8);
+    L.acc = take(nc * kMoments * 8);
+    for (int h = 0; h < 2; ++h) L.f[h] = take(q * nn * rb);
+    L.ctrl = take(CTRL_WORDS * 4);
+    L.counters = take(HYB_NCOUNTERS * 8);
+    L.map_scratch = take(nc * sizeof(GradRec));
+    L.total_bytes = off;
+    L.capacity = d.capacity;
+    L.ncells = d.ncells;
+    L.nnodes = d.nnodes;
+    L.ntiles = (int64_t)ntiles;
+    L.q = d.q;
+    L.real_bytes = p.real_bytes;
+}
+
+hyb_status fail(Ctx& c, hyb_status s, const char* what, cudaError_t e = cudaSuccess) {
+    c.err = what;
+    if (e != cudaSuccess) {
+        c.err += ": ";
+        c.err += cudaGetErrorString(e);
+    }
+    return s;
+}
+
+hyb_status check(Ctx& c, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return HYB_OK;
+    return fail(c, HYB_ECUDA, what, e);
+}
+
+void flip_particles(Ctx& c) { c.cur_p ^= 1; }
+void flip_populations(Ctx& c) { c.cur_f ^= 1; }
+
+ProfPool& pool_of(Ctx& c) { return c.pool; }
+
+}  // namespace
+
+namespace hyb {
+
+void prof_begin(Ctx& c, int k) {
+    if (c.prof_kernel != k) return;
+    ProfPool& P = pool_of(c);
+    if (c.capturing) {
+        const int s = P.capture_slot;
+        if (!P.ga[s]) {
+            cudaEventCreate(&P.ga[s]);
+            cudaEventCreate(&P.gb[s]);
+        }
+        cudaEventRecordWithFlags(P.ga[s], c.stream, cudaEventRecordExternal);
+        return;
+    }
+    if (P.used == P.a.size()) {
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        P.a.push_back(e0);
+        P.b.push_back(e1);
+    }
+    cudaEventRecord(P.a[P.used], c.stream);
+}
+
+void prof_end(Ctx& c, int k) {
+    if (c.prof_kernel != k) return;
+    ProfPool& P = pool_of(c);
+    if (c.capturing) {
+        cudaEventRecordWithFlags(P.gb[P.capture_slot], c.stream, cudaEventRecordExternal);
+        return;
+    }
+    cudaEventRecord(P.b[P.used], c.stream);
+    P.used += 1;
+}
+
+}  // namespace hyb
+
+namespace {
+
+void resolve(Ctx& c) {
+    char* a = c.arena;
+    const hyb_layout& L = c.L;
+    State& s = c.st;
+    for (int h = 0; h < 2; ++h) {
+        s.px[h] = a + L.x[h];
+        s.py[h] = a + L.y[h];
+        s.pvx[h] = a + L.vx[h];
+        s.pvy[h] = a + L.vy[h];
+        s.pvz[h] = a + L.vz[h];
+        s.f[h] = a + L.f[h];
+    }
+    s.key = (uint32_t*)(a + L.key);
+    s.arrival = (uint32_t*)(a + L.arrival);
+    s.perm = (uint32_t*)(a + L.perm);
+    s.count = (uint32_t*)(a + L.count);
+    s.cell_start = (uint32_t*)(a + L.cell_start);
+    s.tile_sum = (uint32_t*)(a + L.tile_sum);
+    s.crmax = a + L.crmax;
+    s.rem = (double*)(a + L.rem);
+    s.nbar_sum = (double*)(a + L.nbar_sum);
+    s.acc = (double*)(a + L.acc);
+    s.ctrl = (uint32_t*)(a + L.ctrl);
+    s.counters = (unsigned long long*)(a + L.counters);
+    s.grad = (GradRec*)(a + L.map_scratch);
+}
+
+hyb_status do_dsmc_step(Ctx& c) {
+    hyb_status s = check(c, launch_dsmc_step(c), "dsmc_step launch");
+    if (s == HYB_OK) flip_particles(c);
+    return s;
+}
+
+hyb_status do_lbm_step(Ctx& c) {
+    hyb_status s = check(c, launch_lbm_step(c), "lbm_step launch");
+    if (s == HYB_OK) flip_populations(c);
+    return s;
+}
+
+hyb_status one_hybrid_step(Ctx& c, const int32_t* nodes, int32_t nn, const int32_t* cells,
+                           int32_t ncl) {
+    hyb_status s = do_dsmc_step(c);
+    if (s != HYB_OK) return s;
+    if (nn > 0) {
+        s = check(c, launch_map_d2l(c, nodes, nn), "map_dsmc_to_lbm launch");
+        if (s != HYB_OK) return s;
+    }
+    s = do_lbm_step(c);
+    if (s != HYB_OK) return s;
+    if (ncl > 0) s = check(c, launch_map_l2d(c, cells, ncl), "map_lbm_to_dsmc launch");
+    return s;
+}
+
+void drop_graphs(Ctx& c) {
+    for (int i = 0; i < 2; ++i)
+        if (c.graph[i]) {
+            cudaGraphExecDestroy(c.graph[i]);
+            c.graph[i] = nullptr;
+        }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hyb_status_string(hyb_status s) {
+    switch (s) {
+        case HYB_OK: return "ok";
+        case HYB_EINVAL: return "invalid argument";
+        case HYB_ENOMEM: return "arena too small";
+        case HYB_ECUDA: return "CUDA error";
+        case HYB_ECAPACITY: return "capacity exceeded";
+        case HYB_ETIMEOUT: return "capped device loop reached its limit";
+        case HYB_ESAMPLING: return "acceptance-rejection attempt cap reached";
+        case HYB_ESTATE: return "call out of order";
+    }
+    return "unknown status";
+}
+
+hyb_status hyb_derive(const hyb_params* p, hyb_derived* out) {
+    if (!params_valid(p) || !out) return HYB_EINVAL;
+    derive(*p, *out);
+    return HYB_OK;
+}
+
+hyb_status hyb_layout_compute(const hyb_params* p, hyb_layout* out) {
+    if (!params_valid(p) || !out) return HYB_EINVAL;
+    hyb_derived d;
+    derive(*p, d);
+    layout(*p, d, *out);
+    return HYB_OK;
+}
+
+hyb_status hyb_lattice(int32_t q, int32_t* e, double* w, double* r) {
+    if ((q != 39 && q != 19) || !e || !w || !r) return HYB_EINVAL;
+    if (q == 39) {
+        for (int a = 0; a < 39; ++a) {
+            for (int i = 0; i < 3; ++i) e[3 * a + i] = LatTab<D3Q39>::e[a][i];
+            w[a] = LatTab<D3Q39>::w_of_shell(a);
+        }
+        *r = lat_r<D3Q39>();
+    } else {
+        for (int a = 0; a < 19; ++a) {
+            for (int i = 0; i < 3; ++i) e[3 * a + i] = LatTab<D3Q19>::e[a][i];
+            w[a] = LatTab<D3Q19>::w_of_shell(a);
+        }
+        *r = lat_r<D3Q19>();
+    }
+    return HYB_OK;
+}
+
+hyb_status dsmc_init(const hyb_params* p, void* arena, uint64_t arena_bytes, void* stream,
+                     hyb_ctx** out) {
+    if (!out || !params_valid(p) || !arena || ((uintptr_t)arena & 255u)) return HYB_EINVAL;
+    *out = nullptr;
+    hyb_ctx* h = new (std::nothrow) hyb_ctx();
+    if (!h) return HYB_ENOMEM;
+    Ctx& c = h->c;
+    c.p = *p;
+    derive(c.p, c.d);
+    layout(c.p, c.d, c.L);
+    if (arena_bytes < c.L.total_bytes) {
+        delete h;
+        return HYB_ENOMEM;
+    }
+    c.arena = (char*)arena;
+    c.stream = (cudaStream_t)stream;
+    resolve(c);
+    cudaGetDevice(&c.device);
+    cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, c.device);
+    // pinned host words for status reads, followed by the timing pool
+    void* hp = nullptr;
+    if (cudaMallocHost(&hp, 256) != cudaSuccess) {
+        delete h;
+        return HYB_ECUDA;
+    }
+    c.h_pinned = (uint32_t*)hp;
+    hyb_status s = check(c, launch_init(c), "dsmc_init launch");
+    if (s != HYB_OK) {
+        cudaFreeHost(hp);
+        delete h;
+        return s;
+    }
+    *out = h;
+    return HYB_OK;
+}
+
+hyb_status dsmc_step(hyb_ctx* h, int32_t nsteps) {
+    if (!h || nsteps < 0) return HYB_EINVAL;
+    for (int i = 0; i < nsteps; ++i) {
+        hyb_status s = do_dsmc_step(h->c);
+        if (s != HYB_OK) return s;
+    }
+    return HYB_OK;
+}
+
+hyb_status lbm_step(hyb_ctx* h, int32_t nsteps) {
+    if (!h || nsteps < 0) return HYB_EINVAL;
+    for (int i = 0; i < nsteps; ++i) {
+        hyb_status s = do_lbm_step(h->c);
+        if (s != HYB_OK) return s;
+    }
+    return HYB_OK;
+}
+
+hyb_status sample_moments(hyb_ctx* h, double* out, int32_t reset) {
+    if (!h) return HYB_EINVAL;
+    Ctx& c = h->c;
+    const size_t bytes = (size_t)c.d.ncells * kMoments * sizeof(double);
+    if (out) {
+        hyb_status s = check(c, cudaMemcpyAsync(out, c.st.acc, bytes, cudaMemcpyDeviceToDevice,
+                                                c.stream), "sample_moments copy");
+        if (s != HYB_OK) return s;
+    }
+    if (reset) {
+        hyb_status s = check(c, cudaMemsetAsync(c.st.acc, 0, bytes, c.stream), "reset sums");
+        if (s != HYB_OK) return s;
+        s = check(c, cudaMemsetAsync(c.st.ctrl + CTRL_NSAMPLES, 0, 4, c.stream), "reset count");
+        if (s != HYB_OK) return s;
+    }
+    return HYB_OK;
+}
+
+hyb_status map_dsmc_to_lbm(hyb_ctx* h, const int32_t* dev_nodes, int32_t n) {
+    if (!h || n < 0 || (n > 0 && !dev_nodes) || n > h->c.d.nnodes) return HYB_EINVAL;
+    if (n == 0) return HYB_OK;
+    return check(h->c, launch_map_d2l(h->c, dev_nodes, n), "map_dsmc_to_lbm launch");
+}
+
+hyb_status map_lbm_to_dsmc(hyb_ctx* h, const int32_t* dev_cells, int32_t n) {
+    if (!h || n < 0 || (n > 0 && !dev_cells) || n > h->c.d.ncells) return HYB_EINVAL;
+    if (n == 0) return HYB_OK;
+    return check(h->c, launch_map_l2d(h->c, dev_cells, n), "map_lbm_to_dsmc launch");
+}
+
+hyb_status hyb_hybrid_step(hyb_ctx* h, const int32_t* dev_nodes, int32_t n_nodes,
+                           const int32_t* dev_cells, int32_t n_cells, int32_t nsteps,
+                           int32_t use_graph) {
+    if (!h || nsteps < 0 || n_nodes < 0 || n_cells < 0) return HYB_EINVAL;
+    Ctx& c = h->c;
+    if ((n_nodes > 0 && !dev_nodes) || (n_cells > 0 && !dev_cells) || n_nodes > c.d.nnodes ||
+        n_cells > c.d.ncells)
+        return HYB_EINVAL;
+    if (!use_graph) {
+        for (int i = 0; i < nsteps; ++i) {
+            hyb_status s = one_hybrid_step(c, dev_nodes, n_nodes, dev_cells, n_cells);
+            if (s != HYB_OK) return s;
+        }
+        return HYB_OK;
+    }
+    if (c.stream == nullptr) return fail(c, HYB_ESTATE, "graph replay needs a non-default stream");
+    if (c.g_nodes != dev_nodes || c.g_cells != dev_cells || c.g_nn != n_nodes ||
+        c.g_nc != n_cells || c.g_prof != c.prof_kernel) {
+        drop_graphs(c);
+        c.g_nodes = dev_nodes;
+        c.g_cells = dev_cells;
+        c.g_nn = n_nodes;
+        c.g_nc = n_cells;
+        c.g_prof = c.prof_kernel;
+    }
+    ProfPool& P = pool_of(c);
+    for (int i = 0; i < nsteps; ++i) {
+        // The graph variant is fixed by the particle parity; the population parity flips in
+        // step with it inside a hybrid step, so it is recorded at capture and checked.
+        const int gi = c.cur_p;
+        if (!c.graph[gi]) {
+            const int save_p = c.cur_p, save_f = c.cur_f;
+            cudaGraph_t g = nullptr;
+            hyb_status s = check(c, cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal),
+                                 "begin capture");
+            if (s != HYB_OK) return s;
+            c.capturing = true;
+            P.capture_slot = gi * 2 + c.cur_f;
+            hyb_status s2 = one_hybrid_step(c, dev_nodes, n_nodes, dev_cells, n_cells);
+            c.capturing = false;
+            cudaError_t e = cudaStreamEndCapture(c.stream, &g);
+            c.cur_p = save_p;
+            c.cur_f = save_f;
+            if (s2 != HYB_OK) {
+                if (g) cudaGraphDestroy(g);
+                return s2;
+            }
+            s = check(c, e, "end capture");
+            if (s != HYB_OK) return s;
+            e = cudaGraphInstantiate(&c.graph[gi], g, 0);
+            cudaGraphDestroy(g);
+            s = check(c, e, "graph instantiate");
+            if (s != HYB_OK) return s;
+            c.g_prof = c.prof_kernel;
+            c.g_curf[gi] = c.cur_f;
+        }
+        if (c.g_curf[gi] != c.cur_f) {
+            // population parity differs from the captured one: recapture this variant
+            cudaGraphExecDestroy(c.graph[gi]);
+            c.graph[gi] = nullptr;
+            --i;
+            continue;
+        }
+        hyb_status s = check(c, cudaGraphLaunch(c.graph[gi], c.stream), "graph launch");
+        if (s != HYB_OK) return s;
+        if (c.prof_kernel >= 0) P.gpending[gi * 2 + c.cur_f] = true;
+        flip_particles(c);
+        flip_populations(c);
+    }
+    return HYB_OK;
+}
+
+hyb_status hyb_current(const hyb_ctx* h, int32_t* particle_half, int32_t* lb_half) {
+    if (!h) return HYB_EINVAL;
+    if (particle_half) *particle_half = h->c.cur_p;
+    if (lb_half) *lb_half = h->c.cur_f;
+    return HYB_OK;
+}
+
+hyb_status hyb_sync_status(hyb_ctx* h, uint32_t* bits) {
+    if (!h) return HYB_EINVAL;
+    Ctx& c = h->c;
+    hyb_status s = check(c, cudaStreamSynchronize(c.stream), "synchronize");
+    if (s != HYB_OK) return s;
+    s = check(c, cudaMemcpy(c.h_pinned, c.st.ctrl, 4, cudaMemcpyDeviceToHost), "read status");
+    if (s != HYB_OK) return s;
+    const uint32_t b = c.h_pinned[0];
+    if (bits) *bits = b;
+    if (b & (HYB_ST_CAPACITY | HYB_ST_CELL_OVERFLOW)) return HYB_ECAPACITY;
+    if (b & HYB_ST_SAMPLING_CAP) return HYB_ESAMPLING;
+    if (b & (HYB_ST_BOUNCE_CAP | HYB_ST_SCATTER_CAP)) return HYB_ETIMEOUT;
+    if (b & HYB_ST_BAD_INPUT) return HYB_EINVAL;
+    return HYB_OK;
+}
+
+hyb_status hyb_read_counters(hyb_ctx* h, uint64_t* out) {
+    if (!h || !out) return HYB_EINVAL;
+    Ctx& c = h->c;
+    hyb_status s = check(c, cudaStreamSynchronize(c.stream), "synchronize");
+    if (s != HYB_OK) return s;
+    return check(c, cudaMemcpy(out, c.st.counters, HYB_NCOUNTERS * 8, cudaMemcpyDeviceToHost),
+                 "read counters");
+}
+
+hyb_status hyb_profile(hyb_ctx* h, int32_t kernel) {
+    if (!h || kernel < -1 || kernel >= K_COUNT) return HYB_EINVAL;
+    h->c.prof_kernel = kernel;
+    return HYB_OK;
+}
+
+hyb_status hyb_profile_harvest(hyb_ctx* h) {
+    if (!h) return HYB_EINVAL;
+    Ctx& c = h->c;
+    hyb_status s = check(c, cudaStreamSynchronize(c.stream), "synchronize");
+    if (s != HYB_OK) return s;
+    ProfPool& P = pool_of(c);
+    for (size_t i = 0; i < P.used; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, P.a[i], P.b[i]) == cudaSuccess) {
+            c.prof_ms += ms;
+            c.prof_launches += 1;
+        }
+    }
+    P.used = 0;
+    for (int g = 0; g < 4; ++g)
+        if (P.gpending[g] && P.ga[g]) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, P.ga[g], P.gb[g]) == cudaSuccess) {
+                c.prof_ms += ms;
+                c.prof_launches += 1;
+            }
+            P.gpending[g] = false;
+        }
+    return HYB_OK;
+}
+
+hyb_status hyb_profile_read(const hyb_ctx* h, double* total_ms, int64_t* launches) {
+    if (!h) return HYB_EINVAL;
+    if (total_ms) *total_ms = h->c.prof_ms;
+    if (launches) *launches = h->c.prof_launches;
+    return HYB_OK;
+}
+
+hyb_status hyb_debug_philox(const uint32_t* dev_ctr, uint64_t seed, uint32_t* dev_out, int64_t n,
+                            void* stream) {
+    if (!dev_ctr || !dev_out || n < 0) return HYB_EINVAL;
+    if (n == 0) return HYB_OK;
+    return launch_debug_philox(dev_ctr, seed, dev_out, n, (cudaStream_t)stream) == cudaSuccess
+               ? HYB_OK
+               : HYB_ECUDA;
+}
+
+const char* hyb_last_error(const hyb_ctx* h) { return h ? h->c.err.c_str() : "null context"; }
+
+void hyb_destroy(hyb_ctx* h) {
+    if (!h) return;
+    Ctx& c = h->c;
+    cudaStreamSynchronize(c.stream);
+    drop_graphs(c);
+    if (c.h_pinned) {
+        ProfPool& P = pool_of(c);
+        for (size_t i = 0; i < P.a.size(); ++i) {
+            cudaEventDestroy(P.a[i]);
+            cudaEventDestroy(P.b[i]);
+        }
+        for (int g = 0; g < 4; ++g)
+            if (P.ga[g]) {
+                cudaEventDestroy(P.ga[g]);
+                cudaEventDestroy(P.gb[g]);
+            }
+        cudaFreeHost(c.h_pinned);
+    }
+    delete h;
+}
+
+}  // extern "C"

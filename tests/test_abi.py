@@ -1,0 +1,102 @@
+"""Host-side checks of the C-ABI library (no GPU): it loads, exports every entry point the
+header declares, derives the same constants as the oracle, lays out the arena sanely, uses
+the same population order, and rejects invalid parameters without launching anything."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1512_08042_gb300 import binding as B
+from paper_1512_08042_gb300 import build as BUILD
+from paper_1512_08042_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    BUILD.build()
+    return B.lib()
+
+
+def declared_functions():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([a-z_][a-z0-9_]*)\s*\(",
+                                src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(B.EXPORTS) <= set(names)
+
+
+@pytest.mark.parametrize("name", sorted(W.WORKLOADS))
+def test_derived_constants_equal_oracle(lib, name):
+    cfg = W.WORKLOADS[name]
+    a = B.derive(cfg)
+    b = O.derive(cfg)
+    for k in a:
+        assert a[k] == b[k], k  # bit-identical: both follow the same written definitions
+
+
+def test_lattice_order_matches_oracle(lib):
+    for q in (39, 19):
+        e1, w1, r1 = B.lattice(q)
+        e2, w2, r2 = O.lattice(q)
+        assert np.array_equal(e1, e2)
+        assert np.array_equal(w1, w2)
+        assert r1 == r2
+
+
+def test_layout_is_aligned_and_disjoint(lib):
+    cfg = W.WORKLOADS["poiseuille_64x256_ppc50_fp32"]
+    L = B.layout(cfg)
+    d = B.derive(cfg)
+    rb = 4
+    regions = []
+    for h in range(2):
+        for k in ("x", "y", "vx", "vy", "vz"):
+            regions.append((getattr(L, k)[h], d["capacity"] * rb))
+        regions.append((L.f[h], d["q"] * d["nnodes"] * rb))
+    for k, sz in (("key", 4 * d["capacity"]), ("arrival", 4 * d["capacity"]),
+                  ("perm", 4 * d["capacity"]), ("count", 4 * d["ncells"]),
+                  ("cell_start", 4 * (d["ncells"] + 1)), ("acc", 160 * d["ncells"]),
+                  ("rem", 8 * d["ncells"]), ("nbar_sum", 8 * d["ncells"]), ("ctrl", 64),
+                  ("counters", 128)):
+        regions.append((getattr(L, k), sz))
+    regions.sort()
+    for (o1, s1), (o2, _) in zip(regions, regions[1:]):
+        assert o1 % 256 == 0
+        assert o1 + s1 <= o2
+    assert regions[-1][0] + regions[-1][1] <= L.total_bytes
+    assert d["capacity"] == int(np.ceil(1.25 * 64 * 256 * 50))
+
+
+def test_invalid_parameters_are_rejected(lib):
+    good = W.config(ncx=8, ncy=2, ppc=5, seed=1)
+    B.derive(good)
+    for bad in (dict(ncx=5), dict(lattice=27), dict(real_bytes=2), dict(lb_ratio=3),
+                dict(kn=0.0), dict(sample_every=0), dict(capacity_factor=0.5), dict(ppc=0)):
+        cfg = dict(good)
+        cfg.update(bad)
+        with pytest.raises(B.HybError) as ei:
+            B.derive(cfg)
+        assert ei.value.status == B.HYB_EINVAL
+    p = B.make_params(good)
+    p.abi_version = 99
+    d = B.HybDerived()
+    assert lib.hyb_derive(ctypes.byref(p), ctypes.byref(d)) == B.HYB_EINVAL
+    # null arguments
+    assert lib.dsmc_step(None, 1) == B.HYB_EINVAL
+    assert lib.map_lbm_to_dsmc(None, None, 1) == B.HYB_EINVAL

@@ -1,0 +1,282 @@
+"""Parity of the CUDA library with the CPU oracle, through the C ABI, on the same seeded
+inputs. Integers (cell keys via cell_start, collision/candidate counts, particle counts) are
+compared bit for bit; floating-point state within the tolerances stated per test."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1512_08042_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # collected on CPU-only machines, never run there
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1512_08042_gb300 import binding as B  # noqa: E402
+from paper_1512_08042_gb300 import build as BUILD  # noqa: E402
+
+BUILD.build()
+
+# Float tolerance for state computed in float on both sides (the FP32 path), and the share
+# of values allowed to differ in the last bit through double transcendentals rounded to float.
+RTOL = 1e-5
+
+
+def cfg_small(**kw):
+    base = dict(ncx=13, ncy=7, ppc=23, real_bytes=4, seed=11, kn=0.1, capacity_factor=1.5)
+    base.update(kw)
+    return W.config(**base)
+
+
+def gpu_particles(h):
+    h.sync()
+    p = h.particles()
+    return {k: v.cpu().numpy() for k, v in p.items()}
+
+
+def assert_particles_match(gp, op, real_bytes, exact_frac=0.9999):
+    for k in ("x", "y", "vx", "vy", "vz"):
+        a, b = gp[k], op[k]
+        assert a.shape == b.shape, k
+        eq = (a == b).mean() if a.size else 1.0
+        if real_bytes == 4:
+            assert eq >= exact_frac, (k, eq)
+            assert np.allclose(a, b, rtol=RTOL, atol=RTOL), (k, np.abs(a - b).max())
+        else:
+            assert np.allclose(a, b, rtol=1e-12, atol=1e-12), (k, np.abs(a - b).max())
+
+
+def test_philox_matches_oracle_word_for_word():
+    rng = np.random.default_rng(0)
+    ctr = rng.integers(0, 2 ** 32, size=(100_000, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:3] = [[0, 0, 0, 0], [0xFFFFFFFF] * 4, [0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344]]
+    seed = 0xDEADBEEF12345678
+    want = O.philox(ctr, seed)
+    c = torch.from_numpy(ctr.view(np.int32)).cuda()
+    out = torch.empty_like(c)
+    B.debug_philox(c, seed, out)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), want)
+
+
+@pytest.mark.parametrize("real_bytes", [4, 8])
+def test_init_matches_oracle(real_bytes):
+    cfg = cfg_small(real_bytes=real_bytes)
+    h = B.Hybrid(cfg)
+    o = O.Oracle(cfg)
+    assert h.n_tot() == o.scalars()["ntot"]
+    gp, op = gpu_particles(h), o.particles()
+    assert np.array_equal(gp["x"], op["x"]) and np.array_equal(gp["y"], op["y"])
+    assert_particles_match(gp, op, real_bytes)
+    assert np.array_equal(h.cell_start().cpu().numpy().astype(np.uint32), o.get(O.A_CELL_START))
+    f = h.f().cpu().numpy()
+    assert np.array_equal(f, o.f())
+
+
+def _compare_dsmc(h, o, real_bytes, acc_rtol=1e-5):
+    assert h.n_tot() == o.scalars()["ntot"]
+    assert np.array_equal(h.cell_start().cpu().numpy().astype(np.uint32), o.get(O.A_CELL_START))
+    assert_particles_match(gpu_particles(h), o.particles(), real_bytes)
+    hc, oc = h.counters(), o.counters()
+    for k in ("candidates", "collisions", "wall_hits", "created", "deleted"):
+        assert hc[k] == oc[k], (k, hc[k], oc[k])
+    assert np.array_equal(h.crmax().cpu().numpy(), o.get(O.A_CRMAX))
+    ga = h.acc().cpu().numpy()
+    oa = o.acc()
+    scale = np.abs(oa).max(axis=0, keepdims=True) + 1e-30
+    assert np.all(np.abs(ga - oa) <= acc_rtol * scale), np.abs((ga - oa) / scale).max()
+    ctrl = h.ctrl().cpu().numpy()
+    s = o.scalars()
+    assert ctrl[B.CTRL_STEP] == s["step"] and ctrl[B.CTRL_NSAMPLES] == s["nsamples"]
+    assert ctrl[B.CTRL_STATUS] == s["status"]
+
+
+@pytest.mark.parametrize("real_bytes,steps", [(4, 1), (4, 4), (8, 3)])
+def test_dsmc_steps_match_oracle(real_bytes, steps):
+    cfg = cfg_small(real_bytes=real_bytes, ma=0.3)
+    h = B.Hybrid(cfg)
+    o = O.Oracle(cfg)
+    for _ in range(steps):
+        h.dsmc_step(1)
+        o.dsmc_step(1)
+    _compare_dsmc(h, o, real_bytes)
+
+
+def test_dsmc_first_step_full_size_64x256_ppc50():
+    # the 819,200-particle channel at its benchmark launch configuration
+    cfg = W.WORKLOADS["poiseuille_64x256_ppc50_fp32"]
+    h = B.Hybrid(cfg)
+    o = O.Oracle(cfg)
+    h.dsmc_step(1)
+    o.dsmc_step(1)
+    _compare_dsmc(h, o, 4)
+
+
+def test_dsmc_synthetic_state_empty_and_crowded_cells():
+    # Poisson cell counts with empty cells and one cell above the shared-memory bound (256)
+    cfg = cfg_small(ncx=9, ncy=5, ppc=20, capacity_factor=4.0, seed=3)
+    st = W.gen_particles(9, 5, 20, seed=5, empty_fraction=0.2)
+    counts = np.diff(st["cell_start"].astype(np.int64))
+    extra = W.gen_particles(1, 1, 300, seed=6)  # crowd cell 17
+    c = 17
+    ix, iy = c % 9, c // 9
+    lo, hi = st["cell_start"][c], st["cell_start"][c + 1]
+    ins = {k: np.concatenate([st[k][:hi], (extra[k] + (ix if k == "x" else iy if k == "y" else 0))
+                              , st[k][hi:]]) for k in ("x", "y", "vx", "vy", "vz")}
+    counts[c] += extra["x"].size
+    cs = np.zeros(46, np.uint32)
+    cs[1:] = np.cumsum(counts)
+    assert counts[c] > 256 and (counts == 0).sum() > 3
+    args = [ins[k].astype(np.float32) for k in ("x", "y", "vx", "vy", "vz")]
+    h = B.Hybrid(cfg)
+    o = O.Oracle(cfg)
+    h.load_particles(*args, cs)
+    o.set_particles(*args, cs)
+    for _ in range(2):
+        h.dsmc_step(1)
+        o.dsmc_step(1)
+    _compare_dsmc(h, o, 4)
+
+
+@pytest.mark.parametrize("lattice,real_bytes", [(39, 4), (39, 8), (19, 4)])
+def test_lbm_steps_match_oracle(lattice, real_bytes):
+    cfg = cfg_small(lattice=lattice, real_bytes=real_bytes, lb_ratio=2, ma=0.5, kn=0.3)
+    h = B.Hybrid(cfg)
+    o = O.Oracle(cfg)
+    e, w, r = O.lattice(lattice)
+    f0 = W.gen_populations(w, h.d["nnodes"], seed=21).astype(np.float32 if real_bytes == 4 else np.float64)
+    h.f().copy_(torch.from_numpy(f0.reshape(h.f().shape)))
+    torch.cuda.synchronize()
+    o.set_f(f0)
+    for step in range(3):
+        h.lbm_step(1)
+        o.lbm_step(1)
+        h.sync()
+        gf, of = h.f().cpu().numpy(), o.f()
+        tol = 2e-5 if real_bytes == 4 else 1e-12
+        err = np.abs(gf - of) / (np.abs(of) + 1e-3 * w[:, None, None])
+        assert err.max() < tol, (step, err.max())
+    # mass is conserved
+    assert abs(h.f().double().sum().item() / f0.astype(np.float64).sum() - 1) < 1e-6
+
+
+def _set_acc(h, o, acc, S):
+    h.acc().copy_(torch.from_numpy(acc))
+    h.set_counters(nsamples=S)
+    o.set(O.A_ACC, acc.reshape(-1))
+    o.set_scalars(o.scalars()["step"], S)
+
+
+@pytest.mark.parametrize("lattice,lb_ratio", [(39, 2), (19, 1), (39, 1)])
+def test_dsmc2lb_matches_oracle(lattice, lb_ratio):
+    cfg = cfg_small(lattice=lattice, lb_ratio=lb_ratio)
+    h = B.Hybrid(cfg)
+    o = O.Oracle(cfg)
+    # cumulative sums from a few real DSMC steps of the oracle
+    src = O.Oracle(cfg_small(lattice=lattice, lb_ratio=lb_ratio, ma=0.4))
+    src.dsmc_step(5)
+    _set_acc(h, o, src.acc().copy(), src.scalars()["nsamples"])
+    nx = h.d["nx"]
+    nodes = np.array([0, 1, nx - 1, nx + 5, h.d["nnodes"] - 1, 3 * nx + 7], np.int32)
+    h.map_dsmc_to_lbm(torch.from_numpy(nodes).cuda())
+    o.map_dsmc_to_lbm(nodes)
+    h.sync()
+    gf = h.f().cpu().numpy().reshape(h.d["q"], -1)[:, nodes]
+    of = o.f().reshape(h.d["q"], -1)[:, nodes]
+    assert np.allclose(gf, of, rtol=1e-6, atol=0), np.abs(gf / of - 1).max()
+    assert h.sync_status()[1] == 0
+
+
+@pytest.mark.parametrize("lattice,real_bytes,lb_ratio", [(39, 4, 2), (39, 8, 1), (19, 4, 1)])
+def test_lb2dsmc_matches_oracle(lattice, real_bytes, lb_ratio):
+    cfg = cfg_small(lattice=lattice, real_bytes=real_bytes, lb_ratio=lb_ratio)
+    h = B.Hybrid(cfg)
+    o = O.Oracle(cfg)
+    h.dsmc_step(1)
+    o.dsmc_step(1)
+    # non-equilibrium populations: DSMC2LB projections of sampled moments, perturbed
+    e, w, r = O.lattice(lattice)
+    f0 = W.gen_populations(w, h.d["nnodes"], seed=8, eps=0.08, rho_eps=0.2)
+    f0 = f0.astype(np.float32 if real_bytes == 4 else np.float64)
+    h.f().copy_(torch.from_numpy(f0.reshape(h.f().shape)))
+    torch.cuda.synchronize()
+    o.set_f(f0)
+    cells = np.array([0, 5, 12, 13, 40, 90], np.int32)
+    n0 = h.n_tot()
+    h.map_lbm_to_dsmc(torch.from_numpy(cells).cuda())
+    o.map_lbm_to_dsmc(cells)
+    assert h.n_tot() == o.scalars()["ntot"] > n0
+    assert_particles_match(gpu_particles(h), o.particles(), real_bytes)
+    hc, oc = h.counters(), o.counters()
+    for k in ("created", "deleted", "l2d_attempts", "envelope"):
+        assert hc[k] == oc[k], (k, hc[k], oc[k])
+    # the next step compacts the deleted particles away identically
+    h.dsmc_step(1)
+    o.dsmc_step(1)
+    _compare_dsmc(h, o, real_bytes)
+
+
+def test_hybrid_steps_fp64_match_oracle():
+    # the 64-cell channel of the paper's mapping tests, FP64, two coupling nodes/cells
+    cfg = W.WORKLOADS["poiseuille_64x1_ppc100_fp64"]
+    nodes, cells = W.coupling_sites(cfg)
+    h = B.Hybrid(cfg)
+    o = O.Oracle(cfg)
+    dn, dc = torch.from_numpy(nodes).cuda(), torch.from_numpy(cells).cuda()
+    for _ in range(4):
+        h.hybrid_step(dn, dc, nsteps=1, use_graph=False)
+        o.dsmc_step(1)
+        o.map_dsmc_to_lbm(nodes)
+        o.lbm_step(1)
+        o.map_lbm_to_dsmc(cells)
+    _compare_dsmc(h, o, 8)
+    h.sync()
+    assert np.allclose(h.f().cpu().numpy(), o.f(), rtol=1e-11, atol=1e-14)
+
+
+def test_graph_replay_equals_direct_launches():
+    cfg = cfg_small(lb_ratio=2, ncy=8)
+    nodes, cells = W.coupling_sites(cfg, strip_cells=2)
+    dn, dc = torch.from_numpy(nodes).cuda(), torch.from_numpy(cells).cuda()
+    a = B.Hybrid(cfg)
+    b = B.Hybrid(cfg)
+    a.hybrid_step(dn, dc, nsteps=5, use_graph=False)
+    for _ in range(5):
+        b.hybrid_step(dn, dc, nsteps=1, use_graph=True)
+    a.sync()
+    b.sync()
+    assert a.current() == b.current()
+    assert torch.equal(a.arena, b.arena)
+
+
+def test_sample_moments_copy_and_reset():
+    cfg = cfg_small()
+    h = B.Hybrid(cfg)
+    h.dsmc_step(3)
+    out = torch.zeros(h.L.ncells, 20, dtype=torch.float64, device="cuda")
+    h.sample_moments(out, reset=True)
+    h.sync()
+    assert out[:, 0].sum().item() == 3 * h.n_tot()
+    assert h.acc().abs().sum().item() == 0
+    assert int(h.ctrl()[B.CTRL_NSAMPLES].item()) == 0
+
+
+def test_status_on_capacity_overflow_and_bad_index():
+    cfg = cfg_small(capacity_factor=1.0)
+    h = B.Hybrid(cfg)
+    h.dsmc_step(1)
+    e, w, r = O.lattice(39)
+    f = torch.from_numpy((w[:, None] * 3.0 * np.ones((1, h.d["nnodes"]))).astype(np.float32))
+    h.f().copy_(f.view(h.f().shape))
+    torch.cuda.synchronize()
+    before = h.n_tot()
+    h.map_lbm_to_dsmc(torch.tensor([4, 5], dtype=torch.int32, device="cuda"))
+    rc, bits = h.sync_status()
+    assert rc == B.HYB_ECAPACITY and bits & B.ST_CAPACITY
+    assert h.n_tot() == before  # nothing appended, nothing deleted
+    h2 = B.Hybrid(cfg_small())
+    h2.dsmc_step(1)
+    h2.map_dsmc_to_lbm(torch.tensor([10 ** 6], dtype=torch.int32, device="cuda"))
+    rc, bits = h2.sync_status()
+    assert rc == B.HYB_EINVAL and bits & B.ST_BAD_INPUT
