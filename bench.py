@@ -51,6 +51,12 @@ def kernel_algorithmic_bytes(name, cfg, d, n_particles, n_nodes_map, n_cells_map
         return ncells * (4 if name == "tile_sums" else 12)
     if name == "dsmc2lb":
         return n_nodes_map * (160 + d["q"] * rb)
+    if name == "lb2dsmc_prep":
+        # populations of the coupling cells' nodes read, one record per cell written
+        return n_cells_map * (cfg["lb_ratio"] ** 2 * d["q"] * rb + 176)
+    if name == "lb2dsmc_sample":
+        # old particles' x read and marked, new particles written (ppc per cell on average)
+        return n_cells_map * cfg["ppc"] * (2 * rb + 5 * rb) + n_cells_map * 176
     return 0
 
 
@@ -195,9 +201,10 @@ def main():
     use_graph = not args.no_graph
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = h.stream
+    torch.cuda.synchronize(dev)
 
     def step():
-        h.hybrid_step(nodes, cells, nsteps=1, use_graph=use_graph)
+        h.hybrid_step(nodes, cells, nsteps=1, use_graph=use_graph, order_inputs=False)
 
     # warm-up, and pick the dominant kernel by timing each one over a few steps
     for _ in range(args.warmup):

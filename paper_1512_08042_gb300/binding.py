@@ -169,7 +169,7 @@ class Hybrid:
         self.real = torch.float32 if cfg["real_bytes"] == 4 else torch.float64
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
-            self.arena = torch.empty(int(self.L.total_bytes), dtype=torch.uint8, device=self.device)
+            self.arena = torch.zeros(int(self.L.total_bytes), dtype=torch.uint8, device=self.device)
         torch.cuda.synchronize(self.device)
         ctx = _vp()
         with torch.cuda.device(self.device):
@@ -190,6 +190,15 @@ class Hybrid:
             pass
 
     # -- steps -------------------------------------------------------------------------
+    def _inputs(self, *tensors):
+        """Order the library's stream after the torch stream that produced `tensors`, and
+        keep their memory from being reused before the library's work on them is done."""
+        torch = self.torch
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        for t in tensors:
+            if t is not None:
+                t.record_stream(self.stream)
+
     def dsmc_step(self, n=1):
         _check(lib().dsmc_step(self.ctx, n), self.ctx)
 
@@ -197,12 +206,18 @@ class Hybrid:
         _check(lib().lbm_step(self.ctx, n), self.ctx)
 
     def map_dsmc_to_lbm(self, nodes):
+        self._inputs(nodes)
         _check(lib().map_dsmc_to_lbm(self.ctx, nodes.data_ptr(), nodes.numel()), self.ctx)
 
     def map_lbm_to_dsmc(self, cells):
+        self._inputs(cells)
         _check(lib().map_lbm_to_dsmc(self.ctx, cells.data_ptr(), cells.numel()), self.ctx)
 
-    def hybrid_step(self, nodes=None, cells=None, nsteps=1, use_graph=True):
+    def hybrid_step(self, nodes=None, cells=None, nsteps=1, use_graph=True, order_inputs=True):
+        """`order_inputs=False` skips the stream ordering of `nodes`/`cells` (for callers
+        that keep them resident and already ordered, e.g. a timed loop)."""
+        if order_inputs:
+            self._inputs(nodes, cells)
         np_ = nodes.data_ptr() if nodes is not None else None
         cp_ = cells.data_ptr() if cells is not None else None
         nn = nodes.numel() if nodes is not None else 0
@@ -211,6 +226,7 @@ class Hybrid:
                self.ctx)
 
     def sample_moments(self, out=None, reset=False):
+        self._inputs(out)
         ptr = out.data_ptr() if out is not None else None
         _check(lib().sample_moments(self.ctx, ptr, 1 if reset else 0), self.ctx)
 

@@ -236,16 +236,21 @@ struct D3Q19 {
 template <class LAT>
 struct LatTab;
 
+// The tables are local constants of __host__ __device__ constexpr functions, so device code
+// may index them at run time as well as fold them at compile time.
 template <>
 struct LatTab<D3Q39> {
-    static constexpr int e[39][3] = {
-        {0, 0, 0},   {1, 0, 0},   {-1, 0, 0},  {0, 1, 0},   {0, -1, 0},  {0, 0, 1},  {0, 0, -1},
-        {1, 1, 1},   {-1, 1, 1},  {1, -1, 1},  {-1, -1, 1}, {1, 1, -1},  {-1, 1, -1}, {1, -1, -1},
-        {-1, -1, -1}, {2, 0, 0},  {-2, 0, 0},  {0, 2, 0},   {0, -2, 0},  {0, 0, 2},  {0, 0, -2},
-        {2, 2, 0},   {-2, 2, 0},  {2, -2, 0},  {-2, -2, 0}, {2, 0, 2},   {-2, 0, 2}, {2, 0, -2},
-        {-2, 0, -2}, {0, 2, 2},   {0, -2, 2},  {0, 2, -2},  {0, -2, -2}, {3, 0, 0},  {-3, 0, 0},
-        {0, 3, 0},   {0, -3, 0},  {0, 0, 3},   {0, 0, -3}};
-    static constexpr double w_of_shell(int a) {
+    __host__ __device__ static constexpr int e(int a, int i) {
+        constexpr int t[39][3] = {
+            {0, 0, 0},   {1, 0, 0},   {-1, 0, 0},  {0, 1, 0},   {0, -1, 0},  {0, 0, 1},  {0, 0, -1},
+            {1, 1, 1},   {-1, 1, 1},  {1, -1, 1},  {-1, -1, 1}, {1, 1, -1},  {-1, 1, -1}, {1, -1, -1},
+            {-1, -1, -1}, {2, 0, 0},  {-2, 0, 0},  {0, 2, 0},   {0, -2, 0},  {0, 0, 2},  {0, 0, -2},
+            {2, 2, 0},   {-2, 2, 0},  {2, -2, 0},  {-2, -2, 0}, {2, 0, 2},   {-2, 0, 2}, {2, 0, -2},
+            {-2, 0, -2}, {0, 2, 2},   {0, -2, 2},  {0, 2, -2},  {0, -2, -2}, {3, 0, 0},  {-3, 0, 0},
+            {0, 3, 0},   {0, -3, 0},  {0, 0, 3},   {0, 0, -3}};
+        return t[a][i];
+    }
+    __host__ __device__ static constexpr double w(int a) {
         return a == 0 ? 1.0 / 12.0
                : a <= 6 ? 1.0 / 12.0
                : a <= 14 ? 1.0 / 27.0
@@ -257,27 +262,30 @@ struct LatTab<D3Q39> {
 
 template <>
 struct LatTab<D3Q19> {
-    static constexpr int e[19][3] = {
-        {0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0}, {0, 0, 1},  {0, 0, -1},
-        {1, 1, 0},  {-1, 1, 0}, {1, -1, 0}, {-1, -1, 0}, {1, 0, 1}, {-1, 0, 1}, {1, 0, -1},
-        {-1, 0, -1}, {0, 1, 1}, {0, -1, 1}, {0, 1, -1}, {0, -1, -1}};
-    static constexpr double w_of_shell(int a) {
+    __host__ __device__ static constexpr int e(int a, int i) {
+        constexpr int t[19][3] = {
+            {0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0}, {0, 0, 1},  {0, 0, -1},
+            {1, 1, 0},  {-1, 1, 0}, {1, -1, 0}, {-1, -1, 0}, {1, 0, 1}, {-1, 0, 1}, {1, 0, -1},
+            {-1, 0, -1}, {0, 1, 1}, {0, -1, 1}, {0, 1, -1}, {0, -1, -1}};
+        return t[a][i];
+    }
+    __host__ __device__ static constexpr double w(int a) {
         return a == 0 ? 1.0 / 3.0 : a <= 6 ? 1.0 / 18.0 : 1.0 / 36.0;
     }
 };
 
 template <class LAT>
-constexpr double lat_r() {
+__host__ __device__ constexpr double lat_r() {
     return LAT::Q == 39 ? 1.2247448713915889 : 1.7320508075688772;
 }
 
 // Sum over populations entering through a wall of e_x * w_a (mass flux of the wall
 // Maxwellian per unit density).
 template <class LAT>
-constexpr double wall_flux_norm() {
+__host__ __device__ constexpr double wall_flux_norm() {
     double s = 0.0;
     for (int a = 0; a < LAT::Q; ++a)
-        if (LatTab<LAT>::e[a][0] > 0) s += LatTab<LAT>::e[a][0] * LatTab<LAT>::w_of_shell(a);
+        if (LatTab<LAT>::e(a, 0) > 0) s += LatTab<LAT>::e(a, 0) * LatTab<LAT>::w(a);
     return s;
 }
 

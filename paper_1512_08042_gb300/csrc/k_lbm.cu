@@ -34,12 +34,12 @@ __device__ __forceinline__ void static_for(F&& f) {
 }
 
 template <class LAT>
-constexpr int E(int a, int i) {
-    return LatTab<LAT>::e[a][i];
+__host__ __device__ constexpr int E(int a, int i) {
+    return LatTab<LAT>::e(a, i);
 }
 template <class LAT>
-constexpr double W(int a) {
-    return LatTab<LAT>::w_of_shell(a);
+__host__ __device__ constexpr double W(int a) {
+    return LatTab<LAT>::w(a);
 }
 
 __device__ __forceinline__ int wrap_y(int v, int ny) {

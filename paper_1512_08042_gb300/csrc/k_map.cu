@@ -22,8 +22,8 @@ namespace hyb {
 namespace {
 
 template <class LAT>
-constexpr int E(int a, int i) {
-    return LatTab<LAT>::e[a][i];
+__host__ __device__ constexpr int E(int a, int i) {
+    return LatTab<LAT>::e(a, i);
 }
 
 template <typename Real, class LAT>
@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(128) k_d2l(MapArgs<Real> a) {
         const double xi[3] = {r * E<LAT>(q, 0), r * E<LAT>(q, 1), r * E<LAT>(q, 2)};
         double s = rho + a1x * xi[0] + a1y * xi[1] + a1z * xi[2] + 0.5 * herm2_contract(a2, xi);
         if (LAT::ORDER >= 3) s += herm3_contract(a3, xi) / 6.0;
-        a.f[(int64_t)q * a.nnodes + node] = (Real)(LatTab<LAT>::w_of_shell(q) * s);
+        a.f[(int64_t)q * a.nnodes + node] = (Real)(LatTab<LAT>::w(q) * s);
     }
 }
 

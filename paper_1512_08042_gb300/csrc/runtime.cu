@@ -250,14 +250,14 @@ hyb_status hyb_lattice(int32_t q, int32_t* e, double* w, double* r) {
     if ((q != 39 && q != 19) || !e || !w || !r) return HYB_EINVAL;
     if (q == 39) {
         for (int a = 0; a < 39; ++a) {
-            for (int i = 0; i < 3; ++i) e[3 * a + i] = LatTab<D3Q39>::e[a][i];
-            w[a] = LatTab<D3Q39>::w_of_shell(a);
+            for (int i = 0; i < 3; ++i) e[3 * a + i] = LatTab<D3Q39>::e(a, i);
+            w[a] = LatTab<D3Q39>::w(a);
         }
         *r = lat_r<D3Q39>();
     } else {
         for (int a = 0; a < 19; ++a) {
-            for (int i = 0; i < 3; ++i) e[3 * a + i] = LatTab<D3Q19>::e[a][i];
-            w[a] = LatTab<D3Q19>::w_of_shell(a);
+            for (int i = 0; i < 3; ++i) e[3 * a + i] = LatTab<D3Q19>::e(a, i);
+            w[a] = LatTab<D3Q19>::w(a);
         }
         *r = lat_r<D3Q19>();
     }
