@@ -217,6 +217,33 @@ int ora_dsmc2lb_node(int q, const double* m, uint64_t S, int ppc, double* out) {
     return 0;
 }
 
+// The float series of ln, sin and cos used by the float state path (for their pins).
+void ora_float_funcs(const float* x, int64_t n, float* ln_out, float* sin_out, float* cos_out) {
+    for (int64_t i = 0; i < n; ++i) {
+        if (ln_out) ln_out[i] = ln_f(x[i]);
+        if (sin_out || cos_out) {
+            float s, c;
+            sincos2pi_f(x[i], s, c);
+            if (sin_out) sin_out[i] = s;
+            if (cos_out) cos_out[i] = c;
+        }
+    }
+}
+
+// Gaussian pairs in the state precision from Philox words (for the float-path pins).
+void ora_gauss_pairs(const uint32_t* r, int64_t n, int real_bytes, double* out) {
+    for (int64_t i = 0; i < n; ++i) {
+        if (real_bytes == 4) {
+            float a, b;
+            gauss_pair<float>(r[2 * i], r[2 * i + 1], a, b);
+            out[2 * i] = a;
+            out[2 * i + 1] = b;
+        } else {
+            gauss_pair<double>(r[2 * i], r[2 * i + 1], out[2 * i], out[2 * i + 1]);
+        }
+    }
+}
+
 // Grad coefficients of a population vector: out = [rho, u(3), a2(9), a3(27), M, C].
 int ora_grad_coeffs(int q, const double* f, double* out) {
     if (q != 39 && q != 19) return 1;

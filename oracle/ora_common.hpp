@@ -143,6 +143,100 @@ inline void box_muller(uint32_t r1, uint32_t r2, double& n1, double& n2) {
     n2 = rad * std::sin(th);
 }
 
+// Float elementary functions used by the float state path. They are written out from their
+// series so that every IEEE operation is fixed and the same float results follow on any
+// machine that rounds each operation (no contraction):
+//   ln x: x = m 2^e with m in [sqrt(1/2), sqrt(2)), ln m = 2 atanh(s), s = (m-1)/(m+1),
+//         atanh s = s + s^3/3 + ... + s^11/11 (Abramowitz & Stegun 4.6.22), ln 2 split into
+//         a float-exact head and a small tail;
+//   sin, cos of 2 pi u (u in [0,1) with 24 bits): exact quadrant and octant reduction on u,
+//         then Taylor series of sin and cos on [0, pi/4] (A&S 4.3.65, 4.3.66).
+inline float ln_f(float x) {
+    uint32_t b;
+    std::memcpy(&b, &x, 4);
+    int e = (int)((b >> 23) & 0xFFu) - 127;
+    const uint32_t mb = (b & 0x7FFFFFu) | 0x3F800000u;
+    float m;
+    std::memcpy(&m, &mb, 4);
+    if (m > 1.41421356f) {
+        m = m * 0.5f;
+        e += 1;
+    }
+    const float s = (m - 1.0f) / (m + 1.0f);
+    const float s2 = s * s;
+    float t = 1.0f / 11.0f;
+    t = t * s2 + 1.0f / 9.0f;
+    t = t * s2 + 1.0f / 7.0f;
+    t = t * s2 + 1.0f / 5.0f;
+    t = t * s2 + 1.0f / 3.0f;
+    t = t * s2 + 1.0f;
+    const float lnm = 2.0f * s * t;
+    const float fe = (float)e;
+    return fe * 0.693145751953125f + (fe * 1.4286068203e-06f + lnm);
+}
+
+inline void sincos2pi_f(float u, float& sn, float& cs) {
+    const float t = 4.0f * u;
+    const float k = std::floor(t);
+    const float f = t - k;
+    const int q = (int)k & 3;
+    const bool swap = f > 0.5f;
+    const float g = swap ? 1.0f - f : f;
+    const float phi = g * 1.57079637f;
+    const float p2 = phi * phi;
+    float ps = 1.0f / 362880.0f;
+    ps = ps * p2 - 1.0f / 5040.0f;
+    ps = ps * p2 + 1.0f / 120.0f;
+    ps = ps * p2 - 1.0f / 6.0f;
+    ps = ps * p2 + 1.0f;
+    const float sp = phi * ps;
+    float pc = -1.0f / 3628800.0f;
+    pc = pc * p2 + 1.0f / 40320.0f;
+    pc = pc * p2 - 1.0f / 720.0f;
+    pc = pc * p2 + 1.0f / 24.0f;
+    pc = pc * p2 - 0.5f;
+    pc = pc * p2 + 1.0f;
+    const float sa = swap ? pc : sp;
+    const float ca = swap ? sp : pc;
+    switch (q) {
+        case 0: sn = sa; cs = ca; break;
+        case 1: sn = ca; cs = -sa; break;
+        case 2: sn = -sa; cs = -ca; break;
+        default: sn = -ca; cs = sa; break;
+    }
+}
+
+// A pair of unit normals (Box-Muller) and the speed of a particle re-emitted by a diffuse
+// wall (sqrt(-2 ln U), the flux-weighted Maxwellian), in the state precision. Float: 24-bit
+// uniforms, U1 in (0, 1]; double: libm in double with 32-bit uniforms.
+template <class Real>
+inline void gauss_pair(uint32_t r1, uint32_t r2, Real& n1, Real& n2);
+template <>
+inline void gauss_pair<float>(uint32_t r1, uint32_t r2, float& n1, float& n2) {
+    const float u1 = (float)((r1 >> 8) + 1u) * 0x1p-24f;
+    const float u2 = (float)(r2 >> 8) * 0x1p-24f;
+    const float rad = std::sqrt(-2.0f * ln_f(u1));
+    float sn, cs;
+    sincos2pi_f(u2, sn, cs);
+    n1 = rad * cs;
+    n2 = rad * sn;
+}
+template <>
+inline void gauss_pair<double>(uint32_t r1, uint32_t r2, double& n1, double& n2) {
+    box_muller(r1, r2, n1, n2);
+}
+template <class Real>
+inline Real wall_speed(uint32_t r);
+template <>
+inline float wall_speed<float>(uint32_t r) {
+    const float u = (float)((r >> 8) + 1u) * 0x1p-24f;
+    return std::sqrt(-2.0f * ln_f(u));
+}
+template <>
+inline double wall_speed<double>(uint32_t r) {
+    return std::sqrt(-2.0 * std::log(u01open(r)));
+}
+
 // ---------------------------------------------------------------------------------------
 // Lattices. The paper names D3Q19 and the 39-speed sixth-order-isotropic Gauss-Hermite set
 // (Sec. 1, Sec. 3.1) without listing them; these are the Shan-Yuan-Chen (2006) sets, pinned

@@ -5,8 +5,8 @@
 // takes them (move -> index -> collide -> sample), which the paper adopts in Sec. 5
 // (Eq. collisionnumber and the NTC scheme it names). With Real = float the arithmetic is the
 // float arithmetic the GPU state uses, step for step, so that cell keys, the sort
-// permutation and the selected collision pairs can be compared bit for bit; transcendental
-// draws (Box-Muller, wall re-emission) are evaluated in double and rounded.
+// permutation and the selected collision pairs can be compared bit for bit; the random
+// normals and wall speeds use the float series of ora_common.hpp in that mode.
 #pragma once
 #include <algorithm>
 #include <cstring>
@@ -42,8 +42,8 @@ struct Dsmc {
     std::vector<uint32_t> cell_start;  // ncells + 1
     // Per-cell collision state of the NTC scheme.
     std::vector<Real> crmax;           // (sigma_T c_r)_max / sigma_T
-    std::vector<double> rem;           // fractional candidate carried to the next step
-    std::vector<double> nbar_sum;      // sum of N over steps, for N-bar = <N>
+    std::vector<Real> rem;             // fractional candidate carried to the next step
+    std::vector<uint32_t> nbar_sum;    // sum of N over steps, for N-bar = <N>
     // Cumulative sums for the DSMC2LB mapping (Sec. 2.1 "cumulative averages"):
     // [N, S vx, vy, vz, S vv (xx xy xz yy yz zz), S vvv (xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz)]
     std::vector<double> acc;
@@ -68,18 +68,18 @@ struct Dsmc {
                 x[s] = (Real)ix + (Real)u01f(rp[0]);
                 y[s] = (Real)iy + (Real)u01f(rp[1]);
                 U4 rv = draw(p.seed, (uint32_t)c, 0, TAG_INIT_VEL, (uint32_t)k, 0);
-                double n0, n1, n2, n3;
-                box_muller(rv[0], rv[1], n0, n1);
-                box_muller(rv[2], rv[3], n2, n3);
-                vx[s] = (Real)n0;
-                vy[s] = (Real)n1;
-                vz[s] = (Real)n2;
+                Real n0, n1, n2, n3;
+                gauss_pair<Real>(rv[0], rv[1], n0, n1);
+                gauss_pair<Real>(rv[2], rv[3], n2, n3);
+                vx[s] = n0;
+                vy[s] = n1;
+                vz[s] = n2;
             }
         }
         cell_start[d.ncells] = (uint32_t)n;
         crmax.assign(d.ncells, (Real)p.crmax_init);
-        rem.assign(d.ncells, 0.0);
-        nbar_sum.assign(d.ncells, 0.0);
+        rem.assign(d.ncells, (Real)0);
+        nbar_sum.assign(d.ncells, 0u);
         acc.assign(d.ncells * kNumMoments, 0.0);
         step = 0;
         nsamples = 0;
@@ -94,12 +94,12 @@ struct Dsmc {
     // components Gaussian. `sign` points into the gas.
     void reemit(uint32_t slot, uint32_t s, int bounce, Real sign, Real& ux, Real& uy, Real& uz) {
         U4 r = draw(p.seed, slot, s, TAG_WALL, (uint32_t)bounce, 0);
-        const double vn = std::sqrt(-2.0 * std::log(u01open(r[0])));
-        double t1, t2;
-        box_muller(r[1], r[2], t1, t2);
-        ux = sign * (Real)vn;
-        uy = (Real)t1;
-        uz = (Real)t2;
+        const Real vn = wall_speed<Real>(r[0]);
+        Real t1, t2;
+        gauss_pair<Real>(r[1], r[2], t1, t2);
+        ux = sign * vn;
+        uy = t1;
+        uz = t2;
     }
 
     uint32_t cell_key(Real xx, Real yy) const {
@@ -206,11 +206,11 @@ struct Dsmc {
     void collide_cell(uint32_t c, uint32_t s) {
         const uint32_t base = cell_start[c];
         const uint32_t n = cell_start[c + 1] - base;
-        nbar_sum[c] += (double)n;
-        const double nbar = nbar_sum[c] / (double)(s + 1);
+        nbar_sum[c] += n;
+        const Real nbar = (Real)nbar_sum[c] / (Real)(s + 1);
         if (n < 2) return;
-        const double ncand = 0.5 * (double)n * nbar * (double)crmax[c] * d.coll_dt + rem[c];
-        const double nsel_d = std::floor(ncand);
+        const Real ncand = (Real)0.5 * (Real)n * nbar * crmax[c] * (Real)d.coll_dt + rem[c];
+        const Real nsel_d = std::floor(ncand);
         rem[c] = ncand - nsel_d;
         uint64_t nsel = (uint64_t)nsel_d;
         if (nsel > 0xFFFFFFu) {

@@ -126,10 +126,10 @@ int grad_sample_one(const GradCell& g, int order, uint64_t seed, uint32_t cell, 
     for (int att = 0; att < kMaxL2DAttempts; ++att) {
         U4 r = draw(seed, cell, t, TAG_L2D_VEL, k, (uint32_t)(2 * att));
         U4 r2 = draw(seed, cell, t, TAG_L2D_VEL, k, (uint32_t)(2 * att + 1));
-        double n0, n1, n2, n3;
-        box_muller(r[0], r[1], n0, n1);
-        box_muller(r[2], r[3], n2, n3);
-        const Real xi[3] = {(Real)n0, (Real)n1, (Real)n2};
+        Real n0, n1, n2, n3;
+        gauss_pair<Real>(r[0], r[1], n0, n1);
+        gauss_pair<Real>(r[2], r[3], n2, n3);
+        const Real xi[3] = {n0, n1, n2};
         const double xd[3] = {(double)xi[0], (double)xi[1], (double)xi[2]};
         const double G = hermite_series(g.ahat, xd, order);
         const double R = u01d(r2[0]);

@@ -89,6 +89,8 @@ def lib():
         L.ora_dsmc2lb_node.argtypes = [ctypes.c_int, vp, u64, ctypes.c_int, vp]
         L.ora_grad_coeffs.argtypes = [ctypes.c_int, vp, vp]
         L.ora_grad_sample.argtypes = [ctypes.c_int, vp, u64, u32, u32, i64, vp, vp]
+        L.ora_float_funcs.argtypes = [vp, i64, vp, vp, vp]
+        L.ora_gauss_pairs.argtypes = [vp, i64, ctypes.c_int, vp]
         _LIB = L
     return _LIB
 
@@ -165,6 +167,21 @@ def grad_sample(q, f, seed, cell, t, n):
     return v, {"attempts": int(info[0]), "envelope": int(info[1]), "cap": int(info[2])}
 
 
+def float_funcs(x):
+    """ln(x), sin(2 pi x), cos(2 pi x) by the float series of the float state path."""
+    x = np.ascontiguousarray(x, np.float32)
+    ln, sn, cs = (np.empty_like(x) for _ in range(3))
+    lib().ora_float_funcs(_ptr(x), x.size, _ptr(ln), _ptr(sn), _ptr(cs))
+    return ln, sn, cs
+
+
+def gauss_pairs(words, real_bytes):
+    w = np.ascontiguousarray(words, np.uint32).reshape(-1, 2)
+    out = np.empty((w.shape[0], 2), np.float64)
+    lib().ora_gauss_pairs(_ptr(w), w.shape[0], real_bytes, _ptr(out))
+    return out
+
+
 class Oracle:
     """One DSMC + LBM state on the host (float or double, per cfg['real_bytes'])."""
 
@@ -200,8 +217,7 @@ class Oracle:
         cells = np.ascontiguousarray(cells, np.int32)
         lib().ora_map_lbm_to_dsmc(self.h, _ptr(cells), len(cells))
 
-    _DT = {A_CELL_START: np.uint32, A_REM: np.float64, A_NBAR_SUM: np.float64,
-           A_ACC: np.float64}
+    _DT = {A_CELL_START: np.uint32, A_NBAR_SUM: np.uint32, A_ACC: np.float64}
 
     def _dtype(self, which):
         return self._DT.get(which, self.real)

@@ -557,3 +557,57 @@ def test_lb2dsmc_sigma_matches_table3_in_si_units(golden_dir):
     # Table 3: sigma_vy of LB2DSMC particles 239.3 m/s (Kn 0.15), within sampling error
     assert abs(sigma / g["table3_sigma_vy_lb2dsmc_kn015"] - 1) < 0.01
     assert abs(v[:, 1].mean() * c_th - 10.5) < 5 * 240 / math.sqrt(200_000)
+
+
+# ---------------------------------------------------------------------------------------
+# Float series used by the float state path (ln by the atanh series, sin/cos of 2 pi u by
+# quadrant reduction and Taylor series): error bounds against numpy's double functions.
+
+def test_float_ln_series_error_bound():
+    x = np.concatenate([np.arange(1, 1 << 16, dtype=np.float64) * 2.0 ** -24,
+                        np.linspace(2.0 ** -8, 1.0, 200_001), np.linspace(1.0, 4.0, 50_001)])
+    x = x.astype(np.float32)
+    ln, _, _ = O.float_funcs(x)
+    want = np.log(x.astype(np.float64))
+    err = np.abs(ln.astype(np.float64) - want)
+    assert np.all(err <= 2.5e-7 * np.abs(want) + 1.2e-7), err.max()
+
+
+def test_float_sincos_series_error_bound():
+    u = (np.arange(0, 1 << 24, 37, dtype=np.float64) * 2.0 ** -24).astype(np.float32)
+    _, s, c = O.float_funcs(u)
+    th = 2 * np.pi * u.astype(np.float64)
+    assert np.abs(s - np.sin(th)).max() < 2.5e-7
+    assert np.abs(c - np.cos(th)).max() < 2.5e-7
+    # exact at the quadrant points
+    _, s4, c4 = O.float_funcs(np.array([0, 0.25, 0.5, 0.75], np.float32))
+    assert np.array_equal(s4, [0, 1, 0, -1]) and np.array_equal(c4, [1, 0, -1, 0])
+
+
+@pytest.mark.parametrize("real_bytes", [4, 8])
+def test_gaussian_pairs_are_unit_normal(real_bytes):
+    n = 400_000
+    ctr = np.zeros((n // 4, 4), np.uint32)
+    ctr[:, 0] = np.arange(n // 4)
+    words = O.philox(ctr, 77).reshape(-1)
+    z = O.gauss_pairs(words, real_bytes).reshape(-1)
+    se = 1 / math.sqrt(z.size)
+    assert abs(z.mean()) < 5 * se
+    assert abs(z.var() - 1) < 5 * math.sqrt(2) * se
+    assert abs((z ** 4).mean() - 3) < 5 * math.sqrt(96) * se
+    # Kolmogorov-Smirnov distance to the normal CDF
+    from math import erf
+    zs = np.sort(z)
+    cdf = 0.5 * (1 + np.vectorize(erf)(zs / math.sqrt(2)))
+    ks = np.max(np.abs(cdf - np.arange(1, zs.size + 1) / zs.size))
+    assert ks < 1.63 / math.sqrt(zs.size)  # 99% critical value
+
+
+def test_float_state_init_is_maxwellian():
+    cfg = small_cfg(ncx=32, ncy=8, ppc=200, real_bytes=4)
+    o = O.Oracle(cfg)
+    p = o.particles()
+    v = np.stack([p["vx"], p["vy"], p["vz"]]).astype(np.float64)
+    se = 1 / math.sqrt(v.shape[1])
+    assert np.all(np.abs(v.mean(1)) < 5 * se)
+    assert np.all(np.abs(v.var(1) - 1) < 5 * math.sqrt(2) * se)
