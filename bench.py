@@ -29,7 +29,7 @@ from paper_1512_08042_gb300 import workloads as W  # noqa: E402
 METRIC = "DSMC particle-updates/s, LBM MLUPS, hybrid steps/s on 1 GB300 at stated tol"
 DEFAULT_WORKLOAD = "poiseuille_64x256_ppc50_fp32"
 FLUSH_BYTES = 512 << 20
-LAUNCHES_PER_STEP = 9  # move, tile sums, scan, rank, collide, dsmc2lb, lbm, lb2dsmc x2
+LAUNCHES_PER_STEP = 10  # move, tile sums, scan, rank, collide, dsmc2lb, lbm, lb2dsmc x3
 
 
 def kernel_algorithmic_bytes(name, cfg, d, n_particles, n_nodes_map, n_cells_map):
@@ -51,9 +51,11 @@ def kernel_algorithmic_bytes(name, cfg, d, n_particles, n_nodes_map, n_cells_map
         return ncells * (4 if name == "tile_sums" else 12)
     if name == "dsmc2lb":
         return n_nodes_map * (160 + d["q"] * rb)
-    if name == "lb2dsmc_prep":
+    if name == "lb2dsmc_coef":
         # populations of the coupling cells' nodes read, one record per cell written
         return n_cells_map * (cfg["lb_ratio"] ** 2 * d["q"] * rb + 176)
+    if name == "lb2dsmc_scan":
+        return n_cells_map * 16
     if name == "lb2dsmc_sample":
         # old particles' x read and marked, new particles written (ppc per cell on average)
         return n_cells_map * cfg["ppc"] * (2 * rb + 5 * rb) + n_cells_map * 176

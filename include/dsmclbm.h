@@ -119,8 +119,8 @@ typedef struct {
  *   cell_start    u32[ncells + 1]  first slot of each cell in the current buffer
  *   tile_sum      u32[ntiles]      per-tile sums of `count` (scan scratch)
  *   crmax         Real[ncells]     (sigma_T c_r)_max / sigma_T per cell
- *   rem           f64[ncells]      NTC fractional candidate carried between steps
- *   nbar_sum      f64[ncells]      running sum of N per cell, for N-bar
+ *   rem           Real[ncells]     NTC fractional candidate carried between steps
+ *   nbar_sum      u32[ncells]      running sum of N per cell, for N-bar
  *   acc           f64[ncells][20]  cumulative sums N, S v (3), S vv (6: xx xy xz yy yz zz),
  *                                  S vvv (10: xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz)
  *   f             Real[q][ny][nx]  populations, x fastest; f[2]
@@ -202,8 +202,8 @@ hyb_status hyb_sync_status(hyb_ctx* ctx, uint32_t* bits);
 hyb_status hyb_read_counters(hyb_ctx* ctx, uint64_t* out);
 
 /* Kernel timing on the context's stream: after hyb_profile(ctx, k) every launch of kernel k
- * (0 move, 1 tile sums, 2 scan, 3 rank, 4 collide, 5 lbm, 6 dsmc2lb, 7 lb2dsmc prepare,
- * 8 lb2dsmc sample; -1 off) is bracketed by CUDA events. hyb_profile_harvest synchronises
+ * (0 move, 1 tile sums, 2 scan, 3 rank, 4 collide, 5 lbm, 6 dsmc2lb, 7 lb2dsmc coefficients,
+ * 8 lb2dsmc sample, 9 lb2dsmc scan; -1 off) is bracketed by CUDA events. hyb_profile_harvest synchronises
  * and adds the elapsed times of the launches since the last harvest; call it after every
  * hybrid step when graphs are used. hyb_profile_read returns the totals. */
 hyb_status hyb_profile(hyb_ctx* ctx, int32_t kernel);

@@ -19,7 +19,7 @@ ST_CAPACITY, ST_BOUNCE_CAP, ST_SCATTER_CAP, ST_SAMPLING_CAP, ST_CELL_OVERFLOW, S
 COUNTER_NAMES = ["wall_hits", "candidates", "collisions", "created", "deleted",
                  "l2d_attempts", "envelope", "bounce_cap"]
 KERNELS = {"move": 0, "tile_sums": 1, "scan": 2, "rank": 3, "collide": 4, "lbm": 5,
-           "dsmc2lb": 6, "lb2dsmc_prep": 7, "lb2dsmc_sample": 8}
+           "dsmc2lb": 6, "lb2dsmc_coef": 7, "lb2dsmc_sample": 8, "lb2dsmc_scan": 9}
 CTRL_STATUS, CTRL_NTOT, CTRL_STEP, CTRL_NSAMPLES = 0, 1, 2, 3
 
 _u32, _i32, _i64, _u64, _dbl, _vp = (ctypes.c_uint32, ctypes.c_int32, ctypes.c_int64,
@@ -292,6 +292,12 @@ class Hybrid:
 
     def crmax(self):
         return self._view(self.L.crmax, self.L.ncells, self.real)
+
+    def rem(self):
+        return self._view(self.L.rem, self.L.ncells, self.real)
+
+    def nbar_sum(self):
+        return self._view(self.L.nbar_sum, self.L.ncells, self.torch.int32)
 
     def f(self, half=None):
         h = self.current()[1] if half is None else half

@@ -27,6 +27,7 @@ enum CtrlWord {
     CTRL_NSAMPLES = 3,
     CTRL_L2D_BASE = 4,
     CTRL_L2D_SKIP = 5,
+    CTRL_L2D_TOTAL = 6,
     CTRL_WORDS = 16,
 };
 
@@ -51,7 +52,8 @@ enum KernelId {
     K_D2L = 6,
     K_L2D_PREP = 7,
     K_L2D_SAMPLE = 8,
-    K_COUNT = 9,
+    K_L2D_SCAN = 9,
+    K_COUNT = 10,
 };
 
 // LB2DSMC per-cell record (map_scratch).
@@ -79,8 +81,8 @@ struct State {
     uint32_t* cell_start;
     uint32_t* tile_sum;
     void* crmax;
-    double* rem;
-    double* nbar_sum;
+    void* rem;
+    uint32_t* nbar_sum;
     double* acc;
     void* f[2];
     uint32_t* ctrl;
@@ -114,8 +116,8 @@ struct DsmcArgs {
     uint32_t* cell_start;
     uint32_t* tile_sum;
     Real* crmax;
-    double* rem;
-    double* nbar_sum;
+    Real* rem;
+    uint32_t* nbar_sum;
     double* acc;
     uint32_t* ctrl;
     unsigned long long* counters;
@@ -187,15 +189,108 @@ __device__ __forceinline__ uint32_t uindex(uint32_t r, uint32_t n) {
     return (uint32_t)(((uint64_t)r * n) >> 32);
 }
 
-// Box-Muller pair in double (the transform Table 1 step 4 names).
-__device__ __forceinline__ void box_muller(uint32_t r1, uint32_t r2, double& n1, double& n2) {
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+// Float elementary functions of the FP32 state path, evaluated from their series with every
+// operation fixed (this code is compiled without FMA contraction), so that the results are
+// reproducible bit for bit:
+//   ln x = e ln 2 + 2 atanh(s), x = m 2^e, m in [sqrt(1/2), sqrt(2)), s = (m-1)/(m+1),
+//          atanh by its odd series to s^11 (Abramowitz & Stegun 4.6.22);
+//   sin, cos (2 pi u), u in [0,1) with 24 bits: exact reduction of 4u to a quadrant and of
+//          the remainder to [0, 1/2], then the Taylor series of sin and cos on [0, pi/4]
+//          (A&S 4.3.65, 4.3.66).
+__device__ __forceinline__ float ln_f(float x) {
+    const uint32_t b = __float_as_uint(x);
+    int e = (int)((b >> 23) & 0xFFu) - 127;
+    float m = __uint_as_float((b & 0x7FFFFFu) | 0x3F800000u);
+    if (m > 1.41421356f) {
+        m = m * 0.5f;
+        e += 1;
+    }
+    const float s = (m - 1.0f) / (m + 1.0f);
+    const float s2 = s * s;
+    float t = 1.0f / 11.0f;
+    t = t * s2 + 1.0f / 9.0f;
+    t = t * s2 + 1.0f / 7.0f;
+    t = t * s2 + 1.0f / 5.0f;
+    t = t * s2 + 1.0f / 3.0f;
+    t = t * s2 + 1.0f;
+    const float lnm = 2.0f * s * t;
+    const float fe = (float)e;
+    return fe * 0.693145751953125f + (fe * 1.4286068203e-06f + lnm);
+}
+
+__device__ __forceinline__ void sincos2pi_f(float u, float& sn, float& cs) {
+    const float t = 4.0f * u;
+    const float k = floorf(t);
+    const float f = t - k;
+    const int q = (int)k & 3;
+    const bool swap = f > 0.5f;
+    const float g = swap ? 1.0f - f : f;
+    const float phi = g * 1.57079637f;
+    const float p2 = phi * phi;
+    float ps = 1.0f / 362880.0f;
+    ps = ps * p2 - 1.0f / 5040.0f;
+    ps = ps * p2 + 1.0f / 120.0f;
+    ps = ps * p2 - 1.0f / 6.0f;
+    ps = ps * p2 + 1.0f;
+    const float sp = phi * ps;
+    float pc = -1.0f / 3628800.0f;
+    pc = pc * p2 + 1.0f / 40320.0f;
+    pc = pc * p2 - 1.0f / 720.0f;
+    pc = pc * p2 + 1.0f / 24.0f;
+    pc = pc * p2 - 0.5f;
+    pc = pc * p2 + 1.0f;
+    const float sa = swap ? pc : sp;
+    const float ca = swap ? sp : pc;
+    if (q == 0) {
+        sn = sa;
+        cs = ca;
+    } else if (q == 1) {
+        sn = ca;
+        cs = -sa;
+    } else if (q == 2) {
+        sn = -sa;
+        cs = -ca;
+    } else {
+        sn = -ca;
+        cs = sa;
+    }
+}
+
+// Unit normal pair (Box-Muller) and diffuse-wall normal speed sqrt(-2 ln U) in the state
+// precision: float uses 24-bit uniforms (U1 in (0,1]) and the series above; double uses the
+// double library functions with 32-bit uniforms.
+template <typename Real>
+__device__ __forceinline__ void gauss_pair(uint32_t r1, uint32_t r2, Real& n1, Real& n2);
+template <>
+__device__ __forceinline__ void gauss_pair<float>(uint32_t r1, uint32_t r2, float& n1, float& n2) {
+    const float u1 = (float)((r1 >> 8) + 1u) * 0x1p-24f;
+    const float u2 = (float)(r2 >> 8) * 0x1p-24f;
+    const float rad = sqrtf(-2.0f * ln_f(u1));
+    float sn, cs;
+    sincos2pi_f(u2, sn, cs);
+    n1 = rad * cs;
+    n2 = rad * sn;
+}
+template <>
+__device__ __forceinline__ void gauss_pair<double>(uint32_t r1, uint32_t r2, double& n1, double& n2) {
     const double rad = sqrt(-2.0 * log(u01open(r1)));
     const double th = 6.283185307179586 * u01open(r2);
     n1 = rad * cos(th);
     n2 = rad * sin(th);
 }
-
-__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+template <typename Real>
+__device__ __forceinline__ Real wall_speed(uint32_t r);
+template <>
+__device__ __forceinline__ float wall_speed<float>(uint32_t r) {
+    const float u = (float)((r >> 8) + 1u) * 0x1p-24f;
+    return sqrtf(-2.0f * ln_f(u));
+}
+template <>
+__device__ __forceinline__ double wall_speed<double>(uint32_t r) {
+    return sqrt(-2.0 * log(u01open(r)));
+}
 
 // Packed symmetric tensors: rank 2 order xx xy xz yy yz zz, rank 3 order xxx xxy xxz xyy
 // xyz xzz yyy yyz yzz zzz. Full contractions weight each packed entry by its number of

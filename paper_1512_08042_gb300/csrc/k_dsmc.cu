@@ -25,12 +25,12 @@ template <typename Real>
 __device__ __forceinline__ void reemit(uint64_t seed, uint32_t slot, uint32_t s, int bounce, Real sign,
                                        Real& ux, Real& uy, Real& uz) {
     const uint4 r = draw(seed, slot, s, TAG_WALL, (uint32_t)bounce, 0);
-    const double vn = sqrt(-2.0 * log(u01open(r.x)));
-    double t1, t2;
-    box_muller(r.y, r.z, t1, t2);
-    ux = sign * (Real)vn;
-    uy = (Real)t1;
-    uz = (Real)t2;
+    const Real vn = wall_speed<Real>(r.x);
+    Real t1, t2;
+    gauss_pair<Real>(r.y, r.z, t1, t2);
+    ux = sign * vn;
+    uy = t1;
+    uz = t2;
 }
 
 // Isotropic unit vector (Marsaglia 1972) from the NTC scattering stream of candidate k.
@@ -82,12 +82,12 @@ __global__ void k_init_particles(DsmcArgs<Real> a) {
         a.dx[s] = (Real)ix + (Real)u01f(rp.x);
         a.dy[s] = (Real)iy + (Real)u01f(rp.y);
         const uint4 rv = draw(a.seed, c, 0, TAG_INIT_VEL, k, 0);
-        double n0, n1, n2, n3;
-        box_muller(rv.x, rv.y, n0, n1);
-        box_muller(rv.z, rv.w, n2, n3);
-        a.dvx[s] = (Real)n0;
-        a.dvy[s] = (Real)n1;
-        a.dvz[s] = (Real)n2;
+        Real n0, n1, n2, n3;
+        gauss_pair<Real>(rv.x, rv.y, n0, n1);
+        gauss_pair<Real>(rv.z, rv.w, n2, n3);
+        a.dvx[s] = n0;
+        a.dvy[s] = n1;
+        a.dvz[s] = n2;
     }
 }
 
@@ -99,8 +99,8 @@ __global__ void k_init_cells(DsmcArgs<Real> a) {
         if (c < a.ncells) {
             a.count[c] = 0;
             a.crmax[c] = (Real)a.crmax_init;
-            a.rem[c] = 0.0;
-            a.nbar_sum[c] = 0.0;
+            a.rem[c] = (Real)0;
+            a.nbar_sum[c] = 0u;
             for (int m = 0; m < kMoments; ++m) a.acc[c * kMoments + m] = 0.0;
         }
         if (c == 0) {
@@ -268,15 +268,76 @@ __global__ void __launch_bounds__(256) k_rank(DsmcArgs<Real> a) {
 // One warp per cell: stable order, gather, NTC collisions, write-out, moment sums.
 constexpr int kCollideWarps = 4;
 
+// Ascending bitonic sort of 32 R keys held R per lane (key r of a lane at position
+// lane + 32 r). All loops have constant trip counts and unroll, so the keys stay in registers.
+template <int R>
+__device__ __forceinline__ void bitonic_sort(uint32_t (&v)[R]) {
+    constexpr int N = 32 * R;
+    const int lane = (int)lane_id();
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+                const int jr = j >> 5;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int o = r ^ jr;
+                    if (r < o) {
+                        const bool asc = ((lane + 32 * r) & k) == 0;
+                        const uint32_t lo = min(v[r], v[o]), hi = max(v[r], v[o]);
+                        v[r] = asc ? lo : hi;
+                        v[o] = asc ? hi : lo;
+                    }
+                }
+            } else {
+                const bool lower = (lane & j) == 0;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const uint32_t o = __shfl_xor_sync(kFull, v[r], j);
+                    const bool asc = ((lane + 32 * r) & k) == 0;
+                    v[r] = (lower == asc) ? min(v[r], o) : max(v[r], o);
+                }
+            }
+        }
+    }
+}
+
+// Sort the cell's n <= 32 R slots from perm and gather them into the destination half.
+template <typename Real, int R>
+__device__ __forceinline__ void sort_gather(const DsmcArgs<Real>& a, uint32_t start, uint32_t n,
+                                            Real* vx, Real* vy, Real* vz) {
+    const unsigned lane = lane_id();
+    uint32_t v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const uint32_t k = lane + 32u * r;
+        v[r] = k < n ? a.perm[start + k] : 0xFFFFFFFFu;
+    }
+    bitonic_sort<R>(v);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const uint32_t k = lane + 32u * r;
+        if (k < n) {
+            const uint32_t src = v[r];
+            a.dx[start + k] = a.sx[src];
+            a.dy[start + k] = a.sy[src];
+            vx[k] = a.svx[src];
+            vy[k] = a.svy[src];
+            vz[k] = a.svz[src];
+        }
+    }
+}
+
 template <typename Real, int MAXP>
 __global__ void __launch_bounds__(kCollideWarps * 32) k_collide(DsmcArgs<Real> a) {
     __shared__ uint32_t s_in[kCollideWarps][MAXP];
-    __shared__ uint32_t s_srt[kCollideWarps][MAXP];
     __shared__ Real s_v[kCollideWarps][3][MAXP];
     const int w = threadIdx.x >> 5;
     const unsigned lane = lane_id();
     const uint32_t s = a.ctrl[CTRL_STEP] - 1u;
     const bool do_sample = (s % (uint32_t)a.sample_every) == 0u;
+    const Real coll_dt = (Real)a.coll_dt;
     unsigned long long ncand_tot = 0, ncoll_tot = 0;
     uint32_t flags = 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) a.ctrl[CTRL_NTOT] = a.cell_start[a.ncells];
@@ -285,45 +346,55 @@ __global__ void __launch_bounds__(kCollideWarps * 32) k_collide(DsmcArgs<Real> a
         const uint32_t start = a.cell_start[c];
         const uint32_t n = a.cell_start[c + 1] - start;
         const bool small = n <= (uint32_t)MAXP;
-        // 1. the cell's old slots in ascending order (rank = number of smaller slots)
-        uint32_t* srt = small ? s_srt[w] : a.arrival + start;
-        const uint32_t* in = small ? s_in[w] : a.perm + start;
-        if (small)
-            for (uint32_t k = lane; k < n; k += 32) s_in[w][k] = a.perm[start + k];
-        __syncwarp();
-        for (uint32_t k = lane; k < n; k += 32) {
-            const uint32_t v = in[k];
-            uint32_t r = 0;
-            for (uint32_t m = 0; m < n; ++m) r += in[m] < v ? 1u : 0u;
-            srt[r] = v;
-        }
-        __syncwarp();
-        // 2. gather into the destination half
         Real* vx = small ? s_v[w][0] : a.dvx + start;
         Real* vy = small ? s_v[w][1] : a.dvy + start;
         Real* vz = small ? s_v[w][2] : a.dvz + start;
-        for (uint32_t k = lane; k < n; k += 32) {
-            const uint32_t src = srt[k];
-            a.dx[start + k] = a.sx[src];
-            a.dy[start + k] = a.sy[src];
-            vx[k] = a.svx[src];
-            vy[k] = a.svy[src];
-            vz[k] = a.svz[src];
+        // 1. the cell's old slots in ascending order, 2. gathered into the other half
+        if (n <= 32) {
+            sort_gather<Real, 1>(a, start, n, vx, vy, vz);
+        } else if (n <= 64) {
+            sort_gather<Real, 2>(a, start, n, vx, vy, vz);
+        } else if (n <= 128) {
+            sort_gather<Real, 4>(a, start, n, vx, vy, vz);
+        } else {
+            // rank of each slot = number of smaller slots in the cell
+            uint32_t* srt = a.arrival + start;
+            const uint32_t* in = small ? s_in[w] : a.perm + start;
+            if (small)
+                for (uint32_t k = lane; k < n; k += 32) s_in[w][k] = a.perm[start + k];
+            __syncwarp();
+            for (uint32_t k = lane; k < n; k += 32) {
+                const uint32_t v = in[k];
+                uint32_t r = 0;
+                for (uint32_t m = 0; m < n; ++m) r += in[m] < v ? 1u : 0u;
+                srt[r] = v;
+            }
+            __syncwarp();
+            for (uint32_t k = lane; k < n; k += 32) {
+                const uint32_t src = srt[k];
+                a.dx[start + k] = a.sx[src];
+                a.dy[start + k] = a.sy[src];
+                vx[k] = a.svx[src];
+                vy[k] = a.svy[src];
+                vz[k] = a.svz[src];
+            }
         }
         __syncwarp();
         // 3. NTC: N_cand = 1/2 N Nbar F_N (sigma c_r)_max dt / V_c + remainder
         uint32_t nsel = 0;
         Real cm = (Real)0;
         if (lane == 0) {
-            const double nb = a.nbar_sum[c] + (double)n;
+            const uint32_t nb = a.nbar_sum[c] + n;
             a.nbar_sum[c] = nb;
             cm = a.crmax[c];
-            if (n >= 2) {
-                const double nbar = nb / (double)(s + 1u);
-                const double ncand = 0.5 * (double)n * nbar * (double)cm * a.coll_dt + a.rem[c];
-                const double fl = floor(ncand);
+            if (n > 32767u) {
+                flags |= HYB_ST_CELL_OVERFLOW;  // pair indices are packed in 15 and 16 bits
+            } else if (n >= 2) {
+                const Real nbar = (Real)nb / (Real)(s + 1u);
+                const Real ncand = (Real)0.5 * (Real)n * nbar * cm * coll_dt + a.rem[c];
+                const Real fl = floor(ncand);
                 a.rem[c] = ncand - fl;
-                if (fl > 16777215.0) {
+                if (fl > (Real)16777215) {
                     nsel = 16777215u;
                     flags |= HYB_ST_CELL_OVERFLOW;
                 } else {
@@ -337,51 +408,52 @@ __global__ void __launch_bounds__(kCollideWarps * 32) k_collide(DsmcArgs<Real> a
         for (uint32_t ch = 0; ch < nsel; ch += 32) {
             // lanes draw 32 candidates in parallel; they are applied in order below
             const uint32_t k = ch + lane;
-            uint32_t ci = 0, cj = 0;
+            uint32_t ij = 0;
             Real R = (Real)0, nx = (Real)0, ny = (Real)0, nz = (Real)0;
-            int ok = 0;
             if (k < nsel) {
                 const uint4 r = draw(a.seed, (uint32_t)c, s, TAG_NTC_PAIR, k, 0);
-                ci = uindex(r.x, n);
-                cj = uindex(r.y, n - 1u);
+                const uint32_t ci = uindex(r.x, n);
+                uint32_t cj = uindex(r.y, n - 1u);
                 if (cj >= ci) cj += 1u;
                 R = (Real)u01f(r.z);
-                ok = unit_vector(a.seed, (uint32_t)c, s, k, nx, ny, nz);
+                const int ok = unit_vector(a.seed, (uint32_t)c, s, k, nx, ny, nz);
+                ij = ci | (cj << 15) | (ok ? 0u : 0x80000000u);
             }
             const uint32_t cnt = min(32u, nsel - ch);
             for (uint32_t m = 0; m < cnt; ++m) {
-                const uint32_t i = __shfl_sync(kFull, ci, m);
-                const uint32_t j = __shfl_sync(kFull, cj, m);
+                const uint32_t ijm = __shfl_sync(kFull, ij, m);
+                const uint32_t i = ijm & 0x7FFFu, j = (ijm >> 15) & 0xFFFFu;
                 const Real Rm = __shfl_sync(kFull, R, m);
-                const Real nxm = __shfl_sync(kFull, nx, m);
-                const Real nym = __shfl_sync(kFull, ny, m);
-                const Real nzm = __shfl_sync(kFull, nz, m);
-                const int okm = __shfl_sync(kFull, ok, m);
                 const Real ax = vx[i], ay = vy[i], az = vz[i];
                 const Real bx = vx[j], by = vy[j], bz = vz[j];
                 const Real ddx = ax - bx, ddy = ay - by, ddz = az - bz;
                 const Real cr = sqrt(ddx * ddx + ddy * ddy + ddz * ddz);
                 if (cr > cm) cm = cr;
                 const bool acc_pair = cr > Rm * cm;
-                __syncwarp();
-                if (acc_pair && okm) {
-                    if (lane == 0) {
-                        const Real cx = (ax + bx) * (Real)0.5;
-                        const Real cy = (ay + by) * (Real)0.5;
-                        const Real cz = (az + bz) * (Real)0.5;
-                        const Real h = cr * (Real)0.5;
-                        vx[i] = cx + h * nxm;
-                        vy[i] = cy + h * nym;
-                        vz[i] = cz + h * nzm;
-                        vx[j] = cx - h * nxm;
-                        vy[j] = cy - h * nym;
-                        vz[j] = cz - h * nzm;
+                if (acc_pair) {
+                    const Real nxm = __shfl_sync(kFull, nx, m);
+                    const Real nym = __shfl_sync(kFull, ny, m);
+                    const Real nzm = __shfl_sync(kFull, nz, m);
+                    if (ijm & 0x80000000u) {
+                        flags |= HYB_ST_SCATTER_CAP;
+                    } else {
+                        __syncwarp();
+                        if (lane == 0) {
+                            const Real cx = (ax + bx) * (Real)0.5;
+                            const Real cy = (ay + by) * (Real)0.5;
+                            const Real cz = (az + bz) * (Real)0.5;
+                            const Real h = cr * (Real)0.5;
+                            vx[i] = cx + h * nxm;
+                            vy[i] = cy + h * nym;
+                            vz[i] = cz + h * nzm;
+                            vx[j] = cx - h * nxm;
+                            vy[j] = cy - h * nym;
+                            vz[j] = cz - h * nzm;
+                        }
+                        __syncwarp();
+                        ncoll += 1;
                     }
-                    ncoll += 1;
-                } else if (acc_pair) {
-                    flags |= HYB_ST_SCATTER_CAP;
                 }
-                __syncwarp();
             }
         }
         if (lane == 0) {
@@ -459,7 +531,7 @@ DsmcArgs<Real> make_args(Ctx& c) {
     a.cell_start = c.st.cell_start;
     a.tile_sum = c.st.tile_sum;
     a.crmax = (Real*)c.st.crmax;
-    a.rem = c.st.rem;
+    a.rem = (Real*)c.st.rem;
     a.nbar_sum = c.st.nbar_sum;
     a.acc = c.st.acc;
     a.ctrl = c.st.ctrl;

@@ -1,20 +1,24 @@
-// The two kinetic mappings of Sec. 2, in FP64 arithmetic with Real (float or double) state.
+// The two kinetic mappings of Sec. 2. The Grad/Hermite coefficients are solved in FP64;
+// populations and particle state are Real (float or double).
 //
 // k_d2l (DSMC2LB, Sec. 2.1): one thread per coupling node. The cumulative sums of the
 // node's DSMC cell give rho = <N>/ppc, the per-particle raw moments <v>, <vv>, <vvv>, and
 // the raw Hermite coefficients a0 = rho, a1 = rho <v>, a2 = rho(<vv> - I),
-// a3 = rho(<vvv> - sym(<v> I)); the populations are f_a = w_a sum_{n<=N} a^(n):H^(n)(xi_a)/n!
-// (Eq. discretefunctions).
+// a3 = rho(<vvv> - sym(<v> I)) (FP64); the populations f_a = w_a sum_{n<=N} a^(n):H^(n)(xi_a)/n!
+// (Eq. discretefunctions) are evaluated in the state precision.
 //
-// k_l2d_prep + k_l2d_sample (LB2DSMC, Sec. 2.2, Table 1): the first (one block) computes per
-// coupling cell the mean populations of its lb_ratio^2 nodes, rho and u, the comoving
-// coefficients a2 = sum f c c / rho - I and a3 = sum f c c c / rho (c = xi - u), M, C = 1 + 30 M
-// (Eq. C), the particle count floor(rho ppc + U), and the append offsets (a block scan);
-// the second (one warp per cell) marks the cell's old particles deleted and draws the new
-// ones: Box-Muller trial xi from the unit Maxwellian, accepted when C R <= G(xi) with
-// G = 1 + a2:H2/2 + a3:H3/6 (Eq. distr_outeq), velocity xi + u (Eq. step6 in c_th units),
-// position uniform in the cell. Draws are keyed by (cell, step, purpose, particle index,
-// trial), so the result does not depend on the launch shape.
+// LB2DSMC (Sec. 2.2, Table 1) in three launches:
+//   k_l2d_coef   one warp per coupling cell: mean populations of the cell's lb_ratio^2
+//                nodes, rho and u, the comoving coefficients a2 = sum f c c / rho - I and
+//                a3 = sum f c c c / rho (c = xi - u), M, C = 1 + 30 M (Eq. C), and the
+//                particle count floor(rho ppc + U) (FP64, lanes over populations);
+//   k_l2d_scan   one block: append offsets (exclusive scan), capacity check, slot count;
+//   k_l2d_sample one thread per new particle: Box-Muller trial xi from the unit Maxwellian,
+//                accepted when C R <= G(xi), G = 1 + a2:H2/2 + a3:H3/6 (Eq. distr_outeq),
+//                velocity xi + u (Eq. step6 in c_th units), position uniform in the cell;
+//                one warp per coupling cell marks the cell's old particles deleted.
+// Draws are keyed by (cell, step, purpose, particle index, trial), so the results do not
+// depend on the launch shape.
 #include "hyb_internal.cuh"
 
 namespace hyb {
@@ -24,6 +28,12 @@ namespace {
 template <class LAT>
 __host__ __device__ constexpr int E(int a, int i) {
     return LatTab<LAT>::e(a, i);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+    return v;
 }
 
 template <typename Real, class LAT>
@@ -44,32 +54,140 @@ __global__ void __launch_bounds__(128) k_d2l(MapArgs<Real> a) {
         atomicOr(&a.ctrl[CTRL_STATUS], HYB_ST_BAD_INPUT);
         return;
     }
+    // FP64 coefficient solve
     const double rho = (NS / (double)S) / (double)a.ppc;
     const double m1x = m[1] / NS, m1y = m[2] / NS, m1z = m[3] / NS;
-    double a2[6], a3[10];
     const double d2[6] = {1, 0, 0, 1, 0, 1};
-    for (int k = 0; k < 6; ++k) a2[k] = rho * (m[4 + k] / NS - d2[k]);
     // sym(<v> I) for the packed entries xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz
     const double s3[10] = {3 * m1x, m1y, m1z, m1x, 0.0, m1x, 3 * m1y, m1z, m1y, 3 * m1z};
-    for (int k = 0; k < 10; ++k) a3[k] = rho * (m[10 + k] / NS - s3[k]);
-    const double a1x = rho * m1x, a1y = rho * m1y, a1z = rho * m1z;
-    const double r = a.r_lat;
+    Real a2[6], a3[10];
+    for (int k = 0; k < 6; ++k) a2[k] = (Real)(rho * (m[4 + k] / NS - d2[k]));
+    for (int k = 0; k < 10; ++k) a3[k] = (Real)(rho * (m[10 + k] / NS - s3[k]));
+    const Real r0 = (Real)rho, a1x = (Real)(rho * m1x), a1y = (Real)(rho * m1y), a1z = (Real)(rho * m1z);
+    const Real tx = a3[0] + a3[3] + a3[5], ty = a3[1] + a3[6] + a3[8], tz = a3[2] + a3[7] + a3[9];
+    const Real tr2 = a2[0] + a2[3] + a2[5];
+    constexpr double R = lat_r<LAT>();
 #pragma unroll
     for (int q = 0; q < LAT::Q; ++q) {
-        const double xi[3] = {r * E<LAT>(q, 0), r * E<LAT>(q, 1), r * E<LAT>(q, 2)};
-        double s = rho + a1x * xi[0] + a1y * xi[1] + a1z * xi[2] + 0.5 * herm2_contract(a2, xi);
-        if (LAT::ORDER >= 3) s += herm3_contract(a3, xi) / 6.0;
-        a.f[(int64_t)q * a.nnodes + node] = (Real)(LatTab<LAT>::w(q) * s);
+        const Real X = (Real)(R * E<LAT>(q, 0)), Y = (Real)(R * E<LAT>(q, 1)), Z = (Real)(R * E<LAT>(q, 2));
+        const Real h2 = a2[0] * X * X + a2[3] * Y * Y + a2[5] * Z * Z - tr2 +
+                        (Real)2 * (a2[1] * X * Y + a2[2] * X * Z + a2[4] * Y * Z);
+        Real sum = r0 + a1x * X + a1y * Y + a1z * Z + (Real)0.5 * h2;
+        if (LAT::ORDER >= 3) {
+            const Real cubic = a3[0] * X * X * X + (Real)3 * a3[1] * X * X * Y + (Real)3 * a3[2] * X * X * Z +
+                               (Real)3 * a3[3] * X * Y * Y + (Real)6 * a3[4] * X * Y * Z +
+                               (Real)3 * a3[5] * X * Z * Z + a3[6] * Y * Y * Y + (Real)3 * a3[7] * Y * Y * Z +
+                               (Real)3 * a3[8] * Y * Z * Z + a3[9] * Z * Z * Z;
+            sum += (cubic - (Real)3 * (tx * X + ty * Y + tz * Z)) * (Real)(1.0 / 6.0);
+        }
+        a.f[(int64_t)q * a.nnodes + node] = (Real)LatTab<LAT>::w(q) * sum;
     }
 }
 
+// One warp per coupling cell: FP64 Grad coefficients and the particle count.
 template <typename Real, class LAT>
-__global__ void __launch_bounds__(256) k_l2d_prep(MapArgs<Real> a) {
-    __shared__ uint32_t warp_tot[8];
-    __shared__ uint32_t s_carry;
+__global__ void __launch_bounds__(128) k_l2d_coef(MapArgs<Real> a) {
     const uint32_t t_step = a.ctrl[CTRL_STEP];
     const int r = a.lb_ratio;
     const double rr = a.r_lat;
+    const unsigned lane = lane_id();
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    constexpr int QL = (LAT::Q + 31) / 32;
+    for (int ci = gw; ci < a.n; ci += nw) {
+        const int32_t cell = a.list[ci];
+        if (cell < 0 || cell >= a.ncx * a.ncy) {
+            if (lane == 0) {
+                a.grad[ci].nnew = 0;
+                a.grad[ci].offset = 0xFFFFFFFFu;  // marks a bad index for the scan
+            }
+            continue;
+        }
+        const int ix = cell % a.ncx, iy = cell / a.ncx;
+        double fb[QL];
+        double rho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+#pragma unroll
+        for (int h = 0; h < QL; ++h) {
+            const int q = lane + 32 * h;
+            double s = 0.0;
+            if (q < LAT::Q) {
+                for (int dy = 0; dy < r; ++dy)
+                    for (int dx = 0; dx < r; ++dx)
+                        s += (double)a.f[(int64_t)q * a.nnodes + (int64_t)(iy * r + dy) * a.nx + (ix * r + dx)];
+                s = s / (double)(r * r);
+                rho += s;
+                jx += s * (rr * LatTab<LAT>::e(q, 0));
+                jy += s * (rr * LatTab<LAT>::e(q, 1));
+                jz += s * (rr * LatTab<LAT>::e(q, 2));
+            }
+            fb[h] = s;
+        }
+        rho = warp_sum(rho);
+        const double ux = warp_sum(jx) / rho, uy = warp_sum(jy) / rho, uz = warp_sum(jz) / rho;
+        double m2[6] = {0, 0, 0, 0, 0, 0}, m3[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+        for (int h = 0; h < QL; ++h) {
+            const int q = lane + 32 * h;
+            if (q < LAT::Q) {
+                const double cx = rr * LatTab<LAT>::e(q, 0) - ux;
+                const double cy = rr * LatTab<LAT>::e(q, 1) - uy;
+                const double cz = rr * LatTab<LAT>::e(q, 2) - uz;
+                const double f = fb[h];
+                m2[0] += f * cx * cx / rho;
+                m2[1] += f * cx * cy / rho;
+                m2[2] += f * cx * cz / rho;
+                m2[3] += f * cy * cy / rho;
+                m2[4] += f * cy * cz / rho;
+                m2[5] += f * cz * cz / rho;
+                if (LAT::ORDER >= 3) {
+                    m3[0] += f * cx * cx * cx / rho;
+                    m3[1] += f * cx * cx * cy / rho;
+                    m3[2] += f * cx * cx * cz / rho;
+                    m3[3] += f * cx * cy * cy / rho;
+                    m3[4] += f * cx * cy * cz / rho;
+                    m3[5] += f * cx * cz * cz / rho;
+                    m3[6] += f * cy * cy * cy / rho;
+                    m3[7] += f * cy * cy * cz / rho;
+                    m3[8] += f * cy * cz * cz / rho;
+                    m3[9] += f * cz * cz * cz / rho;
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) m2[k] = warp_sum(m2[k]);
+        if (LAT::ORDER >= 3) {
+#pragma unroll
+            for (int k = 0; k < 10; ++k) m3[k] = warp_sum(m3[k]);
+        }
+        if (lane == 0) {
+            GradRec g;
+            g.rho = rho;
+            g.u[0] = ux;
+            g.u[1] = uy;
+            g.u[2] = uz;
+            for (int k = 0; k < 6; ++k) g.a2[k] = m2[k];
+            g.a2[0] -= 1.0;
+            g.a2[3] -= 1.0;
+            g.a2[5] -= 1.0;
+            for (int k = 0; k < 10; ++k) g.a3[k] = m3[k];
+            double M = 0.0;
+            for (int k = 0; k < 6; ++k) M = fmax(M, fabs(g.a2[k]));
+            for (int k = 0; k < 10; ++k) M = fmax(M, fabs(g.a3[k]));
+            g.C = 1.0 + 30.0 * M;
+            const double u = u01d(draw(a.seed, (uint32_t)cell, t_step, TAG_L2D_ROUND, 0, 0).x);
+            const double ne = floor(rho * (double)a.ppc + u);
+            g.nnew = ne > 0.0 ? (uint32_t)ne : 0u;
+            g.offset = 0;
+            a.grad[ci] = g;
+        }
+    }
+}
+
+// One block: exclusive scan of the counts into append offsets, then the capacity check.
+template <typename Real>
+__global__ void __launch_bounds__(1024) k_l2d_scan(MapArgs<Real> a) {
+    __shared__ uint32_t warp_tot[32];
+    __shared__ uint32_t s_carry;
     const unsigned lane = lane_id();
     const int w = threadIdx.x >> 5;
     if (threadIdx.x == 0) s_carry = 0;
@@ -79,77 +197,9 @@ __global__ void __launch_bounds__(256) k_l2d_prep(MapArgs<Real> a) {
         const int ci = base + threadIdx.x;
         uint32_t nn = 0;
         if (ci < a.n) {
-            const int32_t cell = a.list[ci];
-            if (cell < 0 || cell >= a.ncx * a.ncy) {
-                bad = 1;
-            } else {
-                const int ix = cell % a.ncx, iy = cell / a.ncx;
-                double fb[LAT::Q];
-                double rho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
-#pragma unroll
-                for (int q = 0; q < LAT::Q; ++q) {
-                    double s = 0.0;
-                    for (int dy = 0; dy < r; ++dy)
-                        for (int dx = 0; dx < r; ++dx)
-                            s += (double)a.f[(int64_t)q * a.nnodes + (int64_t)(iy * r + dy) * a.nx +
-                                             (ix * r + dx)];
-                    fb[q] = s / (double)(r * r);
-                }
-#pragma unroll
-                for (int q = 0; q < LAT::Q; ++q) {
-                    rho += fb[q];
-                    jx += fb[q] * (rr * E<LAT>(q, 0));
-                    jy += fb[q] * (rr * E<LAT>(q, 1));
-                    jz += fb[q] * (rr * E<LAT>(q, 2));
-                }
-                GradRec g;
-                g.rho = rho;
-                g.u[0] = jx / rho;
-                g.u[1] = jy / rho;
-                g.u[2] = jz / rho;
-                for (int k = 0; k < 6; ++k) g.a2[k] = 0.0;
-                for (int k = 0; k < 10; ++k) g.a3[k] = 0.0;
-#pragma unroll
-                for (int q = 0; q < LAT::Q; ++q) {
-                    const double cx = rr * E<LAT>(q, 0) - g.u[0];
-                    const double cy = rr * E<LAT>(q, 1) - g.u[1];
-                    const double cz = rr * E<LAT>(q, 2) - g.u[2];
-                    const double f = fb[q];
-                    g.a2[0] += f * cx * cx / rho;
-                    g.a2[1] += f * cx * cy / rho;
-                    g.a2[2] += f * cx * cz / rho;
-                    g.a2[3] += f * cy * cy / rho;
-                    g.a2[4] += f * cy * cz / rho;
-                    g.a2[5] += f * cz * cz / rho;
-                    if (LAT::ORDER >= 3) {
-                        g.a3[0] += f * cx * cx * cx / rho;
-                        g.a3[1] += f * cx * cx * cy / rho;
-                        g.a3[2] += f * cx * cx * cz / rho;
-                        g.a3[3] += f * cx * cy * cy / rho;
-                        g.a3[4] += f * cx * cy * cz / rho;
-                        g.a3[5] += f * cx * cz * cz / rho;
-                        g.a3[6] += f * cy * cy * cy / rho;
-                        g.a3[7] += f * cy * cy * cz / rho;
-                        g.a3[8] += f * cy * cz * cz / rho;
-                        g.a3[9] += f * cz * cz * cz / rho;
-                    }
-                }
-                g.a2[0] -= 1.0;
-                g.a2[3] -= 1.0;
-                g.a2[5] -= 1.0;
-                double M = 0.0;
-                for (int k = 0; k < 6; ++k) M = fmax(M, fabs(g.a2[k]));
-                for (int k = 0; k < 10; ++k) M = fmax(M, fabs(g.a3[k]));
-                g.C = 1.0 + 30.0 * M;
-                const double u = u01d(draw(a.seed, (uint32_t)cell, t_step, TAG_L2D_ROUND, 0, 0).x);
-                const double ne = floor(rho * (double)a.ppc + u);
-                nn = ne > 0.0 ? (uint32_t)ne : 0u;
-                g.nnew = nn;
-                g.offset = 0;
-                a.grad[ci] = g;
-            }
+            if (a.grad[ci].offset == 0xFFFFFFFFu) bad = 1;
+            nn = a.grad[ci].nnew;
         }
-        // block exclusive scan of nn
         uint32_t incl = nn;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -182,6 +232,7 @@ __global__ void __launch_bounds__(256) k_l2d_prep(MapArgs<Real> a) {
         } else {
             a.ctrl[CTRL_L2D_SKIP] = 0;
             a.ctrl[CTRL_L2D_BASE] = base;
+            a.ctrl[CTRL_L2D_TOTAL] = total;
             a.ctrl[CTRL_NTOT] = base + total;
             atomicAdd(&a.counters[HYB_C_CREATED], (unsigned long long)total);
         }
@@ -192,53 +243,67 @@ template <typename Real, class LAT>
 __global__ void __launch_bounds__(128) k_l2d_sample(MapArgs<Real> a) {
     if (a.ctrl[CTRL_L2D_SKIP]) return;
     const uint32_t base = a.ctrl[CTRL_L2D_BASE];
+    const uint32_t total = a.ctrl[CTRL_L2D_TOTAL];
     const uint32_t t_step = a.ctrl[CTRL_STEP];
     const unsigned lane = lane_id();
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
     unsigned long long deleted = 0, attempts = 0, envelope = 0;
     uint32_t flags = 0;
+    // old particles of the coupling cells are marked deleted: one warp per cell
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int ci = gw; ci < a.n; ci += nw) {
         const uint32_t cell = (uint32_t)a.list[ci];
-        const GradRec g = a.grad[ci];
         const uint32_t s0 = a.cell_start[cell], s1 = a.cell_start[cell + 1];
         for (uint32_t i = s0 + lane; i < s1; i += 32) {
             if (a.x[i] >= (Real)0) deleted += 1;
             a.x[i] = (Real)-1;
         }
-        const int ix = (int)(cell % (uint32_t)a.ncx), iy = (int)(cell / (uint32_t)a.ncx);
-        for (uint32_t k = lane; k < g.nnew; k += 32) {
-            const uint4 rp = draw(a.seed, cell, t_step, TAG_L2D_POS, k, 0);
-            double v[3] = {g.u[0], g.u[1], g.u[2]};
-            int att = 0;
-            bool done = false;
-            for (; att < kMaxL2DAttempts && !done; ++att) {
-                const uint4 r1 = draw(a.seed, cell, t_step, TAG_L2D_VEL, k, (uint32_t)(2 * att));
-                const uint4 r2 = draw(a.seed, cell, t_step, TAG_L2D_VEL, k, (uint32_t)(2 * att + 1));
-                double n0, n1, n2, n3;
-                box_muller(r1.x, r1.y, n0, n1);
-                box_muller(r1.z, r1.w, n2, n3);
-                const double xd[3] = {(double)(Real)n0, (double)(Real)n1, (double)(Real)n2};
-                double G = 1.0 + 0.5 * herm2_contract(g.a2, xd);
-                if (LAT::ORDER >= 3) G += herm3_contract(g.a3, xd) / 6.0;
-                const double R = u01d(r2.x);
-                if (G > g.C) envelope += 1;
-                if (g.C * R <= G) {
-                    v[0] = xd[0] + g.u[0];
-                    v[1] = xd[1] + g.u[1];
-                    v[2] = xd[2] + g.u[2];
-                    done = true;
-                }
-            }
-            if (!done) flags |= HYB_ST_SAMPLING_CAP;
-            attempts += (unsigned long long)att;
-            const uint32_t slot = base + g.offset + k;
-            a.x[slot] = (Real)ix + (Real)u01f(rp.x);
-            a.y[slot] = (Real)iy + (Real)u01f(rp.y);
-            a.vx[slot] = (Real)v[0];
-            a.vy[slot] = (Real)v[1];
-            a.vz[slot] = (Real)v[2];
+    }
+    // new particles: one thread each
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < total; p += stride) {
+        // the coupling cell that owns append position p: the last one whose offset is <= p
+        // (offsets ascend; an empty cell shares its offset with the next cell)
+        int lo = 0, hi = a.n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.grad[mid].offset <= p) lo = mid;
+            else hi = mid - 1;
         }
+        const GradRec& g = a.grad[lo];
+        const uint32_t cell = (uint32_t)a.list[lo];
+        const uint32_t k = p - g.offset;
+        const int ix = (int)(cell % (uint32_t)a.ncx), iy = (int)(cell / (uint32_t)a.ncx);
+        const uint4 rp = draw(a.seed, cell, t_step, TAG_L2D_POS, k, 0);
+        double v[3] = {g.u[0], g.u[1], g.u[2]};
+        int att = 0;
+        bool done = false;
+        for (; att < kMaxL2DAttempts && !done; ++att) {
+            const uint4 r1 = draw(a.seed, cell, t_step, TAG_L2D_VEL, k, (uint32_t)(2 * att));
+            const uint4 r2 = draw(a.seed, cell, t_step, TAG_L2D_VEL, k, (uint32_t)(2 * att + 1));
+            Real n0, n1, n2, n3;
+            gauss_pair<Real>(r1.x, r1.y, n0, n1);
+            gauss_pair<Real>(r1.z, r1.w, n2, n3);
+            const double xd[3] = {(double)n0, (double)n1, (double)n2};
+            double G = 1.0 + 0.5 * herm2_contract(g.a2, xd);
+            if (LAT::ORDER >= 3) G += herm3_contract(g.a3, xd) / 6.0;
+            const double Ru = u01d(r2.x);
+            if (G > g.C) envelope += 1;
+            if (g.C * Ru <= G) {
+                v[0] = xd[0] + g.u[0];
+                v[1] = xd[1] + g.u[1];
+                v[2] = xd[2] + g.u[2];
+                done = true;
+            }
+        }
+        if (!done) flags |= HYB_ST_SAMPLING_CAP;
+        attempts += (unsigned long long)att;
+        const uint32_t slot = base + p;
+        a.x[slot] = (Real)ix + (Real)u01f(rp.x);
+        a.y[slot] = (Real)iy + (Real)u01f(rp.y);
+        a.vx[slot] = (Real)v[0];
+        a.vy[slot] = (Real)v[1];
+        a.vz[slot] = (Real)v[2];
     }
     deleted = __reduce_add_sync(kFull, (unsigned)deleted);
     attempts = __reduce_add_sync(kFull, (unsigned)attempts);
@@ -281,6 +346,12 @@ MapArgs<Real> map_args(Ctx& c, const int32_t* list, int32_t n) {
     return a;
 }
 
+int blocks_for(const Ctx& c, int64_t threads_needed, int block, int per_sm) {
+    int64_t b = (threads_needed + block - 1) / block;
+    if (b > (int64_t)c.num_sms * per_sm) b = (int64_t)c.num_sms * per_sm;
+    return (int)(b < 1 ? 1 : b);
+}
+
 template <typename Real, class LAT>
 cudaError_t d2l_impl(Ctx& c, const int32_t* nodes, int32_t n) {
     MapArgs<Real> a = map_args<Real>(c, nodes, n);
@@ -294,12 +365,15 @@ template <typename Real, class LAT>
 cudaError_t l2d_impl(Ctx& c, const int32_t* cells, int32_t n) {
     MapArgs<Real> a = map_args<Real>(c, cells, n);
     prof_begin(c, K_L2D_PREP);
-    k_l2d_prep<Real, LAT><<<1, 256, 0, c.stream>>>(a);
+    k_l2d_coef<Real, LAT><<<blocks_for(c, (int64_t)n * 32, 128, 16), 128, 0, c.stream>>>(a);
     prof_end(c, K_L2D_PREP);
-    int64_t blocks = ((int64_t)n * 32 + 127) / 128;
-    if (blocks > (int64_t)c.num_sms * 16) blocks = (int64_t)c.num_sms * 16;
+    prof_begin(c, K_L2D_SCAN);
+    k_l2d_scan<Real><<<1, 1024, 0, c.stream>>>(a);
+    prof_end(c, K_L2D_SCAN);
+    // enough threads for about 1.5 ppc new particles per coupling cell
+    const int64_t expect = (int64_t)n * c.p.ppc * 3 / 2 + 32;
     prof_begin(c, K_L2D_SAMPLE);
-    k_l2d_sample<Real, LAT><<<(unsigned)blocks, 128, 0, c.stream>>>(a);
+    k_l2d_sample<Real, LAT><<<blocks_for(c, expect, 128, 16), 128, 0, c.stream>>>(a);
     prof_end(c, K_L2D_SAMPLE);
     return cudaGetLastError();
 }

@@ -77,8 +77,8 @@ void layout(const hyb_params& p, const hyb_derived& d, hyb_layout& L) {
     L.cell_start = take((nc + 1) * 4);
     L.tile_sum = take(ntiles * 4);
     L.crmax = take(nc * rb);
-    L.rem = take(nc * 8);
-    L.nbar_sum = take(nc * 8);
+    L.rem = take(nc * rb);
+    L.nbar_sum = take(nc * 4);
     L.acc = take(nc * kMoments * 8);
     for (int h = 0; h < 2; ++h) L.f[h] = take(q * nn * rb);
     L.ctrl = take(CTRL_WORDS * 4);
@@ -172,8 +172,8 @@ void resolve(Ctx& c) {
     s.cell_start = (uint32_t*)(a + L.cell_start);
     s.tile_sum = (uint32_t*)(a + L.tile_sum);
     s.crmax = a + L.crmax;
-    s.rem = (double*)(a + L.rem);
-    s.nbar_sum = (double*)(a + L.nbar_sum);
+    s.rem = a + L.rem;
+    s.nbar_sum = (uint32_t*)(a + L.nbar_sum);
     s.acc = (double*)(a + L.acc);
     s.ctrl = (uint32_t*)(a + L.ctrl);
     s.counters = (unsigned long long*)(a + L.counters);
