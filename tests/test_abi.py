@@ -72,7 +72,7 @@ def test_layout_is_aligned_and_disjoint(lib):
     for k, sz in (("key", 4 * d["capacity"]), ("arrival", 4 * d["capacity"]),
                   ("perm", 4 * d["capacity"]), ("count", 4 * d["ncells"]),
                   ("cell_start", 4 * (d["ncells"] + 1)), ("acc", 160 * d["ncells"]),
-                  ("rem", 8 * d["ncells"]), ("nbar_sum", 8 * d["ncells"]), ("ctrl", 64),
+                  ("rem", rb * d["ncells"]), ("nbar_sum", 4 * d["ncells"]), ("ctrl", 64),
                   ("counters", 128)):
         regions.append((getattr(L, k), sz))
     regions.sort()
