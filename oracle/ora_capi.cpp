@@ -261,26 +261,46 @@ int ora_grad_coeffs(int q, const double* f, double* out) {
     return 0;
 }
 
-// Table 1 sampler applied nsamp times to one population vector (double velocities).
-// info = [attempts, envelope violations, cap hits].
+// Table 1 sampler: nsamp particles of one cell from one population vector, in double.
+// info = [trials, envelope violations, capped].
 int ora_grad_sample(int q, const double* f, uint64_t seed, uint32_t cell, uint32_t t,
                     int64_t nsamp, double* v_out, uint64_t* info) {
     if (q != 39 && q != 19) return 1;
-    if (nsamp > 0xFFFFFF) return 2;
+    if (nsamp > 4000000) return 2;
     Lattice L = make_lattice(q);
     const int order = q == 39 ? 3 : 2;
     GradCell g = grad_from_populations(L, f, order);
-    uint64_t env = 0, att = 0, cap = 0;
-    for (int64_t k = 0; k < nsamp; ++k) {
-        double v[3];
-        int a = grad_sample_one<double>(g, order, seed, cell, t, (uint32_t)k, v, &env);
-        if (a > kMaxL2DAttempts) cap += 1;
-        att += (uint64_t)std::min(a, kMaxL2DAttempts);
-        for (int i = 0; i < 3; ++i) v_out[3 * k + i] = v[i];
-    }
-    info[0] = att;
+    std::vector<double> out(5 * (size_t)nsamp);
+    uint64_t env = 0;
+    bool capped = false;
+    const uint64_t trials = grad_sample_cell<double>(pack<double>(g), order, seed, cell, t,
+                                                     (uint32_t)nsamp, 0.0, 0.0, out.data(), &env,
+                                                     &capped);
+    for (int64_t k = 0; k < nsamp; ++k)
+        for (int i = 0; i < 3; ++i) v_out[3 * k + i] = out[5 * k + 2 + i];
+    info[0] = trials;
     info[1] = env;
-    info[2] = cap;
+    info[2] = capped ? 1 : 0;
+    return 0;
+}
+
+// G in the state precision (packed grouping) and in double (full tensors), for its pin.
+int ora_grad_G(int q, const double* f, const double* xi, int64_t n, int real_bytes, double* out) {
+    if (q != 39 && q != 19) return 1;
+    Lattice L = make_lattice(q);
+    const int order = q == 39 ? 3 : 2;
+    GradCell g = grad_from_populations(L, f, order);
+    for (int64_t k = 0; k < n; ++k) {
+        if (real_bytes == 4) {
+            GradPacked<float> p = pack<float>(g);
+            const float x[3] = {(float)xi[3 * k], (float)xi[3 * k + 1], (float)xi[3 * k + 2]};
+            out[2 * k] = grad_G<float>(p.a2, p.a3, x, order);
+        } else {
+            GradPacked<double> p = pack<double>(g);
+            out[2 * k] = grad_G<double>(p.a2, p.a3, &xi[3 * k], order);
+        }
+        out[2 * k + 1] = hermite_series(g.ahat, &xi[3 * k], order);
+    }
     return 0;
 }
 

@@ -10,11 +10,11 @@
 // LB2DSMC (Sec. 2.2, Table 1): from the populations, rho and u, then the Grad coefficients
 // of the distribution in the frame moving with u, normalised by rho (so a^(0) = 1 and
 // a^(1) = 0, and G of Eq. distr_outeq starts at n = 2): a2_ij = sum f c_i c_j / rho - d_ij,
-// a3_ijk = sum f c_i c_j c_k / rho with c = xi_a - u. M = largest |component|, C = 1 + 30 M
-// (Eq. C). Trial velocities from the unit Maxwellian by Box-Muller, accepted when
-// C R <= G(xi); the particle velocity is sqrt(kT/m) xi + u, i.e. xi + u in c_th units
-// (Eq. step6 read with the unit-variance weight of Eq. globalMax). The particle count
-// conserves the mapped mass: E[N] = rho * ppc, rounded stochastically.
+// a3_ijk = sum f c_i c_j c_k / rho with c = xi_a - u (FP64). M = largest |component|,
+// C = 1 + 30 M (Eq. C). Trial velocities from the unit Maxwellian by Box-Muller, accepted
+// when C R <= G(xi) (state precision); the particle velocity is sqrt(kT/m) xi + u, i.e.
+// xi + u in c_th units (Eq. step6 read with the unit-variance weight of Eq. globalMax). The
+// particle count conserves the mapped mass: E[N] = rho * ppc, rounded stochastically.
 #pragma once
 #include "ora_dsmc.hpp"
 #include "ora_lbm.hpp"
@@ -118,29 +118,91 @@ inline GradCell grad_from_populations(const Lattice& L, const double* f, int ord
     return g;
 }
 
-// One accepted velocity (Table 1 steps 4-6) for particle k of cell `cell` at step t.
-// Returns the number of attempts (> kMaxL2DAttempts when the cap was hit).
+// G of Eq. distr_outeq in the state precision, from the comoving coefficients packed by
+// symmetry (a2: xx xy xz yy yz zz; a3: xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz), as the full
+// sums over i, j (, k) of Table 1 grouped by distinct entries:
+//   a2 : H2 = sum_i a2_ii (x_i^2 - 1) + 2 sum_{i<j} a2_ij x_i x_j,
+//   a3 : H3 = sum over distinct (i<=j<=k) of (multiplicity) a3_ijk x_i x_j x_k - 3 x . t,
+//   t_i = sum_j a3_ijj. The grouping is fixed so that the accept decision is reproducible.
 template <class Real>
-int grad_sample_one(const GradCell& g, int order, uint64_t seed, uint32_t cell, uint32_t t,
-                    uint32_t k, Real* v, uint64_t* envelope) {
-    for (int att = 0; att < kMaxL2DAttempts; ++att) {
-        U4 r = draw(seed, cell, t, TAG_L2D_VEL, k, (uint32_t)(2 * att));
-        U4 r2 = draw(seed, cell, t, TAG_L2D_VEL, k, (uint32_t)(2 * att + 1));
-        Real n0, n1, n2, n3;
-        gauss_pair<Real>(r[0], r[1], n0, n1);
-        gauss_pair<Real>(r[2], r[3], n2, n3);
-        const Real xi[3] = {n0, n1, n2};
-        const double xd[3] = {(double)xi[0], (double)xi[1], (double)xi[2]};
-        const double G = hermite_series(g.ahat, xd, order);
-        const double R = u01d(r2[0]);
+Real grad_G(const Real* a2, const Real* a3, const Real* xi, int order) {
+    const Real X = xi[0], Y = xi[1], Z = xi[2];
+    const Real h2 = a2[0] * (X * X - (Real)1) + a2[3] * (Y * Y - (Real)1) +
+                    a2[5] * (Z * Z - (Real)1) +
+                    (Real)2 * (a2[1] * X * Y + a2[2] * X * Z + a2[4] * Y * Z);
+    Real G = (Real)1 + (Real)0.5 * h2;
+    if (order >= 3) {
+        const Real cubic = a3[0] * X * X * X + (Real)3 * a3[1] * X * X * Y +
+                           (Real)3 * a3[2] * X * X * Z + (Real)3 * a3[3] * X * Y * Y +
+                           (Real)6 * a3[4] * X * Y * Z + (Real)3 * a3[5] * X * Z * Z +
+                           a3[6] * Y * Y * Y + (Real)3 * a3[7] * Y * Y * Z +
+                           (Real)3 * a3[8] * Y * Z * Z + a3[9] * Z * Z * Z;
+        const Real tx = a3[0] + a3[3] + a3[5];
+        const Real ty = a3[1] + a3[6] + a3[8];
+        const Real tz = a3[2] + a3[7] + a3[9];
+        const Real h3 = cubic - (Real)3 * (tx * X + ty * Y + tz * Z);
+        G = G + h3 * (Real)(1.0 / 6.0);
+    }
+    return G;
+}
+
+// Packed state-precision copies of a cell's Grad coefficients.
+template <class Real>
+struct GradPacked {
+    Real a2[6], a3[10], u[3], C;
+};
+
+template <class Real>
+GradPacked<Real> pack(const GradCell& g) {
+    GradPacked<Real> p;
+    const int i2[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+    const int i3[10][3] = {{0, 0, 0}, {0, 0, 1}, {0, 0, 2}, {0, 1, 1}, {0, 1, 2},
+                           {0, 2, 2}, {1, 1, 1}, {1, 1, 2}, {1, 2, 2}, {2, 2, 2}};
+    for (int k = 0; k < 6; ++k) p.a2[k] = (Real)g.ahat.a2[i2[k][0]][i2[k][1]];
+    for (int k = 0; k < 10; ++k) p.a3[k] = (Real)g.ahat.a3[i3[k][0]][i3[k][1]][i3[k][2]];
+    for (int i = 0; i < 3; ++i) p.u[i] = (Real)g.u[i];
+    p.C = (Real)g.C;
+    return p;
+}
+
+// Table 1 steps 4-6 for one cell: trials j = 0, 1, 2, ... of the cell's stream (Philox
+// blocks 0 and 1 of counter (cell, t, tag, j)); a trial draws xi from the unit Maxwellian
+// by Box-Muller and R uniform, and is accepted when C R <= G(xi). The k-th accepted trial
+// gives the k-th new particle: velocity xi + u, position from the trial's block-1 words.
+// Trials are capped at min(1000 n, 2^24); particles left without a trial are appended as
+// deleted (x = -1). Returns the number of trials used.
+template <class Real>
+uint64_t grad_sample_cell(const GradPacked<Real>& g, int order, uint64_t seed, uint32_t cell,
+                          uint32_t t, uint32_t n, Real ix, Real iy, Real* out /* n x 5 */,
+                          uint64_t* envelope, bool* capped) {
+    const uint64_t cap = std::min<uint64_t>(1000ull * n, 0xFFFFFFull);
+    uint32_t produced = 0;
+    uint64_t j = 0;
+    for (; produced < n && j < cap; ++j) {
+        U4 r = draw(seed, cell, t, TAG_L2D_VEL, (uint32_t)j, 0);
+        U4 r2 = draw(seed, cell, t, TAG_L2D_VEL, (uint32_t)j, 1);
+        Real xi[3], spare;
+        gauss_pair<Real>(r[0], r[1], xi[0], xi[1]);
+        gauss_pair<Real>(r[2], r[3], xi[2], spare);
+        const Real G = grad_G<Real>(g.a2, g.a3, xi, order);
+        const Real R = (Real)u01f(r2[0]);
         if (G > g.C) *envelope += 1;
         if (g.C * R <= G) {
-            for (int i = 0; i < 3; ++i) v[i] = (Real)(xd[i] + g.u[i]);
-            return att + 1;
+            Real* o = out + 5 * (size_t)produced;
+            o[0] = ix + (Real)u01f(r2[1]);
+            o[1] = iy + (Real)u01f(r2[2]);
+            for (int i = 0; i < 3; ++i) o[2 + i] = xi[i] + g.u[i];
+            produced += 1;
         }
     }
-    for (int i = 0; i < 3; ++i) v[i] = (Real)g.u[i];
-    return kMaxL2DAttempts + 1;
+    *capped = produced < n;
+    for (; produced < n; ++produced) {
+        Real* o = out + 5 * (size_t)produced;
+        o[0] = (Real)-1;
+        o[1] = iy;
+        o[2] = o[3] = o[4] = (Real)0;
+    }
+    return j;
 }
 
 template <class Real>
@@ -207,22 +269,19 @@ void map_lbm_to_dsmc(Dsmc<Real>& D, const Lbm<Real>& B, const int32_t* cells, in
     for (int c = 0; c < n; ++c) {
         const uint32_t cell = (uint32_t)cells[c];
         const int ix = (int)(cell % D.p.ncx), iy = (int)(cell / D.p.ncx);
+        std::vector<Real> out(5 * (size_t)nnew[c]);
+        bool capped = false;
+        const uint64_t trials = grad_sample_cell<Real>(pack<Real>(gc[c]), B.d.order, D.p.seed, cell,
+                                                       t, nnew[c], (Real)ix, (Real)iy, out.data(),
+                                                       &D.counters[C_ENVELOPE], &capped);
+        if (capped) D.status |= ST_SAMPLING_CAP;
+        D.counters[C_L2D_ATTEMPTS] += trials;
         for (uint32_t k = 0; k < nnew[c]; ++k) {
-            U4 rp = draw(D.p.seed, cell, t, TAG_L2D_POS, k, 0);
-            Real v[3];
-            const int att = grad_sample_one<Real>(gc[c], B.d.order, D.p.seed, cell, t, k, v,
-                                                  &D.counters[C_ENVELOPE]);
-            if (att > kMaxL2DAttempts) {
-                D.status |= ST_SAMPLING_CAP;
-                D.counters[C_L2D_ATTEMPTS] += kMaxL2DAttempts;
-            } else {
-                D.counters[C_L2D_ATTEMPTS] += (uint64_t)att;
-            }
-            D.x.push_back((Real)ix + (Real)u01f(rp[0]));
-            D.y.push_back((Real)iy + (Real)u01f(rp[1]));
-            D.vx.push_back(v[0]);
-            D.vy.push_back(v[1]);
-            D.vz.push_back(v[2]);
+            D.x.push_back(out[5 * k]);
+            D.y.push_back(out[5 * k + 1]);
+            D.vx.push_back(out[5 * k + 2]);
+            D.vy.push_back(out[5 * k + 3]);
+            D.vz.push_back(out[5 * k + 4]);
         }
         D.counters[C_CREATED] += nnew[c];
     }

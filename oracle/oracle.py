@@ -90,6 +90,7 @@ def lib():
         L.ora_grad_coeffs.argtypes = [ctypes.c_int, vp, vp]
         L.ora_grad_sample.argtypes = [ctypes.c_int, vp, u64, u32, u32, i64, vp, vp]
         L.ora_float_funcs.argtypes = [vp, i64, vp, vp, vp]
+        L.ora_grad_G.argtypes = [ctypes.c_int, vp, vp, i64, ctypes.c_int, vp]
         L.ora_gauss_pairs.argtypes = [vp, i64, ctypes.c_int, vp]
         _LIB = L
     return _LIB
@@ -165,6 +166,15 @@ def grad_sample(q, f, seed, cell, t, n):
     if rc != 0:
         raise ValueError(rc)
     return v, {"attempts": int(info[0]), "envelope": int(info[1]), "cap": int(info[2])}
+
+
+def grad_G(q, f, xi, real_bytes):
+    """G(xi) of the populations f: (packed state-precision form, full-tensor double form)."""
+    f = np.ascontiguousarray(f, np.float64)
+    xi = np.ascontiguousarray(xi, np.float64).reshape(-1, 3)
+    out = np.empty((xi.shape[0], 2), np.float64)
+    lib().ora_grad_G(q, _ptr(f), _ptr(xi), xi.shape[0], real_bytes, _ptr(out))
+    return out[:, 0], out[:, 1]
 
 
 def float_funcs(x):

@@ -611,3 +611,20 @@ def test_float_state_init_is_maxwellian():
     se = 1 / math.sqrt(v.shape[1])
     assert np.all(np.abs(v.mean(1)) < 5 * se)
     assert np.all(np.abs(v.var(1) - 1) < 5 * math.sqrt(2) * se)
+
+
+@pytest.mark.parametrize("real_bytes,tol", [(8, 1e-13), (4, 2e-6)])
+def test_grad_G_packed_form_equals_full_tensor_sum(real_bytes, tol):
+    # the acceptance function G of Eq. distr_outeq in its fixed packed grouping (state
+    # precision) against the full-tensor Hermite sum in double
+    rho, u = 1.0, np.array([0.02, 0.1, -0.03])
+    I = np.eye(3)
+    P = I + np.outer(u, u) + np.array([[0.05, -0.03, 0.01], [-0.03, -0.02, 0.02], [0.01, 0.02, -0.03]])
+    Q = (np.einsum("i,j,k->ijk", u, u, u) + np.einsum("i,jk->ijk", u, I)
+         + np.einsum("j,ik->ijk", u, I) + np.einsum("k,ij->ijk", u, I))
+    for perm in set(itertools.permutations((0, 1, 2))):
+        Q[perm] += 0.03
+    f = O.dsmc2lb_node(39, _sums_from_coeffs(rho, u, P, Q, 1, 100), 1, 100)
+    xi = np.random.default_rng(2).standard_normal((5000, 3)).astype(np.float32).astype(np.float64)
+    gp, gf = O.grad_G(39, f, xi, real_bytes)
+    assert np.all(np.abs(gp - gf) <= tol * (1 + np.abs(gf)))
