@@ -13,12 +13,14 @@
 //                a3 = sum f c c c / rho (c = xi - u), M, C = 1 + 30 M (Eq. C), and the
 //                particle count floor(rho ppc + U) (FP64, lanes over populations);
 //   k_l2d_scan   one block: append offsets (exclusive scan), capacity check, slot count;
-//   k_l2d_sample one thread per new particle: Box-Muller trial xi from the unit Maxwellian,
-//                accepted when C R <= G(xi), G = 1 + a2:H2/2 + a3:H3/6 (Eq. distr_outeq),
-//                velocity xi + u (Eq. step6 in c_th units), position uniform in the cell;
-//                one warp per coupling cell marks the cell's old particles deleted.
-// Draws are keyed by (cell, step, purpose, particle index, trial), so the results do not
-// depend on the launch shape.
+//   k_l2d_sample one warp per coupling cell: the old particles are marked deleted; the
+//                cell's trial stream is evaluated 32 trials at a time: Box-Muller xi from
+//                the unit Maxwellian, accepted when C R <= G(xi), G = 1 + a2:H2/2 + a3:H3/6
+//                (Eq. distr_outeq) in the state precision; the k-th accepted trial becomes
+//                the k-th new particle, velocity xi + u (Eq. step6 in c_th units), position
+//                uniform in the cell from the same trial's draws.
+// Draws are keyed by (cell, step, purpose, trial index), so the results do not depend on
+// the launch shape.
 #include "hyb_internal.cuh"
 
 namespace hyb {
@@ -56,13 +58,14 @@ __global__ void __launch_bounds__(128) k_d2l(MapArgs<Real> a) {
     }
     // FP64 coefficient solve
     const double rho = (NS / (double)S) / (double)a.ppc;
-    const double m1x = m[1] / NS, m1y = m[2] / NS, m1z = m[3] / NS;
+    const double iNS = 1.0 / NS;
+    const double m1x = m[1] * iNS, m1y = m[2] * iNS, m1z = m[3] * iNS;
     const double d2[6] = {1, 0, 0, 1, 0, 1};
     // sym(<v> I) for the packed entries xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz
     const double s3[10] = {3 * m1x, m1y, m1z, m1x, 0.0, m1x, 3 * m1y, m1z, m1y, 3 * m1z};
     Real a2[6], a3[10];
-    for (int k = 0; k < 6; ++k) a2[k] = (Real)(rho * (m[4 + k] / NS - d2[k]));
-    for (int k = 0; k < 10; ++k) a3[k] = (Real)(rho * (m[10 + k] / NS - s3[k]));
+    for (int k = 0; k < 6; ++k) a2[k] = (Real)(rho * (m[4 + k] * iNS - d2[k]));
+    for (int k = 0; k < 10; ++k) a3[k] = (Real)(rho * (m[10 + k] * iNS - s3[k]));
     const Real r0 = (Real)rho, a1x = (Real)(rho * m1x), a1y = (Real)(rho * m1y), a1z = (Real)(rho * m1z);
     const Real tx = a3[0] + a3[3] + a3[5], ty = a3[1] + a3[6] + a3[8], tz = a3[2] + a3[7] + a3[9];
     const Real tr2 = a2[0] + a2[3] + a2[5];
@@ -123,7 +126,8 @@ __global__ void __launch_bounds__(128) k_l2d_coef(MapArgs<Real> a) {
             fb[h] = s;
         }
         rho = warp_sum(rho);
-        const double ux = warp_sum(jx) / rho, uy = warp_sum(jy) / rho, uz = warp_sum(jz) / rho;
+        const double irho = 1.0 / rho;
+        const double ux = warp_sum(jx) * irho, uy = warp_sum(jy) * irho, uz = warp_sum(jz) * irho;
         double m2[6] = {0, 0, 0, 0, 0, 0}, m3[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
         for (int h = 0; h < QL; ++h) {
@@ -133,23 +137,23 @@ __global__ void __launch_bounds__(128) k_l2d_coef(MapArgs<Real> a) {
                 const double cy = rr * LatTab<LAT>::e(q, 1) - uy;
                 const double cz = rr * LatTab<LAT>::e(q, 2) - uz;
                 const double f = fb[h];
-                m2[0] += f * cx * cx / rho;
-                m2[1] += f * cx * cy / rho;
-                m2[2] += f * cx * cz / rho;
-                m2[3] += f * cy * cy / rho;
-                m2[4] += f * cy * cz / rho;
-                m2[5] += f * cz * cz / rho;
+                m2[0] += f * cx * cx * irho;
+                m2[1] += f * cx * cy * irho;
+                m2[2] += f * cx * cz * irho;
+                m2[3] += f * cy * cy * irho;
+                m2[4] += f * cy * cz * irho;
+                m2[5] += f * cz * cz * irho;
                 if (LAT::ORDER >= 3) {
-                    m3[0] += f * cx * cx * cx / rho;
-                    m3[1] += f * cx * cx * cy / rho;
-                    m3[2] += f * cx * cx * cz / rho;
-                    m3[3] += f * cx * cy * cy / rho;
-                    m3[4] += f * cx * cy * cz / rho;
-                    m3[5] += f * cx * cz * cz / rho;
-                    m3[6] += f * cy * cy * cy / rho;
-                    m3[7] += f * cy * cy * cz / rho;
-                    m3[8] += f * cy * cz * cz / rho;
-                    m3[9] += f * cz * cz * cz / rho;
+                    m3[0] += f * cx * cx * cx * irho;
+                    m3[1] += f * cx * cx * cy * irho;
+                    m3[2] += f * cx * cx * cz * irho;
+                    m3[3] += f * cx * cy * cy * irho;
+                    m3[4] += f * cx * cy * cz * irho;
+                    m3[5] += f * cx * cz * cz * irho;
+                    m3[6] += f * cy * cy * cy * irho;
+                    m3[7] += f * cy * cy * cz * irho;
+                    m3[8] += f * cy * cz * cz * irho;
+                    m3[9] += f * cz * cz * cz * irho;
                 }
             }
         }
@@ -239,18 +243,43 @@ __global__ void __launch_bounds__(1024) k_l2d_scan(MapArgs<Real> a) {
     }
 }
 
+// G of Eq. distr_outeq in the state precision, from the comoving coefficients packed by
+// symmetry, with the grouping of the Table 1 sums fixed (distinct entries times their
+// multiplicity) so that the accept decision is reproducible.
+template <typename Real, int ORDER>
+__device__ __forceinline__ Real grad_G(const Real* a2, const Real* a3, Real X, Real Y, Real Z) {
+    const Real h2 = a2[0] * (X * X - (Real)1) + a2[3] * (Y * Y - (Real)1) +
+                    a2[5] * (Z * Z - (Real)1) +
+                    (Real)2 * (a2[1] * X * Y + a2[2] * X * Z + a2[4] * Y * Z);
+    Real G = (Real)1 + (Real)0.5 * h2;
+    if (ORDER >= 3) {
+        const Real cubic = a3[0] * X * X * X + (Real)3 * a3[1] * X * X * Y +
+                           (Real)3 * a3[2] * X * X * Z + (Real)3 * a3[3] * X * Y * Y +
+                           (Real)6 * a3[4] * X * Y * Z + (Real)3 * a3[5] * X * Z * Z +
+                           a3[6] * Y * Y * Y + (Real)3 * a3[7] * Y * Y * Z +
+                           (Real)3 * a3[8] * Y * Z * Z + a3[9] * Z * Z * Z;
+        const Real tx = a3[0] + a3[3] + a3[5];
+        const Real ty = a3[1] + a3[6] + a3[8];
+        const Real tz = a3[2] + a3[7] + a3[9];
+        const Real h3 = cubic - (Real)3 * (tx * X + ty * Y + tz * Z);
+        G = G + h3 * (Real)(1.0 / 6.0);
+    }
+    return G;
+}
+
+// One warp per coupling cell: mark the old particles deleted, then evaluate the cell's trial
+// stream 32 trials at a time; the k-th accepted trial becomes the k-th new particle.
 template <typename Real, class LAT>
-__global__ void __launch_bounds__(128) k_l2d_sample(MapArgs<Real> a) {
+__global__ void __launch_bounds__(64) k_l2d_sample(MapArgs<Real> a) {
     if (a.ctrl[CTRL_L2D_SKIP]) return;
     const uint32_t base = a.ctrl[CTRL_L2D_BASE];
-    const uint32_t total = a.ctrl[CTRL_L2D_TOTAL];
     const uint32_t t_step = a.ctrl[CTRL_STEP];
     const unsigned lane = lane_id();
-    unsigned long long deleted = 0, attempts = 0, envelope = 0;
-    uint32_t flags = 0;
-    // old particles of the coupling cells are marked deleted: one warp per cell
+    const unsigned lt = (1u << lane) - 1u;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
+    unsigned long long deleted = 0, attempts = 0, envelope = 0;
+    uint32_t flags = 0;
     for (int ci = gw; ci < a.n; ci += nw) {
         const uint32_t cell = (uint32_t)a.list[ci];
         const uint32_t s0 = a.cell_start[cell], s1 = a.cell_start[cell + 1];
@@ -258,56 +287,76 @@ __global__ void __launch_bounds__(128) k_l2d_sample(MapArgs<Real> a) {
             if (a.x[i] >= (Real)0) deleted += 1;
             a.x[i] = (Real)-1;
         }
-    }
-    // new particles: one thread each
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < total; p += stride) {
-        // the coupling cell that owns append position p: the last one whose offset is <= p
-        // (offsets ascend; an empty cell shares its offset with the next cell)
-        int lo = 0, hi = a.n - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (a.grad[mid].offset <= p) lo = mid;
-            else hi = mid - 1;
+        const GradRec& g = a.grad[ci];
+        Real a2[6], a3[10];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) a2[k] = (Real)g.a2[k];
+#pragma unroll
+        for (int k = 0; k < 10; ++k) a3[k] = (Real)g.a3[k];
+        const Real C = (Real)g.C;
+        const Real ux = (Real)g.u[0], uy = (Real)g.u[1], uz = (Real)g.u[2];
+        const uint32_t nnew = g.nnew;
+        const uint32_t out0 = base + g.offset;
+        const Real fx = (Real)(cell % (uint32_t)a.ncx), fy = (Real)(cell / (uint32_t)a.ncx);
+        const uint64_t cap64 = 1000ull * nnew;
+        const uint32_t cap = cap64 < 0xFFFFFFull ? (uint32_t)cap64 : 0xFFFFFFu;
+        uint32_t produced = 0, j0 = 0;
+        while (produced < nnew && j0 < cap) {
+            const uint32_t j = j0 + lane;
+            const bool valid = j < cap;
+            bool acc = false, env = false;
+            Real X = 0, Y = 0, Z = 0;
+            uint4 r2 = make_uint4(0, 0, 0, 0);
+            if (valid) {
+                const uint4 r1 = draw(a.seed, cell, t_step, TAG_L2D_VEL, j, 0);
+                r2 = draw(a.seed, cell, t_step, TAG_L2D_VEL, j, 1);
+                Real spare;
+                gauss_pair<Real>(r1.x, r1.y, X, Y);
+                gauss_pair<Real>(r1.z, r1.w, Z, spare);
+                const Real G = grad_G<Real, LAT::ORDER>(a2, a3, X, Y, Z);
+                const Real R = (Real)u01f(r2.x);
+                env = G > C;
+                acc = C * R <= G;
+            }
+            const unsigned amask = __ballot_sync(kFull, acc);
+            const unsigned emask = __ballot_sync(kFull, env);
+            const unsigned vmask = __ballot_sync(kFull, valid);
+            const uint32_t need = nnew - produced;
+            const uint32_t rank = __popc(amask & lt);
+            uint32_t used_mask = vmask;  // trials consumed this round
+            if ((uint32_t)__popc(amask) >= need) {
+                const unsigned lastm = __ballot_sync(kFull, acc && rank == need - 1u);
+                const int last = __ffs(lastm) - 1;
+                used_mask = last == 31 ? 0xFFFFFFFFu : ((2u << last) - 1u);
+            }
+            if (acc && rank < need) {
+                const uint32_t slot = out0 + produced + rank;
+                a.x[slot] = fx + (Real)u01f(r2.y);
+                a.y[slot] = fy + (Real)u01f(r2.z);
+                a.vx[slot] = X + ux;
+                a.vy[slot] = Y + uy;
+                a.vz[slot] = Z + uz;
+            }
+            if (lane == 0) {
+                attempts += (unsigned long long)__popc(used_mask);
+                envelope += (unsigned long long)__popc(emask & used_mask);
+            }
+            produced += min((uint32_t)__popc(amask), need);
+            j0 += 32;
         }
-        const GradRec& g = a.grad[lo];
-        const uint32_t cell = (uint32_t)a.list[lo];
-        const uint32_t k = p - g.offset;
-        const int ix = (int)(cell % (uint32_t)a.ncx), iy = (int)(cell / (uint32_t)a.ncx);
-        const uint4 rp = draw(a.seed, cell, t_step, TAG_L2D_POS, k, 0);
-        double v[3] = {g.u[0], g.u[1], g.u[2]};
-        int att = 0;
-        bool done = false;
-        for (; att < kMaxL2DAttempts && !done; ++att) {
-            const uint4 r1 = draw(a.seed, cell, t_step, TAG_L2D_VEL, k, (uint32_t)(2 * att));
-            const uint4 r2 = draw(a.seed, cell, t_step, TAG_L2D_VEL, k, (uint32_t)(2 * att + 1));
-            Real n0, n1, n2, n3;
-            gauss_pair<Real>(r1.x, r1.y, n0, n1);
-            gauss_pair<Real>(r1.z, r1.w, n2, n3);
-            const double xd[3] = {(double)n0, (double)n1, (double)n2};
-            double G = 1.0 + 0.5 * herm2_contract(g.a2, xd);
-            if (LAT::ORDER >= 3) G += herm3_contract(g.a3, xd) / 6.0;
-            const double Ru = u01d(r2.x);
-            if (G > g.C) envelope += 1;
-            if (g.C * Ru <= G) {
-                v[0] = xd[0] + g.u[0];
-                v[1] = xd[1] + g.u[1];
-                v[2] = xd[2] + g.u[2];
-                done = true;
+        if (produced < nnew) {
+            flags |= HYB_ST_SAMPLING_CAP;
+            for (uint32_t k = produced + lane; k < nnew; k += 32) {
+                const uint32_t slot = out0 + k;
+                a.x[slot] = (Real)-1;
+                a.y[slot] = fy;
+                a.vx[slot] = (Real)0;
+                a.vy[slot] = (Real)0;
+                a.vz[slot] = (Real)0;
             }
         }
-        if (!done) flags |= HYB_ST_SAMPLING_CAP;
-        attempts += (unsigned long long)att;
-        const uint32_t slot = base + p;
-        a.x[slot] = (Real)ix + (Real)u01f(rp.x);
-        a.y[slot] = (Real)iy + (Real)u01f(rp.y);
-        a.vx[slot] = (Real)v[0];
-        a.vy[slot] = (Real)v[1];
-        a.vz[slot] = (Real)v[2];
     }
     deleted = __reduce_add_sync(kFull, (unsigned)deleted);
-    attempts = __reduce_add_sync(kFull, (unsigned)attempts);
-    envelope = __reduce_add_sync(kFull, (unsigned)envelope);
     flags = __reduce_or_sync(kFull, flags);
     if (lane == 0) {
         if (deleted) atomicAdd(&a.counters[HYB_C_DELETED], deleted);
@@ -370,10 +419,8 @@ cudaError_t l2d_impl(Ctx& c, const int32_t* cells, int32_t n) {
     prof_begin(c, K_L2D_SCAN);
     k_l2d_scan<Real><<<1, 1024, 0, c.stream>>>(a);
     prof_end(c, K_L2D_SCAN);
-    // enough threads for about 1.5 ppc new particles per coupling cell
-    const int64_t expect = (int64_t)n * c.p.ppc * 3 / 2 + 32;
     prof_begin(c, K_L2D_SAMPLE);
-    k_l2d_sample<Real, LAT><<<blocks_for(c, expect, 128, 16), 128, 0, c.stream>>>(a);
+    k_l2d_sample<Real, LAT><<<blocks_for(c, (int64_t)n * 32, 64, 32), 64, 0, c.stream>>>(a);
     prof_end(c, K_L2D_SAMPLE);
     return cudaGetLastError();
 }
