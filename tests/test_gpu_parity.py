@@ -81,8 +81,14 @@ def _compare_dsmc(h, o, real_bytes, acc_rtol=1e-5):
     hc, oc = h.counters(), o.counters()
     for k in ("candidates", "collisions", "wall_hits", "created", "deleted"):
         assert hc[k] == oc[k], (k, hc[k], oc[k])
-    assert np.array_equal(h.crmax().cpu().numpy(), o.get(O.A_CRMAX))
-    assert np.array_equal(h.rem().cpu().numpy(), o.get(O.A_REM))
+    if real_bytes == 4:
+        assert np.array_equal(h.crmax().cpu().numpy(), o.get(O.A_CRMAX))
+        assert np.array_equal(h.rem().cpu().numpy(), o.get(O.A_REM))
+    else:
+        # double state draws its normals with the platform's double log/sin/cos, which may
+        # differ in the last bit between the GPU and the host
+        assert np.allclose(h.crmax().cpu().numpy(), o.get(O.A_CRMAX), rtol=1e-12, atol=0)
+        assert np.allclose(h.rem().cpu().numpy(), o.get(O.A_REM), rtol=0, atol=1e-9)
     assert np.array_equal(h.nbar_sum().cpu().numpy().view(np.uint32), o.get(O.A_NBAR_SUM))
     ga = h.acc().cpu().numpy()
     oa = o.acc()
