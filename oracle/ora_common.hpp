@@ -56,6 +56,8 @@ struct Derived {
     double c_th_ms;   // sqrt(k T / m) in m/s
     int64_t ncells, nx, ny, nnodes, capacity;
     int32_t q, order;
+    int32_t bin;   // particle slots per cell in the library's binned layout
+    int32_t pad;
 };
 
 constexpr double kPi = 3.14159265358979323846;
@@ -80,7 +82,8 @@ inline Derived derive(const Params& p) {
     d.nx = (int64_t)p.ncx * p.lb_ratio;
     d.ny = (int64_t)p.ncy * p.lb_ratio;
     d.nnodes = d.nx * d.ny;
-    d.capacity = (int64_t)std::ceil(p.capacity_factor * (double)d.ncells * (double)p.ppc);
+    d.bin = ((int32_t)std::ceil(p.capacity_factor * (double)p.ppc) + 31) / 32 * 32;
+    d.capacity = d.ncells * (int64_t)d.bin;
     d.q = p.lattice;
     d.order = (p.lattice == 39) ? 3 : 2;
     return d;

@@ -91,9 +91,11 @@ struct Dsmc {
 
     // Diffuse isothermal re-emission from a wall at rest (Sec. 3.1, "fully diffuse
     // reflection"): normal speed from the flux-weighted Maxwellian sqrt(-2 ln U), tangential
-    // components Gaussian. `sign` points into the gas.
-    void reemit(uint32_t slot, uint32_t s, int bounce, Real sign, Real& ux, Real& uy, Real& uz) {
-        U4 r = draw(p.seed, slot, s, TAG_WALL, (uint32_t)bounce, 0);
+    // components Gaussian. `sign` points into the gas. Draws are keyed by the particle's cell
+    // and rank in that cell at the start of the step, and the bounce number.
+    void reemit(uint32_t cell, uint32_t rank, uint32_t s, int bounce, Real sign, Real& ux, Real& uy,
+                Real& uz) {
+        U4 r = draw(p.seed, cell, s, TAG_WALL, (rank << 3) | (uint32_t)bounce, 0);
         const Real vn = wall_speed<Real>(r[0]);
         Real t1, t2;
         gauss_pair<Real>(r[1], r[2], t1, t2);
@@ -114,7 +116,7 @@ struct Dsmc {
 
     // Move one particle through one time step: body-force kick, free flight, wall hits,
     // periodic wrap in the streamwise direction. Returns the new cell key.
-    uint32_t move_one(uint32_t i, uint32_t s) {
+    uint32_t move_one(uint32_t i, uint32_t s, uint32_t cell, uint32_t rank) {
         if (!(x[i] >= (Real)0)) return kDeadKey;  // deleted by a coupling step
         const Real H = (Real)p.ncx;
         const Real L = (Real)p.ncy;
@@ -143,7 +145,7 @@ struct Dsmc {
             px = left ? (Real)0 : H;
             t = t - th;
             if (t < (Real)0) t = (Real)0;
-            reemit(i, s, b, left ? (Real)1 : (Real)-1, ux, uy, uz);
+            reemit(cell, rank, s, b, left ? (Real)1 : (Real)-1, ux, uy, uz);
         }
         if (py < (Real)0 || py >= L) {
             py = py - L * std::floor(py / L);
@@ -175,7 +177,10 @@ struct Dsmc {
         permute(x); permute(y); permute(vx); permute(vy); permute(vz);
         std::fill(cell_start.begin(), cell_start.end(), 0u);
         for (uint32_t i : idx) cell_start[key[i] + 1] += 1;
-        for (int64_t c = 0; c < d.ncells; ++c) cell_start[c + 1] += cell_start[c];
+        for (int64_t c = 0; c < d.ncells; ++c) {
+            if (cell_start[c + 1] > (uint32_t)d.bin) status |= ST_CAPACITY;  // bin overflow
+            cell_start[c + 1] += cell_start[c];
+        }
     }
 
     // Isotropic unit vector by Marsaglia (1972): (u1, u2) uniform in the unit disc,
@@ -267,7 +272,9 @@ struct Dsmc {
     void phase_move_sort() {
         const uint32_t s = (uint32_t)step;
         std::vector<uint32_t> key(ntot());
-        for (uint32_t i = 0; i < key.size(); ++i) key[i] = move_one(i, s);
+        for (int64_t c = 0; c < d.ncells; ++c)
+            for (uint32_t i = cell_start[c]; i < cell_start[c + 1]; ++i)
+                key[i] = move_one(i, s, (uint32_t)c, i - cell_start[c]);
         sort_by_cell(key);
     }
     void phase_collide() {

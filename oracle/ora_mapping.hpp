@@ -227,20 +227,24 @@ void map_dsmc_to_lbm(Dsmc<Real>& D, Lbm<Real>& B, const int32_t* nodes, int n) {
     }
 }
 
+// LB2DSMC over a list of distinct cells: each listed cell's particles are replaced by the
+// cell's regenerated ones (Sec. 2.2 "N_LB2DSMC ... conservation of mass at the coupling
+// sites"), so the particle array stays ordered by cell. A cell whose new count exceeds the
+// per-cell slot count `bin` keeps its particles and raises the capacity status.
 template <class Real>
 void map_lbm_to_dsmc(Dsmc<Real>& D, const Lbm<Real>& B, const int32_t* cells, int n) {
     const Lattice& L = B.L;
     const int r = D.p.lb_ratio;
     const uint32_t t = (uint32_t)D.step;
-    std::vector<GradCell> gc(n);
-    std::vector<uint32_t> nnew(n, 0);
-    uint64_t total = 0;
-    for (int c = 0; c < n; ++c) {
-        const int64_t cell = cells[c];
-        if (cell < 0 || cell >= D.d.ncells) {
+    for (int c = 0; c < n; ++c)
+        if (cells[c] < 0 || cells[c] >= D.d.ncells) {
             D.status |= ST_BAD_INPUT;
             return;
         }
+    std::vector<int> slot_of(D.d.ncells, -1);
+    std::vector<std::vector<Real>> fresh(n);
+    for (int c = 0; c < n; ++c) {
+        const int64_t cell = cells[c];
         const int64_t ix = cell % D.p.ncx, iy = cell / D.p.ncx;
         std::vector<double> fbar(L.q, 0.0);
         for (int q = 0; q < L.q; ++q) {
@@ -249,42 +253,56 @@ void map_lbm_to_dsmc(Dsmc<Real>& D, const Lbm<Real>& B, const int32_t* cells, in
                 for (int dx = 0; dx < r; ++dx) s += B.fa(q, ix * r + dx, iy * r + dy);
             fbar[q] = s / (double)(r * r);
         }
-        gc[c] = grad_from_populations(L, fbar.data(), B.d.order);
+        const GradCell g = grad_from_populations(L, fbar.data(), B.d.order);
         const double u = u01d(draw(D.p.seed, (uint32_t)cell, t, TAG_L2D_ROUND, 0, 0)[0]);
-        const double ne = std::floor(gc[c].rho * (double)D.p.ppc + u);
-        nnew[c] = ne > 0.0 ? (uint32_t)ne : 0u;
-        total += nnew[c];
-    }
-    if ((int64_t)(D.ntot() + total) > D.d.capacity) {
-        D.status |= ST_CAPACITY;
-        return;
-    }
-    for (int c = 0; c < n; ++c) {
-        const uint32_t cell = (uint32_t)cells[c];
-        for (uint32_t i = D.cell_start[cell]; i < D.cell_start[cell + 1]; ++i) {
-            if (D.x[i] >= (Real)0) D.counters[C_DELETED] += 1;
-            D.x[i] = (Real)-1;
+        const double ne = std::floor(g.rho * (double)D.p.ppc + u);
+        const uint32_t nnew = ne > 0.0 ? (uint32_t)ne : 0u;
+        if (nnew > (uint32_t)D.d.bin) {
+            D.status |= ST_CAPACITY;
+            continue;
         }
-    }
-    for (int c = 0; c < n; ++c) {
-        const uint32_t cell = (uint32_t)cells[c];
-        const int ix = (int)(cell % D.p.ncx), iy = (int)(cell / D.p.ncx);
-        std::vector<Real> out(5 * (size_t)nnew[c]);
+        fresh[c].resize(5 * (size_t)nnew);
         bool capped = false;
-        const uint64_t trials = grad_sample_cell<Real>(pack<Real>(gc[c]), B.d.order, D.p.seed, cell,
-                                                       t, nnew[c], (Real)ix, (Real)iy, out.data(),
-                                                       &D.counters[C_ENVELOPE], &capped);
+        const uint64_t trials = grad_sample_cell<Real>(pack<Real>(g), B.d.order, D.p.seed,
+                                                       (uint32_t)cell, t, nnew, (Real)ix, (Real)iy,
+                                                       fresh[c].data(), &D.counters[C_ENVELOPE],
+                                                       &capped);
         if (capped) D.status |= ST_SAMPLING_CAP;
         D.counters[C_L2D_ATTEMPTS] += trials;
-        for (uint32_t k = 0; k < nnew[c]; ++k) {
-            D.x.push_back(out[5 * k]);
-            D.y.push_back(out[5 * k + 1]);
-            D.vx.push_back(out[5 * k + 2]);
-            D.vy.push_back(out[5 * k + 3]);
-            D.vz.push_back(out[5 * k + 4]);
-        }
-        D.counters[C_CREATED] += nnew[c];
+        D.counters[C_CREATED] += nnew;
+        D.counters[C_DELETED] += D.cell_start[cell + 1] - D.cell_start[cell];
+        slot_of[cell] = c;
     }
+    std::vector<Real> nx, ny, nvx, nvy, nvz;
+    std::vector<uint32_t> cs(D.d.ncells + 1, 0);
+    for (int64_t cell = 0; cell < D.d.ncells; ++cell) {
+        cs[cell] = (uint32_t)nx.size();
+        if (slot_of[cell] >= 0) {
+            const std::vector<Real>& o = fresh[slot_of[cell]];
+            for (size_t k = 0; k < o.size() / 5; ++k) {
+                nx.push_back(o[5 * k]);
+                ny.push_back(o[5 * k + 1]);
+                nvx.push_back(o[5 * k + 2]);
+                nvy.push_back(o[5 * k + 3]);
+                nvz.push_back(o[5 * k + 4]);
+            }
+        } else {
+            for (uint32_t i = D.cell_start[cell]; i < D.cell_start[cell + 1]; ++i) {
+                nx.push_back(D.x[i]);
+                ny.push_back(D.y[i]);
+                nvx.push_back(D.vx[i]);
+                nvy.push_back(D.vy[i]);
+                nvz.push_back(D.vz[i]);
+            }
+        }
+    }
+    cs[D.d.ncells] = (uint32_t)nx.size();
+    D.x.swap(nx);
+    D.y.swap(ny);
+    D.vx.swap(nvx);
+    D.vy.swap(nvy);
+    D.vz.swap(nvz);
+    D.cell_start.swap(cs);
 }
 
 }  // namespace ora

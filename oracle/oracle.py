@@ -58,6 +58,8 @@ class Derived(ctypes.Structure):
         ("capacity", ctypes.c_int64),
         ("q", ctypes.c_int32),
         ("order", ctypes.c_int32),
+        ("bin", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
     ]
 
 

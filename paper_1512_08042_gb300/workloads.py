@@ -12,7 +12,7 @@ import numpy as np
 ARGON = dict(T_K=273.0, mass_kg=6.63e-26)
 
 _BASE = dict(lb_ratio=1, lattice=39, real_bytes=4, sample_every=1, kn=0.1, ma=0.1,
-             crmax_init=6.0, capacity_factor=1.5, **ARGON)
+             crmax_init=6.0, capacity_factor=2.5, **ARGON)
 
 
 def config(**kw):
@@ -28,12 +28,11 @@ WORKLOADS = {
     "poiseuille_64x1_ppc100_fp64": config(ncx=64, ncy=1, ppc=100, real_bytes=8, kn=0.1, seed=1),
     # 2D channel: 64 x 256 DSMC cells, 50 particles/cell (819,200), Kn 0.05, FP32 state,
     # 128 x 512 D3Q39 lattice (two LB nodes per cell per axis), 8-node coupling strip.
-    "poiseuille_64x256_ppc50_fp32": config(ncx=64, ncy=256, ppc=50, lb_ratio=2, kn=0.05,
-                                            capacity_factor=1.25, seed=2),
+    "poiseuille_64x256_ppc50_fp32": config(ncx=64, ncy=256, ppc=50, lb_ratio=2, kn=0.05, seed=2),
     # Large channel: 512 x 4096 DSMC cells, 50 particles/cell (104,857,600), FP32 state,
     # 1024 x 8192 D3Q39 lattice.
     "poiseuille_512x4096_ppc50_fp32": config(ncx=512, ncy=4096, ppc=50, lb_ratio=2, kn=0.05,
-                                              capacity_factor=1.25, seed=5),
+                                              seed=5),
 }
 
 
