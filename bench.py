@@ -29,36 +29,31 @@ from paper_1512_08042_gb300 import workloads as W  # noqa: E402
 METRIC = "DSMC particle-updates/s, LBM MLUPS, hybrid steps/s on 1 GB300 at stated tol"
 DEFAULT_WORKLOAD = "poiseuille_64x256_ppc50_fp32"
 FLUSH_BYTES = 512 << 20
-LAUNCHES_PER_STEP = 10  # move, tile sums, scan, rank, collide, dsmc2lb, lbm, lb2dsmc x3
+LAUNCHES_PER_STEP = 6  # move, collide, dsmc2lb, lbm, lb2dsmc coefficients and sample
 
 
 def kernel_algorithmic_bytes(name, cfg, d, n_particles, n_nodes_map, n_cells_map):
-    """Bytes a kernel must move per launch (reads + writes of its inputs and outputs)."""
+    """Bytes a kernel must move per launch: reads and writes of its inputs and outputs."""
     rb = cfg["real_bytes"]
     ncells = d["ncells"]
-    if name == "collide":
-        # perm (4) + gather 5 Real + write 5 Real per particle; per cell: cell_start (4),
-        # crmax r/w, rem r/w (16), nbar_sum r/w (16), 20 FP64 sums r/w (320)
-        return n_particles * (4 + 10 * rb) + ncells * (4 + 2 * rb + 16 + 16 + 320)
     if name == "move":
-        # 5 Real read + written in place, key and arrival written, per-cell count atomics
-        return n_particles * (10 * rb + 8) + ncells * 4
-    if name == "rank":
-        return n_particles * 16
+        # 5 Real read, 5 Real + a u32 tag written per particle; per cell: its count read and
+        # the destination counts' atomics
+        return n_particles * (10 * rb + 4) + ncells * 8
+    if name == "collide":
+        # 5 Real + tag read, 5 Real written per particle; per cell: count, crmax, rem, nbar_sum
+        # read and written, the source count cleared, 20 FP64 sums read and written
+        return n_particles * (10 * rb + 4) + ncells * (4 + 2 * rb + 2 * rb + 8 + 4 + 320)
     if name == "lbm":
         return d["nnodes"] * 2 * d["q"] * rb
-    if name in ("tile_sums", "scan"):
-        return ncells * (4 if name == "tile_sums" else 12)
     if name == "dsmc2lb":
         return n_nodes_map * (160 + d["q"] * rb)
     if name == "lb2dsmc_coef":
         # populations of the coupling cells' nodes read, one record per cell written
         return n_cells_map * (cfg["lb_ratio"] ** 2 * d["q"] * rb + 176)
-    if name == "lb2dsmc_scan":
-        return n_cells_map * 16
     if name == "lb2dsmc_sample":
-        # old particles' x read and marked, new particles written (ppc per cell on average)
-        return n_cells_map * cfg["ppc"] * (2 * rb + 5 * rb) + n_cells_map * 176
+        # one record read and ppc new particles written per coupling cell
+        return n_cells_map * (176 + cfg["ppc"] * 5 * rb)
     return 0
 
 

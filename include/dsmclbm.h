@@ -54,7 +54,7 @@ typedef enum {
 } hyb_status;
 
 /* Bits of the sticky device status word. */
-#define HYB_ST_CAPACITY (1u << 0)      /* appended particles would exceed capacity */
+#define HYB_ST_CAPACITY (1u << 0)      /* a cell's particles exceeded its bin of slots */
 #define HYB_ST_BOUNCE_CAP (1u << 1)    /* a particle hit the walls more than 8 times in a step */
 #define HYB_ST_SCATTER_CAP (1u << 2)   /* 32 Marsaglia draws rejected in a row */
 #define HYB_ST_SAMPLING_CAP (1u << 3)  /* 1000 LB2DSMC trials rejected in a row */
@@ -86,7 +86,8 @@ typedef struct {
     double kn;              /* Knudsen number on the channel height (> 0) */
     double ma;              /* Mach number of the no-slip centreline velocity, u_max / c_s */
     double crmax_init;      /* initial (sigma_T c_r)_max / sigma_T in c_th units (> 0) */
-    double capacity_factor; /* particle capacity = ceil(capacity_factor * ncx * ncy * ppc) */
+    double capacity_factor; /* slots per cell: bin = 32 * ceil(capacity_factor * ppc / 32),
+                               at most 256 */
     double T_K;             /* temperature [K], for SI conversion only */
     double mass_kg;         /* molecular mass [kg], for SI conversion only */
 } hyb_params;
@@ -102,38 +103,39 @@ typedef struct {
     double coll_dt;  /* F_N sigma_T dt / V_c of Eq. collisionnumber: dt / (sqrt(2) lambda ppc) */
     double g_step;   /* body-force velocity increment per step, 8 (tau-1/2) Ma cs^2 / H^2 */
     double c_th_ms;  /* sqrt(k T / m) [m/s] */
-    int64_t ncells, nx, ny, nnodes, capacity;
+    int64_t ncells, nx, ny, nnodes;
+    int64_t capacity; /* particle slots: ncells * bin */
     int32_t q, order;
+    int32_t bin;      /* particle slots per cell */
+    int32_t pad;
 } hyb_derived;
 
 /* Byte offsets of the arrays inside the caller's arena (hyb_layout_compute). Arrays marked
  * [2] are ping-pong pairs; hyb_current says which half holds the current state. Real is
- * float or double per real_bytes.
- *   x, y          Real[capacity]   positions in cell units (x across, y streamwise);
- *                                  x < 0 marks a deleted particle
- *   vx, vy, vz    Real[capacity]   velocities in c_th units
- *   key           u32[capacity]    cell of each slot after the move (0xFFFFFFFF deleted)
- *   arrival       u32[capacity]    arrival index of each slot in its new cell
- *   perm          u32[capacity]    old slot of each new position
- *   count         u32[ncells]      particles per cell (zero between steps)
- *   cell_start    u32[ncells + 1]  first slot of each cell in the current buffer
- *   tile_sum      u32[ntiles]      per-tile sums of `count` (scan scratch)
- *   crmax         Real[ncells]     (sigma_T c_r)_max / sigma_T per cell
- *   rem           Real[ncells]     NTC fractional candidate carried between steps
- *   nbar_sum      u32[ncells]      running sum of N per cell, for N-bar
- *   acc           f64[ncells][20]  cumulative sums N, S v (3), S vv (6: xx xy xz yy yz zz),
- *                                  S vvv (10: xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz)
- *   f             Real[q][ny][nx]  populations, x fastest; f[2]
- *   ctrl          u32[16]          [0] status bits, [1] particle slots in use, [2] DSMC
- *                                  steps taken, [3] moment samples taken, [4]..[7] scratch
- *   counters      u64[16]          event counters, HYB_C_*
- *   map_scratch                    LB2DSMC per-cell records */
+ * float or double per real_bytes. Particles are binned by cell: cell c owns slots
+ * [c * bin, (c + 1) * bin) of every particle array and count[half][c] of them are in use,
+ * in the order of the step's stable sort (after dsmc_step) or of their generation (after
+ * dsmc_init and map_lbm_to_dsmc).
+ *   x, y          Real[ncells*bin]  positions in cell units (x across, y streamwise); [2]
+ *   vx, vy, vz    Real[ncells*bin]  velocities in c_th units; [2]
+ *   tag           u32[ncells*bin]   origin slot of each moved particle (stable-order key)
+ *   count         u32[ncells]       particles per cell; [2]
+ *   crmax         Real[ncells]      (sigma_T c_r)_max / sigma_T per cell
+ *   rem           Real[ncells]      NTC fractional candidate carried between steps
+ *   nbar_sum      u32[ncells]       running sum of N per cell, for N-bar
+ *   acc           f64[ncells][20]   cumulative sums N, S v (3), S vv (6: xx xy xz yy yz zz),
+ *                                   S vvv (10: xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz)
+ *   f             Real[q][ny][nx]   populations, x fastest; [2]
+ *   ctrl          u32[16]           [0] status bits, [1] particles in use, [2] DSMC steps
+ *                                   taken, [3] moment samples taken, [4]..[15] scratch
+ *   counters      u64[16]           event counters, HYB_C_*
+ *   map_scratch                     LB2DSMC per-cell records */
 typedef struct {
     uint64_t total_bytes;
-    int64_t capacity, ncells, nnodes, ntiles;
-    int32_t q, real_bytes;
+    int64_t capacity, ncells, nnodes;
+    int32_t q, real_bytes, bin, pad;
     uint64_t x[2], y[2], vx[2], vy[2], vz[2];
-    uint64_t key, arrival, perm, count, cell_start, tile_sum;
+    uint64_t tag, count[2];
     uint64_t crmax, rem, nbar_sum, acc;
     uint64_t f[2];
     uint64_t ctrl, counters, map_scratch;
@@ -158,8 +160,11 @@ const char* hyb_status_string(hyb_status s);
 hyb_status dsmc_init(const hyb_params* p, void* arena, uint64_t arena_bytes, void* stream,
                      hyb_ctx** out);
 
-/* `nsteps` DSMC steps (Sec. 5; the NTC order move -> index -> collide -> sample).
- * Draws are keyed by (seed; slot or cell, step, purpose, index). */
+/* `nsteps` DSMC steps (Sec. 5; the NTC order move -> index -> collide -> sample): each
+ * particle is moved and binned into its new cell of the other half, then every cell puts
+ * its particles in stable order (by origin cell and rank), collides them and adds their
+ * moment sums. Draws are keyed by (seed; cell, step, purpose, index), so results do not
+ * depend on the launch shape. */
 hyb_status dsmc_step(hyb_ctx* ctx, int32_t nsteps);
 
 /* `nsteps` LB stream-collide steps (Sec. 2, Sec. 3.1). */
@@ -176,11 +181,11 @@ hyb_status sample_moments(hyb_ctx* ctx, double* out, int32_t reset);
 hyb_status map_dsmc_to_lbm(hyb_ctx* ctx, const int32_t* dev_nodes, int32_t n);
 
 /* LB2DSMC (Sec. 2.2, Table 1): for each DSMC cell in dev_cells[n] (device int32,
- * cell = iy * ncx + ix, distinct), delete its particles and append floor(rho ppc + U) new
- * ones, with rho the mean LB density of the cell's lb_ratio^2 nodes; velocities drawn from
- * the Grad distribution of the cell's populations by acceptance-rejection with envelope
- * C = 1 + 30 M; positions uniform in the cell. Call at most once between two dsmc_step
- * calls (deletion uses the cell layout of the last step). */
+ * cell = iy * ncx + ix, distinct), replace its particles by floor(rho ppc + U) new ones,
+ * with rho the mean LB density of the cell's lb_ratio^2 nodes; velocities drawn from the
+ * Grad distribution of the cell's populations by acceptance-rejection with envelope
+ * C = 1 + 30 M; positions uniform in the cell. A cell whose new count exceeds its bin keeps
+ * its particles and raises HYB_ST_CAPACITY. */
 hyb_status map_lbm_to_dsmc(hyb_ctx* ctx, const int32_t* dev_cells, int32_t n);
 
 /* One or more hybrid steps: dsmc_step(1), map_dsmc_to_lbm, lbm_step(1), map_lbm_to_dsmc.
@@ -202,8 +207,7 @@ hyb_status hyb_sync_status(hyb_ctx* ctx, uint32_t* bits);
 hyb_status hyb_read_counters(hyb_ctx* ctx, uint64_t* out);
 
 /* Kernel timing on the context's stream: after hyb_profile(ctx, k) every launch of kernel k
- * (0 move, 1 tile sums, 2 scan, 3 rank, 4 collide, 5 lbm, 6 dsmc2lb, 7 lb2dsmc coefficients,
- * 8 lb2dsmc sample, 9 lb2dsmc scan; -1 off) is bracketed by CUDA events. hyb_profile_harvest synchronises
+ * (0 move, 1 collide, 2 lbm, 3 dsmc2lb, 4 lb2dsmc coefficients, 5 lb2dsmc sample; -1 off) is bracketed by CUDA events. hyb_profile_harvest synchronises
  * and adds the elapsed times of the launches since the last harvest; call it after every
  * hybrid step when graphs are used. hyb_profile_read returns the totals. */
 hyb_status hyb_profile(hyb_ctx* ctx, int32_t kernel);

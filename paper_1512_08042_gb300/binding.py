@@ -18,8 +18,8 @@ ST_CAPACITY, ST_BOUNCE_CAP, ST_SCATTER_CAP, ST_SAMPLING_CAP, ST_CELL_OVERFLOW, S
     1, 2, 4, 8, 16, 32)
 COUNTER_NAMES = ["wall_hits", "candidates", "collisions", "created", "deleted",
                  "l2d_attempts", "envelope", "bounce_cap"]
-KERNELS = {"move": 0, "tile_sums": 1, "scan": 2, "rank": 3, "collide": 4, "lbm": 5,
-           "dsmc2lb": 6, "lb2dsmc_coef": 7, "lb2dsmc_sample": 8, "lb2dsmc_scan": 9}
+KERNELS = {"move": 0, "collide": 1, "lbm": 2, "dsmc2lb": 3, "lb2dsmc_coef": 4,
+           "lb2dsmc_sample": 5}
 CTRL_STATUS, CTRL_NTOT, CTRL_STEP, CTRL_NSAMPLES = 0, 1, 2, 3
 
 _u32, _i32, _i64, _u64, _dbl, _vp = (ctypes.c_uint32, ctypes.c_int32, ctypes.c_int64,
@@ -37,15 +37,14 @@ class HybDerived(ctypes.Structure):
     _fields_ = [("r_lat", _dbl), ("cs_lat", _dbl), ("H_lat", _dbl), ("tau", _dbl), ("dt", _dbl),
                 ("lam", _dbl), ("coll_dt", _dbl), ("g_step", _dbl), ("c_th_ms", _dbl),
                 ("ncells", _i64), ("nx", _i64), ("ny", _i64), ("nnodes", _i64),
-                ("capacity", _i64), ("q", _i32), ("order", _i32)]
+                ("capacity", _i64), ("q", _i32), ("order", _i32), ("bin", _i32), ("pad", _i32)]
 
 
 class HybLayout(ctypes.Structure):
     _fields_ = [("total_bytes", _u64), ("capacity", _i64), ("ncells", _i64), ("nnodes", _i64),
-                ("ntiles", _i64), ("q", _i32), ("real_bytes", _i32),
+                ("q", _i32), ("real_bytes", _i32), ("bin", _i32), ("pad", _i32),
                 ("x", _u64 * 2), ("y", _u64 * 2), ("vx", _u64 * 2), ("vy", _u64 * 2),
-                ("vz", _u64 * 2), ("key", _u64), ("arrival", _u64), ("perm", _u64),
-                ("count", _u64), ("cell_start", _u64), ("tile_sum", _u64), ("crmax", _u64),
+                ("vz", _u64 * 2), ("tag", _u64), ("count", _u64 * 2), ("crmax", _u64),
                 ("rem", _u64), ("nbar_sum", _u64), ("acc", _u64), ("f", _u64 * 2),
                 ("ctrl", _u64), ("counters", _u64), ("map_scratch", _u64)]
 
@@ -271,21 +270,34 @@ class Hybrid:
 
     def n_tot(self):
         self.sync()
-        return int(self.ctrl()[CTRL_NTOT].item())
+        return int(self.counts().sum().item())
+
+    def counts(self, half=None):
+        """Particles per cell of the current (or given) half, int64."""
+        h = self.current()[0] if half is None else half
+        return self._view(self.L.count[h], self.L.ncells, self.torch.int32).long()
 
     def particle_arrays(self, half=None):
+        """Binned particle arrays [ncells, bin] of the current (or given) half (views)."""
         h = self.current()[0] if half is None else half
-        cap = self.L.capacity
-        return {k: self._view(getattr(self.L, k)[h], cap, self.real)
+        cap, b = self.L.capacity, self.L.bin
+        return {k: self._view(getattr(self.L, k)[h], cap, self.real).view(-1, b)
                 for k in ("x", "y", "vx", "vy", "vz")}
 
     def particles(self):
-        """Current particle arrays sliced to the slots in use (views)."""
-        n = self.n_tot()
-        return {k: v[:n] for k, v in self.particle_arrays().items()}
+        """Current particles in cell order (copies, compacted from the bins)."""
+        self.sync()
+        torch = self.torch
+        cnt = self.counts()
+        mask = torch.arange(self.L.bin, device=self.device)[None, :] < cnt[:, None]
+        return {k: v[mask] for k, v in self.particle_arrays().items()}
 
     def cell_start(self):
-        return self._view(self.L.cell_start, self.L.ncells + 1, self.torch.int32)
+        """First compacted index of each cell (ncells + 1), int32."""
+        torch = self.torch
+        cs = torch.zeros(self.L.ncells + 1, dtype=torch.int64, device=self.device)
+        cs[1:] = torch.cumsum(self.counts(), 0)
+        return cs.int()
 
     def acc(self):
         return self._view(self.L.acc, self.L.ncells * 20, self.torch.float64).view(-1, 20)
@@ -306,16 +318,25 @@ class Hybrid:
 
     # -- state transfer (checkpoint / restore, synthetic states) ------------------------
     def load_particles(self, x, y, vx, vy, vz, cell_start):
-        """Write a cell-ordered particle set into the current half (host or device arrays)."""
+        """Write a cell-ordered particle set into the bins of the current half (host arrays)."""
         torch = self.torch
-        n = len(x)
-        if n > self.L.capacity:
-            raise ValueError("more particles than capacity")
+        cs = np.asarray(cell_start, np.int64)
+        counts = np.diff(cs)
+        if counts.size != self.L.ncells:
+            raise ValueError("cell_start must have ncells + 1 entries")
+        if counts.max(initial=0) > self.L.bin:
+            raise ValueError("a cell holds more particles than its bin (%d)" % self.L.bin)
+        cell = np.repeat(np.arange(self.L.ncells), counts)
+        slot = torch.as_tensor(cell * self.L.bin + (np.arange(cs[-1]) - cs[cell]),
+                               device=self.device)
         arr = self.particle_arrays()
         for k, v in (("x", x), ("y", y), ("vx", vx), ("vy", vy), ("vz", vz)):
-            arr[k][:n].copy_(torch.as_tensor(np.asarray(v), dtype=self.real))
-        self.cell_start().copy_(torch.as_tensor(np.asarray(cell_start, np.int64).astype(np.int32)))
-        self.ctrl()[CTRL_NTOT] = n
+            arr[k].view(-1)[slot] = torch.as_tensor(np.asarray(v), dtype=self.real,
+                                                    device=self.device)
+        h = self.current()[0]
+        self._view(self.L.count[h], self.L.ncells, torch.int32).copy_(
+            torch.as_tensor(counts.astype(np.int32)))
+        self.ctrl()[CTRL_NTOT] = int(cs[-1])
         torch.cuda.synchronize(self.device)
 
     def set_counters(self, step=None, nsamples=None):

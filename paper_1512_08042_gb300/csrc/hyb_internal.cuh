@@ -17,7 +17,6 @@ constexpr int kMoments = 20;
 constexpr int kMaxBounces = 8;
 constexpr int kMaxScatterBlocks = 16;
 constexpr int kMaxL2DAttempts = 1000;
-constexpr int kScanTile = 4096;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 enum CtrlWord {
@@ -25,9 +24,8 @@ enum CtrlWord {
     CTRL_NTOT = 1,
     CTRL_STEP = 2,
     CTRL_NSAMPLES = 3,
-    CTRL_L2D_BASE = 4,
-    CTRL_L2D_SKIP = 5,
-    CTRL_L2D_TOTAL = 6,
+    CTRL_TICKET = 4,   // blocks finished, for the last-block update of the move kernel
+    CTRL_L2D_BAD = 5,  // an invalid cell index in the current LB2DSMC call
     CTRL_WORDS = 16,
 };
 
@@ -44,16 +42,12 @@ enum Tag : uint32_t {
 
 enum KernelId {
     K_MOVE = 0,
-    K_TILE_SUMS = 1,
-    K_SCAN = 2,
-    K_RANK = 3,
-    K_COLLIDE = 4,
-    K_LBM = 5,
-    K_D2L = 6,
-    K_L2D_PREP = 7,
-    K_L2D_SAMPLE = 8,
-    K_L2D_SCAN = 9,
-    K_COUNT = 10,
+    K_COLLIDE = 1,
+    K_LBM = 2,
+    K_D2L = 3,
+    K_L2D_COEF = 4,
+    K_L2D_SAMPLE = 5,
+    K_COUNT = 6,
 };
 
 // LB2DSMC per-cell record (map_scratch).
@@ -64,22 +58,18 @@ struct GradRec {
     double a3[10];  // packed xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz
     double C;
     uint32_t nnew;
-    uint32_t offset;
+    uint32_t pad;
 };
 
-// Pointers into the arena, resolved for the current ping-pong halves.
+// Pointers into the arena.
 struct State {
     void* px[2];
     void* py[2];
     void* pvx[2];
     void* pvy[2];
     void* pvz[2];
-    uint32_t* key;
-    uint32_t* arrival;
-    uint32_t* perm;
-    uint32_t* count;
-    uint32_t* cell_start;
-    uint32_t* tile_sum;
+    uint32_t* tag;
+    uint32_t* count[2];
     void* crmax;
     void* rem;
     uint32_t* nbar_sum;
@@ -90,8 +80,9 @@ struct State {
     GradRec* grad;
 };
 
-// Everything a kernel needs, passed by value. Particle/population pointers are typed at
-// launch.
+// Everything a DSMC kernel needs, passed by value: the source half (s*, count_s) is read by
+// the move, which bins particles into the destination half (d*, count_d); the collide works
+// in place on the destination half.
 template <typename Real>
 struct DsmcArgs {
     const Real* sx;
@@ -99,30 +90,21 @@ struct DsmcArgs {
     const Real* svx;
     const Real* svy;
     const Real* svz;
-    Real* mx;  // in-place move writes into the source half
-    Real* my;
-    Real* mvx;
-    Real* mvy;
-    Real* mvz;
     Real* dx;
     Real* dy;
     Real* dvx;
     Real* dvy;
     Real* dvz;
-    uint32_t* key;
-    uint32_t* arrival;
-    uint32_t* perm;
-    uint32_t* count;
-    uint32_t* cell_start;
-    uint32_t* tile_sum;
+    uint32_t* tag;
+    uint32_t* count_s;
+    uint32_t* count_d;
     Real* crmax;
     Real* rem;
     uint32_t* nbar_sum;
     double* acc;
     uint32_t* ctrl;
     unsigned long long* counters;
-    int32_t ncx, ncy, ncells, ntiles, sample_every, ppc;
-    int64_t capacity;
+    int32_t ncx, ncy, ncells, bin, sample_every, ppc;
     double dt, g_step, coll_dt, crmax_init;
     uint64_t seed;
 };
@@ -133,14 +115,14 @@ struct LbmArgs {
     Real* dst;
     int32_t nx, ny;
     int64_t nnodes;
-    double tau, g_step;
+    Real om, of, g_step;  // 1 - 1/tau, 1 - 1/(2 tau), force increment per step
 };
 
 template <typename Real>
 struct MapArgs {
     Real* f;  // current populations
-    int32_t nx, ny, ncx, ncy, lb_ratio, ppc, n;
-    int64_t nnodes, capacity;
+    int32_t nx, ny, ncx, ncy, lb_ratio, ppc, n, bin;
+    int64_t nnodes;
     const int32_t* list;
     double r_lat;
     uint64_t seed;
@@ -148,7 +130,7 @@ struct MapArgs {
     uint32_t* ctrl;
     unsigned long long* counters;
     GradRec* grad;
-    const uint32_t* cell_start;
+    uint32_t* count;  // current half
     Real* x;
     Real* y;
     Real* vx;

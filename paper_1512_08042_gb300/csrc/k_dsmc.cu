@@ -1,17 +1,20 @@
-// DSMC kernels: initialisation, move with diffuse isothermal walls, stable counting sort by
-// cell, no-time-counter hard-sphere collisions and per-cell Hermite-moment sampling.
+// DSMC kernels: initialisation, move with diffuse isothermal walls and binning by cell,
+// and the per-cell stable ordering, no-time-counter hard-sphere collisions and
+// Hermite-moment sampling.
 //
-// One DSMC step (Sec. 5, the NTC scheme of Bird that the paper uses) is five launches:
-//   k_move        per particle: body-force kick, free flight, diffuse wall re-emission
-//                 (Sec. 3.1), periodic wrap; new cell key; warp-aggregated arrival count.
-//   k_tile_sums   per 4096-cell tile: sum of the per-cell counts.
-//   k_scan        per tile: exclusive scan -> cell_start; counts cleared for the next step.
-//   k_rank        per particle: perm[cell_start[key] + arrival] = slot.
-//   k_collide     one warp per cell: the cell's slots are put back in ascending old-slot
-//                 order (so the sort is stable whatever order the atomics gave), gathered
-//                 into the other half of the ping-pong buffer, collided by NTC
-//                 (Eq. collisionnumber) in shared memory, written out, and their moment
-//                 sums 1, v, vv, vvv added to the FP64 cumulative sums (Sec. 2.1, Fig. 1).
+// Particles live in per-cell bins of `bin` slots (cell c owns slots [c bin, (c+1) bin) of
+// each state array, count[c] in use) and ping-pong between two halves. One DSMC step (the
+// NTC order of Bird that the paper uses in Sec. 5: move, index, collide, sample) is two
+// launches:
+//   k_move     one warp per source cell: body-force kick, free flight, diffuse wall
+//              re-emission (Sec. 3.1), periodic wrap, new cell; the particle is appended to
+//              its new cell's bin in the other half by a warp-aggregated atomic, with its
+//              origin slot as a tag. The last block to finish advances the step counters.
+//   k_collide  one warp per cell of the new half: the bin is put in stable order (ascending
+//              origin slot = origin cell, then rank in it: a bitonic sort in registers),
+//              NTC collisions (Eq. collisionnumber) run in shared memory, the particles are
+//              written back in order, and their sums 1, v, vv, vvv are added to the FP64
+//              cumulative sums of the cell (Sec. 2.1, Fig. 1).
 // This file is compiled without FMA contraction so that positions, cell keys, pair choices
 // and post-collision velocities are the IEEE float (or double) results of the written
 // expressions.
@@ -22,9 +25,9 @@ namespace hyb {
 namespace {
 
 template <typename Real>
-__device__ __forceinline__ void reemit(uint64_t seed, uint32_t slot, uint32_t s, int bounce, Real sign,
-                                       Real& ux, Real& uy, Real& uz) {
-    const uint4 r = draw(seed, slot, s, TAG_WALL, (uint32_t)bounce, 0);
+__device__ __forceinline__ void reemit(uint64_t seed, uint32_t cell, uint32_t rank, uint32_t s,
+                                       int bounce, Real sign, Real& ux, Real& uy, Real& uz) {
+    const uint4 r = draw(seed, cell, s, TAG_WALL, (rank << 3) | (uint32_t)bounce, 0);
     const Real vn = wall_speed<Real>(r.x);
     Real t1, t2;
     gauss_pair<Real>(r.y, r.z, t1, t2);
@@ -58,18 +61,6 @@ __device__ __forceinline__ int unit_vector(uint64_t seed, uint32_t c, uint32_t s
     return 0;
 }
 
-__device__ __forceinline__ uint32_t block_sum_u32(uint32_t v, uint32_t* sh) {
-    v = __reduce_add_sync(kFull, v);
-    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    __syncthreads();
-    if (lane_id() == 0) sh[w] = v;
-    __syncthreads();
-    uint32_t t = 0;
-    for (int i = 0; i < nw; ++i) t += sh[i];
-    __syncthreads();
-    return t;
-}
-
 // ---------------------------------------------------------------------------------------
 template <typename Real>
 __global__ void k_init_particles(DsmcArgs<Real> a) {
@@ -78,31 +69,30 @@ __global__ void k_init_particles(DsmcArgs<Real> a) {
          s += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t c = (uint32_t)(s / a.ppc), k = (uint32_t)(s % a.ppc);
         const int ix = (int)(c % (uint32_t)a.ncx), iy = (int)(c / (uint32_t)a.ncx);
+        const int64_t slot = (int64_t)c * a.bin + k;
         const uint4 rp = draw(a.seed, c, 0, TAG_INIT_POS, k, 0);
-        a.dx[s] = (Real)ix + (Real)u01f(rp.x);
-        a.dy[s] = (Real)iy + (Real)u01f(rp.y);
+        a.dx[slot] = (Real)ix + (Real)u01f(rp.x);
+        a.dy[slot] = (Real)iy + (Real)u01f(rp.y);
         const uint4 rv = draw(a.seed, c, 0, TAG_INIT_VEL, k, 0);
         Real n0, n1, n2, n3;
         gauss_pair<Real>(rv.x, rv.y, n0, n1);
         gauss_pair<Real>(rv.z, rv.w, n2, n3);
-        a.dvx[s] = n0;
-        a.dvy[s] = n1;
-        a.dvz[s] = n2;
+        a.dvx[slot] = n0;
+        a.dvy[slot] = n1;
+        a.dvz[slot] = n2;
     }
 }
 
 template <typename Real>
 __global__ void k_init_cells(DsmcArgs<Real> a) {
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c <= a.ncells;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < a.ncells;
          c += (int64_t)gridDim.x * blockDim.x) {
-        a.cell_start[c] = (uint32_t)(c * a.ppc);
-        if (c < a.ncells) {
-            a.count[c] = 0;
-            a.crmax[c] = (Real)a.crmax_init;
-            a.rem[c] = (Real)0;
-            a.nbar_sum[c] = 0u;
-            for (int m = 0; m < kMoments; ++m) a.acc[c * kMoments + m] = 0.0;
-        }
+        a.count_d[c] = (uint32_t)a.ppc;
+        a.count_s[c] = 0;
+        a.crmax[c] = (Real)a.crmax_init;
+        a.rem[c] = (Real)0;
+        a.nbar_sum[c] = 0u;
+        for (int m = 0; m < kMoments; ++m) a.acc[c * kMoments + m] = 0.0;
         if (c == 0) {
             for (int w = 0; w < CTRL_WORDS; ++w) a.ctrl[w] = 0;
             a.ctrl[CTRL_NTOT] = (uint32_t)((int64_t)a.ncells * a.ppc);
@@ -112,24 +102,35 @@ __global__ void k_init_cells(DsmcArgs<Real> a) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Move (kick, drift, walls, wrap), cell key, arrival index.
+// Move (kick, drift, walls, wrap) and binning into the other half.
 template <typename Real>
 __global__ void __launch_bounds__(256) k_move(DsmcArgs<Real> a) {
-    const uint32_t n = a.ctrl[CTRL_NTOT];
+    __shared__ bool s_last;
     const uint32_t s = a.ctrl[CTRL_STEP];
     const Real H = (Real)a.ncx, L = (Real)a.ncy;
     const Real g = (Real)a.g_step, dt = (Real)a.dt;
     const unsigned lane = lane_id();
     const unsigned lt = (1u << lane) - 1u;
-    uint32_t hits = 0, caps = 0;
-    for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
-        const uint32_t i = base + threadIdx.x;
-        uint32_t k = kDeadKey;
-        if (i < n) {
-            Real px = a.mx[i];
-            if (px >= (Real)0) {
-                Real py = a.my[i];
-                Real ux = a.mvx[i], uy = a.mvy[i] + g, uz = a.mvz[i];
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t bin = (uint32_t)a.bin;
+    uint32_t hits = 0, caps = 0, lost = 0;
+    for (int c = gw; c < a.ncells; c += nw) {
+        uint32_t n = a.count_s[c];
+        if (n > bin) n = bin;
+        const int64_t base = (int64_t)c * bin;
+        for (uint32_t k0 = 0; k0 < n; k0 += 32) {
+            const uint32_t k = k0 + lane;
+            const bool active = k < n;
+            uint32_t key = 0;
+            Real px = 0, py = 0, ux = 0, uy = 0, uz = 0;
+            if (active) {
+                const int64_t i = base + k;
+                px = a.sx[i];
+                py = a.sy[i];
+                ux = a.svx[i];
+                uy = a.svy[i] + g;
+                uz = a.svz[i];
                 Real t = dt;
                 for (int b = 0;; ++b) {
                     const Real xn = px + ux * t;
@@ -152,126 +153,75 @@ __global__ void __launch_bounds__(256) k_move(DsmcArgs<Real> a) {
                     px = left ? (Real)0 : H;
                     t = t - th;
                     if (t < (Real)0) t = (Real)0;
-                    reemit(a.seed, i, s, b, left ? (Real)1 : (Real)-1, ux, uy, uz);
+                    reemit(a.seed, (uint32_t)c, k, s, b, left ? (Real)1 : (Real)-1, ux, uy, uz);
                 }
                 if (py < (Real)0 || py >= L) {
                     py = py - L * floor(py / L);
                     if (py < (Real)0) py = py + L;
                     if (py >= L) py = py - L;
                 }
-                a.mx[i] = px;
-                a.my[i] = py;
-                a.mvx[i] = ux;
-                a.mvy[i] = uy;
-                a.mvz[i] = uz;
                 int ix = (int)floor(px), iy = (int)floor(py);
                 ix = ix < 0 ? 0 : (ix > a.ncx - 1 ? a.ncx - 1 : ix);
                 iy = iy < 0 ? 0 : (iy > a.ncy - 1 ? a.ncy - 1 : iy);
-                k = (uint32_t)(iy * a.ncx + ix);
+                key = (uint32_t)(iy * a.ncx + ix);
             }
-            a.key[i] = k;
-        }
-        const bool live = k != kDeadKey;
-        const unsigned m = __ballot_sync(kFull, live);
-        if (live) {
-            // lanes with the same cell share one atomic; arrival = base + rank among them
-            const unsigned peers = __match_any_sync(m, k);
-            const int leader = __ffs(peers) - 1;
-            uint32_t b0 = 0;
-            if ((int)lane == leader) b0 = atomicAdd(&a.count[k], (uint32_t)__popc(peers));
-            b0 = __shfl_sync(peers, b0, leader);
-            a.arrival[i] = b0 + (uint32_t)__popc(peers & lt);
+            const unsigned m = __ballot_sync(kFull, active);
+            if (active) {
+                // lanes bound for the same cell share one atomic; arrival = base + rank
+                const unsigned peers = __match_any_sync(m, key);
+                const int leader = __ffs(peers) - 1;
+                uint32_t b0 = 0;
+                if ((int)lane == leader) b0 = atomicAdd(&a.count_d[key], (uint32_t)__popc(peers));
+                b0 = __shfl_sync(peers, b0, leader);
+                const uint32_t arr = b0 + (uint32_t)__popc(peers & lt);
+                if (arr < bin) {
+                    const int64_t j = (int64_t)key * bin + arr;
+                    a.dx[j] = px;
+                    a.dy[j] = py;
+                    a.dvx[j] = ux;
+                    a.dvy[j] = uy;
+                    a.dvz[j] = uz;
+                    a.tag[j] = (uint32_t)(base + k);
+                } else {
+                    lost += 1;
+                }
+            }
         }
     }
     hits = __reduce_add_sync(kFull, hits);
     caps = __reduce_add_sync(kFull, caps);
+    lost = __reduce_add_sync(kFull, lost);
     if (lane == 0) {
         if (hits) atomicAdd(&a.counters[HYB_C_WALL_HITS], (unsigned long long)hits);
         if (caps) {
             atomicAdd(&a.counters[HYB_C_BOUNCE_CAP], (unsigned long long)caps);
             atomicOr(&a.ctrl[CTRL_STATUS], HYB_ST_BOUNCE_CAP);
         }
+        if (lost) atomicOr(&a.ctrl[CTRL_STATUS], HYB_ST_CAPACITY);
     }
-}
-
-__global__ void __launch_bounds__(256) k_tile_sums(const uint32_t* count, uint32_t* tile_sum,
-                                                   int ncells) {
-    __shared__ uint32_t sh[8];
-    const int c0 = blockIdx.x * kScanTile;
-    const int c1 = min(c0 + kScanTile, ncells);
-    uint32_t s = 0;
-    for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) s += count[c];
-    s = block_sum_u32(s, sh);
-    if (threadIdx.x == 0) tile_sum[blockIdx.x] = s;
-}
-
-// Exclusive scan of one tile of counts, offset by the sum of the lower tiles.
-template <typename Real>
-__global__ void __launch_bounds__(256) k_scan(DsmcArgs<Real> a) {
-    constexpr int PER = kScanTile / 256;
-    __shared__ uint32_t sh[8];
-    __shared__ uint32_t warp_tot[8];
-    const int t = blockIdx.x;
-    uint32_t pre = 0;
-    for (int u = threadIdx.x; u < t; u += blockDim.x) pre += a.tile_sum[u];
-    pre = block_sum_u32(pre, sh);
-    const int c0 = t * kScanTile + threadIdx.x * PER;
-    uint32_t v[PER];
-    uint32_t loc = 0;
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        const int c = c0 + k;
-        v[k] = c < a.ncells ? a.count[c] : 0u;
-        loc += v[k];
-    }
-    // block exclusive scan of loc
-    const unsigned lane = lane_id();
-    const int w = threadIdx.x >> 5;
-    uint32_t incl = loc;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t y = __shfl_up_sync(kFull, incl, off);
-        if ((int)lane >= off) incl += y;
-    }
-    if (lane == 31) warp_tot[w] = incl;
+    // the last block to finish advances the step and sample counters
     __syncthreads();
-    uint32_t wpre = 0;
-    for (int i = 0; i < w; ++i) wpre += warp_tot[i];
-    uint32_t run = pre + wpre + incl - loc;
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        const int c = c0 + k;
-        if (c < a.ncells) {
-            a.cell_start[c] = run;
-            a.count[c] = 0;
-        }
-        run += v[k];
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned ticket = atomicAdd(&a.ctrl[CTRL_TICKET], 1u);
+        s_last = ticket == gridDim.x - 1;
     }
-    if (t == a.ntiles - 1 && threadIdx.x == blockDim.x - 1) a.cell_start[a.ncells] = run;
-    if (t == 0 && threadIdx.x == 0) {
-        const uint32_t s = a.ctrl[CTRL_STEP];
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
         if (s % (uint32_t)a.sample_every == 0) a.ctrl[CTRL_NSAMPLES] += 1;
         a.ctrl[CTRL_STEP] = s + 1;
-    }
-}
-
-template <typename Real>
-__global__ void __launch_bounds__(256) k_rank(DsmcArgs<Real> a) {
-    const uint32_t n = a.ctrl[CTRL_NTOT];
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint32_t k = a.key[i];
-        if (k != kDeadKey) a.perm[a.cell_start[k] + a.arrival[i]] = i;
+        a.ctrl[CTRL_NTOT] = 0;
+        a.ctrl[CTRL_TICKET] = 0;
     }
 }
 
 // ---------------------------------------------------------------------------------------
-// One warp per cell: stable order, gather, NTC collisions, write-out, moment sums.
-constexpr int kCollideWarps = 4;
-
-// Ascending bitonic sort of 32 R keys held R per lane (key r of a lane at position
-// lane + 32 r). All loops have constant trip counts and unroll, so the keys stay in registers.
+// Ascending bitonic sort of 32 R (key, value) pairs held R per lane (pair r of a lane at
+// position lane + 32 r). All loops have constant trip counts and unroll, so the pairs stay in
+// registers.
 template <int R>
-__device__ __forceinline__ void bitonic_sort(uint32_t (&v)[R]) {
+__device__ __forceinline__ void bitonic_sort(uint32_t (&key)[R], uint32_t (&val)[R]) {
     constexpr int N = 32 * R;
     const int lane = (int)lane_id();
 #pragma unroll
@@ -285,111 +235,151 @@ __device__ __forceinline__ void bitonic_sort(uint32_t (&v)[R]) {
                     const int o = r ^ jr;
                     if (r < o) {
                         const bool asc = ((lane + 32 * r) & k) == 0;
-                        const uint32_t lo = min(v[r], v[o]), hi = max(v[r], v[o]);
-                        v[r] = asc ? lo : hi;
-                        v[o] = asc ? hi : lo;
+                        const bool swap = asc ? (key[r] > key[o]) : (key[r] < key[o]);
+                        if (swap) {
+                            const uint32_t tk = key[r], tv = val[r];
+                            key[r] = key[o];
+                            val[r] = val[o];
+                            key[o] = tk;
+                            val[o] = tv;
+                        }
                     }
                 }
             } else {
                 const bool lower = (lane & j) == 0;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const uint32_t o = __shfl_xor_sync(kFull, v[r], j);
+                    const uint32_t ok = __shfl_xor_sync(kFull, key[r], j);
+                    const uint32_t ov = __shfl_xor_sync(kFull, val[r], j);
                     const bool asc = ((lane + 32 * r) & k) == 0;
-                    v[r] = (lower == asc) ? min(v[r], o) : max(v[r], o);
+                    const bool take_min = lower == asc;
+                    const bool take_other = take_min ? (ok < key[r]) : (ok > key[r]);
+                    if (take_other) {
+                        key[r] = ok;
+                        val[r] = ov;
+                    }
                 }
             }
         }
     }
 }
 
-// Sort the cell's n <= 32 R slots from perm and gather them into the destination half.
+// Stable order of a bin: the cell's n <= 32 R particles are loaded, sorted by their tag
+// (origin slot), left in shared memory in that order (velocities) and written back to the
+// bin in that order (positions).
 template <typename Real, int R>
-__device__ __forceinline__ void sort_gather(const DsmcArgs<Real>& a, uint32_t start, uint32_t n,
-                                            Real* vx, Real* vy, Real* vz) {
+__device__ __forceinline__ void order_bin(const DsmcArgs<Real>& a, int64_t base, uint32_t n,
+                                          Real* sx, Real* sy, Real* vx, Real* vy, Real* vz) {
     const unsigned lane = lane_id();
-    uint32_t v[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const uint32_t k = lane + 32u * r;
-        v[r] = k < n ? a.perm[start + k] : 0xFFFFFFFFu;
-    }
-    bitonic_sort<R>(v);
+    uint32_t key[R], val[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const uint32_t k = lane + 32u * r;
         if (k < n) {
-            const uint32_t src = v[r];
-            a.dx[start + k] = a.sx[src];
-            a.dy[start + k] = a.sy[src];
-            vx[k] = a.svx[src];
-            vy[k] = a.svy[src];
-            vz[k] = a.svz[src];
+            key[r] = a.tag[base + k];
+            sx[k] = a.dx[base + k];
+            sy[k] = a.dy[base + k];
+            vx[k] = a.dvx[base + k];
+            vy[k] = a.dvy[base + k];
+            vz[k] = a.dvz[base + k];
+        } else {
+            key[r] = 0xFFFFFFFFu;
+        }
+        val[r] = k;
+    }
+    bitonic_sort<R>(key, val);
+    __syncwarp();
+    Real ox[R], oy[R], ovx[R], ovy[R], ovz[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const uint32_t k = lane + 32u * r;
+        if (k < n) {
+            const uint32_t src = val[r];
+            ox[r] = sx[src];
+            oy[r] = sy[src];
+            ovx[r] = vx[src];
+            ovy[r] = vy[src];
+            ovz[r] = vz[src];
         }
     }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const uint32_t k = lane + 32u * r;
+        if (k < n) {
+            a.dx[base + k] = ox[r];
+            a.dy[base + k] = oy[r];
+            vx[k] = ovx[r];
+            vy[k] = ovy[r];
+            vz[k] = ovz[r];
+        }
+    }
+    __syncwarp();
 }
 
-template <typename Real, int MAXP>
+// Reduce 32 per-lane values v[0..31] over the warp so that lane L ends with the total of
+// v[L] (halving exchange: 16 + 8 + 4 + 2 + 1 shuffles).
+template <typename Real>
+__device__ __forceinline__ Real warp_transpose_sum(Real (&v)[32]) {
+    const unsigned lane = lane_id();
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const bool hi = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const Real send = hi ? v[i] : v[i + o];
+            const Real keep = hi ? v[i + o] : v[i];
+            v[i] = keep + __shfl_xor_sync(kFull, send, o);
+        }
+    }
+    return v[0];
+}
+
+constexpr int kCollideWarps = 4;
+
+// MAXR = bin / 32 rounded up to a power of two: the largest register sort instantiated.
+template <typename Real, int MAXR>
 __global__ void __launch_bounds__(kCollideWarps * 32) k_collide(DsmcArgs<Real> a) {
-    __shared__ uint32_t s_in[kCollideWarps][MAXP];
-    __shared__ Real s_v[kCollideWarps][3][MAXP];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int w = threadIdx.x >> 5;
     const unsigned lane = lane_id();
+    const uint32_t bin = (uint32_t)a.bin;
+    Real* sm = reinterpret_cast<Real*>(smem_raw) + (size_t)w * 5 * bin;
+    Real* sx = sm;
+    Real* sy = sm + bin;
+    Real* vx = sm + 2 * bin;
+    Real* vy = sm + 3 * bin;
+    Real* vz = sm + 4 * bin;
     const uint32_t s = a.ctrl[CTRL_STEP] - 1u;
     const bool do_sample = (s % (uint32_t)a.sample_every) == 0u;
     const Real coll_dt = (Real)a.coll_dt;
     unsigned long long ncand_tot = 0, ncoll_tot = 0;
-    uint32_t flags = 0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.ctrl[CTRL_NTOT] = a.cell_start[a.ncells];
+    uint32_t flags = 0, nlive = 0;
 
     for (int c = blockIdx.x * kCollideWarps + w; c < a.ncells; c += gridDim.x * kCollideWarps) {
-        const uint32_t start = a.cell_start[c];
-        const uint32_t n = a.cell_start[c + 1] - start;
-        const bool small = n <= (uint32_t)MAXP;
-        Real* vx = small ? s_v[w][0] : a.dvx + start;
-        Real* vy = small ? s_v[w][1] : a.dvy + start;
-        Real* vz = small ? s_v[w][2] : a.dvz + start;
-        // 1. the cell's old slots in ascending order, 2. gathered into the other half
+        uint32_t n = a.count_d[c];
+        if (n > bin) n = bin;
+        const int64_t base = (int64_t)c * bin;
+        // 1. stable order
         if (n <= 32) {
-            sort_gather<Real, 1>(a, start, n, vx, vy, vz);
-        } else if (n <= 64) {
-            sort_gather<Real, 2>(a, start, n, vx, vy, vz);
-        } else if (n <= 128) {
-            sort_gather<Real, 4>(a, start, n, vx, vy, vz);
+            order_bin<Real, 1>(a, base, n, sx, sy, vx, vy, vz);
+        } else if (MAXR == 2 || n <= 64) {
+            order_bin<Real, (MAXR < 2 ? MAXR : 2)>(a, base, n, sx, sy, vx, vy, vz);
+        } else if (MAXR == 4 || n <= 128) {
+            order_bin<Real, (MAXR < 4 ? MAXR : 4)>(a, base, n, sx, sy, vx, vy, vz);
         } else {
-            // rank of each slot = number of smaller slots in the cell
-            uint32_t* srt = a.arrival + start;
-            const uint32_t* in = small ? s_in[w] : a.perm + start;
-            if (small)
-                for (uint32_t k = lane; k < n; k += 32) s_in[w][k] = a.perm[start + k];
-            __syncwarp();
-            for (uint32_t k = lane; k < n; k += 32) {
-                const uint32_t v = in[k];
-                uint32_t r = 0;
-                for (uint32_t m = 0; m < n; ++m) r += in[m] < v ? 1u : 0u;
-                srt[r] = v;
-            }
-            __syncwarp();
-            for (uint32_t k = lane; k < n; k += 32) {
-                const uint32_t src = srt[k];
-                a.dx[start + k] = a.sx[src];
-                a.dy[start + k] = a.sy[src];
-                vx[k] = a.svx[src];
-                vy[k] = a.svy[src];
-                vz[k] = a.svz[src];
-            }
+            order_bin<Real, MAXR>(a, base, n, sx, sy, vx, vy, vz);
         }
-        __syncwarp();
-        // 3. NTC: N_cand = 1/2 N Nbar F_N (sigma c_r)_max dt / V_c + remainder
+        // 2. NTC: N_cand = 1/2 N Nbar F_N (sigma c_r)_max dt / V_c + remainder
         uint32_t nsel = 0;
         Real cm = (Real)0;
         if (lane == 0) {
             const uint32_t nb = a.nbar_sum[c] + n;
             a.nbar_sum[c] = nb;
+            a.count_s[c] = 0;  // the source half's count is not needed after the move
             cm = a.crmax[c];
-            if (n > 32767u) {
-                flags |= HYB_ST_CELL_OVERFLOW;  // pair indices are packed in 15 and 16 bits
-            } else if (n >= 2) {
+            nlive += n;
+            if (n >= 2) {
                 const Real nbar = (Real)nb / (Real)(s + 1u);
                 const Real ncand = (Real)0.5 * (Real)n * nbar * cm * coll_dt + a.rem[c];
                 const Real fl = floor(ncand);
@@ -429,8 +419,7 @@ __global__ void __launch_bounds__(kCollideWarps * 32) k_collide(DsmcArgs<Real> a
                 const Real ddx = ax - bx, ddy = ay - by, ddz = az - bz;
                 const Real cr = sqrt(ddx * ddx + ddy * ddy + ddz * ddz);
                 if (cr > cm) cm = cr;
-                const bool acc_pair = cr > Rm * cm;
-                if (acc_pair) {
+                if (cr > Rm * cm) {  // the same on every lane
                     const Real nxm = __shfl_sync(kFull, nx, m);
                     const Real nym = __shfl_sync(kFull, ny, m);
                     const Real nzm = __shfl_sync(kFull, nz, m);
@@ -461,17 +450,15 @@ __global__ void __launch_bounds__(kCollideWarps * 32) k_collide(DsmcArgs<Real> a
             ncand_tot += nsel;
             ncoll_tot += ncoll;
         }
-        // 4. write-out and moment sums
-        Real mo[kMoments];
+        // 3. write-out and moment sums
+        Real mo[32];
 #pragma unroll
-        for (int q = 0; q < kMoments; ++q) mo[q] = (Real)0;
+        for (int q = 0; q < 32; ++q) mo[q] = (Real)0;
         for (uint32_t k = lane; k < n; k += 32) {
             const Real ux = vx[k], uy = vy[k], uz = vz[k];
-            if (small) {
-                a.dvx[start + k] = ux;
-                a.dvy[start + k] = uy;
-                a.dvz[start + k] = uz;
-            }
+            a.dvx[base + k] = ux;
+            a.dvy[base + k] = uy;
+            a.dvz[base + k] = uz;
             if (do_sample) {
                 const Real xx = ux * ux, yy = uy * uy, zz = uz * uz;
                 const Real xy = ux * uy, xz = ux * uz, yz = uy * uz;
@@ -484,14 +471,7 @@ __global__ void __launch_bounds__(kCollideWarps * 32) k_collide(DsmcArgs<Real> a
             }
         }
         if (do_sample) {
-            Real mine = (Real)0;
-#pragma unroll
-            for (int q = 0; q < kMoments; ++q) {
-                Real v = mo[q];
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
-                if ((int)lane == q) mine = v;
-            }
+            const Real mine = warp_transpose_sum<Real>(mo);
             if (lane < (unsigned)kMoments) a.acc[(size_t)c * kMoments + lane] += (double)mine;
         }
         __syncwarp();
@@ -500,6 +480,7 @@ __global__ void __launch_bounds__(kCollideWarps * 32) k_collide(DsmcArgs<Real> a
     if (lane == 0) {
         if (ncand_tot) atomicAdd(&a.counters[HYB_C_CANDIDATES], ncand_tot);
         if (ncoll_tot) atomicAdd(&a.counters[HYB_C_COLLISIONS], ncoll_tot);
+        if (nlive) atomicAdd(&a.ctrl[CTRL_NTOT], nlive);
     }
     flags = __reduce_or_sync(kFull, flags);
     if (lane == 0 && flags) atomicOr(&a.ctrl[CTRL_STATUS], flags);
@@ -514,22 +495,14 @@ DsmcArgs<Real> make_args(Ctx& c) {
     a.svx = (const Real*)c.st.pvx[h];
     a.svy = (const Real*)c.st.pvy[h];
     a.svz = (const Real*)c.st.pvz[h];
-    a.mx = (Real*)c.st.px[h];
-    a.my = (Real*)c.st.py[h];
-    a.mvx = (Real*)c.st.pvx[h];
-    a.mvy = (Real*)c.st.pvy[h];
-    a.mvz = (Real*)c.st.pvz[h];
     a.dx = (Real*)c.st.px[o];
     a.dy = (Real*)c.st.py[o];
     a.dvx = (Real*)c.st.pvx[o];
     a.dvy = (Real*)c.st.pvy[o];
     a.dvz = (Real*)c.st.pvz[o];
-    a.key = c.st.key;
-    a.arrival = c.st.arrival;
-    a.perm = c.st.perm;
-    a.count = c.st.count;
-    a.cell_start = c.st.cell_start;
-    a.tile_sum = c.st.tile_sum;
+    a.tag = c.st.tag;
+    a.count_s = c.st.count[h];
+    a.count_d = c.st.count[o];
     a.crmax = (Real*)c.st.crmax;
     a.rem = (Real*)c.st.rem;
     a.nbar_sum = c.st.nbar_sum;
@@ -539,10 +512,9 @@ DsmcArgs<Real> make_args(Ctx& c) {
     a.ncx = c.p.ncx;
     a.ncy = c.p.ncy;
     a.ncells = (int32_t)c.d.ncells;
-    a.ntiles = (int32_t)c.L.ntiles;
+    a.bin = c.d.bin;
     a.sample_every = c.p.sample_every;
     a.ppc = c.p.ppc;
-    a.capacity = c.d.capacity;
     a.dt = c.d.dt;
     a.g_step = c.d.g_step;
     a.coll_dt = c.d.coll_dt;
@@ -561,36 +533,32 @@ int grid_for(const Ctx& c, int64_t work, int threads, int per_sm) {
 
 template <typename Real>
 cudaError_t init_impl(Ctx& c) {
-    // initial particles go to half 0
+    // the initial particles go to half 0: arguments built with half 1 as the source
     c.cur_p = 1;
     DsmcArgs<Real> a = make_args<Real>(c);
     c.cur_p = 0;
     const int64_t n = c.d.ncells * c.p.ppc;
     k_init_particles<Real><<<grid_for(c, n, 256, 16), 256, 0, c.stream>>>(a);
-    k_init_cells<Real><<<grid_for(c, c.d.ncells + 1, 256, 16), 256, 0, c.stream>>>(a);
+    k_init_cells<Real><<<grid_for(c, c.d.ncells, 256, 16), 256, 0, c.stream>>>(a);
     return cudaGetLastError();
 }
 
 template <typename Real>
 cudaError_t step_impl(Ctx& c) {
     DsmcArgs<Real> a = make_args<Real>(c);
-    const int64_t cap = c.d.capacity;
     prof_begin(c, K_MOVE);
-    k_move<Real><<<grid_for(c, cap, 256, 8), 256, 0, c.stream>>>(a);
+    k_move<Real><<<grid_for(c, c.d.ncells * 32, 256, 8), 256, 0, c.stream>>>(a);
     prof_end(c, K_MOVE);
-    prof_begin(c, K_TILE_SUMS);
-    k_tile_sums<<<(int)c.L.ntiles, 256, 0, c.stream>>>(a.count, a.tile_sum, a.ncells);
-    prof_end(c, K_TILE_SUMS);
-    prof_begin(c, K_SCAN);
-    k_scan<Real><<<(int)c.L.ntiles, 256, 0, c.stream>>>(a);
-    prof_end(c, K_SCAN);
-    prof_begin(c, K_RANK);
-    k_rank<Real><<<grid_for(c, cap, 256, 8), 256, 0, c.stream>>>(a);
-    prof_end(c, K_RANK);
-    constexpr int MAXP = sizeof(Real) == 4 ? 256 : 128;
+    // at most 4 warps x 5 x 256 x 8 B = 40 KB of shared memory: below the default limit
+    const size_t smem = (size_t)kCollideWarps * 5 * c.d.bin * sizeof(Real);
+    const int grid = grid_for(c, c.d.ncells * 32, kCollideWarps * 32, 16);
     prof_begin(c, K_COLLIDE);
-    k_collide<Real, MAXP>
-        <<<grid_for(c, c.d.ncells * 32, kCollideWarps * 32, 16), kCollideWarps * 32, 0, c.stream>>>(a);
+    if (c.d.bin <= 64)
+        k_collide<Real, 2><<<grid, kCollideWarps * 32, smem, c.stream>>>(a);
+    else if (c.d.bin <= 128)
+        k_collide<Real, 4><<<grid, kCollideWarps * 32, smem, c.stream>>>(a);
+    else
+        k_collide<Real, 8><<<grid, kCollideWarps * 32, smem, c.stream>>>(a);
     prof_end(c, K_COLLIDE);
     return cudaGetLastError();
 }

@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(128) k_lbm(LbmArgs<Real> a) {
         }
     });
 
-    const Real gy = (Real)a.g_step;
+    const Real gy = a.g_step;
     const Real inv_rho = (Real)1 / rho;
     const Real ux = jx * inv_rho, uy = (jy + (Real)0.5 * rho * gy) * inv_rho, uz = jz * inv_rho;
     const Real u2 = ux * ux + uy * uy + uz * uz;
@@ -158,8 +158,8 @@ __global__ void __launch_bounds__(128) k_lbm(LbmArgs<Real> a) {
         t3y = c3[1] + c3[6] + c3[8];
         t3z = c3[2] + c3[7] + c3[9];
     }
-    const Real om = (Real)(1.0 - 1.0 / a.tau);
-    const Real of = (Real)(1.0 - 0.5 / a.tau);
+    const Real om = a.om;
+    const Real of = a.of;
     const Real gu = gy * uy;
     Real* __restrict__ dst = a.dst;
 
@@ -227,8 +227,9 @@ cudaError_t lbm_impl(Ctx& c) {
     a.nx = (int32_t)c.d.nx;
     a.ny = (int32_t)c.d.ny;
     a.nnodes = c.d.nnodes;
-    a.tau = c.d.tau;
-    a.g_step = c.d.g_step;
+    a.om = (Real)(1.0 - 1.0 / c.d.tau);
+    a.of = (Real)(1.0 - 0.5 / c.d.tau);
+    a.g_step = (Real)c.d.g_step;
     const int64_t blocks = (c.d.nnodes + 127) / 128;
     prof_begin(c, K_LBM);
     k_lbm<Real, LAT><<<(unsigned)blocks, 128, 0, c.stream>>>(a);

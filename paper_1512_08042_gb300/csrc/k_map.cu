@@ -7,18 +7,17 @@
 // a3 = rho(<vvv> - sym(<v> I)) (FP64); the populations f_a = w_a sum_{n<=N} a^(n):H^(n)(xi_a)/n!
 // (Eq. discretefunctions) are evaluated in the state precision.
 //
-// LB2DSMC (Sec. 2.2, Table 1) in three launches:
+// LB2DSMC (Sec. 2.2, Table 1) in two launches:
 //   k_l2d_coef   one warp per coupling cell: mean populations of the cell's lb_ratio^2
 //                nodes, rho and u, the comoving coefficients a2 = sum f c c / rho - I and
 //                a3 = sum f c c c / rho (c = xi - u), M, C = 1 + 30 M (Eq. C), and the
 //                particle count floor(rho ppc + U) (FP64, lanes over populations);
-//   k_l2d_scan   one block: append offsets (exclusive scan), capacity check, slot count;
-//   k_l2d_sample one warp per coupling cell: the old particles are marked deleted; the
-//                cell's trial stream is evaluated 32 trials at a time: Box-Muller xi from
-//                the unit Maxwellian, accepted when C R <= G(xi), G = 1 + a2:H2/2 + a3:H3/6
-//                (Eq. distr_outeq) in the state precision; the k-th accepted trial becomes
-//                the k-th new particle, velocity xi + u (Eq. step6 in c_th units), position
-//                uniform in the cell from the same trial's draws.
+//   k_l2d_sample one warp per coupling cell: the cell's trial stream is evaluated 32 trials
+//                at a time: Box-Muller xi from the unit Maxwellian, accepted when
+//                C R <= G(xi), G = 1 + a2:H2/2 + a3:H3/6 (Eq. distr_outeq) in the state
+//                precision; the k-th accepted trial becomes the k-th particle of the cell's
+//                bin (replacing the old ones), velocity xi + u (Eq. step6 in c_th units),
+//                position uniform in the cell from the same trial's draws.
 // Draws are keyed by (cell, step, purpose, trial index), so the results do not depend on
 // the launch shape.
 #include "hyb_internal.cuh"
@@ -89,7 +88,7 @@ __global__ void __launch_bounds__(128) k_d2l(MapArgs<Real> a) {
 
 // One warp per coupling cell: FP64 Grad coefficients and the particle count.
 template <typename Real, class LAT>
-__global__ void __launch_bounds__(128) k_l2d_coef(MapArgs<Real> a) {
+__global__ void __launch_bounds__(64) k_l2d_coef(MapArgs<Real> a) {
     const uint32_t t_step = a.ctrl[CTRL_STEP];
     const int r = a.lb_ratio;
     const double rr = a.r_lat;
@@ -101,8 +100,8 @@ __global__ void __launch_bounds__(128) k_l2d_coef(MapArgs<Real> a) {
         const int32_t cell = a.list[ci];
         if (cell < 0 || cell >= a.ncx * a.ncy) {
             if (lane == 0) {
-                a.grad[ci].nnew = 0;
-                a.grad[ci].offset = 0xFFFFFFFFu;  // marks a bad index for the scan
+                atomicOr(&a.ctrl[CTRL_STATUS], HYB_ST_BAD_INPUT);
+                a.ctrl[CTRL_L2D_BAD] = 1;
             }
             continue;
         }
@@ -181,64 +180,8 @@ __global__ void __launch_bounds__(128) k_l2d_coef(MapArgs<Real> a) {
             const double u = u01d(draw(a.seed, (uint32_t)cell, t_step, TAG_L2D_ROUND, 0, 0).x);
             const double ne = floor(rho * (double)a.ppc + u);
             g.nnew = ne > 0.0 ? (uint32_t)ne : 0u;
-            g.offset = 0;
+            g.pad = 0;
             a.grad[ci] = g;
-        }
-    }
-}
-
-// One block: exclusive scan of the counts into append offsets, then the capacity check.
-template <typename Real>
-__global__ void __launch_bounds__(1024) k_l2d_scan(MapArgs<Real> a) {
-    __shared__ uint32_t warp_tot[32];
-    __shared__ uint32_t s_carry;
-    const unsigned lane = lane_id();
-    const int w = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_carry = 0;
-    int bad = 0;
-    __syncthreads();
-    for (int base = 0; base < a.n; base += blockDim.x) {
-        const int ci = base + threadIdx.x;
-        uint32_t nn = 0;
-        if (ci < a.n) {
-            if (a.grad[ci].offset == 0xFFFFFFFFu) bad = 1;
-            nn = a.grad[ci].nnew;
-        }
-        uint32_t incl = nn;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const uint32_t yv = __shfl_up_sync(kFull, incl, off);
-            if ((int)lane >= off) incl += yv;
-        }
-        if (lane == 31) warp_tot[w] = incl;
-        __syncthreads();
-        uint32_t wpre = 0, tot = 0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
-            if (i < w) wpre += warp_tot[i];
-            tot += warp_tot[i];
-        }
-        const uint32_t carry = s_carry;
-        if (ci < a.n) a.grad[ci].offset = carry + wpre + incl - nn;
-        __syncthreads();
-        if (threadIdx.x == 0) s_carry = carry + tot;
-        __syncthreads();
-    }
-    const int any_bad = __syncthreads_or(bad);
-    if (threadIdx.x == 0) {
-        const uint32_t total = s_carry;
-        const uint32_t base = a.ctrl[CTRL_NTOT];
-        if (any_bad) {
-            atomicOr(&a.ctrl[CTRL_STATUS], HYB_ST_BAD_INPUT);
-            a.ctrl[CTRL_L2D_SKIP] = 1;
-        } else if ((int64_t)base + total > a.capacity) {
-            atomicOr(&a.ctrl[CTRL_STATUS], HYB_ST_CAPACITY);
-            a.ctrl[CTRL_L2D_SKIP] = 1;
-        } else {
-            a.ctrl[CTRL_L2D_SKIP] = 0;
-            a.ctrl[CTRL_L2D_BASE] = base;
-            a.ctrl[CTRL_L2D_TOTAL] = total;
-            a.ctrl[CTRL_NTOT] = base + total;
-            atomicAdd(&a.counters[HYB_C_CREATED], (unsigned long long)total);
         }
     }
 }
@@ -267,27 +210,29 @@ __device__ __forceinline__ Real grad_G(const Real* a2, const Real* a3, Real X, R
     return G;
 }
 
-// One warp per coupling cell: mark the old particles deleted, then evaluate the cell's trial
-// stream 32 trials at a time; the k-th accepted trial becomes the k-th new particle.
+// One warp per coupling cell: the cell's trial stream is evaluated 32 trials at a time; the
+// k-th accepted trial becomes the k-th particle of the cell's bin, replacing the old ones.
+// Nothing is written if a listed cell index was invalid (the coefficient kernel flagged it).
 template <typename Real, class LAT>
 __global__ void __launch_bounds__(64) k_l2d_sample(MapArgs<Real> a) {
-    if (a.ctrl[CTRL_L2D_SKIP]) return;
-    const uint32_t base = a.ctrl[CTRL_L2D_BASE];
+    if (a.ctrl[CTRL_L2D_BAD]) return;
     const uint32_t t_step = a.ctrl[CTRL_STEP];
     const unsigned lane = lane_id();
     const unsigned lt = (1u << lane) - 1u;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    unsigned long long deleted = 0, attempts = 0, envelope = 0;
+    const uint32_t bin = (uint32_t)a.bin;
+    unsigned long long deleted = 0, created = 0, attempts = 0, envelope = 0;
     uint32_t flags = 0;
+    int32_t dlive = 0;
     for (int ci = gw; ci < a.n; ci += nw) {
         const uint32_t cell = (uint32_t)a.list[ci];
-        const uint32_t s0 = a.cell_start[cell], s1 = a.cell_start[cell + 1];
-        for (uint32_t i = s0 + lane; i < s1; i += 32) {
-            if (a.x[i] >= (Real)0) deleted += 1;
-            a.x[i] = (Real)-1;
-        }
         const GradRec& g = a.grad[ci];
+        const uint32_t nnew = g.nnew;
+        if (nnew > bin) {  // the cell keeps its particles
+            flags |= HYB_ST_CAPACITY;
+            continue;
+        }
         Real a2[6], a3[10];
 #pragma unroll
         for (int k = 0; k < 6; ++k) a2[k] = (Real)g.a2[k];
@@ -295,8 +240,7 @@ __global__ void __launch_bounds__(64) k_l2d_sample(MapArgs<Real> a) {
         for (int k = 0; k < 10; ++k) a3[k] = (Real)g.a3[k];
         const Real C = (Real)g.C;
         const Real ux = (Real)g.u[0], uy = (Real)g.u[1], uz = (Real)g.u[2];
-        const uint32_t nnew = g.nnew;
-        const uint32_t out0 = base + g.offset;
+        const int64_t out0 = (int64_t)cell * bin;
         const Real fx = (Real)(cell % (uint32_t)a.ncx), fy = (Real)(cell / (uint32_t)a.ncx);
         const uint64_t cap64 = 1000ull * nnew;
         const uint32_t cap = cap64 < 0xFFFFFFull ? (uint32_t)cap64 : 0xFFFFFFu;
@@ -330,7 +274,7 @@ __global__ void __launch_bounds__(64) k_l2d_sample(MapArgs<Real> a) {
                 used_mask = last == 31 ? 0xFFFFFFFFu : ((2u << last) - 1u);
             }
             if (acc && rank < need) {
-                const uint32_t slot = out0 + produced + rank;
+                const int64_t slot = out0 + produced + rank;
                 a.x[slot] = fx + (Real)u01f(r2.y);
                 a.y[slot] = fy + (Real)u01f(r2.z);
                 a.vx[slot] = X + ux;
@@ -344,24 +288,22 @@ __global__ void __launch_bounds__(64) k_l2d_sample(MapArgs<Real> a) {
             produced += min((uint32_t)__popc(amask), need);
             j0 += 32;
         }
-        if (produced < nnew) {
-            flags |= HYB_ST_SAMPLING_CAP;
-            for (uint32_t k = produced + lane; k < nnew; k += 32) {
-                const uint32_t slot = out0 + k;
-                a.x[slot] = (Real)-1;
-                a.y[slot] = fy;
-                a.vx[slot] = (Real)0;
-                a.vy[slot] = (Real)0;
-                a.vz[slot] = (Real)0;
-            }
+        if (produced < nnew) flags |= HYB_ST_SAMPLING_CAP;
+        if (lane == 0) {
+            const uint32_t old = a.count[cell];
+            deleted += old;
+            created += produced;
+            dlive += (int32_t)produced - (int32_t)old;
+            a.count[cell] = produced;
         }
     }
-    deleted = __reduce_add_sync(kFull, (unsigned)deleted);
     flags = __reduce_or_sync(kFull, flags);
     if (lane == 0) {
         if (deleted) atomicAdd(&a.counters[HYB_C_DELETED], deleted);
+        if (created) atomicAdd(&a.counters[HYB_C_CREATED], created);
         if (attempts) atomicAdd(&a.counters[HYB_C_L2D_ATTEMPTS], attempts);
         if (envelope) atomicAdd(&a.counters[HYB_C_ENVELOPE], envelope);
+        if (dlive) atomicAdd(&a.ctrl[CTRL_NTOT], (uint32_t)dlive);
         if (flags) atomicOr(&a.ctrl[CTRL_STATUS], flags);
     }
 }
@@ -377,8 +319,8 @@ MapArgs<Real> map_args(Ctx& c, const int32_t* list, int32_t n) {
     a.lb_ratio = c.p.lb_ratio;
     a.ppc = c.p.ppc;
     a.n = n;
+    a.bin = c.d.bin;
     a.nnodes = c.d.nnodes;
-    a.capacity = c.d.capacity;
     a.list = list;
     a.r_lat = c.d.r_lat;
     a.seed = c.p.seed;
@@ -386,7 +328,7 @@ MapArgs<Real> map_args(Ctx& c, const int32_t* list, int32_t n) {
     a.ctrl = c.st.ctrl;
     a.counters = c.st.counters;
     a.grad = c.st.grad;
-    a.cell_start = c.st.cell_start;
+    a.count = c.st.count[c.cur_p];
     a.x = (Real*)c.st.px[c.cur_p];
     a.y = (Real*)c.st.py[c.cur_p];
     a.vx = (Real*)c.st.pvx[c.cur_p];
@@ -413,12 +355,11 @@ cudaError_t d2l_impl(Ctx& c, const int32_t* nodes, int32_t n) {
 template <typename Real, class LAT>
 cudaError_t l2d_impl(Ctx& c, const int32_t* cells, int32_t n) {
     MapArgs<Real> a = map_args<Real>(c, cells, n);
-    prof_begin(c, K_L2D_PREP);
-    k_l2d_coef<Real, LAT><<<blocks_for(c, (int64_t)n * 32, 128, 16), 128, 0, c.stream>>>(a);
-    prof_end(c, K_L2D_PREP);
-    prof_begin(c, K_L2D_SCAN);
-    k_l2d_scan<Real><<<1, 1024, 0, c.stream>>>(a);
-    prof_end(c, K_L2D_SCAN);
+    cudaError_t e = cudaMemsetAsync(c.st.ctrl + CTRL_L2D_BAD, 0, 4, c.stream);
+    if (e != cudaSuccess) return e;
+    prof_begin(c, K_L2D_COEF);
+    k_l2d_coef<Real, LAT><<<blocks_for(c, (int64_t)n * 32, 64, 32), 64, 0, c.stream>>>(a);
+    prof_end(c, K_L2D_COEF);
     prof_begin(c, K_L2D_SAMPLE);
     k_l2d_sample<Real, LAT><<<blocks_for(c, (int64_t)n * 32, 64, 32), 64, 0, c.stream>>>(a);
     prof_end(c, K_L2D_SAMPLE);

@@ -23,9 +23,9 @@ bool params_valid(const hyb_params* p) {
     if (p->sample_every < 1) return false;
     if (!(p->kn > 0.0) || !(p->crmax_init > 0.0) || !(p->capacity_factor >= 1.0)) return false;
     if (!(p->ma >= 0.0) || !(p->T_K > 0.0) || !(p->mass_kg > 0.0)) return false;
-    const double cap = std::ceil(p->capacity_factor * (double)p->ncx * (double)p->ncy * (double)p->ppc);
-    if (cap >= 4294967295.0) return false;          // slot indices are u32
-    if ((double)p->ncx * p->ncy >= 4294967295.0) return false;
+    if (std::ceil(p->capacity_factor * (double)p->ppc) > 256.0) return false;  // bin <= 256
+    const double slots = (double)p->ncx * (double)p->ncy * 256.0;
+    if (slots >= 4294967295.0) return false;  // slot indices are u32
     return true;
 }
 
@@ -46,7 +46,8 @@ void derive(const hyb_params& p, hyb_derived& d) {
     d.nx = (int64_t)p.ncx * p.lb_ratio;
     d.ny = (int64_t)p.ncy * p.lb_ratio;
     d.nnodes = d.nx * d.ny;
-    d.capacity = (int64_t)std::ceil(p.capacity_factor * (double)d.ncells * (double)p.ppc);
+    d.bin = ((int32_t)std::ceil(p.capacity_factor * (double)p.ppc) + 31) / 32 * 32;
+    d.capacity = d.ncells * (int64_t)d.bin;
     d.q = p.lattice;
     d.order = (p.lattice == 39) ? 3 : 2;
 }
@@ -56,7 +57,6 @@ void layout(const hyb_params& p, const hyb_derived& d, hyb_layout& L) {
     const uint64_t rb = (uint64_t)p.real_bytes;
     const uint64_t cap = (uint64_t)d.capacity, nc = (uint64_t)d.ncells, nn = (uint64_t)d.nnodes;
     const uint64_t q = (uint64_t)d.q;
-    const uint64_t ntiles = (nc + kScanTile - 1) / kScanTile;
     uint64_t off = 0;
     auto take = [&](uint64_t bytes) {
         const uint64_t o = off;
@@ -70,12 +70,9 @@ void layout(const hyb_params& p, const hyb_derived& d, hyb_layout& L) {
         L.vy[h] = take(cap * rb);
         L.vz[h] = take(cap * rb);
     }
-    L.key = take(cap * 4);
-    L.arrival = take(cap * 4);
-    L.perm = take(cap * 4);
-    L.count = take(nc * 4);
-    L.cell_start = take((nc + 1) * 4);
-    L.tile_sum = take(ntiles * 4);
+    L.tag = take(cap * 4);
+    L.count[0] = take(nc * 4);
+    L.count[1] = take(nc * 4);
     L.crmax = take(nc * rb);
     L.rem = take(nc * rb);
     L.nbar_sum = take(nc * 4);
@@ -88,9 +85,9 @@ void layout(const hyb_params& p, const hyb_derived& d, hyb_layout& L) {
     L.capacity = d.capacity;
     L.ncells = d.ncells;
     L.nnodes = d.nnodes;
-    L.ntiles = (int64_t)ntiles;
     L.q = d.q;
     L.real_bytes = p.real_bytes;
+    L.bin = d.bin;
 }
 
 hyb_status fail(Ctx& c, hyb_status s, const char* what, cudaError_t e = cudaSuccess) {
@@ -164,13 +161,9 @@ void resolve(Ctx& c) {
         s.pvy[h] = a + L.vy[h];
         s.pvz[h] = a + L.vz[h];
         s.f[h] = a + L.f[h];
+        s.count[h] = (uint32_t*)(a + L.count[h]);
     }
-    s.key = (uint32_t*)(a + L.key);
-    s.arrival = (uint32_t*)(a + L.arrival);
-    s.perm = (uint32_t*)(a + L.perm);
-    s.count = (uint32_t*)(a + L.count);
-    s.cell_start = (uint32_t*)(a + L.cell_start);
-    s.tile_sum = (uint32_t*)(a + L.tile_sum);
+    s.tag = (uint32_t*)(a + L.tag);
     s.crmax = a + L.crmax;
     s.rem = a + L.rem;
     s.nbar_sum = (uint32_t*)(a + L.nbar_sum);

@@ -64,30 +64,30 @@ def test_layout_is_aligned_and_disjoint(lib):
     L = B.layout(cfg)
     d = B.derive(cfg)
     rb = 4
+    assert d["bin"] == 128 and d["capacity"] == 64 * 256 * 128
     regions = []
     for h in range(2):
         for k in ("x", "y", "vx", "vy", "vz"):
             regions.append((getattr(L, k)[h], d["capacity"] * rb))
         regions.append((L.f[h], d["q"] * d["nnodes"] * rb))
-    for k, sz in (("key", 4 * d["capacity"]), ("arrival", 4 * d["capacity"]),
-                  ("perm", 4 * d["capacity"]), ("count", 4 * d["ncells"]),
-                  ("cell_start", 4 * (d["ncells"] + 1)), ("acc", 160 * d["ncells"]),
-                  ("rem", rb * d["ncells"]), ("nbar_sum", 4 * d["ncells"]), ("ctrl", 64),
-                  ("counters", 128)):
+        regions.append((L.count[h], 4 * d["ncells"]))
+    for k, sz in (("tag", 4 * d["capacity"]), ("acc", 160 * d["ncells"]),
+                  ("crmax", rb * d["ncells"]), ("rem", rb * d["ncells"]),
+                  ("nbar_sum", 4 * d["ncells"]), ("ctrl", 64), ("counters", 128)):
         regions.append((getattr(L, k), sz))
     regions.sort()
     for (o1, s1), (o2, _) in zip(regions, regions[1:]):
         assert o1 % 256 == 0
         assert o1 + s1 <= o2
     assert regions[-1][0] + regions[-1][1] <= L.total_bytes
-    assert d["capacity"] == int(np.ceil(1.25 * 64 * 256 * 50))
 
 
 def test_invalid_parameters_are_rejected(lib):
     good = W.config(ncx=8, ncy=2, ppc=5, seed=1)
     B.derive(good)
     for bad in (dict(ncx=5), dict(lattice=27), dict(real_bytes=2), dict(lb_ratio=3),
-                dict(kn=0.0), dict(sample_every=0), dict(capacity_factor=0.5), dict(ppc=0)):
+                dict(kn=0.0), dict(sample_every=0), dict(capacity_factor=0.5), dict(ppc=0),
+                dict(ppc=200)):
         cfg = dict(good)
         cfg.update(bad)
         with pytest.raises(B.HybError) as ei:
