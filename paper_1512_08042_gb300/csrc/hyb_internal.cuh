@@ -80,9 +80,9 @@ struct State {
     GradRec* grad;
 };
 
-// Everything a DSMC kernel needs, passed by value: the source half (s*, count_s) is read by
-// the move, which bins particles into the destination half (d*, count_d); the collide works
-// in place on the destination half.
+// Everything a DSMC kernel needs, passed by value: the move updates the source half in
+// place (m*, the same arrays as s*) and lists each particle's slot in the tag list of its new
+// cell (count_d); the collide gathers from the source half into the destination half (d*).
 template <typename Real>
 struct DsmcArgs {
     const Real* sx;
@@ -90,6 +90,11 @@ struct DsmcArgs {
     const Real* svx;
     const Real* svy;
     const Real* svz;
+    Real* mx;
+    Real* my;
+    Real* mvx;
+    Real* mvy;
+    Real* mvz;
     Real* dx;
     Real* dy;
     Real* dvx;

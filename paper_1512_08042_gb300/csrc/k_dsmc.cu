@@ -7,14 +7,15 @@
 // NTC order of Bird that the paper uses in Sec. 5: move, index, collide, sample) is two
 // launches:
 //   k_move     one warp per source cell: body-force kick, free flight, diffuse wall
-//              re-emission (Sec. 3.1), periodic wrap, new cell; the particle is appended to
-//              its new cell's bin in the other half by a warp-aggregated atomic, with its
-//              origin slot as a tag. The last block to finish advances the step counters.
-//   k_collide  one warp per cell of the new half: the bin is put in stable order (ascending
-//              origin slot = origin cell, then rank in it: a bitonic sort in registers),
-//              NTC collisions (Eq. collisionnumber) run in shared memory, the particles are
-//              written back in order, and their sums 1, v, vv, vvv are added to the FP64
-//              cumulative sums of the cell (Sec. 2.1, Fig. 1).
+//              re-emission (Sec. 3.1), periodic wrap, new cell; the moved particle is written
+//              back in place and its slot is appended to the tag list of its new cell's bin
+//              by a warp-aggregated atomic. The last block to finish advances the step
+//              counters.
+//   k_collide  one warp per cell: the cell's tags are put in stable order (ascending origin
+//              slot = origin cell, then rank in it: a bitonic sort in registers), the
+//              particles are gathered from the source half into the bin of the other half,
+//              NTC collisions (Eq. collisionnumber) run in shared memory, and the sums 1, v,
+//              vv, vvv are added to the FP64 cumulative sums of the cell (Sec. 2.1, Fig. 1).
 // This file is compiled without FMA contraction so that positions, cell keys, pair choices
 // and post-collision velocities are the IEEE float (or double) results of the written
 // expressions.
@@ -174,17 +175,16 @@ __global__ void __launch_bounds__(256) k_move(DsmcArgs<Real> a) {
                 if ((int)lane == leader) b0 = atomicAdd(&a.count_d[key], (uint32_t)__popc(peers));
                 b0 = __shfl_sync(peers, b0, leader);
                 const uint32_t arr = b0 + (uint32_t)__popc(peers & lt);
-                if (arr < bin) {
-                    const int64_t j = (int64_t)key * bin + arr;
-                    a.dx[j] = px;
-                    a.dy[j] = py;
-                    a.dvx[j] = ux;
-                    a.dvy[j] = uy;
-                    a.dvz[j] = uz;
-                    a.tag[j] = (uint32_t)(base + k);
-                } else {
+                const int64_t i = base + k;
+                a.mx[i] = px;
+                a.my[i] = py;
+                a.mvx[i] = ux;
+                a.mvy[i] = uy;
+                a.mvz[i] = uz;
+                if (arr < bin)
+                    a.tag[(int64_t)key * bin + arr] = (uint32_t)i;
+                else
                     lost += 1;
-                }
             }
         }
     }
@@ -217,11 +217,10 @@ __global__ void __launch_bounds__(256) k_move(DsmcArgs<Real> a) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Ascending bitonic sort of 32 R (key, value) pairs held R per lane (pair r of a lane at
-// position lane + 32 r). All loops have constant trip counts and unroll, so the pairs stay in
-// registers.
+// Ascending bitonic sort of 32 R keys held R per lane (key r of a lane at position
+// lane + 32 r). All loops have constant trip counts and unroll, so the keys stay in registers.
 template <int R>
-__device__ __forceinline__ void bitonic_sort(uint32_t (&key)[R], uint32_t (&val)[R]) {
+__device__ __forceinline__ void bitonic_sort(uint32_t (&v)[R]) {
     constexpr int N = 32 * R;
     const int lane = (int)lane_id();
 #pragma unroll
@@ -235,86 +234,68 @@ __device__ __forceinline__ void bitonic_sort(uint32_t (&key)[R], uint32_t (&val)
                     const int o = r ^ jr;
                     if (r < o) {
                         const bool asc = ((lane + 32 * r) & k) == 0;
-                        const bool swap = asc ? (key[r] > key[o]) : (key[r] < key[o]);
-                        if (swap) {
-                            const uint32_t tk = key[r], tv = val[r];
-                            key[r] = key[o];
-                            val[r] = val[o];
-                            key[o] = tk;
-                            val[o] = tv;
-                        }
+                        const uint32_t lo = min(v[r], v[o]), hi = max(v[r], v[o]);
+                        v[r] = asc ? lo : hi;
+                        v[o] = asc ? hi : lo;
                     }
                 }
             } else {
                 const bool lower = (lane & j) == 0;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const uint32_t ok = __shfl_xor_sync(kFull, key[r], j);
-                    const uint32_t ov = __shfl_xor_sync(kFull, val[r], j);
+                    const uint32_t o = __shfl_xor_sync(kFull, v[r], j);
                     const bool asc = ((lane + 32 * r) & k) == 0;
-                    const bool take_min = lower == asc;
-                    const bool take_other = take_min ? (ok < key[r]) : (ok > key[r]);
-                    if (take_other) {
-                        key[r] = ok;
-                        val[r] = ov;
-                    }
+                    v[r] = (lower == asc) ? min(v[r], o) : max(v[r], o);
                 }
             }
         }
     }
 }
 
-// Stable order of a bin: the cell's n <= 32 R particles are loaded, sorted by their tag
-// (origin slot), left in shared memory in that order (velocities) and written back to the
-// bin in that order (positions).
+// Gather one particle from its source slot into position k of the destination bin
+// (positions to global memory, velocities to the warp's shared arrays).
+template <typename Real>
+__device__ __forceinline__ void gather_one(const DsmcArgs<Real>& a, int64_t base, uint32_t k,
+                                           uint32_t src, Real* vx, Real* vy, Real* vz) {
+    a.dx[base + k] = a.sx[src];
+    a.dy[base + k] = a.sy[src];
+    vx[k] = a.svx[src];
+    vy[k] = a.svy[src];
+    vz[k] = a.svz[src];
+}
+
+// Stable order for n <= 32 R: sort the tags in registers, then gather.
 template <typename Real, int R>
-__device__ __forceinline__ void order_bin(const DsmcArgs<Real>& a, int64_t base, uint32_t n,
-                                          Real* sx, Real* sy, Real* vx, Real* vy, Real* vz) {
+__device__ __forceinline__ void order_small(const DsmcArgs<Real>& a, int64_t base, uint32_t n,
+                                            Real* vx, Real* vy, Real* vz) {
     const unsigned lane = lane_id();
-    uint32_t key[R], val[R];
+    uint32_t v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const uint32_t k = lane + 32u * r;
-        if (k < n) {
-            key[r] = a.tag[base + k];
-            sx[k] = a.dx[base + k];
-            sy[k] = a.dy[base + k];
-            vx[k] = a.dvx[base + k];
-            vy[k] = a.dvy[base + k];
-            vz[k] = a.dvz[base + k];
-        } else {
-            key[r] = 0xFFFFFFFFu;
-        }
-        val[r] = k;
+        v[r] = k < n ? a.tag[base + k] : 0xFFFFFFFFu;
     }
-    bitonic_sort<R>(key, val);
-    __syncwarp();
-    Real ox[R], oy[R], ovx[R], ovy[R], ovz[R];
+    bitonic_sort<R>(v);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const uint32_t k = lane + 32u * r;
-        if (k < n) {
-            const uint32_t src = val[r];
-            ox[r] = sx[src];
-            oy[r] = sy[src];
-            ovx[r] = vx[src];
-            ovy[r] = vy[src];
-            ovz[r] = vz[src];
-        }
+        if (k < n) gather_one(a, base, k, v[r], vx, vy, vz);
     }
+}
+
+// Stable order for larger n: rank of each tag = number of smaller tags in the cell.
+template <typename Real>
+__device__ __forceinline__ void order_large(const DsmcArgs<Real>& a, int64_t base, uint32_t n,
+                                            uint32_t* st, Real* vx, Real* vy, Real* vz) {
+    const unsigned lane = lane_id();
+    for (uint32_t k = lane; k < n; k += 32) st[k] = a.tag[base + k];
     __syncwarp();
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const uint32_t k = lane + 32u * r;
-        if (k < n) {
-            a.dx[base + k] = ox[r];
-            a.dy[base + k] = oy[r];
-            vx[k] = ovx[r];
-            vy[k] = ovy[r];
-            vz[k] = ovz[r];
-        }
+    for (uint32_t k = lane; k < n; k += 32) {
+        const uint32_t v = st[k];
+        uint32_t r = 0;
+        for (uint32_t m = 0; m < n; ++m) r += st[m] < v ? 1u : 0u;
+        gather_one(a, base, r, v, vx, vy, vz);
     }
-    __syncwarp();
 }
 
 // Reduce 32 per-lane values v[0..31] over the warp so that lane L ends with the total of
@@ -337,19 +318,18 @@ __device__ __forceinline__ Real warp_transpose_sum(Real (&v)[32]) {
 
 constexpr int kCollideWarps = 4;
 
-// MAXR = bin / 32 rounded up to a power of two: the largest register sort instantiated.
-template <typename Real, int MAXR>
+template <typename Real>
 __global__ void __launch_bounds__(kCollideWarps * 32) k_collide(DsmcArgs<Real> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int w = threadIdx.x >> 5;
     const unsigned lane = lane_id();
     const uint32_t bin = (uint32_t)a.bin;
-    Real* sm = reinterpret_cast<Real*>(smem_raw) + (size_t)w * 5 * bin;
-    Real* sx = sm;
-    Real* sy = sm + bin;
-    Real* vx = sm + 2 * bin;
-    Real* vy = sm + 3 * bin;
-    Real* vz = sm + 4 * bin;
+    Real* sm = reinterpret_cast<Real*>(smem_raw) + (size_t)w * 3 * bin;
+    Real* vx = sm;
+    Real* vy = sm + bin;
+    Real* vz = sm + 2 * bin;
+    uint32_t* st = reinterpret_cast<uint32_t*>(reinterpret_cast<Real*>(smem_raw) +
+                                                (size_t)kCollideWarps * 3 * bin) + (size_t)w * bin;
     const uint32_t s = a.ctrl[CTRL_STEP] - 1u;
     const bool do_sample = (s % (uint32_t)a.sample_every) == 0u;
     const Real coll_dt = (Real)a.coll_dt;
@@ -360,16 +340,11 @@ __global__ void __launch_bounds__(kCollideWarps * 32) k_collide(DsmcArgs<Real> a
         uint32_t n = a.count_d[c];
         if (n > bin) n = bin;
         const int64_t base = (int64_t)c * bin;
-        // 1. stable order
-        if (n <= 32) {
-            order_bin<Real, 1>(a, base, n, sx, sy, vx, vy, vz);
-        } else if (MAXR == 2 || n <= 64) {
-            order_bin<Real, (MAXR < 2 ? MAXR : 2)>(a, base, n, sx, sy, vx, vy, vz);
-        } else if (MAXR == 4 || n <= 128) {
-            order_bin<Real, (MAXR < 4 ? MAXR : 4)>(a, base, n, sx, sy, vx, vy, vz);
-        } else {
-            order_bin<Real, MAXR>(a, base, n, sx, sy, vx, vy, vz);
-        }
+        // 1. stable order and gather
+        if (n <= 32) order_small<Real, 1>(a, base, n, vx, vy, vz);
+        else if (n <= 64) order_small<Real, 2>(a, base, n, vx, vy, vz);
+        else order_large<Real>(a, base, n, st, vx, vy, vz);
+        __syncwarp();
         // 2. NTC: N_cand = 1/2 N Nbar F_N (sigma c_r)_max dt / V_c + remainder
         uint32_t nsel = 0;
         Real cm = (Real)0;
@@ -495,6 +470,11 @@ DsmcArgs<Real> make_args(Ctx& c) {
     a.svx = (const Real*)c.st.pvx[h];
     a.svy = (const Real*)c.st.pvy[h];
     a.svz = (const Real*)c.st.pvz[h];
+    a.mx = (Real*)c.st.px[h];
+    a.my = (Real*)c.st.py[h];
+    a.mvx = (Real*)c.st.pvx[h];
+    a.mvy = (Real*)c.st.pvy[h];
+    a.mvz = (Real*)c.st.pvz[h];
     a.dx = (Real*)c.st.px[o];
     a.dy = (Real*)c.st.py[o];
     a.dvx = (Real*)c.st.pvx[o];
@@ -549,16 +529,11 @@ cudaError_t step_impl(Ctx& c) {
     prof_begin(c, K_MOVE);
     k_move<Real><<<grid_for(c, c.d.ncells * 32, 256, 8), 256, 0, c.stream>>>(a);
     prof_end(c, K_MOVE);
-    // at most 4 warps x 5 x 256 x 8 B = 40 KB of shared memory: below the default limit
-    const size_t smem = (size_t)kCollideWarps * 5 * c.d.bin * sizeof(Real);
+    // at most 4 warps x 256 x (3 x 8 + 4) B = 28 KB of shared memory: below the default limit
+    const size_t smem = (size_t)kCollideWarps * c.d.bin * (3 * sizeof(Real) + 4);
     const int grid = grid_for(c, c.d.ncells * 32, kCollideWarps * 32, 16);
     prof_begin(c, K_COLLIDE);
-    if (c.d.bin <= 64)
-        k_collide<Real, 2><<<grid, kCollideWarps * 32, smem, c.stream>>>(a);
-    else if (c.d.bin <= 128)
-        k_collide<Real, 4><<<grid, kCollideWarps * 32, smem, c.stream>>>(a);
-    else
-        k_collide<Real, 8><<<grid, kCollideWarps * 32, smem, c.stream>>>(a);
+    k_collide<Real><<<grid, kCollideWarps * 32, smem, c.stream>>>(a);
     prof_end(c, K_COLLIDE);
     return cudaGetLastError();
 }
