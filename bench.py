@@ -114,6 +114,23 @@ def traffic_record(kernel):
     return rec["bytes_per_launch"] if h == rec["source_sha"] else None
 
 
+def replica_config(cfg, rank):
+    """Rank r of a replica ensemble runs the same channel with its own Philox key."""
+    out = dict(cfg)
+    out["seed"] = int(cfg["seed"]) + int(rank)
+    return out
+
+
+def max_over_ranks(dist, value, device):
+    """The largest `value` over all ranks (the job is as slow as its slowest rank)."""
+    import torch
+    if dist is None:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_oracle(cfg, steps, budget_s):
     """Time the CPU oracle on hybrid steps of `cfg`; returns (steps/s, steps run)."""
     from oracle import oracle as O
@@ -148,7 +165,7 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    cfg = W.WORKLOADS[args.workload]
+    cfg = replica_config(W.WORKLOADS[args.workload], rank)
     nodes_np, cells_np = W.coupling_sites(cfg)
 
     if args.impl == "reference":
@@ -245,9 +262,7 @@ def main():
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = sum(step_ms)
     if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(dist, total_ms, dev)
         dist.barrier()
     stop.set()
     th.join(timeout=5)
