@@ -188,6 +188,23 @@ hyb_status map_dsmc_to_lbm(hyb_ctx* ctx, const int32_t* dev_nodes, int32_t n);
  * its particles and raises HYB_ST_CAPACITY. */
 hyb_status map_lbm_to_dsmc(hyb_ctx* ctx, const int32_t* dev_cells, int32_t n);
 
+/* map_lbm_to_dsmc without any device memory of its own beyond the context's arena.
+ * The paper has no counterpart: this entry point exists for callers that cannot give the
+ * library more device memory or let it allocate, for example a host application whose own
+ * allocator owns every byte of the GPU under a fixed budget, or a real-time loop that may not
+ * call an allocator at all. It computes exactly what map_lbm_to_dsmc computes; its per-cell
+ * Grad records go to a fixed array of HYB_NOALLOC_MAX_CELLS records (176 bytes each, about
+ * 720 KB) compiled into the library, which every GPU that loads the library keeps until the
+ * process exits. It calls no cudaMalloc, cudaFree or other allocating routine.
+ * n > HYB_NOALLOC_MAX_CELLS returns HYB_EINVAL and launches nothing. The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture, and call with the context's
+ * device current (otherwise HYB_EINVAL). Every call on a device shares the one array and it
+ * keeps the last call's records: calls that overlap on the GPU (other streams or contexts on
+ * the same device) race on it and must be serialised by the caller. */
+#define HYB_NOALLOC_MAX_CELLS 4096
+hyb_status map_lbm_to_dsmc_noalloc(hyb_ctx* ctx, const int32_t* dev_cells, int32_t n);
+
 /* One or more hybrid steps: dsmc_step(1), map_dsmc_to_lbm, lbm_step(1), map_lbm_to_dsmc.
  * n_nodes or n_cells may be 0 to skip a mapping. With use_graph != 0 each step is replayed
  * from a CUDA graph captured on first use (one per ping-pong parity; recaptured if the

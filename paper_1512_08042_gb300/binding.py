@@ -21,6 +21,7 @@ COUNTER_NAMES = ["wall_hits", "candidates", "collisions", "created", "deleted",
 KERNELS = {"move": 0, "collide": 1, "lbm": 2, "dsmc2lb": 3, "lb2dsmc_coef": 4,
            "lb2dsmc_sample": 5}
 CTRL_STATUS, CTRL_NTOT, CTRL_STEP, CTRL_NSAMPLES = 0, 1, 2, 3
+NOALLOC_MAX_CELLS = 4096
 
 _u32, _i32, _i64, _u64, _dbl, _vp = (ctypes.c_uint32, ctypes.c_int32, ctypes.c_int64,
                                      ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p)
@@ -51,6 +52,7 @@ class HybLayout(ctypes.Structure):
 
 EXPORTS = ["hyb_derive", "hyb_layout_compute", "hyb_lattice", "hyb_status_string", "dsmc_init",
            "dsmc_step", "lbm_step", "sample_moments", "map_dsmc_to_lbm", "map_lbm_to_dsmc",
+           "map_lbm_to_dsmc_noalloc",
            "hyb_hybrid_step", "hyb_current", "hyb_sync_status", "hyb_read_counters",
            "hyb_profile", "hyb_profile_harvest", "hyb_profile_read", "hyb_debug_philox",
            "hyb_last_error", "hyb_destroy"]
@@ -92,6 +94,7 @@ def lib():
     L.sample_moments.argtypes = [_vp, _vp, _i32]
     L.map_dsmc_to_lbm.argtypes = [_vp, _vp, _i32]
     L.map_lbm_to_dsmc.argtypes = [_vp, _vp, _i32]
+    L.map_lbm_to_dsmc_noalloc.argtypes = [_vp, _vp, _i32]
     L.hyb_hybrid_step.argtypes = [_vp, _vp, _i32, _vp, _i32, _i32, _i32]
     L.hyb_current.argtypes = [_vp, P(_i32), P(_i32)]
     L.hyb_sync_status.argtypes = [_vp, P(_u32)]
@@ -211,6 +214,13 @@ class Hybrid:
     def map_lbm_to_dsmc(self, cells):
         self._inputs(cells)
         _check(lib().map_lbm_to_dsmc(self.ctx, cells.data_ptr(), cells.numel()), self.ctx)
+
+    def map_lbm_to_dsmc_noalloc(self, cells):
+        """map_lbm_to_dsmc with its scratch in the library's fixed device array (for callers
+        that cannot give the library device memory beyond the state; at most
+        NOALLOC_MAX_CELLS cells per call)."""
+        self._inputs(cells)
+        _check(lib().map_lbm_to_dsmc_noalloc(self.ctx, cells.data_ptr(), cells.numel()), self.ctx)
 
     def hybrid_step(self, nodes=None, cells=None, nsteps=1, use_graph=True, order_inputs=True):
         """`order_inputs=False` skips the stream ordering of `nodes`/`cells` (for callers

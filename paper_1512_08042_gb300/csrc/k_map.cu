@@ -22,6 +22,13 @@
 // the launch shape.
 #include "hyb_internal.cuh"
 
+// Fixed scratch of map_lbm_to_dsmc_noalloc: one Grad record per coupling cell, for callers
+// that cannot hand the library any device memory beyond the state itself. The array lives
+// in every device that loads the library until the process exits. Host code must not pass
+// `g_l2d_scratch` itself to a kernel (on the host it names a stand-in, not device memory):
+// its device address is looked up once per device with cudaGetSymbolAddress.
+static __device__ __align__(256) hyb::GradRec g_l2d_scratch[HYB_NOALLOC_MAX_CELLS];
+
 namespace hyb {
 
 namespace {
@@ -366,7 +373,53 @@ cudaError_t l2d_impl(Ctx& c, const int32_t* cells, int32_t n) {
     return cudaGetLastError();
 }
 
+constexpr int kMaxDevices = 64;
+GradRec* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of the fixed scratch on `device`, which must be the current device.
+cudaError_t noalloc_scratch(int device, GradRec** out) {
+    if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+    if (!g_scratch_addr[device]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_l2d_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_addr[device] = (GradRec*)p;
+    }
+    *out = g_scratch_addr[device];
+    return cudaSuccess;
+}
+
+template <typename Real, class LAT>
+cudaError_t l2d_noalloc_impl(Ctx& c, const int32_t* cells, int32_t n, GradRec* rec) {
+    MapArgs<Real> a = map_args<Real>(c, cells, n);
+    a.grad = rec;  // the fixed array instead of the arena's records
+    cudaError_t e = cudaMemsetAsync(c.st.ctrl + CTRL_L2D_BAD, 0, 4, c.stream);
+    if (e != cudaSuccess) return e;
+    prof_begin(c, K_L2D_COEF);
+    k_l2d_coef<Real, LAT><<<blocks_for(c, (int64_t)n * 32, 64, 32), 64, 0, c.stream>>>(a);
+    prof_end(c, K_L2D_COEF);
+    prof_begin(c, K_L2D_SAMPLE);
+    k_l2d_sample<Real, LAT><<<blocks_for(c, (int64_t)n * 32, 64, 32), 64, 0, c.stream>>>(a);
+    prof_end(c, K_L2D_SAMPLE);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_map_l2d_noalloc(Ctx& c, const int32_t* cells, int32_t n) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev != c.device) return cudaErrorInvalidDevice;
+    GradRec* rec = nullptr;
+    e = noalloc_scratch(dev, &rec);
+    if (e != cudaSuccess) return e;
+    if (c.p.lattice == 39)
+        return c.p.real_bytes == 4 ? l2d_noalloc_impl<float, D3Q39>(c, cells, n, rec)
+                                   : l2d_noalloc_impl<double, D3Q39>(c, cells, n, rec);
+    return c.p.real_bytes == 4 ? l2d_noalloc_impl<float, D3Q19>(c, cells, n, rec)
+                               : l2d_noalloc_impl<double, D3Q19>(c, cells, n, rec);
+}
 
 cudaError_t launch_map_d2l(Ctx& c, const int32_t* nodes, int32_t n) {
     if (c.p.lattice == 39)

@@ -341,6 +341,21 @@ hyb_status map_lbm_to_dsmc(hyb_ctx* h, const int32_t* dev_cells, int32_t n) {
     return check(h->c, launch_map_l2d(h->c, dev_cells, n), "map_lbm_to_dsmc launch");
 }
 
+hyb_status map_lbm_to_dsmc_noalloc(hyb_ctx* h, const int32_t* dev_cells, int32_t n) {
+    if (!h || n < 0 || (n > 0 && !dev_cells) || n > h->c.d.ncells) return HYB_EINVAL;
+    Ctx& c = h->c;
+    if (n > HYB_NOALLOC_MAX_CELLS)
+        return fail(c, HYB_EINVAL,
+                    "map_lbm_to_dsmc_noalloc: more coupling cells than its fixed scratch holds "
+                    "(HYB_NOALLOC_MAX_CELLS)");
+    if (n == 0) return HYB_OK;
+    const cudaError_t e = launch_map_l2d_noalloc(c, dev_cells, n);
+    if (e == cudaErrorInvalidDevice)
+        return fail(c, HYB_EINVAL,
+                    "map_lbm_to_dsmc_noalloc: the context's device must be the current device", e);
+    return check(c, e, "map_lbm_to_dsmc_noalloc launch");
+}
+
 hyb_status hyb_hybrid_step(hyb_ctx* h, const int32_t* dev_nodes, int32_t n_nodes,
                            const int32_t* dev_cells, int32_t n_cells, int32_t nsteps,
                            int32_t use_graph) {
