@@ -158,6 +158,8 @@ def main():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--profile-kernel", default=None)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="run this many hybrid steps with direct launches and exit (for ncu)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -219,6 +221,14 @@ def main():
 
     def step():
         h.hybrid_step(nodes, cells, nsteps=1, use_graph=use_graph, order_inputs=False)
+
+    if args.profile_steps:
+        for _ in range(args.profile_steps):
+            h.hybrid_step(nodes, cells, nsteps=1, use_graph=False, order_inputs=False)
+        rc, bits = h.sync_status()
+        print(json.dumps({"profile_steps": args.profile_steps, "status": rc, "bits": bits}))
+        h.close()
+        return
 
     # warm-up, and pick the dominant kernel by timing each one over a few steps
     for _ in range(args.warmup):
