@@ -93,25 +93,32 @@ inline GradCell grad_from_populations(const Lattice& L, const double* f, int ord
     }
     g.rho = rho;
     for (int i = 0; i < 3; ++i) g.u[i] = j[i] / rho;
-    Coeffs& h = g.ahat;
-    h = Coeffs{};
-    h.a0 = 1.0;
+    // sums of f c c and f c c c over the populations, c = xi - u, then divided by rho
+    double s2[3][3] = {}, s3[3][3][3] = {};
     for (int a = 0; a < L.q; ++a) {
         double c[3];
         for (int i = 0; i < 3; ++i) c[i] = L.xi[a][i] - g.u[i];
         for (int i = 0; i < 3; ++i)
             for (int k = 0; k < 3; ++k) {
-                h.a2[i][k] += f[a] * c[i] * c[k] / rho;
-                if (order >= 3)
-                    for (int l = 0; l < 3; ++l) h.a3[i][k][l] += f[a] * c[i] * c[k] * c[l] / rho;
+                s2[i][k] += f[a] * c[i] * c[k];
+                for (int l = 0; l < 3; ++l) s3[i][k][l] += f[a] * c[i] * c[k] * c[l];
             }
     }
-    for (int i = 0; i < 3; ++i) h.a2[i][i] -= 1.0;
-    double M = 0.0;
+    Coeffs& h = g.ahat;
+    h = Coeffs{};
+    h.a0 = 1.0;
     for (int i = 0; i < 3; ++i)
         for (int k = 0; k < 3; ++k) {
+            h.a2[i][k] = s2[i][k] / rho - kd(i, k);
+            if (order >= 3)
+                for (int l = 0; l < 3; ++l) h.a3[i][k][l] = s3[i][k][l] / rho;
+        }
+    // M over the distinct components (i <= k, i <= k <= l)
+    double M = 0.0;
+    for (int i = 0; i < 3; ++i)
+        for (int k = i; k < 3; ++k) {
             M = std::max(M, std::fabs(h.a2[i][k]));
-            for (int l = 0; l < 3; ++l) M = std::max(M, std::fabs(h.a3[i][k][l]));
+            for (int l = k; l < 3; ++l) M = std::max(M, std::fabs(h.a3[i][k][l]));
         }
     g.M = M;
     g.C = 1.0 + 30.0 * M;
