@@ -38,151 +38,176 @@ __host__ __device__ constexpr int E(int a, int i) {
     return LatTab<LAT>::e(a, i);
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
-    return v;
+// Lattice table in shared memory, for lanes that each handle a different population.
+template <class LAT>
+__device__ __forceinline__ void load_lattice(int* se, float* sw) {
+    for (int q = threadIdx.x; q < LAT::Q; q += blockDim.x) {
+        se[3 * q] = LatTab<LAT>::e(q, 0);
+        se[3 * q + 1] = LatTab<LAT>::e(q, 1);
+        se[3 * q + 2] = LatTab<LAT>::e(q, 2);
+        sw[q] = (float)LatTab<LAT>::w(q);
+    }
 }
 
+// DSMC2LB: one warp per coupling node. Lanes 0-19 read the cell's 20 sums; the FP64
+// coefficient solve is spread over the lanes (one coefficient each); the 19 coefficients
+// are broadcast and each lane evaluates one or two populations in the state precision.
 template <typename Real, class LAT>
 __global__ void __launch_bounds__(128) k_d2l(MapArgs<Real> a) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= a.n) return;
-    const int32_t node = a.list[t];
-    if (node < 0 || (int64_t)node >= a.nnodes) {
-        atomicOr(&a.ctrl[CTRL_STATUS], HYB_ST_BAD_INPUT);
-        return;
-    }
-    const int x = node % a.nx, y = node / a.nx;
-    const int64_t cell = (int64_t)(y / a.lb_ratio) * a.ncx + (x / a.lb_ratio);
-    const uint32_t S = a.ctrl[CTRL_NSAMPLES];
-    const double* m = a.acc + cell * kMoments;
-    const double NS = m[0];
-    if (S == 0 || !(NS > 0.0)) {
-        atomicOr(&a.ctrl[CTRL_STATUS], HYB_ST_BAD_INPUT);
-        return;
-    }
-    // FP64 coefficient solve
-    const double rho = (NS / (double)S) / (double)a.ppc;
-    const double iNS = 1.0 / NS;
-    const double m1x = m[1] * iNS, m1y = m[2] * iNS, m1z = m[3] * iNS;
-    const double d2[6] = {1, 0, 0, 1, 0, 1};
-    // sym(<v> I) for the packed entries xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz
-    const double s3[10] = {3 * m1x, m1y, m1z, m1x, 0.0, m1x, 3 * m1y, m1z, m1y, 3 * m1z};
-    Real a2[6], a3[10];
-    for (int k = 0; k < 6; ++k) a2[k] = (Real)(rho * (m[4 + k] * iNS - d2[k]));
-    for (int k = 0; k < 10; ++k) a3[k] = (Real)(rho * (m[10 + k] * iNS - s3[k]));
-    const Real r0 = (Real)rho, a1x = (Real)(rho * m1x), a1y = (Real)(rho * m1y), a1z = (Real)(rho * m1z);
-    const Real tx = a3[0] + a3[3] + a3[5], ty = a3[1] + a3[6] + a3[8], tz = a3[2] + a3[7] + a3[9];
-    const Real tr2 = a2[0] + a2[3] + a2[5];
-    constexpr double R = lat_r<LAT>();
-#pragma unroll
-    for (int q = 0; q < LAT::Q; ++q) {
-        const Real X = (Real)(R * E<LAT>(q, 0)), Y = (Real)(R * E<LAT>(q, 1)), Z = (Real)(R * E<LAT>(q, 2));
-        const Real h2 = a2[0] * X * X + a2[3] * Y * Y + a2[5] * Z * Z - tr2 +
-                        (Real)2 * (a2[1] * X * Y + a2[2] * X * Z + a2[4] * Y * Z);
-        Real sum = r0 + a1x * X + a1y * Y + a1z * Z + (Real)0.5 * h2;
-        if (LAT::ORDER >= 3) {
-            const Real cubic = a3[0] * X * X * X + (Real)3 * a3[1] * X * X * Y + (Real)3 * a3[2] * X * X * Z +
-                               (Real)3 * a3[3] * X * Y * Y + (Real)6 * a3[4] * X * Y * Z +
-                               (Real)3 * a3[5] * X * Z * Z + a3[6] * Y * Y * Y + (Real)3 * a3[7] * Y * Y * Z +
-                               (Real)3 * a3[8] * Y * Z * Z + a3[9] * Z * Z * Z;
-            sum += (cubic - (Real)3 * (tx * X + ty * Y + tz * Z)) * (Real)(1.0 / 6.0);
-        }
-        a.f[(int64_t)q * a.nnodes + node] = (Real)LatTab<LAT>::w(q) * sum;
-    }
-}
-
-// One warp per coupling cell: FP64 Grad coefficients and the particle count.
-template <typename Real, class LAT>
-__global__ void __launch_bounds__(64) k_l2d_coef(MapArgs<Real> a) {
-    const uint32_t t_step = a.ctrl[CTRL_STEP];
-    const int r = a.lb_ratio;
-    const double rr = a.r_lat;
+    __shared__ int se[3 * LAT::Q];
+    __shared__ float sw[LAT::Q];
+    load_lattice<LAT>(se, sw);
+    __syncthreads();
     const unsigned lane = lane_id();
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    constexpr int QL = (LAT::Q + 31) / 32;
-    for (int ci = gw; ci < a.n; ci += nw) {
+    const uint32_t S = a.ctrl[CTRL_NSAMPLES];
+    constexpr double R = lat_r<LAT>();
+    for (int t = gw; t < a.n; t += nw) {
+        const int32_t node = a.list[t];
+        if (node < 0 || (int64_t)node >= a.nnodes) {
+            if (lane == 0) atomicOr(&a.ctrl[CTRL_STATUS], HYB_ST_BAD_INPUT);
+            continue;
+        }
+        const int x = node % a.nx, y = node / a.nx;
+        const int64_t cell = (int64_t)(y / a.lb_ratio) * a.ncx + (x / a.lb_ratio);
+        const double* m = a.acc + cell * kMoments;
+        const double mk = lane < (unsigned)kMoments ? m[lane] : 0.0;
+        const double NS = __shfl_sync(kFull, mk, 0);
+        if (S == 0 || !(NS > 0.0)) {
+            if (lane == 0) atomicOr(&a.ctrl[CTRL_STATUS], HYB_ST_BAD_INPUT);
+            continue;
+        }
+        // FP64 coefficient solve, one coefficient per lane:
+        // lane 0: rho; 1-3: a1 = rho <v>; 4-9: a2 = rho(<vv> - I); 10-19: a3 = rho(<vvv> - sym(<v> I))
+        const double rho = (NS / (double)S) / (double)a.ppc;
+        const double iNS = 1.0 / NS;
+        const double m1x = __shfl_sync(kFull, mk, 1) * iNS;
+        const double m1y = __shfl_sync(kFull, mk, 2) * iNS;
+        const double m1z = __shfl_sync(kFull, mk, 3) * iNS;
+        double sub = 0.0;
+        switch (lane) {
+            case 4: case 7: case 9: sub = 1.0; break;        // xx yy zz
+            case 10: sub = 3 * m1x; break;                   // xxx
+            case 11: sub = m1y; break;                       // xxy
+            case 12: sub = m1z; break;                       // xxz
+            case 13: sub = m1x; break;                       // xyy
+            case 15: sub = m1x; break;                       // xzz
+            case 16: sub = 3 * m1y; break;                   // yyy
+            case 17: sub = m1z; break;                       // yyz
+            case 18: sub = m1y; break;                       // yzz
+            case 19: sub = 3 * m1z; break;                   // zzz
+            default: break;
+        }
+        const Real coef = lane == 0 ? (Real)rho : (Real)(rho * (mk * iNS - sub));
+        Real cf[kMoments];
+#pragma unroll
+        for (int k = 0; k < kMoments; ++k) cf[k] = __shfl_sync(kFull, coef, k);
+        const Real* a2 = cf + 4;
+        const Real* a3 = cf + 10;
+        const Real tx = a3[0] + a3[3] + a3[5], ty = a3[1] + a3[6] + a3[8], tz = a3[2] + a3[7] + a3[9];
+        const Real tr2 = a2[0] + a2[3] + a2[5];
+#pragma unroll
+        for (int h = 0; h < (LAT::Q + 31) / 32; ++h) {
+            const int q = (int)lane + 32 * h;
+            if (q < LAT::Q) {
+                const Real X = (Real)(R * se[3 * q]), Y = (Real)(R * se[3 * q + 1]), Z = (Real)(R * se[3 * q + 2]);
+                const Real h2 = a2[0] * X * X + a2[3] * Y * Y + a2[5] * Z * Z - tr2 +
+                                (Real)2 * (a2[1] * X * Y + a2[2] * X * Z + a2[4] * Y * Z);
+                Real sum = cf[0] + cf[1] * X + cf[2] * Y + cf[3] * Z + (Real)0.5 * h2;
+                if (LAT::ORDER >= 3) {
+                    const Real cubic = a3[0] * X * X * X + (Real)3 * a3[1] * X * X * Y +
+                                       (Real)3 * a3[2] * X * X * Z + (Real)3 * a3[3] * X * Y * Y +
+                                       (Real)6 * a3[4] * X * Y * Z + (Real)3 * a3[5] * X * Z * Z +
+                                       a3[6] * Y * Y * Y + (Real)3 * a3[7] * Y * Y * Z +
+                                       (Real)3 * a3[8] * Y * Z * Z + a3[9] * Z * Z * Z;
+                    sum += (cubic - (Real)3 * (tx * X + ty * Y + tz * Z)) * (Real)(1.0 / 6.0);
+                }
+                a.f[(int64_t)q * a.nnodes + node] = (Real)sw[q] * sum;
+            }
+        }
+    }
+}
+
+// LB2DSMC coefficients: one block of 64 threads per coupling cell, FP64. Every sum runs
+// over the populations in lattice order in one thread (mean populations of the cell's
+// nodes, rho, rho u, and each of the 16 comoving moments), so the results are those of the
+// same ordered sums; then M, C = 1 + 30 M and the new count floor(rho ppc + U).
+template <typename Real, class LAT>
+__global__ void __launch_bounds__(64) k_l2d_coef(MapArgs<Real> a) {
+    __shared__ double fb[LAT::Q];
+    __shared__ double s_rj[4];
+    __shared__ double s_m[16];
+    const uint32_t t_step = a.ctrl[CTRL_STEP];
+    const int r = a.lb_ratio;
+    const double rr = a.r_lat;
+    const int tid = threadIdx.x;
+    for (int ci = blockIdx.x; ci < a.n; ci += gridDim.x) {
         const int32_t cell = a.list[ci];
         if (cell < 0 || cell >= a.ncx * a.ncy) {
-            if (lane == 0) {
+            if (tid == 0) {
                 atomicOr(&a.ctrl[CTRL_STATUS], HYB_ST_BAD_INPUT);
                 a.ctrl[CTRL_L2D_BAD] = 1;
             }
             continue;
         }
         const int ix = cell % a.ncx, iy = cell / a.ncx;
-        double fb[QL];
-        double rho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
-#pragma unroll
-        for (int h = 0; h < QL; ++h) {
-            const int q = lane + 32 * h;
+        if (tid < LAT::Q) {
             double s = 0.0;
-            if (q < LAT::Q) {
-                for (int dy = 0; dy < r; ++dy)
-                    for (int dx = 0; dx < r; ++dx)
-                        s += (double)a.f[(int64_t)q * a.nnodes + (int64_t)(iy * r + dy) * a.nx + (ix * r + dx)];
-                s = s / (double)(r * r);
-                rho += s;
-                jx += s * (rr * LatTab<LAT>::e(q, 0));
-                jy += s * (rr * LatTab<LAT>::e(q, 1));
-                jz += s * (rr * LatTab<LAT>::e(q, 2));
-            }
-            fb[h] = s;
+            for (int dy = 0; dy < r; ++dy)
+                for (int dx = 0; dx < r; ++dx)
+                    s += (double)a.f[(int64_t)tid * a.nnodes + (int64_t)(iy * r + dy) * a.nx + (ix * r + dx)];
+            fb[tid] = s / (double)(r * r);
         }
-        rho = warp_sum(rho);
-        const double irho = 1.0 / rho;
-        const double ux = warp_sum(jx) * irho, uy = warp_sum(jy) * irho, uz = warp_sum(jz) * irho;
-        double m2[6] = {0, 0, 0, 0, 0, 0}, m3[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-#pragma unroll
-        for (int h = 0; h < QL; ++h) {
-            const int q = lane + 32 * h;
-            if (q < LAT::Q) {
-                const double cx = rr * LatTab<LAT>::e(q, 0) - ux;
-                const double cy = rr * LatTab<LAT>::e(q, 1) - uy;
-                const double cz = rr * LatTab<LAT>::e(q, 2) - uz;
-                const double f = fb[h];
-                m2[0] += f * cx * cx * irho;
-                m2[1] += f * cx * cy * irho;
-                m2[2] += f * cx * cz * irho;
-                m2[3] += f * cy * cy * irho;
-                m2[4] += f * cy * cz * irho;
-                m2[5] += f * cz * cz * irho;
-                if (LAT::ORDER >= 3) {
-                    m3[0] += f * cx * cx * cx * irho;
-                    m3[1] += f * cx * cx * cy * irho;
-                    m3[2] += f * cx * cx * cz * irho;
-                    m3[3] += f * cx * cy * cy * irho;
-                    m3[4] += f * cx * cy * cz * irho;
-                    m3[5] += f * cx * cz * cz * irho;
-                    m3[6] += f * cy * cy * cy * irho;
-                    m3[7] += f * cy * cy * cz * irho;
-                    m3[8] += f * cy * cz * cz * irho;
-                    m3[9] += f * cz * cz * cz * irho;
+        __syncthreads();
+        if (tid < 4) {  // rho (tid 0) and rho u (tid 1-3), summed in lattice order
+            double acc = 0.0;
+            for (int q = 0; q < LAT::Q; ++q)
+                acc += tid == 0 ? fb[q] : fb[q] * (rr * LatTab<LAT>::e(q, tid - 1));
+            s_rj[tid] = acc;
+        }
+        __syncthreads();
+        const double rho = s_rj[0];
+        const double ux = s_rj[1] / rho, uy = s_rj[2] / rho, uz = s_rj[3] / rho;
+        constexpr int NM = LAT::ORDER >= 3 ? 16 : 6;
+        if (tid < NM) {
+            // packed index -> tensor indices (xx xy xz yy yz zz, xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz)
+            const int i0[16] = {0, 0, 0, 1, 1, 2, 0, 0, 0, 0, 0, 0, 1, 1, 1, 2};
+            const int i1[16] = {0, 1, 2, 1, 2, 2, 0, 0, 0, 1, 1, 2, 1, 1, 2, 2};
+            const int i2[16] = {0, 0, 0, 0, 0, 0, 0, 1, 2, 1, 2, 2, 1, 2, 2, 2};
+            const double u3[3] = {ux, uy, uz};
+            const int p = tid, A = i0[p], Bi = i1[p], Ci = i2[p];
+            double acc = 0.0;
+            for (int q = 0; q < LAT::Q; ++q) {
+                const double ca = rr * LatTab<LAT>::e(q, A) - u3[A];
+                const double cb = rr * LatTab<LAT>::e(q, Bi) - u3[Bi];
+                if (p < 6) {
+                    acc += fb[q] * ca * cb;
+                } else {
+                    const double cc = rr * LatTab<LAT>::e(q, Ci) - u3[Ci];
+                    acc += fb[q] * ca * cb * cc;
                 }
             }
+            double v = acc / rho;
+            if (p == 0 || p == 3 || p == 5) v -= 1.0;
+            s_m[p] = v;
         }
-#pragma unroll
-        for (int k = 0; k < 6; ++k) m2[k] = warp_sum(m2[k]);
-        if (LAT::ORDER >= 3) {
-#pragma unroll
-            for (int k = 0; k < 10; ++k) m3[k] = warp_sum(m3[k]);
-        }
-        if (lane == 0) {
+        __syncthreads();
+        if (tid == 0) {
             GradRec g;
             g.rho = rho;
             g.u[0] = ux;
             g.u[1] = uy;
             g.u[2] = uz;
-            for (int k = 0; k < 6; ++k) g.a2[k] = m2[k];
-            g.a2[0] -= 1.0;
-            g.a2[3] -= 1.0;
-            g.a2[5] -= 1.0;
-            for (int k = 0; k < 10; ++k) g.a3[k] = m3[k];
             double M = 0.0;
-            for (int k = 0; k < 6; ++k) M = fmax(M, fabs(g.a2[k]));
-            for (int k = 0; k < 10; ++k) M = fmax(M, fabs(g.a3[k]));
+            for (int k = 0; k < 6; ++k) {
+                g.a2[k] = s_m[k];
+                M = fmax(M, fabs(s_m[k]));
+            }
+            for (int k = 0; k < 10; ++k) {
+                g.a3[k] = NM > 6 ? s_m[6 + k] : 0.0;
+                M = fmax(M, fabs(g.a3[k]));
+            }
             g.C = 1.0 + 30.0 * M;
             const double u = u01d(draw(a.seed, (uint32_t)cell, t_step, TAG_L2D_ROUND, 0, 0).x);
             const double ne = floor(rho * (double)a.ppc + u);
@@ -190,6 +215,7 @@ __global__ void __launch_bounds__(64) k_l2d_coef(MapArgs<Real> a) {
             g.pad = 0;
             a.grad[ci] = g;
         }
+        __syncthreads();
     }
 }
 
@@ -217,22 +243,25 @@ __device__ __forceinline__ Real grad_G(const Real* a2, const Real* a3, Real X, R
     return G;
 }
 
-// One warp per coupling cell: the cell's trial stream is evaluated 32 trials at a time; the
-// k-th accepted trial becomes the k-th particle of the cell's bin, replacing the old ones.
-// Nothing is written if a listed cell index was invalid (the coefficient kernel flagged it).
+constexpr int kSampleWarps = 4;
+
+// One block per coupling cell: the cell's trial stream is evaluated 128 trials at a time;
+// the k-th accepted trial becomes the k-th particle of the cell's bin, replacing the old
+// ones. Nothing is written if a listed cell index was invalid (the coefficient kernel
+// flagged it).
 template <typename Real, class LAT>
-__global__ void __launch_bounds__(64) k_l2d_sample(MapArgs<Real> a) {
+__global__ void __launch_bounds__(kSampleWarps * 32) k_l2d_sample(MapArgs<Real> a) {
+    __shared__ unsigned s_am[kSampleWarps], s_em[kSampleWarps], s_vm[kSampleWarps];
     if (a.ctrl[CTRL_L2D_BAD]) return;
     const uint32_t t_step = a.ctrl[CTRL_STEP];
     const unsigned lane = lane_id();
     const unsigned lt = (1u << lane) - 1u;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int w = threadIdx.x >> 5;
     const uint32_t bin = (uint32_t)a.bin;
     unsigned long long deleted = 0, created = 0, attempts = 0, envelope = 0;
     uint32_t flags = 0;
     int32_t dlive = 0;
-    for (int ci = gw; ci < a.n; ci += nw) {
+    for (int ci = blockIdx.x; ci < a.n; ci += gridDim.x) {
         const uint32_t cell = (uint32_t)a.list[ci];
         const GradRec& g = a.grad[ci];
         const uint32_t nnew = g.nnew;
@@ -253,7 +282,7 @@ __global__ void __launch_bounds__(64) k_l2d_sample(MapArgs<Real> a) {
         const uint32_t cap = cap64 < 0xFFFFFFull ? (uint32_t)cap64 : 0xFFFFFFu;
         uint32_t produced = 0, j0 = 0;
         while (produced < nnew && j0 < cap) {
-            const uint32_t j = j0 + lane;
+            const uint32_t j = j0 + threadIdx.x;
             const bool valid = j < cap;
             bool acc = false, env = false;
             Real X = 0, Y = 0, Z = 0;
@@ -269,17 +298,24 @@ __global__ void __launch_bounds__(64) k_l2d_sample(MapArgs<Real> a) {
                 env = G > C;
                 acc = C * R <= G;
             }
-            const unsigned amask = __ballot_sync(kFull, acc);
-            const unsigned emask = __ballot_sync(kFull, env);
-            const unsigned vmask = __ballot_sync(kFull, valid);
-            const uint32_t need = nnew - produced;
-            const uint32_t rank = __popc(amask & lt);
-            uint32_t used_mask = vmask;  // trials consumed this round
-            if ((uint32_t)__popc(amask) >= need) {
-                const unsigned lastm = __ballot_sync(kFull, acc && rank == need - 1u);
-                const int last = __ffs(lastm) - 1;
-                used_mask = last == 31 ? 0xFFFFFFFFu : ((2u << last) - 1u);
+            const unsigned am = __ballot_sync(kFull, acc);
+            const unsigned em = __ballot_sync(kFull, env);
+            const unsigned vm = __ballot_sync(kFull, valid);
+            if (lane == 0) {
+                s_am[w] = am;
+                s_em[w] = em;
+                s_vm[w] = vm;
             }
+            __syncthreads();
+            uint32_t before = 0, total = 0;
+#pragma unroll
+            for (int v = 0; v < kSampleWarps; ++v) {
+                const uint32_t cv = (uint32_t)__popc(s_am[v]);
+                if (v < w) before += cv;
+                total += cv;
+            }
+            const uint32_t need = nnew - produced;
+            const uint32_t rank = before + (uint32_t)__popc(am & lt);
             if (acc && rank < need) {
                 const int64_t slot = out0 + produced + rank;
                 a.x[slot] = fx + (Real)u01f(r2.y);
@@ -288,15 +324,44 @@ __global__ void __launch_bounds__(64) k_l2d_sample(MapArgs<Real> a) {
                 a.vy[slot] = Y + uy;
                 a.vz[slot] = Z + uz;
             }
-            if (lane == 0) {
-                attempts += (unsigned long long)__popc(used_mask);
-                envelope += (unsigned long long)__popc(emask & used_mask);
+            if (threadIdx.x == 0) {
+                // trials consumed this round: up to the need-th accepted one, or all valid ones
+                uint32_t used = 0, envc = 0;
+                if (total >= need) {
+                    uint32_t left = need;
+                    for (int v = 0; v < kSampleWarps; ++v) {
+                        const uint32_t cv = (uint32_t)__popc(s_am[v]);
+                        if (left > cv) {
+                            left -= cv;
+                            used += 32;
+                            envc += (uint32_t)__popc(s_em[v] & s_vm[v]);
+                            continue;
+                        }
+                        int bit = 0;
+                        for (unsigned mm = s_am[v];; mm &= mm - 1u) {
+                            bit = __ffs(mm) - 1;
+                            if (--left == 0) break;
+                        }
+                        const unsigned upto = bit == 31 ? 0xFFFFFFFFu : ((2u << bit) - 1u);
+                        used += (uint32_t)bit + 1u;
+                        envc += (uint32_t)__popc(s_em[v] & upto);
+                        break;
+                    }
+                } else {
+                    for (int v = 0; v < kSampleWarps; ++v) {
+                        used += (uint32_t)__popc(s_vm[v]);
+                        envc += (uint32_t)__popc(s_em[v] & s_vm[v]);
+                    }
+                }
+                attempts += used;
+                envelope += envc;
             }
-            produced += min((uint32_t)__popc(amask), need);
-            j0 += 32;
+            produced += min(total, need);
+            j0 += kSampleWarps * 32;
+            __syncthreads();
         }
         if (produced < nnew) flags |= HYB_ST_SAMPLING_CAP;
-        if (lane == 0) {
+        if (threadIdx.x == 0) {
             const uint32_t old = a.count[cell];
             deleted += old;
             created += produced;
@@ -305,14 +370,14 @@ __global__ void __launch_bounds__(64) k_l2d_sample(MapArgs<Real> a) {
         }
     }
     flags = __reduce_or_sync(kFull, flags);
-    if (lane == 0) {
+    if (threadIdx.x == 0) {
         if (deleted) atomicAdd(&a.counters[HYB_C_DELETED], deleted);
         if (created) atomicAdd(&a.counters[HYB_C_CREATED], created);
         if (attempts) atomicAdd(&a.counters[HYB_C_L2D_ATTEMPTS], attempts);
         if (envelope) atomicAdd(&a.counters[HYB_C_ENVELOPE], envelope);
         if (dlive) atomicAdd(&a.ctrl[CTRL_NTOT], (uint32_t)dlive);
-        if (flags) atomicOr(&a.ctrl[CTRL_STATUS], flags);
     }
+    if (lane == 0 && flags) atomicOr(&a.ctrl[CTRL_STATUS], flags);
 }
 
 template <typename Real>
@@ -354,7 +419,7 @@ template <typename Real, class LAT>
 cudaError_t d2l_impl(Ctx& c, const int32_t* nodes, int32_t n) {
     MapArgs<Real> a = map_args<Real>(c, nodes, n);
     prof_begin(c, K_D2L);
-    k_d2l<Real, LAT><<<(n + 127) / 128, 128, 0, c.stream>>>(a);
+    k_d2l<Real, LAT><<<blocks_for(c, (int64_t)n * 32, 128, 16), 128, 0, c.stream>>>(a);
     prof_end(c, K_D2L);
     return cudaGetLastError();
 }
@@ -365,10 +430,11 @@ cudaError_t l2d_impl(Ctx& c, const int32_t* cells, int32_t n) {
     cudaError_t e = cudaMemsetAsync(c.st.ctrl + CTRL_L2D_BAD, 0, 4, c.stream);
     if (e != cudaSuccess) return e;
     prof_begin(c, K_L2D_COEF);
-    k_l2d_coef<Real, LAT><<<blocks_for(c, (int64_t)n * 32, 64, 32), 64, 0, c.stream>>>(a);
+    k_l2d_coef<Real, LAT><<<blocks_for(c, (int64_t)n * 64, 64, 32), 64, 0, c.stream>>>(a);
     prof_end(c, K_L2D_COEF);
     prof_begin(c, K_L2D_SAMPLE);
-    k_l2d_sample<Real, LAT><<<blocks_for(c, (int64_t)n * 32, 64, 32), 64, 0, c.stream>>>(a);
+    k_l2d_sample<Real, LAT><<<blocks_for(c, (int64_t)n * 32 * kSampleWarps, 32 * kSampleWarps, 16),
+                              32 * kSampleWarps, 0, c.stream>>>(a);
     prof_end(c, K_L2D_SAMPLE);
     return cudaGetLastError();
 }
@@ -396,10 +462,11 @@ cudaError_t l2d_noalloc_impl(Ctx& c, const int32_t* cells, int32_t n, GradRec* r
     cudaError_t e = cudaMemsetAsync(c.st.ctrl + CTRL_L2D_BAD, 0, 4, c.stream);
     if (e != cudaSuccess) return e;
     prof_begin(c, K_L2D_COEF);
-    k_l2d_coef<Real, LAT><<<blocks_for(c, (int64_t)n * 32, 64, 32), 64, 0, c.stream>>>(a);
+    k_l2d_coef<Real, LAT><<<blocks_for(c, (int64_t)n * 64, 64, 32), 64, 0, c.stream>>>(a);
     prof_end(c, K_L2D_COEF);
     prof_begin(c, K_L2D_SAMPLE);
-    k_l2d_sample<Real, LAT><<<blocks_for(c, (int64_t)n * 32, 64, 32), 64, 0, c.stream>>>(a);
+    k_l2d_sample<Real, LAT><<<blocks_for(c, (int64_t)n * 32 * kSampleWarps, 32 * kSampleWarps, 16),
+                              32 * kSampleWarps, 0, c.stream>>>(a);
     prof_end(c, K_L2D_SAMPLE);
     return cudaGetLastError();
 }
