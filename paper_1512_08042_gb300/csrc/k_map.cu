@@ -40,12 +40,12 @@ __host__ __device__ constexpr int E(int a, int i) {
 
 // Lattice table in shared memory, for lanes that each handle a different population.
 template <class LAT>
-__device__ __forceinline__ void load_lattice(int* se, float* sw) {
+__device__ __forceinline__ void load_lattice(int* se, double* sw) {
     for (int q = threadIdx.x; q < LAT::Q; q += blockDim.x) {
         se[3 * q] = LatTab<LAT>::e(q, 0);
         se[3 * q + 1] = LatTab<LAT>::e(q, 1);
         se[3 * q + 2] = LatTab<LAT>::e(q, 2);
-        sw[q] = (float)LatTab<LAT>::w(q);
+        sw[q] = LatTab<LAT>::w(q);
     }
 }
 
@@ -55,7 +55,7 @@ __device__ __forceinline__ void load_lattice(int* se, float* sw) {
 template <typename Real, class LAT>
 __global__ void __launch_bounds__(128) k_d2l(MapArgs<Real> a) {
     __shared__ int se[3 * LAT::Q];
-    __shared__ float sw[LAT::Q];
+    __shared__ double sw[LAT::Q];
     load_lattice<LAT>(se, sw);
     __syncthreads();
     const unsigned lane = lane_id();
@@ -129,19 +129,30 @@ __global__ void __launch_bounds__(128) k_d2l(MapArgs<Real> a) {
     }
 }
 
-// LB2DSMC coefficients: one block of 64 threads per coupling cell, FP64. Every sum runs
-// over the populations in lattice order in one thread (mean populations of the cell's
-// nodes, rho, rho u, and each of the 16 comoving moments), so the results are those of the
-// same ordered sums; then M, C = 1 + 30 M and the new count floor(rho ppc + U).
+// LB2DSMC coefficients: one block of 64 threads per coupling cell, FP64. Each sum runs over
+// the populations in lattice order: the terms (mean populations of the cell's nodes, their
+// products with the speeds and with the comoving speed components) are formed in parallel,
+// one population per thread, and each sum is then accumulated in order by one thread. Then
+// M, C = 1 + 30 M and the new count floor(rho ppc + U).
 template <typename Real, class LAT>
 __global__ void __launch_bounds__(64) k_l2d_coef(MapArgs<Real> a) {
-    __shared__ double fb[LAT::Q];
+    constexpr int Q = LAT::Q;
+    constexpr int NM = LAT::ORDER >= 3 ? 16 : 6;
+    __shared__ double fb[Q];
+    __shared__ double pj[3][Q];
+    __shared__ double prod[NM][Q];
     __shared__ double s_rj[4];
     __shared__ double s_m[16];
     const uint32_t t_step = a.ctrl[CTRL_STEP];
     const int r = a.lb_ratio;
     const double rr = a.r_lat;
     const int tid = threadIdx.x;
+    int e0 = 0, e1 = 0, e2 = 0;
+    if (tid < Q) {
+        e0 = LatTab<LAT>::e(tid, 0);
+        e1 = LatTab<LAT>::e(tid, 1);
+        e2 = LatTab<LAT>::e(tid, 2);
+    }
     for (int ci = blockIdx.x; ci < a.n; ci += gridDim.x) {
         const int32_t cell = a.list[ci];
         if (cell < 0 || cell >= a.ncx * a.ncy) {
@@ -152,45 +163,57 @@ __global__ void __launch_bounds__(64) k_l2d_coef(MapArgs<Real> a) {
             continue;
         }
         const int ix = cell % a.ncx, iy = cell / a.ncx;
-        if (tid < LAT::Q) {
-            double s = 0.0;
+        if (tid < Q) {
+            double sacc = 0.0;
             for (int dy = 0; dy < r; ++dy)
                 for (int dx = 0; dx < r; ++dx)
-                    s += (double)a.f[(int64_t)tid * a.nnodes + (int64_t)(iy * r + dy) * a.nx + (ix * r + dx)];
-            fb[tid] = s / (double)(r * r);
+                    sacc += (double)a.f[(int64_t)tid * a.nnodes + (int64_t)(iy * r + dy) * a.nx + (ix * r + dx)];
+            const double fq = sacc / (double)(r * r);
+            fb[tid] = fq;
+            pj[0][tid] = fq * (rr * e0);
+            pj[1][tid] = fq * (rr * e1);
+            pj[2][tid] = fq * (rr * e2);
         }
         __syncthreads();
-        if (tid < 4) {  // rho (tid 0) and rho u (tid 1-3), summed in lattice order
+        if (tid < 4) {  // rho (thread 0) and rho u (threads 1-3), summed in lattice order
+            const double* src = tid == 0 ? fb : pj[tid - 1];
             double acc = 0.0;
-            for (int q = 0; q < LAT::Q; ++q)
-                acc += tid == 0 ? fb[q] : fb[q] * (rr * LatTab<LAT>::e(q, tid - 1));
+            for (int q = 0; q < Q; ++q) acc += src[q];
             s_rj[tid] = acc;
         }
         __syncthreads();
         const double rho = s_rj[0];
         const double ux = s_rj[1] / rho, uy = s_rj[2] / rho, uz = s_rj[3] / rho;
-        constexpr int NM = LAT::ORDER >= 3 ? 16 : 6;
-        if (tid < NM) {
-            // packed index -> tensor indices (xx xy xz yy yz zz, xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz)
-            const int i0[16] = {0, 0, 0, 1, 1, 2, 0, 0, 0, 0, 0, 0, 1, 1, 1, 2};
-            const int i1[16] = {0, 1, 2, 1, 2, 2, 0, 0, 0, 1, 1, 2, 1, 1, 2, 2};
-            const int i2[16] = {0, 0, 0, 0, 0, 0, 0, 1, 2, 1, 2, 2, 1, 2, 2, 2};
-            const double u3[3] = {ux, uy, uz};
-            const int p = tid, A = i0[p], Bi = i1[p], Ci = i2[p];
-            double acc = 0.0;
-            for (int q = 0; q < LAT::Q; ++q) {
-                const double ca = rr * LatTab<LAT>::e(q, A) - u3[A];
-                const double cb = rr * LatTab<LAT>::e(q, Bi) - u3[Bi];
-                if (p < 6) {
-                    acc += fb[q] * ca * cb;
-                } else {
-                    const double cc = rr * LatTab<LAT>::e(q, Ci) - u3[Ci];
-                    acc += fb[q] * ca * cb * cc;
-                }
+        if (tid < Q) {
+            const double fq = fb[tid];
+            const double c[3] = {rr * e0 - ux, rr * e1 - uy, rr * e2 - uz};
+            // packed moments xx xy xz yy yz zz, xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz
+            prod[0][tid] = fq * c[0] * c[0];
+            prod[1][tid] = fq * c[0] * c[1];
+            prod[2][tid] = fq * c[0] * c[2];
+            prod[3][tid] = fq * c[1] * c[1];
+            prod[4][tid] = fq * c[1] * c[2];
+            prod[5][tid] = fq * c[2] * c[2];
+            if constexpr (NM > 6) {
+                prod[6][tid] = fq * c[0] * c[0] * c[0];
+                prod[7][tid] = fq * c[0] * c[0] * c[1];
+                prod[8][tid] = fq * c[0] * c[0] * c[2];
+                prod[9][tid] = fq * c[0] * c[1] * c[1];
+                prod[10][tid] = fq * c[0] * c[1] * c[2];
+                prod[11][tid] = fq * c[0] * c[2] * c[2];
+                prod[12][tid] = fq * c[1] * c[1] * c[1];
+                prod[13][tid] = fq * c[1] * c[1] * c[2];
+                prod[14][tid] = fq * c[1] * c[2] * c[2];
+                prod[15][tid] = fq * c[2] * c[2] * c[2];
             }
+        }
+        __syncthreads();
+        if (tid < NM) {
+            double acc = 0.0;
+            for (int q = 0; q < Q; ++q) acc += prod[tid][q];
             double v = acc / rho;
-            if (p == 0 || p == 3 || p == 5) v -= 1.0;
-            s_m[p] = v;
+            if (tid == 0 || tid == 3 || tid == 5) v -= 1.0;
+            s_m[tid] = v;
         }
         __syncthreads();
         if (tid == 0) {
