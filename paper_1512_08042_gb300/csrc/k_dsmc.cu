@@ -11,11 +11,12 @@
 //              back in place and its slot is appended to the tag list of its new cell's bin
 //              by a warp-aggregated atomic. The last block to finish advances the step
 //              counters.
-//   k_collide  one warp per cell: the cell's tags are put in stable order (ascending origin
-//              slot = origin cell, then rank in it: a bitonic sort in registers), the
-//              particles are gathered from the source half into the bin of the other half,
-//              NTC collisions (Eq. collisionnumber) run in shared memory, and the sums 1, v,
-//              vv, vvv are added to the FP64 cumulative sums of the cell (Sec. 2.1, Fig. 1).
+//   k_collide  one group of 8 lanes per cell (4 cells per warp): the cell's tags are put in
+//              stable order (ascending origin slot = origin cell, then rank in it: a bitonic
+//              sort in registers), the particles are gathered from the source half into the
+//              bin of the other half, NTC collisions (Eq. collisionnumber) run in shared
+//              memory, and the sums 1, v, vv, vvv are added to the FP64 cumulative sums of the
+//              cell (Sec. 2.1, Fig. 1).
 // This file is compiled without FMA contraction so that positions, cell keys, pair choices
 // and post-collision velocities are the IEEE float (or double) results of the written
 // expressions.
@@ -217,34 +218,46 @@ __global__ void __launch_bounds__(256) k_move(DsmcArgs<Real> a) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Ascending bitonic sort of 32 R keys held R per lane (key r of a lane at position
-// lane + 32 r). All loops have constant trip counts and unroll, so the keys stay in registers.
-template <int R>
-__device__ __forceinline__ void bitonic_sort(uint32_t (&v)[R]) {
-    constexpr int N = 32 * R;
-    const int lane = (int)lane_id();
+// ---------------------------------------------------------------------------------------
+// Collide: a group of G lanes per cell, 32 / G cells per warp. Every instruction of the
+// serial NTC chain then advances 32 / G cells at once. All loops that contain shuffles have
+// warp-uniform trip counts (groups whose cell has less work are masked), so every shuffle is
+// executed by the full warp.
+constexpr int kGroup = 8;
+
+template <typename Real>
+struct CollideCfg {
+    static constexpr int WARPS = sizeof(Real) == 4 ? 4 : 2;
+};
+
+// Ascending bitonic sort of G R keys held by the G lanes of a group, R per lane (key r of
+// group lane l at position l + G r). Constant trip counts: the keys stay in registers.
+template <int G, int R>
+__device__ __forceinline__ void bitonic_group(uint32_t (&v)[R]) {
+    constexpr int N = G * R;
+    const int gl = (int)(lane_id() % G);
 #pragma unroll
     for (int k = 2; k <= N; k <<= 1) {
 #pragma unroll
         for (int j = k >> 1; j > 0; j >>= 1) {
-            if (j >= 32) {
-                const int jr = j >> 5;
+            if (j >= G) {
+                const int jr = j / G;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const int o = r ^ jr;
                     if (r < o) {
-                        const bool asc = ((lane + 32 * r) & k) == 0;
+                        const bool asc = ((gl + G * r) & k) == 0;
                         const uint32_t lo = min(v[r], v[o]), hi = max(v[r], v[o]);
                         v[r] = asc ? lo : hi;
                         v[o] = asc ? hi : lo;
                     }
                 }
             } else {
-                const bool lower = (lane & j) == 0;
+                const bool lower = (gl & j) == 0;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const uint32_t o = __shfl_xor_sync(kFull, v[r], j);
-                    const bool asc = ((lane + 32 * r) & k) == 0;
+                    const bool asc = ((gl + G * r) & k) == 0;
                     v[r] = (lower == asc) ? min(v[r], o) : max(v[r], o);
                 }
             }
@@ -252,8 +265,6 @@ __device__ __forceinline__ void bitonic_sort(uint32_t (&v)[R]) {
     }
 }
 
-// Gather one particle from its source slot into position k of the destination bin
-// (positions to global memory, velocities to the warp's shared arrays).
 template <typename Real>
 __device__ __forceinline__ void gather_one(const DsmcArgs<Real>& a, int64_t base, uint32_t k,
                                            uint32_t src, Real* vx, Real* vy, Real* vz) {
@@ -264,97 +275,80 @@ __device__ __forceinline__ void gather_one(const DsmcArgs<Real>& a, int64_t base
     vz[k] = a.svz[src];
 }
 
-// Stable order for n <= 32 R: sort the tags in registers, then gather.
-template <typename Real, int R>
-__device__ __forceinline__ void order_small(const DsmcArgs<Real>& a, int64_t base, uint32_t n,
-                                            Real* vx, Real* vy, Real* vz) {
-    const unsigned lane = lane_id();
-    uint32_t v[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const uint32_t k = lane + 32u * r;
-        v[r] = k < n ? a.tag[base + k] : 0xFFFFFFFFu;
-    }
-    bitonic_sort<R>(v);
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const uint32_t k = lane + 32u * r;
-        if (k < n) gather_one(a, base, k, v[r], vx, vy, vz);
-    }
-}
-
-// Stable order for larger n: rank of each tag = number of smaller tags in the cell.
 template <typename Real>
-__device__ __forceinline__ void order_large(const DsmcArgs<Real>& a, int64_t base, uint32_t n,
-                                            uint32_t* st, Real* vx, Real* vy, Real* vz) {
-    const unsigned lane = lane_id();
-    for (uint32_t k = lane; k < n; k += 32) st[k] = a.tag[base + k];
-    __syncwarp();
-    for (uint32_t k = lane; k < n; k += 32) {
-        const uint32_t v = st[k];
-        uint32_t r = 0;
-        for (uint32_t m = 0; m < n; ++m) r += st[m] < v ? 1u : 0u;
-        gather_one(a, base, r, v, vx, vy, vz);
-    }
-}
-
-// Reduce 32 per-lane values v[0..31] over the warp so that lane L ends with the total of
-// v[L] (halving exchange: 16 + 8 + 4 + 2 + 1 shuffles).
-template <typename Real>
-__device__ __forceinline__ Real warp_transpose_sum(Real (&v)[32]) {
-    const unsigned lane = lane_id();
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-        const bool hi = (lane & o) != 0;
-#pragma unroll
-        for (int i = 0; i < o; ++i) {
-            const Real send = hi ? v[i] : v[i + o];
-            const Real keep = hi ? v[i + o] : v[i];
-            v[i] = keep + __shfl_xor_sync(kFull, send, o);
-        }
-    }
-    return v[0];
-}
-
-constexpr int kCollideWarps = 4;
-
-template <typename Real>
-__global__ void __launch_bounds__(kCollideWarps * 32) k_collide(DsmcArgs<Real> a) {
+__global__ void __launch_bounds__(CollideCfg<Real>::WARPS * 32) k_collide(DsmcArgs<Real> a) {
+    constexpr int G = kGroup;
+    constexpr int CPW = 32 / G;         // cells per warp
+    constexpr int SMALL = 64;           // cells up to this size are sorted in registers
+    constexpr int R = SMALL / G;
+    constexpr int WARPS = CollideCfg<Real>::WARPS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int w = threadIdx.x >> 5;
     const unsigned lane = lane_id();
+    const int grp = (int)lane / G, gl = (int)lane % G;
+    const int leader = grp * G;
     const uint32_t bin = (uint32_t)a.bin;
-    Real* sm = reinterpret_cast<Real*>(smem_raw) + (size_t)w * 3 * bin;
-    Real* vx = sm;
-    Real* vy = sm + bin;
-    Real* vz = sm + 2 * bin;
+    // per group: vx, vy, vz (Real) and tags (u32), bin entries each
+    Real* sv = reinterpret_cast<Real*>(smem_raw) + (size_t)(w * CPW + grp) * 3 * bin;
+    Real* vx = sv;
+    Real* vy = sv + bin;
+    Real* vz = sv + 2 * bin;
     uint32_t* st = reinterpret_cast<uint32_t*>(reinterpret_cast<Real*>(smem_raw) +
-                                                (size_t)kCollideWarps * 3 * bin) + (size_t)w * bin;
+                                                (size_t)WARPS * CPW * 3 * bin) +
+                   (size_t)(w * CPW + grp) * bin;
     const uint32_t s = a.ctrl[CTRL_STEP] - 1u;
     const bool do_sample = (s % (uint32_t)a.sample_every) == 0u;
     const Real coll_dt = (Real)a.coll_dt;
     unsigned long long ncand_tot = 0, ncoll_tot = 0;
     uint32_t flags = 0, nlive = 0;
 
-    for (int c = blockIdx.x * kCollideWarps + w; c < a.ncells; c += gridDim.x * kCollideWarps) {
-        uint32_t n = a.count_d[c];
+    for (int cb = (blockIdx.x * WARPS + w) * CPW; cb < a.ncells; cb += gridDim.x * WARPS * CPW) {
+        const int c = cb + grp;
+        const bool has = c < a.ncells;
+        uint32_t n = has ? a.count_d[c] : 0u;
         if (n > bin) n = bin;
         const int64_t base = (int64_t)c * bin;
-        // 1. stable order and gather
-        if (n <= 32) order_small<Real, 1>(a, base, n, vx, vy, vz);
-        else if (n <= 64) order_small<Real, 2>(a, base, n, vx, vy, vz);
-        else order_large<Real>(a, base, n, st, vx, vy, vz);
+        // 1. stable order (ascending origin slot) and gather
+        {
+            uint32_t v[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const uint32_t k = (uint32_t)(gl + G * r);
+                v[r] = (n <= (uint32_t)SMALL && k < n) ? a.tag[base + k] : 0xFFFFFFFFu;
+            }
+            bitonic_group<G, R>(v);
+            if (n > (uint32_t)SMALL)
+                for (uint32_t k = gl; k < n; k += G) st[k] = a.tag[base + k];
+            __syncwarp();
+            if (n <= (uint32_t)SMALL) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const uint32_t k = (uint32_t)(gl + G * r);
+                    if (k < n) gather_one(a, base, k, v[r], vx, vy, vz);
+                }
+            } else {
+                // rank of each tag = number of smaller tags in the cell
+                for (uint32_t k = gl; k < n; k += G) {
+                    const uint32_t t = st[k];
+                    uint32_t r = 0;
+                    for (uint32_t m = 0; m < n; ++m) r += st[m] < t ? 1u : 0u;
+                    gather_one(a, base, r, t, vx, vy, vz);
+                }
+            }
+        }
         __syncwarp();
-        // 2. NTC: N_cand = 1/2 N Nbar F_N (sigma c_r)_max dt / V_c + remainder
+        // 2. NTC: N_cand = 1/2 N Nbar F_N (sigma c_r)_max dt / V_c + remainder (group leader)
         uint32_t nsel = 0;
         Real cm = (Real)0;
-        if (lane == 0) {
+        if (has && gl == 0) {
             const uint32_t nb = a.nbar_sum[c] + n;
             a.nbar_sum[c] = nb;
             a.count_s[c] = 0;  // the source half's count is not needed after the move
             cm = a.crmax[c];
             nlive += n;
-            if (n >= 2) {
+            if (n > 32767u) {
+                flags |= HYB_ST_CELL_OVERFLOW;  // pair indices are packed in 15 and 16 bits
+            } else if (n >= 2) {
                 const Real nbar = (Real)nb / (Real)(s + 1u);
                 const Real ncand = (Real)0.5 * (Real)n * nbar * cm * coll_dt + a.rem[c];
                 const Real fl = floor(ncand);
@@ -367,69 +361,78 @@ __global__ void __launch_bounds__(kCollideWarps * 32) k_collide(DsmcArgs<Real> a
                 }
             }
         }
-        nsel = __shfl_sync(kFull, nsel, 0);
-        cm = __shfl_sync(kFull, cm, 0);
+        nsel = __shfl_sync(kFull, nsel, leader);
+        cm = __shfl_sync(kFull, cm, leader);
+        const uint32_t maxsel = __reduce_max_sync(kFull, nsel);
         uint32_t ncoll = 0;
-        for (uint32_t ch = 0; ch < nsel; ch += 32) {
-            // lanes draw 32 candidates in parallel; they are applied in order below
-            const uint32_t k = ch + lane;
+        for (uint32_t ch = 0; ch < maxsel; ch += G) {
+            // the group's lanes draw G candidates in parallel; they are applied in order below
+            const uint32_t k = ch + gl;
             uint32_t ij = 0;
-            Real R = (Real)0, nx = (Real)0, ny = (Real)0, nz = (Real)0;
+            Real R0 = (Real)0, nx = (Real)0, ny = (Real)0, nz = (Real)0;
             if (k < nsel) {
                 const uint4 r = draw(a.seed, (uint32_t)c, s, TAG_NTC_PAIR, k, 0);
                 const uint32_t ci = uindex(r.x, n);
                 uint32_t cj = uindex(r.y, n - 1u);
                 if (cj >= ci) cj += 1u;
-                R = (Real)u01f(r.z);
+                R0 = (Real)u01f(r.z);
                 const int ok = unit_vector(a.seed, (uint32_t)c, s, k, nx, ny, nz);
                 ij = ci | (cj << 15) | (ok ? 0u : 0x80000000u);
             }
-            const uint32_t cnt = min(32u, nsel - ch);
-            for (uint32_t m = 0; m < cnt; ++m) {
-                const uint32_t ijm = __shfl_sync(kFull, ij, m);
-                const uint32_t i = ijm & 0x7FFFu, j = (ijm >> 15) & 0xFFFFu;
-                const Real Rm = __shfl_sync(kFull, R, m);
-                const Real ax = vx[i], ay = vy[i], az = vz[i];
-                const Real bx = vx[j], by = vy[j], bz = vz[j];
-                const Real ddx = ax - bx, ddy = ay - by, ddz = az - bz;
-                const Real cr = sqrt(ddx * ddx + ddy * ddy + ddz * ddz);
-                if (cr > cm) cm = cr;
-                if (cr > Rm * cm) {  // the same on every lane
-                    const Real nxm = __shfl_sync(kFull, nx, m);
-                    const Real nym = __shfl_sync(kFull, ny, m);
-                    const Real nzm = __shfl_sync(kFull, nz, m);
-                    if (ijm & 0x80000000u) {
-                        flags |= HYB_ST_SCATTER_CAP;
-                    } else {
-                        __syncwarp();
-                        if (lane == 0) {
-                            const Real cx = (ax + bx) * (Real)0.5;
-                            const Real cy = (ay + by) * (Real)0.5;
-                            const Real cz = (az + bz) * (Real)0.5;
-                            const Real h = cr * (Real)0.5;
-                            vx[i] = cx + h * nxm;
-                            vy[i] = cy + h * nym;
-                            vz[i] = cz + h * nzm;
-                            vx[j] = cx - h * nxm;
-                            vy[j] = cy - h * nym;
-                            vz[j] = cz - h * nzm;
+#pragma unroll 1
+            for (int m = 0; m < G; ++m) {
+                const int src = leader + m;
+                const uint32_t ijm = __shfl_sync(kFull, ij, src);
+                const Real Rm = __shfl_sync(kFull, R0, src);
+                const Real nxm = __shfl_sync(kFull, nx, src);
+                const Real nym = __shfl_sync(kFull, ny, src);
+                const Real nzm = __shfl_sync(kFull, nz, src);
+                bool acc_pair = false;
+                Real cx = 0, cy = 0, cz = 0, h = 0;
+                uint32_t i = 0, j = 0;
+                if (ch + (uint32_t)m < nsel) {
+                    i = ijm & 0x7FFFu;
+                    j = (ijm >> 15) & 0xFFFFu;
+                    const Real ax = vx[i], ay = vy[i], az = vz[i];
+                    const Real bx = vx[j], by = vy[j], bz = vz[j];
+                    const Real ddx = ax - bx, ddy = ay - by, ddz = az - bz;
+                    const Real cr = sqrt(ddx * ddx + ddy * ddy + ddz * ddz);
+                    if (cr > cm) cm = cr;
+                    if (cr > Rm * cm) {
+                        if (ijm & 0x80000000u) {
+                            flags |= HYB_ST_SCATTER_CAP;
+                        } else {
+                            acc_pair = true;
+                            cx = (ax + bx) * (Real)0.5;
+                            cy = (ay + by) * (Real)0.5;
+                            cz = (az + bz) * (Real)0.5;
+                            h = cr * (Real)0.5;
                         }
-                        __syncwarp();
-                        ncoll += 1;
                     }
                 }
+                __syncwarp();
+                if (acc_pair && gl == 0) {
+                    vx[i] = cx + h * nxm;
+                    vy[i] = cy + h * nym;
+                    vz[i] = cz + h * nzm;
+                    vx[j] = cx - h * nxm;
+                    vy[j] = cy - h * nym;
+                    vz[j] = cz - h * nzm;
+                }
+                if (acc_pair) ncoll += 1;
+                __syncwarp();
             }
         }
-        if (lane == 0) {
+        if (has && gl == 0) {
             a.crmax[c] = cm;
             ncand_tot += nsel;
             ncoll_tot += ncoll;
         }
-        // 3. write-out and moment sums
-        Real mo[32];
+        // 3. write-out and moment sums (group lanes over the cell's particles)
+        Real mo[kMoments];
 #pragma unroll
-        for (int q = 0; q < 32; ++q) mo[q] = (Real)0;
-        for (uint32_t k = lane; k < n; k += 32) {
+        for (int q = 0; q < kMoments; ++q) mo[q] = (Real)0;
+        for (uint32_t k = gl; k < n; k += G) {
             const Real ux = vx[k], uy = vy[k], uz = vz[k];
             a.dvx[base + k] = ux;
             a.dvy[base + k] = uy;
@@ -446,12 +449,23 @@ __global__ void __launch_bounds__(kCollideWarps * 32) k_collide(DsmcArgs<Real> a
             }
         }
         if (do_sample) {
-            const Real mine = warp_transpose_sum<Real>(mo);
-            if (lane < (unsigned)kMoments) a.acc[(size_t)c * kMoments + lane] += (double)mine;
+#pragma unroll
+            for (int q = 0; q < kMoments; ++q) {
+#pragma unroll
+                for (int off = G / 2; off > 0; off >>= 1) mo[q] += __shfl_xor_sync(kFull, mo[q], off);
+            }
+            if (has) {
+#pragma unroll
+                for (int q = 0; q < kMoments; ++q)
+                    if (q % G == gl) a.acc[(size_t)c * kMoments + q] += (double)mo[q];
+            }
         }
         __syncwarp();
     }
     // event counters
+    ncand_tot = __reduce_add_sync(kFull, (unsigned)ncand_tot);
+    ncoll_tot = __reduce_add_sync(kFull, (unsigned)ncoll_tot);
+    nlive = __reduce_add_sync(kFull, nlive);
     if (lane == 0) {
         if (ncand_tot) atomicAdd(&a.counters[HYB_C_CANDIDATES], ncand_tot);
         if (ncoll_tot) atomicAdd(&a.counters[HYB_C_COLLISIONS], ncoll_tot);
@@ -529,11 +543,17 @@ cudaError_t step_impl(Ctx& c) {
     prof_begin(c, K_MOVE);
     k_move<Real><<<grid_for(c, c.d.ncells * 32, 256, 8), 256, 0, c.stream>>>(a);
     prof_end(c, K_MOVE);
-    // at most 4 warps x 256 x (3 x 8 + 4) B = 28 KB of shared memory: below the default limit
-    const size_t smem = (size_t)kCollideWarps * c.d.bin * (3 * sizeof(Real) + 4);
-    const int grid = grid_for(c, c.d.ncells * 32, kCollideWarps * 32, 16);
+    // shared memory: per group (32 / kGroup per warp) bin x (3 Real + 1 u32)
+    constexpr int WARPS = CollideCfg<Real>::WARPS;
+    const size_t smem = (size_t)WARPS * (32 / kGroup) * c.d.bin * (3 * sizeof(Real) + 4);
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(k_collide<Real>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const int grid = grid_for(c, (c.d.ncells + (32 / kGroup) - 1) / (32 / kGroup) * 32, WARPS * 32, 16);
     prof_begin(c, K_COLLIDE);
-    k_collide<Real><<<grid, kCollideWarps * 32, smem, c.stream>>>(a);
+    k_collide<Real><<<grid, WARPS * 32, smem, c.stream>>>(a);
     prof_end(c, K_COLLIDE);
     return cudaGetLastError();
 }
