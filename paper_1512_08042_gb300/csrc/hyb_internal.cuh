@@ -26,6 +26,7 @@ enum CtrlWord {
     CTRL_NSAMPLES = 3,
     CTRL_TICKET = 4,   // blocks finished, for the last-block update of the move kernel
     CTRL_L2D_BAD = 5,  // an invalid cell index in the current LB2DSMC call
+    CTRL_WORK = 6,     // next batch of cells for the collide kernel
     CTRL_WORDS = 16,
 };
 

@@ -213,6 +213,7 @@ __global__ void __launch_bounds__(256) k_move(DsmcArgs<Real> a) {
         if (s % (uint32_t)a.sample_every == 0) a.ctrl[CTRL_NSAMPLES] += 1;
         a.ctrl[CTRL_STEP] = s + 1;
         a.ctrl[CTRL_NTOT] = 0;
+        a.ctrl[CTRL_WORK] = 0;
         a.ctrl[CTRL_TICKET] = 0;
     }
 }
@@ -228,6 +229,7 @@ constexpr int kGroup = 8;
 template <typename Real>
 struct CollideCfg {
     static constexpr int WARPS = sizeof(Real) == 4 ? 4 : 2;
+    static constexpr int MINB = sizeof(Real) == 4 ? 8 : 4;  // resident blocks per SM
 };
 
 // Ascending bitonic sort of G R keys held by the G lanes of a group, R per lane (key r of
@@ -276,7 +278,7 @@ __device__ __forceinline__ void gather_one(const DsmcArgs<Real>& a, int64_t base
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(CollideCfg<Real>::WARPS * 32) k_collide(DsmcArgs<Real> a) {
+__global__ void __launch_bounds__(CollideCfg<Real>::WARPS * 32, CollideCfg<Real>::MINB) k_collide(DsmcArgs<Real> a) {
     constexpr int G = kGroup;
     constexpr int CPW = 32 / G;         // cells per warp
     constexpr int SMALL = 64;           // cells up to this size are sorted in registers
@@ -302,8 +304,14 @@ __global__ void __launch_bounds__(CollideCfg<Real>::WARPS * 32) k_collide(DsmcAr
     unsigned long long ncand_tot = 0, ncoll_tot = 0;
     uint32_t flags = 0, nlive = 0;
 
-    for (int cb = (blockIdx.x * WARPS + w) * CPW; cb < a.ncells; cb += gridDim.x * WARPS * CPW) {
-        const int c = cb + grp;
+    const int nbatch = (a.ncells + CPW - 1) / CPW;
+    for (;;) {
+        // batches of CPW cells are handed out dynamically, so no warp waits on a tail
+        int bt = 0;
+        if (lane == 0) bt = (int)atomicAdd(&a.ctrl[CTRL_WORK], 1u);
+        bt = __shfl_sync(kFull, bt, 0);
+        if (bt >= nbatch) break;
+        const int c = bt * CPW + grp;
         const bool has = c < a.ncells;
         uint32_t n = has ? a.count_d[c] : 0u;
         if (n > bin) n = bin;
@@ -449,15 +457,27 @@ __global__ void __launch_bounds__(CollideCfg<Real>::WARPS * 32) k_collide(DsmcAr
             }
         }
         if (do_sample) {
+            // halving exchange over the group: lane gl ends with the totals of moments
+            // 3 gl, 3 gl + 1, 3 gl + 2
+            Real t[24];
 #pragma unroll
-            for (int q = 0; q < kMoments; ++q) {
+            for (int q = 0; q < 24; ++q) t[q] = q < kMoments ? mo[q] : (Real)0;
 #pragma unroll
-                for (int off = G / 2; off > 0; off >>= 1) mo[q] += __shfl_xor_sync(kFull, mo[q], off);
+            for (int o = G / 2, len = 12; o >= 1; o >>= 1, len >>= 1) {
+                const bool hi = (gl & o) != 0;
+#pragma unroll
+                for (int q = 0; q < len; ++q) {
+                    const Real send = hi ? t[q] : t[q + len];
+                    const Real keep = hi ? t[q + len] : t[q];
+                    t[q] = keep + __shfl_xor_sync(kFull, send, o);
+                }
             }
             if (has) {
 #pragma unroll
-                for (int q = 0; q < kMoments; ++q)
-                    if (q % G == gl) a.acc[(size_t)c * kMoments + q] += (double)mo[q];
+                for (int q = 0; q < 3; ++q) {
+                    const int mq = 3 * gl + q;
+                    if (mq < kMoments) a.acc[(size_t)c * kMoments + mq] += (double)t[q];
+                }
             }
         }
         __syncwarp();
@@ -551,7 +571,8 @@ cudaError_t step_impl(Ctx& c) {
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    const int grid = grid_for(c, (c.d.ncells + (32 / kGroup) - 1) / (32 / kGroup) * 32, WARPS * 32, 16);
+    const int grid = grid_for(c, (c.d.ncells + (32 / kGroup) - 1) / (32 / kGroup) * 32, WARPS * 32,
+                              CollideCfg<Real>::MINB);
     prof_begin(c, K_COLLIDE);
     k_collide<Real><<<grid, WARPS * 32, smem, c.stream>>>(a);
     prof_end(c, K_COLLIDE);
