@@ -522,6 +522,49 @@ def test_lb2dsmc_sampled_moments_match_grad_coefficients():
     assert info["envelope"] < 1e-3 * info["attempts"]
 
 
+@pytest.mark.parametrize("real_bytes,big", [(8, 2.0 ** 53), (4, 2.0 ** 24)])
+def test_pairwise_sum_order_worked_example(real_bytes, big):
+    # 64 terms: t0 = 2^p (one unit in the last place of 2^p is 2), the other 63 are 1.
+    # Worked by hand from the order: s_0 = 2^p + 1 rounds to 2^p (tie to even), s_i = 2
+    # (i = 1..31); the halvings then add 2, 4, 8, 16, 32 to s_0 exactly, so the sum is
+    # 2^p + 62. A left-to-right sum loses every 1 (2^p), the exact sum is 2^p + 63.
+    t = np.ones(64)
+    t[0] = big
+    assert O.pairwise64(t, real_bytes) == big + 62
+    # the first level pairs t_i with t_(i+32): with t32 = 3, s_0 = 2^p + 3 rounds to 2^p + 4
+    # (tie to even) and the rest adds 62, so 2^p + 66; pairing t_0 with t_1 would lose t_1
+    t[32] = 3.0
+    assert O.pairwise64(t, real_bytes) == big + 66
+    # terms whose partial sums are all exact give the exact sum, zero padding included
+    rng = np.random.default_rng(4)
+    for n in (1, 19, 39, 64):
+        v = rng.integers(-1000, 1000, n).astype(np.float64)
+        assert O.pairwise64(v, real_bytes) == v.sum()
+
+
+@pytest.mark.parametrize("q", [39, 19])
+def test_lb2dsmc_state_precision_coefficients(q):
+    # The float coefficients are the double ones to float accuracy, and at a third-order
+    # equilibrium with velocity u they are u and zero (closed form of Table 1 step 1).
+    u = np.array([0.05, -0.1, 0.02])
+    f_eq = _eq_populations(q, 1.1, u)
+    for rb, tol in ((8, 1e-14), (4, 2e-7)):
+        g = O.grad_coeffs_packed(q, f_eq, rb)
+        assert g["rho"] == pytest.approx(1.1, rel=tol * 4)
+        assert np.allclose(g["u"], u, atol=tol * 4)
+        if q == 39:  # D3Q39 integrates the third-order equilibrium exactly
+            assert g["M"] < tol * 40
+    e, w, r = O.lattice(q)
+    f = W.gen_populations(w, 1, seed=11, eps=0.1, rho_eps=0.1)[:, 0]
+    gd = O.grad_coeffs_packed(q, f, 8)
+    gf = O.grad_coeffs_packed(q, f, 4)
+    full = O.grad_coeffs(q, f)
+    assert gd["C"] == full["C"] and np.array_equal(gd["u"], full["u"])
+    for k in ("a2", "a3"):
+        assert np.all(np.abs(gf[k] - gd[k]) < 2e-6), k
+    assert abs(gf["C"] - gd["C"]) < 6e-5
+
+
 def test_lb2dsmc_particle_count_conserves_mass():
     cfg = small_cfg(ncx=10, ncy=3, ppc=40, real_bytes=8)
     o = O.Oracle(cfg)
