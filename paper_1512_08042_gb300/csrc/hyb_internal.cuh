@@ -52,15 +52,16 @@ enum KernelId {
 };
 
 // LB2DSMC per-cell record (map_scratch).
+// Grad record of one coupling cell (176 bytes). v holds 20 values of the state precision
+// Real, packed from its start: a2[6] (xx xy xz yy yz zz), a3[10] (xxx xxy xxz xyy xyz xzz
+// yyy yyz yzz zzz), u[3], C.
 struct GradRec {
     double rho;
-    double u[3];
-    double a2[6];   // packed xx xy xz yy yz zz
-    double a3[10];  // packed xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz
-    double C;
     uint32_t nnew;
     uint32_t pad;
+    double v[20];
 };
+enum : int { GR_A2 = 0, GR_A3 = 6, GR_U = 16, GR_C = 19 };
 
 // Pointers into the arena.
 struct State {

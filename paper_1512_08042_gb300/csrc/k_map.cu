@@ -1,19 +1,21 @@
 // The two kinetic mappings of Sec. 2. The Grad/Hermite coefficients are solved in FP64;
 // populations and particle state are Real (float or double).
 //
-// k_d2l (DSMC2LB, Sec. 2.1): one thread per coupling node. The cumulative sums of the
-// node's DSMC cell give rho = <N>/ppc, the per-particle raw moments <v>, <vv>, <vvv>, and
-// the raw Hermite coefficients a0 = rho, a1 = rho <v>, a2 = rho(<vv> - I),
-// a3 = rho(<vvv> - sym(<v> I)) (FP64); the populations f_a = w_a sum_{n<=N} a^(n):H^(n)(xi_a)/n!
-// (Eq. discretefunctions) are evaluated in the state precision.
+// k_d2l (DSMC2LB, Sec. 2.1): one warp per coupling node. The cumulative sums of the
+// node's DSMC cell give rho = <N>/ppc, the per-particle raw moments <v>, <vv>, <vvv> (one
+// FP64 reciprocal of the count, the ratios rounded to the state precision), and the raw
+// Hermite coefficients a0 = rho, a1 = rho <v>, a2 = rho(<vv> - I), a3 = rho(<vvv> - sym(<v> I));
+// the populations f_a = w_a sum_{n<=N} a^(n):H^(n)(xi_a)/n! (Eq. discretefunctions) are
+// evaluated in the state precision.
 //
 // LB2DSMC (Sec. 2.2, Table 1) in two launches:
 //   k_l2d_coef   one warp per coupling cell: mean populations of the cell's lb_ratio^2
 //                nodes, rho and u, the comoving coefficients a2 = sum f c c / rho - I and
-//                a3 = sum f c c c / rho (c = xi - u), M, C = 1 + 30 M (Eq. C), and the
-//                particle count floor(rho ppc + U) (FP64, lanes over populations);
-//   k_l2d_sample one warp per coupling cell: the cell's trial stream is evaluated 32 trials
-//                at a time: Box-Muller xi from the unit Maxwellian, accepted when
+//                a3 = sum f c c c / rho (c = xi - u), M, C = 1 + 30 M (Eq. C), all in the
+//                state precision with one fixed pairwise order of every population sum, and
+//                the particle count floor(rho ppc + U);
+//   k_l2d_sample one block per coupling cell: the cell's trial stream is evaluated 128
+//                trials at a time: Box-Muller xi from the unit Maxwellian, accepted when
 //                C R <= G(xi), G = 1 + a2:H2/2 + a3:H3/6 (Eq. distr_outeq) in the state
 //                precision; the k-th accepted trial becomes the k-th particle of the cell's
 //                bin (replacing the old ones), velocity xi + u (Eq. step6 in c_th units),
@@ -33,36 +35,47 @@ namespace hyb {
 
 namespace {
 
+// Speed components of the lattices as device tables, for lanes that each handle a different
+// population (a runtime index into the compile-time table would copy it to local memory).
 template <class LAT>
-__host__ __device__ constexpr int E(int a, int i) {
-    return LatTab<LAT>::e(a, i);
+struct LatSpeeds {
+    int8_t e[3 * LAT::Q];
+};
+template <class LAT>
+constexpr LatSpeeds<LAT> make_speeds() {
+    LatSpeeds<LAT> s{};
+    for (int a = 0; a < LAT::Q; ++a)
+        for (int i = 0; i < 3; ++i) s.e[3 * a + i] = (int8_t)LatTab<LAT>::e(a, i);
+    return s;
+}
+__device__ const LatSpeeds<D3Q39> g_speeds39 = make_speeds<D3Q39>();
+__device__ const LatSpeeds<D3Q19> g_speeds19 = make_speeds<D3Q19>();
+
+template <class LAT>
+__device__ __forceinline__ int lat_e(int a, int i) {
+    if constexpr (LAT::Q == 39)
+        return g_speeds39.e[3 * a + i];
+    else
+        return g_speeds19.e[3 * a + i];
 }
 
-// Lattice table in shared memory, for lanes that each handle a different population.
-template <class LAT>
-__device__ __forceinline__ void load_lattice(int* se, double* sw) {
-    for (int q = threadIdx.x; q < LAT::Q; q += blockDim.x) {
-        se[3 * q] = LatTab<LAT>::e(q, 0);
-        se[3 * q + 1] = LatTab<LAT>::e(q, 1);
-        se[3 * q + 2] = LatTab<LAT>::e(q, 2);
-        sw[q] = LatTab<LAT>::w(q);
-    }
-}
-
-// DSMC2LB: one warp per coupling node. Lanes 0-19 read the cell's 20 sums; the FP64
-// coefficient solve is spread over the lanes (one coefficient each); the 19 coefficients
-// are broadcast and each lane evaluates one or two populations in the state precision.
+// DSMC2LB: one warp per coupling node. Lanes 0-19 read the cell's 20 sums and scale them
+// by one FP64 reciprocal of the particle count; the coefficients (one per lane, state
+// precision) are broadcast and each lane evaluates one or two populations.
 template <typename Real, class LAT>
 __global__ void __launch_bounds__(128) k_d2l(MapArgs<Real> a) {
-    __shared__ int se[3 * LAT::Q];
-    __shared__ double sw[LAT::Q];
-    load_lattice<LAT>(se, sw);
+    __shared__ Real sx[3 * LAT::Q];
+    __shared__ Real sw[LAT::Q];
+    for (int q = threadIdx.x; q < LAT::Q; q += blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) sx[3 * q + i] = (Real)(lat_r<LAT>() * (double)lat_e<LAT>(q, i));
+        sw[q] = (Real)LatTab<LAT>::w(q);
+    }
     __syncthreads();
     const unsigned lane = lane_id();
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const uint32_t S = a.ctrl[CTRL_NSAMPLES];
-    constexpr double R = lat_r<LAT>();
     for (int t = gw; t < a.n; t += nw) {
         const int32_t node = a.list[t];
         if (node < 0 || (int64_t)node >= a.nnodes) {
@@ -78,28 +91,27 @@ __global__ void __launch_bounds__(128) k_d2l(MapArgs<Real> a) {
             if (lane == 0) atomicOr(&a.ctrl[CTRL_STATUS], HYB_ST_BAD_INPUT);
             continue;
         }
-        // FP64 coefficient solve, one coefficient per lane:
-        // lane 0: rho; 1-3: a1 = rho <v>; 4-9: a2 = rho(<vv> - I); 10-19: a3 = rho(<vvv> - sym(<v> I))
-        const double rho = (NS / (double)S) / (double)a.ppc;
-        const double iNS = 1.0 / NS;
-        const double m1x = __shfl_sync(kFull, mk, 1) * iNS;
-        const double m1y = __shfl_sync(kFull, mk, 2) * iNS;
-        const double m1z = __shfl_sync(kFull, mk, 3) * iNS;
-        double sub = 0.0;
+        // per-particle moments, lane k: <v> (1-3), <vv> (4-9), <vvv> (10-19)
+        const Real mr = (Real)(mk * (1.0 / NS));
+        const Real rho = (Real)NS / ((Real)S * (Real)a.ppc);
+        const Real m1x = __shfl_sync(kFull, mr, 1);
+        const Real m1y = __shfl_sync(kFull, mr, 2);
+        const Real m1z = __shfl_sync(kFull, mr, 3);
+        Real sub = 0;
         switch (lane) {
-            case 4: case 7: case 9: sub = 1.0; break;        // xx yy zz
-            case 10: sub = 3 * m1x; break;                   // xxx
-            case 11: sub = m1y; break;                       // xxy
-            case 12: sub = m1z; break;                       // xxz
-            case 13: sub = m1x; break;                       // xyy
-            case 15: sub = m1x; break;                       // xzz
-            case 16: sub = 3 * m1y; break;                   // yyy
-            case 17: sub = m1z; break;                       // yyz
-            case 18: sub = m1y; break;                       // yzz
-            case 19: sub = 3 * m1z; break;                   // zzz
+            case 4: case 7: case 9: sub = (Real)1; break;       // xx yy zz
+            case 10: sub = (Real)3 * m1x; break;                // xxx
+            case 11: sub = m1y; break;                          // xxy
+            case 12: sub = m1z; break;                          // xxz
+            case 13: sub = m1x; break;                          // xyy
+            case 15: sub = m1x; break;                          // xzz
+            case 16: sub = (Real)3 * m1y; break;                // yyy
+            case 17: sub = m1z; break;                          // yyz
+            case 18: sub = m1y; break;                          // yzz
+            case 19: sub = (Real)3 * m1z; break;                // zzz
             default: break;
         }
-        const Real coef = lane == 0 ? (Real)rho : (Real)(rho * (mk * iNS - sub));
+        const Real coef = lane == 0 ? rho : rho * (mr - sub);
         Real cf[kMoments];
 #pragma unroll
         for (int k = 0; k < kMoments; ++k) cf[k] = __shfl_sync(kFull, coef, k);
@@ -111,7 +123,7 @@ __global__ void __launch_bounds__(128) k_d2l(MapArgs<Real> a) {
         for (int h = 0; h < (LAT::Q + 31) / 32; ++h) {
             const int q = (int)lane + 32 * h;
             if (q < LAT::Q) {
-                const Real X = (Real)(R * se[3 * q]), Y = (Real)(R * se[3 * q + 1]), Z = (Real)(R * se[3 * q + 2]);
+                const Real X = sx[3 * q], Y = sx[3 * q + 1], Z = sx[3 * q + 2];
                 const Real h2 = a2[0] * X * X + a2[3] * Y * Y + a2[5] * Z * Z - tr2 +
                                 (Real)2 * (a2[1] * X * Y + a2[2] * X * Z + a2[4] * Y * Z);
                 Real sum = cf[0] + cf[1] * X + cf[2] * Y + cf[3] * Z + (Real)0.5 * h2;
@@ -123,122 +135,160 @@ __global__ void __launch_bounds__(128) k_d2l(MapArgs<Real> a) {
                                        (Real)3 * a3[8] * Y * Z * Z + a3[9] * Z * Z * Z;
                     sum += (cubic - (Real)3 * (tx * X + ty * Y + tz * Z)) * (Real)(1.0 / 6.0);
                 }
-                a.f[(int64_t)q * a.nnodes + node] = (Real)sw[q] * sum;
+                a.f[(int64_t)q * a.nnodes + node] = sw[q] * sum;
             }
         }
     }
 }
 
-// LB2DSMC coefficients: one block of 64 threads per coupling cell, FP64. Each sum runs over
-// the populations in lattice order: the terms (mean populations of the cell's nodes, their
-// products with the speeds and with the comoving speed components) are formed in parallel,
-// one population per thread, and each sum is then accumulated in order by one thread. Then
-// M, C = 1 + 30 M and the new count floor(rho ppc + U).
+// Sums each of the N values (N a power of two, at most 32) over the 32 lanes, combining
+// lanes l and l ^ o for o = 16, 8, 4, 2, 1 in turn; while N > 1 each lane keeps half of its
+// values at every step (a halving exchange). Lane l ends with the total of value
+// l >> (5 - log2 N) in v[0]. Every total is formed by the same tree of additions as a
+// butterfly over each value alone: the pairwise order of the oracle after its first level.
+template <typename Real, int N>
+__device__ __forceinline__ void halving_sum(Real (&v)[N], unsigned lane) {
+    int o = 16;
+#pragma unroll
+    for (int len = N / 2; len >= 1; len >>= 1, o >>= 1) {
+        const bool hi = (lane & (unsigned)o) != 0;
+#pragma unroll
+        for (int q = 0; q < len; ++q) {
+            const Real send = hi ? v[q] : v[q + len];
+            const Real keep = hi ? v[q + len] : v[q];
+            v[q] = keep + __shfl_xor_sync(kFull, send, o);
+        }
+    }
+#pragma unroll
+    for (; o >= 1; o >>= 1) v[0] = v[0] + __shfl_xor_sync(kFull, v[0], o);
+}
+
+__device__ __forceinline__ float warp_max_abs(float x) {
+    return __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(fabsf(x))));
+}
+__device__ __forceinline__ double warp_max_abs(double x) {
+    double m = fabs(x);
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) m = fmax(m, __shfl_xor_sync(kFull, m, o));
+    return m;
+}
+
+// LB2DSMC coefficients (Table 1 step 1): one warp per coupling cell, state precision. Lane
+// l holds the cell-mean populations q = l and l + 32 (zero past Q); each population sum adds
+// the lane's two terms and then reduces over the lanes (halving_sum), which is the oracle's
+// pairwise order. Products are (f c_i) c_j and ((f c_i) c_j) c_k with i <= j <= k.
 template <typename Real, class LAT>
-__global__ void __launch_bounds__(64) k_l2d_coef(MapArgs<Real> a) {
+__global__ void __launch_bounds__(128) k_l2d_coef(MapArgs<Real> a) {
     constexpr int Q = LAT::Q;
-    constexpr int NM = LAT::ORDER >= 3 ? 16 : 6;
-    __shared__ double fb[Q];
-    __shared__ double pj[3][Q];
-    __shared__ double prod[NM][Q];
-    __shared__ double s_rj[4];
-    __shared__ double s_m[16];
+    constexpr int NM = LAT::ORDER >= 3 ? 16 : 6;  // distinct second and third moments
+    constexpr int NP = NM > 8 ? 16 : 8;           // padded to a power of two
+    constexpr int SH = NP == 16 ? 1 : 2;          // lane >> SH: moment held after the sum
+    const unsigned lane = lane_id();
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
     const uint32_t t_step = a.ctrl[CTRL_STEP];
     const int r = a.lb_ratio;
-    const double rr = a.r_lat;
-    const int tid = threadIdx.x;
-    int e0 = 0, e1 = 0, e2 = 0;
-    if (tid < Q) {
-        e0 = LatTab<LAT>::e(tid, 0);
-        e1 = LatTab<LAT>::e(tid, 1);
-        e2 = LatTab<LAT>::e(tid, 2);
+    const int q0 = (int)lane, q1 = (int)lane + 32;
+    const bool v0 = q0 < Q, v1 = q1 < Q;
+    Real xi0[3] = {0, 0, 0}, xi1[3] = {0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        if (v0) xi0[i] = (Real)(a.r_lat * (double)lat_e<LAT>(q0, i));
+        if (v1) xi1[i] = (Real)(a.r_lat * (double)lat_e<LAT>(q1, i));
     }
-    for (int ci = blockIdx.x; ci < a.n; ci += gridDim.x) {
+    for (int ci = gw; ci < a.n; ci += nw) {
         const int32_t cell = a.list[ci];
         if (cell < 0 || cell >= a.ncx * a.ncy) {
-            if (tid == 0) {
+            if (lane == 0) {
                 atomicOr(&a.ctrl[CTRL_STATUS], HYB_ST_BAD_INPUT);
                 a.ctrl[CTRL_L2D_BAD] = 1;
             }
             continue;
         }
         const int ix = cell % a.ncx, iy = cell / a.ncx;
-        if (tid < Q) {
-            double sacc = 0.0;
-            for (int dy = 0; dy < r; ++dy)
-                for (int dx = 0; dx < r; ++dx)
-                    sacc += (double)a.f[(int64_t)tid * a.nnodes + (int64_t)(iy * r + dy) * a.nx + (ix * r + dx)];
-            const double fq = sacc / (double)(r * r);
-            fb[tid] = fq;
-            pj[0][tid] = fq * (rr * e0);
-            pj[1][tid] = fq * (rr * e1);
-            pj[2][tid] = fq * (rr * e2);
-        }
-        __syncthreads();
-        if (tid < 4) {  // rho (thread 0) and rho u (threads 1-3), summed in lattice order
-            const double* src = tid == 0 ? fb : pj[tid - 1];
-            double acc = 0.0;
-            for (int q = 0; q < Q; ++q) acc += src[q];
-            s_rj[tid] = acc;
-        }
-        __syncthreads();
-        const double rho = s_rj[0];
-        const double ux = s_rj[1] / rho, uy = s_rj[2] / rho, uz = s_rj[3] / rho;
-        if (tid < Q) {
-            const double fq = fb[tid];
-            const double c[3] = {rr * e0 - ux, rr * e1 - uy, rr * e2 - uz};
-            // packed moments xx xy xz yy yz zz, xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz
-            prod[0][tid] = fq * c[0] * c[0];
-            prod[1][tid] = fq * c[0] * c[1];
-            prod[2][tid] = fq * c[0] * c[2];
-            prod[3][tid] = fq * c[1] * c[1];
-            prod[4][tid] = fq * c[1] * c[2];
-            prod[5][tid] = fq * c[2] * c[2];
-            if constexpr (NM > 6) {
-                prod[6][tid] = fq * c[0] * c[0] * c[0];
-                prod[7][tid] = fq * c[0] * c[0] * c[1];
-                prod[8][tid] = fq * c[0] * c[0] * c[2];
-                prod[9][tid] = fq * c[0] * c[1] * c[1];
-                prod[10][tid] = fq * c[0] * c[1] * c[2];
-                prod[11][tid] = fq * c[0] * c[2] * c[2];
-                prod[12][tid] = fq * c[1] * c[1] * c[1];
-                prod[13][tid] = fq * c[1] * c[1] * c[2];
-                prod[14][tid] = fq * c[1] * c[2] * c[2];
-                prod[15][tid] = fq * c[2] * c[2] * c[2];
+        // mean populations of the cell's nodes, summed in node order (dy, dx)
+        Real p0[4], p1[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            p0[k] = 0;
+            p1[k] = 0;
+            if (k < r * r) {
+                const int64_t node = (int64_t)(iy * r + k / r) * a.nx + (ix * r + k % r);
+                if (v0) p0[k] = a.f[(int64_t)q0 * a.nnodes + node];
+                if (v1) p1[k] = a.f[(int64_t)q1 * a.nnodes + node];
             }
         }
-        __syncthreads();
-        if (tid < NM) {
-            double acc = 0.0;
-            for (int q = 0; q < Q; ++q) acc += prod[tid][q];
-            double v = acc / rho;
-            if (tid == 0 || tid == 3 || tid == 5) v -= 1.0;
-            s_m[tid] = v;
+        Real s0 = 0, s1 = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (k < r * r) {
+                s0 += p0[k];
+                s1 += p1[k];
+            }
+        const Real nn = (Real)(r * r);
+        const Real f0 = v0 ? s0 / nn : (Real)0;
+        const Real f1 = v1 ? s1 / nn : (Real)0;
+        // rho and j; lanes 0-7 end with rho, 8-15 jx, 16-23 jy, 24-31 jz
+        Real t4[4];
+        t4[0] = f0 + f1;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) t4[1 + i] = f0 * xi0[i] + f1 * xi1[i];
+        halving_sum<Real, 4>(t4, lane);
+        const Real rho = __shfl_sync(kFull, t4[0], 0);
+        Real u[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) u[i] = __shfl_sync(kFull, t4[0], 8 * (i + 1)) / rho;
+        Real c0[3], c1[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            c0[i] = xi0[i] - u[i];
+            c1[i] = xi1[i] - u[i];
         }
-        __syncthreads();
-        if (tid == 0) {
-            GradRec g;
-            g.rho = rho;
-            g.u[0] = ux;
-            g.u[1] = uy;
-            g.u[2] = uz;
-            double M = 0.0;
-            for (int k = 0; k < 6; ++k) {
-                g.a2[k] = s_m[k];
-                M = fmax(M, fabs(s_m[k]));
+        Real tm[NP];
+        int o = 0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = i; j < 3; ++j, ++o) {
+                const Real lo = v0 ? (f0 * c0[i]) * c0[j] : (Real)0;
+                const Real hi = v1 ? (f1 * c1[i]) * c1[j] : (Real)0;
+                tm[o] = lo + hi;
             }
-            for (int k = 0; k < 10; ++k) {
-                g.a3[k] = NM > 6 ? s_m[6 + k] : 0.0;
-                M = fmax(M, fabs(g.a3[k]));
-            }
-            g.C = 1.0 + 30.0 * M;
-            const double u = u01d(draw(a.seed, (uint32_t)cell, t_step, TAG_L2D_ROUND, 0, 0).x);
-            const double ne = floor(rho * (double)a.ppc + u);
+        if constexpr (NM > 6) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = i; j < 3; ++j)
+#pragma unroll
+                    for (int k = j; k < 3; ++k, ++o) {
+                        const Real lo = v0 ? ((f0 * c0[i]) * c0[j]) * c0[k] : (Real)0;
+                        const Real hi = v1 ? ((f1 * c1[i]) * c1[j]) * c1[k] : (Real)0;
+                        tm[o] = lo + hi;
+                    }
+        }
+#pragma unroll
+        for (int k = NM; k < NP; ++k) tm[k] = 0;
+        halving_sum<Real, NP>(tm, lane);
+        const int mom = (int)(lane >> SH);
+        Real val = tm[0] / rho;
+        if (mom == 0 || mom == 3 || mom == 5) val = val - (Real)1;
+        const Real M = warp_max_abs(mom < NM ? val : (Real)0);
+        GradRec& g = a.grad[ci];
+        Real* pv = reinterpret_cast<Real*>(g.v);
+        if (mom < NM && (lane & ((1u << SH) - 1u)) == 0) pv[GR_A2 + mom] = val;
+        if (lane == 0) {
+            if (NM == 6)
+                for (int k = 0; k < 10; ++k) pv[GR_A3 + k] = 0;
+            pv[GR_U] = u[0];
+            pv[GR_U + 1] = u[1];
+            pv[GR_U + 2] = u[2];
+            pv[GR_C] = (Real)1 + (Real)30 * M;
+            const double ur = u01d(draw(a.seed, (uint32_t)cell, t_step, TAG_L2D_ROUND, 0, 0).x);
+            const double ne = floor((double)rho * (double)a.ppc + ur);
+            g.rho = (double)rho;
             g.nnew = ne > 0.0 ? (uint32_t)ne : 0u;
             g.pad = 0;
-            a.grad[ci] = g;
         }
-        __syncthreads();
     }
 }
 
@@ -268,6 +318,21 @@ __device__ __forceinline__ Real grad_G(const Real* a2, const Real* a3, Real X, R
 
 constexpr int kSampleWarps = 4;
 
+// Position of the k-th set bit (k >= 1) of m, which has at least k set bits.
+__device__ __forceinline__ int nth_set_bit(unsigned m, int k) {
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const int c = __popc(m & ((1u << w) - 1u));
+        if (c < k) {
+            k -= c;
+            m >>= w;
+            pos += w;
+        }
+    }
+    return pos;
+}
+
 // One block per coupling cell: the cell's trial stream is evaluated 128 trials at a time;
 // the k-th accepted trial becomes the k-th particle of the cell's bin, replacing the old
 // ones. Nothing is written if a listed cell index was invalid (the coefficient kernel
@@ -292,13 +357,14 @@ __global__ void __launch_bounds__(kSampleWarps * 32) k_l2d_sample(MapArgs<Real> 
             flags |= HYB_ST_CAPACITY;
             continue;
         }
+        const Real* pv = reinterpret_cast<const Real*>(g.v);
         Real a2[6], a3[10];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) a2[k] = (Real)g.a2[k];
+        for (int k = 0; k < 6; ++k) a2[k] = pv[GR_A2 + k];
 #pragma unroll
-        for (int k = 0; k < 10; ++k) a3[k] = (Real)g.a3[k];
-        const Real C = (Real)g.C;
-        const Real ux = (Real)g.u[0], uy = (Real)g.u[1], uz = (Real)g.u[2];
+        for (int k = 0; k < 10; ++k) a3[k] = pv[GR_A3 + k];
+        const Real C = pv[GR_C];
+        const Real ux = pv[GR_U], uy = pv[GR_U + 1], uz = pv[GR_U + 2];
         const int64_t out0 = (int64_t)cell * bin;
         const Real fx = (Real)(cell % (uint32_t)a.ncx), fy = (Real)(cell / (uint32_t)a.ncx);
         const uint64_t cap64 = 1000ull * nnew;
@@ -360,11 +426,7 @@ __global__ void __launch_bounds__(kSampleWarps * 32) k_l2d_sample(MapArgs<Real> 
                             envc += (uint32_t)__popc(s_em[v] & s_vm[v]);
                             continue;
                         }
-                        int bit = 0;
-                        for (unsigned mm = s_am[v];; mm &= mm - 1u) {
-                            bit = __ffs(mm) - 1;
-                            if (--left == 0) break;
-                        }
+                        const int bit = nth_set_bit(s_am[v], (int)left);
                         const unsigned upto = bit == 31 ? 0xFFFFFFFFu : ((2u << bit) - 1u);
                         used += (uint32_t)bit + 1u;
                         envc += (uint32_t)__popc(s_em[v] & upto);
@@ -453,7 +515,7 @@ cudaError_t l2d_impl(Ctx& c, const int32_t* cells, int32_t n) {
     cudaError_t e = cudaMemsetAsync(c.st.ctrl + CTRL_L2D_BAD, 0, 4, c.stream);
     if (e != cudaSuccess) return e;
     prof_begin(c, K_L2D_COEF);
-    k_l2d_coef<Real, LAT><<<blocks_for(c, (int64_t)n * 64, 64, 32), 64, 0, c.stream>>>(a);
+    k_l2d_coef<Real, LAT><<<blocks_for(c, (int64_t)n * 32, 128, 16), 128, 0, c.stream>>>(a);
     prof_end(c, K_L2D_COEF);
     prof_begin(c, K_L2D_SAMPLE);
     k_l2d_sample<Real, LAT><<<blocks_for(c, (int64_t)n * 32 * kSampleWarps, 32 * kSampleWarps, 16),
@@ -485,7 +547,7 @@ cudaError_t l2d_noalloc_impl(Ctx& c, const int32_t* cells, int32_t n, GradRec* r
     cudaError_t e = cudaMemsetAsync(c.st.ctrl + CTRL_L2D_BAD, 0, 4, c.stream);
     if (e != cudaSuccess) return e;
     prof_begin(c, K_L2D_COEF);
-    k_l2d_coef<Real, LAT><<<blocks_for(c, (int64_t)n * 64, 64, 32), 64, 0, c.stream>>>(a);
+    k_l2d_coef<Real, LAT><<<blocks_for(c, (int64_t)n * 32, 128, 16), 128, 0, c.stream>>>(a);
     prof_end(c, K_L2D_COEF);
     prof_begin(c, K_L2D_SAMPLE);
     k_l2d_sample<Real, LAT><<<blocks_for(c, (int64_t)n * 32 * kSampleWarps, 32 * kSampleWarps, 16),
