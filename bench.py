@@ -29,7 +29,7 @@ from paper_1512_08042_gb300 import workloads as W  # noqa: E402
 METRIC = "DSMC particle-updates/s, LBM MLUPS, hybrid steps/s on 1 GB300 at stated tol"
 DEFAULT_WORKLOAD = "poiseuille_64x256_ppc50_fp32"
 FLUSH_BYTES = 512 << 20
-LAUNCHES_PER_STEP = 6  # move, collide, dsmc2lb, lbm, lb2dsmc coefficients and sample
+LAUNCHES_PER_STEP = 5  # move, collide, dsmc2lb, lbm, lb2dsmc
 
 
 def kernel_algorithmic_bytes(name, cfg, d, n_particles, n_nodes_map, n_cells_map):
@@ -48,12 +48,10 @@ def kernel_algorithmic_bytes(name, cfg, d, n_particles, n_nodes_map, n_cells_map
         return d["nnodes"] * 2 * d["q"] * rb
     if name == "dsmc2lb":
         return n_nodes_map * (160 + d["q"] * rb)
-    if name == "lb2dsmc_coef":
-        # populations of the coupling cells' nodes read, one record per cell written
-        return n_cells_map * (cfg["lb_ratio"] ** 2 * d["q"] * rb + 176)
-    if name == "lb2dsmc_sample":
-        # one record read and ppc new particles written per coupling cell
-        return n_cells_map * (176 + cfg["ppc"] * 5 * rb)
+    if name == "lb2dsmc":
+        # populations of the coupling cells' nodes read; one record and ppc new particles
+        # written per coupling cell
+        return n_cells_map * (cfg["lb_ratio"] ** 2 * d["q"] * rb + 176 + cfg["ppc"] * 5 * rb)
     return 0
 
 

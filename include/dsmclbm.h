@@ -184,8 +184,9 @@ hyb_status map_dsmc_to_lbm(hyb_ctx* ctx, const int32_t* dev_nodes, int32_t n);
  * cell = iy * ncx + ix, distinct), replace its particles by floor(rho ppc + U) new ones,
  * with rho the mean LB density of the cell's lb_ratio^2 nodes; velocities drawn from the
  * Grad distribution of the cell's populations by acceptance-rejection with envelope
- * C = 1 + 30 M; positions uniform in the cell. A cell whose new count exceeds its bin keeps
- * its particles and raises HYB_ST_CAPACITY. */
+ * C = 1 + 30 M; positions uniform in the cell. The coefficients are formed in the state
+ * precision. A cell whose new count exceeds its bin keeps its particles and raises
+ * HYB_ST_CAPACITY; an invalid cell index is skipped and raises HYB_ST_BAD_INPUT. */
 hyb_status map_lbm_to_dsmc(hyb_ctx* ctx, const int32_t* dev_cells, int32_t n);
 
 /* map_lbm_to_dsmc without any device memory of its own beyond the context's arena.
@@ -224,7 +225,7 @@ hyb_status hyb_sync_status(hyb_ctx* ctx, uint32_t* bits);
 hyb_status hyb_read_counters(hyb_ctx* ctx, uint64_t* out);
 
 /* Kernel timing on the context's stream: after hyb_profile(ctx, k) every launch of kernel k
- * (0 move, 1 collide, 2 lbm, 3 dsmc2lb, 4 lb2dsmc coefficients, 5 lb2dsmc sample; -1 off) is bracketed by CUDA events. hyb_profile_harvest synchronises
+ * (0 move, 1 collide, 2 lbm, 3 dsmc2lb, 4 lb2dsmc; -1 off) is bracketed by CUDA events. hyb_profile_harvest synchronises
  * and adds the elapsed times of the launches since the last harvest; call it after every
  * hybrid step when graphs are used. hyb_profile_read returns the totals. */
 hyb_status hyb_profile(hyb_ctx* ctx, int32_t kernel);

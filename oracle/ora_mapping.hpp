@@ -294,22 +294,22 @@ void map_dsmc_to_lbm(Dsmc<Real>& D, Lbm<Real>& B, const int32_t* nodes, int n) {
 }
 
 // LB2DSMC over a list of distinct cells: each listed cell's particles are replaced by the
-// cell's regenerated ones (Sec. 2.2 "N_LB2DSMC ... conservation of mass at the coupling
-// sites"), so the particle array stays ordered by cell. A cell whose new count exceeds the
-// per-cell slot count `bin` keeps its particles and raises the capacity status.
+// cell's regenerated ones (Sec. 2.2: their number carries the mapped mass of the coupling
+// site), so the particle array stays ordered by cell. A cell whose new count exceeds the
+// per-cell slot count `bin` keeps its particles and raises the capacity status; an invalid
+// cell index is skipped and raises the bad-input status.
 template <class Real>
 void map_lbm_to_dsmc(Dsmc<Real>& D, const Lbm<Real>& B, const int32_t* cells, int n) {
     const Lattice& L = B.L;
     const int r = D.p.lb_ratio;
     const uint32_t t = (uint32_t)D.step;
-    for (int c = 0; c < n; ++c)
-        if (cells[c] < 0 || cells[c] >= D.d.ncells) {
-            D.status |= ST_BAD_INPUT;
-            return;
-        }
     std::vector<int> slot_of(D.d.ncells, -1);
     std::vector<std::vector<Real>> fresh(n);
     for (int c = 0; c < n; ++c) {
+        if (cells[c] < 0 || cells[c] >= D.d.ncells) {  // skipped and flagged
+            D.status |= ST_BAD_INPUT;
+            continue;
+        }
         const int64_t cell = cells[c];
         const int64_t ix = cell % D.p.ncx, iy = cell / D.p.ncx;
         std::vector<Real> fbar(L.q, (Real)0);

@@ -18,8 +18,7 @@ ST_CAPACITY, ST_BOUNCE_CAP, ST_SCATTER_CAP, ST_SAMPLING_CAP, ST_CELL_OVERFLOW, S
     1, 2, 4, 8, 16, 32)
 COUNTER_NAMES = ["wall_hits", "candidates", "collisions", "created", "deleted",
                  "l2d_attempts", "envelope", "bounce_cap"]
-KERNELS = {"move": 0, "collide": 1, "lbm": 2, "dsmc2lb": 3, "lb2dsmc_coef": 4,
-           "lb2dsmc_sample": 5}
+KERNELS = {"move": 0, "collide": 1, "lbm": 2, "dsmc2lb": 3, "lb2dsmc": 4}
 CTRL_STATUS, CTRL_NTOT, CTRL_STEP, CTRL_NSAMPLES = 0, 1, 2, 3
 NOALLOC_MAX_CELLS = 4096
 

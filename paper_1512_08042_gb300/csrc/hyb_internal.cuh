@@ -25,7 +25,6 @@ enum CtrlWord {
     CTRL_STEP = 2,
     CTRL_NSAMPLES = 3,
     CTRL_TICKET = 4,   // blocks finished, for the last-block update of the move kernel
-    CTRL_L2D_BAD = 5,  // an invalid cell index in the current LB2DSMC call
     CTRL_WORK = 6,     // next batch of cells for the collide kernel
     CTRL_WORDS = 16,
 };
@@ -46,9 +45,8 @@ enum KernelId {
     K_COLLIDE = 1,
     K_LBM = 2,
     K_D2L = 3,
-    K_L2D_COEF = 4,
-    K_L2D_SAMPLE = 5,
-    K_COUNT = 6,
+    K_L2D = 4,
+    K_COUNT = 5,
 };
 
 // LB2DSMC per-cell record (map_scratch).

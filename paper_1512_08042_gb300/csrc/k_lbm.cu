@@ -9,13 +9,18 @@
 // Collision, in the moment space of the Hermite expansion (exact on the quadrature):
 //   rho = sum f, j = sum f xi, Pi = sum f xi xi, Qm = sum f xi xi xi (D3Q39),
 //   u = (j + rho g / 2) / rho,
-//   f_eq = w rho [1 + xi.u + ((xi.u)^2 - u^2)/2 + (xi.u)((xi.u)^2 - 3u^2)/6],
 //   non-equilibrium Hermite coefficients a1 = -rho g / 2, a2 = Pi - rho(uu + I),
 //   a3 = Qm - rho(uuu + sym(u I)) - sym(a1 I),
 //   f' = f_eq + (1 - 1/tau) w [a1.xi + a2:H2/2 + a3:H3/6] + (1 - 1/(2 tau)) F,
-//   F = w rho [g.xi + (g.xi)(u.xi) - g.u + ((g.xi)(u.xi)^2 - (g.xi)u^2 - 2(u.xi)(g.u))/2].
-// Every lattice constant is a compile-time value, so terms with zero speed components
-// vanish at compile time.
+//   f_eq = w rho [1 + xi.u + ((xi.u)^2 - u^2)/2 + (xi.u)((xi.u)^2 - 3u^2)/6],
+//   F = w [rho g.xi + rho (g u + u g):H2/2 + rho sym(g u u):H3/6].
+// All three parts are Hermite series, so f' = w [A0 + A1.xi + A2:H2/2 + A3:H3/6] with
+//   A0 = rho, A1 = rho u + om a1 + of rho g, A2 = rho uu + om a2 + of rho (gu + ug),
+//   A3 = rho uuu + om a3 + of rho sym(guu)      (om = 1 - 1/tau, of = 1 - 1/(2 tau)).
+// The populations come in pairs xi, -xi; with s = f(xi) + f(-xi) and d = f(xi) - f(-xi) the
+// even moments take s and the odd ones d, and f'(+-xi) = w (E +- O) with E the even part
+// (A0, A2) and O the odd part (A1, A3) of the series. Every lattice constant is a
+// compile-time value, so terms with zero speed components vanish at compile time.
 #include <utility>
 
 #include "hyb_internal.cuh"
@@ -41,6 +46,15 @@ template <class LAT>
 __host__ __device__ constexpr double W(int a) {
     return LatTab<LAT>::w(a);
 }
+// Index of the population with the opposite speed.
+template <class LAT>
+__host__ __device__ constexpr int opp(int a) {
+    for (int b = 0; b < LAT::Q; ++b)
+        if (E<LAT>(b, 0) == -E<LAT>(a, 0) && E<LAT>(b, 1) == -E<LAT>(a, 1) &&
+            E<LAT>(b, 2) == -E<LAT>(a, 2))
+            return b;
+    return -1;
+}
 
 __device__ __forceinline__ int wrap_y(int v, int ny) {
     while (v < 0) v += ny;
@@ -59,23 +73,28 @@ __global__ void __launch_bounds__(128) k_lbm(LbmArgs<Real> a) {
     const int64_t nn = a.nnodes;
     const Real* __restrict__ src = a.src;
 
+    // Row offsets y' * nx of the pull sources y' = y - ey (periodic), ey = -MAXV..MAXV.
+    constexpr int MV = LAT::MAXV;
+    int rowoff[2 * MV + 1];
+#pragma unroll
+    for (int i = 0; i < 2 * MV + 1; ++i) rowoff[i] = wrap_y(y - (i - MV), ny) * nx;
+
     // Wall densities for nodes whose pull reaches through a wall: the mass leaving through
     // the wall on this row, re-emitted by the wall Maxwellian at rest.
     Real rhoL = (Real)0, rhoR = (Real)0;
-    if (x < LAT::MAXV || x >= nx - LAT::MAXV) {
+    if (x < MV || x >= nx - MV) {
         Real ml = (Real)0, mr = (Real)0;
         static_for<Q>([&](auto qc) {
             constexpr int q = decltype(qc)::value;
             constexpr int ex = E<LAT>(q, 0), ey = E<LAT>(q, 1);
+            const Real* __restrict__ sq = src + (int64_t)q * nn + rowoff[ey + MV];
             if constexpr (ex < 0) {
-                const int sy = wrap_y(y - ey, ny);
 #pragma unroll
-                for (int i = 0; i < -ex; ++i) ml += src[q * nn + (int64_t)sy * nx + i];
+                for (int i = 0; i < -ex; ++i) ml += sq[i];
             }
             if constexpr (ex > 0) {
-                const int sy = wrap_y(y - ey, ny);
 #pragma unroll
-                for (int i = 0; i < ex; ++i) mr += src[q * nn + (int64_t)sy * nx + (nx - ex + i)];
+                for (int i = 0; i < ex; ++i) mr += sq[nx - ex + i];
             }
         });
         constexpr double inv_flux = 1.0 / wall_flux_norm<LAT>();
@@ -83,127 +102,146 @@ __global__ void __launch_bounds__(128) k_lbm(LbmArgs<Real> a) {
         rhoR = mr * (Real)inv_flux;
     }
 
+    // pull streaming; sources behind a wall take the wall Maxwellian
     Real fs[Q];
     static_for<Q>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
         constexpr int ex = E<LAT>(q, 0), ey = E<LAT>(q, 1);
+        const Real* __restrict__ sq = src + (int64_t)q * nn;
         const int sx = x - ex;
-        const int sy = (ey == 0) ? y : wrap_y(y - ey, ny);
-        if (sx < 0)
-            fs[q] = (Real)W<LAT>(q) * rhoL;
-        else if (sx >= nx)
-            fs[q] = (Real)W<LAT>(q) * rhoR;
+        const int off = rowoff[ey + MV] + sx;
+        if constexpr (ex > 0)
+            fs[q] = sx < 0 ? (Real)W<LAT>(q) * rhoL : sq[off];
+        else if constexpr (ex < 0)
+            fs[q] = sx >= nx ? (Real)W<LAT>(q) * rhoR : sq[off];
         else
-            fs[q] = src[q * nn + (int64_t)sy * nx + sx];
+            fs[q] = sq[off];
     });
 
-    // moments
-    Real rho = 0, jx = 0, jy = 0, jz = 0;
+    // moments, from the pair sums s and differences d
+    Real rho = fs[0], jx = 0, jy = 0, jz = 0;
     Real pxx = 0, pxy = 0, pxz = 0, pyy = 0, pyz = 0, pzz = 0;
     Real q3[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     static_for<Q>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
-        constexpr int ex = E<LAT>(q, 0), ey = E<LAT>(q, 1), ez = E<LAT>(q, 2);
-        const Real f = fs[q];
-        rho += f;
-        if constexpr (ex != 0) jx += f * (Real)(R * ex);
-        if constexpr (ey != 0) jy += f * (Real)(R * ey);
-        if constexpr (ez != 0) jz += f * (Real)(R * ez);
-        if constexpr (ex != 0) pxx += f * (Real)(R * R * ex * ex);
-        if constexpr (ex * ey != 0) pxy += f * (Real)(R * R * ex * ey);
-        if constexpr (ex * ez != 0) pxz += f * (Real)(R * R * ex * ez);
-        if constexpr (ey != 0) pyy += f * (Real)(R * R * ey * ey);
-        if constexpr (ey * ez != 0) pyz += f * (Real)(R * R * ey * ez);
-        if constexpr (ez != 0) pzz += f * (Real)(R * R * ez * ez);
-        if constexpr (LAT::ORDER >= 3) {
-            constexpr double R3 = R * R * R;
-            if constexpr (ex != 0) q3[0] += f * (Real)(R3 * ex * ex * ex);
-            if constexpr (ex * ey != 0) q3[1] += f * (Real)(R3 * ex * ex * ey);
-            if constexpr (ex * ez != 0) q3[2] += f * (Real)(R3 * ex * ex * ez);
-            if constexpr (ex * ey != 0) q3[3] += f * (Real)(R3 * ex * ey * ey);
-            if constexpr (ex * ey * ez != 0) q3[4] += f * (Real)(R3 * ex * ey * ez);
-            if constexpr (ex * ez != 0) q3[5] += f * (Real)(R3 * ex * ez * ez);
-            if constexpr (ey != 0) q3[6] += f * (Real)(R3 * ey * ey * ey);
-            if constexpr (ey * ez != 0) q3[7] += f * (Real)(R3 * ey * ey * ez);
-            if constexpr (ey * ez != 0) q3[8] += f * (Real)(R3 * ey * ez * ez);
-            if constexpr (ez != 0) q3[9] += f * (Real)(R3 * ez * ez * ez);
+        constexpr int p = opp<LAT>(q);
+        if constexpr (q != 0 && q < p) {
+            constexpr int ex = E<LAT>(q, 0), ey = E<LAT>(q, 1), ez = E<LAT>(q, 2);
+            const Real sm = fs[q] + fs[p], df = fs[q] - fs[p];
+            rho += sm;
+            if constexpr (ex != 0) jx += df * (Real)(R * ex);
+            if constexpr (ey != 0) jy += df * (Real)(R * ey);
+            if constexpr (ez != 0) jz += df * (Real)(R * ez);
+            if constexpr (ex != 0) pxx += sm * (Real)(R * R * ex * ex);
+            if constexpr (ex * ey != 0) pxy += sm * (Real)(R * R * ex * ey);
+            if constexpr (ex * ez != 0) pxz += sm * (Real)(R * R * ex * ez);
+            if constexpr (ey != 0) pyy += sm * (Real)(R * R * ey * ey);
+            if constexpr (ey * ez != 0) pyz += sm * (Real)(R * R * ey * ez);
+            if constexpr (ez != 0) pzz += sm * (Real)(R * R * ez * ez);
+            if constexpr (LAT::ORDER >= 3) {
+                constexpr double R3 = R * R * R;
+                if constexpr (ex != 0) q3[0] += df * (Real)(R3 * ex * ex * ex);
+                if constexpr (ex * ey != 0) q3[1] += df * (Real)(R3 * ex * ex * ey);
+                if constexpr (ex * ez != 0) q3[2] += df * (Real)(R3 * ex * ex * ez);
+                if constexpr (ex * ey != 0) q3[3] += df * (Real)(R3 * ex * ey * ey);
+                if constexpr (ex * ey * ez != 0) q3[4] += df * (Real)(R3 * ex * ey * ez);
+                if constexpr (ex * ez != 0) q3[5] += df * (Real)(R3 * ex * ez * ez);
+                if constexpr (ey != 0) q3[6] += df * (Real)(R3 * ey * ey * ey);
+                if constexpr (ey * ez != 0) q3[7] += df * (Real)(R3 * ey * ey * ez);
+                if constexpr (ey * ez != 0) q3[8] += df * (Real)(R3 * ey * ez * ez);
+                if constexpr (ez != 0) q3[9] += df * (Real)(R3 * ez * ez * ez);
+            }
         }
     });
 
     const Real gy = a.g_step;
-    const Real inv_rho = (Real)1 / rho;
-    const Real ux = jx * inv_rho, uy = (jy + (Real)0.5 * rho * gy) * inv_rho, uz = jz * inv_rho;
-    const Real u2 = ux * ux + uy * uy + uz * uz;
-    const Real a1y = (Real)-0.5 * rho * gy;  // H1 part of f_neq
-    // a2 = Pi - rho (uu + I)
-    const Real bxx = pxx - rho * (ux * ux + (Real)1), byy = pyy - rho * (uy * uy + (Real)1),
-               bzz = pzz - rho * (uz * uz + (Real)1);
-    const Real bxy = pxy - rho * ux * uy, bxz = pxz - rho * ux * uz, byz = pyz - rho * uy * uz;
-    const Real tr2 = bxx + byy + bzz;
-    // a3 = Qm - rho(uuu + sym(u I)) - sym(a1 I); a1 has only a y component
-    Real c3[10];
-    Real t3x = 0, t3y = 0, t3z = 0;
-    if constexpr (LAT::ORDER >= 3) {
-        c3[0] = q3[0] - rho * (ux * ux * ux + (Real)3 * ux);
-        c3[1] = q3[1] - rho * (ux * ux * uy + uy) - a1y;
-        c3[2] = q3[2] - rho * (ux * ux * uz + uz);
-        c3[3] = q3[3] - rho * (ux * uy * uy + ux);
-        c3[4] = q3[4] - rho * (ux * uy * uz);
-        c3[5] = q3[5] - rho * (ux * uz * uz + ux);
-        c3[6] = q3[6] - rho * (uy * uy * uy + (Real)3 * uy) - (Real)3 * a1y;
-        c3[7] = q3[7] - rho * (uy * uy * uz + uz);
-        c3[8] = q3[8] - rho * (uy * uz * uz + uy) - a1y;
-        c3[9] = q3[9] - rho * (uz * uz * uz + (Real)3 * uz);
-        t3x = c3[0] + c3[3] + c3[5];
-        t3y = c3[1] + c3[6] + c3[8];
-        t3z = c3[2] + c3[7] + c3[9];
-    }
     const Real om = a.om;
     const Real of = a.of;
-    const Real gu = gy * uy;
-    Real* __restrict__ dst = a.dst;
+    const Real inv_rho = (Real)1 / rho;
+    const Real ux = jx * inv_rho, uy = (jy + (Real)0.5 * rho * gy) * inv_rho, uz = jz * inv_rho;
+    const Real a1y = (Real)-0.5 * rho * gy;  // H1 part of f_neq
+    const Real rg = rho * gy;
+    // combined coefficients of the post-collision series
+    const Real A0 = rho;
+    const Real A1x = rho * ux, A1y = rho * uy + om * a1y + of * rg, A1z = rho * uz;
+    // a2 = Pi - rho (uu + I); A2 = rho uu + om a2 + of rho (gu + ug)
+    const Real Axx = rho * ux * ux + om * (pxx - rho * (ux * ux + (Real)1));
+    const Real Ayy = rho * uy * uy + om * (pyy - rho * (uy * uy + (Real)1)) + of * (Real)2 * rg * uy;
+    const Real Azz = rho * uz * uz + om * (pzz - rho * (uz * uz + (Real)1));
+    const Real Axy = rho * ux * uy + om * (pxy - rho * ux * uy) + of * rg * ux;
+    const Real Axz = rho * ux * uz + om * (pxz - rho * ux * uz);
+    const Real Ayz = rho * uy * uz + om * (pyz - rho * uy * uz) + of * rg * uz;
+    const Real tr2 = Axx + Ayy + Azz;
+    const Real E0 = A0 - (Real)0.5 * tr2;  // even part without the xi xi terms
+    // a3 = Qm - rho(uuu + sym(u I)) - sym(a1 I); A3 = rho uuu + om a3 + of rho sym(guu)
+    Real B3[10];
+    Real t3x = 0, t3y = 0, t3z = 0;
+    if constexpr (LAT::ORDER >= 3) {
+        const Real c0 = q3[0] - rho * (ux * ux * ux + (Real)3 * ux);
+        const Real c1 = q3[1] - rho * (ux * ux * uy + uy) - a1y;
+        const Real c2 = q3[2] - rho * (ux * ux * uz + uz);
+        const Real c3 = q3[3] - rho * (ux * uy * uy + ux);
+        const Real c4 = q3[4] - rho * (ux * uy * uz);
+        const Real c5 = q3[5] - rho * (ux * uz * uz + ux);
+        const Real c6 = q3[6] - rho * (uy * uy * uy + (Real)3 * uy) - (Real)3 * a1y;
+        const Real c7 = q3[7] - rho * (uy * uy * uz + uz);
+        const Real c8 = q3[8] - rho * (uy * uz * uz + uy) - a1y;
+        const Real c9 = q3[9] - rho * (uz * uz * uz + (Real)3 * uz);
+        B3[0] = rho * ux * ux * ux + om * c0;
+        B3[1] = rho * ux * ux * uy + om * c1 + of * rg * ux * ux;
+        B3[2] = rho * ux * ux * uz + om * c2;
+        B3[3] = rho * ux * uy * uy + om * c3 + of * (Real)2 * rg * ux * uy;
+        B3[4] = rho * ux * uy * uz + om * c4 + of * rg * ux * uz;
+        B3[5] = rho * ux * uz * uz + om * c5;
+        B3[6] = rho * uy * uy * uy + om * c6 + of * (Real)3 * rg * uy * uy;
+        B3[7] = rho * uy * uy * uz + om * c7 + of * (Real)2 * rg * uy * uz;
+        B3[8] = rho * uy * uz * uz + om * c8 + of * rg * uz * uz;
+        B3[9] = rho * uz * uz * uz + om * c9;
+        t3x = B3[0] + B3[3] + B3[5];
+        t3y = B3[1] + B3[6] + B3[8];
+        t3z = B3[2] + B3[7] + B3[9];
+    }
+    Real* __restrict__ dst = a.dst + node;
 
     static_for<Q>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
-        constexpr int ex = E<LAT>(q, 0), ey = E<LAT>(q, 1), ez = E<LAT>(q, 2);
-        constexpr double X = R * ex, Y = R * ey, Z = R * ez;
-        Real xu = (Real)0;
-        if constexpr (ex != 0) xu += (Real)X * ux;
-        if constexpr (ey != 0) xu += (Real)Y * uy;
-        if constexpr (ez != 0) xu += (Real)Z * uz;
-        Real feq = (Real)1 + xu + (Real)0.5 * (xu * xu - u2);
-        if constexpr (LAT::ORDER >= 3) feq += (Real)(1.0 / 6.0) * xu * (xu * xu - (Real)3 * u2);
-        // regularised non-equilibrium part
-        Real h2 = -tr2;
-        if constexpr (ex != 0) h2 += (Real)(X * X) * bxx;
-        if constexpr (ey != 0) h2 += (Real)(Y * Y) * byy;
-        if constexpr (ez != 0) h2 += (Real)(Z * Z) * bzz;
-        if constexpr (ex * ey != 0) h2 += (Real)(2 * X * Y) * bxy;
-        if constexpr (ex * ez != 0) h2 += (Real)(2 * X * Z) * bxz;
-        if constexpr (ey * ez != 0) h2 += (Real)(2 * Y * Z) * byz;
-        Real neq = (Real)0.5 * h2;
-        if constexpr (ey != 0) neq += (Real)Y * a1y;
-        if constexpr (LAT::ORDER >= 3) {
-            Real h3 = (Real)0;
-            if constexpr (ex != 0) h3 += (Real)(X * X * X) * c3[0] - (Real)(3 * X) * t3x;
-            if constexpr (ex * ey != 0) h3 += (Real)(3 * X * X * Y) * c3[1];
-            if constexpr (ex * ez != 0) h3 += (Real)(3 * X * X * Z) * c3[2];
-            if constexpr (ex * ey != 0) h3 += (Real)(3 * X * Y * Y) * c3[3];
-            if constexpr (ex * ey * ez != 0) h3 += (Real)(6 * X * Y * Z) * c3[4];
-            if constexpr (ex * ez != 0) h3 += (Real)(3 * X * Z * Z) * c3[5];
-            if constexpr (ey != 0) h3 += (Real)(Y * Y * Y) * c3[6] - (Real)(3 * Y) * t3y;
-            if constexpr (ey * ez != 0) h3 += (Real)(3 * Y * Y * Z) * c3[7];
-            if constexpr (ey * ez != 0) h3 += (Real)(3 * Y * Z * Z) * c3[8];
-            if constexpr (ez != 0) h3 += (Real)(Z * Z * Z) * c3[9] - (Real)(3 * Z) * t3z;
-            neq += (Real)(1.0 / 6.0) * h3;
+        constexpr int p = opp<LAT>(q);
+        if constexpr (q == 0) {
+            dst[0] = (Real)W<LAT>(0) * E0;
+        } else if constexpr (q < p) {
+            constexpr int ex = E<LAT>(q, 0), ey = E<LAT>(q, 1), ez = E<LAT>(q, 2);
+            constexpr double X = R * ex, Y = R * ey, Z = R * ez;
+            // even part: A0 + A2:H2/2
+            Real h2 = (Real)0;
+            if constexpr (ex != 0) h2 += (Real)(0.5 * X * X) * Axx;
+            if constexpr (ey != 0) h2 += (Real)(0.5 * Y * Y) * Ayy;
+            if constexpr (ez != 0) h2 += (Real)(0.5 * Z * Z) * Azz;
+            if constexpr (ex * ey != 0) h2 += (Real)(X * Y) * Axy;
+            if constexpr (ex * ez != 0) h2 += (Real)(X * Z) * Axz;
+            if constexpr (ey * ez != 0) h2 += (Real)(Y * Z) * Ayz;
+            const Real ev = E0 + h2;
+            // odd part: A1.xi + A3:H3/6
+            Real od = (Real)0;
+            if constexpr (ex != 0) od += (Real)X * A1x;
+            if constexpr (ey != 0) od += (Real)Y * A1y;
+            if constexpr (ez != 0) od += (Real)Z * A1z;
+            if constexpr (LAT::ORDER >= 3) {
+                constexpr double s6 = 1.0 / 6.0;
+                if constexpr (ex != 0) od += (Real)(s6 * X * X * X) * B3[0] - (Real)(0.5 * X) * t3x;
+                if constexpr (ex * ey != 0) od += (Real)(0.5 * X * X * Y) * B3[1];
+                if constexpr (ex * ez != 0) od += (Real)(0.5 * X * X * Z) * B3[2];
+                if constexpr (ex * ey != 0) od += (Real)(0.5 * X * Y * Y) * B3[3];
+                if constexpr (ex * ey * ez != 0) od += (Real)(X * Y * Z) * B3[4];
+                if constexpr (ex * ez != 0) od += (Real)(0.5 * X * Z * Z) * B3[5];
+                if constexpr (ey != 0) od += (Real)(s6 * Y * Y * Y) * B3[6] - (Real)(0.5 * Y) * t3y;
+                if constexpr (ey * ez != 0) od += (Real)(0.5 * Y * Y * Z) * B3[7];
+                if constexpr (ey * ez != 0) od += (Real)(0.5 * Y * Z * Z) * B3[8];
+                if constexpr (ez != 0) od += (Real)(s6 * Z * Z * Z) * B3[9] - (Real)(0.5 * Z) * t3z;
+            }
+            constexpr double wq = W<LAT>(q);
+            dst[(int64_t)q * nn] = (Real)wq * (ev + od);
+            dst[(int64_t)p * nn] = (Real)wq * (ev - od);
         }
-        // Hermite force term, g along y
-        const Real gx = (ey != 0) ? (Real)Y * gy : (Real)0;  // g . xi
-        Real F = gx + gx * xu - gu;
-        if constexpr (LAT::ORDER >= 3)
-            F += (Real)0.5 * (gx * xu * xu - gx * u2 - (Real)2 * xu * gu);
-        const Real out = (Real)W<LAT>(q) * (rho * feq + om * neq + of * rho * F);
-        dst[q * nn + node] = out;
     });
 }
 

@@ -8,18 +8,16 @@
 // the populations f_a = w_a sum_{n<=N} a^(n):H^(n)(xi_a)/n! (Eq. discretefunctions) are
 // evaluated in the state precision.
 //
-// LB2DSMC (Sec. 2.2, Table 1) in two launches:
-//   k_l2d_coef   one warp per coupling cell: mean populations of the cell's lb_ratio^2
-//                nodes, rho and u, the comoving coefficients a2 = sum f c c / rho - I and
-//                a3 = sum f c c c / rho (c = xi - u), M, C = 1 + 30 M (Eq. C), all in the
-//                state precision with one fixed pairwise order of every population sum, and
-//                the particle count floor(rho ppc + U);
-//   k_l2d_sample one block per coupling cell: the cell's trial stream is evaluated 128
-//                trials at a time: Box-Muller xi from the unit Maxwellian, accepted when
-//                C R <= G(xi), G = 1 + a2:H2/2 + a3:H3/6 (Eq. distr_outeq) in the state
-//                precision; the k-th accepted trial becomes the k-th particle of the cell's
-//                bin (replacing the old ones), velocity xi + u (Eq. step6 in c_th units),
-//                position uniform in the cell from the same trial's draws.
+// LB2DSMC (Sec. 2.2, Table 1), k_l2d: one block per coupling cell. Warp 0 forms the mean
+// populations of the cell's lb_ratio^2 nodes, rho and u, the comoving coefficients
+// a2 = sum f c c / rho - I and a3 = sum f c c c / rho (c = xi - u), M, C = 1 + 30 M (Eq. C),
+// all in the state precision with one fixed pairwise order of every population sum, and the
+// particle count floor(rho ppc + U); meanwhile the other warps draw their first trials. The
+// cell's trial stream is then evaluated 256 trials at a time: Box-Muller xi from the unit
+// Maxwellian, accepted when C R <= G(xi), G = 1 + a2:H2/2 + a3:H3/6 (Eq. distr_outeq) in
+// the state precision; the k-th accepted trial becomes the k-th particle of the cell's bin
+// (replacing the old ones), velocity xi + u (Eq. step6 in c_th units), position uniform in
+// the cell from the same trial's draws.
 // Draws are keyed by (cell, step, purpose, trial index), so the results do not depend on
 // the launch shape.
 #include "hyb_internal.cuh"
@@ -173,125 +171,6 @@ __device__ __forceinline__ double warp_max_abs(double x) {
     return m;
 }
 
-// LB2DSMC coefficients (Table 1 step 1): one warp per coupling cell, state precision. Lane
-// l holds the cell-mean populations q = l and l + 32 (zero past Q); each population sum adds
-// the lane's two terms and then reduces over the lanes (halving_sum), which is the oracle's
-// pairwise order. Products are (f c_i) c_j and ((f c_i) c_j) c_k with i <= j <= k.
-template <typename Real, class LAT>
-__global__ void __launch_bounds__(128) k_l2d_coef(MapArgs<Real> a) {
-    constexpr int Q = LAT::Q;
-    constexpr int NM = LAT::ORDER >= 3 ? 16 : 6;  // distinct second and third moments
-    constexpr int NP = NM > 8 ? 16 : 8;           // padded to a power of two
-    constexpr int SH = NP == 16 ? 1 : 2;          // lane >> SH: moment held after the sum
-    const unsigned lane = lane_id();
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    const uint32_t t_step = a.ctrl[CTRL_STEP];
-    const int r = a.lb_ratio;
-    const int q0 = (int)lane, q1 = (int)lane + 32;
-    const bool v0 = q0 < Q, v1 = q1 < Q;
-    Real xi0[3] = {0, 0, 0}, xi1[3] = {0, 0, 0};
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        if (v0) xi0[i] = (Real)(a.r_lat * (double)lat_e<LAT>(q0, i));
-        if (v1) xi1[i] = (Real)(a.r_lat * (double)lat_e<LAT>(q1, i));
-    }
-    for (int ci = gw; ci < a.n; ci += nw) {
-        const int32_t cell = a.list[ci];
-        if (cell < 0 || cell >= a.ncx * a.ncy) {
-            if (lane == 0) {
-                atomicOr(&a.ctrl[CTRL_STATUS], HYB_ST_BAD_INPUT);
-                a.ctrl[CTRL_L2D_BAD] = 1;
-            }
-            continue;
-        }
-        const int ix = cell % a.ncx, iy = cell / a.ncx;
-        // mean populations of the cell's nodes, summed in node order (dy, dx)
-        Real p0[4], p1[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            p0[k] = 0;
-            p1[k] = 0;
-            if (k < r * r) {
-                const int64_t node = (int64_t)(iy * r + k / r) * a.nx + (ix * r + k % r);
-                if (v0) p0[k] = a.f[(int64_t)q0 * a.nnodes + node];
-                if (v1) p1[k] = a.f[(int64_t)q1 * a.nnodes + node];
-            }
-        }
-        Real s0 = 0, s1 = 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (k < r * r) {
-                s0 += p0[k];
-                s1 += p1[k];
-            }
-        const Real nn = (Real)(r * r);
-        const Real f0 = v0 ? s0 / nn : (Real)0;
-        const Real f1 = v1 ? s1 / nn : (Real)0;
-        // rho and j; lanes 0-7 end with rho, 8-15 jx, 16-23 jy, 24-31 jz
-        Real t4[4];
-        t4[0] = f0 + f1;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) t4[1 + i] = f0 * xi0[i] + f1 * xi1[i];
-        halving_sum<Real, 4>(t4, lane);
-        const Real rho = __shfl_sync(kFull, t4[0], 0);
-        Real u[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) u[i] = __shfl_sync(kFull, t4[0], 8 * (i + 1)) / rho;
-        Real c0[3], c1[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            c0[i] = xi0[i] - u[i];
-            c1[i] = xi1[i] - u[i];
-        }
-        Real tm[NP];
-        int o = 0;
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = i; j < 3; ++j, ++o) {
-                const Real lo = v0 ? (f0 * c0[i]) * c0[j] : (Real)0;
-                const Real hi = v1 ? (f1 * c1[i]) * c1[j] : (Real)0;
-                tm[o] = lo + hi;
-            }
-        if constexpr (NM > 6) {
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-                for (int j = i; j < 3; ++j)
-#pragma unroll
-                    for (int k = j; k < 3; ++k, ++o) {
-                        const Real lo = v0 ? ((f0 * c0[i]) * c0[j]) * c0[k] : (Real)0;
-                        const Real hi = v1 ? ((f1 * c1[i]) * c1[j]) * c1[k] : (Real)0;
-                        tm[o] = lo + hi;
-                    }
-        }
-#pragma unroll
-        for (int k = NM; k < NP; ++k) tm[k] = 0;
-        halving_sum<Real, NP>(tm, lane);
-        const int mom = (int)(lane >> SH);
-        Real val = tm[0] / rho;
-        if (mom == 0 || mom == 3 || mom == 5) val = val - (Real)1;
-        const Real M = warp_max_abs(mom < NM ? val : (Real)0);
-        GradRec& g = a.grad[ci];
-        Real* pv = reinterpret_cast<Real*>(g.v);
-        if (mom < NM && (lane & ((1u << SH) - 1u)) == 0) pv[GR_A2 + mom] = val;
-        if (lane == 0) {
-            if (NM == 6)
-                for (int k = 0; k < 10; ++k) pv[GR_A3 + k] = 0;
-            pv[GR_U] = u[0];
-            pv[GR_U + 1] = u[1];
-            pv[GR_U + 2] = u[2];
-            pv[GR_C] = (Real)1 + (Real)30 * M;
-            const double ur = u01d(draw(a.seed, (uint32_t)cell, t_step, TAG_L2D_ROUND, 0, 0).x);
-            const double ne = floor((double)rho * (double)a.ppc + ur);
-            g.rho = (double)rho;
-            g.nnew = ne > 0.0 ? (uint32_t)ne : 0u;
-            g.pad = 0;
-        }
-    }
-}
-
 // G of Eq. distr_outeq in the state precision, from the comoving coefficients packed by
 // symmetry, with the grouping of the Table 1 sums fixed (distinct entries times their
 // multiplicity) so that the accept decision is reproducible.
@@ -316,7 +195,7 @@ __device__ __forceinline__ Real grad_G(const Real* a2, const Real* a3, Real X, R
     return G;
 }
 
-constexpr int kSampleWarps = 4;
+constexpr int kL2DWarps = 8;
 
 // Position of the k-th set bit (k >= 1) of m, which has at least k set bits.
 __device__ __forceinline__ int nth_set_bit(unsigned m, int k) {
@@ -333,14 +212,114 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int k) {
     return pos;
 }
 
-// One block per coupling cell: the cell's trial stream is evaluated 128 trials at a time;
-// the k-th accepted trial becomes the k-th particle of the cell's bin, replacing the old
-// ones. Nothing is written if a listed cell index was invalid (the coefficient kernel
-// flagged it).
+// Table 1 step 1 for the cell `cell`, by one warp, in the state precision. Lane l holds the
+// cell-mean populations q = l and l + 32 (zero past Q); each population sum adds the lane's
+// two terms and then reduces over the lanes (halving_sum), which is the oracle's pairwise
+// order. Products are (f c_i) c_j and ((f c_i) c_j) c_k with i <= j <= k. Returns, in every
+// lane, the packed values (lane k < 20 holds value k: a2[6], a3[10], u[3], C) and rho.
 template <typename Real, class LAT>
-__global__ void __launch_bounds__(kSampleWarps * 32) k_l2d_sample(MapArgs<Real> a) {
-    __shared__ unsigned s_am[kSampleWarps], s_em[kSampleWarps], s_vm[kSampleWarps];
-    if (a.ctrl[CTRL_L2D_BAD]) return;
+__device__ __forceinline__ void grad_coefficients(const MapArgs<Real>& a, int cell, unsigned lane,
+                                                  Real& mine, Real& rho_out) {
+    constexpr int Q = LAT::Q;
+    constexpr int NM = LAT::ORDER >= 3 ? 16 : 6;  // distinct second and third moments
+    constexpr int NP = NM > 8 ? 16 : 8;           // padded to a power of two
+    constexpr int SH = NP == 16 ? 1 : 2;          // lane >> SH: moment held after the sum
+    const int r = a.lb_ratio;
+    const int q0 = (int)lane, q1 = (int)lane + 32;
+    const bool v0 = q0 < Q, v1 = q1 < Q;
+    Real xi0[3] = {0, 0, 0}, xi1[3] = {0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        if (v0) xi0[i] = (Real)(a.r_lat * (double)lat_e<LAT>(q0, i));
+        if (v1) xi1[i] = (Real)(a.r_lat * (double)lat_e<LAT>(q1, i));
+    }
+    const int ix = cell % a.ncx, iy = cell / a.ncx;
+    // mean populations of the cell's nodes, summed in node order (dy, dx)
+    Real p0[4], p1[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        p0[k] = 0;
+        p1[k] = 0;
+        if (k < r * r) {
+            const int64_t node = (int64_t)(iy * r + k / r) * a.nx + (ix * r + k % r);
+            if (v0) p0[k] = a.f[(int64_t)q0 * a.nnodes + node];
+            if (v1) p1[k] = a.f[(int64_t)q1 * a.nnodes + node];
+        }
+    }
+    Real s0 = 0, s1 = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (k < r * r) {
+            s0 += p0[k];
+            s1 += p1[k];
+        }
+    const Real nn = (Real)(r * r);
+    const Real f0 = v0 ? s0 / nn : (Real)0;
+    const Real f1 = v1 ? s1 / nn : (Real)0;
+    // rho and j; lanes 0-7 end with rho, 8-15 jx, 16-23 jy, 24-31 jz
+    Real t4[4];
+    t4[0] = f0 + f1;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) t4[1 + i] = f0 * xi0[i] + f1 * xi1[i];
+    halving_sum<Real, 4>(t4, lane);
+    const Real rho = __shfl_sync(kFull, t4[0], 0);
+    Real u[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) u[i] = __shfl_sync(kFull, t4[0], 8 * (i + 1)) / rho;
+    Real c0[3], c1[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        c0[i] = xi0[i] - u[i];
+        c1[i] = xi1[i] - u[i];
+    }
+    Real tm[NP];
+    int o = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j, ++o) {
+            const Real lo = v0 ? (f0 * c0[i]) * c0[j] : (Real)0;
+            const Real hi = v1 ? (f1 * c1[i]) * c1[j] : (Real)0;
+            tm[o] = lo + hi;
+        }
+    if constexpr (NM > 6) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = i; j < 3; ++j)
+#pragma unroll
+                for (int k = j; k < 3; ++k, ++o) {
+                    const Real lo = v0 ? ((f0 * c0[i]) * c0[j]) * c0[k] : (Real)0;
+                    const Real hi = v1 ? ((f1 * c1[i]) * c1[j]) * c1[k] : (Real)0;
+                    tm[o] = lo + hi;
+                }
+    }
+#pragma unroll
+    for (int k = NM; k < NP; ++k) tm[k] = 0;
+    halving_sum<Real, NP>(tm, lane);
+    const int mom = (int)(lane >> SH);
+    Real val = tm[0] / rho;
+    if (mom == 0 || mom == 3 || mom == 5) val = val - (Real)1;
+    const Real M = warp_max_abs(mom < NM ? val : (Real)0);
+    // gather the packed values: lane k < 16 takes moment k, lanes 16-18 u, lane 19 C
+    const Real mv = __shfl_sync(kFull, val, (int)((lane & 15u) << SH));
+    mine = lane < (unsigned)NM ? mv : (Real)0;
+    if (lane == GR_U) mine = u[0];
+    if (lane == GR_U + 1) mine = u[1];
+    if (lane == GR_U + 2) mine = u[2];
+    if (lane == GR_C) mine = (Real)1 + (Real)30 * M;
+    rho_out = rho;
+}
+
+// LB2DSMC for the listed cells: one block per cell (see the top of this file). An invalid
+// cell index is skipped and flagged; a cell whose new count exceeds its bin keeps its
+// particles and raises the capacity status. The Grad record of each listed cell is written
+// to a.grad.
+template <typename Real, class LAT>
+__global__ void __launch_bounds__(kL2DWarps * 32) k_l2d(MapArgs<Real> a) {
+    __shared__ unsigned s_am[kL2DWarps], s_em[kL2DWarps], s_vm[kL2DWarps];
+    __shared__ Real s_c[20];
+    __shared__ uint32_t s_nnew;
     const uint32_t t_step = a.ctrl[CTRL_STEP];
     const unsigned lane = lane_id();
     const unsigned lt = (1u << lane) - 1u;
@@ -350,43 +329,80 @@ __global__ void __launch_bounds__(kSampleWarps * 32) k_l2d_sample(MapArgs<Real> 
     uint32_t flags = 0;
     int32_t dlive = 0;
     for (int ci = blockIdx.x; ci < a.n; ci += gridDim.x) {
-        const uint32_t cell = (uint32_t)a.list[ci];
-        const GradRec& g = a.grad[ci];
-        const uint32_t nnew = g.nnew;
+        const int32_t icell = a.list[ci];
+        if (icell < 0 || icell >= a.ncx * a.ncy) {
+            flags |= HYB_ST_BAD_INPUT;
+            continue;
+        }
+        const uint32_t cell = (uint32_t)icell;
+        const uint32_t old = threadIdx.x == 0 ? a.count[cell] : 0u;
+        if (w == 0) {
+            Real mine, rho;
+            grad_coefficients<Real, LAT>(a, icell, lane, mine, rho);
+            GradRec& g = a.grad[ci];
+            Real* pv = reinterpret_cast<Real*>(g.v);
+            if (lane < 20u) {
+                s_c[lane] = mine;
+                pv[lane] = mine;
+            }
+            if (lane == 0) {
+                const double ur = u01d(draw(a.seed, cell, t_step, TAG_L2D_ROUND, 0, 0).x);
+                const double ne = floor((double)rho * (double)a.ppc + ur);
+                const uint32_t nnew = ne > 0.0 ? (uint32_t)ne : 0u;
+                s_nnew = nnew;
+                g.rho = (double)rho;
+                g.nnew = nnew;
+                g.pad = 0;
+            }
+        }
+        // the first trial of this thread does not depend on the coefficients
+        Real X = 0, Y = 0, Z = 0;
+        uint4 r2;
+        {
+            const uint4 r1 = draw(a.seed, cell, t_step, TAG_L2D_VEL, threadIdx.x, 0);
+            r2 = draw(a.seed, cell, t_step, TAG_L2D_VEL, threadIdx.x, 1);
+            Real spare;
+            gauss_pair<Real>(r1.x, r1.y, X, Y);
+            gauss_pair<Real>(r1.z, r1.w, Z, spare);
+        }
+        __syncthreads();
+        const uint32_t nnew = s_nnew;
+        Real a2[6], a3[10];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) a2[k] = s_c[GR_A2 + k];
+#pragma unroll
+        for (int k = 0; k < 10; ++k) a3[k] = s_c[GR_A3 + k];
+        const Real C = s_c[GR_C];
+        const Real ux = s_c[GR_U], uy = s_c[GR_U + 1], uz = s_c[GR_U + 2];
+        __syncthreads();  // s_c and s_nnew are rewritten for the next cell
         if (nnew > bin) {  // the cell keeps its particles
             flags |= HYB_ST_CAPACITY;
             continue;
         }
-        const Real* pv = reinterpret_cast<const Real*>(g.v);
-        Real a2[6], a3[10];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) a2[k] = pv[GR_A2 + k];
-#pragma unroll
-        for (int k = 0; k < 10; ++k) a3[k] = pv[GR_A3 + k];
-        const Real C = pv[GR_C];
-        const Real ux = pv[GR_U], uy = pv[GR_U + 1], uz = pv[GR_U + 2];
         const int64_t out0 = (int64_t)cell * bin;
         const Real fx = (Real)(cell % (uint32_t)a.ncx), fy = (Real)(cell / (uint32_t)a.ncx);
         const uint64_t cap64 = 1000ull * nnew;
         const uint32_t cap = cap64 < 0xFFFFFFull ? (uint32_t)cap64 : 0xFFFFFFu;
         uint32_t produced = 0, j0 = 0;
+        bool first = true;
         while (produced < nnew && j0 < cap) {
             const uint32_t j = j0 + threadIdx.x;
             const bool valid = j < cap;
             bool acc = false, env = false;
-            Real X = 0, Y = 0, Z = 0;
-            uint4 r2 = make_uint4(0, 0, 0, 0);
             if (valid) {
-                const uint4 r1 = draw(a.seed, cell, t_step, TAG_L2D_VEL, j, 0);
-                r2 = draw(a.seed, cell, t_step, TAG_L2D_VEL, j, 1);
-                Real spare;
-                gauss_pair<Real>(r1.x, r1.y, X, Y);
-                gauss_pair<Real>(r1.z, r1.w, Z, spare);
+                if (!first) {
+                    const uint4 r1 = draw(a.seed, cell, t_step, TAG_L2D_VEL, j, 0);
+                    r2 = draw(a.seed, cell, t_step, TAG_L2D_VEL, j, 1);
+                    Real spare;
+                    gauss_pair<Real>(r1.x, r1.y, X, Y);
+                    gauss_pair<Real>(r1.z, r1.w, Z, spare);
+                }
                 const Real G = grad_G<Real, LAT::ORDER>(a2, a3, X, Y, Z);
                 const Real R = (Real)u01f(r2.x);
                 env = G > C;
                 acc = C * R <= G;
             }
+            first = false;
             const unsigned am = __ballot_sync(kFull, acc);
             const unsigned em = __ballot_sync(kFull, env);
             const unsigned vm = __ballot_sync(kFull, valid);
@@ -398,7 +414,7 @@ __global__ void __launch_bounds__(kSampleWarps * 32) k_l2d_sample(MapArgs<Real> 
             __syncthreads();
             uint32_t before = 0, total = 0;
 #pragma unroll
-            for (int v = 0; v < kSampleWarps; ++v) {
+            for (int v = 0; v < kL2DWarps; ++v) {
                 const uint32_t cv = (uint32_t)__popc(s_am[v]);
                 if (v < w) before += cv;
                 total += cv;
@@ -413,41 +429,47 @@ __global__ void __launch_bounds__(kSampleWarps * 32) k_l2d_sample(MapArgs<Real> 
                 a.vy[slot] = Y + uy;
                 a.vz[slot] = Z + uz;
             }
-            if (threadIdx.x == 0) {
-                // trials consumed this round: up to the need-th accepted one, or all valid ones
-                uint32_t used = 0, envc = 0;
+            if (w == 0) {
+                // trials consumed this round (up to the need-th accepted one, or all valid
+                // ones) and envelope violations among them; lane v looks at warp v's trials
+                const unsigned amv = lane < (unsigned)kL2DWarps ? s_am[lane] : 0u;
+                const unsigned emv = lane < (unsigned)kL2DWarps ? s_em[lane] : 0u;
+                const unsigned vmv = lane < (unsigned)kL2DWarps ? s_vm[lane] : 0u;
+                const uint32_t cv = (uint32_t)__popc(amv);
+                uint32_t inc = cv;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t t = __shfl_up_sync(kFull, inc, o);
+                    if (lane >= (unsigned)o) inc += t;
+                }
+                const uint32_t exc = inc - cv;
+                uint32_t mu = (uint32_t)__popc(vmv), me = (uint32_t)__popc(emv & vmv);
                 if (total >= need) {
-                    uint32_t left = need;
-                    for (int v = 0; v < kSampleWarps; ++v) {
-                        const uint32_t cv = (uint32_t)__popc(s_am[v]);
-                        if (left > cv) {
-                            left -= cv;
-                            used += 32;
-                            envc += (uint32_t)__popc(s_em[v] & s_vm[v]);
-                            continue;
-                        }
-                        const int bit = nth_set_bit(s_am[v], (int)left);
+                    const unsigned last = __ballot_sync(kFull, exc < need && need <= inc);
+                    const unsigned vl = (unsigned)(__ffs(last) - 1);
+                    if (lane == vl) {
+                        const int bit = nth_set_bit(amv, (int)(need - exc));
                         const unsigned upto = bit == 31 ? 0xFFFFFFFFu : ((2u << bit) - 1u);
-                        used += (uint32_t)bit + 1u;
-                        envc += (uint32_t)__popc(s_em[v] & upto);
-                        break;
-                    }
-                } else {
-                    for (int v = 0; v < kSampleWarps; ++v) {
-                        used += (uint32_t)__popc(s_vm[v]);
-                        envc += (uint32_t)__popc(s_em[v] & s_vm[v]);
+                        mu = (uint32_t)bit + 1u;
+                        me = (uint32_t)__popc(emv & upto);
+                    } else if (lane > vl) {
+                        mu = 0;
+                        me = 0;
                     }
                 }
-                attempts += used;
-                envelope += envc;
+                const uint32_t used = __reduce_add_sync(kFull, mu);
+                const uint32_t envc = __reduce_add_sync(kFull, me);
+                if (lane == 0) {
+                    attempts += used;
+                    envelope += envc;
+                }
             }
             produced += min(total, need);
-            j0 += kSampleWarps * 32;
+            j0 += kL2DWarps * 32;
             __syncthreads();
         }
         if (produced < nnew) flags |= HYB_ST_SAMPLING_CAP;
         if (threadIdx.x == 0) {
-            const uint32_t old = a.count[cell];
             deleted += old;
             created += produced;
             dlive += (int32_t)produced - (int32_t)old;
@@ -510,18 +532,17 @@ cudaError_t d2l_impl(Ctx& c, const int32_t* nodes, int32_t n) {
 }
 
 template <typename Real, class LAT>
-cudaError_t l2d_impl(Ctx& c, const int32_t* cells, int32_t n) {
-    MapArgs<Real> a = map_args<Real>(c, cells, n);
-    cudaError_t e = cudaMemsetAsync(c.st.ctrl + CTRL_L2D_BAD, 0, 4, c.stream);
-    if (e != cudaSuccess) return e;
-    prof_begin(c, K_L2D_COEF);
-    k_l2d_coef<Real, LAT><<<blocks_for(c, (int64_t)n * 32, 128, 16), 128, 0, c.stream>>>(a);
-    prof_end(c, K_L2D_COEF);
-    prof_begin(c, K_L2D_SAMPLE);
-    k_l2d_sample<Real, LAT><<<blocks_for(c, (int64_t)n * 32 * kSampleWarps, 32 * kSampleWarps, 16),
-                              32 * kSampleWarps, 0, c.stream>>>(a);
-    prof_end(c, K_L2D_SAMPLE);
+cudaError_t l2d_launch(Ctx& c, const MapArgs<Real>& a, int32_t n) {
+    prof_begin(c, K_L2D);
+    k_l2d<Real, LAT><<<blocks_for(c, (int64_t)n * 32 * kL2DWarps, 32 * kL2DWarps, 8),
+                       32 * kL2DWarps, 0, c.stream>>>(a);
+    prof_end(c, K_L2D);
     return cudaGetLastError();
+}
+
+template <typename Real, class LAT>
+cudaError_t l2d_impl(Ctx& c, const int32_t* cells, int32_t n) {
+    return l2d_launch<Real, LAT>(c, map_args<Real>(c, cells, n), n);
 }
 
 constexpr int kMaxDevices = 64;
@@ -544,16 +565,7 @@ template <typename Real, class LAT>
 cudaError_t l2d_noalloc_impl(Ctx& c, const int32_t* cells, int32_t n, GradRec* rec) {
     MapArgs<Real> a = map_args<Real>(c, cells, n);
     a.grad = rec;  // the fixed array instead of the arena's records
-    cudaError_t e = cudaMemsetAsync(c.st.ctrl + CTRL_L2D_BAD, 0, 4, c.stream);
-    if (e != cudaSuccess) return e;
-    prof_begin(c, K_L2D_COEF);
-    k_l2d_coef<Real, LAT><<<blocks_for(c, (int64_t)n * 32, 128, 16), 128, 0, c.stream>>>(a);
-    prof_end(c, K_L2D_COEF);
-    prof_begin(c, K_L2D_SAMPLE);
-    k_l2d_sample<Real, LAT><<<blocks_for(c, (int64_t)n * 32 * kSampleWarps, 32 * kSampleWarps, 16),
-                              32 * kSampleWarps, 0, c.stream>>>(a);
-    prof_end(c, K_L2D_SAMPLE);
-    return cudaGetLastError();
+    return l2d_launch<Real, LAT>(c, a, n);
 }
 
 }  // namespace

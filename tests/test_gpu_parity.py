@@ -228,6 +228,27 @@ def test_lb2dsmc_matches_oracle(lattice, real_bytes, lb_ratio):
     _compare_dsmc(h, o, real_bytes)
 
 
+def test_lb2dsmc_skips_invalid_cells_like_oracle():
+    cfg = cfg_small(lb_ratio=2)
+    h = B.Hybrid(cfg)
+    o = O.Oracle(cfg)
+    h.dsmc_step(1)
+    o.dsmc_step(1)
+    e, w, r = O.lattice(39)
+    f0 = W.gen_populations(w, h.d["nnodes"], seed=9, eps=0.05).astype(np.float32)
+    h.f().copy_(torch.from_numpy(f0.reshape(h.f().shape)))
+    torch.cuda.synchronize()
+    o.set_f(f0)
+    cells = np.array([3, -1, 17, 10 ** 6, 30], np.int32)
+    h.map_lbm_to_dsmc(torch.from_numpy(cells).cuda())
+    o.map_lbm_to_dsmc(cells)
+    rc, bits = h.sync_status()
+    assert rc == B.HYB_EINVAL and bits & B.ST_BAD_INPUT
+    assert o.scalars()["status"] & B.ST_BAD_INPUT
+    assert h.n_tot() == o.scalars()["ntot"]
+    assert_particles_match(gpu_particles(h), o.particles(), 4)
+
+
 def test_hybrid_steps_fp64_match_oracle():
     # the 64-cell channel of the paper's mapping tests, FP64, two coupling nodes/cells
     cfg = W.WORKLOADS["poiseuille_64x1_ppc100_fp64"]
