@@ -25,7 +25,6 @@ enum CtrlWord {
     CTRL_STEP = 2,
     CTRL_NSAMPLES = 3,
     CTRL_TICKET = 4,   // blocks finished, for the last-block update of the move kernel
-    CTRL_WORK = 6,     // next batch of cells for the collide kernel
     CTRL_WORDS = 16,
 };
 

@@ -11,11 +11,12 @@
 //              back in place and its slot is appended to the tag list of its new cell's bin
 //              by a warp-aggregated atomic. The last block to finish advances the step
 //              counters.
-//   k_collide  one group of 8 lanes per cell (4 cells per warp): the cell's tags are put in
-//              stable order (ascending origin slot = origin cell, then rank in it: a bitonic
-//              sort in registers), the particles are gathered from the source half into the
-//              bin of the other half, NTC collisions (Eq. collisionnumber) run in shared
-//              memory, and the sums 1, v, vv, vvv are added to the FP64 cumulative sums of the
+//   k_collide  one group of 8 lanes per cell, one batch of 4 consecutive cells per warp: the
+//              cell's tags are put in stable order (ascending origin slot = origin cell, then
+//              rank in it: a bitonic sort in registers), the particles are gathered from the
+//              source half into the bin of the other half, NTC collisions (Eq.
+//              collisionnumber) run in shared memory (a pool per warp that the batch's cells
+//              share), and the sums 1, v, vv, vvv are added to the FP64 cumulative sums of the
 //              cell (Sec. 2.1, Fig. 1).
 // This file is compiled without FMA contraction so that positions, cell keys, pair choices
 // and post-collision velocities are the IEEE float (or double) results of the written
@@ -213,7 +214,6 @@ __global__ void __launch_bounds__(256) k_move(DsmcArgs<Real> a) {
         if (s % (uint32_t)a.sample_every == 0) a.ctrl[CTRL_NSAMPLES] += 1;
         a.ctrl[CTRL_STEP] = s + 1;
         a.ctrl[CTRL_NTOT] = 0;
-        a.ctrl[CTRL_WORK] = 0;
         a.ctrl[CTRL_TICKET] = 0;
     }
 }
@@ -228,8 +228,8 @@ constexpr int kGroup = 8;
 
 template <typename Real>
 struct CollideCfg {
-    static constexpr int WARPS = sizeof(Real) == 4 ? 4 : 2;
-    static constexpr int MINB = sizeof(Real) == 4 ? 8 : 4;  // resident blocks per SM
+    static constexpr int WARPS = sizeof(Real) == 4 ? 8 : 4;
+    static constexpr int MINB = sizeof(Real) == 4 ? 4 : 2;  // resident blocks per SM
 };
 
 // Ascending bitonic sort of G R keys held by the G lanes of a group, R per lane (key r of
@@ -278,221 +278,255 @@ __device__ __forceinline__ void gather_one(const DsmcArgs<Real>& a, int64_t base
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(CollideCfg<Real>::WARPS * 32, CollideCfg<Real>::MINB) k_collide(DsmcArgs<Real> a) {
+__global__ void __launch_bounds__(CollideCfg<Real>::WARPS * 32, CollideCfg<Real>::MINB)
+    k_collide(DsmcArgs<Real> a, uint32_t pool) {
     constexpr int G = kGroup;
     constexpr int CPW = 32 / G;         // cells per warp
     constexpr int SMALL = 64;           // cells up to this size are sorted in registers
     constexpr int R = SMALL / G;
     constexpr int WARPS = CollideCfg<Real>::WARPS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ unsigned long long s_cnt[WARPS][2];
+    __shared__ uint32_t s_live[WARPS], s_flags[WARPS];
     const int w = threadIdx.x >> 5;
     const unsigned lane = lane_id();
     const int grp = (int)lane / G, gl = (int)lane % G;
     const int leader = grp * G;
     const uint32_t bin = (uint32_t)a.bin;
-    // per group: vx, vy, vz (Real) and tags (u32), bin entries each
-    Real* sv = reinterpret_cast<Real*>(smem_raw) + (size_t)(w * CPW + grp) * 3 * bin;
-    Real* vx = sv;
-    Real* vy = sv + bin;
-    Real* vz = sv + 2 * bin;
-    uint32_t* st = reinterpret_cast<uint32_t*>(reinterpret_cast<Real*>(smem_raw) +
-                                                (size_t)WARPS * CPW * 3 * bin) +
-                   (size_t)(w * CPW + grp) * bin;
+    // per warp: vx, vy, vz (Real) and tags (u32), `pool` entries each, shared by the warp's
+    // groups (each takes its cell's count, in group order)
+    Real* wv = reinterpret_cast<Real*>(smem_raw) + (size_t)w * 3 * pool;
+    uint32_t* wst = reinterpret_cast<uint32_t*>(reinterpret_cast<Real*>(smem_raw) +
+                                                 (size_t)WARPS * 3 * pool) +
+                    (size_t)w * pool;
     const uint32_t s = a.ctrl[CTRL_STEP] - 1u;
     const bool do_sample = (s % (uint32_t)a.sample_every) == 0u;
     const Real coll_dt = (Real)a.coll_dt;
     unsigned long long ncand_tot = 0, ncoll_tot = 0;
     uint32_t flags = 0, nlive = 0;
 
+    // one batch of CPW consecutive cells per warp
     const int nbatch = (a.ncells + CPW - 1) / CPW;
-    for (;;) {
-        // batches of CPW cells are handed out dynamically, so no warp waits on a tail
-        int bt = 0;
-        if (lane == 0) bt = (int)atomicAdd(&a.ctrl[CTRL_WORK], 1u);
-        bt = __shfl_sync(kFull, bt, 0);
-        if (bt >= nbatch) break;
+    const int bt = blockIdx.x * WARPS + w;
+    if (bt < nbatch) {
         const int c = bt * CPW + grp;
         const bool has = c < a.ncells;
-        uint32_t n = has ? a.count_d[c] : 0u;
-        if (n > bin) n = bin;
+        uint32_t n_all = has ? a.count_d[c] : 0u;
+        if (n_all > bin) n_all = bin;
         const int64_t base = (int64_t)c * bin;
-        // 1. stable order (ascending origin slot) and gather
-        {
-            uint32_t v[R];
+        // the groups' regions of the warp pool; if the batch does not fit, the groups take
+        // the whole pool one after another
+        uint32_t off = 0, total = 0;
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const uint32_t k = (uint32_t)(gl + G * r);
-                v[r] = (n <= (uint32_t)SMALL && k < n) ? a.tag[base + k] : 0xFFFFFFFFu;
-            }
-            bitonic_group<G, R>(v);
-            if (n > (uint32_t)SMALL)
-                for (uint32_t k = gl; k < n; k += G) st[k] = a.tag[base + k];
-            __syncwarp();
-            if (n <= (uint32_t)SMALL) {
+        for (int g = 0; g < CPW; ++g) {
+            const uint32_t ng = __shfl_sync(kFull, n_all, g * G);
+            if (g < grp) off += ng;
+            total += ng;
+        }
+        const bool fits = total <= pool;
+        const int rounds = fits ? 1 : CPW;
+        for (int round = 0; round < rounds; ++round) {
+            const bool act = fits || grp == round;
+            const bool has_r = has && act;
+            const uint32_t n = act ? n_all : 0u;
+            const uint32_t poff = fits ? off : 0u;
+            Real* vx = wv + poff;
+            Real* vy = wv + pool + poff;
+            Real* vz = wv + 2 * pool + poff;
+            uint32_t* st = wst + poff;
+            // 1. stable order (ascending origin slot) and gather
+            {
+                uint32_t v[R];
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const uint32_t k = (uint32_t)(gl + G * r);
-                    if (k < n) gather_one(a, base, k, v[r], vx, vy, vz);
+                    v[r] = (n <= (uint32_t)SMALL && k < n) ? a.tag[base + k] : 0xFFFFFFFFu;
                 }
-            } else {
-                // rank of each tag = number of smaller tags in the cell
-                for (uint32_t k = gl; k < n; k += G) {
-                    const uint32_t t = st[k];
-                    uint32_t r = 0;
-                    for (uint32_t m = 0; m < n; ++m) r += st[m] < t ? 1u : 0u;
-                    gather_one(a, base, r, t, vx, vy, vz);
-                }
-            }
-        }
-        __syncwarp();
-        // 2. NTC: N_cand = 1/2 N Nbar F_N (sigma c_r)_max dt / V_c + remainder (group leader)
-        uint32_t nsel = 0;
-        Real cm = (Real)0;
-        if (has && gl == 0) {
-            const uint32_t nb = a.nbar_sum[c] + n;
-            a.nbar_sum[c] = nb;
-            a.count_s[c] = 0;  // the source half's count is not needed after the move
-            cm = a.crmax[c];
-            nlive += n;
-            if (n > 32767u) {
-                flags |= HYB_ST_CELL_OVERFLOW;  // pair indices are packed in 15 and 16 bits
-            } else if (n >= 2) {
-                const Real nbar = (Real)nb / (Real)(s + 1u);
-                const Real ncand = (Real)0.5 * (Real)n * nbar * cm * coll_dt + a.rem[c];
-                const Real fl = floor(ncand);
-                a.rem[c] = ncand - fl;
-                if (fl > (Real)16777215) {
-                    nsel = 16777215u;
-                    flags |= HYB_ST_CELL_OVERFLOW;
+                bitonic_group<G, R>(v);
+                if (n > (uint32_t)SMALL)
+                    for (uint32_t k = gl; k < n; k += G) st[k] = a.tag[base + k];
+                __syncwarp();
+                if (n <= (uint32_t)SMALL) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const uint32_t k = (uint32_t)(gl + G * r);
+                        if (k < n) gather_one(a, base, k, v[r], vx, vy, vz);
+                    }
                 } else {
-                    nsel = (uint32_t)fl;
-                }
-            }
-        }
-        nsel = __shfl_sync(kFull, nsel, leader);
-        cm = __shfl_sync(kFull, cm, leader);
-        const uint32_t maxsel = __reduce_max_sync(kFull, nsel);
-        uint32_t ncoll = 0;
-        for (uint32_t ch = 0; ch < maxsel; ch += G) {
-            // the group's lanes draw G candidates in parallel; they are applied in order below
-            const uint32_t k = ch + gl;
-            uint32_t ij = 0;
-            Real R0 = (Real)0, nx = (Real)0, ny = (Real)0, nz = (Real)0;
-            if (k < nsel) {
-                const uint4 r = draw(a.seed, (uint32_t)c, s, TAG_NTC_PAIR, k, 0);
-                const uint32_t ci = uindex(r.x, n);
-                uint32_t cj = uindex(r.y, n - 1u);
-                if (cj >= ci) cj += 1u;
-                R0 = (Real)u01f(r.z);
-                const int ok = unit_vector(a.seed, (uint32_t)c, s, k, nx, ny, nz);
-                ij = ci | (cj << 15) | (ok ? 0u : 0x80000000u);
-            }
-#pragma unroll 1
-            for (int m = 0; m < G; ++m) {
-                const int src = leader + m;
-                const uint32_t ijm = __shfl_sync(kFull, ij, src);
-                const Real Rm = __shfl_sync(kFull, R0, src);
-                const Real nxm = __shfl_sync(kFull, nx, src);
-                const Real nym = __shfl_sync(kFull, ny, src);
-                const Real nzm = __shfl_sync(kFull, nz, src);
-                bool acc_pair = false;
-                Real cx = 0, cy = 0, cz = 0, h = 0;
-                uint32_t i = 0, j = 0;
-                if (ch + (uint32_t)m < nsel) {
-                    i = ijm & 0x7FFFu;
-                    j = (ijm >> 15) & 0xFFFFu;
-                    const Real ax = vx[i], ay = vy[i], az = vz[i];
-                    const Real bx = vx[j], by = vy[j], bz = vz[j];
-                    const Real ddx = ax - bx, ddy = ay - by, ddz = az - bz;
-                    const Real cr = sqrt(ddx * ddx + ddy * ddy + ddz * ddz);
-                    if (cr > cm) cm = cr;
-                    if (cr > Rm * cm) {
-                        if (ijm & 0x80000000u) {
-                            flags |= HYB_ST_SCATTER_CAP;
-                        } else {
-                            acc_pair = true;
-                            cx = (ax + bx) * (Real)0.5;
-                            cy = (ay + by) * (Real)0.5;
-                            cz = (az + bz) * (Real)0.5;
-                            h = cr * (Real)0.5;
-                        }
+                    // rank of each tag = number of smaller tags in the cell
+                    for (uint32_t k = gl; k < n; k += G) {
+                        const uint32_t t = st[k];
+                        uint32_t r = 0;
+                        for (uint32_t m = 0; m < n; ++m) r += st[m] < t ? 1u : 0u;
+                        gather_one(a, base, r, t, vx, vy, vz);
                     }
                 }
-                __syncwarp();
-                if (acc_pair && gl == 0) {
-                    vx[i] = cx + h * nxm;
-                    vy[i] = cy + h * nym;
-                    vz[i] = cz + h * nzm;
-                    vx[j] = cx - h * nxm;
-                    vy[j] = cy - h * nym;
-                    vz[j] = cz - h * nzm;
-                }
-                if (acc_pair) ncoll += 1;
-                __syncwarp();
             }
-        }
-        if (has && gl == 0) {
-            a.crmax[c] = cm;
-            ncand_tot += nsel;
-            ncoll_tot += ncoll;
-        }
-        // 3. write-out and moment sums (group lanes over the cell's particles)
-        Real mo[kMoments];
+            __syncwarp();
+            // 2. NTC: N_cand = 1/2 N Nbar F_N (sigma c_r)_max dt / V_c + remainder (group leader)
+            uint32_t nsel = 0;
+            Real cm = (Real)0;
+            if (has_r && gl == 0) {
+                const uint32_t nb = a.nbar_sum[c] + n;
+                a.nbar_sum[c] = nb;
+                a.count_s[c] = 0;  // the source half's count is not needed after the move
+                cm = a.crmax[c];
+                nlive += n;
+                if (n > 32767u) {
+                    flags |= HYB_ST_CELL_OVERFLOW;  // pair indices are packed in 15 and 16 bits
+                } else if (n >= 2) {
+                    const Real nbar = (Real)nb / (Real)(s + 1u);
+                    const Real ncand = (Real)0.5 * (Real)n * nbar * cm * coll_dt + a.rem[c];
+                    const Real fl = floor(ncand);
+                    a.rem[c] = ncand - fl;
+                    if (fl > (Real)16777215) {
+                        nsel = 16777215u;
+                        flags |= HYB_ST_CELL_OVERFLOW;
+                    } else {
+                        nsel = (uint32_t)fl;
+                    }
+                }
+            }
+            nsel = __shfl_sync(kFull, nsel, leader);
+            cm = __shfl_sync(kFull, cm, leader);
+            const uint32_t maxsel = __reduce_max_sync(kFull, nsel);
+            uint32_t ncoll = 0;
+            for (uint32_t ch = 0; ch < maxsel; ch += G) {
+                // the group's lanes draw G candidates in parallel; they are applied in order below
+                const uint32_t k = ch + gl;
+                uint32_t ij = 0;
+                Real R0 = (Real)0, nx = (Real)0, ny = (Real)0, nz = (Real)0;
+                if (k < nsel) {
+                    const uint4 r = draw(a.seed, (uint32_t)c, s, TAG_NTC_PAIR, k, 0);
+                    const uint32_t ci = uindex(r.x, n);
+                    uint32_t cj = uindex(r.y, n - 1u);
+                    if (cj >= ci) cj += 1u;
+                    R0 = (Real)u01f(r.z);
+                    const int ok = unit_vector(a.seed, (uint32_t)c, s, k, nx, ny, nz);
+                    ij = ci | (cj << 15) | (ok ? 0u : 0x80000000u);
+                }
+#pragma unroll 1
+                for (int m = 0; m < G; ++m) {
+                    const int src = leader + m;
+                    const uint32_t ijm = __shfl_sync(kFull, ij, src);
+                    const Real Rm = __shfl_sync(kFull, R0, src);
+                    const Real nxm = __shfl_sync(kFull, nx, src);
+                    const Real nym = __shfl_sync(kFull, ny, src);
+                    const Real nzm = __shfl_sync(kFull, nz, src);
+                    bool acc_pair = false;
+                    Real cx = 0, cy = 0, cz = 0, h = 0;
+                    uint32_t i = 0, j = 0;
+                    if (ch + (uint32_t)m < nsel) {
+                        i = ijm & 0x7FFFu;
+                        j = (ijm >> 15) & 0xFFFFu;
+                        const Real ax = vx[i], ay = vy[i], az = vz[i];
+                        const Real bx = vx[j], by = vy[j], bz = vz[j];
+                        const Real ddx = ax - bx, ddy = ay - by, ddz = az - bz;
+                        const Real cr = sqrt(ddx * ddx + ddy * ddy + ddz * ddz);
+                        if (cr > cm) cm = cr;
+                        if (cr > Rm * cm) {
+                            if (ijm & 0x80000000u) {
+                                flags |= HYB_ST_SCATTER_CAP;
+                            } else {
+                                acc_pair = true;
+                                cx = (ax + bx) * (Real)0.5;
+                                cy = (ay + by) * (Real)0.5;
+                                cz = (az + bz) * (Real)0.5;
+                                h = cr * (Real)0.5;
+                            }
+                        }
+                    }
+                    __syncwarp();
+                    if (acc_pair && gl == 0) {
+                        vx[i] = cx + h * nxm;
+                        vy[i] = cy + h * nym;
+                        vz[i] = cz + h * nzm;
+                        vx[j] = cx - h * nxm;
+                        vy[j] = cy - h * nym;
+                        vz[j] = cz - h * nzm;
+                    }
+                    if (acc_pair) ncoll += 1;
+                    __syncwarp();
+                }
+            }
+            if (has_r && gl == 0) {
+                a.crmax[c] = cm;
+                ncand_tot += nsel;
+                ncoll_tot += ncoll;
+            }
+            // 3. write-out and moment sums (group lanes over the cell's particles)
+            Real mo[kMoments];
 #pragma unroll
-        for (int q = 0; q < kMoments; ++q) mo[q] = (Real)0;
-        for (uint32_t k = gl; k < n; k += G) {
-            const Real ux = vx[k], uy = vy[k], uz = vz[k];
-            a.dvx[base + k] = ux;
-            a.dvy[base + k] = uy;
-            a.dvz[base + k] = uz;
+            for (int q = 0; q < kMoments; ++q) mo[q] = (Real)0;
+            for (uint32_t k = gl; k < n; k += G) {
+                const Real ux = vx[k], uy = vy[k], uz = vz[k];
+                a.dvx[base + k] = ux;
+                a.dvy[base + k] = uy;
+                a.dvz[base + k] = uz;
+                if (do_sample) {
+                    const Real xx = ux * ux, yy = uy * uy, zz = uz * uz;
+                    const Real xy = ux * uy, xz = ux * uz, yz = uy * uz;
+                    mo[0] += (Real)1;
+                    mo[1] += ux; mo[2] += uy; mo[3] += uz;
+                    mo[4] += xx; mo[5] += xy; mo[6] += xz; mo[7] += yy; mo[8] += yz; mo[9] += zz;
+                    mo[10] += xx * ux; mo[11] += xx * uy; mo[12] += xx * uz; mo[13] += yy * ux;
+                    mo[14] += xy * uz; mo[15] += zz * ux; mo[16] += yy * uy; mo[17] += yy * uz;
+                    mo[18] += zz * uy; mo[19] += zz * uz;
+                }
+            }
             if (do_sample) {
-                const Real xx = ux * ux, yy = uy * uy, zz = uz * uz;
-                const Real xy = ux * uy, xz = ux * uz, yz = uy * uz;
-                mo[0] += (Real)1;
-                mo[1] += ux; mo[2] += uy; mo[3] += uz;
-                mo[4] += xx; mo[5] += xy; mo[6] += xz; mo[7] += yy; mo[8] += yz; mo[9] += zz;
-                mo[10] += xx * ux; mo[11] += xx * uy; mo[12] += xx * uz; mo[13] += yy * ux;
-                mo[14] += xy * uz; mo[15] += zz * ux; mo[16] += yy * uy; mo[17] += yy * uz;
-                mo[18] += zz * uy; mo[19] += zz * uz;
-            }
-        }
-        if (do_sample) {
-            // halving exchange over the group: lane gl ends with the totals of moments
-            // 3 gl, 3 gl + 1, 3 gl + 2
-            Real t[24];
+                // halving exchange over the group: lane gl ends with the totals of moments
+                // 3 gl, 3 gl + 1, 3 gl + 2
+                Real t[24];
 #pragma unroll
-            for (int q = 0; q < 24; ++q) t[q] = q < kMoments ? mo[q] : (Real)0;
+                for (int q = 0; q < 24; ++q) t[q] = q < kMoments ? mo[q] : (Real)0;
 #pragma unroll
-            for (int o = G / 2, len = 12; o >= 1; o >>= 1, len >>= 1) {
-                const bool hi = (gl & o) != 0;
+                for (int o = G / 2, len = 12; o >= 1; o >>= 1, len >>= 1) {
+                    const bool hi = (gl & o) != 0;
 #pragma unroll
-                for (int q = 0; q < len; ++q) {
-                    const Real send = hi ? t[q] : t[q + len];
-                    const Real keep = hi ? t[q + len] : t[q];
-                    t[q] = keep + __shfl_xor_sync(kFull, send, o);
+                    for (int q = 0; q < len; ++q) {
+                        const Real send = hi ? t[q] : t[q + len];
+                        const Real keep = hi ? t[q + len] : t[q];
+                        t[q] = keep + __shfl_xor_sync(kFull, send, o);
+                    }
+                }
+                if (has_r) {
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        const int mq = 3 * gl + q;
+                        if (mq < kMoments) a.acc[(size_t)c * kMoments + mq] += (double)t[q];
+                    }
                 }
             }
-            if (has) {
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    const int mq = 3 * gl + q;
-                    if (mq < kMoments) a.acc[(size_t)c * kMoments + mq] += (double)t[q];
-                }
-            }
+            __syncwarp();
         }
-        __syncwarp();
     }
-    // event counters
+    // event counters: per block, one atomic per counter
     ncand_tot = __reduce_add_sync(kFull, (unsigned)ncand_tot);
     ncoll_tot = __reduce_add_sync(kFull, (unsigned)ncoll_tot);
     nlive = __reduce_add_sync(kFull, nlive);
-    if (lane == 0) {
-        if (ncand_tot) atomicAdd(&a.counters[HYB_C_CANDIDATES], ncand_tot);
-        if (ncoll_tot) atomicAdd(&a.counters[HYB_C_COLLISIONS], ncoll_tot);
-        if (nlive) atomicAdd(&a.ctrl[CTRL_NTOT], nlive);
-    }
     flags = __reduce_or_sync(kFull, flags);
-    if (lane == 0 && flags) atomicOr(&a.ctrl[CTRL_STATUS], flags);
+    if (lane == 0) {
+        s_cnt[w][0] = ncand_tot;
+        s_cnt[w][1] = ncoll_tot;
+        s_live[w] = nlive;
+        s_flags[w] = flags;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long c0 = 0, c1 = 0;
+        uint32_t nl = 0, fl = 0;
+        for (int v = 0; v < WARPS; ++v) {
+            c0 += s_cnt[v][0];
+            c1 += s_cnt[v][1];
+            nl += s_live[v];
+            fl |= s_flags[v];
+        }
+        if (c0) atomicAdd(&a.counters[HYB_C_CANDIDATES], c0);
+        if (c1) atomicAdd(&a.counters[HYB_C_COLLISIONS], c1);
+        if (nl) atomicAdd(&a.ctrl[CTRL_NTOT], nl);
+        if (fl) atomicOr(&a.ctrl[CTRL_STATUS], fl);
+    }
 }
 
 template <typename Real>
@@ -563,18 +597,22 @@ cudaError_t step_impl(Ctx& c) {
     prof_begin(c, K_MOVE);
     k_move<Real><<<grid_for(c, c.d.ncells * 32, 256, 8), 256, 0, c.stream>>>(a);
     prof_end(c, K_MOVE);
-    // shared memory: per group (32 / kGroup per warp) bin x (3 Real + 1 u32)
+    // shared memory: per warp a pool of slots for its cells (3 Real + 1 u32 each), room for
+    // 1.75 ppc per cell on average and at least one full bin
     constexpr int WARPS = CollideCfg<Real>::WARPS;
-    const size_t smem = (size_t)WARPS * (32 / kGroup) * c.d.bin * (3 * sizeof(Real) + 4);
+    constexpr int CPW = 32 / kGroup;
+    uint32_t pool = (uint32_t)(((int64_t)CPW * c.p.ppc * 7 / 4 + 31) / 32 * 32);
+    if (pool < (uint32_t)c.d.bin) pool = (uint32_t)c.d.bin;
+    const size_t smem = (size_t)WARPS * pool * (3 * sizeof(Real) + 4);
     if (smem > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(k_collide<Real>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    const int grid = grid_for(c, (c.d.ncells + (32 / kGroup) - 1) / (32 / kGroup) * 32, WARPS * 32,
-                              CollideCfg<Real>::MINB);
+    const int64_t nbatch = (c.d.ncells + CPW - 1) / CPW;
+    const unsigned grid = (unsigned)((nbatch + WARPS - 1) / WARPS);
     prof_begin(c, K_COLLIDE);
-    k_collide<Real><<<grid, WARPS * 32, smem, c.stream>>>(a);
+    k_collide<Real><<<grid, WARPS * 32, smem, c.stream>>>(a, pool);
     prof_end(c, K_COLLIDE);
     return cudaGetLastError();
 }
