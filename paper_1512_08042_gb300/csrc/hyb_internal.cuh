@@ -177,6 +177,32 @@ __device__ __forceinline__ uint32_t uindex(uint32_t r, uint32_t n) {
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
+// Programmatic dependent launch (sm_90 and later). The kernels of a step are launched with
+// launch_pdl: each one first lets the next kernel of the stream be scheduled
+// (launch_dependents), then waits until the previous kernel has completed and its writes are
+// visible (wait). The launch latency and block ramp-up of a kernel so overlap the tail of
+// the one before it; no work that reads the previous kernel's results comes before the wait.
+__device__ __forceinline__ void pdl_begin() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t stream, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Float elementary functions of the FP32 state path, evaluated from their series with every
 // operation fixed (this code is compiled without FMA contraction), so that the results are
 // reproducible bit for bit:

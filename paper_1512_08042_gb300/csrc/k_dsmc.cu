@@ -108,8 +108,9 @@ __global__ void k_init_cells(DsmcArgs<Real> a) {
 // Move (kick, drift, walls, wrap) and binning into the other half.
 template <typename Real>
 __global__ void __launch_bounds__(256) k_move(DsmcArgs<Real> a) {
-    __shared__ bool s_last;
+    pdl_begin();
     const uint32_t s = a.ctrl[CTRL_STEP];
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.ctrl[CTRL_NTOT] = 0;  // the collide recounts
     const Real H = (Real)a.ncx, L = (Real)a.ncy;
     const Real g = (Real)a.g_step, dt = (Real)a.dt;
     const unsigned lane = lane_id();
@@ -201,21 +202,6 @@ __global__ void __launch_bounds__(256) k_move(DsmcArgs<Real> a) {
         }
         if (lost) atomicOr(&a.ctrl[CTRL_STATUS], HYB_ST_CAPACITY);
     }
-    // the last block to finish advances the step and sample counters
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned ticket = atomicAdd(&a.ctrl[CTRL_TICKET], 1u);
-        s_last = ticket == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (s_last && threadIdx.x == 0) {
-        __threadfence();
-        if (s % (uint32_t)a.sample_every == 0) a.ctrl[CTRL_NSAMPLES] += 1;
-        a.ctrl[CTRL_STEP] = s + 1;
-        a.ctrl[CTRL_NTOT] = 0;
-        a.ctrl[CTRL_TICKET] = 0;
-    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -267,19 +253,44 @@ __device__ __forceinline__ void bitonic_group(uint32_t (&v)[R]) {
     }
 }
 
-template <typename Real>
-__device__ __forceinline__ void gather_one(const DsmcArgs<Real>& a, int64_t base, uint32_t k,
-                                           uint32_t src, Real* vx, Real* vy, Real* vz) {
-    a.dx[base + k] = a.sx[src];
-    a.dy[base + k] = a.sy[src];
-    vx[k] = a.svx[src];
-    vy[k] = a.svy[src];
-    vz[k] = a.svz[src];
+// Gathers the particles of sorted positions k = gl + G r (r < RR) from the source slots
+// src[r]: positions into the cell's bin of the other half, velocities into shared memory.
+// Every load is issued before the first store, so the loads of all RR slots are in flight
+// together (the stores could alias the loads as far as the compiler knows).
+template <typename Real, int G, int RR>
+__device__ __forceinline__ void gather_slots(const DsmcArgs<Real>& a, int64_t base, int gl, int r0,
+                                             uint32_t n, const uint32_t* src, Real* vx, Real* vy,
+                                             Real* vz) {
+    Real px[RR], py[RR], ux[RR], uy[RR], uz[RR];
+#pragma unroll
+    for (int r = 0; r < RR; ++r) {
+        const uint32_t k = (uint32_t)(gl + G * (r0 + r));
+        if (k < n) {
+            const uint32_t i = src[r];
+            px[r] = a.sx[i];
+            py[r] = a.sy[i];
+            ux[r] = a.svx[i];
+            uy[r] = a.svy[i];
+            uz[r] = a.svz[i];
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < RR; ++r) {
+        const uint32_t k = (uint32_t)(gl + G * (r0 + r));
+        if (k < n) {
+            a.dx[base + k] = px[r];
+            a.dy[base + k] = py[r];
+            vx[k] = ux[r];
+            vy[k] = uy[r];
+            vz[k] = uz[r];
+        }
+    }
 }
 
 template <typename Real>
 __global__ void __launch_bounds__(CollideCfg<Real>::WARPS * 32, CollideCfg<Real>::MINB)
     k_collide(DsmcArgs<Real> a, uint32_t pool) {
+    pdl_begin();
     constexpr int G = kGroup;
     constexpr int CPW = 32 / G;         // cells per warp
     constexpr int SMALL = 64;           // cells up to this size are sorted in registers
@@ -299,7 +310,7 @@ __global__ void __launch_bounds__(CollideCfg<Real>::WARPS * 32, CollideCfg<Real>
     uint32_t* wst = reinterpret_cast<uint32_t*>(reinterpret_cast<Real*>(smem_raw) +
                                                  (size_t)WARPS * 3 * pool) +
                     (size_t)w * pool;
-    const uint32_t s = a.ctrl[CTRL_STEP] - 1u;
+    const uint32_t s = a.ctrl[CTRL_STEP];
     const bool do_sample = (s % (uint32_t)a.sample_every) == 0u;
     const Real coll_dt = (Real)a.coll_dt;
     unsigned long long ncand_tot = 0, ncoll_tot = 0;
@@ -311,9 +322,30 @@ __global__ void __launch_bounds__(CollideCfg<Real>::WARPS * 32, CollideCfg<Real>
     if (bt < nbatch) {
         const int c = bt * CPW + grp;
         const bool has = c < a.ncells;
-        uint32_t n_all = has ? a.count_d[c] : 0u;
-        if (n_all > bin) n_all = bin;
         const int64_t base = (int64_t)c * bin;
+        // the cell's loads are issued together: count, the first SMALL tag slots, the
+        // leader's NTC state and the lane's three moment sums
+        uint32_t n_all = has ? a.count_d[c] : 0u;
+        uint32_t vl[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint32_t k = (uint32_t)(gl + G * r);
+            vl[r] = (has && k < bin) ? a.tag[base + k] : 0xFFFFFFFFu;
+        }
+        uint32_t nb0 = 0;
+        Real cm0 = (Real)0, rem0 = (Real)0;
+        if (has && gl == 0) {
+            nb0 = a.nbar_sum[c];
+            cm0 = a.crmax[c];
+            rem0 = a.rem[c];
+        }
+        double acc0[3] = {0.0, 0.0, 0.0};
+        if (has && do_sample) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                if (3 * gl + q < kMoments) acc0[q] = a.acc[(size_t)c * kMoments + 3 * gl + q];
+        }
+        if (n_all > bin) n_all = bin;
         // the groups' regions of the warp pool; if the batch does not fit, the groups take
         // the whole pool one after another
         uint32_t off = 0, total = 0;
@@ -340,7 +372,7 @@ __global__ void __launch_bounds__(CollideCfg<Real>::WARPS * 32, CollideCfg<Real>
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const uint32_t k = (uint32_t)(gl + G * r);
-                    v[r] = (n <= (uint32_t)SMALL && k < n) ? a.tag[base + k] : 0xFFFFFFFFu;
+                    v[r] = (n <= (uint32_t)SMALL && k < n) ? vl[r] : 0xFFFFFFFFu;
                 }
                 bitonic_group<G, R>(v);
                 if (n > (uint32_t)SMALL)
@@ -348,17 +380,21 @@ __global__ void __launch_bounds__(CollideCfg<Real>::WARPS * 32, CollideCfg<Real>
                 __syncwarp();
                 if (n <= (uint32_t)SMALL) {
 #pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const uint32_t k = (uint32_t)(gl + G * r);
-                        if (k < n) gather_one(a, base, k, v[r], vx, vy, vz);
-                    }
+                    for (int r0 = 0; r0 < R; r0 += R / 4)
+                        gather_slots<Real, G, R / 4>(a, base, gl, r0, n, v + r0, vx, vy, vz);
                 } else {
                     // rank of each tag = number of smaller tags in the cell
                     for (uint32_t k = gl; k < n; k += G) {
                         const uint32_t t = st[k];
                         uint32_t r = 0;
                         for (uint32_t m = 0; m < n; ++m) r += st[m] < t ? 1u : 0u;
-                        gather_one(a, base, r, t, vx, vy, vz);
+                        const Real px = a.sx[t], py = a.sy[t];
+                        const Real ux = a.svx[t], uy = a.svy[t], uz = a.svz[t];
+                        a.dx[base + r] = px;
+                        a.dy[base + r] = py;
+                        vx[r] = ux;
+                        vy[r] = uy;
+                        vz[r] = uz;
                     }
                 }
             }
@@ -367,16 +403,16 @@ __global__ void __launch_bounds__(CollideCfg<Real>::WARPS * 32, CollideCfg<Real>
             uint32_t nsel = 0;
             Real cm = (Real)0;
             if (has_r && gl == 0) {
-                const uint32_t nb = a.nbar_sum[c] + n;
+                const uint32_t nb = nb0 + n;
                 a.nbar_sum[c] = nb;
                 a.count_s[c] = 0;  // the source half's count is not needed after the move
-                cm = a.crmax[c];
+                cm = cm0;
                 nlive += n;
                 if (n > 32767u) {
                     flags |= HYB_ST_CELL_OVERFLOW;  // pair indices are packed in 15 and 16 bits
                 } else if (n >= 2) {
                     const Real nbar = (Real)nb / (Real)(s + 1u);
-                    const Real ncand = (Real)0.5 * (Real)n * nbar * cm * coll_dt + a.rem[c];
+                    const Real ncand = (Real)0.5 * (Real)n * nbar * cm * coll_dt + rem0;
                     const Real fl = floor(ncand);
                     a.rem[c] = ncand - fl;
                     if (fl > (Real)16777215) {
@@ -494,7 +530,7 @@ __global__ void __launch_bounds__(CollideCfg<Real>::WARPS * 32, CollideCfg<Real>
 #pragma unroll
                     for (int q = 0; q < 3; ++q) {
                         const int mq = 3 * gl + q;
-                        if (mq < kMoments) a.acc[(size_t)c * kMoments + mq] += (double)t[q];
+                        if (mq < kMoments) a.acc[(size_t)c * kMoments + mq] = acc0[q] + (double)t[q];
                     }
                 }
             }
@@ -526,6 +562,16 @@ __global__ void __launch_bounds__(CollideCfg<Real>::WARPS * 32, CollideCfg<Real>
         if (c1) atomicAdd(&a.counters[HYB_C_COLLISIONS], c1);
         if (nl) atomicAdd(&a.ctrl[CTRL_NTOT], nl);
         if (fl) atomicOr(&a.ctrl[CTRL_STATUS], fl);
+        // the last block to finish advances the step and sample counters (every block has
+        // read the step by now)
+        __threadfence();
+        const unsigned ticket = atomicAdd(&a.ctrl[CTRL_TICKET], 1u);
+        if (ticket == gridDim.x - 1) {
+            __threadfence();
+            if (do_sample) a.ctrl[CTRL_NSAMPLES] += 1;
+            a.ctrl[CTRL_STEP] = s + 1;
+            a.ctrl[CTRL_TICKET] = 0;
+        }
     }
 }
 
@@ -595,7 +641,9 @@ template <typename Real>
 cudaError_t step_impl(Ctx& c) {
     DsmcArgs<Real> a = make_args<Real>(c);
     prof_begin(c, K_MOVE);
-    k_move<Real><<<grid_for(c, c.d.ncells * 32, 256, 8), 256, 0, c.stream>>>(a);
+    cudaError_t e = launch_pdl(k_move<Real>, dim3(grid_for(c, c.d.ncells * 32, 256, 8)), dim3(256), 0,
+                               c.stream, a);
+    if (e != cudaSuccess) return e;
     prof_end(c, K_MOVE);
     // shared memory: per warp a pool of slots for its cells (3 Real + 1 u32 each), room for
     // 1.75 ppc per cell on average and at least one full bin
@@ -605,14 +653,14 @@ cudaError_t step_impl(Ctx& c) {
     if (pool < (uint32_t)c.d.bin) pool = (uint32_t)c.d.bin;
     const size_t smem = (size_t)WARPS * pool * (3 * sizeof(Real) + 4);
     if (smem > 48 * 1024) {
-        const cudaError_t e = cudaFuncSetAttribute(k_collide<Real>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_collide<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     const int64_t nbatch = (c.d.ncells + CPW - 1) / CPW;
     const unsigned grid = (unsigned)((nbatch + WARPS - 1) / WARPS);
     prof_begin(c, K_COLLIDE);
-    k_collide<Real><<<grid, WARPS * 32, smem, c.stream>>>(a, pool);
+    e = launch_pdl(k_collide<Real>, dim3(grid), dim3(WARPS * 32), smem, c.stream, a, pool);
+    if (e != cudaSuccess) return e;
     prof_end(c, K_COLLIDE);
     return cudaGetLastError();
 }

@@ -64,6 +64,7 @@ __device__ __forceinline__ int wrap_y(int v, int ny) {
 
 template <typename Real, class LAT>
 __global__ void __launch_bounds__(128) k_lbm(LbmArgs<Real> a) {
+    pdl_begin();
     constexpr int Q = LAT::Q;
     constexpr double R = lat_r<LAT>();
     const int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -270,9 +271,9 @@ cudaError_t lbm_impl(Ctx& c) {
     a.g_step = (Real)c.d.g_step;
     const int64_t blocks = (c.d.nnodes + 127) / 128;
     prof_begin(c, K_LBM);
-    k_lbm<Real, LAT><<<(unsigned)blocks, 128, 0, c.stream>>>(a);
+    const cudaError_t e = launch_pdl(k_lbm<Real, LAT>, dim3((unsigned)blocks), dim3(128), 0, c.stream, a);
     prof_end(c, K_LBM);
-    return cudaGetLastError();
+    return e;
 }
 
 template <typename Real, class LAT>

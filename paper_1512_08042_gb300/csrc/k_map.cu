@@ -62,6 +62,7 @@ __device__ __forceinline__ int lat_e(int a, int i) {
 // precision) are broadcast and each lane evaluates one or two populations.
 template <typename Real, class LAT>
 __global__ void __launch_bounds__(128) k_d2l(MapArgs<Real> a) {
+    pdl_begin();
     __shared__ Real sx[3 * LAT::Q];
     __shared__ Real sw[LAT::Q];
     for (int q = threadIdx.x; q < LAT::Q; q += blockDim.x) {
@@ -317,6 +318,7 @@ __device__ __forceinline__ void grad_coefficients(const MapArgs<Real>& a, int ce
 // to a.grad.
 template <typename Real, class LAT>
 __global__ void __launch_bounds__(kL2DWarps * 32) k_l2d(MapArgs<Real> a) {
+    pdl_begin();
     __shared__ unsigned s_am[kL2DWarps], s_em[kL2DWarps], s_vm[kL2DWarps];
     __shared__ Real s_c[20];
     __shared__ uint32_t s_nnew;
@@ -526,18 +528,20 @@ template <typename Real, class LAT>
 cudaError_t d2l_impl(Ctx& c, const int32_t* nodes, int32_t n) {
     MapArgs<Real> a = map_args<Real>(c, nodes, n);
     prof_begin(c, K_D2L);
-    k_d2l<Real, LAT><<<blocks_for(c, (int64_t)n * 32, 128, 16), 128, 0, c.stream>>>(a);
+    const cudaError_t e = launch_pdl(k_d2l<Real, LAT>, dim3(blocks_for(c, (int64_t)n * 32, 128, 16)),
+                                     dim3(128), 0, c.stream, a);
     prof_end(c, K_D2L);
-    return cudaGetLastError();
+    return e;
 }
 
 template <typename Real, class LAT>
 cudaError_t l2d_launch(Ctx& c, const MapArgs<Real>& a, int32_t n) {
     prof_begin(c, K_L2D);
-    k_l2d<Real, LAT><<<blocks_for(c, (int64_t)n * 32 * kL2DWarps, 32 * kL2DWarps, 8),
-                       32 * kL2DWarps, 0, c.stream>>>(a);
+    const cudaError_t e = launch_pdl(k_l2d<Real, LAT>,
+                                     dim3(blocks_for(c, (int64_t)n * 32 * kL2DWarps, 32 * kL2DWarps, 8)),
+                                     dim3(32 * kL2DWarps), 0, c.stream, a);
     prof_end(c, K_L2D);
-    return cudaGetLastError();
+    return e;
 }
 
 template <typename Real, class LAT>
