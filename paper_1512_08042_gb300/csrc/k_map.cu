@@ -33,28 +33,41 @@ namespace hyb {
 
 namespace {
 
-// Speed components of the lattices as device tables, for lanes that each handle a different
-// population (a runtime index into the compile-time table would copy it to local memory).
-template <class LAT>
-struct LatSpeeds {
-    int8_t e[3 * LAT::Q];
+// Lattice speeds xi = r e in the state precision (r e formed in double and rounded, as the
+// oracle does) and weights, as device tables built at compile time, for lanes that each
+// handle a different population.
+template <class LAT, typename Real>
+struct LatXi {
+    Real x[3 * LAT::Q];
+    Real w[LAT::Q];
 };
-template <class LAT>
-constexpr LatSpeeds<LAT> make_speeds() {
-    LatSpeeds<LAT> s{};
-    for (int a = 0; a < LAT::Q; ++a)
-        for (int i = 0; i < 3; ++i) s.e[3 * a + i] = (int8_t)LatTab<LAT>::e(a, i);
-    return s;
+template <class LAT, typename Real>
+constexpr LatXi<LAT, Real> make_xi() {
+    LatXi<LAT, Real> t{};
+    for (int a = 0; a < LAT::Q; ++a) {
+        for (int i = 0; i < 3; ++i) t.x[3 * a + i] = (Real)(lat_r<LAT>() * (double)LatTab<LAT>::e(a, i));
+        t.w[a] = (Real)LatTab<LAT>::w(a);
+    }
+    return t;
 }
-__device__ const LatSpeeds<D3Q39> g_speeds39 = make_speeds<D3Q39>();
-__device__ const LatSpeeds<D3Q19> g_speeds19 = make_speeds<D3Q19>();
+__device__ const LatXi<D3Q39, float> g_xi39f = make_xi<D3Q39, float>();
+__device__ const LatXi<D3Q39, double> g_xi39d = make_xi<D3Q39, double>();
+__device__ const LatXi<D3Q19, float> g_xi19f = make_xi<D3Q19, float>();
+__device__ const LatXi<D3Q19, double> g_xi19d = make_xi<D3Q19, double>();
 
-template <class LAT>
-__device__ __forceinline__ int lat_e(int a, int i) {
-    if constexpr (LAT::Q == 39)
-        return g_speeds39.e[3 * a + i];
-    else
-        return g_speeds19.e[3 * a + i];
+template <class LAT, typename Real>
+__device__ __forceinline__ const LatXi<LAT, Real>& lat_xi() {
+    if constexpr (LAT::Q == 39) {
+        if constexpr (sizeof(Real) == 4)
+            return g_xi39f;
+        else
+            return g_xi39d;
+    } else {
+        if constexpr (sizeof(Real) == 4)
+            return g_xi19f;
+        else
+            return g_xi19d;
+    }
 }
 
 // DSMC2LB: one warp per coupling node. Lanes 0-19 read the cell's 20 sums and scale them
@@ -63,14 +76,9 @@ __device__ __forceinline__ int lat_e(int a, int i) {
 template <typename Real, class LAT>
 __global__ void __launch_bounds__(128) k_d2l(MapArgs<Real> a) {
     pdl_begin();
-    __shared__ Real sx[3 * LAT::Q];
-    __shared__ Real sw[LAT::Q];
-    for (int q = threadIdx.x; q < LAT::Q; q += blockDim.x) {
-#pragma unroll
-        for (int i = 0; i < 3; ++i) sx[3 * q + i] = (Real)(lat_r<LAT>() * (double)lat_e<LAT>(q, i));
-        sw[q] = (Real)LatTab<LAT>::w(q);
-    }
-    __syncthreads();
+    const LatXi<LAT, Real>& lt = lat_xi<LAT, Real>();
+    const Real* sx = lt.x;
+    const Real* sw = lt.w;
     const unsigned lane = lane_id();
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -228,11 +236,12 @@ __device__ __forceinline__ void grad_coefficients(const MapArgs<Real>& a, int ce
     const int r = a.lb_ratio;
     const int q0 = (int)lane, q1 = (int)lane + 32;
     const bool v0 = q0 < Q, v1 = q1 < Q;
+    const LatXi<LAT, Real>& lt = lat_xi<LAT, Real>();
     Real xi0[3] = {0, 0, 0}, xi1[3] = {0, 0, 0};
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        if (v0) xi0[i] = (Real)(a.r_lat * (double)lat_e<LAT>(q0, i));
-        if (v1) xi1[i] = (Real)(a.r_lat * (double)lat_e<LAT>(q1, i));
+        if (v0) xi0[i] = lt.x[3 * q0 + i];
+        if (v1) xi1[i] = lt.x[3 * q1 + i];
     }
     const int ix = cell % a.ncx, iy = cell / a.ncx;
     // mean populations of the cell's nodes, summed in node order (dy, dx)
