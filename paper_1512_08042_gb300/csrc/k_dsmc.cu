@@ -214,9 +214,10 @@ constexpr int kGroup = 8;
 
 template <typename Real>
 struct CollideCfg {
-    static constexpr int WARPS = sizeof(Real) == 4 ? 8 : 4;
     static constexpr int MINB = sizeof(Real) == 4 ? 4 : 2;  // resident blocks per SM
 };
+constexpr int kCollideWarps = 8;  // 32 cells per block
+constexpr int kChainSteps = 16;   // candidates per cell drawn per pass of the NTC phase
 
 // Ascending bitonic sort of G R keys held by the G lanes of a group, R per lane (key r of
 // group lane l at position l + G r). Constant trip counts: the keys stay in registers.
@@ -288,131 +289,141 @@ __device__ __forceinline__ void gather_slots(const DsmcArgs<Real>& a, int64_t ba
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(CollideCfg<Real>::WARPS * 32, CollideCfg<Real>::MINB)
+__global__ void __launch_bounds__(kCollideWarps * 32, CollideCfg<Real>::MINB)
     k_collide(DsmcArgs<Real> a, uint32_t pool) {
     pdl_begin();
     constexpr int G = kGroup;
-    constexpr int CPW = 32 / G;         // cells per warp
-    constexpr int SMALL = 64;           // cells up to this size are sorted in registers
+    constexpr int CPW = 32 / G;           // cells per warp in phases A and C
+    constexpr int WARPS = kCollideWarps;
+    constexpr int NC = WARPS * CPW;       // cells per block (one chain lane each in phase B)
+    constexpr int SMALL = 64;             // cells up to this size are sorted in registers
     constexpr int R = SMALL / G;
-    constexpr int WARPS = CollideCfg<Real>::WARPS;
+    constexpr int KC = kChainSteps;       // candidates per cell drawn per pass of phase B
+    static_assert(NC == 32, "phase B runs one lane per cell of the block in one warp");
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint32_t s_n[NC], s_off[NC], s_nsel[NC];
+    __shared__ Real s_cm[NC];
+    __shared__ uint32_t s_fits;
     __shared__ unsigned long long s_cnt[WARPS][2];
     __shared__ uint32_t s_live[WARPS], s_flags[WARPS];
     const int w = threadIdx.x >> 5;
     const unsigned lane = lane_id();
     const int grp = (int)lane / G, gl = (int)lane % G;
-    const int leader = grp * G;
+    const int gi = w * CPW + grp;  // the group's cell within the block
     const uint32_t bin = (uint32_t)a.bin;
-    // per warp: vx, vy, vz (Real) and tags (u32), `pool` entries each, shared by the warp's
-    // groups (each takes its cell's count, in group order)
-    Real* wv = reinterpret_cast<Real*>(smem_raw) + (size_t)w * 3 * pool;
-    uint32_t* wst = reinterpret_cast<uint32_t*>(reinterpret_cast<Real*>(smem_raw) +
-                                                 (size_t)WARPS * 3 * pool) +
-                    (size_t)w * pool;
+    // shared memory: the block's pool of vx, vy, vz (Real) and tags (u32), `pool` slots each,
+    // then the candidates of one pass of phase B
+    Real* pv = reinterpret_cast<Real*>(smem_raw);
+    uint32_t* pst = reinterpret_cast<uint32_t*>(pv + 3 * (size_t)pool);
+    uint32_t* c_ij = pst + pool;
+    Real* c_R = reinterpret_cast<Real*>(c_ij + NC * KC);
+    Real* c_nx = c_R + NC * KC;
+    Real* c_ny = c_nx + NC * KC;
+    Real* c_nz = c_ny + NC * KC;
     const uint32_t s = a.ctrl[CTRL_STEP];
     const bool do_sample = (s % (uint32_t)a.sample_every) == 0u;
     const Real coll_dt = (Real)a.coll_dt;
     unsigned long long ncand_tot = 0, ncoll_tot = 0;
     uint32_t flags = 0, nlive = 0;
 
-    // one batch of CPW consecutive cells per warp
-    const int nbatch = (a.ncells + CPW - 1) / CPW;
-    const int bt = blockIdx.x * WARPS + w;
-    if (bt < nbatch) {
-        const int c = bt * CPW + grp;
-        const bool has = c < a.ncells;
-        const int64_t base = (int64_t)c * bin;
-        // the cell's loads are issued together: count, the first SMALL tag slots, the
-        // leader's NTC state and the lane's three moment sums
-        uint32_t n_all = has ? a.count_d[c] : 0u;
-        uint32_t vl[R];
+    const int c = blockIdx.x * NC + gi;
+    const bool has = c < a.ncells;
+    const int64_t base = (int64_t)c * bin;
+    // the cell's loads are issued together: count, the first SMALL tag slots, the leader's
+    // NTC state and the lane's three moment sums
+    uint32_t n_all = has ? a.count_d[c] : 0u;
+    uint32_t vl[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const uint32_t k = (uint32_t)(gl + G * r);
-            vl[r] = (has && k < bin) ? a.tag[base + k] : 0xFFFFFFFFu;
+    for (int r = 0; r < R; ++r) {
+        const uint32_t k = (uint32_t)(gl + G * r);
+        vl[r] = (has && k < bin) ? a.tag[base + k] : 0xFFFFFFFFu;
+    }
+    uint32_t nb0 = 0;
+    Real cm0 = (Real)0, rem0 = (Real)0;
+    if (has && gl == 0) {
+        nb0 = a.nbar_sum[c];
+        cm0 = a.crmax[c];
+        rem0 = a.rem[c];
+    }
+    double acc0[3] = {0.0, 0.0, 0.0};
+    if (has && do_sample) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            if (3 * gl + q < kMoments) acc0[q] = a.acc[(size_t)c * kMoments + 3 * gl + q];
+    }
+    if (n_all > bin) n_all = bin;
+    // the cells' regions of the block pool (exclusive scan of the counts); if they do not
+    // fit, the cells take the whole pool one after another
+    if (gl == 0) s_n[gi] = n_all;
+    __syncthreads();
+    if (w == 0) {
+        const uint32_t x = s_n[lane];
+        uint32_t inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, inc, o);
+            if (lane >= (unsigned)o) inc += t;
         }
-        uint32_t nb0 = 0;
-        Real cm0 = (Real)0, rem0 = (Real)0;
-        if (has && gl == 0) {
-            nb0 = a.nbar_sum[c];
-            cm0 = a.crmax[c];
-            rem0 = a.rem[c];
-        }
-        double acc0[3] = {0.0, 0.0, 0.0};
-        if (has && do_sample) {
+        s_off[lane] = inc - x;
+        if (lane == 31) s_fits = inc <= pool ? 1u : 0u;
+    }
+    __syncthreads();
+    const bool fits = s_fits != 0u;
+    const int rounds = fits ? 1 : NC;
+    for (int round = 0; round < rounds; ++round) {
+        const bool act = fits || gi == round;
+        const bool has_r = has && act;
+        const uint32_t n = act ? n_all : 0u;
+        const uint32_t poff = fits ? s_off[gi] : 0u;
+        Real* vx = pv + poff;
+        Real* vy = pv + pool + poff;
+        Real* vz = pv + 2 * pool + poff;
+        uint32_t* st = pst + poff;
+        // A. stable order (ascending origin slot) and gather
+        {
+            uint32_t v[R];
 #pragma unroll
-            for (int q = 0; q < 3; ++q)
-                if (3 * gl + q < kMoments) acc0[q] = a.acc[(size_t)c * kMoments + 3 * gl + q];
-        }
-        if (n_all > bin) n_all = bin;
-        // the groups' regions of the warp pool; if the batch does not fit, the groups take
-        // the whole pool one after another
-        uint32_t off = 0, total = 0;
+            for (int r = 0; r < R; ++r) {
+                const uint32_t k = (uint32_t)(gl + G * r);
+                v[r] = (n <= (uint32_t)SMALL && k < n) ? vl[r] : 0xFFFFFFFFu;
+            }
+            bitonic_group<G, R>(v);
+            if (n > (uint32_t)SMALL)
+                for (uint32_t k = gl; k < n; k += G) st[k] = a.tag[base + k];
+            __syncwarp();
+            if (n <= (uint32_t)SMALL) {
 #pragma unroll
-        for (int g = 0; g < CPW; ++g) {
-            const uint32_t ng = __shfl_sync(kFull, n_all, g * G);
-            if (g < grp) off += ng;
-            total += ng;
-        }
-        const bool fits = total <= pool;
-        const int rounds = fits ? 1 : CPW;
-        for (int round = 0; round < rounds; ++round) {
-            const bool act = fits || grp == round;
-            const bool has_r = has && act;
-            const uint32_t n = act ? n_all : 0u;
-            const uint32_t poff = fits ? off : 0u;
-            Real* vx = wv + poff;
-            Real* vy = wv + pool + poff;
-            Real* vz = wv + 2 * pool + poff;
-            uint32_t* st = wst + poff;
-            // 1. stable order (ascending origin slot) and gather
-            {
-                uint32_t v[R];
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const uint32_t k = (uint32_t)(gl + G * r);
-                    v[r] = (n <= (uint32_t)SMALL && k < n) ? vl[r] : 0xFFFFFFFFu;
-                }
-                bitonic_group<G, R>(v);
-                if (n > (uint32_t)SMALL)
-                    for (uint32_t k = gl; k < n; k += G) st[k] = a.tag[base + k];
-                __syncwarp();
-                if (n <= (uint32_t)SMALL) {
-#pragma unroll
-                    for (int r0 = 0; r0 < R; r0 += R / 4)
-                        gather_slots<Real, G, R / 4>(a, base, gl, r0, n, v + r0, vx, vy, vz);
-                } else {
-                    // rank of each tag = number of smaller tags in the cell
-                    for (uint32_t k = gl; k < n; k += G) {
-                        const uint32_t t = st[k];
-                        uint32_t r = 0;
-                        for (uint32_t m = 0; m < n; ++m) r += st[m] < t ? 1u : 0u;
-                        const Real px = a.sx[t], py = a.sy[t];
-                        const Real ux = a.svx[t], uy = a.svy[t], uz = a.svz[t];
-                        a.dx[base + r] = px;
-                        a.dy[base + r] = py;
-                        vx[r] = ux;
-                        vy[r] = uy;
-                        vz[r] = uz;
-                    }
+                for (int r0 = 0; r0 < R; r0 += R / 4)
+                    gather_slots<Real, G, R / 4>(a, base, gl, r0, n, v + r0, vx, vy, vz);
+            } else {
+                // rank of each tag = number of smaller tags in the cell
+                for (uint32_t k = gl; k < n; k += G) {
+                    const uint32_t t = st[k];
+                    uint32_t r = 0;
+                    for (uint32_t m = 0; m < n; ++m) r += st[m] < t ? 1u : 0u;
+                    const Real px = a.sx[t], py = a.sy[t];
+                    const Real ux = a.svx[t], uy = a.svy[t], uz = a.svz[t];
+                    a.dx[base + r] = px;
+                    a.dy[base + r] = py;
+                    vx[r] = ux;
+                    vy[r] = uy;
+                    vz[r] = uz;
                 }
             }
-            __syncwarp();
-            // 2. NTC: N_cand = 1/2 N Nbar F_N (sigma c_r)_max dt / V_c + remainder (group leader)
+        }
+        // N_cand = 1/2 N Nbar F_N (sigma c_r)_max dt / V_c + remainder (group leader)
+        if (gl == 0) {
             uint32_t nsel = 0;
-            Real cm = (Real)0;
-            if (has_r && gl == 0) {
+            if (has_r) {
                 const uint32_t nb = nb0 + n;
                 a.nbar_sum[c] = nb;
                 a.count_s[c] = 0;  // the source half's count is not needed after the move
-                cm = cm0;
                 nlive += n;
                 if (n > 32767u) {
                     flags |= HYB_ST_CELL_OVERFLOW;  // pair indices are packed in 15 and 16 bits
                 } else if (n >= 2) {
                     const Real nbar = (Real)nb / (Real)(s + 1u);
-                    const Real ncand = (Real)0.5 * (Real)n * nbar * cm * coll_dt + rem0;
+                    const Real ncand = (Real)0.5 * (Real)n * nbar * cm0 * coll_dt + rem0;
                     const Real fl = floor(ncand);
                     a.rem[c] = ncand - fl;
                     if (fl > (Real)16777215) {
@@ -422,120 +433,134 @@ __global__ void __launch_bounds__(CollideCfg<Real>::WARPS * 32, CollideCfg<Real>
                         nsel = (uint32_t)fl;
                     }
                 }
+                ncand_tot += nsel;
             }
-            nsel = __shfl_sync(kFull, nsel, leader);
-            cm = __shfl_sync(kFull, cm, leader);
-            const uint32_t maxsel = __reduce_max_sync(kFull, nsel);
-            uint32_t ncoll = 0;
-            for (uint32_t ch = 0; ch < maxsel; ch += G) {
-                // the group's lanes draw G candidates in parallel; they are applied in order below
-                const uint32_t k = ch + gl;
-                uint32_t ij = 0;
-                Real R0 = (Real)0, nx = (Real)0, ny = (Real)0, nz = (Real)0;
-                if (k < nsel) {
-                    const uint4 r = draw(a.seed, (uint32_t)c, s, TAG_NTC_PAIR, k, 0);
-                    const uint32_t ci = uindex(r.x, n);
-                    uint32_t cj = uindex(r.y, n - 1u);
+            s_nsel[gi] = nsel;
+            s_cm[gi] = cm0;
+        }
+        __syncthreads();
+        // B. NTC collisions. Each pass draws KC candidates of every cell of the block in
+        // parallel (all threads), then warp 0 applies them in order, one lane per cell.
+        uint32_t maxsel = __reduce_max_sync(kFull, s_nsel[lane]);
+        Real cm = (Real)0;
+        uint32_t ncoll = 0;
+        Real* gvx = nullptr;
+        Real* gvy = nullptr;
+        Real* gvz = nullptr;
+        if (w == 0) {
+            cm = s_cm[lane];
+            const uint32_t go = fits ? s_off[lane] : 0u;
+            gvx = pv + go;
+            gvy = pv + pool + go;
+            gvz = pv + 2 * pool + go;
+        }
+        for (uint32_t k0 = 0; k0 < maxsel; k0 += KC) {
+            for (int t = threadIdx.x; t < NC * KC; t += WARPS * 32) {
+                const int g = t / KC, kk = t % KC;
+                const uint32_t k = k0 + (uint32_t)kk;
+                if (k < s_nsel[g]) {
+                    const uint32_t cg = (uint32_t)(blockIdx.x * NC + g);
+                    const uint32_t ng = s_n[g];
+                    const uint4 r = draw(a.seed, cg, s, TAG_NTC_PAIR, k, 0);
+                    const uint32_t ci = uindex(r.x, ng);
+                    uint32_t cj = uindex(r.y, ng - 1u);
                     if (cj >= ci) cj += 1u;
-                    R0 = (Real)u01f(r.z);
-                    const int ok = unit_vector(a.seed, (uint32_t)c, s, k, nx, ny, nz);
-                    ij = ci | (cj << 15) | (ok ? 0u : 0x80000000u);
+                    Real nx = (Real)0, ny = (Real)0, nz = (Real)0;
+                    const int ok = unit_vector(a.seed, cg, s, k, nx, ny, nz);
+                    c_ij[t] = ci | (cj << 15) | (ok ? 0u : 0x80000000u);
+                    c_R[t] = (Real)u01f(r.z);
+                    c_nx[t] = nx;
+                    c_ny[t] = ny;
+                    c_nz[t] = nz;
                 }
+            }
+            __syncthreads();
+            if (w == 0) {
+                const uint32_t nsel = s_nsel[lane];
 #pragma unroll 1
-                for (int m = 0; m < G; ++m) {
-                    const int src = leader + m;
-                    const uint32_t ijm = __shfl_sync(kFull, ij, src);
-                    const Real Rm = __shfl_sync(kFull, R0, src);
-                    const Real nxm = __shfl_sync(kFull, nx, src);
-                    const Real nym = __shfl_sync(kFull, ny, src);
-                    const Real nzm = __shfl_sync(kFull, nz, src);
-                    bool acc_pair = false;
-                    Real cx = 0, cy = 0, cz = 0, h = 0;
-                    uint32_t i = 0, j = 0;
-                    if (ch + (uint32_t)m < nsel) {
-                        i = ijm & 0x7FFFu;
-                        j = (ijm >> 15) & 0xFFFFu;
-                        const Real ax = vx[i], ay = vy[i], az = vz[i];
-                        const Real bx = vx[j], by = vy[j], bz = vz[j];
+                for (int kk = 0; kk < KC; ++kk) {
+                    if (k0 + (uint32_t)kk < nsel) {
+                        const int t = (int)lane * KC + kk;
+                        const uint32_t ij = c_ij[t];
+                        const uint32_t i = ij & 0x7FFFu, j = (ij >> 15) & 0xFFFFu;
+                        const Real ax = gvx[i], ay = gvy[i], az = gvz[i];
+                        const Real bx = gvx[j], by = gvy[j], bz = gvz[j];
                         const Real ddx = ax - bx, ddy = ay - by, ddz = az - bz;
                         const Real cr = sqrt(ddx * ddx + ddy * ddy + ddz * ddz);
                         if (cr > cm) cm = cr;
-                        if (cr > Rm * cm) {
-                            if (ijm & 0x80000000u) {
+                        if (cr > c_R[t] * cm) {
+                            if (ij & 0x80000000u) {
                                 flags |= HYB_ST_SCATTER_CAP;
                             } else {
-                                acc_pair = true;
-                                cx = (ax + bx) * (Real)0.5;
-                                cy = (ay + by) * (Real)0.5;
-                                cz = (az + bz) * (Real)0.5;
-                                h = cr * (Real)0.5;
+                                const Real cx = (ax + bx) * (Real)0.5;
+                                const Real cy = (ay + by) * (Real)0.5;
+                                const Real cz = (az + bz) * (Real)0.5;
+                                const Real h = cr * (Real)0.5;
+                                const Real hx = h * c_nx[t], hy = h * c_ny[t], hz = h * c_nz[t];
+                                gvx[i] = cx + hx;
+                                gvy[i] = cy + hy;
+                                gvz[i] = cz + hz;
+                                gvx[j] = cx - hx;
+                                gvy[j] = cy - hy;
+                                gvz[j] = cz - hz;
+                                ncoll += 1;
                             }
                         }
                     }
-                    __syncwarp();
-                    if (acc_pair && gl == 0) {
-                        vx[i] = cx + h * nxm;
-                        vy[i] = cy + h * nym;
-                        vz[i] = cz + h * nzm;
-                        vx[j] = cx - h * nxm;
-                        vy[j] = cy - h * nym;
-                        vz[j] = cz - h * nzm;
-                    }
-                    if (acc_pair) ncoll += 1;
-                    __syncwarp();
                 }
             }
-            if (has_r && gl == 0) {
-                a.crmax[c] = cm;
-                ncand_tot += nsel;
-                ncoll_tot += ncoll;
-            }
-            // 3. write-out and moment sums (group lanes over the cell's particles)
-            Real mo[kMoments];
-#pragma unroll
-            for (int q = 0; q < kMoments; ++q) mo[q] = (Real)0;
-            for (uint32_t k = gl; k < n; k += G) {
-                const Real ux = vx[k], uy = vy[k], uz = vz[k];
-                a.dvx[base + k] = ux;
-                a.dvy[base + k] = uy;
-                a.dvz[base + k] = uz;
-                if (do_sample) {
-                    const Real xx = ux * ux, yy = uy * uy, zz = uz * uz;
-                    const Real xy = ux * uy, xz = ux * uz, yz = uy * uz;
-                    mo[0] += (Real)1;
-                    mo[1] += ux; mo[2] += uy; mo[3] += uz;
-                    mo[4] += xx; mo[5] += xy; mo[6] += xz; mo[7] += yy; mo[8] += yz; mo[9] += zz;
-                    mo[10] += xx * ux; mo[11] += xx * uy; mo[12] += xx * uz; mo[13] += yy * ux;
-                    mo[14] += xy * uz; mo[15] += zz * ux; mo[16] += yy * uy; mo[17] += yy * uz;
-                    mo[18] += zz * uy; mo[19] += zz * uz;
-                }
-            }
-            if (do_sample) {
-                // halving exchange over the group: lane gl ends with the totals of moments
-                // 3 gl, 3 gl + 1, 3 gl + 2
-                Real t[24];
-#pragma unroll
-                for (int q = 0; q < 24; ++q) t[q] = q < kMoments ? mo[q] : (Real)0;
-#pragma unroll
-                for (int o = G / 2, len = 12; o >= 1; o >>= 1, len >>= 1) {
-                    const bool hi = (gl & o) != 0;
-#pragma unroll
-                    for (int q = 0; q < len; ++q) {
-                        const Real send = hi ? t[q] : t[q + len];
-                        const Real keep = hi ? t[q + len] : t[q];
-                        t[q] = keep + __shfl_xor_sync(kFull, send, o);
-                    }
-                }
-                if (has_r) {
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        const int mq = 3 * gl + q;
-                        if (mq < kMoments) a.acc[(size_t)c * kMoments + mq] = acc0[q] + (double)t[q];
-                    }
-                }
-            }
-            __syncwarp();
+            __syncthreads();
         }
+        if (w == 0) {
+            const int cl = blockIdx.x * NC + (int)lane;
+            if (cl < a.ncells && (fits || (int)lane == round)) a.crmax[cl] = cm;
+            ncoll_tot += ncoll;
+        }
+        // C. write-out and moment sums (group lanes over the cell's particles)
+        Real mo[kMoments];
+#pragma unroll
+        for (int q = 0; q < kMoments; ++q) mo[q] = (Real)0;
+        for (uint32_t k = gl; k < n; k += G) {
+            const Real ux = vx[k], uy = vy[k], uz = vz[k];
+            a.dvx[base + k] = ux;
+            a.dvy[base + k] = uy;
+            a.dvz[base + k] = uz;
+            if (do_sample) {
+                const Real xx = ux * ux, yy = uy * uy, zz = uz * uz;
+                const Real xy = ux * uy, xz = ux * uz, yz = uy * uz;
+                mo[0] += (Real)1;
+                mo[1] += ux; mo[2] += uy; mo[3] += uz;
+                mo[4] += xx; mo[5] += xy; mo[6] += xz; mo[7] += yy; mo[8] += yz; mo[9] += zz;
+                mo[10] += xx * ux; mo[11] += xx * uy; mo[12] += xx * uz; mo[13] += yy * ux;
+                mo[14] += xy * uz; mo[15] += zz * ux; mo[16] += yy * uy; mo[17] += yy * uz;
+                mo[18] += zz * uy; mo[19] += zz * uz;
+            }
+        }
+        if (do_sample) {
+            // halving exchange over the group: lane gl ends with the totals of moments
+            // 3 gl, 3 gl + 1, 3 gl + 2
+            Real t[24];
+#pragma unroll
+            for (int q = 0; q < 24; ++q) t[q] = q < kMoments ? mo[q] : (Real)0;
+#pragma unroll
+            for (int o = G / 2, len = 12; o >= 1; o >>= 1, len >>= 1) {
+                const bool hi = (gl & o) != 0;
+#pragma unroll
+                for (int q = 0; q < len; ++q) {
+                    const Real send = hi ? t[q] : t[q + len];
+                    const Real keep = hi ? t[q + len] : t[q];
+                    t[q] = keep + __shfl_xor_sync(kFull, send, o);
+                }
+            }
+            if (has_r) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const int mq = 3 * gl + q;
+                    if (mq < kMoments) a.acc[(size_t)c * kMoments + mq] = acc0[q] + (double)t[q];
+                }
+            }
+        }
+        __syncthreads();  // the pool is reused by the next round
     }
     // event counters: per block, one atomic per counter
     ncand_tot = __reduce_add_sync(kFull, (unsigned)ncand_tot);
@@ -645,21 +670,19 @@ cudaError_t step_impl(Ctx& c) {
                                c.stream, a);
     if (e != cudaSuccess) return e;
     prof_end(c, K_MOVE);
-    // shared memory: per warp a pool of slots for its cells (3 Real + 1 u32 each), room for
-    // 1.75 ppc per cell on average and at least one full bin
-    constexpr int WARPS = CollideCfg<Real>::WARPS;
-    constexpr int CPW = 32 / kGroup;
-    uint32_t pool = (uint32_t)(((int64_t)CPW * c.p.ppc * 7 / 4 + 31) / 32 * 32);
+    // shared memory: a pool of slots for the block's cells (3 Real + 1 u32 each), room for
+    // 1.5 ppc per cell on average and at least one full bin, then one pass of NTC candidates
+    constexpr int NC = kCollideWarps * (32 / kGroup);
+    uint32_t pool = (uint32_t)(((int64_t)NC * c.p.ppc * 3 / 2 + 31) / 32 * 32);
     if (pool < (uint32_t)c.d.bin) pool = (uint32_t)c.d.bin;
-    const size_t smem = (size_t)WARPS * pool * (3 * sizeof(Real) + 4);
-    if (smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(k_collide<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    const int64_t nbatch = (c.d.ncells + CPW - 1) / CPW;
-    const unsigned grid = (unsigned)((nbatch + WARPS - 1) / WARPS);
+    const size_t smem = (size_t)pool * (3 * sizeof(Real) + 4) +
+                        (size_t)NC * kChainSteps * (4 + 4 * sizeof(Real));
+    // (dynamic and static shared memory together may exceed the default 48 KB)
+    e = cudaFuncSetAttribute(k_collide<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = (unsigned)((c.d.ncells + NC - 1) / NC);
     prof_begin(c, K_COLLIDE);
-    e = launch_pdl(k_collide<Real>, dim3(grid), dim3(WARPS * 32), smem, c.stream, a, pool);
+    e = launch_pdl(k_collide<Real>, dim3(grid), dim3(kCollideWarps * 32), smem, c.stream, a, pool);
     if (e != cudaSuccess) return e;
     prof_end(c, K_COLLIDE);
     return cudaGetLastError();
