@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define HYB_ABI_VERSION 1u
+#define HYB_ABI_VERSION 2u
 
 typedef enum {
     HYB_OK = 0,
@@ -129,7 +129,11 @@ typedef struct {
  *   ctrl          u32[16]           [0] status bits, [1] particles in use, [2] DSMC steps
  *                                   taken, [3] moment samples taken, [4]..[15] scratch
  *   counters      u64[16]           event counters, HYB_C_*
- *   map_scratch                     LB2DSMC per-cell records */
+ *   map_scratch                     LB2DSMC per-cell records
+ *   moved         Real[ncells*bin][8]  the particles of the DSMC step in progress after the
+ *                                   move, by origin slot: x, y, vx, vy, vz and 3 unused (one
+ *                                   record per 32-byte sector in FP32); scratch between the
+ *                                   two kernels of a step */
 typedef struct {
     uint64_t total_bytes;
     int64_t capacity, ncells, nnodes;
@@ -139,6 +143,7 @@ typedef struct {
     uint64_t crmax, rem, nbar_sum, acc;
     uint64_t f[2];
     uint64_t ctrl, counters, map_scratch;
+    uint64_t moved;
 } hyb_layout;
 
 typedef struct hyb_ctx hyb_ctx; /* opaque, owned by the library */

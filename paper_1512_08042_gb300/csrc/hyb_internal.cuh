@@ -77,6 +77,7 @@ struct State {
     uint32_t* ctrl;
     unsigned long long* counters;
     GradRec* grad;
+    void* moved;
 };
 
 // Everything a DSMC kernel needs, passed by value: the move updates the source half in
@@ -89,11 +90,7 @@ struct DsmcArgs {
     const Real* svx;
     const Real* svy;
     const Real* svz;
-    Real* mx;
-    Real* my;
-    Real* mvx;
-    Real* mvy;
-    Real* mvz;
+    Real* rec;  // moved particles by origin slot, 8 Real per record
     Real* dx;
     Real* dy;
     Real* dvx;

@@ -8,16 +8,17 @@
 // launches:
 //   k_move     one warp per source cell: body-force kick, free flight, diffuse wall
 //              re-emission (Sec. 3.1), periodic wrap, new cell; the moved particle is written
-//              back in place and its slot is appended to the tag list of its new cell's bin
-//              by a warp-aggregated atomic. The last block to finish advances the step
-//              counters.
-//   k_collide  one group of 8 lanes per cell, one batch of 4 consecutive cells per warp: the
-//              cell's tags are put in stable order (ascending origin slot = origin cell, then
-//              rank in it: a bitonic sort in registers), the particles are gathered from the
-//              source half into the bin of the other half, NTC collisions (Eq.
-//              collisionnumber) run in shared memory (a pool per warp that the batch's cells
-//              share), and the sums 1, v, vv, vvv are added to the FP64 cumulative sums of the
-//              cell (Sec. 2.1, Fig. 1).
+//              as one record (x, y, vx, vy, vz) at its origin slot of the `moved` scratch, and
+//              the slot is appended to the tag list of its new cell's bin by a warp-aggregated
+//              atomic.
+//   k_collide  32 consecutive cells per block, a group of 8 lanes per cell: the cell's tags
+//              are put in stable order (ascending origin slot = origin cell, then rank in it:
+//              a bitonic sort in registers), the records are gathered into the bin of the
+//              other half (positions) and a shared-memory pool (velocities), the NTC
+//              candidates of all 32 cells are drawn by the whole block and applied by one
+//              warp with a lane per cell (Eq. collisionnumber), and the sums 1, v, vv, vvv are
+//              added to the FP64 cumulative sums of the cell (Sec. 2.1, Fig. 1). The last
+//              block to finish advances the step counters.
 // This file is compiled without FMA contraction so that positions, cell keys, pair choices
 // and post-collision velocities are the IEEE float (or double) results of the written
 // expressions.
@@ -105,6 +106,43 @@ __global__ void k_init_cells(DsmcArgs<Real> a) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Moved-particle records: 8 Real per origin slot (x, y, vx, vy, vz, 3 unused), written whole
+// by the move and read by the collide with one 32-byte sector per particle (FP32).
+__device__ __forceinline__ void rec_store(float* rec, int64_t i, float x, float y, float u, float v,
+                                          float w) {
+    float4* p = reinterpret_cast<float4*>(rec) + 2 * i;
+    p[0] = make_float4(x, y, u, v);
+    p[1] = make_float4(w, 0.0f, 0.0f, 0.0f);
+}
+__device__ __forceinline__ void rec_store(double* rec, int64_t i, double x, double y, double u,
+                                          double v, double w) {
+    double2* p = reinterpret_cast<double2*>(rec) + 4 * i;
+    p[0] = make_double2(x, y);
+    p[1] = make_double2(u, v);
+    p[2] = make_double2(w, 0.0);
+}
+__device__ __forceinline__ void rec_load(const float* rec, int64_t i, float& x, float& y, float& u,
+                                         float& v, float& w) {
+    const float4* p = reinterpret_cast<const float4*>(rec) + 2 * i;
+    const float4 a = p[0];
+    x = a.x;
+    y = a.y;
+    u = a.z;
+    v = a.w;
+    w = reinterpret_cast<const float*>(p + 1)[0];
+}
+__device__ __forceinline__ void rec_load(const double* rec, int64_t i, double& x, double& y,
+                                         double& u, double& v, double& w) {
+    const double2* p = reinterpret_cast<const double2*>(rec) + 4 * i;
+    const double2 a = p[0], b = p[1];
+    x = a.x;
+    y = a.y;
+    u = b.x;
+    v = b.y;
+    w = reinterpret_cast<const double*>(p + 2)[0];
+}
+
+// ---------------------------------------------------------------------------------------
 // Move (kick, drift, walls, wrap) and binning into the other half.
 template <typename Real>
 __global__ void __launch_bounds__(256) k_move(DsmcArgs<Real> a) {
@@ -179,11 +217,7 @@ __global__ void __launch_bounds__(256) k_move(DsmcArgs<Real> a) {
                 b0 = __shfl_sync(peers, b0, leader);
                 const uint32_t arr = b0 + (uint32_t)__popc(peers & lt);
                 const int64_t i = base + k;
-                a.mx[i] = px;
-                a.my[i] = py;
-                a.mvx[i] = ux;
-                a.mvy[i] = uy;
-                a.mvz[i] = uz;
+                rec_store(a.rec, i, px, py, ux, uy, uz);
                 if (arr < bin)
                     a.tag[(int64_t)key * bin + arr] = (uint32_t)i;
                 else
@@ -254,36 +288,26 @@ __device__ __forceinline__ void bitonic_group(uint32_t (&v)[R]) {
     }
 }
 
-// Gathers the particles of sorted positions k = gl + G r (r < RR) from the source slots
-// src[r]: positions into the cell's bin of the other half, velocities into shared memory.
-// Every load is issued before the first store, so the loads of all RR slots are in flight
-// together (the stores could alias the loads as far as the compiler knows).
+// Gathers the particles of sorted positions k = gl + G r (r < RR) from the records of the
+// origin slots src[r]: positions into the cell's bin of the other half, velocities into
+// shared memory. The record, position and shared-memory pointers are declared free of
+// aliasing, so the loads of all slots can be in flight before the first store.
 template <typename Real, int G, int RR>
-__device__ __forceinline__ void gather_slots(const DsmcArgs<Real>& a, int64_t base, int gl, int r0,
-                                             uint32_t n, const uint32_t* src, Real* vx, Real* vy,
-                                             Real* vz) {
-    Real px[RR], py[RR], ux[RR], uy[RR], uz[RR];
+__device__ __forceinline__ void gather_slots(const Real* __restrict__ rec, Real* __restrict__ dx,
+                                             Real* __restrict__ dy, int gl, uint32_t n,
+                                             const uint32_t* src, Real* __restrict__ vx,
+                                             Real* __restrict__ vy, Real* __restrict__ vz) {
 #pragma unroll
     for (int r = 0; r < RR; ++r) {
-        const uint32_t k = (uint32_t)(gl + G * (r0 + r));
+        const uint32_t k = (uint32_t)(gl + G * r);
         if (k < n) {
-            const uint32_t i = src[r];
-            px[r] = a.sx[i];
-            py[r] = a.sy[i];
-            ux[r] = a.svx[i];
-            uy[r] = a.svy[i];
-            uz[r] = a.svz[i];
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < RR; ++r) {
-        const uint32_t k = (uint32_t)(gl + G * (r0 + r));
-        if (k < n) {
-            a.dx[base + k] = px[r];
-            a.dy[base + k] = py[r];
-            vx[k] = ux[r];
-            vy[k] = uy[r];
-            vz[k] = uz[r];
+            Real px, py, ux, uy, uz;
+            rec_load(rec, (int64_t)src[r], px, py, ux, uy, uz);
+            dx[k] = px;
+            dy[k] = py;
+            vx[k] = ux;
+            vy[k] = uy;
+            vz[k] = uz;
         }
     }
 }
@@ -392,17 +416,15 @@ __global__ void __launch_bounds__(kCollideWarps * 32, CollideCfg<Real>::MINB)
                 for (uint32_t k = gl; k < n; k += G) st[k] = a.tag[base + k];
             __syncwarp();
             if (n <= (uint32_t)SMALL) {
-#pragma unroll
-                for (int r0 = 0; r0 < R; r0 += R / 4)
-                    gather_slots<Real, G, R / 4>(a, base, gl, r0, n, v + r0, vx, vy, vz);
+                gather_slots<Real, G, R>(a.rec, a.dx + base, a.dy + base, gl, n, v, vx, vy, vz);
             } else {
                 // rank of each tag = number of smaller tags in the cell
                 for (uint32_t k = gl; k < n; k += G) {
                     const uint32_t t = st[k];
                     uint32_t r = 0;
                     for (uint32_t m = 0; m < n; ++m) r += st[m] < t ? 1u : 0u;
-                    const Real px = a.sx[t], py = a.sy[t];
-                    const Real ux = a.svx[t], uy = a.svy[t], uz = a.svz[t];
+                    Real px, py, ux, uy, uz;
+                    rec_load(a.rec, (int64_t)t, px, py, ux, uy, uz);
                     a.dx[base + r] = px;
                     a.dy[base + r] = py;
                     vx[r] = ux;
@@ -609,11 +631,7 @@ DsmcArgs<Real> make_args(Ctx& c) {
     a.svx = (const Real*)c.st.pvx[h];
     a.svy = (const Real*)c.st.pvy[h];
     a.svz = (const Real*)c.st.pvz[h];
-    a.mx = (Real*)c.st.px[h];
-    a.my = (Real*)c.st.py[h];
-    a.mvx = (Real*)c.st.pvx[h];
-    a.mvy = (Real*)c.st.pvy[h];
-    a.mvz = (Real*)c.st.pvz[h];
+    a.rec = (Real*)c.st.moved;
     a.dx = (Real*)c.st.px[o];
     a.dy = (Real*)c.st.py[o];
     a.dvx = (Real*)c.st.pvx[o];

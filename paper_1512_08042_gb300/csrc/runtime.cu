@@ -81,6 +81,7 @@ void layout(const hyb_params& p, const hyb_derived& d, hyb_layout& L) {
     L.ctrl = take(CTRL_WORDS * 4);
     L.counters = take(HYB_NCOUNTERS * 8);
     L.map_scratch = take(nc * sizeof(GradRec));
+    L.moved = take(cap * 8 * rb);
     L.total_bytes = off;
     L.capacity = d.capacity;
     L.ncells = d.ncells;
@@ -171,6 +172,7 @@ void resolve(Ctx& c) {
     s.ctrl = (uint32_t*)(a + L.ctrl);
     s.counters = (unsigned long long*)(a + L.counters);
     s.grad = (GradRec*)(a + L.map_scratch);
+    s.moved = a + L.moved;
 }
 
 hyb_status do_dsmc_step(Ctx& c) {

@@ -73,7 +73,8 @@ def test_layout_is_aligned_and_disjoint(lib):
         regions.append((L.count[h], 4 * d["ncells"]))
     for k, sz in (("tag", 4 * d["capacity"]), ("acc", 160 * d["ncells"]),
                   ("crmax", rb * d["ncells"]), ("rem", rb * d["ncells"]),
-                  ("nbar_sum", 4 * d["ncells"]), ("ctrl", 64), ("counters", 128)):
+                  ("nbar_sum", 4 * d["ncells"]), ("ctrl", 64), ("counters", 128),
+                  ("moved", 8 * rb * d["capacity"])):
         regions.append((getattr(L, k), sz))
     regions.sort()
     for (o1, s1), (o2, _) in zip(regions, regions[1:]):
