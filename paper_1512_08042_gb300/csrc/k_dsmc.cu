@@ -144,82 +144,165 @@ __device__ __forceinline__ void rec_load(const double* rec, int64_t i, double& x
 
 // ---------------------------------------------------------------------------------------
 // Move (kick, drift, walls, wrap) and binning into the other half.
+
+// Flight of a particle whose straight flight crosses a wall: it is re-emitted from the wall
+// (diffuse, isothermal), possibly more than once, for the rest of the step.
 template <typename Real>
-__global__ void __launch_bounds__(256) k_move(DsmcArgs<Real> a) {
+__device__ __forceinline__ void wall_flight(uint64_t seed, uint32_t c, uint32_t k, uint32_t s, Real H,
+                                            Real dt, Real& px, Real& py, Real& ux, Real& uy,
+                                            Real& uz, uint32_t& hits, uint32_t& caps) {
+    Real t = dt;
+    for (int b = 0;; ++b) {
+        const Real xn = px + ux * t;
+        const bool left = xn < (Real)0;
+        const bool right = xn > H;
+        if (!left && !right) {
+            px = xn;
+            py = py + uy * t;
+            break;
+        }
+        if (b == kMaxBounces) {
+            caps += 1;
+            px = left ? (Real)0 : H;
+            py = py + uy * t;
+            break;
+        }
+        hits += 1;
+        const Real th = left ? px / (-ux) : (H - px) / ux;
+        py = py + uy * th;
+        px = left ? (Real)0 : H;
+        t = t - th;
+        if (t < (Real)0) t = (Real)0;
+        reemit(seed, c, k, s, b, left ? (Real)1 : (Real)-1, ux, uy, uz);
+    }
+}
+
+// Periodic wrap of y and the cell key of a moved particle.
+template <typename Real>
+__device__ __forceinline__ uint32_t cell_key(const DsmcArgs<Real>& a, Real L, Real px, Real& py) {
+    if (py < (Real)0 || py >= L) {
+        py = py - L * floor(py / L);
+        if (py < (Real)0) py = py + L;
+        if (py >= L) py = py - L;
+    }
+    int ix = (int)floor(px), iy = (int)floor(py);
+    ix = ix < 0 ? 0 : (ix > a.ncx - 1 ? a.ncx - 1 : ix);
+    iy = iy < 0 ? 0 : (iy > a.ncy - 1 ? a.ncy - 1 : iy);
+    return (uint32_t)(iy * a.ncx + ix);
+}
+
+// Appends the active lanes' slots to the bins of their new cells: lanes bound for the same
+// cell share one atomic, and each gets arrival = base + rank among them.
+__device__ __forceinline__ uint32_t bin_arrival(uint32_t* __restrict__ count, uint32_t key, bool active,
+                                                unsigned lane) {
+    const unsigned m = __ballot_sync(kFull, active);
+    uint32_t arr = 0;
+    if (active) {
+        const unsigned peers = __match_any_sync(m, key);
+        const int leader = __ffs(peers) - 1;
+        uint32_t b0 = 0;
+        if ((int)lane == leader) b0 = atomicAdd(&count[key], (uint32_t)__popc(peers));
+        b0 = __shfl_sync(peers, b0, leader);
+        arr = b0 + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+    }
+    return arr;
+}
+
+// One warp per source cell; the first 64 particles of the cell are handled two per lane,
+// loads, flights and binning atomics of both in flight together.
+template <typename Real>
+__global__ void __launch_bounds__(256, 4) k_move(DsmcArgs<Real> a) {
     pdl_begin();
     const uint32_t s = a.ctrl[CTRL_STEP];
     if (blockIdx.x == 0 && threadIdx.x == 0) a.ctrl[CTRL_NTOT] = 0;  // the collide recounts
     const Real H = (Real)a.ncx, L = (Real)a.ncy;
     const Real g = (Real)a.g_step, dt = (Real)a.dt;
     const unsigned lane = lane_id();
-    const unsigned lt = (1u << lane) - 1u;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const uint32_t bin = (uint32_t)a.bin;
+    // the arrays do not overlap: loads of the next slots need not wait for earlier stores
+    const Real* __restrict__ sx = a.sx;
+    const Real* __restrict__ sy = a.sy;
+    const Real* __restrict__ svx = a.svx;
+    const Real* __restrict__ svy = a.svy;
+    const Real* __restrict__ svz = a.svz;
+    Real* __restrict__ rec = a.rec;
+    uint32_t* __restrict__ tag = a.tag;
+    uint32_t* __restrict__ cnt = a.count_d;
     uint32_t hits = 0, caps = 0, lost = 0;
     for (int c = gw; c < a.ncells; c += nw) {
         uint32_t n = a.count_s[c];
         if (n > bin) n = bin;
         const int64_t base = (int64_t)c * bin;
-        for (uint32_t k0 = 0; k0 < n; k0 += 32) {
-            const uint32_t k = k0 + lane;
-            const bool active = k < n;
-            uint32_t key = 0;
-            Real px = 0, py = 0, ux = 0, uy = 0, uz = 0;
-            if (active) {
-                const int64_t i = base + k;
-                px = a.sx[i];
-                py = a.sy[i];
-                ux = a.svx[i];
-                uy = a.svy[i] + g;
-                uz = a.svz[i];
-                Real t = dt;
-                for (int b = 0;; ++b) {
-                    const Real xn = px + ux * t;
-                    const bool left = xn < (Real)0;
-                    const bool right = xn > H;
-                    if (!left && !right) {
-                        px = xn;
-                        py = py + uy * t;
-                        break;
-                    }
-                    if (b == kMaxBounces) {
-                        caps += 1;
-                        px = left ? (Real)0 : H;
-                        py = py + uy * t;
-                        break;
-                    }
-                    hits += 1;
-                    const Real th = left ? px / (-ux) : (H - px) / ux;
-                    py = py + uy * th;
-                    px = left ? (Real)0 : H;
-                    t = t - th;
-                    if (t < (Real)0) t = (Real)0;
-                    reemit(a.seed, (uint32_t)c, k, s, b, left ? (Real)1 : (Real)-1, ux, uy, uz);
-                }
-                if (py < (Real)0 || py >= L) {
-                    py = py - L * floor(py / L);
-                    if (py < (Real)0) py = py + L;
-                    if (py >= L) py = py - L;
-                }
-                int ix = (int)floor(px), iy = (int)floor(py);
-                ix = ix < 0 ? 0 : (ix > a.ncx - 1 ? a.ncx - 1 : ix);
-                iy = iy < 0 ? 0 : (iy > a.ncy - 1 ? a.ncy - 1 : iy);
-                key = (uint32_t)(iy * a.ncx + ix);
+        for (uint32_t k0 = 0; k0 == 0 || k0 < n; k0 += 64) {
+            const uint32_t k1 = k0 + lane, k2 = k1 + 32;
+            const bool act1 = k1 < n, act2 = k2 < n;
+            Real p1[5] = {0, 0, 0, 0, 0}, p2[5] = {0, 0, 0, 0, 0};
+            // the loads need only the bin size, not the count, so they travel with it
+            const bool in1 = k1 < bin, in2 = k2 < bin;
+            if (in1) {
+                p1[0] = sx[base + k1];
+                p1[1] = sy[base + k1];
+                p1[2] = svx[base + k1];
+                p1[3] = svy[base + k1];
+                p1[4] = svz[base + k1];
             }
-            const unsigned m = __ballot_sync(kFull, active);
-            if (active) {
-                // lanes bound for the same cell share one atomic; arrival = base + rank
-                const unsigned peers = __match_any_sync(m, key);
-                const int leader = __ffs(peers) - 1;
-                uint32_t b0 = 0;
-                if ((int)lane == leader) b0 = atomicAdd(&a.count_d[key], (uint32_t)__popc(peers));
-                b0 = __shfl_sync(peers, b0, leader);
-                const uint32_t arr = b0 + (uint32_t)__popc(peers & lt);
-                const int64_t i = base + k;
-                rec_store(a.rec, i, px, py, ux, uy, uz);
-                if (arr < bin)
-                    a.tag[(int64_t)key * bin + arr] = (uint32_t)i;
+            if (in2) {
+                p2[0] = sx[base + k2];
+                p2[1] = sy[base + k2];
+                p2[2] = svx[base + k2];
+                p2[3] = svy[base + k2];
+                p2[4] = svz[base + k2];
+            }
+            // kick and straight flight; flights that cross a wall are redone below
+            p1[3] = p1[3] + g;
+            p2[3] = p2[3] + g;
+            const Real xn1 = p1[0] + p1[2] * dt, xn2 = p2[0] + p2[2] * dt;
+            const bool wall1 = act1 && !(xn1 >= (Real)0 && xn1 <= H);
+            const bool wall2 = act2 && !(xn2 >= (Real)0 && xn2 <= H);
+            if (!wall1) {
+                p1[0] = xn1;
+                p1[1] = p1[1] + p1[3] * dt;
+            }
+            if (!wall2) {
+                p2[0] = xn2;
+                p2[1] = p2[1] + p2[3] * dt;
+            }
+            if (__any_sync(kFull, wall1 || wall2)) {
+#pragma unroll 1
+                for (int h = 0; h < 2; ++h) {
+                    if (h == 0 ? wall1 : wall2) {
+                        Real q[5];
+#pragma unroll
+                        for (int i = 0; i < 5; ++i) q[i] = h == 0 ? p1[i] : p2[i];
+                        wall_flight(a.seed, (uint32_t)c, h == 0 ? k1 : k2, s, H, dt, q[0], q[1], q[2],
+                                    q[3], q[4], hits, caps);
+#pragma unroll
+                        for (int i = 0; i < 5; ++i) {
+                            if (h == 0)
+                                p1[i] = q[i];
+                            else
+                                p2[i] = q[i];
+                        }
+                    }
+                }
+            }
+            const uint32_t key1 = act1 ? cell_key(a, L, p1[0], p1[1]) : 0u;
+            const uint32_t key2 = act2 ? cell_key(a, L, p2[0], p2[1]) : 0u;
+            const uint32_t arr1 = bin_arrival(cnt, key1, act1, lane);
+            const uint32_t arr2 = bin_arrival(cnt, key2, act2, lane);
+            if (act1) {
+                rec_store(rec, base + k1, p1[0], p1[1], p1[2], p1[3], p1[4]);
+                if (arr1 < bin)
+                    tag[(int64_t)key1 * bin + arr1] = (uint32_t)(base + k1);
+                else
+                    lost += 1;
+            }
+            if (act2) {
+                rec_store(rec, base + k2, p2[0], p2[1], p2[2], p2[3], p2[4]);
+                if (arr2 < bin)
+                    tag[(int64_t)key2 * bin + arr2] = (uint32_t)(base + k2);
                 else
                     lost += 1;
             }
@@ -684,7 +767,8 @@ template <typename Real>
 cudaError_t step_impl(Ctx& c) {
     DsmcArgs<Real> a = make_args<Real>(c);
     prof_begin(c, K_MOVE);
-    cudaError_t e = launch_pdl(k_move<Real>, dim3(grid_for(c, c.d.ncells * 32, 256, 8)), dim3(256), 0,
+    // one source cell per warp (the hardware schedules the blocks as resources free up)
+    cudaError_t e = launch_pdl(k_move<Real>, dim3(grid_for(c, c.d.ncells * 32, 256, 64)), dim3(256), 0,
                                c.stream, a);
     if (e != cudaSuccess) return e;
     prof_end(c, K_MOVE);
