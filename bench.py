@@ -99,13 +99,15 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def traffic_record(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None if the
-    kernel source changed since the capture."""
+def traffic_record(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu summary, or None
+    if there is no capture of that workload or the kernel source changed since."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(p))[kernel]
     except Exception:
+        return None
+    if rec.get("workload") != workload:
         return None
     src = os.path.join(ROOT, "paper_1512_08042_gb300", "csrc", rec["source"])
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
@@ -320,7 +322,7 @@ def main():
                      "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak if achieved else None,
                      "algorithmic_bytes_per_launch": alg, "ms_per_launch": dom_ms,
-                     "traffic": traffic_record(dominant)},
+                     "traffic": traffic_record(dominant, args.workload)},
         "kernel_ms": kernel_ms,
         "clocks": summarize_clocks(clock_lines),
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,

@@ -631,14 +631,17 @@ __global__ void __launch_bounds__(kCollideWarps * 32, CollideCfg<Real>::MINB)
             a.dvy[base + k] = uy;
             a.dvz[base + k] = uz;
             if (do_sample) {
-                const Real xx = ux * ux, yy = uy * uy, zz = uz * uz;
-                const Real xy = ux * uy, xz = ux * uz, yz = uy * uz;
-                mo[0] += (Real)1;
+                // the sums are compared with a tolerance, so they use fused multiply-adds
+                // (this file is otherwise compiled without contraction); mo[0] is the count
+                const Real xx = ux * ux, yy = uy * uy, zz = uz * uz, xy = ux * uy;
                 mo[1] += ux; mo[2] += uy; mo[3] += uz;
-                mo[4] += xx; mo[5] += xy; mo[6] += xz; mo[7] += yy; mo[8] += yz; mo[9] += zz;
-                mo[10] += xx * ux; mo[11] += xx * uy; mo[12] += xx * uz; mo[13] += yy * ux;
-                mo[14] += xy * uz; mo[15] += zz * ux; mo[16] += yy * uy; mo[17] += yy * uz;
-                mo[18] += zz * uy; mo[19] += zz * uz;
+                mo[4] += xx; mo[5] = fma(ux, uy, mo[5]); mo[6] = fma(ux, uz, mo[6]);
+                mo[7] += yy; mo[8] = fma(uy, uz, mo[8]); mo[9] += zz;
+                mo[10] = fma(xx, ux, mo[10]); mo[11] = fma(xx, uy, mo[11]);
+                mo[12] = fma(xx, uz, mo[12]); mo[13] = fma(yy, ux, mo[13]);
+                mo[14] = fma(xy, uz, mo[14]); mo[15] = fma(zz, ux, mo[15]);
+                mo[16] = fma(yy, uy, mo[16]); mo[17] = fma(yy, uz, mo[17]);
+                mo[18] = fma(zz, uy, mo[18]); mo[19] = fma(zz, uz, mo[19]);
             }
         }
         if (do_sample) {
@@ -657,6 +660,7 @@ __global__ void __launch_bounds__(kCollideWarps * 32, CollideCfg<Real>::MINB)
                     t[q] = keep + __shfl_xor_sync(kFull, send, o);
                 }
             }
+            if (gl == 0) t[0] = (Real)n;  // the particle count, moment 0
             if (has_r) {
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
