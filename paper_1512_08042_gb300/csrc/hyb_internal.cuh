@@ -174,6 +174,32 @@ __device__ __forceinline__ uint32_t uindex(uint32_t r, uint32_t n) {
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
+// Kernel arguments of one context, or of a batch of independent contexts (replicas). The
+// units of a launch (cells, blocks of cells, nodes or list entries) are numbered across the
+// replicas: unit u belongs to replica r with pre[r] <= u < pre[r + 1] and is unit u - pre[r]
+// of that replica. Kernels are instantiated for both cases; a single context takes its
+// arguments from the launch parameters and pays nothing for the batch form.
+template <class Args>
+struct Launch {
+    Args one;             // the context's arguments (single form)
+    const Args* tab;      // per-replica arguments in device memory (batch form)
+    const int64_t* pre;   // nrep + 1 prefix sums of the units per replica (batch form)
+    int32_t nrep;
+    int64_t total;        // units of the launch
+};
+
+__device__ __forceinline__ int replica_of(const int64_t* pre, int nrep, int64_t u) {
+    int lo = 0, hi = nrep;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pre[mid] <= u)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
 // Programmatic dependent launch (sm_90 and later). The kernels of a step are launched with
 // launch_pdl: each one first lets the next kernel of the stream be scheduled
 // (launch_dependents), then waits until the previous kernel has completed and its writes are

@@ -208,18 +208,14 @@ __device__ __forceinline__ uint32_t bin_arrival(uint32_t* __restrict__ count, ui
     return arr;
 }
 
-// One warp per source cell; the first 64 particles of the cell are handled two per lane,
-// loads, flights and binning atomics of both in flight together.
+// One source cell, by one warp; the first 64 particles of the cell are handled two per
+// lane, loads, flights and binning atomics of both in flight together.
 template <typename Real>
-__global__ void __launch_bounds__(256, 4) k_move(DsmcArgs<Real> a) {
-    pdl_begin();
+__device__ __forceinline__ void move_cell(const DsmcArgs<Real>& a, int c, unsigned lane) {
     const uint32_t s = a.ctrl[CTRL_STEP];
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.ctrl[CTRL_NTOT] = 0;  // the collide recounts
+    if (c == 0 && lane == 0) a.ctrl[CTRL_NTOT] = 0;  // the collide recounts
     const Real H = (Real)a.ncx, L = (Real)a.ncy;
     const Real g = (Real)a.g_step, dt = (Real)a.dt;
-    const unsigned lane = lane_id();
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
     const uint32_t bin = (uint32_t)a.bin;
     // the arrays do not overlap: loads of the next slots need not wait for earlier stores
     const Real* __restrict__ sx = a.sx;
@@ -231,7 +227,7 @@ __global__ void __launch_bounds__(256, 4) k_move(DsmcArgs<Real> a) {
     uint32_t* __restrict__ tag = a.tag;
     uint32_t* __restrict__ cnt = a.count_d;
     uint32_t hits = 0, caps = 0, lost = 0;
-    for (int c = gw; c < a.ncells; c += nw) {
+    {
         uint32_t n = a.count_s[c];
         if (n > bin) n = bin;
         const int64_t base = (int64_t)c * bin;
@@ -308,16 +304,35 @@ __global__ void __launch_bounds__(256, 4) k_move(DsmcArgs<Real> a) {
             }
         }
     }
-    hits = __reduce_add_sync(kFull, hits);
-    caps = __reduce_add_sync(kFull, caps);
-    lost = __reduce_add_sync(kFull, lost);
-    if (lane == 0) {
-        if (hits) atomicAdd(&a.counters[HYB_C_WALL_HITS], (unsigned long long)hits);
-        if (caps) {
-            atomicAdd(&a.counters[HYB_C_BOUNCE_CAP], (unsigned long long)caps);
-            atomicOr(&a.ctrl[CTRL_STATUS], HYB_ST_BOUNCE_CAP);
+    if (__any_sync(kFull, (hits | caps | lost) != 0u)) {  // cells at a wall, or overflow
+        hits = __reduce_add_sync(kFull, hits);
+        caps = __reduce_add_sync(kFull, caps);
+        lost = __reduce_add_sync(kFull, lost);
+        if (lane == 0) {
+            if (hits) atomicAdd(&a.counters[HYB_C_WALL_HITS], (unsigned long long)hits);
+            if (caps) {
+                atomicAdd(&a.counters[HYB_C_BOUNCE_CAP], (unsigned long long)caps);
+                atomicOr(&a.ctrl[CTRL_STATUS], HYB_ST_BOUNCE_CAP);
+            }
+            if (lost) atomicOr(&a.ctrl[CTRL_STATUS], HYB_ST_CAPACITY);
         }
-        if (lost) atomicOr(&a.ctrl[CTRL_STATUS], HYB_ST_CAPACITY);
+    }
+}
+
+// One warp per source cell (the cells of all replicas in the batch form).
+template <typename Real, bool BATCH>
+__global__ void __launch_bounds__(256, 4) k_move(Launch<DsmcArgs<Real>> L) {
+    pdl_begin();
+    const unsigned lane = lane_id();
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = gw; u < L.total; u += nw) {
+        if constexpr (BATCH) {
+            const int r = replica_of(L.pre, L.nrep, u);
+            move_cell(L.tab[r], (int)(u - L.pre[r]), lane);
+        } else {
+            move_cell(L.one, (int)u, lane);
+        }
     }
 }
 
@@ -395,10 +410,10 @@ __device__ __forceinline__ void gather_slots(const Real* __restrict__ rec, Real*
     }
 }
 
+// The block of 32 consecutive cells `blk` (of nblk) of one context.
 template <typename Real>
-__global__ void __launch_bounds__(kCollideWarps * 32, CollideCfg<Real>::MINB)
-    k_collide(DsmcArgs<Real> a, uint32_t pool) {
-    pdl_begin();
+__device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t pool, int blk,
+                                              int nblk) {
     constexpr int G = kGroup;
     constexpr int CPW = 32 / G;           // cells per warp in phases A and C
     constexpr int WARPS = kCollideWarps;
@@ -433,7 +448,7 @@ __global__ void __launch_bounds__(kCollideWarps * 32, CollideCfg<Real>::MINB)
     unsigned long long ncand_tot = 0, ncoll_tot = 0;
     uint32_t flags = 0, nlive = 0;
 
-    const int c = blockIdx.x * NC + gi;
+    const int c = blk * NC + gi;
     const bool has = c < a.ncells;
     const int64_t base = (int64_t)c * bin;
     // the cell's loads are issued together: count, the first SMALL tag slots, the leader's
@@ -564,7 +579,7 @@ __global__ void __launch_bounds__(kCollideWarps * 32, CollideCfg<Real>::MINB)
                 const int g = t / KC, kk = t % KC;
                 const uint32_t k = k0 + (uint32_t)kk;
                 if (k < s_nsel[g]) {
-                    const uint32_t cg = (uint32_t)(blockIdx.x * NC + g);
+                    const uint32_t cg = (uint32_t)(blk * NC + g);
                     const uint32_t ng = s_n[g];
                     const uint4 r = draw(a.seed, cg, s, TAG_NTC_PAIR, k, 0);
                     const uint32_t ci = uindex(r.x, ng);
@@ -617,7 +632,7 @@ __global__ void __launch_bounds__(kCollideWarps * 32, CollideCfg<Real>::MINB)
             __syncthreads();
         }
         if (w == 0) {
-            const int cl = blockIdx.x * NC + (int)lane;
+            const int cl = blk * NC + (int)lane;
             if (cl < a.ncells && (fits || (int)lane == round)) a.crmax[cl] = cm;
             ncoll_tot += ncoll;
         }
@@ -700,12 +715,24 @@ __global__ void __launch_bounds__(kCollideWarps * 32, CollideCfg<Real>::MINB)
         // read the step by now)
         __threadfence();
         const unsigned ticket = atomicAdd(&a.ctrl[CTRL_TICKET], 1u);
-        if (ticket == gridDim.x - 1) {
+        if (ticket == nblk - 1) {
             __threadfence();
             if (do_sample) a.ctrl[CTRL_NSAMPLES] += 1;
             a.ctrl[CTRL_STEP] = s + 1;
             a.ctrl[CTRL_TICKET] = 0;
         }
+    }
+}
+
+template <typename Real, bool BATCH>
+__global__ void __launch_bounds__(kCollideWarps * 32, CollideCfg<Real>::MINB)
+    k_collide(Launch<DsmcArgs<Real>> L, uint32_t pool) {
+    pdl_begin();
+    if constexpr (BATCH) {
+        const int r = replica_of(L.pre, L.nrep, (int64_t)blockIdx.x);
+        collide_block(L.tab[r], pool, (int)(blockIdx.x - L.pre[r]), (int)(L.pre[r + 1] - L.pre[r]));
+    } else {
+        collide_block(L.one, pool, (int)blockIdx.x, (int)gridDim.x);
     }
 }
 
@@ -772,8 +799,11 @@ cudaError_t step_impl(Ctx& c) {
     DsmcArgs<Real> a = make_args<Real>(c);
     prof_begin(c, K_MOVE);
     // one source cell per warp (the hardware schedules the blocks as resources free up)
-    cudaError_t e = launch_pdl(k_move<Real>, dim3(grid_for(c, c.d.ncells * 32, 256, 64)), dim3(256), 0,
-                               c.stream, a);
+    Launch<DsmcArgs<Real>> L{};
+    L.one = a;
+    L.total = c.d.ncells;
+    cudaError_t e = launch_pdl(k_move<Real, false>, dim3(grid_for(c, c.d.ncells * 32, 256, 64)), dim3(256),
+                               0, c.stream, L);
     if (e != cudaSuccess) return e;
     prof_end(c, K_MOVE);
     // shared memory: a pool of slots for the block's cells (3 Real + 1 u32 each), room for
@@ -784,11 +814,12 @@ cudaError_t step_impl(Ctx& c) {
     const size_t smem = (size_t)pool * (3 * sizeof(Real) + 4) +
                         (size_t)NC * kChainSteps * (4 + 4 * sizeof(Real));
     // (dynamic and static shared memory together may exceed the default 48 KB)
-    e = cudaFuncSetAttribute(k_collide<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_collide<Real, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)((c.d.ncells + NC - 1) / NC);
     prof_begin(c, K_COLLIDE);
-    e = launch_pdl(k_collide<Real>, dim3(grid), dim3(kCollideWarps * 32), smem, c.stream, a, pool);
+    L.total = grid;
+    e = launch_pdl(k_collide<Real, false>, dim3(grid), dim3(kCollideWarps * 32), smem, c.stream, L, pool);
     if (e != cudaSuccess) return e;
     prof_end(c, K_COLLIDE);
     return cudaGetLastError();

@@ -62,13 +62,11 @@ __device__ __forceinline__ int wrap_y(int v, int ny) {
     return v;
 }
 
+// One node of one context.
 template <typename Real, class LAT>
-__global__ void __launch_bounds__(128) k_lbm(LbmArgs<Real> a) {
-    pdl_begin();
+__device__ __forceinline__ void lbm_node(const LbmArgs<Real>& a, const int64_t node) {
     constexpr int Q = LAT::Q;
     constexpr double R = lat_r<LAT>();
-    const int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (node >= a.nnodes) return;
     const int nx = a.nx, ny = a.ny;
     const int x = (int)(node % nx), y = (int)(node / nx);
     const int64_t nn = a.nnodes;
@@ -246,6 +244,20 @@ __global__ void __launch_bounds__(128) k_lbm(LbmArgs<Real> a) {
     });
 }
 
+// One thread per node (the nodes of all replicas in the batch form).
+template <typename Real, class LAT, bool BATCH>
+__global__ void __launch_bounds__(128) k_lbm(Launch<LbmArgs<Real>> L) {
+    pdl_begin();
+    const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (u >= L.total) return;
+    if constexpr (BATCH) {
+        const int r = replica_of(L.pre, L.nrep, u);
+        lbm_node<Real, LAT>(L.tab[r], u - L.pre[r]);
+    } else {
+        lbm_node<Real, LAT>(L.one, u);
+    }
+}
+
 template <typename Real, class LAT>
 __global__ void k_lbm_init(Real* f0, Real* f1, int64_t nnodes) {
     for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < nnodes;
@@ -271,7 +283,10 @@ cudaError_t lbm_impl(Ctx& c) {
     a.g_step = (Real)c.d.g_step;
     const int64_t blocks = (c.d.nnodes + 127) / 128;
     prof_begin(c, K_LBM);
-    const cudaError_t e = launch_pdl(k_lbm<Real, LAT>, dim3((unsigned)blocks), dim3(128), 0, c.stream, a);
+    Launch<LbmArgs<Real>> L{};
+    L.one = a;
+    L.total = c.d.nnodes;
+    const cudaError_t e = launch_pdl(k_lbm<Real, LAT, false>, dim3((unsigned)blocks), dim3(128), 0, c.stream, L);
     prof_end(c, K_LBM);
     return e;
 }

@@ -74,16 +74,13 @@ __device__ __forceinline__ const LatXi<LAT, Real>& lat_xi() {
 // by one FP64 reciprocal of the particle count; the coefficients (one per lane, state
 // precision) are broadcast and each lane evaluates one or two populations.
 template <typename Real, class LAT>
-__global__ void __launch_bounds__(128) k_d2l(MapArgs<Real> a) {
-    pdl_begin();
+__device__ __forceinline__ void d2l_entries(const MapArgs<Real>& a, int first, int stride) {
     const LatXi<LAT, Real>& lt = lat_xi<LAT, Real>();
     const Real* sx = lt.x;
     const Real* sw = lt.w;
     const unsigned lane = lane_id();
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
     const uint32_t S = a.ctrl[CTRL_NSAMPLES];
-    for (int t = gw; t < a.n; t += nw) {
+    for (int t = first; t < a.n; t += stride) {
         const int32_t node = a.list[t];
         if (node < 0 || (int64_t)node >= a.nnodes) {
             if (lane == 0) atomicOr(&a.ctrl[CTRL_STATUS], HYB_ST_BAD_INPUT);
@@ -145,6 +142,21 @@ __global__ void __launch_bounds__(128) k_d2l(MapArgs<Real> a) {
                 a.f[(int64_t)q * a.nnodes + node] = sw[q] * sum;
             }
         }
+    }
+}
+
+// DSMC2LB: one warp per listed node (the listed nodes of all replicas in the batch form).
+template <typename Real, class LAT, bool BATCH>
+__global__ void __launch_bounds__(128) k_d2l(Launch<MapArgs<Real>> L) {
+    pdl_begin();
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if constexpr (BATCH) {
+        if (gw >= L.total) return;
+        const int r = replica_of(L.pre, L.nrep, gw);
+        const MapArgs<Real>& a = L.tab[r];
+        d2l_entries<Real, LAT>(a, (int)(gw - L.pre[r]), a.n);
+    } else {
+        d2l_entries<Real, LAT>(L.one, (int)gw, (int)(((int64_t)gridDim.x * blockDim.x) >> 5));
     }
 }
 
@@ -326,8 +338,7 @@ __device__ __forceinline__ void grad_coefficients(const MapArgs<Real>& a, int ce
 // particles and raises the capacity status. The Grad record of each listed cell is written
 // to a.grad.
 template <typename Real, class LAT>
-__global__ void __launch_bounds__(kL2DWarps * 32) k_l2d(MapArgs<Real> a) {
-    pdl_begin();
+__device__ __forceinline__ void l2d_cells(const MapArgs<Real>& a, int first, int stride) {
     __shared__ unsigned s_am[kL2DWarps], s_em[kL2DWarps], s_vm[kL2DWarps];
     __shared__ Real s_c[20];
     __shared__ uint32_t s_nnew;
@@ -339,7 +350,7 @@ __global__ void __launch_bounds__(kL2DWarps * 32) k_l2d(MapArgs<Real> a) {
     unsigned long long deleted = 0, created = 0, attempts = 0, envelope = 0;
     uint32_t flags = 0;
     int32_t dlive = 0;
-    for (int ci = blockIdx.x; ci < a.n; ci += gridDim.x) {
+    for (int ci = first; ci < a.n; ci += stride) {
         const int32_t icell = a.list[ci];
         if (icell < 0 || icell >= a.ncx * a.ncy) {
             flags |= HYB_ST_BAD_INPUT;
@@ -498,6 +509,19 @@ __global__ void __launch_bounds__(kL2DWarps * 32) k_l2d(MapArgs<Real> a) {
     if (lane == 0 && flags) atomicOr(&a.ctrl[CTRL_STATUS], flags);
 }
 
+// LB2DSMC: one block per listed cell (the listed cells of all replicas in the batch form).
+template <typename Real, class LAT, bool BATCH>
+__global__ void __launch_bounds__(kL2DWarps * 32) k_l2d(Launch<MapArgs<Real>> L) {
+    pdl_begin();
+    if constexpr (BATCH) {
+        const int r = replica_of(L.pre, L.nrep, (int64_t)blockIdx.x);
+        const MapArgs<Real>& a = L.tab[r];
+        l2d_cells<Real, LAT>(a, (int)(blockIdx.x - L.pre[r]), a.n);
+    } else {
+        l2d_cells<Real, LAT>(L.one, (int)blockIdx.x, (int)gridDim.x);
+    }
+}
+
 template <typename Real>
 MapArgs<Real> map_args(Ctx& c, const int32_t* list, int32_t n) {
     MapArgs<Real> a{};
@@ -537,8 +561,11 @@ template <typename Real, class LAT>
 cudaError_t d2l_impl(Ctx& c, const int32_t* nodes, int32_t n) {
     MapArgs<Real> a = map_args<Real>(c, nodes, n);
     prof_begin(c, K_D2L);
-    const cudaError_t e = launch_pdl(k_d2l<Real, LAT>, dim3(blocks_for(c, (int64_t)n * 32, 128, 16)),
-                                     dim3(128), 0, c.stream, a);
+    Launch<MapArgs<Real>> L{};
+    L.one = a;
+    L.total = n;
+    const cudaError_t e = launch_pdl(k_d2l<Real, LAT, false>, dim3(blocks_for(c, (int64_t)n * 32, 128, 16)),
+                                     dim3(128), 0, c.stream, L);
     prof_end(c, K_D2L);
     return e;
 }
@@ -546,9 +573,12 @@ cudaError_t d2l_impl(Ctx& c, const int32_t* nodes, int32_t n) {
 template <typename Real, class LAT>
 cudaError_t l2d_launch(Ctx& c, const MapArgs<Real>& a, int32_t n) {
     prof_begin(c, K_L2D);
-    const cudaError_t e = launch_pdl(k_l2d<Real, LAT>,
+    Launch<MapArgs<Real>> L{};
+    L.one = a;
+    L.total = n;
+    const cudaError_t e = launch_pdl(k_l2d<Real, LAT, false>,
                                      dim3(blocks_for(c, (int64_t)n * 32 * kL2DWarps, 32 * kL2DWarps, 8)),
-                                     dim3(32 * kL2DWarps), 0, c.stream, a);
+                                     dim3(32 * kL2DWarps), 0, c.stream, L);
     prof_end(c, K_L2D);
     return e;
 }
