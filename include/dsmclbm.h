@@ -247,6 +247,54 @@ const char* hyb_last_error(const hyb_ctx* ctx);
 /* Synchronises the stream, releases graphs and events; does not touch the arena. */
 void hyb_destroy(hyb_ctx* ctx);
 
+/* ---- Batched ensemble of independent channels ----------------------------------------
+ * Beyond the paper's single channel (it names time or ensemble averaging as the remedy for
+ * DSMC noise, Sec. 5): a batch advances n independent replicas, each with its own
+ * hyb_params (sizes, ppc, Kn, seed...), with one launch per kernel for all of them per hybrid
+ * step, replayed from a CUDA graph. The replicas share real_bytes and lattice. Replica r's
+ * arena is the part of the caller-owned batch arena at offsets[r], with the layout of
+ * hyb_layout_compute(&p[r]); a table region at offsets[n] holds the per-replica kernel
+ * arguments and unit prefix sums, written by the library. A replica advanced in the batch
+ * gives the same results as the same channel advanced alone. */
+typedef struct hyb_batch hyb_batch;
+
+/* offsets[0..n-1]: the replicas' arenas; offsets[n]: the table region; offsets[n+1]: the
+ * total size. offsets has n + 2 entries. HYB_EINVAL for invalid parameters or replicas that
+ * differ in real_bytes or lattice. */
+hyb_status hyb_batch_layout(const hyb_params* p, int32_t n, uint64_t* offsets);
+
+/* Initialises every replica (as dsmc_init) in the batch arena (256-byte aligned, at least
+ * offsets[n+1] bytes) on `stream`. On success *out owns the batch. */
+hyb_status hyb_batch_init(const hyb_params* p, int32_t n, void* arena, uint64_t arena_bytes,
+                          void* stream, hyb_batch** out);
+
+/* The context of replica r, owned by the batch (do not destroy it). Its views, counters and
+ * status are those of the replica. A replica stepped on its own falls out of lockstep, and
+ * the next batch step returns HYB_ESTATE. */
+hyb_status hyb_batch_replica(hyb_batch* b, int32_t r, hyb_ctx** out);
+
+/* nsteps hybrid steps of every replica (the order of hyb_hybrid_step). dev_nodes and
+ * dev_cells are the replicas' coupling lists (device int32, each replica's own node and cell
+ * indices) one after another; node_pre and cell_pre (host int64, n + 1 entries, starting at
+ * 0) are their offsets. Empty lists skip a mapping for a replica. */
+hyb_status hyb_batch_hybrid_step(hyb_batch* b, const int32_t* dev_nodes, const int64_t* node_pre,
+                                 const int32_t* dev_cells, const int64_t* cell_pre,
+                                 int32_t nsteps, int32_t use_graph);
+
+/* Thread-block sizes of the batched move (64, 128 or 256 threads) and LB step (32, 64 or
+ * 128); HYB_EINVAL for others. */
+hyb_status hyb_batch_set_blocks(hyb_batch* b, int32_t move_block, int32_t lbm_block);
+
+/* Autotuner: times replayed hybrid steps of the batch for each move block size, then for each
+ * LB block size, keeps the fastest of each and returns them. The steps it times advance the
+ * batch (42 hybrid steps). */
+hyb_status hyb_batch_tune(hyb_batch* b, const int32_t* dev_nodes, const int64_t* node_pre,
+                          const int32_t* dev_cells, const int64_t* cell_pre, int32_t* move_block,
+                          int32_t* lbm_block);
+
+const char* hyb_batch_last_error(const hyb_batch* b);
+void hyb_batch_destroy(hyb_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

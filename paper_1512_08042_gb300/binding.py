@@ -52,7 +52,9 @@ class HybLayout(ctypes.Structure):
 EXPORTS = ["hyb_derive", "hyb_layout_compute", "hyb_lattice", "hyb_status_string", "dsmc_init",
            "dsmc_step", "lbm_step", "sample_moments", "map_dsmc_to_lbm", "map_lbm_to_dsmc",
            "map_lbm_to_dsmc_noalloc",
-           "hyb_hybrid_step", "hyb_current", "hyb_sync_status", "hyb_read_counters",
+           "hyb_hybrid_step", "hyb_batch_layout", "hyb_batch_init", "hyb_batch_replica",
+           "hyb_batch_hybrid_step", "hyb_batch_set_blocks", "hyb_batch_tune",
+           "hyb_batch_last_error", "hyb_batch_destroy", "hyb_current", "hyb_sync_status", "hyb_read_counters",
            "hyb_profile", "hyb_profile_harvest", "hyb_profile_read", "hyb_debug_philox",
            "hyb_last_error", "hyb_destroy"]
 
@@ -95,6 +97,15 @@ def lib():
     L.map_lbm_to_dsmc.argtypes = [_vp, _vp, _i32]
     L.map_lbm_to_dsmc_noalloc.argtypes = [_vp, _vp, _i32]
     L.hyb_hybrid_step.argtypes = [_vp, _vp, _i32, _vp, _i32, _i32, _i32]
+    L.hyb_batch_layout.argtypes = [_vp, _i32, _vp]
+    L.hyb_batch_init.argtypes = [_vp, _i32, _vp, _u64, _vp, P(_vp)]
+    L.hyb_batch_replica.argtypes = [_vp, _i32, P(_vp)]
+    L.hyb_batch_hybrid_step.argtypes = [_vp, _vp, _vp, _vp, _vp, _i32, _i32]
+    L.hyb_batch_set_blocks.argtypes = [_vp, _i32, _i32]
+    L.hyb_batch_tune.argtypes = [_vp, _vp, _vp, _vp, _vp, P(_i32), P(_i32)]
+    L.hyb_batch_last_error.argtypes = [_vp]
+    L.hyb_batch_last_error.restype = ctypes.c_char_p
+    L.hyb_batch_destroy.argtypes = [_vp]
     L.hyb_current.argtypes = [_vp, P(_i32), P(_i32)]
     L.hyb_sync_status.argtypes = [_vp, P(_u32)]
     L.hyb_read_counters.argtypes = [_vp, _vp]
@@ -179,9 +190,29 @@ class Hybrid:
         _check(rc)
         self.ctx = ctx
 
+    @classmethod
+    def _attach(cls, cfg, device, stream, ctx, arena):
+        """A view of a context owned elsewhere (a replica of a Batch): no allocation, and
+        close() leaves the context to its owner."""
+        import torch
+        self = cls.__new__(cls)
+        self.torch = torch
+        self.cfg = dict(cfg)
+        self.device = torch.device(device)
+        self.params = make_params(cfg)
+        self.d = derive(cfg)
+        self.L = layout(cfg)
+        self.real = torch.float32 if cfg["real_bytes"] == 4 else torch.float64
+        self.stream = stream
+        self.arena = arena
+        self.ctx = ctx
+        self._owned = False
+        return self
+
     def close(self):
         if getattr(self, "ctx", None):
-            lib().hyb_destroy(self.ctx)
+            if getattr(self, "_owned", True):
+                lib().hyb_destroy(self.ctx)
             self.ctx = None
 
     def __del__(self):
@@ -368,3 +399,93 @@ class Hybrid:
         self.sync()
         self.arena.copy_(state["arena"].to(self.device))
         self.torch.cuda.synchronize(self.device)
+
+
+class Batch:
+    """Independent channels (replicas) advanced together: one launch per kernel for all of
+    them per hybrid step. `replicas[r]` is a Hybrid view of replica r (state, counters)."""
+
+    def __init__(self, cfgs, device="cuda:0", stream=None):
+        import torch
+        self.torch = torch
+        self.cfgs = [dict(c) for c in cfgs]
+        n = len(self.cfgs)
+        self.device = torch.device(device)
+        params = (HybParams * n)(*[make_params(c) for c in self.cfgs])
+        offsets = (ctypes.c_uint64 * (n + 2))()
+        _check(lib().hyb_batch_layout(params, n, offsets))
+        self.offsets = [int(o) for o in offsets]
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+            self.arena = torch.zeros(self.offsets[n + 1], dtype=torch.uint8, device=self.device)
+        torch.cuda.synchronize(self.device)
+        b = _vp()
+        with torch.cuda.device(self.device):
+            rc = lib().hyb_batch_init(params, n, self.arena.data_ptr(), self.offsets[n + 1],
+                                      self.stream.cuda_stream, ctypes.byref(b))
+        _check(rc)
+        self.b = b
+        self.replicas = []
+        for r in range(n):
+            ctx = _vp()
+            _check(lib().hyb_batch_replica(self.b, r, ctypes.byref(ctx)))
+            size = int(layout(self.cfgs[r]).total_bytes)
+            view = self.arena[self.offsets[r]:self.offsets[r] + size]
+            self.replicas.append(Hybrid._attach(self.cfgs[r], self.device, self.stream, ctx, view))
+        self._lists = None
+
+    def _prepare(self, nodes, cells):
+        """Concatenated device lists and host offsets, kept alive while the batch uses them."""
+        torch = self.torch
+        key = (tuple(id(x) for x in nodes), tuple(id(x) for x in cells))
+        if self._lists is not None and self._lists[0] == key:
+            return self._lists[1]
+        def cat(lists):
+            pre = np.zeros(len(lists) + 1, np.int64)
+            pre[1:] = np.cumsum([len(x) for x in lists])
+            flat = np.concatenate([np.asarray(x, np.int32) for x in lists]) if pre[-1] else np.zeros(1, np.int32)
+            dev = torch.from_numpy(flat).to(self.device)
+            return dev, pre
+        dn, pn = cat(nodes)
+        dc, pc = cat(cells)
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        prepared = (dn, pn, dc, pc)
+        self._lists = (key, prepared)
+        return prepared
+
+    def hybrid_step(self, nodes, cells, nsteps=1, use_graph=True):
+        """`nodes[r]`, `cells[r]`: replica r's coupling nodes and cells (host int arrays)."""
+        dn, pn, dc, pc = self._prepare(nodes, cells)
+        rc = lib().hyb_batch_hybrid_step(self.b, dn.data_ptr(), pn.ctypes.data_as(_vp), dc.data_ptr(),
+                                         pc.ctypes.data_as(_vp), int(nsteps), 1 if use_graph else 0)
+        if rc != HYB_OK:
+            raise HybError(rc, lib().hyb_batch_last_error(self.b).decode())
+
+    def set_blocks(self, move_block, lbm_block):
+        _check(lib().hyb_batch_set_blocks(self.b, int(move_block), int(lbm_block)))
+
+    def tune(self, nodes, cells):
+        """Picks the block shapes by timing hybrid steps (advances the batch); returns them."""
+        dn, pn, dc, pc = self._prepare(nodes, cells)
+        mb, lb = _i32(), _i32()
+        rc = lib().hyb_batch_tune(self.b, dn.data_ptr(), pn.ctypes.data_as(_vp), dc.data_ptr(),
+                                  pc.ctypes.data_as(_vp), ctypes.byref(mb), ctypes.byref(lb))
+        if rc != HYB_OK:
+            raise HybError(rc, lib().hyb_batch_last_error(self.b).decode())
+        return mb.value, lb.value
+
+    def sync(self):
+        self.stream.synchronize()
+
+    def close(self):
+        if getattr(self, "b", None):
+            for h in self.replicas:
+                h.ctx = None
+            lib().hyb_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -24,6 +24,7 @@ UNITS = {
     "k_dsmc.cu": ["-fmad=false"],
     "k_map.cu": ["-fmad=false"],
     "k_lbm.cu": ["-fmad=true"],
+    "batch.cu": ["-fmad=false"],
 }
 HEADERS = [os.path.join(CSRC, "hyb_internal.cuh"), os.path.join(INCLUDE, "dsmclbm.h")]
 

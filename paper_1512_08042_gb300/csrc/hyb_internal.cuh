@@ -431,6 +431,40 @@ cudaError_t launch_map_l2d_noalloc(Ctx& c, const int32_t* cells, int32_t n);
 cudaError_t launch_debug_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out, int64_t n,
                                 cudaStream_t s);
 
+// A batch of independent replicas (hyb_batch in runtime.cu): the per-replica kernel
+// arguments of each ping-pong parity and the unit prefix sums, in a table region of the
+// batch arena, and the block shapes picked by the tuner.
+struct BatchDev {
+    int32_t nrep = 0;
+    int32_t real_bytes = 4, lattice = 39;
+    int num_sms = 152;
+    cudaStream_t stream = nullptr;
+    const void* dsmc[2] = {nullptr, nullptr};               // DsmcArgs<Real>[nrep], by particle half
+    const void* lbm[2] = {nullptr, nullptr};                // LbmArgs<Real>[nrep], by population half
+    const void* d2l[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // MapArgs, [particle][population]
+    const void* l2d[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    const int64_t* pre_cells = nullptr;
+    const int64_t* pre_blocks = nullptr;
+    const int64_t* pre_nodes = nullptr;
+    const int64_t* pre_d2l = nullptr;
+    const int64_t* pre_l2d = nullptr;
+    int64_t tot_cells = 0, tot_blocks = 0, tot_nodes = 0, tot_d2l = 0, tot_l2d = 0;
+    uint32_t pool = 0;  // collide shared-memory pool: the largest over the replicas
+    int move_block = 256, lbm_block = 128;
+};
+size_t dsmc_args_bytes(int real_bytes);
+void dsmc_args_fill(Ctx& c, int cur_p, void* out);
+size_t lbm_args_bytes(int real_bytes);
+void lbm_args_fill(Ctx& c, int cur_f, void* out);
+size_t map_args_bytes(int real_bytes);
+void map_args_fill(Ctx& c, int cur_p, int cur_f, const int32_t* list, int32_t n, void* out);
+uint32_t collide_pool(const Ctx& c);
+cudaError_t launch_batch_move(BatchDev& b, int cur_p);
+cudaError_t launch_batch_collide(BatchDev& b, int cur_p);
+cudaError_t launch_batch_lbm(BatchDev& b, int cur_f);
+cudaError_t launch_batch_d2l(BatchDev& b, int cur_p, int cur_f);
+cudaError_t launch_batch_l2d(BatchDev& b, int cur_p, int cur_f);
+
 // Kernel timing: a pool of event pairs for direct launches, and one fixed pair per graph
 // variant (a graph replay records into the pair captured in it).
 struct ProfPool {

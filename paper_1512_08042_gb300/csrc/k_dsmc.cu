@@ -22,6 +22,8 @@
 // This file is compiled without FMA contraction so that positions, cell keys, pair choices
 // and post-collision velocities are the IEEE float (or double) results of the written
 // expressions.
+#include <cstring>
+
 #include "hyb_internal.cuh"
 
 namespace hyb {
@@ -849,6 +851,69 @@ cudaError_t launch_init(Ctx& c) {
 
 cudaError_t launch_dsmc_step(Ctx& c) {
     return (c.p.real_bytes == 4) ? step_impl<float>(c) : step_impl<double>(c);
+}
+
+size_t dsmc_args_bytes(int real_bytes) {
+    return real_bytes == 4 ? sizeof(DsmcArgs<float>) : sizeof(DsmcArgs<double>);
+}
+
+void dsmc_args_fill(Ctx& c, int cur_p, void* out) {
+    const int save = c.cur_p;
+    c.cur_p = cur_p;
+    if (c.p.real_bytes == 4) {
+        const DsmcArgs<float> a = make_args<float>(c);
+        std::memcpy(out, &a, sizeof(a));
+    } else {
+        const DsmcArgs<double> a = make_args<double>(c);
+        std::memcpy(out, &a, sizeof(a));
+    }
+    c.cur_p = save;
+}
+
+uint32_t collide_pool(const Ctx& c) {
+    constexpr int NC = kCollideWarps * (32 / kGroup);
+    uint32_t pool = (uint32_t)(((int64_t)NC * c.p.ppc * 3 / 2 + 31) / 32 * 32);
+    if (pool < (uint32_t)c.d.bin) pool = (uint32_t)c.d.bin;
+    return pool;
+}
+
+namespace {
+
+template <typename Real>
+cudaError_t batch_move_impl(BatchDev& b, int cur_p) {
+    Launch<DsmcArgs<Real>> L{};
+    L.tab = (const DsmcArgs<Real>*)b.dsmc[cur_p];
+    L.pre = b.pre_cells;
+    L.nrep = b.nrep;
+    L.total = b.tot_cells;
+    const int64_t blocks = (b.tot_cells * 32 + b.move_block - 1) / b.move_block;
+    return launch_pdl(k_move<Real, true>, dim3((unsigned)blocks), dim3(b.move_block), 0, b.stream, L);
+}
+
+template <typename Real>
+cudaError_t batch_collide_impl(BatchDev& b, int cur_p) {
+    constexpr int NC = kCollideWarps * (32 / kGroup);
+    Launch<DsmcArgs<Real>> L{};
+    L.tab = (const DsmcArgs<Real>*)b.dsmc[cur_p];
+    L.pre = b.pre_blocks;
+    L.nrep = b.nrep;
+    L.total = b.tot_blocks;
+    const size_t smem = (size_t)b.pool * (3 * sizeof(Real) + 4) + (size_t)NC * kChainSteps * (4 + 4 * sizeof(Real));
+    cudaError_t e = cudaFuncSetAttribute(k_collide<Real, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(k_collide<Real, true>, dim3((unsigned)b.tot_blocks), dim3(kCollideWarps * 32), smem,
+                      b.stream, L, b.pool);
+}
+
+}  // namespace
+
+cudaError_t launch_batch_move(BatchDev& b, int cur_p) {
+    return b.real_bytes == 4 ? batch_move_impl<float>(b, cur_p) : batch_move_impl<double>(b, cur_p);
+}
+
+cudaError_t launch_batch_collide(BatchDev& b, int cur_p) {
+    return b.real_bytes == 4 ? batch_collide_impl<float>(b, cur_p) : batch_collide_impl<double>(b, cur_p);
 }
 
 cudaError_t launch_debug_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out, int64_t n,

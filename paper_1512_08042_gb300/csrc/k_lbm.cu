@@ -21,6 +21,7 @@
 // even moments take s and the odd ones d, and f'(+-xi) = w (E +- O) with E the even part
 // (A0, A2) and O the odd part (A1, A3) of the series. Every lattice constant is a
 // compile-time value, so terms with zero speed components vanish at compile time.
+#include <cstring>
 #include <utility>
 
 #include "hyb_internal.cuh"
@@ -270,17 +271,23 @@ __global__ void k_lbm_init(Real* f0, Real* f1, int64_t nnodes) {
     }
 }
 
-template <typename Real, class LAT>
-cudaError_t lbm_impl(Ctx& c) {
+template <typename Real>
+LbmArgs<Real> lbm_args(const Ctx& c, int cur_f) {
     LbmArgs<Real> a;
-    a.src = (const Real*)c.st.f[c.cur_f];
-    a.dst = (Real*)c.st.f[c.cur_f ^ 1];
+    a.src = (const Real*)c.st.f[cur_f];
+    a.dst = (Real*)c.st.f[cur_f ^ 1];
     a.nx = (int32_t)c.d.nx;
     a.ny = (int32_t)c.d.ny;
     a.nnodes = c.d.nnodes;
     a.om = (Real)(1.0 - 1.0 / c.d.tau);
     a.of = (Real)(1.0 - 0.5 / c.d.tau);
     a.g_step = (Real)c.d.g_step;
+    return a;
+}
+
+template <typename Real, class LAT>
+cudaError_t lbm_impl(Ctx& c) {
+    const LbmArgs<Real> a = lbm_args<Real>(c, c.cur_f);
     const int64_t blocks = (c.d.nnodes + 127) / 128;
     prof_begin(c, K_LBM);
     Launch<LbmArgs<Real>> L{};
@@ -302,6 +309,39 @@ cudaError_t lbm_init_impl(Ctx& c) {
 }
 
 }  // namespace
+
+size_t lbm_args_bytes(int real_bytes) {
+    return real_bytes == 4 ? sizeof(LbmArgs<float>) : sizeof(LbmArgs<double>);
+}
+
+void lbm_args_fill(Ctx& c, int cur_f, void* out) {
+    if (c.p.real_bytes == 4) {
+        const LbmArgs<float> a = lbm_args<float>(c, cur_f);
+        std::memcpy(out, &a, sizeof(a));
+    } else {
+        const LbmArgs<double> a = lbm_args<double>(c, cur_f);
+        std::memcpy(out, &a, sizeof(a));
+    }
+}
+
+namespace {
+template <typename Real, class LAT>
+cudaError_t batch_lbm_impl(BatchDev& b, int cur_f) {
+    Launch<LbmArgs<Real>> L{};
+    L.tab = (const LbmArgs<Real>*)b.lbm[cur_f];
+    L.pre = b.pre_nodes;
+    L.nrep = b.nrep;
+    L.total = b.tot_nodes;
+    const int64_t blocks = (b.tot_nodes + b.lbm_block - 1) / b.lbm_block;
+    return launch_pdl(k_lbm<Real, LAT, true>, dim3((unsigned)blocks), dim3(b.lbm_block), 0, b.stream, L);
+}
+}  // namespace
+
+cudaError_t launch_batch_lbm(BatchDev& b, int cur_f) {
+    if (b.lattice == 39)
+        return b.real_bytes == 4 ? batch_lbm_impl<float, D3Q39>(b, cur_f) : batch_lbm_impl<double, D3Q39>(b, cur_f);
+    return b.real_bytes == 4 ? batch_lbm_impl<float, D3Q19>(b, cur_f) : batch_lbm_impl<double, D3Q19>(b, cur_f);
+}
 
 cudaError_t launch_lbm_step(Ctx& c) {
     if (c.p.lattice == 39)

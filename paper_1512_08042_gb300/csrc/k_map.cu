@@ -20,6 +20,8 @@
 // the cell from the same trial's draws.
 // Draws are keyed by (cell, step, purpose, trial index), so the results do not depend on
 // the launch shape.
+#include <cstring>
+
 #include "hyb_internal.cuh"
 
 // Fixed scratch of map_lbm_to_dsmc_noalloc: one Grad record per coupling cell, for callers
@@ -626,6 +628,64 @@ cudaError_t launch_map_l2d_noalloc(Ctx& c, const int32_t* cells, int32_t n) {
                                    : l2d_noalloc_impl<double, D3Q39>(c, cells, n, rec);
     return c.p.real_bytes == 4 ? l2d_noalloc_impl<float, D3Q19>(c, cells, n, rec)
                                : l2d_noalloc_impl<double, D3Q19>(c, cells, n, rec);
+}
+
+size_t map_args_bytes(int real_bytes) {
+    return real_bytes == 4 ? sizeof(MapArgs<float>) : sizeof(MapArgs<double>);
+}
+
+void map_args_fill(Ctx& c, int cur_p, int cur_f, const int32_t* list, int32_t n, void* out) {
+    const int sp = c.cur_p, sf = c.cur_f;
+    c.cur_p = cur_p;
+    c.cur_f = cur_f;
+    if (c.p.real_bytes == 4) {
+        const MapArgs<float> a = map_args<float>(c, list, n);
+        std::memcpy(out, &a, sizeof(a));
+    } else {
+        const MapArgs<double> a = map_args<double>(c, list, n);
+        std::memcpy(out, &a, sizeof(a));
+    }
+    c.cur_p = sp;
+    c.cur_f = sf;
+}
+
+namespace {
+template <typename Real, class LAT>
+cudaError_t batch_d2l_impl(BatchDev& b, int cur_p, int cur_f) {
+    Launch<MapArgs<Real>> L{};
+    L.tab = (const MapArgs<Real>*)b.d2l[cur_p][cur_f];
+    L.pre = b.pre_d2l;
+    L.nrep = b.nrep;
+    L.total = b.tot_d2l;
+    const int64_t blocks = (b.tot_d2l * 32 + 127) / 128;
+    return launch_pdl(k_d2l<Real, LAT, true>, dim3((unsigned)blocks), dim3(128), 0, b.stream, L);
+}
+
+template <typename Real, class LAT>
+cudaError_t batch_l2d_impl(BatchDev& b, int cur_p, int cur_f) {
+    Launch<MapArgs<Real>> L{};
+    L.tab = (const MapArgs<Real>*)b.l2d[cur_p][cur_f];
+    L.pre = b.pre_l2d;
+    L.nrep = b.nrep;
+    L.total = b.tot_l2d;
+    return launch_pdl(k_l2d<Real, LAT, true>, dim3((unsigned)b.tot_l2d), dim3(32 * kL2DWarps), 0, b.stream, L);
+}
+}  // namespace
+
+cudaError_t launch_batch_d2l(BatchDev& b, int cur_p, int cur_f) {
+    if (b.lattice == 39)
+        return b.real_bytes == 4 ? batch_d2l_impl<float, D3Q39>(b, cur_p, cur_f)
+                                 : batch_d2l_impl<double, D3Q39>(b, cur_p, cur_f);
+    return b.real_bytes == 4 ? batch_d2l_impl<float, D3Q19>(b, cur_p, cur_f)
+                             : batch_d2l_impl<double, D3Q19>(b, cur_p, cur_f);
+}
+
+cudaError_t launch_batch_l2d(BatchDev& b, int cur_p, int cur_f) {
+    if (b.lattice == 39)
+        return b.real_bytes == 4 ? batch_l2d_impl<float, D3Q39>(b, cur_p, cur_f)
+                                 : batch_l2d_impl<double, D3Q39>(b, cur_p, cur_f);
+    return b.real_bytes == 4 ? batch_l2d_impl<float, D3Q19>(b, cur_p, cur_f)
+                             : batch_l2d_impl<double, D3Q19>(b, cur_p, cur_f);
 }
 
 cudaError_t launch_map_d2l(Ctx& c, const int32_t* nodes, int32_t n) {

@@ -36,6 +36,19 @@ WORKLOADS = {
 }
 
 
+def ensemble_configs(n=64, seed=1000):
+    """The batched ensemble: n independent channels of the 64 x 1 geometry (walls across,
+    one periodic cell), H uniform in 32..256 cells, 20..100 particles per cell, Kn
+    log-uniform in [0.01, 0.5], one LB node per cell, FP32 state, seeds seed + k."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        out.append(config(ncx=int(rng.integers(32, 257)), ncy=1, ppc=int(rng.integers(20, 101)),
+                          kn=float(np.exp(rng.uniform(np.log(0.01), np.log(0.5)))), lb_ratio=1,
+                          seed=seed + k))
+    return out
+
+
 def coupling_sites(cfg, strip_cells=None):
     """Coupling nodes and cells.
 

@@ -101,3 +101,17 @@ def test_invalid_parameters_are_rejected(lib):
     # null arguments
     assert lib.dsmc_step(None, 1) == B.HYB_EINVAL
     assert lib.map_lbm_to_dsmc(None, None, 1) == B.HYB_EINVAL
+
+
+def test_batch_layout_places_replicas_and_tables(lib):
+    cfgs = [W.config(ncx=40, ncy=1, ppc=30, seed=1), W.config(ncx=13, ncy=8, ppc=23, lb_ratio=2, seed=2)]
+    params = (B.HybParams * 2)(*[B.make_params(c) for c in cfgs])
+    off = (ctypes.c_uint64 * 4)()
+    assert lib.hyb_batch_layout(params, 2, off) == B.HYB_OK
+    sizes = [B.layout(c).total_bytes for c in cfgs]
+    assert off[0] == 0 and off[1] >= sizes[0] and off[1] % 256 == 0
+    assert off[2] >= off[1] + sizes[1] and off[2] % 256 == 0 and off[3] > off[2]
+    mixed = [cfgs[0], dict(cfgs[1], real_bytes=8)]
+    params = (B.HybParams * 2)(*[B.make_params(c) for c in mixed])
+    assert lib.hyb_batch_layout(params, 2, off) == B.HYB_EINVAL
+    assert lib.hyb_batch_layout(params, 0, off) == B.HYB_EINVAL

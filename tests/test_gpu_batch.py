@@ -1,0 +1,78 @@
+"""The batched ensemble against independent contexts: a replica advanced in a batch must give
+bit for bit what the same channel gives when advanced alone (same kernels, same draws)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1512_08042_gb300 import binding as B
+from paper_1512_08042_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _cfgs():
+    return [W.config(ncx=40, ncy=1, ppc=30, kn=0.05, seed=21),
+            W.config(ncx=96, ncy=1, ppc=77, kn=0.3, seed=22),
+            W.config(ncx=13, ncy=8, ppc=23, kn=0.1, lb_ratio=2, capacity_factor=1.5, seed=23),
+            W.config(ncx=33, ncy=1, ppc=55, kn=0.012, seed=24)]
+
+
+def _sites(cfgs):
+    nodes, cells = zip(*[W.coupling_sites(c) for c in cfgs])
+    return list(nodes), list(cells)
+
+
+def _assert_same(h, g):
+    h.sync()
+    g.sync()
+    assert h.current() == g.current()
+    for k, v in h.particles().items():
+        assert torch.equal(v, g.particles()[k]), k
+    for name in ("cell_start", "crmax", "rem", "nbar_sum", "acc", "f"):
+        assert torch.equal(getattr(h, name)(), getattr(g, name)()), name
+    assert torch.equal(h.ctrl()[:4], g.ctrl()[:4])
+    assert h.counters() == g.counters()
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_replicas_equal_single_contexts(use_graph):
+    cfgs = _cfgs()
+    nodes, cells = _sites(cfgs)
+    b = B.Batch(cfgs)
+    singles = [B.Hybrid(c) for c in cfgs]
+    b.hybrid_step(nodes, cells, nsteps=4, use_graph=use_graph)
+    for h, n, c in zip(singles, nodes, cells):
+        h.hybrid_step(torch.from_numpy(n).cuda(), torch.from_numpy(c).cuda(), nsteps=4, use_graph=True)
+    b.sync()
+    for g, h in zip(b.replicas, singles):
+        _assert_same(h, g)
+    assert all(g.sync_status()[1] == 0 for g in b.replicas)
+    b.close()
+
+
+def test_batch_tuner_picks_valid_shapes_and_keeps_results():
+    cfgs = _cfgs()[:3]
+    nodes, cells = _sites(cfgs)
+    b = B.Batch(cfgs)
+    mb, lb = b.tune(nodes, cells)
+    assert mb in (64, 128, 256) and lb in (32, 64, 128)
+    b.hybrid_step(nodes, cells, nsteps=2)
+    steps = 42 + 2
+    for g, cfg, n, c in zip(b.replicas, cfgs, nodes, cells):
+        h = B.Hybrid(cfg)
+        h.hybrid_step(torch.from_numpy(n).cuda(), torch.from_numpy(c).cuda(), nsteps=steps, use_graph=True)
+        _assert_same(h, g)
+    b.close()
+
+
+def test_batch_refuses_a_replica_out_of_lockstep():
+    cfgs = _cfgs()[:2]
+    nodes, cells = _sites(cfgs)
+    b = B.Batch(cfgs)
+    b.hybrid_step(nodes, cells, nsteps=1)
+    b.replicas[1].dsmc_step(1)
+    with pytest.raises(B.HybError) as ei:
+        b.hybrid_step(nodes, cells, nsteps=1)
+    assert ei.value.status == B.HYB_ESTATE
+    b.close()
