@@ -148,6 +148,78 @@ def run_oracle(cfg, steps, budget_s):
     return done / (time.perf_counter() - t0), done
 
 
+def run_ensemble(args):
+    """The batched ensemble against plain contexts: n independent channels advanced one hybrid
+    step at a time, batched (one launch per kernel for all replicas, tuned block shapes) and
+    plain (one context and graph per replica on one stream). Both start from the same states,
+    take the same steps and end bit-identical (checked)."""
+    import torch
+    import __graft_entry__ as G
+    G.build()
+    from paper_1512_08042_gb300 import binding as B
+
+    cfgs = W.ensemble_configs(args.ensemble)
+    nodes, cells = zip(*[W.coupling_sites(c) for c in cfgs])
+    nodes, cells = list(nodes), list(cells)
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    tuner = B.Batch(cfgs)
+    mb, lb = tuner.tune(nodes, cells)
+    tuner.close()
+    batch = B.Batch(cfgs)
+    batch.set_blocks(mb, lb)
+    stream = batch.stream
+    plain = [B.Hybrid(c, stream=stream) for c in cfgs]
+    pn = [torch.from_numpy(x).to(dev) for x in nodes]
+    pc = [torch.from_numpy(x).to(dev) for x in cells]
+
+    def step_batch():
+        batch.hybrid_step(nodes, cells, nsteps=1, use_graph=True)
+
+    def step_plain():
+        for h, a, b in zip(plain, pn, pc):
+            h.hybrid_step(a, b, nsteps=1, use_graph=True, order_inputs=False)
+
+    def timed(step):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize(dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        for a, b in ev:
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            a.record(stream)
+            step()
+            b.record(stream)
+        torch.cuda.synchronize(dev)
+        return sum(a.elapsed_time(b) for a, b in ev) / args.steps
+
+    ms_b = timed(step_batch)
+    ms_p = timed(step_plain)
+    identical = True
+    for g, h in zip(batch.replicas, plain):
+        pg, ph = g.particles(), h.particles()
+        identical &= all(torch.equal(pg[k], ph[k]) for k in pg)
+        identical &= torch.equal(g.f(), h.f()) and torch.equal(g.acc(), h.acc())
+    particles = sum(c["ncx"] * c["ncy"] * c["ppc"] for c in cfgs)
+    line = {
+        "metric": "ensemble hybrid steps/s (every replica advanced one hybrid step)",
+        "value": 1e3 / ms_b, "unit": "ensemble steps/s", "higher_is_better": True,
+        "ms_per_step": ms_b, "plain": {"value": 1e3 / ms_p, "ms_per_step": ms_p,
+                                       "launches": "%d contexts, one graph each" % len(cfgs)},
+        "speedup_vs_plain": ms_p / ms_b, "identical_to_plain": bool(identical),
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "ensemble of %d channels (H 32-256 cells, 20-100 ppc, Kn 0.01-0.5)"
+                               % len(cfgs), "replicas": len(cfgs), "particles": particles,
+                   "block_shapes": {"move": mb, "lbm": lb},
+                   "l2": "flushed before every timed step (512 MB write)"},
+    }
+    print(json.dumps(line), flush=True)
+    batch.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -160,9 +232,14 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="run this many hybrid steps with direct launches and exit (for ncu)")
+    ap.add_argument("--ensemble", type=int, default=0,
+                    help="time a batched ensemble of this many channels against plain contexts")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.ensemble:
+        run_ensemble(args)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
