@@ -598,35 +598,60 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
             }
             __syncthreads();
             if (w == 0) {
+                // the candidates of this pass for the lane's cell; the particles of the next
+                // candidate are loaded before this one is applied, and taken from registers
+                // where this one changes them
                 const uint32_t nsel = s_nsel[lane];
+                const int kend = nsel > k0 ? (int)min(nsel - k0, (uint32_t)KC) : 0;
+                const int t0 = (int)lane * KC;
+                uint32_t ijn = 0;
+                Real nax = 0, nay = 0, naz = 0, nbx = 0, nby = 0, nbz = 0;
+                if (kend > 0) {
+                    ijn = c_ij[t0];
+                    const uint32_t i = ijn & 0x7FFFu, j = (ijn >> 15) & 0xFFFFu;
+                    nax = gvx[i], nay = gvy[i], naz = gvz[i];
+                    nbx = gvx[j], nby = gvy[j], nbz = gvz[j];
+                }
 #pragma unroll 1
-                for (int kk = 0; kk < KC; ++kk) {
-                    if (k0 + (uint32_t)kk < nsel) {
-                        const int t = (int)lane * KC + kk;
-                        const uint32_t ij = c_ij[t];
-                        const uint32_t i = ij & 0x7FFFu, j = (ij >> 15) & 0xFFFFu;
-                        const Real ax = gvx[i], ay = gvy[i], az = gvz[i];
-                        const Real bx = gvx[j], by = gvy[j], bz = gvz[j];
-                        const Real ddx = ax - bx, ddy = ay - by, ddz = az - bz;
-                        const Real cr = sqrt(ddx * ddx + ddy * ddy + ddz * ddz);
-                        if (cr > cm) cm = cr;
-                        if (cr > c_R[t] * cm) {
-                            if (ij & 0x80000000u) {
-                                flags |= HYB_ST_SCATTER_CAP;
-                            } else {
-                                const Real cx = (ax + bx) * (Real)0.5;
-                                const Real cy = (ay + by) * (Real)0.5;
-                                const Real cz = (az + bz) * (Real)0.5;
-                                const Real h = cr * (Real)0.5;
-                                const Real hx = h * c_nx[t], hy = h * c_ny[t], hz = h * c_nz[t];
-                                gvx[i] = cx + hx;
-                                gvy[i] = cy + hy;
-                                gvz[i] = cz + hz;
-                                gvx[j] = cx - hx;
-                                gvy[j] = cy - hy;
-                                gvz[j] = cz - hz;
-                                ncoll += 1;
-                            }
+                for (int kk = 0; kk < kend; ++kk) {
+                    const int t = t0 + kk;
+                    const uint32_t ij = ijn;
+                    const uint32_t i = ij & 0x7FFFu, j = (ij >> 15) & 0xFFFFu;
+                    const Real ax = nax, ay = nay, az = naz;
+                    const Real bx = nbx, by = nby, bz = nbz;
+                    uint32_t in_ = 0xFFFFFFFFu, jn = 0xFFFFFFFFu;
+                    if (kk + 1 < kend) {
+                        ijn = c_ij[t + 1];
+                        in_ = ijn & 0x7FFFu;
+                        jn = (ijn >> 15) & 0xFFFFu;
+                        nax = gvx[in_], nay = gvy[in_], naz = gvz[in_];
+                        nbx = gvx[jn], nby = gvy[jn], nbz = gvz[jn];
+                    }
+                    const Real ddx = ax - bx, ddy = ay - by, ddz = az - bz;
+                    const Real cr = sqrt(ddx * ddx + ddy * ddy + ddz * ddz);
+                    if (cr > cm) cm = cr;
+                    if (cr > c_R[t] * cm) {
+                        if (ij & 0x80000000u) {
+                            flags |= HYB_ST_SCATTER_CAP;
+                        } else {
+                            const Real cx = (ax + bx) * (Real)0.5;
+                            const Real cy = (ay + by) * (Real)0.5;
+                            const Real cz = (az + bz) * (Real)0.5;
+                            const Real h = cr * (Real)0.5;
+                            const Real hx = h * c_nx[t], hy = h * c_ny[t], hz = h * c_nz[t];
+                            const Real pix = cx + hx, piy = cy + hy, piz = cz + hz;
+                            const Real pjx = cx - hx, pjy = cy - hy, pjz = cz - hz;
+                            gvx[i] = pix;
+                            gvy[i] = piy;
+                            gvz[i] = piz;
+                            gvx[j] = pjx;
+                            gvy[j] = pjy;
+                            gvz[j] = pjz;
+                            ncoll += 1;
+                            if (in_ == i) nax = pix, nay = piy, naz = piz;
+                            if (in_ == j) nax = pjx, nay = pjy, naz = pjz;
+                            if (jn == i) nbx = pix, nby = piy, nbz = piz;
+                            if (jn == j) nbx = pjx, nby = pjy, nbz = pjz;
                         }
                     }
                 }
