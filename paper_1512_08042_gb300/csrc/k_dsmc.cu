@@ -503,21 +503,40 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
         Real* vy = pv + pool + poff;
         Real* vz = pv + 2 * pool + poff;
         uint32_t* st = pst + poff;
-        // A. stable order (ascending origin slot) and gather
+        // A. stable order (ascending origin slot) and gather. Cells of up to SMALL particles
+        // are sorted with R keys per lane; a warp that holds a cell of up to 2 SMALL sorts
+        // all of its cells with 2 R keys per lane; larger cells are ranked in shared memory.
         {
-            uint32_t v[R];
+            if (__any_sync(kFull, n > (uint32_t)SMALL && n <= (uint32_t)(2 * SMALL))) {
+                uint32_t v[2 * R];
+                const bool in2 = n <= (uint32_t)(2 * SMALL);
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const uint32_t k = (uint32_t)(gl + G * r);
-                v[r] = (n <= (uint32_t)SMALL && k < n) ? vl[r] : 0xFFFFFFFFu;
+                for (int r = 0; r < 2 * R; ++r) {
+                    const uint32_t k = (uint32_t)(gl + G * r);
+                    v[r] = 0xFFFFFFFFu;
+                    if (in2 && k < n) v[r] = r < R ? vl[r] : a.tag[base + k];
+                }
+                bitonic_group<G, 2 * R>(v);
+                if (in2) {
+                    gather_slots<Real, G, R>(a.rec, a.dx + base, a.dy + base, gl, n, v, vx, vy, vz);
+                    gather_slots<Real, G, R>(a.rec, a.dx + base, a.dy + base, gl + G * R, n, v + R,
+                                             vx, vy, vz);
+                }
+            } else {
+                uint32_t v[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const uint32_t k = (uint32_t)(gl + G * r);
+                    v[r] = (n <= (uint32_t)SMALL && k < n) ? vl[r] : 0xFFFFFFFFu;
+                }
+                bitonic_group<G, R>(v);
+                if (n <= (uint32_t)SMALL)
+                    gather_slots<Real, G, R>(a.rec, a.dx + base, a.dy + base, gl, n, v, vx, vy, vz);
             }
-            bitonic_group<G, R>(v);
-            if (n > (uint32_t)SMALL)
+            if (n > (uint32_t)(2 * SMALL))
                 for (uint32_t k = gl; k < n; k += G) st[k] = a.tag[base + k];
             __syncwarp();
-            if (n <= (uint32_t)SMALL) {
-                gather_slots<Real, G, R>(a.rec, a.dx + base, a.dy + base, gl, n, v, vx, vy, vz);
-            } else {
+            if (n > (uint32_t)(2 * SMALL)) {
                 // rank of each tag = number of smaller tags in the cell
                 for (uint32_t k = gl; k < n; k += G) {
                     const uint32_t t = st[k];
@@ -561,9 +580,23 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
             s_cm[gi] = cm0;
         }
         __syncthreads();
-        // B. NTC collisions. Each pass draws KC candidates of every cell of the block in
-        // parallel (all threads), then warp 0 applies them in order, one lane per cell.
-        uint32_t maxsel = __reduce_max_sync(kFull, s_nsel[lane]);
+        // B. NTC collisions. The candidates of all cells are drawn in parallel by the whole
+        // block, then warp 0 applies them in order, one lane per cell. If the block's
+        // candidates fit the candidate buffer they are packed (cell g at the exclusive scan
+        // of the counts) and drawn in one pass; otherwise every pass draws up to KC
+        // candidates per cell.
+        const uint32_t my_sel = s_nsel[lane];
+        uint32_t sel_inc = my_sel;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, sel_inc, o);
+            if (lane >= (unsigned)o) sel_inc += t;
+        }
+        const uint32_t sel_total = __shfl_sync(kFull, sel_inc, 31);
+        const bool packed = sel_total <= (uint32_t)(NC * KC);
+        const uint32_t maxsel = __reduce_max_sync(kFull, my_sel);
+        const uint32_t npass = packed ? (sel_total > 0u ? 1u : 0u) : (maxsel + KC - 1) / KC;
+        const int tend = packed ? (int)sel_total : NC * KC;
         Real cm = (Real)0;
         uint32_t ncoll = 0;
         Real* gvx = nullptr;
@@ -576,11 +609,33 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
             gvy = pv + pool + go;
             gvz = pv + 2 * pool + go;
         }
-        for (uint32_t k0 = 0; k0 < maxsel; k0 += KC) {
-            for (int t = threadIdx.x; t < NC * KC; t += WARPS * 32) {
-                const int g = t / KC, kk = t % KC;
-                const uint32_t k = k0 + (uint32_t)kk;
-                if (k < s_nsel[g]) {
+        for (uint32_t pass = 0; pass < npass; ++pass) {
+            const uint32_t k0 = pass * (uint32_t)KC;
+            for (int tb = w * 32; tb < tend; tb += WARPS * 32) {  // warp-uniform trip count
+                const int t = tb + (int)lane;
+                int g;
+                uint32_t k;
+                bool valid;
+                if (packed) {
+                    // the cell whose range holds slot t: the number of cells whose inclusive
+                    // count is <= t
+                    int lo = 0;
+#pragma unroll
+                    for (int step = 16; step >= 1; step >>= 1) {
+                        const uint32_t v = __shfl_sync(kFull, sel_inc, lo + step - 1);
+                        if (v <= (uint32_t)t) lo += step;
+                    }
+                    g = lo;
+                    const uint32_t ginc = __shfl_sync(kFull, sel_inc, g);
+                    const uint32_t gsel = __shfl_sync(kFull, my_sel, g);
+                    k = (uint32_t)t - (ginc - gsel);
+                    valid = t < tend;
+                } else {
+                    g = t / KC;
+                    k = k0 + (uint32_t)(t % KC);
+                    valid = t < tend && k < s_nsel[g];
+                }
+                if (valid) {
                     const uint32_t cg = (uint32_t)(blk * NC + g);
                     const uint32_t ng = s_n[g];
                     const uint4 r = draw(a.seed, cg, s, TAG_NTC_PAIR, k, 0);
@@ -601,9 +656,9 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
                 // the candidates of this pass for the lane's cell; the particles of the next
                 // candidate are loaded before this one is applied, and taken from registers
                 // where this one changes them
-                const uint32_t nsel = s_nsel[lane];
-                const int kend = nsel > k0 ? (int)min(nsel - k0, (uint32_t)KC) : 0;
-                const int t0 = (int)lane * KC;
+                const int kend = packed ? (int)my_sel
+                                        : (my_sel > k0 ? (int)min(my_sel - k0, (uint32_t)KC) : 0);
+                const int t0 = packed ? (int)(sel_inc - my_sel) : (int)lane * KC;
                 uint32_t ijn = 0;
                 Real nax = 0, nay = 0, naz = 0, nbx = 0, nby = 0, nbz = 0;
                 if (kend > 0) {
