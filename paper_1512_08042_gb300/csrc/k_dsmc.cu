@@ -193,21 +193,24 @@ __device__ __forceinline__ uint32_t cell_key(const DsmcArgs<Real>& a, Real L, Re
     return (uint32_t)(iy * a.ncx + ix);
 }
 
-// Appends the active lanes' slots to the bins of their new cells: lanes bound for the same
-// cell share one atomic, and each gets arrival = base + rank among them.
-__device__ __forceinline__ uint32_t bin_arrival(uint32_t* __restrict__ count, uint32_t key, bool active,
-                                                unsigned lane) {
-    const unsigned m = __ballot_sync(kFull, active);
-    uint32_t arr = 0;
-    if (active) {
-        const unsigned peers = __match_any_sync(m, key);
-        const int leader = __ffs(peers) - 1;
-        uint32_t b0 = 0;
-        if ((int)lane == leader) b0 = atomicAdd(&count[key], (uint32_t)__popc(peers));
-        b0 = __shfl_sync(peers, b0, leader);
-        arr = b0 + (uint32_t)__popc(peers & ((1u << lane) - 1u));
-    }
-    return arr;
+// Appends the active lanes' two slots to the bins of their new cells: lanes bound for the
+// same cell share one atomic, and each gets arrival = base + rank among them. The atomics
+// of both slots are in flight before either result is used.
+__device__ __forceinline__ void bin_arrival2(uint32_t* __restrict__ count, uint32_t key1, bool act1,
+                                             uint32_t key2, bool act2, unsigned lane, uint32_t& arr1,
+                                             uint32_t& arr2) {
+    // inactive lanes match among themselves under a key no cell has
+    const unsigned peers1 = __match_any_sync(kFull, act1 ? key1 : 0xFFFFFFFFu);
+    const unsigned peers2 = __match_any_sync(kFull, act2 ? key2 : 0xFFFFFFFFu);
+    const int lead1 = __ffs(peers1) - 1, lead2 = __ffs(peers2) - 1;
+    uint32_t b1 = 0, b2 = 0;
+    if (act1 && (int)lane == lead1) b1 = atomicAdd(&count[key1], (uint32_t)__popc(peers1));
+    if (act2 && (int)lane == lead2) b2 = atomicAdd(&count[key2], (uint32_t)__popc(peers2));
+    b1 = __shfl_sync(kFull, b1, lead1);
+    b2 = __shfl_sync(kFull, b2, lead2);
+    const unsigned below = (1u << lane) - 1u;
+    arr1 = b1 + (uint32_t)__popc(peers1 & below);
+    arr2 = b2 + (uint32_t)__popc(peers2 & below);
 }
 
 // One source cell, by one warp; the first 64 particles of the cell are handled two per
@@ -288,8 +291,8 @@ __device__ __forceinline__ void move_cell(const DsmcArgs<Real>& a, int c, unsign
             }
             const uint32_t key1 = act1 ? cell_key(a, L, p1[0], p1[1]) : 0u;
             const uint32_t key2 = act2 ? cell_key(a, L, p2[0], p2[1]) : 0u;
-            const uint32_t arr1 = bin_arrival(cnt, key1, act1, lane);
-            const uint32_t arr2 = bin_arrival(cnt, key2, act2, lane);
+            uint32_t arr1, arr2;
+            bin_arrival2(cnt, key1, act1, key2, act2, lane, arr1, arr2);
             if (act1) {
                 rec_store(rec, base + k1, p1[0], p1[1], p1[2], p1[3], p1[4]);
                 if (arr1 < bin)
