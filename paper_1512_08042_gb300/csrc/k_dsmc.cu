@@ -356,38 +356,63 @@ struct CollideCfg {
 constexpr int kCollideWarps = 8;  // 32 cells per block
 constexpr int kChainSteps = 16;   // candidates per cell drawn per pass of the NTC phase
 
-// Ascending bitonic sort of G R keys held by the G lanes of a group, R per lane (key r of
-// group lane l at position l + G r). Constant trip counts: the keys stay in registers.
-template <int G, int R>
-__device__ __forceinline__ void bitonic_group(uint32_t (&v)[R]) {
+// Ascending bitonic sort of G R keys held by the G lanes of a group, R per lane, in blocked
+// order: key r of group lane l is at position (r % B) + B l + B G (r / B). Exchanges between
+// positions less than B apart, or at least B G apart, stay in the lane's registers; the
+// others are shuffles between the lanes of the group. Constant trip counts: the keys stay
+// in registers.
+template <int G, int R, int B>
+__device__ __forceinline__ void bitonic_blocked(uint32_t (&v)[R]) {
+    static_assert(R % B == 0, "whole blocks of B keys per lane");
     constexpr int N = G * R;
     const int gl = (int)(lane_id() % G);
 #pragma unroll
     for (int k = 2; k <= N; k <<= 1) {
 #pragma unroll
         for (int j = k >> 1; j > 0; j >>= 1) {
-            if (j >= G) {
-                const int jr = j / G;
+            if (j < B || j >= B * G) {
+                const int jr = j < B ? j : j / G;  // distance in registers
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const int o = r ^ jr;
                     if (r < o) {
-                        const bool asc = ((gl + G * r) & k) == 0;
+                        const int pos = (r % B) + B * gl + B * G * (r / B);
+                        const bool asc = (pos & k) == 0;
                         const uint32_t lo = min(v[r], v[o]), hi = max(v[r], v[o]);
                         v[r] = asc ? lo : hi;
                         v[o] = asc ? hi : lo;
                     }
                 }
             } else {
-                const bool lower = (gl & j) == 0;
+                const int jl = j / B;  // distance in lanes
+                const bool lower = (gl & jl) == 0;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const uint32_t o = __shfl_xor_sync(kFull, v[r], j);
-                    const bool asc = ((gl + G * r) & k) == 0;
+                    const uint32_t o = __shfl_xor_sync(kFull, v[r], jl);
+                    const int pos = (r % B) + B * gl + B * G * (r / B);
+                    const bool asc = (pos & k) == 0;
                     v[r] = (lower == asc) ? min(v[r], o) : max(v[r], o);
                 }
             }
         }
+    }
+}
+
+// Writes the sorted keys of blocked positions below n to st and reads back into v the keys
+// of positions gl + G r (the order in which the group gathers); every lane of the warp
+// calls it.
+template <int G, int R, int B>
+__device__ __forceinline__ void blocked_to_strided(uint32_t (&v)[R], uint32_t* st, uint32_t n, int gl) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const uint32_t pos = (uint32_t)((r % B) + B * gl + B * G * (r / B));
+        if (pos < n) st[pos] = v[r];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const uint32_t k = (uint32_t)(gl + G * r);
+        v[r] = k < n ? st[k] : 0u;
     }
 }
 
@@ -456,8 +481,8 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
     const int c = blk * NC + gi;
     const bool has = c < a.ncells;
     const int64_t base = (int64_t)c * bin;
-    // the cell's loads are issued together: count, the first SMALL tag slots, the leader's
-    // NTC state and the lane's three moment sums
+    // the cell's loads are issued together: count, the first SMALL tag slots and the
+    // leader's NTC state
     uint32_t n_all = has ? a.count_d[c] : 0u;
     uint32_t vl[R];
 #pragma unroll
@@ -471,12 +496,6 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
         nb0 = a.nbar_sum[c];
         cm0 = a.crmax[c];
         rem0 = a.rem[c];
-    }
-    double acc0[3] = {0.0, 0.0, 0.0};
-    if (has && do_sample) {
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-            if (3 * gl + q < kMoments) acc0[q] = a.acc[(size_t)c * kMoments + 3 * gl + q];
     }
     if (n_all > bin) n_all = bin;
     // the cells' regions of the block pool (exclusive scan of the counts); if they do not
@@ -507,23 +526,60 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
         Real* vz = pv + 2 * pool + poff;
         uint32_t* st = pst + poff;
         // A. stable order (ascending origin slot) and gather. Cells of up to SMALL particles
-        // are sorted with R keys per lane; a warp that holds a cell of up to 2 SMALL sorts
-        // all of its cells with 2 R keys per lane; larger cells are ranked in shared memory.
+        // are sorted by their group with R keys per lane. A warp that holds a cell of up to
+        // 2 SMALL puts the tags of its cells in their shared-memory tag slots and sorts them
+        // two cells at a time, 2 G lanes with R keys each per cell. Larger cells are ranked
+        // in shared memory.
         {
             if (__any_sync(kFull, n > (uint32_t)SMALL && n <= (uint32_t)(2 * SMALL))) {
-                uint32_t v[2 * R];
                 const bool in2 = n <= (uint32_t)(2 * SMALL);
+                const uint32_t nn = in2 ? n : 0u;
+                uint32_t hi[R];
 #pragma unroll
-                for (int r = 0; r < 2 * R; ++r) {
-                    const uint32_t k = (uint32_t)(gl + G * r);
-                    v[r] = 0xFFFFFFFFu;
-                    if (in2 && k < n) v[r] = r < R ? vl[r] : a.tag[base + k];
+                for (int r = 0; r < R; ++r) {
+                    const uint32_t k = (uint32_t)(SMALL + gl + G * r);
+                    hi[r] = k < nn ? a.tag[base + k] : 0u;
                 }
-                bitonic_group<G, 2 * R>(v);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const uint32_t k = (uint32_t)(gl + G * r);
+                    if (k < nn) st[k] = vl[r];
+                    if (k + SMALL < nn) st[k + SMALL] = hi[r];
+                }
+                __syncwarp();
+#pragma unroll 1
+                for (int h = 0; h < 2; ++h) {
+                    const int g2 = 2 * h + (int)(lane >> 4);  // the group whose cell this half sorts
+                    const int l2 = (int)(lane & 15u);
+                    const uint32_t n2 = __shfl_sync(kFull, nn, g2 * G);
+                    uint32_t* st2 = pst + __shfl_sync(kFull, poff, g2 * G);
+                    uint32_t v[R];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const uint32_t k = (uint32_t)(l2 + 2 * G * r);
+                        v[r] = k < n2 ? st2[k] : 0xFFFFFFFFu;
+                    }
+                    __syncwarp();
+                    bitonic_blocked<2 * G, R, R>(v);
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const uint32_t pos = (uint32_t)(r + R * l2);
+                        if (pos < n2) st2[pos] = v[r];
+                    }
+                    __syncwarp();
+                }
                 if (in2) {
-                    gather_slots<Real, G, R>(a.rec, a.dx + base, a.dy + base, gl, n, v, vx, vy, vz);
-                    gather_slots<Real, G, R>(a.rec, a.dx + base, a.dy + base, gl + G * R, n, v + R,
-                                             vx, vy, vz);
+#pragma unroll 1
+                    for (int q = 0; q < 2; ++q) {
+                        uint32_t src[R];
+#pragma unroll
+                        for (int r = 0; r < R; ++r) {
+                            const uint32_t k = (uint32_t)(SMALL * q + gl + G * r);
+                            src[r] = k < n ? st[k] : 0u;
+                        }
+                        gather_slots<Real, G, R>(a.rec, a.dx + base, a.dy + base, SMALL * q + gl, n,
+                                                 src, vx, vy, vz);
+                    }
                 }
             } else {
                 uint32_t v[R];
@@ -532,7 +588,8 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
                     const uint32_t k = (uint32_t)(gl + G * r);
                     v[r] = (n <= (uint32_t)SMALL && k < n) ? vl[r] : 0xFFFFFFFFu;
                 }
-                bitonic_group<G, R>(v);
+                bitonic_blocked<G, R, R>(v);
+                blocked_to_strided<G, R, R>(v, st, n <= (uint32_t)SMALL ? n : 0u, gl);
                 if (n <= (uint32_t)SMALL)
                     gather_slots<Real, G, R>(a.rec, a.dx + base, a.dy + base, gl, n, v, vx, vy, vz);
             }
@@ -762,10 +819,11 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
             }
             if (gl == 0) t[0] = (Real)n;  // the particle count, moment 0
             if (has_r) {
+                // one FP64 addition per sum, done in L2 (each sum has one writer per step)
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
                     const int mq = 3 * gl + q;
-                    if (mq < kMoments) a.acc[(size_t)c * kMoments + mq] = acc0[q] + (double)t[q];
+                    if (mq < kMoments) atomicAdd(&a.acc[(size_t)c * kMoments + mq], (double)t[q]);
                 }
             }
         }
