@@ -12,8 +12,9 @@
 // populations of the cell's lb_ratio^2 nodes, rho and u, the comoving coefficients
 // a2 = sum f c c / rho - I and a3 = sum f c c c / rho (c = xi - u), M, C = 1 + 30 M (Eq. C),
 // all in the state precision with one fixed pairwise order of every population sum, and the
-// particle count floor(rho ppc + U); meanwhile the other warps draw their first trials. The
-// cell's trial stream is then evaluated 256 trials at a time: Box-Muller xi from the unit
+// particle count floor(rho ppc + U); the other warps wait (trials drawn meanwhile took
+// issue slots from warp 0 and lengthened the path). The cell's trial stream is then
+// evaluated 256 trials at a time: Box-Muller xi from the unit
 // Maxwellian, accepted when C R <= G(xi), G = 1 + a2:H2/2 + a3:H3/6 (Eq. distr_outeq) in
 // the state precision; the k-th accepted trial becomes the k-th particle of the cell's bin
 // (replacing the old ones), velocity xi + u (Eq. step6 in c_th units), position uniform in
@@ -97,8 +98,12 @@ __device__ __forceinline__ void d2l_entries(const MapArgs<Real>& a, int first, i
             if (lane == 0) atomicOr(&a.ctrl[CTRL_STATUS], HYB_ST_BAD_INPUT);
             continue;
         }
-        // per-particle moments, lane k: <v> (1-3), <vv> (4-9), <vvv> (10-19)
-        const Real mr = (Real)(mk * (1.0 / NS));
+        // per-particle moments, lane k: <v> (1-3), <vv> (4-9), <vvv> (10-19); the FP64
+        // reciprocal is formed by one lane (FP64 runs at a small fraction of the FP32 rate)
+        double inv = 0.0;
+        if (lane == 0) inv = 1.0 / NS;
+        inv = __shfl_sync(kFull, inv, 0);
+        const Real mr = (Real)(mk * inv);
         const Real rho = (Real)NS / ((Real)S * (Real)a.ppc);
         const Real m1x = __shfl_sync(kFull, mr, 1);
         const Real m1y = __shfl_sync(kFull, mr, 2);
@@ -379,16 +384,6 @@ __device__ __forceinline__ void l2d_cells(const MapArgs<Real>& a, int first, int
                 g.pad = 0;
             }
         }
-        // the first trial of this thread does not depend on the coefficients
-        Real X = 0, Y = 0, Z = 0;
-        uint4 r2;
-        {
-            const uint4 r1 = draw(a.seed, cell, t_step, TAG_L2D_VEL, threadIdx.x, 0);
-            r2 = draw(a.seed, cell, t_step, TAG_L2D_VEL, threadIdx.x, 1);
-            Real spare;
-            gauss_pair<Real>(r1.x, r1.y, X, Y);
-            gauss_pair<Real>(r1.z, r1.w, Z, spare);
-        }
         __syncthreads();
         const uint32_t nnew = s_nnew;
         Real a2[6], a3[10];
@@ -408,25 +403,23 @@ __device__ __forceinline__ void l2d_cells(const MapArgs<Real>& a, int first, int
         const uint64_t cap64 = 1000ull * nnew;
         const uint32_t cap = cap64 < 0xFFFFFFull ? (uint32_t)cap64 : 0xFFFFFFu;
         uint32_t produced = 0, j0 = 0;
-        bool first = true;
         while (produced < nnew && j0 < cap) {
             const uint32_t j = j0 + threadIdx.x;
             const bool valid = j < cap;
             bool acc = false, env = false;
+            Real X = 0, Y = 0, Z = 0;
+            uint4 r2 = make_uint4(0u, 0u, 0u, 0u);
             if (valid) {
-                if (!first) {
-                    const uint4 r1 = draw(a.seed, cell, t_step, TAG_L2D_VEL, j, 0);
-                    r2 = draw(a.seed, cell, t_step, TAG_L2D_VEL, j, 1);
-                    Real spare;
-                    gauss_pair<Real>(r1.x, r1.y, X, Y);
-                    gauss_pair<Real>(r1.z, r1.w, Z, spare);
-                }
+                const uint4 r1 = draw(a.seed, cell, t_step, TAG_L2D_VEL, j, 0);
+                r2 = draw(a.seed, cell, t_step, TAG_L2D_VEL, j, 1);
+                Real spare;
+                gauss_pair<Real>(r1.x, r1.y, X, Y);
+                gauss_pair<Real>(r1.z, r1.w, Z, spare);
                 const Real G = grad_G<Real, LAT::ORDER>(a2, a3, X, Y, Z);
                 const Real R = (Real)u01f(r2.x);
                 env = G > C;
                 acc = C * R <= G;
             }
-            first = false;
             const unsigned am = __ballot_sync(kFull, acc);
             const unsigned em = __ballot_sync(kFull, env);
             const unsigned vm = __ballot_sync(kFull, valid);
