@@ -196,6 +196,37 @@ void ora_counters(void* hv, uint64_t* out) {
     for (int i = 0; i < C_NUM; ++i) out[i] = c[i];
 }
 
+// Per-node g_y and tau for the LBM of the handle (n = nnodes), or none (n = 0).
+int ora_lbm_node_params(void* hv, const double* g, const double* tau, int64_t n) {
+    Handle* h = (Handle*)hv;
+    auto set = [&](auto& B) {
+        if (n == 0) {
+            B.g_node.clear();
+            B.tau_node.clear();
+            return 0;
+        }
+        if (n != B.d.nnodes) return 1;
+        B.g_node.assign(g, g + n);
+        B.tau_node.assign(tau, tau + n);
+        return 0;
+    };
+    return (h->rb == 4) ? set(h->lf) : set(h->ld);
+}
+
+// Grad coefficients of one node's populations (20 values) and the interface loss over the
+// listed nodes against 20 targets per node.
+int ora_lbm_grad_node(void* hv, int64_t node, double* out) {
+    Handle* h = (Handle*)hv;
+    if (h->rb == 4) h->lf.grad_node(node, out);
+    else h->ld.grad_node(node, out);
+    return 0;
+}
+double ora_lbm_interface_loss(void* hv, const int32_t* nodes, int n, const double* targets) {
+    Handle* h = (Handle*)hv;
+    return (h->rb == 4) ? h->lf.interface_loss(nodes, n, targets)
+                        : h->ld.interface_loss(nodes, n, targets);
+}
+
 // One node's collision from streamed populations fs (double), for pins.
 int ora_lbm_collide(const Params* p, const double* fs, double* out) {
     if (!valid(p)) return 1;

@@ -14,6 +14,13 @@
 //   F = w sum_{n=1..N} n (g (x) a_eq^(n-1)) : H^n / n! (Hermite expansion of -g . grad_xi f);
 //   f' = f_eq + (1 - 1/tau) f_neq_reg + (1 - 1/(2 tau)) F.
 // Relaxation time from Eq. tau. The quasi-2D slab has one periodic layer in z.
+//
+// Optional per-node parameters (for the differentiated LBM): a body-force increment g_y and
+// a relaxation time tau for every node; when set they replace the scalars of Eq. tau and of
+// the force. The coupling-interface loss of the differentiated LBM is defined here too: at
+// each listed node, the Grad coefficients of its populations (rho, u = sum f xi / rho,
+// a2 = sum f c c / rho - I, a3 = sum f c c c / rho with c = xi - u; the comoving coefficients
+// of Table 1) against 20 target values, summed as squares.
 #pragma once
 #include "ora_common.hpp"
 
@@ -25,6 +32,7 @@ struct Lbm {
     Derived d;
     Lattice L;
     std::vector<Real> f;  // f[a * nnodes + y * nx + x]
+    std::vector<double> g_node, tau_node;  // per-node g_y and tau; empty: the scalars
 
     void init(const Params& pp) {
         p = pp;
@@ -41,14 +49,15 @@ struct Lbm {
     int64_t wrap_y(int64_t y) const { return ((y % d.ny) + d.ny) % d.ny; }
 
     // Collision of one node given its streamed populations fs[q]; writes out[q].
-    void collide(const double* fs, double* out) const {
+    void collide(const double* fs, double* out) const { collide(fs, out, d.g_step, d.tau); }
+    void collide(const double* fs, double* out, double gy, double tau) const {
         const int N = d.order;
         double rho = 0.0, j[3] = {0, 0, 0};
         for (int a = 0; a < L.q; ++a) {
             rho += fs[a];
             for (int i = 0; i < 3; ++i) j[i] += fs[a] * L.xi[a][i];
         }
-        const double g[3] = {0.0, d.g_step, 0.0};
+        const double g[3] = {0.0, gy, 0.0};
         double u[3];
         for (int i = 0; i < 3; ++i) u[i] = (j[i] + 0.5 * rho * g[i]) / rho;
 
@@ -80,8 +89,8 @@ struct Lbm {
                 for (int l = 0; l < 3; ++l) bf.a3[i][k][l] = 3.0 * g[i] * aeq.a2[k][l];
             }
         }
-        const double om = 1.0 - 1.0 / d.tau;
-        const double of = 1.0 - 1.0 / (2.0 * d.tau);
+        const double om = 1.0 - 1.0 / tau;
+        const double of = 1.0 - 1.0 / (2.0 * tau);
         for (int a = 0; a < L.q; ++a) {
             const double* x = L.xi[a].data();
             const double freg = L.w[a] * hermite_series(aneq, x, N);
@@ -124,11 +133,65 @@ struct Lbm {
                     else
                         fs[a] = fa(a, sx, sy);
                 }
-                collide(fs.data(), out.data());
+                const int64_t node = y * nx + x;
+                if (g_node.empty())
+                    collide(fs.data(), out.data());
+                else
+                    collide(fs.data(), out.data(), g_node[(size_t)node], tau_node[(size_t)node]);
                 for (int a = 0; a < L.q; ++a)
                     nf[(size_t)a * d.nnodes + y * nx + x] = (Real)out[a];
             }
         f.swap(nf);
+    }
+
+    // Grad coefficients of the populations of one node, by their definitions: out[0] rho,
+    // out[1..3] u, out[4..9] a2 (xx xy xz yy yz zz), out[10..19] a3 (xxx xxy xxz xyy xyz
+    // xzz yyy yyz yzz zzz).
+    void grad_node(int64_t node, double* out) const {
+        double rho = 0.0, j[3] = {0, 0, 0};
+        for (int a = 0; a < L.q; ++a) {
+            const double fa_ = (double)f[(size_t)a * d.nnodes + node];
+            rho += fa_;
+            for (int i = 0; i < 3; ++i) j[i] += fa_ * L.xi[a][i];
+        }
+        double u[3];
+        for (int i = 0; i < 3; ++i) u[i] = j[i] / rho;
+        double m2[3][3] = {}, m3[3][3][3] = {};
+        for (int a = 0; a < L.q; ++a) {
+            const double fa_ = (double)f[(size_t)a * d.nnodes + node];
+            double c[3];
+            for (int i = 0; i < 3; ++i) c[i] = L.xi[a][i] - u[i];
+            for (int i = 0; i < 3; ++i)
+                for (int k = 0; k < 3; ++k) {
+                    m2[i][k] += fa_ * c[i] * c[k];
+                    for (int l = 0; l < 3; ++l) m3[i][k][l] += fa_ * c[i] * c[k] * c[l];
+                }
+        }
+        out[0] = rho;
+        for (int i = 0; i < 3; ++i) out[1 + i] = u[i];
+        const int p2[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+        for (int k = 0; k < 6; ++k) {
+            const int i = p2[k][0], l = p2[k][1];
+            out[4 + k] = m2[i][l] / rho - (i == l ? 1.0 : 0.0);
+        }
+        const int p3[10][3] = {{0, 0, 0}, {0, 0, 1}, {0, 0, 2}, {0, 1, 1}, {0, 1, 2},
+                               {0, 2, 2}, {1, 1, 1}, {1, 1, 2}, {1, 2, 2}, {2, 2, 2}};
+        for (int k = 0; k < 10; ++k) out[10 + k] = m3[p3[k][0]][p3[k][1]][p3[k][2]] / rho;
+    }
+
+    // Coupling-interface loss: sum over the listed nodes of the squared differences between
+    // their 20 Grad coefficients and the targets (20 per node).
+    double interface_loss(const int32_t* nodes, int n, const double* targets) const {
+        double loss = 0.0;
+        for (int k = 0; k < n; ++k) {
+            double m[20];
+            grad_node(nodes[k], m);
+            for (int i = 0; i < 20; ++i) {
+                const double e = m[i] - targets[20 * k + i];
+                loss += e * e;
+            }
+        }
+        return loss;
     }
 };
 

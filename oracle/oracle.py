@@ -96,6 +96,10 @@ def lib():
         L.ora_float_funcs.argtypes = [vp, i64, vp, vp, vp]
         L.ora_grad_G.argtypes = [ctypes.c_int, vp, vp, i64, ctypes.c_int, vp]
         L.ora_gauss_pairs.argtypes = [vp, i64, ctypes.c_int, vp]
+        L.ora_lbm_node_params.argtypes = [vp, vp, vp, i64]
+        L.ora_lbm_grad_node.argtypes = [vp, i64, vp]
+        L.ora_lbm_interface_loss.argtypes = [vp, vp, ctypes.c_int, vp]
+        L.ora_lbm_interface_loss.restype = ctypes.c_double
         _LIB = L
     return _LIB
 
@@ -284,6 +288,26 @@ class Oracle:
     def acc(self):
         return self.get(A_ACC).reshape(-1, 20)
 
+    def set_node_params(self, g=None, tau=None):
+        """Per-node body-force increment g_y and relaxation time tau (None: the scalars)."""
+        if g is None:
+            lib().ora_lbm_node_params(self.h, None, None, 0)
+            return
+        g = np.ascontiguousarray(g, np.float64).reshape(-1)
+        tau = np.ascontiguousarray(tau, np.float64).reshape(-1)
+        if lib().ora_lbm_node_params(self.h, _ptr(g), _ptr(tau), g.size) != 0:
+            raise ValueError("one g and one tau per node")
+
+    def grad_node(self, node):
+        out = np.empty(20, np.float64)
+        lib().ora_lbm_grad_node(self.h, int(node), _ptr(out))
+        return out
+
+    def interface_loss(self, nodes, targets):
+        nodes = np.ascontiguousarray(nodes, np.int32)
+        targets = np.ascontiguousarray(targets, np.float64).reshape(-1)
+        return float(lib().ora_lbm_interface_loss(self.h, _ptr(nodes), len(nodes), _ptr(targets)))
+
     def scalars(self):
         out = np.zeros(4, np.uint64)
         lib().ora_scalars(self.h, _ptr(out))
@@ -297,3 +321,41 @@ class Oracle:
         out = np.zeros(16, np.uint64)
         lib().ora_counters(self.h, _ptr(out))
         return {n: int(out[i]) for i, n in enumerate(COUNTER_NAMES)}
+
+
+def interface_loss_after(cfg, f0, g, tau, nodes, targets, nsteps):
+    """The coupling-interface loss after nsteps LBM steps from f0 with per-node g and tau."""
+    o = Oracle(cfg)
+    o.set_f(f0)
+    o.set_node_params(g, tau)
+    o.lbm_step(nsteps)
+    return o.interface_loss(nodes, targets)
+
+
+def interface_loss_fd_gradient(cfg, f0, g, tau, nodes, targets, nsteps, h=1e-6, which=None):
+    """Central finite differences of the interface loss with respect to g and tau at the
+    nodes `which` (all nodes when None): the oracle's reference gradient."""
+    g = np.asarray(g, np.float64).reshape(-1)
+    tau = np.asarray(tau, np.float64).reshape(-1)
+    idx = np.arange(g.size) if which is None else np.asarray(which)
+    o = Oracle(cfg)
+    f0 = np.asarray(f0).reshape(-1)
+
+    def loss(gg, tt):
+        o.set_f(f0)
+        o.set_node_params(gg, tt)
+        o.lbm_step(nsteps)
+        return o.interface_loss(nodes, targets)
+
+    dg = np.zeros(idx.size)
+    dt = np.zeros(idx.size)
+    for k, n in enumerate(idx):
+        for arr, out, step in ((g, dg, h * max(1e-3, abs(g[n]))), (tau, dt, h * tau[n])):
+            save = arr[n]
+            arr[n] = save + step
+            lp = loss(g, tau)
+            arr[n] = save - step
+            lm = loss(g, tau)
+            arr[n] = save
+            out[k] = (lp - lm) / (2.0 * step)
+    return dg, dt

@@ -678,3 +678,117 @@ def test_grad_G_packed_form_equals_full_tensor_sum(real_bytes, tol):
     xi = np.random.default_rng(2).standard_normal((5000, 3)).astype(np.float32).astype(np.float64)
     gp, gf = O.grad_G(39, f, xi, real_bytes)
     assert np.all(np.abs(gp - gf) <= tol * (1 + np.abs(gf)))
+
+
+# ---------------------------------------------------------------------------------------
+# Differentiated LBM: per-node parameters, the coupling-interface loss, and the oracle's
+# reference gradient (central differences of the FP64 forward)
+
+def _lbm_cfg(**kw):
+    base = dict(ncx=6, ncy=4, ppc=10, lb_ratio=2, real_bytes=8, seed=3, kn=0.3, ma=0.5)
+    base.update(kw)
+    return W.config(**base)
+
+
+def _perturbed_f(cfg, seed):
+    e, w, r = O.lattice(cfg.get("lattice", 39))
+    return W.gen_populations(w, O.derive(cfg)["nnodes"], seed=seed)
+
+
+def test_node_params_equal_to_the_scalars_give_the_plain_step():
+    cfg = _lbm_cfg()
+    f0 = _perturbed_f(cfg, 5)
+    a, b = O.Oracle(cfg), O.Oracle(cfg)
+    a.set_f(f0)
+    b.set_f(f0)
+    n = a.d["nnodes"]
+    b.set_node_params(np.full(n, a.d["g_step"]), np.full(n, a.d["tau"]))
+    a.lbm_step(3)
+    b.lbm_step(3)
+    assert np.array_equal(a.f(), b.f())
+
+
+def test_interface_coefficients_of_dsmc2lb_populations_are_the_central_moments():
+    # DSMC2LB builds populations whose raw moments up to order 3 are those of the particle
+    # sample (quadrature exact to degree 7), so the Grad coefficients of the loss must be the
+    # sample's central moments: rho, u, <cc> - I, <ccc>.
+    rng = np.random.default_rng(4)
+    rho, u = 0.97, np.array([0.05, -0.08, 0.02])
+    A = rng.normal(0, 0.05, (3, 3))
+    P = np.eye(3) + np.outer(u, u) + (A + A.T) / 2
+    B = rng.normal(0, 0.05, (3, 3, 3))
+    Q = sum(np.transpose(B, p) for p in itertools.permutations(range(3))) / 6
+    S, ppc = 19, 40
+    f = O.dsmc2lb_node(39, _sums_from_coeffs(rho, u, P, Q, S, ppc), S, ppc)
+    cfg = _lbm_cfg()
+    o = O.Oracle(cfg)
+    e, w, r = O.lattice(39)
+    full = np.tile(w[:, None], (1, o.d["nnodes"]))
+    full[:, 7] = f
+    o.set_f(full)
+    m = o.grad_node(7)
+    C2 = P - np.outer(u, u) - np.eye(3)
+    C3 = (Q - np.einsum("i,jk->ijk", u, P) - np.einsum("j,ik->ijk", u, P)
+          - np.einsum("k,ij->ijk", u, P) + 2 * np.einsum("i,j,k->ijk", u, u, u))
+    p2 = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+    p3 = [(0, 0, 0), (0, 0, 1), (0, 0, 2), (0, 1, 1), (0, 1, 2), (0, 2, 2), (1, 1, 1),
+          (1, 1, 2), (1, 2, 2), (2, 2, 2)]
+    assert m[0] == pytest.approx(rho, rel=1e-13)
+    assert np.allclose(m[1:4], u, atol=1e-13)
+    assert np.allclose(m[4:10], [C2[i, j] for i, j in p2], atol=1e-12)
+    assert np.allclose(m[10:20], [C3[i, j, k] for i, j, k in p3], atol=1e-12)
+    # at the lattice equilibrium at rest every coefficient but rho vanishes
+    o.set_f(np.tile(w[:, None], (1, o.d["nnodes"])))
+    m0 = o.grad_node(3)
+    assert m0[0] == pytest.approx(1.0, rel=1e-14)
+    assert np.abs(m0[1:]).max() < 1e-14
+
+
+def test_interface_loss_gradient_vanishes_outside_the_light_cone():
+    # f_T at a node depends on the parameters within MAXV (= 3) rows per step, walls included
+    # (a wall density sums rows y -+ 3), so after T steps rows farther than 3 T are exactly
+    # outside: the central differences there are exactly zero.
+    cfg = _lbm_cfg(ncx=6, ncy=10)  # 12 x 20 nodes
+    d = O.derive(cfg)
+    nx, ny, n = d["nx"], d["ny"], d["nnodes"]
+    rng = np.random.default_rng(9)
+    g = d["g_step"] * (1 + 0.3 * rng.standard_normal(n))
+    tau = d["tau"] * (1 + 0.1 * rng.standard_normal(n))
+    f0 = _perturbed_f(cfg, 6)
+    node = 10 * nx + 3
+    o = O.Oracle(cfg)
+    o.set_f(f0)
+    o.set_node_params(g, tau)
+    o.lbm_step(2)
+    targets = o.grad_node(node) + 0.01 * rng.standard_normal(20)
+    far = [y * nx + x for y in (0, 1, 2, 3, 17, 18, 19) for x in (0, 3, 11)]
+    near = [node, node + 1, 9 * nx + 3, 10 * nx + 0]
+    dg, dt = O.interface_loss_fd_gradient(cfg, f0, g, tau, [node], targets, 2, which=far + near)
+    assert np.all(dg[:len(far)] == 0.0) and np.all(dt[:len(far)] == 0.0)
+    assert np.all(np.abs(dg[len(far):]) > 0) and np.abs(dt[len(far)]) > 0
+
+
+def test_interface_loss_gradient_of_one_step_at_tau_one():
+    # At tau = 1 (om = 0, of = 1/2) one step gives j' = j + rho g exactly (the quadrature
+    # reproduces the first moment of the series), so u'_y = j_y / rho + g and du'_y/dg = 1.
+    # With every target equal to the reached value except u_y (shifted by delta),
+    # L = delta^2 and dL/dg at the node is 2 delta.
+    cfg = _lbm_cfg()
+    d = O.derive(cfg)
+    n = d["nnodes"]
+    rng = np.random.default_rng(12)
+    g = d["g_step"] * (1 + 0.2 * rng.standard_normal(n))
+    tau = np.ones(n)
+    f0 = _perturbed_f(cfg, 8)
+    node = 2 * d["nx"] + 5
+    o = O.Oracle(cfg)
+    o.set_f(f0)
+    o.set_node_params(g, tau)
+    o.lbm_step(1)
+    targets = o.grad_node(node)
+    delta = 0.01
+    targets[2] -= delta
+    assert O.interface_loss_after(cfg, f0, g, tau, [node], targets, 1) == pytest.approx(
+        delta * delta, rel=1e-12)
+    dg, dt = O.interface_loss_fd_gradient(cfg, f0, g, tau, [node], targets, 1, which=[node])
+    assert dg[0] == pytest.approx(2 * delta, rel=1e-6)
