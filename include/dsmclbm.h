@@ -211,6 +211,39 @@ hyb_status map_lbm_to_dsmc(hyb_ctx* ctx, const int32_t* dev_cells, int32_t n);
 #define HYB_NOALLOC_MAX_CELLS 4096
 hyb_status map_lbm_to_dsmc_noalloc(hyb_ctx* ctx, const int32_t* dev_cells, int32_t n);
 
+/* ---- Differentiated LBM (an extension beyond the paper) --------------------------------
+ * The LB stream-collide of Sec. 2 (regularised BGK, kinetic walls, body force; tau from
+ * Eq. tau) with a force increment g_y and a relaxation time tau per node, its adjoint, and a
+ * coupling-interface loss: at each listed node, the 20 Grad coefficients of its populations
+ * (rho; u = sum f xi / rho; a2 = sum f c c / rho - I and a3 = sum f c c c / rho with
+ * c = xi - u, the comoving coefficients of Table 1; packed xx xy xz yy yz zz and xxx xxy xxz
+ * xyy xyz xzz yyy yyz yzz zzz) against 20 targets, summed as squares. Populations and their
+ * adjoints use the layout of the context's populations: [q][y][x], q < Q, nx * ny nodes,
+ * state precision (real_bytes). g, tau and their gradients are one value per node in the
+ * state precision. All buffers are device memory owned by the caller; every call is
+ * enqueued on the context's stream; invalid pointers or sizes return HYB_EINVAL without
+ * launching; the context's own populations are not touched. */
+
+/* One LB step f_dst = LB(f_src) with per-node g (force increment per step along the
+ * streamwise axis) and tau. f_src and f_dst must differ. */
+hyb_status lbm_step_nodes(hyb_ctx* ctx, const void* f_src, void* f_dst, const void* g_node,
+                          const void* tau_node);
+
+/* Interface loss of the populations f at the n listed nodes (node index y * nx + x) against
+ * targets (n * 20 values): adds the loss to *dev_loss (one double, device) and adds dL/df
+ * at the listed nodes to lam (populations-shaped; other entries untouched). A node index out
+ * of range is skipped and raises HYB_ST_BAD_INPUT in the sticky status. */
+hyb_status lbm_interface_loss(hyb_ctx* ctx, const void* f, const int32_t* dev_nodes, int32_t n,
+                              const void* dev_targets, double* dev_loss, void* lam);
+
+/* One step of the adjoint: with f the populations at step t and lam_next = dL/df_{t+1},
+ * writes lam = dL/df_t (every entry) and adds dL/dg and dL/dtau of this step to grad_g and
+ * grad_tau. wall is a scratch of 2 * ny values that must be zero before the first call; it
+ * is left zero. lam and lam_next must differ. */
+hyb_status lbm_adjoint_step(hyb_ctx* ctx, const void* f, const void* lam_next, void* lam,
+                            const void* g_node, const void* tau_node, void* grad_g,
+                            void* grad_tau, void* wall);
+
 /* One or more hybrid steps: dsmc_step(1), map_dsmc_to_lbm, lbm_step(1), map_lbm_to_dsmc.
  * n_nodes or n_cells may be 0 to skip a mapping. With use_graph != 0 each step is replayed
  * from a CUDA graph captured on first use (one per ping-pong parity; recaptured if the

@@ -51,7 +51,7 @@ class HybLayout(ctypes.Structure):
 
 EXPORTS = ["hyb_derive", "hyb_layout_compute", "hyb_lattice", "hyb_status_string", "dsmc_init",
            "dsmc_step", "lbm_step", "sample_moments", "map_dsmc_to_lbm", "map_lbm_to_dsmc",
-           "map_lbm_to_dsmc_noalloc",
+           "map_lbm_to_dsmc_noalloc", "lbm_step_nodes", "lbm_interface_loss", "lbm_adjoint_step",
            "hyb_hybrid_step", "hyb_batch_layout", "hyb_batch_init", "hyb_batch_replica",
            "hyb_batch_hybrid_step", "hyb_batch_set_blocks", "hyb_batch_tune",
            "hyb_batch_last_error", "hyb_batch_destroy", "hyb_current", "hyb_sync_status", "hyb_read_counters",
@@ -96,6 +96,9 @@ def lib():
     L.map_dsmc_to_lbm.argtypes = [_vp, _vp, _i32]
     L.map_lbm_to_dsmc.argtypes = [_vp, _vp, _i32]
     L.map_lbm_to_dsmc_noalloc.argtypes = [_vp, _vp, _i32]
+    L.lbm_step_nodes.argtypes = [_vp, _vp, _vp, _vp, _vp]
+    L.lbm_interface_loss.argtypes = [_vp, _vp, _vp, _i32, _vp, _vp, _vp]
+    L.lbm_adjoint_step.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
     L.hyb_hybrid_step.argtypes = [_vp, _vp, _i32, _vp, _i32, _i32, _i32]
     L.hyb_batch_layout.argtypes = [_vp, _i32, _vp]
     L.hyb_batch_init.argtypes = [_vp, _i32, _vp, _u64, _vp, P(_vp)]
@@ -251,6 +254,55 @@ class Hybrid:
         NOALLOC_MAX_CELLS cells per call)."""
         self._inputs(cells)
         _check(lib().map_lbm_to_dsmc_noalloc(self.ctx, cells.data_ptr(), cells.numel()), self.ctx)
+
+    # -- differentiated LBM (per-node g and tau, adjoint, interface loss) ----------------
+    def _pop_shape(self):
+        return (int(self.d["q"]), int(self.d["ny"]), int(self.d["nx"]))
+
+    def _check_pop(self, *ts):
+        for t in ts:
+            if tuple(t.shape) != self._pop_shape() or t.dtype != self.real or not t.is_contiguous():
+                raise ValueError("populations must be contiguous %s %s" % (self._pop_shape(), self.real))
+
+    def _check_node(self, *ts):
+        n = int(self.d["nnodes"])
+        for t in ts:
+            if t.numel() != n or t.dtype != self.real or not t.is_contiguous():
+                raise ValueError("per-node arrays must be contiguous, %d values of %s" % (n, self.real))
+
+    def lbm_step_nodes(self, f_src, f_dst, g, tau):
+        """One LB step f_dst = LB(f_src) with per-node force increment g and relaxation time
+        tau (the context's own populations are not touched)."""
+        self._check_pop(f_src, f_dst)
+        self._check_node(g, tau)
+        self._inputs(f_src, f_dst, g, tau)
+        _check(lib().lbm_step_nodes(self.ctx, f_src.data_ptr(), f_dst.data_ptr(), g.data_ptr(),
+                                    tau.data_ptr()), self.ctx)
+
+    def lbm_interface_loss(self, f, nodes, targets, loss, lam):
+        """Adds the interface loss of f at `nodes` (int32) against `targets` (n x 20) to
+        `loss` (one float64) and dL/df at those nodes to `lam`."""
+        self._check_pop(f, lam)
+        if targets.dtype != self.real or targets.numel() != 20 * nodes.numel():
+            raise ValueError("20 targets per node in the state precision")
+        if nodes.dtype != self.torch.int32 or loss.dtype != self.torch.float64:
+            raise ValueError("int32 nodes and a float64 loss")
+        self._inputs(f, nodes, targets, loss, lam)
+        _check(lib().lbm_interface_loss(self.ctx, f.data_ptr(), nodes.data_ptr(), nodes.numel(),
+                                        targets.data_ptr(), loss.data_ptr(), lam.data_ptr()),
+               self.ctx)
+
+    def lbm_adjoint_step(self, f, lam_next, lam, g, tau, grad_g, grad_tau, wall):
+        """lam = dL/df_t from f_t and lam_next = dL/df_{t+1}; adds this step's dL/dg and
+        dL/dtau to grad_g and grad_tau. wall: 2 ny zeros, left zero."""
+        self._check_pop(f, lam_next, lam)
+        self._check_node(g, tau, grad_g, grad_tau)
+        if wall.numel() != 2 * int(self.d["ny"]) or wall.dtype != self.real:
+            raise ValueError("wall scratch: 2 ny values in the state precision")
+        self._inputs(f, lam_next, lam, g, tau, grad_g, grad_tau, wall)
+        _check(lib().lbm_adjoint_step(self.ctx, f.data_ptr(), lam_next.data_ptr(), lam.data_ptr(),
+                                      g.data_ptr(), tau.data_ptr(), grad_g.data_ptr(),
+                                      grad_tau.data_ptr(), wall.data_ptr()), self.ctx)
 
     def hybrid_step(self, nodes=None, cells=None, nsteps=1, use_graph=True, order_inputs=True):
         """`order_inputs=False` skips the stream ordering of `nodes`/`cells` (for callers
@@ -489,3 +541,88 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def interface_loss(h, g, tau, f0, nodes, targets, nsteps, ckpt_every=100):
+    """Coupling-interface loss after `nsteps` LB steps from populations f0 with per-node force
+    increment g and relaxation time tau (tensors of the context's shape and precision), as a
+    differentiable function of g, tau and f0. The backward pass is the library's adjoint
+    step, run over the steps in reverse; the states are recomputed segment by segment from
+    checkpoints stored every `ckpt_every` steps."""
+    return _InterfaceLoss.apply(g, tau, f0, h, nodes, targets, int(nsteps), int(ckpt_every))
+
+
+def _lb_forward(h, g, tau, f0, nsteps, ckpt_every):
+    """f_T and the checkpoints f_0, f_K, f_2K, ... (K = ckpt_every)."""
+    a = f0.detach().clone()
+    b = h.torch.empty_like(a)
+    ckpts = [a.clone()]
+    for t in range(nsteps):
+        h.lbm_step_nodes(a, b, g, tau)
+        a, b = b, a
+        if (t + 1) % ckpt_every == 0 and t + 1 < nsteps:
+            ckpts.append(a.clone())
+    return a, ckpts
+
+
+def _make_interface_loss():
+    import torch
+
+    class InterfaceLoss(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, g, tau, f0, h, nodes, targets, nsteps, ckpt_every):
+            g, tau = g.detach().contiguous(), tau.detach().contiguous()
+            with torch.cuda.stream(h.stream):
+                fT, ckpts = _lb_forward(h, g, tau, f0, nsteps, ckpt_every)
+                loss = torch.zeros(1, dtype=torch.float64, device=f0.device)
+                lam = torch.zeros_like(fT)
+                h.lbm_interface_loss(fT, nodes, targets, loss, lam)
+            torch.cuda.current_stream(f0.device).wait_stream(h.stream)
+            ctx.h = h
+            ctx.nsteps, ctx.ckpt_every = nsteps, ckpt_every
+            ctx.save_for_backward(g, tau, lam, *ckpts)
+            return loss[0]
+
+        @staticmethod
+        def backward(ctx, gout):
+            h = ctx.h
+            g, tau, lam_T, *ckpts = ctx.saved_tensors
+            K, T = ctx.ckpt_every, ctx.nsteps
+            h.stream.wait_stream(torch.cuda.current_stream(g.device))
+            with torch.cuda.stream(h.stream):
+                grad_g = torch.zeros_like(g)
+                grad_tau = torch.zeros_like(tau)
+                wall = torch.zeros(2 * int(h.d["ny"]), dtype=g.dtype, device=g.device)
+                lam_next = lam_T.clone()
+                lam = torch.empty_like(lam_next)
+                for s in reversed(range(len(ckpts))):
+                    t0, t1 = s * K, min(T, (s + 1) * K)
+                    states = [ckpts[s]]
+                    for _ in range(t0, t1 - 1):
+                        nxt = torch.empty_like(states[-1])
+                        h.lbm_step_nodes(states[-1], nxt, g, tau)
+                        states.append(nxt)
+                    for t in reversed(range(t0, t1)):
+                        h.lbm_adjoint_step(states[t - t0], lam_next, lam, g, tau, grad_g,
+                                           grad_tau, wall)
+                        lam_next, lam = lam, lam_next
+                gg = grad_g * gout.to(g.dtype)
+                gt = grad_tau * gout.to(g.dtype)
+                gf = lam_next * gout.to(g.dtype)
+            torch.cuda.current_stream(g.device).wait_stream(h.stream)
+            return gg, gt, gf, None, None, None, None, None
+
+    return InterfaceLoss
+
+
+class _Lazy:
+    def __init__(self, make):
+        self._make, self._cls = make, None
+
+    def apply(self, *args):
+        if self._cls is None:
+            self._cls = self._make()
+        return self._cls.apply(*args)
+
+
+_InterfaceLoss = _Lazy(_make_interface_loss)

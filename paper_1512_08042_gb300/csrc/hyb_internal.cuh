@@ -117,6 +117,27 @@ struct LbmArgs {
     int32_t nx, ny;
     int64_t nnodes;
     Real om, of, g_step;  // 1 - 1/tau, 1 - 1/(2 tau), force increment per step
+    // per-node force increment and relaxation time (differentiated LBM); unused by the
+    // plain step
+    const Real* g_node;
+    const Real* tau_node;
+};
+
+// One step of the adjoint of the LBM with per-node parameters: lam_next = dL/df_{t+1} in,
+// lam = dL/df_t out, the parameter gradients accumulated; wall = 2 ny adjoint wall
+// densities (left rows, then right rows), zero on entry and left zero.
+template <typename Real>
+struct LbmAdjArgs {
+    const Real* f;         // populations at t
+    const Real* lam_next;  // adjoint at t + 1
+    Real* lam;             // adjoint at t
+    const Real* g_node;
+    const Real* tau_node;
+    Real* grad_g;
+    Real* grad_tau;
+    Real* wall;
+    int32_t nx, ny;
+    int64_t nnodes;
 };
 
 template <typename Real>
@@ -425,6 +446,12 @@ struct Ctx;
 cudaError_t launch_init(Ctx& c);
 cudaError_t launch_dsmc_step(Ctx& c);
 cudaError_t launch_lbm_step(Ctx& c);
+cudaError_t launch_lbm_step_nodes(Ctx& c, const void* f_src, void* f_dst, const void* g, const void* tau);
+cudaError_t launch_lbm_adjoint_step(Ctx& c, const void* f, const void* lam_next, void* lam,
+                                    const void* g, const void* tau, void* grad_g, void* grad_tau,
+                                    void* wall);
+cudaError_t launch_interface_loss(Ctx& c, const void* f, const int32_t* nodes, int32_t n,
+                                  const void* targets, double* loss, void* lam);
 cudaError_t launch_map_d2l(Ctx& c, const int32_t* nodes, int32_t n);
 cudaError_t launch_map_l2d(Ctx& c, const int32_t* cells, int32_t n);
 cudaError_t launch_map_l2d_noalloc(Ctx& c, const int32_t* cells, int32_t n);

@@ -63,24 +63,19 @@ __device__ __forceinline__ int wrap_y(int v, int ny) {
     return v;
 }
 
-// One node of one context.
+// Pull streaming of node (x, y): fs[q] = f[q](x - e_q), periodic in y; sources behind a wall
+// take the wall Maxwellian with the wall density of the row (the mass leaving through that
+// wall, re-emitted at rest).
 template <typename Real, class LAT>
-__device__ __forceinline__ void lbm_node(const LbmArgs<Real>& a, const int64_t node) {
+__device__ __forceinline__ void pull_node(const Real* __restrict__ src, int x, int y, int nx, int ny,
+                                          int64_t nn, Real (&fs)[LAT::Q]) {
     constexpr int Q = LAT::Q;
-    constexpr double R = lat_r<LAT>();
-    const int nx = a.nx, ny = a.ny;
-    const int x = (int)(node % nx), y = (int)(node / nx);
-    const int64_t nn = a.nnodes;
-    const Real* __restrict__ src = a.src;
-
     // Row offsets y' * nx of the pull sources y' = y - ey (periodic), ey = -MAXV..MAXV.
     constexpr int MV = LAT::MAXV;
     int rowoff[2 * MV + 1];
 #pragma unroll
     for (int i = 0; i < 2 * MV + 1; ++i) rowoff[i] = wrap_y(y - (i - MV), ny) * nx;
 
-    // Wall densities for nodes whose pull reaches through a wall: the mass leaving through
-    // the wall on this row, re-emitted by the wall Maxwellian at rest.
     Real rhoL = (Real)0, rhoR = (Real)0;
     if (x < MV || x >= nx - MV) {
         Real ml = (Real)0, mr = (Real)0;
@@ -102,8 +97,6 @@ __device__ __forceinline__ void lbm_node(const LbmArgs<Real>& a, const int64_t n
         rhoR = mr * (Real)inv_flux;
     }
 
-    // pull streaming; sources behind a wall take the wall Maxwellian
-    Real fs[Q];
     static_for<Q>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
         constexpr int ex = E<LAT>(q, 0), ey = E<LAT>(q, 1);
@@ -117,11 +110,21 @@ __device__ __forceinline__ void lbm_node(const LbmArgs<Real>& a, const int64_t n
         else
             fs[q] = sq[off];
     });
+}
 
-    // moments, from the pair sums s and differences d
-    Real rho = fs[0], jx = 0, jy = 0, jz = 0;
-    Real pxx = 0, pxy = 0, pxz = 0, pyy = 0, pyz = 0, pzz = 0;
-    Real q3[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+// Raw moments of the streamed populations from the pair sums s and differences d:
+// rho, j, P (xx xy xz yy yz zz) and, for order 3, Q3 (xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz).
+template <typename Real, class LAT>
+__device__ __forceinline__ void node_moments(const Real (&fs)[LAT::Q], Real& rho, Real& jx, Real& jy,
+                                             Real& jz, Real (&pm)[6], Real (&q3)[10]) {
+    constexpr int Q = LAT::Q;
+    constexpr double R = lat_r<LAT>();
+    rho = fs[0];
+    jx = jy = jz = (Real)0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) pm[k] = (Real)0;
+#pragma unroll
+    for (int k = 0; k < 10; ++k) q3[k] = (Real)0;
     static_for<Q>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
         constexpr int p = opp<LAT>(q);
@@ -132,12 +135,12 @@ __device__ __forceinline__ void lbm_node(const LbmArgs<Real>& a, const int64_t n
             if constexpr (ex != 0) jx += df * (Real)(R * ex);
             if constexpr (ey != 0) jy += df * (Real)(R * ey);
             if constexpr (ez != 0) jz += df * (Real)(R * ez);
-            if constexpr (ex != 0) pxx += sm * (Real)(R * R * ex * ex);
-            if constexpr (ex * ey != 0) pxy += sm * (Real)(R * R * ex * ey);
-            if constexpr (ex * ez != 0) pxz += sm * (Real)(R * R * ex * ez);
-            if constexpr (ey != 0) pyy += sm * (Real)(R * R * ey * ey);
-            if constexpr (ey * ez != 0) pyz += sm * (Real)(R * R * ey * ez);
-            if constexpr (ez != 0) pzz += sm * (Real)(R * R * ez * ez);
+            if constexpr (ex != 0) pm[0] += sm * (Real)(R * R * ex * ex);
+            if constexpr (ex * ey != 0) pm[1] += sm * (Real)(R * R * ex * ey);
+            if constexpr (ex * ez != 0) pm[2] += sm * (Real)(R * R * ex * ez);
+            if constexpr (ey != 0) pm[3] += sm * (Real)(R * R * ey * ey);
+            if constexpr (ey * ez != 0) pm[4] += sm * (Real)(R * R * ey * ez);
+            if constexpr (ez != 0) pm[5] += sm * (Real)(R * R * ez * ez);
             if constexpr (LAT::ORDER >= 3) {
                 constexpr double R3 = R * R * R;
                 if constexpr (ex != 0) q3[0] += df * (Real)(R3 * ex * ex * ex);
@@ -153,10 +156,31 @@ __device__ __forceinline__ void lbm_node(const LbmArgs<Real>& a, const int64_t n
             }
         }
     });
+}
 
-    const Real gy = a.g_step;
-    const Real om = a.om;
-    const Real of = a.of;
+// One node of one context; PARAM: the force increment and relaxation time of the node come
+// from the per-node arrays.
+template <typename Real, class LAT, bool PARAM>
+__device__ __forceinline__ void lbm_node(const LbmArgs<Real>& a, const int64_t node) {
+    constexpr int Q = LAT::Q;
+    constexpr double R = lat_r<LAT>();
+    const int nx = a.nx, ny = a.ny;
+    const int x = (int)(node % nx), y = (int)(node / nx);
+    const int64_t nn = a.nnodes;
+
+    Real fs[Q];
+    pull_node<Real, LAT>(a.src, x, y, nx, ny, nn, fs);
+    Real rho, jx, jy, jz, pm[6], q3[10];
+    node_moments<Real, LAT>(fs, rho, jx, jy, jz, pm, q3);
+    const Real pxx = pm[0], pxy = pm[1], pxz = pm[2], pyy = pm[3], pyz = pm[4], pzz = pm[5];
+
+    Real gy = a.g_step, om = a.om, of = a.of;
+    if constexpr (PARAM) {
+        gy = a.g_node[node];
+        const Real tau = a.tau_node[node];
+        om = (Real)1 - (Real)1 / tau;
+        of = (Real)1 - (Real)0.5 / tau;
+    }
     const Real inv_rho = (Real)1 / rho;
     const Real ux = jx * inv_rho, uy = (jy + (Real)0.5 * rho * gy) * inv_rho, uz = jz * inv_rho;
     const Real a1y = (Real)-0.5 * rho * gy;  // H1 part of f_neq
@@ -253,10 +277,377 @@ __global__ void __launch_bounds__(128) k_lbm(Launch<LbmArgs<Real>> L) {
     if (u >= L.total) return;
     if constexpr (BATCH) {
         const int r = replica_of(L.pre, L.nrep, u);
-        lbm_node<Real, LAT>(L.tab[r], u - L.pre[r]);
+        lbm_node<Real, LAT, false>(L.tab[r], u - L.pre[r]);
     } else {
-        lbm_node<Real, LAT>(L.one, u);
+        lbm_node<Real, LAT, false>(L.one, u);
     }
+}
+
+// One thread per node, with per-node force increment and relaxation time.
+template <typename Real, class LAT>
+__global__ void __launch_bounds__(128) k_lbm_param(LbmArgs<Real> a) {
+    const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (u < a.nnodes) lbm_node<Real, LAT, true>(a, u);
+}
+
+// ---------------------------------------------------------------------------------------
+// Adjoint of one LBM step with per-node force increment g and relaxation time tau. With
+// f_{t+1}(x) = C(fs(x); g_x, tau_x) and fs = the pull streaming (with the wall densities) of
+// f_t, the adjoint lam_t = dL/df_t is P^T mu, mu(x) = (dC/dfs)^T lam_{t+1}(x), and
+// dL/dg_x, dL/dtau_x gather (dC/dg)^T lam_{t+1}(x) and (dC/dtau)^T lam_{t+1}(x) over the
+// steps. mu is formed in reverse through the same intermediates as the forward node:
+// populations -> combined coefficients (A0, A1, A2, B3) -> (rho, u, P, Q3, g, om, of) ->
+// raw moments -> streamed populations. P^T is a permutation: mu_q(x) goes to
+// lam_t[q](x - e_q), except for sources behind a wall, whose mu feeds the wall density of
+// the row (summed in `wall` and spread over the populations leaving through that wall by
+// k_lbm_adj_wall).
+
+// Third-order terms of B3[k] (k = xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz):
+//   B3[k] = rho M_k(u) + om (Q3_k - rho (M_k + L_k(u)) - kap_k a1y) + of rho g f_k(u),
+// M_k = u_i u_j u_k, L_k the sym(u I) terms, kap_k the sym(a1 I) multiplicity of a1y,
+// f_k the force terms of sym(g u u) / rho g. Returns M, L, f and their u-gradients.
+template <typename Real>
+__device__ __forceinline__ void b3_terms(int k, Real ux, Real uy, Real uz, Real& M, Real (&dM)[3],
+                                         Real& Lk, Real (&dL)[3], Real& kap, Real& fk,
+                                         Real (&df)[3]) {
+    constexpr int I[10][3] = {{0, 0, 0}, {0, 0, 1}, {0, 0, 2}, {0, 1, 1}, {0, 1, 2},
+                              {0, 2, 2}, {1, 1, 1}, {1, 1, 2}, {1, 2, 2}, {2, 2, 2}};
+    const Real u[3] = {ux, uy, uz};
+    const int i = I[k][0], j = I[k][1], l = I[k][2];
+    M = u[i] * u[j] * u[l];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        Real d = (Real)0;
+        if (i == c) d += u[j] * u[l];
+        if (j == c) d += u[i] * u[l];
+        if (l == c) d += u[i] * u[j];
+        dM[c] = d;
+        dL[c] = (Real)0;
+        df[c] = (Real)0;
+    }
+    // L: xxx 3ux, xxy uy, xxz uz, xyy ux, xyz 0, xzz ux, yyy 3uy, yyz uz, yzz uy, zzz 3uz
+    constexpr int lc[10] = {0, 1, 2, 0, -1, 0, 1, 2, 1, 2};
+    constexpr int lm[10] = {3, 1, 1, 1, 0, 1, 3, 1, 1, 3};
+    Lk = lc[k] >= 0 ? (Real)lm[k] * u[lc[k]] : (Real)0;
+    if (lc[k] >= 0) dL[lc[k]] = (Real)lm[k];
+    constexpr int kp[10] = {0, 1, 0, 0, 0, 0, 3, 0, 1, 0};
+    kap = (Real)kp[k];
+    // f: xxy ux^2, xyy 2 ux uy, xyz ux uz, yyy 3 uy^2, yyz 2 uy uz, yzz uz^2
+    fk = (Real)0;
+    switch (k) {
+        case 1: fk = ux * ux; df[0] = (Real)2 * ux; break;
+        case 3: fk = (Real)2 * ux * uy; df[0] = (Real)2 * uy; df[1] = (Real)2 * ux; break;
+        case 4: fk = ux * uz; df[0] = uz; df[2] = ux; break;
+        case 6: fk = (Real)3 * uy * uy; df[1] = (Real)6 * uy; break;
+        case 7: fk = (Real)2 * uy * uz; df[1] = (Real)2 * uz; df[2] = (Real)2 * uy; break;
+        case 8: fk = uz * uz; df[2] = (Real)2 * uz; break;
+        default: break;
+    }
+}
+
+template <typename Real, class LAT>
+__device__ __forceinline__ void lbm_adjoint_node(const LbmAdjArgs<Real>& a, const int64_t node) {
+    constexpr int Q = LAT::Q;
+    constexpr double R = lat_r<LAT>();
+    const int nx = a.nx, ny = a.ny;
+    const int x = (int)(node % nx), y = (int)(node / nx);
+    const int64_t nn = a.nnodes;
+
+    // forward intermediates of the node at t
+    Real fs[Q];
+    pull_node<Real, LAT>(a.f, x, y, nx, ny, nn, fs);
+    Real rho, jx, jy, jz, pm[6], q3[10];
+    node_moments<Real, LAT>(fs, rho, jx, jy, jz, pm, q3);
+    const Real gy = a.g_node[node];
+    const Real tau = a.tau_node[node];
+    const Real om = (Real)1 - (Real)1 / tau, of = (Real)1 - (Real)0.5 / tau;
+    const Real inv_rho = (Real)1 / rho;
+    const Real ux = jx * inv_rho, uy = (jy + (Real)0.5 * rho * gy) * inv_rho, uz = jz * inv_rho;
+    const Real a1y = (Real)-0.5 * rho * gy, rg = rho * gy;
+    const Real om1 = (Real)1 - om;
+
+    // adjoints of the combined coefficients from lam_{t+1}(x): f'(+-xi) = w (E +- O)
+    const Real* __restrict__ ln = a.lam_next + node;
+    Real E0b = (Real)W<LAT>(0) * ln[0];
+    Real A1b[3] = {0, 0, 0}, A2b[6] = {0, 0, 0, 0, 0, 0};
+    Real B3b[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0}, t3b[3] = {0, 0, 0};
+    static_for<Q>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        constexpr int p = opp<LAT>(q);
+        if constexpr (q != 0 && q < p) {
+            constexpr int ex = E<LAT>(q, 0), ey = E<LAT>(q, 1), ez = E<LAT>(q, 2);
+            constexpr double X = R * ex, Y = R * ey, Z = R * ez;
+            constexpr double wq = W<LAT>(q);
+            const Real lq = ln[(int64_t)q * nn], lp = ln[(int64_t)p * nn];
+            const Real evb = (Real)wq * (lq + lp), odb = (Real)wq * (lq - lp);
+            E0b += evb;
+            if constexpr (ex != 0) A2b[0] += (Real)(0.5 * X * X) * evb;
+            if constexpr (ex * ey != 0) A2b[1] += (Real)(X * Y) * evb;
+            if constexpr (ex * ez != 0) A2b[2] += (Real)(X * Z) * evb;
+            if constexpr (ey != 0) A2b[3] += (Real)(0.5 * Y * Y) * evb;
+            if constexpr (ey * ez != 0) A2b[4] += (Real)(Y * Z) * evb;
+            if constexpr (ez != 0) A2b[5] += (Real)(0.5 * Z * Z) * evb;
+            if constexpr (ex != 0) A1b[0] += (Real)X * odb;
+            if constexpr (ey != 0) A1b[1] += (Real)Y * odb;
+            if constexpr (ez != 0) A1b[2] += (Real)Z * odb;
+            if constexpr (LAT::ORDER >= 3) {
+                constexpr double s6 = 1.0 / 6.0;
+                if constexpr (ex != 0) {
+                    B3b[0] += (Real)(s6 * X * X * X) * odb;
+                    t3b[0] -= (Real)(0.5 * X) * odb;
+                }
+                if constexpr (ex * ey != 0) B3b[1] += (Real)(0.5 * X * X * Y) * odb;
+                if constexpr (ex * ez != 0) B3b[2] += (Real)(0.5 * X * X * Z) * odb;
+                if constexpr (ex * ey != 0) B3b[3] += (Real)(0.5 * X * Y * Y) * odb;
+                if constexpr (ex * ey * ez != 0) B3b[4] += (Real)(X * Y * Z) * odb;
+                if constexpr (ex * ez != 0) B3b[5] += (Real)(0.5 * X * Z * Z) * odb;
+                if constexpr (ey != 0) {
+                    B3b[6] += (Real)(s6 * Y * Y * Y) * odb;
+                    t3b[1] -= (Real)(0.5 * Y) * odb;
+                }
+                if constexpr (ey * ez != 0) B3b[7] += (Real)(0.5 * Y * Y * Z) * odb;
+                if constexpr (ey * ez != 0) B3b[8] += (Real)(0.5 * Y * Z * Z) * odb;
+                if constexpr (ez != 0) {
+                    B3b[9] += (Real)(s6 * Z * Z * Z) * odb;
+                    t3b[2] -= (Real)(0.5 * Z) * odb;
+                }
+            }
+        }
+    });
+    // t3 = trace terms of B3; E0 = A0 - tr(A2) / 2, A0 = rho
+    B3b[0] += t3b[0], B3b[3] += t3b[0], B3b[5] += t3b[0];
+    B3b[1] += t3b[1], B3b[6] += t3b[1], B3b[8] += t3b[1];
+    B3b[2] += t3b[2], B3b[7] += t3b[2], B3b[9] += t3b[2];
+    Real rhob = E0b;
+    A2b[0] -= (Real)0.5 * E0b, A2b[3] -= (Real)0.5 * E0b, A2b[5] -= (Real)0.5 * E0b;
+
+    // coefficients -> (rho, u, P, Q3, a1y, rg, om, of)
+    Real ub[3] = {0, 0, 0}, pb[6], qb[10];
+    Real omb = 0, ofb = 0, a1yb = 0, rgb = 0;
+    // A1 = (rho ux, rho uy + om a1y + of rg, rho uz)
+    rhob += A1b[0] * ux + A1b[1] * uy + A1b[2] * uz;
+    ub[0] += A1b[0] * rho, ub[1] += A1b[1] * rho, ub[2] += A1b[2] * rho;
+    omb += A1b[1] * a1y, a1yb += A1b[1] * om, ofb += A1b[1] * rg, rgb += A1b[1] * of;
+    // A2_ii = rho u_i^2 + om (P_ii - rho (u_i^2 + 1)) [+ 2 of rg uy for yy]
+    // A2_ij = rho u_i u_j + om (P_ij - rho u_i u_j) [+ of rg u_other for xy, yz]
+    {
+        const Real u[3] = {ux, uy, uz};
+        constexpr int I[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const int i = I[k][0], j = I[k][1];
+            const Real b = A2b[k];
+            const Real uu = u[i] * u[j];
+            const Real diag = i == j ? (Real)1 : (Real)0;
+            rhob += b * (uu - om * (uu + diag));
+            ub[i] += b * rho * u[j] * om1;
+            ub[j] += b * rho * u[i] * om1;
+            pb[k] = b * om;
+            omb += b * (pm[k] - rho * (uu + diag));
+        }
+        // force terms: yy 2 of rg uy, xy of rg ux, yz of rg uz
+        ub[1] += A2b[3] * (Real)2 * of * rg;
+        ofb += A2b[3] * (Real)2 * rg * uy, rgb += A2b[3] * (Real)2 * of * uy;
+        ub[0] += A2b[1] * of * rg;
+        ofb += A2b[1] * rg * ux, rgb += A2b[1] * of * ux;
+        ub[2] += A2b[4] * of * rg;
+        ofb += A2b[4] * rg * uz, rgb += A2b[4] * of * uz;
+    }
+#pragma unroll
+    for (int k = 0; k < 10; ++k) qb[k] = (Real)0;
+    if constexpr (LAT::ORDER >= 3) {
+#pragma unroll
+        for (int k = 0; k < 10; ++k) {
+            Real M, dM[3], Lk, dL[3], kap, fk, df[3];
+            b3_terms<Real>(k, ux, uy, uz, M, dM, Lk, dL, kap, fk, df);
+            const Real b = B3b[k];
+            rhob += b * (om1 * M - om * Lk);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ub[c] += b * (om1 * rho * dM[c] - om * rho * dL[c] + of * rg * df[c]);
+            qb[k] = b * om;
+            omb += b * (q3[k] - rho * (M + Lk) - kap * a1y);
+            a1yb -= b * om * kap;
+            ofb += b * rg * fk;
+            rgb += b * of * fk;
+        }
+    }
+    // a1y = -rho g / 2, rg = rho g; u = (j + rho g e_y / 2) / rho
+    rhob += (Real)-0.5 * gy * a1yb + gy * rgb;
+    Real gyb = (Real)-0.5 * rho * a1yb + rho * rgb + (Real)0.5 * ub[1];
+    rhob -= (ub[0] * ux + ub[1] * (uy - (Real)0.5 * gy) + ub[2] * uz) * inv_rho;
+    const Real jxb = ub[0] * inv_rho, jyb = ub[1] * inv_rho, jzb = ub[2] * inv_rho;
+    // om = 1 - 1/tau, of = 1 - 1/(2 tau)
+    a.grad_g[node] += gyb;
+    a.grad_tau[node] += (omb + (Real)0.5 * ofb) / (tau * tau);
+
+    // mu_q = d rho/dfs_q rhob + ... (the moments are sums over q), then P^T
+    constexpr int MV = LAT::MAXV;
+    static_for<Q>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        constexpr int ex = E<LAT>(q, 0), ey = E<LAT>(q, 1), ez = E<LAT>(q, 2);
+        constexpr double X = R * ex, Y = R * ey, Z = R * ez;
+        Real mu = rhob;
+        if constexpr (ex != 0) mu += (Real)X * jxb + (Real)(X * X) * pb[0];
+        if constexpr (ey != 0) mu += (Real)Y * jyb + (Real)(Y * Y) * pb[3];
+        if constexpr (ez != 0) mu += (Real)Z * jzb + (Real)(Z * Z) * pb[5];
+        if constexpr (ex * ey != 0) mu += (Real)(X * Y) * pb[1];
+        if constexpr (ex * ez != 0) mu += (Real)(X * Z) * pb[2];
+        if constexpr (ey * ez != 0) mu += (Real)(Y * Z) * pb[4];
+        if constexpr (LAT::ORDER >= 3) {
+            if constexpr (ex != 0) mu += (Real)(X * X * X) * qb[0];
+            if constexpr (ex * ey != 0) mu += (Real)(X * X * Y) * qb[1] + (Real)(X * Y * Y) * qb[3];
+            if constexpr (ex * ez != 0) mu += (Real)(X * X * Z) * qb[2] + (Real)(X * Z * Z) * qb[5];
+            if constexpr (ex * ey * ez != 0) mu += (Real)(X * Y * Z) * qb[4];
+            if constexpr (ey != 0) mu += (Real)(Y * Y * Y) * qb[6];
+            if constexpr (ey * ez != 0) mu += (Real)(Y * Y * Z) * qb[7] + (Real)(Y * Z * Z) * qb[8];
+            if constexpr (ez != 0) mu += (Real)(Z * Z * Z) * qb[9];
+        }
+        const int sx = x - ex;
+        if (sx >= 0 && sx < nx) {
+            a.lam[(int64_t)q * nn + (int64_t)wrap_y(y - ey, ny) * nx + sx] = mu;
+        } else if constexpr (ex != 0) {
+            // a source behind a wall: fs_q = w_q rho_wall(row y)
+            atomicAdd(&a.wall[(sx < 0 ? 0 : ny) + y], (Real)W<LAT>(q) * mu);
+        }
+    });
+    (void)MV;
+}
+
+// One thread per node: the collision adjoint and the transposed pull.
+template <typename Real, class LAT>
+__global__ void __launch_bounds__(128) k_lbm_adj(LbmAdjArgs<Real> a) {
+    const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (u < a.nnodes) lbm_adjoint_node<Real, LAT>(a, u);
+}
+
+// One thread per row and wall: the populations leaving through the wall on row y' feed the
+// wall density of row y' + e_y; their adjoint is that row's wall adjoint times the flux
+// normalisation. The wall sums are cleared for the next step.
+template <typename Real, class LAT>
+__global__ void k_lbm_adj_wall(LbmAdjArgs<Real> a) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ny = a.ny, nx = a.nx;
+    if (t >= 2 * ny) return;
+    const bool left = t < ny;
+    const int yr = left ? t : t - ny;  // the source row y'
+    constexpr double inv_flux = 1.0 / wall_flux_norm<LAT>();
+    static_for<LAT::Q>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        constexpr int ex = E<LAT>(q, 0), ey = E<LAT>(q, 1);
+        const Real wb = (Real)inv_flux * a.wall[(left ? 0 : ny) + wrap_y(yr + ey, ny)];
+        if constexpr (ex < 0) {
+            if (left)
+                for (int i = 0; i < -ex; ++i) a.lam[(int64_t)q * a.nnodes + (int64_t)yr * nx + i] = wb;
+        }
+        if constexpr (ex > 0) {
+            if (!left)
+                for (int i = nx - ex; i < nx; ++i) a.lam[(int64_t)q * a.nnodes + (int64_t)yr * nx + i] = wb;
+        }
+    });
+}
+
+
+// Packed index of the symmetric pair (i, j): xx xy xz yy yz zz.
+__device__ __forceinline__ int pidx2(int i, int j) {
+    if (i > j) { const int t = i; i = j; j = t; }
+    return i == 0 ? j : (i == 1 ? 2 + j : 5);
+}
+// Coupling-interface loss of the differentiated LBM, one thread per listed node: the Grad
+// coefficients of the node's populations (rho, u = j / rho, a2 = P / rho - u u - I,
+// a3 = Q3 / rho - sym(u P) / rho + 2 u u u, the comoving coefficients written with the raw
+// moments) against 20 targets, summed as squares into *loss, and the adjoint of the
+// populations of the node added to lam. Formed in FP64 (a handful of nodes).
+template <typename Real, class LAT>
+__global__ void k_interface_loss(const Real* __restrict__ f, int64_t nn, const int32_t* __restrict__ nodes,
+                                 int n, const Real* __restrict__ targets, double* loss, Real* lam,
+                                 unsigned* status) {
+    constexpr int Q = LAT::Q;
+    constexpr double R = lat_r<LAT>();
+    constexpr int I2[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+    constexpr int I3[10][3] = {{0, 0, 0}, {0, 0, 1}, {0, 0, 2}, {0, 1, 1}, {0, 1, 2},
+                               {0, 2, 2}, {1, 1, 1}, {1, 1, 2}, {1, 2, 2}, {2, 2, 2}};
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t node = nodes[k];
+    if (node < 0 || node >= nn) {
+        atomicOr(status, HYB_ST_BAD_INPUT);
+        return;
+    }
+    double rho = 0, J[3] = {0, 0, 0}, P2[6] = {0, 0, 0, 0, 0, 0};
+    double P3[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    static_for<Q>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        const double xi[3] = {R * E<LAT>(q, 0), R * E<LAT>(q, 1), R * E<LAT>(q, 2)};
+        const double fq = (double)f[(int64_t)q * nn + node];
+        rho += fq;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) J[i] += fq * xi[i];
+#pragma unroll
+        for (int m = 0; m < 6; ++m) P2[m] += fq * xi[I2[m][0]] * xi[I2[m][1]];
+#pragma unroll
+        for (int m = 0; m < 10; ++m) P3[m] += fq * xi[I3[m][0]] * xi[I3[m][1]] * xi[I3[m][2]];
+    });
+    const double u[3] = {J[0] / rho, J[1] / rho, J[2] / rho};
+    double mb[20], err = 0;
+    {
+        double mv[20];
+        mv[0] = rho;
+        for (int i = 0; i < 3; ++i) mv[1 + i] = u[i];
+        for (int m = 0; m < 6; ++m) {
+            const int i = I2[m][0], j = I2[m][1];
+            mv[4 + m] = P2[m] / rho - u[i] * u[j] - (i == j ? 1.0 : 0.0);
+        }
+        for (int m = 0; m < 10; ++m) {
+            const int i = I3[m][0], j = I3[m][1], l = I3[m][2];
+            const double S = u[i] * P2[pidx2(j, l)] + u[j] * P2[pidx2(i, l)] + u[l] * P2[pidx2(i, j)];
+            mv[10 + m] = P3[m] / rho - S / rho + 2.0 * u[i] * u[j] * u[l];
+        }
+        for (int m = 0; m < 20; ++m) {
+            const double e = mv[m] - (double)targets[20 * (int64_t)k + m];
+            err += e * e;
+            mb[m] = 2.0 * e;
+        }
+    }
+    atomicAdd(loss, err);
+    // reverse: the 20 coefficients -> raw moments
+    double rb = mb[0], ub[3] = {mb[1], mb[2], mb[3]}, P2b[6] = {0, 0, 0, 0, 0, 0};
+    double P3b[10];
+    for (int m = 0; m < 6; ++m) {
+        const int i = I2[m][0], j = I2[m][1];
+        const double b = mb[4 + m];
+        P2b[m] += b / rho;
+        rb -= b * P2[m] / (rho * rho);
+        ub[i] -= b * u[j];
+        ub[j] -= b * u[i];
+    }
+    for (int m = 0; m < 10; ++m) {
+        const int i = I3[m][0], j = I3[m][1], l = I3[m][2];
+        const double b = mb[10 + m];
+        const int jl = pidx2(j, l), il = pidx2(i, l), ij = pidx2(i, j);
+        const double S = u[i] * P2[jl] + u[j] * P2[il] + u[l] * P2[ij];
+        P3b[m] = b / rho;
+        rb -= b * (P3[m] - S) / (rho * rho);
+        ub[i] += b * (-P2[jl] / rho + 2.0 * u[j] * u[l]);
+        ub[j] += b * (-P2[il] / rho + 2.0 * u[i] * u[l]);
+        ub[l] += b * (-P2[ij] / rho + 2.0 * u[i] * u[j]);
+        P2b[jl] -= b * u[i] / rho;
+        P2b[il] -= b * u[j] / rho;
+        P2b[ij] -= b * u[l] / rho;
+    }
+    double Jb[3];
+    for (int i = 0; i < 3; ++i) {
+        Jb[i] = ub[i] / rho;
+        rb -= ub[i] * u[i] / rho;
+    }
+    static_for<Q>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        const double xi[3] = {R * E<LAT>(q, 0), R * E<LAT>(q, 1), R * E<LAT>(q, 2)};
+        double g = rb;
+        for (int i = 0; i < 3; ++i) g += Jb[i] * xi[i];
+        for (int m = 0; m < 6; ++m) g += P2b[m] * xi[I2[m][0]] * xi[I2[m][1]];
+        for (int m = 0; m < 10; ++m) g += P3b[m] * xi[I3[m][0]] * xi[I3[m][1]] * xi[I3[m][2]];
+        atomicAdd(&lam[(int64_t)q * nn + node], (Real)g);
+    });
 }
 
 template <typename Real, class LAT>
@@ -308,6 +699,50 @@ cudaError_t lbm_init_impl(Ctx& c) {
     return cudaGetLastError();
 }
 
+
+template <typename Real, class LAT>
+cudaError_t lbm_nodes_impl(Ctx& c, const void* f_src, void* f_dst, const void* g, const void* tau) {
+    LbmArgs<Real> a = lbm_args<Real>(c, c.cur_f);
+    a.src = (const Real*)f_src;
+    a.dst = (Real*)f_dst;
+    a.g_node = (const Real*)g;
+    a.tau_node = (const Real*)tau;
+    const int64_t blocks = (c.d.nnodes + 127) / 128;
+    k_lbm_param<Real, LAT><<<(unsigned)blocks, 128, 0, c.stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename Real, class LAT>
+cudaError_t lbm_adj_impl(Ctx& c, const void* f, const void* lam_next, void* lam, const void* g,
+                         const void* tau, void* grad_g, void* grad_tau, void* wall) {
+    LbmAdjArgs<Real> a;
+    a.f = (const Real*)f;
+    a.lam_next = (const Real*)lam_next;
+    a.lam = (Real*)lam;
+    a.g_node = (const Real*)g;
+    a.tau_node = (const Real*)tau;
+    a.grad_g = (Real*)grad_g;
+    a.grad_tau = (Real*)grad_tau;
+    a.wall = (Real*)wall;
+    a.nx = (int32_t)c.d.nx;
+    a.ny = (int32_t)c.d.ny;
+    a.nnodes = c.d.nnodes;
+    const int64_t blocks = (c.d.nnodes + 127) / 128;
+    k_lbm_adj<Real, LAT><<<(unsigned)blocks, 128, 0, c.stream>>>(a);
+    k_lbm_adj_wall<Real, LAT><<<(unsigned)((2 * a.ny + 127) / 128), 128, 0, c.stream>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return cudaMemsetAsync(wall, 0, (size_t)2 * a.ny * sizeof(Real), c.stream);
+}
+
+template <typename Real, class LAT>
+cudaError_t loss_impl(Ctx& c, const void* f, const int32_t* nodes, int32_t n, const void* targets,
+                      double* loss, void* lam) {
+    k_interface_loss<Real, LAT><<<(unsigned)((n + 63) / 64), 64, 0, c.stream>>>(
+        (const Real*)f, c.d.nnodes, nodes, n, (const Real*)targets, loss, (Real*)lam,
+        (unsigned*)c.st.ctrl + CTRL_STATUS);
+    return cudaGetLastError();
+}
 }  // namespace
 
 size_t lbm_args_bytes(int real_bytes) {
@@ -353,6 +788,36 @@ cudaError_t launch_lbm_init(Ctx& c) {
     if (c.p.lattice == 39)
         return c.p.real_bytes == 4 ? lbm_init_impl<float, D3Q39>(c) : lbm_init_impl<double, D3Q39>(c);
     return c.p.real_bytes == 4 ? lbm_init_impl<float, D3Q19>(c) : lbm_init_impl<double, D3Q19>(c);
+}
+
+
+cudaError_t launch_lbm_step_nodes(Ctx& c, const void* f_src, void* f_dst, const void* g, const void* tau) {
+    if (c.p.lattice == 39)
+        return c.p.real_bytes == 4 ? lbm_nodes_impl<float, D3Q39>(c, f_src, f_dst, g, tau)
+                                   : lbm_nodes_impl<double, D3Q39>(c, f_src, f_dst, g, tau);
+    return c.p.real_bytes == 4 ? lbm_nodes_impl<float, D3Q19>(c, f_src, f_dst, g, tau)
+                               : lbm_nodes_impl<double, D3Q19>(c, f_src, f_dst, g, tau);
+}
+
+cudaError_t launch_lbm_adjoint_step(Ctx& c, const void* f, const void* lam_next, void* lam,
+                                    const void* g, const void* tau, void* grad_g, void* grad_tau,
+                                    void* wall) {
+    if (c.p.lattice == 39)
+        return c.p.real_bytes == 4
+                   ? lbm_adj_impl<float, D3Q39>(c, f, lam_next, lam, g, tau, grad_g, grad_tau, wall)
+                   : lbm_adj_impl<double, D3Q39>(c, f, lam_next, lam, g, tau, grad_g, grad_tau, wall);
+    return c.p.real_bytes == 4
+               ? lbm_adj_impl<float, D3Q19>(c, f, lam_next, lam, g, tau, grad_g, grad_tau, wall)
+               : lbm_adj_impl<double, D3Q19>(c, f, lam_next, lam, g, tau, grad_g, grad_tau, wall);
+}
+
+cudaError_t launch_interface_loss(Ctx& c, const void* f, const int32_t* nodes, int32_t n,
+                                  const void* targets, double* loss, void* lam) {
+    if (c.p.lattice == 39)
+        return c.p.real_bytes == 4 ? loss_impl<float, D3Q39>(c, f, nodes, n, targets, loss, lam)
+                                   : loss_impl<double, D3Q39>(c, f, nodes, n, targets, loss, lam);
+    return c.p.real_bytes == 4 ? loss_impl<float, D3Q19>(c, f, nodes, n, targets, loss, lam)
+                               : loss_impl<double, D3Q19>(c, f, nodes, n, targets, loss, lam);
 }
 
 }  // namespace hyb

@@ -343,6 +343,33 @@ hyb_status map_lbm_to_dsmc(hyb_ctx* h, const int32_t* dev_cells, int32_t n) {
     return check(h->c, launch_map_l2d(h->c, dev_cells, n), "map_lbm_to_dsmc launch");
 }
 
+hyb_status lbm_step_nodes(hyb_ctx* h, const void* f_src, void* f_dst, const void* g_node,
+                          const void* tau_node) {
+    if (!h || !f_src || !f_dst || f_src == f_dst || !g_node || !tau_node) return HYB_EINVAL;
+    return check(h->c, launch_lbm_step_nodes(h->c, f_src, f_dst, g_node, tau_node),
+                 "lbm_step_nodes launch");
+}
+
+hyb_status lbm_interface_loss(hyb_ctx* h, const void* f, const int32_t* dev_nodes, int32_t n,
+                              const void* dev_targets, double* dev_loss, void* lam) {
+    if (!h || !f || n < 0 || (n > 0 && (!dev_nodes || !dev_targets || !dev_loss || !lam)))
+        return HYB_EINVAL;
+    if (n == 0) return HYB_OK;
+    return check(h->c, launch_interface_loss(h->c, f, dev_nodes, n, dev_targets, dev_loss, lam),
+                 "lbm_interface_loss launch");
+}
+
+hyb_status lbm_adjoint_step(hyb_ctx* h, const void* f, const void* lam_next, void* lam,
+                            const void* g_node, const void* tau_node, void* grad_g,
+                            void* grad_tau, void* wall) {
+    if (!h || !f || !lam_next || !lam || lam == lam_next || !g_node || !tau_node || !grad_g ||
+        !grad_tau || !wall)
+        return HYB_EINVAL;
+    return check(h->c, launch_lbm_adjoint_step(h->c, f, lam_next, lam, g_node, tau_node, grad_g,
+                                               grad_tau, wall),
+                 "lbm_adjoint_step launch");
+}
+
 hyb_status map_lbm_to_dsmc_noalloc(hyb_ctx* h, const int32_t* dev_cells, int32_t n) {
     if (!h || n < 0 || (n > 0 && !dev_cells) || n > h->c.d.ncells) return HYB_EINVAL;
     Ctx& c = h->c;

@@ -1,0 +1,215 @@
+"""The differentiated LBM through the C ABI: the LB step with per-node force increment and
+relaxation time against the oracle, the coupling-interface loss against the oracle, and the
+adjoint gradient (checkpointed recomputation) against the oracle's central differences and
+against directional differences of the GPU forward."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1512_08042_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # collected on CPU-only machines, never run there
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1512_08042_gb300 import binding as B  # noqa: E402
+from paper_1512_08042_gb300 import build as BUILD  # noqa: E402
+
+BUILD.build()
+
+
+def cfg_lb(**kw):
+    base = dict(ncx=6, ncy=4, ppc=10, lb_ratio=2, real_bytes=8, seed=3, kn=0.3, ma=0.5)
+    base.update(kw)
+    return W.config(**base)
+
+
+def setup(cfg, seed=1, spread_g=0.3, spread_tau=0.1):
+    """A context, seeded populations and per-node parameters around the scalars."""
+    h = B.Hybrid(cfg)
+    d = h.d
+    n = d["nnodes"]
+    e, w, r = O.lattice(cfg.get("lattice", 39))
+    rng = np.random.default_rng(seed)
+    f0 = W.gen_populations(w, n, seed=seed + 100)
+    g = d["g_step"] * (1 + spread_g * rng.standard_normal(n))
+    tau = d["tau"] * (1 + spread_tau * rng.standard_normal(n))
+    real = np.float32 if cfg["real_bytes"] == 4 else np.float64
+    f0, g, tau = f0.astype(real), g.astype(real), tau.astype(real)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    return h, dev(f0.reshape(h.d["q"], h.d["ny"], h.d["nx"])), dev(g), dev(tau), f0, g, tau
+
+
+def oracle_after(cfg, f0, g, tau, nsteps):
+    o = O.Oracle(cfg)
+    o.set_f(f0.astype(np.float32 if cfg["real_bytes"] == 4 else np.float64))
+    o.set_node_params(g.astype(np.float64), tau.astype(np.float64))
+    o.lbm_step(nsteps)
+    return o
+
+
+def gpu_after(h, f, g, tau, nsteps):
+    a, b = f.clone(), torch.empty_like(f)
+    for _ in range(nsteps):
+        h.lbm_step_nodes(a, b, g, tau)
+        a, b = b, a
+    h.sync()
+    return a
+
+
+@pytest.mark.parametrize("lattice,real_bytes", [(39, 8), (39, 4), (19, 4)])
+def test_lbm_step_nodes_matches_oracle(lattice, real_bytes):
+    cfg = cfg_lb(lattice=lattice, real_bytes=real_bytes)
+    h, f, g, tau, f0, gn, tn = setup(cfg)
+    e, w, r = O.lattice(lattice)
+    o = O.Oracle(cfg)
+    o.set_f(f0)
+    o.set_node_params(gn.astype(np.float64), tn.astype(np.float64))
+    a, b = f.clone(), torch.empty_like(f)
+    for step in range(3):
+        h.lbm_step_nodes(a, b, g, tau)
+        a, b = b, a
+        o.lbm_step(1)
+        h.sync()
+        err = np.abs(a.cpu().numpy() - o.f()) / (np.abs(o.f()) + 1e-3 * w[:, None, None])
+        assert err.max() < (2e-5 if real_bytes == 4 else 1e-12), (step, err.max())
+    # the context's own populations were not touched
+    assert torch.equal(h.f(), torch.from_numpy(np.tile(w[:, None], (1, h.d["nnodes"])).astype(
+        f0.dtype).reshape(h.f().shape)).cuda())
+
+
+@pytest.mark.parametrize("real_bytes", [8, 4])
+def test_interface_loss_matches_oracle(real_bytes):
+    cfg = cfg_lb(real_bytes=real_bytes)
+    h, f, g, tau, f0, gn, tn = setup(cfg, seed=2)
+    nodes_np = np.array([5, 17, 30, 30, 77], np.int32)  # a repeated node counts twice
+    o = oracle_after(cfg, f0, gn, tn, 2)
+    rng = np.random.default_rng(3)
+    targets_np = np.stack([o.grad_node(k) for k in nodes_np]) + 0.02 * rng.standard_normal((5, 20))
+    want = o.interface_loss(nodes_np, targets_np)
+    fT = gpu_after(h, f, g, tau, 2)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    lam = torch.zeros_like(fT)
+    h.lbm_interface_loss(fT, torch.from_numpy(nodes_np).cuda(), torch.from_numpy(
+        targets_np.astype(fT.cpu().numpy().dtype)).cuda(), loss, lam)
+    h.sync()
+    assert loss.item() == pytest.approx(want, rel=1e-10 if real_bytes == 8 else 2e-4)
+    # lam is non-zero only at the listed nodes
+    nz = (lam.reshape(lam.shape[0], -1) != 0).any(0).nonzero().flatten().cpu().numpy()
+    assert set(nz) <= set(nodes_np.tolist())
+
+
+def gpu_gradient(cfg, h, f, g, tau, nodes, targets, nsteps, ckpt):
+    g = g.clone().requires_grad_(True)
+    tau = tau.clone().requires_grad_(True)
+    f0 = f.clone().requires_grad_(True)
+    L = B.interface_loss(h, g, tau, f0, nodes, targets, nsteps, ckpt)
+    L.backward()
+    torch.cuda.synchronize()
+    return L.item(), g.grad.cpu().numpy(), tau.grad.cpu().numpy(), f0.grad
+
+
+@pytest.mark.parametrize("lattice,real_bytes,tol", [(39, 8, 1e-6), (19, 8, 1e-6), (39, 4, 2e-3)])
+def test_adjoint_gradient_matches_oracle_central_differences(lattice, real_bytes, tol):
+    cfg = cfg_lb(lattice=lattice, real_bytes=real_bytes)
+    h, f, g, tau, f0, gn, tn = setup(cfg, seed=4)
+    T, K = 5, 2  # three checkpoint segments
+    nodes_np = np.array([2 * h.d["nx"] + 1, 5 * h.d["nx"] + 6, 6 * h.d["nx"] + 11], np.int32)
+    o = oracle_after(cfg, f0, gn, tn, T)
+    rng = np.random.default_rng(5)
+    targets_np = np.stack([o.grad_node(k) for k in nodes_np]) + 0.02 * rng.standard_normal((3, 20))
+    loss, dg, dt, _ = gpu_gradient(cfg, h, f, g, tau, torch.from_numpy(nodes_np).cuda(),
+                                   torch.from_numpy(targets_np.astype(f0.dtype)).cuda(), T, K)
+    cfg64 = dict(cfg, real_bytes=8)
+    want_g, want_t = O.interface_loss_fd_gradient(cfg64, f0.astype(np.float64), gn, tn, nodes_np,
+                                                  targets_np, T)
+    assert loss == pytest.approx(O.interface_loss_after(cfg64, f0.astype(np.float64), gn, tn,
+                                                        nodes_np, targets_np, T),
+                                 rel=1e-10 if real_bytes == 8 else 1e-3)
+    for got, want in ((dg, want_g), (dt, want_t)):
+        scale = np.abs(want).max()
+        assert scale > 0
+        assert np.abs(got - want).max() < tol * scale, np.abs(got - want).max() / scale
+
+
+def test_adjoint_gradient_is_exactly_zero_outside_the_light_cone():
+    cfg = cfg_lb(ncx=6, ncy=10)  # 12 x 20 nodes
+    h, f, g, tau, f0, gn, tn = setup(cfg, seed=6)
+    nx = h.d["nx"]
+    node = 10 * nx + 3
+    T = 2
+    o = oracle_after(cfg, f0, gn, tn, T)
+    targets = o.grad_node(node)[None, :] + 0.01
+    _, dg, dt, _ = gpu_gradient(cfg, h, f, g, tau, torch.tensor([node], dtype=torch.int32,
+                                device="cuda"), torch.from_numpy(targets).cuda(), T, 1)
+    rows = np.arange(h.d["nnodes"]) // nx
+    far = np.minimum(np.abs(rows - 10), h.d["ny"] - np.abs(rows - 10)) > 3 * T
+    assert np.all(dg[far] == 0) and np.all(dt[far] == 0)
+    assert dg[node] != 0 and dt[node] != 0
+
+
+def test_adjoint_populations_gradient_matches_directional_differences():
+    # dL/df0 is the adjoint carried back through every step (streaming transposes and wall
+    # densities included); its projection on a random direction must match the central
+    # difference of the GPU forward in FP64.
+    cfg = cfg_lb()
+    h, f, g, tau, f0, gn, tn = setup(cfg, seed=7)
+    T = 4
+    nodes = torch.tensor([1, h.d["nx"] * 3 + 11, h.d["nx"] * 5 + 4], dtype=torch.int32, device="cuda")
+    o = oracle_after(cfg, f0, gn, tn, T)
+    targets = torch.from_numpy(np.stack([o.grad_node(int(k)) for k in nodes.cpu()]) + 0.03).cuda()
+    _, _, _, gf = gpu_gradient(cfg, h, f, g, tau, nodes, targets, T, 3)
+    v = torch.randn_like(f) * 1e-2 * f
+    eps = 1e-5
+
+    def loss_at(ff):
+        fT = gpu_after(h, ff, g, tau, T)
+        L = torch.zeros(1, dtype=torch.float64, device="cuda")
+        h.lbm_interface_loss(fT, nodes, targets, L, torch.zeros_like(fT))
+        h.sync()
+        return L.item()
+
+    fd = (loss_at(f + eps * v) - loss_at(f - eps * v)) / (2 * eps)
+    assert (gf * v).sum().item() == pytest.approx(fd, rel=1e-6)
+
+
+def test_adjoint_at_the_differentiated_lbm_size_256x128_2000_steps():
+    # The differentiated configuration: 256 x 128 lattice, 2000 steps, checkpoints every 100,
+    # FP32. Checked by properties that hold at any size: a finite gradient, zero outside the
+    # rows the loss can reach (none here: 2000 steps cover the channel), and agreement of the
+    # FP32 directional derivative in g with central differences of an FP64 run.
+    cfg = W.config(ncx=128, ncy=64, ppc=10, lb_ratio=2, real_bytes=4, seed=9, kn=0.1, ma=0.1)
+    h, f, g, tau, f0, gn, tn = setup(cfg, seed=9, spread_g=0.1, spread_tau=0.02)
+    assert (h.d["nx"], h.d["ny"]) == (256, 128)
+    nx = h.d["nx"]
+    nodes_np = np.array([y * nx + x for y in range(0, 128, 16) for x in (8, 9, 10, 11)], np.int32)
+    nodes = torch.from_numpy(nodes_np).cuda()
+    rng = np.random.default_rng(10)
+    targets_np = np.zeros((len(nodes_np), 20))
+    targets_np[:, 0] = 1.0
+    targets_np[:, 2] = 0.05 + 0.01 * rng.standard_normal(len(nodes_np))
+    targets = torch.from_numpy(targets_np.astype(np.float32)).cuda()
+    loss, dg, dt, _ = gpu_gradient(cfg, h, f, g, tau, nodes, targets, 2000, 100)
+    assert np.isfinite(loss) and np.all(np.isfinite(dg)) and np.all(np.isfinite(dt))
+    # FP64 directional check along a random perturbation of g
+    cfg64 = dict(cfg, real_bytes=8)
+    h64 = B.Hybrid(cfg64)
+    f64, g64, t64 = (torch.from_numpy(a.astype(np.float64)).cuda() for a in (f0, gn, tn))
+    f64 = f64.reshape(h64.d["q"], h64.d["ny"], h64.d["nx"])
+    _, dg64, _, _ = gpu_gradient(cfg64, h64, f64, g64, t64, nodes, targets.double(), 2000, 100)
+    dirv = torch.from_numpy(rng.standard_normal(h.d["nnodes"])).cuda() * float(np.abs(gn).mean()) * 1e-3
+
+    def loss64(gg):
+        fT = gpu_after(h64, f64, gg, t64, 2000)
+        L = torch.zeros(1, dtype=torch.float64, device="cuda")
+        h64.lbm_interface_loss(fT, nodes, targets.double(), L, torch.zeros_like(fT))
+        h64.sync()
+        return L.item()
+
+    fd = (loss64(g64 + dirv) - loss64(g64 - dirv)) / 2.0
+    got64 = float((torch.from_numpy(dg64).cuda() * dirv).sum())
+    got32 = float((torch.from_numpy(dg).cuda().double() * dirv).sum())
+    assert got64 == pytest.approx(fd, rel=1e-5)
+    assert got32 == pytest.approx(fd, rel=2e-2)
