@@ -21,6 +21,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -220,6 +222,101 @@ def run_ensemble(args):
     batch.close()
 
 
+def run_adjoint(args):
+    """The differentiated LBM against the plain forward on the same GPU: one gradient of the
+    coupling-interface loss (2000 LB steps with per-node force and relaxation time, forward
+    with checkpoints every 100 steps, then recomputation and the adjoint step in reverse)
+    against the same 2000 forward steps alone; plus the adjoint kernel's achieved bandwidth
+    and the FP32 gradient's error against an FP64 gradient."""
+    import torch
+    import __graft_entry__ as G
+    G.build()
+    from paper_1512_08042_gb300 import binding as B
+
+    cfg = dict(W.DIFF_LBM, real_bytes=4)
+    T, K = W.DIFF_LBM_STEPS, W.DIFF_LBM_CKPT
+    dev = torch.device("cuda", 0)
+    h = B.Hybrid(cfg, device=dev)
+    d = h.d
+    e, w, r = B.lattice(cfg["lattice"])
+    f0, sg, st, nodes_np, targets_np = W.diff_lbm_inputs(cfg, w)
+    shape = (d["q"], d["ny"], d["nx"])
+    mk = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a).astype(dt)).to(dev)
+    f = mk(f0, np.float32).reshape(shape)
+    g = mk(d["g_step"] * (1 + sg), np.float32)
+    tau = mk(d["tau"] * (1 + st), np.float32)
+    nodes = mk(nodes_np, np.int32)
+    targets = mk(targets_np, np.float32)
+    stream = h.stream
+
+    def grad(hh, ff, gg, tt, tg):
+        gg = gg.clone().requires_grad_(True)
+        tt = tt.clone().requires_grad_(True)
+        L = B.interface_loss(hh, gg, tt, ff, nodes, tg, T, K)
+        L.backward()
+        return L, gg.grad, tt.grad
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / reps
+
+    def forward_only():
+        x, y = f.clone(), torch.empty_like(f)
+        for _ in range(T):
+            h.lbm_step_nodes(x, y, g, tau)
+            x, y = y, x
+
+    reps = max(1, min(args.steps, 5))
+    ms_fwd = timed(forward_only, reps)
+    ms_grad = timed(lambda: grad(h, f, g, tau, targets), reps)
+    # the adjoint step alone, 200 steps on fixed inputs
+    lam_a, lam_b = torch.rand_like(f), torch.empty_like(f)
+    gg, gt = torch.zeros_like(g), torch.zeros_like(tau)
+    wall = torch.zeros(2 * d["ny"], dtype=torch.float32, device=dev)
+
+    def adj200():
+        for _ in range(200):
+            h.lbm_adjoint_step(f, lam_a, lam_b, g, tau, gg, gt, wall)
+
+    ms_adj = timed(adj200, 1) / 200
+    bytes_adj = d["nnodes"] * (3 * d["q"] * 4 + 4 * 4 + 2 * 4)
+    peak, peak_kind = measured_peak_hbm()
+    # accuracy of the FP32 gradient against FP64
+    cfg64 = dict(cfg, real_bytes=8)
+    h64 = B.Hybrid(cfg64, device=dev)
+    L32, g32, t32 = grad(h, f, g, tau, targets)
+    L64, g64, t64 = grad(h64, f.double(), g.double(), tau.double(), targets.double())
+    torch.cuda.synchronize(dev)
+    err = lambda a, b: float((a.double() - b).abs().max() / b.abs().max())
+    line = {
+        "metric": "differentiated LBM: interface-loss gradients/s (2000 LB steps, checkpoints every 100)",
+        "value": 1e3 / ms_grad, "unit": "gradients/s", "higher_is_better": True,
+        "ms_per_gradient": ms_grad, "forward_only": {"ms": ms_fwd, "lb_steps_per_s": T * 1e3 / ms_fwd,
+                                                    "mlups": T * d["nnodes"] / (ms_fwd * 1e3)},
+        "gradient_over_forward": ms_grad / ms_fwd,
+        "adjoint_step": {"us": ms_adj * 1e3, "achieved_gbs": bytes_adj / (ms_adj * 1e-3) / 1e9,
+                         "peak_gbs": peak, "peak_kind": peak_kind,
+                         "frac": bytes_adj / (ms_adj * 1e-3) / 1e9 / peak,
+                         "bytes_per_node": bytes_adj / d["nnodes"]},
+        "fp32_vs_fp64": {"loss_rel": abs(L32.item() - L64.item()) / abs(L64.item()),
+                         "grad_g_rel_maxnorm": err(g32, g64), "grad_tau_rel_maxnorm": err(t32, t64)},
+        "n_gpus": 1, "steps": reps, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "differentiated LBM, 256 x 128 D3Q39, %d steps, checkpoints every %d"
+                               % (T, K), "coupling_nodes": int(len(nodes_np)),
+                   "l2": "inputs not flushed: every gradient sweeps 2000 states"},
+    }
+    print(json.dumps(line), flush=True)
+    h.close()
+    h64.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -232,6 +329,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="run this many hybrid steps with direct launches and exit (for ncu)")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="time the differentiated LBM (gradient vs forward) on the 256 x 128 lattice")
     ap.add_argument("--ensemble", type=int, default=0,
                     help="time a batched ensemble of this many channels against plain contexts")
     args = ap.parse_args()
@@ -239,6 +338,9 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.ensemble:
         run_ensemble(args)
+        return
+    if args.adjoint:
+        run_adjoint(args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -36,6 +36,29 @@ WORKLOADS = {
 }
 
 
+# The differentiated LBM: a 256 x 128 D3Q39 lattice (128 x 64 DSMC cells at two LB nodes per
+# cell per axis), FP32, differentiated through 2000 steps with checkpoints every 100.
+DIFF_LBM = config(ncx=128, ncy=64, ppc=10, lb_ratio=2, kn=0.1, ma=0.1, seed=9)
+DIFF_LBM_STEPS, DIFF_LBM_CKPT = 2000, 100
+
+
+def diff_lbm_inputs(cfg, weights, seed=9, spread_g=0.1, spread_tau=0.02):
+    """Seeded populations around rest, per-node force increments and relaxation times around
+    the channel's scalars, coupling nodes on an 8-node-wide strip (x = 8..15, every y) and
+    targets (rho 1, u_y 0.05, other coefficients 0) for the differentiated LBM."""
+    nx, ny = cfg["ncx"] * cfg["lb_ratio"], cfg["ncy"] * cfg["lb_ratio"]
+    n = nx * ny
+    rng = np.random.default_rng(seed)
+    f0 = gen_populations(weights, n, seed=seed + 100)
+    g = rng.standard_normal(n)
+    tau = rng.standard_normal(n)
+    nodes = np.array([y * nx + x for y in range(ny) for x in range(8, 16)], np.int32)
+    targets = np.zeros((len(nodes), 20))
+    targets[:, 0] = 1.0
+    targets[:, 2] = 0.05
+    return f0, spread_g * g, spread_tau * tau, nodes, targets
+
+
 def ensemble_configs(n=64, seed=1000):
     """The batched ensemble: n independent channels of the 64 x 1 geometry (walls across,
     one periodic cell), H uniform in 32..256 cells, 20..100 particles per cell, Kn
