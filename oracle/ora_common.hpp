@@ -41,6 +41,8 @@ struct Params {
     double capacity_factor;
     double T_K;            // temperature [K], SI reporting only
     double mass_kg;        // molecular mass [kg], SI reporting only
+    int32_t lb_collision;  // 0 regularised BGK (Sec. 2), 1 plain BGK (Sec. 4)
+    int32_t d2l_mode;      // 0 Grad to the lattice order (Sec. 2.1), 1 equilibrium (Eq. feq_dsmc)
 };
 
 // Derived constants. Field order is a binary interface with oracle.py.

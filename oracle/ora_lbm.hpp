@@ -12,7 +12,9 @@
 //   f_neq projected onto H1, H2 (and H3) by the quadrature (the "regularization" of
 //   Sec. 2);
 //   F = w sum_{n=1..N} n (g (x) a_eq^(n-1)) : H^n / n! (Hermite expansion of -g . grad_xi f);
-//   f' = f_eq + (1 - 1/tau) f_neq_reg + (1 - 1/(2 tau)) F.
+//   f' = f_eq + (1 - 1/tau) f_neq_reg + (1 - 1/(2 tau)) F,
+// or, with lb_collision = 1 (the unregularised LB of the proof-of-concept hybrid, Sec. 4),
+//   f' = f_eq + (1 - 1/tau) (f - f_eq) + (1 - 1/(2 tau)) F.
 // Relaxation time from Eq. tau. The quasi-2D slab has one periodic layer in z.
 //
 // Optional per-node parameters (for the differentiated LBM): a body-force increment g_y and
@@ -93,7 +95,7 @@ struct Lbm {
         const double of = 1.0 - 1.0 / (2.0 * tau);
         for (int a = 0; a < L.q; ++a) {
             const double* x = L.xi[a].data();
-            const double freg = L.w[a] * hermite_series(aneq, x, N);
+            const double freg = p.lb_collision == 1 ? fneq[a] : L.w[a] * hermite_series(aneq, x, N);
             const double F = L.w[a] * hermite_series(bf, x, N);
             out[a] = feq[a] + om * freg + of * F;
         }

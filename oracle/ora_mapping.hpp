@@ -287,6 +287,15 @@ void map_dsmc_to_lbm(Dsmc<Real>& D, Lbm<Real>& B, const int32_t* nodes, int n) {
             D.status |= ST_BAD_INPUT;
             continue;
         }
+        if (D.p.d2l_mode == 1) {  // the local equilibrium of rho and u (Sec. 4, Eq. feq_dsmc)
+            double u[3];
+            for (int i = 0; i < 3; ++i) u[i] = a.a1[i] / a.a0;
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    a.a2[i][j] = a.a0 * u[i] * u[j];
+                    for (int k = 0; k < 3; ++k) a.a3[i][j][k] = a.a0 * u[i] * u[j] * u[k];
+                }
+        }
         for (int q = 0; q < L.q; ++q)
             B.f[(size_t)q * B.d.nnodes + node] =
                 (Real)(L.w[q] * hermite_series(a, L.xi[q].data(), B.d.order));

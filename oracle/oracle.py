@@ -37,6 +37,8 @@ class Params(ctypes.Structure):
         ("capacity_factor", ctypes.c_double),
         ("T_K", ctypes.c_double),
         ("mass_kg", ctypes.c_double),
+        ("lb_collision", ctypes.c_int32),
+        ("d2l_mode", ctypes.c_int32),
     ]
 
 

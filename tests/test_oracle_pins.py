@@ -792,3 +792,87 @@ def test_interface_loss_gradient_of_one_step_at_tau_one():
         delta * delta, rel=1e-12)
     dg, dt = O.interface_loss_fd_gradient(cfg, f0, g, tau, [node], targets, 1, which=[node])
     assert dg[0] == pytest.approx(2 * delta, rel=1e-6)
+
+
+# ---------------------------------------------------------------------------------------
+# The proof-of-concept hybrid of Sec. 4: unregularised BGK and the equilibrium DSMC2LB
+
+def _moment_matrix(q):
+    """Rows: the 20 moment functions 1, xi, xi xi (6), xi xi xi (10) at the lattice speeds."""
+    e, w, r = O.lattice(q)
+    xi = e * r
+    rows = [np.ones(len(w))] + [xi[:, i] for i in range(3)]
+    rows += [xi[:, i] * xi[:, j] for i in range(3) for j in range(i, 3)]
+    rows += [xi[:, i] * xi[:, j] * xi[:, k] for i in range(3) for j in range(i, 3)
+             for k in range(j, 3)]
+    return np.array(rows)
+
+
+@pytest.mark.parametrize("q", [19, 39])
+def test_bgk_relaxes_a_ghost_mode_that_the_regularisation_removes(q):
+    # A perturbation with no moment up to order 3 (a "ghost" mode of the lattice): the
+    # regularised collision projects it out (f' = f_eq), plain BGK relaxes it by 1 - 1/tau
+    # per step (f' = f_eq + (1 - 1/tau) delta). No force, so u is the flow velocity of f.
+    e, w, r = O.lattice(q)
+    cfg0 = small_cfg(lattice=q, ma=0.0, kn=0.2, lb_ratio=1)
+    cfg1 = dict(cfg0, lb_collision=1)
+    d = O.derive(cfg0)
+    assert d["g_step"] == 0.0
+    rho, u = 1.03, np.array([0.04, -0.07, 0.02])
+    xu = (e * r) @ u
+    u2 = u @ u
+    feq = w * rho * (1 + xu + 0.5 * (xu ** 2 - u2)
+                     + (xu * (xu ** 2 - 3 * u2) / 6 if q == 39 else 0))
+    M = _moment_matrix(q)
+    rng = np.random.default_rng(2)
+    z = rng.standard_normal(len(w)) * w
+    delta = z - np.linalg.pinv(M) @ (M @ z)
+    assert np.abs(M @ delta).max() < 1e-14 and np.abs(delta).max() > 1e-4
+    fs = feq + 0.05 * delta
+    om = 1 - 1 / d["tau"]
+    reg = O.lbm_collide(cfg0, fs)
+    bgk = O.lbm_collide(cfg1, fs)
+    assert np.allclose(reg, feq, rtol=0, atol=1e-15)
+    assert np.allclose(bgk, feq + om * 0.05 * delta, rtol=0, atol=1e-15)
+
+
+def test_bgk_conserves_mass_and_adds_rho_g():
+    cfg = small_cfg(lattice=19, lb_ratio=1, lb_collision=1, ma=0.3, kn=0.1)
+    d = O.derive(cfg)
+    e, w, r = O.lattice(19)
+    fs = W.gen_populations(w, 1, seed=3)[:, 0]
+    out = O.lbm_collide(cfg, fs)
+    xi = e * r
+    assert out.sum() == pytest.approx(fs.sum(), rel=1e-14)
+    j0, j1 = fs @ xi, out @ xi
+    assert np.allclose(j1 - j0, [0, fs.sum() * d["g_step"], 0], atol=1e-15)
+
+
+def test_equilibrium_dsmc2lb_is_eq_feq_dsmc_for_any_stress():
+    # Sec. 4, Eq. feq_dsmc (lattice units, c_s^2 = 1/3): the populations depend on rho and u
+    # only, whatever the sample's stress and heat flux; the Grad mapping does not.
+    cfg = small_cfg(lattice=19, lb_ratio=1, d2l_mode=1)
+    rng = np.random.default_rng(6)
+    rho, uH = 0.98, np.array([0.02, 0.11, -0.04])
+    A = rng.normal(0, 0.1, (3, 3))
+    P = np.eye(3) + np.outer(uH, uH) + (A + A.T) / 2
+    B = rng.normal(0, 0.1, (3, 3, 3))
+    Q = sum(np.transpose(B, p) for p in itertools.permutations(range(3))) / 6
+    S, ppc = 7, cfg["ppc"]
+    sums = _sums_from_coeffs(rho, uH, P, Q, S, ppc)
+    out = {}
+    for mode in (1, 0):
+        o = O.Oracle(dict(cfg, d2l_mode=mode))
+        acc = o.acc().copy()
+        acc[5] = sums
+        o.set(O.A_ACC, acc.reshape(-1))
+        o.set_scalars(o.scalars()["step"], S)
+        o.map_dsmc_to_lbm(np.array([5], np.int32))
+        out[mode] = o.f().reshape(19, -1)[:, 5]
+    e, w, r = O.lattice(19)
+    u_lat = uH / r
+    cs2 = 1.0 / 3.0
+    eu = e @ u_lat
+    feq = w * rho * (1 + eu / cs2 + eu ** 2 / (2 * cs2 ** 2) - (u_lat @ u_lat) / (2 * cs2))
+    assert np.allclose(out[1], feq, rtol=1e-13, atol=1e-16)
+    assert np.abs(out[0] - feq).max() > 1e-4
