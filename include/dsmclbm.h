@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define HYB_ABI_VERSION 2u
+#define HYB_ABI_VERSION 3u
 
 typedef enum {
     HYB_OK = 0,
@@ -90,6 +90,12 @@ typedef struct {
                                at most 256 */
     double T_K;             /* temperature [K], for SI conversion only */
     double mass_kg;         /* molecular mass [kg], for SI conversion only */
+    int32_t lb_collision;   /* 0: regularised BGK (Sec. 2); 1: plain BGK, f' = f_eq +
+                               (1 - 1/tau)(f - f_eq) + (1 - 1/(2 tau)) F, the LB model of the
+                               proof-of-concept hybrid (Sec. 4) */
+    int32_t d2l_mode;       /* 0: DSMC2LB to the lattice's Hermite order from rho, u, P, Q
+                               (Sec. 2.1); 1: the local equilibrium from rho and u only
+                               (Sec. 4, Eq. feq_dsmc; to order 3 on D3Q39) */
 } hyb_params;
 
 /* Constants derived from hyb_params (hyb_derive). */
@@ -239,7 +245,8 @@ hyb_status lbm_interface_loss(hyb_ctx* ctx, const void* f, const int32_t* dev_no
 /* One step of the adjoint: with f the populations at step t and lam_next = dL/df_{t+1},
  * writes lam = dL/df_t (every entry) and adds dL/dg and dL/dtau of this step to grad_g and
  * grad_tau. wall is a scratch of 2 * ny values that must be zero before the first call; it
- * is left zero. lam and lam_next must differ. */
+ * is left zero. lam and lam_next must differ. The adjoint is that of the regularised
+ * collision: a context with lb_collision = 1 returns HYB_EINVAL. */
 hyb_status lbm_adjoint_step(hyb_ctx* ctx, const void* f, const void* lam_next, void* lam,
                             const void* g_node, const void* tau_node, void* grad_g,
                             void* grad_tau, void* wall);

@@ -11,7 +11,7 @@ import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "libdsmclbm.so")
-ABI_VERSION = 2
+ABI_VERSION = 3
 
 HYB_OK, HYB_EINVAL, HYB_ENOMEM, HYB_ECUDA, HYB_ECAPACITY, HYB_ETIMEOUT, HYB_ESAMPLING, HYB_ESTATE = range(8)
 ST_CAPACITY, ST_BOUNCE_CAP, ST_SCATTER_CAP, ST_SAMPLING_CAP, ST_CELL_OVERFLOW, ST_BAD_INPUT = (
@@ -30,7 +30,8 @@ class HybParams(ctypes.Structure):
     _fields_ = [("abi_version", _u32), ("ncx", _i32), ("ncy", _i32), ("lb_ratio", _i32),
                 ("ppc", _i32), ("lattice", _i32), ("real_bytes", _i32), ("sample_every", _i32),
                 ("seed", _u64), ("kn", _dbl), ("ma", _dbl), ("crmax_init", _dbl),
-                ("capacity_factor", _dbl), ("T_K", _dbl), ("mass_kg", _dbl)]
+                ("capacity_factor", _dbl), ("T_K", _dbl), ("mass_kg", _dbl),
+                ("lb_collision", _i32), ("d2l_mode", _i32)]
 
 
 class HybDerived(ctypes.Structure):

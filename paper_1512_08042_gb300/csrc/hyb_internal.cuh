@@ -121,6 +121,7 @@ struct LbmArgs {
     // plain step
     const Real* g_node;
     const Real* tau_node;
+    int32_t bgk;  // 1: unregularised BGK collision (lb_collision)
 };
 
 // One step of the adjoint of the LBM with per-node parameters: lam_next = dL/df_{t+1} in,
@@ -146,6 +147,7 @@ struct MapArgs {
     int32_t nx, ny, ncx, ncy, lb_ratio, ppc, n, bin;
     int64_t nnodes;
     const int32_t* list;
+    int32_t eq_mode;  // DSMC2LB: 1 the local equilibrium of rho, u only (d2l_mode)
     double r_lat;
     uint64_t seed;
     const double* acc;

@@ -159,8 +159,10 @@ __device__ __forceinline__ void node_moments(const Real (&fs)[LAT::Q], Real& rho
 }
 
 // One node of one context; PARAM: the force increment and relaxation time of the node come
-// from the per-node arrays.
-template <typename Real, class LAT, bool PARAM>
+// from the per-node arrays. BGK: the unregularised collision of the proof-of-concept hybrid
+// (Sec. 4), f' = (1 - om) f_eq + om f + of F: the series then carries (1 - om) times the
+// equilibrium coefficients plus the force, and om f is added per population.
+template <typename Real, class LAT, bool PARAM, bool BGK = false>
 __device__ __forceinline__ void lbm_node(const LbmArgs<Real>& a, const int64_t node) {
     constexpr int Q = LAT::Q;
     constexpr double R = lat_r<LAT>();
@@ -185,16 +187,20 @@ __device__ __forceinline__ void lbm_node(const LbmArgs<Real>& a, const int64_t n
     const Real ux = jx * inv_rho, uy = (jy + (Real)0.5 * rho * gy) * inv_rho, uz = jz * inv_rho;
     const Real a1y = (Real)-0.5 * rho * gy;  // H1 part of f_neq
     const Real rg = rho * gy;
-    // combined coefficients of the post-collision series
-    const Real A0 = rho;
-    const Real A1x = rho * ux, A1y = rho * uy + om * a1y + of * rg, A1z = rho * uz;
+    // combined coefficients of the post-collision series (BGK: the equilibrium weighted by
+    // ke = 1 - om and no projected non-equilibrium part, om_r = 0)
+    const Real ke = BGK ? (Real)1 - om : (Real)1;
+    const Real omr = BGK ? (Real)0 : om;
+    const Real rk = ke * rho;
+    const Real A0 = rk;
+    const Real A1x = rk * ux, A1y = rk * uy + omr * a1y + of * rg, A1z = rk * uz;
     // a2 = Pi - rho (uu + I); A2 = rho uu + om a2 + of rho (gu + ug)
-    const Real Axx = rho * ux * ux + om * (pxx - rho * (ux * ux + (Real)1));
-    const Real Ayy = rho * uy * uy + om * (pyy - rho * (uy * uy + (Real)1)) + of * (Real)2 * rg * uy;
-    const Real Azz = rho * uz * uz + om * (pzz - rho * (uz * uz + (Real)1));
-    const Real Axy = rho * ux * uy + om * (pxy - rho * ux * uy) + of * rg * ux;
-    const Real Axz = rho * ux * uz + om * (pxz - rho * ux * uz);
-    const Real Ayz = rho * uy * uz + om * (pyz - rho * uy * uz) + of * rg * uz;
+    const Real Axx = rk * ux * ux + omr * (pxx - rho * (ux * ux + (Real)1));
+    const Real Ayy = rk * uy * uy + omr * (pyy - rho * (uy * uy + (Real)1)) + of * (Real)2 * rg * uy;
+    const Real Azz = rk * uz * uz + omr * (pzz - rho * (uz * uz + (Real)1));
+    const Real Axy = rk * ux * uy + omr * (pxy - rho * ux * uy) + of * rg * ux;
+    const Real Axz = rk * ux * uz + omr * (pxz - rho * ux * uz);
+    const Real Ayz = rk * uy * uz + omr * (pyz - rho * uy * uz) + of * rg * uz;
     const Real tr2 = Axx + Ayy + Azz;
     const Real E0 = A0 - (Real)0.5 * tr2;  // even part without the xi xi terms
     // a3 = Qm - rho(uuu + sym(u I)) - sym(a1 I); A3 = rho uuu + om a3 + of rho sym(guu)
@@ -211,16 +217,16 @@ __device__ __forceinline__ void lbm_node(const LbmArgs<Real>& a, const int64_t n
         const Real c7 = q3[7] - rho * (uy * uy * uz + uz);
         const Real c8 = q3[8] - rho * (uy * uz * uz + uy) - a1y;
         const Real c9 = q3[9] - rho * (uz * uz * uz + (Real)3 * uz);
-        B3[0] = rho * ux * ux * ux + om * c0;
-        B3[1] = rho * ux * ux * uy + om * c1 + of * rg * ux * ux;
-        B3[2] = rho * ux * ux * uz + om * c2;
-        B3[3] = rho * ux * uy * uy + om * c3 + of * (Real)2 * rg * ux * uy;
-        B3[4] = rho * ux * uy * uz + om * c4 + of * rg * ux * uz;
-        B3[5] = rho * ux * uz * uz + om * c5;
-        B3[6] = rho * uy * uy * uy + om * c6 + of * (Real)3 * rg * uy * uy;
-        B3[7] = rho * uy * uy * uz + om * c7 + of * (Real)2 * rg * uy * uz;
-        B3[8] = rho * uy * uz * uz + om * c8 + of * rg * uz * uz;
-        B3[9] = rho * uz * uz * uz + om * c9;
+        B3[0] = rk * ux * ux * ux + omr * c0;
+        B3[1] = rk * ux * ux * uy + omr * c1 + of * rg * ux * ux;
+        B3[2] = rk * ux * ux * uz + omr * c2;
+        B3[3] = rk * ux * uy * uy + omr * c3 + of * (Real)2 * rg * ux * uy;
+        B3[4] = rk * ux * uy * uz + omr * c4 + of * rg * ux * uz;
+        B3[5] = rk * ux * uz * uz + omr * c5;
+        B3[6] = rk * uy * uy * uy + omr * c6 + of * (Real)3 * rg * uy * uy;
+        B3[7] = rk * uy * uy * uz + omr * c7 + of * (Real)2 * rg * uy * uz;
+        B3[8] = rk * uy * uz * uz + omr * c8 + of * rg * uz * uz;
+        B3[9] = rk * uz * uz * uz + omr * c9;
         t3x = B3[0] + B3[3] + B3[5];
         t3y = B3[1] + B3[6] + B3[8];
         t3z = B3[2] + B3[7] + B3[9];
@@ -231,7 +237,10 @@ __device__ __forceinline__ void lbm_node(const LbmArgs<Real>& a, const int64_t n
         constexpr int q = decltype(qc)::value;
         constexpr int p = opp<LAT>(q);
         if constexpr (q == 0) {
-            dst[0] = (Real)W<LAT>(0) * E0;
+            if constexpr (BGK)
+                dst[0] = (Real)W<LAT>(0) * E0 + om * fs[0];
+            else
+                dst[0] = (Real)W<LAT>(0) * E0;
         } else if constexpr (q < p) {
             constexpr int ex = E<LAT>(q, 0), ey = E<LAT>(q, 1), ez = E<LAT>(q, 2);
             constexpr double X = R * ex, Y = R * ey, Z = R * ez;
@@ -263,8 +272,13 @@ __device__ __forceinline__ void lbm_node(const LbmArgs<Real>& a, const int64_t n
                 if constexpr (ez != 0) od += (Real)(s6 * Z * Z * Z) * B3[9] - (Real)(0.5 * Z) * t3z;
             }
             constexpr double wq = W<LAT>(q);
-            dst[(int64_t)q * nn] = (Real)wq * (ev + od);
-            dst[(int64_t)p * nn] = (Real)wq * (ev - od);
+            if constexpr (BGK) {
+                dst[(int64_t)q * nn] = (Real)wq * (ev + od) + om * fs[q];
+                dst[(int64_t)p * nn] = (Real)wq * (ev - od) + om * fs[p];
+            } else {
+                dst[(int64_t)q * nn] = (Real)wq * (ev + od);
+                dst[(int64_t)p * nn] = (Real)wq * (ev - od);
+            }
         }
     });
 }
@@ -277,9 +291,16 @@ __global__ void __launch_bounds__(128) k_lbm(Launch<LbmArgs<Real>> L) {
     if (u >= L.total) return;
     if constexpr (BATCH) {
         const int r = replica_of(L.pre, L.nrep, u);
-        lbm_node<Real, LAT, false>(L.tab[r], u - L.pre[r]);
+        const LbmArgs<Real>& a = L.tab[r];
+        if (a.bgk)
+            lbm_node<Real, LAT, false, true>(a, u - L.pre[r]);
+        else
+            lbm_node<Real, LAT, false>(a, u - L.pre[r]);
     } else {
-        lbm_node<Real, LAT, false>(L.one, u);
+        if (L.one.bgk)
+            lbm_node<Real, LAT, false, true>(L.one, u);
+        else
+            lbm_node<Real, LAT, false>(L.one, u);
     }
 }
 
@@ -287,7 +308,12 @@ __global__ void __launch_bounds__(128) k_lbm(Launch<LbmArgs<Real>> L) {
 template <typename Real, class LAT>
 __global__ void __launch_bounds__(128) k_lbm_param(LbmArgs<Real> a) {
     const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (u < a.nnodes) lbm_node<Real, LAT, true>(a, u);
+    if (u < a.nnodes) {
+        if (a.bgk)
+            lbm_node<Real, LAT, true, true>(a, u);
+        else
+            lbm_node<Real, LAT, true>(a, u);
+    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -673,6 +699,9 @@ LbmArgs<Real> lbm_args(const Ctx& c, int cur_f) {
     a.om = (Real)(1.0 - 1.0 / c.d.tau);
     a.of = (Real)(1.0 - 0.5 / c.d.tau);
     a.g_step = (Real)c.d.g_step;
+    a.g_node = nullptr;
+    a.tau_node = nullptr;
+    a.bgk = c.p.lb_collision;
     return a;
 }
 

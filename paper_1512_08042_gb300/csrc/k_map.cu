@@ -122,7 +122,19 @@ __device__ __forceinline__ void d2l_entries(const MapArgs<Real>& a, int first, i
             case 19: sub = (Real)3 * m1z; break;                // zzz
             default: break;
         }
-        const Real coef = lane == 0 ? rho : rho * (mr - sub);
+        Real coef = lane == 0 ? rho : rho * (mr - sub);
+        if (a.eq_mode && lane >= 4u && lane < (unsigned)kMoments) {
+            // the local equilibrium of rho and u (Sec. 4, Eq. feq_dsmc): a2 = rho u u,
+            // a3 = rho u u u
+            constexpr int I[16][3] = {{0, 0, -1}, {0, 1, -1}, {0, 2, -1}, {1, 1, -1}, {1, 2, -1},
+                                      {2, 2, -1}, {0, 0, 0}, {0, 0, 1}, {0, 0, 2}, {0, 1, 1},
+                                      {0, 1, 2}, {0, 2, 2}, {1, 1, 1}, {1, 1, 2}, {1, 2, 2},
+                                      {2, 2, 2}};
+            const Real uu[3] = {m1x, m1y, m1z};
+            const int* ix = I[lane - 4u];
+            coef = rho * uu[ix[0]] * uu[ix[1]];
+            if (ix[2] >= 0) coef = coef * uu[ix[2]];
+        }
         Real cf[kMoments];
 #pragma unroll
         for (int k = 0; k < kMoments; ++k) cf[k] = __shfl_sync(kFull, coef, k);
@@ -531,6 +543,7 @@ MapArgs<Real> map_args(Ctx& c, const int32_t* list, int32_t n) {
     a.bin = c.d.bin;
     a.nnodes = c.d.nnodes;
     a.list = list;
+    a.eq_mode = c.p.d2l_mode;
     a.r_lat = c.d.r_lat;
     a.seed = c.p.seed;
     a.acc = c.st.acc;

@@ -21,6 +21,8 @@ bool params_valid(const hyb_params* p) {
     if (p->lattice != 39 && p->lattice != 19) return false;
     if (p->real_bytes != 4 && p->real_bytes != 8) return false;
     if (p->sample_every < 1) return false;
+    if ((p->lb_collision != 0 && p->lb_collision != 1) || (p->d2l_mode != 0 && p->d2l_mode != 1))
+        return false;
     if (!(p->kn > 0.0) || !(p->crmax_init > 0.0) || !(p->capacity_factor >= 1.0)) return false;
     if (!(p->ma >= 0.0) || !(p->T_K > 0.0) || !(p->mass_kg > 0.0)) return false;
     if (std::ceil(p->capacity_factor * (double)p->ppc) > 256.0) return false;  // bin <= 256
@@ -363,7 +365,7 @@ hyb_status lbm_adjoint_step(hyb_ctx* h, const void* f, const void* lam_next, voi
                             const void* g_node, const void* tau_node, void* grad_g,
                             void* grad_tau, void* wall) {
     if (!h || !f || !lam_next || !lam || lam == lam_next || !g_node || !tau_node || !grad_g ||
-        !grad_tau || !wall)
+        !grad_tau || !wall || h->c.p.lb_collision != 0)
         return HYB_EINVAL;
     return check(h->c, launch_lbm_adjoint_step(h->c, f, lam_next, lam, g_node, tau_node, grad_g,
                                                grad_tau, wall),

@@ -33,6 +33,13 @@ WORKLOADS = {
     # 1024 x 8192 D3Q39 lattice.
     "poiseuille_512x4096_ppc50_fp32": config(ncx=512, ncy=4096, ppc=50, lb_ratio=2, kn=0.05,
                                               seed=5),
+    # The proof-of-concept hybrid of Sec. 4: plane Poiseuille at Kn 0.05 and Ma 0.1, D3Q19
+    # without regularisation, DSMC2LB to the local equilibrium of rho and u (Eq. feq_dsmc)
+    # on a buffer layer one cell long at y = L0/2 across the whole height, DSMC solved on its
+    # own (no LB2DSMC). The channel sizes are not printed: 64 x 64 cells, 50 per cell, FP64.
+    "poc_hybrid_64x64_d3q19_fp64": config(ncx=64, ncy=64, ppc=50, lattice=19, lb_ratio=1,
+                                           kn=0.05, ma=0.1, real_bytes=8, lb_collision=1,
+                                           d2l_mode=1, coupling="buffer_row", seed=4),
 }
 
 
@@ -83,6 +90,11 @@ def coupling_sites(cfg, strip_cells=None):
     """
     ncx, ncy, r = cfg["ncx"], cfg["ncy"], cfg["lb_ratio"]
     nx = ncx * r
+    if cfg.get("coupling") == "buffer_row":
+        # the buffer layer of Sec. 4: the LB nodes of the cell row at y = L0/2, DSMC2LB only
+        y0 = (ncy // 2) * r
+        nodes = np.array([y * nx + x for y in range(y0, y0 + r) for x in range(nx)], np.int32)
+        return nodes, np.zeros(0, np.int32)
     if ncy == 1:
         cells = np.array([1, ncx - 2], np.int32)
         nodes = []

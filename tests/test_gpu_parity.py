@@ -319,3 +319,75 @@ def test_status_on_capacity_overflow_and_bad_index():
     h2.map_dsmc_to_lbm(torch.tensor([10 ** 6], dtype=torch.int32, device="cuda"))
     rc, bits = h2.sync_status()
     assert rc == B.HYB_EINVAL and bits & B.ST_BAD_INPUT
+
+
+# ---------------------------------------------------------------------------------------
+# The proof-of-concept hybrid of Sec. 4: unregularised BGK, equilibrium DSMC2LB
+
+@pytest.mark.parametrize("lattice,real_bytes", [(19, 4), (19, 8), (39, 8)])
+def test_lbm_bgk_steps_match_oracle(lattice, real_bytes):
+    cfg = cfg_small(lattice=lattice, real_bytes=real_bytes, lb_ratio=2, ma=0.5, kn=0.3,
+                    lb_collision=1)
+    h = B.Hybrid(cfg)
+    o = O.Oracle(cfg)
+    e, w, r = O.lattice(lattice)
+    f0 = W.gen_populations(w, h.d["nnodes"], seed=23).astype(np.float32 if real_bytes == 4 else np.float64)
+    h.f().copy_(torch.from_numpy(f0.reshape(h.f().shape)))
+    torch.cuda.synchronize()
+    o.set_f(f0)
+    for step in range(3):
+        h.lbm_step(1)
+        o.lbm_step(1)
+        h.sync()
+        gf, of = h.f().cpu().numpy(), o.f()
+        err = np.abs(gf - of) / (np.abs(of) + 1e-3 * w[:, None, None])
+        assert err.max() < (2e-5 if real_bytes == 4 else 1e-12), (step, err.max())
+    # differs from the regularised step (the ghost modes of the perturbed state survive)
+    cfg_r = dict(cfg, lb_collision=0)
+    o2 = O.Oracle(cfg_r)
+    o2.set_f(f0)
+    o2.lbm_step(3)
+    assert np.abs(o2.f() - o.f()).max() > 1e-6
+
+
+@pytest.mark.parametrize("lattice", [19, 39])
+def test_dsmc2lb_equilibrium_mode_matches_oracle(lattice):
+    cfg = cfg_small(lattice=lattice, lb_ratio=1, real_bytes=8, d2l_mode=1)
+    h = B.Hybrid(cfg)
+    o = O.Oracle(cfg)
+    rng = np.random.default_rng(31)
+    n = h.d["ncells"]
+    S = 9
+    acc = np.zeros((n, 20))
+    for c in range(n):
+        v = rng.standard_normal((cfg["ppc"] * S, 3)) * (1 + 0.2 * rng.random(3)) + 0.1 * rng.standard_normal(3)
+        m = [np.ones(len(v))] + [v[:, i] for i in range(3)]
+        m += [v[:, i] * v[:, j] for i in range(3) for j in range(i, 3)]
+        m += [v[:, i] * v[:, j] * v[:, k] for i in range(3) for j in range(i, 3) for k in range(j, 3)]
+        acc[c] = [x.sum() for x in m]
+    _set_acc(h, o, acc, S)
+    nodes = np.arange(0, h.d["nnodes"], 3, dtype=np.int32)
+    h.map_dsmc_to_lbm(torch.from_numpy(nodes).cuda())
+    o.map_dsmc_to_lbm(nodes)
+    h.sync()
+    assert np.allclose(h.f().cpu().numpy(), o.f(), rtol=1e-12, atol=1e-15)
+
+
+def test_proof_of_concept_hybrid_steps_match_oracle():
+    # Sec. 4 at a reduced size: D3Q19 without regularisation, equilibrium DSMC2LB on the
+    # buffer row at y = L0/2, no LB2DSMC; FP64, four hybrid steps
+    cfg = W.config(ncx=12, ncy=8, ppc=30, lattice=19, lb_ratio=1, kn=0.05, ma=0.1, real_bytes=8,
+                   lb_collision=1, d2l_mode=1, coupling="buffer_row", seed=4)
+    nodes, cells = W.coupling_sites(cfg)
+    assert len(cells) == 0 and len(nodes) == cfg["ncx"]
+    h = B.Hybrid(cfg)
+    o = O.Oracle(cfg)
+    dn, dc = torch.from_numpy(nodes).cuda(), torch.from_numpy(cells).cuda()
+    for _ in range(4):
+        h.hybrid_step(dn, dc, nsteps=1, use_graph=False)
+        o.dsmc_step(1)
+        o.map_dsmc_to_lbm(nodes)
+        o.lbm_step(1)
+    _compare_dsmc(h, o, 8)
+    h.sync()
+    assert np.allclose(h.f().cpu().numpy(), o.f(), rtol=1e-11, atol=1e-14)
