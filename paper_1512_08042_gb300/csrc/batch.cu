@@ -79,7 +79,9 @@ uint64_t table_layout(int n, int real_bytes, hyb_batch* b) {
 
 bool same_kind(const hyb_params* p, int n) {
     for (int r = 1; r < n; ++r)
-        if (p[r].real_bytes != p[0].real_bytes || p[r].lattice != p[0].lattice) return false;
+        if (p[r].real_bytes != p[0].real_bytes || p[r].lattice != p[0].lattice ||
+            p[r].lb_collision != p[0].lb_collision)
+            return false;
     return true;
 }
 
@@ -224,6 +226,7 @@ hyb_status hyb_batch_init(const hyb_params* p, int32_t n, void* arena, uint64_t 
     d.nrep = n;
     d.real_bytes = p[0].real_bytes;
     d.lattice = p[0].lattice;
+    d.lb_collision = p[0].lb_collision;
     d.stream = b->stream;
     d.num_sms = b->reps[0]->c.num_sms;
     b->cur_p = b->reps[0]->c.cur_p;

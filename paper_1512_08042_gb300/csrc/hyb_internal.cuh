@@ -466,6 +466,7 @@ cudaError_t launch_debug_philox(const uint32_t* ctr, uint64_t seed, uint32_t* ou
 struct BatchDev {
     int32_t nrep = 0;
     int32_t real_bytes = 4, lattice = 39;
+    int32_t lb_collision = 0;  // one collision for all replicas
     int num_sms = 152;
     cudaStream_t stream = nullptr;
     const void* dsmc[2] = {nullptr, nullptr};               // DsmcArgs<Real>[nrep], by particle half

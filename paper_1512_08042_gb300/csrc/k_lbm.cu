@@ -283,37 +283,26 @@ __device__ __forceinline__ void lbm_node(const LbmArgs<Real>& a, const int64_t n
     });
 }
 
-// One thread per node (the nodes of all replicas in the batch form).
-template <typename Real, class LAT, bool BATCH>
+// One thread per node (the nodes of all replicas in the batch form); BGK selects the
+// unregularised collision (one instantiation per collision keeps each one's registers).
+template <typename Real, class LAT, bool BATCH, bool BGK = false>
 __global__ void __launch_bounds__(128) k_lbm(Launch<LbmArgs<Real>> L) {
     pdl_begin();
     const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (u >= L.total) return;
     if constexpr (BATCH) {
         const int r = replica_of(L.pre, L.nrep, u);
-        const LbmArgs<Real>& a = L.tab[r];
-        if (a.bgk)
-            lbm_node<Real, LAT, false, true>(a, u - L.pre[r]);
-        else
-            lbm_node<Real, LAT, false>(a, u - L.pre[r]);
+        lbm_node<Real, LAT, false, BGK>(L.tab[r], u - L.pre[r]);
     } else {
-        if (L.one.bgk)
-            lbm_node<Real, LAT, false, true>(L.one, u);
-        else
-            lbm_node<Real, LAT, false>(L.one, u);
+        lbm_node<Real, LAT, false, BGK>(L.one, u);
     }
 }
 
 // One thread per node, with per-node force increment and relaxation time.
-template <typename Real, class LAT>
+template <typename Real, class LAT, bool BGK>
 __global__ void __launch_bounds__(128) k_lbm_param(LbmArgs<Real> a) {
     const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (u < a.nnodes) {
-        if (a.bgk)
-            lbm_node<Real, LAT, true, true>(a, u);
-        else
-            lbm_node<Real, LAT, true>(a, u);
-    }
+    if (u < a.nnodes) lbm_node<Real, LAT, true, BGK>(a, u);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -713,7 +702,9 @@ cudaError_t lbm_impl(Ctx& c) {
     Launch<LbmArgs<Real>> L{};
     L.one = a;
     L.total = c.d.nnodes;
-    const cudaError_t e = launch_pdl(k_lbm<Real, LAT, false>, dim3((unsigned)blocks), dim3(128), 0, c.stream, L);
+    const cudaError_t e =
+        a.bgk ? launch_pdl(k_lbm<Real, LAT, false, true>, dim3((unsigned)blocks), dim3(128), 0, c.stream, L)
+              : launch_pdl(k_lbm<Real, LAT, false>, dim3((unsigned)blocks), dim3(128), 0, c.stream, L);
     prof_end(c, K_LBM);
     return e;
 }
@@ -737,7 +728,10 @@ cudaError_t lbm_nodes_impl(Ctx& c, const void* f_src, void* f_dst, const void* g
     a.g_node = (const Real*)g;
     a.tau_node = (const Real*)tau;
     const int64_t blocks = (c.d.nnodes + 127) / 128;
-    k_lbm_param<Real, LAT><<<(unsigned)blocks, 128, 0, c.stream>>>(a);
+    if (a.bgk)
+        k_lbm_param<Real, LAT, true><<<(unsigned)blocks, 128, 0, c.stream>>>(a);
+    else
+        k_lbm_param<Real, LAT, false><<<(unsigned)blocks, 128, 0, c.stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -797,6 +791,9 @@ cudaError_t batch_lbm_impl(BatchDev& b, int cur_f) {
     L.nrep = b.nrep;
     L.total = b.tot_nodes;
     const int64_t blocks = (b.tot_nodes + b.lbm_block - 1) / b.lbm_block;
+    if (b.lb_collision)
+        return launch_pdl(k_lbm<Real, LAT, true, true>, dim3((unsigned)blocks), dim3(b.lbm_block), 0,
+                          b.stream, L);
     return launch_pdl(k_lbm<Real, LAT, true>, dim3((unsigned)blocks), dim3(b.lbm_block), 0, b.stream, L);
 }
 }  // namespace
