@@ -75,7 +75,8 @@ bool valid(const Params* p) {
            p->ppc >= 1 && (p->lattice == 39 || p->lattice == 19) &&
            (p->real_bytes == 4 || p->real_bytes == 8) && p->sample_every >= 1 && p->kn > 0.0 &&
            p->capacity_factor >= 1.0 && std::ceil(p->capacity_factor * p->ppc) <= 256.0 &&
-           (p->lb_collision == 0 || p->lb_collision == 1) && (p->d2l_mode == 0 || p->d2l_mode == 1);
+           (p->lb_collision == 0 || p->lb_collision == 1) && (p->d2l_mode == 0 || p->d2l_mode == 1) &&
+           (p->kn_profile == 0 || (p->kn_profile == 1 && p->kn_end > 0.0));
 }
 
 }  // namespace

@@ -43,6 +43,9 @@ struct Params {
     double mass_kg;        // molecular mass [kg], SI reporting only
     int32_t lb_collision;  // 0 regularised BGK (Sec. 2), 1 plain BGK (Sec. 4)
     int32_t d2l_mode;      // 0 Grad to the lattice order (Sec. 2.1), 1 equilibrium (Eq. feq_dsmc)
+    int32_t kn_profile;    // 1: Kn varies along the channel (kn_at)
+    int32_t pad0;
+    double kn_end;         // Kn at y = ncy / 2 when kn_profile = 1
 };
 
 // Derived constants. Field order is a binary interface with oracle.py.
@@ -89,6 +92,15 @@ inline Derived derive(const Params& p) {
     d.q = p.lattice;
     d.order = (p.lattice == 39) ? 3 : 2;
     return d;
+}
+
+// Kn along the channel when kn_profile = 1: log-linear in the streamwise coordinate y (DSMC
+// cell units, period ncy) from kn at y = 0 to kn_end at y = ncy / 2 and back,
+// Kn(y) = kn (kn_end / kn)^s with s = 1 - |2 y / ncy - 1|. A DSMC cell takes the NTC factor
+// of Eq. collisionnumber at its centre's Kn, an LB node the tau of Eq. tau at its own.
+inline double kn_at(const Params& p, double y) {
+    const double s = 1.0 - std::fabs(2.0 * y / (double)p.ncy - 1.0);
+    return p.kn * std::exp(s * std::log(p.kn_end / p.kn));
 }
 
 // ---------------------------------------------------------------------------------------

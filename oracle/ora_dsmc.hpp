@@ -43,6 +43,7 @@ struct Dsmc {
     // Per-cell collision state of the NTC scheme.
     std::vector<Real> crmax;           // (sigma_T c_r)_max / sigma_T
     std::vector<Real> rem;             // fractional candidate carried to the next step
+    std::vector<double> coll_cell;     // per-cell NTC factor (kn_profile = 1), else empty
     std::vector<uint32_t> nbar_sum;    // sum of N over steps, for N-bar = <N>
     // Cumulative sums for the DSMC2LB mapping (Sec. 2.1 "cumulative averages"):
     // [N, S vx, vy, vz, S vv (xx xy xz yy yz zz), S vvv (xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz)]
@@ -79,6 +80,14 @@ struct Dsmc {
         cell_start[d.ncells] = (uint32_t)n;
         crmax.assign(d.ncells, (Real)p.crmax_init);
         rem.assign(d.ncells, (Real)0);
+        coll_cell.clear();
+        if (p.kn_profile == 1) {  // Eq. collisionnumber at each cell centre's Kn
+            coll_cell.resize((size_t)d.ncells);
+            for (int64_t c = 0; c < d.ncells; ++c) {
+                const double kn = kn_at(p, (double)(c / p.ncx) + 0.5);
+                coll_cell[(size_t)c] = d.dt / (std::sqrt(2.0) * (kn * (double)p.ncx) * (double)p.ppc);
+            }
+        }
         nbar_sum.assign(d.ncells, 0u);
         acc.assign(d.ncells * kNumMoments, 0.0);
         step = 0;
@@ -214,7 +223,8 @@ struct Dsmc {
         nbar_sum[c] += n;
         const Real nbar = (Real)nbar_sum[c] / (Real)(s + 1);
         if (n < 2) return;
-        const Real ncand = (Real)0.5 * (Real)n * nbar * crmax[c] * (Real)d.coll_dt + rem[c];
+        const Real cdt = (Real)(coll_cell.empty() ? d.coll_dt : coll_cell[c]);
+        const Real ncand = (Real)0.5 * (Real)n * nbar * crmax[c] * cdt + rem[c];
         const Real nsel_d = std::floor(ncand);
         rem[c] = ncand - nsel_d;
         uint64_t nsel = (uint64_t)nsel_d;

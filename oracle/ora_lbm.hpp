@@ -43,6 +43,16 @@ struct Lbm {
         f.assign((size_t)L.q * d.nnodes, 0);
         for (int a = 0; a < L.q; ++a)
             for (int64_t n = 0; n < d.nnodes; ++n) f[(size_t)a * d.nnodes + n] = (Real)L.w[a];
+        g_node.clear();
+        tau_node.clear();
+        if (p.kn_profile == 1) {  // tau of Eq. tau at each node's Kn, the force of kn
+            g_node.assign((size_t)d.nnodes, d.g_step);
+            tau_node.resize((size_t)d.nnodes);
+            for (int64_t n = 0; n < d.nnodes; ++n) {
+                const double kn = kn_at(p, ((double)(n / d.nx) + 0.5) / (double)p.lb_ratio);
+                tau_node[(size_t)n] = std::sqrt(kPi / 8.0) * d.r_lat * kn * d.H_lat + 0.5;
+            }
+        }
     }
 
     double fa(int a, int64_t x, int64_t y) const {

@@ -39,6 +39,9 @@ class Params(ctypes.Structure):
         ("mass_kg", ctypes.c_double),
         ("lb_collision", ctypes.c_int32),
         ("d2l_mode", ctypes.c_int32),
+        ("kn_profile", ctypes.c_int32),
+        ("pad0", ctypes.c_int32),
+        ("kn_end", ctypes.c_double),
     ]
 
 

@@ -876,3 +876,41 @@ def test_equilibrium_dsmc2lb_is_eq_feq_dsmc_for_any_stress():
     feq = w * rho * (1 + eu / cs2 + eu ** 2 / (2 * cs2 ** 2) - (u_lat @ u_lat) / (2 * cs2))
     assert np.allclose(out[1], feq, rtol=1e-13, atol=1e-16)
     assert np.abs(out[0] - feq).max() > 1e-4
+
+
+# ---------------------------------------------------------------------------------------
+# Kn varying along the channel
+
+def test_kn_profile_at_constant_kn_is_the_plain_run():
+    cfg = small_cfg(ncx=12, ncy=6, ppc=20, lb_ratio=2, ma=0.3)
+    a = O.Oracle(cfg)
+    b = O.Oracle(dict(cfg, kn_profile=1, kn_end=cfg["kn"]))
+    for o in (a, b):
+        o.dsmc_step(3)
+        o.lbm_step(3)
+    for k in ("x", "y", "vx", "vy", "vz"):
+        assert np.array_equal(a.particles()[k], b.particles()[k])
+    assert np.array_equal(a.f(), b.f())
+    assert a.counters() == b.counters()
+
+
+def test_kn_profile_collision_rate_follows_the_local_mean_free_path():
+    # Equilibrium box with Kn from 0.04 (y = 0) to 0.4 (y = L/2): the collisions per step are
+    # the hard-sphere rate 1/2 N <c> dt / lambda(y) summed over the cells, lambda(y) the
+    # local mean free path, not the rate of any single Kn.
+    cfg = small_cfg(ncx=24, ncy=16, ppc=40, ma=0.0, kn=0.04, kn_profile=1, kn_end=0.4,
+                    crmax_init=5.0)
+    o = O.Oracle(cfg)
+    d = o.d
+    o.dsmc_step(20)
+    c0 = o.counters()["collisions"]
+    steps = 150
+    o.dsmc_step(steps)
+    got = (o.counters()["collisions"] - c0) / steps
+    ys = np.arange(16) + 0.5
+    s = 1 - np.abs(2 * ys / 16 - 1)
+    kn = 0.04 * (0.4 / 0.04) ** s
+    want = sum(0.5 * 24 * 40 * math.sqrt(8 / math.pi) / (k * 24) * d["dt"] for k in kn)
+    assert abs(got - want) < 4 * math.sqrt(want / steps) + 0.01 * want
+    plain = 0.5 * 24 * 16 * 40 * math.sqrt(8 / math.pi) / d["lam"] * d["dt"]
+    assert want < 0.6 * plain  # the profile's rate is far from the rate at kn
