@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define HYB_ABI_VERSION 3u
+#define HYB_ABI_VERSION 4u
 
 typedef enum {
     HYB_OK = 0,
@@ -96,6 +96,15 @@ typedef struct {
     int32_t d2l_mode;       /* 0: DSMC2LB to the lattice's Hermite order from rho, u, P, Q
                                (Sec. 2.1); 1: the local equilibrium from rho and u only
                                (Sec. 4, Eq. feq_dsmc; to order 3 on D3Q39) */
+    int32_t kn_profile;     /* 0: one Kn; 1: Kn varies along the channel, log-linear in the
+                               streamwise coordinate y (cell units) from kn at y = 0 to kn_end
+                               at y = ncy / 2 and back: Kn(y) = kn (kn_end / kn)^s,
+                               s = 1 - |2 y / ncy - 1|. Each DSMC cell takes the NTC factor
+                               of Eq. collisionnumber at Kn(iy + 1/2), each LB node the tau
+                               of Eq. tau at Kn((j + 1/2) / lb_ratio) (j its row); the body
+                               force stays that of kn. Not with a batch. */
+    int32_t pad0;
+    double kn_end;          /* Kn at y = ncy / 2 when kn_profile = 1 (> 0) */
 } hyb_params;
 
 /* Constants derived from hyb_params (hyb_derive). */
@@ -150,6 +159,8 @@ typedef struct {
     uint64_t f[2];
     uint64_t ctrl, counters, map_scratch;
     uint64_t moved;
+    uint64_t coll_cell;     /* Real[ncells]: per-cell NTC factor (kn_profile = 1; size 0 otherwise) */
+    uint64_t tau_node;      /* Real[nnodes]: per-node relaxation time (kn_profile = 1) */
 } hyb_layout;
 
 typedef struct hyb_ctx hyb_ctx; /* opaque, owned by the library */

@@ -11,7 +11,7 @@ import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "libdsmclbm.so")
-ABI_VERSION = 3
+ABI_VERSION = 4
 
 HYB_OK, HYB_EINVAL, HYB_ENOMEM, HYB_ECUDA, HYB_ECAPACITY, HYB_ETIMEOUT, HYB_ESAMPLING, HYB_ESTATE = range(8)
 ST_CAPACITY, ST_BOUNCE_CAP, ST_SCATTER_CAP, ST_SAMPLING_CAP, ST_CELL_OVERFLOW, ST_BAD_INPUT = (
@@ -31,7 +31,8 @@ class HybParams(ctypes.Structure):
                 ("ppc", _i32), ("lattice", _i32), ("real_bytes", _i32), ("sample_every", _i32),
                 ("seed", _u64), ("kn", _dbl), ("ma", _dbl), ("crmax_init", _dbl),
                 ("capacity_factor", _dbl), ("T_K", _dbl), ("mass_kg", _dbl),
-                ("lb_collision", _i32), ("d2l_mode", _i32)]
+                ("lb_collision", _i32), ("d2l_mode", _i32), ("kn_profile", _i32),
+                ("pad0", _i32), ("kn_end", _dbl)]
 
 
 class HybDerived(ctypes.Structure):
@@ -47,7 +48,8 @@ class HybLayout(ctypes.Structure):
                 ("x", _u64 * 2), ("y", _u64 * 2), ("vx", _u64 * 2), ("vy", _u64 * 2),
                 ("vz", _u64 * 2), ("tag", _u64), ("count", _u64 * 2), ("crmax", _u64),
                 ("rem", _u64), ("nbar_sum", _u64), ("acc", _u64), ("f", _u64 * 2),
-                ("ctrl", _u64), ("counters", _u64), ("map_scratch", _u64), ("moved", _u64)]
+                ("ctrl", _u64), ("counters", _u64), ("map_scratch", _u64), ("moved", _u64),
+                ("coll_cell", _u64), ("tau_node", _u64)]
 
 
 EXPORTS = ["hyb_derive", "hyb_layout_compute", "hyb_lattice", "hyb_status_string", "dsmc_init",

@@ -78,6 +78,8 @@ struct State {
     unsigned long long* counters;
     GradRec* grad;
     void* moved;
+    void* coll_cell;  // per-cell NTC factor (Kn profile), or null
+    void* tau_node;   // per-node relaxation time (Kn profile), or null
 };
 
 // Everything a DSMC kernel needs, passed by value: the move updates the source half in
@@ -107,6 +109,7 @@ struct DsmcArgs {
     unsigned long long* counters;
     int32_t ncx, ncy, ncells, bin, sample_every, ppc;
     double dt, g_step, coll_dt, crmax_init;
+    const Real* coll_cell;  // per-cell NTC factor, or null for coll_dt everywhere
     uint64_t seed;
 };
 

@@ -624,7 +624,8 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
                     flags |= HYB_ST_CELL_OVERFLOW;  // pair indices are packed in 15 and 16 bits
                 } else if (n >= 2) {
                     const Real nbar = (Real)nb / (Real)(s + 1u);
-                    const Real ncand = (Real)0.5 * (Real)n * nbar * cm0 * coll_dt + rem0;
+                    const Real cdt = a.coll_cell ? a.coll_cell[c] : coll_dt;
+                    const Real ncand = (Real)0.5 * (Real)n * nbar * cm0 * cdt + rem0;
                     const Real fl = floor(ncand);
                     a.rem[c] = ncand - fl;
                     if (fl > (Real)16777215) {
@@ -912,6 +913,7 @@ DsmcArgs<Real> make_args(Ctx& c) {
     a.dt = c.d.dt;
     a.g_step = c.d.g_step;
     a.coll_dt = c.d.coll_dt;
+    a.coll_cell = (const Real*)c.st.coll_cell;
     a.crmax_init = c.p.crmax_init;
     a.seed = c.p.seed;
     return a;

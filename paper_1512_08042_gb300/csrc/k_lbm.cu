@@ -177,11 +177,13 @@ __device__ __forceinline__ void lbm_node(const LbmArgs<Real>& a, const int64_t n
     const Real pxx = pm[0], pxy = pm[1], pxz = pm[2], pyy = pm[3], pyz = pm[4], pzz = pm[5];
 
     Real gy = a.g_step, om = a.om, of = a.of;
-    if constexpr (PARAM) {
-        gy = a.g_node[node];
-        const Real tau = a.tau_node[node];
-        om = (Real)1 - (Real)1 / tau;
-        of = (Real)1 - (Real)0.5 / tau;
+    if constexpr (PARAM) {  // per-node values where given (a Kn profile gives tau only)
+        if (a.g_node) gy = a.g_node[node];
+        if (a.tau_node) {
+            const Real tau = a.tau_node[node];
+            om = (Real)1 - (Real)1 / tau;
+            of = (Real)1 - (Real)0.5 / tau;
+        }
     }
     const Real inv_rho = (Real)1 / rho;
     const Real ux = jx * inv_rho, uy = (jy + (Real)0.5 * rho * gy) * inv_rho, uz = jz * inv_rho;
@@ -285,16 +287,16 @@ __device__ __forceinline__ void lbm_node(const LbmArgs<Real>& a, const int64_t n
 
 // One thread per node (the nodes of all replicas in the batch form); BGK selects the
 // unregularised collision (one instantiation per collision keeps each one's registers).
-template <typename Real, class LAT, bool BATCH, bool BGK = false>
+template <typename Real, class LAT, bool BATCH, bool BGK = false, bool PARAM = false>
 __global__ void __launch_bounds__(128) k_lbm(Launch<LbmArgs<Real>> L) {
     pdl_begin();
     const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (u >= L.total) return;
     if constexpr (BATCH) {
         const int r = replica_of(L.pre, L.nrep, u);
-        lbm_node<Real, LAT, false, BGK>(L.tab[r], u - L.pre[r]);
+        lbm_node<Real, LAT, PARAM, BGK>(L.tab[r], u - L.pre[r]);
     } else {
-        lbm_node<Real, LAT, false, BGK>(L.one, u);
+        lbm_node<Real, LAT, PARAM, BGK>(L.one, u);
     }
 }
 
@@ -689,7 +691,7 @@ LbmArgs<Real> lbm_args(const Ctx& c, int cur_f) {
     a.of = (Real)(1.0 - 0.5 / c.d.tau);
     a.g_step = (Real)c.d.g_step;
     a.g_node = nullptr;
-    a.tau_node = nullptr;
+    a.tau_node = (const Real*)c.st.tau_node;  // Kn profile, or null
     a.bgk = c.p.lb_collision;
     return a;
 }
@@ -702,9 +704,14 @@ cudaError_t lbm_impl(Ctx& c) {
     Launch<LbmArgs<Real>> L{};
     L.one = a;
     L.total = c.d.nnodes;
-    const cudaError_t e =
-        a.bgk ? launch_pdl(k_lbm<Real, LAT, false, true>, dim3((unsigned)blocks), dim3(128), 0, c.stream, L)
-              : launch_pdl(k_lbm<Real, LAT, false>, dim3((unsigned)blocks), dim3(128), 0, c.stream, L);
+    const dim3 g((unsigned)blocks), b(128);
+    cudaError_t e;
+    if (a.tau_node)  // Kn profile: per-node tau
+        e = a.bgk ? launch_pdl(k_lbm<Real, LAT, false, true, true>, g, b, 0, c.stream, L)
+                  : launch_pdl(k_lbm<Real, LAT, false, false, true>, g, b, 0, c.stream, L);
+    else
+        e = a.bgk ? launch_pdl(k_lbm<Real, LAT, false, true>, g, b, 0, c.stream, L)
+                  : launch_pdl(k_lbm<Real, LAT, false>, g, b, 0, c.stream, L);
     prof_end(c, K_LBM);
     return e;
 }

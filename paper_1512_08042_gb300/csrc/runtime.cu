@@ -23,6 +23,8 @@ bool params_valid(const hyb_params* p) {
     if (p->sample_every < 1) return false;
     if ((p->lb_collision != 0 && p->lb_collision != 1) || (p->d2l_mode != 0 && p->d2l_mode != 1))
         return false;
+    if (p->kn_profile != 0 && p->kn_profile != 1) return false;
+    if (p->kn_profile == 1 && !(p->kn_end > 0.0)) return false;
     if (!(p->kn > 0.0) || !(p->crmax_init > 0.0) || !(p->capacity_factor >= 1.0)) return false;
     if (!(p->ma >= 0.0) || !(p->T_K > 0.0) || !(p->mass_kg > 0.0)) return false;
     if (std::ceil(p->capacity_factor * (double)p->ppc) > 256.0) return false;  // bin <= 256
@@ -84,6 +86,9 @@ void layout(const hyb_params& p, const hyb_derived& d, hyb_layout& L) {
     L.counters = take(HYB_NCOUNTERS * 8);
     L.map_scratch = take(nc * sizeof(GradRec));
     L.moved = take(cap * 8 * rb);
+    const bool prof = p.kn_profile == 1;
+    L.coll_cell = take(prof ? nc * rb : 0);
+    L.tau_node = take(prof ? nn * rb : 0);
     L.total_bytes = off;
     L.capacity = d.capacity;
     L.ncells = d.ncells;
@@ -91,6 +96,13 @@ void layout(const hyb_params& p, const hyb_derived& d, hyb_layout& L) {
     L.q = d.q;
     L.real_bytes = p.real_bytes;
     L.bin = d.bin;
+}
+
+// Kn along the channel (kn_profile = 1): log-linear in the streamwise coordinate y (cell
+// units, period ncy) from kn at y = 0 to kn_end at y = ncy / 2.
+double kn_at(const hyb_params& p, double y) {
+    const double s = 1.0 - std::fabs(2.0 * y / (double)p.ncy - 1.0);
+    return p.kn * std::exp(s * std::log(p.kn_end / p.kn));
 }
 
 hyb_status fail(Ctx& c, hyb_status s, const char* what, cudaError_t e = cudaSuccess) {
@@ -175,6 +187,8 @@ void resolve(Ctx& c) {
     s.counters = (unsigned long long*)(a + L.counters);
     s.grad = (GradRec*)(a + L.map_scratch);
     s.moved = a + L.moved;
+    s.coll_cell = c.p.kn_profile == 1 ? a + L.coll_cell : nullptr;
+    s.tau_node = c.p.kn_profile == 1 ? a + L.tau_node : nullptr;
 }
 
 hyb_status do_dsmc_step(Ctx& c) {
@@ -200,6 +214,29 @@ hyb_status one_hybrid_step(Ctx& c, const int32_t* nodes, int32_t nn, const int32
     s = do_lbm_step(c);
     if (s != HYB_OK) return s;
     if (ncl > 0) s = check(c, launch_map_l2d(c, cells, ncl), "map_lbm_to_dsmc launch");
+    return s;
+}
+
+// The per-cell NTC factor (Eq. collisionnumber at the cell's Kn) and per-node relaxation
+// time (Eq. tau at the node's Kn), formed on the host in FP64 and copied to the arena.
+hyb_status fill_kn_profile(Ctx& c) {
+    const int64_t nc = c.d.ncells, nn = c.d.nnodes;
+    std::vector<double> cell(nc), node(nn);
+    for (int64_t k = 0; k < nc; ++k) {
+        const double kn = kn_at(c.p, (double)(k / c.p.ncx) + 0.5);
+        cell[k] = c.d.dt / (std::sqrt(2.0) * (kn * (double)c.p.ncx) * (double)c.p.ppc);
+    }
+    for (int64_t k = 0; k < nn; ++k) {
+        const double kn = kn_at(c.p, ((double)(k / c.d.nx) + 0.5) / (double)c.p.lb_ratio);
+        node[k] = std::sqrt(kPi / 8.0) * c.d.r_lat * kn * c.d.H_lat + 0.5;
+    }
+    auto put = [&](const std::vector<double>& v, void* dst) {
+        if (c.p.real_bytes == 8) return cudaMemcpy(dst, v.data(), v.size() * 8, cudaMemcpyHostToDevice);
+        std::vector<float> w(v.begin(), v.end());
+        return cudaMemcpy(dst, w.data(), w.size() * 4, cudaMemcpyHostToDevice);
+    };
+    hyb_status s = check(c, put(cell, c.st.coll_cell), "kn profile copy");
+    if (s == HYB_OK) s = check(c, put(node, c.st.tau_node), "kn profile copy");
     return s;
 }
 
@@ -288,6 +325,7 @@ hyb_status dsmc_init(const hyb_params* p, void* arena, uint64_t arena_bytes, voi
     }
     c.h_pinned = (uint32_t*)hp;
     hyb_status s = check(c, launch_init(c), "dsmc_init launch");
+    if (s == HYB_OK && c.p.kn_profile == 1) s = fill_kn_profile(c);
     if (s != HYB_OK) {
         cudaFreeHost(hp);
         delete h;

@@ -33,6 +33,10 @@ WORKLOADS = {
     # 1024 x 8192 D3Q39 lattice.
     "poiseuille_512x4096_ppc50_fp32": config(ncx=512, ncy=4096, ppc=50, lb_ratio=2, kn=0.05,
                                               seed=5),
+    # The large channel with Kn varying along it, log-linear from 0.005 (y = 0) to 0.5
+    # (y = L/2) and back: per-cell NTC factors and per-node relaxation times.
+    "poiseuille_512x4096_ppc50_knvar_fp32": config(ncx=512, ncy=4096, ppc=50, lb_ratio=2,
+                                                    kn=0.005, kn_profile=1, kn_end=0.5, seed=6),
     # The proof-of-concept hybrid of Sec. 4: plane Poiseuille at Kn 0.05 and Ma 0.1, D3Q19
     # without regularisation, DSMC2LB to the local equilibrium of rho and u (Eq. feq_dsmc)
     # on a buffer layer one cell long at y = L0/2 across the whole height, DSMC solved on its

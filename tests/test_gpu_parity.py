@@ -391,3 +391,56 @@ def test_proof_of_concept_hybrid_steps_match_oracle():
     _compare_dsmc(h, o, 8)
     h.sync()
     assert np.allclose(h.f().cpu().numpy(), o.f(), rtol=1e-11, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------------------
+# Kn varying along the channel
+
+@pytest.mark.parametrize("real_bytes,steps", [(4, 3), (8, 2)])
+def test_dsmc_steps_with_kn_profile_match_oracle(real_bytes, steps):
+    cfg = cfg_small(real_bytes=real_bytes, ncy=12, kn=0.03, kn_profile=1, kn_end=0.6)
+    h = B.Hybrid(cfg)
+    o = O.Oracle(cfg)
+    for _ in range(steps):
+        h.dsmc_step(1)
+        o.dsmc_step(1)
+    _compare_dsmc(h, o, real_bytes)
+    c = h.counters()
+    oc = o.counters()
+    assert c["candidates"] == oc["candidates"] and c["collisions"] == oc["collisions"]
+
+
+@pytest.mark.parametrize("lattice,real_bytes", [(39, 4), (39, 8)])
+def test_lbm_steps_with_kn_profile_match_oracle(lattice, real_bytes):
+    cfg = cfg_small(lattice=lattice, real_bytes=real_bytes, lb_ratio=2, ncy=8, ma=0.5, kn=0.05,
+                    kn_profile=1, kn_end=0.5)
+    h = B.Hybrid(cfg)
+    o = O.Oracle(cfg)
+    e, w, r = O.lattice(lattice)
+    f0 = W.gen_populations(w, h.d["nnodes"], seed=29).astype(np.float32 if real_bytes == 4 else np.float64)
+    h.f().copy_(torch.from_numpy(f0.reshape(h.f().shape)))
+    torch.cuda.synchronize()
+    o.set_f(f0)
+    for step in range(3):
+        h.lbm_step(1)
+        o.lbm_step(1)
+        h.sync()
+        err = np.abs(h.f().cpu().numpy() - o.f()) / (np.abs(o.f()) + 1e-3 * w[:, None, None])
+        assert err.max() < (2e-5 if real_bytes == 4 else 1e-12), (step, err.max())
+
+
+def test_hybrid_steps_with_kn_profile_fp64_match_oracle():
+    cfg = cfg_small(real_bytes=8, lb_ratio=2, ncy=8, kn=0.05, kn_profile=1, kn_end=0.5)
+    nodes, cells = W.coupling_sites(cfg, strip_cells=2)
+    h = B.Hybrid(cfg)
+    o = O.Oracle(cfg)
+    dn, dc = torch.from_numpy(nodes).cuda(), torch.from_numpy(cells).cuda()
+    for _ in range(3):
+        h.hybrid_step(dn, dc, nsteps=1, use_graph=True)
+        o.dsmc_step(1)
+        o.map_dsmc_to_lbm(nodes)
+        o.lbm_step(1)
+        o.map_lbm_to_dsmc(cells)
+    _compare_dsmc(h, o, 8)
+    h.sync()
+    assert np.allclose(h.f().cpu().numpy(), o.f(), rtol=1e-11, atol=1e-14)
