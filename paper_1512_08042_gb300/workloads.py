@@ -29,6 +29,10 @@ WORKLOADS = {
     # 2D channel: 64 x 256 DSMC cells, 50 particles/cell (819,200), Kn 0.05, FP32 state,
     # 128 x 512 D3Q39 lattice (two LB nodes per cell per axis), 8-node coupling strip.
     "poiseuille_64x256_ppc50_fp32": config(ncx=64, ncy=256, ppc=50, lb_ratio=2, kn=0.05, seed=2),
+    # Mid-size channel for profiling many-wave behaviour on a small device footprint:
+    # 128 x 1024 DSMC cells, 50 particles/cell (6,553,600), 256 x 2048 D3Q39 lattice.
+    "poiseuille_128x1024_ppc50_fp32": config(ncx=128, ncy=1024, ppc=50, lb_ratio=2, kn=0.05,
+                                              seed=7),
     # Large channel: 512 x 4096 DSMC cells, 50 particles/cell (104,857,600), FP32 state,
     # 1024 x 8192 D3Q39 lattice.
     "poiseuille_512x4096_ppc50_fp32": config(ncx=512, ncy=4096, ppc=50, lb_ratio=2, kn=0.05,
