@@ -856,8 +856,8 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
         if (nl) atomicAdd(&a.ctrl[CTRL_NTOT], nl);
         if (fl) atomicOr(&a.ctrl[CTRL_STATUS], fl);
         // the last block to finish advances the step and sample counters (every block has
-        // read the step by now)
-        __threadfence();
+        // read the step by now; nothing written by other blocks is read here, so no fence
+        // is needed before the ticket)
         const unsigned ticket = atomicAdd(&a.ctrl[CTRL_TICKET], 1u);
         if (ticket == nblk - 1) {
             __threadfence();
