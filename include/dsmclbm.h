@@ -255,8 +255,8 @@ hyb_status lbm_interface_loss(hyb_ctx* ctx, const void* f, const int32_t* dev_no
 
 /* One step of the adjoint: with f the populations at step t and lam_next = dL/df_{t+1},
  * writes lam = dL/df_t (every entry) and adds dL/dg and dL/dtau of this step to grad_g and
- * grad_tau. wall is a scratch of 2 * ny values that must be zero before the first call; it
- * is left zero. lam and lam_next must differ. The adjoint is that of the regularised
+ * grad_tau. wall is a scratch of 2 * ny + 1 values (state precision) that must be zero
+ * before the first call; it is left zero. lam and lam_next must differ. The adjoint is that of the regularised
  * collision: a context with lb_collision = 1 returns HYB_EINVAL. */
 hyb_status lbm_adjoint_step(hyb_ctx* ctx, const void* f, const void* lam_next, void* lam,
                             const void* g_node, const void* tau_node, void* grad_g,

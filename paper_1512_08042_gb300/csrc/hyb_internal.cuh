@@ -129,7 +129,8 @@ struct LbmArgs {
 
 // One step of the adjoint of the LBM with per-node parameters: lam_next = dL/df_{t+1} in,
 // lam = dL/df_t out, the parameter gradients accumulated; wall = 2 ny adjoint wall
-// densities (left rows, then right rows), zero on entry and left zero.
+// densities (left rows, then right rows) followed by a 32-bit block ticket, all zero on entry
+// and left zero.
 template <typename Real>
 struct LbmAdjArgs {
     const Real* f;         // populations at t

@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(128) k_lbm_param(LbmArgs<Real> a) {
 // raw moments -> streamed populations. P^T is a permutation: mu_q(x) goes to
 // lam_t[q](x - e_q), except for sources behind a wall, whose mu feeds the wall density of
 // the row (summed in `wall` and spread over the populations leaving through that wall by
-// k_lbm_adj_wall).
+// the last block of k_lbm_adj).
 
 // Third-order terms of B3[k] (k = xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz):
 //   B3[k] = rho M_k(u) + om (Q3_k - rho (M_k + L_k(u)) - kap_k a1y) + of rho g f_k(u),
@@ -530,39 +530,53 @@ __device__ __forceinline__ void lbm_adjoint_node(const LbmAdjArgs<Real>& a, cons
     (void)MV;
 }
 
-// One thread per node: the collision adjoint and the transposed pull.
+// The populations leaving through a wall on row y' feed the wall density of row y' + e_y;
+// their adjoint is that row's wall adjoint times the flux normalisation. Task t < 2 ny: the
+// left (t < ny) or right wall of source row y'. The wall sums are read from L2.
 template <typename Real, class LAT>
-__global__ void __launch_bounds__(128) k_lbm_adj(LbmAdjArgs<Real> a) {
-    const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (u < a.nnodes) lbm_adjoint_node<Real, LAT>(a, u);
-}
-
-// One thread per row and wall: the populations leaving through the wall on row y' feed the
-// wall density of row y' + e_y; their adjoint is that row's wall adjoint times the flux
-// normalisation. The wall sums are cleared for the next step.
-template <typename Real, class LAT>
-__global__ void k_lbm_adj_wall(LbmAdjArgs<Real> a) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void adj_wall_row(const LbmAdjArgs<Real>& a, int t) {
     const int ny = a.ny, nx = a.nx;
-    if (t >= 2 * ny) return;
     const bool left = t < ny;
     const int yr = left ? t : t - ny;  // the source row y'
     constexpr double inv_flux = 1.0 / wall_flux_norm<LAT>();
     static_for<LAT::Q>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
         constexpr int ex = E<LAT>(q, 0), ey = E<LAT>(q, 1);
-        const Real wb = (Real)inv_flux * a.wall[(left ? 0 : ny) + wrap_y(yr + ey, ny)];
-        if constexpr (ex < 0) {
-            if (left)
-                for (int i = 0; i < -ex; ++i) a.lam[(int64_t)q * a.nnodes + (int64_t)yr * nx + i] = wb;
-        }
-        if constexpr (ex > 0) {
-            if (!left)
-                for (int i = nx - ex; i < nx; ++i) a.lam[(int64_t)q * a.nnodes + (int64_t)yr * nx + i] = wb;
+        if constexpr (ex != 0) {
+            if ((ex < 0) == left) {
+                const Real wb = (Real)inv_flux * __ldcg(&a.wall[(left ? 0 : ny) + wrap_y(yr + ey, ny)]);
+                Real* lq = a.lam + (int64_t)q * a.nnodes + (int64_t)yr * nx;
+                if (ex < 0)
+                    for (int i = 0; i < -ex; ++i) lq[i] = wb;
+                else
+                    for (int i = nx - ex; i < nx; ++i) lq[i] = wb;
+            }
         }
     });
 }
 
+// One thread per node: the collision adjoint and the transposed pull. The last block to
+// finish (a ticket after the wall sums of every block) spreads the wall adjoints over the
+// populations leaving through the walls, which no node writes, and clears the sums.
+template <typename Real, class LAT>
+__global__ void __launch_bounds__(128) k_lbm_adj(LbmAdjArgs<Real> a) {
+    __shared__ int s_last;
+    const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (u < a.nnodes) lbm_adjoint_node<Real, LAT>(a, u);
+    __syncthreads();
+    unsigned* ticket = reinterpret_cast<unsigned*>(a.wall + 2 * a.ny);
+    if (threadIdx.x == 0) {
+        __threadfence();  // this block's wall sums are visible before its ticket
+        s_last = atomicAdd(ticket, 1u) == gridDim.x - 1u;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int t = threadIdx.x; t < 2 * a.ny; t += blockDim.x) adj_wall_row<Real, LAT>(a, t);
+    __syncthreads();
+    for (int t = threadIdx.x; t < 2 * a.ny; t += blockDim.x) a.wall[t] = (Real)0;
+    if (threadIdx.x == 0) *ticket = 0u;
+}
 
 // Packed index of the symmetric pair (i, j): xx xy xz yy yz zz.
 __device__ __forceinline__ int pidx2(int i, int j) {
@@ -759,10 +773,7 @@ cudaError_t lbm_adj_impl(Ctx& c, const void* f, const void* lam_next, void* lam,
     a.nnodes = c.d.nnodes;
     const int64_t blocks = (c.d.nnodes + 127) / 128;
     k_lbm_adj<Real, LAT><<<(unsigned)blocks, 128, 0, c.stream>>>(a);
-    k_lbm_adj_wall<Real, LAT><<<(unsigned)((2 * a.ny + 127) / 128), 128, 0, c.stream>>>(a);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    return cudaMemsetAsync(wall, 0, (size_t)2 * a.ny * sizeof(Real), c.stream);
+    return cudaGetLastError();
 }
 
 template <typename Real, class LAT>
