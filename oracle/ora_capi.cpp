@@ -18,7 +18,7 @@ struct Handle {
 
 enum ArrayId {
     A_X = 0, A_Y = 1, A_VX = 2, A_VY = 3, A_VZ = 4, A_CELL_START = 5, A_CRMAX = 6,
-    A_REM = 7, A_NBAR_SUM = 8, A_ACC = 9, A_F = 10,
+    A_REM = 7, A_NBAR_SUM = 8, A_ACC = 9, A_F = 10, A_Z = 11,
 };
 
 template <class T>
@@ -48,6 +48,7 @@ int64_t get_impl(Dsmc<Real>& D, Lbm<Real>& B, int which, void* out) {
         case A_NBAR_SUM: return copy_out(D.nbar_sum, out);
         case A_ACC: return copy_out(D.acc, out);
         case A_F: return copy_out(B.f, out);
+        case A_Z: return copy_out(D.z, out);
     }
     return -1;
 }
@@ -66,6 +67,7 @@ int set_impl(Dsmc<Real>& D, Lbm<Real>& B, int which, const void* in, int64_t n) 
         case A_NBAR_SUM: return set_in(D.nbar_sum, in, n, false);
         case A_ACC: return set_in(D.acc, in, n, false);
         case A_F: return set_in(B.f, in, n, false);
+        case A_Z: return set_in(D.z, in, n, true);
     }
     return -1;
 }
@@ -76,7 +78,7 @@ bool valid(const Params* p) {
            (p->real_bytes == 4 || p->real_bytes == 8) && p->sample_every >= 1 && p->kn > 0.0 &&
            p->capacity_factor >= 1.0 && std::ceil(p->capacity_factor * p->ppc) <= 256.0 &&
            (p->lb_collision == 0 || p->lb_collision == 1) && (p->d2l_mode == 0 || p->d2l_mode == 1) &&
-           (p->kn_profile == 0 || (p->kn_profile == 1 && p->kn_end > 0.0));
+           (p->kn_profile == 0 || (p->kn_profile == 1 && p->kn_end > 0.0)) && p->ncz >= 0;
 }
 
 }  // namespace
@@ -338,14 +340,14 @@ int ora_grad_sample(int q, const double* f, uint64_t seed, uint32_t cell, uint32
     Lattice L = make_lattice(q);
     const int order = q == 39 ? 3 : 2;
     GradCell g = grad_from_populations(L, f, order);
-    std::vector<double> out(5 * (size_t)nsamp);
+    std::vector<double> out(6 * (size_t)nsamp);
     uint64_t env = 0;
     bool capped = false;
     const uint64_t trials = grad_sample_cell<double>(pack<double>(g), order, seed, cell, t,
-                                                     (uint32_t)nsamp, 0.0, 0.0, out.data(), &env,
-                                                     &capped);
+                                                     (uint32_t)nsamp, 0.0, 0.0, 0.0, false, out.data(),
+                                                     &env, &capped);
     for (int64_t k = 0; k < nsamp; ++k)
-        for (int i = 0; i < 3; ++i) v_out[3 * k + i] = out[5 * k + 2 + i];
+        for (int i = 0; i < 3; ++i) v_out[3 * k + i] = out[6 * k + 3 + i];
     info[0] = trials;
     info[1] = env;
     info[2] = capped ? 1 : 0;

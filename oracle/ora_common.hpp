@@ -46,6 +46,8 @@ struct Params {
     int32_t kn_profile;    // 1: Kn varies along the channel (kn_at)
     int32_t pad0;
     double kn_end;         // Kn at y = ncy / 2 when kn_profile = 1
+    int32_t ncz;           // DSMC cells along z (periodic); 0 or 1: the quasi-2D slab
+    int32_t pad1;
 };
 
 // Derived constants. Field order is a binary interface with oracle.py.
@@ -63,6 +65,8 @@ struct Derived {
     int32_t q, order;
     int32_t bin;   // particle slots per cell in the library's binned layout
     int32_t pad;
+    int64_t nz;    // LB layers along z: 1 for the slab, ncz * lb_ratio in 3D
+    int64_t ncz;   // DSMC cells along z: 1 for the slab
 };
 
 constexpr double kPi = 3.14159265358979323846;
@@ -83,10 +87,14 @@ inline Derived derive(const Params& p) {
     d.coll_dt = d.dt / (std::sqrt(2.0) * d.lambda * (double)p.ppc);
     d.g_step = 8.0 * (d.tau - 0.5) * p.ma * d.cs_lat * d.cs_lat / (d.H_lat * d.H_lat);
     d.c_th_ms = std::sqrt(kBoltzmann * p.T_K / p.mass_kg);
-    d.ncells = (int64_t)p.ncx * p.ncy;
+    // 3D when ncz >= 2: cells (iz ncy + iy) ncx + ix, nodes (z ny + y) nx + x, periodic in z;
+    // otherwise the quasi-2D slab of one cell and one LB layer
+    d.ncz = p.ncz >= 2 ? p.ncz : 1;
+    d.ncells = (int64_t)p.ncx * p.ncy * d.ncz;
     d.nx = (int64_t)p.ncx * p.lb_ratio;
     d.ny = (int64_t)p.ncy * p.lb_ratio;
-    d.nnodes = d.nx * d.ny;
+    d.nz = p.ncz >= 2 ? d.ncz * p.lb_ratio : 1;
+    d.nnodes = d.nx * d.ny * d.nz;
     d.bin = ((int32_t)std::ceil(p.capacity_factor * (double)p.ppc) + 31) / 32 * 32;
     d.capacity = d.ncells * (int64_t)d.bin;
     d.q = p.lattice;

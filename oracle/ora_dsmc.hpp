@@ -39,6 +39,7 @@ struct Dsmc {
     Derived d;
     // Particle state, ordered by cell after every step (Sec. 5, "per cell" NTC).
     std::vector<Real> x, y, vx, vy, vz;
+    std::vector<Real> z;  // 3D only (ncz >= 2), else empty
     std::vector<uint32_t> cell_start;  // ncells + 1
     // Per-cell collision state of the NTC scheme.
     std::vector<Real> crmax;           // (sigma_T c_r)_max / sigma_T
@@ -57,17 +58,20 @@ struct Dsmc {
         d = derive(p);
         const int64_t n = d.ncells * p.ppc;
         x.assign(n, 0); y.assign(n, 0); vx.assign(n, 0); vy.assign(n, 0); vz.assign(n, 0);
+        z.assign(three_d() ? n : 0, 0);
         cell_start.assign(d.ncells + 1, 0);
         // Sec. 3.1: a fixed number of particles placed in each cell, Maxwellian at T
         // (Eq. globalMax with unit variance), drawn by Box-Muller.
         for (int64_t c = 0; c < d.ncells; ++c) {
-            const int ix = (int)(c % p.ncx), iy = (int)(c / p.ncx);
+            const int ix = (int)(c % p.ncx), iy = (int)((c / p.ncx) % p.ncy);
+            const int iz = (int)(c / ((int64_t)p.ncx * p.ncy));
             cell_start[c] = (uint32_t)(c * p.ppc);
             for (int k = 0; k < p.ppc; ++k) {
                 const int64_t s = c * p.ppc + k;
                 U4 rp = draw(p.seed, (uint32_t)c, 0, TAG_INIT_POS, (uint32_t)k, 0);
                 x[s] = (Real)ix + (Real)u01f(rp[0]);
                 y[s] = (Real)iy + (Real)u01f(rp[1]);
+                if (three_d()) z[s] = (Real)iz + (Real)u01f(rp[2]);
                 U4 rv = draw(p.seed, (uint32_t)c, 0, TAG_INIT_VEL, (uint32_t)k, 0);
                 Real n0, n1, n2, n3;
                 gauss_pair<Real>(rv[0], rv[1], n0, n1);
@@ -84,7 +88,7 @@ struct Dsmc {
         if (p.kn_profile == 1) {  // Eq. collisionnumber at each cell centre's Kn
             coll_cell.resize((size_t)d.ncells);
             for (int64_t c = 0; c < d.ncells; ++c) {
-                const double kn = kn_at(p, (double)(c / p.ncx) + 0.5);
+                const double kn = kn_at(p, (double)((c / p.ncx) % p.ncy) + 0.5);
                 coll_cell[(size_t)c] = d.dt / (std::sqrt(2.0) * (kn * (double)p.ncx) * (double)p.ppc);
             }
         }
@@ -97,6 +101,7 @@ struct Dsmc {
     }
 
     size_t ntot() const { return x.size(); }
+    bool three_d() const { return p.ncz >= 2; }
 
     // Diffuse isothermal re-emission from a wall at rest (Sec. 3.1, "fully diffuse
     // reflection"): normal speed from the flux-weighted Maxwellian sqrt(-2 ln U), tangential
@@ -113,14 +118,30 @@ struct Dsmc {
         uz = t2;
     }
 
-    uint32_t cell_key(Real xx, Real yy) const {
+    uint32_t cell_key(Real xx, Real yy, Real zz) const {
         int ix = (int)std::floor(xx);
         int iy = (int)std::floor(yy);
         if (ix < 0) ix = 0;
         if (ix > p.ncx - 1) ix = p.ncx - 1;
         if (iy < 0) iy = 0;
         if (iy > p.ncy - 1) iy = p.ncy - 1;
-        return (uint32_t)(iy * p.ncx + ix);
+        int iz = 0;
+        if (three_d()) {
+            iz = (int)std::floor(zz);
+            if (iz < 0) iz = 0;
+            if (iz > p.ncz - 1) iz = p.ncz - 1;
+        }
+        return (uint32_t)(((int64_t)iz * p.ncy + iy) * p.ncx + ix);
+    }
+
+    // Periodic wrap of a coordinate into [0, period).
+    static Real wrap(Real v, Real period) {
+        if (v < (Real)0 || v >= period) {
+            v = v - period * std::floor(v / period);
+            if (v < (Real)0) v = v + period;
+            if (v >= period) v = v - period;
+        }
+        return v;
     }
 
     // Move one particle through one time step: body-force kick, free flight, wall hits,
@@ -129,7 +150,8 @@ struct Dsmc {
         if (!(x[i] >= (Real)0)) return kDeadKey;  // deleted by a coupling step
         const Real H = (Real)p.ncx;
         const Real L = (Real)p.ncy;
-        Real px = x[i], py = y[i];
+        const bool td = three_d();
+        Real px = x[i], py = y[i], pz = td ? z[i] : (Real)0;
         Real ux = vx[i], uy = vy[i] + (Real)d.g_step, uz = vz[i];
         Real t = (Real)d.dt;
         for (int b = 0;; ++b) {
@@ -139,6 +161,7 @@ struct Dsmc {
             if (!left && !right) {
                 px = xn;
                 py = py + uy * t;
+                if (td) pz = pz + uz * t;
                 break;
             }
             if (b == kMaxBounces) {
@@ -146,27 +169,27 @@ struct Dsmc {
                 counters[C_BOUNCE_CAP] += 1;
                 px = left ? (Real)0 : H;
                 py = py + uy * t;
+                if (td) pz = pz + uz * t;
                 break;
             }
             counters[C_WALL_HITS] += 1;
             Real th = left ? px / (-ux) : (H - px) / ux;
             py = py + uy * th;
+            if (td) pz = pz + uz * th;
             px = left ? (Real)0 : H;
             t = t - th;
             if (t < (Real)0) t = (Real)0;
             reemit(cell, rank, s, b, left ? (Real)1 : (Real)-1, ux, uy, uz);
         }
-        if (py < (Real)0 || py >= L) {
-            py = py - L * std::floor(py / L);
-            if (py < (Real)0) py = py + L;
-            if (py >= L) py = py - L;
-        }
+        py = wrap(py, L);
+        if (td) pz = wrap(pz, (Real)p.ncz);
         x[i] = px;
         y[i] = py;
+        if (td) z[i] = pz;
         vx[i] = ux;
         vy[i] = uy;
         vz[i] = uz;
-        return cell_key(px, py);
+        return cell_key(px, py, pz);
     }
 
     // Stable counting order by cell key: ties keep the previous slot order. Deleted
@@ -184,6 +207,7 @@ struct Dsmc {
             v.swap(o);
         };
         permute(x); permute(y); permute(vx); permute(vy); permute(vz);
+        if (three_d()) permute(z);
         std::fill(cell_start.begin(), cell_start.end(), 0u);
         for (uint32_t i : idx) cell_start[key[i] + 1] += 1;
         for (int64_t c = 0; c < d.ncells; ++c) {

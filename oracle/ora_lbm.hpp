@@ -49,16 +49,17 @@ struct Lbm {
             g_node.assign((size_t)d.nnodes, d.g_step);
             tau_node.resize((size_t)d.nnodes);
             for (int64_t n = 0; n < d.nnodes; ++n) {
-                const double kn = kn_at(p, ((double)(n / d.nx) + 0.5) / (double)p.lb_ratio);
+                const double kn = kn_at(p, ((double)((n / d.nx) % d.ny) + 0.5) / (double)p.lb_ratio);
                 tau_node[(size_t)n] = std::sqrt(kPi / 8.0) * d.r_lat * kn * d.H_lat + 0.5;
             }
         }
     }
 
-    double fa(int a, int64_t x, int64_t y) const {
-        return (double)f[(size_t)a * d.nnodes + y * d.nx + x];
+    double fa(int a, int64_t x, int64_t y, int64_t z = 0) const {
+        return (double)f[(size_t)a * d.nnodes + (z * d.ny + y) * d.nx + x];
     }
     int64_t wrap_y(int64_t y) const { return ((y % d.ny) + d.ny) % d.ny; }
+    int64_t wrap_z(int64_t z) const { return ((z % d.nz) + d.nz) % d.nz; }
 
     // Collision of one node given its streamed populations fs[q]; writes out[q].
     void collide(const double* fs, double* out) const { collide(fs, out, d.g_step, d.tau); }
@@ -118,40 +119,45 @@ struct Lbm {
         double flux_norm = 0.0;
         for (int a = 0; a < L.q; ++a)
             if (L.e[a][0] > 0) flux_norm += L.e[a][0] * L.w[a];
-        std::vector<double> rhoL(ny), rhoR(ny);
-        for (int64_t y = 0; y < ny; ++y) {
-            double ml = 0.0, mr = 0.0;
-            for (int a = 0; a < L.q; ++a) {
-                const int ex = L.e[a][0];
-                const int64_t sy = wrap_y(y - L.e[a][1]);
-                if (ex < 0)
-                    for (int64_t i = 0; i < -ex; ++i) ml += fa(a, i, sy);
-                if (ex > 0)
-                    for (int64_t i = nx - ex; i < nx; ++i) mr += fa(a, i, sy);
+        // wall densities of every streamwise row (y, z); in 3D the pull is periodic in z too
+        const int64_t nz = d.nz;
+        std::vector<double> rhoL(ny * nz), rhoR(ny * nz);
+        for (int64_t z = 0; z < nz; ++z)
+            for (int64_t y = 0; y < ny; ++y) {
+                double ml = 0.0, mr = 0.0;
+                for (int a = 0; a < L.q; ++a) {
+                    const int ex = L.e[a][0];
+                    const int64_t sy = wrap_y(y - L.e[a][1]);
+                    const int64_t sz = wrap_z(z - L.e[a][2]);
+                    if (ex < 0)
+                        for (int64_t i = 0; i < -ex; ++i) ml += fa(a, i, sy, sz);
+                    if (ex > 0)
+                        for (int64_t i = nx - ex; i < nx; ++i) mr += fa(a, i, sy, sz);
+                }
+                rhoL[z * ny + y] = ml / flux_norm;
+                rhoR[z * ny + y] = mr / flux_norm;
             }
-            rhoL[y] = ml / flux_norm;
-            rhoR[y] = mr / flux_norm;
-        }
         std::vector<double> fs(L.q), out(L.q);
+        for (int64_t z = 0; z < nz; ++z)
         for (int64_t y = 0; y < ny; ++y)
             for (int64_t x = 0; x < nx; ++x) {
                 for (int a = 0; a < L.q; ++a) {
                     const int64_t sx = x - L.e[a][0];
                     const int64_t sy = wrap_y(y - L.e[a][1]);
+                    const int64_t sz = wrap_z(z - L.e[a][2]);
                     if (sx < 0)
-                        fs[a] = L.w[a] * rhoL[y];
+                        fs[a] = L.w[a] * rhoL[z * ny + y];
                     else if (sx >= nx)
-                        fs[a] = L.w[a] * rhoR[y];
+                        fs[a] = L.w[a] * rhoR[z * ny + y];
                     else
-                        fs[a] = fa(a, sx, sy);
+                        fs[a] = fa(a, sx, sy, sz);
                 }
-                const int64_t node = y * nx + x;
+                const int64_t node = (z * ny + y) * nx + x;
                 if (g_node.empty())
                     collide(fs.data(), out.data());
                 else
                     collide(fs.data(), out.data(), g_node[(size_t)node], tau_node[(size_t)node]);
-                for (int a = 0; a < L.q; ++a)
-                    nf[(size_t)a * d.nnodes + y * nx + x] = (Real)out[a];
+                for (int a = 0; a < L.q; ++a) nf[(size_t)a * d.nnodes + node] = (Real)out[a];
             }
         f.swap(nf);
     }

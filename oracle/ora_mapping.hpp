@@ -239,8 +239,9 @@ GradPacked<Real> pack(const GradCell& g) {
 // deleted (x = -1). Returns the number of trials used.
 template <class Real>
 uint64_t grad_sample_cell(const GradPacked<Real>& g, int order, uint64_t seed, uint32_t cell,
-                          uint32_t t, uint32_t n, Real ix, Real iy, Real* out /* n x 5 */,
-                          uint64_t* envelope, bool* capped) {
+                          uint32_t t, uint32_t n, Real ix, Real iy, Real iz, bool three_d,
+                          Real* out /* n x 6: x y z vx vy vz */, uint64_t* envelope,
+                          bool* capped) {
     const uint64_t cap = std::min<uint64_t>(1000ull * n, 0xFFFFFFull);
     uint32_t produced = 0;
     uint64_t j = 0;
@@ -254,19 +255,21 @@ uint64_t grad_sample_cell(const GradPacked<Real>& g, int order, uint64_t seed, u
         const Real R = (Real)u01f(r2[0]);
         if (G > g.C) *envelope += 1;
         if (g.C * R <= G) {
-            Real* o = out + 5 * (size_t)produced;
+            Real* o = out + 6 * (size_t)produced;
             o[0] = ix + (Real)u01f(r2[1]);
             o[1] = iy + (Real)u01f(r2[2]);
-            for (int i = 0; i < 3; ++i) o[2 + i] = xi[i] + g.u[i];
+            o[2] = three_d ? iz + (Real)u01f(r2[3]) : (Real)0;
+            for (int i = 0; i < 3; ++i) o[3 + i] = xi[i] + g.u[i];
             produced += 1;
         }
     }
     *capped = produced < n;
     for (; produced < n; ++produced) {
-        Real* o = out + 5 * (size_t)produced;
+        Real* o = out + 6 * (size_t)produced;
         o[0] = (Real)-1;
         o[1] = iy;
-        o[2] = o[3] = o[4] = (Real)0;
+        o[2] = iz;
+        o[3] = o[4] = o[5] = (Real)0;
     }
     return j;
 }
@@ -280,8 +283,10 @@ void map_dsmc_to_lbm(Dsmc<Real>& D, Lbm<Real>& B, const int32_t* nodes, int n) {
             D.status |= ST_BAD_INPUT;
             continue;
         }
-        const int64_t x = node % B.d.nx, y = node / B.d.nx;
-        const int64_t cell = (y / D.p.lb_ratio) * D.p.ncx + (x / D.p.lb_ratio);
+        const int64_t x = node % B.d.nx, y = (node / B.d.nx) % B.d.ny;
+        const int64_t z = node / (B.d.nx * B.d.ny);
+        const int64_t zc = D.three_d() ? z / D.p.lb_ratio : 0;
+        const int64_t cell = (zc * D.p.ncy + y / D.p.lb_ratio) * D.p.ncx + (x / D.p.lb_ratio);
         Coeffs a;
         if (!dsmc_coefficients(&D.acc[(size_t)cell * kNumMoments], D.nsamples, D.p.ppc, a)) {
             D.status |= ST_BAD_INPUT;
@@ -320,13 +325,17 @@ void map_lbm_to_dsmc(Dsmc<Real>& D, const Lbm<Real>& B, const int32_t* cells, in
             continue;
         }
         const int64_t cell = cells[c];
-        const int64_t ix = cell % D.p.ncx, iy = cell / D.p.ncx;
+        const int64_t ix = cell % D.p.ncx, iy = (cell / D.p.ncx) % D.p.ncy;
+        const int64_t iz = cell / ((int64_t)D.p.ncx * D.p.ncy);
+        const int rz = D.three_d() ? r : 1;  // LB layers of the cell along z
         std::vector<Real> fbar(L.q, (Real)0);
         for (int q = 0; q < L.q; ++q) {
             Real s = 0;
-            for (int dy = 0; dy < r; ++dy)
-                for (int dx = 0; dx < r; ++dx) s += (Real)B.fa(q, ix * r + dx, iy * r + dy);
-            fbar[q] = s / (Real)(r * r);
+            for (int dz = 0; dz < rz; ++dz)
+                for (int dy = 0; dy < r; ++dy)
+                    for (int dx = 0; dx < r; ++dx)
+                        s += (Real)B.fa(q, ix * r + dx, iy * r + dy, iz * rz + dz);
+            fbar[q] = s / (Real)(r * r * rz);
         }
         const GradCellT<Real> g = grad_cell<Real>(L, fbar.data(), B.d.order);
         const double u = u01d(draw(D.p.seed, (uint32_t)cell, t, TAG_L2D_ROUND, 0, 0)[0]);
@@ -336,35 +345,38 @@ void map_lbm_to_dsmc(Dsmc<Real>& D, const Lbm<Real>& B, const int32_t* cells, in
             D.status |= ST_CAPACITY;
             continue;
         }
-        fresh[c].resize(5 * (size_t)nnew);
+        fresh[c].resize(6 * (size_t)nnew);
         bool capped = false;
         const uint64_t trials = grad_sample_cell<Real>(pack<Real>(g), B.d.order, D.p.seed,
                                                        (uint32_t)cell, t, nnew, (Real)ix, (Real)iy,
-                                                       fresh[c].data(), &D.counters[C_ENVELOPE],
-                                                       &capped);
+                                                       (Real)iz, D.three_d(), fresh[c].data(),
+                                                       &D.counters[C_ENVELOPE], &capped);
         if (capped) D.status |= ST_SAMPLING_CAP;
         D.counters[C_L2D_ATTEMPTS] += trials;
         D.counters[C_CREATED] += nnew;
         D.counters[C_DELETED] += D.cell_start[cell + 1] - D.cell_start[cell];
         slot_of[cell] = c;
     }
-    std::vector<Real> nx, ny, nvx, nvy, nvz;
+    const bool td = D.three_d();
+    std::vector<Real> nx, ny, nz, nvx, nvy, nvz;
     std::vector<uint32_t> cs(D.d.ncells + 1, 0);
     for (int64_t cell = 0; cell < D.d.ncells; ++cell) {
         cs[cell] = (uint32_t)nx.size();
         if (slot_of[cell] >= 0) {
             const std::vector<Real>& o = fresh[slot_of[cell]];
-            for (size_t k = 0; k < o.size() / 5; ++k) {
-                nx.push_back(o[5 * k]);
-                ny.push_back(o[5 * k + 1]);
-                nvx.push_back(o[5 * k + 2]);
-                nvy.push_back(o[5 * k + 3]);
-                nvz.push_back(o[5 * k + 4]);
+            for (size_t k = 0; k < o.size() / 6; ++k) {
+                nx.push_back(o[6 * k]);
+                ny.push_back(o[6 * k + 1]);
+                if (td) nz.push_back(o[6 * k + 2]);
+                nvx.push_back(o[6 * k + 3]);
+                nvy.push_back(o[6 * k + 4]);
+                nvz.push_back(o[6 * k + 5]);
             }
         } else {
             for (uint32_t i = D.cell_start[cell]; i < D.cell_start[cell + 1]; ++i) {
                 nx.push_back(D.x[i]);
                 ny.push_back(D.y[i]);
+                if (td) nz.push_back(D.z[i]);
                 nvx.push_back(D.vx[i]);
                 nvy.push_back(D.vy[i]);
                 nvz.push_back(D.vz[i]);
@@ -374,6 +386,7 @@ void map_lbm_to_dsmc(Dsmc<Real>& D, const Lbm<Real>& B, const int32_t* cells, in
     cs[D.d.ncells] = (uint32_t)nx.size();
     D.x.swap(nx);
     D.y.swap(ny);
+    D.z.swap(nz);
     D.vx.swap(nvx);
     D.vy.swap(nvy);
     D.vz.swap(nvz);

@@ -13,7 +13,7 @@ from . import build as _build
 
 _LIB = None
 
-A_X, A_Y, A_VX, A_VY, A_VZ, A_CELL_START, A_CRMAX, A_REM, A_NBAR_SUM, A_ACC, A_F = range(11)
+A_X, A_Y, A_VX, A_VY, A_VZ, A_CELL_START, A_CRMAX, A_REM, A_NBAR_SUM, A_ACC, A_F, A_Z = range(12)
 COUNTER_NAMES = ["wall_hits", "candidates", "collisions", "created", "deleted",
                  "l2d_attempts", "envelope", "bounce_cap"]
 ST_CAPACITY, ST_BOUNCE_CAP, ST_SCATTER_CAP, ST_SAMPLING_CAP, ST_CELL_OVERFLOW, ST_BAD_INPUT = (
@@ -42,6 +42,8 @@ class Params(ctypes.Structure):
         ("kn_profile", ctypes.c_int32),
         ("pad0", ctypes.c_int32),
         ("kn_end", ctypes.c_double),
+        ("ncz", ctypes.c_int32),
+        ("pad1", ctypes.c_int32),
     ]
 
 
@@ -65,6 +67,8 @@ class Derived(ctypes.Structure):
         ("order", ctypes.c_int32),
         ("bin", ctypes.c_int32),
         ("pad", ctypes.c_int32),
+        ("nz", ctypes.c_int64),
+        ("ncz", ctypes.c_int64),
     ]
 
 
@@ -276,15 +280,22 @@ class Oracle:
             raise ValueError("size mismatch for array %d" % which)
 
     def particles(self):
-        return {k: self.get(a) for k, a in
-                (("x", A_X), ("y", A_Y), ("vx", A_VX), ("vy", A_VY), ("vz", A_VZ))}
+        keys = [("x", A_X), ("y", A_Y), ("vx", A_VX), ("vy", A_VY), ("vz", A_VZ)]
+        if self.d["ncz"] >= 2:
+            keys.append(("z", A_Z))
+        return {k: self.get(a) for k, a in keys}
 
-    def set_particles(self, x, y, vx, vy, vz, cell_start):
+    def set_particles(self, x, y, vx, vy, vz, cell_start, z=None):
         for a, v in ((A_X, x), (A_Y, y), (A_VX, vx), (A_VY, vy), (A_VZ, vz)):
             self.set(a, v)
+        if z is not None:
+            self.set(A_Z, z)
         self.set(A_CELL_START, cell_start)
 
     def f(self):
+        """Populations [q][y][x], or [q][z][y][x] in 3D."""
+        if self.d["nz"] > 1:
+            return self.get(A_F).reshape(self.d["q"], self.d["nz"], self.d["ny"], self.d["nx"])
         return self.get(A_F).reshape(self.d["q"], self.d["ny"], self.d["nx"])
 
     def set_f(self, f):

@@ -914,3 +914,58 @@ def test_kn_profile_collision_rate_follows_the_local_mean_free_path():
     assert abs(got - want) < 4 * math.sqrt(want / steps) + 0.01 * want
     plain = 0.5 * 24 * 16 * 40 * math.sqrt(8 / math.pi) / d["lam"] * d["dt"]
     assert want < 0.6 * plain  # the profile's rate is far from the rate at kn
+
+
+# ---------------------------------------------------------------------------------------
+# Full 3D (ncz >= 2): periodic z for the particles and the lattice
+
+def test_lbm_3d_with_z_uniform_populations_steps_like_the_slab_in_every_layer():
+    # Populations that do not depend on z pull the same values from every layer, and the
+    # wall densities of every (y, z) row equal those of the slab row y, so each layer of the
+    # 3D step is exactly the quasi-2D step.
+    for q in (39, 19):
+        cfg2 = small_cfg(ncx=8, ncy=3, lb_ratio=2, lattice=q, ma=0.4, kn=0.15)
+        cfg3 = dict(cfg2, ncz=3)
+        a, b = O.Oracle(cfg2), O.Oracle(cfg3)
+        e, w, r = O.lattice(q)
+        f2 = W.gen_populations(w, a.d["nnodes"], seed=3).reshape(q, a.d["ny"], a.d["nx"])
+        assert b.d["nz"] == 6
+        a.set_f(f2)
+        b.set_f(np.repeat(f2[:, None], b.d["nz"], axis=1))
+        a.lbm_step(3)
+        b.lbm_step(3)
+        for z in range(b.d["nz"]):
+            assert np.array_equal(b.f()[:, z], a.f()), (q, z)
+
+
+def test_dsmc_3d_equilibrium_box_collision_rate_and_wall_flux():
+    # A 3D box at rest: the hard-sphere collision rate 1/2 N <c> dt / lambda, the one-sided
+    # flux n <c> / 4 through each wall of area ncy ncz, z positions inside [0, ncz) and the
+    # z velocities of unit variance.
+    cfg = small_cfg(ncx=12, ncy=4, ppc=30, ma=0.0, kn=0.1, crmax_init=5.0, ncz=5)
+    o = O.Oracle(cfg)
+    d = o.d
+    assert d["ncells"] == 12 * 4 * 5
+    o.dsmc_step(20)
+    c0 = o.counters()["collisions"]
+    h0 = o.counters()["wall_hits"]
+    steps = 120
+    o.dsmc_step(steps)
+    ntot = 12 * 4 * 5 * 30
+    got = (o.counters()["collisions"] - c0) / steps
+    want = 0.5 * ntot * math.sqrt(8 / math.pi) / d["lam"] * d["dt"]
+    assert abs(got - want) < 4 * math.sqrt(want / steps) + 0.01 * want
+    hits = (o.counters()["wall_hits"] - h0) / steps
+    want_h = 2 * 30 * math.sqrt(8 / math.pi) / 4 * (4 * 5) * d["dt"]
+    assert abs(hits / want_h - 1) < 0.06
+    p = o.particles()
+    assert p["z"].min() >= 0 and p["z"].max() < 5
+    assert abs(p["vz"].var() - 1) < 0.05
+    assert o.scalars()["ntot"] == ntot
+    # the particles of a cell lie in it
+    cs = o.get(O.A_CELL_START)
+    for c in (0, 77, 239):
+        ix, iy, iz = c % 12, (c // 12) % 4, c // 48
+        s = slice(cs[c], cs[c + 1])
+        assert np.all(np.floor(p["x"][s]) == ix) and np.all(np.floor(p["y"][s]) == iy)
+        assert np.all(np.floor(p["z"][s]) == iz)
