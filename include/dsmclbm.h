@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define HYB_ABI_VERSION 4u
+#define HYB_ABI_VERSION 5u
 
 typedef enum {
     HYB_OK = 0,
@@ -105,6 +105,12 @@ typedef struct {
                                force stays that of kn. Not with a batch. */
     int32_t pad0;
     double kn_end;          /* Kn at y = ncy / 2 when kn_profile = 1 (> 0) */
+    int32_t ncz;            /* DSMC cells along z, periodic (the paper's solvers are 3D with
+                               periodic y and z, Sec. 3.1): 0 or 1 for the quasi-2D slab of
+                               one cell and one LB layer; >= 2 for full 3D, with particle z
+                               positions, ncz * lb_ratio LB layers, cells (iz ncy + iy) ncx + ix
+                               and nodes (z ny + y) nx + x. Not with a batch or the adjoint. */
+    int32_t pad1;
 } hyb_params;
 
 /* Constants derived from hyb_params (hyb_derive). */
@@ -123,6 +129,8 @@ typedef struct {
     int32_t q, order;
     int32_t bin;      /* particle slots per cell */
     int32_t pad;
+    int64_t nz;       /* LB layers along z: 1 for the slab, ncz * lb_ratio in 3D */
+    int64_t ncz;      /* DSMC cells along z: 1 for the slab */
 } hyb_derived;
 
 /* Byte offsets of the arrays inside the caller's arena (hyb_layout_compute). Arrays marked
@@ -140,15 +148,16 @@ typedef struct {
  *   nbar_sum      u32[ncells]       running sum of N per cell, for N-bar
  *   acc           f64[ncells][20]   cumulative sums N, S v (3), S vv (6: xx xy xz yy yz zz),
  *                                   S vvv (10: xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz)
- *   f             Real[q][ny][nx]   populations, x fastest; [2]
+ *   f             Real[q][nz][ny][nx]  populations, x fastest (nz = 1 for the slab); [2]
  *   ctrl          u32[16]           [0] status bits, [1] particles in use, [2] DSMC steps
  *                                   taken, [3] moment samples taken, [4]..[15] scratch
  *   counters      u64[16]           event counters, HYB_C_*
  *   map_scratch                     LB2DSMC per-cell records
  *   moved         Real[ncells*bin][8]  the particles of the DSMC step in progress after the
- *                                   move, by origin slot: x, y, vx, vy, vz and 3 unused (one
- *                                   record per 32-byte sector in FP32); scratch between the
- *                                   two kernels of a step */
+ *                                   move, by origin slot: x, y, vx, vy, vz, z (3D only) and
+ *                                   2 unused (one record per 32-byte sector in FP32); scratch
+ *                                   between the two kernels of a step
+ *   z             Real[ncells*bin]  z positions in cell units (3D only); [2] */
 typedef struct {
     uint64_t total_bytes;
     int64_t capacity, ncells, nnodes;
@@ -161,6 +170,7 @@ typedef struct {
     uint64_t moved;
     uint64_t coll_cell;     /* Real[ncells]: per-cell NTC factor (kn_profile = 1; size 0 otherwise) */
     uint64_t tau_node;      /* Real[nnodes]: per-node relaxation time (kn_profile = 1) */
+    uint64_t z[2];          /* Real[ncells*bin]: particle z positions (3D only; size 0 else) */
 } hyb_layout;
 
 typedef struct hyb_ctx hyb_ctx; /* opaque, owned by the library */
@@ -239,7 +249,8 @@ hyb_status map_lbm_to_dsmc_noalloc(hyb_ctx* ctx, const int32_t* dev_cells, int32
  * state precision (real_bytes). g, tau and their gradients are one value per node in the
  * state precision. All buffers are device memory owned by the caller; every call is
  * enqueued on the context's stream; invalid pointers or sizes return HYB_EINVAL without
- * launching; the context's own populations are not touched. */
+ * launching; the context's own populations are not touched. lbm_step_nodes and
+ * lbm_adjoint_step are for the slab (ncz < 2): a 3D context returns HYB_EINVAL. */
 
 /* One LB step f_dst = LB(f_src) with per-node g (force increment per step along the
  * streamwise axis) and tau. f_src and f_dst must differ. */

@@ -11,7 +11,7 @@ import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "libdsmclbm.so")
-ABI_VERSION = 4
+ABI_VERSION = 5
 
 HYB_OK, HYB_EINVAL, HYB_ENOMEM, HYB_ECUDA, HYB_ECAPACITY, HYB_ETIMEOUT, HYB_ESAMPLING, HYB_ESTATE = range(8)
 ST_CAPACITY, ST_BOUNCE_CAP, ST_SCATTER_CAP, ST_SAMPLING_CAP, ST_CELL_OVERFLOW, ST_BAD_INPUT = (
@@ -32,14 +32,15 @@ class HybParams(ctypes.Structure):
                 ("seed", _u64), ("kn", _dbl), ("ma", _dbl), ("crmax_init", _dbl),
                 ("capacity_factor", _dbl), ("T_K", _dbl), ("mass_kg", _dbl),
                 ("lb_collision", _i32), ("d2l_mode", _i32), ("kn_profile", _i32),
-                ("pad0", _i32), ("kn_end", _dbl)]
+                ("pad0", _i32), ("kn_end", _dbl), ("ncz", _i32), ("pad1", _i32)]
 
 
 class HybDerived(ctypes.Structure):
     _fields_ = [("r_lat", _dbl), ("cs_lat", _dbl), ("H_lat", _dbl), ("tau", _dbl), ("dt", _dbl),
                 ("lam", _dbl), ("coll_dt", _dbl), ("g_step", _dbl), ("c_th_ms", _dbl),
                 ("ncells", _i64), ("nx", _i64), ("ny", _i64), ("nnodes", _i64),
-                ("capacity", _i64), ("q", _i32), ("order", _i32), ("bin", _i32), ("pad", _i32)]
+                ("capacity", _i64), ("q", _i32), ("order", _i32), ("bin", _i32), ("pad", _i32),
+                ("nz", _i64), ("ncz", _i64)]
 
 
 class HybLayout(ctypes.Structure):
@@ -49,7 +50,7 @@ class HybLayout(ctypes.Structure):
                 ("vz", _u64 * 2), ("tag", _u64), ("count", _u64 * 2), ("crmax", _u64),
                 ("rem", _u64), ("nbar_sum", _u64), ("acc", _u64), ("f", _u64 * 2),
                 ("ctrl", _u64), ("counters", _u64), ("map_scratch", _u64), ("moved", _u64),
-                ("coll_cell", _u64), ("tau_node", _u64)]
+                ("coll_cell", _u64), ("tau_node", _u64), ("z", _u64 * 2)]
 
 
 EXPORTS = ["hyb_derive", "hyb_layout_compute", "hyb_lattice", "hyb_status_string", "dsmc_init",
@@ -260,7 +261,7 @@ class Hybrid:
 
     # -- differentiated LBM (per-node g and tau, adjoint, interface loss) ----------------
     def _pop_shape(self):
-        return (int(self.d["q"]), int(self.d["ny"]), int(self.d["nx"]))
+        return tuple(self.f().shape)
 
     def _check_pop(self, *ts):
         for t in ts:
@@ -372,12 +373,19 @@ class Hybrid:
         h = self.current()[0] if half is None else half
         return self._view(self.L.count[h], self.L.ncells, self.torch.int32).long()
 
+    def three_d(self):
+        return int(self.d["ncz"]) >= 2
+
+    def _pkeys(self):
+        return ("x", "y", "z", "vx", "vy", "vz") if self.three_d() else ("x", "y", "vx", "vy", "vz")
+
     def particle_arrays(self, half=None):
-        """Binned particle arrays [ncells, bin] of the current (or given) half (views)."""
+        """Binned particle arrays [ncells, bin] of the current (or given) half (views); z only
+        in 3D."""
         h = self.current()[0] if half is None else half
         cap, b = self.L.capacity, self.L.bin
         return {k: self._view(getattr(self.L, k)[h], cap, self.real).view(-1, b)
-                for k in ("x", "y", "vx", "vy", "vz")}
+                for k in self._pkeys()}
 
     def particles(self):
         """Current particles in cell order (copies, compacted from the bins)."""
@@ -407,13 +415,17 @@ class Hybrid:
         return self._view(self.L.nbar_sum, self.L.ncells, self.torch.int32)
 
     def f(self, half=None):
+        """Populations [q, ny, nx] (slab) or [q, nz, ny, nx] (3D) of the current (or given)
+        half (a view)."""
         h = self.current()[1] if half is None else half
-        q, ny, nx = self.d["q"], self.d["ny"], self.d["nx"]
-        return self._view(self.L.f[h], q * nx * ny, self.real).view(q, ny, nx)
+        q, ny, nx, nz = self.d["q"], self.d["ny"], self.d["nx"], self.d["nz"]
+        v = self._view(self.L.f[h], q * nx * ny * nz, self.real)
+        return v.view(q, nz, ny, nx) if self.three_d() else v.view(q, ny, nx)
 
     # -- state transfer (checkpoint / restore, synthetic states) ------------------------
-    def load_particles(self, x, y, vx, vy, vz, cell_start):
-        """Write a cell-ordered particle set into the bins of the current half (host arrays)."""
+    def load_particles(self, x, y, vx, vy, vz, cell_start, z=None):
+        """Write a cell-ordered particle set into the bins of the current half (host arrays);
+        z is required in 3D."""
         torch = self.torch
         cs = np.asarray(cell_start, np.int64)
         counts = np.diff(cs)
@@ -425,7 +437,12 @@ class Hybrid:
         slot = torch.as_tensor(cell * self.L.bin + (np.arange(cs[-1]) - cs[cell]),
                                device=self.device)
         arr = self.particle_arrays()
-        for k, v in (("x", x), ("y", y), ("vx", vx), ("vy", vy), ("vz", vz)):
+        vals = [("x", x), ("y", y), ("vx", vx), ("vy", vy), ("vz", vz)]
+        if self.three_d():
+            if z is None:
+                raise ValueError("a 3D context needs the z positions")
+            vals.append(("z", z))
+        for k, v in vals:
             arr[k].view(-1)[slot] = torch.as_tensor(np.asarray(v), dtype=self.real,
                                                     device=self.device)
         h = self.current()[0]

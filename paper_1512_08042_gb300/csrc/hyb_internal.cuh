@@ -62,6 +62,7 @@ enum : int { GR_A2 = 0, GR_A3 = 6, GR_U = 16, GR_C = 19 };
 
 // Pointers into the arena.
 struct State {
+    void* pz[2];  // 3D only, else null
     void* px[2];
     void* py[2];
     void* pvx[2];
@@ -111,6 +112,10 @@ struct DsmcArgs {
     double dt, g_step, coll_dt, crmax_init;
     const Real* coll_cell;  // per-cell NTC factor, or null for coll_dt everywhere
     uint64_t seed;
+    // 3D (ncz >= 2): z positions of the source and destination sets; ncz is 0 in 2D
+    const Real* sz;
+    Real* dz;
+    int32_t ncz;
 };
 
 template <typename Real>
@@ -125,6 +130,7 @@ struct LbmArgs {
     const Real* g_node;
     const Real* tau_node;
     int32_t bgk;  // 1: unregularised BGK collision (lb_collision)
+    int32_t nz;   // lattice layers along z (1 in 2D)
 };
 
 // One step of the adjoint of the LBM with per-node parameters: lam_next = dL/df_{t+1} in,
@@ -164,6 +170,8 @@ struct MapArgs {
     Real* vx;
     Real* vy;
     Real* vz;
+    int32_t ncz;  // 3D (ncz >= 2): cells along z and the z positions; 0 and null in 2D
+    Real* z;
 };
 
 // ---------------------------------------------------------------------------------------

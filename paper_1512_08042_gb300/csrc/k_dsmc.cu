@@ -74,11 +74,12 @@ __global__ void k_init_particles(DsmcArgs<Real> a) {
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
          s += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t c = (uint32_t)(s / a.ppc), k = (uint32_t)(s % a.ppc);
-        const int ix = (int)(c % (uint32_t)a.ncx), iy = (int)(c / (uint32_t)a.ncx);
+        const int ix = (int)(c % (uint32_t)a.ncx), iy = (int)((c / (uint32_t)a.ncx) % (uint32_t)a.ncy);
         const int64_t slot = (int64_t)c * a.bin + k;
         const uint4 rp = draw(a.seed, c, 0, TAG_INIT_POS, k, 0);
         a.dx[slot] = (Real)ix + (Real)u01f(rp.x);
         a.dy[slot] = (Real)iy + (Real)u01f(rp.y);
+        if (a.ncz) a.dz[slot] = (Real)(c / ((uint32_t)a.ncx * (uint32_t)a.ncy)) + (Real)u01f(rp.z);
         const uint4 rv = draw(a.seed, c, 0, TAG_INIT_VEL, k, 0);
         Real n0, n1, n2, n3;
         gauss_pair<Real>(rv.x, rv.y, n0, n1);
@@ -111,37 +112,52 @@ __global__ void k_init_cells(DsmcArgs<Real> a) {
 // Moved-particle records: 8 Real per origin slot (x, y, vx, vy, vz, 3 unused), written whole
 // by the move and read by the collide with one 32-byte sector per particle (FP32).
 __device__ __forceinline__ void rec_store(float* rec, int64_t i, float x, float y, float u, float v,
-                                          float w) {
+                                          float w, float z = 0.0f) {
     float4* p = reinterpret_cast<float4*>(rec) + 2 * i;
     p[0] = make_float4(x, y, u, v);
-    p[1] = make_float4(w, 0.0f, 0.0f, 0.0f);
+    p[1] = make_float4(w, z, 0.0f, 0.0f);
 }
 __device__ __forceinline__ void rec_store(double* rec, int64_t i, double x, double y, double u,
-                                          double v, double w) {
+                                          double v, double w, double z = 0.0) {
     double2* p = reinterpret_cast<double2*>(rec) + 4 * i;
     p[0] = make_double2(x, y);
     p[1] = make_double2(u, v);
-    p[2] = make_double2(w, 0.0);
+    p[2] = make_double2(w, z);
 }
+// Z3: also the z position (3D), stored beside vz.
+template <bool Z3>
 __device__ __forceinline__ void rec_load(const float* rec, int64_t i, float& x, float& y, float& u,
-                                         float& v, float& w) {
+                                         float& v, float& w, float& z) {
     const float4* p = reinterpret_cast<const float4*>(rec) + 2 * i;
     const float4 a = p[0];
     x = a.x;
     y = a.y;
     u = a.z;
     v = a.w;
-    w = reinterpret_cast<const float*>(p + 1)[0];
+    if constexpr (Z3) {
+        const float2 b = reinterpret_cast<const float2*>(p + 1)[0];
+        w = b.x;
+        z = b.y;
+    } else {
+        w = reinterpret_cast<const float*>(p + 1)[0];
+    }
 }
+template <bool Z3>
 __device__ __forceinline__ void rec_load(const double* rec, int64_t i, double& x, double& y,
-                                         double& u, double& v, double& w) {
+                                         double& u, double& v, double& w, double& z) {
     const double2* p = reinterpret_cast<const double2*>(rec) + 4 * i;
     const double2 a = p[0], b = p[1];
     x = a.x;
     y = a.y;
     u = b.x;
     v = b.y;
-    w = reinterpret_cast<const double*>(p + 2)[0];
+    if constexpr (Z3) {
+        const double2 c = p[2];
+        w = c.x;
+        z = c.y;
+    } else {
+        w = reinterpret_cast<const double*>(p + 2)[0];
+    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -149,10 +165,10 @@ __device__ __forceinline__ void rec_load(const double* rec, int64_t i, double& x
 
 // Flight of a particle whose straight flight crosses a wall: it is re-emitted from the wall
 // (diffuse, isothermal), possibly more than once, for the rest of the step.
-template <typename Real>
+template <typename Real, bool Z3 = false>
 __device__ __forceinline__ void wall_flight(uint64_t seed, uint32_t c, uint32_t k, uint32_t s, Real H,
                                             Real dt, Real& px, Real& py, Real& ux, Real& uy,
-                                            Real& uz, uint32_t& hits, uint32_t& caps) {
+                                            Real& uz, uint32_t& hits, uint32_t& caps, Real& pz) {
     Real t = dt;
     for (int b = 0;; ++b) {
         const Real xn = px + ux * t;
@@ -161,17 +177,20 @@ __device__ __forceinline__ void wall_flight(uint64_t seed, uint32_t c, uint32_t 
         if (!left && !right) {
             px = xn;
             py = py + uy * t;
+            if constexpr (Z3) pz = pz + uz * t;
             break;
         }
         if (b == kMaxBounces) {
             caps += 1;
             px = left ? (Real)0 : H;
             py = py + uy * t;
+            if constexpr (Z3) pz = pz + uz * t;
             break;
         }
         hits += 1;
         const Real th = left ? px / (-ux) : (H - px) / ux;
         py = py + uy * th;
+        if constexpr (Z3) pz = pz + uz * th;
         px = left ? (Real)0 : H;
         t = t - th;
         if (t < (Real)0) t = (Real)0;
@@ -179,18 +198,32 @@ __device__ __forceinline__ void wall_flight(uint64_t seed, uint32_t c, uint32_t 
     }
 }
 
-// Periodic wrap of y and the cell key of a moved particle.
+// Periodic wrap of v into [0, period).
 template <typename Real>
-__device__ __forceinline__ uint32_t cell_key(const DsmcArgs<Real>& a, Real L, Real px, Real& py) {
-    if (py < (Real)0 || py >= L) {
-        py = py - L * floor(py / L);
-        if (py < (Real)0) py = py + L;
-        if (py >= L) py = py - L;
+__device__ __forceinline__ Real wrap_periodic(Real v, Real period) {
+    if (v < (Real)0 || v >= period) {
+        v = v - period * floor(v / period);
+        if (v < (Real)0) v = v + period;
+        if (v >= period) v = v - period;
     }
+    return v;
+}
+
+// Periodic wrap of y (and z in 3D) and the cell key (iz ncy + iy) ncx + ix of a moved particle.
+template <typename Real, bool Z3 = false>
+__device__ __forceinline__ uint32_t cell_key(const DsmcArgs<Real>& a, Real L, Real px, Real& py,
+                                             Real& pz) {
+    py = wrap_periodic(py, L);
     int ix = (int)floor(px), iy = (int)floor(py);
     ix = ix < 0 ? 0 : (ix > a.ncx - 1 ? a.ncx - 1 : ix);
     iy = iy < 0 ? 0 : (iy > a.ncy - 1 ? a.ncy - 1 : iy);
-    return (uint32_t)(iy * a.ncx + ix);
+    int iz = 0;
+    if constexpr (Z3) {
+        pz = wrap_periodic(pz, (Real)a.ncz);
+        iz = (int)floor(pz);
+        iz = iz < 0 ? 0 : (iz > a.ncz - 1 ? a.ncz - 1 : iz);
+    }
+    return (uint32_t)((iz * a.ncy + iy) * a.ncx + ix);
 }
 
 // Appends the active lanes' two slots to the bins of their new cells: lanes bound for the
@@ -215,7 +248,7 @@ __device__ __forceinline__ void bin_arrival2(uint32_t* __restrict__ count, uint3
 
 // One source cell, by one warp; the first 64 particles of the cell are handled two per
 // lane, loads, flights and binning atomics of both in flight together.
-template <typename Real>
+template <typename Real, bool Z3>
 __device__ __forceinline__ void move_cell(const DsmcArgs<Real>& a, int c, unsigned lane) {
     const uint32_t s = a.ctrl[CTRL_STEP];
     if (c == 0 && lane == 0) a.ctrl[CTRL_NTOT] = 0;  // the collide recounts
@@ -240,6 +273,7 @@ __device__ __forceinline__ void move_cell(const DsmcArgs<Real>& a, int c, unsign
             const uint32_t k1 = k0 + lane, k2 = k1 + 32;
             const bool act1 = k1 < n, act2 = k2 < n;
             Real p1[5] = {0, 0, 0, 0, 0}, p2[5] = {0, 0, 0, 0, 0};
+            Real z1 = 0, z2 = 0;  // 3D only
             // the loads need only the bin size, not the count, so they travel with it
             const bool in1 = k1 < bin, in2 = k2 < bin;
             if (in1) {
@@ -248,6 +282,7 @@ __device__ __forceinline__ void move_cell(const DsmcArgs<Real>& a, int c, unsign
                 p1[2] = svx[base + k1];
                 p1[3] = svy[base + k1];
                 p1[4] = svz[base + k1];
+                if constexpr (Z3) z1 = a.sz[base + k1];
             }
             if (in2) {
                 p2[0] = sx[base + k2];
@@ -255,6 +290,7 @@ __device__ __forceinline__ void move_cell(const DsmcArgs<Real>& a, int c, unsign
                 p2[2] = svx[base + k2];
                 p2[3] = svy[base + k2];
                 p2[4] = svz[base + k2];
+                if constexpr (Z3) z2 = a.sz[base + k2];
             }
             // kick and straight flight; flights that cross a wall are redone below
             p1[3] = p1[3] + g;
@@ -265,10 +301,12 @@ __device__ __forceinline__ void move_cell(const DsmcArgs<Real>& a, int c, unsign
             if (!wall1) {
                 p1[0] = xn1;
                 p1[1] = p1[1] + p1[3] * dt;
+                if constexpr (Z3) z1 = z1 + p1[4] * dt;
             }
             if (!wall2) {
                 p2[0] = xn2;
                 p2[1] = p2[1] + p2[3] * dt;
+                if constexpr (Z3) z2 = z2 + p2[4] * dt;
             }
             if (__any_sync(kFull, wall1 || wall2)) {
 #pragma unroll 1
@@ -277,8 +315,13 @@ __device__ __forceinline__ void move_cell(const DsmcArgs<Real>& a, int c, unsign
                         Real q[5];
 #pragma unroll
                         for (int i = 0; i < 5; ++i) q[i] = h == 0 ? p1[i] : p2[i];
-                        wall_flight(a.seed, (uint32_t)c, h == 0 ? k1 : k2, s, H, dt, q[0], q[1], q[2],
-                                    q[3], q[4], hits, caps);
+                        Real qz = h == 0 ? z1 : z2;
+                        wall_flight<Real, Z3>(a.seed, (uint32_t)c, h == 0 ? k1 : k2, s, H, dt, q[0],
+                                              q[1], q[2], q[3], q[4], hits, caps, qz);
+                        if (h == 0)
+                            z1 = qz;
+                        else
+                            z2 = qz;
 #pragma unroll
                         for (int i = 0; i < 5; ++i) {
                             if (h == 0)
@@ -289,19 +332,19 @@ __device__ __forceinline__ void move_cell(const DsmcArgs<Real>& a, int c, unsign
                     }
                 }
             }
-            const uint32_t key1 = act1 ? cell_key(a, L, p1[0], p1[1]) : 0u;
-            const uint32_t key2 = act2 ? cell_key(a, L, p2[0], p2[1]) : 0u;
+            const uint32_t key1 = act1 ? cell_key<Real, Z3>(a, L, p1[0], p1[1], z1) : 0u;
+            const uint32_t key2 = act2 ? cell_key<Real, Z3>(a, L, p2[0], p2[1], z2) : 0u;
             uint32_t arr1, arr2;
             bin_arrival2(cnt, key1, act1, key2, act2, lane, arr1, arr2);
             if (act1) {
-                rec_store(rec, base + k1, p1[0], p1[1], p1[2], p1[3], p1[4]);
+                rec_store(rec, base + k1, p1[0], p1[1], p1[2], p1[3], p1[4], z1);
                 if (arr1 < bin)
                     tag[(int64_t)key1 * bin + arr1] = (uint32_t)(base + k1);
                 else
                     lost += 1;
             }
             if (act2) {
-                rec_store(rec, base + k2, p2[0], p2[1], p2[2], p2[3], p2[4]);
+                rec_store(rec, base + k2, p2[0], p2[1], p2[2], p2[3], p2[4], z2);
                 if (arr2 < bin)
                     tag[(int64_t)key2 * bin + arr2] = (uint32_t)(base + k2);
                 else
@@ -325,7 +368,7 @@ __device__ __forceinline__ void move_cell(const DsmcArgs<Real>& a, int c, unsign
 }
 
 // One warp per source cell (the cells of all replicas in the batch form).
-template <typename Real, bool BATCH>
+template <typename Real, bool BATCH, bool Z3 = false>
 __global__ void __launch_bounds__(256, 4) k_move(Launch<DsmcArgs<Real>> L) {
     pdl_begin();
     const unsigned lane = lane_id();
@@ -334,9 +377,9 @@ __global__ void __launch_bounds__(256, 4) k_move(Launch<DsmcArgs<Real>> L) {
     for (int64_t u = gw; u < L.total; u += nw) {
         if constexpr (BATCH) {
             const int r = replica_of(L.pre, L.nrep, u);
-            move_cell(L.tab[r], (int)(u - L.pre[r]), lane);
+            move_cell<Real, Z3>(L.tab[r], (int)(u - L.pre[r]), lane);
         } else {
-            move_cell(L.one, (int)u, lane);
+            move_cell<Real, Z3>(L.one, (int)u, lane);
         }
     }
 }
@@ -420,19 +463,20 @@ __device__ __forceinline__ void blocked_to_strided(uint32_t (&v)[R], uint32_t* s
 // origin slots src[r]: positions into the cell's bin of the other half, velocities into
 // shared memory. The record, position and shared-memory pointers are declared free of
 // aliasing, so the loads of all slots can be in flight before the first store.
-template <typename Real, int G, int RR>
+template <typename Real, int G, int RR, bool Z3>
 __device__ __forceinline__ void gather_slots(const Real* __restrict__ rec, Real* __restrict__ dx,
-                                             Real* __restrict__ dy, int gl, uint32_t n,
-                                             const uint32_t* src, Real* __restrict__ vx,
+                                             Real* __restrict__ dy, Real* __restrict__ dz, int gl,
+                                             uint32_t n, const uint32_t* src, Real* __restrict__ vx,
                                              Real* __restrict__ vy, Real* __restrict__ vz) {
 #pragma unroll
     for (int r = 0; r < RR; ++r) {
         const uint32_t k = (uint32_t)(gl + G * r);
         if (k < n) {
-            Real px, py, ux, uy, uz;
-            rec_load(rec, (int64_t)src[r], px, py, ux, uy, uz);
+            Real px, py, ux, uy, uz, pz;
+            rec_load<Z3>(rec, (int64_t)src[r], px, py, ux, uy, uz, pz);
             dx[k] = px;
             dy[k] = py;
+            if constexpr (Z3) dz[k] = pz;
             vx[k] = ux;
             vy[k] = uy;
             vz[k] = uz;
@@ -441,7 +485,7 @@ __device__ __forceinline__ void gather_slots(const Real* __restrict__ rec, Real*
 }
 
 // The block of 32 consecutive cells `blk` (of nblk) of one context.
-template <typename Real>
+template <typename Real, bool Z3>
 __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t pool, int blk,
                                               int nblk) {
     constexpr int G = kGroup;
@@ -577,8 +621,8 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
                             const uint32_t k = (uint32_t)(SMALL * q + gl + G * r);
                             src[r] = k < n ? st[k] : 0u;
                         }
-                        gather_slots<Real, G, R>(a.rec, a.dx + base, a.dy + base, SMALL * q + gl, n,
-                                                 src, vx, vy, vz);
+                        gather_slots<Real, G, R, Z3>(a.rec, a.dx + base, a.dy + base, a.dz + base,
+                                                     SMALL * q + gl, n, src, vx, vy, vz);
                     }
                 }
             } else {
@@ -591,7 +635,8 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
                 bitonic_blocked<G, R, R>(v);
                 blocked_to_strided<G, R, R>(v, st, n <= (uint32_t)SMALL ? n : 0u, gl);
                 if (n <= (uint32_t)SMALL)
-                    gather_slots<Real, G, R>(a.rec, a.dx + base, a.dy + base, gl, n, v, vx, vy, vz);
+                    gather_slots<Real, G, R, Z3>(a.rec, a.dx + base, a.dy + base, a.dz + base, gl,
+                                                 n, v, vx, vy, vz);
             }
             if (n > (uint32_t)(2 * SMALL))
                 for (uint32_t k = gl; k < n; k += G) st[k] = a.tag[base + k];
@@ -602,10 +647,11 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
                     const uint32_t t = st[k];
                     uint32_t r = 0;
                     for (uint32_t m = 0; m < n; ++m) r += st[m] < t ? 1u : 0u;
-                    Real px, py, ux, uy, uz;
-                    rec_load(a.rec, (int64_t)t, px, py, ux, uy, uz);
+                    Real px, py, ux, uy, uz, pz;
+                    rec_load<Z3>(a.rec, (int64_t)t, px, py, ux, uy, uz, pz);
                     a.dx[base + r] = px;
                     a.dy[base + r] = py;
+                    if constexpr (Z3) a.dz[base + r] = pz;
                     vx[r] = ux;
                     vy[r] = uy;
                     vz[r] = uz;
@@ -868,15 +914,16 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
     }
 }
 
-template <typename Real, bool BATCH>
+template <typename Real, bool BATCH, bool Z3 = false>
 __global__ void __launch_bounds__(kCollideWarps * 32, CollideCfg<Real>::MINB)
     k_collide(Launch<DsmcArgs<Real>> L, uint32_t pool) {
     pdl_begin();
     if constexpr (BATCH) {
         const int r = replica_of(L.pre, L.nrep, (int64_t)blockIdx.x);
-        collide_block(L.tab[r], pool, (int)(blockIdx.x - L.pre[r]), (int)(L.pre[r + 1] - L.pre[r]));
+        collide_block<Real, Z3>(L.tab[r], pool, (int)(blockIdx.x - L.pre[r]),
+                                (int)(L.pre[r + 1] - L.pre[r]));
     } else {
-        collide_block(L.one, pool, (int)blockIdx.x, (int)gridDim.x);
+        collide_block<Real, Z3>(L.one, pool, (int)blockIdx.x, (int)gridDim.x);
     }
 }
 
@@ -914,6 +961,9 @@ DsmcArgs<Real> make_args(Ctx& c) {
     a.g_step = c.d.g_step;
     a.coll_dt = c.d.coll_dt;
     a.coll_cell = (const Real*)c.st.coll_cell;
+    a.sz = (const Real*)c.st.pz[h];
+    a.dz = (Real*)c.st.pz[o];
+    a.ncz = c.p.ncz >= 2 ? c.p.ncz : 0;
     a.crmax_init = c.p.crmax_init;
     a.seed = c.p.seed;
     return a;
@@ -939,7 +989,7 @@ cudaError_t init_impl(Ctx& c) {
     return cudaGetLastError();
 }
 
-template <typename Real>
+template <typename Real, bool Z3>
 cudaError_t step_impl(Ctx& c) {
     DsmcArgs<Real> a = make_args<Real>(c);
     prof_begin(c, K_MOVE);
@@ -947,8 +997,8 @@ cudaError_t step_impl(Ctx& c) {
     Launch<DsmcArgs<Real>> L{};
     L.one = a;
     L.total = c.d.ncells;
-    cudaError_t e = launch_pdl(k_move<Real, false>, dim3(grid_for(c, c.d.ncells * 32, 256, 64)), dim3(256),
-                               0, c.stream, L);
+    cudaError_t e = launch_pdl(k_move<Real, false, Z3>, dim3(grid_for(c, c.d.ncells * 32, 256, 64)),
+                               dim3(256), 0, c.stream, L);
     if (e != cudaSuccess) return e;
     prof_end(c, K_MOVE);
     // shared memory: a pool of slots for the block's cells (3 Real + 1 u32 each), room for
@@ -959,12 +1009,14 @@ cudaError_t step_impl(Ctx& c) {
     const size_t smem = (size_t)pool * (3 * sizeof(Real) + 4) +
                         (size_t)NC * kChainSteps * (4 + 4 * sizeof(Real));
     // (dynamic and static shared memory together may exceed the default 48 KB)
-    e = cudaFuncSetAttribute(k_collide<Real, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_collide<Real, false, Z3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)((c.d.ncells + NC - 1) / NC);
     prof_begin(c, K_COLLIDE);
     L.total = grid;
-    e = launch_pdl(k_collide<Real, false>, dim3(grid), dim3(kCollideWarps * 32), smem, c.stream, L, pool);
+    e = launch_pdl(k_collide<Real, false, Z3>, dim3(grid), dim3(kCollideWarps * 32), smem, c.stream, L,
+                   pool);
     if (e != cudaSuccess) return e;
     prof_end(c, K_COLLIDE);
     return cudaGetLastError();
@@ -993,7 +1045,8 @@ cudaError_t launch_init(Ctx& c) {
 }
 
 cudaError_t launch_dsmc_step(Ctx& c) {
-    return (c.p.real_bytes == 4) ? step_impl<float>(c) : step_impl<double>(c);
+    if (c.p.ncz >= 2) return (c.p.real_bytes == 4) ? step_impl<float, true>(c) : step_impl<double, true>(c);
+    return (c.p.real_bytes == 4) ? step_impl<float, false>(c) : step_impl<double, false>(c);
 }
 
 size_t dsmc_args_bytes(int real_bytes) {

@@ -63,26 +63,35 @@ __device__ __forceinline__ int wrap_y(int v, int ny) {
     return v;
 }
 
-// Pull streaming of node (x, y): fs[q] = f[q](x - e_q), periodic in y; sources behind a wall
-// take the wall Maxwellian with the wall density of the row (the mass leaving through that
-// wall, re-emitted at rest).
-template <typename Real, class LAT>
+// Pull streaming of node (x, y[, z]): fs[q] = f[q](x - e_q), periodic in y (and in z in 3D);
+// sources behind a wall take the wall Maxwellian with the wall density of the streamwise row
+// (y, z) (the mass leaving through that wall, re-emitted at rest).
+template <typename Real, class LAT, bool Z3 = false>
 __device__ __forceinline__ void pull_node(const Real* __restrict__ src, int x, int y, int nx, int ny,
-                                          int64_t nn, Real (&fs)[LAT::Q]) {
+                                          int64_t nn, Real (&fs)[LAT::Q], int z = 0, int nz = 1) {
     constexpr int Q = LAT::Q;
-    // Row offsets y' * nx of the pull sources y' = y - ey (periodic), ey = -MAXV..MAXV.
+    // Row offsets y' * nx of the pull sources y' = y - ey (periodic), ey = -MAXV..MAXV, and in
+    // 3D the layer offsets z' nx ny of z' = z - ez (periodic).
     constexpr int MV = LAT::MAXV;
     int rowoff[2 * MV + 1];
 #pragma unroll
     for (int i = 0; i < 2 * MV + 1; ++i) rowoff[i] = wrap_y(y - (i - MV), ny) * nx;
+    int64_t layoff[Z3 ? 2 * MV + 1 : 1];
+    layoff[0] = 0;
+    if constexpr (Z3) {
+#pragma unroll
+        for (int i = 0; i < 2 * MV + 1; ++i) layoff[i] = (int64_t)wrap_y(z - (i - MV), nz) * nx * ny;
+    }
+    (void)nz;
 
     Real rhoL = (Real)0, rhoR = (Real)0;
     if (x < MV || x >= nx - MV) {
         Real ml = (Real)0, mr = (Real)0;
         static_for<Q>([&](auto qc) {
             constexpr int q = decltype(qc)::value;
-            constexpr int ex = E<LAT>(q, 0), ey = E<LAT>(q, 1);
-            const Real* __restrict__ sq = src + (int64_t)q * nn + rowoff[ey + MV];
+            constexpr int ex = E<LAT>(q, 0), ey = E<LAT>(q, 1), ez = E<LAT>(q, 2);
+            const Real* __restrict__ sq =
+                src + (int64_t)q * nn + rowoff[ey + MV] + (Z3 ? layoff[Z3 ? ez + MV : 0] : 0);
             if constexpr (ex < 0) {
 #pragma unroll
                 for (int i = 0; i < -ex; ++i) ml += sq[i];
@@ -99,8 +108,8 @@ __device__ __forceinline__ void pull_node(const Real* __restrict__ src, int x, i
 
     static_for<Q>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
-        constexpr int ex = E<LAT>(q, 0), ey = E<LAT>(q, 1);
-        const Real* __restrict__ sq = src + (int64_t)q * nn;
+        constexpr int ex = E<LAT>(q, 0), ey = E<LAT>(q, 1), ez = E<LAT>(q, 2);
+        const Real* __restrict__ sq = src + (int64_t)q * nn + (Z3 ? layoff[Z3 ? ez + MV : 0] : 0);
         const int sx = x - ex;
         const int off = rowoff[ey + MV] + sx;
         if constexpr (ex > 0)
@@ -162,16 +171,21 @@ __device__ __forceinline__ void node_moments(const Real (&fs)[LAT::Q], Real& rho
 // from the per-node arrays. BGK: the unregularised collision of the proof-of-concept hybrid
 // (Sec. 4), f' = (1 - om) f_eq + om f + of F: the series then carries (1 - om) times the
 // equilibrium coefficients plus the force, and om f is added per population.
-template <typename Real, class LAT, bool PARAM, bool BGK = false>
+template <typename Real, class LAT, bool PARAM, bool BGK = false, bool Z3 = false>
 __device__ __forceinline__ void lbm_node(const LbmArgs<Real>& a, const int64_t node) {
     constexpr int Q = LAT::Q;
     constexpr double R = lat_r<LAT>();
     const int nx = a.nx, ny = a.ny;
-    const int x = (int)(node % nx), y = (int)(node / nx);
     const int64_t nn = a.nnodes;
 
     Real fs[Q];
-    pull_node<Real, LAT>(a.src, x, y, nx, ny, nn, fs);
+    if constexpr (Z3) {  // node (z ny + y) nx + x
+        const int64_t row = node / nx;
+        pull_node<Real, LAT, true>(a.src, (int)(node % nx), (int)(row % ny), nx, ny, nn, fs,
+                                   (int)(row / ny), a.nz);
+    } else {
+        pull_node<Real, LAT>(a.src, (int)(node % nx), (int)(node / nx), nx, ny, nn, fs);
+    }
     Real rho, jx, jy, jz, pm[6], q3[10];
     node_moments<Real, LAT>(fs, rho, jx, jy, jz, pm, q3);
     const Real pxx = pm[0], pxy = pm[1], pxz = pm[2], pyy = pm[3], pyz = pm[4], pzz = pm[5];
@@ -287,7 +301,7 @@ __device__ __forceinline__ void lbm_node(const LbmArgs<Real>& a, const int64_t n
 
 // One thread per node (the nodes of all replicas in the batch form); BGK selects the
 // unregularised collision (one instantiation per collision keeps each one's registers).
-template <typename Real, class LAT, bool BATCH, bool BGK = false, bool PARAM = false>
+template <typename Real, class LAT, bool BATCH, bool BGK = false, bool PARAM = false, bool Z3 = false>
 __global__ void __launch_bounds__(128) k_lbm(Launch<LbmArgs<Real>> L) {
     pdl_begin();
     const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -296,7 +310,7 @@ __global__ void __launch_bounds__(128) k_lbm(Launch<LbmArgs<Real>> L) {
         const int r = replica_of(L.pre, L.nrep, u);
         lbm_node<Real, LAT, PARAM, BGK>(L.tab[r], u - L.pre[r]);
     } else {
-        lbm_node<Real, LAT, PARAM, BGK>(L.one, u);
+        lbm_node<Real, LAT, PARAM, BGK, Z3>(L.one, u);
     }
 }
 
@@ -707,6 +721,7 @@ LbmArgs<Real> lbm_args(const Ctx& c, int cur_f) {
     a.g_node = nullptr;
     a.tau_node = (const Real*)c.st.tau_node;  // Kn profile, or null
     a.bgk = c.p.lb_collision;
+    a.nz = (int32_t)c.d.nz;
     return a;
 }
 
@@ -720,7 +735,12 @@ cudaError_t lbm_impl(Ctx& c) {
     L.total = c.d.nnodes;
     const dim3 g((unsigned)blocks), b(128);
     cudaError_t e;
-    if (a.tau_node)  // Kn profile: per-node tau
+    if (a.nz > 1)  // 3D: periodic in z
+        e = a.tau_node ? (a.bgk ? launch_pdl(k_lbm<Real, LAT, false, true, true, true>, g, b, 0, c.stream, L)
+                                : launch_pdl(k_lbm<Real, LAT, false, false, true, true>, g, b, 0, c.stream, L))
+                       : (a.bgk ? launch_pdl(k_lbm<Real, LAT, false, true, false, true>, g, b, 0, c.stream, L)
+                                : launch_pdl(k_lbm<Real, LAT, false, false, false, true>, g, b, 0, c.stream, L));
+    else if (a.tau_node)  // Kn profile: per-node tau
         e = a.bgk ? launch_pdl(k_lbm<Real, LAT, false, true, true>, g, b, 0, c.stream, L)
                   : launch_pdl(k_lbm<Real, LAT, false, false, true>, g, b, 0, c.stream, L);
     else

@@ -89,8 +89,10 @@ __device__ __forceinline__ void d2l_entries(const MapArgs<Real>& a, int first, i
             if (lane == 0) atomicOr(&a.ctrl[CTRL_STATUS], HYB_ST_BAD_INPUT);
             continue;
         }
-        const int x = node % a.nx, y = node / a.nx;
-        const int64_t cell = (int64_t)(y / a.lb_ratio) * a.ncx + (x / a.lb_ratio);
+        // node (z ny + y) nx + x lies in cell (iz ncy + iy) ncx + ix (z = 0 in 2D)
+        const int x = node % a.nx, y = (node / a.nx) % a.ny, z = node / (a.nx * a.ny);
+        const int64_t cell =
+            ((int64_t)(z / a.lb_ratio) * a.ncy + y / a.lb_ratio) * a.ncx + (x / a.lb_ratio);
         const double* m = a.acc + cell * kMoments;
         const double mk = lane < (unsigned)kMoments ? m[lane] : 0.0;
         const double NS = __shfl_sync(kFull, mk, 0);
@@ -257,7 +259,7 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int k) {
 // two terms and then reduces over the lanes (halving_sum), which is the oracle's pairwise
 // order. Products are (f c_i) c_j and ((f c_i) c_j) c_k with i <= j <= k. Returns, in every
 // lane, the packed values (lane k < 20 holds value k: a2[6], a3[10], u[3], C) and rho.
-template <typename Real, class LAT>
+template <typename Real, class LAT, bool Z3>
 __device__ __forceinline__ void grad_coefficients(const MapArgs<Real>& a, int cell, unsigned lane,
                                                   Real& mine, Real& rho_out) {
     constexpr int Q = LAT::Q;
@@ -274,27 +276,32 @@ __device__ __forceinline__ void grad_coefficients(const MapArgs<Real>& a, int ce
         if (v0) xi0[i] = lt.x[3 * q0 + i];
         if (v1) xi1[i] = lt.x[3 * q1 + i];
     }
-    const int ix = cell % a.ncx, iy = cell / a.ncx;
-    // mean populations of the cell's nodes, summed in node order (dy, dx)
-    Real p0[4], p1[4];
+    const int ix = cell % a.ncx, iy = (cell / a.ncx) % a.ncy, iz = cell / (a.ncx * a.ncy);
+    // mean populations of the cell's nodes (r^2 in 2D, r^3 in 3D), summed in node order
+    // (dz, dy, dx)
+    constexpr int KN = Z3 ? 8 : 4;  // lb_ratio <= 2
+    const int nk = Z3 ? r * r * r : r * r;
+    Real p0[KN], p1[KN];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < KN; ++k) {
         p0[k] = 0;
         p1[k] = 0;
-        if (k < r * r) {
-            const int64_t node = (int64_t)(iy * r + k / r) * a.nx + (ix * r + k % r);
+        if (k < nk) {
+            const int dz = Z3 ? k / (r * r) : 0, dy = (k / r) % r, dx = k % r;
+            const int64_t node =
+                ((int64_t)(iz * r + dz) * a.ny + (iy * r + dy)) * a.nx + (ix * r + dx);
             if (v0) p0[k] = a.f[(int64_t)q0 * a.nnodes + node];
             if (v1) p1[k] = a.f[(int64_t)q1 * a.nnodes + node];
         }
     }
     Real s0 = 0, s1 = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-        if (k < r * r) {
+    for (int k = 0; k < KN; ++k)
+        if (k < nk) {
             s0 += p0[k];
             s1 += p1[k];
         }
-    const Real nn = (Real)(r * r);
+    const Real nn = (Real)nk;
     const Real f0 = v0 ? s0 / nn : (Real)0;
     const Real f1 = v1 ? s1 / nn : (Real)0;
     // rho and j; lanes 0-7 end with rho, 8-15 jx, 16-23 jy, 24-31 jz
@@ -356,7 +363,7 @@ __device__ __forceinline__ void grad_coefficients(const MapArgs<Real>& a, int ce
 // cell index is skipped and flagged; a cell whose new count exceeds its bin keeps its
 // particles and raises the capacity status. The Grad record of each listed cell is written
 // to a.grad.
-template <typename Real, class LAT>
+template <typename Real, class LAT, bool Z3>
 __device__ __forceinline__ void l2d_cells(const MapArgs<Real>& a, int first, int stride) {
     __shared__ unsigned s_am[kL2DWarps], s_em[kL2DWarps], s_vm[kL2DWarps];
     __shared__ Real s_c[20];
@@ -371,7 +378,7 @@ __device__ __forceinline__ void l2d_cells(const MapArgs<Real>& a, int first, int
     int32_t dlive = 0;
     for (int ci = first; ci < a.n; ci += stride) {
         const int32_t icell = a.list[ci];
-        if (icell < 0 || icell >= a.ncx * a.ncy) {
+        if (icell < 0 || icell >= a.ncx * a.ncy * (Z3 ? a.ncz : 1)) {
             flags |= HYB_ST_BAD_INPUT;
             continue;
         }
@@ -379,7 +386,7 @@ __device__ __forceinline__ void l2d_cells(const MapArgs<Real>& a, int first, int
         const uint32_t old = threadIdx.x == 0 ? a.count[cell] : 0u;
         if (w == 0) {
             Real mine, rho;
-            grad_coefficients<Real, LAT>(a, icell, lane, mine, rho);
+            grad_coefficients<Real, LAT, Z3>(a, icell, lane, mine, rho);
             GradRec& g = a.grad[ci];
             Real* pv = reinterpret_cast<Real*>(g.v);
             if (lane < 20u) {
@@ -411,7 +418,9 @@ __device__ __forceinline__ void l2d_cells(const MapArgs<Real>& a, int first, int
             continue;
         }
         const int64_t out0 = (int64_t)cell * bin;
-        const Real fx = (Real)(cell % (uint32_t)a.ncx), fy = (Real)(cell / (uint32_t)a.ncx);
+        const Real fx = (Real)(cell % (uint32_t)a.ncx);
+        const Real fy = (Real)((cell / (uint32_t)a.ncx) % (uint32_t)a.ncy);
+        const Real fz = Z3 ? (Real)(cell / ((uint32_t)a.ncx * (uint32_t)a.ncy)) : (Real)0;
         const uint64_t cap64 = 1000ull * nnew;
         const uint32_t cap = cap64 < 0xFFFFFFull ? (uint32_t)cap64 : 0xFFFFFFu;
         uint32_t produced = 0, j0 = 0;
@@ -454,6 +463,7 @@ __device__ __forceinline__ void l2d_cells(const MapArgs<Real>& a, int first, int
                 const int64_t slot = out0 + produced + rank;
                 a.x[slot] = fx + (Real)u01f(r2.y);
                 a.y[slot] = fy + (Real)u01f(r2.z);
+                if constexpr (Z3) a.z[slot] = fz + (Real)u01f(r2.w);
                 a.vx[slot] = X + ux;
                 a.vy[slot] = Y + uy;
                 a.vz[slot] = Z + uz;
@@ -517,15 +527,15 @@ __device__ __forceinline__ void l2d_cells(const MapArgs<Real>& a, int first, int
 }
 
 // LB2DSMC: one block per listed cell (the listed cells of all replicas in the batch form).
-template <typename Real, class LAT, bool BATCH>
+template <typename Real, class LAT, bool BATCH, bool Z3 = false>
 __global__ void __launch_bounds__(kL2DWarps * 32) k_l2d(Launch<MapArgs<Real>> L) {
     pdl_begin();
     if constexpr (BATCH) {
         const int r = replica_of(L.pre, L.nrep, (int64_t)blockIdx.x);
         const MapArgs<Real>& a = L.tab[r];
-        l2d_cells<Real, LAT>(a, (int)(blockIdx.x - L.pre[r]), a.n);
+        l2d_cells<Real, LAT, Z3>(a, (int)(blockIdx.x - L.pre[r]), a.n);
     } else {
-        l2d_cells<Real, LAT>(L.one, (int)blockIdx.x, (int)gridDim.x);
+        l2d_cells<Real, LAT, Z3>(L.one, (int)blockIdx.x, (int)gridDim.x);
     }
 }
 
@@ -556,6 +566,8 @@ MapArgs<Real> map_args(Ctx& c, const int32_t* list, int32_t n) {
     a.vx = (Real*)c.st.pvx[c.cur_p];
     a.vy = (Real*)c.st.pvy[c.cur_p];
     a.vz = (Real*)c.st.pvz[c.cur_p];
+    a.ncz = c.p.ncz >= 2 ? c.p.ncz : 0;
+    a.z = (Real*)c.st.pz[c.cur_p];
     return a;
 }
 
@@ -584,9 +596,10 @@ cudaError_t l2d_launch(Ctx& c, const MapArgs<Real>& a, int32_t n) {
     Launch<MapArgs<Real>> L{};
     L.one = a;
     L.total = n;
-    const cudaError_t e = launch_pdl(k_l2d<Real, LAT, false>,
-                                     dim3(blocks_for(c, (int64_t)n * 32 * kL2DWarps, 32 * kL2DWarps, 8)),
-                                     dim3(32 * kL2DWarps), 0, c.stream, L);
+    const dim3 grid(blocks_for(c, (int64_t)n * 32 * kL2DWarps, 32 * kL2DWarps, 8));
+    const cudaError_t e =
+        a.ncz ? launch_pdl(k_l2d<Real, LAT, false, true>, grid, dim3(32 * kL2DWarps), 0, c.stream, L)
+              : launch_pdl(k_l2d<Real, LAT, false, false>, grid, dim3(32 * kL2DWarps), 0, c.stream, L);
     prof_end(c, K_L2D);
     return e;
 }

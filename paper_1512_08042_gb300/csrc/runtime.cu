@@ -25,10 +25,11 @@ bool params_valid(const hyb_params* p) {
         return false;
     if (p->kn_profile != 0 && p->kn_profile != 1) return false;
     if (p->kn_profile == 1 && !(p->kn_end > 0.0)) return false;
+    if (p->ncz < 0) return false;
     if (!(p->kn > 0.0) || !(p->crmax_init > 0.0) || !(p->capacity_factor >= 1.0)) return false;
     if (!(p->ma >= 0.0) || !(p->T_K > 0.0) || !(p->mass_kg > 0.0)) return false;
     if (std::ceil(p->capacity_factor * (double)p->ppc) > 256.0) return false;  // bin <= 256
-    const double slots = (double)p->ncx * (double)p->ncy * 256.0;
+    const double slots = (double)p->ncx * (double)p->ncy * (double)(p->ncz >= 2 ? p->ncz : 1) * 256.0;
     if (slots >= 4294967295.0) return false;  // slot indices are u32
     return true;
 }
@@ -46,10 +47,13 @@ void derive(const hyb_params& p, hyb_derived& d) {
     d.coll_dt = d.dt / (std::sqrt(2.0) * d.lambda * (double)p.ppc);
     d.g_step = 8.0 * (d.tau - 0.5) * p.ma * d.cs_lat * d.cs_lat / (d.H_lat * d.H_lat);
     d.c_th_ms = std::sqrt(kBoltzmann * p.T_K / p.mass_kg);
-    d.ncells = (int64_t)p.ncx * p.ncy;
+    // 3D when ncz >= 2: cells (iz ncy + iy) ncx + ix, nodes (z ny + y) nx + x
+    d.ncz = p.ncz >= 2 ? p.ncz : 1;
+    d.ncells = (int64_t)p.ncx * p.ncy * d.ncz;
     d.nx = (int64_t)p.ncx * p.lb_ratio;
     d.ny = (int64_t)p.ncy * p.lb_ratio;
-    d.nnodes = d.nx * d.ny;
+    d.nz = p.ncz >= 2 ? d.ncz * p.lb_ratio : 1;
+    d.nnodes = d.nx * d.ny * d.nz;
     d.bin = ((int32_t)std::ceil(p.capacity_factor * (double)p.ppc) + 31) / 32 * 32;
     d.capacity = d.ncells * (int64_t)d.bin;
     d.q = p.lattice;
@@ -89,6 +93,7 @@ void layout(const hyb_params& p, const hyb_derived& d, hyb_layout& L) {
     const bool prof = p.kn_profile == 1;
     L.coll_cell = take(prof ? nc * rb : 0);
     L.tau_node = take(prof ? nn * rb : 0);
+    for (int h = 0; h < 2; ++h) L.z[h] = take(p.ncz >= 2 ? cap * rb : 0);
     L.total_bytes = off;
     L.capacity = d.capacity;
     L.ncells = d.ncells;
@@ -175,6 +180,7 @@ void resolve(Ctx& c) {
         s.pvx[h] = a + L.vx[h];
         s.pvy[h] = a + L.vy[h];
         s.pvz[h] = a + L.vz[h];
+        s.pz[h] = c.p.ncz >= 2 ? a + L.z[h] : nullptr;
         s.f[h] = a + L.f[h];
         s.count[h] = (uint32_t*)(a + L.count[h]);
     }
@@ -223,11 +229,11 @@ hyb_status fill_kn_profile(Ctx& c) {
     const int64_t nc = c.d.ncells, nn = c.d.nnodes;
     std::vector<double> cell(nc), node(nn);
     for (int64_t k = 0; k < nc; ++k) {
-        const double kn = kn_at(c.p, (double)(k / c.p.ncx) + 0.5);
+        const double kn = kn_at(c.p, (double)((k / c.p.ncx) % c.p.ncy) + 0.5);
         cell[k] = c.d.dt / (std::sqrt(2.0) * (kn * (double)c.p.ncx) * (double)c.p.ppc);
     }
     for (int64_t k = 0; k < nn; ++k) {
-        const double kn = kn_at(c.p, ((double)(k / c.d.nx) + 0.5) / (double)c.p.lb_ratio);
+        const double kn = kn_at(c.p, ((double)((k / c.d.nx) % c.d.ny) + 0.5) / (double)c.p.lb_ratio);
         node[k] = std::sqrt(kPi / 8.0) * c.d.r_lat * kn * c.d.H_lat + 0.5;
     }
     auto put = [&](const std::vector<double>& v, void* dst) {
@@ -385,7 +391,8 @@ hyb_status map_lbm_to_dsmc(hyb_ctx* h, const int32_t* dev_cells, int32_t n) {
 
 hyb_status lbm_step_nodes(hyb_ctx* h, const void* f_src, void* f_dst, const void* g_node,
                           const void* tau_node) {
-    if (!h || !f_src || !f_dst || f_src == f_dst || !g_node || !tau_node) return HYB_EINVAL;
+    if (!h || !f_src || !f_dst || f_src == f_dst || !g_node || !tau_node || h->c.d.nz != 1)
+        return HYB_EINVAL;
     return check(h->c, launch_lbm_step_nodes(h->c, f_src, f_dst, g_node, tau_node),
                  "lbm_step_nodes launch");
 }
@@ -403,7 +410,7 @@ hyb_status lbm_adjoint_step(hyb_ctx* h, const void* f, const void* lam_next, voi
                             const void* g_node, const void* tau_node, void* grad_g,
                             void* grad_tau, void* wall) {
     if (!h || !f || !lam_next || !lam || lam == lam_next || !g_node || !tau_node || !grad_g ||
-        !grad_tau || !wall || h->c.p.lb_collision != 0)
+        !grad_tau || !wall || h->c.p.lb_collision != 0 || h->c.d.nz != 1)
         return HYB_EINVAL;
     return check(h->c, launch_lbm_adjoint_step(h->c, f, lam_next, lam, g_node, tau_node, grad_g,
                                                grad_tau, wall),

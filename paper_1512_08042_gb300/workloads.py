@@ -94,8 +94,20 @@ def coupling_sites(cfg, strip_cells=None):
     to each wall (i = 1 and i = H - 2). Otherwise a strip `strip_cells` DSMC cells wide
     (default 4, i.e. 8 LB nodes at two nodes per cell) across the whole channel height, in
     the middle of the streamwise period, as the one-cell buffer layer of Sec. 4 widened.
-    Returns (nodes, cells) as int32 arrays; node = y * nx + x, cell = iy * ncx + ix.
+    Returns (nodes, cells) as int32 arrays; node = y * nx + x, cell = iy * ncx + ix. In 3D
+    (ncz >= 2) the same sites in every layer: node (z ny + y) nx + x, cell (iz ncy + iy) ncx + ix.
     """
+    nodes, cells = _coupling_sites_2d(cfg, strip_cells)
+    ncz = cfg.get("ncz", 0)
+    if ncz >= 2:
+        r = cfg["lb_ratio"]
+        nn2, nc2 = cfg["ncx"] * cfg["ncy"] * r * r, cfg["ncx"] * cfg["ncy"]
+        nodes = (np.arange(ncz * r, dtype=np.int64)[:, None] * nn2 + nodes[None, :]).reshape(-1)
+        cells = (np.arange(ncz, dtype=np.int64)[:, None] * nc2 + cells[None, :]).reshape(-1)
+    return nodes.astype(np.int32), cells.astype(np.int32)
+
+
+def _coupling_sites_2d(cfg, strip_cells):
     ncx, ncy, r = cfg["ncx"], cfg["ncy"], cfg["lb_ratio"]
     nx = ncx * r
     if cfg.get("coupling") == "buffer_row":

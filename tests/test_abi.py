@@ -115,3 +115,38 @@ def test_batch_layout_places_replicas_and_tables(lib):
     params = (B.HybParams * 2)(*[B.make_params(c) for c in mixed])
     assert lib.hyb_batch_layout(params, 2, off) == B.HYB_EINVAL
     assert lib.hyb_batch_layout(params, 0, off) == B.HYB_EINVAL
+
+
+@pytest.mark.parametrize("ncz", [0, 1, 2, 5])
+def test_3d_derive_and_layout(lib, ncz):
+    # ncz < 2 is the slab; ncz >= 2 adds ncz * lb_ratio LB layers and the z positions
+    cfg = W.config(ncx=12, ncy=4, ppc=30, lb_ratio=2, ncz=ncz, real_bytes=8)
+    a, b = B.derive(cfg), O.derive(cfg)
+    for k in a:
+        assert a[k] == b[k], k
+    three_d = ncz >= 2
+    assert a["ncells"] == 12 * 4 * (ncz if three_d else 1)
+    assert a["nz"] == (2 * ncz if three_d else 1)
+    assert a["nnodes"] == 24 * 8 * a["nz"]
+    L = B.layout(cfg)
+    if three_d:
+        regions = sorted([(L.z[0], 8 * a["capacity"]), (L.z[1], 8 * a["capacity"])] +
+                         [(getattr(L, k)[h], 8 * a["capacity"]) for k in ("x", "y", "vx", "vy", "vz")
+                          for h in range(2)] + [(L.f[h], 8 * a["q"] * a["nnodes"]) for h in range(2)])
+        for (o1, s1), (o2, _) in zip(regions, regions[1:]):
+            assert o1 % 256 == 0 and o1 + s1 <= o2
+        assert regions[-1][0] + regions[-1][1] <= L.total_bytes
+    else:
+        assert L.z[0] == L.z[1] == L.total_bytes  # empty
+
+
+def test_3d_restrictions_are_rejected(lib):
+    cfg3 = W.config(ncx=8, ncy=2, ppc=5, ncz=2, seed=1)
+    B.derive(cfg3)
+    with pytest.raises(B.HybError) as ei:
+        B.derive(dict(cfg3, ncz=-1))
+    assert ei.value.status == B.HYB_EINVAL
+    # a batch is for slabs only
+    params = (B.HybParams * 2)(*[B.make_params(c) for c in (cfg3, cfg3)])
+    off = (ctypes.c_uint64 * 4)()
+    assert lib.hyb_batch_layout(params, 2, off) == B.HYB_EINVAL
