@@ -38,22 +38,25 @@ def kernel_algorithmic_bytes(name, cfg, d, n_particles, n_nodes_map, n_cells_map
     """Bytes a kernel must move per launch: reads and writes of its inputs and outputs."""
     rb = cfg["real_bytes"]
     ncells = d["ncells"]
+    three_d = d["ncz"] >= 2
+    pr = 6 if three_d else 5  # Reals per particle: x, y (, z), vx, vy, vz
     if name == "move":
-        # 5 Real read, 5 Real + a u32 tag written per particle; per cell: its count read and
+        # pr Real read, pr Real + a u32 tag written per particle; per cell: its count read and
         # the destination counts' atomics
-        return n_particles * (10 * rb + 4) + ncells * 8
+        return n_particles * (2 * pr * rb + 4) + ncells * 8
     if name == "collide":
-        # 5 Real + tag read, 5 Real written per particle; per cell: count, crmax, rem, nbar_sum
-        # read and written, the source count cleared, 20 FP64 sums read and written
-        return n_particles * (10 * rb + 4) + ncells * (4 + 2 * rb + 2 * rb + 8 + 4 + 320)
+        # pr Real + tag read, pr Real written per particle; per cell: count, crmax, rem,
+        # nbar_sum read and written, the source count cleared, 20 FP64 sums read and written
+        return n_particles * (2 * pr * rb + 4) + ncells * (4 + 2 * rb + 2 * rb + 8 + 4 + 320)
     if name == "lbm":
         return d["nnodes"] * 2 * d["q"] * rb
     if name == "dsmc2lb":
         return n_nodes_map * (160 + d["q"] * rb)
     if name == "lb2dsmc":
-        # populations of the coupling cells' nodes read; one record and ppc new particles
-        # written per coupling cell
-        return n_cells_map * (cfg["lb_ratio"] ** 2 * d["q"] * rb + 176 + cfg["ppc"] * 5 * rb)
+        # populations of the coupling cells' nodes (r^2, or r^3 in 3D) read; one record and
+        # ppc new particles written per coupling cell
+        nodes_per_cell = cfg["lb_ratio"] ** (3 if three_d else 2)
+        return n_cells_map * (nodes_per_cell * d["q"] * rb + 176 + cfg["ppc"] * pr * rb)
     return 0
 
 

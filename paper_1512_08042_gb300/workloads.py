@@ -41,6 +41,11 @@ WORKLOADS = {
     # (y = L/2) and back: per-cell NTC factors and per-node relaxation times.
     "poiseuille_512x4096_ppc50_knvar_fp32": config(ncx=512, ncy=4096, ppc=50, lb_ratio=2,
                                                     kn=0.005, kn_profile=1, kn_end=0.5, seed=6),
+    # Full 3D channel: 64 x 256 x 8 DSMC cells (periodic y and z, Sec. 3.1), 50 per cell
+    # (6,553,600), FP32 state, 128 x 512 x 16 D3Q39 lattice, the 4-cell coupling strip in
+    # every layer.
+    "poiseuille3d_64x256x8_ppc50_fp32": config(ncx=64, ncy=256, ncz=8, ppc=50, lb_ratio=2,
+                                                kn=0.05, seed=8),
     # The proof-of-concept hybrid of Sec. 4: plane Poiseuille at Kn 0.05 and Ma 0.1, D3Q19
     # without regularisation, DSMC2LB to the local equilibrium of rho and u (Eq. feq_dsmc)
     # on a buffer layer one cell long at y = L0/2 across the whole height, DSMC solved on its

@@ -969,3 +969,74 @@ def test_dsmc_3d_equilibrium_box_collision_rate_and_wall_flux():
         s = slice(cs[c], cs[c + 1])
         assert np.all(np.floor(p["x"][s]) == ix) and np.all(np.floor(p["y"][s]) == iy)
         assert np.all(np.floor(p["z"][s]) == iz)
+
+
+def test_lbm_3d_without_force_commutes_with_swapping_y_and_z():
+    # y and z are both periodic and the walls are normal to x, so without the body force the
+    # lattice step is symmetric under the exchange of y and z (with e_y and e_z exchanged in
+    # the velocity set). Populations that vary in x, y and z pin the sign and the layer of
+    # the z pull and the per-(y, z) wall rows: stepping the exchanged populations gives the
+    # exchanged result.
+    for q in (39, 19):
+        cfg = small_cfg(ncx=7, ncy=3, ncz=3, lb_ratio=2, lattice=q, ma=0.0, kn=0.2)
+        o = O.Oracle(cfg)
+        d = o.d
+        assert d["g_step"] == 0.0 and d["ny"] == d["nz"] == 6
+        e, w, r = O.lattice(q)
+        idx = {tuple(v): k for k, v in enumerate(e.tolist())}
+        perm = np.array([idx[(v[0], v[2], v[1])] for v in e.tolist()])
+        shape = (q, d["nz"], d["ny"], d["nx"])
+        fa = W.gen_populations(w, d["nnodes"], seed=19, eps=0.1, rho_eps=0.2).reshape(shape)
+        fb = np.empty_like(fa)
+        fb[perm] = fa.transpose(0, 2, 1, 3)  # f_b(x, y, z) at e' = f_a(x, z, y) at e
+        o.set_f(fa)
+        o.lbm_step(2)
+        ga = o.f().copy()
+        o2 = O.Oracle(cfg)
+        o2.set_f(fb)
+        o2.lbm_step(2)
+        gb = o2.f()
+        want = np.empty_like(ga)
+        want[perm] = ga.transpose(0, 2, 1, 3)
+        assert np.allclose(gb, want, rtol=1e-13, atol=1e-15), (q, np.abs(gb - want).max())
+        assert not np.allclose(ga, ga[:, :1])  # the state does vary along z
+
+
+def test_dsmc_3d_free_flight_moves_z_by_vz_dt_and_wraps():
+    # At a huge Kn no pair is selected, and without the body force each particle flies
+    # straight: z' = z + vz dt wrapped into [0, ncz), likewise y, x' = x + vx dt (no wall is
+    # reached), and the velocities are unchanged. Each particle lands in the bin of the cell
+    # holding it.
+    cfg = small_cfg(ncx=6, ncy=3, ncz=4, ppc=10, kn=1e6, ma=0.0, capacity_factor=6.0)
+    o = O.Oracle(cfg)
+    d = o.d
+    dt = d["dt"]
+    rng = np.random.default_rng(4)
+    n = 300
+    x = rng.uniform(2.0, 4.0, n)
+    y = rng.uniform(0.0, 3.0, n)
+    z = rng.uniform(0.0, 4.0, n)
+    vx = rng.uniform(-2.0, 2.0, n)  # |vx| dt < 2: no wall
+    vy = rng.normal(0.0, 3.0, n)
+    vz = rng.normal(0.0, 3.0, n)
+    cell = (np.floor(z).astype(int) * 3 + np.floor(y).astype(int)) * 6 + np.floor(x).astype(int)
+    order = np.argsort(cell, kind="stable")
+    counts = np.bincount(cell, minlength=d["ncells"])
+    cs = np.zeros(d["ncells"] + 1, np.uint32)
+    cs[1:] = np.cumsum(counts)
+    o.set_particles(x[order], y[order], vx[order], vy[order], vz[order], cs, z=z[order])
+    o.dsmc_step(1)
+    assert o.counters()["collisions"] == 0 and o.counters()["wall_hits"] == 0
+    p = o.particles()
+    got = np.argsort(p["vx"])
+    ref = np.argsort(vx)
+    assert np.array_equal(p["vx"][got], vx[ref]) and np.array_equal(p["vz"][got], vz[ref])
+    assert np.array_equal(p["vy"][got], vy[ref])
+    assert np.allclose(p["x"][got], (x + vx * dt)[ref], rtol=0, atol=1e-12)
+    assert np.allclose(p["y"][got], np.mod(y + vy * dt, 3.0)[ref], rtol=0, atol=1e-12)
+    assert np.allclose(p["z"][got], np.mod(z + vz * dt, 4.0)[ref], rtol=0, atol=1e-12)
+    assert (np.abs(vz * dt) > 1).sum() > 50 and ((z + vz * dt < 0) | (z + vz * dt >= 4)).sum() > 20
+    cs1 = o.get(O.A_CELL_START).astype(np.int64)
+    own = np.repeat(np.arange(d["ncells"]), np.diff(cs1))
+    c1 = (np.floor(p["z"]).astype(int) * 3 + np.floor(p["y"]).astype(int)) * 6 + np.floor(p["x"]).astype(int)
+    assert np.array_equal(c1, own)
