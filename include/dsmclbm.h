@@ -281,6 +281,30 @@ hyb_status hyb_hybrid_step(hyb_ctx* ctx, const int32_t* dev_nodes, int32_t n_nod
                            const int32_t* dev_cells, int32_t n_cells, int32_t nsteps,
                            int32_t use_graph);
 
+/* One hybrid step with the coupling lists and the results in HOST memory, for a host
+ * application that holds its lists and reads the coupling moments every step. Enqueued on
+ * the context's stream, in order:
+ *   - the n_nodes nodes and n_cells cells (host int32) are copied to device staging owned by
+ *     the context;
+ *   - hyb_hybrid_step(ctx, staging, n_nodes, staging, n_cells, 1, use_graph = 1);
+ *   - the 20 cumulative moment sums of each listed cell (the layout of hyb_layout.acc; zeros
+ *     for an index out of range) are copied to host_acc (n_cells x 20 doubles, list order);
+ *   - the sticky status word (HYB_ST_* bits) is copied to *host_status.
+ * The call returns once the work is enqueued; the host buffers must stay valid and
+ * untouched until hyb_host_wait says the step is done. With page-locked host buffers
+ * (cudaMallocHost, cudaHostRegister) the copies are asynchronous; pageable buffers work but
+ * make the copies synchronous. The first call, and any call with longer lists, allocates
+ * the staging (4 n_nodes + 164 n_cells bytes, rounded up) on the device; hyb_destroy frees
+ * it. host_acc may be NULL when n_cells is 0. Invalid sizes or pointers: HYB_EINVAL. */
+hyb_status hyb_hybrid_step_host(hyb_ctx* ctx, const int32_t* host_nodes, int32_t n_nodes,
+                                const int32_t* host_cells, int32_t n_cells, double* host_acc,
+                                uint32_t* host_status);
+
+/* Waits until at most `pending` (0 to 3) of the steps issued by hyb_hybrid_step_host are
+ * still in flight, so their results have landed in the host buffers: pending = 0 waits for
+ * all of them, pending = 1 lets the newest run on while the host reads the one before. */
+hyb_status hyb_host_wait(hyb_ctx* ctx, int32_t pending);
+
 /* Which ping-pong halves hold the current particle and population state (0 or 1). */
 hyb_status hyb_current(const hyb_ctx* ctx, int32_t* particle_half, int32_t* lb_half);
 

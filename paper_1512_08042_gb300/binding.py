@@ -56,7 +56,7 @@ class HybLayout(ctypes.Structure):
 EXPORTS = ["hyb_derive", "hyb_layout_compute", "hyb_lattice", "hyb_status_string", "dsmc_init",
            "dsmc_step", "lbm_step", "sample_moments", "map_dsmc_to_lbm", "map_lbm_to_dsmc",
            "map_lbm_to_dsmc_noalloc", "lbm_step_nodes", "lbm_interface_loss", "lbm_adjoint_step",
-           "hyb_hybrid_step", "hyb_batch_layout", "hyb_batch_init", "hyb_batch_replica",
+           "hyb_hybrid_step", "hyb_hybrid_step_host", "hyb_host_wait", "hyb_batch_layout", "hyb_batch_init", "hyb_batch_replica",
            "hyb_batch_hybrid_step", "hyb_batch_set_blocks", "hyb_batch_tune",
            "hyb_batch_last_error", "hyb_batch_destroy", "hyb_current", "hyb_sync_status", "hyb_read_counters",
            "hyb_profile", "hyb_profile_harvest", "hyb_profile_read", "hyb_debug_philox",
@@ -104,6 +104,8 @@ def lib():
     L.lbm_interface_loss.argtypes = [_vp, _vp, _vp, _i32, _vp, _vp, _vp]
     L.lbm_adjoint_step.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
     L.hyb_hybrid_step.argtypes = [_vp, _vp, _i32, _vp, _i32, _i32, _i32]
+    L.hyb_hybrid_step_host.argtypes = [_vp, _vp, _i32, _vp, _i32, _vp, _vp]
+    L.hyb_host_wait.argtypes = [_vp, _i32]
     L.hyb_batch_layout.argtypes = [_vp, _i32, _vp]
     L.hyb_batch_init.argtypes = [_vp, _i32, _vp, _u64, _vp, P(_vp)]
     L.hyb_batch_replica.argtypes = [_vp, _i32, P(_vp)]
@@ -319,6 +321,35 @@ class Hybrid:
         nc = cells.numel() if cells is not None else 0
         _check(lib().hyb_hybrid_step(self.ctx, np_, nn, cp_, nc, nsteps, 1 if use_graph else 0),
                self.ctx)
+
+    def hybrid_step_host(self, nodes, cells, out_acc, out_status):
+        """One hybrid step with host lists and host results (hyb_hybrid_step_host): `nodes`,
+        `cells` int32 and `out_acc` float64 [len(cells), 20], `out_status` int32 [>= 1], CPU
+        tensors or arrays (page-locked for asynchronous copies). Returns once enqueued; the
+        results are valid after host_wait()."""
+        def ptr(a):
+            return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+
+        def check(a, dtype, n, what):
+            if hasattr(a, "data_ptr"):
+                ok = (a.device.type == "cpu" and a.is_contiguous() and a.numel() >= n and
+                      str(a.dtype) == "torch." + dtype)
+            else:
+                ok = a.flags["C_CONTIGUOUS"] and a.size >= n and a.dtype == np.dtype(dtype)
+            if not ok:
+                raise ValueError("%s must be a contiguous host %s buffer of >= %d values" % (what, dtype, n))
+        nn, nc = len(nodes), len(cells)
+        check(nodes, "int32", nn, "nodes")
+        check(cells, "int32", nc, "cells")
+        check(out_acc, "float64", 20 * nc, "out_acc")
+        check(out_status, "int32", 1, "out_status")
+        _check(lib().hyb_hybrid_step_host(self.ctx, ptr(nodes) if nn else None, nn,
+                                          ptr(cells) if nc else None, nc,
+                                          ptr(out_acc) if nc else None, ptr(out_status)), self.ctx)
+
+    def host_wait(self, pending=0):
+        """Wait until at most `pending` host steps are in flight (hyb_host_wait)."""
+        _check(lib().hyb_host_wait(self.ctx, int(pending)), self.ctx)
 
     def sample_moments(self, out=None, reset=False):
         self._inputs(out)

@@ -469,6 +469,7 @@ cudaError_t launch_interface_loss(Ctx& c, const void* f, const int32_t* nodes, i
 cudaError_t launch_map_d2l(Ctx& c, const int32_t* nodes, int32_t n);
 cudaError_t launch_map_l2d(Ctx& c, const int32_t* cells, int32_t n);
 cudaError_t launch_map_l2d_noalloc(Ctx& c, const int32_t* cells, int32_t n);
+cudaError_t launch_gather_acc(Ctx& c, const int32_t* cells, int32_t n, double* out);
 cudaError_t launch_debug_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out, int64_t n,
                                 cudaStream_t s);
 
@@ -545,6 +546,12 @@ struct Ctx {
     int g_prof = -2;
     int g_curf[2] = {0, 0};        // population parity each graph variant was captured with
     uint32_t* h_pinned = nullptr;  // pinned host words for status reads
+    // hyb_hybrid_step_host: device staging of the lists and the gathered moment sums, and a
+    // ring of completion events of the steps in flight
+    char* io_dev = nullptr;
+    size_t io_bytes = 0;
+    cudaEvent_t io_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    int64_t io_issued = 0, io_done = 0;
 };
 
 // Bracket a launch with the timing events when kernel `k` is being profiled.

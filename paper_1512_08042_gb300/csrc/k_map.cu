@@ -634,6 +634,25 @@ cudaError_t l2d_noalloc_impl(Ctx& c, const int32_t* cells, int32_t n, GradRec* r
 
 }  // namespace
 
+namespace {
+// The cumulative moment sums of the listed cells, in list order (zeros for an index out of
+// range): one thread per value.
+__global__ void k_gather_acc(const double* __restrict__ acc, const int32_t* __restrict__ cells,
+                             int32_t n, int64_t ncells, double* __restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)n * kMoments) return;
+    const int32_t c = cells[i / kMoments];
+    out[i] = (c >= 0 && (int64_t)c < ncells) ? acc[(int64_t)c * kMoments + i % kMoments] : 0.0;
+}
+}  // namespace
+
+cudaError_t launch_gather_acc(Ctx& c, const int32_t* cells, int32_t n, double* out) {
+    const int64_t total = (int64_t)n * kMoments;
+    k_gather_acc<<<(unsigned)((total + 255) / 256), 256, 0, c.stream>>>(c.st.acc, cells, n,
+                                                                        c.d.ncells, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_map_l2d_noalloc(Ctx& c, const int32_t* cells, int32_t n) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);

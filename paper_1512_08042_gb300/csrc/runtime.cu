@@ -586,11 +586,83 @@ hyb_status hyb_debug_philox(const uint32_t* dev_ctr, uint64_t seed, uint32_t* de
 
 const char* hyb_last_error(const hyb_ctx* h) { return h ? h->c.err.c_str() : "null context"; }
 
+hyb_status hyb_hybrid_step_host(hyb_ctx* h, const int32_t* host_nodes, int32_t n_nodes,
+                                const int32_t* host_cells, int32_t n_cells, double* host_acc,
+                                uint32_t* host_status) {
+    if (!h || n_nodes < 0 || n_cells < 0 || !host_status) return HYB_EINVAL;
+    Ctx& c = h->c;
+    if ((n_nodes > 0 && !host_nodes) || (n_cells > 0 && (!host_cells || !host_acc)) ||
+        n_nodes > c.d.nnodes || n_cells > c.d.ncells)
+        return HYB_EINVAL;
+    if (c.stream == nullptr) return fail(c, HYB_ESTATE, "host steps need a non-default stream");
+    // staging: nodes, cells, gathered sums, each 256-byte aligned
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t off_c = up(4 * (size_t)n_nodes), off_a = off_c + up(4 * (size_t)n_cells);
+    const size_t need = off_a + up(8 * (size_t)kMoments * n_cells) + 256;
+    if (need > c.io_bytes) {
+        hyb_status s = check(c, cudaStreamSynchronize(c.stream), "synchronize");
+        if (s != HYB_OK) return s;
+        if (c.io_dev) cudaFree(c.io_dev);
+        c.io_dev = nullptr;
+        c.io_bytes = 0;
+        s = check(c, cudaMalloc((void**)&c.io_dev, need), "host-step staging");
+        if (s != HYB_OK) return s;
+        c.io_bytes = need;
+    }
+    for (int i = 0; i < 4; ++i)
+        if (!c.io_ev[i]) {
+            hyb_status s = check(c, cudaEventCreateWithFlags(&c.io_ev[i], cudaEventDisableTiming),
+                                 "event create");
+            if (s != HYB_OK) return s;
+        }
+    // a free slot in the ring of completion events
+    if (c.io_issued - c.io_done >= 4) {
+        hyb_status s = hyb_host_wait(h, 3);
+        if (s != HYB_OK) return s;
+    }
+    int32_t* dn = (int32_t*)c.io_dev;
+    int32_t* dc = (int32_t*)(c.io_dev + off_c);
+    double* da = (double*)(c.io_dev + off_a);
+    hyb_status s = HYB_OK;
+    if (n_nodes > 0)
+        s = check(c, cudaMemcpyAsync(dn, host_nodes, 4 * (size_t)n_nodes, cudaMemcpyHostToDevice, c.stream),
+                  "copy nodes in");
+    if (s == HYB_OK && n_cells > 0)
+        s = check(c, cudaMemcpyAsync(dc, host_cells, 4 * (size_t)n_cells, cudaMemcpyHostToDevice, c.stream),
+                  "copy cells in");
+    if (s == HYB_OK) s = hyb_hybrid_step(h, dn, n_nodes, dc, n_cells, 1, 1);
+    if (s == HYB_OK && n_cells > 0) s = check(c, launch_gather_acc(c, dc, n_cells, da), "gather launch");
+    if (s == HYB_OK && n_cells > 0)
+        s = check(c, cudaMemcpyAsync(host_acc, da, 8 * (size_t)kMoments * n_cells, cudaMemcpyDeviceToHost,
+                                     c.stream),
+                  "copy moments out");
+    if (s == HYB_OK)
+        s = check(c, cudaMemcpyAsync(host_status, c.st.ctrl + CTRL_STATUS, 4, cudaMemcpyDeviceToHost, c.stream),
+                  "copy status out");
+    if (s == HYB_OK) s = check(c, cudaEventRecord(c.io_ev[c.io_issued % 4], c.stream), "event record");
+    if (s == HYB_OK) c.io_issued += 1;
+    return s;
+}
+
+hyb_status hyb_host_wait(hyb_ctx* h, int32_t pending) {
+    if (!h || pending < 0 || pending > 3) return HYB_EINVAL;
+    Ctx& c = h->c;
+    while (c.io_issued - c.io_done > pending) {
+        hyb_status s = check(c, cudaEventSynchronize(c.io_ev[c.io_done % 4]), "wait for a host step");
+        if (s != HYB_OK) return s;
+        c.io_done += 1;
+    }
+    return HYB_OK;
+}
+
 void hyb_destroy(hyb_ctx* h) {
     if (!h) return;
     Ctx& c = h->c;
     cudaStreamSynchronize(c.stream);
     drop_graphs(c);
+    if (c.io_dev) cudaFree(c.io_dev);
+    for (int i = 0; i < 4; ++i)
+        if (c.io_ev[i]) cudaEventDestroy(c.io_ev[i]);
     if (c.h_pinned) {
         ProfPool& P = pool_of(c);
         for (size_t i = 0; i < P.a.size(); ++i) {

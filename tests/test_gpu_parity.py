@@ -444,3 +444,40 @@ def test_hybrid_steps_with_kn_profile_fp64_match_oracle():
     _compare_dsmc(h, o, 8)
     h.sync()
     assert np.allclose(h.f().cpu().numpy(), o.f(), rtol=1e-11, atol=1e-14)
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_buffer_steps_equal_device_list_steps(pinned):
+    # hyb_hybrid_step_host: host lists in, the listed cells' moment sums and the status out;
+    # the state equals that of the same steps with device lists, and the returned sums are
+    # the arena's rows of the listed cells (zeros for an index out of range)
+    cfg = cfg_small(lb_ratio=2, ma=0.3)
+    nodes, cells = W.coupling_sites(cfg, strip_cells=2)
+    cells_h = np.concatenate([cells, [10 ** 6]]).astype(np.int32)  # one index out of range
+    a, b = B.Hybrid(cfg), B.Hybrid(cfg)
+    dn, dc = torch.from_numpy(nodes).cuda(), torch.from_numpy(cells_h).cuda()
+    mk = (lambda x: torch.from_numpy(x).pin_memory()) if pinned else torch.from_numpy
+    hn, hc = mk(nodes), mk(cells_h)
+    outs = [mk(np.zeros((len(cells_h), 20))), mk(np.zeros((len(cells_h), 20)))]
+    st = [mk(np.zeros(1, np.int32)), mk(np.zeros(1, np.int32))]
+    for k in range(5):
+        a.hybrid_step(dn, dc, nsteps=1, use_graph=True)
+        b.hybrid_step_host(hn, hc, outs[k % 2], st[k % 2])
+        if k > 0:
+            b.host_wait(1)
+    b.host_wait(0)
+    a.sync()
+    last = outs[4 % 2].numpy()
+    acc = b.acc().cpu().numpy()
+    assert np.array_equal(last[:-1], acc[cells]) and np.all(last[-1] == 0)
+    assert np.array_equal(a.acc().cpu().numpy(), acc)
+    for k in ("x", "y", "vx", "vy", "vz"):
+        assert np.array_equal(gpu_particles(a)[k], gpu_particles(b)[k]), k
+    assert np.array_equal(a.f().cpu().numpy(), b.f().cpu().numpy())
+    bits = b.ctrl().cpu().numpy()[B.CTRL_STATUS]
+    assert int(st[0].numpy()[0]) == int(st[1].numpy()[0]) == bits
+    assert bits & B.ST_BAD_INPUT  # the out-of-range cell was flagged by LB2DSMC
+    with pytest.raises(ValueError):
+        b.hybrid_step_host(hn, hc, outs[0][:1], st[0])  # result buffer too small
+    with pytest.raises(B.HybError):
+        b.host_wait(4)
