@@ -110,6 +110,9 @@ struct DsmcArgs {
     unsigned long long* counters;
     int32_t ncx, ncy, ncells, bin, sample_every, ppc;
     double dt, g_step, coll_dt, crmax_init;
+    // dt, g_step and coll_dt rounded to the state precision on the host (the kernels take
+    // no FP64 conversion per cell)
+    Real dt_r, g_r, coll_r;
     const Real* coll_cell;  // per-cell NTC factor, or null for coll_dt everywhere
     uint64_t seed;
     // 3D (ncz >= 2): z positions of the source and destination sets; ncz is 0 in 2D

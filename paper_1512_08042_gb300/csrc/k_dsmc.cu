@@ -198,6 +198,20 @@ __device__ __forceinline__ void wall_flight(uint64_t seed, uint32_t c, uint32_t 
     }
 }
 
+// Exact widening of a float to double on the integer pipe (the FP64 pipe is slow on this
+// part): a normal float's sign, exponent rebiased from 127 to 1023 and mantissa shifted to
+// the top of the 52-bit field (IEEE 754 binary32 and binary64 formats). Zeros, subnormals,
+// infinities and NaNs take the plain conversion.
+__device__ __forceinline__ double widen(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xFFu;
+    if (e == 0u || e == 0xFFu) return (double)f;
+    const uint64_t bits = ((uint64_t)(u >> 31) << 63) | ((uint64_t)(e + 896u) << 52) |
+                          ((uint64_t)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+__device__ __forceinline__ double widen(double d) { return d; }
+
 // Periodic wrap of v into [0, period).
 template <typename Real>
 __device__ __forceinline__ Real wrap_periodic(Real v, Real period) {
@@ -253,7 +267,7 @@ __device__ __forceinline__ void move_cell(const DsmcArgs<Real>& a, int c, unsign
     const uint32_t s = a.ctrl[CTRL_STEP];
     if (c == 0 && lane == 0) a.ctrl[CTRL_NTOT] = 0;  // the collide recounts
     const Real H = (Real)a.ncx, L = (Real)a.ncy;
-    const Real g = (Real)a.g_step, dt = (Real)a.dt;
+    const Real g = a.g_r, dt = a.dt_r;
     const uint32_t bin = (uint32_t)a.bin;
     // the arrays do not overlap: loads of the next slots need not wait for earlier stores
     const Real* __restrict__ sx = a.sx;
@@ -518,7 +532,7 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
     Real* c_nz = c_ny + NC * KC;
     const uint32_t s = a.ctrl[CTRL_STEP];
     const bool do_sample = (s % (uint32_t)a.sample_every) == 0u;
-    const Real coll_dt = (Real)a.coll_dt;
+    const Real coll_dt = a.coll_r;
     unsigned long long ncand_tot = 0, ncoll_tot = 0;
     uint32_t flags = 0, nlive = 0;
 
@@ -870,7 +884,7 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
                     const int mq = 3 * gl + q;
-                    if (mq < kMoments) atomicAdd(&a.acc[(size_t)c * kMoments + mq], (double)t[q]);
+                    if (mq < kMoments) atomicAdd(&a.acc[(size_t)c * kMoments + mq], widen(t[q]));
                 }
             }
         }
@@ -960,6 +974,9 @@ DsmcArgs<Real> make_args(Ctx& c) {
     a.dt = c.d.dt;
     a.g_step = c.d.g_step;
     a.coll_dt = c.d.coll_dt;
+    a.dt_r = (Real)c.d.dt;
+    a.g_r = (Real)c.d.g_step;
+    a.coll_r = (Real)c.d.coll_dt;
     a.coll_cell = (const Real*)c.st.coll_cell;
     a.sz = (const Real*)c.st.pz[h];
     a.dz = (Real*)c.st.pz[o];
