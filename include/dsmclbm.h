@@ -281,6 +281,19 @@ hyb_status hyb_hybrid_step(hyb_ctx* ctx, const int32_t* dev_nodes, int32_t n_nod
                            const int32_t* dev_cells, int32_t n_cells, int32_t nsteps,
                            int32_t use_graph);
 
+/* Adjoint of map_dsmc_to_lbm (Sec. 2.1, Eq. coefficients and Eq. discretefunctions, raw
+ * coefficients; an extension beyond the paper, for the differentiated coupling). lam is
+ * dL/df for the context's population layout ([q][nz][ny][nx], state precision, device),
+ * taken right after map_dsmc_to_lbm wrote the n listed nodes (distinct, device int32).
+ * Adds dL/d(acc) of the cells holding those nodes to grad_acc (device f64[ncells][20], the
+ * layout of hyb_layout.acc) and sets lam at the listed nodes to zero, since the mapping
+ * overwrote those populations. For a fixed sample count S (ctrl[3], which the forward call
+ * used) the coefficients are linear in the sums, so acc itself is not read. A node index out
+ * of range, or S = 0, is skipped and raises HYB_ST_BAD_INPUT. A context with d2l_mode = 1
+ * (the equilibrium mapping) returns HYB_EINVAL. Enqueued on the context's stream. */
+hyb_status map_dsmc_to_lbm_adjoint(hyb_ctx* ctx, const int32_t* dev_nodes, int32_t n, void* lam,
+                                   double* grad_acc);
+
 /* One hybrid step with the coupling lists and the results in HOST memory, for a host
  * application that holds its lists and reads the coupling moments every step. Enqueued on
  * the context's stream, in order:

@@ -348,6 +348,37 @@ def interface_loss_after(cfg, f0, g, tau, nodes, targets, nsteps):
     return o.interface_loss(nodes, targets)
 
 
+def coupled_loss_after(cfg, acc, nsamples, d2l_nodes, f0, g, tau, nodes, targets, nsteps):
+    """The interface loss after DSMC2LB of the sums `acc` (S = nsamples) into f0 at
+    d2l_nodes, then nsteps LBM steps with per-node g and tau."""
+    o = Oracle(cfg)
+    o.set_f(f0)
+    o.set(A_ACC, np.asarray(acc, np.float64).reshape(-1))
+    o.set_scalars(0, nsamples)
+    o.map_dsmc_to_lbm(np.ascontiguousarray(d2l_nodes, np.int32))
+    o.set_node_params(g, tau)
+    o.lbm_step(nsteps)
+    return o.interface_loss(nodes, targets)
+
+
+def coupled_loss_fd_gradient(cfg, acc, nsamples, d2l_nodes, f0, g, tau, nodes, targets, nsteps,
+                             entries, h=1e-6):
+    """Central finite differences of coupled_loss_after with respect to the sums
+    acc[cell, k] for each (cell, k) in `entries`: the oracle's reference gradient."""
+    acc = np.array(acc, np.float64).reshape(-1, 20)
+    out = np.zeros(len(entries))
+    for i, (c, k) in enumerate(entries):
+        step = h * max(1.0, abs(acc[c, k]))
+        save = acc[c, k]
+        acc[c, k] = save + step
+        lp = coupled_loss_after(cfg, acc, nsamples, d2l_nodes, f0, g, tau, nodes, targets, nsteps)
+        acc[c, k] = save - step
+        lm = coupled_loss_after(cfg, acc, nsamples, d2l_nodes, f0, g, tau, nodes, targets, nsteps)
+        acc[c, k] = save
+        out[i] = (lp - lm) / (2.0 * step)
+    return out
+
+
 def interface_loss_fd_gradient(cfg, f0, g, tau, nodes, targets, nsteps, h=1e-6, which=None):
     """Central finite differences of the interface loss with respect to g and tau at the
     nodes `which` (all nodes when None): the oracle's reference gradient."""

@@ -55,7 +55,7 @@ class HybLayout(ctypes.Structure):
 
 EXPORTS = ["hyb_derive", "hyb_layout_compute", "hyb_lattice", "hyb_status_string", "dsmc_init",
            "dsmc_step", "lbm_step", "sample_moments", "map_dsmc_to_lbm", "map_lbm_to_dsmc",
-           "map_lbm_to_dsmc_noalloc", "lbm_step_nodes", "lbm_interface_loss", "lbm_adjoint_step",
+           "map_lbm_to_dsmc_noalloc", "map_dsmc_to_lbm_adjoint", "lbm_step_nodes", "lbm_interface_loss", "lbm_adjoint_step",
            "hyb_hybrid_step", "hyb_hybrid_step_host", "hyb_host_wait", "hyb_batch_layout", "hyb_batch_init", "hyb_batch_replica",
            "hyb_batch_hybrid_step", "hyb_batch_set_blocks", "hyb_batch_tune",
            "hyb_batch_last_error", "hyb_batch_destroy", "hyb_current", "hyb_sync_status", "hyb_read_counters",
@@ -100,6 +100,7 @@ def lib():
     L.map_dsmc_to_lbm.argtypes = [_vp, _vp, _i32]
     L.map_lbm_to_dsmc.argtypes = [_vp, _vp, _i32]
     L.map_lbm_to_dsmc_noalloc.argtypes = [_vp, _vp, _i32]
+    L.map_dsmc_to_lbm_adjoint.argtypes = [_vp, _vp, _i32, _vp, _vp]
     L.lbm_step_nodes.argtypes = [_vp, _vp, _vp, _vp, _vp]
     L.lbm_interface_loss.argtypes = [_vp, _vp, _vp, _i32, _vp, _vp, _vp]
     L.lbm_adjoint_step.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
@@ -297,6 +298,18 @@ class Hybrid:
         _check(lib().lbm_interface_loss(self.ctx, f.data_ptr(), nodes.data_ptr(), nodes.numel(),
                                         targets.data_ptr(), loss.data_ptr(), lam.data_ptr()),
                self.ctx)
+
+    def map_dsmc_to_lbm_adjoint(self, nodes, lam, grad_acc):
+        """Adds dL/d(acc) to grad_acc (float64 [ncells, 20]) from lam = dL/df after
+        map_dsmc_to_lbm at `nodes` (distinct int32), and zeroes lam at those nodes."""
+        self._check_pop(lam)
+        torch = self.torch
+        if nodes.dtype != torch.int32 or grad_acc.dtype != torch.float64 or \
+                grad_acc.numel() != 20 * int(self.L.ncells) or not grad_acc.is_contiguous():
+            raise ValueError("int32 nodes and a contiguous float64 [ncells, 20] gradient")
+        self._inputs(nodes, lam, grad_acc)
+        _check(lib().map_dsmc_to_lbm_adjoint(self.ctx, nodes.data_ptr(), nodes.numel(),
+                                             lam.data_ptr(), grad_acc.data_ptr()), self.ctx)
 
     def lbm_adjoint_step(self, f, lam_next, lam, g, tau, grad_g, grad_tau, wall):
         """lam = dL/df_t from f_t and lam_next = dL/df_{t+1}; adds this step's dL/dg and
@@ -603,6 +616,64 @@ def interface_loss(h, g, tau, f0, nodes, targets, nsteps, ckpt_every=100):
     return _InterfaceLoss.apply(g, tau, f0, h, nodes, targets, int(nsteps), int(ckpt_every))
 
 
+def coupled_interface_loss(h, acc, nsamples, d2l_nodes, g, tau, f0, nodes, targets, nsteps,
+                           ckpt_every=100):
+    """The interface loss of the differentiated coupling: DSMC2LB maps the cumulative sums
+    `acc` (float64 [ncells, 20], `nsamples` samples) into the populations f0 at `d2l_nodes`
+    (distinct int32), then `nsteps` LB steps run with per-node g and tau, and the loss is
+    taken at `nodes` against `targets` (as interface_loss). Differentiable with respect to
+    acc, g, tau and f0. The context's own sums, sample count and current populations serve
+    as scratch for the mapping."""
+    return _CoupledLoss.apply(acc, g, tau, f0, h, int(nsamples), d2l_nodes, nodes, targets,
+                              int(nsteps), int(ckpt_every))
+
+
+def _d2l_into(h, acc, nsamples, d2l_nodes, f0):
+    """f0 with DSMC2LB of `acc` written at `d2l_nodes` (a new tensor), through the context."""
+    h._inputs(acc, f0)
+    with h.torch.cuda.stream(h.stream):
+        h.acc().copy_(acc)
+        h.f().copy_(f0)
+    h.set_counters(nsamples=nsamples)
+    h.map_dsmc_to_lbm(d2l_nodes)
+    with h.torch.cuda.stream(h.stream):
+        return h.f().clone()
+
+
+def _make_coupled_loss():
+    import torch
+
+    class CoupledLoss(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, acc, g, tau, f0, h, nsamples, d2l_nodes, nodes, targets, nsteps,
+                    ckpt_every):
+            g, tau = g.detach().contiguous(), tau.detach().contiguous()
+            fm = _d2l_into(h, acc.detach().contiguous(), nsamples, d2l_nodes, f0.detach())
+            loss, lam_T, ckpts = _loss_forward(h, g, tau, fm, nodes, targets, nsteps, ckpt_every)
+            ctx.h, ctx.nsamples = h, nsamples
+            ctx.nsteps, ctx.ckpt_every = nsteps, ckpt_every
+            ctx.save_for_backward(g, tau, lam_T, d2l_nodes, *ckpts)
+            return loss[0]
+
+        @staticmethod
+        def backward(ctx, gout):
+            h = ctx.h
+            g, tau, lam_T, d2l_nodes, *ckpts = ctx.saved_tensors
+            h.stream.wait_stream(torch.cuda.current_stream(g.device))
+            grad_g, grad_tau, lam = _loss_adjoint(h, g, tau, lam_T, ckpts, ctx.nsteps,
+                                                  ctx.ckpt_every)
+            grad_acc = torch.zeros(int(h.L.ncells), 20, dtype=torch.float64, device=g.device)
+            h.set_counters(nsamples=ctx.nsamples)
+            h.map_dsmc_to_lbm_adjoint(d2l_nodes, lam, grad_acc)  # zeroes lam at d2l_nodes
+            with torch.cuda.stream(h.stream):
+                s = gout.to(g.dtype)
+                out = (grad_acc * gout.to(torch.float64), grad_g * s, grad_tau * s, lam * s)
+            torch.cuda.current_stream(g.device).wait_stream(h.stream)
+            return out + (None,) * 7
+
+    return CoupledLoss
+
+
 def _lb_forward(h, g, tau, f0, nsteps, ckpt_every):
     """f_T and the checkpoints f_0, f_K, f_2K, ... (K = ckpt_every)."""
     a = f0.detach().clone()
@@ -616,6 +687,41 @@ def _lb_forward(h, g, tau, f0, nsteps, ckpt_every):
     return a, ckpts
 
 
+def _loss_forward(h, g, tau, f0, nodes, targets, nsteps, ckpt_every):
+    """Loss after nsteps LB steps from f0, dL/df_T, and the checkpoints of the states."""
+    torch = h.torch
+    with torch.cuda.stream(h.stream):
+        fT, ckpts = _lb_forward(h, g, tau, f0, nsteps, ckpt_every)
+        loss = torch.zeros(1, dtype=torch.float64, device=f0.device)
+        lam = torch.zeros_like(fT)
+        h.lbm_interface_loss(fT, nodes, targets, loss, lam)
+    torch.cuda.current_stream(f0.device).wait_stream(h.stream)
+    return loss, lam, ckpts
+
+
+def _loss_adjoint(h, g, tau, lam_T, ckpts, T, K):
+    """The adjoint sweep: (dL/dg, dL/dtau, dL/df_0) from dL/df_T, recomputing the states of
+    each checkpoint segment forward and running the adjoint steps over them in reverse."""
+    torch = h.torch
+    with torch.cuda.stream(h.stream):
+        grad_g = torch.zeros_like(g)
+        grad_tau = torch.zeros_like(tau)
+        wall = torch.zeros(2 * int(h.d["ny"]) + 1, dtype=g.dtype, device=g.device)
+        lam_next = lam_T.clone()
+        lam = torch.empty_like(lam_next)
+        for s in reversed(range(len(ckpts))):
+            t0, t1 = s * K, min(T, (s + 1) * K)
+            states = [ckpts[s]]
+            for _ in range(t0, t1 - 1):
+                nxt = torch.empty_like(states[-1])
+                h.lbm_step_nodes(states[-1], nxt, g, tau)
+                states.append(nxt)
+            for t in reversed(range(t0, t1)):
+                h.lbm_adjoint_step(states[t - t0], lam_next, lam, g, tau, grad_g, grad_tau, wall)
+                lam_next, lam = lam, lam_next
+    return grad_g, grad_tau, lam_next
+
+
 def _make_interface_loss():
     import torch
 
@@ -623,12 +729,7 @@ def _make_interface_loss():
         @staticmethod
         def forward(ctx, g, tau, f0, h, nodes, targets, nsteps, ckpt_every):
             g, tau = g.detach().contiguous(), tau.detach().contiguous()
-            with torch.cuda.stream(h.stream):
-                fT, ckpts = _lb_forward(h, g, tau, f0, nsteps, ckpt_every)
-                loss = torch.zeros(1, dtype=torch.float64, device=f0.device)
-                lam = torch.zeros_like(fT)
-                h.lbm_interface_loss(fT, nodes, targets, loss, lam)
-            torch.cuda.current_stream(f0.device).wait_stream(h.stream)
+            loss, lam, ckpts = _loss_forward(h, g, tau, f0, nodes, targets, nsteps, ckpt_every)
             ctx.h = h
             ctx.nsteps, ctx.ckpt_every = nsteps, ckpt_every
             ctx.save_for_backward(g, tau, lam, *ckpts)
@@ -638,28 +739,12 @@ def _make_interface_loss():
         def backward(ctx, gout):
             h = ctx.h
             g, tau, lam_T, *ckpts = ctx.saved_tensors
-            K, T = ctx.ckpt_every, ctx.nsteps
             h.stream.wait_stream(torch.cuda.current_stream(g.device))
+            grad_g, grad_tau, lam = _loss_adjoint(h, g, tau, lam_T, ckpts, ctx.nsteps,
+                                                  ctx.ckpt_every)
             with torch.cuda.stream(h.stream):
-                grad_g = torch.zeros_like(g)
-                grad_tau = torch.zeros_like(tau)
-                wall = torch.zeros(2 * int(h.d["ny"]) + 1, dtype=g.dtype, device=g.device)
-                lam_next = lam_T.clone()
-                lam = torch.empty_like(lam_next)
-                for s in reversed(range(len(ckpts))):
-                    t0, t1 = s * K, min(T, (s + 1) * K)
-                    states = [ckpts[s]]
-                    for _ in range(t0, t1 - 1):
-                        nxt = torch.empty_like(states[-1])
-                        h.lbm_step_nodes(states[-1], nxt, g, tau)
-                        states.append(nxt)
-                    for t in reversed(range(t0, t1)):
-                        h.lbm_adjoint_step(states[t - t0], lam_next, lam, g, tau, grad_g,
-                                           grad_tau, wall)
-                        lam_next, lam = lam, lam_next
-                gg = grad_g * gout.to(g.dtype)
-                gt = grad_tau * gout.to(g.dtype)
-                gf = lam_next * gout.to(g.dtype)
+                s = gout.to(g.dtype)
+                gg, gt, gf = grad_g * s, grad_tau * s, lam * s
             torch.cuda.current_stream(g.device).wait_stream(h.stream)
             return gg, gt, gf, None, None, None, None, None
 
@@ -677,3 +762,4 @@ class _Lazy:
 
 
 _InterfaceLoss = _Lazy(_make_interface_loss)
+_CoupledLoss = _Lazy(_make_coupled_loss)

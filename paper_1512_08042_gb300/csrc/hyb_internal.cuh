@@ -473,6 +473,8 @@ cudaError_t launch_map_d2l(Ctx& c, const int32_t* nodes, int32_t n);
 cudaError_t launch_map_l2d(Ctx& c, const int32_t* cells, int32_t n);
 cudaError_t launch_map_l2d_noalloc(Ctx& c, const int32_t* cells, int32_t n);
 cudaError_t launch_gather_acc(Ctx& c, const int32_t* cells, int32_t n, double* out);
+cudaError_t launch_map_d2l_adjoint(Ctx& c, const int32_t* nodes, int32_t n, void* lam,
+                                   double* grad_acc);
 cudaError_t launch_debug_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out, int64_t n,
                                 cudaStream_t s);
 

@@ -254,6 +254,92 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int k) {
     return pos;
 }
 
+// Adjoint of DSMC2LB (the raw-coefficient mapping) at the listed nodes, one warp per node.
+// With S and ppc fixed, every coefficient of the forward mapping is linear in the cell's
+// cumulative sums M: c_0 = M_0 / (S ppc), and c_k = (M_k - s_k M_j) / (S ppc) where the
+// forward subtracts s_k times the mean of component j (s_k M_0 for the diagonal second
+// moments). The populations are f_q = w_q sum_k c_k B_k(xi_q) with the Hermite basis B of
+// the forward series, so dL/dM = T^T (sum_q lam_q w_q B(xi_q)) / (S ppc). Lane l projects
+// populations l and l + 32; the 20 projections are summed over the lanes by halving_sum.
+// The forward overwrote the node's populations, so lam there is set to zero.
+template <typename Real, class LAT>
+__device__ __forceinline__ void d2l_adjoint_entries(const MapArgs<Real>& a, Real* lam,
+                                                    double* grad_acc, int first, int stride) {
+    const LatXi<LAT, Real>& lt = lat_xi<LAT, Real>();
+    const unsigned lane = lane_id();
+    const uint32_t S = a.ctrl[CTRL_NSAMPLES];
+    for (int t = first; t < a.n; t += stride) {
+        const int32_t node = a.list[t];
+        if (node < 0 || (int64_t)node >= a.nnodes || S == 0) {
+            if (lane == 0) atomicOr(&a.ctrl[CTRL_STATUS], HYB_ST_BAD_INPUT);
+            continue;
+        }
+        const int x = node % a.nx, y = (node / a.nx) % a.ny, z = node / (a.nx * a.ny);
+        const int64_t cell =
+            ((int64_t)(z / a.lb_ratio) * a.ncy + y / a.lb_ratio) * a.ncx + (x / a.lb_ratio);
+        Real v[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k] = (Real)0;
+#pragma unroll
+        for (int h = 0; h < (LAT::Q + 31) / 32; ++h) {
+            const int q = (int)lane + 32 * h;
+            if (q < LAT::Q) {
+                const int64_t at = (int64_t)q * a.nnodes + node;
+                const Real lw = lam[at] * lt.w[q];
+                lam[at] = (Real)0;
+                const Real X = lt.x[3 * q], Y = lt.x[3 * q + 1], Z = lt.x[3 * q + 2];
+                const Real hf = (Real)0.5;
+                v[0] += lw;
+                v[1] += lw * X;
+                v[2] += lw * Y;
+                v[3] += lw * Z;
+                v[4] += lw * hf * (X * X - (Real)1);
+                v[5] += lw * X * Y;
+                v[6] += lw * X * Z;
+                v[7] += lw * hf * (Y * Y - (Real)1);
+                v[8] += lw * Y * Z;
+                v[9] += lw * hf * (Z * Z - (Real)1);
+                if (LAT::ORDER >= 3) {
+                    const Real s6 = (Real)(1.0 / 6.0);
+                    v[10] += lw * s6 * (X * X * X - (Real)3 * X);
+                    v[11] += lw * hf * (X * X * Y - Y);
+                    v[12] += lw * hf * (X * X * Z - Z);
+                    v[13] += lw * hf * (X * Y * Y - X);
+                    v[14] += lw * X * Y * Z;
+                    v[15] += lw * hf * (X * Z * Z - X);
+                    v[16] += lw * s6 * (Y * Y * Y - (Real)3 * Y);
+                    v[17] += lw * hf * (Y * Y * Z - Z);
+                    v[18] += lw * hf * (Y * Z * Z - Y);
+                    v[19] += lw * s6 * (Z * Z * Z - (Real)3 * Z);
+                }
+            }
+        }
+        halving_sum<Real, 32>(v, lane);  // lane k holds projection k
+        const double gk = (double)v[0];
+        auto g = [&](int k) { return __shfl_sync(kFull, gk, k); };
+        double d = gk;
+        const double c0 = g(4) + g(7) + g(9);
+        const double c1 = 3.0 * g(10) + g(13) + g(15);
+        const double c2 = g(11) + 3.0 * g(16) + g(18);
+        const double c3 = g(12) + g(17) + 3.0 * g(19);
+        if (lane == 0) d -= c0;
+        if (lane == 1) d -= c1;
+        if (lane == 2) d -= c2;
+        if (lane == 3) d -= c3;
+        if (lane < (unsigned)kMoments) {
+            double inv = 1.0 / ((double)S * (double)a.ppc);
+            atomicAdd(&grad_acc[cell * kMoments + lane], d * inv);
+        }
+    }
+}
+
+template <typename Real, class LAT>
+__global__ void __launch_bounds__(128) k_d2l_adj(MapArgs<Real> a, Real* lam, double* grad_acc) {
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    d2l_adjoint_entries<Real, LAT>(a, lam, grad_acc, (int)gw,
+                                   (int)(((int64_t)gridDim.x * blockDim.x) >> 5));
+}
+
 // Table 1 step 1 for the cell `cell`, by one warp, in the state precision. Lane l holds the
 // cell-mean populations q = l and l + 32 (zero past Q); each population sum adds the lane's
 // two terms and then reduces over the lanes (halving_sum), which is the oracle's pairwise
@@ -724,6 +810,25 @@ cudaError_t launch_batch_l2d(BatchDev& b, int cur_p, int cur_f) {
                                  : batch_l2d_impl<double, D3Q39>(b, cur_p, cur_f);
     return b.real_bytes == 4 ? batch_l2d_impl<float, D3Q19>(b, cur_p, cur_f)
                              : batch_l2d_impl<double, D3Q19>(b, cur_p, cur_f);
+}
+
+namespace {
+template <typename Real, class LAT>
+cudaError_t d2l_adj_impl(Ctx& c, const int32_t* nodes, int32_t n, void* lam, double* grad_acc) {
+    const MapArgs<Real> a = map_args<Real>(c, nodes, n);
+    k_d2l_adj<Real, LAT><<<blocks_for(c, (int64_t)n * 32, 128, 16), 128, 0, c.stream>>>(
+        a, (Real*)lam, grad_acc);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_map_d2l_adjoint(Ctx& c, const int32_t* nodes, int32_t n, void* lam,
+                                   double* grad_acc) {
+    if (c.p.lattice == 39)
+        return c.p.real_bytes == 4 ? d2l_adj_impl<float, D3Q39>(c, nodes, n, lam, grad_acc)
+                                   : d2l_adj_impl<double, D3Q39>(c, nodes, n, lam, grad_acc);
+    return c.p.real_bytes == 4 ? d2l_adj_impl<float, D3Q19>(c, nodes, n, lam, grad_acc)
+                               : d2l_adj_impl<double, D3Q19>(c, nodes, n, lam, grad_acc);
 }
 
 cudaError_t launch_map_d2l(Ctx& c, const int32_t* nodes, int32_t n) {

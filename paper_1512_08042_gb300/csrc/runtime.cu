@@ -417,6 +417,16 @@ hyb_status lbm_adjoint_step(hyb_ctx* h, const void* f, const void* lam_next, voi
                  "lbm_adjoint_step launch");
 }
 
+hyb_status map_dsmc_to_lbm_adjoint(hyb_ctx* h, const int32_t* dev_nodes, int32_t n, void* lam,
+                                   double* grad_acc) {
+    if (!h || n < 0 || (n > 0 && (!dev_nodes || !lam || !grad_acc)) || n > h->c.d.nnodes ||
+        h->c.p.d2l_mode != 0)
+        return HYB_EINVAL;
+    if (n == 0) return HYB_OK;
+    return check(h->c, launch_map_d2l_adjoint(h->c, dev_nodes, n, lam, grad_acc),
+                 "map_dsmc_to_lbm_adjoint launch");
+}
+
 hyb_status map_lbm_to_dsmc_noalloc(hyb_ctx* h, const int32_t* dev_cells, int32_t n) {
     if (!h || n < 0 || (n > 0 && !dev_cells) || n > h->c.d.ncells) return HYB_EINVAL;
     Ctx& c = h->c;

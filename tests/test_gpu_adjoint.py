@@ -213,3 +213,83 @@ def test_adjoint_at_the_differentiated_lbm_size_256x128_2000_steps():
     got32 = float((torch.from_numpy(dg).cuda().double() * dirv).sum())
     assert got64 == pytest.approx(fd, rel=1e-5)
     assert got32 == pytest.approx(fd, rel=2e-2)
+
+
+# ---------------------------------------------------------------------------------------
+# The differentiated coupling: DSMC2LB of the cumulative sums, LB steps, interface loss
+
+def coupled_inputs(cfg, seed=4):
+    """Sums from a few oracle DSMC steps of the same channel, the mapped nodes (the cells of
+    column ix = 1, every row), and loss nodes two columns further on."""
+    src = O.Oracle(dict(cfg, ma=0.4))
+    src.dsmc_step(5)
+    acc, S = src.acc().copy(), src.scalars()["nsamples"]
+    nx, ny = cfg["ncx"] * cfg["lb_ratio"], cfg["ncy"] * cfg["lb_ratio"]
+    d2l = np.array([y * nx + x for y in range(ny) for x in (2, 3)], np.int32)
+    nodes = np.array([y * nx + x for y in range(ny) for x in (5, 6)], np.int32)
+    rng = np.random.default_rng(seed)
+    targets = np.zeros((len(nodes), 20))
+    targets[:, 0] = 1.0
+    targets[:, 2] = 0.05
+    targets[:, 4:] = 0.01 * rng.standard_normal((len(nodes), 16))
+    return acc, S, d2l, nodes, targets
+
+
+@pytest.mark.parametrize("lattice", [39, 19])
+def test_coupled_gradient_matches_oracle_central_differences(lattice):
+    cfg = cfg_lb(lattice=lattice, real_bytes=8)
+    h, f, g, tau, f0, gn, tn = setup(cfg, seed=2)
+    acc, S, d2l, nodes, targets = coupled_inputs(cfg)
+    T = 3
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    acc_t = dev(acc).requires_grad_(True)
+    f_t = f.clone().requires_grad_(True)
+    g_t = g.clone().requires_grad_(True)
+    loss = B.coupled_interface_loss(h, acc_t, S, dev(d2l), g_t, tau, f_t, dev(nodes),
+                                    dev(targets), T, ckpt_every=2)
+    loss.backward()
+    want_loss = O.coupled_loss_after(cfg, acc, S, d2l, f0, gn, tn, nodes, targets, T)
+    assert float(loss.detach()) == pytest.approx(want_loss, rel=1e-10)
+    grad = acc_t.grad.cpu().numpy()
+    # sums of the mapped cells (column ix = 1) and of an unmapped cell (ix = 4)
+    ks = [0, 1, 2, 3, 4, 5, 7, 9, 10, 13, 14, 16, 19]
+    entries = [(iy * 6 + 1, k) for iy in (0, 2, 3) for k in ks] + [(2 * 6 + 4, 0), (2 * 6 + 4, 4)]
+    want = O.coupled_loss_fd_gradient(cfg, acc, S, d2l, f0, gn, tn, nodes, targets, T, entries)
+    got = np.array([grad[c, k] for c, k in entries])
+    scale = np.abs(want).max()
+    assert scale > 0
+    assert np.abs(got - want).max() < 1e-6 * scale, np.abs(got - want).max() / scale
+    assert np.all(grad[[iy * 6 + ix for iy in range(4) for ix in (0, 2, 3, 4, 5)]] == 0)
+    if lattice == 19:  # the second-order mapping has no third-order coefficients
+        assert np.all(grad[:, 10:] == 0)
+    # the mapped nodes' populations were overwritten: no gradient reaches them
+    gf = f_t.grad.cpu().numpy().reshape(h.d["q"], -1)
+    assert np.all(gf[:, d2l] == 0) and np.abs(gf).max() > 0
+    assert np.abs(g_t.grad.cpu().numpy()).max() > 0
+
+
+def test_coupled_gradient_fp32_close_to_fp64():
+    grads = []
+    for rb in (8, 4):
+        cfg = cfg_lb(real_bytes=rb)
+        h, f, g, tau, f0, gn, tn = setup(cfg, seed=5)
+        acc, S, d2l, nodes, targets = coupled_inputs(cfg)
+        real = torch.float32 if rb == 4 else torch.float64
+        acc_t = torch.from_numpy(acc).cuda().requires_grad_(True)
+        loss = B.coupled_interface_loss(h, acc_t, S, torch.from_numpy(d2l).cuda(), g, tau, f,
+                                        torch.from_numpy(nodes).cuda(),
+                                        torch.from_numpy(targets).to(real).cuda(), 4, 2)
+        loss.backward()
+        grads.append(acc_t.grad.cpu().numpy())
+    scale = np.abs(grads[0]).max()
+    assert scale > 0 and np.abs(grads[1] - grads[0]).max() < 2e-3 * scale
+
+
+def test_dsmc2lb_adjoint_rejects_the_equilibrium_mapping():
+    cfg = cfg_lb(d2l_mode=1)
+    h = B.Hybrid(cfg)
+    lam = torch.zeros_like(h.f())
+    grad = torch.zeros(int(h.L.ncells), 20, dtype=torch.float64, device="cuda")
+    with pytest.raises(B.HybError) as ei:
+        h.map_dsmc_to_lbm_adjoint(torch.tensor([0, 1], dtype=torch.int32, device="cuda"), lam, grad)
+    assert ei.value.status == B.HYB_EINVAL

@@ -1040,3 +1040,30 @@ def test_dsmc_3d_free_flight_moves_z_by_vz_dt_and_wraps():
     own = np.repeat(np.arange(d["ncells"]), np.diff(cs1))
     c1 = (np.floor(p["z"]).astype(int) * 3 + np.floor(p["y"]).astype(int)) * 6 + np.floor(p["x"]).astype(int)
     assert np.array_equal(c1, own)
+
+
+def test_dsmc2lb_is_linear_in_the_cumulative_sums_for_a_fixed_sample_count():
+    # Eq. coefficients with rho = N / (S ppc) and the means M / N: every raw coefficient is
+    # a sum over the cell's samples divided by S ppc (the N of rho cancels the N of the
+    # means), so the mapped populations are linear in the sums. The adjoint of the mapping
+    # is the transpose of this linear map.
+    for q in (39, 19):
+        cfg = small_cfg(ncx=6, ncy=2, lb_ratio=1, lattice=q)
+        src = O.Oracle(dict(cfg, ma=0.4))
+        src.dsmc_step(3)
+        a = src.acc().copy()
+        src.dsmc_step(4)
+        b = src.acc().copy() - a
+        S = 5
+        nodes = np.arange(O.derive(cfg)["nnodes"], dtype=np.int32)
+
+        def mapped(acc):
+            o = O.Oracle(cfg)
+            o.set(O.A_ACC, acc.reshape(-1))
+            o.set_scalars(0, S)
+            o.map_dsmc_to_lbm(nodes)
+            return o.f().astype(np.float64)
+
+        fa, fb, fab = mapped(a), mapped(b), mapped(0.3 * a + 1.7 * b)
+        assert np.allclose(fab, 0.3 * fa + 1.7 * fb, rtol=1e-12, atol=1e-14)
+        assert not np.allclose(fa, fb)
