@@ -201,6 +201,31 @@ void ora_counters(void* hv, uint64_t* out) {
 }
 
 // Per-node g_y and tau for the LBM of the handle (n = nnodes), or none (n = 0).
+// The Kn profile of the configuration p at its own rows: the NTC factors of DSMC cell rows
+// [crow0, crow0 + ncrows) and tau of LB rows [nrow0, nrow0 + nnrows) (either count may be 0).
+int ora_kn_profile_rows(const Params* p, int64_t crow0, int64_t ncrows, double* coll,
+                        int64_t nrow0, int64_t nnrows, double* tau) {
+    const Derived d = derive(*p);
+    for (int64_t i = 0; i < ncrows; ++i) coll[i] = kn_cell_coll(*p, d, crow0 + i);
+    for (int64_t i = 0; i < nnrows; ++i) tau[i] = kn_node_tau(*p, d, nrow0 + i);
+    return 0;
+}
+
+// Per-cell NTC factors (n = ncells), or the scalar factor again (n = 0).
+int ora_dsmc_cell_coll(void* hv, const double* coll, int64_t n) {
+    Handle* h = (Handle*)hv;
+    auto set = [&](auto& D) {
+        if (n == 0) {
+            D.coll_cell.clear();
+            return 0;
+        }
+        if (n != D.d.ncells) return 1;
+        D.coll_cell.assign(coll, coll + n);
+        return 0;
+    };
+    return (h->rb == 4) ? set(h->df) : set(h->dd);
+}
+
 int ora_lbm_node_params(void* hv, const double* g, const double* tau, int64_t n) {
     Handle* h = (Handle*)hv;
     auto set = [&](auto& B) {

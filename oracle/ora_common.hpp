@@ -111,6 +111,18 @@ inline double kn_at(const Params& p, double y) {
     return p.kn * std::exp(s * std::log(p.kn_end / p.kn));
 }
 
+// With the Kn profile: the NTC factor of Eq. collisionnumber (F_N sigma_T dt / V_c) of a DSMC
+// cell in row iy, at the Kn of the cell's centre, and tau of Eq. tau of an LB node in row j,
+// at the Kn of the row's centre.
+inline double kn_cell_coll(const Params& p, const Derived& d, int64_t iy) {
+    const double kn = kn_at(p, (double)iy + 0.5);
+    return d.dt / (std::sqrt(2.0) * (kn * (double)p.ncx) * (double)p.ppc);
+}
+inline double kn_node_tau(const Params& p, const Derived& d, int64_t j) {
+    const double kn = kn_at(p, ((double)j + 0.5) / (double)p.lb_ratio);
+    return std::sqrt(kPi / 8.0) * d.r_lat * kn * d.H_lat + 0.5;
+}
+
 // ---------------------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3",
 // SC'11): ten rounds of two 32x32->64 multiplies; the key is bumped by the Weyl constants

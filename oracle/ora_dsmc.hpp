@@ -87,10 +87,8 @@ struct Dsmc {
         coll_cell.clear();
         if (p.kn_profile == 1) {  // Eq. collisionnumber at each cell centre's Kn
             coll_cell.resize((size_t)d.ncells);
-            for (int64_t c = 0; c < d.ncells; ++c) {
-                const double kn = kn_at(p, (double)((c / p.ncx) % p.ncy) + 0.5);
-                coll_cell[(size_t)c] = d.dt / (std::sqrt(2.0) * (kn * (double)p.ncx) * (double)p.ppc);
-            }
+            for (int64_t c = 0; c < d.ncells; ++c)
+                coll_cell[(size_t)c] = kn_cell_coll(p, d, (c / p.ncx) % p.ncy);
         }
         nbar_sum.assign(d.ncells, 0u);
         acc.assign(d.ncells * kNumMoments, 0.0);

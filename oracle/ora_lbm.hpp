@@ -48,10 +48,8 @@ struct Lbm {
         if (p.kn_profile == 1) {  // tau of Eq. tau at each node's Kn, the force of kn
             g_node.assign((size_t)d.nnodes, d.g_step);
             tau_node.resize((size_t)d.nnodes);
-            for (int64_t n = 0; n < d.nnodes; ++n) {
-                const double kn = kn_at(p, ((double)((n / d.nx) % d.ny) + 0.5) / (double)p.lb_ratio);
-                tau_node[(size_t)n] = std::sqrt(kPi / 8.0) * d.r_lat * kn * d.H_lat + 0.5;
-            }
+            for (int64_t n = 0; n < d.nnodes; ++n)
+                tau_node[(size_t)n] = kn_node_tau(p, d, (n / d.nx) % d.ny);
         }
     }
 

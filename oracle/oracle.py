@@ -106,6 +106,8 @@ def lib():
         L.ora_grad_G.argtypes = [ctypes.c_int, vp, vp, i64, ctypes.c_int, vp]
         L.ora_gauss_pairs.argtypes = [vp, i64, ctypes.c_int, vp]
         L.ora_lbm_node_params.argtypes = [vp, vp, vp, i64]
+        L.ora_dsmc_cell_coll.argtypes = [vp, vp, i64]
+        L.ora_kn_profile_rows.argtypes = [ctypes.POINTER(Params), i64, i64, vp, i64, i64, vp]
         L.ora_lbm_grad_node.argtypes = [vp, i64, vp]
         L.ora_lbm_interface_loss.argtypes = [vp, vp, ctypes.c_int, vp]
         L.ora_lbm_interface_loss.restype = ctypes.c_double
@@ -304,6 +306,15 @@ class Oracle:
     def acc(self):
         return self.get(A_ACC).reshape(-1, 20)
 
+    def set_cell_coll(self, coll=None):
+        """Per-cell NTC factors (None: the scalar factor)."""
+        if coll is None:
+            lib().ora_dsmc_cell_coll(self.h, None, 0)
+            return
+        coll = np.ascontiguousarray(coll, np.float64).reshape(-1)
+        if lib().ora_dsmc_cell_coll(self.h, _ptr(coll), coll.size) != 0:
+            raise ValueError("one factor per cell")
+
     def set_node_params(self, g=None, tau=None):
         """Per-node body-force increment g_y and relaxation time tau (None: the scalars)."""
         if g is None:
@@ -337,6 +348,16 @@ class Oracle:
         out = np.zeros(16, np.uint64)
         lib().ora_counters(self.h, _ptr(out))
         return {n: int(out[i]) for i, n in enumerate(COUNTER_NAMES)}
+
+
+def kn_profile_rows(cfg, cell_rows, node_rows):
+    """The Kn profile of `cfg` at its own rows: NTC factors of the DSMC cell rows `cell_rows`
+    and tau of the LB rows `node_rows` (ranges)."""
+    coll = np.zeros(len(cell_rows))
+    tau = np.zeros(len(node_rows))
+    lib().ora_kn_profile_rows(ctypes.byref(make_params(cfg)), cell_rows.start, len(cell_rows),
+                              _ptr(coll), node_rows.start, len(node_rows), _ptr(tau))
+    return coll, tau
 
 
 def interface_loss_after(cfg, f0, g, tau, nodes, targets, nsteps):

@@ -1067,3 +1067,28 @@ def test_dsmc2lb_is_linear_in_the_cumulative_sums_for_a_fixed_sample_count():
         fa, fb, fab = mapped(a), mapped(b), mapped(0.3 * a + 1.7 * b)
         assert np.allclose(fab, 0.3 * fa + 1.7 * fb, rtol=1e-12, atol=1e-14)
         assert not np.allclose(fa, fb)
+
+
+def test_kn_profile_rows_and_setters_reproduce_the_built_in_profile():
+    # An oracle given the profile's per-cell NTC factors and per-node tau through the setters
+    # steps exactly like one that builds the profile itself: this is what lets a window of
+    # a large channel take the factors of the channel's own rows.
+    cfg = small_cfg(ncx=8, ncy=6, ppc=12, lb_ratio=2, kn=0.01, kn_profile=1, kn_end=0.3,
+                    real_bytes=4, ma=0.3)
+    d = O.derive(cfg)
+    coll, tau = O.kn_profile_rows(cfg, range(0, 6), range(0, d["ny"]))
+    assert coll[0] > coll[3] and tau[0] < tau[d["ny"] // 2]  # Kn rises towards y = L/2
+    a = O.Oracle(cfg)
+    b = O.Oracle(dict(cfg, kn_profile=0))
+    b.set_cell_coll(np.repeat(coll, 8))
+    b.set_node_params(np.full(d["nnodes"], d["g_step"]), np.repeat(tau, d["nx"]))
+    e, w, r = O.lattice(39)
+    f0 = W.gen_populations(w, d["nnodes"], seed=5).astype(np.float32)
+    for o in (a, b):
+        o.set_f(f0)
+        o.dsmc_step(3)
+        o.lbm_step(2)
+    for k in ("x", "y", "vx", "vy", "vz"):
+        assert np.array_equal(a.particles()[k], b.particles()[k]), k
+    assert a.counters() == b.counters()
+    assert np.array_equal(a.f(), b.f())
