@@ -282,7 +282,7 @@ def run_adjoint(args):
     # the adjoint step alone, 200 steps on fixed inputs
     lam_a, lam_b = torch.rand_like(f), torch.empty_like(f)
     gg, gt = torch.zeros_like(g), torch.zeros_like(tau)
-    wall = torch.zeros(2 * d["ny"] + 1, dtype=torch.float32, device=dev)
+    wall = torch.zeros(h.wall_scratch_size(), dtype=torch.float32, device=dev)
 
     def adj200():
         for _ in range(200):

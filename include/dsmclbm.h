@@ -249,8 +249,8 @@ hyb_status map_lbm_to_dsmc_noalloc(hyb_ctx* ctx, const int32_t* dev_cells, int32
  * state precision (real_bytes). g, tau and their gradients are one value per node in the
  * state precision. All buffers are device memory owned by the caller; every call is
  * enqueued on the context's stream; invalid pointers or sizes return HYB_EINVAL without
- * launching; the context's own populations are not touched. lbm_step_nodes and
- * lbm_adjoint_step are for the slab (ncz < 2): a 3D context returns HYB_EINVAL. */
+ * launching; the context's own populations are not touched. In 3D the populations are
+ * [q][nz][ny][nx] and nodes (z ny + y) nx + x. */
 
 /* One LB step f_dst = LB(f_src) with per-node g (force increment per step along the
  * streamwise axis) and tau. f_src and f_dst must differ. */
@@ -266,8 +266,8 @@ hyb_status lbm_interface_loss(hyb_ctx* ctx, const void* f, const int32_t* dev_no
 
 /* One step of the adjoint: with f the populations at step t and lam_next = dL/df_{t+1},
  * writes lam = dL/df_t (every entry) and adds dL/dg and dL/dtau of this step to grad_g and
- * grad_tau. wall is a scratch of 2 * ny + 1 values (state precision) that must be zero
- * before the first call; it is left zero. lam and lam_next must differ. The adjoint is that of the regularised
+ * grad_tau. wall is a scratch of 2 * ny * nz + 1 values (state precision; nz = 1 for the
+ * slab) that must be zero before the first call; it is left zero. lam and lam_next must differ. The adjoint is that of the regularised
  * collision: a context with lb_collision = 1 returns HYB_EINVAL. */
 hyb_status lbm_adjoint_step(hyb_ctx* ctx, const void* f, const void* lam_next, void* lam,
                             const void* g_node, const void* tau_node, void* grad_g,

@@ -299,6 +299,10 @@ class Hybrid:
                                         targets.data_ptr(), loss.data_ptr(), lam.data_ptr()),
                self.ctx)
 
+    def wall_scratch_size(self):
+        """Values of the adjoint's wall scratch: two sums per streamwise row (y, z), a ticket."""
+        return 2 * int(self.d["ny"]) * int(self.d["nz"]) + 1
+
     def map_dsmc_to_lbm_adjoint(self, nodes, lam, grad_acc):
         """Adds dL/d(acc) to grad_acc (float64 [ncells, 20]) from lam = dL/df after
         map_dsmc_to_lbm at `nodes` (distinct int32), and zeroes lam at those nodes."""
@@ -313,11 +317,11 @@ class Hybrid:
 
     def lbm_adjoint_step(self, f, lam_next, lam, g, tau, grad_g, grad_tau, wall):
         """lam = dL/df_t from f_t and lam_next = dL/df_{t+1}; adds this step's dL/dg and
-        dL/dtau to grad_g and grad_tau. wall: 2 ny + 1 zeros, left zero."""
+        dL/dtau to grad_g and grad_tau. wall: 2 ny nz + 1 zeros, left zero."""
         self._check_pop(f, lam_next, lam)
         self._check_node(g, tau, grad_g, grad_tau)
-        if wall.numel() != 2 * int(self.d["ny"]) + 1 or wall.dtype != self.real:
-            raise ValueError("wall scratch: 2 ny + 1 values in the state precision")
+        if wall.numel() != self.wall_scratch_size() or wall.dtype != self.real:
+            raise ValueError("wall scratch: 2 ny nz + 1 values in the state precision")
         self._inputs(f, lam_next, lam, g, tau, grad_g, grad_tau, wall)
         _check(lib().lbm_adjoint_step(self.ctx, f.data_ptr(), lam_next.data_ptr(), lam.data_ptr(),
                                       g.data_ptr(), tau.data_ptr(), grad_g.data_ptr(),
@@ -706,7 +710,7 @@ def _loss_adjoint(h, g, tau, lam_T, ckpts, T, K):
     with torch.cuda.stream(h.stream):
         grad_g = torch.zeros_like(g)
         grad_tau = torch.zeros_like(tau)
-        wall = torch.zeros(2 * int(h.d["ny"]) + 1, dtype=g.dtype, device=g.device)
+        wall = torch.zeros(h.wall_scratch_size(), dtype=g.dtype, device=g.device)
         lam_next = lam_T.clone()
         lam = torch.empty_like(lam_next)
         for s in reversed(range(len(ckpts))):

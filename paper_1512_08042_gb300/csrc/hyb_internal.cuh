@@ -149,8 +149,8 @@ struct LbmAdjArgs {
     const Real* tau_node;
     Real* grad_g;
     Real* grad_tau;
-    Real* wall;
-    int32_t nx, ny;
+    Real* wall;  // 2 nrows wall sums (left, right; row z ny + y) and a ticket
+    int32_t nx, ny, nz;
     int64_t nnodes;
 };
 

@@ -315,10 +315,10 @@ __global__ void __launch_bounds__(128) k_lbm(Launch<LbmArgs<Real>> L) {
 }
 
 // One thread per node, with per-node force increment and relaxation time.
-template <typename Real, class LAT, bool BGK>
+template <typename Real, class LAT, bool BGK, bool Z3 = false>
 __global__ void __launch_bounds__(128) k_lbm_param(LbmArgs<Real> a) {
     const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (u < a.nnodes) lbm_node<Real, LAT, true, BGK>(a, u);
+    if (u < a.nnodes) lbm_node<Real, LAT, true, BGK, Z3>(a, u);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -376,17 +376,22 @@ __device__ __forceinline__ void b3_terms(int k, Real ux, Real uy, Real uz, Real&
     }
 }
 
-template <typename Real, class LAT>
+template <typename Real, class LAT, bool Z3>
 __device__ __forceinline__ void lbm_adjoint_node(const LbmAdjArgs<Real>& a, const int64_t node) {
     constexpr int Q = LAT::Q;
     constexpr double R = lat_r<LAT>();
     const int nx = a.nx, ny = a.ny;
-    const int x = (int)(node % nx), y = (int)(node / nx);
+    const int x = (int)(node % nx);
+    const int y = Z3 ? (int)((node / nx) % ny) : (int)(node / nx);
+    const int z = Z3 ? (int)(node / ((int64_t)nx * ny)) : 0;
     const int64_t nn = a.nnodes;
 
     // forward intermediates of the node at t
     Real fs[Q];
-    pull_node<Real, LAT>(a.f, x, y, nx, ny, nn, fs);
+    if constexpr (Z3)
+        pull_node<Real, LAT, true>(a.f, x, y, nx, ny, nn, fs, z, a.nz);
+    else
+        pull_node<Real, LAT>(a.f, x, y, nx, ny, nn, fs);
     Real rho, jx, jy, jz, pm[6], q3[10];
     node_moments<Real, LAT>(fs, rho, jx, jy, jz, pm, q3);
     const Real gy = a.g_node[node];
@@ -535,31 +540,40 @@ __device__ __forceinline__ void lbm_adjoint_node(const LbmAdjArgs<Real>& a, cons
         }
         const int sx = x - ex;
         if (sx >= 0 && sx < nx) {
-            a.lam[(int64_t)q * nn + (int64_t)wrap_y(y - ey, ny) * nx + sx] = mu;
+            int64_t srow = wrap_y(y - ey, ny);  // the source row (z - ez) ny + (y - ey)
+            if constexpr (Z3) srow += (int64_t)wrap_y(z - ez, a.nz) * ny;
+            a.lam[(int64_t)q * nn + srow * nx + sx] = mu;
         } else if constexpr (ex != 0) {
-            // a source behind a wall: fs_q = w_q rho_wall(row y)
-            atomicAdd(&a.wall[(sx < 0 ? 0 : ny) + y], (Real)W<LAT>(q) * mu);
+            // a source behind a wall: fs_q = w_q rho_wall(row (y, z))
+            const int64_t nrows = Z3 ? (int64_t)ny * a.nz : (int64_t)ny;
+            const int64_t row = Z3 ? (int64_t)z * ny + y : (int64_t)y;
+            atomicAdd(&a.wall[(sx < 0 ? 0 : nrows) + row], (Real)W<LAT>(q) * mu);
         }
     });
     (void)MV;
 }
 
-// The populations leaving through a wall on row y' feed the wall density of row y' + e_y;
-// their adjoint is that row's wall adjoint times the flux normalisation. Task t < 2 ny: the
-// left (t < ny) or right wall of source row y'. The wall sums are read from L2.
-template <typename Real, class LAT>
-__device__ __forceinline__ void adj_wall_row(const LbmAdjArgs<Real>& a, int t) {
+// The populations leaving through a wall on row (y', z') feed the wall density of row
+// (y' + e_y, z' + e_z); their adjoint is that row's wall adjoint times the flux
+// normalisation. Task t < 2 nrows: the left (t < nrows) or right wall of source row
+// z' ny + y' (z' = 0 for the slab). The wall sums are read from L2.
+template <typename Real, class LAT, bool Z3>
+__device__ __forceinline__ void adj_wall_row(const LbmAdjArgs<Real>& a, int64_t t) {
     const int ny = a.ny, nx = a.nx;
-    const bool left = t < ny;
-    const int yr = left ? t : t - ny;  // the source row y'
+    const int64_t nrows = Z3 ? (int64_t)ny * a.nz : (int64_t)ny;
+    const bool left = t < nrows;
+    const int64_t r = left ? t : t - nrows;  // the source row
+    const int yr = (int)(r % ny), zr = (int)(r / ny);
     constexpr double inv_flux = 1.0 / wall_flux_norm<LAT>();
     static_for<LAT::Q>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
-        constexpr int ex = E<LAT>(q, 0), ey = E<LAT>(q, 1);
+        constexpr int ex = E<LAT>(q, 0), ey = E<LAT>(q, 1), ez = E<LAT>(q, 2);
         if constexpr (ex != 0) {
             if ((ex < 0) == left) {
-                const Real wb = (Real)inv_flux * __ldcg(&a.wall[(left ? 0 : ny) + wrap_y(yr + ey, ny)]);
-                Real* lq = a.lam + (int64_t)q * a.nnodes + (int64_t)yr * nx;
+                int64_t drow = wrap_y(yr + ey, ny);
+                if constexpr (Z3) drow += (int64_t)wrap_y(zr + ez, a.nz) * ny;
+                const Real wb = (Real)inv_flux * __ldcg(&a.wall[(left ? 0 : nrows) + drow]);
+                Real* lq = a.lam + (int64_t)q * a.nnodes + r * nx;
                 if (ex < 0)
                     for (int i = 0; i < -ex; ++i) lq[i] = wb;
                 else
@@ -572,13 +586,14 @@ __device__ __forceinline__ void adj_wall_row(const LbmAdjArgs<Real>& a, int t) {
 // One thread per node: the collision adjoint and the transposed pull. The last block to
 // finish (a ticket after the wall sums of every block) spreads the wall adjoints over the
 // populations leaving through the walls, which no node writes, and clears the sums.
-template <typename Real, class LAT>
+template <typename Real, class LAT, bool Z3 = false>
 __global__ void __launch_bounds__(128) k_lbm_adj(LbmAdjArgs<Real> a) {
     __shared__ int s_last;
     const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (u < a.nnodes) lbm_adjoint_node<Real, LAT>(a, u);
+    if (u < a.nnodes) lbm_adjoint_node<Real, LAT, Z3>(a, u);
     __syncthreads();
-    unsigned* ticket = reinterpret_cast<unsigned*>(a.wall + 2 * a.ny);
+    const int64_t nrows = Z3 ? (int64_t)a.ny * a.nz : (int64_t)a.ny;
+    unsigned* ticket = reinterpret_cast<unsigned*>(a.wall + 2 * nrows);
     if (threadIdx.x == 0) {
         __threadfence();  // this block's wall sums are visible before its ticket
         s_last = atomicAdd(ticket, 1u) == gridDim.x - 1u;
@@ -586,9 +601,9 @@ __global__ void __launch_bounds__(128) k_lbm_adj(LbmAdjArgs<Real> a) {
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    for (int t = threadIdx.x; t < 2 * a.ny; t += blockDim.x) adj_wall_row<Real, LAT>(a, t);
+    for (int64_t t = threadIdx.x; t < 2 * nrows; t += blockDim.x) adj_wall_row<Real, LAT, Z3>(a, t);
     __syncthreads();
-    for (int t = threadIdx.x; t < 2 * a.ny; t += blockDim.x) a.wall[t] = (Real)0;
+    for (int64_t t = threadIdx.x; t < 2 * nrows; t += blockDim.x) a.wall[t] = (Real)0;
     if (threadIdx.x == 0) *ticket = 0u;
 }
 
@@ -769,10 +784,16 @@ cudaError_t lbm_nodes_impl(Ctx& c, const void* f_src, void* f_dst, const void* g
     a.g_node = (const Real*)g;
     a.tau_node = (const Real*)tau;
     const int64_t blocks = (c.d.nnodes + 127) / 128;
-    if (a.bgk)
+    if (a.nz > 1) {
+        if (a.bgk)
+            k_lbm_param<Real, LAT, true, true><<<(unsigned)blocks, 128, 0, c.stream>>>(a);
+        else
+            k_lbm_param<Real, LAT, false, true><<<(unsigned)blocks, 128, 0, c.stream>>>(a);
+    } else if (a.bgk) {
         k_lbm_param<Real, LAT, true><<<(unsigned)blocks, 128, 0, c.stream>>>(a);
-    else
+    } else {
         k_lbm_param<Real, LAT, false><<<(unsigned)blocks, 128, 0, c.stream>>>(a);
+    }
     return cudaGetLastError();
 }
 
@@ -790,9 +811,13 @@ cudaError_t lbm_adj_impl(Ctx& c, const void* f, const void* lam_next, void* lam,
     a.wall = (Real*)wall;
     a.nx = (int32_t)c.d.nx;
     a.ny = (int32_t)c.d.ny;
+    a.nz = (int32_t)c.d.nz;
     a.nnodes = c.d.nnodes;
     const int64_t blocks = (c.d.nnodes + 127) / 128;
-    k_lbm_adj<Real, LAT><<<(unsigned)blocks, 128, 0, c.stream>>>(a);
+    if (a.nz > 1)
+        k_lbm_adj<Real, LAT, true><<<(unsigned)blocks, 128, 0, c.stream>>>(a);
+    else
+        k_lbm_adj<Real, LAT><<<(unsigned)blocks, 128, 0, c.stream>>>(a);
     return cudaGetLastError();
 }
 

@@ -391,8 +391,7 @@ hyb_status map_lbm_to_dsmc(hyb_ctx* h, const int32_t* dev_cells, int32_t n) {
 
 hyb_status lbm_step_nodes(hyb_ctx* h, const void* f_src, void* f_dst, const void* g_node,
                           const void* tau_node) {
-    if (!h || !f_src || !f_dst || f_src == f_dst || !g_node || !tau_node || h->c.d.nz != 1)
-        return HYB_EINVAL;
+    if (!h || !f_src || !f_dst || f_src == f_dst || !g_node || !tau_node) return HYB_EINVAL;
     return check(h->c, launch_lbm_step_nodes(h->c, f_src, f_dst, g_node, tau_node),
                  "lbm_step_nodes launch");
 }
@@ -410,7 +409,7 @@ hyb_status lbm_adjoint_step(hyb_ctx* h, const void* f, const void* lam_next, voi
                             const void* g_node, const void* tau_node, void* grad_g,
                             void* grad_tau, void* wall) {
     if (!h || !f || !lam_next || !lam || lam == lam_next || !g_node || !tau_node || !grad_g ||
-        !grad_tau || !wall || h->c.p.lb_collision != 0 || h->c.d.nz != 1)
+        !grad_tau || !wall || h->c.p.lb_collision != 0)
         return HYB_EINVAL;
     return check(h->c, launch_lbm_adjoint_step(h->c, f, lam_next, lam, g_node, tau_node, grad_g,
                                                grad_tau, wall),

@@ -241,11 +241,66 @@ def test_hybrid_3d_fp64_graph_matches_oracle():
     assert np.allclose(h.f().cpu().numpy(), o.f(), rtol=1e-11, atol=1e-14)
 
 
-def test_3d_context_rejects_the_slab_only_calls():
-    cfg = cfg3(ncz=2, lb_ratio=1)
+@pytest.mark.parametrize("lattice", [39, 19])
+def test_lbm_step_nodes_3d_matches_oracle(lattice):
+    # the differentiated LBM's forward in 3D: per-node g and tau
+    cfg = cfg3(ncx=6, ncy=3, ncz=2, lb_ratio=1, lattice=lattice, real_bytes=8, ma=0.5, kn=0.3)
+    h, o = B.Hybrid(cfg), O.Oracle(cfg)
+    d = h.d
+    e, w, r = O.lattice(lattice)
+    rng = np.random.default_rng(3)
+    f0 = W.gen_populations(w, d["nnodes"], seed=13)
+    g = d["g_step"] * (1 + 0.3 * rng.standard_normal(d["nnodes"]))
+    tau = d["tau"] * (1 + 0.1 * rng.standard_normal(d["nnodes"]))
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    a_, b_ = dev(f0.reshape(h.f().shape)), torch.empty(h.f().shape, dtype=torch.float64, device="cuda")
+    o.set_f(f0)
+    o.set_node_params(g, tau)
+    for _ in range(2):
+        h.lbm_step_nodes(a_, b_, dev(g), dev(tau))
+        a_, b_ = b_, a_
+    o.lbm_step(2)
+    h.sync()
+    err = np.abs(a_.cpu().numpy() - o.f()) / (np.abs(o.f()) + 1e-3 * w[:, None, None, None])
+    assert err.max() < 1e-12
+
+
+@pytest.mark.parametrize("lattice", [39, 19])
+def test_adjoint_gradient_3d_matches_oracle_central_differences(lattice):
+    # the adjoint in 3D (pull transposed over z too, wall sums per (y, z) row) against the
+    # oracle's central differences of the FP64 forward, over every node's g and tau
+    cfg = cfg3(ncx=6, ncy=3, ncz=2, lb_ratio=1, lattice=lattice, real_bytes=8, ma=0.5, kn=0.3)
     h = B.Hybrid(cfg)
-    f = torch.zeros_like(h.f())
-    g = torch.zeros(h.d["nnodes"], dtype=f.dtype, device=f.device)
-    with pytest.raises(B.HybError) as ei:
-        h.lbm_step_nodes(h.f(), f, g, g + 1.0)
-    assert ei.value.status == B.HYB_EINVAL
+    d = h.d
+    assert d["nz"] == 2 and d["nnodes"] == 36
+    e, w, r = O.lattice(lattice)
+    rng = np.random.default_rng(4)
+    f0 = W.gen_populations(w, d["nnodes"], seed=14)
+    g = d["g_step"] * (1 + 0.3 * rng.standard_normal(d["nnodes"]))
+    tau = d["tau"] * (1 + 0.1 * rng.standard_normal(d["nnodes"]))
+    nodes = np.array([1, 8, 13, 20, 27, 34], np.int32)  # both layers, near both walls
+    o = O.Oracle(cfg)
+    o.set_f(f0)
+    o.set_node_params(g, tau)
+    o.lbm_step(3)
+    targets = np.stack([o.grad_node(n) for n in nodes]) + 0.02 * rng.standard_normal((len(nodes), 20))
+    T = 3
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    g_t, tau_t = dev(g).requires_grad_(True), dev(tau).requires_grad_(True)
+    f_t = dev(f0.reshape(h.f().shape)).requires_grad_(True)
+    loss = B.interface_loss(h, g_t, tau_t, f_t, dev(nodes), dev(targets), T, ckpt_every=2)
+    loss.backward()
+    want_loss = O.interface_loss_after(cfg, f0, g, tau, nodes, targets, T)
+    assert float(loss.detach()) == pytest.approx(want_loss, rel=1e-10)
+    want_g, want_t = O.interface_loss_fd_gradient(cfg, f0, g, tau, nodes, targets, T)
+    for got, want in ((g_t.grad.cpu().numpy(), want_g), (tau_t.grad.cpu().numpy(), want_t)):
+        scale = np.abs(want).max()
+        assert scale > 0
+        assert np.abs(got - want).max() < 1e-6 * scale, np.abs(got - want).max() / scale
+    # populations: a directional derivative of the FP64 forward
+    v = rng.standard_normal(f0.shape)
+    eps = 1e-6
+    lp = O.interface_loss_after(cfg, f0 + eps * v, g, tau, nodes, targets, T)
+    lm = O.interface_loss_after(cfg, f0 - eps * v, g, tau, nodes, targets, T)
+    got = float((f_t.grad.cpu().numpy().reshape(f0.shape) * v).sum())
+    assert got == pytest.approx((lp - lm) / (2 * eps), rel=1e-6)
