@@ -1092,3 +1092,54 @@ def test_kn_profile_rows_and_setters_reproduce_the_built_in_profile():
         assert np.array_equal(a.particles()[k], b.particles()[k]), k
     assert a.counters() == b.counters()
     assert np.array_equal(a.f(), b.f())
+
+
+def test_mappings_3d_reduce_to_the_slab_in_layer_zero():
+    # With one LB node per cell and populations uniform in z, the cells and nodes of layer 0
+    # keep the slab's ids and Philox keys: LB2DSMC gives the slab's particles exactly (x, y
+    # and velocities), with z inside the cell; DSMC2LB of the same sums gives the slab's
+    # populations. Cells of other layers draw their own particles, inside their own cells.
+    for q in (39, 19):
+        cfg2 = small_cfg(ncx=8, ncy=3, ppc=20, lb_ratio=1, lattice=q, real_bytes=8)
+        cfg3 = dict(cfg2, ncz=3)
+        a, b = O.Oracle(cfg2), O.Oracle(cfg3)
+        e, w, r = O.lattice(q)
+        f2 = W.gen_populations(w, O.derive(cfg2)["nnodes"], seed=6, eps=0.08, rho_eps=0.2)
+        a.set_f(f2)
+        b.set_f(np.tile(f2.reshape(q, 1, -1), (1, 3, 1)))
+        cells2 = np.array([0, 5, 13, 23], np.int32)
+        cells3 = np.concatenate([cells2, cells2 + 24, [47, 71]]).astype(np.int32)
+        a.map_lbm_to_dsmc(cells2)
+        b.map_lbm_to_dsmc(cells3)
+        pa, pb = a.particles(), b.particles()
+        csa = a.get(O.A_CELL_START).astype(np.int64)
+        csb = b.get(O.A_CELL_START).astype(np.int64)
+        for c in cells2:
+            sa, sb = slice(csa[c], csa[c + 1]), slice(csb[c], csb[c + 1])
+            for k in ("x", "y", "vx", "vy", "vz"):
+                assert np.array_equal(pa[k][sa], pb[k][sb]), (q, c, k)
+            assert np.all((pb["z"][sb] >= 0) & (pb["z"][sb] < 1))
+        for c in cells3[4:]:
+            sb = slice(csb[c], csb[c + 1])
+            iz, iy, ix = c // 24, (c // 8) % 3, c % 8
+            assert np.all(np.floor(pb["z"][sb]) == iz) and np.all(np.floor(pb["y"][sb]) == iy)
+            assert np.all(np.floor(pb["x"][sb]) == ix)
+        assert not np.array_equal(pb["vx"][csb[24]:csb[25]], pb["vx"][csb[0]:csb[1]])
+        # DSMC2LB: layer-0 nodes from the same sums
+        # (each layer has its own sums: layer 2 must take its own cells' sums)
+        src = O.Oracle(dict(cfg2, ma=0.4))
+        src.dsmc_step(4)
+        acc0, S = src.acc().copy(), src.scalars()["nsamples"]
+        src.dsmc_step(4)
+        acc_l2 = src.acc().copy() * 0.5
+        acc3 = np.concatenate([acc0, 0.9 * acc0, acc_l2])
+        b.set(O.A_ACC, acc3.reshape(-1))
+        b.set_scalars(0, S)
+        nodes2 = np.arange(24, dtype=np.int32)
+        b.map_dsmc_to_lbm(np.concatenate([nodes2, nodes2 + 48]).astype(np.int32))
+        fb = b.f().reshape(q, -1)
+        for acc, off in ((acc0, 0), (acc_l2, 48)):
+            a.set(O.A_ACC, acc.reshape(-1))
+            a.set_scalars(0, S)
+            a.map_dsmc_to_lbm(nodes2)
+            assert np.array_equal(a.f().reshape(q, -1)[:, nodes2], fb[:, nodes2 + off]), (q, off)
