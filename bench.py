@@ -242,7 +242,14 @@ def run_adjoint(args):
     h = B.Hybrid(cfg, device=dev)
     d = h.d
     e, w, r = B.lattice(cfg["lattice"])
-    f0, sg, st, nodes_np, targets_np = W.diff_lbm_inputs(cfg, w)
+    f0, sg, st, nodes_np, _ = W.diff_lbm_inputs(cfg, w)
+    # targets sampled from the DSMC gas of the same channel: 200 DSMC steps, then the Grad
+    # coefficients of the cell holding each coupling node
+    h.dsmc_step(200)
+    h.sync()
+    nsamples = int(h.ctrl().cpu()[B.CTRL_NSAMPLES])
+    node_cells = (nodes_np // d["nx"]) // cfg["lb_ratio"] * cfg["ncx"] + (nodes_np % d["nx"]) // cfg["lb_ratio"]
+    targets_np = W.grad_targets_from_sums(h.acc().cpu().numpy(), nsamples, cfg["ppc"], node_cells)
     shape = (d["q"], d["ny"], d["nx"])
     mk = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a).astype(dt)).to(dev)
     f = mk(f0, np.float32).reshape(shape)
@@ -310,7 +317,8 @@ def run_adjoint(args):
                          "bytes_per_node": bytes_adj / d["nnodes"]},
         "fp32_vs_fp64": {"loss_rel": abs(L32.item() - L64.item()) / abs(L64.item()),
                          "grad_g_rel_maxnorm": err(g32, g64), "grad_tau_rel_maxnorm": err(t32, t64)},
-        "n_gpus": 1, "steps": reps, "dtype": "f32", "data": "synthetic",
+        "n_gpus": 1, "steps": reps, "dtype": "f32",
+        "data": "synthetic populations; targets sampled from 200 DSMC steps of the same channel",
         "config": {"workload": "differentiated LBM, 256 x 128 D3Q39, %d steps, checkpoints every %d"
                                % (T, K), "coupling_nodes": int(len(nodes_np)),
                    "l2": "inputs not flushed: every gradient sweeps 2000 states"},

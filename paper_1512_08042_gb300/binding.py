@@ -264,7 +264,9 @@ class Hybrid:
 
     # -- differentiated LBM (per-node g and tau, adjoint, interface loss) ----------------
     def _pop_shape(self):
-        return tuple(self.f().shape)
+        # from the derived constants: this check runs on every step call, so it builds no view
+        q, ny, nx, nz = (int(self.d[k]) for k in ("q", "ny", "nx", "nz"))
+        return (q, nz, ny, nx) if int(self.d["ncz"]) >= 2 else (q, ny, nx)
 
     def _check_pop(self, *ts):
         for t in ts:

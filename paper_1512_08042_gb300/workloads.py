@@ -79,6 +79,33 @@ def diff_lbm_inputs(cfg, weights, seed=9, spread_g=0.1, spread_tau=0.02):
     return f0, spread_g * g, spread_tau * tau, nodes, targets
 
 
+def grad_targets_from_sums(acc, nsamples, ppc, cells):
+    """Interface-loss targets sampled from a DSMC gas: for each listed cell, the 20 Grad
+    coefficients of its particles from the cumulative sums acc[cell] = (N, S v, S vv, S vvv)
+    over `nsamples` samples: rho = N / (S ppc), the mean velocity u, the comoving second
+    moments minus the identity (xx xy xz yy yz zz) and the comoving third moments (xxx xxy xxz
+    xyy xyz xzz yyy yyz yzz zzz), in thermal units like the populations' coefficients."""
+    a = np.asarray(acc, np.float64)[np.asarray(cells)]
+    n = a[:, 0]
+    u = a[:, 1:4] / n[:, None]
+    m2 = a[:, 4:10] / n[:, None]
+    m3 = a[:, 10:20] / n[:, None]
+    pairs = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+    triples = [(0, 0, 0), (0, 0, 1), (0, 0, 2), (0, 1, 1), (0, 1, 2), (0, 2, 2), (1, 1, 1),
+               (1, 1, 2), (1, 2, 2), (2, 2, 2)]
+    p2 = {ij: k for k, ij in enumerate(pairs)}
+    raw2 = lambda i, j: m2[:, p2[(min(i, j), max(i, j))]]
+    out = np.zeros((len(a), 20))
+    out[:, 0] = n / (nsamples * ppc)
+    out[:, 1:4] = u
+    for k, (i, j) in enumerate(pairs):
+        out[:, 4 + k] = raw2(i, j) - u[:, i] * u[:, j] - (1.0 if i == j else 0.0)
+    for k, (i, j, l) in enumerate(triples):
+        out[:, 10 + k] = (m3[:, k] - u[:, i] * raw2(j, l) - u[:, j] * raw2(i, l) - u[:, l] * raw2(i, j)
+                          + 2.0 * u[:, i] * u[:, j] * u[:, l])
+    return out
+
+
 def ensemble_configs(n=64, seed=1000):
     """The batched ensemble: n independent channels of the 64 x 1 geometry (walls across,
     one periodic cell), H uniform in 32..256 cells, 20..100 particles per cell, Kn
