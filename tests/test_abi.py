@@ -150,3 +150,15 @@ def test_3d_restrictions_are_rejected(lib):
     params = (B.HybParams * 2)(*[B.make_params(c) for c in (cfg3, cfg3)])
     off = (ctypes.c_uint64 * 4)()
     assert lib.hyb_batch_layout(params, 2, off) == B.HYB_EINVAL
+
+
+@pytest.mark.parametrize("ncz", [0, 3])
+def test_population_shape_check_uses_the_lattice_shape(lib, ncz):
+    # the shape every population argument must have: [q][ny][nx] for the slab and
+    # [q][nz][ny][nx] in 3D, formed from the derived constants alone (no device memory)
+    cfg = W.config(ncx=8, ncy=3, ppc=5, lb_ratio=2, ncz=ncz, seed=1)
+    h = B.Hybrid.__new__(B.Hybrid)
+    h.d = B.derive(cfg)
+    want = (39, 6, 16) if ncz < 2 else (39, 6, 6, 16)
+    assert h._pop_shape() == want
+    assert h.wall_scratch_size() == 2 * 6 * (6 if ncz >= 2 else 1) + 1
