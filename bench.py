@@ -373,7 +373,10 @@ def main():
             "impl": "reference", "metric": METRIC, "value": rate, "unit": "hybrid steps/s",
             "n_gpus": args.gpus, "steps": done, "warmup": 0,
             "ms_per_step": 1e3 / rate, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32" if cfg["real_bytes"] == 4 else "f64",
+            "precision": "oracle: DSMC state and arithmetic in the state precision, LB "
+                         "collision and moment sums in FP64",
+            "data": "synthetic",
             "config": {"workload": args.workload, "particles": n, "lb_nodes": d["nnodes"]},
             "cpu_baseline": {"value": rate, "unit": "hybrid steps/s", "cores": 1,
                              "kind": "oracle",
