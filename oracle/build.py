@@ -1,6 +1,6 @@
 """Compile the CPU oracle into oracle/_build/liboracle.so.
 
-Test infrastructure only: the oracle is the checker for the CUDA library, never part of it.
+Test infrastructure only: the oracle checks the CUDA library and is never part of it.
 Plain g++ with floating-point contraction off, so that float arithmetic is performed one
 IEEE operation at a time on x86-64 and AArch64 alike.
 """
