@@ -109,7 +109,7 @@ typedef struct {
                                periodic y and z, Sec. 3.1): 0 or 1 for the quasi-2D slab of
                                one cell and one LB layer; >= 2 for full 3D, with particle z
                                positions, ncz * lb_ratio LB layers, cells (iz ncy + iy) ncx + ix
-                               and nodes (z ny + y) nx + x. Not with a batch or the adjoint. */
+                               and nodes (z ny + y) nx + x. Not with a batch. */
     int32_t pad1;
 } hyb_params;
 
