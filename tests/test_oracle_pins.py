@@ -1143,3 +1143,28 @@ def test_mappings_3d_reduce_to_the_slab_in_layer_zero():
             a.set_scalars(0, S)
             a.map_dsmc_to_lbm(nodes2)
             assert np.array_equal(a.f().reshape(q, -1)[:, nodes2], fb[:, nodes2 + off]), (q, off)
+
+
+def test_interface_loss_3d_with_z_uniform_inputs_is_nz_times_the_slab():
+    # populations, force increments and relaxation times that do not depend on z: every
+    # layer steps like the slab, so the loss over each layer's copy of the slab's nodes is
+    # nz times the slab's loss (the per-node step and the loss in 3D, against the slab)
+    cfg2 = small_cfg(ncx=6, ncy=3, lb_ratio=1, ma=0.4, kn=0.2)
+    cfg3 = dict(cfg2, ncz=3)
+    d2 = O.derive(cfg2)
+    e, w, r = O.lattice(39)
+    rng = np.random.default_rng(8)
+    n2 = d2["nnodes"]
+    f2 = W.gen_populations(w, n2, seed=9)
+    g2 = d2["g_step"] * (1 + 0.3 * rng.standard_normal(n2))
+    t2 = d2["tau"] * (1 + 0.1 * rng.standard_normal(n2))
+    nodes2 = np.array([0, 4, 7, 11, 17], np.int32)
+    targets2 = 0.05 * rng.standard_normal((len(nodes2), 20))
+    targets2[:, 0] += 1.0
+    l2 = O.interface_loss_after(cfg2, f2, g2, t2, nodes2, targets2, 3)
+    f3 = np.tile(f2.reshape(39, 1, n2), (1, 3, 1))
+    nodes3 = np.concatenate([nodes2 + k * n2 for k in range(3)]).astype(np.int32)
+    l3 = O.interface_loss_after(cfg3, f3, np.tile(g2, 3), np.tile(t2, 3), nodes3,
+                                np.tile(targets2, (3, 1)), 3)
+    assert l3 == pytest.approx(3 * l2, rel=1e-13)
+    assert l2 > 0
