@@ -216,8 +216,9 @@ hyb_status map_dsmc_to_lbm(hyb_ctx* ctx, const int32_t* dev_nodes, int32_t n);
  * cell = iy * ncx + ix, distinct), replace its particles by floor(rho ppc + U) new ones,
  * with rho the mean LB density of the cell's lb_ratio^2 nodes; velocities drawn from the
  * Grad distribution of the cell's populations by acceptance-rejection with envelope
- * C = 1 + 30 M; positions uniform in the cell. The coefficients are formed in the state
- * precision. A cell whose new count exceeds its bin keeps its particles and raises
+ * C = 1 + 30 M; positions uniform in the cell. The mean populations, rho, u and the Grad
+ * coefficients are formed in FP64; the trials are evaluated in the state precision with the
+ * coefficients rounded to it. A cell whose new count exceeds its bin keeps its particles and raises
  * HYB_ST_CAPACITY; an invalid cell index is skipped and raises HYB_ST_BAD_INPUT. */
 hyb_status map_lbm_to_dsmc(hyb_ctx* ctx, const int32_t* dev_cells, int32_t n);
 
@@ -232,7 +233,9 @@ hyb_status map_lbm_to_dsmc(hyb_ctx* ctx, const int32_t* dev_cells, int32_t n);
  * n > HYB_NOALLOC_MAX_CELLS returns HYB_EINVAL and launches nothing. The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) with that device
  * current; make that first call before any stream capture, and call with the context's
- * device current (otherwise HYB_EINVAL). Every call on a device shares the one array and it
+ * device current (otherwise HYB_EINVAL). Calls outside a capture look the address up again,
+ * so a call after cudaDeviceReset or from another context of the device uses its own
+ * context's array; concurrent first calls from several host threads are serialised. Every call on a device shares the one array and it
  * keeps the last call's records: calls that overlap on the GPU (other streams or contexts on
  * the same device) race on it and must be serialised by the caller. */
 #define HYB_NOALLOC_MAX_CELLS 4096

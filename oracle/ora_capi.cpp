@@ -321,38 +321,25 @@ int ora_grad_coeffs(int q, const double* f, double* out) {
     return 0;
 }
 
-// The same coefficients computed in the precision real_bytes from f rounded to it:
-// out = [rho, u(3), a2(6), a3(10), M, C] (packed order).
+// The FP64 coefficients packed by symmetry and rounded to the precision real_bytes, as the
+// sampler uses them: out = [rho, u(3), a2(6), a3(10), M, C] (packed order; rho and M in FP64).
 int ora_grad_coeffs_packed(int q, const double* f, int real_bytes, double* out) {
     if (q != 39 && q != 19) return 1;
     Lattice L = make_lattice(q);
     const int order = q == 39 ? 3 : 2;
-    auto put = [&](const auto& g) {
+    const GradCell g = grad_from_populations(L, f, order);
+    auto put = [&](const auto& p) {
         out[0] = g.rho;
-        for (int i = 0; i < 3; ++i) out[1 + i] = g.u[i];
-        for (int k = 0; k < 6; ++k) out[4 + k] = g.a2[k];
-        for (int k = 0; k < 10; ++k) out[10 + k] = g.a3[k];
+        for (int i = 0; i < 3; ++i) out[1 + i] = p.u[i];
+        for (int k = 0; k < 6; ++k) out[4 + k] = p.a2[k];
+        for (int k = 0; k < 10; ++k) out[10 + k] = p.a3[k];
         out[20] = g.M;
-        out[21] = g.C;
+        out[21] = p.C;
     };
-    if (real_bytes == 4) {
-        std::vector<float> ff(f, f + q);
-        put(grad_cell<float>(L, ff.data(), order));
-    } else {
-        put(grad_cell<double>(L, f, order));
-    }
-    return 0;
-}
-
-// The fixed pairwise sum of n <= 64 terms, in the precision real_bytes.
-int ora_pairwise64(const double* t, int n, int real_bytes, double* out) {
-    if (n < 0 || n > 64) return 1;
-    if (real_bytes == 4) {
-        std::vector<float> tf(t, t + n);
-        *out = pairwise64<float>(tf.data(), n);
-    } else {
-        *out = pairwise64<double>(t, n);
-    }
+    if (real_bytes == 4)
+        put(pack<float>(g));
+    else
+        put(pack<double>(g));
     return 0;
 }
 

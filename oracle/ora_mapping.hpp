@@ -10,9 +10,10 @@
 // LB2DSMC (Sec. 2.2, Table 1): from the populations, rho and u, then the Grad coefficients
 // of the distribution in the frame moving with u, normalised by rho (so a^(0) = 1 and
 // a^(1) = 0, and G of Eq. distr_outeq starts at n = 2): a2_ij = sum f c_i c_j / rho - d_ij,
-// a3_ijk = sum f c_i c_j c_k / rho with c = xi_a - u, in the state precision, every sum over
-// the populations in one fixed pairwise order. M = largest |component|, C = 1 + 30 M (Eq. C). Trial velocities from the unit Maxwellian by Box-Muller, accepted
-// when C R <= G(xi) (state precision); the particle velocity is sqrt(kT/m) xi + u, i.e.
+// a3_ijk = sum f c_i c_j c_k / rho with c = xi_a - u, in FP64. M = largest |component|,
+// C = 1 + 30 M (Eq. C). Trial velocities from the unit Maxwellian by Box-Muller, accepted
+// when C R <= G(xi), taken in the state precision with the coefficients rounded to it; the
+// particle velocity is sqrt(kT/m) xi + u, i.e.
 // xi + u in c_th units (Eq. step6 read with the unit-variance weight of Eq. globalMax). The
 // particle count conserves the mapped mass: E[N] = rho * ppc, rounded stochastically.
 #pragma once
@@ -76,75 +77,13 @@ inline bool dsmc_coefficients(const double* m, uint64_t S, int ppc, Coeffs& a) {
     return true;
 }
 
-// Sum of the terms t[0..n), n <= 64, in the one fixed pairwise order used by every sum over
-// the populations in the LB2DSMC coefficients (the paper leaves the order open): the terms
-// are padded with zeros to 64, s_i = t_i + t_{i+32} for i < 32, then s_i = s_i + s_{i+h} for
-// i < h with h = 16, 8, 4, 2, 1 in turn; the sum is s_0.
-template <class Real>
-Real pairwise64(const Real* t, int n) {
-    Real s[32];
-    for (int i = 0; i < 32; ++i) {
-        const Real lo = i < n ? t[i] : (Real)0;
-        const Real hi = i + 32 < n ? t[i + 32] : (Real)0;
-        s[i] = lo + hi;
-    }
-    for (int h = 16; h >= 1; h /= 2)
-        for (int i = 0; i < h; ++i) s[i] = s[i] + s[i + h];
-    return s[0];
-}
-
-// Grad coefficients of Table 1 step 1, in the frame moving with u and normalised by rho,
-// computed in the precision Real from the populations f[q] (q < L.q <= 64):
-//   rho = sum f,  u_i = (sum f xi_i) / rho,  c = xi - u,
-//   a2_ij = (sum (f c_i) c_j) / rho - d_ij          (i <= j: xx xy xz yy yz zz),
-//   a3_ijk = (sum ((f c_i) c_j) c_k) / rho          (i <= j <= k: xxx xxy ... zzz),
-// each sum by pairwise64, xi = r e rounded to Real; M = largest |a2|, |a3| component and
+// Grad coefficients of Table 1 step 1, written out from their definition in FP64 (the
+// precision the Grad solve takes), in the frame moving with u and normalised by rho, from
+// the populations f[q] (q < L.q):
+//   rho = sum_a f_a,  u_i = (sum_a f_a xi_ai) / rho,  c_a = xi_a - u,
+//   a2_ij = (sum_a f_a c_ai c_aj) / rho - d_ij,  a3_ijk = (sum_a f_a c_ai c_aj c_ak) / rho,
+// every sum taken over a in population order. M = largest |component| of a2 and a3 and
 // C = 1 + 30 M (Eq. C).
-template <class Real>
-struct GradCellT {
-    Real rho, u[3], a2[6], a3[10], M, C;
-};
-
-template <class Real>
-GradCellT<Real> grad_cell(const Lattice& L, const Real* f, int order) {
-    const int Q = L.q;
-    Real xi[64][3], c[64][3], t[64];
-    for (int q = 0; q < Q; ++q)
-        for (int i = 0; i < 3; ++i) xi[q][i] = (Real)L.xi[q][i];
-    GradCellT<Real> g{};
-    for (int q = 0; q < Q; ++q) t[q] = f[q];
-    g.rho = pairwise64(t, Q);
-    for (int i = 0; i < 3; ++i) {
-        for (int q = 0; q < Q; ++q) t[q] = f[q] * xi[q][i];
-        g.u[i] = pairwise64(t, Q) / g.rho;
-    }
-    for (int q = 0; q < Q; ++q)
-        for (int i = 0; i < 3; ++i) c[q][i] = xi[q][i] - g.u[i];
-    int o = 0;
-    for (int i = 0; i < 3; ++i)
-        for (int j = i; j < 3; ++j, ++o) {
-            for (int q = 0; q < Q; ++q) t[q] = (f[q] * c[q][i]) * c[q][j];
-            Real v = pairwise64(t, Q) / g.rho;
-            if (i == j) v = v - (Real)1;
-            g.a2[o] = v;
-        }
-    o = 0;
-    if (order >= 3)
-        for (int i = 0; i < 3; ++i)
-            for (int j = i; j < 3; ++j)
-                for (int k = j; k < 3; ++k, ++o) {
-                    for (int q = 0; q < Q; ++q) t[q] = ((f[q] * c[q][i]) * c[q][j]) * c[q][k];
-                    g.a3[o] = pairwise64(t, Q) / g.rho;
-                }
-    Real M = 0;
-    for (int k = 0; k < 6; ++k) M = std::max(M, (Real)std::fabs(g.a2[k]));
-    for (int k = 0; k < 10; ++k) M = std::max(M, (Real)std::fabs(g.a3[k]));
-    g.M = M;
-    g.C = (Real)1 + (Real)30 * M;
-    return g;
-}
-
-// The same coefficients in double as full symmetric tensors (for the pins).
 struct GradCell {
     double rho;
     double u[3];
@@ -153,23 +92,37 @@ struct GradCell {
 };
 
 inline GradCell grad_from_populations(const Lattice& L, const double* f, int order) {
-    const GradCellT<double> p = grad_cell<double>(L, f, order);
+    const int Q = L.q;
     GradCell g{};
-    g.rho = p.rho;
-    for (int i = 0; i < 3; ++i) g.u[i] = p.u[i];
+    g.rho = 0.0;
+    for (int q = 0; q < Q; ++q) g.rho += f[q];
+    for (int i = 0; i < 3; ++i) {
+        double s = 0.0;
+        for (int q = 0; q < Q; ++q) s += f[q] * L.xi[q][i];
+        g.u[i] = s / g.rho;
+    }
+    std::vector<std::array<double, 3>> c((size_t)Q);
+    for (int q = 0; q < Q; ++q)
+        for (int i = 0; i < 3; ++i) c[q][i] = L.xi[q][i] - g.u[i];
     g.ahat = Coeffs{};
     g.ahat.a0 = 1.0;
+    double M = 0.0;
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {
-            g.ahat.a2[i][j] = p.a2[packed2(std::min(i, j), std::max(i, j))];
+            double s = 0.0;
+            for (int q = 0; q < Q; ++q) s += f[q] * c[q][i] * c[q][j];
+            g.ahat.a2[i][j] = s / g.rho - kd(i, j);
+            M = std::max(M, std::fabs(g.ahat.a2[i][j]));
+            if (order < 3) continue;
             for (int k = 0; k < 3; ++k) {
-                int x = i, y = j, z = k;
-                sort3(x, y, z);
-                g.ahat.a3[i][j][k] = p.a3[packed3(x, y, z)];
+                double s3 = 0.0;
+                for (int q = 0; q < Q; ++q) s3 += f[q] * c[q][i] * c[q][j] * c[q][k];
+                g.ahat.a3[i][j][k] = s3 / g.rho;
+                M = std::max(M, std::fabs(g.ahat.a3[i][j][k]));
             }
         }
-    g.M = p.M;
-    g.C = p.C;
+    g.M = M;
+    g.C = 1.0 + 30.0 * M;
     return g;
 }
 
@@ -207,17 +160,8 @@ struct GradPacked {
     Real a2[6], a3[10], u[3], C;
 };
 
-template <class Real>
-GradPacked<Real> pack(const GradCellT<Real>& g) {
-    GradPacked<Real> p;
-    for (int k = 0; k < 6; ++k) p.a2[k] = g.a2[k];
-    for (int k = 0; k < 10; ++k) p.a3[k] = g.a3[k];
-    for (int i = 0; i < 3; ++i) p.u[i] = g.u[i];
-    p.C = g.C;
-    return p;
-}
-
-// Packed copies of double coefficients rounded to Real (for the pin of G's grouping).
+// The FP64 coefficients packed by symmetry and rounded to the state precision Real, in which
+// the sampler takes its accept decisions (Table 1 steps 4-6).
 template <class Real>
 GradPacked<Real> pack(const GradCell& g) {
     GradPacked<Real> p;
@@ -328,18 +272,19 @@ void map_lbm_to_dsmc(Dsmc<Real>& D, const Lbm<Real>& B, const int32_t* cells, in
         const int64_t ix = cell % D.p.ncx, iy = (cell / D.p.ncx) % D.p.ncy;
         const int64_t iz = cell / ((int64_t)D.p.ncx * D.p.ncy);
         const int rz = D.three_d() ? r : 1;  // LB layers of the cell along z
-        std::vector<Real> fbar(L.q, (Real)0);
+        // the mean populations of the cell's nodes and its Grad coefficients, in FP64
+        std::vector<double> fbar(L.q, 0.0);
         for (int q = 0; q < L.q; ++q) {
-            Real s = 0;
+            double s = 0.0;
             for (int dz = 0; dz < rz; ++dz)
                 for (int dy = 0; dy < r; ++dy)
                     for (int dx = 0; dx < r; ++dx)
-                        s += (Real)B.fa(q, ix * r + dx, iy * r + dy, iz * rz + dz);
-            fbar[q] = s / (Real)(r * r * rz);
+                        s += (double)B.fa(q, ix * r + dx, iy * r + dy, iz * rz + dz);
+            fbar[q] = s / (double)(r * r * rz);
         }
-        const GradCellT<Real> g = grad_cell<Real>(L, fbar.data(), B.d.order);
+        const GradCell g = grad_from_populations(L, fbar.data(), B.d.order);
         const double u = u01d(draw(D.p.seed, (uint32_t)cell, t, TAG_L2D_ROUND, 0, 0)[0]);
-        const double ne = std::floor((double)g.rho * (double)D.p.ppc + u);
+        const double ne = std::floor(g.rho * (double)D.p.ppc + u);
         const uint32_t nnew = ne > 0.0 ? (uint32_t)ne : 0u;
         if (nnew > (uint32_t)D.d.bin) {
             D.status |= ST_CAPACITY;

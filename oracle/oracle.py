@@ -100,7 +100,6 @@ def lib():
         L.ora_dsmc2lb_node.argtypes = [ctypes.c_int, vp, u64, ctypes.c_int, vp]
         L.ora_grad_coeffs.argtypes = [ctypes.c_int, vp, vp]
         L.ora_grad_coeffs_packed.argtypes = [ctypes.c_int, vp, ctypes.c_int, vp]
-        L.ora_pairwise64.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
         L.ora_grad_sample.argtypes = [ctypes.c_int, vp, u64, u32, u32, i64, vp, vp]
         L.ora_float_funcs.argtypes = [vp, i64, vp, vp, vp]
         L.ora_grad_G.argtypes = [ctypes.c_int, vp, vp, i64, ctypes.c_int, vp]
@@ -178,22 +177,14 @@ def grad_coeffs(q, f):
 
 
 def grad_coeffs_packed(q, f, real_bytes):
-    """LB2DSMC coefficients computed in the precision real_bytes from f rounded to it."""
+    """LB2DSMC coefficients in FP64, packed and rounded to the precision real_bytes (rho and
+    M stay FP64), as the sampler takes them."""
     f = np.ascontiguousarray(f, np.float64)
     out = np.empty(22, np.float64)
     if lib().ora_grad_coeffs_packed(q, _ptr(f), real_bytes, _ptr(out)) != 0:
         raise ValueError(q)
     return {"rho": out[0], "u": out[1:4].copy(), "a2": out[4:10].copy(),
             "a3": out[10:20].copy(), "M": out[20], "C": out[21]}
-
-
-def pairwise64(t, real_bytes=8):
-    """The fixed pairwise sum of up to 64 terms used by the LB2DSMC coefficients."""
-    t = np.ascontiguousarray(t, np.float64)
-    out = np.empty(1, np.float64)
-    if lib().ora_pairwise64(_ptr(t), t.size, real_bytes, _ptr(out)) != 0:
-        raise ValueError(t.size)
-    return float(out[0])
 
 
 def grad_sample(q, f, seed, cell, t, n):

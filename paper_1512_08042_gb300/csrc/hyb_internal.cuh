@@ -48,10 +48,9 @@ enum KernelId {
     K_COUNT = 5,
 };
 
-// LB2DSMC per-cell record (map_scratch).
-// Grad record of one coupling cell (176 bytes). v holds 20 values of the state precision
-// Real, packed from its start: a2[6] (xx xy xz yy yz zz), a3[10] (xxx xxy xxz xyy xyz xzz
-// yyy yyz yzz zzz), u[3], C.
+// LB2DSMC per-cell record (map_scratch): the Grad record of one coupling cell (176 bytes),
+// FP64: rho, the new particle count and v = a2[6] (xx xy xz yy yz zz), a3[10] (xxx xxy xxz
+// xyy xyz xzz yyy yyz yzz zzz), u[3], C.
 struct GradRec {
     double rho;
     uint32_t nnew;

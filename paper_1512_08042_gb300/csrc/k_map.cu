@@ -1,27 +1,28 @@
-// The two kinetic mappings of Sec. 2. The Grad/Hermite coefficients are solved in FP64;
+// The two kinetic mappings of Sec. 2. The Grad/Hermite coefficients are formed in FP64;
 // populations and particle state are Real (float or double).
 //
 // k_d2l (DSMC2LB, Sec. 2.1): one warp per coupling node. The cumulative sums of the
 // node's DSMC cell give rho = <N>/ppc, the per-particle raw moments <v>, <vv>, <vvv> (one
-// FP64 reciprocal of the count, the ratios rounded to the state precision), and the raw
-// Hermite coefficients a0 = rho, a1 = rho <v>, a2 = rho(<vv> - I), a3 = rho(<vvv> - sym(<v> I));
-// the populations f_a = w_a sum_{n<=N} a^(n):H^(n)(xi_a)/n! (Eq. discretefunctions) are
-// evaluated in the state precision.
+// FP64 reciprocal of the count) and the raw Hermite coefficients a0 = rho, a1 = rho <v>,
+// a2 = rho(<vv> - I), a3 = rho(<vvv> - sym(<v> I)), all in FP64 (the stress and heat-flux
+// parts are differences of nearly equal moments); the populations
+// f_a = w_a sum_{n<=N} a^(n):H^(n)(xi_a)/n! (Eq. discretefunctions) are evaluated in the
+// state precision from the coefficients rounded to it.
 //
-// LB2DSMC (Sec. 2.2, Table 1), k_l2d: one block per coupling cell. Warp 0 forms the mean
-// populations of the cell's lb_ratio^2 nodes, rho and u, the comoving coefficients
-// a2 = sum f c c / rho - I and a3 = sum f c c c / rho (c = xi - u), M, C = 1 + 30 M (Eq. C),
-// all in the state precision with one fixed pairwise order of every population sum, and the
-// particle count floor(rho ppc + U); the other warps wait (trials drawn meanwhile took
-// issue slots from warp 0 and lengthened the path). The cell's trial stream is then
-// evaluated 256 trials at a time: Box-Muller xi from the unit
-// Maxwellian, accepted when C R <= G(xi), G = 1 + a2:H2/2 + a3:H3/6 (Eq. distr_outeq) in
-// the state precision; the k-th accepted trial becomes the k-th particle of the cell's bin
-// (replacing the old ones), velocity xi + u (Eq. step6 in c_th units), position uniform in
-// the cell from the same trial's draws.
+// LB2DSMC (Sec. 2.2, Table 1), k_l2d: one block per coupling cell. Warp 0 forms, in FP64, the
+// mean populations of the cell's lb_ratio^2 nodes, rho and u, the comoving coefficients
+// a2 = sum f c c / rho - I and a3 = sum f c c c / rho (c = xi - u), M, C = 1 + 30 M (Eq. C)
+// and the particle count floor(rho ppc + U); the other warps wait (trials drawn meanwhile
+// took issue slots from warp 0 and lengthened the path). The cell's trial stream is then
+// evaluated 256 trials at a time in the state precision, with the coefficients rounded to
+// it: Box-Muller xi from the unit Maxwellian, accepted when C R <= G(xi),
+// G = 1 + a2:H2/2 + a3:H3/6 (Eq. distr_outeq); the k-th accepted trial becomes the k-th
+// particle of the cell's bin (replacing the old ones), velocity xi + u (Eq. step6 in c_th
+// units), position uniform in the cell from the same trial's draws.
 // Draws are keyed by (cell, step, purpose, trial index), so the results do not depend on
 // the launch shape.
 #include <cstring>
+#include <mutex>
 
 #include "hyb_internal.cuh"
 
@@ -100,31 +101,31 @@ __device__ __forceinline__ void d2l_entries(const MapArgs<Real>& a, int first, i
             if (lane == 0) atomicOr(&a.ctrl[CTRL_STATUS], HYB_ST_BAD_INPUT);
             continue;
         }
-        // per-particle moments, lane k: <v> (1-3), <vv> (4-9), <vvv> (10-19); the FP64
-        // reciprocal is formed by one lane (FP64 runs at a small fraction of the FP32 rate)
+        // per-particle moments, lane k: <v> (1-3), <vv> (4-9), <vvv> (10-19), and the raw
+        // Hermite coefficients, in FP64; the reciprocal of the count is formed by one lane
         double inv = 0.0;
         if (lane == 0) inv = 1.0 / NS;
         inv = __shfl_sync(kFull, inv, 0);
-        const Real mr = (Real)(mk * inv);
-        const Real rho = (Real)NS / ((Real)S * (Real)a.ppc);
-        const Real m1x = __shfl_sync(kFull, mr, 1);
-        const Real m1y = __shfl_sync(kFull, mr, 2);
-        const Real m1z = __shfl_sync(kFull, mr, 3);
-        Real sub = 0;
+        const double mr = mk * inv;
+        const double rho = NS / ((double)S * (double)a.ppc);
+        const double m1x = __shfl_sync(kFull, mr, 1);
+        const double m1y = __shfl_sync(kFull, mr, 2);
+        const double m1z = __shfl_sync(kFull, mr, 3);
+        double sub = 0.0;
         switch (lane) {
-            case 4: case 7: case 9: sub = (Real)1; break;       // xx yy zz
-            case 10: sub = (Real)3 * m1x; break;                // xxx
-            case 11: sub = m1y; break;                          // xxy
-            case 12: sub = m1z; break;                          // xxz
-            case 13: sub = m1x; break;                          // xyy
-            case 15: sub = m1x; break;                          // xzz
-            case 16: sub = (Real)3 * m1y; break;                // yyy
-            case 17: sub = m1z; break;                          // yyz
-            case 18: sub = m1y; break;                          // yzz
-            case 19: sub = (Real)3 * m1z; break;                // zzz
+            case 4: case 7: case 9: sub = 1.0; break;       // xx yy zz
+            case 10: sub = 3.0 * m1x; break;                // xxx
+            case 11: sub = m1y; break;                      // xxy
+            case 12: sub = m1z; break;                      // xxz
+            case 13: sub = m1x; break;                      // xyy
+            case 15: sub = m1x; break;                      // xzz
+            case 16: sub = 3.0 * m1y; break;                // yyy
+            case 17: sub = m1z; break;                      // yyz
+            case 18: sub = m1y; break;                      // yzz
+            case 19: sub = 3.0 * m1z; break;                // zzz
             default: break;
         }
-        Real coef = lane == 0 ? rho : rho * (mr - sub);
+        double coef = lane == 0 ? rho : rho * (mr - sub);
         if (a.eq_mode && lane >= 4u && lane < (unsigned)kMoments) {
             // the local equilibrium of rho and u (Sec. 4, Eq. feq_dsmc): a2 = rho u u,
             // a3 = rho u u u
@@ -132,14 +133,15 @@ __device__ __forceinline__ void d2l_entries(const MapArgs<Real>& a, int first, i
                                       {2, 2, -1}, {0, 0, 0}, {0, 0, 1}, {0, 0, 2}, {0, 1, 1},
                                       {0, 1, 2}, {0, 2, 2}, {1, 1, 1}, {1, 1, 2}, {1, 2, 2},
                                       {2, 2, 2}};
-            const Real uu[3] = {m1x, m1y, m1z};
+            const double uu[3] = {m1x, m1y, m1z};
             const int* ix = I[lane - 4u];
             coef = rho * uu[ix[0]] * uu[ix[1]];
             if (ix[2] >= 0) coef = coef * uu[ix[2]];
         }
+        const Real coef_r = (Real)coef;
         Real cf[kMoments];
 #pragma unroll
-        for (int k = 0; k < kMoments; ++k) cf[k] = __shfl_sync(kFull, coef, k);
+        for (int k = 0; k < kMoments; ++k) cf[k] = __shfl_sync(kFull, coef_r, k);
         const Real* a2 = cf + 4;
         const Real* a3 = cf + 10;
         const Real tx = a3[0] + a3[3] + a3[5], ty = a3[1] + a3[6] + a3[8], tz = a3[2] + a3[7] + a3[9];
@@ -201,16 +203,6 @@ __device__ __forceinline__ void halving_sum(Real (&v)[N], unsigned lane) {
     }
 #pragma unroll
     for (; o >= 1; o >>= 1) v[0] = v[0] + __shfl_xor_sync(kFull, v[0], o);
-}
-
-__device__ __forceinline__ float warp_max_abs(float x) {
-    return __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(fabsf(x))));
-}
-__device__ __forceinline__ double warp_max_abs(double x) {
-    double m = fabs(x);
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) m = fmax(m, __shfl_xor_sync(kFull, m, o));
-    return m;
 }
 
 // G of Eq. distr_outeq in the state precision, from the comoving coefficients packed by
@@ -340,31 +332,75 @@ __global__ void __launch_bounds__(128) k_d2l_adj(MapArgs<Real> a, Real* lam, dou
                                    (int)(((int64_t)gridDim.x * blockDim.x) >> 5));
 }
 
-// Table 1 step 1 for the cell `cell`, by one warp, in the state precision. Lane l holds the
-// cell-mean populations q = l and l + 32 (zero past Q); each population sum adds the lane's
-// two terms and then reduces over the lanes (halving_sum), which is the oracle's pairwise
-// order. Products are (f c_i) c_j and ((f c_i) c_j) c_k with i <= j <= k. Returns, in every
-// lane, the packed values (lane k < 20 holds value k: a2[6], a3[10], u[3], C) and rho.
+// Raw Hermite basis of each lattice speed in FP64, for the LB2DSMC coefficient solve:
+// B[q] = (1, xi_x, xi_y, xi_z, xi_i xi_j (xx xy xz yy yz zz), xi_i xi_j xi_k (xxx xxy xxz xyy
+// xyz xzz yyy yyz yzz zzz)), xi = r e formed in double, built at compile time.
+template <class LAT>
+struct LatBasis {
+    double b[LAT::Q][kMoments];
+};
+template <class LAT>
+constexpr LatBasis<LAT> make_basis() {
+    LatBasis<LAT> t{};
+    for (int a = 0; a < LAT::Q; ++a) {
+        double x[3] = {};
+        for (int i = 0; i < 3; ++i) x[i] = lat_r<LAT>() * (double)LatTab<LAT>::e(a, i);
+        int o = 0;
+        t.b[a][o++] = 1.0;
+        for (int i = 0; i < 3; ++i) t.b[a][o++] = x[i];
+        for (int i = 0; i < 3; ++i)
+            for (int j = i; j < 3; ++j) t.b[a][o++] = x[i] * x[j];
+        for (int i = 0; i < 3; ++i)
+            for (int j = i; j < 3; ++j)
+                for (int k = j; k < 3; ++k) t.b[a][o++] = x[i] * x[j] * x[k];
+    }
+    return t;
+}
+__device__ const LatBasis<D3Q39> g_basis39 = make_basis<D3Q39>();
+__device__ const LatBasis<D3Q19> g_basis19 = make_basis<D3Q19>();
+
+template <class LAT>
+__device__ __forceinline__ const LatBasis<LAT>& lat_basis() {
+    if constexpr (LAT::Q == 39)
+        return g_basis39;
+    else
+        return g_basis19;
+}
+
+// Index pairs and triples of the packed second and third moments.
+__device__ __forceinline__ void packed_pair(int k, int& i, int& j) {
+    constexpr int P[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+    i = P[k][0];
+    j = P[k][1];
+}
+__device__ __forceinline__ int packed_pair_index(int i, int j) {
+    if (i > j) {
+        const int t = i;
+        i = j;
+        j = t;
+    }
+    return i == 0 ? j : (i == 1 ? 2 + j : 5);
+}
+
+// Table 1 step 1 for the cell `cell`, by one warp, in FP64 (the Grad-coefficient solve).
+// Lane l holds the cell-mean populations q = l and l + 32 (zero past Q), the mean of the
+// cell's lb_ratio^2 (3D: ^3) nodes summed in FP64. The raw moments R_k = sum_q f_q B_k(xi_q)
+// (k < 20) are summed over the lanes; lane k then forms one comoving coefficient from them:
+//   u_i = R_i / rho,
+//   a2_ij = R_ij / rho - u_i u_j - d_ij                                     (= sum f c c / rho - d),
+//   a3_ijk = (R_ijk - u_i R_jk - u_j R_ik - u_k R_ij) / rho + 2 u_i u_j u_k   (= sum f c c c / rho),
+// c = xi - u, exact identities of the centred sums. Returns, in every lane, the packed FP64
+// value (lane k < 20 holds value k: a2[6], a3[10], u[3], C = 1 + 30 M) and rho.
 template <typename Real, class LAT, bool Z3>
 __device__ __forceinline__ void grad_coefficients(const MapArgs<Real>& a, int cell, unsigned lane,
-                                                  Real& mine, Real& rho_out) {
+                                                  double& mine, double& rho_out) {
     constexpr int Q = LAT::Q;
-    constexpr int NM = LAT::ORDER >= 3 ? 16 : 6;  // distinct second and third moments
-    constexpr int NP = NM > 8 ? 16 : 8;           // padded to a power of two
-    constexpr int SH = NP == 16 ? 1 : 2;          // lane >> SH: moment held after the sum
+    constexpr int NM = LAT::ORDER >= 3 ? kMoments : 10;  // raw moments of the order
     const int r = a.lb_ratio;
     const int q0 = (int)lane, q1 = (int)lane + 32;
     const bool v0 = q0 < Q, v1 = q1 < Q;
-    const LatXi<LAT, Real>& lt = lat_xi<LAT, Real>();
-    Real xi0[3] = {0, 0, 0}, xi1[3] = {0, 0, 0};
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        if (v0) xi0[i] = lt.x[3 * q0 + i];
-        if (v1) xi1[i] = lt.x[3 * q1 + i];
-    }
     const int ix = cell % a.ncx, iy = (cell / a.ncx) % a.ncy, iz = cell / (a.ncx * a.ncy);
-    // mean populations of the cell's nodes (r^2 in 2D, r^3 in 3D), summed in node order
-    // (dz, dy, dx)
+    // mean populations of the cell's nodes (r^2 in 2D, r^3 in 3D)
     constexpr int KN = Z3 ? 8 : 4;  // lb_ratio <= 2
     const int nk = Z3 ? r * r * r : r * r;
     Real p0[KN], p1[KN];
@@ -380,68 +416,60 @@ __device__ __forceinline__ void grad_coefficients(const MapArgs<Real>& a, int ce
             if (v1) p1[k] = a.f[(int64_t)q1 * a.nnodes + node];
         }
     }
-    Real s0 = 0, s1 = 0;
+    double s0 = 0.0, s1 = 0.0;
 #pragma unroll
     for (int k = 0; k < KN; ++k)
         if (k < nk) {
-            s0 += p0[k];
-            s1 += p1[k];
+            s0 += (double)p0[k];
+            s1 += (double)p1[k];
         }
-    const Real nn = (Real)nk;
-    const Real f0 = v0 ? s0 / nn : (Real)0;
-    const Real f1 = v1 ? s1 / nn : (Real)0;
-    // rho and j; lanes 0-7 end with rho, 8-15 jx, 16-23 jy, 24-31 jz
-    Real t4[4];
-    t4[0] = f0 + f1;
+    const double f0 = v0 ? s0 / (double)nk : 0.0;
+    const double f1 = v1 ? s1 / (double)nk : 0.0;
+    const LatBasis<LAT>& B = lat_basis<LAT>();
+    double t[32];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) t4[1 + i] = f0 * xi0[i] + f1 * xi1[i];
-    halving_sum<Real, 4>(t4, lane);
-    const Real rho = __shfl_sync(kFull, t4[0], 0);
-    Real u[3];
+    for (int k = 0; k < 32; ++k) t[k] = 0.0;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) u[i] = __shfl_sync(kFull, t4[0], 8 * (i + 1)) / rho;
-    Real c0[3], c1[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        c0[i] = xi0[i] - u[i];
-        c1[i] = xi1[i] - u[i];
+    for (int k = 0; k < NM; ++k) {
+        const double lo = v0 ? f0 * B.b[q0][k] : 0.0;
+        const double hi = v1 ? f1 * B.b[q1][k] : 0.0;
+        t[k] = lo + hi;
     }
-    Real tm[NP];
-    int o = 0;
+    halving_sum<double, 32>(t, lane);  // lane k holds R_k
+    const double R = t[0];
+    auto at = [&](int k) { return __shfl_sync(kFull, R, k); };
+    const double rho = at(0);
+    double inv = 0.0;
+    if (lane == 0) inv = 1.0 / rho;  // one FP64 reciprocal, broadcast
+    inv = __shfl_sync(kFull, inv, 0);
+    const double u[3] = {at(1) * inv, at(2) * inv, at(3) * inv};
+    double R2[6];
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = i; j < 3; ++j, ++o) {
-            const Real lo = v0 ? (f0 * c0[i]) * c0[j] : (Real)0;
-            const Real hi = v1 ? (f1 * c1[i]) * c1[j] : (Real)0;
-            tm[o] = lo + hi;
-        }
-    if constexpr (NM > 6) {
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = i; j < 3; ++j)
-#pragma unroll
-                for (int k = j; k < 3; ++k, ++o) {
-                    const Real lo = v0 ? ((f0 * c0[i]) * c0[j]) * c0[k] : (Real)0;
-                    const Real hi = v1 ? ((f1 * c1[i]) * c1[j]) * c1[k] : (Real)0;
-                    tm[o] = lo + hi;
-                }
+    for (int k = 0; k < 6; ++k) R2[k] = at(4 + k);
+    double val = 0.0;
+    if (lane >= 4u && lane < 10u) {
+        int i, j;
+        packed_pair((int)lane - 4, i, j);
+        val = R * inv - u[i] * u[j] - (i == j ? 1.0 : 0.0);
+    } else if (lane >= 10u && lane < (unsigned)NM) {
+        constexpr int T[10][3] = {{0, 0, 0}, {0, 0, 1}, {0, 0, 2}, {0, 1, 1}, {0, 1, 2},
+                                  {0, 2, 2}, {1, 1, 1}, {1, 1, 2}, {1, 2, 2}, {2, 2, 2}};
+        const int i = T[lane - 10u][0], j = T[lane - 10u][1], k = T[lane - 10u][2];
+        const double cross = u[i] * R2[packed_pair_index(j, k)] + u[j] * R2[packed_pair_index(i, k)] +
+                             u[k] * R2[packed_pair_index(i, j)];
+        val = (R - cross) * inv + 2.0 * u[i] * u[j] * u[k];
     }
+    double M = fabs(val);
 #pragma unroll
-    for (int k = NM; k < NP; ++k) tm[k] = 0;
-    halving_sum<Real, NP>(tm, lane);
-    const int mom = (int)(lane >> SH);
-    Real val = tm[0] / rho;
-    if (mom == 0 || mom == 3 || mom == 5) val = val - (Real)1;
-    const Real M = warp_max_abs(mom < NM ? val : (Real)0);
-    // gather the packed values: lane k < 16 takes moment k, lanes 16-18 u, lane 19 C
-    const Real mv = __shfl_sync(kFull, val, (int)((lane & 15u) << SH));
-    mine = lane < (unsigned)NM ? mv : (Real)0;
+    for (int o = 16; o >= 1; o >>= 1) M = fmax(M, __shfl_xor_sync(kFull, M, o));
+    // packed values: lane k < 16 takes coefficient k (a2 at lanes 4-9, a3 at 10-19), lanes
+    // 16-18 u, lane 19 C
+    const double mv = __shfl_sync(kFull, val, (int)(lane + 4u) & 31);
+    mine = lane < (unsigned)(NM - 4) ? mv : 0.0;
     if (lane == GR_U) mine = u[0];
     if (lane == GR_U + 1) mine = u[1];
     if (lane == GR_U + 2) mine = u[2];
-    if (lane == GR_C) mine = (Real)1 + (Real)30 * M;
+    if (lane == GR_C) mine = 1.0 + 30.0 * M;
     rho_out = rho;
 }
 
@@ -471,20 +499,19 @@ __device__ __forceinline__ void l2d_cells(const MapArgs<Real>& a, int first, int
         const uint32_t cell = (uint32_t)icell;
         const uint32_t old = threadIdx.x == 0 ? a.count[cell] : 0u;
         if (w == 0) {
-            Real mine, rho;
+            double mine, rho;
             grad_coefficients<Real, LAT, Z3>(a, icell, lane, mine, rho);
             GradRec& g = a.grad[ci];
-            Real* pv = reinterpret_cast<Real*>(g.v);
             if (lane < 20u) {
-                s_c[lane] = mine;
-                pv[lane] = mine;
+                s_c[lane] = (Real)mine;  // the sampler takes its decisions in the state precision
+                g.v[lane] = mine;
             }
             if (lane == 0) {
                 const double ur = u01d(draw(a.seed, cell, t_step, TAG_L2D_ROUND, 0, 0).x);
-                const double ne = floor((double)rho * (double)a.ppc + ur);
+                const double ne = floor(rho * (double)a.ppc + ur);
                 const uint32_t nnew = ne > 0.0 ? (uint32_t)ne : 0u;
                 s_nnew = nnew;
-                g.rho = (double)rho;
+                g.rho = rho;
                 g.nnew = nnew;
                 g.pad = 0;
             }
@@ -696,17 +723,29 @@ cudaError_t l2d_impl(Ctx& c, const int32_t* cells, int32_t n) {
 }
 
 constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
 GradRec* g_scratch_addr[kMaxDevices] = {};
 
-// Device address of the fixed scratch on `device`, which must be the current device.
-cudaError_t noalloc_scratch(int device, GradRec** out) {
+// Device address of the fixed scratch on `device`, which must be the current device. A
+// __device__ array's address belongs to the CUDA context that loaded the module, so it is
+// looked up again on every call whose stream is not being captured (a call after
+// cudaDeviceReset, or from another context on the same device, gets its own context's
+// address); during a capture the address of the last lookup on that device is used, which is
+// why the first call on a device must come before any capture. The lock serialises
+// concurrent first calls from several host threads.
+cudaError_t noalloc_scratch(int device, cudaStream_t stream, GradRec** out) {
     if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
-    if (!g_scratch_addr[device]) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(stream, &cap);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_l2d_scratch);
+        e = cudaGetSymbolAddress(&p, g_l2d_scratch);
         if (e != cudaSuccess) return e;
         g_scratch_addr[device] = (GradRec*)p;
     }
+    if (!g_scratch_addr[device]) return cudaErrorStreamCaptureUnsupported;
     *out = g_scratch_addr[device];
     return cudaSuccess;
 }
@@ -745,7 +784,7 @@ cudaError_t launch_map_l2d_noalloc(Ctx& c, const int32_t* cells, int32_t n) {
     if (e != cudaSuccess) return e;
     if (dev != c.device) return cudaErrorInvalidDevice;
     GradRec* rec = nullptr;
-    e = noalloc_scratch(dev, &rec);
+    e = noalloc_scratch(dev, c.stream, &rec);
     if (e != cudaSuccess) return e;
     if (c.p.lattice == 39)
         return c.p.real_bytes == 4 ? l2d_noalloc_impl<float, D3Q39>(c, cells, n, rec)
