@@ -2,15 +2,18 @@
 
 One step = one hybrid step over the whole channel: DSMC step (move, sort, NTC collisions,
 sampling), DSMC2LB on the coupling strip, LB stream-collide, LB2DSMC on the coupling strip.
-Default workload: 64 x 256 DSMC cells at 50 particles/cell (819,200 particles), Kn 0.05,
-FP32 state with FP64 moment sums, 128 x 512 D3Q39 lattice, 8-node-wide coupling strip.
-Inputs are synthetic (seeded Maxwellian start). The L2 cache is flushed before every timed
-step (a 512 MB write), and every step is timed with CUDA events on the library's stream.
+Default workload: the large channel, 512 x 4096 DSMC cells at 50 particles/cell
+(104,857,600 particles), Kn varying log-linearly from 0.005 to 0.5 along the channel, FP32
+state with FP64 moment sums, 1024 x 8192 D3Q39 lattice with per-node relaxation times,
+coupled every step on a 4-cell (8-node) strip. Inputs are synthetic (seeded Maxwellian
+start) and larger than the L2 cache (about 23 GB of state); the L2 is also flushed before
+every timed step (a 512 MB write), and every step is timed with CUDA events on the library's
+stream.
 
 Prints one JSON line. `--impl reference` times the CPU oracle instead (the reference arm:
-there is no reference implementation of the paper's method to run, only its restatement).
-Under torchrun each rank runs an independent replica on its own GPU (replicas only: the
-paper's method has no exchange between ranks at this workload).
+there is no reference implementation of the paper's method to run, only its restatement),
+on windows of the same channel in one process per host core. Under torchrun each rank runs
+an independent replica on its own GPU (replicas only).
 """
 import argparse
 import hashlib
@@ -29,9 +32,10 @@ sys.path.insert(0, ROOT)
 from paper_1512_08042_gb300 import workloads as W  # noqa: E402
 
 METRIC = "DSMC particle-updates/s, LBM MLUPS, hybrid steps/s on 1 GB300 at stated tol"
-DEFAULT_WORKLOAD = "poiseuille_64x256_ppc50_fp32"
+DEFAULT_WORKLOAD = "poiseuille_512x4096_ppc50_knvar_fp32"
+WINDOW_ROWS = 16  # DSMC cell rows of the oracle windows (CPU baseline, FP64 error sample)
 FLUSH_BYTES = 512 << 20
-LAUNCHES_PER_STEP = 5  # move, collide, dsmc2lb, lbm, lb2dsmc
+LAUNCHES_PER_STEP = 4  # fused collide-and-move, dsmc2lb, lbm, lb2dsmc (plus one move per call)
 
 
 def kernel_algorithmic_bytes(name, cfg, d, n_particles, n_nodes_map, n_cells_map):
@@ -41,13 +45,17 @@ def kernel_algorithmic_bytes(name, cfg, d, n_particles, n_nodes_map, n_cells_map
     three_d = d["ncz"] >= 2
     pr = 6 if three_d else 5  # Reals per particle: x, y (, z), vx, vy, vz
     if name == "move":
-        # pr Real read, pr Real + a u32 tag written per particle; per cell: its count read and
-        # the destination counts' atomics
-        return n_particles * (2 * pr * rb + 4) + ncells * 8
+        # pr Real read, pr Real + a u32 key written per particle (into its new cell's bin);
+        # per cell: its count read and cleared, the destination counts' atomics
+        return n_particles * (2 * pr * rb + 4) + ncells * 12
     if name == "collide":
-        # pr Real + tag read, pr Real written per particle; per cell: count, crmax, rem,
-        # nbar_sum read and written, the source count cleared, 20 FP64 sums read and written
-        return n_particles * (2 * pr * rb + 4) + ncells * (4 + 2 * rb + 2 * rb + 8 + 4 + 320)
+        # pr Real + key read, pr Real written per particle (in place); per cell: count, crmax,
+        # rem, nbar_sum read and written, 20 FP64 sums read and written
+        return n_particles * (2 * pr * rb + 4) + ncells * (4 + 2 * rb + 2 * rb + 8 + 320)
+    if name == "fused":
+        # the collide's reads and per-cell state, then the move's writes: pr Real + key read
+        # and written per particle; per cell also the count cleared and the destination atomics
+        return n_particles * 2 * (pr * rb + 4) + ncells * (4 + 2 * rb + 2 * rb + 8 + 320 + 8)
     if name == "lbm":
         return d["nnodes"] * 2 * d["q"] * rb
     if name == "dsmc2lb":
@@ -58,6 +66,19 @@ def kernel_algorithmic_bytes(name, cfg, d, n_particles, n_nodes_map, n_cells_map
         nodes_per_cell = cfg["lb_ratio"] ** (3 if three_d else 2)
         return n_cells_map * (nodes_per_cell * d["q"] * rb + 176 + cfg["ppc"] * pr * rb)
     return 0
+
+
+def method_bytes(cfg, d):
+    """Algorithmic bytes of the method per unit, as the survey's measurement table counts
+    them: per DSMC particle-update the particle state read and written once (2 x x, y(, z),
+    vx, vy, vz) plus 344 B of per-cell state (20 FP64 sums read and written, count and offset,
+    (sigma c)max, remainder and N-bar) amortised over ppc; per LB node-update the populations
+    read and written once, plus 8 B where tau (and g) are per-node fields."""
+    rb = cfg["real_bytes"]
+    pr = 6 if d["ncz"] >= 2 else 5
+    dsmc = 2 * pr * rb + 344.0 / cfg["ppc"]
+    lbm = 2 * d["q"] * rb + (8 if cfg.get("kn_profile", 0) == 1 else 0)
+    return dsmc, lbm
 
 
 def sample_clocks(stop, out):
@@ -136,21 +157,187 @@ def max_over_ranks(dist, value, device):
     return float(t.item())
 
 
-def run_oracle(cfg, steps, budget_s):
-    """Time the CPU oracle on hybrid steps of `cfg`; returns (steps/s, steps run)."""
+def window_config(cfg, rows, real_bytes):
+    """The channel's first `rows` DSMC cell rows as a periodic channel of their own (the
+    oracle window): the same cell ids, Philox keys and derived constants."""
+    return dict(cfg, ncy=rows, kn_profile=0, real_bytes=real_bytes)
+
+
+def window_oracle(cfg, rows, real_bytes):
+    """The oracle of the window, with the channel's Kn profile evaluated at its rows."""
     from oracle import oracle as O
-    nodes, cells = W.coupling_sites(cfg)
-    o = O.Oracle(cfg)
-    done, t0 = 0, time.perf_counter()
-    while done < steps:
+    wcfg = window_config(cfg, rows, real_bytes)
+    o = O.Oracle(wcfg)
+    if cfg.get("kn_profile", 0) == 1:
+        d = O.derive(wcfg)
+        coll, tau = O.kn_profile_rows(cfg, range(0, rows), range(0, d["ny"]))
+        o.set_cell_coll(np.repeat(coll, cfg["ncx"]))
+        o.set_node_params(np.full(d["nnodes"], d["g_step"]), np.repeat(tau, d["nx"]))
+    return o, wcfg
+
+
+def oracle_window_worker(job):
+    """One host process: hybrid steps (DSMC step, DSMC2LB, LB step, LB2DSMC on the window's own
+    strip) of an FP64 oracle window. job = (cfg, rows, nsteps, nwarm, budget_s): nwarm untimed
+    steps, then nsteps timed ones, or as many as fit in budget_s if nsteps is 0. Returns
+    (steps timed, seconds)."""
+    cfg, rows, nsteps, nwarm, budget_s = job
+    o, wcfg = window_oracle(cfg, rows, 8)
+    nodes, cells = W.coupling_sites(wcfg)
+
+    def one():
         o.dsmc_step(1)
         o.map_dsmc_to_lbm(nodes)
         o.lbm_step(1)
         o.map_lbm_to_dsmc(cells)
+
+    for _ in range(nwarm):
+        one()
+    done, t0 = 0, time.perf_counter()
+    while (nsteps and done < nsteps) or (not nsteps and time.perf_counter() - t0 < budget_s):
+        one()
         done += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
-    return done / (time.perf_counter() - t0), done
+    return done, time.perf_counter() - t0
+
+
+def run_oracle_windows(cfg, procs, nsteps=0, nwarm=1, budget_s=8.0, rows=WINDOW_ROWS):
+    """The FP64 oracle on `procs` windows of the channel at once, one process per window
+    (processes started with spawn). Returns the equivalent rate of the whole channel in
+    hybrid steps/s (window steps/s summed over the processes, times rows / ncy), the summed
+    window steps/s and the steps each process timed."""
+    import multiprocessing as mp
+    from oracle import build as OB
+    OB.build()
+    job = (cfg, rows, nsteps, nwarm, budget_s)
+    if procs == 1:
+        res = [oracle_window_worker(job)]
+    else:
+        with mp.get_context("spawn").Pool(procs) as pool:
+            res = pool.map(oracle_window_worker, [job] * procs)
+    win_rate = sum(n / t for n, t in res)
+    return win_rate * rows / cfg["ncy"], win_rate, [n for n, _ in res]
+
+
+def host_cores():
+    """Cores of the host: os.cpu_count() and, where lscpu runs, its count."""
+    n = os.cpu_count() or 1
+    try:
+        r = subprocess.run(["lscpu", "-p=CPU"], capture_output=True, text=True, timeout=10)
+        cpus = [ln for ln in r.stdout.splitlines() if ln and not ln.startswith("#")]
+        if cpus:
+            n = min(n, len(cpus)) if n else len(cpus)
+    except Exception:
+        pass
+    return n
+
+
+def fp64_error_sample(h, cfg, B, cells_np, rows=WINDOW_ROWS):
+    """The error of the GPU's results against the FP64 oracle at the benchmarked size.
+
+    (1) LB2DSMC coefficients: the FP64 Grad records the GPU wrote at its last coupling step
+    against the oracle's FP64 coefficients of the same populations, for every coupling cell.
+    (2) One DSMC step and one LB step from the GPU's own current state: the state of the
+    channel's first `rows` cell rows is loaded (in FP64) into an oracle window, both sides
+    step, and the interior rows are compared: cells whose count agrees, particles within
+    1e-5, the largest velocity error among the rest of the matching particles, the moment
+    sums the step added (per particle), and the populations relative to w_a rho."""
+    import torch
+    from oracle import oracle as O
+    d = h.d
+    ncx, r, q = cfg["ncx"], cfg["lb_ratio"], d["q"]
+    nx = d["nx"]
+    e, w, _ = O.lattice(q)
+    out = {}
+    # (1) LB2DSMC coefficients of the last coupling step
+    rho_g, nnew_g, v_g = h.grad_records(len(cells_np))
+    y0 = int(cells_np.min()) // ncx
+    y1 = int(cells_np.max()) // ncx + 1
+    f = h.f()[:, y0 * r:y1 * r].double().cpu().numpy()  # the strip's node rows
+    coef_err, rho_err = 0.0, 0.0
+    for k, c in enumerate(cells_np):
+        ix, iy = c % ncx, c // ncx - y0
+        fb = f[:, iy * r:(iy + 1) * r, ix * r:(ix + 1) * r].reshape(q, -1).sum(1) / (r * r)
+        g = O.grad_coeffs_packed(q, fb, 8)
+        want = np.concatenate([g["a2"], g["a3"], g["u"], [g["C"]]])
+        coef_err = max(coef_err, float(np.abs(v_g[k].numpy() - want).max()))
+        rho_err = max(rho_err, abs(float(rho_g[k]) / g["rho"] - 1))
+    out["lb2dsmc_coefficients"] = {"cells": int(len(cells_np)), "max_abs_err": coef_err,
+                                   "rho_max_rel_err": rho_err,
+                                   "gpu": "FP64 raw moments and centring identities",
+                                   "oracle": "FP64 definition, left-to-right sums"}
+    # (2) one step from the GPU's own state
+    c1 = rows * ncx
+    h.sync()
+    cnt = h.counts()[:c1].cpu().numpy()
+    arr = h.particle_arrays()
+    mask = torch.arange(d["bin"], device=h.device)[None, :] < h.counts()[:c1, None]
+    pk = {k: arr[k][:c1][mask].double().cpu().numpy() for k in ("x", "y", "vx", "vy", "vz")}
+    cs = np.zeros(c1 + 1, np.int64)
+    cs[1:] = np.cumsum(cnt)
+    ctrl = h.ctrl().cpu().numpy()
+    state = {"crmax": h.crmax()[:c1].double().cpu().numpy(), "rem": h.rem()[:c1].double().cpu().numpy(),
+             "nbar": h.nbar_sum()[:c1].cpu().numpy().view(np.uint32).copy(),
+             "acc": h.acc()[:c1].cpu().numpy().copy(),
+             "f": h.f()[:, :rows * r].double().cpu().numpy().copy()}
+    h.dsmc_step(1)
+    h.lbm_step(1)
+    h.sync()
+    o, wcfg = window_oracle(cfg, rows, 8)
+    o.set_particles(pk["x"], pk["y"], pk["vx"], pk["vy"], pk["vz"], cs.astype(np.uint32))
+    o.set(O.A_CRMAX, state["crmax"])
+    o.set(O.A_REM, state["rem"])
+    o.set(O.A_NBAR_SUM, state["nbar"])
+    o.set(O.A_ACC, state["acc"].reshape(-1))
+    o.set_scalars(int(ctrl[B.CTRL_STEP]), int(ctrl[B.CTRL_NSAMPLES]))
+    o.set_f(np.ascontiguousarray(state["f"]))
+    o.dsmc_step(1)
+    o.lbm_step(1)
+    lo, hi = 5 * ncx, (rows - 5) * ncx  # rows at least 5 cells from the window's ends
+    gcnt = h.counts()[lo:hi].cpu().numpy()
+    ocs = o.get(O.A_CELL_START).astype(np.int64)
+    ocnt = np.diff(ocs)[lo:hi]
+    same = gcnt == ocnt
+    arr = h.particle_arrays()
+    gmask = torch.arange(d["bin"], device=h.device)[None, :] < h.counts()[lo:hi, None]
+    gp = {k: arr[k][lo:hi][gmask].double().cpu().numpy() for k in ("x", "y", "vx", "vy", "vz")}
+    op = o.particles()
+    gcs = np.zeros(hi - lo + 1, np.int64)
+    gcs[1:] = np.cumsum(gcnt)
+    within, total, worst = 0, 0, 0.0
+    dacc_err = 0.0
+    ga_acc = h.acc()[lo:hi].cpu().numpy()
+    oa_acc = o.acc()[lo:hi]
+    base_acc = state["acc"][lo:hi]
+    for j in np.nonzero(same)[0]:
+        n = gcnt[j]
+        if n == 0:
+            continue
+        a, b = gcs[j], ocs[lo + j]
+        err = np.zeros(n)
+        for k in ("x", "y", "vx", "vy", "vz"):
+            gv, ov = gp[k][a:a + n], op[k][b:b + n]
+            err = np.maximum(err, np.abs(gv - ov) / (1 + np.abs(ov)))
+        total += n
+        ok = err <= 1e-5
+        within += int(ok.sum())
+        if ok.all():
+            worst = max(worst, float(err.max()))
+            inc_g, inc_o = ga_acc[j] - base_acc[j], oa_acc[j] - base_acc[j]
+            dacc_err = max(dacc_err, float(np.abs(inc_g - inc_o).max() / n))
+    out["dsmc_step"] = {
+        "cells": int(hi - lo), "cells_same_count_frac": float(same.mean()),
+        "particles_within_1e-5_frac": within / max(1, total),
+        "max_rel_err_of_cells_within_1e-5": worst,
+        "moment_sums_step_max_err_per_particle": dacc_err,
+        "note": "FP32 GPU step against the FP64 oracle from the same (FP32) state"}
+    rl, rh = 3, rows * r - 3  # node rows the window's periodic ends do not reach in one step
+    gf = h.f()[:, rl:rh].double().cpu().numpy()
+    of = o.f()[:, rl:rh]
+    rho = of.sum(0)
+    out["lbm_step"] = {"node_rows": int(rh - rl),
+                       "max_err_over_w_rho": float((np.abs(gf - of) / (w[:, None, None] * rho)).max()),
+                       "rho_max_rel_err": float(np.abs(gf.sum(0) / rho - 1).max())}
+    return out
 
 
 def run_ensemble(args):
@@ -331,13 +518,15 @@ def run_adjoint(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(W.WORKLOADS))
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--profile-kernel", default=None)
-    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--cpu-budget", type=float, default=16.0)
+    ap.add_argument("--no-cpu", action="store_true",
+                    help="skip the FP64 oracle error sample and the CPU baseline")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="run this many hybrid steps with direct launches and exit (for ncu)")
     ap.add_argument("--adjoint", action="store_true",
@@ -363,24 +552,28 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        from oracle import build as OB
-        OB.build()
-        per_step_budget = max(5.0, args.cpu_budget)
-        rate, done = run_oracle(cfg, args.warmup + args.steps, per_step_budget * 4)
         d = __import__("oracle.oracle", fromlist=["x"]).derive(cfg)
         n = d["ncells"] * cfg["ppc"]
+        procs = host_cores()
+        # one step = one hybrid step of a window of the channel in every process
+        rate, win_rate, done = run_oracle_windows(cfg, procs, nsteps=args.steps,
+                                                  nwarm=args.warmup)
+        sample = ("%d processes, each an FP64 oracle window of the channel's first %d cell rows "
+                  "(%d particles, %d LB node rows, its own 4-row coupling strip); %d timed hybrid "
+                  "steps per process after %d warm-up steps; rate scaled to the whole channel by "
+                  "rows" % (procs, WINDOW_ROWS, WINDOW_ROWS * cfg["ncx"] * cfg["ppc"],
+                            WINDOW_ROWS * cfg["lb_ratio"], done[0], args.warmup))
         line = {
             "impl": "reference", "metric": METRIC, "value": rate, "unit": "hybrid steps/s",
-            "n_gpus": args.gpus, "steps": done, "warmup": 0,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 / rate, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if cfg["real_bytes"] == 4 else "f64",
-            "precision": "oracle: DSMC state and arithmetic in the state precision, LB "
-                         "collision and moment sums in FP64",
+            "vs_baseline": None, "dtype": "f64",
+            "precision": "oracle: FP64 state and arithmetic throughout",
             "data": "synthetic",
             "config": {"workload": args.workload, "particles": n, "lb_nodes": d["nnodes"]},
-            "cpu_baseline": {"value": rate, "unit": "hybrid steps/s", "cores": 1,
-                             "kind": "oracle",
-                             "sample": "%d hybrid steps of the full workload (time-bounded)" % done},
+            "dsmc_particle_updates_per_s": rate * n,
+            "cpu_baseline": {"value": rate, "unit": "hybrid steps/s", "cores": procs,
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": rate, "unit": "hybrid steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
         }
@@ -415,62 +608,79 @@ def main():
     def step():
         h.hybrid_step(nodes, cells, nsteps=1, use_graph=use_graph, order_inputs=False)
 
+    def run(n, graph=use_graph):
+        # n hybrid steps in one call: the DSMC passes fused across steps
+        h.hybrid_step(nodes, cells, nsteps=n, use_graph=graph, order_inputs=False)
+
     if args.profile_steps:
-        for _ in range(args.profile_steps):
-            h.hybrid_step(nodes, cells, nsteps=1, use_graph=False, order_inputs=False)
+        run(args.profile_steps, graph=False)
         rc, bits = h.sync_status()
         print(json.dumps({"profile_steps": args.profile_steps, "status": rc, "bits": bits}))
         h.close()
         return
 
-    # warm-up, and pick the dominant kernel by timing each one over a few steps
+    # warm-up (the first fused call of args.steps captures its graph), then every kernel's
+    # average time per launch over fused runs of direct launches with CUDA events on the
+    # library's stream (kernel timing is taken apart from the timed region)
     for _ in range(args.warmup):
         step()
+    run(args.steps)
     h.sync()
-    kernel_ms = {}
+    kernel_ms, kernel_launches = {}, {}
+    prof_steps = 6
     for name, kid in B.KERNELS.items():
         h.profile(kid)
         h.profile_harvest()
         ms0, n0 = h.profile_read()
-        for _ in range(3):
-            with torch.cuda.stream(stream):
-                flush.zero_()
-            step()
-            h.profile_harvest()
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        run(prof_steps, graph=False)
+        h.profile_harvest()
         ms1, n1 = h.profile_read()
-        kernel_ms[name] = (ms1 - ms0) / max(1, n1 - n0)
-    dominant = args.profile_kernel or max(kernel_ms, key=kernel_ms.get)
-    h.profile(B.KERNELS[dominant])
-    h.profile_harvest()
-    kms0, kn0 = h.profile_read()
+        if n1 > n0:
+            kernel_ms[name] = (ms1 - ms0) / (n1 - n0)
+            kernel_launches[name] = (n1 - n0) / prof_steps
+    h.profile(-1)
+    # the dominant kernel of a step of the timed (fused) run
+    per_step = {k: kernel_ms[k] for k in ("fused", "lbm", "dsmc2lb", "lb2dsmc") if k in kernel_ms}
+    dominant = args.profile_kernel or max(per_step, key=per_step.get)
+    dom_ms = kernel_ms[dominant]
 
-    # timed region
+    # single steps (one call per step, L2 flushed before each), for comparison
+    single_ms = []
+    for _ in range(min(args.steps, 20)):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        step()
+        a1.record(stream)
+        single_ms.append((a0, a1))
+    torch.cuda.synchronize(dev)
+    single_ms = sum(x.elapsed_time(y) for x, y in single_ms) / len(single_ms)
+
+    # timed region: args.steps hybrid steps in one call, inputs larger than L2 (and the L2
+    # flushed before the region)
     clock_lines, stop = [], threading.Event()
     th = threading.Thread(target=sample_clocks, args=(stop, clock_lines), daemon=True)
     th.start()
     time.sleep(0.3)
+    with torch.cuda.stream(stream):
+        flush.zero_()
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    for k in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.zero_()
-        starts[k].record(stream)
-        step()
-        ends[k].record(stream)
-        h.profile_harvest()
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    run(args.steps)
+    t_end.record(stream)
     torch.cuda.synchronize(dev)
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
+    total_ms = t_start.elapsed_time(t_end)
     if dist:
         total_ms = max_over_ranks(dist, total_ms, dev)
         dist.barrier()
     stop.set()
     th.join(timeout=5)
-    kms1, kn1 = h.profile_read()
-    dom_ms = (kms1 - kms0) / max(1, kn1 - kn0)
     rc, bits = h.sync_status()
 
     # end to end through the C-ABI call with host buffers (hyb_hybrid_step_host): every step
@@ -519,8 +729,15 @@ def main():
 
     value = world * args.steps / (total_ms / 1e3)
     peak, peak_kind = measured_peak_hbm()
-    alg = kernel_algorithmic_bytes(dominant, cfg, d, n_particles, len(nodes_np), len(cells_np))
+    dsmc_b, lbm_b = method_bytes(cfg, d)
+    units = {"move": n_particles * dsmc_b, "collide": n_particles * dsmc_b,
+             "fused": n_particles * dsmc_b, "lbm": d["nnodes"] * lbm_b}
+    alg_design = kernel_algorithmic_bytes(dominant, cfg, d, n_particles, len(nodes_np), len(cells_np))
+    alg = units.get(dominant, alg_design)
     achieved = alg / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else None
+    step_bytes = n_particles * dsmc_b + d["nnodes"] * lbm_b
+    step_ms = total_ms / args.steps / world
+    dsmc_ms = kernel_ms.get("fused", 0.0)
     line = {
         "metric": METRIC, "value": value, "unit": "hybrid steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -529,18 +746,40 @@ def main():
         "config": {"workload": args.workload, "particles": n_particles, "lb_nodes": d["nnodes"],
                    "lattice": "D3Q%d" % d["q"], "coupling_nodes": len(nodes_np),
                    "coupling_cells": len(cells_np), "graph": use_graph,
-                   "l2": "flushed before every timed step (512 MB write)",
+                   "kn": [cfg["kn"], cfg.get("kn_end", cfg["kn"])] if cfg.get("kn_profile") else cfg["kn"],
+                   "l2": "inputs larger than L2, and flushed before every timed step (512 MB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "dsmc_particle_updates_per_s": value * n_particles,
         "lbm_mlups": value * d["nnodes"] / 1e6,
         "roofline": {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak if achieved else None,
-                     "algorithmic_bytes_per_launch": alg, "ms_per_launch": dom_ms,
-                     "traffic": traffic_record(dominant, args.workload)},
+                     "algorithmic_bytes_per_launch": alg,
+                     "bytes_basis": "method bytes per unit (%.1f B per particle-update, %d B per "
+                                    "node-update) x units per launch" % (dsmc_b, lbm_b)
+                                    if dominant in units else "design bytes (no method figure)",
+                     "ms_per_launch": dom_ms,
+                     "traffic": traffic_record(dominant, args.workload),
+                     "design_bytes_per_launch": alg_design,
+                     "design_frac": (alg_design / (dom_ms / 1e3) / 1e9 / peak) if dom_ms > 0 else None},
+        "roofline_step": {"bytes_per_step": step_bytes, "achieved": step_bytes / (step_ms / 1e3) / 1e9,
+                          "peak": peak, "unit": "GB/s",
+                          "frac": step_bytes / (step_ms / 1e3) / 1e9 / peak,
+                          "steps_per_s_at_peak": peak * 1e9 / step_bytes,
+                          "dsmc_frac": (n_particles * dsmc_b) / (dsmc_ms / 1e3) / 1e9 / peak
+                          if dsmc_ms > 0 else None,
+                          "lbm_frac": (d["nnodes"] * lbm_b) / (kernel_ms["lbm"] / 1e3) / 1e9 / peak
+                          if kernel_ms.get("lbm") else None,
+                          "note": "per-kernel times are CUDA-event brackets taken apart from the "
+                                  "timed steps (upper bounds: they break the overlap of "
+                                  "programmatic dependent launch)"},
         "kernel_ms": kernel_ms,
+        "kernel_launches_per_step": kernel_launches,
+        "single_step": {"ms_per_step": single_ms, "value": world * 1e3 / single_ms,
+                        "note": "one call per hybrid step (move and collide as two passes), "
+                                "L2 flushed before each"},
         "clocks": summarize_clocks(clock_lines),
-        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+        "gpu_launches": LAUNCHES_PER_STEP * args.steps + 1,
         "status": {"code": rc, "bits": bits},
         "e2e": {"value": world * e2e_steps / e2e_s, "unit": "hybrid steps/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -549,15 +788,23 @@ def main():
                 "synchronous_value": world * e2e_steps / e2e_sync_s,
                 "status_bits_seen": seen["bad"]},
     }
-    if rank == 0 and world == 1:
-        from oracle import build as OB
-        OB.build()
-        rate, done = run_oracle(cfg, 10 ** 9, args.cpu_budget)
-        line["cpu_baseline"] = {"value": rate, "unit": "hybrid steps/s", "cores": 1,
-                                "kind": "oracle",
-                                "sample": "%d hybrid steps of the full workload, FP%d oracle, "
-                                          "single thread, %.0f s budget"
-                                          % (done, 8 * cfg["real_bytes"], args.cpu_budget)}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        # the FP64 oracle: its error against the GPU at this size, then its speed on windows
+        # of the channel, single-threaded and in one process per host core
+        line["error_vs_fp64_oracle"] = fp64_error_sample(h, cfg, B, cells_np)
+        rate1, win1, done1 = run_oracle_windows(cfg, 1, budget_s=args.cpu_budget / 2)
+        procs = host_cores()
+        rate_n, win_n, done_n = run_oracle_windows(cfg, procs, budget_s=args.cpu_budget / 2)
+        line["cpu_baseline"] = {
+            "value": rate_n, "unit": "hybrid steps/s", "cores": procs, "kind": "oracle",
+            "sample": "FP64 oracle windows of the channel's first %d cell rows (%d particles, "
+                      "its own 4-row coupling strip), one process per core, %d hybrid steps each "
+                      "in %.0f s; rate scaled to the whole channel by rows"
+                      % (WINDOW_ROWS, WINDOW_ROWS * cfg["ncx"] * cfg["ppc"], min(done_n),
+                         args.cpu_budget / 2),
+            "single_thread": {"value": rate1, "cores": 1,
+                              "particle_updates_per_s": win1 * WINDOW_ROWS * cfg["ncx"] * cfg["ppc"]},
+            "particle_updates_per_s": win_n * WINDOW_ROWS * cfg["ncx"] * cfg["ppc"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     h.close()

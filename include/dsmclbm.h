@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define HYB_ABI_VERSION 5u
+#define HYB_ABI_VERSION 6u
 
 typedef enum {
     HYB_OK = 0,
@@ -110,7 +110,25 @@ typedef struct {
                                one cell and one LB layer; >= 2 for full 3D, with particle z
                                positions, ncz * lb_ratio LB layers, cells (iz ncy + iy) ncx + ix
                                and nodes (z ny + y) nx + x. Not with a batch. */
-    int32_t pad1;
+    int32_t accum_mode;     /* moment sums: 0 = FP64 cumulative sums (one FP64 addition per sum
+                               per step, of that step's cell sum); 1 = Kahan-compensated FP32,
+                               not built: HYB_EINVAL */
+    int32_t ncy_global;     /* 0: the context holds the whole channel. > 0: the context is one
+                               streamwise slab of a channel of ncy_global DSMC rows (periodic):
+                               the rows [y0, y0 + ncy) (ncy >= 4), with the channel's ncx, ncz,
+                               ppc, Kn, seed and lattice. Cell ids in the random streams and the
+                               stable-order keys, and particle y positions, are the channel's, so
+                               slabs stepped with the exchange below give the whole channel's
+                               results bit for bit. The LB lattice of a slab has yh ghost rows
+                               below and above its ncy * lb_ratio rows (hyb_derived.yh), filled
+                               from the neighbours by lbm_halo_pack / lbm_halo_unpack before each
+                               LB step; particles leaving the slab go to its two send buffers
+                               (hyb_layout.xsend: 0 towards lower rows, 1 towards higher), which
+                               the caller copies into the neighbours' receive buffers (xrecv: 0
+                               from the slab below, 1 from the slab above) before dsmc_merge.
+                               A slab is advanced with dsmc_move, dsmc_merge, dsmc_collide and
+                               lbm_step; dsmc_step and hyb_hybrid_step return HYB_EINVAL. */
+    int32_t y0;             /* first global DSMC row of the slab (ncy_global > 0) */
 } hyb_params;
 
 /* Constants derived from hyb_params (hyb_derive). */
@@ -131,6 +149,11 @@ typedef struct {
     int32_t pad;
     int64_t nz;       /* LB layers along z: 1 for the slab, ncz * lb_ratio in 3D */
     int64_t ncz;      /* DSMC cells along z: 1 for the slab */
+    int64_t yh;       /* LB ghost rows below and above the rows of a streamwise slab context (the
+                         lattice's largest speed: 3 for D3Q39, 1 for D3Q19); 0 otherwise. The
+                         lattice then has ny = ncy lb_ratio + 2 yh rows and node row y holds the
+                         slab's LB row y - yh */
+    int64_t xcap;     /* particles each exchange buffer of a slab holds (0 otherwise) */
 } hyb_derived;
 
 /* Byte offsets of the arrays inside the caller's arena (hyb_layout_compute). Arrays marked
@@ -138,10 +161,12 @@ typedef struct {
  * float or double per real_bytes. Particles are binned by cell: cell c owns slots
  * [c * bin, (c + 1) * bin) of every particle array and count[half][c] of them are in use,
  * in the order of the step's stable sort (after dsmc_step) or of their generation (after
- * dsmc_init and map_lbm_to_dsmc).
- *   x, y          Real[ncells*bin]  positions in cell units (x across, y streamwise); [2]
- *   vx, vy, vz    Real[ncells*bin]  velocities in c_th units; [2]
- *   tag           u32[ncells*bin]   origin slot of each moved particle (stable-order key)
+ * dsmc_init and map_lbm_to_dsmc); the other half's counts are zero between calls.
+ *   part          Real[ncells*bin][8]  particle records: x, y (positions in cell units, x
+ *                                   across, y streamwise), vx, vy, vz (velocities in c_th
+ *                                   units), z (3D only; else 0), the bits of a u32 stable-order
+ *                                   key (the particle's origin slot c * bin + rank, written by
+ *                                   the move; scratch within a step) and one unused value; [2]
  *   count         u32[ncells]       particles per cell; [2]
  *   crmax         Real[ncells]      (sigma_T c_r)_max / sigma_T per cell
  *   rem           Real[ncells]      NTC fractional candidate carried between steps
@@ -152,25 +177,26 @@ typedef struct {
  *   ctrl          u32[16]           [0] status bits, [1] particles in use, [2] DSMC steps
  *                                   taken, [3] moment samples taken, [4]..[15] scratch
  *   counters      u64[16]           event counters, HYB_C_*
- *   map_scratch                     LB2DSMC per-cell records
- *   moved         Real[ncells*bin][8]  the particles of the DSMC step in progress after the
- *                                   move, by origin slot: x, y, vx, vy, vz, z (3D only) and
- *                                   2 unused (one record per 32-byte sector in FP32); scratch
- *                                   between the two kernels of a step
- *   z             Real[ncells*bin]  z positions in cell units (3D only); [2] */
+ *   map_scratch                     LB2DSMC per-cell Grad records (FP64: rho, new count,
+ *                                   a2[6], a3[10], u[3], C; 176 bytes per listed cell)
+ *   coupled       u8[ncells]        coupling cells of a multi-step hybrid call in progress
+ *                                   (zero between calls)
+ */
 typedef struct {
     uint64_t total_bytes;
     int64_t capacity, ncells, nnodes;
     int32_t q, real_bytes, bin, pad;
-    uint64_t x[2], y[2], vx[2], vy[2], vz[2];
-    uint64_t tag, count[2];
+    uint64_t part[2], count[2];
     uint64_t crmax, rem, nbar_sum, acc;
     uint64_t f[2];
     uint64_t ctrl, counters, map_scratch;
-    uint64_t moved;
+    uint64_t coupled;
     uint64_t coll_cell;     /* Real[ncells]: per-cell NTC factor (kn_profile = 1; size 0 otherwise) */
     uint64_t tau_node;      /* Real[nnodes]: per-node relaxation time (kn_profile = 1) */
-    uint64_t z[2];          /* Real[ncells*bin]: particle z positions (3D only; size 0 else) */
+    /* exchange buffers of a streamwise slab (size 0 otherwise), xbytes each: a u32 count, then
+     * xcap particle records (Real[8], as part) from byte 256, then xcap u32 channel cell ids
+     * (the particle's new cell) */
+    uint64_t xsend[2], xrecv[2], xbytes;
 } hyb_layout;
 
 typedef struct hyb_ctx hyb_ctx; /* opaque, owned by the library */
@@ -195,9 +221,45 @@ hyb_status dsmc_init(const hyb_params* p, void* arena, uint64_t arena_bytes, voi
 /* `nsteps` DSMC steps (Sec. 5; the NTC order move -> index -> collide -> sample): each
  * particle is moved and binned into its new cell of the other half, then every cell puts
  * its particles in stable order (by origin cell and rank), collides them and adds their
- * moment sums. Draws are keyed by (seed; cell, step, purpose, index), so results do not
- * depend on the launch shape. */
+ * moment sums. With nsteps >= 2 the collide of each step and the move of the next run as
+ * one pass over the particles (the same results). Draws are keyed by (seed; cell, step,
+ * purpose, index), so results do not depend on the launch shape. */
 hyb_status dsmc_step(hyb_ctx* ctx, int32_t nsteps);
+
+/* The passes of one DSMC step, for a streamwise slab (hyb_params.ncy_global > 0; the multi-GPU
+ * decomposition of the channel into streamwise slabs) or any context. In this order:
+ *   dsmc_move     moves and bins the particles (as dsmc_step); a slab's particles whose new
+ *                 cell lies outside its rows go to its send buffers (xsend[0]: lower rows,
+ *                 xsend[1]: higher rows, across the periodic end included) with their
+ *                 stable-order keys and channel cells;
+ *                 -- the caller then copies each neighbour's send buffer into this slab's
+ *                    receive buffer (xrecv[0] <- the slab below's xsend[1], xrecv[1] <- the
+ *                    slab above's xsend[0]; hyb_layout.xbytes each, on this context's stream or
+ *                    ordered before dsmc_merge), e.g. by NCCL send/recv between ranks --
+ *   dsmc_merge    appends the received particles to their cells (a no-op for a context that
+ *                 holds the whole channel) and clears the slab's send counts;
+ *   dsmc_collide  sorts, collides and samples every cell (as dsmc_step) and flips the
+ *                 particle half.
+ * dsmc_move + dsmc_merge + dsmc_collide of every slab give the whole channel's dsmc_step(1) bit
+ * for bit. A call out of this order returns HYB_ESTATE; a received particle whose cell is not
+ * the slab's raises HYB_ST_BAD_INPUT, a full send buffer or bin HYB_ST_CAPACITY. */
+hyb_status dsmc_move(hyb_ctx* ctx);
+hyb_status dsmc_merge(hyb_ctx* ctx);
+hyb_status dsmc_collide(hyb_ctx* ctx);
+
+/* LB ghost rows of a streamwise slab (the lattice's yh rows below and above the slab's rows,
+ * hyb_derived.yh). Before each lbm_step of the slabs (and after any map_dsmc_to_lbm), every
+ * slab packs, for each side (0: its lower boundary, 1: its upper one), the populations that
+ * the neighbour on that side pulls across it (e_y < 0 at the lower boundary, e_y > 0 at the
+ * upper one, from the |e_y| rows next to the boundary: only the outgoing populations), and
+ * unpacks the neighbour's packed side into its own ghost rows (side 0: the buffer packed by the
+ * slab below at its side 1; side 1: by the slab above at its side 0). lbm_halo_size gives the
+ * values (Real) of one side's buffer: nz nx times the sum of the positive e_y (18 rows for
+ * D3Q39, 5 for D3Q19). dev_buf is caller-owned device memory. HYB_EINVAL for a context that
+ * holds the whole channel. */
+hyb_status lbm_halo_size(const hyb_ctx* ctx, int64_t* values);
+hyb_status lbm_halo_pack(hyb_ctx* ctx, int32_t side, void* dev_buf);
+hyb_status lbm_halo_unpack(hyb_ctx* ctx, int32_t side, const void* dev_buf);
 
 /* `nsteps` LB stream-collide steps (Sec. 2, Sec. 3.1). */
 hyb_status lbm_step(hyb_ctx* ctx, int32_t nsteps);
@@ -277,9 +339,14 @@ hyb_status lbm_adjoint_step(hyb_ctx* ctx, const void* f, const void* lam_next, v
                             void* grad_tau, void* wall);
 
 /* One or more hybrid steps: dsmc_step(1), map_dsmc_to_lbm, lbm_step(1), map_lbm_to_dsmc.
- * n_nodes or n_cells may be 0 to skip a mapping. With use_graph != 0 each step is replayed
- * from a CUDA graph captured on first use (one per ping-pong parity; recaptured if the
- * arguments change); the stream must not be the legacy default stream. */
+ * n_nodes or n_cells may be 0 to skip a mapping. With nsteps >= 2 the DSMC passes are fused
+ * across steps: the collide of a step and the move of the next are one pass over the
+ * particles, and LB2DSMC moves the particles it creates on at once; the results equal nsteps
+ * single hybrid steps bit for bit (the state is complete only when the call's work is done).
+ * With use_graph != 0 the work is replayed from a CUDA graph captured on first use (one step
+ * per ping-pong parity, or, for nsteps >= 2 without kernel timing, the whole call per step
+ * count and starting parities; recaptured if the arguments change); the stream must not be
+ * the legacy default stream. */
 hyb_status hyb_hybrid_step(hyb_ctx* ctx, const int32_t* dev_nodes, int32_t n_nodes,
                            const int32_t* dev_cells, int32_t n_cells, int32_t nsteps,
                            int32_t use_graph);
@@ -332,7 +399,8 @@ hyb_status hyb_sync_status(hyb_ctx* ctx, uint32_t* bits);
 hyb_status hyb_read_counters(hyb_ctx* ctx, uint64_t* out);
 
 /* Kernel timing on the context's stream: after hyb_profile(ctx, k) every launch of kernel k
- * (0 move, 1 collide, 2 lbm, 3 dsmc2lb, 4 lb2dsmc; -1 off) is bracketed by CUDA events. hyb_profile_harvest synchronises
+ * (0 move, 1 collide, 2 lbm, 3 dsmc2lb, 4 lb2dsmc, 5 the fused collide-and-move pass of
+ * multi-step calls; -1 off) is bracketed by CUDA events. hyb_profile_harvest synchronises
  * and adds the elapsed times of the launches since the last harvest; call it after every
  * hybrid step when graphs are used. hyb_profile_read returns the totals. */
 hyb_status hyb_profile(hyb_ctx* ctx, int32_t kernel);

@@ -47,7 +47,9 @@ struct Params {
     int32_t pad0;
     double kn_end;         // Kn at y = ncy / 2 when kn_profile = 1
     int32_t ncz;           // DSMC cells along z (periodic); 0 or 1: the quasi-2D slab
-    int32_t pad1;
+    int32_t accum_mode;    // moment sums: 0 FP64
+    int32_t ncy_global;    // > 0: a streamwise slab of a channel of ncy_global rows
+    int32_t y0;            // its first row in the channel
 };
 
 // Derived constants. Field order is a binary interface with oracle.py.
@@ -67,6 +69,8 @@ struct Derived {
     int32_t pad;
     int64_t nz;    // LB layers along z: 1 for the slab, ncz * lb_ratio in 3D
     int64_t ncz;   // DSMC cells along z: 1 for the slab
+    int64_t yh;    // LB ghost rows below and above a streamwise slab's rows (0 otherwise)
+    int64_t xcap;  // particles per exchange buffer of the library's slab layout
 };
 
 constexpr double kPi = 3.14159265358979323846;
@@ -92,11 +96,14 @@ inline Derived derive(const Params& p) {
     d.ncz = p.ncz >= 2 ? p.ncz : 1;
     d.ncells = (int64_t)p.ncx * p.ncy * d.ncz;
     d.nx = (int64_t)p.ncx * p.lb_ratio;
-    d.ny = (int64_t)p.ncy * p.lb_ratio;
+    // a streamwise slab's lattice carries yh ghost rows below and above its own rows
+    d.yh = p.ncy_global > 0 ? (p.lattice == 39 ? 3 : 1) : 0;
+    d.ny = (int64_t)p.ncy * p.lb_ratio + 2 * d.yh;
     d.nz = p.ncz >= 2 ? d.ncz * p.lb_ratio : 1;
     d.nnodes = d.nx * d.ny * d.nz;
     d.bin = ((int32_t)std::ceil(p.capacity_factor * (double)p.ppc) + 31) / 32 * 32;
     d.capacity = d.ncells * (int64_t)d.bin;
+    d.xcap = p.ncy_global > 0 ? (int64_t)p.ncx * d.ncz * d.bin : 0;
     d.q = p.lattice;
     d.order = (p.lattice == 39) ? 3 : 2;
     return d;

@@ -43,7 +43,9 @@ class Params(ctypes.Structure):
         ("pad0", ctypes.c_int32),
         ("kn_end", ctypes.c_double),
         ("ncz", ctypes.c_int32),
-        ("pad1", ctypes.c_int32),
+        ("accum_mode", ctypes.c_int32),
+        ("ncy_global", ctypes.c_int32),
+        ("y0", ctypes.c_int32),
     ]
 
 
@@ -69,6 +71,8 @@ class Derived(ctypes.Structure):
         ("pad", ctypes.c_int32),
         ("nz", ctypes.c_int64),
         ("ncz", ctypes.c_int64),
+        ("yh", ctypes.c_int64),
+        ("xcap", ctypes.c_int64),
     ]
 
 

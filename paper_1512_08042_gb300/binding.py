@@ -11,14 +11,14 @@ import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "libdsmclbm.so")
-ABI_VERSION = 5
+ABI_VERSION = 6
 
 HYB_OK, HYB_EINVAL, HYB_ENOMEM, HYB_ECUDA, HYB_ECAPACITY, HYB_ETIMEOUT, HYB_ESAMPLING, HYB_ESTATE = range(8)
 ST_CAPACITY, ST_BOUNCE_CAP, ST_SCATTER_CAP, ST_SAMPLING_CAP, ST_CELL_OVERFLOW, ST_BAD_INPUT = (
     1, 2, 4, 8, 16, 32)
 COUNTER_NAMES = ["wall_hits", "candidates", "collisions", "created", "deleted",
                  "l2d_attempts", "envelope", "bounce_cap"]
-KERNELS = {"move": 0, "collide": 1, "lbm": 2, "dsmc2lb": 3, "lb2dsmc": 4}
+KERNELS = {"move": 0, "collide": 1, "lbm": 2, "dsmc2lb": 3, "lb2dsmc": 4, "fused": 5}
 CTRL_STATUS, CTRL_NTOT, CTRL_STEP, CTRL_NSAMPLES = 0, 1, 2, 3
 NOALLOC_MAX_CELLS = 4096
 
@@ -32,7 +32,8 @@ class HybParams(ctypes.Structure):
                 ("seed", _u64), ("kn", _dbl), ("ma", _dbl), ("crmax_init", _dbl),
                 ("capacity_factor", _dbl), ("T_K", _dbl), ("mass_kg", _dbl),
                 ("lb_collision", _i32), ("d2l_mode", _i32), ("kn_profile", _i32),
-                ("pad0", _i32), ("kn_end", _dbl), ("ncz", _i32), ("pad1", _i32)]
+                ("pad0", _i32), ("kn_end", _dbl), ("ncz", _i32), ("accum_mode", _i32),
+                ("ncy_global", _i32), ("y0", _i32)]
 
 
 class HybDerived(ctypes.Structure):
@@ -40,21 +41,22 @@ class HybDerived(ctypes.Structure):
                 ("lam", _dbl), ("coll_dt", _dbl), ("g_step", _dbl), ("c_th_ms", _dbl),
                 ("ncells", _i64), ("nx", _i64), ("ny", _i64), ("nnodes", _i64),
                 ("capacity", _i64), ("q", _i32), ("order", _i32), ("bin", _i32), ("pad", _i32),
-                ("nz", _i64), ("ncz", _i64)]
+                ("nz", _i64), ("ncz", _i64), ("yh", _i64), ("xcap", _i64)]
 
 
 class HybLayout(ctypes.Structure):
     _fields_ = [("total_bytes", _u64), ("capacity", _i64), ("ncells", _i64), ("nnodes", _i64),
                 ("q", _i32), ("real_bytes", _i32), ("bin", _i32), ("pad", _i32),
-                ("x", _u64 * 2), ("y", _u64 * 2), ("vx", _u64 * 2), ("vy", _u64 * 2),
-                ("vz", _u64 * 2), ("tag", _u64), ("count", _u64 * 2), ("crmax", _u64),
+                ("part", _u64 * 2), ("count", _u64 * 2), ("crmax", _u64),
                 ("rem", _u64), ("nbar_sum", _u64), ("acc", _u64), ("f", _u64 * 2),
-                ("ctrl", _u64), ("counters", _u64), ("map_scratch", _u64), ("moved", _u64),
-                ("coll_cell", _u64), ("tau_node", _u64), ("z", _u64 * 2)]
+                ("ctrl", _u64), ("counters", _u64), ("map_scratch", _u64), ("coupled", _u64),
+                ("coll_cell", _u64), ("tau_node", _u64), ("xsend", _u64 * 2),
+                ("xrecv", _u64 * 2), ("xbytes", _u64)]
 
 
 EXPORTS = ["hyb_derive", "hyb_layout_compute", "hyb_lattice", "hyb_status_string", "dsmc_init",
-           "dsmc_step", "lbm_step", "sample_moments", "map_dsmc_to_lbm", "map_lbm_to_dsmc",
+           "dsmc_step", "dsmc_move", "dsmc_merge", "dsmc_collide", "lbm_halo_size", "lbm_halo_pack",
+           "lbm_halo_unpack", "lbm_step", "sample_moments", "map_dsmc_to_lbm", "map_lbm_to_dsmc",
            "map_lbm_to_dsmc_noalloc", "map_dsmc_to_lbm_adjoint", "lbm_step_nodes", "lbm_interface_loss", "lbm_adjoint_step",
            "hyb_hybrid_step", "hyb_hybrid_step_host", "hyb_host_wait", "hyb_batch_layout", "hyb_batch_init", "hyb_batch_replica",
            "hyb_batch_hybrid_step", "hyb_batch_set_blocks", "hyb_batch_tune",
@@ -95,6 +97,12 @@ def lib():
     L.hyb_status_string.restype = ctypes.c_char_p
     L.dsmc_init.argtypes = [P(HybParams), _vp, _u64, _vp, P(_vp)]
     L.dsmc_step.argtypes = [_vp, _i32]
+    L.dsmc_move.argtypes = [_vp]
+    L.dsmc_merge.argtypes = [_vp]
+    L.dsmc_collide.argtypes = [_vp]
+    L.lbm_halo_size.argtypes = [_vp, P(_i64)]
+    L.lbm_halo_pack.argtypes = [_vp, _i32, _vp]
+    L.lbm_halo_unpack.argtypes = [_vp, _i32, _vp]
     L.lbm_step.argtypes = [_vp, _i32]
     L.sample_moments.argtypes = [_vp, _vp, _i32]
     L.map_dsmc_to_lbm.argtypes = [_vp, _vp, _i32]
@@ -246,6 +254,41 @@ class Hybrid:
 
     def lbm_step(self, n=1):
         _check(lib().lbm_step(self.ctx, n), self.ctx)
+
+    # -- a streamwise slab (cfg["ncy_global"] > 0): the split DSMC step and the LB ghost rows --
+    def dsmc_move(self):
+        _check(lib().dsmc_move(self.ctx), self.ctx)
+
+    def dsmc_merge(self):
+        _check(lib().dsmc_merge(self.ctx), self.ctx)
+
+    def dsmc_collide(self):
+        _check(lib().dsmc_collide(self.ctx), self.ctx)
+
+    def xfer(self, which, d):
+        """The exchange buffer `which` ("send" or "recv") of direction d as a uint8 view."""
+        off = (self.L.xsend if which == "send" else self.L.xrecv)[d]
+        return self.arena[int(off):int(off) + int(self.L.xbytes)]
+
+    def halo_size(self):
+        n = ctypes.c_int64()
+        _check(lib().lbm_halo_size(self.ctx, ctypes.byref(n)), self.ctx)
+        return n.value
+
+    def halo_pack(self, side, buf):
+        _check(lib().lbm_halo_pack(self.ctx, int(side), buf.data_ptr()), self.ctx)
+
+    def halo_unpack(self, side, buf):
+        self._inputs(buf)
+        _check(lib().lbm_halo_unpack(self.ctx, int(side), buf.data_ptr()), self.ctx)
+
+    def f_rows(self, half=None):
+        """The populations of the context's own LB rows (a slab's ghost rows left out)."""
+        yh = int(self.d["yh"])
+        f = self.f(half)
+        if yh == 0:
+            return f
+        return f[..., yh:f.shape[-2] - yh, :]
 
     def map_dsmc_to_lbm(self, nodes):
         self._inputs(nodes)
@@ -429,13 +472,17 @@ class Hybrid:
     def _pkeys(self):
         return ("x", "y", "z", "vx", "vy", "vz") if self.three_d() else ("x", "y", "vx", "vy", "vz")
 
+    # slots of a particle record (x, y, vx, vy, vz, z, key bits, unused)
+    REC = 8
+    SLOT = {"x": 0, "y": 1, "vx": 2, "vy": 3, "vz": 4, "z": 5}
+
     def particle_arrays(self, half=None):
-        """Binned particle arrays [ncells, bin] of the current (or given) half (views); z only
-        in 3D."""
+        """Binned particle arrays [ncells, bin] of the current (or given) half: strided views
+        of the particle records; z only in 3D."""
         h = self.current()[0] if half is None else half
         cap, b = self.L.capacity, self.L.bin
-        return {k: self._view(getattr(self.L, k)[h], cap, self.real).view(-1, b)
-                for k in self._pkeys()}
+        rec = self._view(self.L.part[h], cap * self.REC, self.real).view(cap, self.REC)
+        return {k: rec[:, self.SLOT[k]].view(-1, b) for k in self._pkeys()}
 
     def particles(self):
         """Current particles in cell order (copies, compacted from the bins)."""
@@ -454,6 +501,18 @@ class Hybrid:
 
     def acc(self):
         return self._view(self.L.acc, self.L.ncells * 20, self.torch.float64).view(-1, 20)
+
+    def grad_records(self, n):
+        """The Grad records the last map_lbm_to_dsmc wrote for its n listed cells, in list
+        order: (rho [n] f64, new counts [n] int64, v [n, 20] f64 = a2 (6), a3 (10), u (3), C),
+        the FP64 coefficients of Table 1 step 1 (copies)."""
+        torch = self.torch
+        self.sync()
+        raw = self._view(self.L.map_scratch, n * 176, torch.uint8).view(n, 176).cpu()
+        rho = raw[:, 0:8].contiguous().view(torch.float64).view(n)
+        nnew = raw[:, 8:12].contiguous().view(torch.int32).view(n).long()
+        v = raw[:, 16:176].contiguous().view(torch.float64).view(n, 20)
+        return rho, nnew, v
 
     def crmax(self):
         return self._view(self.L.crmax, self.L.ncells, self.real)
@@ -611,6 +670,107 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class SlabGroup:
+    """A channel of ncy DSMC rows cut into streamwise slabs (the multi-GPU decomposition), all
+    on one device: slab i is a Hybrid of the rows [y0_i, y0_i + rows_i) (periodic channel). A
+    step runs every slab's split DSMC step and LB step with the exchanges between them as
+    device copies on the slabs' shared stream: the particles that leave a slab (send buffers
+    into the neighbours' receive buffers), and before every LB step the outgoing populations
+    of the rows next to each boundary (packed by the library into staging, copied, unpacked
+    into the neighbours' ghost rows). Across ranks the same buffers go through
+    torch.distributed send/recv (see exchange_dist). The results equal the whole channel's."""
+
+    def __init__(self, cfg, cuts, device="cuda:0"):
+        import torch
+        self.torch = torch
+        self.cfg = dict(cfg)
+        ncy = cfg["ncy"]
+        bounds = [0] + list(cuts) + [ncy]
+        self.stream = torch.cuda.Stream(torch.device(device))
+        self.slabs = []
+        for i in range(len(bounds) - 1):
+            c = dict(cfg, ncy=bounds[i + 1] - bounds[i], ncy_global=ncy, y0=bounds[i])
+            self.slabs.append(Hybrid(c, device=device, stream=self.stream))
+        n = self.slabs[0].halo_size()
+        dt = self.slabs[0].real
+        self.halo = [[torch.empty(n, dtype=dt, device=device) for _ in range(2)] for _ in self.slabs]
+
+    def close(self):
+        for h in self.slabs:
+            h.close()
+
+    def _copy(self, dst, src):
+        with self.torch.cuda.stream(self.stream):
+            dst.copy_(src)
+
+    def exchange_particles(self):
+        k = len(self.slabs)
+        for i, h in enumerate(self.slabs):
+            below, above = self.slabs[(i - 1) % k], self.slabs[(i + 1) % k]
+            self._copy(h.xfer("recv", 0), below.xfer("send", 1))
+            self._copy(h.xfer("recv", 1), above.xfer("send", 0))
+
+    def exchange_halo(self):
+        k = len(self.slabs)
+        for i, h in enumerate(self.slabs):
+            h.halo_pack(0, self.halo[i][0])
+            h.halo_pack(1, self.halo[i][1])
+        for i, h in enumerate(self.slabs):
+            h.halo_unpack(0, self.halo[(i - 1) % k][1])
+            h.halo_unpack(1, self.halo[(i + 1) % k][0])
+
+    def dsmc_step(self):
+        for h in self.slabs:
+            h.dsmc_move()
+        self.exchange_particles()
+        for h in self.slabs:
+            h.dsmc_merge()
+        for h in self.slabs:
+            h.dsmc_collide()
+
+    def lbm_step(self):
+        self.exchange_halo()
+        for h in self.slabs:
+            h.lbm_step(1)
+
+    def hybrid_step(self, nodes=None, cells=None):
+        """One hybrid step; nodes[i] / cells[i]: slab i's coupling lists (device int32, the
+        slab's own node and cell indices, or None)."""
+        self.dsmc_step()
+        for i, h in enumerate(self.slabs):
+            if nodes is not None and nodes[i] is not None and nodes[i].numel():
+                h.map_dsmc_to_lbm(nodes[i])
+        self.lbm_step()
+        for i, h in enumerate(self.slabs):
+            if cells is not None and cells[i] is not None and cells[i].numel():
+                h.map_lbm_to_dsmc(cells[i])
+
+    def sync(self):
+        self.torch.cuda.synchronize()
+
+
+def exchange_dist(h, dist, rank, world, halo_bufs=None):
+    """The exchanges of a slab whose neighbours are other ranks (NCCL or gloo through
+    torch.distributed): the send buffers to the ranks below and above into this slab's
+    receive buffers, or, with halo_bufs = (packed side 0, packed side 1, received side 0,
+    received side 1), the packed populations. Blocking point-to-point pairs, ordered so that
+    even ranks send first."""
+    below, above = (rank - 1) % world, (rank + 1) % world
+    if halo_bufs is None:
+        pairs = [(h.xfer("send", 1), above, h.xfer("recv", 0), below),
+                 (h.xfer("send", 0), below, h.xfer("recv", 1), above)]
+    else:
+        p0, p1, r0, r1 = halo_bufs
+        pairs = [(p1, above, r0, below), (p0, below, r1, above)]
+    for sbuf, sto, rbuf, rfrom in pairs:
+        if rank % 2 == 0:
+            dist.send(sbuf, sto)
+            dist.recv(rbuf, rfrom)
+        else:
+            dist.recv(rbuf, rfrom)
+            dist.send(sbuf, sto)
 
 
 def interface_loss(h, g, tau, f0, nodes, targets, nsteps, ckpt_every=100):

@@ -26,7 +26,8 @@ UNITS = {
     "k_lbm.cu": ["-fmad=true"],
     "batch.cu": ["-fmad=false"],
 }
-HEADERS = [os.path.join(CSRC, "hyb_internal.cuh"), os.path.join(INCLUDE, "dsmclbm.h")]
+HEADERS = [os.path.join(CSRC, "hyb_internal.cuh"), os.path.join(CSRC, "dsmc_move.cuh"),
+           os.path.join(INCLUDE, "dsmclbm.h")]
 
 
 def nvcc():

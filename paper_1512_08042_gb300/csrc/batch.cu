@@ -78,9 +78,10 @@ uint64_t table_layout(int n, int real_bytes, hyb_batch* b) {
 }
 
 bool same_kind(const hyb_params* p, int n) {
-    for (int r = 1; r < n; ++r)
+    for (int r = 0; r < n; ++r)
         if (p[r].real_bytes != p[0].real_bytes || p[r].lattice != p[0].lattice ||
-            p[r].lb_collision != p[0].lb_collision || p[r].kn_profile != 0 || p[r].ncz >= 2)
+            p[r].lb_collision != p[0].lb_collision || p[r].kn_profile != 0 || p[r].ncz >= 2 ||
+            p[r].ncy_global != 0)
             return false;
     return true;
 }

@@ -24,7 +24,8 @@ enum CtrlWord {
     CTRL_NTOT = 1,
     CTRL_STEP = 2,
     CTRL_NSAMPLES = 3,
-    CTRL_TICKET = 4,   // blocks finished, for the last-block update of the move kernel
+    CTRL_TICKET = 4,   // blocks finished, for the last-block update of the collide kernel
+    CTRL_NACC = 5,     // particles counted by the collide pass in progress
     CTRL_WORDS = 16,
 };
 
@@ -45,7 +46,8 @@ enum KernelId {
     K_LBM = 2,
     K_D2L = 3,
     K_L2D = 4,
-    K_COUNT = 5,
+    K_FUSED = 5,  // the fused collide-and-move pass of multi-step calls
+    K_COUNT = 6,
 };
 
 // LB2DSMC per-cell record (map_scratch): the Grad record of one coupling cell (176 bytes),
@@ -59,16 +61,20 @@ struct GradRec {
 };
 enum : int { GR_A2 = 0, GR_A3 = 6, GR_U = 16, GR_C = 19 };
 
+// A particle is one record of kRec Real values: x, y, vx, vy, vz, z (3D only), its
+// stable-order key (the bits of a u32, written by the move) and one unused value, so that in
+// FP32 one record fills one 32-byte sector and a scattered write of a moved particle writes
+// whole sectors.
+constexpr int kRec = 8;
+enum RecSlot : int { RS_X = 0, RS_Y = 1, RS_VX = 2, RS_VY = 3, RS_VZ = 4, RS_Z = 5, RS_TAG = 6 };
+
 // Pointers into the arena.
 struct State {
-    void* pz[2];  // 3D only, else null
-    void* px[2];
-    void* py[2];
-    void* pvx[2];
-    void* pvy[2];
-    void* pvz[2];
-    uint32_t* tag;
+    void* part[2];  // particle records, Real[capacity][kRec]
     uint32_t* count[2];
+    uint8_t* coupled;  // per cell: 1 while a fused multi-step call regenerates the cell
+    char* xsend[2];    // a slab's exchange buffers (count, records, cell ids)
+    char* xrecv[2];
     void* crmax;
     void* rem;
     uint32_t* nbar_sum;
@@ -77,28 +83,19 @@ struct State {
     uint32_t* ctrl;
     unsigned long long* counters;
     GradRec* grad;
-    void* moved;
     void* coll_cell;  // per-cell NTC factor (Kn profile), or null
     void* tau_node;   // per-node relaxation time (Kn profile), or null
 };
 
-// Everything a DSMC kernel needs, passed by value: the move updates the source half in
-// place (m*, the same arrays as s*) and lists each particle's slot in the tag list of its new
-// cell (count_d); the collide gathers from the source half into the destination half (d*).
+// Everything a DSMC kernel needs, passed by value, for a step that starts from the sorted
+// particles of half p (srec): the move appends each particle, with its origin slot as its
+// stable-order key, to the bin of its new cell in half p^1 (drec); the collide puts each cell
+// of half p^1 in stable order in place, collides and samples it; the fused pass takes the
+// arrivals of half p^1 through the collide and moves them on into half p for the next step.
 template <typename Real>
 struct DsmcArgs {
-    const Real* sx;
-    const Real* sy;
-    const Real* svx;
-    const Real* svy;
-    const Real* svz;
-    Real* rec;  // moved particles by origin slot, 8 Real per record
-    Real* dx;
-    Real* dy;
-    Real* dvx;
-    Real* dvy;
-    Real* dvz;
-    uint32_t* tag;
+    Real* srec;  // particle records of half p
+    Real* drec;  // particle records of half p^1
     uint32_t* count_s;
     uint32_t* count_d;
     Real* crmax;
@@ -107,6 +104,7 @@ struct DsmcArgs {
     double* acc;
     uint32_t* ctrl;
     unsigned long long* counters;
+    const uint8_t* coupled;  // cells regenerated by the step's LB2DSMC (fused pass), or null
     int32_t ncx, ncy, ncells, bin, sample_every, ppc;
     double dt, g_step, coll_dt, crmax_init;
     // dt, g_step and coll_dt rounded to the state precision on the host (the kernels take
@@ -114,10 +112,19 @@ struct DsmcArgs {
     Real dt_r, g_r, coll_r;
     const Real* coll_cell;  // per-cell NTC factor, or null for coll_dt everywhere
     uint64_t seed;
-    // 3D (ncz >= 2): z positions of the source and destination sets; ncz is 0 in 2D
-    const Real* sz;
-    Real* dz;
-    int32_t ncz;
+    int32_t ncz;  // 3D (ncz >= 2): cells along z; 0 in 2D
+    // a streamwise slab: its first row in the channel and the channel's rows (0 and ncy for
+    // the whole channel); its exchange buffers: send records towards lower (0) and higher (1)
+    // rows with the particles' channel cells and counts, and the records received from the
+    // slab below (0) and above (1)
+    int32_t y0, ncy_g;
+    int32_t xcap;
+    Real* xrec[2];
+    uint32_t* xkey[2];
+    uint32_t* xcount[2];
+    const Real* rrec[2];
+    const uint32_t* rkey[2];
+    const uint32_t* rcount[2];
 };
 
 template <typename Real>
@@ -167,13 +174,16 @@ struct MapArgs {
     unsigned long long* counters;
     GradRec* grad;
     uint32_t* count;  // current half
-    Real* x;
-    Real* y;
-    Real* vx;
-    Real* vy;
-    Real* vz;
-    int32_t ncz;  // 3D (ncz >= 2): cells along z and the z positions; 0 and null in 2D
-    Real* z;
+    Real* rec;        // particle records of the current half
+    int32_t ncz;      // 3D (ncz >= 2): cells along z; 0 in 2D
+    // fused multi-step pass (LB2DSMC that moves what it creates): the half that receives the
+    // next step's arrivals and its counts, and the move's step constants
+    Real* arec;
+    uint32_t* acount;
+    Real dt_r, g_r;
+    // a streamwise slab: its first row in the channel and the channel's rows (cell ids of the
+    // random streams and y positions are the channel's) and the ghost rows below its LB rows
+    int32_t y0, ncy_g, yh;
 };
 
 // ---------------------------------------------------------------------------------------
@@ -210,6 +220,17 @@ __device__ __forceinline__ uint32_t uindex(uint32_t r, uint32_t n) {
 }
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+// The channel's id of cell c = (iz nly + iy) ncx + ix of a streamwise slab whose rows start
+// at row y0 of a channel of ncy_g rows: (iz ncy_g + y0 + iy) ncx + ix (c itself for the whole
+// channel, y0 = 0 and nly = ncy_g).
+__host__ __device__ __forceinline__ uint32_t global_cell(uint32_t c, int ncx, int nly, int y0,
+                                                          int ncy_g) {
+    if (y0 == 0 && nly == ncy_g) return c;
+    const uint32_t plane = (uint32_t)ncx * (uint32_t)nly;
+    const uint32_t iz = c / plane, r = c - iz * plane;
+    return (iz * (uint32_t)ncy_g + (uint32_t)y0) * (uint32_t)ncx + r;
+}
 
 // Kernel arguments of one context, or of a batch of independent contexts (replicas). The
 // units of a launch (cells, blocks of cells, nodes or list entries) are numbered across the
@@ -460,8 +481,21 @@ __host__ __device__ constexpr double wall_flux_norm() {
 // Launchers (defined in the kernel translation units).
 struct Ctx;
 cudaError_t launch_init(Ctx& c);
-cudaError_t launch_dsmc_step(Ctx& c);
+cudaError_t launch_dsmc_step(Ctx& c);  // move and collide of one step from half cur_p
+// The passes of a DSMC step from half p (DsmcArgs of parity p): the move (p -> p^1), the
+// collide (p^1 in place) and the fused pass (collide p^1, then move into p).
+cudaError_t launch_dsmc_move(Ctx& c, int p);
+cudaError_t launch_dsmc_collide(Ctx& c, int p);
+cudaError_t launch_dsmc_fused(Ctx& c, int p);
+// A streamwise slab: appends the received particles to the bins of half p^1 after the move.
+cudaError_t launch_dsmc_merge(Ctx& c, int p);
+// Marks (v = 1) or clears (v = 0) the listed cells in the coupled-cell mask.
+cudaError_t launch_mark_cells(Ctx& c, const int32_t* cells, int32_t n, uint8_t v);
 cudaError_t launch_lbm_step(Ctx& c);
+// A streamwise slab's LB ghost rows: values per side, and the pack (unpack = 0) or unpack of
+// one side's exchanged populations.
+int64_t lbm_halo_values(const Ctx& c);
+cudaError_t launch_lbm_halo(Ctx& c, int side, void* buf, int unpack);
 cudaError_t launch_lbm_step_nodes(Ctx& c, const void* f_src, void* f_dst, const void* g, const void* tau);
 cudaError_t launch_lbm_adjoint_step(Ctx& c, const void* f, const void* lam_next, void* lam,
                                     const void* g, const void* tau, void* grad_g, void* grad_tau,
@@ -471,6 +505,10 @@ cudaError_t launch_interface_loss(Ctx& c, const void* f, const int32_t* nodes, i
 cudaError_t launch_map_d2l(Ctx& c, const int32_t* nodes, int32_t n);
 cudaError_t launch_map_l2d(Ctx& c, const int32_t* cells, int32_t n);
 cudaError_t launch_map_l2d_noalloc(Ctx& c, const int32_t* cells, int32_t n);
+// LB2DSMC within the fused pass: the listed cells' particles are in half p^1 (left there in
+// stable order by the fused pass of parity p); the cells are regenerated (or, if the new
+// count exceeds the bin, kept) and their particles moved on into half p.
+cudaError_t launch_map_l2d_move(Ctx& c, const int32_t* cells, int32_t n, int p);
 cudaError_t launch_gather_acc(Ctx& c, const int32_t* cells, int32_t n, double* out);
 cudaError_t launch_map_d2l_adjoint(Ctx& c, const int32_t* nodes, int32_t n, void* lam,
                                    double* grad_acc);
@@ -544,12 +582,18 @@ struct Ctx {
     bool capturing = false;
     // graphs of one hybrid step, per particle parity
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    // graphs of a whole multi-step (fused) hybrid call: two slots keyed by the step count and
+    // the parities it starts from
+    cudaGraphExec_t mgraph[2] = {nullptr, nullptr};
+    int32_t mkey[2][3] = {{-1, -1, -1}, {-1, -1, -1}};
+    int mnext = 0;
     const int32_t* g_nodes = nullptr;
     const int32_t* g_cells = nullptr;
     int32_t g_nn = -1, g_nc = -1;
     int g_prof = -2;
     int g_curf[2] = {0, 0};        // population parity each graph variant was captured with
     uint32_t* h_pinned = nullptr;  // pinned host words for status reads
+    bool split_pending = false;    // a slab's dsmc_move was issued, its collide is due
     // hyb_hybrid_step_host: device staging of the lists and the gathered moment sums, and a
     // ring of completion events of the steps in flight
     char* io_dev = nullptr;

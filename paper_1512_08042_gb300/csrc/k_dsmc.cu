@@ -1,46 +1,36 @@
-// DSMC kernels: initialisation, move with diffuse isothermal walls and binning by cell,
+// DSMC kernels: initialisation, the move with diffuse isothermal walls and binning by cell,
 // and the per-cell stable ordering, no-time-counter hard-sphere collisions and
 // Hermite-moment sampling.
 //
 // Particles live in per-cell bins of `bin` slots (cell c owns slots [c bin, (c+1) bin) of
-// each state array, count[c] in use) and ping-pong between two halves. One DSMC step (the
-// NTC order of Bird that the paper uses in Sec. 5: move, index, collide, sample) is two
-// launches:
+// each state array, count[c] in use) and ping-pong between two halves. A DSMC step (the NTC
+// order of Bird that the paper uses in Sec. 5: move, index, collide, sample) from the sorted
+// particles of half p takes two passes:
 //   k_move     one warp per source cell: body-force kick, free flight, diffuse wall
-//              re-emission (Sec. 3.1), periodic wrap, new cell; the moved particle is written
-//              as one record (x, y, vx, vy, vz) at its origin slot of the `moved` scratch, and
-//              the slot is appended to the tag list of its new cell's bin by a warp-aggregated
-//              atomic.
-//   k_collide  32 consecutive cells per block, a group of 8 lanes per cell: the cell's tags
-//              are put in stable order (ascending origin slot = origin cell, then rank in it:
-//              a bitonic sort in registers), the records are gathered into the bin of the
-//              other half (positions) and a shared-memory pool (velocities), the NTC
-//              candidates of all 32 cells are drawn by the whole block and applied by one
-//              warp with a lane per cell (Eq. collisionnumber), and the sums 1, v, vv, vvv are
-//              added to the FP64 cumulative sums of the cell (Sec. 2.1, Fig. 1). The last
-//              block to finish advances the step counters.
+//              re-emission (Sec. 3.1), periodic wrap, new cell; the moved particle and its
+//              stable-order key (origin slot = origin cell, then rank in it) are appended to
+//              the bin of its new cell in half p^1 by a warp-aggregated atomic.
+//   k_collide  32 consecutive cells per block, a group of 8 lanes per cell: the cell's keys
+//              are sorted (a bitonic sort in registers), each arrival is placed at its rank in
+//              a shared-memory pool, the NTC candidates of all 32 cells are drawn by the whole
+//              block and applied by one warp with a lane per cell (Eq. collisionnumber), the
+//              sums 1, v, vv, vvv are added to the FP64 cumulative sums of the cell (Sec. 2.1,
+//              Fig. 1) and the sorted cell is written back in place. The last block to finish
+//              advances the step counters.
+// Several steps in one call fuse the collide of step s with the move of step s + 1: the
+// fused pass collides and samples a cell as above and then moves its particles straight from
+// the pool into the bins of the other half, so a particle's state is read and written once
+// per step. Cells that the step's LB2DSMC regenerates are written back in place instead.
 // This file is compiled without FMA contraction so that positions, cell keys, pair choices
 // and post-collision velocities are the IEEE float (or double) results of the written
 // expressions.
 #include <cstring>
 
-#include "hyb_internal.cuh"
+#include "dsmc_move.cuh"
 
 namespace hyb {
 
 namespace {
-
-template <typename Real>
-__device__ __forceinline__ void reemit(uint64_t seed, uint32_t cell, uint32_t rank, uint32_t s,
-                                       int bounce, Real sign, Real& ux, Real& uy, Real& uz) {
-    const uint4 r = draw(seed, cell, s, TAG_WALL, (rank << 3) | (uint32_t)bounce, 0);
-    const Real vn = wall_speed<Real>(r.x);
-    Real t1, t2;
-    gauss_pair<Real>(r.y, r.z, t1, t2);
-    ux = sign * vn;
-    uy = t1;
-    uz = t2;
-}
 
 // Isotropic unit vector (Marsaglia 1972) from the NTC scattering stream of candidate k.
 template <typename Real>
@@ -73,20 +63,21 @@ __global__ void k_init_particles(DsmcArgs<Real> a) {
     const int64_t n = (int64_t)a.ncells * a.ppc;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
          s += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t c = (uint32_t)(s / a.ppc), k = (uint32_t)(s % a.ppc);
-        const int ix = (int)(c % (uint32_t)a.ncx), iy = (int)((c / (uint32_t)a.ncx) % (uint32_t)a.ncy);
-        const int64_t slot = (int64_t)c * a.bin + k;
+        const uint32_t cl = (uint32_t)(s / a.ppc), k = (uint32_t)(s % a.ppc);
+        const int ix = (int)(cl % (uint32_t)a.ncx);
+        const int iy = a.y0 + (int)((cl / (uint32_t)a.ncx) % (uint32_t)a.ncy);  // the channel's row
+        const int64_t slot = (int64_t)cl * a.bin + k;
+        const uint32_t c = global_cell(cl, a.ncx, a.ncy, a.y0, a.ncy_g);  // key of the draws
         const uint4 rp = draw(a.seed, c, 0, TAG_INIT_POS, k, 0);
-        a.dx[slot] = (Real)ix + (Real)u01f(rp.x);
-        a.dy[slot] = (Real)iy + (Real)u01f(rp.y);
-        if (a.ncz) a.dz[slot] = (Real)(c / ((uint32_t)a.ncx * (uint32_t)a.ncy)) + (Real)u01f(rp.z);
+        const Real px = (Real)ix + (Real)u01f(rp.x);
+        const Real py = (Real)iy + (Real)u01f(rp.y);
+        const Real pz = a.ncz ? (Real)(cl / ((uint32_t)a.ncx * (uint32_t)a.ncy)) + (Real)u01f(rp.z)
+                              : (Real)0;
         const uint4 rv = draw(a.seed, c, 0, TAG_INIT_VEL, k, 0);
         Real n0, n1, n2, n3;
         gauss_pair<Real>(rv.x, rv.y, n0, n1);
         gauss_pair<Real>(rv.z, rv.w, n2, n3);
-        a.dvx[slot] = n0;
-        a.dvy[slot] = n1;
-        a.dvz[slot] = n2;
+        rec_put(a.drec, slot, px, py, pz, n0, n1, n2, 0u);
     }
 }
 
@@ -108,96 +99,6 @@ __global__ void k_init_cells(DsmcArgs<Real> a) {
     }
 }
 
-// ---------------------------------------------------------------------------------------
-// Moved-particle records: 8 Real per origin slot (x, y, vx, vy, vz, 3 unused), written whole
-// by the move and read by the collide with one 32-byte sector per particle (FP32).
-__device__ __forceinline__ void rec_store(float* rec, int64_t i, float x, float y, float u, float v,
-                                          float w, float z = 0.0f) {
-    float4* p = reinterpret_cast<float4*>(rec) + 2 * i;
-    p[0] = make_float4(x, y, u, v);
-    p[1] = make_float4(w, z, 0.0f, 0.0f);
-}
-__device__ __forceinline__ void rec_store(double* rec, int64_t i, double x, double y, double u,
-                                          double v, double w, double z = 0.0) {
-    double2* p = reinterpret_cast<double2*>(rec) + 4 * i;
-    p[0] = make_double2(x, y);
-    p[1] = make_double2(u, v);
-    p[2] = make_double2(w, z);
-}
-// Z3: also the z position (3D), stored beside vz.
-template <bool Z3>
-__device__ __forceinline__ void rec_load(const float* rec, int64_t i, float& x, float& y, float& u,
-                                         float& v, float& w, float& z) {
-    const float4* p = reinterpret_cast<const float4*>(rec) + 2 * i;
-    const float4 a = p[0];
-    x = a.x;
-    y = a.y;
-    u = a.z;
-    v = a.w;
-    if constexpr (Z3) {
-        const float2 b = reinterpret_cast<const float2*>(p + 1)[0];
-        w = b.x;
-        z = b.y;
-    } else {
-        w = reinterpret_cast<const float*>(p + 1)[0];
-    }
-}
-template <bool Z3>
-__device__ __forceinline__ void rec_load(const double* rec, int64_t i, double& x, double& y,
-                                         double& u, double& v, double& w, double& z) {
-    const double2* p = reinterpret_cast<const double2*>(rec) + 4 * i;
-    const double2 a = p[0], b = p[1];
-    x = a.x;
-    y = a.y;
-    u = b.x;
-    v = b.y;
-    if constexpr (Z3) {
-        const double2 c = p[2];
-        w = c.x;
-        z = c.y;
-    } else {
-        w = reinterpret_cast<const double*>(p + 2)[0];
-    }
-}
-
-// ---------------------------------------------------------------------------------------
-// Move (kick, drift, walls, wrap) and binning into the other half.
-
-// Flight of a particle whose straight flight crosses a wall: it is re-emitted from the wall
-// (diffuse, isothermal), possibly more than once, for the rest of the step.
-template <typename Real, bool Z3 = false>
-__device__ __forceinline__ void wall_flight(uint64_t seed, uint32_t c, uint32_t k, uint32_t s, Real H,
-                                            Real dt, Real& px, Real& py, Real& ux, Real& uy,
-                                            Real& uz, uint32_t& hits, uint32_t& caps, Real& pz) {
-    Real t = dt;
-    for (int b = 0;; ++b) {
-        const Real xn = px + ux * t;
-        const bool left = xn < (Real)0;
-        const bool right = xn > H;
-        if (!left && !right) {
-            px = xn;
-            py = py + uy * t;
-            if constexpr (Z3) pz = pz + uz * t;
-            break;
-        }
-        if (b == kMaxBounces) {
-            caps += 1;
-            px = left ? (Real)0 : H;
-            py = py + uy * t;
-            if constexpr (Z3) pz = pz + uz * t;
-            break;
-        }
-        hits += 1;
-        const Real th = left ? px / (-ux) : (H - px) / ux;
-        py = py + uy * th;
-        if constexpr (Z3) pz = pz + uz * th;
-        px = left ? (Real)0 : H;
-        t = t - th;
-        if (t < (Real)0) t = (Real)0;
-        reemit(seed, c, k, s, b, left ? (Real)1 : (Real)-1, ux, uy, uz);
-    }
-}
-
 // Exact widening of a float to double on the integer pipe (the FP64 pipe is slow on this
 // part): a normal float's sign, exponent rebiased from 127 to 1023 and mantissa shifted to
 // the top of the 52-bit field (IEEE 754 binary32 and binary64 formats). Zeros, subnormals,
@@ -212,173 +113,95 @@ __device__ __forceinline__ double widen(float f) {
 }
 __device__ __forceinline__ double widen(double d) { return d; }
 
-// Periodic wrap of v into [0, period).
+// ---------------------------------------------------------------------------------------
+// Move (kick, drift, walls, wrap) of the sorted particles of half p into the bins of p^1.
+
 template <typename Real>
-__device__ __forceinline__ Real wrap_periodic(Real v, Real period) {
-    if (v < (Real)0 || v >= period) {
-        v = v - period * floor(v / period);
-        if (v < (Real)0) v = v + period;
-        if (v >= period) v = v - period;
-    }
-    return v;
+__device__ __forceinline__ MoveCtx<Real> move_ctx(const DsmcArgs<Real>& a) {
+    MoveCtx<Real> m;
+    m.H = (Real)a.ncx;
+    m.L = (Real)a.ncy_g;
+    m.Lz = (Real)(a.ncz ? a.ncz : 1);
+    m.dt = a.dt_r;
+    m.g = a.g_r;
+    m.ncx = a.ncx;
+    m.ncy = a.ncy_g;
+    m.ncz = a.ncz;
+    m.y0 = a.y0;
+    m.nly = a.ncy;
+    m.seed = a.seed;
+    return m;
 }
 
-// Periodic wrap of y (and z in 3D) and the cell key (iz ncy + iy) ncx + ix of a moved particle.
-template <typename Real, bool Z3 = false>
-__device__ __forceinline__ uint32_t cell_key(const DsmcArgs<Real>& a, Real L, Real px, Real& py,
-                                             Real& pz) {
-    py = wrap_periodic(py, L);
-    int ix = (int)floor(px), iy = (int)floor(py);
-    ix = ix < 0 ? 0 : (ix > a.ncx - 1 ? a.ncx - 1 : ix);
-    iy = iy < 0 ? 0 : (iy > a.ncy - 1 ? a.ncy - 1 : iy);
-    int iz = 0;
-    if constexpr (Z3) {
-        pz = wrap_periodic(pz, (Real)a.ncz);
-        iz = (int)floor(pz);
-        iz = iz < 0 ? 0 : (iz > a.ncz - 1 ? a.ncz - 1 : iz);
-    }
-    return (uint32_t)((iz * a.ncy + iy) * a.ncx + ix);
+template <typename Real>
+__device__ __forceinline__ Half<Real> half_s(const DsmcArgs<Real>& a) {
+    return Half<Real>{a.srec, a.count_s};
+}
+template <typename Real>
+__device__ __forceinline__ Half<Real> half_d(const DsmcArgs<Real>& a) {
+    return Half<Real>{a.drec, a.count_d};
 }
 
-// Appends the active lanes' two slots to the bins of their new cells: lanes bound for the
-// same cell share one atomic, and each gets arrival = base + rank among them. The atomics
-// of both slots are in flight before either result is used.
-__device__ __forceinline__ void bin_arrival2(uint32_t* __restrict__ count, uint32_t key1, bool act1,
-                                             uint32_t key2, bool act2, unsigned lane, uint32_t& arr1,
-                                             uint32_t& arr2) {
-    // inactive lanes match among themselves under a key no cell has
-    const unsigned peers1 = __match_any_sync(kFull, act1 ? key1 : 0xFFFFFFFFu);
-    const unsigned peers2 = __match_any_sync(kFull, act2 ? key2 : 0xFFFFFFFFu);
-    const int lead1 = __ffs(peers1) - 1, lead2 = __ffs(peers2) - 1;
-    uint32_t b1 = 0, b2 = 0;
-    if (act1 && (int)lane == lead1) b1 = atomicAdd(&count[key1], (uint32_t)__popc(peers1));
-    if (act2 && (int)lane == lead2) b2 = atomicAdd(&count[key2], (uint32_t)__popc(peers2));
-    b1 = __shfl_sync(kFull, b1, lead1);
-    b2 = __shfl_sync(kFull, b2, lead2);
-    const unsigned below = (1u << lane) - 1u;
-    arr1 = b1 + (uint32_t)__popc(peers1 & below);
-    arr2 = b2 + (uint32_t)__popc(peers2 & below);
-}
-
-// One source cell, by one warp; the first 64 particles of the cell are handled two per
-// lane, loads, flights and binning atomics of both in flight together.
+// One source cell, by one warp; 64 particles of the cell at a time, two per lane, with the
+// loads, flights and binning atomics of both in flight together.
 template <typename Real, bool Z3>
 __device__ __forceinline__ void move_cell(const DsmcArgs<Real>& a, int c, unsigned lane) {
     const uint32_t s = a.ctrl[CTRL_STEP];
-    if (c == 0 && lane == 0) a.ctrl[CTRL_NTOT] = 0;  // the collide recounts
-    const Real H = (Real)a.ncx, L = (Real)a.ncy;
-    const Real g = a.g_r, dt = a.dt_r;
+    const MoveCtx<Real> m = move_ctx(a);
     const uint32_t bin = (uint32_t)a.bin;
-    // the arrays do not overlap: loads of the next slots need not wait for earlier stores
-    const Real* __restrict__ sx = a.sx;
-    const Real* __restrict__ sy = a.sy;
-    const Real* __restrict__ svx = a.svx;
-    const Real* __restrict__ svy = a.svy;
-    const Real* __restrict__ svz = a.svz;
-    Real* __restrict__ rec = a.rec;
-    uint32_t* __restrict__ tag = a.tag;
-    uint32_t* __restrict__ cnt = a.count_d;
+    // the halves do not overlap: loads of the next records need not wait for earlier stores
+    const Real* __restrict__ src = a.srec;
+    const Half<Real> dst = half_d(a);
     uint32_t hits = 0, caps = 0, lost = 0;
-    {
-        uint32_t n = a.count_s[c];
-        if (n > bin) n = bin;
-        const int64_t base = (int64_t)c * bin;
-        for (uint32_t k0 = 0; k0 == 0 || k0 < n; k0 += 64) {
-            const uint32_t k1 = k0 + lane, k2 = k1 + 32;
-            const bool act1 = k1 < n, act2 = k2 < n;
-            Real p1[5] = {0, 0, 0, 0, 0}, p2[5] = {0, 0, 0, 0, 0};
-            Real z1 = 0, z2 = 0;  // 3D only
-            // the loads need only the bin size, not the count, so they travel with it
-            const bool in1 = k1 < bin, in2 = k2 < bin;
-            if (in1) {
-                p1[0] = sx[base + k1];
-                p1[1] = sy[base + k1];
-                p1[2] = svx[base + k1];
-                p1[3] = svy[base + k1];
-                p1[4] = svz[base + k1];
-                if constexpr (Z3) z1 = a.sz[base + k1];
-            }
-            if (in2) {
-                p2[0] = sx[base + k2];
-                p2[1] = sy[base + k2];
-                p2[2] = svx[base + k2];
-                p2[3] = svy[base + k2];
-                p2[4] = svz[base + k2];
-                if constexpr (Z3) z2 = a.sz[base + k2];
-            }
-            // kick and straight flight; flights that cross a wall are redone below
-            p1[3] = p1[3] + g;
-            p2[3] = p2[3] + g;
-            const Real xn1 = p1[0] + p1[2] * dt, xn2 = p2[0] + p2[2] * dt;
-            const bool wall1 = act1 && !(xn1 >= (Real)0 && xn1 <= H);
-            const bool wall2 = act2 && !(xn2 >= (Real)0 && xn2 <= H);
-            if (!wall1) {
-                p1[0] = xn1;
-                p1[1] = p1[1] + p1[3] * dt;
-                if constexpr (Z3) z1 = z1 + p1[4] * dt;
-            }
-            if (!wall2) {
-                p2[0] = xn2;
-                p2[1] = p2[1] + p2[3] * dt;
-                if constexpr (Z3) z2 = z2 + p2[4] * dt;
-            }
-            if (__any_sync(kFull, wall1 || wall2)) {
-#pragma unroll 1
-                for (int h = 0; h < 2; ++h) {
-                    if (h == 0 ? wall1 : wall2) {
-                        Real q[5];
-#pragma unroll
-                        for (int i = 0; i < 5; ++i) q[i] = h == 0 ? p1[i] : p2[i];
-                        Real qz = h == 0 ? z1 : z2;
-                        wall_flight<Real, Z3>(a.seed, (uint32_t)c, h == 0 ? k1 : k2, s, H, dt, q[0],
-                                              q[1], q[2], q[3], q[4], hits, caps, qz);
-                        if (h == 0)
-                            z1 = qz;
-                        else
-                            z2 = qz;
-#pragma unroll
-                        for (int i = 0; i < 5; ++i) {
-                            if (h == 0)
-                                p1[i] = q[i];
-                            else
-                                p2[i] = q[i];
-                        }
-                    }
-                }
-            }
-            const uint32_t key1 = act1 ? cell_key<Real, Z3>(a, L, p1[0], p1[1], z1) : 0u;
-            const uint32_t key2 = act2 ? cell_key<Real, Z3>(a, L, p2[0], p2[1], z2) : 0u;
-            uint32_t arr1, arr2;
-            bin_arrival2(cnt, key1, act1, key2, act2, lane, arr1, arr2);
-            if (act1) {
-                rec_store(rec, base + k1, p1[0], p1[1], p1[2], p1[3], p1[4], z1);
-                if (arr1 < bin)
-                    tag[(int64_t)key1 * bin + arr1] = (uint32_t)(base + k1);
-                else
-                    lost += 1;
-            }
-            if (act2) {
-                rec_store(rec, base + k2, p2[0], p2[1], p2[2], p2[3], p2[4], z2);
-                if (arr2 < bin)
-                    tag[(int64_t)key2 * bin + arr2] = (uint32_t)(base + k2);
-                else
-                    lost += 1;
-            }
+    uint32_t n = a.count_s[c];
+    __syncwarp();
+    if (lane == 0) a.count_s[c] = 0;  // half p is consumed; its counts start the next arrivals
+    if (n > bin) n = bin;
+    const int64_t base = (int64_t)c * bin;
+    // the channel's cell: the key of the wall draws and of the stable order
+    const uint32_t gc = global_cell((uint32_t)c, a.ncx, a.ncy, a.y0, a.ncy_g);
+    const int64_t gbase = (int64_t)gc * bin;
+    for (uint32_t k0 = 0; k0 == 0 || k0 < n; k0 += 64) {
+        const uint32_t k1 = k0 + lane, k2 = k1 + 32;
+        const bool act1 = k1 < n, act2 = k2 < n;
+        Real p1[6] = {0, 0, 0, 0, 0, 0}, p2[6] = {0, 0, 0, 0, 0, 0};  // x y z vx vy vz
+        uint32_t t1, t2;
+        // the loads need only the bin size, not the count, so they travel with it
+        if (k1 < bin) rec_get(src, base + k1, p1[0], p1[1], p1[2], p1[3], p1[4], p1[5], t1);
+        if (k2 < bin) rec_get(src, base + k2, p2[0], p2[1], p2[2], p2[3], p2[4], p2[5], t2);
+        uint32_t key1 = 0, key2 = 0;
+        int dir1 = -1, dir2 = -1;
+        if (act1)
+            key1 = move_particle<Real, Z3>(m, gc, k1, s, p1[0], p1[1], p1[2], p1[3], p1[4], p1[5], hits,
+                                           caps, dir1);
+        if (act2)
+            key2 = move_particle<Real, Z3>(m, gc, k2, s, p2[0], p2[1], p2[2], p2[3], p2[4], p2[5], hits,
+                                           caps, dir2);
+        const bool loc1 = act1 && dir1 < 0, loc2 = act2 && dir2 < 0;
+        uint32_t arr1, arr2;
+        bin_arrival2(dst.count, key1, loc1, key2, loc2, lane, arr1, arr2);
+        if (loc1) {
+            if (arr1 < bin)
+                put_particle<Real, Z3>(dst, (int64_t)key1 * bin + arr1, (uint32_t)(gbase + k1), p1[0],
+                                       p1[1], p1[2], p1[3], p1[4], p1[5]);
+            else
+                lost += 1;
+        } else if (act1) {
+            send_particle<Real, Z3>(a.xrec, a.xkey, a.xcount, a.xcap, dir1, key1, (uint32_t)(gbase + k1),
+                                    p1[0], p1[1], p1[2], p1[3], p1[4], p1[5], lost);
+        }
+        if (loc2) {
+            if (arr2 < bin)
+                put_particle<Real, Z3>(dst, (int64_t)key2 * bin + arr2, (uint32_t)(gbase + k2), p2[0],
+                                       p2[1], p2[2], p2[3], p2[4], p2[5]);
+            else
+                lost += 1;
+        } else if (act2) {
+            send_particle<Real, Z3>(a.xrec, a.xkey, a.xcount, a.xcap, dir2, key2, (uint32_t)(gbase + k2),
+                                    p2[0], p2[1], p2[2], p2[3], p2[4], p2[5], lost);
         }
     }
-    if (__any_sync(kFull, (hits | caps | lost) != 0u)) {  // cells at a wall, or overflow
-        hits = __reduce_add_sync(kFull, hits);
-        caps = __reduce_add_sync(kFull, caps);
-        lost = __reduce_add_sync(kFull, lost);
-        if (lane == 0) {
-            if (hits) atomicAdd(&a.counters[HYB_C_WALL_HITS], (unsigned long long)hits);
-            if (caps) {
-                atomicAdd(&a.counters[HYB_C_BOUNCE_CAP], (unsigned long long)caps);
-                atomicOr(&a.ctrl[CTRL_STATUS], HYB_ST_BOUNCE_CAP);
-            }
-            if (lost) atomicOr(&a.ctrl[CTRL_STATUS], HYB_ST_CAPACITY);
-        }
-    }
+    move_events(a.counters, a.ctrl, hits, caps, lost, lane);
 }
 
 // One warp per source cell (the cells of all replicas in the batch form).
@@ -399,7 +222,6 @@ __global__ void __launch_bounds__(256, 4) k_move(Launch<DsmcArgs<Real>> L) {
 }
 
 // ---------------------------------------------------------------------------------------
-// ---------------------------------------------------------------------------------------
 // Collide: a group of G lanes per cell, 32 / G cells per warp. Every instruction of the
 // serial NTC chain then advances 32 / G cells at once. All loops that contain shuffles have
 // warp-uniform trip counts (groups whose cell has less work are masked), so every shuffle is
@@ -412,6 +234,13 @@ struct CollideCfg {
 };
 constexpr int kCollideWarps = 8;  // 32 cells per block
 constexpr int kChainSteps = 16;   // candidates per cell drawn per pass of the NTC phase
+enum CollideMode : int { MODE_COLLIDE = 0, MODE_FUSED = 1 };
+
+// Real arrays of the shared-memory pool per slot: vx, vy, vz, x, y (, z)
+template <bool Z3>
+__host__ __device__ constexpr int pool_reals() {
+    return Z3 ? 6 : 5;
+}
 
 // Ascending bitonic sort of G R keys held by the G lanes of a group, R per lane, in blocked
 // order: key r of group lane l is at position (r % B) + B l + B G (r / B). Exchanges between
@@ -455,51 +284,26 @@ __device__ __forceinline__ void bitonic_blocked(uint32_t (&v)[R]) {
     }
 }
 
-// Writes the sorted keys of blocked positions below n to st and reads back into v the keys
-// of positions gl + G r (the order in which the group gathers); every lane of the warp
-// calls it.
-template <int G, int R, int B>
-__device__ __forceinline__ void blocked_to_strided(uint32_t (&v)[R], uint32_t* st, uint32_t n, int gl) {
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const uint32_t pos = (uint32_t)((r % B) + B * gl + B * G * (r / B));
-        if (pos < n) st[pos] = v[r];
-    }
-    __syncwarp();
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const uint32_t k = (uint32_t)(gl + G * r);
-        v[r] = k < n ? st[k] : 0u;
-    }
-}
-
-// Gathers the particles of sorted positions k = gl + G r (r < RR) from the records of the
-// origin slots src[r]: positions into the cell's bin of the other half, velocities into
-// shared memory. The record, position and shared-memory pointers are declared free of
-// aliasing, so the loads of all slots can be in flight before the first store.
-template <typename Real, int G, int RR, bool Z3>
-__device__ __forceinline__ void gather_slots(const Real* __restrict__ rec, Real* __restrict__ dx,
-                                             Real* __restrict__ dy, Real* __restrict__ dz, int gl,
-                                             uint32_t n, const uint32_t* src, Real* __restrict__ vx,
-                                             Real* __restrict__ vy, Real* __restrict__ vz) {
-#pragma unroll
-    for (int r = 0; r < RR; ++r) {
-        const uint32_t k = (uint32_t)(gl + G * r);
-        if (k < n) {
-            Real px, py, ux, uy, uz, pz;
-            rec_load<Z3>(rec, (int64_t)src[r], px, py, ux, uy, uz, pz);
-            dx[k] = px;
-            dy[k] = py;
-            if constexpr (Z3) dz[k] = pz;
-            vx[k] = ux;
-            vy[k] = uy;
-            vz[k] = uz;
+// Ascending position of tag t among the n sorted keys st[0..n) (keys are distinct).
+__device__ __forceinline__ uint32_t sorted_rank(const uint32_t* st, uint32_t n, uint32_t t) {
+    uint32_t lo = 0, len = n;
+    while (len > 0) {
+        const uint32_t half = len >> 1;
+        if (st[lo + half] < t) {
+            lo += half + 1;
+            len -= half + 1;
+        } else {
+            len = half;
         }
     }
+    return lo;
 }
 
-// The block of 32 consecutive cells `blk` (of nblk) of one context.
-template <typename Real, bool Z3>
+// The block of 32 consecutive cells `blk` (of nblk) of one context: the arrivals of half
+// p^1 (d*) are put in stable order, collided and sampled; MODE_COLLIDE writes them back in
+// place, MODE_FUSED moves them on (step s + 1) into the bins of half p (s*), except cells
+// marked in a.coupled, which are written back in place for LB2DSMC.
+template <typename Real, bool Z3, int MODE>
 __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t pool, int blk,
                                               int nblk) {
     constexpr int G = kGroup;
@@ -509,6 +313,7 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
     constexpr int SMALL = 64;             // cells up to this size are sorted in registers
     constexpr int R = SMALL / G;
     constexpr int KC = kChainSteps;       // candidates per cell drawn per pass of phase B
+    constexpr int NR = pool_reals<Z3>();
     static_assert(NC == 32, "phase B runs one lane per cell of the block in one warp");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ uint32_t s_n[NC], s_off[NC], s_nsel[NC];
@@ -521,10 +326,10 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
     const int grp = (int)lane / G, gl = (int)lane % G;
     const int gi = w * CPW + grp;  // the group's cell within the block
     const uint32_t bin = (uint32_t)a.bin;
-    // shared memory: the block's pool of vx, vy, vz (Real) and tags (u32), `pool` slots each,
-    // then the candidates of one pass of phase B
+    // shared memory: the block's pool of vx, vy, vz, x, y (, z) (Real) and sorted keys (u32),
+    // `pool` slots each, then the candidates of one pass of phase B
     Real* pv = reinterpret_cast<Real*>(smem_raw);
-    uint32_t* pst = reinterpret_cast<uint32_t*>(pv + 3 * (size_t)pool);
+    uint32_t* pst = reinterpret_cast<uint32_t*>(pv + NR * (size_t)pool);
     uint32_t* c_ij = pst + pool;
     Real* c_R = reinterpret_cast<Real*>(c_ij + NC * KC);
     Real* c_nx = c_R + NC * KC;
@@ -535,18 +340,24 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
     const Real coll_dt = a.coll_r;
     unsigned long long ncand_tot = 0, ncoll_tot = 0;
     uint32_t flags = 0, nlive = 0;
+    uint32_t hits = 0, caps = 0, lost = 0;
 
     const int c = blk * NC + gi;
     const bool has = c < a.ncells;
     const int64_t base = (int64_t)c * bin;
-    // the cell's loads are issued together: count, the first SMALL tag slots and the
-    // leader's NTC state
+    // the channel's cell: the key of the random streams and of the stable order
+    const uint32_t gc = global_cell((uint32_t)c, a.ncx, a.ncy, a.y0, a.ncy_g);
+    const int64_t gbase = (int64_t)gc * bin;
+    (void)gbase;
+    const Real* __restrict__ drec = a.drec;
+    // the cell's loads are issued together: count, the first SMALL keys and the leader's NTC
+    // state
     uint32_t n_all = has ? a.count_d[c] : 0u;
     uint32_t vl[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const uint32_t k = (uint32_t)(gl + G * r);
-        vl[r] = (has && k < bin) ? a.tag[base + k] : 0xFFFFFFFFu;
+        vl[r] = (has && k < bin) ? rec_tag(drec, base + k) : 0xFFFFFFFFu;
     }
     uint32_t nb0 = 0;
     Real cm0 = (Real)0, rem0 = (Real)0;
@@ -555,6 +366,7 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
         cm0 = a.crmax[c];
         rem0 = a.rem[c];
     }
+    const bool moving = MODE == MODE_FUSED && has && !(a.coupled && a.coupled[c]);
     if (n_all > bin) n_all = bin;
     // the cells' regions of the block pool (exclusive scan of the counts); if they do not
     // fit, the cells take the whole pool one after another
@@ -582,12 +394,15 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
         Real* vx = pv + poff;
         Real* vy = pv + pool + poff;
         Real* vz = pv + 2 * pool + poff;
+        Real* qx = pv + 3 * pool + poff;
+        Real* qy = pv + 4 * pool + poff;
+        Real* qz = pv + 5 * (size_t)pool + poff;  // 3D only
         uint32_t* st = pst + poff;
-        // A. stable order (ascending origin slot) and gather. Cells of up to SMALL particles
-        // are sorted by their group with R keys per lane. A warp that holds a cell of up to
-        // 2 SMALL puts the tags of its cells in their shared-memory tag slots and sorts them
-        // two cells at a time, 2 G lanes with R keys each per cell. Larger cells are ranked
-        // in shared memory.
+        // A. stable order: the keys (origin slots) of cells of up to SMALL particles are
+        // sorted by their group with R keys per lane; a warp that holds a cell of up to
+        // 2 SMALL puts the keys of its cells in their shared-memory slots and sorts them two
+        // cells at a time, 2 G lanes with R keys each per cell. st[0..n) then holds the sorted
+        // keys. Larger cells keep their keys unsorted in st and rank each by counting.
         {
             if (__any_sync(kFull, n > (uint32_t)SMALL && n <= (uint32_t)(2 * SMALL))) {
                 const bool in2 = n <= (uint32_t)(2 * SMALL);
@@ -596,7 +411,7 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const uint32_t k = (uint32_t)(SMALL + gl + G * r);
-                    hi[r] = k < nn ? a.tag[base + k] : 0u;
+                    hi[r] = k < nn ? rec_tag(drec, base + k) : 0u;
                 }
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
@@ -626,19 +441,6 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
                     }
                     __syncwarp();
                 }
-                if (in2) {
-#pragma unroll 1
-                    for (int q = 0; q < 2; ++q) {
-                        uint32_t src[R];
-#pragma unroll
-                        for (int r = 0; r < R; ++r) {
-                            const uint32_t k = (uint32_t)(SMALL * q + gl + G * r);
-                            src[r] = k < n ? st[k] : 0u;
-                        }
-                        gather_slots<Real, G, R, Z3>(a.rec, a.dx + base, a.dy + base, a.dz + base,
-                                                     SMALL * q + gl, n, src, vx, vy, vz);
-                    }
-                }
             } else {
                 uint32_t v[R];
 #pragma unroll
@@ -647,28 +449,46 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
                     v[r] = (n <= (uint32_t)SMALL && k < n) ? vl[r] : 0xFFFFFFFFu;
                 }
                 bitonic_blocked<G, R, R>(v);
-                blocked_to_strided<G, R, R>(v, st, n <= (uint32_t)SMALL ? n : 0u, gl);
-                if (n <= (uint32_t)SMALL)
-                    gather_slots<Real, G, R, Z3>(a.rec, a.dx + base, a.dy + base, a.dz + base, gl,
-                                                 n, v, vx, vy, vz);
+                if (n <= (uint32_t)SMALL) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const uint32_t pos = (uint32_t)(r + R * gl);
+                        if (pos < n) st[pos] = v[r];
+                    }
+                }
             }
             if (n > (uint32_t)(2 * SMALL))
-                for (uint32_t k = gl; k < n; k += G) st[k] = a.tag[base + k];
+                for (uint32_t k = gl; k < n; k += G) st[k] = rec_tag(drec, base + k);
             __syncwarp();
-            if (n > (uint32_t)(2 * SMALL)) {
-                // rank of each tag = number of smaller tags in the cell
-                for (uint32_t k = gl; k < n; k += G) {
-                    const uint32_t t = st[k];
-                    uint32_t r = 0;
-                    for (uint32_t m = 0; m < n; ++m) r += st[m] < t ? 1u : 0u;
-                    Real px, py, ux, uy, uz, pz;
-                    rec_load<Z3>(a.rec, (int64_t)t, px, py, ux, uy, uz, pz);
-                    a.dx[base + r] = px;
-                    a.dy[base + r] = py;
-                    if constexpr (Z3) a.dz[base + r] = pz;
-                    vx[r] = ux;
-                    vy[r] = uy;
-                    vz[r] = uz;
+            // each arrival k goes to the pool slot of its rank (its record carries its key);
+            // the loads of a lane's arrivals can be in flight together
+            const bool big = n > (uint32_t)(2 * SMALL);
+            for (uint32_t k0 = 0; k0 < n; k0 += 4 * G) {
+                Real p[4][6];
+                uint32_t t[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t k = k0 + (uint32_t)(gl + G * j);
+                    if (k < n) rec_get(drec, base + k, p[j][3], p[j][4], p[j][5], p[j][0], p[j][1], p[j][2], t[j]);
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t k = k0 + (uint32_t)(gl + G * j);
+                    if (k < n) {
+                        uint32_t rk;
+                        if (big) {
+                            rk = 0;
+                            for (uint32_t m2 = 0; m2 < n; ++m2) rk += st[m2] < t[j] ? 1u : 0u;
+                        } else {
+                            rk = sorted_rank(st, n, t[j]);
+                        }
+                        vx[rk] = p[j][0];
+                        vy[rk] = p[j][1];
+                        vz[rk] = p[j][2];
+                        qx[rk] = p[j][3];
+                        qy[rk] = p[j][4];
+                        if constexpr (Z3) qz[rk] = p[j][5];
+                    }
                 }
             }
         }
@@ -678,7 +498,6 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
             if (has_r) {
                 const uint32_t nb = nb0 + n;
                 a.nbar_sum[c] = nb;
-                a.count_s[c] = 0;  // the source half's count is not needed after the move
                 nlive += n;
                 if (n > 32767u) {
                     flags |= HYB_ST_CELL_OVERFLOW;  // pair indices are packed in 15 and 16 bits
@@ -757,7 +576,7 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
                     valid = t < tend && k < s_nsel[g];
                 }
                 if (valid) {
-                    const uint32_t cg = (uint32_t)(blk * NC + g);
+                    const uint32_t cg = global_cell((uint32_t)(blk * NC + g), a.ncx, a.ncy, a.y0, a.ncy_g);
                     const uint32_t ng = s_n[g];
                     const uint4 r = draw(a.seed, cg, s, TAG_NTC_PAIR, k, 0);
                     const uint32_t ci = uindex(r.x, ng);
@@ -839,15 +658,15 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
             if (cl < a.ncells && (fits || (int)lane == round)) a.crmax[cl] = cm;
             ncoll_tot += ncoll;
         }
-        // C. write-out and moment sums (group lanes over the cell's particles)
+        // C. moment sums of the collided particles; the cell is written back in place in
+        // stable order (the collide, and cells the step's LB2DSMC regenerates), or moved on
         Real mo[kMoments];
 #pragma unroll
         for (int q = 0; q < kMoments; ++q) mo[q] = (Real)0;
+        const bool back = has_r && !moving;
         for (uint32_t k = gl; k < n; k += G) {
             const Real ux = vx[k], uy = vy[k], uz = vz[k];
-            a.dvx[base + k] = ux;
-            a.dvy[base + k] = uy;
-            a.dvz[base + k] = uz;
+            if (back) rec_put(a.drec, base + k, qx[k], qy[k], Z3 ? qz[k] : (Real)0, ux, uy, uz, 0u);
             if (do_sample) {
                 // the sums are compared with a tolerance, so they use fused multiply-adds
                 // (this file is otherwise compiled without contraction); mo[0] is the count
@@ -888,8 +707,66 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
                 }
             }
         }
+        if constexpr (MODE == MODE_FUSED) {
+            // the move of step s + 1, straight from the pool: particle k of cell c, two per
+            // lane, into the bins of half p with its origin slot as its stable-order key
+            const MoveCtx<Real> m = move_ctx(a);
+            const Half<Real> dst = half_s(a);
+            const uint32_t nm = moving && act ? n : 0u;
+            const uint32_t nmax = __reduce_max_sync(kFull, nm);
+            for (uint32_t k0 = 0; k0 < nmax; k0 += 2 * G) {
+                const uint32_t k1 = k0 + (uint32_t)gl, k2 = k1 + G;
+                const bool act1 = k1 < nm, act2 = k2 < nm;
+                Real p1[6] = {0, 0, 0, 0, 0, 0}, p2[6] = {0, 0, 0, 0, 0, 0};
+                if (act1) {
+                    p1[0] = qx[k1]; p1[1] = qy[k1]; if constexpr (Z3) p1[2] = qz[k1];
+                    p1[3] = vx[k1]; p1[4] = vy[k1]; p1[5] = vz[k1];
+                }
+                if (act2) {
+                    p2[0] = qx[k2]; p2[1] = qy[k2]; if constexpr (Z3) p2[2] = qz[k2];
+                    p2[3] = vx[k2]; p2[4] = vy[k2]; p2[5] = vz[k2];
+                }
+                uint32_t key1 = 0, key2 = 0;
+                int dir1 = -1, dir2 = -1;
+                if (act1)
+                    key1 = move_particle<Real, Z3>(m, gc, k1, s + 1u, p1[0], p1[1], p1[2], p1[3], p1[4],
+                                                   p1[5], hits, caps, dir1);
+                if (act2)
+                    key2 = move_particle<Real, Z3>(m, gc, k2, s + 1u, p2[0], p2[1], p2[2], p2[3], p2[4],
+                                                   p2[5], hits, caps, dir2);
+                const bool loc1 = act1 && dir1 < 0, loc2 = act2 && dir2 < 0;
+                uint32_t arr1, arr2;
+                bin_arrival2(dst.count, key1, loc1, key2, loc2, lane, arr1, arr2);
+                if (loc1) {
+                    if (arr1 < bin)
+                        put_particle<Real, Z3>(dst, (int64_t)key1 * bin + arr1, (uint32_t)(gbase + k1),
+                                               p1[0], p1[1], p1[2], p1[3], p1[4], p1[5]);
+                    else
+                        lost += 1;
+                } else if (act1) {
+                    send_particle<Real, Z3>(a.xrec, a.xkey, a.xcount, a.xcap, dir1, key1,
+                                            (uint32_t)(gbase + k1), p1[0], p1[1], p1[2], p1[3], p1[4],
+                                            p1[5], lost);
+                }
+                if (loc2) {
+                    if (arr2 < bin)
+                        put_particle<Real, Z3>(dst, (int64_t)key2 * bin + arr2, (uint32_t)(gbase + k2),
+                                               p2[0], p2[1], p2[2], p2[3], p2[4], p2[5]);
+                    else
+                        lost += 1;
+                } else if (act2) {
+                    send_particle<Real, Z3>(a.xrec, a.xkey, a.xcount, a.xcap, dir2, key2,
+                                            (uint32_t)(gbase + k2), p2[0], p2[1], p2[2], p2[3], p2[4],
+                                            p2[5], lost);
+                }
+            }
+            // the arrivals of half p^1 are consumed: their count starts the next step's
+            // arrivals (a regenerated cell's count is consumed by LB2DSMC)
+            if (moving && act && gl == 0) a.count_d[c] = 0;
+        }
         __syncthreads();  // the pool is reused by the next round
     }
+    if constexpr (MODE == MODE_FUSED) move_events(a.counters, a.ctrl, hits, caps, lost, lane);
     // event counters: per block, one atomic per counter
     ncand_tot = __reduce_add_sync(kFull, (unsigned)ncand_tot);
     ncoll_tot = __reduce_add_sync(kFull, (unsigned)ncoll_tot);
@@ -913,14 +790,16 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
         }
         if (c0) atomicAdd(&a.counters[HYB_C_CANDIDATES], c0);
         if (c1) atomicAdd(&a.counters[HYB_C_COLLISIONS], c1);
-        if (nl) atomicAdd(&a.ctrl[CTRL_NTOT], nl);
+        if (nl) atomicAdd(&a.ctrl[CTRL_NACC], nl);
         if (fl) atomicOr(&a.ctrl[CTRL_STATUS], fl);
-        // the last block to finish advances the step and sample counters (every block has
-        // read the step by now; nothing written by other blocks is read here, so no fence
-        // is needed before the ticket)
+        // the last block to finish publishes the particle count and advances the step and
+        // sample counters (every block has read the step by now); the fence orders this
+        // block's count before its ticket
+        __threadfence();
         const unsigned ticket = atomicAdd(&a.ctrl[CTRL_TICKET], 1u);
         if (ticket == nblk - 1) {
             __threadfence();
+            a.ctrl[CTRL_NTOT] = atomicExch(&a.ctrl[CTRL_NACC], 0u);
             if (do_sample) a.ctrl[CTRL_NSAMPLES] += 1;
             a.ctrl[CTRL_STEP] = s + 1;
             a.ctrl[CTRL_TICKET] = 0;
@@ -928,16 +807,83 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
     }
 }
 
-template <typename Real, bool BATCH, bool Z3 = false>
+template <typename Real, bool BATCH, bool Z3 = false, int MODE = MODE_COLLIDE>
 __global__ void __launch_bounds__(kCollideWarps * 32, CollideCfg<Real>::MINB)
     k_collide(Launch<DsmcArgs<Real>> L, uint32_t pool) {
     pdl_begin();
     if constexpr (BATCH) {
         const int r = replica_of(L.pre, L.nrep, (int64_t)blockIdx.x);
-        collide_block<Real, Z3>(L.tab[r], pool, (int)(blockIdx.x - L.pre[r]),
-                                (int)(L.pre[r + 1] - L.pre[r]));
+        collide_block<Real, Z3, MODE>(L.tab[r], pool, (int)(blockIdx.x - L.pre[r]),
+                                      (int)(L.pre[r + 1] - L.pre[r]));
     } else {
-        collide_block<Real, Z3>(L.one, pool, (int)blockIdx.x, (int)gridDim.x);
+        collide_block<Real, Z3, MODE>(L.one, pool, (int)blockIdx.x, (int)gridDim.x);
+    }
+}
+
+// Appends the particles a streamwise slab received from its neighbours (records and channel
+// cells from the slab below, then above) to the bins of their cells in half p^1, after the
+// slab's move, with their stable-order keys; then clears the slab's own send counts for its
+// next move (the caller has copied its send buffers out by then). A received cell outside the
+// slab is skipped and raises HYB_ST_BAD_INPUT.
+template <typename Real, bool Z3>
+__global__ void __launch_bounds__(256) k_merge(DsmcArgs<Real> a) {
+    pdl_begin();
+    const unsigned lane = lane_id();
+    const uint32_t bin = (uint32_t)a.bin;
+    const Half<Real> dst = half_d(a);
+    const uint32_t cap = (uint32_t)a.xcap;
+    const uint32_t n0 = min(*a.rcount[0], cap), n1 = min(*a.rcount[1], cap);
+    const uint32_t total = n0 + n1;
+    const uint32_t nz = a.ncz ? (uint32_t)a.ncz : 1u;
+    uint32_t lost = 0, bad = 0;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32 * 32;
+    const int64_t wstride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = w0; i0 < (int64_t)total; i0 += wstride) {  // warp-uniform trip count
+        const int64_t i = i0 + lane;
+        bool loc = false;
+        uint32_t key = 0, tag = 0;
+        Real px = 0, py = 0, pz = 0, ux = 0, uy = 0, uz = 0;
+        if (i < (int64_t)total) {
+            const int d = i < (int64_t)n0 ? 0 : 1;
+            const int64_t j = d ? i - n0 : i;
+            rec_get(a.rrec[d], j, px, py, pz, ux, uy, uz, tag);
+            const uint32_t gk = a.rkey[d][j];
+            const uint32_t plane = (uint32_t)a.ncx * (uint32_t)a.ncy_g;
+            const uint32_t iz = gk / plane, r = gk - iz * plane;
+            const uint32_t iy = r / (uint32_t)a.ncx, ix = r - iy * (uint32_t)a.ncx;
+            const int iyl = (int)iy - a.y0;
+            if (iyl >= 0 && iyl < a.ncy && iz < nz) {
+                key = (iz * (uint32_t)a.ncy + (uint32_t)iyl) * (uint32_t)a.ncx + ix;
+                loc = true;
+            } else {
+                bad += 1;
+            }
+        }
+        const uint32_t arr = bin_arrival1(dst.count, key, loc, lane);
+        if (loc) {
+            if (arr < bin)
+                put_particle<Real, Z3>(dst, (int64_t)key * bin + arr, tag, px, py, pz, ux, uy, uz);
+            else
+                lost += 1;
+        }
+    }
+    lost = __reduce_add_sync(kFull, lost);
+    bad = __reduce_add_sync(kFull, bad);
+    if (lane == 0 && (lost | bad))
+        atomicOr(&a.ctrl[CTRL_STATUS], (lost ? HYB_ST_CAPACITY : 0u) | (bad ? HYB_ST_BAD_INPUT : 0u));
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *a.xcount[0] = 0u;
+        *a.xcount[1] = 0u;
+    }
+}
+
+// Sets coupled[cells[i]] = v for the listed cells (indices out of range are skipped).
+__global__ void k_mark_cells(uint8_t* coupled, const int32_t* cells, int32_t n, int64_t ncells,
+                             uint8_t v) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) {
+        const int32_t c = cells[i];
+        if (c >= 0 && (int64_t)c < ncells) coupled[c] = v;
     }
 }
 
@@ -945,18 +891,8 @@ template <typename Real>
 DsmcArgs<Real> make_args(Ctx& c) {
     DsmcArgs<Real> a{};
     const int h = c.cur_p, o = c.cur_p ^ 1;
-    a.sx = (const Real*)c.st.px[h];
-    a.sy = (const Real*)c.st.py[h];
-    a.svx = (const Real*)c.st.pvx[h];
-    a.svy = (const Real*)c.st.pvy[h];
-    a.svz = (const Real*)c.st.pvz[h];
-    a.rec = (Real*)c.st.moved;
-    a.dx = (Real*)c.st.px[o];
-    a.dy = (Real*)c.st.py[o];
-    a.dvx = (Real*)c.st.pvx[o];
-    a.dvy = (Real*)c.st.pvy[o];
-    a.dvz = (Real*)c.st.pvz[o];
-    a.tag = c.st.tag;
+    a.srec = (Real*)c.st.part[h];
+    a.drec = (Real*)c.st.part[o];
     a.count_s = c.st.count[h];
     a.count_d = c.st.count[o];
     a.crmax = (Real*)c.st.crmax;
@@ -965,6 +901,7 @@ DsmcArgs<Real> make_args(Ctx& c) {
     a.acc = c.st.acc;
     a.ctrl = c.st.ctrl;
     a.counters = c.st.counters;
+    a.coupled = c.st.coupled;
     a.ncx = c.p.ncx;
     a.ncy = c.p.ncy;
     a.ncells = (int32_t)c.d.ncells;
@@ -978,11 +915,23 @@ DsmcArgs<Real> make_args(Ctx& c) {
     a.g_r = (Real)c.d.g_step;
     a.coll_r = (Real)c.d.coll_dt;
     a.coll_cell = (const Real*)c.st.coll_cell;
-    a.sz = (const Real*)c.st.pz[h];
-    a.dz = (Real*)c.st.pz[o];
     a.ncz = c.p.ncz >= 2 ? c.p.ncz : 0;
     a.crmax_init = c.p.crmax_init;
     a.seed = c.p.seed;
+    a.y0 = c.p.ncy_global > 0 ? c.p.y0 : 0;
+    a.ncy_g = c.p.ncy_global > 0 ? c.p.ncy_global : c.p.ncy;
+    a.xcap = (int32_t)c.d.xcap;
+    for (int d = 0; d < 2; ++d) {
+        char* xs = c.st.xsend[d];
+        char* xr = c.st.xrecv[d];
+        const size_t keys = 256 + (size_t)c.d.xcap * kRec * sizeof(Real);
+        a.xcount[d] = c.d.xcap ? (uint32_t*)xs : nullptr;
+        a.xrec[d] = c.d.xcap ? (Real*)(xs + 256) : nullptr;
+        a.xkey[d] = c.d.xcap ? (uint32_t*)(xs + keys) : nullptr;
+        a.rcount[d] = c.d.xcap ? (const uint32_t*)xr : nullptr;
+        a.rrec[d] = c.d.xcap ? (const Real*)(xr + 256) : nullptr;
+        a.rkey[d] = c.d.xcap ? (const uint32_t*)(xr + keys) : nullptr;
+    }
     return a;
 }
 
@@ -994,6 +943,15 @@ int grid_for(const Ctx& c, int64_t work, int threads, int per_sm) {
     return (int)g;
 }
 
+// Shared memory of a collide block: the pool (pool_reals Real and one u32 per slot) and one
+// pass of NTC candidates (u32 and 4 Real each).
+template <typename Real, bool Z3>
+size_t collide_smem(uint32_t pool) {
+    constexpr int NC = kCollideWarps * (32 / kGroup);
+    return (size_t)pool * (pool_reals<Z3>() * sizeof(Real) + 4) +
+           (size_t)NC * kChainSteps * (4 + 4 * sizeof(Real));
+}
+
 template <typename Real>
 cudaError_t init_impl(Ctx& c) {
     // the initial particles go to half 0: arguments built with half 1 as the source
@@ -1003,40 +961,52 @@ cudaError_t init_impl(Ctx& c) {
     const int64_t n = c.d.ncells * c.p.ppc;
     k_init_particles<Real><<<grid_for(c, n, 256, 16), 256, 0, c.stream>>>(a);
     k_init_cells<Real><<<grid_for(c, c.d.ncells, 256, 16), 256, 0, c.stream>>>(a);
+    if (c.st.coupled) cudaMemsetAsync(c.st.coupled, 0, (size_t)c.d.ncells, c.stream);
+    for (int d = 0; d < 2 && c.d.xcap; ++d) {  // the exchange counts start at zero
+        cudaMemsetAsync(c.st.xsend[d], 0, 4, c.stream);
+        cudaMemsetAsync(c.st.xrecv[d], 0, 4, c.stream);
+    }
     return cudaGetLastError();
 }
 
 template <typename Real, bool Z3>
-cudaError_t step_impl(Ctx& c) {
-    DsmcArgs<Real> a = make_args<Real>(c);
+cudaError_t move_impl(Ctx& c, int p) {
+    const int save = c.cur_p;
+    c.cur_p = p;
+    Launch<DsmcArgs<Real>> L{};
+    L.one = make_args<Real>(c);
+    c.cur_p = save;
+    L.total = c.d.ncells;
     prof_begin(c, K_MOVE);
     // one source cell per warp (the hardware schedules the blocks as resources free up)
-    Launch<DsmcArgs<Real>> L{};
-    L.one = a;
-    L.total = c.d.ncells;
-    cudaError_t e = launch_pdl(k_move<Real, false, Z3>, dim3(grid_for(c, c.d.ncells * 32, 256, 64)),
-                               dim3(256), 0, c.stream, L);
-    if (e != cudaSuccess) return e;
+    const cudaError_t e = launch_pdl(k_move<Real, false, Z3>, dim3(grid_for(c, c.d.ncells * 32, 256, 64)),
+                                     dim3(256), 0, c.stream, L);
     prof_end(c, K_MOVE);
-    // shared memory: a pool of slots for the block's cells (3 Real + 1 u32 each), room for
-    // 1.5 ppc per cell on average and at least one full bin, then one pass of NTC candidates
+    return e;
+}
+
+template <typename Real, bool Z3, int MODE>
+cudaError_t collide_impl(Ctx& c, int p) {
+    const int save = c.cur_p;
+    c.cur_p = p;
+    Launch<DsmcArgs<Real>> L{};
+    L.one = make_args<Real>(c);
+    c.cur_p = save;
     constexpr int NC = kCollideWarps * (32 / kGroup);
-    uint32_t pool = (uint32_t)(((int64_t)NC * c.p.ppc * 3 / 2 + 31) / 32 * 32);
-    if (pool < (uint32_t)c.d.bin) pool = (uint32_t)c.d.bin;
-    const size_t smem = (size_t)pool * (3 * sizeof(Real) + 4) +
-                        (size_t)NC * kChainSteps * (4 + 4 * sizeof(Real));
+    const uint32_t pool = collide_pool(c);
+    const size_t smem = collide_smem<Real, Z3>(pool);
     // (dynamic and static shared memory together may exceed the default 48 KB)
-    e = cudaFuncSetAttribute(k_collide<Real, false, Z3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_collide<Real, false, Z3, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)((c.d.ncells + NC - 1) / NC);
-    prof_begin(c, K_COLLIDE);
     L.total = grid;
-    e = launch_pdl(k_collide<Real, false, Z3>, dim3(grid), dim3(kCollideWarps * 32), smem, c.stream, L,
-                   pool);
-    if (e != cudaSuccess) return e;
-    prof_end(c, K_COLLIDE);
-    return cudaGetLastError();
+    constexpr int kid = MODE == MODE_FUSED ? K_FUSED : K_COLLIDE;
+    prof_begin(c, kid);
+    e = launch_pdl(k_collide<Real, false, Z3, MODE>, dim3(grid), dim3(kCollideWarps * 32), smem,
+                   c.stream, L, pool);
+    prof_end(c, kid);
+    return e;
 }
 
 __global__ void k_debug_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out, int64_t n) {
@@ -1061,9 +1031,56 @@ cudaError_t launch_init(Ctx& c) {
     return launch_lbm_init(c);
 }
 
+cudaError_t launch_dsmc_move(Ctx& c, int p) {
+    if (c.p.ncz >= 2) return c.p.real_bytes == 4 ? move_impl<float, true>(c, p) : move_impl<double, true>(c, p);
+    return c.p.real_bytes == 4 ? move_impl<float, false>(c, p) : move_impl<double, false>(c, p);
+}
+
+cudaError_t launch_dsmc_collide(Ctx& c, int p) {
+    if (c.p.ncz >= 2)
+        return c.p.real_bytes == 4 ? collide_impl<float, true, MODE_COLLIDE>(c, p)
+                                   : collide_impl<double, true, MODE_COLLIDE>(c, p);
+    return c.p.real_bytes == 4 ? collide_impl<float, false, MODE_COLLIDE>(c, p)
+                               : collide_impl<double, false, MODE_COLLIDE>(c, p);
+}
+
+cudaError_t launch_dsmc_fused(Ctx& c, int p) {
+    if (c.p.ncz >= 2)
+        return c.p.real_bytes == 4 ? collide_impl<float, true, MODE_FUSED>(c, p)
+                                   : collide_impl<double, true, MODE_FUSED>(c, p);
+    return c.p.real_bytes == 4 ? collide_impl<float, false, MODE_FUSED>(c, p)
+                               : collide_impl<double, false, MODE_FUSED>(c, p);
+}
+
 cudaError_t launch_dsmc_step(Ctx& c) {
-    if (c.p.ncz >= 2) return (c.p.real_bytes == 4) ? step_impl<float, true>(c) : step_impl<double, true>(c);
-    return (c.p.real_bytes == 4) ? step_impl<float, false>(c) : step_impl<double, false>(c);
+    cudaError_t e = launch_dsmc_move(c, c.cur_p);
+    if (e != cudaSuccess) return e;
+    return launch_dsmc_collide(c, c.cur_p);
+}
+
+namespace {
+template <typename Real, bool Z3>
+cudaError_t merge_impl(Ctx& c, int p) {
+    const int save = c.cur_p;
+    c.cur_p = p;
+    const DsmcArgs<Real> a = make_args<Real>(c);
+    c.cur_p = save;
+    return launch_pdl(k_merge<Real, Z3>, dim3(grid_for(c, c.d.xcap * 2, 256, 4)), dim3(256), 0,
+                      c.stream, a);
+}
+}  // namespace
+
+cudaError_t launch_dsmc_merge(Ctx& c, int p) {
+    if (!c.d.xcap) return cudaSuccess;
+    if (c.p.ncz >= 2) return c.p.real_bytes == 4 ? merge_impl<float, true>(c, p) : merge_impl<double, true>(c, p);
+    return c.p.real_bytes == 4 ? merge_impl<float, false>(c, p) : merge_impl<double, false>(c, p);
+}
+
+cudaError_t launch_mark_cells(Ctx& c, const int32_t* cells, int32_t n, uint8_t v) {
+    if (n <= 0) return cudaSuccess;
+    k_mark_cells<<<(unsigned)((n + 255) / 256), 256, 0, c.stream>>>(c.st.coupled, cells, n,
+                                                                    c.d.ncells, v);
+    return cudaGetLastError();
 }
 
 size_t dsmc_args_bytes(int real_bytes) {
@@ -1083,9 +1100,11 @@ void dsmc_args_fill(Ctx& c, int cur_p, void* out) {
     c.cur_p = save;
 }
 
+// Pool slots of a collide block: room for 1.25 ppc per cell on average (the 32 cells' counts
+// add up to about 32 ppc with a spread of sqrt(32 ppc)), and at least one full bin.
 uint32_t collide_pool(const Ctx& c) {
     constexpr int NC = kCollideWarps * (32 / kGroup);
-    uint32_t pool = (uint32_t)(((int64_t)NC * c.p.ppc * 3 / 2 + 31) / 32 * 32);
+    uint32_t pool = (uint32_t)(((int64_t)NC * c.p.ppc * 11 / 10 + 31) / 32 * 32);
     if (pool < (uint32_t)c.d.bin) pool = (uint32_t)c.d.bin;
     return pool;
 }
@@ -1105,13 +1124,12 @@ cudaError_t batch_move_impl(BatchDev& b, int cur_p) {
 
 template <typename Real>
 cudaError_t batch_collide_impl(BatchDev& b, int cur_p) {
-    constexpr int NC = kCollideWarps * (32 / kGroup);
     Launch<DsmcArgs<Real>> L{};
     L.tab = (const DsmcArgs<Real>*)b.dsmc[cur_p];
     L.pre = b.pre_blocks;
     L.nrep = b.nrep;
     L.total = b.tot_blocks;
-    const size_t smem = (size_t)b.pool * (3 * sizeof(Real) + 4) + (size_t)NC * kChainSteps * (4 + 4 * sizeof(Real));
+    const size_t smem = collide_smem<Real, false>(b.pool);
     cudaError_t e = cudaFuncSetAttribute(k_collide<Real, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;

@@ -867,6 +867,76 @@ cudaError_t launch_batch_lbm(BatchDev& b, int cur_f) {
     return b.real_bytes == 4 ? batch_lbm_impl<float, D3Q19>(b, cur_f) : batch_lbm_impl<double, D3Q19>(b, cur_f);
 }
 
+namespace {
+
+// The LB ghost rows of a streamwise slab (Sec. 3.1: the channel is periodic streamwise; a slab
+// holds a range of its rows). side 0 is the slab's lower boundary, side 1 its upper one.
+// Pack: the populations a neighbour pulls across that boundary (e_y < 0 at the lower, e_y > 0
+// at the upper boundary) from the |e_y| rows of the slab next to it, into buf. Unpack: the
+// same populations of the neighbour's rows into the ghost rows (e_y > 0 below the lower
+// boundary, e_y < 0 above the upper one). buf holds, for each such q in ascending order, the
+// rows at distance k = 0 .. |e_y| - 1 from the boundary, each nz x nx (x fastest).
+template <typename Real, class LAT>
+__global__ void k_halo(Real* __restrict__ f, Real* __restrict__ buf, int nx, int ny, int nz, int yh,
+                       int64_t nn, int side, int unpack) {
+    const int64_t plane = (int64_t)nz * nx;
+    const bool neg = (side == 0) != (unpack != 0);  // the sign of e_y of the populations in buf
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < plane;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int z = (int)(t / nx), x = (int)(t % nx);
+        int64_t off = 0;
+        static_for<LAT::Q>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            constexpr int ey = E<LAT>(q, 1);
+            const int e = neg ? -ey : ey;
+            for (int k = 0; k < e; ++k) {
+                const int y = unpack ? (side == 0 ? yh - 1 - k : ny - yh + k)
+                                     : (side == 0 ? yh + k : ny - yh - 1 - k);
+                const int64_t node = ((int64_t)z * ny + y) * nx + x;
+                const int64_t bi = off + (int64_t)k * plane + t;
+                if (unpack)
+                    f[(int64_t)q * nn + node] = buf[bi];
+                else
+                    buf[bi] = f[(int64_t)q * nn + node];
+            }
+            if (e > 0) off += (int64_t)e * plane;
+        });
+    }
+}
+
+// Values per side: sum over q of max(e_y, 0), times nz nx.
+template <class LAT>
+int64_t halo_rows() {
+    int64_t s = 0;
+    for (int q = 0; q < LAT::Q; ++q) s += LatTab<LAT>::e(q, 1) > 0 ? LatTab<LAT>::e(q, 1) : 0;
+    return s;
+}
+
+template <typename Real, class LAT>
+cudaError_t halo_impl(Ctx& c, int side, void* buf, int unpack) {
+    const int64_t plane = c.d.nz * c.d.nx;
+    int64_t g = (plane + 255) / 256;
+    if (g > (int64_t)c.num_sms * 8) g = (int64_t)c.num_sms * 8;
+    k_halo<Real, LAT><<<(unsigned)g, 256, 0, c.stream>>>((Real*)c.st.f[c.cur_f], (Real*)buf,
+                                                          (int)c.d.nx, (int)c.d.ny, (int)c.d.nz,
+                                                          (int)c.d.yh, c.d.nnodes, side, unpack);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int64_t lbm_halo_values(const Ctx& c) {
+    return (c.p.lattice == 39 ? halo_rows<D3Q39>() : halo_rows<D3Q19>()) * c.d.nz * c.d.nx;
+}
+
+cudaError_t launch_lbm_halo(Ctx& c, int side, void* buf, int unpack) {
+    if (c.p.lattice == 39)
+        return c.p.real_bytes == 4 ? halo_impl<float, D3Q39>(c, side, buf, unpack)
+                                   : halo_impl<double, D3Q39>(c, side, buf, unpack);
+    return c.p.real_bytes == 4 ? halo_impl<float, D3Q19>(c, side, buf, unpack)
+                               : halo_impl<double, D3Q19>(c, side, buf, unpack);
+}
+
 cudaError_t launch_lbm_step(Ctx& c) {
     if (c.p.lattice == 39)
         return c.p.real_bytes == 4 ? lbm_impl<float, D3Q39>(c) : lbm_impl<double, D3Q39>(c);

@@ -24,7 +24,7 @@
 #include <cstring>
 #include <mutex>
 
-#include "hyb_internal.cuh"
+#include "dsmc_move.cuh"
 
 // Fixed scratch of map_lbm_to_dsmc_noalloc: one Grad record per coupling cell, for callers
 // that cannot hand the library any device memory beyond the state itself. The array lives
@@ -90,8 +90,13 @@ __device__ __forceinline__ void d2l_entries(const MapArgs<Real>& a, int first, i
             if (lane == 0) atomicOr(&a.ctrl[CTRL_STATUS], HYB_ST_BAD_INPUT);
             continue;
         }
-        // node (z ny + y) nx + x lies in cell (iz ncy + iy) ncx + ix (z = 0 in 2D)
-        const int x = node % a.nx, y = (node / a.nx) % a.ny, z = node / (a.nx * a.ny);
+        // node (z ny + y) nx + x lies in cell (iz ncy + iy) ncx + ix (z = 0 in 2D); a slab's
+        // ghost rows (the yh rows below and above its own) belong to no cell of the context
+        const int x = node % a.nx, y = (node / a.nx) % a.ny - a.yh, z = node / (a.nx * a.ny);
+        if (y < 0 || y >= a.ncy * a.lb_ratio) {
+            if (lane == 0) atomicOr(&a.ctrl[CTRL_STATUS], HYB_ST_BAD_INPUT);
+            continue;
+        }
         const int64_t cell =
             ((int64_t)(z / a.lb_ratio) * a.ncy + y / a.lb_ratio) * a.ncx + (x / a.lb_ratio);
         const double* m = a.acc + cell * kMoments;
@@ -266,7 +271,11 @@ __device__ __forceinline__ void d2l_adjoint_entries(const MapArgs<Real>& a, Real
             if (lane == 0) atomicOr(&a.ctrl[CTRL_STATUS], HYB_ST_BAD_INPUT);
             continue;
         }
-        const int x = node % a.nx, y = (node / a.nx) % a.ny, z = node / (a.nx * a.ny);
+        const int x = node % a.nx, y = (node / a.nx) % a.ny - a.yh, z = node / (a.nx * a.ny);
+        if (y < 0 || y >= a.ncy * a.lb_ratio) {
+            if (lane == 0) atomicOr(&a.ctrl[CTRL_STATUS], HYB_ST_BAD_INPUT);
+            continue;
+        }
         const int64_t cell =
             ((int64_t)(z / a.lb_ratio) * a.ncy + y / a.lb_ratio) * a.ncx + (x / a.lb_ratio);
         Real v[32];
@@ -411,7 +420,7 @@ __device__ __forceinline__ void grad_coefficients(const MapArgs<Real>& a, int ce
         if (k < nk) {
             const int dz = Z3 ? k / (r * r) : 0, dy = (k / r) % r, dx = k % r;
             const int64_t node =
-                ((int64_t)(iz * r + dz) * a.ny + (iy * r + dy)) * a.nx + (ix * r + dx);
+                ((int64_t)(iz * r + dz) * a.ny + (iy * r + dy + a.yh)) * a.nx + (ix * r + dx);
             if (v0) p0[k] = a.f[(int64_t)q0 * a.nnodes + node];
             if (v1) p1[k] = a.f[(int64_t)q1 * a.nnodes + node];
         }
@@ -477,7 +486,29 @@ __device__ __forceinline__ void grad_coefficients(const MapArgs<Real>& a, int ce
 // cell index is skipped and flagged; a cell whose new count exceeds its bin keeps its
 // particles and raises the capacity status. The Grad record of each listed cell is written
 // to a.grad.
-template <typename Real, class LAT, bool Z3>
+// MOVE (the fused multi-step pass): the listed cells' particles were left in the half of
+// x.. (counts `count`) by the fused pass, the new particles are moved on at once (the move of
+// the next step, keyed like the particle's slot) into the bins of the half of ax.. with their
+// origin slots as stable-order keys, and a kept cell's particles are moved on likewise.
+template <typename Real, bool Z3>
+__device__ __forceinline__ MoveCtx<Real> l2d_move_ctx(const MapArgs<Real>& a) {
+    MoveCtx<Real> m;
+    m.H = (Real)a.ncx;
+    // the fused pass (and so this move) runs on contexts that hold the whole channel
+    m.L = (Real)a.ncy;
+    m.Lz = (Real)(a.ncz ? a.ncz : 1);
+    m.dt = a.dt_r;
+    m.g = a.g_r;
+    m.ncx = a.ncx;
+    m.ncy = a.ncy;
+    m.y0 = 0;
+    m.nly = a.ncy;
+    m.ncz = a.ncz;
+    m.seed = a.seed;
+    return m;
+}
+
+template <typename Real, class LAT, bool Z3, bool MOVE = false>
 __device__ __forceinline__ void l2d_cells(const MapArgs<Real>& a, int first, int stride) {
     __shared__ unsigned s_am[kL2DWarps], s_em[kL2DWarps], s_vm[kL2DWarps];
     __shared__ Real s_c[20];
@@ -490,6 +521,8 @@ __device__ __forceinline__ void l2d_cells(const MapArgs<Real>& a, int first, int
     unsigned long long deleted = 0, created = 0, attempts = 0, envelope = 0;
     uint32_t flags = 0;
     int32_t dlive = 0;
+    uint32_t hits = 0, caps = 0, lost = 0;  // moves of the fused pass
+    const Half<Real> dst{a.arec, a.acount};
     for (int ci = first; ci < a.n; ci += stride) {
         const int32_t icell = a.list[ci];
         if (icell < 0 || icell >= a.ncx * a.ncy * (Z3 ? a.ncz : 1)) {
@@ -497,6 +530,8 @@ __device__ __forceinline__ void l2d_cells(const MapArgs<Real>& a, int first, int
             continue;
         }
         const uint32_t cell = (uint32_t)icell;
+        // the channel's cell: the key of the cell's random streams and of the stable order
+        const uint32_t gcell = global_cell(cell, a.ncx, a.ncy, a.y0, a.ncy_g);
         const uint32_t old = threadIdx.x == 0 ? a.count[cell] : 0u;
         if (w == 0) {
             double mine, rho;
@@ -507,7 +542,7 @@ __device__ __forceinline__ void l2d_cells(const MapArgs<Real>& a, int first, int
                 g.v[lane] = mine;
             }
             if (lane == 0) {
-                const double ur = u01d(draw(a.seed, cell, t_step, TAG_L2D_ROUND, 0, 0).x);
+                const double ur = u01d(draw(a.seed, gcell, t_step, TAG_L2D_ROUND, 0, 0).x);
                 const double ne = floor(rho * (double)a.ppc + ur);
                 const uint32_t nnew = ne > 0.0 ? (uint32_t)ne : 0u;
                 s_nnew = nnew;
@@ -526,13 +561,41 @@ __device__ __forceinline__ void l2d_cells(const MapArgs<Real>& a, int first, int
         const Real C = s_c[GR_C];
         const Real ux = s_c[GR_U], uy = s_c[GR_U + 1], uz = s_c[GR_U + 2];
         __syncthreads();  // s_c and s_nnew are rewritten for the next cell
+        const int64_t out0 = (int64_t)cell * bin;
         if (nnew > bin) {  // the cell keeps its particles
             flags |= HYB_ST_CAPACITY;
+            if constexpr (MOVE) {
+                // ... and moves them on; the cell's count is read by every thread
+                uint32_t nold = a.count[cell];
+                if (nold > bin) nold = bin;
+                const MoveCtx<Real> m = l2d_move_ctx<Real, Z3>(a);
+                for (uint32_t k0 = 0; k0 < nold; k0 += kL2DWarps * 32) {
+                    const uint32_t k = k0 + threadIdx.x;
+                    const bool act = k < nold;
+                    Real px = 0, py = 0, pz = 0, ux = 0, uy = 0, uz = 0;
+                    uint32_t key = 0, tg;
+                    if (act) {
+                        rec_get(a.rec, out0 + k, px, py, pz, ux, uy, uz, tg);
+                        int dir;
+                        key = move_particle<Real, Z3>(m, gcell, k, t_step, px, py, pz, ux, uy, uz, hits, caps,
+                                                      dir);
+                    }
+                    const uint32_t arr = bin_arrival1(dst.count, key, act, lane);
+                    if (act) {
+                        if (arr < bin)
+                            put_particle<Real, Z3>(dst, (int64_t)key * bin + arr, (uint32_t)(gcell * bin + k), px,
+                                                   py, pz, ux, uy, uz);
+                        else
+                            lost += 1;
+                    }
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) a.count[cell] = 0;
+            }
             continue;
         }
-        const int64_t out0 = (int64_t)cell * bin;
         const Real fx = (Real)(cell % (uint32_t)a.ncx);
-        const Real fy = (Real)((cell / (uint32_t)a.ncx) % (uint32_t)a.ncy);
+        const Real fy = (Real)(a.y0 + (int)((cell / (uint32_t)a.ncx) % (uint32_t)a.ncy));
         const Real fz = Z3 ? (Real)(cell / ((uint32_t)a.ncx * (uint32_t)a.ncy)) : (Real)0;
         const uint64_t cap64 = 1000ull * nnew;
         const uint32_t cap = cap64 < 0xFFFFFFull ? (uint32_t)cap64 : 0xFFFFFFu;
@@ -544,8 +607,8 @@ __device__ __forceinline__ void l2d_cells(const MapArgs<Real>& a, int first, int
             Real X = 0, Y = 0, Z = 0;
             uint4 r2 = make_uint4(0u, 0u, 0u, 0u);
             if (valid) {
-                const uint4 r1 = draw(a.seed, cell, t_step, TAG_L2D_VEL, j, 0);
-                r2 = draw(a.seed, cell, t_step, TAG_L2D_VEL, j, 1);
+                const uint4 r1 = draw(a.seed, gcell, t_step, TAG_L2D_VEL, j, 0);
+                r2 = draw(a.seed, gcell, t_step, TAG_L2D_VEL, j, 1);
                 Real spare;
                 gauss_pair<Real>(r1.x, r1.y, X, Y);
                 gauss_pair<Real>(r1.z, r1.w, Z, spare);
@@ -572,14 +635,35 @@ __device__ __forceinline__ void l2d_cells(const MapArgs<Real>& a, int first, int
             }
             const uint32_t need = nnew - produced;
             const uint32_t rank = before + (uint32_t)__popc(am & lt);
-            if (acc && rank < need) {
+            if constexpr (MOVE) {
+                // the new particle of slot produced + rank, moved on at once
+                const bool mk = acc && rank < need;
+                const uint32_t k = produced + rank;
+                Real px = 0, py = 0, pz = 0, vx = 0, vy = 0, vz = 0;
+                uint32_t key = 0;
+                if (mk) {
+                    px = fx + (Real)u01f(r2.y);
+                    py = fy + (Real)u01f(r2.z);
+                    if constexpr (Z3) pz = fz + (Real)u01f(r2.w);
+                    vx = X + ux;
+                    vy = Y + uy;
+                    vz = Z + uz;
+                    int dir;
+                    key = move_particle<Real, Z3>(l2d_move_ctx<Real, Z3>(a), gcell, k, t_step, px, py, pz,
+                                                  vx, vy, vz, hits, caps, dir);
+                }
+                const uint32_t arr = bin_arrival1(dst.count, key, mk, lane);
+                if (mk) {
+                    if (arr < bin)
+                        put_particle<Real, Z3>(dst, (int64_t)key * bin + arr, (uint32_t)(gcell * bin + k), px,
+                                               py, pz, vx, vy, vz);
+                    else
+                        lost += 1;
+                }
+            } else if (acc && rank < need) {
                 const int64_t slot = out0 + produced + rank;
-                a.x[slot] = fx + (Real)u01f(r2.y);
-                a.y[slot] = fy + (Real)u01f(r2.z);
-                if constexpr (Z3) a.z[slot] = fz + (Real)u01f(r2.w);
-                a.vx[slot] = X + ux;
-                a.vy[slot] = Y + uy;
-                a.vz[slot] = Z + uz;
+                rec_put(a.rec, slot, fx + (Real)u01f(r2.y), fy + (Real)u01f(r2.z),
+                        Z3 ? fz + (Real)u01f(r2.w) : (Real)0, X + ux, Y + uy, Z + uz, 0u);
             }
             if (w == 0) {
                 // trials consumed this round (up to the need-th accepted one, or all valid
@@ -625,9 +709,11 @@ __device__ __forceinline__ void l2d_cells(const MapArgs<Real>& a, int first, int
             deleted += old;
             created += produced;
             dlive += (int32_t)produced - (int32_t)old;
-            a.count[cell] = produced;
+            // the fused pass's cell is consumed: its half's count starts the next arrivals
+            a.count[cell] = MOVE ? 0u : produced;
         }
     }
+    if constexpr (MOVE) move_events(a.counters, a.ctrl, hits, caps, lost, lane);
     flags = __reduce_or_sync(kFull, flags);
     if (threadIdx.x == 0) {
         if (deleted) atomicAdd(&a.counters[HYB_C_DELETED], deleted);
@@ -640,15 +726,15 @@ __device__ __forceinline__ void l2d_cells(const MapArgs<Real>& a, int first, int
 }
 
 // LB2DSMC: one block per listed cell (the listed cells of all replicas in the batch form).
-template <typename Real, class LAT, bool BATCH, bool Z3 = false>
+template <typename Real, class LAT, bool BATCH, bool Z3 = false, bool MOVE = false>
 __global__ void __launch_bounds__(kL2DWarps * 32) k_l2d(Launch<MapArgs<Real>> L) {
     pdl_begin();
     if constexpr (BATCH) {
         const int r = replica_of(L.pre, L.nrep, (int64_t)blockIdx.x);
         const MapArgs<Real>& a = L.tab[r];
-        l2d_cells<Real, LAT, Z3>(a, (int)(blockIdx.x - L.pre[r]), a.n);
+        l2d_cells<Real, LAT, Z3, MOVE>(a, (int)(blockIdx.x - L.pre[r]), a.n);
     } else {
-        l2d_cells<Real, LAT, Z3>(L.one, (int)blockIdx.x, (int)gridDim.x);
+        l2d_cells<Real, LAT, Z3, MOVE>(L.one, (int)blockIdx.x, (int)gridDim.x);
     }
 }
 
@@ -674,13 +760,11 @@ MapArgs<Real> map_args(Ctx& c, const int32_t* list, int32_t n) {
     a.counters = c.st.counters;
     a.grad = c.st.grad;
     a.count = c.st.count[c.cur_p];
-    a.x = (Real*)c.st.px[c.cur_p];
-    a.y = (Real*)c.st.py[c.cur_p];
-    a.vx = (Real*)c.st.pvx[c.cur_p];
-    a.vy = (Real*)c.st.pvy[c.cur_p];
-    a.vz = (Real*)c.st.pvz[c.cur_p];
+    a.rec = (Real*)c.st.part[c.cur_p];
     a.ncz = c.p.ncz >= 2 ? c.p.ncz : 0;
-    a.z = (Real*)c.st.pz[c.cur_p];
+    a.y0 = c.p.ncy_global > 0 ? c.p.y0 : 0;
+    a.ncy_g = c.p.ncy_global > 0 ? c.p.ncy_global : c.p.ncy;
+    a.yh = (int32_t)c.d.yh;
     return a;
 }
 
@@ -720,6 +804,30 @@ cudaError_t l2d_launch(Ctx& c, const MapArgs<Real>& a, int32_t n) {
 template <typename Real, class LAT>
 cudaError_t l2d_impl(Ctx& c, const int32_t* cells, int32_t n) {
     return l2d_launch<Real, LAT>(c, map_args<Real>(c, cells, n), n);
+}
+
+// LB2DSMC of the fused pass of parity p: the listed cells' particles are in half p^1, the
+// moved particles go to half p.
+template <typename Real, class LAT>
+cudaError_t l2d_move_impl(Ctx& c, const int32_t* cells, int32_t n, int p) {
+    const int save = c.cur_p;
+    c.cur_p = p ^ 1;
+    MapArgs<Real> a = map_args<Real>(c, cells, n);
+    c.cur_p = save;
+    a.arec = (Real*)c.st.part[p];
+    a.acount = c.st.count[p];
+    a.dt_r = (Real)c.d.dt;
+    a.g_r = (Real)c.d.g_step;
+    prof_begin(c, K_L2D);
+    Launch<MapArgs<Real>> L{};
+    L.one = a;
+    L.total = n;
+    const dim3 grid(blocks_for(c, (int64_t)n * 32 * kL2DWarps, 32 * kL2DWarps, 8));
+    const cudaError_t e =
+        a.ncz ? launch_pdl(k_l2d<Real, LAT, false, true, true>, grid, dim3(32 * kL2DWarps), 0, c.stream, L)
+              : launch_pdl(k_l2d<Real, LAT, false, false, true>, grid, dim3(32 * kL2DWarps), 0, c.stream, L);
+    prof_end(c, K_L2D);
+    return e;
 }
 
 constexpr int kMaxDevices = 64;
@@ -776,6 +884,14 @@ cudaError_t launch_gather_acc(Ctx& c, const int32_t* cells, int32_t n, double* o
     k_gather_acc<<<(unsigned)((total + 255) / 256), 256, 0, c.stream>>>(c.st.acc, cells, n,
                                                                         c.d.ncells, out);
     return cudaGetLastError();
+}
+
+cudaError_t launch_map_l2d_move(Ctx& c, const int32_t* cells, int32_t n, int p) {
+    if (c.p.lattice == 39)
+        return c.p.real_bytes == 4 ? l2d_move_impl<float, D3Q39>(c, cells, n, p)
+                                   : l2d_move_impl<double, D3Q39>(c, cells, n, p);
+    return c.p.real_bytes == 4 ? l2d_move_impl<float, D3Q19>(c, cells, n, p)
+                               : l2d_move_impl<double, D3Q19>(c, cells, n, p);
 }
 
 cudaError_t launch_map_l2d_noalloc(Ctx& c, const int32_t* cells, int32_t n) {

@@ -26,10 +26,19 @@ bool params_valid(const hyb_params* p) {
     if (p->kn_profile != 0 && p->kn_profile != 1) return false;
     if (p->kn_profile == 1 && !(p->kn_end > 0.0)) return false;
     if (p->ncz < 0) return false;
+    if (p->accum_mode != 0) return false;  // only FP64 moment sums are built
+    if (p->ncy_global < 0) return false;
+    if (p->ncy_global > 0) {  // a streamwise slab of a channel of ncy_global rows
+        if (p->y0 < 0 || p->ncy < 4 || (int64_t)p->y0 + p->ncy > p->ncy_global) return false;
+        if (p->kn_profile == 1 && p->ncy_global < 2) return false;
+    } else if (p->y0 != 0) {
+        return false;
+    }
     if (!(p->kn > 0.0) || !(p->crmax_init > 0.0) || !(p->capacity_factor >= 1.0)) return false;
     if (!(p->ma >= 0.0) || !(p->T_K > 0.0) || !(p->mass_kg > 0.0)) return false;
     if (std::ceil(p->capacity_factor * (double)p->ppc) > 256.0) return false;  // bin <= 256
-    const double slots = (double)p->ncx * (double)p->ncy * (double)(p->ncz >= 2 ? p->ncz : 1) * 256.0;
+    const double rows = p->ncy_global > 0 ? (double)p->ncy_global : (double)p->ncy;
+    const double slots = (double)p->ncx * rows * (double)(p->ncz >= 2 ? p->ncz : 1) * 256.0;
     if (slots >= 4294967295.0) return false;  // slot indices are u32
     return true;
 }
@@ -51,11 +60,14 @@ void derive(const hyb_params& p, hyb_derived& d) {
     d.ncz = p.ncz >= 2 ? p.ncz : 1;
     d.ncells = (int64_t)p.ncx * p.ncy * d.ncz;
     d.nx = (int64_t)p.ncx * p.lb_ratio;
-    d.ny = (int64_t)p.ncy * p.lb_ratio;
+    // a slab's lattice has yh ghost rows below and above its own rows
+    d.yh = p.ncy_global > 0 ? (p.lattice == 39 ? 3 : 1) : 0;
+    d.ny = (int64_t)p.ncy * p.lb_ratio + 2 * d.yh;
     d.nz = p.ncz >= 2 ? d.ncz * p.lb_ratio : 1;
     d.nnodes = d.nx * d.ny * d.nz;
     d.bin = ((int32_t)std::ceil(p.capacity_factor * (double)p.ppc) + 31) / 32 * 32;
     d.capacity = d.ncells * (int64_t)d.bin;
+    d.xcap = p.ncy_global > 0 ? (int64_t)p.ncx * d.ncz * d.bin : 0;
     d.q = p.lattice;
     d.order = (p.lattice == 39) ? 3 : 2;
 }
@@ -71,14 +83,7 @@ void layout(const hyb_params& p, const hyb_derived& d, hyb_layout& L) {
         off = (off + bytes + 255) & ~255ull;
         return o;
     };
-    for (int h = 0; h < 2; ++h) {
-        L.x[h] = take(cap * rb);
-        L.y[h] = take(cap * rb);
-        L.vx[h] = take(cap * rb);
-        L.vy[h] = take(cap * rb);
-        L.vz[h] = take(cap * rb);
-    }
-    L.tag = take(cap * 4);
+    for (int h = 0; h < 2; ++h) L.part[h] = take(cap * (uint64_t)kRec * rb);
     L.count[0] = take(nc * 4);
     L.count[1] = take(nc * 4);
     L.crmax = take(nc * rb);
@@ -89,11 +94,14 @@ void layout(const hyb_params& p, const hyb_derived& d, hyb_layout& L) {
     L.ctrl = take(CTRL_WORDS * 4);
     L.counters = take(HYB_NCOUNTERS * 8);
     L.map_scratch = take(nc * sizeof(GradRec));
-    L.moved = take(cap * 8 * rb);
+    L.coupled = take(nc);
+    // a slab's exchange buffers: a count, xcap records, xcap cell ids
+    L.xbytes = d.xcap > 0 ? 256 + (uint64_t)d.xcap * ((uint64_t)kRec * rb + 4) : 0;
+    for (int h = 0; h < 2; ++h) L.xsend[h] = take(L.xbytes);
+    for (int h = 0; h < 2; ++h) L.xrecv[h] = take(L.xbytes);
     const bool prof = p.kn_profile == 1;
     L.coll_cell = take(prof ? nc * rb : 0);
     L.tau_node = take(prof ? nn * rb : 0);
-    for (int h = 0; h < 2; ++h) L.z[h] = take(p.ncz >= 2 ? cap * rb : 0);
     L.total_bytes = off;
     L.capacity = d.capacity;
     L.ncells = d.ncells;
@@ -104,9 +112,10 @@ void layout(const hyb_params& p, const hyb_derived& d, hyb_layout& L) {
 }
 
 // Kn along the channel (kn_profile = 1): log-linear in the streamwise coordinate y (cell
-// units, period ncy) from kn at y = 0 to kn_end at y = ncy / 2.
+// units, period the channel's rows) from kn at y = 0 to kn_end at half the period.
 double kn_at(const hyb_params& p, double y) {
-    const double s = 1.0 - std::fabs(2.0 * y / (double)p.ncy - 1.0);
+    const double period = p.ncy_global > 0 ? (double)p.ncy_global : (double)p.ncy;
+    const double s = 1.0 - std::fabs(2.0 * y / period - 1.0);
     return p.kn * std::exp(s * std::log(p.kn_end / p.kn));
 }
 
@@ -175,16 +184,15 @@ void resolve(Ctx& c) {
     const hyb_layout& L = c.L;
     State& s = c.st;
     for (int h = 0; h < 2; ++h) {
-        s.px[h] = a + L.x[h];
-        s.py[h] = a + L.y[h];
-        s.pvx[h] = a + L.vx[h];
-        s.pvy[h] = a + L.vy[h];
-        s.pvz[h] = a + L.vz[h];
-        s.pz[h] = c.p.ncz >= 2 ? a + L.z[h] : nullptr;
+        s.part[h] = a + L.part[h];
         s.f[h] = a + L.f[h];
         s.count[h] = (uint32_t*)(a + L.count[h]);
     }
-    s.tag = (uint32_t*)(a + L.tag);
+    s.coupled = (uint8_t*)(a + L.coupled);
+    for (int d = 0; d < 2; ++d) {
+        s.xsend[d] = a + L.xsend[d];
+        s.xrecv[d] = a + L.xrecv[d];
+    }
     s.crmax = a + L.crmax;
     s.rem = a + L.rem;
     s.nbar_sum = (uint32_t*)(a + L.nbar_sum);
@@ -192,7 +200,6 @@ void resolve(Ctx& c) {
     s.ctrl = (uint32_t*)(a + L.ctrl);
     s.counters = (unsigned long long*)(a + L.counters);
     s.grad = (GradRec*)(a + L.map_scratch);
-    s.moved = a + L.moved;
     s.coll_cell = c.p.kn_profile == 1 ? a + L.coll_cell : nullptr;
     s.tau_node = c.p.kn_profile == 1 ? a + L.tau_node : nullptr;
 }
@@ -206,6 +213,53 @@ hyb_status do_dsmc_step(Ctx& c) {
 hyb_status do_lbm_step(Ctx& c) {
     hyb_status s = check(c, launch_lbm_step(c), "lbm_step launch");
     if (s == HYB_OK) flip_populations(c);
+    return s;
+}
+
+// n DSMC steps: the move of the first, then n - 1 fused passes (the collide of one step and
+// the move of the next), then the collide of the last. The particle parity flips once per step.
+hyb_status dsmc_steps(Ctx& c, int n) {
+    if (n <= 0) return HYB_OK;
+    int p = c.cur_p;
+    hyb_status s = check(c, launch_dsmc_move(c, p), "dsmc move launch");
+    for (int k = 1; k < n && s == HYB_OK; ++k) {
+        s = check(c, launch_dsmc_fused(c, p), "dsmc fused launch");
+        p ^= 1;
+    }
+    if (s == HYB_OK) s = check(c, launch_dsmc_collide(c, p), "dsmc collide launch");
+    if (s == HYB_OK) c.cur_p = p ^ 1;
+    return s;
+}
+
+// n hybrid steps in the order of one_hybrid_step, with the DSMC passes fused across steps:
+// move; then per step the fused pass (the last step: the collide), DSMC2LB, the LB step and
+// LB2DSMC, which within the fused run regenerates the coupling cells and moves their new
+// particles on at once. The coupling cells are marked for the fused passes for the call's
+// duration. The results equal n calls of one_hybrid_step bit for bit.
+hyb_status fused_hybrid_steps(Ctx& c, const int32_t* nodes, int32_t nn, const int32_t* cells,
+                              int32_t ncl, int n) {
+    if (n <= 0) return HYB_OK;
+    int p = c.cur_p;
+    hyb_status s = HYB_OK;
+    const bool mark = ncl > 0 && n > 1;
+    if (mark) s = check(c, launch_mark_cells(c, cells, ncl, 1), "mark coupling cells");
+    if (s == HYB_OK) s = check(c, launch_dsmc_move(c, p), "dsmc move launch");
+    for (int k = 0; k < n && s == HYB_OK; ++k) {
+        const bool last = k == n - 1;
+        s = last ? check(c, launch_dsmc_collide(c, p), "dsmc collide launch")
+                 : check(c, launch_dsmc_fused(c, p), "dsmc fused launch");
+        if (s == HYB_OK && nn > 0) s = check(c, launch_map_d2l(c, nodes, nn), "map_dsmc_to_lbm launch");
+        if (s == HYB_OK) s = do_lbm_step(c);
+        if (s != HYB_OK) break;
+        if (last) {
+            c.cur_p = p ^ 1;
+            if (ncl > 0) s = check(c, launch_map_l2d(c, cells, ncl), "map_lbm_to_dsmc launch");
+        } else {
+            if (ncl > 0) s = check(c, launch_map_l2d_move(c, cells, ncl, p), "map_lbm_to_dsmc launch");
+            p ^= 1;
+        }
+    }
+    if (s == HYB_OK && mark) s = check(c, launch_mark_cells(c, cells, ncl, 0), "clear coupling cells");
     return s;
 }
 
@@ -229,11 +283,16 @@ hyb_status fill_kn_profile(Ctx& c) {
     const int64_t nc = c.d.ncells, nn = c.d.nnodes;
     std::vector<double> cell(nc), node(nn);
     for (int64_t k = 0; k < nc; ++k) {
-        const double kn = kn_at(c.p, (double)((k / c.p.ncx) % c.p.ncy) + 0.5);
+        // the channel's row of the cell (a slab's rows start at y0)
+        const double kn = kn_at(c.p, (double)(c.p.y0 + (k / c.p.ncx) % c.p.ncy) + 0.5);
         cell[k] = c.d.dt / (std::sqrt(2.0) * (kn * (double)c.p.ncx) * (double)c.p.ppc);
     }
     for (int64_t k = 0; k < nn; ++k) {
-        const double kn = kn_at(c.p, ((double)((k / c.d.nx) % c.d.ny) + 0.5) / (double)c.p.lb_ratio);
+        // the channel's LB row of the node (a slab's ghost rows hold its neighbours' rows)
+        int64_t row = (int64_t)c.p.y0 * c.p.lb_ratio + (k / c.d.nx) % c.d.ny - c.d.yh;
+        const int64_t nrows = (int64_t)(c.p.ncy_global > 0 ? c.p.ncy_global : c.p.ncy) * c.p.lb_ratio;
+        row = ((row % nrows) + nrows) % nrows;
+        const double kn = kn_at(c.p, ((double)row + 0.5) / (double)c.p.lb_ratio);
         node[k] = std::sqrt(kPi / 8.0) * c.d.r_lat * kn * c.d.H_lat + 0.5;
     }
     auto put = [&](const std::vector<double>& v, void* dst) {
@@ -247,11 +306,65 @@ hyb_status fill_kn_profile(Ctx& c) {
 }
 
 void drop_graphs(Ctx& c) {
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 2; ++i) {
         if (c.graph[i]) {
             cudaGraphExecDestroy(c.graph[i]);
             c.graph[i] = nullptr;
         }
+        if (c.mgraph[i]) {
+            cudaGraphExecDestroy(c.mgraph[i]);
+            c.mgraph[i] = nullptr;
+        }
+        c.mkey[i][0] = c.mkey[i][1] = c.mkey[i][2] = -1;
+    }
+}
+
+// A multi-step fused hybrid call replayed from a graph captured on first use (per step
+// count and starting parities; the lists and profiling state are checked by the caller).
+hyb_status fused_graph_run(Ctx& c, const int32_t* nodes, int32_t nn, const int32_t* cells, int32_t ncl,
+                           int n) {
+    int slot = -1;
+    for (int i = 0; i < 2; ++i)
+        if (c.mgraph[i] && c.mkey[i][0] == n && c.mkey[i][1] == c.cur_p && c.mkey[i][2] == c.cur_f)
+            slot = i;
+    const int cp = c.cur_p, cf = c.cur_f;
+    if (slot < 0) {
+        slot = c.mnext;
+        c.mnext ^= 1;
+        if (c.mgraph[slot]) {
+            cudaGraphExecDestroy(c.mgraph[slot]);
+            c.mgraph[slot] = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        hyb_status s = check(c, cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal),
+                             "begin capture");
+        if (s != HYB_OK) return s;
+        c.capturing = true;
+        hyb_status s2 = fused_hybrid_steps(c, nodes, nn, cells, ncl, n);
+        c.capturing = false;
+        cudaError_t e = cudaStreamEndCapture(c.stream, &g);
+        c.cur_p = cp;
+        c.cur_f = cf;
+        if (s2 != HYB_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s2;
+        }
+        s = check(c, e, "end capture");
+        if (s != HYB_OK) return s;
+        e = cudaGraphInstantiate(&c.mgraph[slot], g, 0);
+        cudaGraphDestroy(g);
+        s = check(c, e, "graph instantiate");
+        if (s != HYB_OK) return s;
+        c.mkey[slot][0] = n;
+        c.mkey[slot][1] = cp;
+        c.mkey[slot][2] = cf;
+    }
+    hyb_status s = check(c, cudaGraphLaunch(c.mgraph[slot], c.stream), "graph launch");
+    if (s != HYB_OK) return s;
+    // each step flips both parities once
+    c.cur_p = cp ^ (n & 1);
+    c.cur_f = cf ^ (n & 1);
+    return HYB_OK;
 }
 
 }  // namespace
@@ -343,11 +456,53 @@ hyb_status dsmc_init(const hyb_params* p, void* arena, uint64_t arena_bytes, voi
 
 hyb_status dsmc_step(hyb_ctx* h, int32_t nsteps) {
     if (!h || nsteps < 0) return HYB_EINVAL;
-    for (int i = 0; i < nsteps; ++i) {
-        hyb_status s = do_dsmc_step(h->c);
-        if (s != HYB_OK) return s;
+    if (h->c.p.ncy_global > 0 || h->c.split_pending)
+        return fail(h->c, HYB_EINVAL, "dsmc_step: a slab steps with dsmc_move, dsmc_merge and dsmc_collide");
+    return dsmc_steps(h->c, nsteps);
+}
+
+hyb_status dsmc_move(hyb_ctx* h) {
+    if (!h) return HYB_EINVAL;
+    Ctx& c = h->c;
+    if (c.split_pending) return fail(c, HYB_ESTATE, "dsmc_move: the previous move has no collide yet");
+    hyb_status s = check(c, launch_dsmc_move(c, c.cur_p), "dsmc_move launch");
+    if (s == HYB_OK) c.split_pending = true;
+    return s;
+}
+
+hyb_status dsmc_merge(hyb_ctx* h) {
+    if (!h) return HYB_EINVAL;
+    Ctx& c = h->c;
+    if (!c.split_pending) return fail(c, HYB_ESTATE, "dsmc_merge: no move to merge into");
+    return check(c, launch_dsmc_merge(c, c.cur_p), "dsmc_merge launch");
+}
+
+hyb_status dsmc_collide(hyb_ctx* h) {
+    if (!h) return HYB_EINVAL;
+    Ctx& c = h->c;
+    if (!c.split_pending) return fail(c, HYB_ESTATE, "dsmc_collide: no move to collide");
+    hyb_status s = check(c, launch_dsmc_collide(c, c.cur_p), "dsmc_collide launch");
+    if (s == HYB_OK) {
+        c.split_pending = false;
+        flip_particles(c);
     }
+    return s;
+}
+
+hyb_status lbm_halo_size(const hyb_ctx* h, int64_t* values) {
+    if (!h || !values || h->c.d.yh == 0) return HYB_EINVAL;
+    *values = lbm_halo_values(h->c);
     return HYB_OK;
+}
+
+hyb_status lbm_halo_pack(hyb_ctx* h, int32_t side, void* dev_buf) {
+    if (!h || !dev_buf || (side != 0 && side != 1) || h->c.d.yh == 0) return HYB_EINVAL;
+    return check(h->c, launch_lbm_halo(h->c, side, dev_buf, 0), "lbm_halo_pack launch");
+}
+
+hyb_status lbm_halo_unpack(hyb_ctx* h, int32_t side, const void* dev_buf) {
+    if (!h || !dev_buf || (side != 0 && side != 1) || h->c.d.yh == 0) return HYB_EINVAL;
+    return check(h->c, launch_lbm_halo(h->c, side, (void*)dev_buf, 1), "lbm_halo_unpack launch");
 }
 
 hyb_status lbm_step(hyb_ctx* h, int32_t nsteps) {
@@ -446,16 +601,12 @@ hyb_status hyb_hybrid_step(hyb_ctx* h, const int32_t* dev_nodes, int32_t n_nodes
                            int32_t use_graph) {
     if (!h || nsteps < 0 || n_nodes < 0 || n_cells < 0) return HYB_EINVAL;
     Ctx& c = h->c;
+    if (c.p.ncy_global > 0 || c.split_pending)
+        return fail(c, HYB_EINVAL, "hyb_hybrid_step: a slab steps with the split calls");
     if ((n_nodes > 0 && !dev_nodes) || (n_cells > 0 && !dev_cells) || n_nodes > c.d.nnodes ||
         n_cells > c.d.ncells)
         return HYB_EINVAL;
-    if (!use_graph) {
-        for (int i = 0; i < nsteps; ++i) {
-            hyb_status s = one_hybrid_step(c, dev_nodes, n_nodes, dev_cells, n_cells);
-            if (s != HYB_OK) return s;
-        }
-        return HYB_OK;
-    }
+    if (!use_graph) return fused_hybrid_steps(c, dev_nodes, n_nodes, dev_cells, n_cells, nsteps);
     if (c.stream == nullptr) return fail(c, HYB_ESTATE, "graph replay needs a non-default stream");
     if (c.g_nodes != dev_nodes || c.g_cells != dev_cells || c.g_nn != n_nodes ||
         c.g_nc != n_cells || c.g_prof != c.prof_kernel) {
@@ -466,6 +617,9 @@ hyb_status hyb_hybrid_step(hyb_ctx* h, const int32_t* dev_nodes, int32_t n_nodes
         c.g_nc = n_cells;
         c.g_prof = c.prof_kernel;
     }
+    // several steps with no kernel timing: one graph of the fused run
+    if (nsteps > 1 && c.prof_kernel < 0)
+        return fused_graph_run(c, dev_nodes, n_nodes, dev_cells, n_cells, nsteps);
     ProfPool& P = pool_of(c);
     for (int i = 0; i < nsteps; ++i) {
         // The graph variant is fixed by the particle parity; the population parity flips in

@@ -67,14 +67,13 @@ def test_layout_is_aligned_and_disjoint(lib):
     assert d["bin"] == 128 and d["capacity"] == 64 * 256 * 128
     regions = []
     for h in range(2):
-        for k in ("x", "y", "vx", "vy", "vz"):
-            regions.append((getattr(L, k)[h], d["capacity"] * rb))
+        regions.append((L.part[h], 8 * rb * d["capacity"]))  # records of 8 Real per particle
         regions.append((L.f[h], d["q"] * d["nnodes"] * rb))
         regions.append((L.count[h], 4 * d["ncells"]))
-    for k, sz in (("tag", 4 * d["capacity"]), ("acc", 160 * d["ncells"]),
+    for k, sz in (("acc", 160 * d["ncells"]),
                   ("crmax", rb * d["ncells"]), ("rem", rb * d["ncells"]),
                   ("nbar_sum", 4 * d["ncells"]), ("ctrl", 64), ("counters", 128),
-                  ("moved", 8 * rb * d["capacity"])):
+                  ("map_scratch", 176 * d["ncells"]), ("coupled", d["ncells"])):
         regions.append((getattr(L, k), sz))
     regions.sort()
     for (o1, s1), (o2, _) in zip(regions, regions[1:]):
@@ -88,7 +87,8 @@ def test_invalid_parameters_are_rejected(lib):
     B.derive(good)
     for bad in (dict(ncx=5), dict(lattice=27), dict(real_bytes=2), dict(lb_ratio=3),
                 dict(kn=0.0), dict(sample_every=0), dict(capacity_factor=0.5), dict(ppc=0),
-                dict(ppc=200)):
+                dict(ppc=200), dict(accum_mode=1), dict(accum_mode=2)):
+        # accum_mode 1 (Kahan-compensated FP32 sums) is not built: only FP64 sums are
         cfg = dict(good)
         cfg.update(bad)
         with pytest.raises(B.HybError) as ei:
@@ -133,15 +133,13 @@ def test_3d_derive_and_layout(lib, ncz):
     assert a["nz"] == (2 * ncz if three_d else 1)
     assert a["nnodes"] == 24 * 8 * a["nz"]
     L = B.layout(cfg)
-    if three_d:
-        regions = sorted([(L.z[0], 8 * a["capacity"]), (L.z[1], 8 * a["capacity"])] +
-                         [(getattr(L, k)[h], 8 * a["capacity"]) for k in ("x", "y", "vx", "vy", "vz")
-                          for h in range(2)] + [(L.f[h], 8 * a["q"] * a["nnodes"]) for h in range(2)])
-        for (o1, s1), (o2, _) in zip(regions, regions[1:]):
-            assert o1 % 256 == 0 and o1 + s1 <= o2
-        assert regions[-1][0] + regions[-1][1] <= L.total_bytes
-    else:
-        assert L.z[0] == L.z[1] == L.total_bytes  # empty
+    # z lives in the particle records (slot 5) in 3D and the slab alike: the record arrays
+    # and populations are disjoint and inside the arena
+    regions = sorted([(L.part[h], 8 * 8 * a["capacity"]) for h in range(2)] +
+                     [(L.f[h], 8 * a["q"] * a["nnodes"]) for h in range(2)])
+    for (o1, s1), (o2, _) in zip(regions, regions[1:]):
+        assert o1 % 256 == 0 and o1 + s1 <= o2
+    assert regions[-1][0] + regions[-1][1] <= L.total_bytes
 
 
 def test_3d_restrictions_are_rejected(lib):
@@ -166,3 +164,36 @@ def test_population_shape_check_uses_the_lattice_shape(lib, ncz):
     want = (39, 6, 16) if ncz < 2 else (39, 6, 6, 16)
     assert h._pop_shape() == want
     assert h.wall_scratch_size() == 2 * 6 * (6 if ncz >= 2 else 1) + 1
+
+
+def test_streamwise_slab_derive_layout_and_limits(lib):
+    # a slab of rows [4, 12) of a 20-row channel: the channel's constants, yh ghost rows on
+    # each side of its LB rows, two send and two receive buffers of xcap particles each
+    cfg = W.config(ncx=10, ncy=8, ppc=20, lb_ratio=2, seed=3, ncy_global=20, y0=4)
+    whole = W.config(ncx=10, ncy=20, ppc=20, lb_ratio=2, seed=3)
+    a, b, w = B.derive(cfg), O.derive(cfg), B.derive(whole)
+    for k in a:
+        assert a[k] == b[k], k
+    for k in ("tau", "dt", "lam", "coll_dt", "g_step", "bin"):
+        assert a[k] == w[k], k
+    assert a["yh"] == 3 and a["ny"] == 8 * 2 + 6 and a["xcap"] == 10 * a["bin"]
+    L = B.layout(cfg)
+    xb = 256 + a["xcap"] * (8 * 4 + 4)
+    assert L.xbytes == xb
+    regions = sorted([(L.xsend[d], xb) for d in range(2)] + [(L.xrecv[d], xb) for d in range(2)] +
+                     [(L.part[h], 32 * a["capacity"]) for h in range(2)] +
+                     [(L.f[h], 4 * a["q"] * a["nnodes"]) for h in range(2)])
+    for (o1, s1), (o2, _) in zip(regions, regions[1:]):
+        assert o1 % 256 == 0 and o1 + s1 <= o2
+    assert regions[-1][0] + regions[-1][1] <= L.total_bytes
+    d19 = B.derive(dict(cfg, lattice=19))
+    assert d19["yh"] == 1 and B.derive(whole)["yh"] == 0 and B.layout(whole).xbytes == 0
+    for bad in (dict(y0=13), dict(ncy=3), dict(y0=-1), dict(ncy_global=-2)):
+        with pytest.raises(B.HybError):
+            B.derive(dict(cfg, **bad))
+    with pytest.raises(B.HybError):
+        B.derive(dict(whole, y0=2))  # y0 without a channel to cut
+    # a batch holds whole channels only
+    params = (B.HybParams * 2)(B.make_params(cfg), B.make_params(cfg))
+    off = (ctypes.c_uint64 * 4)()
+    assert lib.hyb_batch_layout(params, 2, off) == B.HYB_EINVAL

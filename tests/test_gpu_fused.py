@@ -1,0 +1,127 @@
+"""The fused multi-step DSMC pass (the collide of step s and the move of step s + 1 in one
+pass over the particles, and LB2DSMC moving the particles it creates on at once) gives the
+same results as the same steps taken one at a time, bit for bit, and as the oracle; in 2D
+and 3D, FP32 and FP64, with walls, body force, coupling and the capacity fallback of
+LB2DSMC."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1512_08042_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # collected on CPU-only machines, never run there
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1512_08042_gb300 import binding as B  # noqa: E402
+from paper_1512_08042_gb300 import build as BUILD  # noqa: E402
+
+BUILD.build()
+
+
+def cfg_small(**kw):
+    base = dict(ncx=13, ncy=7, ppc=23, real_bytes=4, seed=11, kn=0.1, ma=0.3, capacity_factor=1.5)
+    base.update(kw)
+    return W.config(**base)
+
+
+def assert_same_state(a, b, counters=True):
+    a.sync()
+    b.sync()
+    assert a.current() == b.current()
+    assert a.n_tot() == b.n_tot()
+    pa, pb = a.particles(), b.particles()
+    for k in pa:
+        assert torch.equal(pa[k], pb[k]), k
+    for name in ("cell_start", "crmax", "rem", "nbar_sum", "acc", "f"):
+        assert torch.equal(getattr(a, name)(), getattr(b, name)()), name
+    assert torch.equal(a.ctrl()[:4], b.ctrl()[:4])
+    if counters:
+        assert a.counters() == b.counters()
+    # between calls the other half holds no particles
+    assert int(a.counts(a.current()[0] ^ 1).sum()) == 0
+    assert int(b.counts(b.current()[0] ^ 1).sum()) == 0
+
+
+@pytest.mark.parametrize("real_bytes,ncz,steps", [(4, 0, 5), (8, 0, 3), (4, 3, 4)])
+def test_fused_dsmc_steps_equal_single_steps_and_the_oracle(real_bytes, ncz, steps):
+    cfg = cfg_small(real_bytes=real_bytes, ncz=ncz)
+    a, b = B.Hybrid(cfg), B.Hybrid(cfg)
+    a.dsmc_step(steps)  # fused: move, steps - 1 fused passes, collide
+    for _ in range(steps):
+        b.dsmc_step(1)
+    assert_same_state(a, b)
+    o = O.Oracle(cfg)
+    o.dsmc_step(steps)
+    assert a.n_tot() == o.scalars()["ntot"]
+    assert np.array_equal(a.cell_start().cpu().numpy().astype(np.uint32), o.get(O.A_CELL_START))
+    hc, oc = a.counters(), o.counters()
+    for k in ("candidates", "collisions", "wall_hits"):
+        assert hc[k] == oc[k], k
+    pa, op = a.particles(), o.particles()
+    for k in op:
+        g = pa[k].cpu().numpy()
+        if real_bytes == 4:
+            assert (g == op[k]).mean() >= 0.9999, k
+            assert np.allclose(g, op[k], rtol=1e-5, atol=1e-5), k
+        else:
+            assert np.allclose(g, op[k], rtol=1e-12, atol=1e-12), k
+
+
+@pytest.mark.parametrize("real_bytes,ncz,graph", [(4, 0, True), (4, 0, False), (8, 0, True),
+                                                  (4, 2, True)])
+def test_fused_hybrid_steps_equal_single_steps(real_bytes, ncz, graph):
+    cfg = cfg_small(real_bytes=real_bytes, ncz=ncz, lb_ratio=2, ncy=10)
+    nodes, cells = W.coupling_sites(cfg, strip_cells=2)
+    dn, dc = torch.from_numpy(nodes).cuda(), torch.from_numpy(cells).cuda()
+    a, b = B.Hybrid(cfg), B.Hybrid(cfg)
+    for _ in range(2):  # the second call replays the graph captured by the first
+        a.hybrid_step(dn, dc, nsteps=4, use_graph=graph)
+        for _ in range(4):
+            b.hybrid_step(dn, dc, nsteps=1, use_graph=True)
+        assert_same_state(a, b)
+    c = a.counters()
+    assert c["created"] > 0 and c["deleted"] > 0 and c["collisions"] > 0
+    assert a.sync_status()[0] == B.HYB_OK
+    # an odd step count flips the parities: two graph slots
+    a.hybrid_step(dn, dc, nsteps=3, use_graph=graph)
+    a.hybrid_step(dn, dc, nsteps=3, use_graph=graph)
+    for _ in range(6):
+        b.hybrid_step(dn, dc, nsteps=1, use_graph=False)
+    assert_same_state(a, b)
+
+
+def test_fused_hybrid_keeps_cells_whose_new_count_exceeds_the_bin():
+    # LB2DSMC only (no DSMC2LB), populations at density 4 everywhere: every coupling cell's new
+    # count (about 40) exceeds its bin of 32 slots, so each keeps (and the fused run moves on)
+    # its own particles and the capacity status is raised, as in the steps taken one at a time
+    cfg = cfg_small(ppc=10, capacity_factor=3.0, lb_ratio=1, ncy=8)
+    _, cells = W.coupling_sites(cfg, strip_cells=2)
+    dc = torch.from_numpy(cells).cuda()
+    e, w, r = O.lattice(39)
+    a, b = B.Hybrid(cfg), B.Hybrid(cfg)
+    f = torch.from_numpy((w[:, None] * 4.0 * np.ones((1, a.d["nnodes"]))).astype(np.float32))
+    for h in (a, b):
+        h.f().copy_(f.view(h.f().shape))
+    torch.cuda.synchronize()
+    a.hybrid_step(None, dc, nsteps=3, use_graph=False)
+    for _ in range(3):
+        b.hybrid_step(None, dc, nsteps=1, use_graph=False)
+    assert_same_state(a, b)
+    for h in (a, b):
+        rc, bits = h.sync_status()
+        assert rc == B.HYB_ECAPACITY and bits & B.ST_CAPACITY
+    assert a.counters()["created"] == 0 and a.n_tot() == cfg["ppc"] * a.L.ncells
+
+
+def test_fused_hybrid_at_the_819k_particle_channel_equals_single_steps():
+    cfg = W.WORKLOADS["poiseuille_64x256_ppc50_fp32"]
+    nodes, cells = W.coupling_sites(cfg)
+    dn, dc = torch.from_numpy(nodes).cuda(), torch.from_numpy(cells).cuda()
+    a, b = B.Hybrid(cfg), B.Hybrid(cfg)
+    a.hybrid_step(dn, dc, nsteps=3, use_graph=True)
+    for _ in range(3):
+        b.hybrid_step(dn, dc, nsteps=1, use_graph=True)
+    assert_same_state(a, b)

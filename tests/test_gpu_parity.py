@@ -481,3 +481,181 @@ def test_host_buffer_steps_equal_device_list_steps(pinned):
         b.hybrid_step_host(hn, hc, outs[0][:1], st[0])  # result buffer too small
     with pytest.raises(B.HybError):
         b.host_wait(4)
+
+
+# ---------------------------------------------------------------------------------------
+# The benchmarked FP32 coupled step, from the GPU's own state, sub-step by sub-step
+
+def load_oracle_from_gpu(o, h):
+    """The oracle takes the GPU's whole state: particles in cell order, the per-cell NTC
+    state, the cumulative sums, the populations and the step and sample counts."""
+    h.sync()
+    p = gpu_particles(h)
+    cs = h.cell_start().cpu().numpy().astype(np.uint32)
+    o.set_particles(p["x"], p["y"], p["vx"], p["vy"], p["vz"], cs, z=p.get("z"))
+    o.set(O.A_CRMAX, h.crmax().cpu().numpy())
+    o.set(O.A_REM, h.rem().cpu().numpy())
+    o.set(O.A_NBAR_SUM, h.nbar_sum().cpu().numpy().view(np.uint32))
+    o.set(O.A_ACC, h.acc().cpu().numpy().reshape(-1))
+    o.set_f(h.f().cpu().numpy())
+    ctrl = h.ctrl().cpu().numpy()
+    o.set_scalars(int(ctrl[B.CTRL_STEP]), int(ctrl[B.CTRL_NSAMPLES]))
+
+
+def moment_abs_sums(p, cs):
+    """Per cell and moment, the sum over the cell's particles of the absolute value of the
+    moment's term (1, |v_i|, |v_i v_j|, |v_i v_j v_k|): the scale of the rounding error of a
+    sum of those terms."""
+    v = np.stack([p["vx"], p["vy"], p["vz"]], 1).astype(np.float64)
+    ncell = len(cs) - 1
+    cell = np.repeat(np.arange(ncell), np.diff(cs.astype(np.int64)))
+    terms = [np.ones(len(v))] + [np.abs(v[:, i]) for i in range(3)]
+    terms += [np.abs(v[:, i] * v[:, j]) for i in range(3) for j in range(i, 3)]
+    terms += [np.abs(v[:, i] * v[:, j] * v[:, k]) for i in range(3) for j in range(i, 3)
+              for k in range(j, 3)]
+    return np.stack([np.bincount(cell, weights=t, minlength=ncell) for t in terms], 1)
+
+
+def test_coupled_fp32_step_of_the_819k_channel_matches_the_oracle_sub_step_by_sub_step():
+    # The benchmarked FP32 coupled hybrid step (the 64 x 256-cell channel, 819,200 particles,
+    # 8-node strip): from a coupled state reached by the fused run, the oracle takes the GPU's
+    # state before each sub-step (DSMC step, DSMC2LB, LB step, LB2DSMC) and both take it.
+    # Integers exact (counts, candidates, collisions, created and deleted particles); particle
+    # state bit for bit (floats within 1e-5); the step's FP32 moment partials within 1e-5 of
+    # each sum's scale, per element; populations within 1e-5 of w_a rho.
+    cfg = W.WORKLOADS["poiseuille_64x256_ppc50_fp32"]
+    nodes, cells = W.coupling_sites(cfg)
+    dn, dc = torch.from_numpy(nodes).cuda(), torch.from_numpy(cells).cuda()
+    h = B.Hybrid(cfg)
+    h.hybrid_step(dn, dc, nsteps=3, use_graph=True)
+    o = O.Oracle(cfg)
+    e, w, r = O.lattice(39)
+    # DSMC step
+    load_oracle_from_gpu(o, h)
+    g0, o0, a0 = h.counters(), o.counters(), h.acc().cpu().numpy().copy()
+    h.dsmc_step(1)
+    o.dsmc_step(1)
+    assert np.array_equal(h.cell_start().cpu().numpy().astype(np.uint32), o.get(O.A_CELL_START))
+    assert_particles_match(gpu_particles(h), o.particles(), 4)
+    g1, o1 = h.counters(), o.counters()
+    for k in ("candidates", "collisions", "wall_hits"):
+        assert g1[k] - g0[k] == o1[k] - o0[k], k
+    assert np.array_equal(h.crmax().cpu().numpy(), o.get(O.A_CRMAX))
+    assert np.array_equal(h.rem().cpu().numpy(), o.get(O.A_REM))
+    scale = moment_abs_sums(o.particles(), o.get(O.A_CELL_START))
+    inc_g, inc_o = h.acc().cpu().numpy() - a0, o.acc() - a0
+    assert np.all(np.abs(inc_g - inc_o) <= 1e-5 * scale + 1e-300), np.abs(inc_g - inc_o).max()
+    # DSMC2LB from the same sums
+    load_oracle_from_gpu(o, h)
+    h.map_dsmc_to_lbm(dn)
+    o.map_dsmc_to_lbm(nodes)
+    h.sync()
+    gf = h.f().cpu().numpy().reshape(39, -1)[:, nodes].astype(np.float64)
+    of = o.f().reshape(39, -1)[:, nodes].astype(np.float64)
+    assert np.all(np.abs(gf - of) <= 2e-6 * (np.abs(of) + w[:, None]))
+    # LB step from the same populations
+    load_oracle_from_gpu(o, h)
+    h.lbm_step(1)
+    o.lbm_step(1)
+    h.sync()
+    gf, of = h.f().cpu().numpy().astype(np.float64), o.f().astype(np.float64)
+    rho = of.sum(0)
+    assert (np.abs(gf - of) / (w[:, None, None] * rho)).max() < 1e-5
+    # LB2DSMC from the same populations
+    load_oracle_from_gpu(o, h)
+    g0, o0 = h.counters(), o.counters()
+    h.map_lbm_to_dsmc(dc)
+    o.map_lbm_to_dsmc(cells)
+    assert h.n_tot() == o.scalars()["ntot"]
+    assert np.array_equal(h.cell_start().cpu().numpy().astype(np.uint32), o.get(O.A_CELL_START))
+    gp, op = gpu_particles(h), o.particles()
+    for k in op:
+        assert np.array_equal(gp[k], op[k]), k
+    g1, o1 = h.counters(), o.counters()
+    for k in ("created", "deleted", "l2d_attempts", "envelope"):
+        assert g1[k] - g0[k] == o1[k] - o0[k], k
+    assert g1["created"] > g0["created"]
+    assert h.sync_status()[0] == B.HYB_OK
+
+
+def _grad_populations():
+    """Populations at one node of a Grad distribution with a sizable stress and heat flux:
+    DSMC2LB (oracle) of cumulative sums with rho 1.05, u (0.04, 0.08, -0.02), <vv> and <vvv>
+    of a non-equilibrium gas."""
+    import itertools
+    rho, u = 1.05, np.array([0.04, 0.08, -0.02])
+    I = np.eye(3)
+    P = I + np.outer(u, u) + np.array([[0.12, 0.05, 0.0], [0.05, -0.08, 0.03], [0.0, 0.03, -0.04]])
+    Q = (np.einsum("i,jk->ijk", u, I) + np.einsum("j,ik->ijk", u, I) + np.einsum("k,ij->ijk", u, I))
+    for perm in set(itertools.permutations((0, 1, 1))):
+        Q[perm] += 0.06
+    for perm in set(itertools.permutations((0, 0, 0))):
+        Q[perm] += 0.05
+    S, ppc = 1, 100
+    NS = rho * ppc * S
+    m = np.zeros(20)
+    m[0], m[1:4] = NS, NS * u
+    o = 4
+    for a in range(3):
+        for b in range(a, 3):
+            m[o] = NS * P[a, b]
+            o += 1
+    for a in range(3):
+        for b in range(a, 3):
+            for c in range(b, 3):
+                m[o] = NS * Q[a, b, c]
+                o += 1
+    return O.dsmc2lb_node(39, m, S, ppc)
+
+
+def test_lb2dsmc_on_2048_cells_matches_the_oracle_and_the_grad_law():
+    # 2048 coupling cells (a strip 4 cells wide across a 512-cell channel, as on the large
+    # channel) exceed the mapping's grid of 8 blocks per SM, so every block takes several
+    # cells. From the same Grad populations in every strip node: new particles bit for bit
+    # as the oracle; the FP64 Grad records equal the oracle's FP64 coefficients to 1e-13; and
+    # the regenerated gas has E[c c] = I + a2 and E[c c c] = a3 (Table 1) within 5 sigma of
+    # the about 100,000 particles' sample.
+    cfg = W.config(ncx=512, ncy=16, ppc=50, lb_ratio=2, kn=0.05, seed=23)
+    nodes, cells = W.coupling_sites(cfg)
+    assert len(cells) == 2048
+    h = B.Hybrid(cfg)
+    o = O.Oracle(cfg)
+    fnode = _grad_populations()
+    f = h.f().cpu().numpy().astype(np.float64).reshape(39, -1)
+    f[:, nodes] = fnode[:, None]
+    f32 = f.astype(np.float32).reshape(h.f().shape)
+    h.f().copy_(torch.from_numpy(f32))
+    torch.cuda.synchronize()
+    o.set_f(f32)
+    dc = torch.from_numpy(cells).cuda()
+    h.map_lbm_to_dsmc(dc)
+    o.map_lbm_to_dsmc(cells)
+    assert h.n_tot() == o.scalars()["ntot"]
+    gp, op = gpu_particles(h), o.particles()
+    for k in op:
+        assert np.array_equal(gp[k], op[k]), k
+    hc, oc = h.counters(), o.counters()
+    for k in ("created", "deleted", "l2d_attempts", "envelope"):
+        assert hc[k] == oc[k], k
+    rho_g, nnew_g, v_g = h.grad_records(len(cells))
+    g = O.grad_coeffs_packed(39, f32.reshape(39, -1)[:, nodes[0]].astype(np.float64), 8)
+    want = np.concatenate([g["a2"], g["a3"], g["u"], [g["C"]]])
+    assert np.abs(v_g.numpy() - want[None, :]).max() < 1e-13
+    assert np.abs(rho_g.numpy() / g["rho"] - 1).max() < 1e-14
+    # the regenerated velocities follow the Grad distribution of those coefficients
+    cs = h.cell_start().cpu().numpy().astype(np.int64)
+    sel = np.concatenate([np.arange(cs[c], cs[c + 1]) for c in cells])
+    v = np.stack([gp["vx"][sel], gp["vy"][sel], gp["vz"][sel]], 1).astype(np.float64)
+    c = v - g["u"]
+    n = len(c)
+    assert n > 90_000
+    se = 1 / np.sqrt(n)
+    pairs = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+    for k, (i, j) in enumerate(pairs):
+        m2 = (c[:, i] * c[:, j]).mean()
+        assert abs(m2 - ((1.0 if i == j else 0.0) + g["a2"][k])) < 5 * np.sqrt(3) * se, (i, j)
+    triples = [(0, 0, 0), (0, 0, 1), (0, 0, 2), (0, 1, 1), (0, 1, 2), (0, 2, 2), (1, 1, 1),
+               (1, 1, 2), (1, 2, 2), (2, 2, 2)]
+    for k, (i, j, l) in enumerate(triples):
+        m3 = (c[:, i] * c[:, j] * c[:, l]).mean()
+        assert abs(m3 - g["a3"][k]) < 5 * np.sqrt(15) * se, (i, j, l)
