@@ -78,7 +78,40 @@ bool valid(const Params* p) {
            (p->real_bytes == 4 || p->real_bytes == 8) && p->sample_every >= 1 && p->kn > 0.0 &&
            p->capacity_factor >= 1.0 && std::ceil(p->capacity_factor * p->ppc) <= 256.0 &&
            (p->lb_collision == 0 || p->lb_collision == 1) && (p->d2l_mode == 0 || p->d2l_mode == 1) &&
-           (p->kn_profile == 0 || (p->kn_profile == 1 && p->kn_end > 0.0)) && p->ncz >= 0;
+           (p->kn_profile == 0 || (p->kn_profile == 1 && p->kn_end > 0.0)) && p->ncz >= 0 &&
+           p->accum_mode == 0 && p->ncy_global >= 0 &&
+           (p->ncy_global > 0 ? (p->y0 >= 0 && p->ncy >= 4 && (int64_t)p->y0 + p->ncy <= p->ncy_global)
+                              : p->y0 == 0);
+}
+
+// A streamwise slab's split move (phase_move), its outbox towards lower (dir 0) or higher
+// (dir 1) rows as rows of 8 doubles (x, y, z, vx, vy, vz, tag >> 32, tag & 0xFFFFFFFF) and
+// their channel cells, and the merge of the particles received from the slab below (in0) and
+// above (in1) followed by the sort (phase_accept_sort).
+template <class Real>
+void outbox_get(Dsmc<Real>& D, int dir, double* out, uint32_t* gkey) {
+    const auto& o = D.outbox[dir];
+    for (size_t k = 0; k < o.size(); ++k) {
+        double* r = out + 8 * k;
+        r[0] = o.x[k]; r[1] = o.y[k]; r[2] = o.z[k];
+        r[3] = o.vx[k]; r[4] = o.vy[k]; r[5] = o.vz[k];
+        r[6] = (double)(o.tag[k] >> 32);
+        r[7] = (double)(o.tag[k] & 0xFFFFFFFFull);
+        gkey[k] = o.gkey[k];
+    }
+}
+template <class Real>
+void accept(Dsmc<Real>& D, const double* in[2], const uint32_t* keys[2], const int64_t n[2]) {
+    typename Dsmc<Real>::Moved m[2];
+    for (int b = 0; b < 2; ++b)
+        for (int64_t k = 0; k < n[b]; ++k) {
+            const double* r = in[b] + 8 * k;
+            m[b].x.push_back((Real)r[0]); m[b].y.push_back((Real)r[1]); m[b].z.push_back((Real)r[2]);
+            m[b].vx.push_back((Real)r[3]); m[b].vy.push_back((Real)r[4]); m[b].vz.push_back((Real)r[5]);
+            m[b].tag.push_back(((uint64_t)r[6] << 32) | (uint64_t)r[7]);
+            m[b].gkey.push_back(keys[b][k]);
+        }
+    D.phase_accept_sort(m, 2);
 }
 
 }  // namespace
@@ -146,6 +179,33 @@ int ora_dsmc_phase(void* hv, int phase) {
         if (phase == 2) h->dd.phase_sample_advance();
     }
     return 0;
+}
+
+// A streamwise slab's split move, its outboxes and the merge of what it received.
+void ora_dsmc_move(void* hv) {
+    Handle* h = (Handle*)hv;
+    (h->rb == 4) ? h->df.phase_move() : h->dd.phase_move();
+}
+
+int64_t ora_outbox_size(void* hv, int dir) {
+    Handle* h = (Handle*)hv;
+    return (int64_t)((h->rb == 4) ? h->df.outbox[dir & 1].size() : h->dd.outbox[dir & 1].size());
+}
+
+void ora_outbox_get(void* hv, int dir, double* out, uint32_t* gkey) {
+    Handle* h = (Handle*)hv;
+    if (h->rb == 4) outbox_get(h->df, dir & 1, out, gkey);
+    else outbox_get(h->dd, dir & 1, out, gkey);
+}
+
+void ora_dsmc_accept(void* hv, const double* in0, const uint32_t* k0, int64_t n0, const double* in1,
+                     const uint32_t* k1, int64_t n1) {
+    Handle* h = (Handle*)hv;
+    const double* in[2] = {in0, in1};
+    const uint32_t* keys[2] = {k0, k1};
+    const int64_t n[2] = {n0, n1};
+    if (h->rb == 4) accept(h->df, in, keys, n);
+    else accept(h->dd, in, keys, n);
 }
 
 int ora_lbm_step(void* hv, int n) {

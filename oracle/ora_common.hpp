@@ -114,13 +114,14 @@ inline Derived derive(const Params& p) {
 // Kn(y) = kn (kn_end / kn)^s with s = 1 - |2 y / ncy - 1|. A DSMC cell takes the NTC factor
 // of Eq. collisionnumber at its centre's Kn, an LB node the tau of Eq. tau at its own.
 inline double kn_at(const Params& p, double y) {
-    const double s = 1.0 - std::fabs(2.0 * y / (double)p.ncy - 1.0);
+    const double period = p.ncy_global > 0 ? (double)p.ncy_global : (double)p.ncy;
+    const double s = 1.0 - std::fabs(2.0 * y / period - 1.0);
     return p.kn * std::exp(s * std::log(p.kn_end / p.kn));
 }
 
 // With the Kn profile: the NTC factor of Eq. collisionnumber (F_N sigma_T dt / V_c) of a DSMC
-// cell in row iy, at the Kn of the cell's centre, and tau of Eq. tau of an LB node in row j,
-// at the Kn of the row's centre.
+// cell in the channel's row iy, at the Kn of the cell's centre, and tau of Eq. tau of an LB
+// node in the channel's LB row j, at the Kn of the row's centre.
 inline double kn_cell_coll(const Params& p, const Derived& d, int64_t iy) {
     const double kn = kn_at(p, (double)iy + 0.5);
     return d.dt / (std::sqrt(2.0) * (kn * (double)p.ncx) * (double)p.ppc);
@@ -128,6 +129,24 @@ inline double kn_cell_coll(const Params& p, const Derived& d, int64_t iy) {
 inline double kn_node_tau(const Params& p, const Derived& d, int64_t j) {
     const double kn = kn_at(p, ((double)j + 0.5) / (double)p.lb_ratio);
     return std::sqrt(kPi / 8.0) * d.r_lat * kn * d.H_lat + 0.5;
+}
+
+// A streamwise slab (ncy_global > 0) holds the channel's rows [y0, y0 + ncy): the channel's
+// row of the slab's row iy, the channel's cell id of the slab's cell c = (iz ncy + iy) ncx + ix,
+// and the channel's LB row of the slab's lattice row j (its yh ghost rows hold the
+// neighbours' rows, periodically). For a context that holds the whole channel these are
+// identities.
+inline int64_t channel_rows(const Params& p) { return p.ncy_global > 0 ? p.ncy_global : p.ncy; }
+inline uint32_t channel_cell(const Params& p, int64_t c) {
+    const int64_t plane = (int64_t)p.ncx * p.ncy;
+    const int64_t iz = c / plane, r = c % plane;
+    const int64_t y0 = p.ncy_global > 0 ? p.y0 : 0;
+    return (uint32_t)((iz * channel_rows(p) + y0 + r / p.ncx) * p.ncx + r % p.ncx);
+}
+inline int64_t channel_lb_row(const Params& p, const Derived& d, int64_t j) {
+    const int64_t rows = channel_rows(p) * p.lb_ratio;
+    const int64_t y0 = p.ncy_global > 0 ? p.y0 : 0;
+    return (((y0 * p.lb_ratio + j - d.yh) % rows) + rows) % rows;
 }
 
 // ---------------------------------------------------------------------------------------

@@ -63,16 +63,18 @@ struct Dsmc {
         // Sec. 3.1: a fixed number of particles placed in each cell, Maxwellian at T
         // (Eq. globalMax with unit variance), drawn by Box-Muller.
         for (int64_t c = 0; c < d.ncells; ++c) {
-            const int ix = (int)(c % p.ncx), iy = (int)((c / p.ncx) % p.ncy);
+            // the channel's row and cell id (a streamwise slab holds rows y0 .. y0 + ncy - 1)
+            const int ix = (int)(c % p.ncx), iy = y0() + (int)((c / p.ncx) % p.ncy);
             const int iz = (int)(c / ((int64_t)p.ncx * p.ncy));
+            const uint32_t gc = channel_cell(p, c);
             cell_start[c] = (uint32_t)(c * p.ppc);
             for (int k = 0; k < p.ppc; ++k) {
                 const int64_t s = c * p.ppc + k;
-                U4 rp = draw(p.seed, (uint32_t)c, 0, TAG_INIT_POS, (uint32_t)k, 0);
+                U4 rp = draw(p.seed, gc, 0, TAG_INIT_POS, (uint32_t)k, 0);
                 x[s] = (Real)ix + (Real)u01f(rp[0]);
                 y[s] = (Real)iy + (Real)u01f(rp[1]);
                 if (three_d()) z[s] = (Real)iz + (Real)u01f(rp[2]);
-                U4 rv = draw(p.seed, (uint32_t)c, 0, TAG_INIT_VEL, (uint32_t)k, 0);
+                U4 rv = draw(p.seed, gc, 0, TAG_INIT_VEL, (uint32_t)k, 0);
                 Real n0, n1, n2, n3;
                 gauss_pair<Real>(rv[0], rv[1], n0, n1);
                 gauss_pair<Real>(rv[2], rv[3], n2, n3);
@@ -88,7 +90,7 @@ struct Dsmc {
         if (p.kn_profile == 1) {  // Eq. collisionnumber at each cell centre's Kn
             coll_cell.resize((size_t)d.ncells);
             for (int64_t c = 0; c < d.ncells; ++c)
-                coll_cell[(size_t)c] = kn_cell_coll(p, d, (c / p.ncx) % p.ncy);
+                coll_cell[(size_t)c] = kn_cell_coll(p, d, y0() + (c / p.ncx) % p.ncy);
         }
         nbar_sum.assign(d.ncells, 0u);
         acc.assign(d.ncells * kNumMoments, 0.0);
@@ -100,6 +102,24 @@ struct Dsmc {
 
     size_t ntot() const { return x.size(); }
     bool three_d() const { return p.ncz >= 2; }
+    int y0() const { return p.ncy_global > 0 ? p.y0 : 0; }
+
+    // Particles that left a streamwise slab in the last move, towards lower (0) and higher
+    // (1) rows of the channel, with their stable-order keys (channel origin cell << 32 |
+    // rank) and new channel cells; and the particles received from the neighbours.
+    struct Moved {
+        std::vector<Real> x, y, z, vx, vy, vz;
+        std::vector<uint64_t> tag;
+        std::vector<uint32_t> gkey;
+        void clear() {
+            x.clear(); y.clear(); z.clear(); vx.clear(); vy.clear(); vz.clear();
+            tag.clear(); gkey.clear();
+        }
+        size_t size() const { return x.size(); }
+    };
+    Moved outbox[2];
+    std::vector<uint32_t> key_;   // new local cell of each particle after the move
+    std::vector<uint64_t> tag_;   // stable-order key of each particle
 
     // Diffuse isothermal re-emission from a wall at rest (Sec. 3.1, "fully diffuse
     // reflection"): normal speed from the flux-weighted Maxwellian sqrt(-2 ln U), tangential
@@ -116,20 +136,39 @@ struct Dsmc {
         uz = t2;
     }
 
+    // The channel's cell (iz rows + iy) ncx + ix of a position.
     uint32_t cell_key(Real xx, Real yy, Real zz) const {
+        const int rows = (int)channel_rows(p);
         int ix = (int)std::floor(xx);
         int iy = (int)std::floor(yy);
         if (ix < 0) ix = 0;
         if (ix > p.ncx - 1) ix = p.ncx - 1;
         if (iy < 0) iy = 0;
-        if (iy > p.ncy - 1) iy = p.ncy - 1;
+        if (iy > rows - 1) iy = rows - 1;
         int iz = 0;
         if (three_d()) {
             iz = (int)std::floor(zz);
             if (iz < 0) iz = 0;
             if (iz > p.ncz - 1) iz = p.ncz - 1;
         }
-        return (uint32_t)(((int64_t)iz * p.ncy + iy) * p.ncx + ix);
+        return (uint32_t)(((int64_t)iz * rows + iy) * p.ncx + ix);
+    }
+
+    // The slab's own cell of a channel cell, or -1 (with the direction to the neighbour that
+    // holds it: 0 lower rows, 1 higher rows, the nearer way around the periodic channel).
+    int64_t local_cell(uint32_t gk, int& dir) const {
+        const int64_t rows = channel_rows(p);
+        const int64_t plane = (int64_t)p.ncx * rows;
+        const int64_t iz = gk / plane, r = gk % plane, iy = r / p.ncx, ix = r % p.ncx;
+        const int64_t iyl = iy - y0();
+        if (iyl >= 0 && iyl < p.ncy) {
+            dir = -1;
+            return (iz * p.ncy + iyl) * p.ncx + ix;
+        }
+        const int64_t above = ((iy - (y0() + p.ncy)) % rows + rows) % rows;
+        const int64_t below = ((y0() - 1 - iy) % rows + rows) % rows;
+        dir = above <= below ? 1 : 0;
+        return -1;
     }
 
     // Periodic wrap of a coordinate into [0, period).
@@ -143,11 +182,12 @@ struct Dsmc {
     }
 
     // Move one particle through one time step: body-force kick, free flight, wall hits,
-    // periodic wrap in the streamwise direction. Returns the new cell key.
+    // periodic wrap in the streamwise direction. `cell` is the particle's channel cell (the
+    // key of its wall draws). Returns the new channel cell.
     uint32_t move_one(uint32_t i, uint32_t s, uint32_t cell, uint32_t rank) {
         if (!(x[i] >= (Real)0)) return kDeadKey;  // deleted by a coupling step
         const Real H = (Real)p.ncx;
-        const Real L = (Real)p.ncy;
+        const Real L = (Real)channel_rows(p);
         const bool td = three_d();
         Real px = x[i], py = y[i], pz = td ? z[i] : (Real)0;
         Real ux = vx[i], uy = vy[i] + (Real)d.g_step, uz = vz[i];
@@ -190,15 +230,18 @@ struct Dsmc {
         return cell_key(px, py, pz);
     }
 
-    // Stable counting order by cell key: ties keep the previous slot order. Deleted
-    // particles are dropped.
-    void sort_by_cell(const std::vector<uint32_t>& key) {
+    // Order by cell key; within a cell by the particles' previous order in the channel
+    // (origin cell, then rank in it: the tag), which is the previous slot order of the
+    // particles a context held, with received particles merged in. Deleted particles are
+    // dropped.
+    void sort_by_cell(const std::vector<uint32_t>& key, const std::vector<uint64_t>& tag) {
         std::vector<uint32_t> idx;
         idx.reserve(key.size());
         for (uint32_t i = 0; i < key.size(); ++i)
             if (key[i] != kDeadKey) idx.push_back(i);
-        std::stable_sort(idx.begin(), idx.end(),
-                         [&](uint32_t a, uint32_t b) { return key[a] < key[b]; });
+        std::stable_sort(idx.begin(), idx.end(), [&](uint32_t a, uint32_t b) {
+            return key[a] < key[b] || (key[a] == key[b] && tag[a] < tag[b]);
+        });
         auto permute = [&](std::vector<Real>& v) {
             std::vector<Real> o(idx.size());
             for (size_t k = 0; k < idx.size(); ++k) o[k] = v[idx[k]];
@@ -240,6 +283,7 @@ struct Dsmc {
     // candidate pair (i, j != i) collides with probability c_r / c_r,max; post-collision
     // velocities are v_cm +- c_r n / 2 with n isotropic (hard spheres).
     void collide_cell(uint32_t c, uint32_t s) {
+        const uint32_t gc = channel_cell(p, c);  // the key of the cell's random streams
         const uint32_t base = cell_start[c];
         const uint32_t n = cell_start[c + 1] - base;
         nbar_sum[c] += n;
@@ -256,7 +300,7 @@ struct Dsmc {
         }
         counters[C_CANDIDATES] += nsel;
         for (uint32_t k = 0; k < nsel; ++k) {
-            U4 r = draw(p.seed, c, s, TAG_NTC_PAIR, k, 0);
+            U4 r = draw(p.seed, gc, s, TAG_NTC_PAIR, k, 0);
             const uint32_t i = uindex(r[0], n);
             uint32_t j = uindex(r[1], n - 1);
             if (j >= i) j += 1;
@@ -267,7 +311,7 @@ struct Dsmc {
             if (cr > crmax[c]) crmax[c] = cr;
             if (cr > R * crmax[c]) {
                 Real nv[3];
-                if (!unit_vector(c, s, k, nv)) {
+                if (!unit_vector(gc, s, k, nv)) {
                     status |= ST_SCATTER_CAP;
                     continue;
                 }
@@ -301,13 +345,56 @@ struct Dsmc {
     }
 
     // The three phases of one step; step_once runs them in order.
-    void phase_move_sort() {
+    // The move of every particle; a streamwise slab's particles whose new cell is a
+    // neighbour's go to the outbox.
+    void phase_move() {
         const uint32_t s = (uint32_t)step;
-        std::vector<uint32_t> key(ntot());
-        for (int64_t c = 0; c < d.ncells; ++c)
-            for (uint32_t i = cell_start[c]; i < cell_start[c + 1]; ++i)
-                key[i] = move_one(i, s, (uint32_t)c, i - cell_start[c]);
-        sort_by_cell(key);
+        outbox[0].clear();
+        outbox[1].clear();
+        key_.assign(ntot(), kDeadKey);
+        tag_.assign(ntot(), 0);
+        for (int64_t c = 0; c < d.ncells; ++c) {
+            const uint32_t gc = channel_cell(p, c);
+            for (uint32_t i = cell_start[c]; i < cell_start[c + 1]; ++i) {
+                const uint32_t rank = i - cell_start[c];
+                tag_[i] = ((uint64_t)gc << 32) | rank;
+                const uint32_t gk = move_one(i, s, gc, rank);
+                if (gk == kDeadKey) continue;
+                int dir;
+                const int64_t lc = local_cell(gk, dir);
+                if (lc >= 0) {
+                    key_[i] = (uint32_t)lc;
+                    continue;
+                }
+                Moved& o = outbox[dir];
+                o.x.push_back(x[i]); o.y.push_back(y[i]); o.z.push_back(three_d() ? z[i] : (Real)0);
+                o.vx.push_back(vx[i]); o.vy.push_back(vy[i]); o.vz.push_back(vz[i]);
+                o.tag.push_back(tag_[i]);
+                o.gkey.push_back(gk);
+            }
+        }
+    }
+    // The particles received from the neighbours join, and all are ordered by cell.
+    void phase_accept_sort(const Moved* in, int nin) {
+        for (int b = 0; b < nin; ++b)
+            for (size_t k = 0; k < in[b].size(); ++k) {
+                int dir;
+                const int64_t lc = local_cell(in[b].gkey[k], dir);
+                if (lc < 0) {
+                    status |= ST_BAD_INPUT;
+                    continue;
+                }
+                x.push_back(in[b].x[k]); y.push_back(in[b].y[k]);
+                if (three_d()) z.push_back(in[b].z[k]);
+                vx.push_back(in[b].vx[k]); vy.push_back(in[b].vy[k]); vz.push_back(in[b].vz[k]);
+                key_.push_back((uint32_t)lc);
+                tag_.push_back(in[b].tag[k]);
+            }
+        sort_by_cell(key_, tag_);
+    }
+    void phase_move_sort() {
+        phase_move();
+        phase_accept_sort(nullptr, 0);
     }
     void phase_collide() {
         const uint32_t s = (uint32_t)step;

@@ -49,7 +49,7 @@ struct Lbm {
             g_node.assign((size_t)d.nnodes, d.g_step);
             tau_node.resize((size_t)d.nnodes);
             for (int64_t n = 0; n < d.nnodes; ++n)
-                tau_node[(size_t)n] = kn_node_tau(p, d, (n / d.nx) % d.ny);
+                tau_node[(size_t)n] = kn_node_tau(p, d, channel_lb_row(p, d, (n / d.nx) % d.ny));
         }
     }
 

@@ -227,8 +227,13 @@ void map_dsmc_to_lbm(Dsmc<Real>& D, Lbm<Real>& B, const int32_t* nodes, int n) {
             D.status |= ST_BAD_INPUT;
             continue;
         }
-        const int64_t x = node % B.d.nx, y = (node / B.d.nx) % B.d.ny;
+        // a streamwise slab's yh ghost rows below and above its rows hold no cell of its own
+        const int64_t x = node % B.d.nx, y = (node / B.d.nx) % B.d.ny - B.d.yh;
         const int64_t z = node / (B.d.nx * B.d.ny);
+        if (y < 0 || y >= (int64_t)D.p.ncy * D.p.lb_ratio) {
+            D.status |= ST_BAD_INPUT;
+            continue;
+        }
         const int64_t zc = D.three_d() ? z / D.p.lb_ratio : 0;
         const int64_t cell = (zc * D.p.ncy + y / D.p.lb_ratio) * D.p.ncx + (x / D.p.lb_ratio);
         Coeffs a;
@@ -271,6 +276,8 @@ void map_lbm_to_dsmc(Dsmc<Real>& D, const Lbm<Real>& B, const int32_t* cells, in
         const int64_t cell = cells[c];
         const int64_t ix = cell % D.p.ncx, iy = (cell / D.p.ncx) % D.p.ncy;
         const int64_t iz = cell / ((int64_t)D.p.ncx * D.p.ncy);
+        const uint32_t gc = channel_cell(D.p, cell);  // the key of the cell's random streams
+        const int64_t yh = B.d.yh;                    // a slab's ghost rows below its LB rows
         const int rz = D.three_d() ? r : 1;  // LB layers of the cell along z
         // the mean populations of the cell's nodes and its Grad coefficients, in FP64
         std::vector<double> fbar(L.q, 0.0);
@@ -279,11 +286,11 @@ void map_lbm_to_dsmc(Dsmc<Real>& D, const Lbm<Real>& B, const int32_t* cells, in
             for (int dz = 0; dz < rz; ++dz)
                 for (int dy = 0; dy < r; ++dy)
                     for (int dx = 0; dx < r; ++dx)
-                        s += (double)B.fa(q, ix * r + dx, iy * r + dy, iz * rz + dz);
+                        s += (double)B.fa(q, ix * r + dx, iy * r + dy + yh, iz * rz + dz);
             fbar[q] = s / (double)(r * r * rz);
         }
         const GradCell g = grad_from_populations(L, fbar.data(), B.d.order);
-        const double u = u01d(draw(D.p.seed, (uint32_t)cell, t, TAG_L2D_ROUND, 0, 0)[0]);
+        const double u = u01d(draw(D.p.seed, gc, t, TAG_L2D_ROUND, 0, 0)[0]);
         const double ne = std::floor(g.rho * (double)D.p.ppc + u);
         const uint32_t nnew = ne > 0.0 ? (uint32_t)ne : 0u;
         if (nnew > (uint32_t)D.d.bin) {
@@ -292,8 +299,8 @@ void map_lbm_to_dsmc(Dsmc<Real>& D, const Lbm<Real>& B, const int32_t* cells, in
         }
         fresh[c].resize(6 * (size_t)nnew);
         bool capped = false;
-        const uint64_t trials = grad_sample_cell<Real>(pack<Real>(g), B.d.order, D.p.seed,
-                                                       (uint32_t)cell, t, nnew, (Real)ix, (Real)iy,
+        const uint64_t trials = grad_sample_cell<Real>(pack<Real>(g), B.d.order, D.p.seed, gc, t,
+                                                       nnew, (Real)ix, (Real)(D.y0() + iy),
                                                        (Real)iz, D.three_d(), fresh[c].data(),
                                                        &D.counters[C_ENVELOPE], &capped);
         if (capped) D.status |= ST_SAMPLING_CAP;

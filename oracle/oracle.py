@@ -103,6 +103,14 @@ def lib():
         L.ora_lbm_collide.argtypes = [ctypes.POINTER(Params), vp, vp]
         L.ora_dsmc2lb_node.argtypes = [ctypes.c_int, vp, u64, ctypes.c_int, vp]
         L.ora_grad_coeffs.argtypes = [ctypes.c_int, vp, vp]
+        L.ora_dsmc_move.argtypes = [vp]
+        L.ora_dsmc_move.restype = None
+        L.ora_outbox_size.argtypes = [vp, ctypes.c_int]
+        L.ora_outbox_size.restype = i64
+        L.ora_outbox_get.argtypes = [vp, ctypes.c_int, vp, vp]
+        L.ora_outbox_get.restype = None
+        L.ora_dsmc_accept.argtypes = [vp, vp, vp, i64, vp, vp, i64]
+        L.ora_dsmc_accept.restype = None
         L.ora_grad_coeffs_packed.argtypes = [ctypes.c_int, vp, ctypes.c_int, vp]
         L.ora_grad_sample.argtypes = [ctypes.c_int, vp, u64, u32, u32, i64, vp, vp]
         L.ora_float_funcs.argtypes = [vp, i64, vp, vp, vp]
@@ -244,6 +252,28 @@ class Oracle:
 
     def dsmc_step(self, n=1):
         lib().ora_dsmc_step(self.h, n)
+
+    # -- a streamwise slab (cfg["ncy_global"] > 0): the split DSMC step -------------------
+    def dsmc_move_out(self):
+        """Phase 0 without the sort: moves every particle; returns the outboxes towards lower
+        (0) and higher (1) rows: (rows of x, y, z, vx, vy, vz, tag >> 32, tag & 0xFFFFFFFF as
+        float64, channel cells as uint32)."""
+        lib().ora_dsmc_move(self.h)
+        out = []
+        for d in (0, 1):
+            n = lib().ora_outbox_size(self.h, d)
+            rec = np.zeros((n, 8), np.float64)
+            key = np.zeros(n, np.uint32)
+            lib().ora_outbox_get(self.h, d, _ptr(rec), _ptr(key))
+            out.append((rec, key))
+        return out
+
+    def dsmc_accept(self, in0, in1):
+        """The particles received from the slab below (in0) and above (in1), each (rec, key)
+        as dsmc_move_out gives them, join; then the sort that ends phase 0."""
+        r0, k0 = (np.ascontiguousarray(a) for a in in0)
+        r1, k1 = (np.ascontiguousarray(a) for a in in1)
+        lib().ora_dsmc_accept(self.h, _ptr(r0), _ptr(k0), len(k0), _ptr(r1), _ptr(k1), len(k1))
 
     def dsmc_phase(self, phase):
         """0: move + sort, 1: collide, 2: sample + advance the step counter."""

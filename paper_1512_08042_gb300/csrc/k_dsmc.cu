@@ -230,10 +230,10 @@ constexpr int kGroup = 8;
 
 template <typename Real>
 struct CollideCfg {
-    static constexpr int MINB = sizeof(Real) == 4 ? 4 : 2;  // resident blocks per SM
+    static constexpr int MINB = sizeof(Real) == 4 ? 3 : 2;  // resident blocks per SM
 };
 constexpr int kCollideWarps = 8;  // 32 cells per block
-constexpr int kChainSteps = 16;   // candidates per cell drawn per pass of the NTC phase
+constexpr int kChainSteps = 24;   // candidates per cell drawn per pass of the NTC phase
 enum CollideMode : int { MODE_COLLIDE = 0, MODE_FUSED = 1 };
 
 // Real arrays of the shared-memory pool per slot: vx, vy, vz, x, y (, z)
@@ -314,6 +314,7 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
     constexpr int R = SMALL / G;
     constexpr int KC = kChainSteps;       // candidates per cell drawn per pass of phase B
     constexpr int NR = pool_reals<Z3>();
+    constexpr int SJ = 2;                 // arrivals per lane whose loads are in flight together
     static_assert(NC == 32, "phase B runs one lane per cell of the block in one warp");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ uint32_t s_n[NC], s_off[NC], s_nsel[NC];
@@ -463,16 +464,16 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
             // each arrival k goes to the pool slot of its rank (its record carries its key);
             // the loads of a lane's arrivals can be in flight together
             const bool big = n > (uint32_t)(2 * SMALL);
-            for (uint32_t k0 = 0; k0 < n; k0 += 4 * G) {
-                Real p[4][6];
-                uint32_t t[4];
+            for (uint32_t k0 = 0; k0 < n; k0 += SJ * G) {
+                Real p[SJ][6];
+                uint32_t t[SJ];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
+                for (int j = 0; j < SJ; ++j) {
                     const uint32_t k = k0 + (uint32_t)(gl + G * j);
                     if (k < n) rec_get(drec, base + k, p[j][3], p[j][4], p[j][5], p[j][0], p[j][1], p[j][2], t[j]);
                 }
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
+                for (int j = 0; j < SJ; ++j) {
                     const uint32_t k = k0 + (uint32_t)(gl + G * j);
                     if (k < n) {
                         uint32_t rk;

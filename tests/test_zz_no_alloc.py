@@ -82,3 +82,44 @@ def test_noalloc_rejects_lists_beyond_its_scratch():
     assert b"HYB_NOALLOC_MAX_CELLS" in B.lib().hyb_last_error(h.ctx)
     after = _state(h)
     assert np.array_equal(before["counts"], after["counts"])
+
+
+def test_noalloc_3d_and_a_full_scratch_allocate_nothing():
+    # a 3D channel (the mappings over the cell's r^3 nodes) and a list of exactly
+    # HYB_NOALLOC_MAX_CELLS cells, the largest the fixed scratch holds: results equal the
+    # allocating entry point's, and after a warm-up call neither torch's caching allocator
+    # nor the device's free memory changes across a call
+    cfg = W.config(ncx=64, ncy=32, ncz=2, ppc=6, lb_ratio=2, real_bytes=4, seed=21,
+                   capacity_factor=3.0)
+    ref = B.Hybrid(cfg)
+    na = B.Hybrid(cfg)
+    n = B.NOALLOC_MAX_CELLS
+    assert ref.L.ncells == n
+    e, w, r = O.lattice(39)
+    f0 = W.gen_populations(w, ref.d["nnodes"], seed=4, eps=0.05, rho_eps=0.1).astype(np.float32)
+    for h in (ref, na):
+        h.f().copy_(torch.from_numpy(f0).view(h.f().shape))
+    cells = torch.arange(n, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+
+    def noalloc():
+        return B.lib().map_lbm_to_dsmc_noalloc(na.ctx, ctypes.c_void_p(cells.data_ptr()), n)
+
+    ref.map_lbm_to_dsmc(cells)
+    assert noalloc() == B.HYB_OK  # warm-up: the first call looks up the scratch address
+    _same(_state(ref), _state(na))
+    for h in (ref, na):
+        h.dsmc_step(1)
+    torch.cuda.synchronize()
+    stats0 = torch.cuda.memory_stats()
+    free0, _ = torch.cuda.mem_get_info()
+    ref.map_lbm_to_dsmc(cells)
+    assert noalloc() == B.HYB_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    stats1 = torch.cuda.memory_stats()
+    assert free1 == free0
+    for k in ("allocation.all.allocated", "segment.all.allocated", "reserved_bytes.all.current"):
+        assert stats1.get(k, 0) == stats0.get(k, 0), k
+    _same(_state(ref), _state(na))
+    assert ref.counters()["created"] > 0
