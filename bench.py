@@ -12,8 +12,11 @@ stream.
 
 Prints one JSON line. `--impl reference` times the CPU oracle instead (the reference arm:
 there is no reference implementation of the paper's method to run, only its restatement),
-on windows of the same channel in one process per host core. Under torchrun each rank runs
-an independent replica on its own GPU (replicas only).
+on windows of the same channel in one process per host core. Under torchrun (N > 1) the
+channel is cut into streamwise slabs, one per rank (each rank keeps the single-GPU channel's
+rows of a channel N times as long: weak scaling), exchanging the particles that leave a slab
+and the LB rows next to its boundaries point to point every step; `--replicas` runs
+independent replicas instead.
 """
 import argparse
 import hashlib
@@ -125,19 +128,25 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def traffic_record(kernel, workload):
-    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu summary, or None
-    if there is no capture of that workload or the kernel source changed since."""
+def traffic_record(kernel, workload, units):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary (profiles/traffic.json),
+    or None if the kernel's source changed since the capture. A capture of a smaller case of
+    the same kernel is scaled by the units (particles or nodes) one launch processes: the
+    traffic grows in proportion to them (the record states the bytes per unit)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(p))[kernel]
     except Exception:
         return None
-    if rec.get("workload") != workload:
-        return None
     src = os.path.join(ROOT, "paper_1512_08042_gb300", "csrc", rec["source"])
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return rec["bytes_per_launch"] if h == rec["source_sha"] else None
+    if h != rec["source_sha"]:
+        return None
+    if rec.get("workload") == workload:
+        return rec["bytes_per_launch"]
+    if "bytes_per_unit" in rec:
+        return rec["bytes_per_unit"] * units
+    return None
 
 
 def replica_config(cfg, rank):
@@ -145,6 +154,106 @@ def replica_config(cfg, rank):
     out = dict(cfg)
     out["seed"] = int(cfg["seed"]) + int(rank)
     return out
+
+
+def slab_step(h, dist, rank, world, nodes, cells, halo):
+    """One hybrid step of rank `rank`'s streamwise slab: the split DSMC step with the particle
+    exchange between neighbouring ranks, DSMC2LB, the exchange of the LB rows next to the
+    slab's boundaries, the LB step and LB2DSMC. The exchanges are point-to-point over
+    torch.distributed (NCCL between GPUs); the library's stream is synchronised around them."""
+    import torch
+    from paper_1512_08042_gb300 import binding as B
+    h.dsmc_move()
+    h.sync()
+    B.exchange_dist(h, dist, rank, world)
+    torch.cuda.synchronize()
+    h.dsmc_merge()
+    h.dsmc_collide()
+    if nodes.numel():
+        h.map_dsmc_to_lbm(nodes)
+    h.halo_pack(0, halo[0])
+    h.halo_pack(1, halo[1])
+    h.sync()
+    B.exchange_dist(h, dist, rank, world, halo)
+    torch.cuda.synchronize()
+    h.halo_unpack(0, halo[2])
+    h.halo_unpack(1, halo[3])
+    h.lbm_step(1)
+    if cells.numel():
+        h.map_lbm_to_dsmc(cells)
+
+
+def run_slab_rank(args, base, rank, world, local_rank, dist):
+    """Rank r of the streamwise decomposition (weak scaling: every rank holds base's rows of a
+    channel world times as long, with base's coupling strip placed in the middle of the whole
+    channel). Returns the rank's line pieces; times are the max over ranks."""
+    import torch
+    from paper_1512_08042_gb300 import binding as B
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    whole = dict(base, ncy=world * base["ncy"])
+    cfg = W.slab_config(base, rank, world)
+    h = B.Hybrid(cfg, device=dev)
+    d = h.d
+    gn, gc = W.coupling_sites(whole)
+    ln, lc = W.slab_sites(whole, cfg, d["yh"], gn, gc)
+    nodes = torch.from_numpy(ln).to(dev)
+    cells = torch.from_numpy(lc).to(dev)
+    nh = h.halo_size()
+    halo = [torch.empty(nh, dtype=h.real, device=dev) for _ in range(4)]
+    for _ in range(args.warmup):
+        slab_step(h, dist, rank, world, nodes, cells, halo)
+    torch.cuda.synchronize(dev)
+    dist.barrier()
+    clock_lines, stop = [], threading.Event()
+    th = threading.Thread(target=sample_clocks, args=(stop, clock_lines), daemon=True)
+    th.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize(dev)
+    dist.barrier()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(h.stream)
+    for _ in range(args.steps):
+        slab_step(h, dist, rank, world, nodes, cells, halo)
+    t1.record(h.stream)
+    torch.cuda.synchronize(dev)
+    total_ms = max_over_ranks(dist, t0.elapsed_time(t1), dev)
+    dist.barrier()
+    stop.set()
+    th.join(timeout=5)
+    # end to end: the same steps with the strip's moment sums read to the host every step
+    out = torch.empty((max(1, len(lc)), 20), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize(dev)
+    dist.barrier()
+    e0 = time.perf_counter()
+    e2e_steps = max(5, args.steps // 4)
+    for _ in range(e2e_steps):
+        slab_step(h, dist, rank, world, nodes, cells, halo)
+        if len(lc):
+            out[:len(lc)].copy_(h.acc()[cells.long()])
+        torch.cuda.synchronize(dev)
+    e2e_s = max_over_ranks(dist, time.perf_counter() - e0, dev)
+    rc, bits = h.sync_status()
+    n_particles = d["ncells"] * cfg["ppc"]
+    value = world * args.steps / (total_ms / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "hybrid steps/s (of a rank's slab, times ranks)",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if cfg["real_bytes"] == 4 else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "particles_per_rank": n_particles,
+                   "lb_nodes_per_rank": d["nnodes"], "parallelism": "streamwise slabs",
+                   "channel_rows": whole["ncy"], "l2": "inputs larger than L2"},
+        "dsmc_particle_updates_per_s": value * n_particles,
+        "clocks": summarize_clocks(clock_lines),
+        "gpu_launches": args.steps * 9,
+        "status": {"code": rc, "bits": bits},
+        "e2e": {"value": world * e2e_steps / e2e_s, "unit": "hybrid steps/s",
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": len(lc) * 160,
+                "api": "slab calls with the strip's moment sums read every step"},
+    }
+    h.close()
+    return line
 
 
 def max_over_ranks(dist, value, device):
@@ -525,6 +634,8 @@ def main():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--profile-kernel", default=None)
     ap.add_argument("--cpu-budget", type=float, default=16.0)
+    ap.add_argument("--replicas", action="store_true",
+                    help="with several GPUs, independent replicas instead of streamwise slabs")
     ap.add_argument("--no-cpu", action="store_true",
                     help="skip the FP64 oracle error sample and the CPU baseline")
     ap.add_argument("--profile-steps", type=int, default=0,
@@ -546,6 +657,22 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and args.impl == "ours" and not args.replicas:
+        # several GPUs: the channel in streamwise slabs, one per rank
+        import torch
+        import torch.distributed as tdist
+        import __graft_entry__ as G
+        if rank == 0:
+            G.build()
+        tdist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        tdist.barrier()
+        if rank != 0:
+            G.build()
+        line = run_slab_rank(args, W.WORKLOADS[args.workload], rank, world, local_rank, tdist)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        tdist.destroy_process_group()
+        return
     cfg = replica_config(W.WORKLOADS[args.workload], rank)
     nodes_np, cells_np = W.coupling_sites(cfg)
 
@@ -759,7 +886,9 @@ def main():
                                     "node-update) x units per launch" % (dsmc_b, lbm_b)
                                     if dominant in units else "design bytes (no method figure)",
                      "ms_per_launch": dom_ms,
-                     "traffic": traffic_record(dominant, args.workload),
+                     "traffic": traffic_record(dominant, args.workload,
+                                               n_particles if dominant in ("move", "collide", "fused")
+                                               else d["nnodes"]),
                      "design_bytes_per_launch": alg_design,
                      "design_frac": (alg_design / (dom_ms / 1e3) / 1e9 / peak) if dom_ms > 0 else None},
         "roofline_step": {"bytes_per_step": step_bytes, "achieved": step_bytes / (step_ms / 1e3) / 1e9,

@@ -199,3 +199,33 @@ def gen_particles(ncx, ncy, mean_ppc, seed, empty_fraction=0.0, vel_scale=1.0, d
     cs[1:] = np.cumsum(counts)
     out["cell_start"] = cs
     return out
+
+
+def slab_config(cfg, rank, world):
+    """Rank r of the streamwise decomposition of a channel world times as long as cfg's: the
+    rows [r ncy, (r + 1) ncy) of a channel of world * ncy rows (each rank keeps cfg's rows:
+    the work per GPU is fixed as ranks are added)."""
+    out = dict(cfg)
+    out["ncy_global"] = int(world) * int(cfg["ncy"])
+    out["y0"] = int(rank) * int(cfg["ncy"])
+    return out
+
+
+def slab_sites(whole_cfg, slab_cfg, yh, nodes, cells):
+    """The slab's own node and cell indices of the whole channel's coupling lists (node
+    (z ny + y) nx + x and cell (iz ncy + iy) ncx + ix of the whole channel; the slab's lattice
+    has yh ghost rows below its rows)."""
+    ncx, ncy, r = whole_cfg["ncx"], whole_cfg["ncy"], whole_cfg["lb_ratio"]
+    nly, y0 = slab_cfg["ncy"], slab_cfg["y0"]
+    nx, ny_w, ny_s = ncx * r, ncy * r, nly * r + 2 * yh
+    nodes = np.asarray(nodes, np.int64)
+    cells = np.asarray(cells, np.int64)
+    z, rem = nodes // (nx * ny_w), nodes % (nx * ny_w)
+    y, x = rem // nx, rem % nx
+    keep = (y >= y0 * r) & (y < (y0 + nly) * r)
+    ln = ((z * ny_s + (y - y0 * r + yh)) * nx + x)[keep]
+    cz, crem = cells // (ncx * ncy), cells % (ncx * ncy)
+    cy, cx = crem // ncx, crem % ncx
+    keepc = (cy >= y0) & (cy < y0 + nly)
+    lc = ((cz * nly + (cy - y0)) * ncx + cx)[keepc]
+    return ln.astype(np.int32), lc.astype(np.int32)

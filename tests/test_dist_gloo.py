@@ -203,3 +203,54 @@ def test_slab_oracle_ranks_equal_the_single_rank_oracle(tmp_path):
     want = np.array([o.counters()[k] for k in O.COUNTER_NAMES])
     assert np.array_equal(counters, want)
     assert want[O.COUNTER_NAMES.index("created")] > 0 and want[O.COUNTER_NAMES.index("collisions")] > 0
+
+
+# ---------------------------------------------------------------------------------------
+# The pairing of the slab exchange between ranks (binding.exchange_dist, which bench.py's
+# multi-GPU path uses): with stand-in buffers on CPU ranks over gloo, every rank's receive
+# buffers hold exactly its neighbours' send buffers (from below: the lower rank's "towards
+# higher rows" buffer; from above: the higher rank's "towards lower rows" one), in a ring of
+# two and of three ranks, for the particle buffers and the packed LB rows alike.
+
+class _StandInSlab:
+    def __init__(self, rank, nbytes):
+        g = torch.Generator().manual_seed(100 + rank)
+        self.buf = {("send", d): torch.randint(0, 255, (nbytes,), dtype=torch.uint8, generator=g)
+                    for d in (0, 1)}
+        self.buf.update({("recv", d): torch.zeros(nbytes, dtype=torch.uint8) for d in (0, 1)})
+
+    def xfer(self, which, d):
+        return self.buf[(which, d)]
+
+
+def _exchange_rank_main(rank, world, port, out_dir):
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    from paper_1512_08042_gb300 import binding as B
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    h = _StandInSlab(rank, 1000 + rank * 0)
+    B.exchange_dist(h, dist, rank, world)
+    halo = [torch.full((37,), float(10 * rank + k)) for k in range(2)] + [torch.zeros(37), torch.zeros(37)]
+    B.exchange_dist(h, dist, rank, world, halo)
+    torch.save({"send0": h.xfer("send", 0), "send1": h.xfer("send", 1), "recv0": h.xfer("recv", 0),
+                "recv1": h.xfer("recv", 1), "halo": halo}, os.path.join(out_dir, "x%d.pt" % rank))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_slab_exchange_pairs_neighbours(tmp_path, world):
+    port = _free_port()
+    mp.spawn(_exchange_rank_main, args=(world, port, str(tmp_path)), nprocs=world, join=True)
+    got = [torch.load(tmp_path / ("x%d.pt" % r)) for r in range(world)]
+    for r in range(world):
+        below, above = (r - 1) % world, (r + 1) % world
+        assert torch.equal(got[r]["recv0"], got[below]["send1"])
+        assert torch.equal(got[r]["recv1"], got[above]["send0"])
+        # packed LB rows: side 0 holds the slab below's side-1 pack, side 1 the slab above's
+        assert torch.equal(got[r]["halo"][2], got[below]["halo"][1])
+        assert torch.equal(got[r]["halo"][3], got[above]["halo"][0])
