@@ -7,6 +7,8 @@ within 1e-5 (FP32) or 1e-12 (FP64)."""
 import numpy as np
 import pytest
 
+from conftest import LB_TOL_FP32, LB_TOL_FP64, lb_err
+
 from oracle import oracle as O
 from paper_1512_08042_gb300 import workloads as W
 
@@ -140,15 +142,15 @@ def test_lbm_3d_steps_match_oracle(lattice, real_bytes, bgk):
     h.f().copy_(torch.from_numpy(f0.reshape(h.f().shape)))
     torch.cuda.synchronize()
     o.set_f(f0)
-    tol = 2e-5 if real_bytes == 4 else 1e-12
+    tol = LB_TOL_FP32 if real_bytes == 4 else LB_TOL_FP64
     for step in range(3):
         h.lbm_step(1)
         o.lbm_step(1)
         h.sync()
         gf, of = h.f().cpu().numpy(), o.f()
         assert gf.shape == of.shape == (lattice, 4, h.d["ny"], h.d["nx"])
-        err = np.abs(gf - of) / (np.abs(of) + 1e-3 * w[:, None, None, None])
-        assert err.max() < tol, (step, err.max())
+        err = lb_err(gf, of, w)
+        assert err < tol, (step, err)
     assert abs(h.f().double().sum().item() / f0.astype(np.float64).sum() - 1) < 1e-6
 
 
@@ -165,8 +167,8 @@ def test_lbm_3d_with_kn_profile_matches_oracle():
         o.lbm_step(1)
     h.sync()
     gf, of = h.f().cpu().numpy(), o.f()
-    err = np.abs(gf - of) / (np.abs(of) + 1e-3 * w[:, None, None, None])
-    assert err.max() < 2e-5
+    err = lb_err(gf, of, w)
+    assert err < LB_TOL_FP32, err
 
 
 @pytest.mark.parametrize("lattice,lb_ratio", [(39, 2), (19, 1)])

@@ -5,6 +5,8 @@ against directional differences of the GPU forward."""
 import numpy as np
 import pytest
 
+from conftest import LB_TOL_FP32, LB_TOL_FP64, lb_err
+
 from oracle import oracle as O
 from paper_1512_08042_gb300 import workloads as W
 
@@ -73,8 +75,8 @@ def test_lbm_step_nodes_matches_oracle(lattice, real_bytes):
         a, b = b, a
         o.lbm_step(1)
         h.sync()
-        err = np.abs(a.cpu().numpy() - o.f()) / (np.abs(o.f()) + 1e-3 * w[:, None, None])
-        assert err.max() < (2e-5 if real_bytes == 4 else 1e-12), (step, err.max())
+        err = lb_err(a.cpu().numpy(), o.f(), w)
+        assert err < (LB_TOL_FP32 if real_bytes == 4 else LB_TOL_FP64), (step, err)
     # the context's own populations were not touched
     assert torch.equal(h.f(), torch.from_numpy(np.tile(w[:, None], (1, h.d["nnodes"])).astype(
         f0.dtype).reshape(h.f().shape)).cuda())

@@ -12,6 +12,8 @@ of the whole channel, evaluated at those rows)."""
 import numpy as np
 import pytest
 
+from conftest import LB_TOL_FP32, LB_TOL_FP64, lb_err
+
 from oracle import oracle as O
 from paper_1512_08042_gb300 import workloads as W
 
@@ -106,8 +108,8 @@ def test_large_channel_lbm_steps_match_an_oracle_window(name):
     lo, hi = 3 * steps, rows_nodes - 3 * steps  # the pull reaches 3 rows per step
     gf = h.f()[:, lo:hi].cpu().numpy()
     of = o.f()[:, lo:hi]
-    err = np.abs(gf - of) / (np.abs(of) + 1e-3 * w[:, None, None])
-    assert err.max() < 2e-5, err.max()
+    err = lb_err(gf, of, w)
+    assert err < LB_TOL_FP32, err
     h.close()
     del h
     torch.cuda.empty_cache()

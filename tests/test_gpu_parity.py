@@ -4,6 +4,8 @@ compared bit for bit; floating-point state within the tolerances stated per test
 import numpy as np
 import pytest
 
+from conftest import LB_TOL_FP32, LB_TOL_FP64, lb_err
+
 from oracle import oracle as O
 from paper_1512_08042_gb300 import workloads as W
 
@@ -74,7 +76,9 @@ def test_init_matches_oracle(real_bytes):
     assert np.array_equal(f, o.f())
 
 
-def _compare_dsmc(h, o, real_bytes, acc_rtol=1e-5):
+def _compare_dsmc(h, o, real_bytes, acc_rtol=1e-5, acc_scale=None):
+    """acc_scale: per cell and moment, the sum over the steps of the cell's sums of |term|
+    (moment_abs_sums), the scale of each FP64 sum's rounding; else the column's largest sum."""
     assert h.n_tot() == o.scalars()["ntot"]
     assert np.array_equal(h.cell_start().cpu().numpy().astype(np.uint32), o.get(O.A_CELL_START))
     assert_particles_match(gpu_particles(h), o.particles(), real_bytes)
@@ -92,8 +96,8 @@ def _compare_dsmc(h, o, real_bytes, acc_rtol=1e-5):
     assert np.array_equal(h.nbar_sum().cpu().numpy().view(np.uint32), o.get(O.A_NBAR_SUM))
     ga = h.acc().cpu().numpy()
     oa = o.acc()
-    scale = np.abs(oa).max(axis=0, keepdims=True) + 1e-30
-    assert np.all(np.abs(ga - oa) <= acc_rtol * scale), np.abs((ga - oa) / scale).max()
+    scale = acc_scale if acc_scale is not None else np.abs(oa).max(axis=0, keepdims=True) + 1e-30
+    assert np.all(np.abs(ga - oa) <= acc_rtol * scale), np.abs((ga - oa) / (scale + 1e-300)).max()
     ctrl = h.ctrl().cpu().numpy()
     s = o.scalars()
     assert ctrl[B.CTRL_STEP] == s["step"] and ctrl[B.CTRL_NSAMPLES] == s["nsamples"]
@@ -102,13 +106,17 @@ def _compare_dsmc(h, o, real_bytes, acc_rtol=1e-5):
 
 @pytest.mark.parametrize("real_bytes,steps", [(4, 1), (4, 4), (8, 3)])
 def test_dsmc_steps_match_oracle(real_bytes, steps):
+    # the moment sums per element, each to 1e-5 of its own scale (the sum of |term| of the
+    # samples it holds)
     cfg = cfg_small(real_bytes=real_bytes, ma=0.3)
     h = B.Hybrid(cfg)
     o = O.Oracle(cfg)
+    scale = 0.0
     for _ in range(steps):
         h.dsmc_step(1)
         o.dsmc_step(1)
-    _compare_dsmc(h, o, real_bytes)
+        scale = scale + moment_abs_sums(o.particles(), o.get(O.A_CELL_START))
+    _compare_dsmc(h, o, real_bytes, acc_scale=scale)
 
 
 def test_dsmc_first_step_full_size_64x256_ppc50():
@@ -118,7 +126,7 @@ def test_dsmc_first_step_full_size_64x256_ppc50():
     o = O.Oracle(cfg)
     h.dsmc_step(1)
     o.dsmc_step(1)
-    _compare_dsmc(h, o, 4)
+    _compare_dsmc(h, o, 4, acc_scale=moment_abs_sums(o.particles(), o.get(O.A_CELL_START)))
 
 
 def test_dsmc_synthetic_state_empty_and_crowded_cells():
@@ -162,9 +170,9 @@ def test_lbm_steps_match_oracle(lattice, real_bytes):
         o.lbm_step(1)
         h.sync()
         gf, of = h.f().cpu().numpy(), o.f()
-        tol = 2e-5 if real_bytes == 4 else 1e-12
-        err = np.abs(gf - of) / (np.abs(of) + 1e-3 * w[:, None, None])
-        assert err.max() < tol, (step, err.max())
+        tol = LB_TOL_FP32 if real_bytes == 4 else LB_TOL_FP64
+        err = lb_err(gf, of, w)
+        assert err < tol, (step, err)
     # mass is conserved
     assert abs(h.f().double().sum().item() / f0.astype(np.float64).sum() - 1) < 1e-6
 
@@ -340,8 +348,8 @@ def test_lbm_bgk_steps_match_oracle(lattice, real_bytes):
         o.lbm_step(1)
         h.sync()
         gf, of = h.f().cpu().numpy(), o.f()
-        err = np.abs(gf - of) / (np.abs(of) + 1e-3 * w[:, None, None])
-        assert err.max() < (2e-5 if real_bytes == 4 else 1e-12), (step, err.max())
+        err = lb_err(gf, of, w)
+        assert err < (LB_TOL_FP32 if real_bytes == 4 else LB_TOL_FP64), (step, err)
     # differs from the regularised step (the ghost modes of the perturbed state survive)
     cfg_r = dict(cfg, lb_collision=0)
     o2 = O.Oracle(cfg_r)
@@ -425,8 +433,8 @@ def test_lbm_steps_with_kn_profile_match_oracle(lattice, real_bytes):
         h.lbm_step(1)
         o.lbm_step(1)
         h.sync()
-        err = np.abs(h.f().cpu().numpy() - o.f()) / (np.abs(o.f()) + 1e-3 * w[:, None, None])
-        assert err.max() < (2e-5 if real_bytes == 4 else 1e-12), (step, err.max())
+        err = lb_err(h.f().cpu().numpy(), o.f(), w)
+        assert err < (LB_TOL_FP32 if real_bytes == 4 else LB_TOL_FP64), (step, err)
 
 
 def test_hybrid_steps_with_kn_profile_fp64_match_oracle():
