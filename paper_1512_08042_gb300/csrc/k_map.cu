@@ -432,8 +432,10 @@ __device__ __forceinline__ void grad_coefficients(const MapArgs<Real>& a, int ce
             s0 += (double)p0[k];
             s1 += (double)p1[k];
         }
-    const double f0 = v0 ? s0 / (double)nk : 0.0;
-    const double f1 = v1 ? s1 / (double)nk : 0.0;
+    // nk is 1, 4 or 8: the product by its reciprocal is the exact quotient
+    const double inv_nk = 1.0 / (double)nk;
+    const double f0 = v0 ? s0 * inv_nk : 0.0;
+    const double f1 = v1 ? s1 * inv_nk : 0.0;
     const LatBasis<LAT>& B = lat_basis<LAT>();
     double t[32];
 #pragma unroll
