@@ -164,9 +164,12 @@ typedef struct {
  * dsmc_init and map_lbm_to_dsmc); the other half's counts are zero between calls.
  *   part          Real[ncells*bin][8]  particle records: x, y (positions in cell units, x
  *                                   across, y streamwise), vx, vy, vz (velocities in c_th
- *                                   units), z (3D only; else 0), the bits of a u32 stable-order
- *                                   key (the particle's origin slot c * bin + rank, written by
- *                                   the move; scratch within a step) and one unused value; [2]
+ *                                   units), z (3D only; else 0), the bits of a u32 order key
+ *                                   (written by the move, scratch within a step: o * bin + rank
+ *                                   for a particle displaced by at most one cell along every
+ *                                   axis, o = (3 (dz+1) + dy+1) 3 + dx+1 its neighbour offset;
+ *                                   else 2^31 + origin slot c * bin + rank; the collide orders
+ *                                   a cell's arrivals by it) and one unused value; [2]
  *   count         u32[ncells]       particles per cell; [2]
  *   crmax         Real[ncells]      (sigma_T c_r)_max / sigma_T per cell
  *   rem           Real[ncells]      NTC fractional candidate carried between steps
@@ -201,7 +204,9 @@ typedef struct {
 
 typedef struct hyb_ctx hyb_ctx; /* opaque, owned by the library */
 
-/* Host-only helpers (no GPU needed). Return HYB_EINVAL for invalid parameters. */
+/* Host-only helpers (no GPU needed). Return HYB_EINVAL for invalid parameters (among the
+ * limits: the channel's cells (ncx * rows * max(ncz, 1)) times 256 below 2^31, so that an
+ * origin slot fits an order key's 31 bits). */
 hyb_status hyb_derive(const hyb_params* p, hyb_derived* out);
 hyb_status hyb_layout_compute(const hyb_params* p, hyb_layout* out);
 /* The library's lattice: e[q][3] integer speeds, w[q] weights, r = c/c_s. Row order is the

@@ -81,7 +81,10 @@ bool valid(const Params* p) {
            (p->kn_profile == 0 || (p->kn_profile == 1 && p->kn_end > 0.0)) && p->ncz >= 0 &&
            p->accum_mode == 0 && p->ncy_global >= 0 &&
            (p->ncy_global > 0 ? (p->y0 >= 0 && p->ncy >= 4 && (int64_t)p->y0 + p->ncy <= p->ncy_global)
-                              : p->y0 == 0);
+                              : p->y0 == 0) &&
+           // the channel's cells times 256 slots below 2^31 (the library's order keys)
+           (double)p->ncx * (double)(p->ncy_global > 0 ? p->ncy_global : p->ncy) *
+                   (double)(p->ncz >= 2 ? p->ncz : 1) * 256.0 < 2147483648.0;
 }
 
 // A streamwise slab's split move (phase_move), its outbox towards lower (dir 0) or higher

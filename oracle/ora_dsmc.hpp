@@ -105,8 +105,8 @@ struct Dsmc {
     int y0() const { return p.ncy_global > 0 ? p.y0 : 0; }
 
     // Particles that left a streamwise slab in the last move, towards lower (0) and higher
-    // (1) rows of the channel, with their stable-order keys (channel origin cell << 32 |
-    // rank) and new channel cells; and the particles received from the neighbours.
+    // (1) rows of the channel, with their order tags (order_tag) and new channel cells; and
+    // the particles received from the neighbours.
     struct Moved {
         std::vector<Real> x, y, z, vx, vy, vz;
         std::vector<uint64_t> tag;
@@ -119,7 +119,7 @@ struct Dsmc {
     };
     Moved outbox[2];
     std::vector<uint32_t> key_;   // new local cell of each particle after the move
-    std::vector<uint64_t> tag_;   // stable-order key of each particle
+    std::vector<uint64_t> tag_;   // order tag of each particle (order_tag)
 
     // Diffuse isothermal re-emission from a wall at rest (Sec. 3.1, "fully diffuse
     // reflection"): normal speed from the flux-weighted Maxwellian sqrt(-2 ln U), tangential
@@ -230,10 +230,37 @@ struct Dsmc {
         return cell_key(px, py, pz);
     }
 
-    // Order by cell key; within a cell by the particles' previous order in the channel
-    // (origin cell, then rank in it: the tag), which is the previous slot order of the
-    // particles a context held, with received particles merged in. Deleted particles are
-    // dropped.
+    // The order of the particles of a cell before its collide (the paper does not fix one): a
+    // particle that came from a cell at most one cell away along every axis comes first,
+    // ordered by the offset o = 3 (dy + 1) + dx + 1 in 2D, 9 (dz + 1) + 3 (dy + 1) + dx + 1
+    // in 3D, of its displacement (dx, dy, dz) from its old cell to its new one, then by its
+    // rank in its old cell. The streamwise and spanwise displacements are periodic; where
+    // +1 and -1 are the same cell (a period of two), it counts as +1. Every other particle
+    // follows, ordered by its old channel cell, then rank. Returns the particle's tag, which
+    // sorts in this order.
+    uint64_t order_tag(uint32_t g_old, uint32_t g_new, uint32_t rank) const {
+        const int64_t nx = p.ncx, ny = channel_rows(p);
+        const int64_t ox = g_old % nx, oy = (g_old / nx) % ny, oz = g_old / (nx * ny);
+        const int64_t mx = g_new % nx, my = (g_new / nx) % ny, mz = g_new / (nx * ny);
+        auto periodic = [](int64_t d, int64_t period) -> int {  // -1, 0, 1, or 2: farther
+            const int64_t e = ((d % period) + period) % period;
+            if (e == 0) return 0;
+            if (e == 1) return 1;
+            if (e == period - 1) return -1;
+            return 2;
+        };
+        const int64_t dx = mx - ox;
+        const int dy = periodic(my - oy, ny);
+        const int dz = three_d() ? periodic(mz - oz, p.ncz) : 0;
+        if (dx < -1 || dx > 1 || dy == 2 || dz == 2)
+            return (1ull << 63) | ((uint64_t)g_old << 32) | rank;
+        const uint64_t o = three_d() ? (uint64_t)(9 * (dz + 1) + 3 * (dy + 1) + (dx + 1))
+                                     : (uint64_t)(3 * (dy + 1) + (dx + 1));
+        return (o << 32) | rank;
+    }
+
+    // Order by cell key; within a cell by the particles' tags (order_tag), the received
+    // particles of a streamwise slab merged in. Deleted particles are dropped.
     void sort_by_cell(const std::vector<uint32_t>& key, const std::vector<uint64_t>& tag) {
         std::vector<uint32_t> idx;
         idx.reserve(key.size());
@@ -357,9 +384,9 @@ struct Dsmc {
             const uint32_t gc = channel_cell(p, c);
             for (uint32_t i = cell_start[c]; i < cell_start[c + 1]; ++i) {
                 const uint32_t rank = i - cell_start[c];
-                tag_[i] = ((uint64_t)gc << 32) | rank;
                 const uint32_t gk = move_one(i, s, gc, rank);
                 if (gk == kDeadKey) continue;
+                tag_[i] = order_tag(gc, gk, rank);
                 int dir;
                 const int64_t lc = local_cell(gk, dir);
                 if (lc >= 0) {

@@ -244,6 +244,7 @@ hyb_status hyb_batch_init(const hyb_params* p, int32_t n, void* arena, uint64_t 
         pn[r + 1] = pn[r] + c.d.nnodes;
         const uint32_t pool = hyb::collide_pool(c);
         if (pool > d.pool) d.pool = pool;
+        if ((uint32_t)c.d.bin > d.maxbin) d.maxbin = (uint32_t)c.d.bin;
     }
     d.tot_cells = pc[n];
     d.tot_blocks = pb[n];

@@ -64,8 +64,51 @@ struct MoveCtx {
     Real dt, g;     // step and body-force velocity increment per step
     int32_t ncx, ncy, ncz;  // the channel's cells; ncz = 0 in 2D
     int32_t y0, nly;        // the rows [y0, y0 + nly) the context holds (0, ncy: all)
+    uint32_t bin;           // particle slots per cell
     uint64_t seed;
 };
+
+// The cell a particle leaves: its channel cell (the key of its wall draws) and its column,
+// channel row and spanwise layer.
+struct Origin {
+    uint32_t gc;
+    int32_t x, y, z;
+};
+
+template <typename Real>
+__device__ __forceinline__ Origin origin_of(const MoveCtx<Real>& m, uint32_t gc) {
+    Origin o;
+    o.gc = gc;
+    const uint32_t r = gc / (uint32_t)m.ncx;
+    o.x = (int32_t)(gc - r * (uint32_t)m.ncx);
+    o.y = (int32_t)(r % (uint32_t)m.ncy);
+    o.z = (int32_t)(r / (uint32_t)m.ncy);
+    return o;
+}
+
+// The particles of a cell are ordered, before its collide, by a key their move gives them. A
+// particle whose displacement (dx, dy, dz) from its old cell to its new one is at most one
+// cell along every axis (the channel and spanwise directions periodic, dy = +1 and -1 the
+// same cell in a channel of two rows) gets o bin + k, with o = (3 (dz + 1) + dy + 1) 3 + dx + 1
+// (dz = 0 in 2D, o < 9) and k its rank in its old cell; any other particle bit 31 and its
+// origin slot, old cell bin + k, so it follows the near ones. Keys are distinct within a cell.
+template <typename Real, bool Z3>
+__device__ __forceinline__ uint32_t order_key(const MoveCtx<Real>& m, const Origin& o, uint32_t k, int ix,
+                                              int iy, int iz) {
+    const int dx = ix - o.x;
+    int ey = iy - o.y;
+    if (ey < 0) ey += m.ncy;
+    const int dy = ey == 0 ? 0 : (ey == 1 ? 1 : (ey == m.ncy - 1 ? -1 : 2));
+    int dz = 0;
+    if constexpr (Z3) {
+        int ez = iz - o.z;
+        if (ez < 0) ez += m.ncz;
+        dz = ez == 0 ? 0 : (ez == 1 ? 1 : (ez == m.ncz - 1 ? -1 : 2));
+    }
+    if (dx < -1 || dx > 1 || dy > 1 || dz > 1) return 0x80000000u | (o.gc * m.bin + k);
+    const int off = (Z3 ? 9 * (dz + 1) : 0) + 3 * (dy + 1) + (dx + 1);
+    return (uint32_t)off * m.bin + k;
+}
 
 // Diffuse isothermal re-emission from a wall at rest: normal speed sqrt(-2 ln U) into the
 // gas, tangential components Gaussian, keyed by (cell, step, rank in cell, bounce).
@@ -128,15 +171,17 @@ __device__ __forceinline__ Real wrap_periodic(Real v, Real period) {
 }
 
 // Kick (v_y += g), then the flight of one step from (px, py, pz) with walls and periodic
-// wrap; the particle is rank k of the channel's cell c at the start of step s (the key of its
+// wrap; the particle is rank k of the channel's cell o at the start of step s (the key of its
 // wall draws). Returns its new cell of the context, (iz nly + iy - y0) ncx + ix, with dir = -1;
 // for a particle that leaves a streamwise slab, the channel's cell (iz ncy + iy) ncx + ix and
-// dir = 0 (towards lower rows) or 1 (higher rows, across the periodic end included).
+// dir = 0 (towards lower rows) or 1 (higher rows, across the periodic end included). `key` is
+// its order key in the new cell.
 template <typename Real, bool Z3>
-__device__ __forceinline__ uint32_t move_particle(const MoveCtx<Real>& m, uint32_t c, uint32_t k,
+__device__ __forceinline__ uint32_t move_particle(const MoveCtx<Real>& m, const Origin& o, uint32_t k,
                                                   uint32_t s, Real& px, Real& py, Real& pz, Real& ux,
                                                   Real& uy, Real& uz, uint32_t& hits, uint32_t& caps,
-                                                  int& dir) {
+                                                  int& dir, uint32_t& key) {
+    const uint32_t c = o.gc;
     uy = uy + m.g;
     const Real xn = px + ux * m.dt;
     if (xn >= (Real)0 && xn <= m.H) {
@@ -156,6 +201,7 @@ __device__ __forceinline__ uint32_t move_particle(const MoveCtx<Real>& m, uint32
         iz = (int)floor(pz);
         iz = iz < 0 ? 0 : (iz > m.ncz - 1 ? m.ncz - 1 : iz);
     }
+    key = order_key<Real, Z3>(m, o, k, ix, iy, iz);
     const int iyl = iy - m.y0;
     if (iyl >= 0 && iyl < m.nly) {
         dir = -1;
@@ -215,8 +261,8 @@ __device__ __forceinline__ uint32_t bin_arrival1(uint32_t* __restrict__ count, u
     return b + (uint32_t)__popc(peers & ((1u << lane) - 1u));
 }
 
-// One particle half as the move writes it: a moved particle goes to record key bin +
-// arrival, with its stable-order key (origin slot).
+// One particle half as the move writes it: a moved particle goes to record cell bin +
+// arrival, with its order key.
 template <typename Real>
 struct Half {
     Real* rec;

@@ -24,7 +24,7 @@ enum CtrlWord {
     CTRL_NTOT = 1,
     CTRL_STEP = 2,
     CTRL_NSAMPLES = 3,
-    CTRL_TICKET = 4,   // blocks finished, for the last-block update of the collide kernel
+    CTRL_RESERVED4 = 4,
     CTRL_NACC = 5,     // particles counted by the collide pass in progress
     CTRL_WORDS = 16,
 };
@@ -62,7 +62,7 @@ struct GradRec {
 enum : int { GR_A2 = 0, GR_A3 = 6, GR_U = 16, GR_C = 19 };
 
 // A particle is one record of kRec Real values: x, y, vx, vy, vz, z (3D only), its
-// stable-order key (the bits of a u32, written by the move) and one unused value, so that in
+// order key (the bits of a u32, written by the move) and one unused value, so that in
 // FP32 one record fills one 32-byte sector and a scattered write of a moved particle writes
 // whole sectors.
 constexpr int kRec = 8;
@@ -88,8 +88,8 @@ struct State {
 };
 
 // Everything a DSMC kernel needs, passed by value, for a step that starts from the sorted
-// particles of half p (srec): the move appends each particle, with its origin slot as its
-// stable-order key, to the bin of its new cell in half p^1 (drec); the collide puts each cell
+// particles of half p (srec): the move appends each particle, with its order key, to the
+// bin of its new cell in half p^1 (drec); the collide puts each cell
 // of half p^1 in stable order in place, collides and samples it; the fused pass takes the
 // arrivals of half p^1 through the collide and moves them on into half p for the next step.
 template <typename Real>
@@ -535,6 +535,7 @@ struct BatchDev {
     const int64_t* pre_l2d = nullptr;
     int64_t tot_cells = 0, tot_blocks = 0, tot_nodes = 0, tot_d2l = 0, tot_l2d = 0;
     uint32_t pool = 0;  // collide shared-memory pool: the largest over the replicas
+    uint32_t maxbin = 0;  // the largest bin over the replicas (the collide's key bitmaps)
     int move_block = 256, lbm_block = 128;
 };
 size_t dsmc_args_bytes(int real_bytes);

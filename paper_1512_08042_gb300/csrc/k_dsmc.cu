@@ -8,15 +8,18 @@
 // particles of half p takes two passes:
 //   k_move     one warp per source cell: body-force kick, free flight, diffuse wall
 //              re-emission (Sec. 3.1), periodic wrap, new cell; the moved particle and its
-//              stable-order key (origin slot = origin cell, then rank in it) are appended to
-//              the bin of its new cell in half p^1 by a warp-aggregated atomic.
-//   k_collide  32 consecutive cells per block, a group of 8 lanes per cell: the cell's keys
-//              are sorted (a bitonic sort in registers), each arrival is placed at its rank in
-//              a shared-memory pool, the NTC candidates of all 32 cells are drawn by the whole
+//              order key (its displacement's neighbour offset, then its rank in the old cell;
+//              see order_key) are appended to the bin of its new cell in half p^1 by a
+//              warp-aggregated atomic.
+//   k_collide  32 consecutive cells per block, a group of 8 lanes per cell: each arrival's
+//              rank by key comes from a bitmap of the cell's keys with prefix counts, each
+//              arrival is placed at its rank in a shared-memory pool, the NTC candidates of
+//              all 32 cells are drawn by the whole
 //              block and applied by one warp with a lane per cell (Eq. collisionnumber), the
 //              sums 1, v, vv, vvv are added to the FP64 cumulative sums of the cell (Sec. 2.1,
-//              Fig. 1) and the sorted cell is written back in place. The last block to finish
-//              advances the step counters.
+//              Fig. 1) and the sorted cell is written back in place.
+//   k_step_end one thread per context after each collide pass: publishes the particle count
+//              and advances the step and sample counters.
 // Several steps in one call fuse the collide of step s with the move of step s + 1: the
 // fused pass collides and samples a cell as above and then moves its particles straight from
 // the pool into the bins of the other half, so a particle's state is read and written once
@@ -129,6 +132,7 @@ __device__ __forceinline__ MoveCtx<Real> move_ctx(const DsmcArgs<Real>& a) {
     m.ncz = a.ncz;
     m.y0 = a.y0;
     m.nly = a.ncy;
+    m.bin = (uint32_t)a.bin;
     m.seed = a.seed;
     return m;
 }
@@ -158,9 +162,8 @@ __device__ __forceinline__ void move_cell(const DsmcArgs<Real>& a, int c, unsign
     if (lane == 0) a.count_s[c] = 0;  // half p is consumed; its counts start the next arrivals
     if (n > bin) n = bin;
     const int64_t base = (int64_t)c * bin;
-    // the channel's cell: the key of the wall draws and of the stable order
-    const uint32_t gc = global_cell((uint32_t)c, a.ncx, a.ncy, a.y0, a.ncy_g);
-    const int64_t gbase = (int64_t)gc * bin;
+    // the channel's cell: the key of the wall draws and of the order keys
+    const Origin org = origin_of(m, global_cell((uint32_t)c, a.ncx, a.ncy, a.y0, a.ncy_g));
     for (uint32_t k0 = 0; k0 == 0 || k0 < n; k0 += 64) {
         const uint32_t k1 = k0 + lane, k2 = k1 + 32;
         const bool act1 = k1 < n, act2 = k2 < n;
@@ -169,36 +172,36 @@ __device__ __forceinline__ void move_cell(const DsmcArgs<Real>& a, int c, unsign
         // the loads need only the bin size, not the count, so they travel with it
         if (k1 < bin) rec_get(src, base + k1, p1[0], p1[1], p1[2], p1[3], p1[4], p1[5], t1);
         if (k2 < bin) rec_get(src, base + k2, p2[0], p2[1], p2[2], p2[3], p2[4], p2[5], t2);
-        uint32_t key1 = 0, key2 = 0;
+        uint32_t key1 = 0, key2 = 0, ok1 = 0, ok2 = 0;
         int dir1 = -1, dir2 = -1;
         if (act1)
-            key1 = move_particle<Real, Z3>(m, gc, k1, s, p1[0], p1[1], p1[2], p1[3], p1[4], p1[5], hits,
-                                           caps, dir1);
+            key1 = move_particle<Real, Z3>(m, org, k1, s, p1[0], p1[1], p1[2], p1[3], p1[4], p1[5], hits,
+                                           caps, dir1, ok1);
         if (act2)
-            key2 = move_particle<Real, Z3>(m, gc, k2, s, p2[0], p2[1], p2[2], p2[3], p2[4], p2[5], hits,
-                                           caps, dir2);
+            key2 = move_particle<Real, Z3>(m, org, k2, s, p2[0], p2[1], p2[2], p2[3], p2[4], p2[5], hits,
+                                           caps, dir2, ok2);
         const bool loc1 = act1 && dir1 < 0, loc2 = act2 && dir2 < 0;
         uint32_t arr1, arr2;
         bin_arrival2(dst.count, key1, loc1, key2, loc2, lane, arr1, arr2);
         if (loc1) {
             if (arr1 < bin)
-                put_particle<Real, Z3>(dst, (int64_t)key1 * bin + arr1, (uint32_t)(gbase + k1), p1[0],
-                                       p1[1], p1[2], p1[3], p1[4], p1[5]);
+                put_particle<Real, Z3>(dst, (int64_t)key1 * bin + arr1, ok1, p1[0], p1[1], p1[2], p1[3],
+                                       p1[4], p1[5]);
             else
                 lost += 1;
         } else if (act1) {
-            send_particle<Real, Z3>(a.xrec, a.xkey, a.xcount, a.xcap, dir1, key1, (uint32_t)(gbase + k1),
-                                    p1[0], p1[1], p1[2], p1[3], p1[4], p1[5], lost);
+            send_particle<Real, Z3>(a.xrec, a.xkey, a.xcount, a.xcap, dir1, key1, ok1, p1[0], p1[1],
+                                    p1[2], p1[3], p1[4], p1[5], lost);
         }
         if (loc2) {
             if (arr2 < bin)
-                put_particle<Real, Z3>(dst, (int64_t)key2 * bin + arr2, (uint32_t)(gbase + k2), p2[0],
-                                       p2[1], p2[2], p2[3], p2[4], p2[5]);
+                put_particle<Real, Z3>(dst, (int64_t)key2 * bin + arr2, ok2, p2[0], p2[1], p2[2], p2[3],
+                                       p2[4], p2[5]);
             else
                 lost += 1;
         } else if (act2) {
-            send_particle<Real, Z3>(a.xrec, a.xkey, a.xcount, a.xcap, dir2, key2, (uint32_t)(gbase + k2),
-                                    p2[0], p2[1], p2[2], p2[3], p2[4], p2[5], lost);
+            send_particle<Real, Z3>(a.xrec, a.xkey, a.xcount, a.xcap, dir2, key2, ok2, p2[0], p2[1],
+                                    p2[2], p2[3], p2[4], p2[5], lost);
         }
     }
     move_events(a.counters, a.ctrl, hits, caps, lost, lane);
@@ -242,61 +245,28 @@ __host__ __device__ constexpr int pool_reals() {
     return Z3 ? 6 : 5;
 }
 
-// Ascending bitonic sort of G R keys held by the G lanes of a group, R per lane, in blocked
-// order: key r of group lane l is at position (r % B) + B l + B G (r / B). Exchanges between
-// positions less than B apart, or at least B G apart, stay in the lane's registers; the
-// others are shuffles between the lanes of the group. Constant trip counts: the keys stay
-// in registers.
-template <int G, int R, int B>
-__device__ __forceinline__ void bitonic_blocked(uint32_t (&v)[R]) {
-    static_assert(R % B == 0, "whole blocks of B keys per lane");
-    constexpr int N = G * R;
-    const int gl = (int)(lane_id() % G);
-#pragma unroll
-    for (int k = 2; k <= N; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            if (j < B || j >= B * G) {
-                const int jr = j < B ? j : j / G;  // distance in registers
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const int o = r ^ jr;
-                    if (r < o) {
-                        const int pos = (r % B) + B * gl + B * G * (r / B);
-                        const bool asc = (pos & k) == 0;
-                        const uint32_t lo = min(v[r], v[o]), hi = max(v[r], v[o]);
-                        v[r] = asc ? lo : hi;
-                        v[o] = asc ? hi : lo;
-                    }
-                }
-            } else {
-                const int jl = j / B;  // distance in lanes
-                const bool lower = (gl & jl) == 0;
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const uint32_t o = __shfl_xor_sync(kFull, v[r], jl);
-                    const int pos = (r % B) + B * gl + B * G * (r / B);
-                    const bool asc = (pos & k) == 0;
-                    v[r] = (lower == asc) ? min(v[r], o) : max(v[r], o);
-                }
-            }
-        }
-    }
+// Words of a cell's order-key bitmap: one bit per key below W bin, W = 9 neighbour offsets in
+// 2D and 27 in 3D (bin is a multiple of 32).
+template <bool Z3>
+__host__ __device__ constexpr int bitmap_words(uint32_t bin) {
+    return (Z3 ? 27 : 9) * (int)(bin / 32u);
 }
 
-// Ascending position of tag t among the n sorted keys st[0..n) (keys are distinct).
-__device__ __forceinline__ uint32_t sorted_rank(const uint32_t* st, uint32_t n, uint32_t t) {
-    uint32_t lo = 0, len = n;
-    while (len > 0) {
-        const uint32_t half = len >> 1;
-        if (st[lo + half] < t) {
-            lo += half + 1;
-            len -= half + 1;
-        } else {
-            len = half;
-        }
-    }
-    return lo;
+// Adds a particle's velocity moments to a lane's partial sums: u, the six distinct products
+// u_i u_j and the ten distinct u_i u_j u_k, in the order of the sampled sums (mo[0], the count,
+// is set after the reduction). The sums are compared with a tolerance, so they use fused
+// multiply-adds (this file is otherwise compiled without contraction).
+template <typename Real>
+__device__ __forceinline__ void add_moments(Real (&mo)[kMoments], Real ux, Real uy, Real uz) {
+    const Real xx = ux * ux, yy = uy * uy, zz = uz * uz, xy = ux * uy;
+    mo[1] += ux; mo[2] += uy; mo[3] += uz;
+    mo[4] += xx; mo[5] = fma(ux, uy, mo[5]); mo[6] = fma(ux, uz, mo[6]);
+    mo[7] += yy; mo[8] = fma(uy, uz, mo[8]); mo[9] += zz;
+    mo[10] = fma(xx, ux, mo[10]); mo[11] = fma(xx, uy, mo[11]);
+    mo[12] = fma(xx, uz, mo[12]); mo[13] = fma(yy, ux, mo[13]);
+    mo[14] = fma(xy, uz, mo[14]); mo[15] = fma(zz, ux, mo[15]);
+    mo[16] = fma(yy, uy, mo[16]); mo[17] = fma(yy, uz, mo[17]);
+    mo[18] = fma(zz, uy, mo[18]); mo[19] = fma(zz, uz, mo[19]);
 }
 
 // The block of 32 consecutive cells `blk` (of nblk) of one context: the arrivals of half
@@ -304,13 +274,12 @@ __device__ __forceinline__ uint32_t sorted_rank(const uint32_t* st, uint32_t n, 
 // place, MODE_FUSED moves them on (step s + 1) into the bins of half p (s*), except cells
 // marked in a.coupled, which are written back in place for LB2DSMC.
 template <typename Real, bool Z3, int MODE>
-__device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t pool, int blk,
-                                              int nblk) {
+__device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t pool, int blk) {
     constexpr int G = kGroup;
     constexpr int CPW = 32 / G;           // cells per warp in phases A and C
     constexpr int WARPS = kCollideWarps;
     constexpr int NC = WARPS * CPW;       // cells per block (one chain lane each in phase B)
-    constexpr int SMALL = 64;             // cells up to this size are sorted in registers
+    constexpr int SMALL = 64;             // keys of the first SMALL slots loaded with the count
     constexpr int R = SMALL / G;
     constexpr int KC = kChainSteps;       // candidates per cell drawn per pass of phase B
     constexpr int NR = pool_reals<Z3>();
@@ -327,11 +296,17 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
     const int grp = (int)lane / G, gl = (int)lane % G;
     const int gi = w * CPW + grp;  // the group's cell within the block
     const uint32_t bin = (uint32_t)a.bin;
-    // shared memory: the block's pool of vx, vy, vz, x, y (, z) (Real) and sorted keys (u32),
-    // `pool` slots each, then the candidates of one pass of phase B
+    // shared memory: the block's pool of vx, vy, vz, x, y (, z) (Real) and keys (u32), `pool`
+    // slots each, then the candidates of one pass of phase B, in the same space as the cells'
+    // key bitmaps of phase A (BW words and BW prefix bytes per cell)
     Real* pv = reinterpret_cast<Real*>(smem_raw);
     uint32_t* pst = reinterpret_cast<uint32_t*>(pv + NR * (size_t)pool);
     uint32_t* c_ij = pst + pool;
+    const int BW = bitmap_words<Z3>(bin);
+    const int CW = (BW + G - 1) / G;
+    const uint32_t lim = (uint32_t)BW * 32u;
+    uint32_t* s_bm = c_ij;
+    uint8_t* s_pf = reinterpret_cast<uint8_t*>(s_bm + NC * BW);
     Real* c_R = reinterpret_cast<Real*>(c_ij + NC * KC);
     Real* c_nx = c_R + NC * KC;
     Real* c_ny = c_nx + NC * KC;
@@ -348,8 +323,6 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
     const int64_t base = (int64_t)c * bin;
     // the channel's cell: the key of the random streams and of the stable order
     const uint32_t gc = global_cell((uint32_t)c, a.ncx, a.ncy, a.y0, a.ncy_g);
-    const int64_t gbase = (int64_t)gc * bin;
-    (void)gbase;
     const Real* __restrict__ drec = a.drec;
     // the cell's loads are issued together: count, the first SMALL keys and the leader's NTC
     // state
@@ -399,71 +372,56 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
         Real* qy = pv + 4 * pool + poff;
         Real* qz = pv + 5 * (size_t)pool + poff;  // 3D only
         uint32_t* st = pst + poff;
-        // A. stable order: the keys (origin slots) of cells of up to SMALL particles are
-        // sorted by their group with R keys per lane; a warp that holds a cell of up to
-        // 2 SMALL puts the keys of its cells in their shared-memory slots and sorts them two
-        // cells at a time, 2 G lanes with R keys each per cell. st[0..n) then holds the sorted
-        // keys. Larger cells keep their keys unsorted in st and rank each by counting.
+        // A. stable order: every arrival's rank among the cell's arrivals by order key. A key
+        // below W bin (a particle from a neighbouring cell) sets bit `key` of the cell's
+        // bitmap, and its rank is the number of set bits below it: the count before its word
+        // (a prefix over the words, kept modulo 256: a queried word holds its own bit, so
+        // the count is below bin) plus those below it within the word. Larger keys follow
+        // all of these, each ranked by counting the larger keys below it.
         {
-            if (__any_sync(kFull, n > (uint32_t)SMALL && n <= (uint32_t)(2 * SMALL))) {
-                const bool in2 = n <= (uint32_t)(2 * SMALL);
-                const uint32_t nn = in2 ? n : 0u;
-                uint32_t hi[R];
+            uint32_t* bm = s_bm + gi * BW;
+            uint8_t* pf = s_pf + gi * BW;
+            for (int q = gl; q < BW; q += G) bm[q] = 0u;
+            __syncwarp();
+            uint32_t nfar = 0;
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const uint32_t k = (uint32_t)(SMALL + gl + G * r);
-                    hi[r] = k < nn ? rec_tag(drec, base + k) : 0u;
-                }
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const uint32_t k = (uint32_t)(gl + G * r);
-                    if (k < nn) st[k] = vl[r];
-                    if (k + SMALL < nn) st[k + SMALL] = hi[r];
-                }
-                __syncwarp();
-#pragma unroll 1
-                for (int h = 0; h < 2; ++h) {
-                    const int g2 = 2 * h + (int)(lane >> 4);  // the group whose cell this half sorts
-                    const int l2 = (int)(lane & 15u);
-                    const uint32_t n2 = __shfl_sync(kFull, nn, g2 * G);
-                    uint32_t* st2 = pst + __shfl_sync(kFull, poff, g2 * G);
-                    uint32_t v[R];
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const uint32_t k = (uint32_t)(l2 + 2 * G * r);
-                        v[r] = k < n2 ? st2[k] : 0xFFFFFFFFu;
-                    }
-                    __syncwarp();
-                    bitonic_blocked<2 * G, R, R>(v);
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const uint32_t pos = (uint32_t)(r + R * l2);
-                        if (pos < n2) st2[pos] = v[r];
-                    }
-                    __syncwarp();
-                }
-            } else {
-                uint32_t v[R];
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const uint32_t k = (uint32_t)(gl + G * r);
-                    v[r] = (n <= (uint32_t)SMALL && k < n) ? vl[r] : 0xFFFFFFFFu;
-                }
-                bitonic_blocked<G, R, R>(v);
-                if (n <= (uint32_t)SMALL) {
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const uint32_t pos = (uint32_t)(r + R * gl);
-                        if (pos < n) st[pos] = v[r];
-                    }
+            for (int r = 0; r < R; ++r) {
+                const uint32_t k = (uint32_t)(gl + G * r);
+                if (k < n) {
+                    const uint32_t t = vl[r];
+                    st[k] = t;
+                    if (t < lim) atomicOr(&bm[t >> 5], 1u << (t & 31u));
+                    else ++nfar;
                 }
             }
-            if (n > (uint32_t)(2 * SMALL))
-                for (uint32_t k = gl; k < n; k += G) st[k] = rec_tag(drec, base + k);
+            for (uint32_t k = SMALL + gl; k < n; k += G) {
+                const uint32_t t = rec_tag(drec, base + k);
+                st[k] = t;
+                if (t < lim) atomicOr(&bm[t >> 5], 1u << (t & 31u));
+                else ++nfar;
+            }
             __syncwarp();
-            // each arrival k goes to the pool slot of its rank (its record carries its key);
-            // the loads of a lane's arrivals can be in flight together
-            const bool big = n > (uint32_t)(2 * SMALL);
+            // the prefix counts: lane gl owns words [gl CW, gl CW + CW)
+            const int q0 = gl * CW, q1 = min(q0 + CW, BW);
+            uint32_t tot = 0;
+            for (int q = q0; q < q1; ++q) tot += (uint32_t)__popc(bm[q]);
+            uint32_t inc = tot;
+#pragma unroll
+            for (int o = 1; o < G; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(kFull, inc, o, G);
+                if (gl >= o) inc += t;
+            }
+            uint32_t run = inc - tot;
+            for (int q = q0; q < q1; ++q) {
+                pf[q] = (uint8_t)run;
+                run += (uint32_t)__popc(bm[q]);
+            }
+#pragma unroll
+            for (int o = G / 2; o >= 1; o >>= 1) nfar += __shfl_xor_sync(kFull, nfar, o);
+            const uint32_t nnear = n - nfar;
+            __syncwarp();
+            // each arrival goes to the pool slot of its rank (its record carries its key); the
+            // loads of a lane's arrivals can be in flight together
             for (uint32_t k0 = 0; k0 < n; k0 += SJ * G) {
                 Real p[SJ][6];
                 uint32_t t[SJ];
@@ -477,11 +435,15 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
                     const uint32_t k = k0 + (uint32_t)(gl + G * j);
                     if (k < n) {
                         uint32_t rk;
-                        if (big) {
-                            rk = 0;
-                            for (uint32_t m2 = 0; m2 < n; ++m2) rk += st[m2] < t[j] ? 1u : 0u;
+                        if (t[j] < lim) {
+                            const uint32_t q = t[j] >> 5;
+                            rk = (uint32_t)pf[q] + (uint32_t)__popc(bm[q] & ((1u << (t[j] & 31u)) - 1u));
                         } else {
-                            rk = sorted_rank(st, n, t[j]);
+                            rk = nnear;
+                            for (uint32_t m2 = 0; m2 < n; ++m2) {
+                                const uint32_t u = st[m2];
+                                rk += (u >= lim && u < t[j]) ? 1u : 0u;
+                            }
                         }
                         vx[rk] = p[j][0];
                         vy[rk] = p[j][1];
@@ -661,26 +623,76 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
         }
         // C. moment sums of the collided particles; the cell is written back in place in
         // stable order (the collide, and cells the step's LB2DSMC regenerates), or moved on
+        // Every lane sums its particles gl, gl + G, gl + 2 G, ... in this order, whether in
+        // the loop below (cells written back) or in the move (cells moved on), so that the
+        // sums of a fused pass equal those of single steps bit for bit.
         Real mo[kMoments];
 #pragma unroll
         for (int q = 0; q < kMoments; ++q) mo[q] = (Real)0;
         const bool back = has_r && !moving;
-        for (uint32_t k = gl; k < n; k += G) {
+        const uint32_t nback = back ? n : 0u;
+        for (uint32_t k = gl; k < nback; k += G) {
             const Real ux = vx[k], uy = vy[k], uz = vz[k];
-            if (back) rec_put(a.drec, base + k, qx[k], qy[k], Z3 ? qz[k] : (Real)0, ux, uy, uz, 0u);
-            if (do_sample) {
-                // the sums are compared with a tolerance, so they use fused multiply-adds
-                // (this file is otherwise compiled without contraction); mo[0] is the count
-                const Real xx = ux * ux, yy = uy * uy, zz = uz * uz, xy = ux * uy;
-                mo[1] += ux; mo[2] += uy; mo[3] += uz;
-                mo[4] += xx; mo[5] = fma(ux, uy, mo[5]); mo[6] = fma(ux, uz, mo[6]);
-                mo[7] += yy; mo[8] = fma(uy, uz, mo[8]); mo[9] += zz;
-                mo[10] = fma(xx, ux, mo[10]); mo[11] = fma(xx, uy, mo[11]);
-                mo[12] = fma(xx, uz, mo[12]); mo[13] = fma(yy, ux, mo[13]);
-                mo[14] = fma(xy, uz, mo[14]); mo[15] = fma(zz, ux, mo[15]);
-                mo[16] = fma(yy, uy, mo[16]); mo[17] = fma(yy, uz, mo[17]);
-                mo[18] = fma(zz, uy, mo[18]); mo[19] = fma(zz, uz, mo[19]);
+            rec_put(a.drec, base + k, qx[k], qy[k], Z3 ? qz[k] : (Real)0, ux, uy, uz, 0u);
+            if (do_sample) add_moments(mo, ux, uy, uz);
+        }
+        if constexpr (MODE == MODE_FUSED) {
+            // the move of step s + 1, straight from the pool: particle k of cell c, two per
+            // lane, into the bins of half p with its order key
+            const MoveCtx<Real> m = move_ctx(a);
+            const Origin org = origin_of(m, gc);
+            const Half<Real> dst = half_s(a);
+            const uint32_t nm = moving && act ? n : 0u;
+            const uint32_t nmax = __reduce_max_sync(kFull, nm);
+            for (uint32_t k0 = 0; k0 < nmax; k0 += 2 * G) {
+                const uint32_t k1 = k0 + (uint32_t)gl, k2 = k1 + G;
+                const bool act1 = k1 < nm, act2 = k2 < nm;
+                Real p1[6] = {0, 0, 0, 0, 0, 0}, p2[6] = {0, 0, 0, 0, 0, 0};
+                if (act1) {
+                    p1[0] = qx[k1]; p1[1] = qy[k1]; if constexpr (Z3) p1[2] = qz[k1];
+                    p1[3] = vx[k1]; p1[4] = vy[k1]; p1[5] = vz[k1];
+                    if (do_sample) add_moments(mo, p1[3], p1[4], p1[5]);
+                }
+                if (act2) {
+                    p2[0] = qx[k2]; p2[1] = qy[k2]; if constexpr (Z3) p2[2] = qz[k2];
+                    p2[3] = vx[k2]; p2[4] = vy[k2]; p2[5] = vz[k2];
+                    if (do_sample) add_moments(mo, p2[3], p2[4], p2[5]);
+                }
+                uint32_t key1 = 0, key2 = 0, ok1 = 0, ok2 = 0;
+                int dir1 = -1, dir2 = -1;
+                if (act1)
+                    key1 = move_particle<Real, Z3>(m, org, k1, s + 1u, p1[0], p1[1], p1[2], p1[3], p1[4],
+                                                   p1[5], hits, caps, dir1, ok1);
+                if (act2)
+                    key2 = move_particle<Real, Z3>(m, org, k2, s + 1u, p2[0], p2[1], p2[2], p2[3], p2[4],
+                                                   p2[5], hits, caps, dir2, ok2);
+                const bool loc1 = act1 && dir1 < 0, loc2 = act2 && dir2 < 0;
+                uint32_t arr1, arr2;
+                bin_arrival2(dst.count, key1, loc1, key2, loc2, lane, arr1, arr2);
+                if (loc1) {
+                    if (arr1 < bin)
+                        put_particle<Real, Z3>(dst, (int64_t)key1 * bin + arr1, ok1, p1[0], p1[1], p1[2],
+                                               p1[3], p1[4], p1[5]);
+                    else
+                        lost += 1;
+                } else if (act1) {
+                    send_particle<Real, Z3>(a.xrec, a.xkey, a.xcount, a.xcap, dir1, key1, ok1, p1[0],
+                                            p1[1], p1[2], p1[3], p1[4], p1[5], lost);
+                }
+                if (loc2) {
+                    if (arr2 < bin)
+                        put_particle<Real, Z3>(dst, (int64_t)key2 * bin + arr2, ok2, p2[0], p2[1], p2[2],
+                                               p2[3], p2[4], p2[5]);
+                    else
+                        lost += 1;
+                } else if (act2) {
+                    send_particle<Real, Z3>(a.xrec, a.xkey, a.xcount, a.xcap, dir2, key2, ok2, p2[0],
+                                            p2[1], p2[2], p2[3], p2[4], p2[5], lost);
+                }
             }
+            // the arrivals of half p^1 are consumed: their count starts the next step's
+            // arrivals (a regenerated cell's count is consumed by LB2DSMC)
+            if (moving && act && gl == 0) a.count_d[c] = 0;
         }
         if (do_sample) {
             // halving exchange over the group: lane gl ends with the totals of moments
@@ -707,63 +719,6 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
                     if (mq < kMoments) atomicAdd(&a.acc[(size_t)c * kMoments + mq], widen(t[q]));
                 }
             }
-        }
-        if constexpr (MODE == MODE_FUSED) {
-            // the move of step s + 1, straight from the pool: particle k of cell c, two per
-            // lane, into the bins of half p with its origin slot as its stable-order key
-            const MoveCtx<Real> m = move_ctx(a);
-            const Half<Real> dst = half_s(a);
-            const uint32_t nm = moving && act ? n : 0u;
-            const uint32_t nmax = __reduce_max_sync(kFull, nm);
-            for (uint32_t k0 = 0; k0 < nmax; k0 += 2 * G) {
-                const uint32_t k1 = k0 + (uint32_t)gl, k2 = k1 + G;
-                const bool act1 = k1 < nm, act2 = k2 < nm;
-                Real p1[6] = {0, 0, 0, 0, 0, 0}, p2[6] = {0, 0, 0, 0, 0, 0};
-                if (act1) {
-                    p1[0] = qx[k1]; p1[1] = qy[k1]; if constexpr (Z3) p1[2] = qz[k1];
-                    p1[3] = vx[k1]; p1[4] = vy[k1]; p1[5] = vz[k1];
-                }
-                if (act2) {
-                    p2[0] = qx[k2]; p2[1] = qy[k2]; if constexpr (Z3) p2[2] = qz[k2];
-                    p2[3] = vx[k2]; p2[4] = vy[k2]; p2[5] = vz[k2];
-                }
-                uint32_t key1 = 0, key2 = 0;
-                int dir1 = -1, dir2 = -1;
-                if (act1)
-                    key1 = move_particle<Real, Z3>(m, gc, k1, s + 1u, p1[0], p1[1], p1[2], p1[3], p1[4],
-                                                   p1[5], hits, caps, dir1);
-                if (act2)
-                    key2 = move_particle<Real, Z3>(m, gc, k2, s + 1u, p2[0], p2[1], p2[2], p2[3], p2[4],
-                                                   p2[5], hits, caps, dir2);
-                const bool loc1 = act1 && dir1 < 0, loc2 = act2 && dir2 < 0;
-                uint32_t arr1, arr2;
-                bin_arrival2(dst.count, key1, loc1, key2, loc2, lane, arr1, arr2);
-                if (loc1) {
-                    if (arr1 < bin)
-                        put_particle<Real, Z3>(dst, (int64_t)key1 * bin + arr1, (uint32_t)(gbase + k1),
-                                               p1[0], p1[1], p1[2], p1[3], p1[4], p1[5]);
-                    else
-                        lost += 1;
-                } else if (act1) {
-                    send_particle<Real, Z3>(a.xrec, a.xkey, a.xcount, a.xcap, dir1, key1,
-                                            (uint32_t)(gbase + k1), p1[0], p1[1], p1[2], p1[3], p1[4],
-                                            p1[5], lost);
-                }
-                if (loc2) {
-                    if (arr2 < bin)
-                        put_particle<Real, Z3>(dst, (int64_t)key2 * bin + arr2, (uint32_t)(gbase + k2),
-                                               p2[0], p2[1], p2[2], p2[3], p2[4], p2[5]);
-                    else
-                        lost += 1;
-                } else if (act2) {
-                    send_particle<Real, Z3>(a.xrec, a.xkey, a.xcount, a.xcap, dir2, key2,
-                                            (uint32_t)(gbase + k2), p2[0], p2[1], p2[2], p2[3], p2[4],
-                                            p2[5], lost);
-                }
-            }
-            // the arrivals of half p^1 are consumed: their count starts the next step's
-            // arrivals (a regenerated cell's count is consumed by LB2DSMC)
-            if (moving && act && gl == 0) a.count_d[c] = 0;
         }
         __syncthreads();  // the pool is reused by the next round
     }
@@ -793,18 +748,8 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
         if (c1) atomicAdd(&a.counters[HYB_C_COLLISIONS], c1);
         if (nl) atomicAdd(&a.ctrl[CTRL_NACC], nl);
         if (fl) atomicOr(&a.ctrl[CTRL_STATUS], fl);
-        // the last block to finish publishes the particle count and advances the step and
-        // sample counters (every block has read the step by now); the fence orders this
-        // block's count before its ticket
-        __threadfence();
-        const unsigned ticket = atomicAdd(&a.ctrl[CTRL_TICKET], 1u);
-        if (ticket == nblk - 1) {
-            __threadfence();
-            a.ctrl[CTRL_NTOT] = atomicExch(&a.ctrl[CTRL_NACC], 0u);
-            if (do_sample) a.ctrl[CTRL_NSAMPLES] += 1;
-            a.ctrl[CTRL_STEP] = s + 1;
-            a.ctrl[CTRL_TICKET] = 0;
-        }
+        // (k_step_end, launched after the pass, publishes the count and advances the step: no
+        // block waits here for a grid-wide ticket while it holds its shared memory)
     }
 }
 
@@ -814,16 +759,31 @@ __global__ void __launch_bounds__(kCollideWarps * 32, CollideCfg<Real>::MINB)
     pdl_begin();
     if constexpr (BATCH) {
         const int r = replica_of(L.pre, L.nrep, (int64_t)blockIdx.x);
-        collide_block<Real, Z3, MODE>(L.tab[r], pool, (int)(blockIdx.x - L.pre[r]),
-                                      (int)(L.pre[r + 1] - L.pre[r]));
+        collide_block<Real, Z3, MODE>(L.tab[r], pool, (int)(blockIdx.x - L.pre[r]));
     } else {
-        collide_block<Real, Z3, MODE>(L.one, pool, (int)blockIdx.x, (int)gridDim.x);
+        collide_block<Real, Z3, MODE>(L.one, pool, (int)blockIdx.x);
     }
+}
+
+// The end of a DSMC step, after its collide pass: the particles the pass counted become the
+// live count, and the step and sample counters advance. One thread per context.
+template <typename Real, bool BATCH>
+__global__ void k_step_end(Launch<DsmcArgs<Real>> L) {
+    pdl_begin();
+    const int r = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (r >= (BATCH ? L.nrep : 1)) return;
+    const DsmcArgs<Real>& a = BATCH ? L.tab[r] : L.one;
+    uint32_t* ctrl = a.ctrl;
+    const uint32_t s = ctrl[CTRL_STEP];
+    ctrl[CTRL_NTOT] = ctrl[CTRL_NACC];
+    ctrl[CTRL_NACC] = 0u;
+    if (s % (uint32_t)a.sample_every == 0u) ctrl[CTRL_NSAMPLES] += 1u;
+    ctrl[CTRL_STEP] = s + 1u;
 }
 
 // Appends the particles a streamwise slab received from its neighbours (records and channel
 // cells from the slab below, then above) to the bins of their cells in half p^1, after the
-// slab's move, with their stable-order keys; then clears the slab's own send counts for its
+// slab's move, with their order keys; then clears the slab's own send counts for its
 // next move (the caller has copied its send buffers out by then). A received cell outside the
 // slab is skipped and raises HYB_ST_BAD_INPUT.
 template <typename Real, bool Z3>
@@ -947,10 +907,11 @@ int grid_for(const Ctx& c, int64_t work, int threads, int per_sm) {
 // Shared memory of a collide block: the pool (pool_reals Real and one u32 per slot) and one
 // pass of NTC candidates (u32 and 4 Real each).
 template <typename Real, bool Z3>
-size_t collide_smem(uint32_t pool) {
+size_t collide_smem(uint32_t pool, uint32_t bin) {
     constexpr int NC = kCollideWarps * (32 / kGroup);
-    return (size_t)pool * (pool_reals<Z3>() * sizeof(Real) + 4) +
-           (size_t)NC * kChainSteps * (4 + 4 * sizeof(Real));
+    const size_t cand = (size_t)NC * kChainSteps * (4 + 4 * sizeof(Real));
+    const size_t bits = ((size_t)NC * bitmap_words<Z3>(bin) * 5 + 15) / 16 * 16;
+    return (size_t)pool * (pool_reals<Z3>() * sizeof(Real) + 4) + (cand > bits ? cand : bits);
 }
 
 template <typename Real>
@@ -995,7 +956,7 @@ cudaError_t collide_impl(Ctx& c, int p) {
     c.cur_p = save;
     constexpr int NC = kCollideWarps * (32 / kGroup);
     const uint32_t pool = collide_pool(c);
-    const size_t smem = collide_smem<Real, Z3>(pool);
+    const size_t smem = collide_smem<Real, Z3>(pool, (uint32_t)c.d.bin);
     // (dynamic and static shared memory together may exceed the default 48 KB)
     cudaError_t e = cudaFuncSetAttribute(k_collide<Real, false, Z3, MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1007,7 +968,8 @@ cudaError_t collide_impl(Ctx& c, int p) {
     e = launch_pdl(k_collide<Real, false, Z3, MODE>, dim3(grid), dim3(kCollideWarps * 32), smem,
                    c.stream, L, pool);
     prof_end(c, kid);
-    return e;
+    if (e != cudaSuccess) return e;
+    return launch_pdl(k_step_end<Real, false>, dim3(1), dim3(32), 0, c.stream, L);
 }
 
 __global__ void k_debug_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out, int64_t n) {
@@ -1130,12 +1092,15 @@ cudaError_t batch_collide_impl(BatchDev& b, int cur_p) {
     L.pre = b.pre_blocks;
     L.nrep = b.nrep;
     L.total = b.tot_blocks;
-    const size_t smem = collide_smem<Real, false>(b.pool);
+    const size_t smem = collide_smem<Real, false>(b.pool, b.maxbin);
     cudaError_t e = cudaFuncSetAttribute(k_collide<Real, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    return launch_pdl(k_collide<Real, true>, dim3((unsigned)b.tot_blocks), dim3(kCollideWarps * 32), smem,
-                      b.stream, L, b.pool);
+    e = launch_pdl(k_collide<Real, true>, dim3((unsigned)b.tot_blocks), dim3(kCollideWarps * 32), smem,
+                   b.stream, L, b.pool);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(k_step_end<Real, true>, dim3((unsigned)((L.nrep + 127) / 128)), dim3(128), 0,
+                      b.stream, L);
 }
 
 }  // namespace

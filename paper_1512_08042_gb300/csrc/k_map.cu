@@ -491,7 +491,7 @@ __device__ __forceinline__ void grad_coefficients(const MapArgs<Real>& a, int ce
 // MOVE (the fused multi-step pass): the listed cells' particles were left in the half of
 // x.. (counts `count`) by the fused pass, the new particles are moved on at once (the move of
 // the next step, keyed like the particle's slot) into the bins of the half of ax.. with their
-// origin slots as stable-order keys, and a kept cell's particles are moved on likewise.
+// order keys, and a kept cell's particles are moved on likewise.
 template <typename Real, bool Z3>
 __device__ __forceinline__ MoveCtx<Real> l2d_move_ctx(const MapArgs<Real>& a) {
     MoveCtx<Real> m;
@@ -506,6 +506,7 @@ __device__ __forceinline__ MoveCtx<Real> l2d_move_ctx(const MapArgs<Real>& a) {
     m.y0 = 0;
     m.nly = a.ncy;
     m.ncz = a.ncz;
+    m.bin = (uint32_t)a.bin;
     m.seed = a.seed;
     return m;
 }
@@ -575,18 +576,17 @@ __device__ __forceinline__ void l2d_cells(const MapArgs<Real>& a, int first, int
                     const uint32_t k = k0 + threadIdx.x;
                     const bool act = k < nold;
                     Real px = 0, py = 0, pz = 0, ux = 0, uy = 0, uz = 0;
-                    uint32_t key = 0, tg;
+                    uint32_t key = 0, tg, ok = 0;
                     if (act) {
                         rec_get(a.rec, out0 + k, px, py, pz, ux, uy, uz, tg);
                         int dir;
-                        key = move_particle<Real, Z3>(m, gcell, k, t_step, px, py, pz, ux, uy, uz, hits, caps,
-                                                      dir);
+                        key = move_particle<Real, Z3>(m, origin_of(m, gcell), k, t_step, px, py, pz, ux, uy,
+                                                      uz, hits, caps, dir, ok);
                     }
                     const uint32_t arr = bin_arrival1(dst.count, key, act, lane);
                     if (act) {
                         if (arr < bin)
-                            put_particle<Real, Z3>(dst, (int64_t)key * bin + arr, (uint32_t)(gcell * bin + k), px,
-                                                   py, pz, ux, uy, uz);
+                            put_particle<Real, Z3>(dst, (int64_t)key * bin + arr, ok, px, py, pz, ux, uy, uz);
                         else
                             lost += 1;
                     }
@@ -642,7 +642,7 @@ __device__ __forceinline__ void l2d_cells(const MapArgs<Real>& a, int first, int
                 const bool mk = acc && rank < need;
                 const uint32_t k = produced + rank;
                 Real px = 0, py = 0, pz = 0, vx = 0, vy = 0, vz = 0;
-                uint32_t key = 0;
+                uint32_t key = 0, ok = 0;
                 if (mk) {
                     px = fx + (Real)u01f(r2.y);
                     py = fy + (Real)u01f(r2.z);
@@ -651,14 +651,14 @@ __device__ __forceinline__ void l2d_cells(const MapArgs<Real>& a, int first, int
                     vy = Y + uy;
                     vz = Z + uz;
                     int dir;
-                    key = move_particle<Real, Z3>(l2d_move_ctx<Real, Z3>(a), gcell, k, t_step, px, py, pz,
-                                                  vx, vy, vz, hits, caps, dir);
+                    const MoveCtx<Real> m = l2d_move_ctx<Real, Z3>(a);
+                    key = move_particle<Real, Z3>(m, origin_of(m, gcell), k, t_step, px, py, pz, vx, vy, vz,
+                                                  hits, caps, dir, ok);
                 }
                 const uint32_t arr = bin_arrival1(dst.count, key, mk, lane);
                 if (mk) {
                     if (arr < bin)
-                        put_particle<Real, Z3>(dst, (int64_t)key * bin + arr, (uint32_t)(gcell * bin + k), px,
-                                               py, pz, vx, vy, vz);
+                        put_particle<Real, Z3>(dst, (int64_t)key * bin + arr, ok, px, py, pz, vx, vy, vz);
                     else
                         lost += 1;
                 }

@@ -39,7 +39,7 @@ bool params_valid(const hyb_params* p) {
     if (std::ceil(p->capacity_factor * (double)p->ppc) > 256.0) return false;  // bin <= 256
     const double rows = p->ncy_global > 0 ? (double)p->ncy_global : (double)p->ncy;
     const double slots = (double)p->ncx * rows * (double)(p->ncz >= 2 ? p->ncz : 1) * 256.0;
-    if (slots >= 4294967295.0) return false;  // slot indices are u32
+    if (slots >= 2147483648.0) return false;  // origin slots fit the 31 bits of an order key
     return true;
 }
 

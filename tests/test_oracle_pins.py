@@ -317,6 +317,84 @@ def test_dsmc_poiseuille_bulk_curvature_follows_chapman_enskog_viscosity():
     assert abs(rel) < 4 * se + 0.04, (rel, se)
 
 
+@pytest.mark.parametrize("ncy,ncz", [(5, 0), (2, 0), (4, 3), (3, 2)])
+def test_order_in_a_cell_by_neighbour_offset_then_rank_far_ones_after(ncy, ncz):
+    # One collisionless, force-free step of particles displaced by up to two cells along every
+    # axis. The order of every cell's particles afterwards is recomputed here from its
+    # definition: particles displaced by at most one cell along every axis (streamwise and
+    # spanwise periodic, +1 taken where +1 and -1 are the same cell) first, by the offset
+    # o = [9 (dz + 1) +] 3 (dy + 1) + dx + 1, then by their rank in their old cell; the others
+    # after them, by old cell, then rank. Channels of two rows or layers cover the +1 = -1 case.
+    ncx = 8
+    cfg = small_cfg(ncx=ncx, ncy=ncy, ncz=ncz, ppc=6, kn=1e6, ma=0.0, capacity_factor=10.0)
+    o = O.Oracle(cfg)
+    d = o.d
+    dt = d["dt"]
+    td = ncz >= 2
+    nz = ncz if td else 1
+    rng = np.random.default_rng(11)
+    ncell = ncx * ncy * nz
+    per = rng.integers(2, 9, ncell)
+    cell = np.repeat(np.arange(ncell), per)  # grouped by old cell: rank = index in the group
+    n = len(cell)
+    ix, iy, iz = cell % ncx, (cell // ncx) % ncy, cell // (ncx * ncy)
+    ix = np.clip(ix, 2, 5)  # keep away from the walls: |vx dt| < 2 hits none
+    cell = (iz * ncy + iy) * ncx + ix
+    order = np.argsort(cell, kind="stable")
+    cell = cell[order]
+    ix, iy, iz = ix[order], iy[order], iz[order]
+    x = ix + rng.uniform(0.05, 0.95, n)
+    y = iy + rng.uniform(0.05, 0.95, n)
+    z = iz + rng.uniform(0.05, 0.95, n) if td else np.zeros(n)
+    vx = rng.uniform(-1.9, 1.9, n) / dt
+    vy = rng.uniform(-2.4, 2.4, n) / dt
+    vz = (rng.uniform(-2.4, 2.4, n) / dt) if td else rng.normal(0.0, 1.0, n)
+    counts = np.bincount(cell, minlength=ncell)
+    cs = np.zeros(ncell + 1, np.uint32)
+    cs[1:] = np.cumsum(counts)
+    rank = np.arange(n) - cs[cell]
+    o.set_particles(x, y, vx, vy, vz, cs, z=z if td else None)
+    o.dsmc_step(1)
+    assert o.counters()["collisions"] == 0 and o.counters()["wall_hits"] == 0
+
+    def wrap(v, period):
+        v = v - period * np.floor(v / period)
+        return np.where(v >= period, v - period, v)
+
+    nxp = np.floor(x + vx * dt).astype(int)
+    nyp = np.floor(wrap(y + vy * dt, ncy)).astype(int)
+    nzp = np.floor(wrap(z + vz * dt, nz)).astype(int) if td else np.zeros(n, int)
+    new = (nzp * ncy + nyp) * ncx + nxp
+
+    def disp(dlt, period):  # -1, 0, 1, or None (farther)
+        e = dlt % period
+        if e == 0:
+            return 0
+        if e == 1:
+            return 1
+        if e == period - 1:
+            return -1
+        return None
+
+    keys = []
+    nfar = 0
+    for i in range(n):
+        dx = int(nxp[i] - ix[i])
+        dy = disp(int(nyp[i] - iy[i]), ncy)
+        dz = disp(int(nzp[i] - iz[i]), nz) if td else 0
+        if abs(dx) <= 1 and dy is not None and dz is not None:
+            off = (9 * (dz + 1) if td else 0) + 3 * (dy + 1) + dx + 1
+            keys.append((int(new[i]), 0, off, int(rank[i])))
+        else:
+            nfar += 1
+            keys.append((int(new[i]), 1, int(cell[i]), int(rank[i])))
+    assert nfar >= 5 and n - nfar >= 20  # both kinds occur
+    want = sorted(range(n), key=lambda i: keys[i])
+    p = o.particles()
+    assert np.array_equal(p["vx"], vx[want]) and np.array_equal(p["vy"], vy[want])
+    assert np.array_equal(np.diff(o.get(O.A_CELL_START)), np.bincount(new, minlength=ncell))
+
+
 def test_sort_is_stable_by_cell_brute_force():
     # zero velocities and no force: a step is sort + sampling only
     cfg = small_cfg(ncx=7, ncy=3, ppc=5, ma=0.0, real_bytes=4, capacity_factor=12.0)
