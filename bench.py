@@ -470,10 +470,12 @@ def run_ensemble(args):
     dev = torch.device("cuda", 0)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     tuner = B.Batch(cfgs)
-    mb, lb = tuner.tune(nodes, cells)
+    tuner.tune(nodes, cells)
+    shapes = tuner.blocks()
     tuner.close()
     batch = B.Batch(cfgs)
-    batch.set_blocks(mb, lb)
+    for k, v in shapes.items():
+        batch.set_block(k, v)
     stream = batch.stream
     plain = [B.Hybrid(c, stream=stream) for c in cfgs]
     pn = [torch.from_numpy(x).to(dev) for x in nodes]
@@ -519,7 +521,7 @@ def run_ensemble(args):
         "data": "synthetic",
         "config": {"workload": "ensemble of %d channels (H 32-256 cells, 20-100 ppc, Kn 0.01-0.5)"
                                % len(cfgs), "replicas": len(cfgs), "particles": particles,
-                   "block_shapes": {"move": mb, "lbm": lb},
+                   "block_shapes": shapes,
                    "l2": "flushed before every timed step (512 MB write)"},
     }
     print(json.dumps(line), flush=True)

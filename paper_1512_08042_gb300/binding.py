@@ -11,7 +11,7 @@ import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "libdsmclbm.so")
-ABI_VERSION = 6
+ABI_VERSION = 7
 
 HYB_OK, HYB_EINVAL, HYB_ENOMEM, HYB_ECUDA, HYB_ECAPACITY, HYB_ETIMEOUT, HYB_ESAMPLING, HYB_ESTATE = range(8)
 ST_CAPACITY, ST_BOUNCE_CAP, ST_SCATTER_CAP, ST_SAMPLING_CAP, ST_CELL_OVERFLOW, ST_BAD_INPUT = (
@@ -59,7 +59,8 @@ EXPORTS = ["hyb_derive", "hyb_layout_compute", "hyb_lattice", "hyb_status_string
            "lbm_halo_unpack", "lbm_step", "sample_moments", "map_dsmc_to_lbm", "map_lbm_to_dsmc",
            "map_lbm_to_dsmc_noalloc", "map_dsmc_to_lbm_adjoint", "lbm_step_nodes", "lbm_interface_loss", "lbm_adjoint_step",
            "hyb_hybrid_step", "hyb_hybrid_step_host", "hyb_host_wait", "hyb_batch_layout", "hyb_batch_init", "hyb_batch_replica",
-           "hyb_batch_hybrid_step", "hyb_batch_set_blocks", "hyb_batch_tune",
+           "hyb_batch_hybrid_step", "hyb_batch_set_blocks", "hyb_batch_set_block", "hyb_batch_get_block",
+           "hyb_batch_tune",
            "hyb_batch_last_error", "hyb_batch_destroy", "hyb_current", "hyb_sync_status", "hyb_read_counters",
            "hyb_profile", "hyb_profile_harvest", "hyb_profile_read", "hyb_debug_philox",
            "hyb_last_error", "hyb_destroy"]
@@ -120,6 +121,9 @@ def lib():
     L.hyb_batch_replica.argtypes = [_vp, _i32, P(_vp)]
     L.hyb_batch_hybrid_step.argtypes = [_vp, _vp, _vp, _vp, _vp, _i32, _i32]
     L.hyb_batch_set_blocks.argtypes = [_vp, _i32, _i32]
+    L.hyb_batch_set_block.argtypes = [_vp, _i32, _i32]
+    L.hyb_batch_get_block.argtypes = [_vp, _i32]
+    L.hyb_batch_get_block.restype = _i32
     L.hyb_batch_tune.argtypes = [_vp, _vp, _vp, _vp, _vp, P(_i32), P(_i32)]
     L.hyb_batch_last_error.argtypes = [_vp]
     L.hyb_batch_last_error.restype = ctypes.c_char_p
@@ -645,8 +649,18 @@ class Batch:
     def set_blocks(self, move_block, lbm_block):
         _check(lib().hyb_batch_set_blocks(self.b, int(move_block), int(lbm_block)))
 
+    def set_block(self, kernel, threads):
+        """Block size of one kernel class (a name of KERNELS: move, collide, lbm, dsmc2lb, lb2dsmc)."""
+        _check(lib().hyb_batch_set_block(self.b, KERNELS[kernel], int(threads)))
+
+    def blocks(self):
+        """The block size of every kernel class of the batch."""
+        return {k: int(lib().hyb_batch_get_block(self.b, KERNELS[k]))
+                for k in ("move", "collide", "lbm", "dsmc2lb", "lb2dsmc")}
+
     def tune(self, nodes, cells):
-        """Picks the block shapes by timing hybrid steps (advances the batch); returns them."""
+        """Picks the block shapes by timing hybrid steps (advances the batch); returns the move
+        and LB sizes (blocks() gives every class)."""
         dn, pn, dc, pc = self._prepare(nodes, cells)
         mb, lb = _i32(), _i32()
         rc = lib().hyb_batch_tune(self.b, dn.data_ptr(), pn.ctypes.data_as(_vp), dc.data_ptr(),

@@ -353,28 +353,59 @@ hyb_status hyb_batch_hybrid_step(hyb_batch* b, const int32_t* dev_nodes, const i
     return HYB_OK;
 }
 
-hyb_status hyb_batch_set_blocks(hyb_batch* b, int32_t move_block, int32_t lbm_block) {
-    if (!b) return HYB_EINVAL;
-    const bool ok_m = move_block == 64 || move_block == 128 || move_block == 256;
-    const bool ok_l = lbm_block == 32 || lbm_block == 64 || lbm_block == 128;
-    if (!ok_m || !ok_l) return HYB_EINVAL;
-    b->dev.move_block = move_block;
-    b->dev.lbm_block = lbm_block;
-    drop_graphs(b);
+namespace {
+// Block sizes each kernel class of the batch may take (0 ends a list): the collide and LB2DSMC
+// have one, fixed by their design (32 cells of 8 lanes per block; 8 warps per cell).
+const int kShapes[5][4] = {{64, 128, 256, 0}, {256, 0, 0, 0}, {32, 64, 128, 0}, {64, 128, 256, 0},
+                           {256, 0, 0, 0}};
+int* block_of(hyb_batch* b, int kernel) {
+    switch (kernel) {
+        case hyb::K_MOVE: return &b->dev.move_block;
+        case hyb::K_LBM: return &b->dev.lbm_block;
+        case hyb::K_D2L: return &b->dev.d2l_block;
+        default: return nullptr;
+    }
+}
+bool shape_ok(int kernel, int threads) {
+    if (kernel < 0 || kernel > 4) return false;
+    for (int i = 0; i < 4 && kShapes[kernel][i]; ++i)
+        if (kShapes[kernel][i] == threads) return true;
+    return false;
+}
+}  // namespace
+
+hyb_status hyb_batch_set_block(hyb_batch* b, int32_t kernel, int32_t threads) {
+    if (!b || !shape_ok(kernel, threads)) return HYB_EINVAL;
+    int* p = block_of(b, kernel);
+    if (p && *p != threads) {
+        *p = threads;
+        drop_graphs(b);
+    }
     return HYB_OK;
+}
+
+int32_t hyb_batch_get_block(const hyb_batch* b, int32_t kernel) {
+    if (!b || kernel < 0 || kernel > 4) return -1;
+    int* p = block_of(const_cast<hyb_batch*>(b), kernel);
+    return p ? *p : kShapes[kernel][0];
+}
+
+hyb_status hyb_batch_set_blocks(hyb_batch* b, int32_t move_block, int32_t lbm_block) {
+    if (!b || !shape_ok(hyb::K_MOVE, move_block) || !shape_ok(hyb::K_LBM, lbm_block)) return HYB_EINVAL;
+    hyb_status s = hyb_batch_set_block(b, hyb::K_MOVE, move_block);
+    if (s == HYB_OK) s = hyb_batch_set_block(b, hyb::K_LBM, lbm_block);
+    return s;
 }
 
 hyb_status hyb_batch_tune(hyb_batch* b, const int32_t* dev_nodes, const int64_t* node_pre,
                           const int32_t* dev_cells, const int64_t* cell_pre, int32_t* move_block,
                           int32_t* lbm_block) {
     if (!b) return HYB_EINVAL;
-    const int mc[3] = {64, 128, 256}, lc[3] = {32, 64, 128};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return HYB_ECUDA;
-    auto time_steps = [&](int mb, int lb, float* ms) -> hyb_status {
-        hyb_status s = hyb_batch_set_blocks(b, mb, lb);
-        if (s != HYB_OK) return s;
-        s = hyb_batch_hybrid_step(b, dev_nodes, node_pre, dev_cells, cell_pre, 1, 1);  // capture
+    // the best of three replays of two hybrid steps from a captured graph
+    auto time_steps = [&](float* ms) -> hyb_status {
+        hyb_status s = hyb_batch_hybrid_step(b, dev_nodes, node_pre, dev_cells, cell_pre, 1, 1);  // capture
         if (s != HYB_OK) return s;
         float best = 1e30f;
         for (int k = 0; k < 3; ++k) {
@@ -390,32 +421,29 @@ hyb_status hyb_batch_tune(hyb_batch* b, const int32_t* dev_nodes, const int64_t*
         *ms = best;
         return HYB_OK;
     };
+    // one kernel class at a time, the others at their current shapes: move, LB, DSMC2LB
     hyb_status s = HYB_OK;
-    int bm = 256, bl = 128;
-    float best = 1e30f;
-    for (int i = 0; i < 3 && s == HYB_OK; ++i) {
-        float t = 0.f;
-        s = time_steps(mc[i], bl, &t);
-        if (s == HYB_OK && t < best) {
-            best = t;
-            bm = mc[i];
+    const int order[3] = {hyb::K_MOVE, hyb::K_LBM, hyb::K_D2L};
+    for (int ki = 0; ki < 3 && s == HYB_OK; ++ki) {
+        const int k = order[ki];
+        int best_t = hyb_batch_get_block(b, k);
+        float best = 1e30f;
+        for (int i = 0; i < 4 && kShapes[k][i] && s == HYB_OK; ++i) {
+            float t = 0.f;
+            s = hyb_batch_set_block(b, k, kShapes[k][i]);
+            if (s == HYB_OK) s = time_steps(&t);
+            if (s == HYB_OK && t < best) {
+                best = t;
+                best_t = kShapes[k][i];
+            }
         }
-    }
-    best = 1e30f;
-    for (int i = 0; i < 3 && s == HYB_OK; ++i) {
-        float t = 0.f;
-        s = time_steps(bm, lc[i], &t);
-        if (s == HYB_OK && t < best) {
-            best = t;
-            bl = lc[i];
-        }
+        if (s == HYB_OK) s = hyb_batch_set_block(b, k, best_t);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (s != HYB_OK) return s;
-    s = hyb_batch_set_blocks(b, bm, bl);
-    if (move_block) *move_block = bm;
-    if (lbm_block) *lbm_block = bl;
+    if (move_block) *move_block = b->dev.move_block;
+    if (lbm_block) *lbm_block = b->dev.lbm_block;
     return s;
 }
 

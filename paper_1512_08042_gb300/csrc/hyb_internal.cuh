@@ -268,6 +268,15 @@ __device__ __forceinline__ void pdl_begin() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
+// Asynchronous 16-byte copies from global to shared memory (cp.async, sm_80 and later),
+// committed as one group; wait_all waits for all of the thread's groups.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 template <typename... KArgs, typename... Args>
 cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
                        cudaStream_t stream, Args... args) {
@@ -536,7 +545,7 @@ struct BatchDev {
     int64_t tot_cells = 0, tot_blocks = 0, tot_nodes = 0, tot_d2l = 0, tot_l2d = 0;
     uint32_t pool = 0;  // collide shared-memory pool: the largest over the replicas
     uint32_t maxbin = 0;  // the largest bin over the replicas (the collide's key bitmaps)
-    int move_block = 256, lbm_block = 128;
+    int move_block = 256, lbm_block = 128, d2l_block = 128;
 };
 size_t dsmc_args_bytes(int real_bytes);
 void dsmc_args_fill(Ctx& c, int cur_p, void* out);

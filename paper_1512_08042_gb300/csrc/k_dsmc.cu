@@ -251,6 +251,8 @@ template <bool Z3>
 __host__ __device__ constexpr int bitmap_words(uint32_t bin) {
     return (Z3 ? 27 : 9) * (int)(bin / 32u);
 }
+// Keys of farther-displaced particles a cell lists for their ranks (more are counted in full).
+constexpr int kFarList = 8;
 
 // Adds a particle's velocity moments to a lane's partial sums: u, the six distinct products
 // u_i u_j and the ten distinct u_i u_j u_k, in the order of the sampled sums (mo[0], the count,
@@ -291,6 +293,7 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
     __shared__ uint32_t s_fits;
     __shared__ unsigned long long s_cnt[WARPS][2];
     __shared__ uint32_t s_live[WARPS], s_flags[WARPS];
+    __shared__ __align__(16) double s_acc[NC][kMoments];
     const int w = threadIdx.x >> 5;
     const unsigned lane = lane_id();
     const int grp = (int)lane / G, gl = (int)lane % G;
@@ -306,7 +309,8 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
     const int CW = (BW + G - 1) / G;
     const uint32_t lim = (uint32_t)BW * 32u;
     uint32_t* s_bm = c_ij;
-    uint8_t* s_pf = reinterpret_cast<uint8_t*>(s_bm + NC * BW);
+    uint32_t* s_fl = s_bm + NC * BW;
+    uint8_t* s_pf = reinterpret_cast<uint8_t*>(s_fl + NC * (kFarList + 1));
     Real* c_R = reinterpret_cast<Real*>(c_ij + NC * KC);
     Real* c_nx = c_R + NC * KC;
     Real* c_ny = c_nx + NC * KC;
@@ -327,6 +331,11 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
     // the cell's loads are issued together: count, the first SMALL keys and the leader's NTC
     // state
     uint32_t n_all = has ? a.count_d[c] : 0u;
+    // the cell's FP64 sums, copied to shared memory while the block works (10 x 16 bytes)
+    if (has && do_sample)
+        for (int j = gl; j < 2 * kMoments / 4; j += G)
+            cp_async16(&s_acc[gi][2 * j], &a.acc[(size_t)c * kMoments + 2 * j]);
+    cp_async_commit();
     uint32_t vl[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -377,28 +386,38 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
         // bitmap, and its rank is the number of set bits below it: the count before its word
         // (a prefix over the words, kept modulo 256: a queried word holds its own bit, so
         // the count is below bin) plus those below it within the word. Larger keys follow
-        // all of these, each ranked by counting the larger keys below it.
+        // all of these, each ranked by counting the larger keys below it (from a list of the
+        // cell's larger keys while they are few).
         {
             uint32_t* bm = s_bm + gi * BW;
             uint8_t* pf = s_pf + gi * BW;
+            uint32_t* fl = s_fl + gi * (kFarList + 1);  // count, then the first kFarList keys
             for (int q = gl; q < BW; q += G) bm[q] = 0u;
+            if (gl == 0) fl[0] = 0u;
             __syncwarp();
-            uint32_t nfar = 0;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const uint32_t k = (uint32_t)(gl + G * r);
                 if (k < n) {
                     const uint32_t t = vl[r];
                     st[k] = t;
-                    if (t < lim) atomicOr(&bm[t >> 5], 1u << (t & 31u));
-                    else ++nfar;
+                    if (t < lim) {
+                        atomicOr(&bm[t >> 5], 1u << (t & 31u));
+                    } else {
+                        const uint32_t j = atomicAdd(&fl[0], 1u);
+                        if (j < (uint32_t)kFarList) fl[1 + j] = t;
+                    }
                 }
             }
             for (uint32_t k = SMALL + gl; k < n; k += G) {
                 const uint32_t t = rec_tag(drec, base + k);
                 st[k] = t;
-                if (t < lim) atomicOr(&bm[t >> 5], 1u << (t & 31u));
-                else ++nfar;
+                if (t < lim) {
+                    atomicOr(&bm[t >> 5], 1u << (t & 31u));
+                } else {
+                    const uint32_t j = atomicAdd(&fl[0], 1u);
+                    if (j < (uint32_t)kFarList) fl[1 + j] = t;
+                }
             }
             __syncwarp();
             // the prefix counts: lane gl owns words [gl CW, gl CW + CW)
@@ -416,8 +435,7 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
                 pf[q] = (uint8_t)run;
                 run += (uint32_t)__popc(bm[q]);
             }
-#pragma unroll
-            for (int o = G / 2; o >= 1; o >>= 1) nfar += __shfl_xor_sync(kFull, nfar, o);
+            const uint32_t nfar = fl[0];
             const uint32_t nnear = n - nfar;
             __syncwarp();
             // each arrival goes to the pool slot of its rank (its record carries its key); the
@@ -438,6 +456,9 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
                         if (t[j] < lim) {
                             const uint32_t q = t[j] >> 5;
                             rk = (uint32_t)pf[q] + (uint32_t)__popc(bm[q] & ((1u << (t[j] & 31u)) - 1u));
+                        } else if (nfar <= (uint32_t)kFarList) {
+                            rk = nnear;
+                            for (uint32_t m2 = 0; m2 < nfar; ++m2) rk += fl[1 + m2] < t[j] ? 1u : 0u;
                         } else {
                             rk = nnear;
                             for (uint32_t m2 = 0; m2 < n; ++m2) {
@@ -637,38 +658,29 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
             if (do_sample) add_moments(mo, ux, uy, uz);
         }
         if constexpr (MODE == MODE_FUSED) {
-            // the move of step s + 1, straight from the pool: particle k of cell c, two per
-            // lane, into the bins of half p with its order key
+            // the move of step s + 1, straight from the pool: particle k of cell c, one per
+            // lane at a time, into the bins of half p with its order key
             const MoveCtx<Real> m = move_ctx(a);
             const Origin org = origin_of(m, gc);
             const Half<Real> dst = half_s(a);
             const uint32_t nm = moving && act ? n : 0u;
             const uint32_t nmax = __reduce_max_sync(kFull, nm);
-            for (uint32_t k0 = 0; k0 < nmax; k0 += 2 * G) {
-                const uint32_t k1 = k0 + (uint32_t)gl, k2 = k1 + G;
-                const bool act1 = k1 < nm, act2 = k2 < nm;
-                Real p1[6] = {0, 0, 0, 0, 0, 0}, p2[6] = {0, 0, 0, 0, 0, 0};
+            for (uint32_t k0 = 0; k0 < nmax; k0 += G) {
+                const uint32_t k1 = k0 + (uint32_t)gl;
+                const bool act1 = k1 < nm;
+                Real p1[6] = {0, 0, 0, 0, 0, 0};
                 if (act1) {
                     p1[0] = qx[k1]; p1[1] = qy[k1]; if constexpr (Z3) p1[2] = qz[k1];
                     p1[3] = vx[k1]; p1[4] = vy[k1]; p1[5] = vz[k1];
                     if (do_sample) add_moments(mo, p1[3], p1[4], p1[5]);
                 }
-                if (act2) {
-                    p2[0] = qx[k2]; p2[1] = qy[k2]; if constexpr (Z3) p2[2] = qz[k2];
-                    p2[3] = vx[k2]; p2[4] = vy[k2]; p2[5] = vz[k2];
-                    if (do_sample) add_moments(mo, p2[3], p2[4], p2[5]);
-                }
-                uint32_t key1 = 0, key2 = 0, ok1 = 0, ok2 = 0;
-                int dir1 = -1, dir2 = -1;
+                uint32_t key1 = 0, ok1 = 0;
+                int dir1 = -1;
                 if (act1)
                     key1 = move_particle<Real, Z3>(m, org, k1, s + 1u, p1[0], p1[1], p1[2], p1[3], p1[4],
                                                    p1[5], hits, caps, dir1, ok1);
-                if (act2)
-                    key2 = move_particle<Real, Z3>(m, org, k2, s + 1u, p2[0], p2[1], p2[2], p2[3], p2[4],
-                                                   p2[5], hits, caps, dir2, ok2);
-                const bool loc1 = act1 && dir1 < 0, loc2 = act2 && dir2 < 0;
-                uint32_t arr1, arr2;
-                bin_arrival2(dst.count, key1, loc1, key2, loc2, lane, arr1, arr2);
+                const bool loc1 = act1 && dir1 < 0;
+                const uint32_t arr1 = bin_arrival1(dst.count, key1, loc1, lane);
                 if (loc1) {
                     if (arr1 < bin)
                         put_particle<Real, Z3>(dst, (int64_t)key1 * bin + arr1, ok1, p1[0], p1[1], p1[2],
@@ -678,16 +690,6 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
                 } else if (act1) {
                     send_particle<Real, Z3>(a.xrec, a.xkey, a.xcount, a.xcap, dir1, key1, ok1, p1[0],
                                             p1[1], p1[2], p1[3], p1[4], p1[5], lost);
-                }
-                if (loc2) {
-                    if (arr2 < bin)
-                        put_particle<Real, Z3>(dst, (int64_t)key2 * bin + arr2, ok2, p2[0], p2[1], p2[2],
-                                               p2[3], p2[4], p2[5]);
-                    else
-                        lost += 1;
-                } else if (act2) {
-                    send_particle<Real, Z3>(a.xrec, a.xkey, a.xcount, a.xcap, dir2, key2, ok2, p2[0],
-                                            p2[1], p2[2], p2[3], p2[4], p2[5], lost);
                 }
             }
             // the arrivals of half p^1 are consumed: their count starts the next step's
@@ -712,11 +714,14 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
             }
             if (gl == 0) t[0] = (Real)n;  // the particle count, moment 0
             if (has_r) {
-                // one FP64 addition per sum, done in L2 (each sum has one writer per step)
+                // one FP64 addition per sum to the cell's sums copied in at the block's start
+                // (each sum has one writer per step)
+                cp_async_wait_all();
+                __syncwarp(0xFFu << (8 * grp));
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
                     const int mq = 3 * gl + q;
-                    if (mq < kMoments) atomicAdd(&a.acc[(size_t)c * kMoments + mq], widen(t[q]));
+                    if (mq < kMoments) a.acc[(size_t)c * kMoments + mq] = s_acc[gi][mq] + widen(t[q]);
                 }
             }
         }
@@ -910,7 +915,7 @@ template <typename Real, bool Z3>
 size_t collide_smem(uint32_t pool, uint32_t bin) {
     constexpr int NC = kCollideWarps * (32 / kGroup);
     const size_t cand = (size_t)NC * kChainSteps * (4 + 4 * sizeof(Real));
-    const size_t bits = ((size_t)NC * bitmap_words<Z3>(bin) * 5 + 15) / 16 * 16;
+    const size_t bits = ((size_t)NC * (bitmap_words<Z3>(bin) * 5 + (kFarList + 1) * 4) + 15) / 16 * 16;
     return (size_t)pool * (pool_reals<Z3>() * sizeof(Real) + 4) + (cand > bits ? cand : bits);
 }
 

@@ -175,7 +175,7 @@ __device__ __forceinline__ void d2l_entries(const MapArgs<Real>& a, int first, i
 
 // DSMC2LB: one warp per listed node (the listed nodes of all replicas in the batch form).
 template <typename Real, class LAT, bool BATCH>
-__global__ void __launch_bounds__(128) k_d2l(Launch<MapArgs<Real>> L) {
+__global__ void __launch_bounds__(256) k_d2l(Launch<MapArgs<Real>> L) {
     pdl_begin();
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if constexpr (BATCH) {
@@ -938,8 +938,8 @@ cudaError_t batch_d2l_impl(BatchDev& b, int cur_p, int cur_f) {
     L.pre = b.pre_d2l;
     L.nrep = b.nrep;
     L.total = b.tot_d2l;
-    const int64_t blocks = (b.tot_d2l * 32 + 127) / 128;
-    return launch_pdl(k_d2l<Real, LAT, true>, dim3((unsigned)blocks), dim3(128), 0, b.stream, L);
+    const int64_t blocks = (b.tot_d2l * 32 + b.d2l_block - 1) / b.d2l_block;
+    return launch_pdl(k_d2l<Real, LAT, true>, dim3((unsigned)blocks), dim3(b.d2l_block), 0, b.stream, L);
 }
 
 template <typename Real, class LAT>

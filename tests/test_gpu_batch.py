@@ -59,8 +59,13 @@ def test_batch_tuner_picks_valid_shapes_and_keeps_results():
     b = B.Batch(cfgs)
     mb, lb = b.tune(nodes, cells)
     assert mb in (64, 128, 256) and lb in (32, 64, 128)
+    shapes = b.blocks()
+    assert shapes["move"] == mb and shapes["lbm"] == lb and shapes["dsmc2lb"] in (64, 128, 256)
+    assert shapes["collide"] == 256 and shapes["lb2dsmc"] == 256
+    with pytest.raises(B.HybError):
+        b.set_block("collide", 128)  # one shape, fixed by the kernel's design
     b.hybrid_step(nodes, cells, nsteps=2)
-    steps = 42 + 2
+    steps = 63 + 2  # 7 steps per shape tried: 3 move, 3 LB, 3 DSMC2LB
     for g, cfg, n, c in zip(b.replicas, cfgs, nodes, cells):
         h = B.Hybrid(cfg)
         h.hybrid_step(torch.from_numpy(n).cuda(), torch.from_numpy(c).cuda(), nsteps=steps, use_graph=True)
