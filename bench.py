@@ -141,9 +141,11 @@ def traffic_record(kernel, workload, units):
         rec = json.load(open(p))[kernel]
     except Exception:
         return None
-    src = os.path.join(ROOT, "paper_1512_08042_gb300", "csrc", rec["source"])
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if h != rec["source_sha"]:
+    srcs = rec["source"] if isinstance(rec["source"], list) else [rec["source"]]
+    sha = hashlib.sha256()
+    for f in srcs:  # the kernel's translation unit and the headers it includes, in this order
+        sha.update(open(os.path.join(ROOT, "paper_1512_08042_gb300", "csrc", f), "rb").read())
+    if sha.hexdigest()[:16] != rec["source_sha"]:
         return None
     if rec.get("workload") == workload:
         return rec["bytes_per_launch"]
