@@ -391,63 +391,69 @@ __device__ __forceinline__ int packed_pair_index(int i, int j) {
     return i == 0 ? j : (i == 1 ? 2 + j : 5);
 }
 
-// Table 1 step 1 for the cell `cell`, by one warp, in FP64 (the Grad-coefficient solve).
-// Lane l holds the cell-mean populations q = l and l + 32 (zero past Q), the mean of the
-// cell's lb_ratio^2 (3D: ^3) nodes summed in FP64. The raw moments R_k = sum_q f_q B_k(xi_q)
-// (k < 20) are summed over the lanes; lane k then forms one comoving coefficient from them:
-//   u_i = R_i / rho,
-//   a2_ij = R_ij / rho - u_i u_j - d_ij                                     (= sum f c c / rho - d),
-//   a3_ijk = (R_ijk - u_i R_jk - u_j R_ik - u_k R_ij) / rho + 2 u_i u_j u_k   (= sum f c c c / rho),
-// c = xi - u, exact identities of the centred sums. Returns, in every lane, the packed FP64
-// value (lane k < 20 holds value k: a2[6], a3[10], u[3], C = 1 + 30 M) and rho.
+// Table 1 step 1 for the cell `cell`, in FP64 (the Grad-coefficient solve), by the whole
+// block of kL2DWarps warps: FP64 runs at a small fraction of the FP32 rate, so its work is
+// spread over the SM's four schedulers.
+//   1. thread q < Q: the cell-mean population f_q, the mean of the cell's lb_ratio^2 (3D: ^3)
+//      nodes summed in FP64;
+//   2. warp w, lane k < 20: the partial raw moment sum_q f_q B_k(xi_q) over the populations
+//      q in [w QW, (w + 1) QW) (fused multiply-adds, q ascending);
+//   3. warp 0, lane k: R_k, the sum of the warps' partials (w ascending), then one comoving
+//      coefficient from the raw moments:
+//        u_i = R_i / rho,
+//        a2_ij = R_ij / rho - u_i u_j - d_ij                                 (= sum f c c / rho - d),
+//        a3_ijk = (R_ijk - u_i R_jk - u_j R_ik - u_k R_ij) / rho + 2 u_i u_j u_k (= sum f c c c / rho),
+//      c = xi - u, exact identities of the centred sums.
+// Every thread of the block calls it. Returns, in the lanes of warp 0, the packed FP64 value
+// (lane k < 20 holds value k: a2[6], a3[10], u[3], C = 1 + 30 M) and rho.
 template <typename Real, class LAT, bool Z3>
-__device__ __forceinline__ void grad_coefficients(const MapArgs<Real>& a, int cell, unsigned lane,
-                                                  double& mine, double& rho_out) {
+__device__ __forceinline__ void grad_coefficients(const MapArgs<Real>& a, int cell, double& mine,
+                                                  double& rho_out) {
     constexpr int Q = LAT::Q;
     constexpr int NM = LAT::ORDER >= 3 ? kMoments : 10;  // raw moments of the order
+    constexpr int W = kL2DWarps;
+    constexpr int QW = (Q + W - 1) / W;
+    __shared__ double s_f[Q];
+    __shared__ double s_part[W][kMoments];
+    const int t = (int)threadIdx.x, w = t >> 5;
+    const unsigned lane = lane_id();
     const int r = a.lb_ratio;
-    const int q0 = (int)lane, q1 = (int)lane + 32;
-    const bool v0 = q0 < Q, v1 = q1 < Q;
     const int ix = cell % a.ncx, iy = (cell / a.ncx) % a.ncy, iz = cell / (a.ncx * a.ncy);
-    // mean populations of the cell's nodes (r^2 in 2D, r^3 in 3D)
     constexpr int KN = Z3 ? 8 : 4;  // lb_ratio <= 2
     const int nk = Z3 ? r * r * r : r * r;
-    Real p0[KN], p1[KN];
+    if (t < Q) {
+        Real p[KN];
 #pragma unroll
-    for (int k = 0; k < KN; ++k) {
-        p0[k] = 0;
-        p1[k] = 0;
-        if (k < nk) {
-            const int dz = Z3 ? k / (r * r) : 0, dy = (k / r) % r, dx = k % r;
-            const int64_t node =
-                ((int64_t)(iz * r + dz) * a.ny + (iy * r + dy + a.yh)) * a.nx + (ix * r + dx);
-            if (v0) p0[k] = a.f[(int64_t)q0 * a.nnodes + node];
-            if (v1) p1[k] = a.f[(int64_t)q1 * a.nnodes + node];
+        for (int k = 0; k < KN; ++k) {
+            p[k] = 0;
+            if (k < nk) {
+                const int dz = Z3 ? k / (r * r) : 0, dy = (k / r) % r, dx = k % r;
+                const int64_t node =
+                    ((int64_t)(iz * r + dz) * a.ny + (iy * r + dy + a.yh)) * a.nx + (ix * r + dx);
+                p[k] = a.f[(int64_t)t * a.nnodes + node];
+            }
         }
+        double sum = 0.0;
+#pragma unroll
+        for (int k = 0; k < KN; ++k)
+            if (k < nk) sum += (double)p[k];
+        // nk is 1, 4 or 8: the product by its reciprocal is the exact quotient
+        s_f[t] = sum * (nk == 1 ? 1.0 : (nk == 4 ? 0.25 : 0.125));
     }
-    double s0 = 0.0, s1 = 0.0;
-#pragma unroll
-    for (int k = 0; k < KN; ++k)
-        if (k < nk) {
-            s0 += (double)p0[k];
-            s1 += (double)p1[k];
-        }
-    // nk is 1, 4 or 8: the product by its reciprocal is the exact quotient
-    const double inv_nk = 1.0 / (double)nk;
-    const double f0 = v0 ? s0 * inv_nk : 0.0;
-    const double f1 = v1 ? s1 * inv_nk : 0.0;
-    const LatBasis<LAT>& B = lat_basis<LAT>();
-    double t[32];
-#pragma unroll
-    for (int k = 0; k < 32; ++k) t[k] = 0.0;
-#pragma unroll
-    for (int k = 0; k < NM; ++k) {
-        const double lo = v0 ? f0 * B.b[q0][k] : 0.0;
-        const double hi = v1 ? f1 * B.b[q1][k] : 0.0;
-        t[k] = lo + hi;
+    __syncthreads();
+    if (lane < (unsigned)NM) {
+        const LatBasis<LAT>& B = lat_basis<LAT>();
+        const int qa = w * QW, qb = qa + QW < Q ? qa + QW : Q;
+        double part = 0.0;
+        for (int q = qa; q < qb; ++q) part = fma(s_f[q], B.b[q][lane], part);
+        s_part[w][lane] = part;
     }
-    halving_sum<double, 32>(t, lane);  // lane k holds R_k
-    const double R = t[0];
+    __syncthreads();
+    if (w != 0) return;
+    double R = 0.0;
+    if (lane < (unsigned)NM)
+#pragma unroll
+        for (int v = 0; v < W; ++v) R += s_part[v][lane];
     auto at = [&](int k) { return __shfl_sync(kFull, R, k); };
     const double rho = at(0);
     double inv = 0.0;
@@ -470,9 +476,15 @@ __device__ __forceinline__ void grad_coefficients(const MapArgs<Real>& a, int ce
                              u[k] * R2[packed_pair_index(i, j)];
         val = (R - cross) * inv + 2.0 * u[i] * u[j] * u[k];
     }
-    double M = fabs(val);
+    // M = max |val| over the lanes: the bits of non-negative doubles order as unsigned integers
+    // (a NaN coefficient is left out, as fmax does)
+    unsigned long long mb = val == val ? (unsigned long long)__double_as_longlong(fabs(val)) : 0ull;
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) M = fmax(M, __shfl_xor_sync(kFull, M, o));
+    for (int o = 16; o >= 1; o >>= 1) {
+        const unsigned long long ob = (unsigned long long)__shfl_xor_sync(kFull, (long long)mb, o);
+        mb = ob > mb ? ob : mb;
+    }
+    const double M = __longlong_as_double((long long)mb);
     // packed values: lane k < 16 takes coefficient k (a2 at lanes 4-9, a3 at 10-19), lanes
     // 16-18 u, lane 19 C
     const double mv = __shfl_sync(kFull, val, (int)(lane + 4u) & 31);
@@ -536,9 +548,9 @@ __device__ __forceinline__ void l2d_cells(const MapArgs<Real>& a, int first, int
         // the channel's cell: the key of the cell's random streams and of the stable order
         const uint32_t gcell = global_cell(cell, a.ncx, a.ncy, a.y0, a.ncy_g);
         const uint32_t old = threadIdx.x == 0 ? a.count[cell] : 0u;
+        double mine = 0.0, rho = 0.0;
+        grad_coefficients<Real, LAT, Z3>(a, icell, mine, rho);  // the block; results in warp 0
         if (w == 0) {
-            double mine, rho;
-            grad_coefficients<Real, LAT, Z3>(a, icell, lane, mine, rho);
             GradRec& g = a.grad[ci];
             if (lane < 20u) {
                 s_c[lane] = (Real)mine;  // the sampler takes its decisions in the state precision
