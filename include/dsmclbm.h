@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define HYB_ABI_VERSION 7u
+#define HYB_ABI_VERSION 8u
 
 typedef enum {
     HYB_OK = 0,
@@ -395,6 +395,16 @@ hyb_status hyb_host_wait(hyb_ctx* ctx, int32_t pending);
 
 /* Which ping-pong halves hold the current particle and population state (0 or 1). */
 hyb_status hyb_current(const hyb_ctx* ctx, int32_t* particle_half, int32_t* lb_half);
+
+/* Whether dsmc_step and hyb_hybrid_step with nsteps > 1 fuse the collide of a step with the
+ * move of the next (one pass over the particles per step). HYB_FUSE_AUTO (the default) fuses
+ * when the fused pass's grid fills the GPU (at least as many blocks of 32 cells as are
+ * resident at once), where it is faster; below that two passes per step are. The results are
+ * the same bit for bit. HYB_EINVAL for another mode. */
+#define HYB_FUSE_AUTO 0
+#define HYB_FUSE_ALWAYS 1
+#define HYB_FUSE_NEVER 2
+hyb_status hyb_set_fuse(hyb_ctx* ctx, int32_t mode);
 
 /* Synchronises. Returns the sticky device status mapped to a hyb_status (HYB_OK if clear),
  * and the raw bits in *bits if not NULL. */

@@ -11,7 +11,7 @@ import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "libdsmclbm.so")
-ABI_VERSION = 7
+ABI_VERSION = 8
 
 HYB_OK, HYB_EINVAL, HYB_ENOMEM, HYB_ECUDA, HYB_ECAPACITY, HYB_ETIMEOUT, HYB_ESAMPLING, HYB_ESTATE = range(8)
 ST_CAPACITY, ST_BOUNCE_CAP, ST_SCATTER_CAP, ST_SAMPLING_CAP, ST_CELL_OVERFLOW, ST_BAD_INPUT = (
@@ -62,7 +62,7 @@ EXPORTS = ["hyb_derive", "hyb_layout_compute", "hyb_lattice", "hyb_status_string
            "hyb_batch_hybrid_step", "hyb_batch_set_blocks", "hyb_batch_set_block", "hyb_batch_get_block",
            "hyb_batch_tune",
            "hyb_batch_last_error", "hyb_batch_destroy", "hyb_current", "hyb_sync_status", "hyb_read_counters",
-           "hyb_profile", "hyb_profile_harvest", "hyb_profile_read", "hyb_debug_philox",
+           "hyb_set_fuse", "hyb_profile", "hyb_profile_harvest", "hyb_profile_read", "hyb_debug_philox",
            "hyb_last_error", "hyb_destroy"]
 
 _LIB = None
@@ -129,6 +129,7 @@ def lib():
     L.hyb_batch_last_error.restype = ctypes.c_char_p
     L.hyb_batch_destroy.argtypes = [_vp]
     L.hyb_current.argtypes = [_vp, P(_i32), P(_i32)]
+    L.hyb_set_fuse.argtypes = [_vp, _i32]
     L.hyb_sync_status.argtypes = [_vp, P(_u32)]
     L.hyb_read_counters.argtypes = [_vp, _vp]
     L.hyb_profile.argtypes = [_vp, _i32]
@@ -440,6 +441,11 @@ class Hybrid:
         p, f = _i32(), _i32()
         _check(lib().hyb_current(self.ctx, ctypes.byref(p), ctypes.byref(f)))
         return p.value, f.value
+
+    def set_fuse(self, mode):
+        """Multi-step calls: "auto" (fuse the DSMC passes when the fused grid fills the GPU),
+        "always" or "never"; the results are the same."""
+        _check(lib().hyb_set_fuse(self.ctx, {"auto": 0, "always": 1, "never": 2}[mode]))
 
     def profile(self, kernel):
         _check(lib().hyb_profile(self.ctx, KERNELS[kernel] if isinstance(kernel, str) else kernel))

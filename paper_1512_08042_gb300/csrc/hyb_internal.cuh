@@ -496,6 +496,7 @@ cudaError_t launch_dsmc_step(Ctx& c);  // move and collide of one step from half
 cudaError_t launch_dsmc_move(Ctx& c, int p);
 cudaError_t launch_dsmc_collide(Ctx& c, int p);
 cudaError_t launch_dsmc_fused(Ctx& c, int p);
+bool dsmc_fused_fills_gpu(const Ctx& c);
 // A streamwise slab: appends the received particles to the bins of half p^1 after the move.
 cudaError_t launch_dsmc_merge(Ctx& c, int p);
 // Marks (v = 1) or clears (v = 0) the listed cells in the coupled-cell mask.
@@ -604,6 +605,8 @@ struct Ctx {
     int g_curf[2] = {0, 0};        // population parity each graph variant was captured with
     uint32_t* h_pinned = nullptr;  // pinned host words for status reads
     bool split_pending = false;    // a slab's dsmc_move was issued, its collide is due
+    int fuse_mode = 0;             // HYB_FUSE_*: multi-step calls fuse the DSMC passes
+    int fuse_pays = -1;            // HYB_FUSE_AUTO's choice, formed at the first multi-step call
     // hyb_hybrid_step_host: device staging of the lists and the gathered moment sums, and a
     // ring of completion events of the steps in flight
     char* io_dev = nullptr;

@@ -1070,6 +1070,40 @@ void dsmc_args_fill(Ctx& c, int cur_p, void* out) {
 
 // Pool slots of a collide block: room for 1.25 ppc per cell on average (the 32 cells' counts
 // add up to about 32 ppc with a spread of sqrt(32 ppc)), and at least one full bin.
+namespace {
+// Blocks of a collide kernel resident per SM at `smem` bytes of dynamic shared memory (the
+// kernel's limit is raised to it first, as for a launch); 0 if the query fails.
+template <typename Kern>
+int collide_per_sm(Kern kernel, size_t smem) {
+    int per_sm = 0;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kCollideWarps * 32, smem) != cudaSuccess)
+        return 0;
+    return per_sm;
+}
+}  // namespace
+
+// Whether the fused pass's grid fills the GPU: at least as many blocks of 32 cells as fit on
+// it at once. Below that a launch is one partial wave whose time is the latency of its
+// slowest block, which the fused pass lengthens (a collide and a move in one block), and two
+// separate passes are faster.
+bool dsmc_fused_fills_gpu(const Ctx& c) {
+    constexpr int NC = kCollideWarps * (32 / kGroup);
+    const uint32_t pool = collide_pool(c);
+    const uint32_t bin = (uint32_t)c.d.bin;
+    const bool z3 = c.p.ncz >= 2;
+    int per_sm;
+    if (c.p.real_bytes == 4)
+        per_sm = z3 ? collide_per_sm(k_collide<float, false, true, MODE_FUSED>, collide_smem<float, true>(pool, bin))
+                    : collide_per_sm(k_collide<float, false, false, MODE_FUSED>, collide_smem<float, false>(pool, bin));
+    else
+        per_sm = z3 ? collide_per_sm(k_collide<double, false, true, MODE_FUSED>, collide_smem<double, true>(pool, bin))
+                    : collide_per_sm(k_collide<double, false, false, MODE_FUSED>, collide_smem<double, false>(pool, bin));
+    if (per_sm < 1) return true;
+    const int64_t blocks = (c.d.ncells + NC - 1) / NC;
+    return blocks >= (int64_t)per_sm * c.num_sms;
+}
+
 uint32_t collide_pool(const Ctx& c) {
     constexpr int NC = kCollideWarps * (32 / kGroup);
     uint32_t pool = (uint32_t)(((int64_t)NC * c.p.ppc * 11 / 10 + 31) / 32 * 32);

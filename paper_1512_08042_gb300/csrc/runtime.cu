@@ -218,8 +218,24 @@ hyb_status do_lbm_step(Ctx& c) {
 
 // n DSMC steps: the move of the first, then n - 1 fused passes (the collide of one step and
 // the move of the next), then the collide of the last. The particle parity flips once per step.
+// Whether multi-step calls fuse the DSMC passes (HYB_FUSE_AUTO: when the fused grid fills the
+// GPU). Either way the results are the same bit for bit.
+bool fuse_steps(Ctx& c) {
+    if (c.fuse_mode == HYB_FUSE_ALWAYS) return true;
+    if (c.fuse_mode == HYB_FUSE_NEVER) return false;
+    if (c.fuse_pays < 0) c.fuse_pays = dsmc_fused_fills_gpu(c) ? 1 : 0;
+    return c.fuse_pays == 1;
+}
+
+hyb_status one_hybrid_step(Ctx& c, const int32_t* nodes, int32_t nn, const int32_t* cells, int32_t ncl);
+
 hyb_status dsmc_steps(Ctx& c, int n) {
     if (n <= 0) return HYB_OK;
+    if (n > 1 && !fuse_steps(c)) {
+        hyb_status s = HYB_OK;
+        for (int k = 0; k < n && s == HYB_OK; ++k) s = do_dsmc_step(c);
+        return s;
+    }
     int p = c.cur_p;
     hyb_status s = check(c, launch_dsmc_move(c, p), "dsmc move launch");
     for (int k = 1; k < n && s == HYB_OK; ++k) {
@@ -239,6 +255,11 @@ hyb_status dsmc_steps(Ctx& c, int n) {
 hyb_status fused_hybrid_steps(Ctx& c, const int32_t* nodes, int32_t nn, const int32_t* cells,
                               int32_t ncl, int n) {
     if (n <= 0) return HYB_OK;
+    if (n > 1 && !fuse_steps(c)) {
+        hyb_status s = HYB_OK;
+        for (int k = 0; k < n && s == HYB_OK; ++k) s = one_hybrid_step(c, nodes, nn, cells, ncl);
+        return s;
+    }
     int p = c.cur_p;
     hyb_status s = HYB_OK;
     const bool mark = ncl > 0 && n > 1;
@@ -663,6 +684,15 @@ hyb_status hyb_hybrid_step(hyb_ctx* h, const int32_t* dev_nodes, int32_t n_nodes
         if (c.prof_kernel >= 0) P.gpending[gi * 2 + c.cur_f] = true;
         flip_particles(c);
         flip_populations(c);
+    }
+    return HYB_OK;
+}
+
+hyb_status hyb_set_fuse(hyb_ctx* h, int32_t mode) {
+    if (!h || mode < HYB_FUSE_AUTO || mode > HYB_FUSE_NEVER) return HYB_EINVAL;
+    if (h->c.fuse_mode != mode) {
+        h->c.fuse_mode = mode;
+        drop_graphs(h->c);  // graphs hold the passes of the mode they were captured in
     }
     return HYB_OK;
 }

@@ -2,7 +2,8 @@
 pass over the particles, and LB2DSMC moving the particles it creates on at once) gives the
 same results as the same steps taken one at a time, bit for bit, and as the oracle; in 2D
 and 3D, FP32 and FP64, with walls, body force, coupling and the capacity fallback of
-LB2DSMC."""
+LB2DSMC. The contexts here are small, so the fused pass is forced (HYB_FUSE_ALWAYS); the
+automatic choice takes it only where its grid fills the GPU."""
 import numpy as np
 import pytest
 
@@ -19,6 +20,12 @@ from paper_1512_08042_gb300 import binding as B  # noqa: E402
 from paper_1512_08042_gb300 import build as BUILD  # noqa: E402
 
 BUILD.build()
+
+
+def fused(cfg):
+    h = B.Hybrid(cfg)
+    h.set_fuse("always")
+    return h
 
 
 def cfg_small(**kw):
@@ -48,7 +55,7 @@ def assert_same_state(a, b, counters=True):
 @pytest.mark.parametrize("real_bytes,ncz,steps", [(4, 0, 5), (8, 0, 3), (4, 3, 4)])
 def test_fused_dsmc_steps_equal_single_steps_and_the_oracle(real_bytes, ncz, steps):
     cfg = cfg_small(real_bytes=real_bytes, ncz=ncz)
-    a, b = B.Hybrid(cfg), B.Hybrid(cfg)
+    a, b = fused(cfg), B.Hybrid(cfg)
     a.dsmc_step(steps)  # fused: move, steps - 1 fused passes, collide
     for _ in range(steps):
         b.dsmc_step(1)
@@ -76,7 +83,7 @@ def test_fused_hybrid_steps_equal_single_steps(real_bytes, ncz, graph):
     cfg = cfg_small(real_bytes=real_bytes, ncz=ncz, lb_ratio=2, ncy=10)
     nodes, cells = W.coupling_sites(cfg, strip_cells=2)
     dn, dc = torch.from_numpy(nodes).cuda(), torch.from_numpy(cells).cuda()
-    a, b = B.Hybrid(cfg), B.Hybrid(cfg)
+    a, b = fused(cfg), B.Hybrid(cfg)
     for _ in range(2):  # the second call replays the graph captured by the first
         a.hybrid_step(dn, dc, nsteps=4, use_graph=graph)
         for _ in range(4):
@@ -101,7 +108,7 @@ def test_fused_hybrid_keeps_cells_whose_new_count_exceeds_the_bin():
     _, cells = W.coupling_sites(cfg, strip_cells=2)
     dc = torch.from_numpy(cells).cuda()
     e, w, r = O.lattice(39)
-    a, b = B.Hybrid(cfg), B.Hybrid(cfg)
+    a, b = fused(cfg), B.Hybrid(cfg)
     f = torch.from_numpy((w[:, None] * 4.0 * np.ones((1, a.d["nnodes"]))).astype(np.float32))
     for h in (a, b):
         h.f().copy_(f.view(h.f().shape))
@@ -120,8 +127,33 @@ def test_fused_hybrid_at_the_819k_particle_channel_equals_single_steps():
     cfg = W.WORKLOADS["poiseuille_64x256_ppc50_fp32"]
     nodes, cells = W.coupling_sites(cfg)
     dn, dc = torch.from_numpy(nodes).cuda(), torch.from_numpy(cells).cuda()
-    a, b = B.Hybrid(cfg), B.Hybrid(cfg)
+    a, b = fused(cfg), B.Hybrid(cfg)
     a.hybrid_step(dn, dc, nsteps=3, use_graph=True)
     for _ in range(3):
         b.hybrid_step(dn, dc, nsteps=1, use_graph=True)
     assert_same_state(a, b)
+
+
+def test_fuse_modes_give_the_same_results_and_auto_skips_a_grid_below_the_gpu():
+    # HYB_FUSE_AUTO fuses only where the fused grid fills the GPU; a 13 x 10-cell channel (5
+    # blocks of 32 cells) takes a move and a collide per step. Every mode gives the same state.
+    cfg = cfg_small(lb_ratio=2, ncy=10)
+    nodes, cells = W.coupling_sites(cfg, strip_cells=2)
+    dn, dc = torch.from_numpy(nodes).cuda(), torch.from_numpy(cells).cuda()
+    hs = {}
+    for mode in ("auto", "always", "never"):
+        h = B.Hybrid(cfg)
+        h.set_fuse(mode)
+        h.profile("fused")
+        h.profile_harvest()
+        h.hybrid_step(dn, dc, nsteps=4, use_graph=False)
+        h.profile_harvest()
+        ms, n = h.profile_read()
+        h.profile(-1)
+        assert (n > 0) == (mode == "always"), (mode, n)
+        h.dsmc_step(3)
+        hs[mode] = h
+    assert_same_state(hs["always"], hs["never"])
+    assert_same_state(hs["auto"], hs["never"])
+    with pytest.raises(B.HybError):
+        B._check(B.lib().hyb_set_fuse(hs["auto"].ctx, 3))
