@@ -5,8 +5,8 @@
  *
  * The library advances a force-driven plane channel (Sec. 3.1) with two solvers and maps
  * between them (Sec. 2):
- *   dsmc_step        DSMC of a hard-sphere gas: move with diffuse isothermal walls, stable
- *                    counting sort by cell, no-time-counter collisions (Sec. 5,
+ *   dsmc_step        DSMC of a hard-sphere gas: move with diffuse isothermal walls, binning
+ *                    by cell in a fixed order, no-time-counter collisions (Sec. 5,
  *                    Eq. collisionnumber), per-cell Hermite-moment sampling.
  *   lbm_step         regularised BGK lattice Boltzmann on D3Q39 (Hermite order 3) or D3Q19
  *                    (order 2) with kinetic walls and a body force (Sec. 2 "ingredients",
@@ -117,7 +117,7 @@ typedef struct {
                                streamwise slab of a channel of ncy_global DSMC rows (periodic):
                                the rows [y0, y0 + ncy) (ncy >= 4), with the channel's ncx, ncz,
                                ppc, Kn, seed and lattice. Cell ids in the random streams and the
-                               stable-order keys, and particle y positions, are the channel's, so
+                               order keys, and particle y positions, are the channel's, so
                                slabs stepped with the exchange below give the whole channel's
                                results bit for bit. The LB lattice of a slab has yh ghost rows
                                below and above its ncy * lb_ratio rows (hyb_derived.yh), filled
@@ -160,7 +160,7 @@ typedef struct {
  * [2] are ping-pong pairs; hyb_current says which half holds the current state. Real is
  * float or double per real_bytes. Particles are binned by cell: cell c owns slots
  * [c * bin, (c + 1) * bin) of every particle array and count[half][c] of them are in use,
- * in the order of the step's stable sort (after dsmc_step) or of their generation (after
+ * in the order of their order keys (after dsmc_step; see part) or of their generation (after
  * dsmc_init and map_lbm_to_dsmc); the other half's counts are zero between calls.
  *   part          Real[ncells*bin][8]  particle records: x, y (positions in cell units, x
  *                                   across, y streamwise), vx, vy, vz (velocities in c_th
@@ -224,11 +224,12 @@ hyb_status dsmc_init(const hyb_params* p, void* arena, uint64_t arena_bytes, voi
                      hyb_ctx** out);
 
 /* `nsteps` DSMC steps (Sec. 5; the NTC order move -> index -> collide -> sample): each
- * particle is moved and binned into its new cell of the other half, then every cell puts
- * its particles in stable order (by origin cell and rank), collides them and adds their
- * moment sums. With nsteps >= 2 the collide of each step and the move of the next run as
- * one pass over the particles (the same results). Draws are keyed by (seed; cell, step,
- * purpose, index), so results do not depend on the launch shape. */
+ * particle is moved and binned into its new cell of the other half with its order key (see
+ * part: the neighbour offset of its displacement, then its rank in its old cell), then every
+ * cell puts its particles in the order of their keys, collides them and adds their moment
+ * sums. With nsteps >= 2 the collide of each step and the move of the next may run as one
+ * pass over the particles (hyb_set_fuse; the same results). Draws are keyed by (seed; cell,
+ * step, purpose, index), so results do not depend on the launch shape. */
 hyb_status dsmc_step(hyb_ctx* ctx, int32_t nsteps);
 
 /* The passes of one DSMC step, for a streamwise slab (hyb_params.ncy_global > 0; the multi-GPU
@@ -236,14 +237,14 @@ hyb_status dsmc_step(hyb_ctx* ctx, int32_t nsteps);
  *   dsmc_move     moves and bins the particles (as dsmc_step); a slab's particles whose new
  *                 cell lies outside its rows go to its send buffers (xsend[0]: lower rows,
  *                 xsend[1]: higher rows, across the periodic end included) with their
- *                 stable-order keys and channel cells;
+ *                 order keys and channel cells;
  *                 -- the caller then copies each neighbour's send buffer into this slab's
  *                    receive buffer (xrecv[0] <- the slab below's xsend[1], xrecv[1] <- the
  *                    slab above's xsend[0]; hyb_layout.xbytes each, on this context's stream or
  *                    ordered before dsmc_merge), e.g. by NCCL send/recv between ranks --
  *   dsmc_merge    appends the received particles to their cells (a no-op for a context that
  *                 holds the whole channel) and clears the slab's send counts;
- *   dsmc_collide  sorts, collides and samples every cell (as dsmc_step) and flips the
+ *   dsmc_collide  orders, collides and samples every cell (as dsmc_step) and flips the
  *                 particle half.
  * dsmc_move + dsmc_merge + dsmc_collide of every slab give the whole channel's dsmc_step(1) bit
  * for bit. A call out of this order returns HYB_ESTATE; a received particle whose cell is not

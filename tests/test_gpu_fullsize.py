@@ -3,7 +3,7 @@ particles; 1024 x 8192 D3Q39 nodes), with Kn 0.05 and with Kn 0.005-0.5 along th
 in the launch configuration bench.py times.
 
 The oracle cannot step the whole channel in a test's time, so it steps a window: the first
-rows of the same channel. Those rows keep the channel's cell ids, origin slots and Philox
+rows of the same channel. Those rows keep the channel's cell ids, order keys and Philox
 keys, so their particles are the channel's own from the first draw on. The window is
 periodic over its own rows, so only rows within a few cells of its ends see different
 neighbours; the rows in between are compared. With the Kn profile the window takes the

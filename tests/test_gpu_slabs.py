@@ -4,7 +4,8 @@ exchanged through its send and receive buffers, and the LB ghost rows are filled
 neighbours' outgoing populations before every LB step. Hybrid steps of the slabs must give
 the whole channel's results bit for bit: particles, per-cell collision state, moment sums,
 populations, counters. The random streams are keyed by the channel's cell ids and the
-stable order by the channel's origin slots, which makes this exact."""
+order keys by the channel's cells (displacements in channel coordinates), which makes this
+exact."""
 import numpy as np
 import pytest
 
