@@ -647,6 +647,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(W.WORKLOADS))
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--collide-block", default="tune", choices=["tune", "4", "8"],
+                    help="the collide's block shape in warps, or timed by the library's tuner "
+                         "before the warm-up (hyb_tune_collide)")
     ap.add_argument("--profile-kernel", default=None)
     ap.add_argument("--cpu-budget", type=float, default=16.0)
     ap.add_argument("--replicas", action="store_true",
@@ -753,6 +756,14 @@ def main():
     def run(n, graph=use_graph):
         # n hybrid steps in one call: the DSMC passes fused across steps
         h.hybrid_step(nodes, cells, nsteps=n, use_graph=graph, order_inputs=False)
+
+    # the collide's block shape (the same results either way): the tuner times both on this
+    # channel, outside the timed region
+    if args.collide_block == "tune":
+        collide_warps = h.tune_collide(nodes, cells)
+    else:
+        h.set_collide_block(int(args.collide_block))
+        collide_warps = int(args.collide_block)
 
     if args.profile_steps:
         run(args.profile_steps, graph=False)
@@ -891,6 +902,7 @@ def main():
         "config": {"workload": args.workload, "particles": n_particles, "lb_nodes": d["nnodes"],
                    "lattice": "D3Q%d" % d["q"], "coupling_nodes": len(nodes_np),
                    "coupling_cells": len(cells_np), "graph": use_graph,
+                   "collide_block_warps": collide_warps,
                    "kn": [cfg["kn"], cfg.get("kn_end", cfg["kn"])] if cfg.get("kn_profile") else cfg["kn"],
                    "l2": "inputs larger than L2, and flushed before every timed step (512 MB write)",
                    "parallelism": "replicas" if world > 1 else "single"},

@@ -11,7 +11,7 @@ import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "libdsmclbm.so")
-ABI_VERSION = 8
+ABI_VERSION = 9
 
 HYB_OK, HYB_EINVAL, HYB_ENOMEM, HYB_ECUDA, HYB_ECAPACITY, HYB_ETIMEOUT, HYB_ESAMPLING, HYB_ESTATE = range(8)
 ST_CAPACITY, ST_BOUNCE_CAP, ST_SCATTER_CAP, ST_SAMPLING_CAP, ST_CELL_OVERFLOW, ST_BAD_INPUT = (
@@ -62,7 +62,8 @@ EXPORTS = ["hyb_derive", "hyb_layout_compute", "hyb_lattice", "hyb_status_string
            "hyb_batch_hybrid_step", "hyb_batch_set_blocks", "hyb_batch_set_block", "hyb_batch_get_block",
            "hyb_batch_tune",
            "hyb_batch_last_error", "hyb_batch_destroy", "hyb_current", "hyb_sync_status", "hyb_read_counters",
-           "hyb_set_fuse", "hyb_profile", "hyb_profile_harvest", "hyb_profile_read", "hyb_debug_philox",
+           "hyb_set_fuse", "hyb_set_collide_block", "hyb_get_collide_block", "hyb_tune_collide",
+           "hyb_profile", "hyb_profile_harvest", "hyb_profile_read", "hyb_debug_philox",
            "hyb_last_error", "hyb_destroy"]
 
 _LIB = None
@@ -130,6 +131,10 @@ def lib():
     L.hyb_batch_destroy.argtypes = [_vp]
     L.hyb_current.argtypes = [_vp, P(_i32), P(_i32)]
     L.hyb_set_fuse.argtypes = [_vp, _i32]
+    L.hyb_set_collide_block.argtypes = [_vp, _i32]
+    L.hyb_get_collide_block.argtypes = [_vp]
+    L.hyb_get_collide_block.restype = _i32
+    L.hyb_tune_collide.argtypes = [_vp, _vp, _i32, _vp, _i32, P(_i32)]
     L.hyb_sync_status.argtypes = [_vp, P(_u32)]
     L.hyb_read_counters.argtypes = [_vp, _vp]
     L.hyb_profile.argtypes = [_vp, _i32]
@@ -446,6 +451,26 @@ class Hybrid:
         """Multi-step calls: "auto" (fuse the DSMC passes when the fused grid fills the GPU),
         "always" or "never"; the results are the same."""
         _check(lib().hyb_set_fuse(self.ctx, {"auto": 0, "always": 1, "never": 2}[mode]))
+
+    def set_collide_block(self, warps):
+        """The collide's block shape: 8 warps (32 cells) or 4 (16 cells); the same results."""
+        _check(lib().hyb_set_collide_block(self.ctx, int(warps)))
+
+    def collide_block(self):
+        return int(lib().hyb_get_collide_block(self.ctx))
+
+    def tune_collide(self, nodes=None, cells=None):
+        """Picks the faster collide block shape by timing hybrid steps with these coupling
+        lists (device int32 tensors or None); advances the context by 12 hybrid steps."""
+        nn = 0 if nodes is None else nodes.numel()
+        nc = 0 if cells is None else cells.numel()
+        self._inputs(nodes, cells)
+        w = _i32()
+        rc = lib().hyb_tune_collide(self.ctx, nodes.data_ptr() if nn else None, nn,
+                                    cells.data_ptr() if nc else None, nc, ctypes.byref(w))
+        if rc != HYB_OK:
+            raise HybError(rc, lib().hyb_last_error(self.ctx).decode())
+        return w.value
 
     def profile(self, kernel):
         _check(lib().hyb_profile(self.ctx, KERNELS[kernel] if isinstance(kernel, str) else kernel))

@@ -554,7 +554,7 @@ size_t lbm_args_bytes(int real_bytes);
 void lbm_args_fill(Ctx& c, int cur_f, void* out);
 size_t map_args_bytes(int real_bytes);
 void map_args_fill(Ctx& c, int cur_p, int cur_f, const int32_t* list, int32_t n, void* out);
-uint32_t collide_pool(const Ctx& c);
+uint32_t collide_pool(const Ctx& c, int warps = 8);
 cudaError_t launch_batch_move(BatchDev& b, int cur_p);
 cudaError_t launch_batch_collide(BatchDev& b, int cur_p);
 cudaError_t launch_batch_lbm(BatchDev& b, int cur_f);
@@ -607,6 +607,7 @@ struct Ctx {
     bool split_pending = false;    // a slab's dsmc_move was issued, its collide is due
     int fuse_mode = 0;             // HYB_FUSE_*: multi-step calls fuse the DSMC passes
     int fuse_pays = -1;            // HYB_FUSE_AUTO's choice, formed at the first multi-step call
+    int collide_warps = 8;         // collide block shape: 8 warps (32 cells) or 4 (16 cells)
     // hyb_hybrid_step_host: device staging of the lists and the gathered moment sums, and a
     // ring of completion events of the steps in flight
     char* io_dev = nullptr;

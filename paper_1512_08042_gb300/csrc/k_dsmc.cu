@@ -231,11 +231,13 @@ __global__ void __launch_bounds__(256, 4) k_move(Launch<DsmcArgs<Real>> L) {
 // executed by the full warp.
 constexpr int kGroup = 8;
 
-template <typename Real>
+// A collide block has W warps for 4 W cells (W = 8: 32 cells, the default; W = 4: 16 cells,
+// twice the blocks per SM); its launch bounds keep 80 registers (FP32) or 128 (FP64).
+constexpr int kCollideWarps = 8;
+template <typename Real, int W>
 struct CollideCfg {
-    static constexpr int MINB = sizeof(Real) == 4 ? 3 : 2;  // resident blocks per SM
+    static constexpr int MINB = (sizeof(Real) == 4 ? 3 : 2) * 8 / W;  // resident blocks per SM
 };
-constexpr int kCollideWarps = 8;  // 32 cells per block
 constexpr int kChainSteps = 24;   // candidates per cell drawn per pass of the NTC phase
 enum CollideMode : int { MODE_COLLIDE = 0, MODE_FUSED = 1 };
 
@@ -275,21 +277,27 @@ __device__ __forceinline__ void add_moments(Real (&mo)[kMoments], Real ux, Real 
 // p^1 (d*) are put in stable order, collided and sampled; MODE_COLLIDE writes them back in
 // place, MODE_FUSED moves them on (step s + 1) into the bins of half p (s*), except cells
 // marked in a.coupled, which are written back in place for LB2DSMC.
-template <typename Real, bool Z3, int MODE>
+template <typename Real, bool Z3, int MODE, int W>
 __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t pool, int blk) {
     constexpr int G = kGroup;
     constexpr int CPW = 32 / G;           // cells per warp in phases A and C
-    constexpr int WARPS = kCollideWarps;
+    constexpr int WARPS = W;
     constexpr int NC = WARPS * CPW;       // cells per block (one chain lane each in phase B)
     constexpr int SMALL = 64;             // keys of the first SMALL slots loaded with the count
     constexpr int R = SMALL / G;
     constexpr int KC = kChainSteps;       // candidates per cell drawn per pass of phase B
     constexpr int NR = pool_reals<Z3>();
     constexpr int SJ = 2;                 // arrivals per lane whose loads are in flight together
-    static_assert(NC == 32, "phase B runs one lane per cell of the block in one warp");
+    static_assert(NC <= 32, "phase B runs one lane per cell of the block in one warp");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ uint32_t s_n[NC], s_off[NC], s_nsel[NC];
-    __shared__ Real s_cm[NC];
+    // per cell of the block, by phase B's lanes (lanes past NC are empty cells)
+    __shared__ uint32_t s_n[32], s_off[32], s_nsel[32];
+    __shared__ Real s_cm[32];
+    if (NC < 32 && threadIdx.x >= NC && threadIdx.x < 32) {
+        s_n[threadIdx.x] = 0u;
+        s_nsel[threadIdx.x] = 0u;
+        s_cm[threadIdx.x] = (Real)0;
+    }
     __shared__ uint32_t s_fits;
     __shared__ unsigned long long s_cnt[WARPS][2];
     __shared__ uint32_t s_live[WARPS], s_flags[WARPS];
@@ -639,7 +647,7 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
         }
         if (w == 0) {
             const int cl = blk * NC + (int)lane;
-            if (cl < a.ncells && (fits || (int)lane == round)) a.crmax[cl] = cm;
+            if ((int)lane < NC && cl < a.ncells && (fits || (int)lane == round)) a.crmax[cl] = cm;
             ncoll_tot += ncoll;
         }
         // C. moment sums of the collided particles; the cell is written back in place in
@@ -758,15 +766,15 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
     }
 }
 
-template <typename Real, bool BATCH, bool Z3 = false, int MODE = MODE_COLLIDE>
-__global__ void __launch_bounds__(kCollideWarps * 32, CollideCfg<Real>::MINB)
+template <typename Real, bool BATCH, bool Z3 = false, int MODE = MODE_COLLIDE, int W = kCollideWarps>
+__global__ void __launch_bounds__(W * 32, (CollideCfg<Real, W>::MINB))
     k_collide(Launch<DsmcArgs<Real>> L, uint32_t pool) {
     pdl_begin();
     if constexpr (BATCH) {
         const int r = replica_of(L.pre, L.nrep, (int64_t)blockIdx.x);
-        collide_block<Real, Z3, MODE>(L.tab[r], pool, (int)(blockIdx.x - L.pre[r]));
+        collide_block<Real, Z3, MODE, W>(L.tab[r], pool, (int)(blockIdx.x - L.pre[r]));
     } else {
-        collide_block<Real, Z3, MODE>(L.one, pool, (int)blockIdx.x);
+        collide_block<Real, Z3, MODE, W>(L.one, pool, (int)blockIdx.x);
     }
 }
 
@@ -911,9 +919,9 @@ int grid_for(const Ctx& c, int64_t work, int threads, int per_sm) {
 
 // Shared memory of a collide block: the pool (pool_reals Real and one u32 per slot) and one
 // pass of NTC candidates (u32 and 4 Real each).
-template <typename Real, bool Z3>
+template <typename Real, bool Z3, int W = kCollideWarps>
 size_t collide_smem(uint32_t pool, uint32_t bin) {
-    constexpr int NC = kCollideWarps * (32 / kGroup);
+    constexpr int NC = W * (32 / kGroup);
     const size_t cand = (size_t)NC * kChainSteps * (4 + 4 * sizeof(Real));
     const size_t bits = ((size_t)NC * (bitmap_words<Z3>(bin) * 5 + (kFarList + 1) * 4) + 15) / 16 * 16;
     return (size_t)pool * (pool_reals<Z3>() * sizeof(Real) + 4) + (cand > bits ? cand : bits);
@@ -952,29 +960,34 @@ cudaError_t move_impl(Ctx& c, int p) {
     return e;
 }
 
-template <typename Real, bool Z3, int MODE>
-cudaError_t collide_impl(Ctx& c, int p) {
+template <typename Real, bool Z3, int MODE, int W>
+cudaError_t collide_impl_w(Ctx& c, int p) {
     const int save = c.cur_p;
     c.cur_p = p;
     Launch<DsmcArgs<Real>> L{};
     L.one = make_args<Real>(c);
     c.cur_p = save;
-    constexpr int NC = kCollideWarps * (32 / kGroup);
-    const uint32_t pool = collide_pool(c);
-    const size_t smem = collide_smem<Real, Z3>(pool, (uint32_t)c.d.bin);
+    constexpr int NC = W * (32 / kGroup);
+    const uint32_t pool = collide_pool(c, W);
+    const size_t smem = collide_smem<Real, Z3, W>(pool, (uint32_t)c.d.bin);
     // (dynamic and static shared memory together may exceed the default 48 KB)
-    cudaError_t e = cudaFuncSetAttribute(k_collide<Real, false, Z3, MODE>,
+    cudaError_t e = cudaFuncSetAttribute(k_collide<Real, false, Z3, MODE, W>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)((c.d.ncells + NC - 1) / NC);
     L.total = grid;
     constexpr int kid = MODE == MODE_FUSED ? K_FUSED : K_COLLIDE;
     prof_begin(c, kid);
-    e = launch_pdl(k_collide<Real, false, Z3, MODE>, dim3(grid), dim3(kCollideWarps * 32), smem,
-                   c.stream, L, pool);
+    e = launch_pdl(k_collide<Real, false, Z3, MODE, W>, dim3(grid), dim3(W * 32), smem, c.stream, L, pool);
     prof_end(c, kid);
     if (e != cudaSuccess) return e;
     return launch_pdl(k_step_end<Real, false>, dim3(1), dim3(32), 0, c.stream, L);
+}
+
+// The context's collide block shape: 8 warps (32 cells) or 4 (16 cells).
+template <typename Real, bool Z3, int MODE>
+cudaError_t collide_impl(Ctx& c, int p) {
+    return c.collide_warps == 4 ? collide_impl_w<Real, Z3, MODE, 4>(c, p) : collide_impl_w<Real, Z3, MODE, 8>(c, p);
 }
 
 __global__ void k_debug_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out, int64_t n) {
@@ -1068,16 +1081,14 @@ void dsmc_args_fill(Ctx& c, int cur_p, void* out) {
     c.cur_p = save;
 }
 
-// Pool slots of a collide block: room for 1.25 ppc per cell on average (the 32 cells' counts
-// add up to about 32 ppc with a spread of sqrt(32 ppc)), and at least one full bin.
 namespace {
 // Blocks of a collide kernel resident per SM at `smem` bytes of dynamic shared memory (the
 // kernel's limit is raised to it first, as for a launch); 0 if the query fails.
 template <typename Kern>
-int collide_per_sm(Kern kernel, size_t smem) {
+int collide_per_sm(Kern kernel, int threads, size_t smem) {
     int per_sm = 0;
     if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kCollideWarps * 32, smem) != cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess)
         return 0;
     return per_sm;
 }
@@ -1087,25 +1098,39 @@ int collide_per_sm(Kern kernel, size_t smem) {
 // it at once. Below that a launch is one partial wave whose time is the latency of its
 // slowest block, which the fused pass lengthens (a collide and a move in one block), and two
 // separate passes are faster.
-bool dsmc_fused_fills_gpu(const Ctx& c) {
-    constexpr int NC = kCollideWarps * (32 / kGroup);
-    const uint32_t pool = collide_pool(c);
+namespace {
+template <int W>
+bool fused_fills_gpu_w(const Ctx& c) {
+    constexpr int NC = W * (32 / kGroup);
+    const uint32_t pool = collide_pool(c, W);
     const uint32_t bin = (uint32_t)c.d.bin;
     const bool z3 = c.p.ncz >= 2;
     int per_sm;
     if (c.p.real_bytes == 4)
-        per_sm = z3 ? collide_per_sm(k_collide<float, false, true, MODE_FUSED>, collide_smem<float, true>(pool, bin))
-                    : collide_per_sm(k_collide<float, false, false, MODE_FUSED>, collide_smem<float, false>(pool, bin));
+        per_sm = z3 ? collide_per_sm(k_collide<float, false, true, MODE_FUSED, W>, W * 32,
+                                     collide_smem<float, true, W>(pool, bin))
+                    : collide_per_sm(k_collide<float, false, false, MODE_FUSED, W>, W * 32,
+                                     collide_smem<float, false, W>(pool, bin));
     else
-        per_sm = z3 ? collide_per_sm(k_collide<double, false, true, MODE_FUSED>, collide_smem<double, true>(pool, bin))
-                    : collide_per_sm(k_collide<double, false, false, MODE_FUSED>, collide_smem<double, false>(pool, bin));
+        per_sm = z3 ? collide_per_sm(k_collide<double, false, true, MODE_FUSED, W>, W * 32,
+                                     collide_smem<double, true, W>(pool, bin))
+                    : collide_per_sm(k_collide<double, false, false, MODE_FUSED, W>, W * 32,
+                                     collide_smem<double, false, W>(pool, bin));
     if (per_sm < 1) return true;
     const int64_t blocks = (c.d.ncells + NC - 1) / NC;
     return blocks >= (int64_t)per_sm * c.num_sms;
 }
+}  // namespace
 
-uint32_t collide_pool(const Ctx& c) {
-    constexpr int NC = kCollideWarps * (32 / kGroup);
+bool dsmc_fused_fills_gpu(const Ctx& c) {
+    return c.collide_warps == 4 ? fused_fills_gpu_w<4>(c) : fused_fills_gpu_w<8>(c);
+}
+
+// Pool slots of a collide block of `warps` warps (4 cells each): room for 1.1 ppc per cell on
+// average (the cells' counts add up to about NC ppc with a spread of sqrt(NC ppc); a block
+// whose cells do not fit takes the pool one cell at a time), and at least one full bin.
+uint32_t collide_pool(const Ctx& c, int warps) {
+    const int NC = warps * (32 / kGroup);
     uint32_t pool = (uint32_t)(((int64_t)NC * c.p.ppc * 11 / 10 + 31) / 32 * 32);
     if (pool < (uint32_t)c.d.bin) pool = (uint32_t)c.d.bin;
     return pool;

@@ -688,6 +688,55 @@ hyb_status hyb_hybrid_step(hyb_ctx* h, const int32_t* dev_nodes, int32_t n_nodes
     return HYB_OK;
 }
 
+hyb_status hyb_set_collide_block(hyb_ctx* h, int32_t warps) {
+    if (!h || (warps != 4 && warps != 8)) return HYB_EINVAL;
+    if (h->c.collide_warps != warps) {
+        h->c.collide_warps = warps;
+        h->c.fuse_pays = -1;  // formed again for this shape
+        drop_graphs(h->c);
+    }
+    return HYB_OK;
+}
+
+int32_t hyb_get_collide_block(const hyb_ctx* h) { return h ? h->c.collide_warps : -1; }
+
+hyb_status hyb_tune_collide(hyb_ctx* h, const int32_t* dev_nodes, int32_t n_nodes, const int32_t* dev_cells,
+                            int32_t n_cells, int32_t* warps) {
+    if (!h) return HYB_EINVAL;
+    Ctx& c = h->c;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return HYB_ECUDA;
+    const int shapes[2] = {8, 4};
+    float best = 1e30f;
+    int best_w = c.collide_warps;
+    hyb_status s = HYB_OK;
+    for (int i = 0; i < 2 && s == HYB_OK; ++i) {
+        s = hyb_set_collide_block(h, shapes[i]);
+        // a captured two-step graph, then the best of two replays
+        if (s == HYB_OK) s = hyb_hybrid_step(h, dev_nodes, n_nodes, dev_cells, n_cells, 2, 1);
+        float t_best = 1e30f;
+        for (int k = 0; k < 2 && s == HYB_OK; ++k) {
+            cudaEventRecord(e0, c.stream);
+            s = hyb_hybrid_step(h, dev_nodes, n_nodes, dev_cells, n_cells, 2, 1);
+            cudaEventRecord(e1, c.stream);
+            if (s == HYB_OK && cudaEventSynchronize(e1) != cudaSuccess) s = HYB_ECUDA;
+            float t = 0.f;
+            if (s == HYB_OK) cudaEventElapsedTime(&t, e0, e1);
+            if (t < t_best) t_best = t;
+        }
+        if (s == HYB_OK && t_best < best) {
+            best = t_best;
+            best_w = shapes[i];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != HYB_OK) return s;
+    s = hyb_set_collide_block(h, best_w);
+    if (warps) *warps = best_w;
+    return s;
+}
+
 hyb_status hyb_set_fuse(hyb_ctx* h, int32_t mode) {
     if (!h || mode < HYB_FUSE_AUTO || mode > HYB_FUSE_NEVER) return HYB_EINVAL;
     if (h->c.fuse_mode != mode) {

@@ -157,3 +157,35 @@ def test_fuse_modes_give_the_same_results_and_auto_skips_a_grid_below_the_gpu():
     assert_same_state(hs["auto"], hs["never"])
     with pytest.raises(B.HybError):
         B._check(B.lib().hyb_set_fuse(hs["auto"].ctx, 3))
+
+
+@pytest.mark.parametrize("real_bytes,ncz", [(4, 0), (8, 0), (4, 2)])
+def test_collide_block_shapes_give_the_same_results(real_bytes, ncz):
+    # 16-cell blocks (4 warps) and 32-cell blocks (8 warps), fused and plain passes, with
+    # coupling: the per-cell work is the same, only its grouping into blocks differs
+    cfg = cfg_small(ncx=24, ncy=20, real_bytes=real_bytes, ncz=ncz, lb_ratio=2)
+    nodes, cells = W.coupling_sites(cfg, strip_cells=2)
+    dn, dc = torch.from_numpy(nodes).cuda(), torch.from_numpy(cells).cuda()
+    a, b = fused(cfg), fused(cfg)
+    a.set_collide_block(8)
+    b.set_collide_block(4)
+    assert (a.collide_block(), b.collide_block()) == (8, 4)
+    for h in (a, b):
+        h.hybrid_step(dn, dc, nsteps=3, use_graph=True)
+        h.dsmc_step(2)
+        h.hybrid_step(dn, dc, nsteps=1, use_graph=False)
+    assert_same_state(a, b)
+    with pytest.raises(B.HybError):
+        a.set_collide_block(2)
+
+
+def test_collide_tuner_keeps_results():
+    cfg = cfg_small(ncx=24, ncy=20, lb_ratio=2)
+    nodes, cells = W.coupling_sites(cfg, strip_cells=2)
+    dn, dc = torch.from_numpy(nodes).cuda(), torch.from_numpy(cells).cuda()
+    a, b = B.Hybrid(cfg), B.Hybrid(cfg)
+    w = a.tune_collide(dn, dc)
+    assert w in (4, 8) and a.collide_block() == w
+    a.hybrid_step(dn, dc, nsteps=2, use_graph=True)
+    b.hybrid_step(dn, dc, nsteps=12 + 2, use_graph=True)  # the tuner's 12 steps, then 2
+    assert_same_state(a, b)
