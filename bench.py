@@ -757,13 +757,18 @@ def main():
         # n hybrid steps in one call: the DSMC passes fused across steps
         h.hybrid_step(nodes, cells, nsteps=n, use_graph=graph, order_inputs=False)
 
-    # the collide's block shape (the same results either way): the tuner times both on this
-    # channel, outside the timed region
+    # the collide's block shape (the same results either way): the tuner times both on a
+    # second context of this channel from the same initial state (it advances the context it
+    # times), outside the timed region
     if args.collide_block == "tune":
-        collide_warps = h.tune_collide(nodes, cells)
+        tuner = B.Hybrid(cfg, device=dev)
+        collide_warps = tuner.tune_collide(nodes, cells)
+        tuner.close()
+        del tuner
+        torch.cuda.empty_cache()
     else:
-        h.set_collide_block(int(args.collide_block))
         collide_warps = int(args.collide_block)
+    h.set_collide_block(collide_warps)
 
     if args.profile_steps:
         run(args.profile_steps, graph=False)
