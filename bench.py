@@ -466,31 +466,53 @@ def run_ensemble(args):
     """The batched ensemble against plain contexts: n independent channels advanced one hybrid
     step at a time, batched (one launch per kernel for all replicas, tuned block shapes) and
     plain (one context and graph per replica on one stream). Both start from the same states,
-    take the same steps and end bit-identical (checked)."""
+    take the same steps and end bit-identical (checked). Under torchrun every rank runs the
+    same n channels with its own seeds (weak scaling) and the ranks sum the replicas' moment
+    sums every step (one all-reduce: the ensemble average over the GPUs); the plain contexts
+    are compared on one GPU only."""
     import torch
     import __graft_entry__ as G
-    G.build()
     from paper_1512_08042_gb300 import binding as B
 
-    cfgs = W.ensemble_configs(args.ensemble)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+        if rank == 0:
+            G.build()
+        dist.barrier()
+        if rank != 0:
+            G.build()
+    else:
+        G.build()
+    cfgs = W.ensemble_configs(args.ensemble, rank=rank)
     nodes, cells = zip(*[W.coupling_sites(c) for c in cfgs])
     nodes, cells = list(nodes), list(cells)
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", local_rank)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    tuner = B.Batch(cfgs)
+    tuner = B.Batch(cfgs, device=dev)
     tuner.tune(nodes, cells)
     shapes = tuner.blocks()
     tuner.close()
-    batch = B.Batch(cfgs)
+    batch = B.Batch(cfgs, device=dev)
     for k, v in shapes.items():
         batch.set_block(k, v)
     stream = batch.stream
-    plain = [B.Hybrid(c, stream=stream) for c in cfgs]
+    plain = [B.Hybrid(c, stream=stream, device=dev) for c in cfgs] if world == 1 else []
     pn = [torch.from_numpy(x).to(dev) for x in nodes]
     pc = [torch.from_numpy(x).to(dev) for x in cells]
+    acc_sum = batch.moment_sums() if world > 1 else None
 
     def step_batch():
         batch.hybrid_step(nodes, cells, nsteps=1, use_graph=True)
+        if world > 1:
+            with torch.cuda.stream(stream):
+                batch.moment_sums(acc_sum)
+                dist.all_reduce(acc_sum)
 
     def step_plain():
         for h, a, b in zip(plain, pn, pc):
@@ -511,7 +533,28 @@ def run_ensemble(args):
         torch.cuda.synchronize(dev)
         return sum(a.elapsed_time(b) for a, b in ev) / args.steps
 
+    if dist:
+        dist.barrier()
     ms_b = timed(step_batch)
+    if dist:
+        ms_b = max_over_ranks(dist, ms_b, dev)
+        dist.barrier()
+        line = {
+            "metric": "ensemble hybrid steps/s (every replica of every rank advanced one hybrid step)",
+            "value": world * 1e3 / ms_b, "unit": "ensemble steps/s (a rank's ensemble, times ranks)",
+            "higher_is_better": True, "ms_per_step": ms_b, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "scaling": "weak", "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "ensemble of %d channels per rank (H 32-256 cells, 20-100 ppc, "
+                                   "Kn 0.01-0.5), each rank its own seeds" % len(cfgs),
+                       "replicas_per_rank": len(cfgs), "block_shapes": shapes,
+                       "collective": "all-reduce (sum) of the replicas' FP64 moment sums every step",
+                       "l2": "flushed before every timed step (512 MB write)"},
+        }
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        batch.close()
+        dist.destroy_process_group()
+        return
     ms_p = timed(step_plain)
     identical = True
     for g, h in zip(batch.replicas, plain):

@@ -669,6 +669,20 @@ class Batch:
         self._lists = (key, prepared)
         return prepared
 
+    def moment_sums(self, out=None):
+        """The replicas' cumulative FP64 moment sums, one after another in replica order, as one
+        flat device tensor (copied into `out` if given): the buffer a multi-GPU ensemble sums
+        over its ranks."""
+        accs = [r.acc().reshape(-1) for r in self.replicas]
+        n = sum(a.numel() for a in accs)
+        if out is None:
+            out = accs[0].new_empty(n)
+        o = 0
+        for a in accs:
+            out[o:o + a.numel()].copy_(a)
+            o += a.numel()
+        return out
+
     def hybrid_step(self, nodes, cells, nsteps=1, use_graph=True):
         """`nodes[r]`, `cells[r]`: replica r's coupling nodes and cells (host int arrays)."""
         dn, pn, dc, pc = self._prepare(nodes, cells)

@@ -106,16 +106,18 @@ def grad_targets_from_sums(acc, nsamples, ppc, cells):
     return out
 
 
-def ensemble_configs(n=64, seed=1000):
+def ensemble_configs(n=64, seed=1000, rank=0):
     """The batched ensemble: n independent channels of the 64 x 1 geometry (walls across,
     one periodic cell), H uniform in 32..256 cells, 20..100 particles per cell, Kn
-    log-uniform in [0.01, 0.5], one LB node per cell, FP32 state, seeds seed + k."""
+    log-uniform in [0.01, 0.5], one LB node per cell, FP32 state, seeds seed + k. Rank r of a
+    multi-GPU ensemble runs the same n channels with the Philox seeds seed + k + r * 2^20, so
+    that channel k of every rank is one more sample of the same flow."""
     rng = np.random.default_rng(seed)
     out = []
     for k in range(n):
         out.append(config(ncx=int(rng.integers(32, 257)), ncy=1, ppc=int(rng.integers(20, 101)),
                           kn=float(np.exp(rng.uniform(np.log(0.01), np.log(0.5)))), lb_ratio=1,
-                          seed=seed + k))
+                          seed=seed + k + (rank << 20)))
     return out
 
 

@@ -254,3 +254,58 @@ def test_slab_exchange_pairs_neighbours(tmp_path, world):
         # packed LB rows: side 0 holds the slab below's side-1 pack, side 1 the slab above's
         assert torch.equal(got[r]["halo"][2], got[below]["halo"][1])
         assert torch.equal(got[r]["halo"][3], got[above]["halo"][0])
+
+
+def _ensemble_rank_main(rank, world, port, out_dir):
+    # a multi-GPU ensemble's host logic on CPU ranks: every rank runs the same channels with
+    # its own seeds (the oracle stands in for the batch) and the ranks sum the replicas' moment
+    # sums with one all-reduce
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    import numpy as np
+    from oracle import oracle as O
+    from paper_1512_08042_gb300 import workloads as W
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    cfgs = [dict(c, ncx=min(c["ncx"], 40), ppc=min(c["ppc"], 30)) for c in W.ensemble_configs(3, rank=rank)]
+    geom = torch.tensor([[c["ncx"], c["ppc"], c["kn"]] for c in cfgs], dtype=torch.float64)
+    seeds = torch.tensor([c["seed"] for c in cfgs], dtype=torch.int64)
+    geoms = [torch.zeros_like(geom) for _ in range(world)]
+    seedl = [torch.zeros_like(seeds) for _ in range(world)]
+    dist.all_gather(geoms, geom)
+    dist.all_gather(seedl, seeds)
+    accs = []
+    for c in cfgs:
+        o = O.Oracle(c)
+        nodes, cells = W.coupling_sites(c)
+        for _ in range(3):
+            o.dsmc_step(1)
+            o.map_dsmc_to_lbm(nodes)
+            o.lbm_step(1)
+            o.map_lbm_to_dsmc(cells)
+        accs.append(o.get(O.A_ACC).astype(np.float64).reshape(-1))
+    flat = torch.from_numpy(np.concatenate(accs))
+    mine = flat.clone()
+    dist.all_reduce(flat)
+    np.save(os.path.join(out_dir, "ens%d_mine.npy" % rank), mine.numpy())
+    np.save(os.path.join(out_dir, "ens%d_sum.npy" % rank), flat.numpy())
+    same_geom = all(torch.equal(g, geoms[0]) for g in geoms)
+    distinct = len(set(int(s) for sl in seedl for s in sl)) == world * len(cfgs)
+    with open(os.path.join(out_dir, "ens%d.txt" % rank), "w") as fh:
+        fh.write("%d %d\n" % (int(same_geom), int(distinct)))
+    dist.destroy_process_group()
+
+
+def test_ensemble_ranks_share_channels_and_sum_their_moment_sums(tmp_path):
+    port = _free_port()
+    mp.spawn(_ensemble_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True)
+    for r in range(2):
+        same_geom, distinct = open(tmp_path / ("ens%d.txt" % r)).read().split()
+        assert same_geom == "1" and distinct == "1"
+    m0, m1 = np.load(tmp_path / "ens0_mine.npy"), np.load(tmp_path / "ens1_mine.npy")
+    assert not np.array_equal(m0, m1)  # different seeds, different samples
+    for r in range(2):
+        assert np.array_equal(np.load(tmp_path / ("ens%d_sum.npy" % r)), m0 + m1)
