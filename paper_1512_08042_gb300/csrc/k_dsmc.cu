@@ -307,12 +307,10 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
     const int grp = (int)lane / G, gl = (int)lane % G;
     const int gi = w * CPW + grp;  // the group's cell within the block
     const uint32_t bin = (uint32_t)a.bin;
-    // shared memory: the block's pool of vx, vy, vz, x, y (, z) (Real) and keys (u32), `pool`
-    // slots each, then the candidates of one pass of phase B, in the same space as the cells'
+    // shared memory: the block's pool of vx, vy, vz, x, y (, z) (Real), `pool` slots each, then the candidates of one pass of phase B, in the same space as the cells'
     // key bitmaps of phase A (BW words and BW prefix bytes per cell)
     Real* pv = reinterpret_cast<Real*>(smem_raw);
-    uint32_t* pst = reinterpret_cast<uint32_t*>(pv + NR * (size_t)pool);
-    uint32_t* c_ij = pst + pool;
+    uint32_t* c_ij = reinterpret_cast<uint32_t*>(pv + NR * (size_t)pool);
     const int BW = bitmap_words<Z3>(bin);
     const int CW = (BW + G - 1) / G;
     const uint32_t lim = (uint32_t)BW * 32u;
@@ -388,14 +386,13 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
         Real* qx = pv + 3 * pool + poff;
         Real* qy = pv + 4 * pool + poff;
         Real* qz = pv + 5 * (size_t)pool + poff;  // 3D only
-        uint32_t* st = pst + poff;
         // A. stable order: every arrival's rank among the cell's arrivals by order key. A key
         // below W bin (a particle from a neighbouring cell) sets bit `key` of the cell's
         // bitmap, and its rank is the number of set bits below it: the count before its word
         // (a prefix over the words, kept modulo 256: a queried word holds its own bit, so
         // the count is below bin) plus those below it within the word. Larger keys follow
         // all of these, each ranked by counting the larger keys below it (from a list of the
-        // cell's larger keys while they are few).
+        // cell's larger keys while they are few, else from the records).
         {
             uint32_t* bm = s_bm + gi * BW;
             uint8_t* pf = s_pf + gi * BW;
@@ -408,7 +405,6 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
                 const uint32_t k = (uint32_t)(gl + G * r);
                 if (k < n) {
                     const uint32_t t = vl[r];
-                    st[k] = t;
                     if (t < lim) {
                         atomicOr(&bm[t >> 5], 1u << (t & 31u));
                     } else {
@@ -419,7 +415,6 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
             }
             for (uint32_t k = SMALL + gl; k < n; k += G) {
                 const uint32_t t = rec_tag(drec, base + k);
-                st[k] = t;
                 if (t < lim) {
                     atomicOr(&bm[t >> 5], 1u << (t & 31u));
                 } else {
@@ -470,7 +465,7 @@ __device__ __forceinline__ void collide_block(const DsmcArgs<Real>& a, uint32_t 
                         } else {
                             rk = nnear;
                             for (uint32_t m2 = 0; m2 < n; ++m2) {
-                                const uint32_t u = st[m2];
+                                const uint32_t u = rec_tag(drec, base + m2);
                                 rk += (u >= lim && u < t[j]) ? 1u : 0u;
                             }
                         }
@@ -924,7 +919,7 @@ size_t collide_smem(uint32_t pool, uint32_t bin) {
     constexpr int NC = W * (32 / kGroup);
     const size_t cand = (size_t)NC * kChainSteps * (4 + 4 * sizeof(Real));
     const size_t bits = ((size_t)NC * (bitmap_words<Z3>(bin) * 5 + (kFarList + 1) * 4) + 15) / 16 * 16;
-    return (size_t)pool * (pool_reals<Z3>() * sizeof(Real) + 4) + (cand > bits ? cand : bits);
+    return (size_t)pool * (pool_reals<Z3>() * sizeof(Real)) + (cand > bits ? cand : bits);
 }
 
 template <typename Real>
