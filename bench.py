@@ -691,8 +691,8 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(W.WORKLOADS))
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--collide-block", default="tune", choices=["tune", "4", "8"],
-                    help="the collide's block shape in warps, or timed by the library's tuner "
-                         "before the warm-up (hyb_tune_collide)")
+                    help="the collide's block shape in warps (multi-step fusion automatic), or both "
+                         "picked by the library's tuner before the warm-up (hyb_tune_collide)")
     ap.add_argument("--profile-kernel", default=None)
     ap.add_argument("--cpu-budget", type=float, default=16.0)
     ap.add_argument("--replicas", action="store_true",
@@ -803,15 +803,17 @@ def main():
     # the collide's block shape (the same results either way): the tuner times both on a
     # second context of this channel from the same initial state (it advances the context it
     # times), outside the timed region
+    fuse = "auto"
     if args.collide_block == "tune":
         tuner = B.Hybrid(cfg, device=dev)
-        collide_warps = tuner.tune_collide(nodes, cells)
+        collide_warps, fuse = tuner.tune_collide(nodes, cells)
         tuner.close()
         del tuner
         torch.cuda.empty_cache()
     else:
         collide_warps = int(args.collide_block)
     h.set_collide_block(collide_warps)
+    h.set_fuse(fuse)
 
     if args.profile_steps:
         run(args.profile_steps, graph=False)
@@ -950,7 +952,7 @@ def main():
         "config": {"workload": args.workload, "particles": n_particles, "lb_nodes": d["nnodes"],
                    "lattice": "D3Q%d" % d["q"], "coupling_nodes": len(nodes_np),
                    "coupling_cells": len(cells_np), "graph": use_graph,
-                   "collide_block_warps": collide_warps,
+                   "collide_block_warps": collide_warps, "fuse": fuse,
                    "kn": [cfg["kn"], cfg.get("kn_end", cfg["kn"])] if cfg.get("kn_profile") else cfg["kn"],
                    "l2": "inputs larger than L2, and flushed before every timed step (512 MB write)",
                    "parallelism": "replicas" if world > 1 else "single"},

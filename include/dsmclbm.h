@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define HYB_ABI_VERSION 9u
+#define HYB_ABI_VERSION 10u
 
 typedef enum {
     HYB_OK = 0,
@@ -410,13 +410,14 @@ hyb_status hyb_set_fuse(hyb_ctx* ctx, int32_t mode);
 /* The collide's block shape: 8 warps for 32 cells (the default) or 4 warps for 16 (twice the
  * blocks per SM; the NTC chain of a block then runs on 16 lanes); HYB_EINVAL for others. The
  * shape changes no result. get returns the shape in use (-1 for a null context).
- * hyb_tune_collide times, for each shape, a captured two-step hyb_hybrid_step with these
- * lists (the best of two replays, after the capture call), keeps the faster and returns it
- * in *warps if not NULL; it advances the context by 12 hybrid steps. */
+ * hyb_tune_collide times, for each shape, with and without fusion (HYB_FUSE_ALWAYS,
+ * HYB_FUSE_NEVER), a captured eight-step hyb_hybrid_step with these lists (the best of four
+ * replays, after the capture call and one replay), keeps the fastest pair and returns it in
+ * *warps and *fuse (either may be NULL); it advances the context by 192 hybrid steps. */
 hyb_status hyb_set_collide_block(hyb_ctx* ctx, int32_t warps);
 int32_t hyb_get_collide_block(const hyb_ctx* ctx);
 hyb_status hyb_tune_collide(hyb_ctx* ctx, const int32_t* dev_nodes, int32_t n_nodes,
-                            const int32_t* dev_cells, int32_t n_cells, int32_t* warps);
+                            const int32_t* dev_cells, int32_t n_cells, int32_t* warps, int32_t* fuse);
 
 /* Synchronises. Returns the sticky device status mapped to a hyb_status (HYB_OK if clear),
  * and the raw bits in *bits if not NULL. */

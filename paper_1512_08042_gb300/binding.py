@@ -11,7 +11,7 @@ import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "libdsmclbm.so")
-ABI_VERSION = 9
+ABI_VERSION = 10
 
 HYB_OK, HYB_EINVAL, HYB_ENOMEM, HYB_ECUDA, HYB_ECAPACITY, HYB_ETIMEOUT, HYB_ESAMPLING, HYB_ESTATE = range(8)
 ST_CAPACITY, ST_BOUNCE_CAP, ST_SCATTER_CAP, ST_SAMPLING_CAP, ST_CELL_OVERFLOW, ST_BAD_INPUT = (
@@ -134,7 +134,7 @@ def lib():
     L.hyb_set_collide_block.argtypes = [_vp, _i32]
     L.hyb_get_collide_block.argtypes = [_vp]
     L.hyb_get_collide_block.restype = _i32
-    L.hyb_tune_collide.argtypes = [_vp, _vp, _i32, _vp, _i32, P(_i32)]
+    L.hyb_tune_collide.argtypes = [_vp, _vp, _i32, _vp, _i32, P(_i32), P(_i32)]
     L.hyb_sync_status.argtypes = [_vp, P(_u32)]
     L.hyb_read_counters.argtypes = [_vp, _vp]
     L.hyb_profile.argtypes = [_vp, _i32]
@@ -460,17 +460,18 @@ class Hybrid:
         return int(lib().hyb_get_collide_block(self.ctx))
 
     def tune_collide(self, nodes=None, cells=None):
-        """Picks the faster collide block shape by timing hybrid steps with these coupling
-        lists (device int32 tensors or None); advances the context by 12 hybrid steps."""
+        """Picks the fastest collide block shape and fusion of multi-step calls by timing
+        hybrid steps with these coupling lists (device int32 tensors or None); advances the
+        context by 192 hybrid steps. Returns (warps, fuse), fuse "always" or "never"."""
         nn = 0 if nodes is None else nodes.numel()
         nc = 0 if cells is None else cells.numel()
         self._inputs(nodes, cells)
-        w = _i32()
+        w, f = _i32(), _i32()
         rc = lib().hyb_tune_collide(self.ctx, nodes.data_ptr() if nn else None, nn,
-                                    cells.data_ptr() if nc else None, nc, ctypes.byref(w))
+                                    cells.data_ptr() if nc else None, nc, ctypes.byref(w), ctypes.byref(f))
         if rc != HYB_OK:
             raise HybError(rc, lib().hyb_last_error(self.ctx).decode())
-        return w.value
+        return w.value, {1: "always", 2: "never"}[f.value]
 
     def profile(self, kernel):
         _check(lib().hyb_profile(self.ctx, KERNELS[kernel] if isinstance(kernel, str) else kernel))

@@ -701,23 +701,29 @@ hyb_status hyb_set_collide_block(hyb_ctx* h, int32_t warps) {
 int32_t hyb_get_collide_block(const hyb_ctx* h) { return h ? h->c.collide_warps : -1; }
 
 hyb_status hyb_tune_collide(hyb_ctx* h, const int32_t* dev_nodes, int32_t n_nodes, const int32_t* dev_cells,
-                            int32_t n_cells, int32_t* warps) {
+                            int32_t n_cells, int32_t* warps, int32_t* fuse) {
     if (!h) return HYB_EINVAL;
     Ctx& c = h->c;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return HYB_ECUDA;
-    const int shapes[2] = {8, 4};
+    // (block shape, fusion) pairs, each timed on captured eight-step calls: the capture call
+    // and one replay untimed, then the best of four replays (short calls on small channels
+    // vary by tens of percent from call to call)
+    constexpr int kSteps = 8, kReplays = 4;
+    const int shapes[4] = {8, 4, 8, 4};
+    const int modes[4] = {HYB_FUSE_ALWAYS, HYB_FUSE_ALWAYS, HYB_FUSE_NEVER, HYB_FUSE_NEVER};
     float best = 1e30f;
-    int best_w = c.collide_warps;
+    int best_i = 0;
     hyb_status s = HYB_OK;
-    for (int i = 0; i < 2 && s == HYB_OK; ++i) {
+    for (int i = 0; i < 4 && s == HYB_OK; ++i) {
         s = hyb_set_collide_block(h, shapes[i]);
-        // a captured two-step graph, then the best of two replays
-        if (s == HYB_OK) s = hyb_hybrid_step(h, dev_nodes, n_nodes, dev_cells, n_cells, 2, 1);
+        if (s == HYB_OK) s = hyb_set_fuse(h, modes[i]);
+        for (int k = 0; k < 2 && s == HYB_OK; ++k)
+            s = hyb_hybrid_step(h, dev_nodes, n_nodes, dev_cells, n_cells, kSteps, 1);
         float t_best = 1e30f;
-        for (int k = 0; k < 2 && s == HYB_OK; ++k) {
+        for (int k = 0; k < kReplays && s == HYB_OK; ++k) {
             cudaEventRecord(e0, c.stream);
-            s = hyb_hybrid_step(h, dev_nodes, n_nodes, dev_cells, n_cells, 2, 1);
+            s = hyb_hybrid_step(h, dev_nodes, n_nodes, dev_cells, n_cells, kSteps, 1);
             cudaEventRecord(e1, c.stream);
             if (s == HYB_OK && cudaEventSynchronize(e1) != cudaSuccess) s = HYB_ECUDA;
             float t = 0.f;
@@ -726,14 +732,16 @@ hyb_status hyb_tune_collide(hyb_ctx* h, const int32_t* dev_nodes, int32_t n_node
         }
         if (s == HYB_OK && t_best < best) {
             best = t_best;
-            best_w = shapes[i];
+            best_i = i;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (s != HYB_OK) return s;
-    s = hyb_set_collide_block(h, best_w);
-    if (warps) *warps = best_w;
+    s = hyb_set_collide_block(h, shapes[best_i]);
+    if (s == HYB_OK) s = hyb_set_fuse(h, modes[best_i]);
+    if (warps) *warps = shapes[best_i];
+    if (fuse) *fuse = modes[best_i];
     return s;
 }
 

@@ -184,10 +184,10 @@ def test_collide_tuner_keeps_results():
     nodes, cells = W.coupling_sites(cfg, strip_cells=2)
     dn, dc = torch.from_numpy(nodes).cuda(), torch.from_numpy(cells).cuda()
     a, b = B.Hybrid(cfg), B.Hybrid(cfg)
-    w = a.tune_collide(dn, dc)
-    assert w in (4, 8) and a.collide_block() == w
+    w, fuse = a.tune_collide(dn, dc)
+    assert w in (4, 8) and a.collide_block() == w and fuse in ("always", "never")
     a.hybrid_step(dn, dc, nsteps=2, use_graph=True)
-    b.hybrid_step(dn, dc, nsteps=12 + 2, use_graph=True)  # the tuner's 12 steps, then 2
+    b.hybrid_step(dn, dc, nsteps=192 + 2, use_graph=True)  # the tuner's 192 steps, then 2
     assert_same_state(a, b)
 
 
