@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define HYB_ABI_VERSION 10u
+#define HYB_ABI_VERSION 11u
 
 typedef enum {
     HYB_OK = 0,
@@ -388,6 +388,18 @@ hyb_status map_dsmc_to_lbm_adjoint(hyb_ctx* ctx, const int32_t* dev_nodes, int32
 hyb_status hyb_hybrid_step_host(hyb_ctx* ctx, const int32_t* host_nodes, int32_t n_nodes,
                                 const int32_t* host_cells, int32_t n_cells, double* host_acc,
                                 uint32_t* host_status);
+
+/* nsteps hybrid steps with host buffers in one call, as nsteps calls of hyb_hybrid_step_host
+ * with the same lists (each step copies the lists in before its first kernel and its strip
+ * sums and status out after its LB2DSMC), but with the DSMC passes of consecutive steps fused
+ * as in hyb_hybrid_step (hyb_set_fuse, hyb_set_collide_block; the same results). host_acc
+ * holds nsteps x n_cells x 20 doubles (step k's sums at k n_cells 20), host_status nsteps
+ * words. Enqueued with direct launches on the context's stream, completed as one entry of the
+ * ring that hyb_host_wait counts. The staging and errors are those of hyb_hybrid_step_host;
+ * nsteps < 1 is HYB_EINVAL. */
+hyb_status hyb_hybrid_steps_host(hyb_ctx* ctx, int32_t nsteps, const int32_t* host_nodes, int32_t n_nodes,
+                                 const int32_t* host_cells, int32_t n_cells, double* host_acc,
+                                 uint32_t* host_status);
 
 /* Waits until at most `pending` (0 to 3) of the steps issued by hyb_hybrid_step_host are
  * still in flight, so their results have landed in the host buffers: pending = 0 waits for

@@ -11,7 +11,7 @@ import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "libdsmclbm.so")
-ABI_VERSION = 10
+ABI_VERSION = 11
 
 HYB_OK, HYB_EINVAL, HYB_ENOMEM, HYB_ECUDA, HYB_ECAPACITY, HYB_ETIMEOUT, HYB_ESAMPLING, HYB_ESTATE = range(8)
 ST_CAPACITY, ST_BOUNCE_CAP, ST_SCATTER_CAP, ST_SAMPLING_CAP, ST_CELL_OVERFLOW, ST_BAD_INPUT = (
@@ -58,7 +58,7 @@ EXPORTS = ["hyb_derive", "hyb_layout_compute", "hyb_lattice", "hyb_status_string
            "dsmc_step", "dsmc_move", "dsmc_merge", "dsmc_collide", "lbm_halo_size", "lbm_halo_pack",
            "lbm_halo_unpack", "lbm_step", "sample_moments", "map_dsmc_to_lbm", "map_lbm_to_dsmc",
            "map_lbm_to_dsmc_noalloc", "map_dsmc_to_lbm_adjoint", "lbm_step_nodes", "lbm_interface_loss", "lbm_adjoint_step",
-           "hyb_hybrid_step", "hyb_hybrid_step_host", "hyb_host_wait", "hyb_batch_layout", "hyb_batch_init", "hyb_batch_replica",
+           "hyb_hybrid_step", "hyb_hybrid_step_host", "hyb_hybrid_steps_host", "hyb_host_wait", "hyb_batch_layout", "hyb_batch_init", "hyb_batch_replica",
            "hyb_batch_hybrid_step", "hyb_batch_set_blocks", "hyb_batch_set_block", "hyb_batch_get_block",
            "hyb_batch_tune",
            "hyb_batch_last_error", "hyb_batch_destroy", "hyb_current", "hyb_sync_status", "hyb_read_counters",
@@ -116,6 +116,7 @@ def lib():
     L.lbm_adjoint_step.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
     L.hyb_hybrid_step.argtypes = [_vp, _vp, _i32, _vp, _i32, _i32, _i32]
     L.hyb_hybrid_step_host.argtypes = [_vp, _vp, _i32, _vp, _i32, _vp, _vp]
+    L.hyb_hybrid_steps_host.argtypes = [_vp, _i32, _vp, _i32, _vp, _i32, _vp, _vp]
     L.hyb_host_wait.argtypes = [_vp, _i32]
     L.hyb_batch_layout.argtypes = [_vp, _i32, _vp]
     L.hyb_batch_init.argtypes = [_vp, _i32, _vp, _u64, _vp, P(_vp)]
@@ -394,11 +395,12 @@ class Hybrid:
         _check(lib().hyb_hybrid_step(self.ctx, np_, nn, cp_, nc, nsteps, 1 if use_graph else 0),
                self.ctx)
 
-    def hybrid_step_host(self, nodes, cells, out_acc, out_status):
-        """One hybrid step with host lists and host results (hyb_hybrid_step_host): `nodes`,
-        `cells` int32 and `out_acc` float64 [len(cells), 20], `out_status` int32 [>= 1], CPU
-        tensors or arrays (page-locked for asynchronous copies). Returns once enqueued; the
-        results are valid after host_wait()."""
+    def hybrid_step_host(self, nodes, cells, out_acc, out_status, nsteps=1):
+        """Hybrid steps with host lists and host results (hyb_hybrid_step_host for one step,
+        hyb_hybrid_steps_host for several, each step copying its lists in and its results out):
+        `nodes`, `cells` int32 and `out_acc` float64 [nsteps, len(cells), 20], `out_status`
+        int32 [>= nsteps], CPU tensors or arrays (page-locked for asynchronous copies). Returns
+        once enqueued; the results are valid after host_wait()."""
         def ptr(a):
             return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
 
@@ -411,13 +413,19 @@ class Hybrid:
             if not ok:
                 raise ValueError("%s must be a contiguous host %s buffer of >= %d values" % (what, dtype, n))
         nn, nc = len(nodes), len(cells)
+        nsteps = int(nsteps)
         check(nodes, "int32", nn, "nodes")
         check(cells, "int32", nc, "cells")
-        check(out_acc, "float64", 20 * nc, "out_acc")
-        check(out_status, "int32", 1, "out_status")
-        _check(lib().hyb_hybrid_step_host(self.ctx, ptr(nodes) if nn else None, nn,
-                                          ptr(cells) if nc else None, nc,
-                                          ptr(out_acc) if nc else None, ptr(out_status)), self.ctx)
+        check(out_acc, "float64", 20 * nc * nsteps, "out_acc")
+        check(out_status, "int32", nsteps, "out_status")
+        if nsteps == 1:
+            _check(lib().hyb_hybrid_step_host(self.ctx, ptr(nodes) if nn else None, nn,
+                                              ptr(cells) if nc else None, nc,
+                                              ptr(out_acc) if nc else None, ptr(out_status)), self.ctx)
+        else:
+            _check(lib().hyb_hybrid_steps_host(self.ctx, nsteps, ptr(nodes) if nn else None, nn,
+                                               ptr(cells) if nc else None, nc,
+                                               ptr(out_acc) if nc else None, ptr(out_status)), self.ctx)
 
     def host_wait(self, pending=0):
         """Wait until at most `pending` host steps are in flight (hyb_host_wait)."""

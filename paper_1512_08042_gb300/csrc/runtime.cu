@@ -3,6 +3,7 @@
 // timing and error reporting. Every entry point of include/dsmclbm.h is defined here.
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <new>
 #include <vector>
 
@@ -247,17 +248,27 @@ hyb_status dsmc_steps(Ctx& c, int n) {
     return s;
 }
 
+// Work a caller adds around each step of a multi-step call: before step k >= 1 (ahead of its
+// first kernel) and after step k's LB2DSMC, on the context's stream.
+struct StepHooks {
+    std::function<hyb_status(int)> before, after;
+};
+
 // n hybrid steps in the order of one_hybrid_step, with the DSMC passes fused across steps:
 // move; then per step the fused pass (the last step: the collide), DSMC2LB, the LB step and
 // LB2DSMC, which within the fused run regenerates the coupling cells and moves their new
 // particles on at once. The coupling cells are marked for the fused passes for the call's
 // duration. The results equal n calls of one_hybrid_step bit for bit.
 hyb_status fused_hybrid_steps(Ctx& c, const int32_t* nodes, int32_t nn, const int32_t* cells,
-                              int32_t ncl, int n) {
+                              int32_t ncl, int n, const StepHooks* hk = nullptr) {
     if (n <= 0) return HYB_OK;
     if (n > 1 && !fuse_steps(c)) {
         hyb_status s = HYB_OK;
-        for (int k = 0; k < n && s == HYB_OK; ++k) s = one_hybrid_step(c, nodes, nn, cells, ncl);
+        for (int k = 0; k < n && s == HYB_OK; ++k) {
+            if (hk && k > 0) s = hk->before(k);
+            if (s == HYB_OK) s = one_hybrid_step(c, nodes, nn, cells, ncl);
+            if (s == HYB_OK && hk) s = hk->after(k);
+        }
         return s;
     }
     int p = c.cur_p;
@@ -267,6 +278,8 @@ hyb_status fused_hybrid_steps(Ctx& c, const int32_t* nodes, int32_t nn, const in
     if (s == HYB_OK) s = check(c, launch_dsmc_move(c, p), "dsmc move launch");
     for (int k = 0; k < n && s == HYB_OK; ++k) {
         const bool last = k == n - 1;
+        if (hk && k > 0) s = hk->before(k);
+        if (s != HYB_OK) break;
         s = last ? check(c, launch_dsmc_collide(c, p), "dsmc collide launch")
                  : check(c, launch_dsmc_fused(c, p), "dsmc fused launch");
         if (s == HYB_OK && nn > 0) s = check(c, launch_map_d2l(c, nodes, nn), "map_dsmc_to_lbm launch");
@@ -279,6 +292,7 @@ hyb_status fused_hybrid_steps(Ctx& c, const int32_t* nodes, int32_t nn, const in
             if (ncl > 0) s = check(c, launch_map_l2d_move(c, cells, ncl, p), "map_lbm_to_dsmc launch");
             p ^= 1;
         }
+        if (s == HYB_OK && hk) s = hk->after(k);
     }
     if (s == HYB_OK && mark) s = check(c, launch_mark_cells(c, cells, ncl, 0), "clear coupling cells");
     return s;
@@ -889,6 +903,75 @@ hyb_status hyb_hybrid_step_host(hyb_ctx* h, const int32_t* host_nodes, int32_t n
     if (s == HYB_OK)
         s = check(c, cudaMemcpyAsync(host_status, c.st.ctrl + CTRL_STATUS, 4, cudaMemcpyDeviceToHost, c.stream),
                   "copy status out");
+    if (s == HYB_OK) s = check(c, cudaEventRecord(c.io_ev[c.io_issued % 4], c.stream), "event record");
+    if (s == HYB_OK) c.io_issued += 1;
+    return s;
+}
+
+hyb_status hyb_hybrid_steps_host(hyb_ctx* h, int32_t nsteps, const int32_t* host_nodes, int32_t n_nodes,
+                                 const int32_t* host_cells, int32_t n_cells, double* host_acc,
+                                 uint32_t* host_status) {
+    if (!h || nsteps < 1 || n_nodes < 0 || n_cells < 0 || !host_status) return HYB_EINVAL;
+    Ctx& c = h->c;
+    if ((n_nodes > 0 && !host_nodes) || (n_cells > 0 && (!host_cells || !host_acc)) ||
+        n_nodes > c.d.nnodes || n_cells > c.d.ncells)
+        return HYB_EINVAL;
+    if (c.p.ncy_global > 0 || c.split_pending)
+        return fail(c, HYB_EINVAL, "hyb_hybrid_steps_host: a slab steps with the split calls");
+    if (c.stream == nullptr) return fail(c, HYB_ESTATE, "host steps need a non-default stream");
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t off_c = up(4 * (size_t)n_nodes), off_a = off_c + up(4 * (size_t)n_cells);
+    const size_t need = off_a + up(8 * (size_t)kMoments * n_cells) + 256;
+    if (need > c.io_bytes) {
+        hyb_status s = check(c, cudaStreamSynchronize(c.stream), "synchronize");
+        if (s != HYB_OK) return s;
+        if (c.io_dev) cudaFree(c.io_dev);
+        c.io_dev = nullptr;
+        c.io_bytes = 0;
+        s = check(c, cudaMalloc((void**)&c.io_dev, need), "host-step staging");
+        if (s != HYB_OK) return s;
+        c.io_bytes = need;
+    }
+    for (int i = 0; i < 4; ++i)
+        if (!c.io_ev[i]) {
+            hyb_status s = check(c, cudaEventCreateWithFlags(&c.io_ev[i], cudaEventDisableTiming),
+                                 "event create");
+            if (s != HYB_OK) return s;
+        }
+    if (c.io_issued - c.io_done >= 4) {
+        hyb_status s = hyb_host_wait(h, 3);
+        if (s != HYB_OK) return s;
+    }
+    int32_t* dn = (int32_t*)c.io_dev;
+    int32_t* dc = (int32_t*)(c.io_dev + off_c);
+    double* da = (double*)(c.io_dev + off_a);
+    // every step copies the lists in before its first kernel and its strip sums and status out
+    auto copy_in = [&](int) -> hyb_status {
+        hyb_status s = HYB_OK;
+        if (n_nodes > 0)
+            s = check(c, cudaMemcpyAsync(dn, host_nodes, 4 * (size_t)n_nodes, cudaMemcpyHostToDevice, c.stream),
+                      "copy nodes in");
+        if (s == HYB_OK && n_cells > 0)
+            s = check(c, cudaMemcpyAsync(dc, host_cells, 4 * (size_t)n_cells, cudaMemcpyHostToDevice, c.stream),
+                      "copy cells in");
+        return s;
+    };
+    auto copy_out = [&](int k) -> hyb_status {
+        hyb_status s = HYB_OK;
+        if (n_cells > 0) s = check(c, launch_gather_acc(c, dc, n_cells, da), "gather launch");
+        if (s == HYB_OK && n_cells > 0)
+            s = check(c, cudaMemcpyAsync(host_acc + (size_t)k * kMoments * n_cells, da,
+                                         8 * (size_t)kMoments * n_cells, cudaMemcpyDeviceToHost, c.stream),
+                      "copy moments out");
+        if (s == HYB_OK)
+            s = check(c, cudaMemcpyAsync(host_status + k, c.st.ctrl + CTRL_STATUS, 4, cudaMemcpyDeviceToHost,
+                                         c.stream),
+                      "copy status out");
+        return s;
+    };
+    StepHooks hk{copy_in, copy_out};
+    hyb_status s = copy_in(0);
+    if (s == HYB_OK) s = fused_hybrid_steps(c, dn, n_nodes, dc, n_cells, nsteps, &hk);
     if (s == HYB_OK) s = check(c, cudaEventRecord(c.io_ev[c.io_issued % 4], c.stream), "event record");
     if (s == HYB_OK) c.io_issued += 1;
     return s;

@@ -102,6 +102,7 @@ def test_invalid_parameters_are_rejected(lib):
     assert lib.dsmc_step(None, 1) == B.HYB_EINVAL
     assert lib.map_lbm_to_dsmc(None, None, 1) == B.HYB_EINVAL
     assert lib.hyb_hybrid_step_host(None, None, 0, None, 0, None, None) == B.HYB_EINVAL
+    assert lib.hyb_hybrid_steps_host(None, 2, None, 0, None, 0, None, None) == B.HYB_EINVAL
     assert lib.hyb_host_wait(None, 0) == B.HYB_EINVAL
     assert lib.map_dsmc_to_lbm_adjoint(None, None, 1, None, None) == B.HYB_EINVAL
     assert lib.lbm_adjoint_step(None, None, None, None, None, None, None, None, None) == B.HYB_EINVAL

@@ -491,6 +491,38 @@ def test_host_buffer_steps_equal_device_list_steps(pinned):
         b.host_wait(4)
 
 
+@pytest.mark.parametrize("fuse", ["always", "never"])
+def test_multi_step_host_calls_equal_one_step_host_calls(fuse):
+    # hyb_hybrid_steps_host: several steps per call, each copying its lists in and its sums and
+    # status out, the DSMC passes fused across the call's steps (or not): every step's returned
+    # sums and the final state equal those of one-step host calls
+    cfg = cfg_small(lb_ratio=2, ma=0.3)
+    nodes, cells = W.coupling_sites(cfg, strip_cells=2)
+    a, b = B.Hybrid(cfg), B.Hybrid(cfg)
+    b.set_fuse(fuse)
+    hn, hc = torch.from_numpy(nodes).pin_memory(), torch.from_numpy(cells).pin_memory()
+    n = 6
+    one = np.zeros((n, len(cells), 20))
+    for k in range(n):
+        out = torch.zeros(1, len(cells), 20, dtype=torch.float64).pin_memory()
+        st = torch.zeros(1, dtype=torch.int32).pin_memory()
+        a.hybrid_step_host(hn, hc, out, st)
+        a.host_wait(0)
+        one[k] = out.numpy()[0]
+    many = [torch.zeros(3, len(cells), 20, dtype=torch.float64).pin_memory() for _ in range(2)]
+    sts = [torch.zeros(3, dtype=torch.int32).pin_memory() for _ in range(2)]
+    b.hybrid_step_host(hn, hc, many[0], sts[0], nsteps=3)
+    b.hybrid_step_host(hn, hc, many[1], sts[1], nsteps=3)
+    b.host_wait(0)
+    got = np.concatenate([many[0].numpy(), many[1].numpy()])
+    assert np.array_equal(got, one)
+    assert np.all(np.concatenate([sts[0].numpy(), sts[1].numpy()]) == 0)
+    for k in ("x", "y", "vx", "vy", "vz"):
+        assert np.array_equal(gpu_particles(a)[k], gpu_particles(b)[k]), k
+    assert np.array_equal(a.f().cpu().numpy(), b.f().cpu().numpy())
+    assert a.counters() == b.counters()
+
+
 # ---------------------------------------------------------------------------------------
 # The benchmarked FP32 coupled step, from the GPU's own state, sub-step by sub-step
 
