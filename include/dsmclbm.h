@@ -394,9 +394,11 @@ hyb_status hyb_hybrid_step_host(hyb_ctx* ctx, const int32_t* host_nodes, int32_t
  * sums and status out after its LB2DSMC), but with the DSMC passes of consecutive steps fused
  * as in hyb_hybrid_step (hyb_set_fuse, hyb_set_collide_block; the same results). host_acc
  * holds nsteps x n_cells x 20 doubles (step k's sums at k n_cells 20), host_status nsteps
- * words. Enqueued with direct launches on the context's stream, completed as one entry of the
- * ring that hyb_host_wait counts. The staging and errors are those of hyb_hybrid_step_host;
- * nsteps < 1 is HYB_EINVAL. */
+ * words. With page-locked host buffers the call is enqueued as one CUDA graph (captured at
+ * the first call with the same steps, lists, buffers and state halves; the context keeps the
+ * two latest), with pageable ones as direct launches, on the context's stream; either way it
+ * completes as one entry of the ring that hyb_host_wait counts. The staging and errors are
+ * those of hyb_hybrid_step_host; nsteps < 1 is HYB_EINVAL. */
 hyb_status hyb_hybrid_steps_host(hyb_ctx* ctx, int32_t nsteps, const int32_t* host_nodes, int32_t n_nodes,
                                  const int32_t* host_cells, int32_t n_cells, double* host_acc,
                                  uint32_t* host_status);

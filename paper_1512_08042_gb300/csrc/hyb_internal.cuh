@@ -598,6 +598,19 @@ struct Ctx {
     cudaGraphExec_t mgraph[2] = {nullptr, nullptr};
     int32_t mkey[2][3] = {{-1, -1, -1}, {-1, -1, -1}};
     int mnext = 0;
+    // graphs of multi-step host-buffer calls, keyed by steps, parities, lists and buffers
+    struct HostKey {
+        int32_t nsteps = -1, cur_p = -1, cur_f = -1, nn = -1, nc = -1;
+        const void *nodes = nullptr, *cells = nullptr, *acc = nullptr, *status = nullptr, *staging = nullptr;
+        bool operator==(const HostKey& o) const {
+            return nsteps == o.nsteps && cur_p == o.cur_p && cur_f == o.cur_f && nn == o.nn && nc == o.nc &&
+                   nodes == o.nodes && cells == o.cells && acc == o.acc && status == o.status &&
+                   staging == o.staging;
+        }
+    };
+    cudaGraphExec_t hgraph[2] = {nullptr, nullptr};
+    HostKey hkey[2];
+    int hnext = 0;
     const int32_t* g_nodes = nullptr;
     const int32_t* g_cells = nullptr;
     int32_t g_nn = -1, g_nc = -1;

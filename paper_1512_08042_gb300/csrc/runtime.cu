@@ -351,6 +351,11 @@ void drop_graphs(Ctx& c) {
             c.mgraph[i] = nullptr;
         }
         c.mkey[i][0] = c.mkey[i][1] = c.mkey[i][2] = -1;
+        if (c.hgraph[i]) {
+            cudaGraphExecDestroy(c.hgraph[i]);
+            c.hgraph[i] = nullptr;
+        }
+        c.hkey[i] = Ctx::HostKey{};
     }
 }
 
@@ -970,8 +975,73 @@ hyb_status hyb_hybrid_steps_host(hyb_ctx* h, int32_t nsteps, const int32_t* host
         return s;
     };
     StepHooks hk{copy_in, copy_out};
-    hyb_status s = copy_in(0);
-    if (s == HYB_OK) s = fused_hybrid_steps(c, dn, n_nodes, dc, n_cells, nsteps, &hk);
+    // a graph only copies page-locked host buffers asynchronously; pageable ones (and kernel
+    // timing) take direct launches
+    auto locked = [](const void* p) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        return a.type == cudaMemoryTypeHost;
+    };
+    const bool graph = c.prof_kernel < 0 && (n_nodes == 0 || locked(host_nodes)) &&
+                       (n_cells == 0 || (locked(host_cells) && locked(host_acc))) && locked(host_status);
+    hyb_status s = HYB_OK;
+    if (!graph) {
+        s = copy_in(0);
+        if (s == HYB_OK) s = fused_hybrid_steps(c, dn, n_nodes, dc, n_cells, nsteps, &hk);
+    } else {
+        // the call's graph (copies and kernels), captured once per steps, parities and buffers
+        Ctx::HostKey key;
+        key.nsteps = nsteps;
+        key.cur_p = c.cur_p;
+        key.cur_f = c.cur_f;
+        key.nn = n_nodes;
+        key.nc = n_cells;
+        key.nodes = host_nodes;
+        key.cells = host_cells;
+        key.acc = host_acc;
+        key.status = host_status;
+        key.staging = c.io_dev;
+        int slot = -1;
+        for (int i = 0; i < 2; ++i)
+            if (c.hgraph[i] && c.hkey[i] == key) slot = i;
+        if (slot < 0) {
+            slot = c.hnext;
+            c.hnext ^= 1;
+            if (c.hgraph[slot]) {
+                cudaGraphExecDestroy(c.hgraph[slot]);
+                c.hgraph[slot] = nullptr;
+            }
+            cudaGraph_t g = nullptr;
+            s = check(c, cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+            if (s != HYB_OK) return s;
+            c.capturing = true;
+            hyb_status s2 = copy_in(0);
+            if (s2 == HYB_OK) s2 = fused_hybrid_steps(c, dn, n_nodes, dc, n_cells, nsteps, &hk);
+            c.capturing = false;
+            cudaError_t e = cudaStreamEndCapture(c.stream, &g);
+            c.cur_p = key.cur_p;
+            c.cur_f = key.cur_f;
+            if (s2 != HYB_OK) {
+                if (g) cudaGraphDestroy(g);
+                return s2;
+            }
+            s = check(c, e, "end capture");
+            if (s != HYB_OK) return s;
+            e = cudaGraphInstantiate(&c.hgraph[slot], g, 0);
+            cudaGraphDestroy(g);
+            s = check(c, e, "graph instantiate");
+            if (s != HYB_OK) return s;
+            c.hkey[slot] = key;
+        }
+        s = check(c, cudaGraphLaunch(c.hgraph[slot], c.stream), "graph launch");
+        if (s == HYB_OK) {  // each step flips both parities once
+            c.cur_p = key.cur_p ^ (nsteps & 1);
+            c.cur_f = key.cur_f ^ (nsteps & 1);
+        }
+    }
     if (s == HYB_OK) s = check(c, cudaEventRecord(c.io_ev[c.io_issued % 4], c.stream), "event record");
     if (s == HYB_OK) c.io_issued += 1;
     return s;

@@ -491,17 +491,20 @@ def test_host_buffer_steps_equal_device_list_steps(pinned):
         b.host_wait(4)
 
 
-@pytest.mark.parametrize("fuse", ["always", "never"])
-def test_multi_step_host_calls_equal_one_step_host_calls(fuse):
+@pytest.mark.parametrize("fuse,pinned", [("always", True), ("never", True), ("always", False)])
+def test_multi_step_host_calls_equal_one_step_host_calls(fuse, pinned):
     # hyb_hybrid_steps_host: several steps per call, each copying its lists in and its sums and
     # status out, the DSMC passes fused across the call's steps (or not): every step's returned
-    # sums and the final state equal those of one-step host calls
+    # sums and the final state equal those of one-step host calls. With page-locked buffers
+    # the call is a graph, captured at the first two calls and replayed at the third (the same
+    # buffers and state halves as the first); pageable buffers take direct launches.
     cfg = cfg_small(lb_ratio=2, ma=0.3)
     nodes, cells = W.coupling_sites(cfg, strip_cells=2)
     a, b = B.Hybrid(cfg), B.Hybrid(cfg)
     b.set_fuse(fuse)
-    hn, hc = torch.from_numpy(nodes).pin_memory(), torch.from_numpy(cells).pin_memory()
-    n = 6
+    mk = (lambda x: x.pin_memory()) if pinned else (lambda x: x)
+    hn, hc = mk(torch.from_numpy(nodes)), mk(torch.from_numpy(cells))
+    n = 9
     one = np.zeros((n, len(cells), 20))
     for k in range(n):
         out = torch.zeros(1, len(cells), 20, dtype=torch.float64).pin_memory()
@@ -509,14 +512,16 @@ def test_multi_step_host_calls_equal_one_step_host_calls(fuse):
         a.hybrid_step_host(hn, hc, out, st)
         a.host_wait(0)
         one[k] = out.numpy()[0]
-    many = [torch.zeros(3, len(cells), 20, dtype=torch.float64).pin_memory() for _ in range(2)]
-    sts = [torch.zeros(3, dtype=torch.int32).pin_memory() for _ in range(2)]
-    b.hybrid_step_host(hn, hc, many[0], sts[0], nsteps=3)
-    b.hybrid_step_host(hn, hc, many[1], sts[1], nsteps=3)
-    b.host_wait(0)
-    got = np.concatenate([many[0].numpy(), many[1].numpy()])
-    assert np.array_equal(got, one)
-    assert np.all(np.concatenate([sts[0].numpy(), sts[1].numpy()]) == 0)
+    many = [mk(torch.zeros(3, len(cells), 20, dtype=torch.float64)) for _ in range(2)]
+    sts = [mk(torch.zeros(3, dtype=torch.int32)) for _ in range(2)]
+    got, got_st = [], []
+    for call in range(3):
+        b.hybrid_step_host(hn, hc, many[call % 2], sts[call % 2], nsteps=3)
+        b.host_wait(0)
+        got.append(many[call % 2].numpy().copy())
+        got_st.append(sts[call % 2].numpy().copy())
+    assert np.array_equal(np.concatenate(got), one)
+    assert np.all(np.concatenate(got_st) == 0)
     for k in ("x", "y", "vx", "vy", "vz"):
         assert np.array_equal(gpu_particles(a)[k], gpu_particles(b)[k]), k
     assert np.array_equal(a.f().cpu().numpy(), b.f().cpu().numpy())
