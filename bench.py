@@ -892,7 +892,8 @@ def main():
 
     # end to end through the C-ABI calls with host buffers: every step copies the coupling
     # lists in from page-locked host memory and the strip's moment sums and the status word
-    # out. The headline form takes E2E_CALL steps per call (hyb_hybrid_steps_host: the DSMC
+    # out (two of the library's kernels per step, which read and write the host buffers
+    # through their device addresses; the call is one CUDA graph). The headline form takes E2E_CALL steps per call (hyb_hybrid_steps_host: the DSMC
     # passes fused across the call's steps as in the device-timed run), pipelined: the host
     # reads call j's results (two result buffers) while call j + 1 runs. One step per call
     # (hyb_hybrid_step_host), pipelined and synchronous, is reported beside it.
@@ -1001,6 +1002,10 @@ def main():
                 "api": "hyb_hybrid_steps_host, %d steps per call (every step: host lists in, "
                        "strip moments and status out)" % E2E_CALL,
                 "mode": "pipelined: the host reads a call's results while the next call runs",
+                "transfers": "page-locked host buffers read and written by two library kernels per "
+                             "step through their device addresses; each call one CUDA graph",
+                "gpu_launches_per_call": launches_in_call(E2E_CALL, "fused" in kernel_ms, len(nodes_np),
+                                                          len(cells_np)) + 2 * E2E_CALL,
                 "one_step_per_call": {"api": "hyb_hybrid_step_host", "value": world * e2e_one,
                                       "synchronous_value": world * e2e_one_sync},
                 "status_bits_seen": seen["bad"]},

@@ -375,14 +375,16 @@ hyb_status map_dsmc_to_lbm_adjoint(hyb_ctx* ctx, const int32_t* dev_nodes, int32
  * the context's stream, in order:
  *   - the n_nodes nodes and n_cells cells (host int32) are copied to device staging owned by
  *     the context;
- *   - hyb_hybrid_step(ctx, staging, n_nodes, staging, n_cells, 1, use_graph = 1);
+ *   - one hybrid step, as hyb_hybrid_step(ctx, staging, n_nodes, staging, n_cells, 1, 1);
  *   - the 20 cumulative moment sums of each listed cell (the layout of hyb_layout.acc; zeros
  *     for an index out of range) are copied to host_acc (n_cells x 20 doubles, list order);
  *   - the sticky status word (HYB_ST_* bits) is copied to *host_status.
  * The call returns once the work is enqueued; the host buffers must stay valid and
  * untouched until hyb_host_wait says the step is done. With page-locked host buffers
- * (cudaMallocHost, cudaHostRegister) the copies are asynchronous; pageable buffers work but
- * make the copies synchronous. The first call, and any call with longer lists, allocates
+ * (cudaMallocHost, cudaHostRegister) the transfers are made by two kernels that read and
+ * write the buffers through their device addresses, and the whole call is one CUDA graph
+ * (as in hyb_hybrid_steps_host); pageable buffers work but take cudaMemcpyAsync copies, which
+ * are then synchronous. The first call, and any call with longer lists, allocates
  * the staging (4 n_nodes + 164 n_cells bytes, rounded up) on the device; hyb_destroy frees
  * it. host_acc may be NULL when n_cells is 0. Invalid sizes or pointers: HYB_EINVAL. */
 hyb_status hyb_hybrid_step_host(hyb_ctx* ctx, const int32_t* host_nodes, int32_t n_nodes,
@@ -394,11 +396,12 @@ hyb_status hyb_hybrid_step_host(hyb_ctx* ctx, const int32_t* host_nodes, int32_t
  * sums and status out after its LB2DSMC), but with the DSMC passes of consecutive steps fused
  * as in hyb_hybrid_step (hyb_set_fuse, hyb_set_collide_block; the same results). host_acc
  * holds nsteps x n_cells x 20 doubles (step k's sums at k n_cells 20), host_status nsteps
- * words. With page-locked host buffers the call is enqueued as one CUDA graph (captured at
- * the first call with the same steps, lists, buffers and state halves; the context keeps the
- * two latest), with pageable ones as direct launches, on the context's stream; either way it
- * completes as one entry of the ring that hyb_host_wait counts. The staging and errors are
- * those of hyb_hybrid_step_host; nsteps < 1 is HYB_EINVAL. */
+ * words. With page-locked host buffers each step's transfers are two kernels (the lists read
+ * from host memory, the sums and status written to it) and the call is enqueued as one CUDA
+ * graph (captured at the first call with the same steps, lists, buffers and state halves; the
+ * context keeps the two latest); pageable buffers take copies and direct launches. Either way
+ * the call completes as one entry of the ring that hyb_host_wait counts. The staging and
+ * errors are those of hyb_hybrid_step_host; nsteps < 1 is HYB_EINVAL. */
 hyb_status hyb_hybrid_steps_host(hyb_ctx* ctx, int32_t nsteps, const int32_t* host_nodes, int32_t n_nodes,
                                  const int32_t* host_cells, int32_t n_cells, double* host_acc,
                                  uint32_t* host_status);

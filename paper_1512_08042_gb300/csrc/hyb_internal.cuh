@@ -520,6 +520,13 @@ cudaError_t launch_map_l2d_noalloc(Ctx& c, const int32_t* cells, int32_t n);
 // count exceeds the bin, kept) and their particles moved on into half p.
 cudaError_t launch_map_l2d_move(Ctx& c, const int32_t* cells, int32_t n, int p);
 cudaError_t launch_gather_acc(Ctx& c, const int32_t* cells, int32_t n, double* out);
+// Host-buffer steps with page-locked buffers: the lists copied in by a kernel that reads host
+// memory, the listed cells' sums and the status word written to host memory by one kernel
+// (device-addressable pointers of the host buffers).
+cudaError_t launch_lists_in(Ctx& c, const int32_t* hn, int32_t nn, const int32_t* hc, int32_t nc,
+                            int32_t* dn, int32_t* dc);
+cudaError_t launch_results_out(Ctx& c, const int32_t* cells, int32_t n, double* out,
+                               uint32_t* status_out);
 cudaError_t launch_map_d2l_adjoint(Ctx& c, const int32_t* nodes, int32_t n, void* lam,
                                    double* grad_acc);
 cudaError_t launch_debug_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out, int64_t n,

@@ -900,6 +900,48 @@ cudaError_t launch_gather_acc(Ctx& c, const int32_t* cells, int32_t n, double* o
     return cudaGetLastError();
 }
 
+namespace {
+// The coupling lists read from page-locked host memory (device-addressable) into the
+// device staging: one thread per entry.
+__global__ void k_lists_in(const int32_t* __restrict__ hn, int32_t nn, const int32_t* __restrict__ hc,
+                           int32_t nc, int32_t* __restrict__ dn, int32_t* __restrict__ dc) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < nn)
+        dn[i] = hn[i];
+    else if (i < (int64_t)nn + nc)
+        dc[i - nn] = hc[i - nn];
+}
+
+// The listed cells' moment sums (as k_gather_acc) and the status word, written straight to
+// page-locked host memory.
+__global__ void k_results_out(const double* __restrict__ acc, const int32_t* __restrict__ cells,
+                              int32_t n, int64_t ncells, const uint32_t* __restrict__ status,
+                              double* __restrict__ out, uint32_t* __restrict__ status_out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i == 0) *status_out = *status;
+    if (i >= (int64_t)n * kMoments) return;
+    const int32_t c = cells[i / kMoments];
+    out[i] = (c >= 0 && (int64_t)c < ncells) ? acc[(int64_t)c * kMoments + i % kMoments] : 0.0;
+}
+}  // namespace
+
+cudaError_t launch_lists_in(Ctx& c, const int32_t* hn, int32_t nn, const int32_t* hc, int32_t nc,
+                            int32_t* dn, int32_t* dc) {
+    const int64_t total = (int64_t)nn + nc;
+    if (total == 0) return cudaSuccess;
+    k_lists_in<<<(unsigned)((total + 255) / 256), 256, 0, c.stream>>>(hn, nn, hc, nc, dn, dc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_results_out(Ctx& c, const int32_t* cells, int32_t n, double* out,
+                               uint32_t* status_out) {
+    const int64_t total = (int64_t)n * kMoments;
+    const unsigned grid = total > 0 ? (unsigned)((total + 255) / 256) : 1u;
+    k_results_out<<<grid, 256, 0, c.stream>>>(c.st.acc, cells, n, c.d.ncells, c.st.ctrl + CTRL_STATUS,
+                                              out, status_out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_map_l2d_move(Ctx& c, const int32_t* cells, int32_t n, int p) {
     if (c.p.lattice == 39)
         return c.p.real_bytes == 4 ? l2d_move_impl<float, D3Q39>(c, cells, n, p)

@@ -855,62 +855,23 @@ hyb_status hyb_debug_philox(const uint32_t* dev_ctr, uint64_t seed, uint32_t* de
 
 const char* hyb_last_error(const hyb_ctx* h) { return h ? h->c.err.c_str() : "null context"; }
 
+// The device address of page-locked host memory (cudaMallocHost, cudaHostRegister), false for
+// pageable memory.
+static bool device_view(const void* p, void** dev) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type != cudaMemoryTypeHost || a.devicePointer == nullptr) return false;
+    *dev = a.devicePointer;
+    return true;
+}
+
 hyb_status hyb_hybrid_step_host(hyb_ctx* h, const int32_t* host_nodes, int32_t n_nodes,
                                 const int32_t* host_cells, int32_t n_cells, double* host_acc,
                                 uint32_t* host_status) {
-    if (!h || n_nodes < 0 || n_cells < 0 || !host_status) return HYB_EINVAL;
-    Ctx& c = h->c;
-    if ((n_nodes > 0 && !host_nodes) || (n_cells > 0 && (!host_cells || !host_acc)) ||
-        n_nodes > c.d.nnodes || n_cells > c.d.ncells)
-        return HYB_EINVAL;
-    if (c.stream == nullptr) return fail(c, HYB_ESTATE, "host steps need a non-default stream");
-    // staging: nodes, cells, gathered sums, each 256-byte aligned
-    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-    const size_t off_c = up(4 * (size_t)n_nodes), off_a = off_c + up(4 * (size_t)n_cells);
-    const size_t need = off_a + up(8 * (size_t)kMoments * n_cells) + 256;
-    if (need > c.io_bytes) {
-        hyb_status s = check(c, cudaStreamSynchronize(c.stream), "synchronize");
-        if (s != HYB_OK) return s;
-        if (c.io_dev) cudaFree(c.io_dev);
-        c.io_dev = nullptr;
-        c.io_bytes = 0;
-        s = check(c, cudaMalloc((void**)&c.io_dev, need), "host-step staging");
-        if (s != HYB_OK) return s;
-        c.io_bytes = need;
-    }
-    for (int i = 0; i < 4; ++i)
-        if (!c.io_ev[i]) {
-            hyb_status s = check(c, cudaEventCreateWithFlags(&c.io_ev[i], cudaEventDisableTiming),
-                                 "event create");
-            if (s != HYB_OK) return s;
-        }
-    // a free slot in the ring of completion events
-    if (c.io_issued - c.io_done >= 4) {
-        hyb_status s = hyb_host_wait(h, 3);
-        if (s != HYB_OK) return s;
-    }
-    int32_t* dn = (int32_t*)c.io_dev;
-    int32_t* dc = (int32_t*)(c.io_dev + off_c);
-    double* da = (double*)(c.io_dev + off_a);
-    hyb_status s = HYB_OK;
-    if (n_nodes > 0)
-        s = check(c, cudaMemcpyAsync(dn, host_nodes, 4 * (size_t)n_nodes, cudaMemcpyHostToDevice, c.stream),
-                  "copy nodes in");
-    if (s == HYB_OK && n_cells > 0)
-        s = check(c, cudaMemcpyAsync(dc, host_cells, 4 * (size_t)n_cells, cudaMemcpyHostToDevice, c.stream),
-                  "copy cells in");
-    if (s == HYB_OK) s = hyb_hybrid_step(h, dn, n_nodes, dc, n_cells, 1, 1);
-    if (s == HYB_OK && n_cells > 0) s = check(c, launch_gather_acc(c, dc, n_cells, da), "gather launch");
-    if (s == HYB_OK && n_cells > 0)
-        s = check(c, cudaMemcpyAsync(host_acc, da, 8 * (size_t)kMoments * n_cells, cudaMemcpyDeviceToHost,
-                                     c.stream),
-                  "copy moments out");
-    if (s == HYB_OK)
-        s = check(c, cudaMemcpyAsync(host_status, c.st.ctrl + CTRL_STATUS, 4, cudaMemcpyDeviceToHost, c.stream),
-                  "copy status out");
-    if (s == HYB_OK) s = check(c, cudaEventRecord(c.io_ev[c.io_issued % 4], c.stream), "event record");
-    if (s == HYB_OK) c.io_issued += 1;
-    return s;
+    return hyb_hybrid_steps_host(h, 1, host_nodes, n_nodes, host_cells, n_cells, host_acc, host_status);
 }
 
 hyb_status hyb_hybrid_steps_host(hyb_ctx* h, int32_t nsteps, const int32_t* host_nodes, int32_t n_nodes,
@@ -950,8 +911,20 @@ hyb_status hyb_hybrid_steps_host(hyb_ctx* h, int32_t nsteps, const int32_t* host
     int32_t* dn = (int32_t*)c.io_dev;
     int32_t* dc = (int32_t*)(c.io_dev + off_c);
     double* da = (double*)(c.io_dev + off_a);
+    // Page-locked host buffers are addressable from the device: a kernel reads the lists from
+    // them and another writes the sums and the status word into them, so a step's transfers
+    // are two kernel launches (and the call one CUDA graph). Pageable buffers take copies.
+    void *vn = nullptr, *vc = nullptr, *va = nullptr, *vs = nullptr;
+    const bool mapped = (n_nodes == 0 || device_view(host_nodes, &vn)) &&
+                        (n_cells == 0 || (device_view(host_cells, &vc) && device_view(host_acc, &va))) &&
+                        device_view(host_status, &vs);
+    const int32_t* mn = (const int32_t*)vn;
+    const int32_t* mc = (const int32_t*)vc;
+    double* ma = (double*)va;
+    uint32_t* ms = (uint32_t*)vs;
     // every step copies the lists in before its first kernel and its strip sums and status out
     auto copy_in = [&](int) -> hyb_status {
+        if (mapped) return check(c, launch_lists_in(c, mn, n_nodes, mc, n_cells, dn, dc), "lists-in launch");
         hyb_status s = HYB_OK;
         if (n_nodes > 0)
             s = check(c, cudaMemcpyAsync(dn, host_nodes, 4 * (size_t)n_nodes, cudaMemcpyHostToDevice, c.stream),
@@ -962,6 +935,10 @@ hyb_status hyb_hybrid_steps_host(hyb_ctx* h, int32_t nsteps, const int32_t* host
         return s;
     };
     auto copy_out = [&](int k) -> hyb_status {
+        if (mapped)
+            return check(c, launch_results_out(c, dc, n_cells, ma ? ma + (size_t)k * kMoments * n_cells : nullptr,
+                                               ms + k),
+                         "results-out launch");
         hyb_status s = HYB_OK;
         if (n_cells > 0) s = check(c, launch_gather_acc(c, dc, n_cells, da), "gather launch");
         if (s == HYB_OK && n_cells > 0)
@@ -975,24 +952,16 @@ hyb_status hyb_hybrid_steps_host(hyb_ctx* h, int32_t nsteps, const int32_t* host
         return s;
     };
     StepHooks hk{copy_in, copy_out};
-    // a graph only copies page-locked host buffers asynchronously; pageable ones (and kernel
-    // timing) take direct launches
-    auto locked = [](const void* p) {
-        cudaPointerAttributes a;
-        if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-            cudaGetLastError();
-            return false;
-        }
-        return a.type == cudaMemoryTypeHost;
-    };
-    const bool graph = c.prof_kernel < 0 && (n_nodes == 0 || locked(host_nodes)) &&
-                       (n_cells == 0 || (locked(host_cells) && locked(host_acc))) && locked(host_status);
     hyb_status s = HYB_OK;
-    if (!graph) {
+    if (!mapped && nsteps == 1) {  // one step: the step's cached graph between the copies
+        s = copy_in(0);
+        if (s == HYB_OK) s = hyb_hybrid_step(h, dn, n_nodes, dc, n_cells, 1, 1);
+        if (s == HYB_OK) s = copy_out(0);
+    } else if (!mapped || c.prof_kernel >= 0) {  // pageable buffers or kernel timing: direct launches
         s = copy_in(0);
         if (s == HYB_OK) s = fused_hybrid_steps(c, dn, n_nodes, dc, n_cells, nsteps, &hk);
     } else {
-        // the call's graph (copies and kernels), captured once per steps, parities and buffers
+        // the call's graph (transfers and kernels), captured once per steps, parities and buffers
         Ctx::HostKey key;
         key.nsteps = nsteps;
         key.cur_p = c.cur_p;

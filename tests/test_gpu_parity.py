@@ -528,6 +528,28 @@ def test_multi_step_host_calls_equal_one_step_host_calls(fuse, pinned):
     assert a.counters() == b.counters()
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_steps_with_empty_lists(pinned):
+    # host-buffer steps with no coupling nodes or cells: only the status words come back, and
+    # the state equals that of uncoupled device steps
+    cfg = cfg_small(lb_ratio=2, ma=0.3)
+    a, b = B.Hybrid(cfg), B.Hybrid(cfg)
+    mk = (lambda x: x.pin_memory()) if pinned else (lambda x: x)
+    none = mk(torch.zeros(0, dtype=torch.int32))
+    acc = mk(torch.zeros(0, dtype=torch.float64))
+    st = mk(torch.full((2,), -1, dtype=torch.int32))
+    e = torch.zeros(0, dtype=torch.int32, device="cuda")
+    a.hybrid_step(e, e, nsteps=3, use_graph=False)
+    b.hybrid_step_host(none, none, acc, st[:1])
+    b.hybrid_step_host(none, none, acc, st, nsteps=2)
+    b.host_wait(0)
+    a.sync()
+    assert np.all(st.numpy() == 0)
+    for k in ("x", "y", "vx", "vy", "vz"):
+        assert np.array_equal(gpu_particles(a)[k], gpu_particles(b)[k]), k
+    assert np.array_equal(a.f().cpu().numpy(), b.f().cpu().numpy())
+
+
 # ---------------------------------------------------------------------------------------
 # The benchmarked FP32 coupled step, from the GPU's own state, sub-step by sub-step
 
