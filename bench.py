@@ -900,7 +900,7 @@ def main():
     h.profile(-1)
     pin_nodes = torch.from_numpy(nodes_np).pin_memory()
     pin_cells = torch.from_numpy(cells_np).pin_memory()
-    e2e_steps = max(10, args.steps // 2)
+    e2e_steps = max(20 * E2E_CALL, args.steps)  # at least 20 calls: the pipeline's fill is amortised
 
     def e2e_run(per_call, pipelined, seen):
         out_acc = [torch.empty(per_call, len(cells_np), 20, dtype=torch.float64).pin_memory() for _ in range(2)]
