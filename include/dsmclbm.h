@@ -497,20 +497,20 @@ hyb_status hyb_batch_hybrid_step(hyb_batch* b, const int32_t* dev_nodes, const i
                                  int32_t nsteps, int32_t use_graph);
 
 /* Thread-block size of one kernel class of the batch, by the ids of hyb_profile (0 move: 64,
- * 128 or 256 threads; 1 collide: 256; 2 LB step: 32, 64 or 128; 3 DSMC2LB: 64, 128 or 256;
- * 4 LB2DSMC: 256); HYB_EINVAL for others. The collide and LB2DSMC have one shape each, fixed
- * by their design (32 cells of 8 lanes per block; 8 warps per cell). get returns the size in
- * use, -1 for an invalid id. */
+ * 128 or 256 threads; 1 collide: 256 for blocks of 32 cells or 128 for 16 cells, 8 lanes per
+ * cell, as hyb_set_collide_block; 2 LB step: 32, 64 or 128; 3 DSMC2LB: 64, 128 or 256;
+ * 4 LB2DSMC: 256, fixed by its design of 8 warps per cell); HYB_EINVAL for others. The results
+ * do not depend on the shapes. get returns the size in use, -1 for an invalid id. */
 hyb_status hyb_batch_set_block(hyb_batch* b, int32_t kernel, int32_t threads);
 int32_t hyb_batch_get_block(const hyb_batch* b, int32_t kernel);
 
 /* The move and LB block sizes in one call (hyb_batch_set_block for kernels 0 and 2). */
 hyb_status hyb_batch_set_blocks(hyb_batch* b, int32_t move_block, int32_t lbm_block);
 
-/* Autotuner: for each kernel class with more than one shape (move, LB step, DSMC2LB), one
- * after another, times replayed hybrid steps of the batch at each of its block sizes and keeps
- * the fastest; returns the move and LB sizes (hyb_batch_get_block gives all). The steps it
- * times advance the batch (7 hybrid steps per shape tried, 63 in all). */
+/* Autotuner: for each kernel class with more than one shape (move, collide, LB step,
+ * DSMC2LB), one after another, times replayed hybrid steps of the batch at each of its block
+ * sizes and keeps the fastest; returns the move and LB sizes (hyb_batch_get_block gives all).
+ * The steps it times advance the batch (7 hybrid steps per shape tried, 77 in all). */
 hyb_status hyb_batch_tune(hyb_batch* b, const int32_t* dev_nodes, const int64_t* node_pre,
                           const int32_t* dev_cells, const int64_t* cell_pre, int32_t* move_block,
                           int32_t* lbm_block);

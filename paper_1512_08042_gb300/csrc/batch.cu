@@ -23,7 +23,8 @@ struct hyb_batch {
     // table region
     char* tab = nullptr;
     uint64_t off_dsmc[2] = {}, off_lbm[2] = {}, off_d2l[2][2] = {}, off_l2d[2][2] = {};
-    uint64_t off_pre_cells = 0, off_pre_blocks = 0, off_pre_nodes = 0, off_pre_d2l = 0, off_pre_l2d = 0;
+    uint64_t off_pre_cells = 0, off_pre_blocks = 0, off_pre_blocks4 = 0, off_pre_nodes = 0, off_pre_d2l = 0,
+             off_pre_l2d = 0;
     // coupling lists of the tables and graphs
     const int32_t* nodes = nullptr;
     const int32_t* cells = nullptr;
@@ -56,8 +57,8 @@ uint64_t table_layout(int n, int real_bytes, hyb_batch* b) {
             md[p][f] = take(n * ms);
             ml[p][f] = take(n * ms);
         }
-    const uint64_t pc = take((n + 1) * 8), pb = take((n + 1) * 8), pn = take((n + 1) * 8),
-                   pd = take((n + 1) * 8), pl = take((n + 1) * 8);
+    const uint64_t pc = take((n + 1) * 8), pb = take((n + 1) * 8), pb4 = take((n + 1) * 8),
+                   pn = take((n + 1) * 8), pd = take((n + 1) * 8), pl = take((n + 1) * 8);
     if (b) {
         b->off_dsmc[0] = d0;
         b->off_dsmc[1] = d1;
@@ -70,6 +71,7 @@ uint64_t table_layout(int n, int real_bytes, hyb_batch* b) {
             }
         b->off_pre_cells = pc;
         b->off_pre_blocks = pb;
+        b->off_pre_blocks4 = pb4;
         b->off_pre_nodes = pn;
         b->off_pre_d2l = pd;
         b->off_pre_l2d = pl;
@@ -235,19 +237,21 @@ hyb_status hyb_batch_init(const hyb_params* p, int32_t n, void* arena, uint64_t 
     b->tab = b->arena + off[n];
     table_layout(n, d.real_bytes, b);
     // prefix sums of the units and the DSMC and LB argument tables of both parities
-    std::vector<int64_t> pc(n + 1, 0), pb(n + 1, 0), pn(n + 1, 0);
-    constexpr int kCellsPerBlock = 32;
+    std::vector<int64_t> pc(n + 1, 0), pb(n + 1, 0), pb4(n + 1, 0), pn(n + 1, 0);
     for (int r = 0; r < n; ++r) {
         const Ctx& c = b->reps[r]->c;
         pc[r + 1] = pc[r] + c.d.ncells;
-        pb[r + 1] = pb[r] + (c.d.ncells + kCellsPerBlock - 1) / kCellsPerBlock;
+        pb[r + 1] = pb[r] + (c.d.ncells + 31) / 32;  // collide blocks of 32 cells
+        pb4[r + 1] = pb4[r] + (c.d.ncells + 15) / 16;  // and of 16
         pn[r + 1] = pn[r] + c.d.nnodes;
-        const uint32_t pool = hyb::collide_pool(c);
+        const uint32_t pool = hyb::collide_pool(c, 8), pool4 = hyb::collide_pool(c, 4);
         if (pool > d.pool) d.pool = pool;
+        if (pool4 > d.pool4) d.pool4 = pool4;
         if ((uint32_t)c.d.bin > d.maxbin) d.maxbin = (uint32_t)c.d.bin;
     }
     d.tot_cells = pc[n];
     d.tot_blocks = pb[n];
+    d.tot_blocks4 = pb4[n];
     d.tot_nodes = pn[n];
     const uint64_t ds = hyb::dsmc_args_bytes(d.real_bytes), ls = hyb::lbm_args_bytes(d.real_bytes);
     std::vector<char> host(n * (ds > ls ? ds : ls));
@@ -263,6 +267,7 @@ hyb_status hyb_batch_init(const hyb_params* p, int32_t n, void* arena, uint64_t 
     }
     if (s == HYB_OK) s = bcheck(b, cudaMemcpy(b->tab + b->off_pre_cells, pc.data(), (n + 1) * 8, cudaMemcpyHostToDevice), "upload offsets");
     if (s == HYB_OK) s = bcheck(b, cudaMemcpy(b->tab + b->off_pre_blocks, pb.data(), (n + 1) * 8, cudaMemcpyHostToDevice), "upload offsets");
+    if (s == HYB_OK) s = bcheck(b, cudaMemcpy(b->tab + b->off_pre_blocks4, pb4.data(), (n + 1) * 8, cudaMemcpyHostToDevice), "upload offsets");
     if (s == HYB_OK) s = bcheck(b, cudaMemcpy(b->tab + b->off_pre_nodes, pn.data(), (n + 1) * 8, cudaMemcpyHostToDevice), "upload offsets");
     if (s != HYB_OK) {
         hyb_batch_destroy(b);
@@ -278,6 +283,7 @@ hyb_status hyb_batch_init(const hyb_params* p, int32_t n, void* arena, uint64_t 
     }
     d.pre_cells = (const int64_t*)(b->tab + b->off_pre_cells);
     d.pre_blocks = (const int64_t*)(b->tab + b->off_pre_blocks);
+    d.pre_blocks4 = (const int64_t*)(b->tab + b->off_pre_blocks4);
     d.pre_nodes = (const int64_t*)(b->tab + b->off_pre_nodes);
     d.pre_d2l = (const int64_t*)(b->tab + b->off_pre_d2l);
     d.pre_l2d = (const int64_t*)(b->tab + b->off_pre_l2d);
@@ -354,13 +360,14 @@ hyb_status hyb_batch_hybrid_step(hyb_batch* b, const int32_t* dev_nodes, const i
 }
 
 namespace {
-// Block sizes each kernel class of the batch may take (0 ends a list): the collide and LB2DSMC
-// have one, fixed by their design (32 cells of 8 lanes per block; 8 warps per cell).
-const int kShapes[5][4] = {{64, 128, 256, 0}, {256, 0, 0, 0}, {32, 64, 128, 0}, {64, 128, 256, 0},
+// Block sizes each kernel class of the batch may take (0 ends a list): the collide 32 or 16
+// cells of 8 lanes per block; LB2DSMC one, fixed by its design (8 warps per cell).
+const int kShapes[5][4] = {{64, 128, 256, 0}, {256, 128, 0, 0}, {32, 64, 128, 0}, {64, 128, 256, 0},
                            {256, 0, 0, 0}};
 int* block_of(hyb_batch* b, int kernel) {
     switch (kernel) {
         case hyb::K_MOVE: return &b->dev.move_block;
+        case hyb::K_COLLIDE: return &b->dev.collide_block;
         case hyb::K_LBM: return &b->dev.lbm_block;
         case hyb::K_D2L: return &b->dev.d2l_block;
         default: return nullptr;
@@ -421,10 +428,11 @@ hyb_status hyb_batch_tune(hyb_batch* b, const int32_t* dev_nodes, const int64_t*
         *ms = best;
         return HYB_OK;
     };
-    // one kernel class at a time, the others at their current shapes: move, LB, DSMC2LB
+    // one kernel class at a time, the others at their current shapes: move, collide, LB,
+    // DSMC2LB
     hyb_status s = HYB_OK;
-    const int order[3] = {hyb::K_MOVE, hyb::K_LBM, hyb::K_D2L};
-    for (int ki = 0; ki < 3 && s == HYB_OK; ++ki) {
+    const int order[4] = {hyb::K_MOVE, hyb::K_COLLIDE, hyb::K_LBM, hyb::K_D2L};
+    for (int ki = 0; ki < 4 && s == HYB_OK; ++ki) {
         const int k = order[ki];
         int best_t = hyb_batch_get_block(b, k);
         float best = 1e30f;

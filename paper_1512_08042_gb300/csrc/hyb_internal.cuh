@@ -546,14 +546,17 @@ struct BatchDev {
     const void* d2l[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // MapArgs, [particle][population]
     const void* l2d[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     const int64_t* pre_cells = nullptr;
-    const int64_t* pre_blocks = nullptr;
+    const int64_t* pre_blocks = nullptr;   // collide blocks of 32 cells
+    const int64_t* pre_blocks4 = nullptr;  // collide blocks of 16 cells
     const int64_t* pre_nodes = nullptr;
     const int64_t* pre_d2l = nullptr;
     const int64_t* pre_l2d = nullptr;
-    int64_t tot_cells = 0, tot_blocks = 0, tot_nodes = 0, tot_d2l = 0, tot_l2d = 0;
-    uint32_t pool = 0;  // collide shared-memory pool: the largest over the replicas
+    int64_t tot_cells = 0, tot_blocks = 0, tot_blocks4 = 0, tot_nodes = 0, tot_d2l = 0, tot_l2d = 0;
+    // collide shared-memory pools of 32- and 16-cell blocks: the largest over the replicas
+    uint32_t pool = 0, pool4 = 0;
     uint32_t maxbin = 0;  // the largest bin over the replicas (the collide's key bitmaps)
-    int move_block = 256, lbm_block = 128, d2l_block = 128;
+    // threads per block of each tuned class (the collide: 256 for 32 cells, 128 for 16)
+    int move_block = 256, lbm_block = 128, d2l_block = 128, collide_block = 256;
 };
 size_t dsmc_args_bytes(int real_bytes);
 void dsmc_args_fill(Ctx& c, int cur_p, void* out);

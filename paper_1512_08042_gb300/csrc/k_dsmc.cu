@@ -1148,15 +1148,23 @@ template <typename Real>
 cudaError_t batch_collide_impl(BatchDev& b, int cur_p) {
     Launch<DsmcArgs<Real>> L{};
     L.tab = (const DsmcArgs<Real>*)b.dsmc[cur_p];
-    L.pre = b.pre_blocks;
     L.nrep = b.nrep;
-    L.total = b.tot_blocks;
-    const size_t smem = collide_smem<Real, false>(b.pool, b.maxbin);
-    cudaError_t e = cudaFuncSetAttribute(k_collide<Real, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    e = launch_pdl(k_collide<Real, true>, dim3((unsigned)b.tot_blocks), dim3(kCollideWarps * 32), smem,
-                   b.stream, L, b.pool);
+    cudaError_t e;
+    if (b.collide_block == 128) {  // blocks of 16 cells
+        L.pre = b.pre_blocks4;
+        L.total = b.tot_blocks4;
+        const size_t smem = collide_smem<Real, false, 4>(b.pool4, b.maxbin);
+        auto k = k_collide<Real, true, false, MODE_COLLIDE, 4>;
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) e = launch_pdl(k, dim3((unsigned)L.total), dim3(128), smem, b.stream, L, b.pool4);
+    } else {  // blocks of 32 cells
+        L.pre = b.pre_blocks;
+        L.total = b.tot_blocks;
+        const size_t smem = collide_smem<Real, false, 8>(b.pool, b.maxbin);
+        auto k = k_collide<Real, true, false, MODE_COLLIDE, 8>;
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) e = launch_pdl(k, dim3((unsigned)L.total), dim3(256), smem, b.stream, L, b.pool);
+    }
     if (e != cudaSuccess) return e;
     return launch_pdl(k_step_end<Real, true>, dim3((unsigned)((L.nrep + 127) / 128)), dim3(128), 0,
                       b.stream, L);

@@ -37,11 +37,14 @@ def _assert_same(h, g):
     assert h.counters() == g.counters()
 
 
-@pytest.mark.parametrize("use_graph", [False, True])
-def test_batch_replicas_equal_single_contexts(use_graph):
+@pytest.mark.parametrize("use_graph,collide", [(False, 256), (True, 256), (True, 128)])
+def test_batch_replicas_equal_single_contexts(use_graph, collide):
+    # (collide: the batch's collide in blocks of 32 or 16 cells; the single contexts keep theirs)
     cfgs = _cfgs()
     nodes, cells = _sites(cfgs)
     b = B.Batch(cfgs)
+    b.set_block("collide", collide)
+    assert b.blocks()["collide"] == collide
     singles = [B.Hybrid(c) for c in cfgs]
     b.hybrid_step(nodes, cells, nsteps=4, use_graph=use_graph)
     for h, n, c in zip(singles, nodes, cells):
@@ -61,11 +64,13 @@ def test_batch_tuner_picks_valid_shapes_and_keeps_results():
     assert mb in (64, 128, 256) and lb in (32, 64, 128)
     shapes = b.blocks()
     assert shapes["move"] == mb and shapes["lbm"] == lb and shapes["dsmc2lb"] in (64, 128, 256)
-    assert shapes["collide"] == 256 and shapes["lb2dsmc"] == 256
+    assert shapes["collide"] in (256, 128) and shapes["lb2dsmc"] == 256
     with pytest.raises(B.HybError):
-        b.set_block("collide", 128)  # one shape, fixed by the kernel's design
+        b.set_block("lb2dsmc", 128)  # one shape, fixed by the kernel's design
+    with pytest.raises(B.HybError):
+        b.set_block("collide", 64)
     b.hybrid_step(nodes, cells, nsteps=2)
-    steps = 63 + 2  # 7 steps per shape tried: 3 move, 3 LB, 3 DSMC2LB
+    steps = 77 + 2  # 7 steps per shape tried: 3 move, 2 collide, 3 LB, 3 DSMC2LB
     for g, cfg, n, c in zip(b.replicas, cfgs, nodes, cells):
         h = B.Hybrid(cfg)
         h.hybrid_step(torch.from_numpy(n).cuda(), torch.from_numpy(c).cuda(), nsteps=steps, use_graph=True)
