@@ -82,11 +82,11 @@ def kernel_algorithmic_bytes(name, cfg, d, n_particles, n_nodes_map, n_cells_map
 
 
 def method_bytes(cfg, d):
-    """Algorithmic bytes of the method per unit, as the survey's measurement table counts
-    them: per DSMC particle-update the particle state read and written once (2 x x, y(, z),
-    vx, vy, vz) plus 344 B of per-cell state (20 FP64 sums read and written, count and offset,
-    (sigma c)max, remainder and N-bar) amortised over ppc; per LB node-update the populations
-    read and written once, plus 8 B where tau (and g) are per-node fields."""
+    """Algorithmic bytes of the method per unit: per DSMC particle-update the particle state
+    read and written once (2 x x, y(, z), vx, vy, vz) plus 344 B of per-cell state (20 FP64
+    sums read and written, count and offset, (sigma c)max, remainder and N-bar) amortised over
+    ppc; per LB node-update the populations read and written once, plus 8 B where tau (and g)
+    are per-node fields."""
     rb = cfg["real_bytes"]
     pr = 6 if d["ncz"] >= 2 else 5
     dsmc = 2 * pr * rb + 344.0 / cfg["ppc"]
