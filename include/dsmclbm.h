@@ -383,8 +383,9 @@ hyb_status map_dsmc_to_lbm_adjoint(hyb_ctx* ctx, const int32_t* dev_nodes, int32
  * untouched until hyb_host_wait says the step is done. With page-locked host buffers
  * (cudaMallocHost, cudaHostRegister) the transfers are made by two kernels that read and
  * write the buffers through their device addresses, and the whole call is one CUDA graph
- * (as in hyb_hybrid_steps_host); pageable buffers work but take cudaMemcpyAsync copies, which
- * are then synchronous. The first call, and any call with longer lists, allocates
+ * (as in hyb_hybrid_steps_host); host_acc and host_status must then be writable by the device
+ * (not registered with cudaHostRegisterReadOnly). Pageable buffers work but take
+ * cudaMemcpyAsync copies, which are then synchronous. The first call, and any call with longer lists, allocates
  * the staging (4 n_nodes + 164 n_cells bytes, rounded up) on the device; hyb_destroy frees
  * it. host_acc may be NULL when n_cells is 0. Invalid sizes or pointers: HYB_EINVAL. */
 hyb_status hyb_hybrid_step_host(hyb_ctx* ctx, const int32_t* host_nodes, int32_t n_nodes,
