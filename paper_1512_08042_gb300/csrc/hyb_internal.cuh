@@ -609,13 +609,17 @@ struct Ctx {
     int32_t mkey[2][3] = {{-1, -1, -1}, {-1, -1, -1}};
     int mnext = 0;
     // graphs of multi-step host-buffer calls, keyed by steps, parities, lists and buffers
+    // (the host buffers by their host and device addresses: a buffer registered again at the
+    // same host address may get another device address)
     struct HostKey {
         int32_t nsteps = -1, cur_p = -1, cur_f = -1, nn = -1, nc = -1;
         const void *nodes = nullptr, *cells = nullptr, *acc = nullptr, *status = nullptr, *staging = nullptr;
+        const void* dev[4] = {nullptr, nullptr, nullptr, nullptr};
         bool operator==(const HostKey& o) const {
             return nsteps == o.nsteps && cur_p == o.cur_p && cur_f == o.cur_f && nn == o.nn && nc == o.nc &&
                    nodes == o.nodes && cells == o.cells && acc == o.acc && status == o.status &&
-                   staging == o.staging;
+                   staging == o.staging && dev[0] == o.dev[0] && dev[1] == o.dev[1] && dev[2] == o.dev[2] &&
+                   dev[3] == o.dev[3];
         }
     };
     cudaGraphExec_t hgraph[2] = {nullptr, nullptr};

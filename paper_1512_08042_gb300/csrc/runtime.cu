@@ -973,6 +973,10 @@ hyb_status hyb_hybrid_steps_host(hyb_ctx* h, int32_t nsteps, const int32_t* host
         key.acc = host_acc;
         key.status = host_status;
         key.staging = c.io_dev;
+        key.dev[0] = mn;
+        key.dev[1] = mc;
+        key.dev[2] = ma;
+        key.dev[3] = ms;
         int slot = -1;
         for (int i = 0; i < 2; ++i)
             if (c.hgraph[i] && c.hkey[i] == key) slot = i;
