@@ -528,6 +528,37 @@ def test_multi_step_host_calls_equal_one_step_host_calls(fuse, pinned):
     assert a.counters() == b.counters()
 
 
+def test_host_step_graphs_follow_the_fuse_mode_and_3d():
+    # a captured host call is replayed only while the step it captured still applies: after
+    # hyb_set_fuse changes the pass structure the call is captured again, and the results stay
+    # those of one-step host calls; the same on a 3D channel (ncz >= 2)
+    for cfg in (cfg_small(lb_ratio=2, ma=0.3), cfg_small(ncz=3, lb_ratio=2, ma=0.3, kn=0.3)):
+        nodes, cells = W.coupling_sites(cfg, strip_cells=2)
+        a, b = B.Hybrid(cfg), B.Hybrid(cfg)
+        hn, hc = torch.from_numpy(nodes).pin_memory(), torch.from_numpy(cells).pin_memory()
+        n = 8
+        one = np.zeros((n, len(cells), 20))
+        out = torch.zeros(1, len(cells), 20, dtype=torch.float64).pin_memory()
+        st = torch.zeros(1, dtype=torch.int32).pin_memory()
+        for k in range(n):
+            a.hybrid_step_host(hn, hc, out, st)
+            a.host_wait(0)
+            one[k] = out.numpy()[0]
+        many = torch.zeros(2, len(cells), 20, dtype=torch.float64).pin_memory()
+        sts = torch.zeros(2, dtype=torch.int32).pin_memory()
+        got = []
+        for call, mode in enumerate(("always", "always", "never", "always")):
+            b.set_fuse(mode)
+            b.hybrid_step_host(hn, hc, many, sts, nsteps=2)
+            b.host_wait(0)
+            got.append(many.numpy().copy())
+            assert np.all(sts.numpy() == 0)
+        assert np.array_equal(np.concatenate(got), one)
+        for k in ("x", "y", "vx", "vy", "vz"):
+            assert np.array_equal(gpu_particles(a)[k], gpu_particles(b)[k]), k
+        assert np.array_equal(a.f().cpu().numpy(), b.f().cpu().numpy())
+
+
 @pytest.mark.parametrize("pinned", [True, False])
 def test_host_steps_with_empty_lists(pinned):
     # host-buffer steps with no coupling nodes or cells: only the status words come back, and
