@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define HYB_ABI_VERSION 11u
+#define HYB_ABI_VERSION 12u
 
 typedef enum {
     HYB_OK = 0,
@@ -343,6 +343,25 @@ hyb_status lbm_interface_loss(hyb_ctx* ctx, const void* f, const int32_t* dev_no
 hyb_status lbm_adjoint_step(hyb_ctx* ctx, const void* f, const void* lam_next, void* lam,
                             const void* g_node, const void* tau_node, void* grad_g,
                             void* grad_tau, void* wall);
+
+/* nsteps LB steps in one call, as nsteps calls of lbm_step_nodes alternating between f_a
+ * (holding f_0 on entry) and f_b: f_T ends in f_a when nsteps is even, else in f_b. The
+ * states f_K, f_2K, ... before f_T (K = ckpt_every >= 1) are also copied to ckpt, one
+ * population array each in order (floor((nsteps - 1) / K) of them; ckpt may be NULL when
+ * there are none). HYB_EINVAL for nsteps < 0, ckpt_every < 1, f_a == f_b or a missing
+ * pointer. */
+hyb_status lbm_steps_nodes(hyb_ctx* ctx, void* f_a, void* f_b, const void* g_node, const void* tau_node,
+                           int32_t nsteps, int32_t ckpt_every, void* ckpt);
+
+/* The adjoint of n >= 1 LB steps from the state f_t0 (`state0`) in one call: the states
+ * f_t0+1 .. f_t0+n-1 are recomputed into `states` (n - 1 population arrays of caller scratch;
+ * NULL when n = 1), then n adjoint steps run from the last to the first, as n calls of
+ * lbm_adjoint_step alternating between lam_a (dL/df_t0+n on entry) and lam_b: dL/df_t0 ends
+ * in lam_a when n is even, else in lam_b. grad_g, grad_tau and wall as lbm_adjoint_step.
+ * HYB_EINVAL for n < 1, lam_a == lam_b, a missing pointer or lb_collision = 1. */
+hyb_status lbm_adjoint_segment(hyb_ctx* ctx, const void* state0, void* states, int32_t n, void* lam_a,
+                               void* lam_b, const void* g_node, const void* tau_node, void* grad_g,
+                               void* grad_tau, void* wall);
 
 /* One or more hybrid steps: dsmc_step(1), map_dsmc_to_lbm, lbm_step(1), map_lbm_to_dsmc.
  * n_nodes or n_cells may be 0 to skip a mapping. With nsteps >= 2 the DSMC passes are fused

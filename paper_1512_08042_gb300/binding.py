@@ -11,7 +11,7 @@ import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "libdsmclbm.so")
-ABI_VERSION = 11
+ABI_VERSION = 12
 
 HYB_OK, HYB_EINVAL, HYB_ENOMEM, HYB_ECUDA, HYB_ECAPACITY, HYB_ETIMEOUT, HYB_ESAMPLING, HYB_ESTATE = range(8)
 ST_CAPACITY, ST_BOUNCE_CAP, ST_SCATTER_CAP, ST_SAMPLING_CAP, ST_CELL_OVERFLOW, ST_BAD_INPUT = (
@@ -58,6 +58,7 @@ EXPORTS = ["hyb_derive", "hyb_layout_compute", "hyb_lattice", "hyb_status_string
            "dsmc_step", "dsmc_move", "dsmc_merge", "dsmc_collide", "lbm_halo_size", "lbm_halo_pack",
            "lbm_halo_unpack", "lbm_step", "sample_moments", "map_dsmc_to_lbm", "map_lbm_to_dsmc",
            "map_lbm_to_dsmc_noalloc", "map_dsmc_to_lbm_adjoint", "lbm_step_nodes", "lbm_interface_loss", "lbm_adjoint_step",
+           "lbm_steps_nodes", "lbm_adjoint_segment",
            "hyb_hybrid_step", "hyb_hybrid_step_host", "hyb_hybrid_steps_host", "hyb_host_wait", "hyb_batch_layout", "hyb_batch_init", "hyb_batch_replica",
            "hyb_batch_hybrid_step", "hyb_batch_set_blocks", "hyb_batch_set_block", "hyb_batch_get_block",
            "hyb_batch_tune",
@@ -114,6 +115,8 @@ def lib():
     L.lbm_step_nodes.argtypes = [_vp, _vp, _vp, _vp, _vp]
     L.lbm_interface_loss.argtypes = [_vp, _vp, _vp, _i32, _vp, _vp, _vp]
     L.lbm_adjoint_step.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+    L.lbm_steps_nodes.argtypes = [_vp, _vp, _vp, _vp, _vp, _i32, _i32, _vp]
+    L.lbm_adjoint_segment.argtypes = [_vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
     L.hyb_hybrid_step.argtypes = [_vp, _vp, _i32, _vp, _i32, _i32, _i32]
     L.hyb_hybrid_step_host.argtypes = [_vp, _vp, _i32, _vp, _i32, _vp, _vp]
     L.hyb_hybrid_steps_host.argtypes = [_vp, _i32, _vp, _i32, _vp, _i32, _vp, _vp]
@@ -383,6 +386,40 @@ class Hybrid:
                                       g.data_ptr(), tau.data_ptr(), grad_g.data_ptr(),
                                       grad_tau.data_ptr(), wall.data_ptr()), self.ctx)
 
+
+    def lbm_steps_nodes(self, f_a, f_b, g, tau, nsteps, ckpt_every=1, ckpt=None):
+        """nsteps LB steps alternating between f_a (f_0 on entry) and f_b in one call
+        (lbm_steps_nodes); the states f_K, f_2K, ... before the last go to ckpt (a tensor of
+        (nsteps - 1) // ckpt_every population arrays, or None when there are none). Returns the
+        tensor that holds f_T."""
+        self._check_pop(f_a, f_b)
+        self._check_node(g, tau)
+        nck = (nsteps - 1) // ckpt_every if nsteps > 0 else 0
+        if nck > 0 and (ckpt is None or ckpt.dtype != self.real or not ckpt.is_contiguous() or
+                        ckpt.numel() < nck * f_a.numel()):
+            raise ValueError("ckpt must hold %d contiguous population arrays" % nck)
+        self._inputs(f_a, f_b, g, tau, *([ckpt] if ckpt is not None else []))
+        _check(lib().lbm_steps_nodes(self.ctx, f_a.data_ptr(), f_b.data_ptr(), g.data_ptr(), tau.data_ptr(),
+                                     int(nsteps), int(ckpt_every),
+                                     ckpt.data_ptr() if ckpt is not None else None), self.ctx)
+        return f_a if nsteps % 2 == 0 else f_b
+
+    def lbm_adjoint_segment(self, state0, states, n, lam_a, lam_b, g, tau, grad_g, grad_tau, wall):
+        """The adjoint of n LB steps from state0 in one call (lbm_adjoint_segment): states is
+        scratch for n - 1 population arrays (None for n = 1), lam_a holds dL/df at the end of
+        the segment on entry. Returns the tensor that holds dL/df at its start."""
+        self._check_pop(state0, lam_a, lam_b)
+        self._check_node(g, tau, grad_g, grad_tau)
+        if n > 1 and (states is None or states.dtype != self.real or not states.is_contiguous() or
+                      states.numel() < (n - 1) * state0.numel()):
+            raise ValueError("states must hold %d contiguous population arrays" % (n - 1))
+        self._inputs(state0, lam_a, lam_b, g, tau, grad_g, grad_tau, wall,
+                     *([states] if states is not None else []))
+        _check(lib().lbm_adjoint_segment(self.ctx, state0.data_ptr(),
+                                         states.data_ptr() if states is not None else None, int(n),
+                                         lam_a.data_ptr(), lam_b.data_ptr(), g.data_ptr(), tau.data_ptr(),
+                                         grad_g.data_ptr(), grad_tau.data_ptr(), wall.data_ptr()), self.ctx)
+        return lam_a if n % 2 == 0 else lam_b
     def hybrid_step(self, nodes=None, cells=None, nsteps=1, use_graph=True, order_inputs=True):
         """`order_inputs=False` skips the stream ordering of `nodes`/`cells` (for callers
         that keep them resident and already ordered, e.g. a timed loop)."""
@@ -909,16 +946,16 @@ def _make_coupled_loss():
 
 
 def _lb_forward(h, g, tau, f0, nsteps, ckpt_every):
-    """f_T and the checkpoints f_0, f_K, f_2K, ... (K = ckpt_every)."""
+    """f_T and the checkpoints f_0, f_K, f_2K, ... (K = ckpt_every), the steps in one library
+    call."""
     a = f0.detach().clone()
     b = h.torch.empty_like(a)
+    nck = (nsteps - 1) // ckpt_every if nsteps > 0 else 0
+    ck = h.torch.empty((max(nck, 1),) + tuple(a.shape), dtype=a.dtype, device=a.device)
     ckpts = [a.clone()]
-    for t in range(nsteps):
-        h.lbm_step_nodes(a, b, g, tau)
-        a, b = b, a
-        if (t + 1) % ckpt_every == 0 and t + 1 < nsteps:
-            ckpts.append(a.clone())
-    return a, ckpts
+    fT = h.lbm_steps_nodes(a, b, g, tau, nsteps, ckpt_every, ck if nck else None)
+    ckpts += [ck[i] for i in range(nck)]
+    return fT, ckpts
 
 
 def _loss_forward(h, g, tau, f0, nodes, targets, nsteps, ckpt_every):
@@ -943,15 +980,13 @@ def _loss_adjoint(h, g, tau, lam_T, ckpts, T, K):
         wall = torch.zeros(h.wall_scratch_size(), dtype=g.dtype, device=g.device)
         lam_next = lam_T.clone()
         lam = torch.empty_like(lam_next)
+        scratch = torch.empty((max(K - 1, 1),) + tuple(lam_next.shape), dtype=lam_next.dtype,
+                              device=lam_next.device)
         for s in reversed(range(len(ckpts))):
             t0, t1 = s * K, min(T, (s + 1) * K)
-            states = [ckpts[s]]
-            for _ in range(t0, t1 - 1):
-                nxt = torch.empty_like(states[-1])
-                h.lbm_step_nodes(states[-1], nxt, g, tau)
-                states.append(nxt)
-            for t in reversed(range(t0, t1)):
-                h.lbm_adjoint_step(states[t - t0], lam_next, lam, g, tau, grad_g, grad_tau, wall)
+            out = h.lbm_adjoint_segment(ckpts[s], scratch if t1 - t0 > 1 else None, t1 - t0, lam_next,
+                                        lam, g, tau, grad_g, grad_tau, wall)
+            if out is not lam_next:
                 lam_next, lam = lam, lam_next
     return grad_g, grad_tau, lam_next
 

@@ -6,6 +6,7 @@
 #include <functional>
 #include <new>
 #include <vector>
+#include <utility>
 
 #include "hyb_internal.cuh"
 
@@ -609,6 +610,58 @@ hyb_status lbm_adjoint_step(hyb_ctx* h, const void* f, const void* lam_next, voi
     return check(h->c, launch_lbm_adjoint_step(h->c, f, lam_next, lam, g_node, tau_node, grad_g,
                                                grad_tau, wall),
                  "lbm_adjoint_step launch");
+}
+
+hyb_status lbm_steps_nodes(hyb_ctx* h, void* f_a, void* f_b, const void* g_node, const void* tau_node,
+                           int32_t nsteps, int32_t ckpt_every, void* ckpt) {
+    if (!h || !f_a || !f_b || f_a == f_b || !g_node || !tau_node || nsteps < 0 || ckpt_every < 1)
+        return HYB_EINVAL;
+    const int32_t nck = nsteps > 0 ? (nsteps - 1) / ckpt_every : 0;
+    if (nck > 0 && !ckpt) return HYB_EINVAL;
+    Ctx& c = h->c;
+    const size_t bytes = (size_t)c.d.q * (size_t)c.d.nnodes * (size_t)c.p.real_bytes;
+    void* src = f_a;
+    void* dst = f_b;
+    for (int32_t t = 0; t < nsteps; ++t) {
+        hyb_status s = check(c, launch_lbm_step_nodes(c, src, dst, g_node, tau_node), "lbm_steps_nodes launch");
+        if (s != HYB_OK) return s;
+        std::swap(src, dst);
+        if ((t + 1) % ckpt_every == 0 && t + 1 < nsteps) {
+            char* out = (char*)ckpt + (size_t)((t + 1) / ckpt_every - 1) * bytes;
+            s = check(c, cudaMemcpyAsync(out, src, bytes, cudaMemcpyDeviceToDevice, c.stream), "checkpoint copy");
+            if (s != HYB_OK) return s;
+        }
+    }
+    return HYB_OK;
+}
+
+hyb_status lbm_adjoint_segment(hyb_ctx* h, const void* state0, void* states, int32_t n, void* lam_a,
+                               void* lam_b, const void* g_node, const void* tau_node, void* grad_g,
+                               void* grad_tau, void* wall) {
+    if (!h || !state0 || n < 1 || (n > 1 && !states) || !lam_a || !lam_b || lam_a == lam_b || !g_node ||
+        !tau_node || !grad_g || !grad_tau || !wall || h->c.p.lb_collision != 0)
+        return HYB_EINVAL;
+    Ctx& c = h->c;
+    const size_t bytes = (size_t)c.d.q * (size_t)c.d.nnodes * (size_t)c.p.real_bytes;
+    // f_t0 + k for k = 0 .. n - 1: the given state, then the recomputed ones
+    auto state = [&](int32_t k) -> const void* {
+        return k == 0 ? state0 : (const void*)((const char*)states + (size_t)(k - 1) * bytes);
+    };
+    for (int32_t k = 1; k < n; ++k) {
+        hyb_status s = check(c, launch_lbm_step_nodes(c, state(k - 1), (void*)state(k), g_node, tau_node),
+                             "lbm_adjoint_segment recompute");
+        if (s != HYB_OK) return s;
+    }
+    void* next = lam_a;
+    void* cur = lam_b;
+    for (int32_t k = n - 1; k >= 0; --k) {
+        hyb_status s = check(c, launch_lbm_adjoint_step(c, state(k), next, cur, g_node, tau_node, grad_g,
+                                                        grad_tau, wall),
+                             "lbm_adjoint_segment step");
+        if (s != HYB_OK) return s;
+        std::swap(next, cur);
+    }
+    return HYB_OK;
 }
 
 hyb_status map_dsmc_to_lbm_adjoint(hyb_ctx* h, const int32_t* dev_nodes, int32_t n, void* lam,

@@ -106,6 +106,9 @@ def test_invalid_parameters_are_rejected(lib):
     assert lib.hyb_host_wait(None, 0) == B.HYB_EINVAL
     assert lib.map_dsmc_to_lbm_adjoint(None, None, 1, None, None) == B.HYB_EINVAL
     assert lib.lbm_adjoint_step(None, None, None, None, None, None, None, None, None) == B.HYB_EINVAL
+    assert lib.lbm_steps_nodes(None, None, None, None, None, 4, 2, None) == B.HYB_EINVAL
+    assert lib.lbm_adjoint_segment(None, None, None, 2, None, None, None, None, None, None,
+                                   None) == B.HYB_EINVAL
 
 
 def test_batch_layout_places_replicas_and_tables(lib):

@@ -300,3 +300,42 @@ def test_dsmc2lb_adjoint_rejects_the_equilibrium_mapping():
     with pytest.raises(B.HybError) as ei:
         h.map_dsmc_to_lbm_adjoint(torch.tensor([0, 1], dtype=torch.int32, device="cuda"), lam, grad)
     assert ei.value.status == B.HYB_EINVAL
+
+
+@pytest.mark.parametrize("real_bytes", [8, 4])
+def test_one_call_forward_and_adjoint_segment_equal_the_step_calls(real_bytes):
+    # lbm_steps_nodes (7 steps, a checkpoint every 3) and lbm_adjoint_segment (4 and 1 steps)
+    # compute exactly what the same lbm_step_nodes and lbm_adjoint_step calls compute
+    cfg = cfg_lb(real_bytes=real_bytes)
+    h, f, g, tau, *_ = setup(cfg, seed=8)
+    T, K = 7, 3
+    a, b = f.clone(), torch.empty_like(f)
+    ck = torch.empty((2,) + tuple(f.shape), dtype=f.dtype, device=f.device)
+    fT = h.lbm_steps_nodes(a, b, g, tau, T, K, ck)
+    ref, states = f.clone(), [f.clone()]
+    for _ in range(T):
+        nxt = torch.empty_like(ref)
+        h.lbm_step_nodes(ref, nxt, g, tau)
+        ref = nxt
+        states.append(ref)
+    h.sync()
+    assert torch.equal(fT, ref)
+    assert torch.equal(ck[0], states[3]) and torch.equal(ck[1], states[6])
+    rng = np.random.default_rng(5)
+    lam_T = torch.from_numpy(rng.standard_normal(tuple(f.shape)).astype(
+        np.float32 if real_bytes == 4 else np.float64)).cuda()
+    wall = torch.zeros(h.wall_scratch_size(), dtype=f.dtype, device=f.device)
+    for n in (4, 1):
+        gg1, gt1 = torch.zeros_like(g), torch.zeros_like(tau)
+        la, lb = lam_T.clone(), torch.empty_like(lam_T)
+        scratch = torch.empty((3,) + tuple(f.shape), dtype=f.dtype, device=f.device)
+        out = h.lbm_adjoint_segment(states[2], scratch if n > 1 else None, n, la, lb, g, tau, gg1, gt1,
+                                    wall)
+        gg2, gt2 = torch.zeros_like(g), torch.zeros_like(tau)
+        nxt, cur = lam_T.clone(), torch.empty_like(lam_T)
+        for t in reversed(range(2, 2 + n)):
+            h.lbm_adjoint_step(states[t], nxt, cur, g, tau, gg2, gt2, wall)
+            nxt, cur = cur, nxt
+        h.sync()
+        assert torch.equal(out, nxt) and torch.equal(gg1, gg2) and torch.equal(gt1, gt2)
+        assert torch.count_nonzero(wall) == 0
