@@ -305,7 +305,9 @@ def test_dsmc2lb_adjoint_rejects_the_equilibrium_mapping():
 @pytest.mark.parametrize("real_bytes", [8, 4])
 def test_one_call_forward_and_adjoint_segment_equal_the_step_calls(real_bytes):
     # lbm_steps_nodes (7 steps, a checkpoint every 3) and lbm_adjoint_segment (4 and 1 steps)
-    # compute exactly what the same lbm_step_nodes and lbm_adjoint_step calls compute
+    # compute what the same lbm_step_nodes and lbm_adjoint_step calls compute: the forward bit
+    # for bit; the adjoint up to the order of the wall rows' atomic sums (the populations
+    # leaving through a wall take their row's sum, added by several nodes in any order)
     cfg = cfg_lb(real_bytes=real_bytes)
     h, f, g, tau, *_ = setup(cfg, seed=8)
     T, K = 7, 3
@@ -337,5 +339,7 @@ def test_one_call_forward_and_adjoint_segment_equal_the_step_calls(real_bytes):
             h.lbm_adjoint_step(states[t], nxt, cur, g, tau, gg2, gt2, wall)
             nxt, cur = cur, nxt
         h.sync()
-        assert torch.equal(out, nxt) and torch.equal(gg1, gg2) and torch.equal(gt1, gt2)
+        tol = 1e-12 if real_bytes == 8 else 1e-5
+        for u, v in ((out, nxt), (gg1, gg2), (gt1, gt2)):
+            assert float((u - v).abs().max()) <= tol * float(v.abs().max()), n
         assert torch.count_nonzero(wall) == 0
