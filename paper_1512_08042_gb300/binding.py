@@ -984,6 +984,8 @@ def _loss_adjoint(h, g, tau, lam_T, ckpts, T, K):
                               device=lam_next.device)
         for s in reversed(range(len(ckpts))):
             t0, t1 = s * K, min(T, (s + 1) * K)
+            if t1 <= t0:  # no steps (T = 0)
+                continue
             out = h.lbm_adjoint_segment(ckpts[s], scratch if t1 - t0 > 1 else None, t1 - t0, lam_next,
                                         lam, g, tau, grad_g, grad_tau, wall)
             if out is not lam_next:
