@@ -343,3 +343,20 @@ def test_one_call_forward_and_adjoint_segment_equal_the_step_calls(real_bytes):
         for u, v in ((out, nxt), (gg1, gg2), (gt1, gt2)):
             assert float((u - v).abs().max()) <= tol * float(v.abs().max()), n
         assert torch.count_nonzero(wall) == 0
+
+
+def test_gradient_of_zero_steps_is_the_loss_adjoint_at_f0():
+    # T = 0: the loss is taken at f0 itself, so dL/dg = dL/dtau = 0 and dL/df0 is the loss's own
+    # adjoint (lbm_interface_loss)
+    cfg = cfg_lb()
+    h, f, g, tau, *_ = setup(cfg, seed=9)
+    nodes = torch.tensor([h.d["nx"] + 2, 3 * h.d["nx"] + 5], dtype=torch.int32, device="cuda")
+    targets = torch.full((2, 20), 0.01, dtype=f.dtype, device="cuda")
+    loss, dg, dt, df = gpu_gradient(cfg, h, f, g, tau, nodes, targets, 0, 4)
+    want_loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    lam = torch.zeros_like(f)
+    h.lbm_interface_loss(f, nodes, targets, want_loss, lam)
+    h.sync()
+    assert loss == want_loss.item()
+    assert np.all(dg == 0) and np.all(dt == 0)
+    assert torch.equal(df, lam)
